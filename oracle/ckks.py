@@ -1,0 +1,577 @@
+"""RNS-CKKS oracle (TEST INFRASTRUCTURE ONLY).
+
+Plain CPU CKKS for the Blind-Match match path, written from the paper's
+definitions (Sec. 2 "Homomorphic Encryption": Add, Mul(P), Rot, Res) with the
+readings the paper leaves open fixed explicitly:
+
+* primes: the largest primes below 2^bits with q = 1 (mod 2N); the paper is
+  silent on moduli (Sec. 5.1 names only N = 8192, log PQ ~ 158, l = 3);
+* slot j <-> the root zeta^(5^j) (zeta = exp(i*pi/N)), so Rot(v, r) with r > 0
+  is the left rotation of Sec. 2 ("(v_r, v_(r+1), ...)");
+* rescale rounds to nearest (centred lift of the dropped limb);
+* rotation = Galois automorphism sigma_(5^r) followed by hybrid key switching
+  (ModUp with the non-centred fast base conversion, inner product with the
+  rotation key, ModDown), digits of the modulus chain, automorphism applied
+  before ModUp;
+* randomness from Philox4x64-10 with the samplers documented in ckks_oracle.c.
+
+Ciphertexts and plaintexts are kept in coefficient form, one uint64 row per
+RNS limb; products go through the C core's NTT.  Only tests, the smoke check
+and the benchmark's CPU-baseline leg may import this module.
+"""
+import ctypes
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build_oracle
+
+# Philox key tags (key = (seed, tag)); see the samplers in ckks_oracle.c.
+TAG_SECRET = 1
+TAG_PK_A = 2
+TAG_PK_E = 3
+TAG_RK_A = 4
+TAG_RK_E = 5
+TAG_ENC_V = 6
+TAG_ENC_E0 = 7
+TAG_ENC_E1 = 8
+
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_LIB = None
+
+
+def lib():
+    """Load (building if needed) the oracle's C core."""
+    global _LIB
+    if _LIB is None:
+        L = ctypes.CDLL(build_oracle.build())
+        u64, u32, i32, dbl = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_double
+        sig = {
+            "orc_powmod": (u64, [u64, u64, u64]),
+            "orc_invmod": (u64, [u64, u64]),
+            "orc_is_prime": (i32, [u64]),
+            "orc_gen_primes": (i32, [u32, u32, u32, _U64P, u32, _U64P]),
+            "orc_find_psi": (u64, [u64, u32]),
+            "orc_ntt": (None, [_U64P, u32, u64, u64]),
+            "orc_intt": (None, [_U64P, u32, u64, u64]),
+            "orc_pointwise_mul": (None, [_U64P, _U64P, _U64P, u64, u64]),
+            "orc_scalar_mul": (None, [_U64P, u64, _U64P, u64, u64]),
+            "orc_poly_mul": (None, [_U64P, _U64P, _U64P, u32, u64, u64]),
+            "orc_automorphism": (None, [_U64P, _U64P, u32, u64, u64]),
+            "orc_bconv": (None, [_U64P, _U64P, u32, u64, _U64P, u64]),
+            "orc_rescale": (None, [_U64P, _U64P, u32, _U64P, u64]),
+            "orc_philox4x64": (None, [u64, u64, _U64P, _U64P]),
+            "orc_sample_uniform": (None, [u64, u64, u64, u64, u64, _U64P, u64]),
+            "orc_cdt_table": (None, [dbl, u32, _U64P]),
+            "orc_sample_gauss": (None, [u64, u64, u64, dbl, u32, _I64P, u64]),
+            "orc_sample_zo": (None, [u64, u64, u64, _I64P, u64]),
+            "orc_sample_hw": (None, [u64, u64, u32, u32, _I64P]),
+            "orc_signed_to_mod": (None, [_I64P, u64, _U64P, u64]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _p(a):
+    assert a.flags["C_CONTIGUOUS"]
+    if a.dtype == np.uint64:
+        return a.ctypes.data_as(_U64P)
+    if a.dtype == np.int64:
+        return a.ctypes.data_as(_I64P)
+    raise TypeError(a.dtype)
+
+
+def _u64(shape):
+    return np.zeros(shape, dtype=np.uint64)
+
+
+# ---------------------------------------------------------------------------
+# scalar helpers on the C core
+# ---------------------------------------------------------------------------
+
+def is_prime(n):
+    return bool(lib().orc_is_prime(n))
+
+
+def philox4x64(k0, k1, ctr):
+    c = np.array(ctr, dtype=np.uint64)
+    out = _u64(4)
+    lib().orc_philox4x64(k0, k1, _p(c), _p(out))
+    return [int(x) for x in out]
+
+
+def cdt_table(sigma, kmax):
+    t = _u64(kmax + 1)
+    lib().orc_cdt_table(sigma, kmax, _p(t))
+    return [int(x) for x in t]
+
+
+def ntt(a, log_n, q, psi):
+    out = np.ascontiguousarray(a, dtype=np.uint64).copy()
+    lib().orc_ntt(_p(out), log_n, q, psi)
+    return out
+
+
+def intt(a, log_n, q, psi):
+    out = np.ascontiguousarray(a, dtype=np.uint64).copy()
+    lib().orc_intt(_p(out), log_n, q, psi)
+    return out
+
+
+def pointwise_mul(a, b, q):
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    b = np.ascontiguousarray(b, dtype=np.uint64)
+    out = np.empty_like(a)
+    lib().orc_pointwise_mul(_p(a), _p(b), _p(out), a.size, q)
+    return out
+
+
+def scalar_mul(a, c, q):
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    out = np.empty_like(a)
+    lib().orc_scalar_mul(_p(a), c % q, _p(out), a.size, q)
+    return out
+
+
+def poly_mul(a, b, log_n, q, psi):
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    b = np.ascontiguousarray(b, dtype=np.uint64)
+    out = np.empty_like(a)
+    lib().orc_poly_mul(_p(a), _p(b), _p(out), log_n, q, psi)
+    return out
+
+
+def automorphism(a, log_n, k, q):
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    out = np.empty_like(a)
+    lib().orc_automorphism(_p(a), _p(out), log_n, k, q)
+    return out
+
+
+def bconv(x, src_primes, t):
+    """Fast base conversion of the limbs x (len(src_primes), n) to prime t."""
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    src = np.array(src_primes, dtype=np.uint64)
+    out = _u64(x.shape[1])
+    lib().orc_bconv(_p(x), _p(src), len(src_primes), t, _p(out), x.shape[1])
+    return out
+
+
+def rescale_poly(x, primes, level):
+    """Res on one polynomial with limbs q_0..q_level -> limbs q_0..q_(level-1)."""
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    pr = np.array(primes, dtype=np.uint64)
+    out = _u64((level, x.shape[1]))
+    lib().orc_rescale(_p(x), _p(pr), level, _p(out), x.shape[1])
+    return out
+
+
+def add_mod(a, b, q):
+    s = a + b
+    return np.where(s >= np.uint64(q), s - np.uint64(q), s)
+
+
+def sub_mod(a, b, q):
+    return np.where(a >= b, a - b, a + np.uint64(q) - b)
+
+
+def neg_mod(a, q):
+    return np.where(a == 0, a, np.uint64(q) - a)
+
+
+def signed_to_mod(v, q):
+    v = np.ascontiguousarray(v, dtype=np.int64)
+    out = _u64(v.size)
+    lib().orc_signed_to_mod(_p(v), q, _p(out), v.size)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# parameters
+# ---------------------------------------------------------------------------
+
+@dataclass(frozen=True)
+class Params:
+    """RNS-CKKS parameter set.
+
+    q_bits[0] is the base prime, q_bits[1:] the rescale primes (dropped in the
+    order q_L, q_(L-1), ...); p_bits are the special primes of key switching;
+    dnum is the number of key-switching digits; secret_hw = 0 selects the
+    ZO(1/2) ternary secret, otherwise a ternary secret of that Hamming weight.
+    """
+    log_n: int
+    q_bits: tuple
+    p_bits: tuple
+    dnum: int
+    log_scale: int = 40
+    secret_hw: int = 0
+    sigma: float = 3.2
+    kmax: int = 19
+
+
+PRESETS = {
+    # Toy, not secure: ring 2^12, q0 50-bit + one 40-bit rescale prime, one 50-bit special prime.
+    "toy": Params(12, (50, 40), (50,), dnum=2, secret_hw=0),
+    # Face/fingerprint scale: ring 2^16, 60 + 3x40-bit chain, 2x60-bit special primes, dnum 2, HW 192.
+    "ring16": Params(16, (60, 40, 40, 40), (60, 60), dnum=2, secret_hw=192),
+    # The ring16 modulus layout on a 2^12 ring: same level plan, fast enough for CPU tests.
+    "small4": Params(12, (60, 40, 40, 40), (60, 60), dnum=2, secret_hw=192),
+}
+
+
+def gen_chain(log_n, q_bits, p_bits):
+    """Q primes in q_bits order, then P primes; each the largest unused prime < 2^bits, = 1 mod 2N."""
+    used = []
+    out = []
+    for bits in list(q_bits) + list(p_bits):
+        excl = np.array(used if used else [0], dtype=np.uint64)
+        got = _u64(1)
+        n = lib().orc_gen_primes(log_n, bits, 1, _p(excl), len(used), _p(got))
+        if n != 1:
+            raise ValueError(f"no prime of {bits} bits for N=2^{log_n}")
+        used.append(int(got[0]))
+        out.append(int(got[0]))
+    return out[: len(q_bits)], out[len(q_bits):]
+
+
+class Context:
+    """Primes, roots and derived constants of one parameter set."""
+
+    def __init__(self, params):
+        if isinstance(params, str):
+            params = PRESETS[params]
+        self.params = params
+        self.log_n = params.log_n
+        self.n = 1 << params.log_n
+        self.slots = self.n // 2
+        self.q, self.p = gen_chain(params.log_n, params.q_bits, params.p_bits)
+        self.L = len(self.q) - 1
+        self.alpha = len(self.p)
+        self.primes = self.q + self.p                 # full basis Q_L u P
+        self.psi = [lib().orc_find_psi(x, self.log_n) for x in self.primes]
+        self.dnum = params.dnum
+        dsize = -(-(self.L + 1) // self.dnum)
+        self.digits = [list(range(d * dsize, min((d + 1) * dsize, self.L + 1)))
+                       for d in range(self.dnum)]
+        self.P = math.prod(self.p)
+        self.scale = float(1 << params.log_scale)
+        self.slot_exp = np.array([pow(5, j, 2 * self.n) for j in range(self.slots)], dtype=np.int64)
+
+    # index helpers -----------------------------------------------------
+    def level_primes(self, level):
+        return self.q[: level + 1]
+
+    def ext_index(self, level):
+        """Global basis indices of Q_level u P (the extended basis of key switching)."""
+        return list(range(level + 1)) + list(range(self.L + 1, self.L + 1 + self.alpha))
+
+    def galois_left(self, r):
+        """Galois element of the left rotation by r slots (negative r: right)."""
+        return pow(5, r % self.slots, 2 * self.n)
+
+    # NTT on a prime of the full basis -------------------------------------
+    def ntt(self, a, gi):
+        return ntt(a, self.log_n, self.primes[gi], self.psi[gi])
+
+    def intt(self, a, gi):
+        return intt(a, self.log_n, self.primes[gi], self.psi[gi])
+
+    def mul(self, a, b, gi):
+        return poly_mul(a, b, self.log_n, self.primes[gi], self.psi[gi])
+
+    # encoding (canonical embedding on the slots zeta^(5^j)) -----------------
+    def encode_int(self, z, scale):
+        """Integer coefficients round(scale * tau^{-1}(z)), round half away from zero."""
+        n = self.n
+        z = np.asarray(z, dtype=np.complex128)
+        assert z.shape == (self.slots,)
+        v = np.zeros(n, dtype=np.complex128)
+        e = self.slot_exp
+        v[(e - 1) // 2] = z                           # value at zeta^(5^j)
+        v[(2 * n - e - 1) // 2] = np.conj(z)          # value at zeta^(-5^j)
+        k = np.arange(n)
+        # v[t] = m(zeta^(2t+1)) = sum_k (m_k zeta^k) omega^(tk), omega = zeta^2
+        w = np.fft.fft(v) / n                          # = m_k zeta^k
+        m = (w * np.exp(-1j * np.pi * k / n)).real * float(scale)
+        r = np.where(m >= 0, np.floor(m + 0.5), -np.floor(-m + 0.5))
+        return r.astype(np.int64)
+
+    def encode(self, z, scale, level):
+        """Plaintext limbs (level+1, N) of z at the given scale."""
+        c = self.encode_int(z, scale)
+        return Plaintext(np.stack([signed_to_mod(c, self.q[j]) for j in range(level + 1)]),
+                         level, float(scale))
+
+    def decode(self, coeffs, scale):
+        """Slots z_j = m(zeta^(5^j)) / scale of integer coefficients (any ints)."""
+        n = self.n
+        p = np.array([float(c) for c in coeffs], dtype=np.float64) / float(scale)
+        k = np.arange(n)
+        w = p * np.exp(1j * np.pi * k / n)
+        v = np.fft.ifft(w) * n
+        return v[(self.slot_exp - 1) // 2]
+
+    # exact integers from residues ------------------------------------------
+    def crt(self, limbs, primes):
+        """Centred integers (python ints) of the residues limbs[j] mod primes[j]."""
+        Q = math.prod(primes)
+        acc = np.zeros(limbs.shape[1], dtype=object)
+        for j, qj in enumerate(primes):
+            hat = Q // qj
+            coef = hat * pow(hat % qj, -1, qj)
+            acc = acc + limbs[j].astype(object) * coef
+        acc = acc % Q
+        return [int(x) - Q if x > Q // 2 else int(x) for x in acc]
+
+
+@dataclass
+class Plaintext:
+    limbs: np.ndarray       # (level+1, N) coefficient form
+    level: int
+    scale: float
+
+
+@dataclass
+class Ciphertext:
+    c0: np.ndarray          # (level+1, N) coefficient form
+    c1: np.ndarray
+    level: int
+    scale: float
+
+    def copy(self):
+        return Ciphertext(self.c0.copy(), self.c1.copy(), self.level, self.scale)
+
+
+@dataclass
+class SecretKey:
+    coeffs: np.ndarray      # int64 ternary, length N
+
+    def limb(self, q):
+        return signed_to_mod(self.coeffs, q)
+
+
+@dataclass
+class PublicKey:
+    b: np.ndarray           # (L+1, N)
+    a: np.ndarray
+
+
+@dataclass
+class RotationKey:
+    galois: int
+    data: np.ndarray                          # (dnum, 2, L+1+alpha, N) coefficient form
+    ntt_data: np.ndarray = field(default=None, repr=False)
+
+
+# ---------------------------------------------------------------------------
+# sampling
+# ---------------------------------------------------------------------------
+
+def sample_uniform(ctx, seed, tag, obj, gi):
+    out = _u64(ctx.n)
+    lib().orc_sample_uniform(seed, tag, obj, gi, ctx.primes[gi], _p(out), ctx.n)
+    return out
+
+
+def sample_gauss(ctx, seed, tag, obj):
+    out = np.zeros(ctx.n, dtype=np.int64)
+    lib().orc_sample_gauss(seed, tag, obj, ctx.params.sigma, ctx.params.kmax, _p(out), ctx.n)
+    return out
+
+
+def sample_zo(ctx, seed, tag, obj):
+    out = np.zeros(ctx.n, dtype=np.int64)
+    lib().orc_sample_zo(seed, tag, obj, _p(out), ctx.n)
+    return out
+
+
+def sample_secret(ctx, seed):
+    out = np.zeros(ctx.n, dtype=np.int64)
+    if ctx.params.secret_hw:
+        lib().orc_sample_hw(seed, TAG_SECRET, ctx.params.secret_hw, ctx.log_n, _p(out))
+    else:
+        lib().orc_sample_zo(seed, TAG_SECRET, 0, _p(out), ctx.n)
+    return SecretKey(out)
+
+
+# ---------------------------------------------------------------------------
+# keys, encryption, decryption (Sec. 3.1: the client keeps sk, sends pk and evk)
+# ---------------------------------------------------------------------------
+
+def keygen_public(ctx, seed, sk):
+    """pk = (-a*s + e, a) mod Q_L; a uniform (tag PK_A, object 0), e Gaussian (tag PK_E)."""
+    e = sample_gauss(ctx, seed, TAG_PK_E, 0)
+    b = _u64((ctx.L + 1, ctx.n))
+    a = _u64((ctx.L + 1, ctx.n))
+    for j in range(ctx.L + 1):
+        qj = ctx.q[j]
+        a[j] = sample_uniform(ctx, seed, TAG_PK_A, 0, j)
+        b[j] = add_mod(neg_mod(ctx.mul(a[j], sk.limb(qj), j), qj), signed_to_mod(e, qj), qj)
+    return PublicKey(b, a)
+
+
+def rotation_key_object(galois, digit):
+    return galois * 16 + digit
+
+
+def keygen_rotation(ctx, seed, sk, galois):
+    """Hybrid key-switching key from sigma_k(s) to s, one component pair per digit d:
+    b_d = -a_d*s + e_d + P * [Q_hat_d * (Q_hat_d^{-1} mod Q_d)] * sigma_k(s)  mod P*Q_L,
+    a_d uniform.  The gadget factor is P mod q_j on the limbs of digit d and 0 elsewhere."""
+    nb = ctx.L + 1 + ctx.alpha
+    data = _u64((ctx.dnum, 2, nb, ctx.n))
+    s_rot = None
+    for d, dl in enumerate(ctx.digits):
+        obj = rotation_key_object(galois, d)
+        e = sample_gauss(ctx, seed, TAG_RK_E, obj)
+        for gi in range(nb):
+            t = ctx.primes[gi]
+            s_t = sk.limb(t)
+            a = sample_uniform(ctx, seed, TAG_RK_A, obj, gi)
+            b = add_mod(neg_mod(ctx.mul(a, s_t, gi), t), signed_to_mod(e, t), t)
+            if gi in dl:
+                s_rot = automorphism(s_t, ctx.log_n, galois, t)
+                b = add_mod(b, scalar_mul(s_rot, ctx.P % t, t), t)
+            data[d, 0, gi] = b
+            data[d, 1, gi] = a
+    key = RotationKey(galois, data)
+    key.ntt_data = np.stack([np.stack([np.stack([ctx.ntt(data[d, c, gi], gi) for gi in range(nb)])
+                                       for c in range(2)]) for d in range(ctx.dnum)])
+    return key
+
+
+def keygen(ctx, seed, rotations):
+    """sk, pk and the rotation keys for the given left-rotation amounts (negative = right)."""
+    sk = sample_secret(ctx, seed)
+    pk = keygen_public(ctx, seed, sk)
+    rks = {}
+    for r in rotations:
+        k = ctx.galois_left(r)
+        if k not in rks:
+            rks[k] = keygen_rotation(ctx, seed, sk, k)
+    return sk, pk, rks
+
+
+def encrypt(ctx, pk, pt, seed, obj):
+    """ct = (v*b + e0 + m, v*a + e1) mod Q_L with v ~ ZO(1/2), e0, e1 Gaussian (object `obj`)."""
+    assert pt.level == ctx.L
+    v = sample_zo(ctx, seed, TAG_ENC_V, obj)
+    e0 = sample_gauss(ctx, seed, TAG_ENC_E0, obj)
+    e1 = sample_gauss(ctx, seed, TAG_ENC_E1, obj)
+    c0 = _u64((ctx.L + 1, ctx.n))
+    c1 = _u64((ctx.L + 1, ctx.n))
+    for j in range(ctx.L + 1):
+        qj = ctx.q[j]
+        vj = signed_to_mod(v, qj)
+        c0[j] = add_mod(add_mod(ctx.mul(vj, pk.b[j], j), signed_to_mod(e0, qj), qj), pt.limbs[j], qj)
+        c1[j] = add_mod(ctx.mul(vj, pk.a[j], j), signed_to_mod(e1, qj), qj)
+    return Ciphertext(c0, c1, ctx.L, pt.scale)
+
+
+def decrypt_int(ctx, ct, sk):
+    """Centred integer coefficients of c0 + c1*s mod Q_level."""
+    m = _u64((ct.level + 1, ctx.n))
+    for j in range(ct.level + 1):
+        qj = ctx.q[j]
+        m[j] = add_mod(ct.c0[j], ctx.mul(ct.c1[j], sk.limb(qj), j), qj)
+    return ctx.crt(m, ctx.q[: ct.level + 1])
+
+
+def decrypt_decode(ctx, ct, sk):
+    return ctx.decode(decrypt_int(ctx, ct, sk), ct.scale)
+
+
+# ---------------------------------------------------------------------------
+# evaluator: Add, Mul(P), Res, Rot (Sec. 2)
+# ---------------------------------------------------------------------------
+
+class Evaluator:
+    """Exact RNS-CKKS evaluator on coefficient-form ciphertexts."""
+
+    def __init__(self, ctx, rot_keys):
+        self.ctx = ctx
+        self.keys = rot_keys
+
+    def zero_like(self, ct, level=None):
+        """Encryption of zero: the identity of add (Algorithm 2 starts from it)."""
+        return None
+
+    def add(self, a, b):
+        if a is None:
+            return b.copy()
+        if b is None:
+            return a.copy()
+        assert a.level == b.level and a.scale == b.scale
+        c0 = np.stack([add_mod(a.c0[j], b.c0[j], self.ctx.q[j]) for j in range(a.level + 1)])
+        c1 = np.stack([add_mod(a.c1[j], b.c1[j], self.ctx.q[j]) for j in range(a.level + 1)])
+        return Ciphertext(c0, c1, a.level, a.scale)
+
+    def mul_plain(self, ct, pt):
+        assert ct.level == pt.level
+        c0 = np.stack([self.ctx.mul(ct.c0[j], pt.limbs[j], j) for j in range(ct.level + 1)])
+        c1 = np.stack([self.ctx.mul(ct.c1[j], pt.limbs[j], j) for j in range(ct.level + 1)])
+        return Ciphertext(c0, c1, ct.level, ct.scale * pt.scale)
+
+    def rescale(self, ct):
+        assert ct.level >= 1
+        ql = self.ctx.q[ct.level]
+        c0 = rescale_poly(ct.c0, self.ctx.q, ct.level)
+        c1 = rescale_poly(ct.c1, self.ctx.q, ct.level)
+        return Ciphertext(c0, c1, ct.level - 1, ct.scale / ql)
+
+    def rotate(self, ct, r):
+        """Rot(ct, r): left rotation by r slots (right for r < 0)."""
+        if r % self.ctx.slots == 0:
+            return ct.copy()
+        return self.apply_galois(ct, self.ctx.galois_left(r))
+
+    def apply_galois(self, ct, k):
+        ctx, lvl = self.ctx, ct.level
+        key = self.keys[k]
+        c0s = np.stack([automorphism(ct.c0[j], ctx.log_n, k, ctx.q[j]) for j in range(lvl + 1)])
+        c1s = np.stack([automorphism(ct.c1[j], ctx.log_n, k, ctx.q[j]) for j in range(lvl + 1)])
+        d0, d1 = keyswitch(ctx, c1s, lvl, key)
+        c0 = np.stack([add_mod(c0s[j], d0[j], ctx.q[j]) for j in range(lvl + 1)])
+        return Ciphertext(c0, d1, lvl, ct.scale)
+
+
+def keyswitch(ctx, c, level, key):
+    """Hybrid key switching of the polynomial c (limbs q_0..q_level, coefficient form).
+
+    ModUp: per digit d (limbs of Q_d at or below `level`), the digit's own limbs
+    are kept and every other limb of Q_level u P is the fast base conversion
+    of those limbs.  Inner product with the key's digit-d pair in the NTT
+    domain, summed over digits.  ModDown: out_j = (x_j - Conv_P->q_j([x]_P)) * P^{-1}.
+    Returns the two output polynomials (limbs q_0..q_level)."""
+    ext = ctx.ext_index(level)                     # global basis indices
+    acc = np.zeros((2, len(ext), ctx.n), dtype=np.uint64)
+    for d, dl in enumerate(ctx.digits):
+        dl = [j for j in dl if j <= level]
+        if not dl:
+            continue
+        src_primes = [ctx.q[j] for j in dl]
+        src = np.stack([c[j] for j in dl])
+        for jj, gi in enumerate(ext):
+            t = ctx.primes[gi]
+            limb = c[gi] if gi in dl else bconv(src, src_primes, t)
+            f = ctx.ntt(limb, gi)
+            for comp in range(2):
+                acc[comp, jj] = add_mod(acc[comp, jj], pointwise_mul(f, key.ntt_data[d, comp, gi], t), t)
+    out = []
+    for comp in range(2):
+        x = np.stack([ctx.intt(acc[comp, jj], gi) for jj, gi in enumerate(ext)])
+        xp = x[level + 1:]
+        res = _u64((level + 1, ctx.n))
+        for j in range(level + 1):
+            qj = ctx.q[j]
+            conv = bconv(xp, ctx.p, qj)
+            p_inv = pow(ctx.P % qj, -1, qj)
+            res[j] = scalar_mul(sub_mod(x[j], conv, qj), p_inv, qj)
+        out.append(res)
+    return out[0], out[1]

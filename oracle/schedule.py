@@ -1,0 +1,229 @@
+"""Blind-Match match schedule (TEST INFRASTRUCTURE ONLY).
+
+The server side of recognition (Sec. 3.3): Input Ciphertext Expansion
+(Algorithm 1), HE-C^3 (Algorithm 2), then the compression step, written once
+against an evaluator interface (add, mul_plain, mul_cipher, rescale, rotate).
+`oracle.ckks.Evaluator` runs it exactly; `CountingEvaluator` only tracks
+levels and records (op, level) pairs, which reproduces the cost model F(N_in)
+of Sec. 4 (Propositions 1-3 with Table 1).
+
+Readings of passages that are garbled or silent in the paper:
+
+* Algorithm 1's rotation amounts: the printed offset 2^(j + log m - log N_in)
+  skips odd sub-windows and at j = log N_in rotates by m (a no-op on data of
+  period m), so the replication step here is T_i += Rot(T_i, s * 2^(j-1)),
+  j = 1..log2(N_in), always leftwards (the sign alternation is irrelevant for
+  period-m data).  After it, slot k of T_i holds q[i*s + (k mod s)].
+* The mask of Algorithm 1 selects part i inside every length-m window:
+  mask_i[k] = 1 iff floor((k mod m) / s) = i.
+* Algorithm 2 rescales every product (Res(Mul(...)) inside the loop); the
+  default here accumulates the N_in products and rescales once (same
+  message, one rescale instead of N_in).  `rescale_each_part=True` gives the
+  printed form.  The loop bound log(m - log N_in) is read as log m - log N_in.
+* Compression (the method is only cited; its cost is Proposition 3): each
+  group output is masked to the slots k = 0 (mod s) and packed s groups per
+  ciphertext, group g going to offset r = g mod s of pack floor(g / s), by a
+  radix-2 tree of right rotations (level b: Y_2k + Rot(Y_2k+1, -2^b)), then
+  one rescale per pack.  `tree=False` gives the linear form (each group
+  rotated right by its offset and added; Proposition 3 charges one Mul, one
+  Rot and one Add per group).
+"""
+import math
+
+
+def log2i(x):
+    v = int(round(math.log2(x)))
+    assert 1 << v == x, x
+    return v
+
+
+# ---------------------------------------------------------------------------
+# slot layouts (Sec. 3.2 enrollment layout; Sec. 3.3 recognition)
+# ---------------------------------------------------------------------------
+
+def tiled_query_slots(q, slots):
+    """Query replicated with period m over all slots: z[k] = q[k mod m]."""
+    m = len(q)
+    return [q[k % m] for k in range(slots)]
+
+
+def expanded_query_slots(q, s, i, slots):
+    """Part i replicated with period s: z[k] = q[i*s + (k mod s)] (client-side expansion)."""
+    return [q[i * s + (k % s)] for k in range(slots)]
+
+
+def gallery_slots(feats, g, i, s, slots):
+    """Group g, part i: identity u of the group sits at slots [u*s, u*s+s)
+    (z[u*s + t] = g_(g*G+u)[i*s + t], zero past the last identity)."""
+    G = slots // s
+    R = len(feats)
+    z = [0.0] * slots
+    for u in range(G):
+        idx = g * G + u
+        if idx >= R:
+            break
+        for t in range(s):
+            z[u * s + t] = float(feats[idx][i * s + t])
+    return z
+
+
+def alg1_mask_slots(m, s, i, slots):
+    """mask_i[k] = 1 iff floor((k mod m)/s) = i."""
+    return [1.0 if (k % m) // s == i else 0.0 for k in range(slots)]
+
+
+def compression_mask_slots(s, slots):
+    """M[k] = 1 iff k = 0 (mod s): keeps the slot that holds each identity's score."""
+    return [1.0 if k % s == 0 else 0.0 for k in range(slots)]
+
+
+def n_groups(R, s, slots):
+    return -(-R // (slots // s))
+
+
+def identity_slot(idx, s, slots, packed):
+    """(output ciphertext, slot) holding the score of identity idx."""
+    G = slots // s
+    g, u = divmod(idx, G)
+    if packed:
+        p, r = divmod(g, s)
+        return p, u * s + r
+    return g, u * s
+
+
+# ---------------------------------------------------------------------------
+# the three stages
+# ---------------------------------------------------------------------------
+
+def expand_query(ev, ct, masks, m, s):
+    """Algorithm 1: one tiled ciphertext -> N_in ciphertexts, part i replicated."""
+    n_in = m // s
+    out = []
+    for i in range(n_in):
+        c = ev.rescale(ev.mul_plain(ct, masks[i]))
+        for j in range(1, log2i(n_in) + 1):
+            c = ev.add(c, ev.rotate(c, s * (1 << (j - 1))))
+        out.append(c)
+    return out
+
+
+def hec3(ev, cu, cs, s, rescale_each_part=False, encrypted_gallery=False):
+    """Algorithm 2 for one group: sum_i Mul(C_u,i, C_s,i), then log2(s) rotate-and-add steps.
+
+    Slot u*s of the result holds <q, g_u> for every identity u of the group."""
+    mul = ev.mul_cipher if encrypted_gallery else ev.mul_plain
+    if rescale_each_part:
+        acc = ev.zero_like(cu[0], level=cu[0].level - 1)
+        for i in range(len(cu)):
+            acc = ev.add(acc, ev.rescale(mul(cu[i], cs[i])))
+    else:
+        acc = mul(cu[0], cs[0])
+        for i in range(1, len(cu)):
+            acc = ev.add(acc, mul(cu[i], cs[i]))
+        acc = ev.rescale(acc)
+    for t in range(1, log2i(s) + 1):
+        acc = ev.add(ev.rotate(acc, 1 << (t - 1)), acc)
+    return acc
+
+
+def compress(ev, accs, mask_m, s, tree=True, final_rescale=True):
+    """Compression: mask each group output and pack s groups per ciphertext."""
+    xs = [ev.mul_plain(a, mask_m) for a in accs]
+    packs = []
+    for p in range(-(-len(xs) // s)):
+        ys = xs[p * s:(p + 1) * s]
+        if tree:
+            b = 0
+            while len(ys) > 1:
+                nxt = []
+                for k in range(0, len(ys), 2):
+                    if k + 1 < len(ys):
+                        nxt.append(ev.add(ys[k], ev.rotate(ys[k + 1], -(1 << b))))
+                    else:
+                        nxt.append(ys[k])
+                ys = nxt
+                b += 1
+            y = ys[0]
+        else:
+            y = ev.zero_like(ys[0])
+            for r, x in enumerate(ys):
+                y = ev.add(y, ev.rotate(x, -r))
+        packs.append(ev.rescale(y) if final_rescale else y)
+    return packs
+
+
+def match(ev, query_cts, gallery_pts, masks, mask_m, m, s, expanded=False,
+          rescale_each_part=False, tree=True):
+    """Full server-side match for one query.
+
+    query_cts: [ct] (tiled, run through Algorithm 1) or the N_in client-expanded cts.
+    gallery_pts[g][i]: plaintext of group g, part i.
+    Returns (outputs, packed): the score ciphertexts and whether they are packed."""
+    cu = query_cts if expanded else expand_query(ev, query_cts[0], masks, m, s)
+    accs = [hec3(ev, cu, gallery_pts[g], s, rescale_each_part) for g in range(len(gallery_pts))]
+    if accs[0].level >= 1 and mask_m is not None:
+        return compress(ev, accs, mask_m, s, tree=tree), True
+    return accs, False
+
+
+# ---------------------------------------------------------------------------
+# op counting (Sec. 4, Propositions 1-3)
+# ---------------------------------------------------------------------------
+
+class SymCt:
+    def __init__(self, level):
+        self.level = level
+
+
+class CountingEvaluator:
+    """Evaluator that only tracks levels and counts (op, input level)."""
+
+    def __init__(self):
+        self.ops = []
+
+    def _rec(self, op, level):
+        self.ops.append((op, level))
+
+    def add(self, a, b):
+        self._rec("Add", a.level)
+        return SymCt(a.level)
+
+    def mul_plain(self, ct, pt):
+        self._rec("MulP", ct.level)
+        return SymCt(ct.level)
+
+    def mul_cipher(self, a, b):
+        self._rec("MulC", a.level)
+        return SymCt(a.level)
+
+    def rescale(self, ct):
+        self._rec("Res", ct.level)
+        return SymCt(ct.level - 1)
+
+    def rotate(self, ct, r):
+        self._rec("Rot", ct.level)
+        return SymCt(ct.level)
+
+    def zero_like(self, ct, level=None):
+        return SymCt(ct.level if level is None else level)
+
+    def counts(self):
+        out = {}
+        for k in self.ops:
+            out[k] = out.get(k, 0) + 1
+        return out
+
+
+def paper_literal_ops(n_slots, m, R, n_in, level=3):
+    """(op, level) counts of the printed schedule at the paper's setting: encrypted
+    gallery (Mul(C)), Res after every product, linear compression without a final
+    rescale, ceil(m*R/(n_slots*n_in)) groups served by one expanded query."""
+    s = m // n_in
+    groups = -(-(m * R // n_slots) // n_in)
+    ev = CountingEvaluator()
+    masks = [None] * n_in
+    cu = expand_query(ev, SymCt(level), masks, m, s)
+    accs = [hec3(ev, cu, [SymCt(level - 1)] * n_in, s, rescale_each_part=True,
+                 encrypted_gallery=True) for _ in range(groups)]
+    compress(ev, accs, None, max(s, groups), tree=False, final_rescale=False)
+    return ev.counts()

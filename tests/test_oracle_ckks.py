@@ -1,0 +1,172 @@
+"""Pins of the oracle's CKKS layer and match schedule.
+
+Encoding against brute-force evaluation of the polynomial at the slot roots,
+decryption against the encoded message, rotation against a slot permutation
+(Sec. 2's Rot), the Algorithm-1 and Algorithm-2 slot invariants, the final
+scores against the FP64 plaintext cosine with its Rank-1, and the schedule's
+operation counts against the paper's cost model F(N_in) (Sec. 4, Table 1).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ckks
+from oracle import schedule as sch
+from paper_2408_06167_gb300 import workload as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table1_cost_model.json")
+
+
+def test_encoding_evaluates_to_slots_at_the_5j_roots():
+    ctx = ckks.Context(ckks.Params(8, (50,), (), dnum=1))
+    rng = np.random.default_rng(0)
+    z = rng.normal(size=ctx.slots) + 1j * rng.normal(size=ctx.slots)
+    scale = 2.0 ** 40
+    m = ctx.encode_int(z, scale).astype(np.float64) / scale
+    n = ctx.n
+    for j in range(ctx.slots):
+        root = np.exp(1j * np.pi * pow(5, j, 2 * n) / n)
+        val = np.polyval(m[::-1], root)
+        assert abs(val - z[j]) < 1e-9, j
+
+
+@pytest.mark.parametrize("name", ["toy", "ring16"])
+def test_decode_inverts_encode(name):
+    ctx = ckks.Context(name)
+    rng = np.random.default_rng(1)
+    z = rng.uniform(-1, 1, size=ctx.slots)
+    c = ctx.encode_int(z, ctx.scale)
+    assert np.abs(ctx.decode(c.tolist(), ctx.scale) - z).max() < 2.0 ** -30
+
+
+@pytest.mark.parametrize("name", ["toy", "small4"])
+def test_encrypt_decrypt_and_rotation_permutes_slots(name):
+    ctx = ckks.Context(name)
+    sk, pk, rks = ckks.keygen(ctx, 3, [1, 5, -1, -6])
+    rng = np.random.default_rng(2)
+    z = rng.uniform(-1, 1, size=ctx.slots)
+    ct = ckks.encrypt(ctx, pk, ctx.encode(z, ctx.scale, ctx.L), 4, 0)
+    assert np.abs(ckks.decrypt_decode(ctx, ct, sk) - z).max() < 1e-6
+    ev = ckks.Evaluator(ctx, rks)
+    for r in [1, 5, -1, -6]:
+        d = ckks.decrypt_decode(ctx, ev.rotate(ct, r), sk)
+        assert np.abs(d - np.roll(z, -r)).max() < 1e-6, r
+    # a rotation at every level down to 0 (the toy's HE-C^3 runs at level 0)
+    c = ct
+    while c.level > 0:
+        pt = ctx.encode(np.ones(ctx.slots), ctx.q[c.level], c.level)
+        c = ev.rescale(ev.mul_plain(c, pt))
+        d = ckks.decrypt_decode(ctx, ev.rotate(c, 1), sk)
+        assert np.abs(d - np.roll(z, -1)).max() < 1e-6, c.level
+
+
+def _setup(name, m, s, R, seed=3, extra_rots=()):
+    ctx = ckks.Context(name)
+    n_in = m // s
+    rots = ([s << j for j in range(sch.log2i(n_in))] + [1 << t for t in range(sch.log2i(s))]
+            + [-(1 << t) for t in range(sch.log2i(s))] + list(extra_rots))
+    sk, pk, rks = ckks.keygen(ctx, seed, rots)
+    return ctx, sk, pk, ckks.Evaluator(ctx, rks)
+
+
+@pytest.mark.parametrize("m,s,R", [(128, 16, 2500), (16, 4, 3000)])
+def test_match_invariants_and_scores_small4(m, s, R):
+    ctx, sk, pk, ev = _setup("small4", m, s, R)
+    S, L, n_in = ctx.slots, ctx.L, m // s
+    feats = wl.gallery(R, m)
+    qs, _ = wl.queries(feats, 1)
+    q = qs[0]
+    ct = ckks.encrypt(ctx, pk, ctx.encode(sch.tiled_query_slots(q, S), ctx.scale, L), 4, 0)
+    masks = [ctx.encode(sch.alg1_mask_slots(m, s, i, S), ctx.q[L], L) for i in range(n_in)]
+    cu = sch.expand_query(ev, ct, masks, m, s)
+    # Algorithm 1 invariant: part i replicated at period s in every slot
+    for i in range(n_in):
+        d = ckks.decrypt_decode(ctx, cu[i], sk).real
+        assert np.abs(d - np.array(sch.expanded_query_slots(q, s, i, S))).max() < 1e-6
+    ng = sch.n_groups(R, s, S)
+    gal = [[ctx.encode(sch.gallery_slots(feats, g, i, s, S), ctx.q[L - 1], L - 1) for i in range(n_in)]
+           for g in range(ng)]
+    accs = [sch.hec3(ev, cu, gal[g], s) for g in range(ng)]
+    # Algorithm 2 invariant: slot u*s of group g holds <q, g_(gG+u)>
+    G = S // s
+    ref = wl.plaintext_scores(feats, q)
+    d = ckks.decrypt_decode(ctx, accs[1], sk).real
+    for u in range(0, min(G, R - G), 7):
+        assert abs(d[u * s] - ref[G + u]) < 1e-6
+    mm = ctx.encode(sch.compression_mask_slots(s, S), ctx.q[L - 2], L - 2)
+    packs = sch.compress(ev, accs, mm, s)
+    assert len(packs) == -(-ng // s) and packs[0].level == 0
+    dec = [ckks.decrypt_decode(ctx, p, sk).real for p in packs]
+    got = np.array([dec[o][slot] for o, slot in (sch.identity_slot(i, s, S, True) for i in range(R))])
+    assert np.abs(got - ref).max() < 1e-5
+    top2 = np.sort(ref)[-2:]
+    if top2[1] - top2[0] > 2e-5:
+        assert got.argmax() == ref.argmax()
+    # masked slots of the packs carry nothing: only slots u*s + r (r < groups in pack) are set
+    assert np.abs(dec[-1][np.arange(S) % s >= ng - s * (len(packs) - 1)]).max() < 1e-6
+
+
+def test_linear_compression_and_per_part_rescale_agree_with_default():
+    m, s, R = 16, 4, 2100
+    ctx, sk, pk, ev = _setup("small4", m, s, R, extra_rots=[-3])
+    S, L, n_in = ctx.slots, ctx.L, m // s
+    feats = wl.gallery(R, m)
+    q = wl.queries(feats, 1)[0][0]
+    ct = ckks.encrypt(ctx, pk, ctx.encode(sch.tiled_query_slots(q, S), ctx.scale, L), 4, 0)
+    masks = [ctx.encode(sch.alg1_mask_slots(m, s, i, S), ctx.q[L], L) for i in range(n_in)]
+    gal = [[ctx.encode(sch.gallery_slots(feats, g, i, s, S), ctx.q[L - 1], L - 1) for i in range(n_in)]
+           for g in range(sch.n_groups(R, s, S))]
+    mm = ctx.encode(sch.compression_mask_slots(s, S), ctx.q[L - 2], L - 2)
+    ref = wl.plaintext_scores(feats, q)
+    for kw in [dict(tree=False), dict(rescale_each_part=True)]:
+        outs, packed = sch.match(ev, [ct], gal, masks, mm, m, s, **kw)
+        dec = [ckks.decrypt_decode(ctx, p, sk).real for p in outs]
+        got = np.array([dec[o][slot] for o, slot in (sch.identity_slot(i, s, S, packed) for i in range(R))])
+        assert np.abs(got - ref).max() < 1e-5, kw
+
+
+def test_toy_expanded_queries_match_plaintext_cosine():
+    """Toy ring 2^12 (one rescale prime): client-expanded query, HE-C^3 at level 1 -> 0."""
+    m, s, R = 16, 4, 512
+    ctx, sk, pk, ev = _setup("toy", m, s, R)
+    S, n_in = ctx.slots, m // s
+    feats = wl.gallery(R, m)
+    qs, _ = wl.queries(feats, 8)
+    gal = [[ctx.encode(sch.gallery_slots(feats, 0, i, s, S), ctx.q[1], 1) for i in range(n_in)]]
+    for qi, q in enumerate(qs[:3]):
+        cts = [ckks.encrypt(ctx, pk, ctx.encode(sch.expanded_query_slots(q, s, i, S), ctx.scale, 1), 4,
+                            qi * 256 + i) for i in range(n_in)]
+        outs, packed = sch.match(ev, cts, gal, None, None, m, s, expanded=True)
+        assert not packed and outs[0].level == 0
+        d = ckks.decrypt_decode(ctx, outs[0], sk).real
+        got = d[np.arange(R) * s]
+        ref = wl.plaintext_scores(feats, q)
+        assert np.abs(got - ref).max() < 1e-5
+        assert got.argmax() == ref.argmax()
+
+
+# ------------------------------------------------------------- cost model
+
+
+def _golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("n_in", [2, 4, 8, 16, 32])
+def test_schedule_op_counts_reproduce_cost_model(n_in):
+    """The printed schedule's (op, level) counts weighted by Table 1 give F(N_in) of Sec. 4."""
+    g = _golden()
+    st = g["setting"]
+    counts = sch.paper_literal_ops(st["n_slots"], st["m"], st["R_per_cluster"], n_in, st["level"])
+    total = sum(c * g["table1_ms"][str(lvl)][op] for (op, lvl), c in counts.items())
+    assert round(total, 2) == pytest.approx(g["F_ms"][str(n_in)], abs=1e-9)
+
+
+def test_identities_per_ciphertext_example():
+    ex = _golden()["vectors_per_ciphertext_example"]
+    s = ex["m"] // ex["n_in"]
+    assert ex["n_slots"] // s == ex["value"]        # (N * N_in) / m vectors per ciphertext
