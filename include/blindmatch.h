@@ -1,0 +1,225 @@
+/*
+ * blindmatch.h -- C ABI of the GB300 Blind-Match library: encrypted 1:N
+ * cosine-similarity matching of biometric templates under RNS-CKKS
+ * (Choi, Kim, Song, Woo: "Blind-Match", CIKM 2024, arXiv 2408.06167).
+ *
+ * The calls follow the paper's statement of the protocol:
+ *   bm_keygen          Sec. 3.1 Key Generation and Management
+ *   bm_encode_gallery  Sec. 3.2 Enrollment (layout: identity u of a group at slots [u*s, u*s+s))
+ *   bm_encrypt_query   Sec. 3.3 Recognition (client encrypts the query feature vector)
+ *   bm_match           Sec. 3.3: Algorithm 1 (Input Ciphertext Expansion), Algorithm 2 (HE-C^3)
+ *                      and the compression step, on the GPU
+ *   bm_decrypt_scores  Sec. 3.3 Decryption (client decrypts, takes the argmax = Rank-1)
+ *
+ * Conventions shared by every call:
+ *  - A ciphertext at level l has the RNS limbs q_0..q_l; its wire layout is
+ *    [2][l+1][N] uint64 residues in coefficient order (c0 then c1).
+ *  - Slot j of a plaintext is its value at the root zeta^(5^j), zeta = exp(i*pi/N);
+ *    a rotation by r > 0 is the left rotation of Sec. 2 (slot j <- slot j + r).
+ *  - Handles are opaque and owned by the caller once returned; free each with its
+ *    _destroy call.  Inputs passed by pointer are borrowed for the duration of the
+ *    call and copied.  Calls on one context are not thread-safe.
+ *  - Every call returns a bm_status; on failure bm_last_error() (thread-local)
+ *    describes the cause and no output handle is written.
+ *  - Device memory is allocated with the CUDA runtime on the context's device.
+ */
+#ifndef BLINDMATCH_H
+#define BLINDMATCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum bm_status {
+    BM_OK = 0,
+    BM_E_ARG = 1,          /* null pointer, size mismatch, index out of range */
+    BM_E_PARAM = 2,        /* parameter set not supported (ring size, prime sizes, digits) */
+    BM_E_LEVEL = 3,        /* not enough levels for the requested schedule / mode */
+    BM_E_KEY_MISSING = 4,  /* no rotation key for a needed Galois element */
+    BM_E_DIM = 5,          /* dim or part size not a power of two, part does not divide dim,
+                              or dim larger than the slot count (Sec. 3.2) */
+    BM_E_OOM = 6,          /* device or host allocation failed */
+    BM_E_HBM_BUDGET = 7,   /* request exceeds the configured device-memory budget */
+    BM_E_CUDA = 8,         /* a CUDA runtime call failed */
+    BM_E_TIMEOUT = 9,      /* a bounded wait expired */
+    BM_E_CANCELLED = 10,   /* the request was cancelled */
+    BM_E_FORMAT = 11       /* malformed import data (level, sizes) */
+} bm_status;
+
+#define BM_MAX_Q 6   /* primes in the ciphertext modulus chain q_0..q_L */
+#define BM_MAX_P 3   /* special primes of key switching */
+
+/* RNS-CKKS parameters.  The primes are derived deterministically: q_0 is the
+ * largest prime below 2^q_bits[0] with q = 1 (mod 2N); each later prime (the
+ * rescale primes, then the special primes) is the largest such prime below
+ * 2^bits not used before it.  The paper fixes none of this (Sec. 5.1 names only
+ * N = 8192, log PQ ~ 158, l = 3, under Lattigo). */
+typedef struct bm_params {
+    uint32_t log_n;               /* ring degree N = 2^log_n, 12 <= log_n <= 16 */
+    uint32_t n_q;                 /* primes in Q (L = n_q - 1), 2 <= n_q <= BM_MAX_Q */
+    uint32_t q_bits[BM_MAX_Q];    /* q_bits[0]: base prime; then rescale primes; each 30..60 */
+    uint32_t n_p;                 /* special primes, 1 <= n_p <= BM_MAX_P */
+    uint32_t p_bits[BM_MAX_P];    /* 30..60 */
+    uint32_t dnum;                /* key-switching digits (ceil(n_q/dnum) <= 3), 1..4 */
+    uint32_t log_scale;           /* encoding scale Delta = 2^log_scale */
+    uint32_t secret_hw;           /* 0: ZO(1/2) ternary secret; else ternary of this Hamming weight */
+    double sigma;                 /* discrete Gaussian width of the errors (3.2) */
+} bm_params;
+
+enum {
+    BM_PRESET_TOY = 0,     /* N = 2^12, q 50 + 40 bits, p 50 bits, dnum 2, ZO secret: not secure */
+    BM_PRESET_RING16 = 1,  /* N = 2^16, q 60 + 3x40 bits, p 2x60 bits, dnum 2, HW-192 secret */
+    BM_PRESET_SMALL4 = 2   /* the RING16 chain on N = 2^12 (test size) */
+};
+
+/* Query layouts of bm_encrypt_query (Sec. 3.3). */
+enum {
+    BM_QUERY_TILED = 0,    /* one ciphertext, q tiled with period dim; the server runs Algorithm 1 */
+    BM_QUERY_EXPANDED = 1  /* dim/part ciphertexts, part i tiled with period part (client-side
+                              expansion; required when the chain has fewer than 3 rescale primes) */
+};
+
+typedef struct bm_context bm_context;
+typedef struct bm_secret_key bm_secret_key;
+typedef struct bm_public_key bm_public_key;
+typedef struct bm_eval_keys bm_eval_keys;
+typedef struct bm_gallery bm_gallery;
+typedef struct bm_ciphertext bm_ciphertext;
+typedef struct bm_result bm_result;
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* bm_last_error(void);
+/* Fills *out with a preset (BM_PRESET_*).  BM_E_ARG for an unknown preset. */
+bm_status bm_params_preset(int preset, bm_params* out);
+
+/* Creates a context on CUDA device `device`: derives primes and roots, uploads the
+ * NTT tables.  BM_E_PARAM if the parameters are outside the ranges above or a prime
+ * cannot be found; BM_E_CUDA if the device cannot be used. */
+bm_status bm_context_create(const bm_params* params, int device, bm_context** out);
+void bm_context_destroy(bm_context* ctx);
+/* Writes the n_q + n_p primes (q_0..q_L, then p_0..) to primes_out. */
+bm_status bm_context_primes(const bm_context* ctx, uint64_t* primes_out, size_t capacity);
+
+/* Sec. 3.1: samples the secret key, the public key and the rotation keys that the
+ * match schedule for (dim, part_size) needs -- left rotations by part*2^j
+ * (Algorithm 1, tiled schedule only), left rotations by 2^t (Algorithm 2) and right
+ * rotations by 2^t (compression, when the chain has a level for it).  All randomness
+ * comes from Philox4x64-10 keyed by `seed`.  Keys stay resident on the device.
+ * BM_E_DIM for an invalid (dim, part_size). */
+bm_status bm_keygen(bm_context* ctx, uint64_t seed, uint32_t dim, uint32_t part_size,
+                    bm_secret_key** sk, bm_public_key** pk, bm_eval_keys** evk);
+void bm_secret_key_destroy(bm_secret_key* sk);
+void bm_public_key_destroy(bm_public_key* pk);
+void bm_eval_keys_destroy(bm_eval_keys* evk);
+/* Number of rotation keys and their left-rotation amounts (negative = right). */
+bm_status bm_eval_keys_rotations(const bm_eval_keys* evk, int32_t* rotations, size_t capacity,
+                                 uint32_t* count);
+/* Coefficient-form copies for checking: secret key (N signed values), public key
+ * [2][L+1][N], rotation key of a left rotation `rotation` [dnum][2][n_q+n_p][N]
+ * (component 0 = b, 1 = a; limbs over q_0..q_L then p_0..).  BM_E_KEY_MISSING if
+ * the rotation has no key; BM_E_ARG if `capacity` (words) is too small. */
+bm_status bm_secret_key_export(const bm_secret_key* sk, int64_t* out, size_t capacity);
+bm_status bm_public_key_export(const bm_public_key* pk, uint64_t* out, size_t capacity);
+bm_status bm_eval_keys_export(const bm_eval_keys* evk, int32_t rotation, uint64_t* out,
+                              size_t capacity);
+
+/* Sec. 3.2 (enrollment, with a plaintext gallery): feats is n_ids x dim row-major
+ * float64, L2-normalised.  Identities are grouped G = (N/2)/part_size per group;
+ * identity u of group g fills slots [u*part, u*part+part) of the group's plaintext
+ * for part i (its i-th sub-vector), zero past the last identity.  Also encodes the
+ * Algorithm-1 masks (mask_i[k] = 1 iff floor((k mod dim)/part) = i) and the
+ * compression mask (M[k] = 1 iff k = 0 mod part).  Everything stays resident on
+ * the device.  BM_E_DIM for an invalid (dim, part_size); BM_E_LEVEL if the chain
+ * is too short for any schedule (n_q < 2). */
+bm_status bm_encode_gallery(bm_context* ctx, const double* feats, uint64_t n_ids, uint32_t dim,
+                            uint32_t part_size, bm_gallery** out);
+/* Same gallery from coefficient-form plaintexts produced elsewhere:
+ * pts [groups][dim/part][level+1][N], masks [dim/part][n_q][N] (tiled schedule; NULL
+ * otherwise), cmask [level][N] (when compressing; NULL otherwise), where `level`
+ * and the schedule are those bm_gallery_layout reports. */
+bm_status bm_gallery_import(bm_context* ctx, const uint64_t* pts, const uint64_t* masks,
+                            const uint64_t* cmask, uint64_t n_ids, uint32_t dim,
+                            uint32_t part_size, bm_gallery** out);
+/* Layout of a gallery for (n_ids, dim, part_size) under this context: number of
+ * groups, level of the gallery plaintexts, tiled (1) or expanded (0) queries,
+ * compressed (1) or per-group (0) outputs, output ciphertexts per query. */
+bm_status bm_gallery_layout(const bm_context* ctx, uint64_t n_ids, uint32_t dim,
+                            uint32_t part_size, uint32_t* groups, uint32_t* level,
+                            uint32_t* tiled, uint32_t* compressed, uint32_t* n_out);
+/* Coefficient-form copies of the resident plaintexts (layouts as in the import;
+ * pass NULL to skip a part). */
+bm_status bm_gallery_export(const bm_gallery* g, uint64_t* pts, uint64_t* masks, uint64_t* cmask);
+void bm_gallery_destroy(bm_gallery* g);
+
+/* Sec. 3.3: encrypts the L2-normalised query q[dim] under pk at the top level
+ * with scale 2^log_scale: ct = (v*pk0 + e0 + m, v*pk1 + e1), v ~ ZO(1/2), e0, e1
+ * Gaussian, drawn from Philox4x64-10 keyed by `seed`, object query_id*256 + part.
+ * mode BM_QUERY_TILED gives one ciphertext, BM_QUERY_EXPANDED dim/part_size.
+ * The ciphertext is host-resident (coefficient form, the client-to-server message). */
+bm_status bm_encrypt_query(bm_context* ctx, const bm_public_key* pk, const double* q, uint32_t dim,
+                           uint32_t part_size, uint32_t mode, uint64_t seed, uint64_t query_id,
+                           bm_ciphertext** out);
+/* Wraps n_cts coefficient-form ciphertexts [n_cts][2][level+1][N].  BM_E_FORMAT for
+ * a level above L. */
+bm_status bm_ciphertext_import(bm_context* ctx, const uint64_t* data, uint32_t n_cts,
+                               uint32_t level, bm_ciphertext** out);
+bm_status bm_ciphertext_info(const bm_ciphertext* ct, uint32_t* n_cts, uint32_t* level);
+bm_status bm_ciphertext_export(const bm_ciphertext* ct, uint64_t* out, size_t capacity);
+/* Stages the ciphertext on the device (H2D + NTT) on `stream` (a cudaStream_t, NULL
+ * for the legacy default stream); later bm_match calls skip their own upload. */
+bm_status bm_ciphertext_upload(bm_ciphertext* ct, void* stream);
+void bm_ciphertext_destroy(bm_ciphertext* ct);
+
+/* Sec. 3.3, the server side, on the GPU: for each query, Algorithm 1 (tiled
+ * queries), then for every group HE-C^3 (Algorithm 2: ct x pt products summed
+ * over the parts, one rescale, log2(part) rotate-and-add steps), then the
+ * compression step (mask, pack `part` groups per ciphertext by a tree of right
+ * rotations, rescale).  Scores end at slot u*part + r of pack floor(g/part) for
+ * identity u of group g = pack*part + r (packed), or at slot u*part of the group's
+ * output (per-group).  Runs on `stream` and returns after the result is complete;
+ * the score ciphertexts stay on the device in *out.  BM_E_LEVEL if a query's
+ * mode/level does not match the gallery; BM_E_KEY_MISSING if evk lacks a rotation. */
+bm_status bm_match(bm_context* ctx, const bm_eval_keys* evk, const bm_gallery* gallery,
+                   bm_ciphertext* const* queries, uint32_t n_queries, void* stream,
+                   bm_result** out);
+bm_status bm_result_info(const bm_result* r, uint32_t* n_queries, uint32_t* n_out,
+                         uint32_t* packed);
+/* Score ciphertexts of one query: [n_out][2][N] coefficient form at level 0. */
+bm_status bm_result_export(const bm_result* r, uint32_t query_index, uint64_t* out,
+                           size_t capacity);
+void bm_result_destroy(bm_result* r);
+/* Sec. 3.3 Decryption: decrypts the score ciphertexts of one query with sk and maps
+ * slots back to identities: scores[u] ~ <q, g_u> (the cosine similarity of unit
+ * vectors).  rank1 = argmax (lowest id on ties), rank1_score its score; the caller
+ * applies its own threshold to reject unenrolled users. */
+bm_status bm_decrypt_scores(bm_context* ctx, const bm_secret_key* sk, const bm_result* r,
+                            uint32_t query_index, double* scores, uint64_t n_ids,
+                            int64_t* rank1, double* rank1_score);
+
+/* ---- single operations, for checking the kernels against a reference ---- */
+
+/* Negacyclic products out = a * b in Z_q[X]/(X^N+1), limb k on prime k of the full
+ * basis (k < n_q + n_p), host arrays [n_limbs][N], through the GPU NTT. */
+bm_status bm_poly_mul(bm_context* ctx, const uint64_t* a, const uint64_t* b, uint64_t* out,
+                      uint32_t n_limbs);
+/* Rot(ct, rotation) (Sec. 2) of every ciphertext in `in` at its level, through the
+ * GPU key switch; result is a new host ciphertext. */
+bm_status bm_ct_rotate(bm_context* ctx, const bm_eval_keys* evk, const bm_ciphertext* in,
+                       int32_t rotation, bm_ciphertext** out);
+/* Res (Sec. 2) of every ciphertext in `in`: level l -> l-1.  BM_E_LEVEL at level 0. */
+bm_status bm_ct_rescale(bm_context* ctx, const bm_ciphertext* in, bm_ciphertext** out);
+/* In-place NTT / inverse NTT of device limbs d_data[n_polys][n_limbs][N]; limb k
+ * uses prime k of the full basis.  The forward transform's output order is the
+ * library's own (bit-reversed evaluation order); only the inverse undoes it. */
+bm_status bm_ntt_forward(bm_context* ctx, uint64_t* d_data, uint32_t n_polys, uint32_t n_limbs,
+                         void* stream);
+bm_status bm_ntt_inverse(bm_context* ctx, uint64_t* d_data, uint32_t n_polys, uint32_t n_limbs,
+                         void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BLINDMATCH_H */

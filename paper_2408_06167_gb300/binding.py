@@ -1,0 +1,327 @@
+"""Thin ctypes binding of libblindmatch.so: the C-ABI of include/blindmatch.h
+under the same names, marshalling numpy arrays and handles only.  Every step
+of the match runs in the CUDA library; there is no Python or CPU fallback: if
+the library cannot be loaded, importing this module raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB_PATH = _build.LIB
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libblindmatch.so is not built ({_LIB_PATH}); run paper_2408_06167_gb300/build.py")
+_L = ctypes.CDLL(_LIB_PATH)
+
+_vp = ctypes.c_void_p
+_u32, _u64, _i32, _i64, _dbl = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_U32P = ctypes.POINTER(ctypes.c_uint32)
+_DP = ctypes.POINTER(ctypes.c_double)
+_PP = ctypes.POINTER(ctypes.c_void_p)
+
+BM_QUERY_TILED = 0
+BM_QUERY_EXPANDED = 1
+PRESETS = {"toy": 0, "ring16": 1, "small4": 2}
+STATUS = ["BM_OK", "BM_E_ARG", "BM_E_PARAM", "BM_E_LEVEL", "BM_E_KEY_MISSING", "BM_E_DIM", "BM_E_OOM",
+          "BM_E_HBM_BUDGET", "BM_E_CUDA", "BM_E_TIMEOUT", "BM_E_CANCELLED", "BM_E_FORMAT"]
+
+
+class bm_params(ctypes.Structure):
+    _fields_ = [("log_n", _u32), ("n_q", _u32), ("q_bits", _u32 * 6), ("n_p", _u32), ("p_bits", _u32 * 3),
+                ("dnum", _u32), ("log_scale", _u32), ("secret_hw", _u32), ("sigma", _dbl)]
+
+
+_SIGS = {
+    "bm_last_error": (ctypes.c_char_p, []),
+    "bm_params_preset": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(bm_params)]),
+    "bm_context_create": (ctypes.c_int, [ctypes.POINTER(bm_params), ctypes.c_int, _PP]),
+    "bm_context_destroy": (None, [_vp]),
+    "bm_context_primes": (ctypes.c_int, [_vp, _U64P, ctypes.c_size_t]),
+    "bm_keygen": (ctypes.c_int, [_vp, _u64, _u32, _u32, _PP, _PP, _PP]),
+    "bm_secret_key_destroy": (None, [_vp]),
+    "bm_public_key_destroy": (None, [_vp]),
+    "bm_eval_keys_destroy": (None, [_vp]),
+    "bm_eval_keys_rotations": (ctypes.c_int, [_vp, _I32P, ctypes.c_size_t, _U32P]),
+    "bm_secret_key_export": (ctypes.c_int, [_vp, _I64P, ctypes.c_size_t]),
+    "bm_public_key_export": (ctypes.c_int, [_vp, _U64P, ctypes.c_size_t]),
+    "bm_eval_keys_export": (ctypes.c_int, [_vp, _i32, _U64P, ctypes.c_size_t]),
+    "bm_encode_gallery": (ctypes.c_int, [_vp, _DP, _u64, _u32, _u32, _PP]),
+    "bm_gallery_import": (ctypes.c_int, [_vp, _U64P, _U64P, _U64P, _u64, _u32, _u32, _PP]),
+    "bm_gallery_layout": (ctypes.c_int, [_vp, _u64, _u32, _u32, _U32P, _U32P, _U32P, _U32P, _U32P]),
+    "bm_gallery_export": (ctypes.c_int, [_vp, _U64P, _U64P, _U64P]),
+    "bm_gallery_destroy": (None, [_vp]),
+    "bm_encrypt_query": (ctypes.c_int, [_vp, _vp, _DP, _u32, _u32, _u32, _u64, _u64, _PP]),
+    "bm_ciphertext_import": (ctypes.c_int, [_vp, _U64P, _u32, _u32, _PP]),
+    "bm_ciphertext_info": (ctypes.c_int, [_vp, _U32P, _U32P]),
+    "bm_ciphertext_export": (ctypes.c_int, [_vp, _U64P, ctypes.c_size_t]),
+    "bm_ciphertext_upload": (ctypes.c_int, [_vp, _vp]),
+    "bm_ciphertext_destroy": (None, [_vp]),
+    "bm_match": (ctypes.c_int, [_vp, _vp, _vp, _PP, _u32, _vp, _PP]),
+    "bm_result_info": (ctypes.c_int, [_vp, _U32P, _U32P, _U32P]),
+    "bm_result_export": (ctypes.c_int, [_vp, _u32, _U64P, ctypes.c_size_t]),
+    "bm_result_destroy": (None, [_vp]),
+    "bm_decrypt_scores": (ctypes.c_int, [_vp, _vp, _vp, _u32, _DP, _u64, _I64P, _DP]),
+    "bm_poly_mul": (ctypes.c_int, [_vp, _U64P, _U64P, _U64P, _u32]),
+    "bm_ct_rotate": (ctypes.c_int, [_vp, _vp, _vp, _i32, _PP]),
+    "bm_ct_rescale": (ctypes.c_int, [_vp, _vp, _PP]),
+    "bm_ntt_forward": (ctypes.c_int, [_vp, _vp, _u32, _u32, _vp]),
+    "bm_ntt_inverse": (ctypes.c_int, [_vp, _vp, _u32, _u32, _vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(_L, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+class BlindMatchError(RuntimeError):
+    def __init__(self, status, msg):
+        name = STATUS[status] if 0 <= status < len(STATUS) else str(status)
+        super().__init__(f"{name}: {msg}")
+        self.status = status
+
+
+def _check(st):
+    if st != 0:
+        raise BlindMatchError(st, _L.bm_last_error().decode())
+
+
+def _u64p(a):
+    assert a.dtype == np.uint64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_U64P)
+
+
+class _Handle:
+    """Owns one opaque handle; frees it with its _destroy call."""
+    _destroy = None
+
+    def __init__(self, ptr, owner=None):
+        self.ptr = ptr
+        self.owner = owner      # keeps the context alive
+
+    def __del__(self):
+        if self.ptr and self._destroy:
+            getattr(_L, self._destroy)(self.ptr)
+            self.ptr = None
+
+
+class Context(_Handle):
+    _destroy = "bm_context_destroy"
+
+
+class SecretKey(_Handle):
+    _destroy = "bm_secret_key_destroy"
+
+
+class PublicKey(_Handle):
+    _destroy = "bm_public_key_destroy"
+
+
+class EvalKeys(_Handle):
+    _destroy = "bm_eval_keys_destroy"
+
+
+class Gallery(_Handle):
+    _destroy = "bm_gallery_destroy"
+
+
+class Ciphertext(_Handle):
+    _destroy = "bm_ciphertext_destroy"
+
+
+class Result(_Handle):
+    _destroy = "bm_result_destroy"
+
+
+def _out():
+    return ctypes.c_void_p()
+
+
+# ---- the C-ABI under its own names ----
+
+def bm_params_preset(name):
+    p = bm_params()
+    _check(_L.bm_params_preset(PRESETS[name] if isinstance(name, str) else name, ctypes.byref(p)))
+    return p
+
+
+def bm_context_create(params, device=0):
+    if isinstance(params, (str, int)):
+        params = bm_params_preset(params)
+    h = _out()
+    _check(_L.bm_context_create(ctypes.byref(params), device, ctypes.byref(h)))
+    ctx = Context(h.value)
+    ctx.params = params
+    ctx.n = 1 << params.log_n
+    ctx.n_q, ctx.n_p, ctx.dnum = params.n_q, params.n_p, params.dnum
+    return ctx
+
+
+def bm_context_primes(ctx):
+    out = np.zeros(ctx.n_q + ctx.n_p, dtype=np.uint64)
+    _check(_L.bm_context_primes(ctx.ptr, _u64p(out), out.size))
+    return [int(x) for x in out]
+
+
+def bm_keygen(ctx, seed, dim, part):
+    sk, pk, ek = _out(), _out(), _out()
+    _check(_L.bm_keygen(ctx.ptr, seed, dim, part, ctypes.byref(sk), ctypes.byref(pk), ctypes.byref(ek)))
+    return SecretKey(sk.value, ctx), PublicKey(pk.value, ctx), EvalKeys(ek.value, ctx)
+
+
+def bm_eval_keys_rotations(evk):
+    cnt = _u32()
+    _check(_L.bm_eval_keys_rotations(evk.ptr, None, 0, ctypes.byref(cnt)))
+    out = (ctypes.c_int32 * max(cnt.value, 1))()
+    _check(_L.bm_eval_keys_rotations(evk.ptr, out, cnt.value, ctypes.byref(cnt)))
+    return sorted(out[i] for i in range(cnt.value))
+
+
+def bm_secret_key_export(sk):
+    ctx = sk.owner
+    out = np.zeros(ctx.n, dtype=np.int64)
+    _check(_L.bm_secret_key_export(sk.ptr, out.ctypes.data_as(_I64P), out.size))
+    return out
+
+
+def bm_public_key_export(pk):
+    ctx = pk.owner
+    out = np.zeros((2, ctx.n_q, ctx.n), dtype=np.uint64)
+    _check(_L.bm_public_key_export(pk.ptr, _u64p(out), out.size))
+    return out
+
+
+def bm_eval_keys_export(evk, rotation):
+    ctx = evk.owner
+    out = np.zeros((ctx.dnum, 2, ctx.n_q + ctx.n_p, ctx.n), dtype=np.uint64)
+    _check(_L.bm_eval_keys_export(evk.ptr, rotation, _u64p(out), out.size))
+    return out
+
+
+def bm_gallery_layout(ctx, n_ids, dim, part):
+    v = [_u32() for _ in range(5)]
+    _check(_L.bm_gallery_layout(ctx.ptr, n_ids, dim, part, *[ctypes.byref(x) for x in v]))
+    return dict(zip(["groups", "level", "tiled", "compressed", "n_out"], [x.value for x in v]))
+
+
+def bm_encode_gallery(ctx, feats, dim, part):
+    f = np.ascontiguousarray(feats, dtype=np.float64)
+    h = _out()
+    _check(_L.bm_encode_gallery(ctx.ptr, f.ctypes.data_as(_DP), f.shape[0], dim, part, ctypes.byref(h)))
+    g = Gallery(h.value, ctx)
+    g.n_ids, g.dim, g.part = f.shape[0], dim, part
+    return g
+
+
+def bm_gallery_import(ctx, pts, masks, cmask, n_ids, dim, part):
+    arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.uint64) for a in (pts, masks, cmask)]
+    ptrs = [None if a is None else _u64p(a) for a in arrs]
+    h = _out()
+    _check(_L.bm_gallery_import(ctx.ptr, *ptrs, n_ids, dim, part, ctypes.byref(h)))
+    g = Gallery(h.value, ctx)
+    g.n_ids, g.dim, g.part = n_ids, dim, part
+    return g
+
+
+def bm_gallery_export(g):
+    ctx = g.owner
+    lo = bm_gallery_layout(ctx, g.n_ids, g.dim, g.part)
+    n_in, lvl = g.dim // g.part, lo["level"]
+    pts = np.zeros((lo["groups"], n_in, lvl + 1, ctx.n), dtype=np.uint64)
+    masks = np.zeros((n_in, ctx.n_q, ctx.n), dtype=np.uint64) if lo["tiled"] else None
+    cmask = np.zeros((lvl, ctx.n), dtype=np.uint64) if lo["compressed"] else None
+    _check(_L.bm_gallery_export(g.ptr, _u64p(pts), None if masks is None else _u64p(masks),
+                                None if cmask is None else _u64p(cmask)))
+    return pts, masks, cmask
+
+
+def bm_encrypt_query(ctx, pk, q, dim, part, mode, seed, query_id):
+    qa = np.ascontiguousarray(q, dtype=np.float64)
+    h = _out()
+    _check(_L.bm_encrypt_query(ctx.ptr, pk.ptr, qa.ctypes.data_as(_DP), dim, part, mode, seed, query_id,
+                               ctypes.byref(h)))
+    return Ciphertext(h.value, ctx)
+
+
+def bm_ciphertext_import(ctx, data, level):
+    d = np.ascontiguousarray(data, dtype=np.uint64).reshape(-1, 2, level + 1, ctx.n)
+    h = _out()
+    _check(_L.bm_ciphertext_import(ctx.ptr, _u64p(d), d.shape[0], level, ctypes.byref(h)))
+    return Ciphertext(h.value, ctx)
+
+
+def bm_ciphertext_info(ct):
+    n, l = _u32(), _u32()
+    _check(_L.bm_ciphertext_info(ct.ptr, ctypes.byref(n), ctypes.byref(l)))
+    return n.value, l.value
+
+
+def bm_ciphertext_export(ct):
+    n_cts, level = bm_ciphertext_info(ct)
+    out = np.zeros((n_cts, 2, level + 1, ct.owner.n), dtype=np.uint64)
+    _check(_L.bm_ciphertext_export(ct.ptr, _u64p(out), out.size))
+    return out
+
+
+def bm_ciphertext_upload(ct, stream=None):
+    _check(_L.bm_ciphertext_upload(ct.ptr, stream))
+
+
+def bm_match(ctx, evk, gallery, queries, stream=None):
+    arr = (ctypes.c_void_p * len(queries))(*[q.ptr for q in queries])
+    h = _out()
+    _check(_L.bm_match(ctx.ptr, evk.ptr, gallery.ptr, arr, len(queries), stream, ctypes.byref(h)))
+    return Result(h.value, ctx)
+
+
+def bm_result_info(r):
+    a, b, c = _u32(), _u32(), _u32()
+    _check(_L.bm_result_info(r.ptr, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, bool(c.value)
+
+
+def bm_result_export(r, query_index):
+    _, n_out, _ = bm_result_info(r)
+    out = np.zeros((n_out, 2, 1, r.owner.n), dtype=np.uint64)
+    _check(_L.bm_result_export(r.ptr, query_index, _u64p(out), out.size))
+    return out
+
+
+def bm_decrypt_scores(ctx, sk, r, query_index, n_ids):
+    scores = np.zeros(n_ids, dtype=np.float64)
+    rank1, best = _i64(), _dbl()
+    _check(_L.bm_decrypt_scores(ctx.ptr, sk.ptr, r.ptr, query_index, scores.ctypes.data_as(_DP), n_ids,
+                                ctypes.byref(rank1), ctypes.byref(best)))
+    return scores, rank1.value, best.value
+
+
+def bm_poly_mul(ctx, a, b):
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    b = np.ascontiguousarray(b, dtype=np.uint64)
+    out = np.zeros_like(a)
+    _check(_L.bm_poly_mul(ctx.ptr, _u64p(a), _u64p(b), _u64p(out), a.shape[0]))
+    return out
+
+
+def bm_ct_rotate(ctx, evk, ct, rotation):
+    h = _out()
+    _check(_L.bm_ct_rotate(ctx.ptr, evk.ptr, ct.ptr, rotation, ctypes.byref(h)))
+    return Ciphertext(h.value, ctx)
+
+
+def bm_ct_rescale(ctx, ct):
+    h = _out()
+    _check(_L.bm_ct_rescale(ctx.ptr, ct.ptr, ctypes.byref(h)))
+    return Ciphertext(h.value, ctx)
+
+
+def bm_ntt_forward(ctx, d_ptr, n_polys, n_limbs, stream=None):
+    _check(_L.bm_ntt_forward(ctx.ptr, d_ptr, n_polys, n_limbs, stream))
+
+
+def bm_ntt_inverse(ctx, d_ptr, n_polys, n_limbs, stream=None):
+    _check(_L.bm_ntt_inverse(ctx.ptr, d_ptr, n_polys, n_limbs, stream))

@@ -1,0 +1,1136 @@
+// api.cu -- C-ABI of the Blind-Match GPU library (declared in include/blindmatch.h).
+//
+// Client-side calls (keygen, encrypt, decrypt) sample on the host and do their
+// polynomial arithmetic with the same GPU kernels as the match; bm_match runs
+// the server side of Sec. 3.3 entirely on the device: Algorithm 1 (Input
+// Ciphertext Expansion), Algorithm 2 (HE-C^3) for every gallery group, and the
+// compression step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bm_internal.h"
+
+namespace bm {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+static bm_status fail(bm_status s, const std::string& msg) {
+    set_error(msg);
+    return s;
+}
+
+#define BM_TRY(expr)                              \
+    do {                                          \
+        bm_status st_ = (expr);                   \
+        if (st_ != BM_OK) return st_;             \
+    } while (0)
+
+static bool is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
+static uint32_t ilog2(uint64_t x) {
+    uint32_t r = 0;
+    while ((1ull << r) < x) r++;
+    return r;
+}
+static size_t ct_words(const Context& c, uint32_t level) { return (size_t)2 * (level + 1) * c.n; }
+
+// RAII device buffer
+struct DevBuf {
+    uint64_t* p = nullptr;
+    size_t words = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t alloc(size_t w) {
+        words = w;
+        return cudaMalloc(&p, std::max<size_t>(w, 1) * sizeof(uint64_t));
+    }
+    uint64_t* release() {
+        uint64_t* r = p;
+        p = nullptr;
+        return r;
+    }
+};
+
+static LimbBatch limbs_of(uint64_t* base, uint32_t n_polys, uint32_t nl, uint64_t poly_stride,
+                          uint32_t first_prime = 0, uint32_t limb_off = 0) {
+    LimbBatch b{base, n_polys, poly_stride, limb_off, nl, {}};
+    for (uint32_t k = 0; k < nl; k++) b.pi[k] = (uint8_t)(first_prime + k);
+    return b;
+}
+// polys of `nl` consecutive limbs starting at prime 0, packed
+static LimbBatch packed(const Context& c, uint64_t* base, uint32_t n_polys, uint32_t nl) {
+    return limbs_of(base, n_polys, nl, (uint64_t)nl * c.n);
+}
+
+// ---------------------------------------------------------------------------
+// schedule layout for (n_ids, dim, part) under a context
+// ---------------------------------------------------------------------------
+
+struct Layout {
+    uint32_t n_in, G, groups, level, n_out;
+    bool tiled, compress;
+};
+
+static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uint32_t part, Layout& lo) {
+    if (!is_pow2(dim) || !is_pow2(part) || part > dim || dim > c.slots)
+        return fail(BM_E_DIM, "dim and part size must be powers of two with part <= dim <= N/2");
+    if (c.L < 1) return fail(BM_E_LEVEL, "the modulus chain needs at least one rescale prime");
+    lo.n_in = dim / part;
+    lo.G = c.slots / part;
+    lo.groups = (uint32_t)((n_ids + lo.G - 1) / lo.G);
+    lo.tiled = c.L >= 3;                    // Algorithm 1 (1 level) + HE-C^3 (1) + compression (1)
+    lo.level = lo.tiled ? c.L - 1 : c.L;    // level of the query parts entering HE-C^3
+    lo.compress = lo.level >= 2;            // a level left after HE-C^3 for the mask
+    lo.n_out = lo.compress ? (lo.groups + part - 1) / part : lo.groups;
+    return BM_OK;
+}
+
+// left-rotation amounts the schedule uses (negative = right)
+static std::vector<int32_t> schedule_rotations(const Context& c, const Layout& lo, uint32_t part) {
+    std::vector<int32_t> r;
+    if (lo.tiled)
+        for (uint32_t j = 0; (1u << j) < lo.n_in; j++) r.push_back((int32_t)(part << j));
+    for (uint32_t t = 0; (1u << t) < part; t++) r.push_back((int32_t)(1u << t));
+    if (lo.compress)
+        for (uint32_t t = 0; (1u << t) < part; t++) r.push_back(-(int32_t)(1u << t));
+    (void)c;
+    return r;
+}
+
+static uint64_t galois_of(const Context& c, int32_t rot) {
+    const uint64_t two_n = 2ull * c.n;
+    int64_t r = rot % (int64_t)c.slots;
+    if (r < 0) r += c.slots;
+    return h_powmod(5, (uint64_t)r, two_n);
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+
+static bm_status context_init(Context& c, const bm_params& p, int device) {
+    if (p.log_n < 12 || p.log_n > 16) return fail(BM_E_PARAM, "log_n must be in [12, 16]");
+    if (p.n_q < 2 || p.n_q > BM_MAX_Q || p.n_p < 1 || p.n_p > BM_MAX_P)
+        return fail(BM_E_PARAM, "n_q must be in [2, 6] and n_p in [1, 3]");
+    std::vector<uint32_t> bits;
+    for (uint32_t i = 0; i < p.n_q; i++) bits.push_back(p.q_bits[i]);
+    for (uint32_t i = 0; i < p.n_p; i++) bits.push_back(p.p_bits[i]);
+    for (uint32_t b : bits)
+        if (b < 30 || b > 60) return fail(BM_E_PARAM, "prime sizes must be in [30, 60] bits");
+    if (p.dnum < 1 || p.dnum > MAXD) return fail(BM_E_PARAM, "dnum must be in [1, 4]");
+    const uint32_t dsize = (p.n_q + p.dnum - 1) / p.dnum;
+    if (dsize > MAXDS || (p.dnum - 1) * dsize >= p.n_q)
+        return fail(BM_E_PARAM, "digits must be non-empty and hold at most 3 primes");
+    if (p.log_scale < 20 || p.log_scale > 50) return fail(BM_E_PARAM, "log_scale must be in [20, 50]");
+    c.params = p;
+    c.device = device;
+    c.log_n = p.log_n;
+    c.n = 1u << p.log_n;
+    c.slots = c.n / 2;
+    c.L = p.n_q - 1;
+    c.alpha = p.n_p;
+    c.nb = p.n_q + p.n_p;
+    c.scale = std::ldexp(1.0, (int)p.log_scale);
+    if (!gen_primes(c.log_n, bits, c.primes)) return fail(BM_E_PARAM, "prime search failed");
+    c.digits.clear();
+    for (uint32_t d = 0; d < p.dnum; d++) {
+        std::vector<uint32_t> dg;
+        for (uint32_t j = d * dsize; j < std::min(p.n_q, (d + 1) * dsize); j++) dg.push_back(j);
+        c.digits.push_back(dg);
+    }
+    for (uint32_t j = 0; j < c.nb; j++) {
+        uint64_t P = 1;
+        for (uint32_t k = 0; k < c.alpha; k++) P = h_mulmod(P, c.primes[c.L + 1 + k] % c.primes[j], c.primes[j]);
+        c.P_mod[j] = P;
+    }
+    BM_CUDA_TRY(cudaSetDevice(device));
+    BM_CUDA_TRY(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+    // twiddles: per prime, N forward pairs then N inverse pairs
+    const size_t per = (size_t)2 * c.n;
+    std::vector<ulonglong2> tw(per * c.nb);
+    for (uint32_t j = 0; j < c.nb; j++) {
+        const uint64_t q = c.primes[j];
+        const uint64_t psi = find_psi(q, c.log_n);
+        if (!psi) return fail(BM_E_PARAM, "no primitive 2N-th root");
+        c.psi.push_back(psi);
+        const uint64_t ipsi = h_invmod(psi, q);
+        std::vector<uint64_t> pw(c.n), ipw(c.n);
+        pw[0] = ipw[0] = 1;
+        for (uint32_t i = 1; i < c.n; i++) {
+            pw[i] = h_mulmod(pw[i - 1], psi, q);
+            ipw[i] = h_mulmod(ipw[i - 1], ipsi, q);
+        }
+        for (uint32_t k = 0; k < c.n; k++) {
+            uint32_t r = 0;
+            for (uint32_t b = 0; b < c.log_n; b++) r |= ((k >> b) & 1u) << (c.log_n - 1 - b);
+            tw[j * per + k] = make_ulonglong2(pw[r], h_shoup_companion(pw[r], q));
+            tw[j * per + c.n + k] = make_ulonglong2(ipw[r], h_shoup_companion(ipw[r], q));
+        }
+        c.tab.q[j] = q;
+        c.tab.qneg[j] = h_mont_qneg(q);
+        c.tab.rsh[j] = h_shoup_companion(1, q);
+        c.tab.r2[j] = h_r2(q);
+        c.tab.ninv[j] = h_invmod(c.n % q, q);
+        c.tab.ninv_sh[j] = h_shoup_companion(c.tab.ninv[j], q);
+    }
+    BM_CUDA_TRY(cudaMalloc(&c.d_twiddles, tw.size() * sizeof(ulonglong2)));
+    BM_CUDA_TRY(cudaMemcpy(c.d_twiddles, tw.data(), tw.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice));
+    for (uint32_t j = 0; j < c.nb; j++) {
+        c.tab.tw[j] = (const ulonglong2*)c.d_twiddles + j * per;
+        c.tab.itw[j] = (const ulonglong2*)c.d_twiddles + j * per + c.n;
+    }
+    return BM_OK;
+}
+
+// signed coefficients -> NTT form on limbs [first, first+nl) of dst (one poly)
+static bm_status upload_signed_ntt(const Context& c, const int64_t* h, uint64_t* dst, uint32_t nl, uint32_t first_prime,
+                                   cudaStream_t s, bool montgomery) {
+    int64_t* d = nullptr;
+    BM_CUDA_TRY(cudaMallocAsync(&d, sizeof(int64_t) * c.n, s));
+    BM_CUDA_TRY(cudaMemcpyAsync(d, h, sizeof(int64_t) * c.n, cudaMemcpyHostToDevice, s));
+    LimbBatch b = limbs_of(dst, 1, nl, (uint64_t)nl * c.n, first_prime);
+    BM_CUDA_TRY(lift_signed(c, d, b, s));
+    BM_CUDA_TRY(ntt_forward(c, b, s));
+    if (montgomery) BM_CUDA_TRY(to_montgomery(c, b, false, s));
+    BM_CUDA_TRY(cudaFreeAsync(d, s));
+    return BM_OK;
+}
+
+}  // namespace bm
+
+using namespace bm;
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+const char* bm_last_error(void) { return g_last_error.c_str(); }
+
+bm_status bm_params_preset(int preset, bm_params* out) {
+    if (!out) return fail(BM_E_ARG, "null output");
+    bm_params p{};
+    p.log_scale = 40;
+    p.sigma = 3.2;
+    p.dnum = 2;
+    switch (preset) {
+        case BM_PRESET_TOY:
+            p.log_n = 12; p.n_q = 2; p.q_bits[0] = 50; p.q_bits[1] = 40;
+            p.n_p = 1; p.p_bits[0] = 50; p.secret_hw = 0;
+            break;
+        case BM_PRESET_RING16:
+        case BM_PRESET_SMALL4:
+            p.log_n = preset == BM_PRESET_RING16 ? 16 : 12;
+            p.n_q = 4; p.q_bits[0] = 60; p.q_bits[1] = p.q_bits[2] = p.q_bits[3] = 40;
+            p.n_p = 2; p.p_bits[0] = p.p_bits[1] = 60; p.secret_hw = 192;
+            break;
+        default:
+            return fail(BM_E_ARG, "unknown preset");
+    }
+    *out = p;
+    return BM_OK;
+}
+
+bm_status bm_context_create(const bm_params* params, int device, bm_context** out) {
+    if (!params || !out) return fail(BM_E_ARG, "null argument");
+    auto* h = new bm_context();
+    bm_status s = context_init(h->c, *params, device);
+    if (s != BM_OK) {
+        bm_context_destroy(h);
+        return s;
+    }
+    *out = h;
+    return BM_OK;
+}
+
+void bm_context_destroy(bm_context* ctx) {
+    if (!ctx) return;
+    if (ctx->c.d_twiddles) cudaFree(ctx->c.d_twiddles);
+    if (ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
+    delete ctx;
+}
+
+bm_status bm_context_primes(const bm_context* ctx, uint64_t* primes_out, size_t capacity) {
+    if (!ctx || !primes_out) return fail(BM_E_ARG, "null argument");
+    if (capacity < ctx->c.primes.size()) return fail(BM_E_ARG, "capacity too small");
+    std::copy(ctx->c.primes.begin(), ctx->c.primes.end(), primes_out);
+    return BM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// keys
+// ---------------------------------------------------------------------------
+
+bm_status bm_keygen(bm_context* ctxh, uint64_t seed, uint32_t dim, uint32_t part_size, bm_secret_key** sk_out,
+                    bm_public_key** pk_out, bm_eval_keys** evk_out) {
+    if (!ctxh || !sk_out || !pk_out || !evk_out) return fail(BM_E_ARG, "null argument");
+    Context& c = ctxh->c;
+    Layout lo;
+    BM_TRY(make_layout(c, 1, dim, part_size, lo));
+    BM_CUDA_TRY(cudaSetDevice(c.device));
+    cudaStream_t s = c.stream;
+    const size_t n = c.n, nb = c.nb, L1 = c.L + 1;
+
+    auto* skh = new bm_secret_key();
+    skh->k.ctx = &c;
+    skh->k.coeffs.resize(n);
+    sample_secret(seed, c.params.secret_hw, c.log_n, skh->k.coeffs.data());
+    DevBuf s_plain, s_mont;
+    if (s_plain.alloc(nb * n) || s_mont.alloc(nb * n)) {
+        delete skh;
+        return fail(BM_E_OOM, "device allocation failed");
+    }
+    bm_status st = upload_signed_ntt(c, skh->k.coeffs.data(), s_plain.p, nb, 0, s, false);
+    if (st != BM_OK) { delete skh; return st; }
+    cudaMemcpyAsync(s_mont.p, s_plain.p, nb * n * 8, cudaMemcpyDeviceToDevice, s);
+    to_montgomery(c, packed(c, s_mont.p, 1, nb), false, s);
+    skh->k.d_ntt = s_mont.release();
+
+    // public key (b, a) over Q_L: b = e - a*s
+    auto* pkh = new bm_public_key();
+    pkh->k.ctx = &c;
+    DevBuf pkb, tmp;
+    pkb.alloc(2 * L1 * n);
+    tmp.alloc(L1 * n);
+    std::vector<uint64_t> host(nb * n);
+    std::vector<int64_t> e(n);
+    for (uint32_t j = 0; j < L1; j++) sample_uniform(seed, TAG_PK_A, 0, j, c.primes[j], host.data() + j * n, c.n);
+    sample_gauss(seed, TAG_PK_E, 0, c.params.sigma, e.data(), c.n);
+    uint64_t* pk_b = pkb.p;
+    uint64_t* pk_a = pkb.p + L1 * n;
+    cudaMemcpyAsync(pk_a, host.data(), L1 * n * 8, cudaMemcpyHostToDevice, s);
+    ntt_forward(c, packed(c, pk_a, 1, L1), s);
+    upload_signed_ntt(c, e.data(), pk_b, L1, 0, s, false);
+    pointwise_mul(c, packed(c, pk_a, 1, L1), limbs_of(skh->k.d_ntt, 1, L1, nb * n),
+                  packed(c, tmp.p, 1, L1), s);
+    pointwise_addsub(c, packed(c, pk_b, 1, L1), packed(c, tmp.p, 1, L1), packed(c, pk_b, 1, L1), true, s);
+    to_montgomery(c, packed(c, pkb.p, 2, L1), false, s);
+    pkh->k.d_ntt = pkb.release();
+
+    // rotation keys: per digit d, b_d = e_d - a_d*s + P*[limb in digit d]*sigma_k(s) over Q_L u P
+    auto* evh = new bm_eval_keys();
+    evh->k.ctx = &c;
+    evh->k.dim = dim;
+    evh->k.part = part_size;
+    const uint32_t nd = (uint32_t)c.digits.size();
+    DevBuf srot, prod;
+    srot.alloc(nb * n);
+    prod.alloc(nb * n);
+    for (int32_t rot : schedule_rotations(c, lo, part_size)) {
+        const uint64_t k = galois_of(c, rot);
+        if (evh->k.keys.count(k)) continue;
+        DevBuf key;
+        if (key.alloc((size_t)nd * 2 * nb * n) != cudaSuccess) {
+            delete skh; delete pkh; delete evh;
+            return fail(BM_E_OOM, "rotation key allocation failed");
+        }
+        permute_ntt(c, packed(c, s_plain.p, 1, nb), packed(c, srot.p, 1, nb), k, s);
+        for (uint32_t d = 0; d < nd; d++) {
+            const uint64_t obj = k * 16 + d;
+            uint64_t* kb = key.p + ((size_t)d * 2 + 0) * nb * n;
+            uint64_t* ka = key.p + ((size_t)d * 2 + 1) * nb * n;
+            for (uint32_t j = 0; j < nb; j++) sample_uniform(seed, TAG_RK_A, obj, j, c.primes[j], host.data() + j * n, c.n);
+            sample_gauss(seed, TAG_RK_E, obj, c.params.sigma, e.data(), c.n);
+            cudaMemcpyAsync(ka, host.data(), nb * n * 8, cudaMemcpyHostToDevice, s);
+            ntt_forward(c, packed(c, ka, 1, nb), s);
+            upload_signed_ntt(c, e.data(), kb, nb, 0, s, false);
+            pointwise_mul(c, packed(c, ka, 1, nb), packed(c, skh->k.d_ntt, 1, nb), packed(c, prod.p, 1, nb), s);
+            pointwise_addsub(c, packed(c, kb, 1, nb), packed(c, prod.p, 1, nb), packed(c, kb, 1, nb), true, s);
+            for (uint32_t j : c.digits[d]) {
+                LimbBatch one = limbs_of(srot.p + (size_t)j * n, 1, 1, n, j);
+                LimbBatch dst = limbs_of(prod.p + (size_t)j * n, 1, 1, n, j);
+                scalar_mul(c, one, &c.P_mod[j], dst, s);
+                LimbBatch kbj = limbs_of(kb + (size_t)j * n, 1, 1, n, j);
+                pointwise_addsub(c, kbj, dst, kbj, false, s);
+            }
+            // the host staging buffers are reused by the next digit: wait for the copies
+            cudaStreamSynchronize(s);
+        }
+        to_montgomery(c, packed(c, key.p, nd * 2, nb), false, s);
+        evh->k.keys[k] = key.release();
+    }
+    cudaError_t ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) {
+        delete skh; delete pkh; delete evh;
+        return fail(BM_E_CUDA, std::string("keygen: ") + cudaGetErrorString(ce));
+    }
+    *sk_out = skh;
+    *pk_out = pkh;
+    *evk_out = evh;
+    return BM_OK;
+}
+
+void bm_secret_key_destroy(bm_secret_key* sk) {
+    if (!sk) return;
+    if (sk->k.d_ntt) cudaFree(sk->k.d_ntt);
+    delete sk;
+}
+void bm_public_key_destroy(bm_public_key* pk) {
+    if (!pk) return;
+    if (pk->k.d_ntt) cudaFree(pk->k.d_ntt);
+    delete pk;
+}
+void bm_eval_keys_destroy(bm_eval_keys* evk) { delete evk; }
+
+bm_status bm_eval_keys_rotations(const bm_eval_keys* evk, int32_t* rotations, size_t capacity, uint32_t* count) {
+    if (!evk || !count) return fail(BM_E_ARG, "null argument");
+    const Context& c = *evk->k.ctx;
+    std::vector<int32_t> rots;
+    for (auto& kv : evk->k.keys) {
+        for (int32_t r = 1; r < (int32_t)c.slots; r++)
+            if (galois_of(c, r) == kv.first) {
+                rots.push_back(r > (int32_t)c.slots / 2 ? r - (int32_t)c.slots : r);
+                break;
+            }
+    }
+    *count = (uint32_t)rots.size();
+    if (rotations) {
+        if (capacity < rots.size()) return fail(BM_E_ARG, "capacity too small");
+        std::copy(rots.begin(), rots.end(), rotations);
+    }
+    return BM_OK;
+}
+
+static bm_status download_coeff(const Context& c, const uint64_t* d_src, uint32_t n_polys, uint32_t nl,
+                                bool from_mont, uint64_t* out) {
+    cudaStream_t s = c.stream;
+    const size_t words = (size_t)n_polys * nl * c.n;
+    DevBuf t;
+    BM_CUDA_TRY(t.alloc(words));
+    BM_CUDA_TRY(cudaMemcpyAsync(t.p, d_src, words * 8, cudaMemcpyDeviceToDevice, s));
+    if (from_mont) BM_CUDA_TRY(to_montgomery(c, packed(c, t.p, n_polys, nl), true, s));
+    BM_CUDA_TRY(ntt_inverse(c, packed(c, t.p, n_polys, nl), s));
+    BM_CUDA_TRY(cudaMemcpyAsync(out, t.p, words * 8, cudaMemcpyDeviceToHost, s));
+    BM_CUDA_TRY(cudaStreamSynchronize(s));
+    return BM_OK;
+}
+
+bm_status bm_secret_key_export(const bm_secret_key* sk, int64_t* out, size_t capacity) {
+    if (!sk || !out) return fail(BM_E_ARG, "null argument");
+    if (capacity < sk->k.coeffs.size()) return fail(BM_E_ARG, "capacity too small");
+    std::copy(sk->k.coeffs.begin(), sk->k.coeffs.end(), out);
+    return BM_OK;
+}
+
+bm_status bm_public_key_export(const bm_public_key* pk, uint64_t* out, size_t capacity) {
+    if (!pk || !out) return fail(BM_E_ARG, "null argument");
+    const Context& c = *pk->k.ctx;
+    if (capacity < (size_t)2 * (c.L + 1) * c.n) return fail(BM_E_ARG, "capacity too small");
+    BM_CUDA_TRY(cudaSetDevice(c.device));
+    return download_coeff(c, pk->k.d_ntt, 2, c.L + 1, true, out);
+}
+
+bm_status bm_eval_keys_export(const bm_eval_keys* evk, int32_t rotation, uint64_t* out, size_t capacity) {
+    if (!evk || !out) return fail(BM_E_ARG, "null argument");
+    const Context& c = *evk->k.ctx;
+    auto it = evk->k.keys.find(galois_of(c, rotation));
+    if (it == evk->k.keys.end()) return fail(BM_E_KEY_MISSING, "no key for this rotation");
+    const uint32_t nd = (uint32_t)c.digits.size();
+    if (capacity < (size_t)nd * 2 * c.nb * c.n) return fail(BM_E_ARG, "capacity too small");
+    BM_CUDA_TRY(cudaSetDevice(c.device));
+    return download_coeff(c, it->second, nd * 2, c.nb, true, out);
+}
+
+}  // extern "C"
+
+bm::EvalKeys::~EvalKeys() {
+    for (auto& kv : keys) cudaFree(kv.second);
+}
+bm::Gallery::~Gallery() {
+    if (d_pts) cudaFree(d_pts);
+    if (d_masks) cudaFree(d_masks);
+    if (d_cmask) cudaFree(d_cmask);
+}
+bm::Ciphertext::~Ciphertext() {
+    if (d_ntt) cudaFree(d_ntt);
+}
+bm::Result::~Result() {
+    if (d_data) cudaFree(d_data);
+}
+
+// ---------------------------------------------------------------------------
+// gallery
+// ---------------------------------------------------------------------------
+
+namespace bm {
+
+static bm_status gallery_alloc(Context& c, const Layout& lo, uint64_t n_ids, uint32_t dim, uint32_t part,
+                               bm_gallery** out, bm_gallery*& gh) {
+    gh = new bm_gallery();
+    Gallery& g = gh->g;
+    g.ctx = &c;
+    g.n_ids = n_ids;
+    g.dim = dim;
+    g.part = part;
+    g.n_in = lo.n_in;
+    g.groups = lo.groups;
+    g.level = lo.level;
+    g.tiled = lo.tiled;
+    g.compress = lo.compress;
+    const size_t n = c.n;
+    cudaError_t e = cudaMalloc(&g.d_pts, (size_t)lo.groups * lo.n_in * (lo.level + 1) * n * 8);
+    if (e == cudaSuccess && lo.tiled) e = cudaMalloc(&g.d_masks, (size_t)lo.n_in * (c.L + 1) * n * 8);
+    if (e == cudaSuccess && lo.compress) e = cudaMalloc(&g.d_cmask, (size_t)lo.level * n * 8);
+    if (e != cudaSuccess) {
+        delete gh;
+        gh = nullptr;
+        return fail(BM_E_OOM, "gallery allocation failed");
+    }
+    (void)out;
+    return BM_OK;
+}
+
+// encode real slots z at `scale` into limbs 0..level of dst (NTT + Montgomery)
+static bm_status encode_to_device(Context& c, const std::vector<double>& z, double scale, uint32_t level,
+                                  uint64_t* dst) {
+    std::vector<int64_t> m(c.n);
+    encode_real(c, z.data(), scale, m.data());
+    BM_TRY(upload_signed_ntt(c, m.data(), dst, level + 1, 0, c.stream, true));
+    BM_CUDA_TRY(cudaStreamSynchronize(c.stream));   // m is a host temporary
+    return BM_OK;
+}
+
+}  // namespace bm
+
+extern "C" {
+
+bm_status bm_gallery_layout(const bm_context* ctx, uint64_t n_ids, uint32_t dim, uint32_t part_size, uint32_t* groups,
+                            uint32_t* level, uint32_t* tiled, uint32_t* compressed, uint32_t* n_out) {
+    if (!ctx) return fail(BM_E_ARG, "null context");
+    Layout lo;
+    BM_TRY(make_layout(ctx->c, n_ids, dim, part_size, lo));
+    if (groups) *groups = lo.groups;
+    if (level) *level = lo.level;
+    if (tiled) *tiled = lo.tiled;
+    if (compressed) *compressed = lo.compress;
+    if (n_out) *n_out = lo.n_out;
+    return BM_OK;
+}
+
+bm_status bm_encode_gallery(bm_context* ctxh, const double* feats, uint64_t n_ids, uint32_t dim, uint32_t part_size,
+                            bm_gallery** out) {
+    if (!ctxh || !feats || !out || n_ids == 0) return fail(BM_E_ARG, "null argument or empty gallery");
+    Context& c = ctxh->c;
+    Layout lo;
+    BM_TRY(make_layout(c, n_ids, dim, part_size, lo));
+    BM_CUDA_TRY(cudaSetDevice(c.device));
+    bm_gallery* gh;
+    BM_TRY(gallery_alloc(c, lo, n_ids, dim, part_size, out, gh));
+    Gallery& g = gh->g;
+    const size_t n = c.n, S = c.slots;
+    std::vector<double> z(S);
+    for (uint32_t grp = 0; grp < lo.groups; grp++) {
+        for (uint32_t i = 0; i < lo.n_in; i++) {
+            std::fill(z.begin(), z.end(), 0.0);
+            for (uint32_t u = 0; u < lo.G; u++) {
+                const uint64_t id = (uint64_t)grp * lo.G + u;
+                if (id >= n_ids) break;
+                for (uint32_t t = 0; t < part_size; t++) z[u * part_size + t] = feats[id * dim + i * part_size + t];
+            }
+            uint64_t* dst = g.d_pts + ((size_t)grp * lo.n_in + i) * (lo.level + 1) * n;
+            bm_status st = encode_to_device(c, z, (double)c.primes[lo.level], lo.level, dst);
+            if (st != BM_OK) { delete gh; return st; }
+        }
+    }
+    if (lo.tiled) {
+        for (uint32_t i = 0; i < lo.n_in; i++) {
+            for (size_t k = 0; k < S; k++) z[k] = ((k % dim) / part_size == i) ? 1.0 : 0.0;
+            bm_status st = encode_to_device(c, z, (double)c.primes[c.L], c.L, g.d_masks + (size_t)i * (c.L + 1) * n);
+            if (st != BM_OK) { delete gh; return st; }
+        }
+    }
+    if (lo.compress) {
+        for (size_t k = 0; k < S; k++) z[k] = (k % part_size == 0) ? 1.0 : 0.0;
+        bm_status st = encode_to_device(c, z, (double)c.primes[lo.level - 1], lo.level - 1, g.d_cmask);
+        if (st != BM_OK) { delete gh; return st; }
+    }
+    *out = gh;
+    return BM_OK;
+}
+
+bm_status bm_gallery_import(bm_context* ctxh, const uint64_t* pts, const uint64_t* masks, const uint64_t* cmask,
+                            uint64_t n_ids, uint32_t dim, uint32_t part_size, bm_gallery** out) {
+    if (!ctxh || !pts || !out || n_ids == 0) return fail(BM_E_ARG, "null argument or empty gallery");
+    Context& c = ctxh->c;
+    Layout lo;
+    BM_TRY(make_layout(c, n_ids, dim, part_size, lo));
+    if ((lo.tiled && !masks) || (lo.compress && !cmask)) return fail(BM_E_ARG, "masks required by this layout");
+    BM_CUDA_TRY(cudaSetDevice(c.device));
+    bm_gallery* gh;
+    BM_TRY(gallery_alloc(c, lo, n_ids, dim, part_size, out, gh));
+    Gallery& g = gh->g;
+    cudaStream_t s = c.stream;
+    const size_t n = c.n;
+    auto up = [&](uint64_t* dst, const uint64_t* src, uint32_t polys, uint32_t nl) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(dst, src, (size_t)polys * nl * n * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = ntt_forward(c, packed(c, dst, polys, nl), s);
+        if (e == cudaSuccess) e = to_montgomery(c, packed(c, dst, polys, nl), false, s);
+        return e;
+    };
+    cudaError_t e = up(g.d_pts, pts, lo.groups * lo.n_in, lo.level + 1);
+    if (e == cudaSuccess && lo.tiled) e = up(g.d_masks, masks, lo.n_in, c.L + 1);
+    if (e == cudaSuccess && lo.compress) e = up(g.d_cmask, cmask, 1, lo.level);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        delete gh;
+        return fail(BM_E_CUDA, std::string("gallery import: ") + cudaGetErrorString(e));
+    }
+    *out = gh;
+    return BM_OK;
+}
+
+bm_status bm_gallery_export(const bm_gallery* gh, uint64_t* pts, uint64_t* masks, uint64_t* cmask) {
+    if (!gh) return fail(BM_E_ARG, "null gallery");
+    const Gallery& g = gh->g;
+    const Context& c = *g.ctx;
+    BM_CUDA_TRY(cudaSetDevice(c.device));
+    if (pts) BM_TRY(download_coeff(c, g.d_pts, g.groups * g.n_in, g.level + 1, true, pts));
+    if (masks && g.tiled) BM_TRY(download_coeff(c, g.d_masks, g.n_in, c.L + 1, true, masks));
+    if (cmask && g.compress) BM_TRY(download_coeff(c, g.d_cmask, 1, g.level, true, cmask));
+    return BM_OK;
+}
+
+void bm_gallery_destroy(bm_gallery* g) { delete g; }
+
+// ---------------------------------------------------------------------------
+// ciphertexts
+// ---------------------------------------------------------------------------
+
+bm_status bm_encrypt_query(bm_context* ctxh, const bm_public_key* pk, const double* q, uint32_t dim,
+                           uint32_t part_size, uint32_t mode, uint64_t seed, uint64_t query_id,
+                           bm_ciphertext** out) {
+    if (!ctxh || !pk || !q || !out) return fail(BM_E_ARG, "null argument");
+    if (mode != BM_QUERY_TILED && mode != BM_QUERY_EXPANDED) return fail(BM_E_ARG, "unknown query mode");
+    Context& c = ctxh->c;
+    Layout lo;
+    BM_TRY(make_layout(c, 1, dim, part_size, lo));
+    BM_CUDA_TRY(cudaSetDevice(c.device));
+    cudaStream_t s = c.stream;
+    const size_t n = c.n, S = c.slots, L1 = c.L + 1;
+    const uint32_t n_cts = mode == BM_QUERY_TILED ? 1 : lo.n_in;
+    auto* ch = new bm_ciphertext();
+    Ciphertext& ct = ch->ct;
+    ct.ctx = &c;
+    ct.n_cts = n_cts;
+    ct.level = c.L;
+    ct.host.resize((size_t)n_cts * 2 * L1 * n);
+    DevBuf v, w;
+    if (v.alloc(L1 * n) || w.alloc(2 * L1 * n)) {
+        delete ch;
+        return fail(BM_E_OOM, "device allocation failed");
+    }
+    std::vector<double> z(S);
+    std::vector<int64_t> m(n), vv(n), e0(n), e1(n);
+    for (uint32_t k = 0; k < n_cts; k++) {
+        for (size_t j = 0; j < S; j++)
+            z[j] = mode == BM_QUERY_TILED ? q[j % dim] : q[k * part_size + (j % part_size)];
+        encode_real(c, z.data(), c.scale, m.data());
+        const uint64_t obj = query_id * 256 + k;
+        sample_zo(seed, TAG_ENC_V, obj, vv.data(), c.n);
+        sample_gauss(seed, TAG_ENC_E0, obj, c.params.sigma, e0.data(), c.n);
+        sample_gauss(seed, TAG_ENC_E1, obj, c.params.sigma, e1.data(), c.n);
+        for (size_t i = 0; i < n; i++) e0[i] += m[i];
+        bm_status st = upload_signed_ntt(c, vv.data(), v.p, L1, 0, s, false);
+        if (st == BM_OK) st = upload_signed_ntt(c, e0.data(), w.p, L1, 0, s, false);
+        if (st == BM_OK) st = upload_signed_ntt(c, e1.data(), w.p + L1 * n, L1, 0, s, false);
+        if (st != BM_OK) { delete ch; return st; }
+        DevBuf prod;
+        prod.alloc(2 * L1 * n);
+        for (int comp = 0; comp < 2; comp++) {
+            pointwise_mul(c, packed(c, v.p, 1, L1), packed(c, pk->k.d_ntt + comp * L1 * n, 1, L1),
+                          packed(c, prod.p + comp * L1 * n, 1, L1), s);
+        }
+        pointwise_addsub(c, packed(c, prod.p, 2, L1), packed(c, w.p, 2, L1), packed(c, prod.p, 2, L1), false, s);
+        ntt_inverse(c, packed(c, prod.p, 2, L1), s);
+        cudaMemcpyAsync(ct.host.data() + (size_t)k * 2 * L1 * n, prod.p, 2 * L1 * n * 8, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            delete ch;
+            return fail(BM_E_CUDA, std::string("encrypt: ") + cudaGetErrorString(e));
+        }
+    }
+    *out = ch;
+    return BM_OK;
+}
+
+bm_status bm_ciphertext_import(bm_context* ctxh, const uint64_t* data, uint32_t n_cts, uint32_t level,
+                               bm_ciphertext** out) {
+    if (!ctxh || !data || !out || n_cts == 0) return fail(BM_E_ARG, "null argument");
+    Context& c = ctxh->c;
+    if (level > c.L) return fail(BM_E_FORMAT, "level above the chain");
+    auto* ch = new bm_ciphertext();
+    ch->ct.ctx = &c;
+    ch->ct.n_cts = n_cts;
+    ch->ct.level = level;
+    ch->ct.host.assign(data, data + (size_t)n_cts * ct_words(c, level));
+    *out = ch;
+    return BM_OK;
+}
+
+bm_status bm_ciphertext_info(const bm_ciphertext* ct, uint32_t* n_cts, uint32_t* level) {
+    if (!ct) return fail(BM_E_ARG, "null ciphertext");
+    if (n_cts) *n_cts = ct->ct.n_cts;
+    if (level) *level = ct->ct.level;
+    return BM_OK;
+}
+
+bm_status bm_ciphertext_export(const bm_ciphertext* ct, uint64_t* out, size_t capacity) {
+    if (!ct || !out) return fail(BM_E_ARG, "null argument");
+    if (capacity < ct->ct.host.size()) return fail(BM_E_ARG, "capacity too small");
+    std::copy(ct->ct.host.begin(), ct->ct.host.end(), out);
+    return BM_OK;
+}
+
+bm_status bm_ciphertext_upload(bm_ciphertext* cth, void* stream) {
+    if (!cth) return fail(BM_E_ARG, "null ciphertext");
+    Ciphertext& ct = cth->ct;
+    const Context& c = *ct.ctx;
+    cudaStream_t s = (cudaStream_t)stream;
+    BM_CUDA_TRY(cudaSetDevice(c.device));
+    if (!ct.d_ntt) BM_CUDA_TRY(cudaMalloc(&ct.d_ntt, ct.host.size() * 8));
+    BM_CUDA_TRY(cudaMemcpyAsync(ct.d_ntt, ct.host.data(), ct.host.size() * 8, cudaMemcpyHostToDevice, s));
+    BM_CUDA_TRY(ntt_forward(c, packed(c, ct.d_ntt, ct.n_cts * 2, ct.level + 1), s));
+    BM_CUDA_TRY(cudaStreamSynchronize(s));
+    return BM_OK;
+}
+
+void bm_ciphertext_destroy(bm_ciphertext* ct) { delete ct; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// the match schedule (Sec. 3.3)
+// ---------------------------------------------------------------------------
+
+namespace bm {
+
+// Device arrays of ciphertext pointers for one schedule.  The schedule runs twice:
+// a dry pass that only collects the arrays, then (after one upload) the launch pass.
+struct PtrArena {
+    std::vector<uint64_t*> host;
+    uint64_t** dev = nullptr;
+    bool live = false;
+    size_t cursor = 0;
+    uint64_t* const* list(const std::vector<uint64_t*>& v) {
+        if (!live) {
+            host.insert(host.end(), v.begin(), v.end());
+            return nullptr;
+        }
+        uint64_t* const* p = dev + cursor;
+        cursor += v.size();
+        return p;
+    }
+};
+
+struct MatchRun {
+    Context& c;
+    const Gallery& g;
+    const EvalKeys& ek;
+    cudaStream_t s;
+    PtrArena arena;
+    uint32_t Q = 0, ncts = 0, chunk = 0, ksb = 128;
+    uint64_t *qin = nullptr, *t0 = nullptr, *T = nullptr, *accA = nullptr, *accB = nullptr, *scratch = nullptr;
+    uint64_t* result = nullptr;
+    uint32_t n_out = 0;
+    cudaError_t err = cudaSuccess;
+
+    MatchRun(Context& c_, const Gallery& g_, const EvalKeys& ek_, cudaStream_t s_) : c(c_), g(g_), ek(ek_), s(s_) {}
+
+    void check(cudaError_t e) {
+        if (err == cudaSuccess && e != cudaSuccess) err = e;
+    }
+    size_t cw(uint32_t level) const { return ct_words(c, level); }
+    const uint64_t* key(int32_t rot) const {
+        auto it = ek.keys.find(galois_of(c, rot));
+        return it == ek.keys.end() ? nullptr : it->second;
+    }
+
+    void rotate_batch(uint32_t level, int32_t rot, const std::vector<uint64_t*>& in,
+                      const std::vector<uint64_t*>& out, const std::vector<uint64_t*>* add) {
+        auto din = arena.list(in);
+        auto dout = arena.list(out);
+        auto dadd = add ? arena.list(*add) : nullptr;
+        if (!arena.live) return;
+        const uint64_t gk = galois_of(c, rot);
+        for (size_t b0 = 0; b0 < in.size(); b0 += ksb) {
+            const uint32_t B = (uint32_t)std::min<size_t>(ksb, in.size() - b0);
+            check(ks_rotate(c, key(rot), gk, level, B, din + b0, dout + b0, dadd ? dadd + b0 : nullptr, scratch, s));
+        }
+    }
+    void rescale_batch(uint32_t level, const std::vector<uint64_t*>& in, const std::vector<uint64_t*>& out) {
+        auto din = arena.list(in);
+        auto dout = arena.list(out);
+        if (!arena.live) return;
+        for (size_t b0 = 0; b0 < in.size(); b0 += ksb) {
+            const uint32_t B = (uint32_t)std::min<size_t>(ksb, in.size() - b0);
+            check(rescale(c, level, B, din + b0, dout + b0, scratch, s));
+        }
+    }
+    void mulplain_batch(uint32_t level, const std::vector<uint64_t*>& in, const std::vector<uint64_t*>& pt,
+                        const std::vector<uint64_t*>& out) {
+        auto din = arena.list(in);
+        auto dpt = arena.list(pt);
+        auto dout = arena.list(out);
+        if (!arena.live) return;
+        check(mul_plain(c, level, (uint32_t)in.size(), din, dpt, dout, s));
+    }
+
+    // The whole schedule; with arena.live == false only the pointer arrays are collected.
+    void schedule() {
+        const uint32_t n_in = g.n_in, part = g.part, lg = g.level;
+        // Algorithm 1: C_out,i = Res(Mul(P)(C_in, mask_i)), then log2(N_in) rotate-and-add by part*2^(j-1)
+        if (g.tiled) {
+            std::vector<uint64_t*> in, pt, o0, o1;
+            for (uint32_t q = 0; q < Q; q++)
+                for (uint32_t i = 0; i < n_in; i++) {
+                    in.push_back(qin + (size_t)q * cw(c.L));
+                    pt.push_back(g.d_masks + (size_t)i * (c.L + 1) * c.n);
+                    o0.push_back(t0 + ((size_t)q * n_in + i) * cw(c.L));
+                    o1.push_back(T + ((size_t)q * n_in + i) * cw(lg));
+                }
+            mulplain_batch(c.L, in, pt, o0);
+            rescale_batch(c.L, o0, o1);
+            for (uint32_t j = 1; (1u << (j - 1)) < n_in; j++) rotate_batch(lg, (int32_t)(part << (j - 1)), o1, o1, &o1);
+        }
+        const uint64_t* Tsrc = g.tiled ? T : qin;
+        // HE-C^3 per chunk of groups, then compression
+        for (uint32_t g0 = 0; g0 < g.groups; g0 += chunk) {
+            const uint32_t G = std::min(chunk, g.groups - g0);
+            if (arena.live)
+                check(mac(c, lg, Q, G, n_in, Tsrc, g.d_pts + (size_t)g0 * n_in * (lg + 1) * c.n, accA, s));
+            std::vector<uint64_t*> a, b;
+            for (uint32_t q = 0; q < Q; q++)
+                for (uint32_t k = 0; k < G; k++) {
+                    a.push_back(accA + ((size_t)q * G + k) * cw(lg));
+                    b.push_back(accB + ((size_t)q * G + k) * cw(lg - 1));
+                }
+            rescale_batch(lg, a, b);
+            for (uint32_t t = 1; (1u << (t - 1)) < part; t++) rotate_batch(lg - 1, (int32_t)(1u << (t - 1)), b, b, &b);
+            if (!g.compress) {
+                // per-group outputs at level 0: copy into the result
+                if (arena.live)
+                    for (uint32_t q = 0; q < Q; q++)
+                        check(cudaMemcpyAsync(result + ((size_t)q * n_out + g0) * cw(0), accB + (size_t)q * G * cw(0),
+                                              (size_t)G * cw(0) * 8, cudaMemcpyDeviceToDevice, s));
+                continue;
+            }
+            const uint32_t lc = lg - 1;
+            std::vector<uint64_t*> mp(b.size(), g.d_cmask);
+            mulplain_batch(lc, b, mp, b);
+            // tree of right rotations: level bb pairs r and r + 2^bb (r = 0 mod 2^(bb+1)) inside each pack
+            for (uint32_t bb = 0; (1u << bb) < part; bb++) {
+                std::vector<uint64_t*> odd, even;
+                for (uint32_t q = 0; q < Q; q++)
+                    for (uint32_t k = 0; k < G; k += (2u << bb)) {
+                        const uint32_t gl = g0 + k;                 // global group of the even element
+                        const uint32_t r = gl % part;
+                        const uint32_t go = gl + (1u << bb);
+                        if (r + (1u << bb) >= part || go >= g.groups || k + (1u << bb) >= G) continue;
+                        even.push_back(accB + ((size_t)q * G + k) * cw(lc));
+                        odd.push_back(accB + ((size_t)q * G + k + (1u << bb)) * cw(lc));
+                    }
+                if (!odd.empty()) rotate_batch(lc, -(int32_t)(1u << bb), odd, even, &even);
+            }
+            std::vector<uint64_t*> heads, outs;
+            for (uint32_t q = 0; q < Q; q++)
+                for (uint32_t k = 0; k < G; k += part) {
+                    heads.push_back(accB + ((size_t)q * G + k) * cw(lc));
+                    outs.push_back(result + ((size_t)q * n_out + (g0 + k) / part) * cw(0));
+                }
+            rescale_batch(lc, heads, outs);
+        }
+    }
+};
+
+}  // namespace bm
+
+extern "C" {
+
+bm_status bm_match(bm_context* ctxh, const bm_eval_keys* evk, const bm_gallery* gal, bm_ciphertext* const* queries,
+                   uint32_t n_queries, void* stream, bm_result** out) {
+    if (!ctxh || !evk || !gal || !queries || !out || n_queries == 0) return fail(BM_E_ARG, "null argument");
+    Context& c = ctxh->c;
+    const Gallery& g = gal->g;
+    if (g.ctx != &c || evk->k.ctx != &c) return fail(BM_E_ARG, "handles belong to another context");
+    const uint32_t ncts = g.tiled ? 1 : g.n_in;
+    for (uint32_t i = 0; i < n_queries; i++) {
+        if (!queries[i]) return fail(BM_E_ARG, "null query");
+        if (queries[i]->ct.n_cts != ncts || queries[i]->ct.level != c.L)
+            return fail(BM_E_LEVEL, "query layout does not match the gallery's schedule");
+    }
+    Layout lo;
+    BM_TRY(make_layout(c, g.n_ids, g.dim, g.part, lo));
+    for (int32_t r : schedule_rotations(c, lo, g.part))
+        if (!evk->k.keys.count(galois_of(c, r))) return fail(BM_E_KEY_MISSING, "missing rotation key");
+    BM_CUDA_TRY(cudaSetDevice(c.device));
+    cudaStream_t s = (cudaStream_t)stream;
+
+    MatchRun run(c, g, evk->k, s);
+    run.Q = n_queries;
+    run.ncts = ncts;
+    run.n_out = lo.n_out;
+    const uint32_t lg = g.level;
+    // group chunk: whole packs, bounded by a temporary-memory budget
+    const size_t per_group = (size_t)n_queries * (ct_words(c, lg) + ct_words(c, lg - 1)) * 8;
+    const size_t budget = (size_t)8 << 30;
+    uint32_t chunk = (uint32_t)std::max<size_t>(1, budget / std::max<size_t>(per_group, 1));
+    if (g.compress) chunk = std::max(g.part, chunk / g.part * g.part);
+    run.chunk = std::min(chunk, g.groups);
+    if (g.compress && run.chunk < g.groups) run.chunk = std::max(g.part, run.chunk / g.part * g.part);
+
+    const size_t qwords = (size_t)n_queries * ncts * ct_words(c, c.L);
+    size_t scratch = 0;
+    for (uint32_t lvl = 0; lvl <= c.L; lvl++) {
+        scratch = std::max(scratch, ks_scratch_words(c, lvl, run.ksb));
+        if (lvl) scratch = std::max(scratch, rescale_scratch_words(c, lvl, run.ksb));
+    }
+    auto* rh = new bm_result();
+    Result& res = rh->r;
+    res.ctx = &c;
+    res.n_queries = n_queries;
+    res.n_out = lo.n_out;
+    res.n_ids = g.n_ids;
+    res.dim = g.dim;
+    res.part = g.part;
+    res.packed = g.compress;
+    std::vector<void*> temps;
+    auto talloc = [&](uint64_t*& p, size_t words) -> bool {
+        if (cudaMallocAsync((void**)&p, std::max<size_t>(words, 1) * 8, s) != cudaSuccess) return false;
+        temps.push_back(p);
+        return true;
+    };
+    auto cleanup = [&]() {
+        for (void* p : temps) cudaFreeAsync(p, s);
+        temps.clear();
+    };
+    bool ok = cudaMalloc(&res.d_data, (size_t)n_queries * lo.n_out * ct_words(c, 0) * 8) == cudaSuccess;
+    ok = ok && talloc(run.qin, qwords);
+    if (g.tiled) {
+        ok = ok && talloc(run.t0, (size_t)n_queries * g.n_in * ct_words(c, c.L));
+        ok = ok && talloc(run.T, (size_t)n_queries * g.n_in * ct_words(c, lg));
+    }
+    ok = ok && talloc(run.accA, (size_t)n_queries * run.chunk * ct_words(c, lg));
+    ok = ok && talloc(run.accB, (size_t)n_queries * run.chunk * ct_words(c, lg - 1));
+    ok = ok && talloc(run.scratch, scratch);
+    if (!ok) {
+        cleanup();
+        delete rh;
+        return fail(BM_E_OOM, "match workspace allocation failed");
+    }
+    run.result = res.d_data;
+    // a0: queries to the device (H2D unless staged) and into the NTT domain
+    for (uint32_t i = 0; i < n_queries; i++) {
+        const Ciphertext& ct = queries[i]->ct;
+        uint64_t* dst = run.qin + (size_t)i * ncts * ct_words(c, c.L);
+        if (ct.d_ntt) {
+            run.check(cudaMemcpyAsync(dst, ct.d_ntt, ct.host.size() * 8, cudaMemcpyDeviceToDevice, s));
+        } else {
+            run.check(cudaMemcpyAsync(dst, ct.host.data(), ct.host.size() * 8, cudaMemcpyHostToDevice, s));
+            run.check(ntt_forward(c, packed(c, dst, ncts * 2, c.L + 1), s));
+        }
+    }
+    run.schedule();   // dry pass: pointer arrays
+    if (!run.arena.host.empty()) {
+        uint64_t* arr = nullptr;
+        ok = talloc(arr, run.arena.host.size());
+        run.arena.dev = (uint64_t**)arr;
+        if (ok)
+            run.check(cudaMemcpyAsync(run.arena.dev, run.arena.host.data(), run.arena.host.size() * sizeof(void*),
+                                      cudaMemcpyHostToDevice, s));
+    }
+    run.arena.live = true;
+    run.schedule();
+    // a6: score ciphertexts back to coefficient form
+    run.check(ntt_inverse(c, limbs_of(res.d_data, n_queries * lo.n_out * 2, 1, c.n), s));
+    cleanup();
+    run.check(cudaStreamSynchronize(s));
+    if (!ok || run.err != cudaSuccess) {
+        delete rh;
+        return fail(ok ? BM_E_CUDA : BM_E_OOM, std::string("match: ") + cudaGetErrorString(run.err));
+    }
+    *out = rh;
+    return BM_OK;
+}
+
+bm_status bm_result_info(const bm_result* r, uint32_t* n_queries, uint32_t* n_out, uint32_t* packed_out) {
+    if (!r) return fail(BM_E_ARG, "null result");
+    if (n_queries) *n_queries = r->r.n_queries;
+    if (n_out) *n_out = r->r.n_out;
+    if (packed_out) *packed_out = r->r.packed;
+    return BM_OK;
+}
+
+bm_status bm_result_export(const bm_result* r, uint32_t query_index, uint64_t* out, size_t capacity) {
+    if (!r || !out) return fail(BM_E_ARG, "null argument");
+    const Result& res = r->r;
+    const Context& c = *res.ctx;
+    if (query_index >= res.n_queries) return fail(BM_E_ARG, "query index out of range");
+    const size_t words = (size_t)res.n_out * ct_words(c, 0);
+    if (capacity < words) return fail(BM_E_ARG, "capacity too small");
+    BM_CUDA_TRY(cudaSetDevice(c.device));
+    BM_CUDA_TRY(cudaMemcpy(out, res.d_data + (size_t)query_index * words, words * 8, cudaMemcpyDeviceToHost));
+    return BM_OK;
+}
+
+void bm_result_destroy(bm_result* r) { delete r; }
+
+bm_status bm_decrypt_scores(bm_context* ctxh, const bm_secret_key* sk, const bm_result* r, uint32_t query_index,
+                            double* scores, uint64_t n_ids, int64_t* rank1, double* rank1_score) {
+    if (!ctxh || !sk || !r || !scores) return fail(BM_E_ARG, "null argument");
+    Context& c = ctxh->c;
+    const Result& res = r->r;
+    if (query_index >= res.n_queries) return fail(BM_E_ARG, "query index out of range");
+    if (n_ids != res.n_ids) return fail(BM_E_ARG, "n_ids does not match the gallery");
+    BM_CUDA_TRY(cudaSetDevice(c.device));
+    cudaStream_t s = c.stream;
+    const size_t n = c.n, nout = res.n_out;
+    DevBuf t;
+    BM_CUDA_TRY(t.alloc(nout * 2 * n));
+    BM_CUDA_TRY(cudaMemcpyAsync(t.p, res.d_data + (size_t)query_index * nout * 2 * n, nout * 2 * n * 8,
+                                cudaMemcpyDeviceToDevice, s));
+    // m = c0 + c1 * s  (mod q_0)
+    LimbBatch c1 = limbs_of(t.p + n, (uint32_t)nout, 1, 2 * n);
+    BM_CUDA_TRY(ntt_forward(c, c1, s));
+    BM_CUDA_TRY(pointwise_mul(c, c1, limbs_of(sk->k.d_ntt, (uint32_t)nout, 1, 0), c1, s));
+    BM_CUDA_TRY(ntt_inverse(c, c1, s));
+    LimbBatch c0 = limbs_of(t.p, (uint32_t)nout, 1, 2 * n);
+    BM_CUDA_TRY(pointwise_addsub(c, c0, c1, c0, false, s));
+    std::vector<uint64_t> h(nout * 2 * n);
+    BM_CUDA_TRY(cudaMemcpyAsync(h.data(), t.p, h.size() * 8, cudaMemcpyDeviceToHost, s));
+    BM_CUDA_TRY(cudaStreamSynchronize(s));
+    const uint64_t q0 = c.primes[0];
+    const uint32_t part = res.part, G = c.slots / part;
+    std::vector<double> coef(n), slots(c.slots);
+    std::vector<std::vector<double>> dec(nout);
+    for (size_t o = 0; o < nout; o++) {
+        for (size_t i = 0; i < n; i++) {
+            const uint64_t v = h[o * 2 * n + i];
+            coef[i] = v > q0 / 2 ? -(double)(q0 - v) : (double)v;
+        }
+        decode_real(c, coef.data(), c.scale, slots.data());
+        dec[o] = slots;
+    }
+    int64_t best = -1;
+    double best_score = -INFINITY;
+    for (uint64_t id = 0; id < n_ids; id++) {
+        const uint64_t grp = id / G, u = id % G;
+        double v;
+        if (res.packed) v = dec[grp / part][u * part + grp % part];
+        else v = dec[grp][u * part];
+        scores[id] = v;
+        if (v > best_score) {
+            best_score = v;
+            best = (int64_t)id;
+        }
+    }
+    if (rank1) *rank1 = best;
+    if (rank1_score) *rank1_score = best_score;
+    return BM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// single operations
+// ---------------------------------------------------------------------------
+
+bm_status bm_poly_mul(bm_context* ctxh, const uint64_t* a, const uint64_t* b, uint64_t* out, uint32_t n_limbs) {
+    if (!ctxh || !a || !b || !out) return fail(BM_E_ARG, "null argument");
+    Context& c = ctxh->c;
+    if (n_limbs == 0 || n_limbs > c.nb) return fail(BM_E_ARG, "n_limbs out of range");
+    BM_CUDA_TRY(cudaSetDevice(c.device));
+    cudaStream_t s = c.stream;
+    const size_t w = (size_t)n_limbs * c.n;
+    DevBuf da, db;
+    BM_CUDA_TRY(da.alloc(w));
+    BM_CUDA_TRY(db.alloc(w));
+    BM_CUDA_TRY(cudaMemcpyAsync(da.p, a, w * 8, cudaMemcpyHostToDevice, s));
+    BM_CUDA_TRY(cudaMemcpyAsync(db.p, b, w * 8, cudaMemcpyHostToDevice, s));
+    BM_CUDA_TRY(ntt_forward(c, packed(c, da.p, 1, n_limbs), s));
+    BM_CUDA_TRY(ntt_forward(c, packed(c, db.p, 1, n_limbs), s));
+    BM_CUDA_TRY(to_montgomery(c, packed(c, db.p, 1, n_limbs), false, s));
+    BM_CUDA_TRY(pointwise_mul(c, packed(c, da.p, 1, n_limbs), packed(c, db.p, 1, n_limbs), packed(c, da.p, 1, n_limbs), s));
+    BM_CUDA_TRY(ntt_inverse(c, packed(c, da.p, 1, n_limbs), s));
+    BM_CUDA_TRY(cudaMemcpyAsync(out, da.p, w * 8, cudaMemcpyDeviceToHost, s));
+    BM_CUDA_TRY(cudaStreamSynchronize(s));
+    return BM_OK;
+}
+
+static bm_status ct_op(bm_context* ctxh, const bm_ciphertext* in, int op, const bm_eval_keys* evk, int32_t rot,
+                       bm_ciphertext** out) {
+    if (!ctxh || !in || !out) return fail(BM_E_ARG, "null argument");
+    Context& c = ctxh->c;
+    const Ciphertext& ct = in->ct;
+    const uint32_t l = ct.level, B = ct.n_cts;
+    const uint32_t lo = op == 1 ? l - 1 : l;
+    if (op == 1 && l == 0) return fail(BM_E_LEVEL, "cannot rescale at level 0");
+    const uint64_t* key = nullptr;
+    if (op == 0) {
+        auto it = evk->k.keys.find(galois_of(c, rot));
+        if (it == evk->k.keys.end()) return fail(BM_E_KEY_MISSING, "no key for this rotation");
+        key = it->second;
+    }
+    BM_CUDA_TRY(cudaSetDevice(c.device));
+    cudaStream_t s = c.stream;
+    DevBuf din, dout, scr, lists;
+    BM_CUDA_TRY(din.alloc(ct.host.size()));
+    BM_CUDA_TRY(dout.alloc((size_t)B * ct_words(c, lo)));
+    BM_CUDA_TRY(scr.alloc(std::max(ks_scratch_words(c, l, B), l ? rescale_scratch_words(c, l, B) : 0)));
+    std::vector<uint64_t*> h;
+    for (uint32_t b = 0; b < B; b++) h.push_back(din.p + (size_t)b * ct_words(c, l));
+    for (uint32_t b = 0; b < B; b++) h.push_back(dout.p + (size_t)b * ct_words(c, lo));
+    BM_CUDA_TRY(lists.alloc(h.size()));
+    BM_CUDA_TRY(cudaMemcpyAsync(lists.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice, s));
+    BM_CUDA_TRY(cudaMemcpyAsync(din.p, ct.host.data(), ct.host.size() * 8, cudaMemcpyHostToDevice, s));
+    BM_CUDA_TRY(ntt_forward(c, packed(c, din.p, B * 2, l + 1), s));
+    uint64_t* const* lin = (uint64_t* const*)lists.p;
+    uint64_t* const* lout = lin + B;
+    if (op == 0) BM_CUDA_TRY(ks_rotate(c, key, galois_of(c, rot), l, B, lin, lout, nullptr, scr.p, s));
+    else BM_CUDA_TRY(rescale(c, l, B, lin, lout, scr.p, s));
+    BM_CUDA_TRY(ntt_inverse(c, packed(c, dout.p, B * 2, lo + 1), s));
+    auto* ch = new bm_ciphertext();
+    ch->ct.ctx = &c;
+    ch->ct.n_cts = B;
+    ch->ct.level = lo;
+    ch->ct.host.resize((size_t)B * ct_words(c, lo));
+    cudaError_t e = cudaMemcpyAsync(ch->ct.host.data(), dout.p, ch->ct.host.size() * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        delete ch;
+        return fail(BM_E_CUDA, std::string("ct op: ") + cudaGetErrorString(e));
+    }
+    *out = ch;
+    return BM_OK;
+}
+
+bm_status bm_ct_rotate(bm_context* ctx, const bm_eval_keys* evk, const bm_ciphertext* in, int32_t rotation,
+                       bm_ciphertext** out) {
+    if (!evk) return fail(BM_E_ARG, "null keys");
+    return ct_op(ctx, in, 0, evk, rotation, out);
+}
+
+bm_status bm_ct_rescale(bm_context* ctx, const bm_ciphertext* in, bm_ciphertext** out) {
+    return ct_op(ctx, in, 1, nullptr, 0, out);
+}
+
+bm_status bm_ntt_forward(bm_context* ctxh, uint64_t* d_data, uint32_t n_polys, uint32_t n_limbs, void* stream) {
+    if (!ctxh || !d_data || n_limbs == 0 || n_limbs > ctxh->c.nb) return fail(BM_E_ARG, "bad argument");
+    BM_CUDA_TRY(ntt_forward(ctxh->c, packed(ctxh->c, d_data, n_polys, n_limbs), (cudaStream_t)stream));
+    return BM_OK;
+}
+
+bm_status bm_ntt_inverse(bm_context* ctxh, uint64_t* d_data, uint32_t n_polys, uint32_t n_limbs, void* stream) {
+    if (!ctxh || !d_data || n_limbs == 0 || n_limbs > ctxh->c.nb) return fail(BM_E_ARG, "bad argument");
+    BM_CUDA_TRY(ntt_inverse(ctxh->c, packed(ctxh->c, d_data, n_polys, n_limbs), (cudaStream_t)stream));
+    return BM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,182 @@
+// bm_internal.h -- internal types of the Blind-Match GPU library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "blindmatch.h"
+#include "bm_math.cuh"
+
+namespace bm {
+
+constexpr int MAXB = BM_MAX_Q + BM_MAX_P;   // primes in the full basis Q_L u P
+constexpr int MAXD = 4;                     // key-switching digits
+constexpr int MAXDS = 3;                    // limbs per digit
+
+// Per-prime constants and twiddle tables, passed to kernels by value.
+struct DevTables {
+    uint64_t q[MAXB];
+    uint64_t qneg[MAXB];        // -q^{-1} mod 2^64 (Montgomery)
+    uint64_t rsh[MAXB];         // floor(2^64 / q): reduces any 64-bit word with one mulhi
+    uint64_t r2[MAXB];          // 2^128 mod q: mont(x, r2) = x * 2^64 mod q
+    uint64_t ninv[MAXB], ninv_sh[MAXB];
+    const ulonglong2* tw[MAXB];     // forward: (psi^brv(k), Shoup companion), k < N
+    const ulonglong2* itw[MAXB];    // inverse: (psi^-brv(k), companion)
+};
+
+// A set of limbs: n_polys polynomials at base + poly*poly_stride (words); limb k of
+// each (k < nl) starts at (limb_off + k) * N and uses prime pi[k].
+struct LimbBatch {
+    uint64_t* base;
+    uint32_t n_polys;
+    uint64_t poly_stride;
+    uint32_t limb_off;
+    uint32_t nl;
+    uint8_t pi[MAXB];
+};
+
+struct Context {
+    bm_params params{};
+    int device = 0;
+    uint32_t log_n = 0, n = 0, slots = 0, L = 0, alpha = 0, nb = 0;
+    std::vector<uint64_t> primes;             // q_0..q_L, p_0..p_(alpha-1)
+    std::vector<uint64_t> psi;
+    std::vector<std::vector<uint32_t>> digits;   // Q-limb indices of each digit
+    DevTables tab{};
+    void* d_twiddles = nullptr;
+    cudaStream_t stream = nullptr;            // for client-side helpers (keygen, encrypt)
+    uint64_t P_mod[MAXB]{};                   // P mod each prime
+    double scale = 0;
+};
+
+struct SecretKey {
+    Context* ctx;
+    std::vector<int64_t> coeffs;             // ternary, length N
+    uint64_t* d_ntt = nullptr;                // NTT(s) on every prime of the full basis, Montgomery form
+};
+
+struct PublicKey {
+    Context* ctx;
+    uint64_t* d_ntt = nullptr;                // [2][L+1][N] NTT + Montgomery
+};
+
+struct EvalKeys {
+    Context* ctx;
+    uint32_t dim = 0, part = 0;
+    std::map<uint64_t, uint64_t*> keys;       // galois element -> [dnum][2][nb][N] NTT + Montgomery
+    ~EvalKeys();
+};
+
+struct Gallery {
+    Context* ctx;
+    uint64_t n_ids = 0;
+    uint32_t dim = 0, part = 0, n_in = 0, groups = 0, level = 0;  // level of the gallery pts
+    bool tiled = true;                        // queries arrive tiled (Algorithm 1 on the server)
+    bool compress = true;                     // outputs are masked and packed
+    uint64_t* d_pts = nullptr;                // [groups][n_in][level+1][N] NTT + Montgomery
+    uint64_t* d_masks = nullptr;              // [n_in][L+1][N] Algorithm-1 masks (tiled only)
+    uint64_t* d_cmask = nullptr;              // [level][N] compression mask at level-1
+    ~Gallery();
+};
+
+struct Ciphertext {
+    Context* ctx;
+    uint32_t n_cts = 1, level = 0;
+    std::vector<uint64_t> host;               // [n_cts][2][level+1][N] coefficient form
+    uint64_t* d_ntt = nullptr;                // optional staged device copy, NTT form
+    ~Ciphertext();
+};
+
+struct Result {
+    Context* ctx;
+    uint32_t n_queries = 0, n_out = 0;
+    uint64_t n_ids = 0;
+    uint32_t dim = 0, part = 0;
+    bool packed = true;
+    uint64_t* d_data = nullptr;               // [n_queries][n_out][2][N] coefficient form, level 0
+    ~Result();
+};
+
+// ---- error reporting ----
+void set_error(const std::string& msg);
+#define BM_CUDA_TRY(expr)                                                              \
+    do {                                                                               \
+        cudaError_t e_ = (expr);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            ::bm::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));       \
+            return BM_E_CUDA;                                                          \
+        }                                                                              \
+    } while (0)
+
+// ---- host-side number theory, randomness, encoding (host.cpp) ----
+bool is_prime_u64(uint64_t n);
+bool gen_primes(uint32_t log_n, const std::vector<uint32_t>& bits, std::vector<uint64_t>& out);
+uint64_t find_psi(uint64_t q, uint32_t log_n);
+void philox4x64_10(uint64_t k0, uint64_t k1, const uint64_t ctr[4], uint64_t out[4]);
+enum : uint64_t {
+    TAG_SECRET = 1, TAG_PK_A = 2, TAG_PK_E = 3, TAG_RK_A = 4, TAG_RK_E = 5,
+    TAG_ENC_V = 6, TAG_ENC_E0 = 7, TAG_ENC_E1 = 8
+};
+void sample_uniform(uint64_t seed, uint64_t tag, uint64_t obj, uint64_t limb, uint64_t q,
+                    uint64_t* out, uint32_t n);
+void sample_gauss(uint64_t seed, uint64_t tag, uint64_t obj, double sigma, int64_t* out, uint32_t n);
+void sample_zo(uint64_t seed, uint64_t tag, uint64_t obj, int64_t* out, uint32_t n);
+void sample_secret(uint64_t seed, uint32_t hw, uint32_t log_n, int64_t* out);
+void cdt_table(double sigma, uint32_t kmax, uint64_t* table);
+// round(scale * tau^{-1}(z)) for real slot values z[slots]; coefficients out[N]
+void encode_real(const Context& ctx, const double* z, double scale, int64_t* out);
+// slots of integer coefficients / scale (real parts)
+void decode_real(const Context& ctx, const double* coeffs, double scale, double* z);
+
+// ---- kernel launchers (kernels.cu) ----
+cudaError_t ntt_forward(const Context& c, const LimbBatch& b, cudaStream_t s);
+cudaError_t ntt_inverse(const Context& c, const LimbBatch& b, cudaStream_t s);
+// x -> x * 2^64 mod q (Montgomery form) / back, on a limb batch
+cudaError_t to_montgomery(const Context& c, const LimbBatch& b, bool inverse, cudaStream_t s);
+// out[i] = signed v[i] mod q on each limb (v: device int64[N])
+cudaError_t lift_signed(const Context& c, const int64_t* d_v, const LimbBatch& out, cudaStream_t s);
+
+// Rotation (automorphism + hybrid key switch) of B ciphertexts at `level`, NTT form:
+// out[b] = Rot(in[b]) (+ add[b] if add != nullptr).  in/out/add are device arrays of
+// B pointers to [2][level+1][N] ciphertexts; out may alias add, not in.
+cudaError_t ks_rotate(const Context& c, const uint64_t* key, uint64_t galois, uint32_t level,
+                      uint32_t B, uint64_t* const* d_in, uint64_t* const* d_out,
+                      uint64_t* const* d_add, uint64_t* scratch, cudaStream_t s);
+size_t ks_scratch_words(const Context& c, uint32_t level, uint32_t B);
+// out[b] = Res(in[b]); in at level, out at level-1 (no aliasing)
+cudaError_t rescale(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,
+                    uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s);
+size_t rescale_scratch_words(const Context& c, uint32_t level, uint32_t B);
+// out[b] = in[b] * pt[b] (pt Montgomery, [level+1][N]); out may alias in
+cudaError_t mul_plain(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,
+                      const uint64_t* const* d_pt, uint64_t* const* d_out, cudaStream_t s);
+// acc[q][g] = sum_i T[q][i] * P[g][i]  (T: [Q][n_in][2][level+1][N], P: [G][n_in][level+1][N])
+cudaError_t mac(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32_t n_in,
+                const uint64_t* T, const uint64_t* P, uint64_t* acc, cudaStream_t s);
+// plain products a*b on each limb (NTT form, b Montgomery)
+cudaError_t pointwise_mul(const Context& c, const LimbBatch& a, const LimbBatch& b,
+                          const LimbBatch& out, cudaStream_t s);
+// out = a + b, a - b on each limb
+cudaError_t pointwise_addsub(const Context& c, const LimbBatch& a, const LimbBatch& b,
+                             const LimbBatch& out, bool sub, cudaStream_t s);
+// NTT-domain automorphism: out[i] = in[perm_k(i)] on each limb
+cudaError_t permute_ntt(const Context& c, const LimbBatch& in, const LimbBatch& out,
+                        uint64_t galois, cudaStream_t s);
+// out = in * c (per-limb constants c[k], plain form) on each limb
+cudaError_t scalar_mul(const Context& c, const LimbBatch& in, const uint64_t* cst,
+                       const LimbBatch& out, cudaStream_t s);
+
+}  // namespace bm
+
+// opaque handle types of the C-ABI
+struct bm_context { bm::Context c; };
+struct bm_secret_key { bm::SecretKey k; };
+struct bm_public_key { bm::PublicKey k; };
+struct bm_eval_keys { bm::EvalKeys k; };
+struct bm_gallery { bm::Gallery g; };
+struct bm_ciphertext { bm::Ciphertext ct; };
+struct bm_result { bm::Result r; };

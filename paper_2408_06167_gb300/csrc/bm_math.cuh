@@ -1,0 +1,89 @@
+// bm_math.cuh -- 64-bit modular arithmetic shared by the host and device code
+// of the Blind-Match GPU library (RNS-CKKS, Sec. 2 of the paper).
+//
+// Residues live in 64-bit words, moduli are primes below 2^61.
+//  * Shoup multiplication by a constant w with companion w' = floor(w*2^64/q)
+//    (V. Shoup, NTL): one high and two low 64-bit products, result in [0, 2q)
+//    for any x < 2^64.
+//  * Montgomery multiplication with R = 2^64 (P. Montgomery, 1985): used for
+//    variable x variable products where one operand is stored pre-multiplied
+//    by R (rotation keys, plaintexts), result in [0, 2q) when a*b < q*2^64.
+#pragma once
+#include <cstdint>
+
+#if defined(__CUDACC__)
+#define BM_HD __host__ __device__ __forceinline__
+#else
+#define BM_HD inline
+#endif
+
+namespace bm {
+
+BM_HD uint64_t mulhi64(uint64_t a, uint64_t b) {
+#if defined(__CUDA_ARCH__)
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+// x * w mod q, lazily in [0, 2q); w' = floor(w * 2^64 / q).
+BM_HD uint64_t shoup_lazy(uint64_t x, uint64_t w, uint64_t wsh, uint64_t q) {
+    return x * w - mulhi64(x, wsh) * q;
+}
+BM_HD uint64_t shoup(uint64_t x, uint64_t w, uint64_t wsh, uint64_t q) {
+    uint64_t r = shoup_lazy(x, w, wsh, q);
+    return r >= q ? r - q : r;
+}
+
+// a * b * 2^-64 mod q, lazily in [0, 2q); qneg = -q^{-1} mod 2^64.
+BM_HD uint64_t mont_lazy(uint64_t a, uint64_t b, uint64_t q, uint64_t qneg) {
+    uint64_t lo = a * b;
+    uint64_t hi = mulhi64(a, b);
+    uint64_t m = lo * qneg;
+    return hi + mulhi64(m, q) + (lo != 0);
+}
+BM_HD uint64_t mont(uint64_t a, uint64_t b, uint64_t q, uint64_t qneg) {
+    uint64_t r = mont_lazy(a, b, q, qneg);
+    return r >= q ? r - q : r;
+}
+
+BM_HD uint64_t reduce2(uint64_t x, uint64_t q) { return x >= q ? x - q : x; }
+BM_HD uint64_t addm(uint64_t a, uint64_t b, uint64_t q) { return reduce2(a + b, q); }
+BM_HD uint64_t subm(uint64_t a, uint64_t b, uint64_t q) { return a >= b ? a - b : a + q - b; }
+BM_HD uint64_t negm(uint64_t a, uint64_t q) { return a ? q - a : 0; }
+
+// ---- host-only helpers (128-bit integer arithmetic) ----
+inline uint64_t h_mulmod(uint64_t a, uint64_t b, uint64_t q) {
+    return (uint64_t)(((unsigned __int128)a * b) % q);
+}
+inline uint64_t h_powmod(uint64_t a, uint64_t e, uint64_t q) {
+    uint64_t r = 1 % q;
+    a %= q;
+    for (; e; e >>= 1) {
+        if (e & 1) r = h_mulmod(r, a, q);
+        a = h_mulmod(a, a, q);
+    }
+    return r;
+}
+inline uint64_t h_invmod(uint64_t a, uint64_t q) { return h_powmod(a, q - 2, q); }
+inline uint64_t h_shoup_companion(uint64_t w, uint64_t q) {
+    return (uint64_t)(((unsigned __int128)w << 64) / q);
+}
+// -q^{-1} mod 2^64 by Newton iteration (q odd).
+inline uint64_t h_mont_qneg(uint64_t q) {
+    uint64_t inv = q;                 // correct to 3 bits for odd q
+    for (int i = 0; i < 6; i++) inv *= 2 - q * inv;
+    return (uint64_t)0 - inv;
+}
+// a^{-1} mod m for odd a and m a power of two (m <= 2^63)
+inline uint64_t h_invmod_pow2(uint64_t a, uint64_t m) {
+    uint64_t inv = a;
+    for (int i = 0; i < 6; i++) inv *= 2 - a * inv;
+    return inv & (m - 1);
+}
+// 2^64 mod q, 2^128 mod q
+inline uint64_t h_r1(uint64_t q) { return (uint64_t)(((unsigned __int128)1 << 64) % q); }
+inline uint64_t h_r2(uint64_t q) { return h_mulmod(h_r1(q), h_r1(q), q); }
+
+}  // namespace bm

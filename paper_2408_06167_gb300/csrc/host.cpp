@@ -1,0 +1,238 @@
+// host.cpp -- client-side number theory, randomness and encoding of the
+// Blind-Match library (host code; the match path itself runs in kernels.cu).
+//
+//  * NTT-friendly primes: the largest primes below 2^bits with q = 1 (mod 2N),
+//    by deterministic Miller-Rabin; psi of order 2N from the smallest base g
+//    whose power g^((q-1)/2N) is a root of X^N + 1.
+//  * Philox4x64-10 (Salmon et al., "Parallel random numbers: as easy as 1, 2, 3",
+//    SC'11) keyed by (seed, tag), counter (object, limb, coefficient, 0), and the
+//    samplers on top of it: uniform residues (128 bits reduced mod q), discrete
+//    Gaussian by cumulative table on 63 bits with a sign bit, ZO(1/2) ternary,
+//    ternary of fixed Hamming weight by rejection of occupied positions.
+//  * CKKS canonical embedding (Sec. 2: batches of real values in the slots):
+//    slot j is the evaluation at zeta^(5^j), zeta = exp(i*pi/N).  Encoding maps
+//    the slots to the N odd powers of zeta and applies one length-N inverse DFT,
+//    computed by an iterative radix-2 FFT.
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "bm_internal.h"
+
+namespace bm {
+
+using u128 = unsigned __int128;
+
+static bool mr_witness(uint64_t n, uint64_t a, uint64_t d, int r) {
+    uint64_t x = h_powmod(a, d, n);
+    if (x == 1 || x == n - 1) return false;
+    for (int i = 1; i < r; i++) {
+        x = h_mulmod(x, x, n);
+        if (x == n - 1) return false;
+    }
+    return true;   // a proves n composite
+}
+
+bool is_prime_u64(uint64_t n) {
+    if (n < 2) return false;
+    static const uint64_t small[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    for (uint64_t p : small) {
+        if (n == p) return true;
+        if (n % p == 0) return false;
+    }
+    uint64_t d = n - 1;
+    int r = 0;
+    while (!(d & 1)) { d >>= 1; r++; }
+    for (uint64_t a : small)
+        if (mr_witness(n, a, d, r)) return false;
+    return true;
+}
+
+bool gen_primes(uint32_t log_n, const std::vector<uint32_t>& bits, std::vector<uint64_t>& out) {
+    const uint64_t step = 2ull << log_n;
+    out.clear();
+    for (uint32_t b : bits) {
+        uint64_t top = (1ull << b) - 1;
+        uint64_t cand = top - (top % step) + 1;   // largest value = 1 mod 2N not above 2^b - 1 ...
+        if (cand > top) cand -= step;             // ... kept strictly below 2^b
+        bool found = false;
+        for (; cand > step; cand -= step) {
+            bool used = false;
+            for (uint64_t u : out) used |= (u == cand);
+            if (!used && is_prime_u64(cand)) { found = true; break; }
+        }
+        if (!found) return false;
+        out.push_back(cand);
+    }
+    return true;
+}
+
+uint64_t find_psi(uint64_t q, uint32_t log_n) {
+    const uint64_t n = 1ull << log_n;
+    const uint64_t e = (q - 1) / (2 * n);
+    for (uint64_t g = 2; g < 1000000; g++) {
+        uint64_t w = h_powmod(g, e, q);
+        if (h_powmod(w, n, q) == q - 1) return w;
+    }
+    return 0;
+}
+
+void philox4x64_10(uint64_t k0, uint64_t k1, const uint64_t ctr[4], uint64_t out[4]) {
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    for (int round = 0; round < 10; ++round) {
+        u128 m0 = (u128)0xD2E7470EE14C6C93ull * x0;
+        u128 m1 = (u128)0xCA5A826395121157ull * x2;
+        uint64_t y0 = (uint64_t)(m1 >> 64) ^ x1 ^ k0;
+        uint64_t y2 = (uint64_t)(m0 >> 64) ^ x3 ^ k1;
+        x1 = (uint64_t)m1;
+        x3 = (uint64_t)m0;
+        x0 = y0;
+        x2 = y2;
+        k0 += 0x9E3779B97F4A7C15ull;   // key schedule (Weyl sequence)
+        k1 += 0xBB67AE8584CAA73Bull;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static inline void draw(uint64_t seed, uint64_t tag, uint64_t a, uint64_t b, uint64_t c, uint64_t w[4]) {
+    const uint64_t ctr[4] = {a, b, c, 0};
+    philox4x64_10(seed, tag, ctr, w);
+}
+
+void sample_uniform(uint64_t seed, uint64_t tag, uint64_t obj, uint64_t limb, uint64_t q,
+                    uint64_t* out, uint32_t n) {
+    uint64_t w[4];
+    for (uint32_t i = 0; i < n; i++) {
+        draw(seed, tag, obj, limb, i, w);
+        out[i] = (uint64_t)((((u128)w[1]) << 64 | w[0]) % q);
+    }
+}
+
+void cdt_table(double sigma, uint32_t kmax, uint64_t* table) {
+    std::vector<double> weight(kmax + 1);
+    double total = 0;
+    for (uint32_t k = 0; k <= kmax; k++) {
+        weight[k] = (k ? 2.0 : 1.0) * std::exp(-double(k) * double(k) / (2.0 * sigma * sigma));
+        total += weight[k];
+    }
+    double run = 0;
+    for (uint32_t k = 0; k <= kmax; k++) {
+        run += weight[k];
+        table[k] = (k == kmax) ? (1ull << 63) : (uint64_t)(run / total * 9223372036854775808.0);
+    }
+}
+
+void sample_gauss(uint64_t seed, uint64_t tag, uint64_t obj, double sigma, int64_t* out, uint32_t n) {
+    const uint32_t kmax = 19;
+    uint64_t table[kmax + 1];
+    cdt_table(sigma, kmax, table);
+    uint64_t w[4];
+    for (uint32_t i = 0; i < n; i++) {
+        draw(seed, tag, obj, 0, i, w);
+        const uint64_t u = w[0] >> 1;
+        int64_t mag = 0;
+        while (u >= table[mag]) mag++;
+        out[i] = (w[0] & 1) ? -mag : mag;
+    }
+}
+
+void sample_zo(uint64_t seed, uint64_t tag, uint64_t obj, int64_t* out, uint32_t n) {
+    static const int64_t lut[4] = {0, 0, 1, -1};
+    uint64_t w[4];
+    for (uint32_t i = 0; i < n; i++) {
+        draw(seed, tag, obj, 0, i, w);
+        out[i] = lut[w[0] & 3];
+    }
+}
+
+void sample_secret(uint64_t seed, uint32_t hw, uint32_t log_n, int64_t* out) {
+    const uint32_t n = 1u << log_n;
+    if (hw == 0) {
+        sample_zo(seed, TAG_SECRET, 0, out, n);
+        return;
+    }
+    std::memset(out, 0, sizeof(int64_t) * n);
+    uint64_t w[4];
+    uint32_t placed = 0;
+    for (uint64_t k = 0; placed < hw; k++) {
+        draw(seed, TAG_SECRET, 0, 0, k, w);
+        const uint64_t pos = w[0] >> (64 - log_n);
+        if (out[pos] != 0) continue;
+        out[pos] = (w[1] & 1) ? -1 : 1;
+        placed++;
+    }
+}
+
+// ---- FFT-based encoder ----
+
+using cplx = std::complex<double>;
+
+// In-place iterative radix-2 DFT: X[k] = sum_t x[t] exp(sign * 2 pi i t k / n).
+static void fft(std::vector<cplx>& a, int sign) {
+    const size_t n = a.size();
+    for (size_t i = 1, j = 0; i < n; i++) {
+        size_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (size_t len = 2; len <= n; len <<= 1) {
+        const double ang = sign * 2.0 * M_PI / double(len);
+        std::vector<cplx> w(len / 2);
+        for (size_t k = 0; k < len / 2; k++) w[k] = cplx(std::cos(ang * k), std::sin(ang * k));
+        for (size_t i = 0; i < n; i += len)
+            for (size_t k = 0; k < len / 2; k++) {
+                cplx u = a[i + k], v = a[i + k + len / 2] * w[k];
+                a[i + k] = u + v;
+                a[i + k + len / 2] = u - v;
+            }
+    }
+}
+
+// index t of the odd exponent 2t+1 = 5^j mod 2N (and of its conjugate -5^j)
+static void slot_positions(const Context& ctx, std::vector<uint32_t>& pos, std::vector<uint32_t>& cpos) {
+    const uint64_t two_n = 2ull * ctx.n;
+    pos.resize(ctx.slots);
+    cpos.resize(ctx.slots);
+    uint64_t e = 1;
+    for (uint32_t j = 0; j < ctx.slots; j++) {
+        pos[j] = (uint32_t)((e - 1) / 2);
+        cpos[j] = (uint32_t)((two_n - e - 1) / 2);
+        e = (e * 5) % two_n;
+    }
+}
+
+void encode_real(const Context& ctx, const double* z, double scale, int64_t* out) {
+    const uint32_t n = ctx.n;
+    std::vector<uint32_t> pos, cpos;
+    slot_positions(ctx, pos, cpos);
+    // values at zeta^(2t+1): m(zeta^(2t+1)) = sum_k (m_k zeta^k) w^(tk), w = exp(2 pi i / N)
+    std::vector<cplx> v(n);
+    for (uint32_t j = 0; j < ctx.slots; j++) {
+        v[pos[j]] = cplx(z[j], 0.0);
+        v[cpos[j]] = cplx(z[j], 0.0);   // conjugate of a real value
+    }
+    fft(v, -1);   // sum_t v_t w^(-tk) = N * m_k zeta^k
+    for (uint32_t k = 0; k < n; k++) {
+        const double ang = -M_PI * double(k) / double(n);
+        const double mk = (v[k] * cplx(std::cos(ang), std::sin(ang))).real() / double(n);
+        const double x = mk * scale;
+        out[k] = (int64_t)(x >= 0 ? std::floor(x + 0.5) : -std::floor(-x + 0.5));
+    }
+}
+
+void decode_real(const Context& ctx, const double* coeffs, double scale, double* z) {
+    const uint32_t n = ctx.n;
+    std::vector<cplx> w(n);
+    for (uint32_t k = 0; k < n; k++) {
+        const double ang = M_PI * double(k) / double(n);
+        w[k] = cplx(std::cos(ang), std::sin(ang)) * (coeffs[k] / scale);
+    }
+    fft(w, +1);   // value at zeta^(2t+1)
+    std::vector<uint32_t> pos, cpos;
+    slot_positions(ctx, pos, cpos);
+    for (uint32_t j = 0; j < ctx.slots; j++) z[j] = w[pos[j]].real();
+}
+
+}  // namespace bm

@@ -1,0 +1,698 @@
+// kernels.cu -- GPU kernels of the Blind-Match match path (sm_103a).
+//
+// RNS-CKKS operations of Sec. 2 (Add, Mul(P), Rot, Res) on limb-major
+// uint64 buffers ([ct][poly][limb][N]), in the NTT domain:
+//  * negacyclic NTT (Cooley-Tukey, bit-reversed psi twiddles, natural -> bit-
+//    reversed order; Gentleman-Sande inverse) split in two passes over an
+//    N1 x N2 view: a column pass for the first log N1 stages and a row pass
+//    for the rest, each staged through shared memory;
+//  * rotation = Galois automorphism + hybrid key switching: the automorphism is
+//    fused into the ModUp gather (coefficient domain) and into the final
+//    combine (NTT-domain permutation of c0); ModUp's fast base conversion, the
+//    inner product with the rotation key (Montgomery products) and ModDown's
+//    conversion and scaling by P^{-1} are one kernel each;
+//  * rescale by the last prime with a centred lift (rounding division);
+//  * ct x pt products and the HE-C^3 multiply-accumulate over the parts.
+#include <cuda_runtime.h>
+
+#include "bm_internal.h"
+
+namespace bm {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ uint32_t brev_bits(uint32_t x, uint32_t bits) {
+    return __brev(x) >> (32 - bits);
+}
+
+// NTT-domain index of the automorphism X -> X^k: out[i] = in[src(i)].
+__device__ __forceinline__ uint32_t ntt_perm_src(uint32_t i, uint32_t log_n, uint64_t galois) {
+    const uint32_t mask2n = (2u << log_n) - 1;
+    const uint32_t r = brev_bits(i, log_n);
+    const uint32_t e = ((2u * r + 1u) * (uint32_t)galois) & mask2n;
+    return brev_bits((e - 1u) >> 1, log_n);
+}
+
+__device__ __forceinline__ uint64_t* limb_ptr(const LimbBatch& b, uint32_t limb, uint32_t n) {
+    const uint32_t poly = limb / b.nl, k = limb % b.nl;
+    return b.base + (size_t)poly * b.poly_stride + (size_t)(b.limb_off + k) * n;
+}
+
+// ---------------------------------------------------------------------------
+// NTT passes.  View a limb as N1 x N2 (index r*N2 + c).  Stages 0..LA-1 pair
+// rows (same column); stages LA..log N-1 pair columns inside a row.
+// ---------------------------------------------------------------------------
+
+template <int LA, int LB, int COLS, bool INV>
+__global__ void __launch_bounds__(kThreads) k_ntt_cols(LimbBatch lb, DevTables tab) {
+    constexpr int N1 = 1 << LA, N2 = 1 << LB, TILE = N1 * COLS;
+    __shared__ uint64_t sm[TILE];
+    const int pi = lb.pi[blockIdx.x % lb.nl];
+    uint64_t* a = limb_ptr(lb, blockIdx.x, N1 * N2);
+    const uint64_t q = tab.q[pi];
+    const int c0 = blockIdx.y * COLS;
+    for (int e = threadIdx.x; e < TILE; e += kThreads) sm[e] = a[(e / COLS) * N2 + c0 + (e % COLS)];
+    __syncthreads();
+    if (!INV) {
+        const ulonglong2* tw = tab.tw[pi];
+        for (int s = 0; s < LA; s++) {
+            const int half = N1 >> (s + 1);
+            for (int b = threadIdx.x; b < TILE / 2; b += kThreads) {
+                const int c = b % COLS, bi = b / COLS, i = bi / half, j = bi % half;
+                const int r0 = i * 2 * half + j, r1 = r0 + half;
+                const ulonglong2 w = tw[(1 << s) + i];
+                const uint64_t u = sm[r0 * COLS + c];
+                const uint64_t v = shoup(sm[r1 * COLS + c], w.x, w.y, q);
+                sm[r0 * COLS + c] = addm(u, v, q);
+                sm[r1 * COLS + c] = subm(u, v, q);
+            }
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < TILE; e += kThreads) a[(e / COLS) * N2 + c0 + (e % COLS)] = sm[e];
+    } else {
+        const ulonglong2* tw = tab.itw[pi];
+        for (int s = LA - 1; s >= 0; s--) {
+            const int half = N1 >> (s + 1);
+            for (int b = threadIdx.x; b < TILE / 2; b += kThreads) {
+                const int c = b % COLS, bi = b / COLS, i = bi / half, j = bi % half;
+                const int r0 = i * 2 * half + j, r1 = r0 + half;
+                const ulonglong2 w = tw[(1 << s) + i];
+                const uint64_t u = sm[r0 * COLS + c], v = sm[r1 * COLS + c];
+                sm[r0 * COLS + c] = addm(u, v, q);
+                sm[r1 * COLS + c] = shoup(subm(u, v, q), w.x, w.y, q);
+            }
+            __syncthreads();
+        }
+        const uint64_t ni = tab.ninv[pi], nis = tab.ninv_sh[pi];
+        for (int e = threadIdx.x; e < TILE; e += kThreads)
+            a[(e / COLS) * N2 + c0 + (e % COLS)] = shoup(sm[e], ni, nis, q);
+    }
+}
+
+template <int LA, int LB, int ROWS, bool INV>
+__global__ void __launch_bounds__(kThreads) k_ntt_rows(LimbBatch lb, DevTables tab) {
+    constexpr int N2 = 1 << LB, TILE = ROWS * N2;
+    __shared__ uint64_t sm[TILE];
+    const int pi = lb.pi[blockIdx.x % lb.nl];
+    uint64_t* a = limb_ptr(lb, blockIdx.x, (1 << LA) * N2) + (size_t)blockIdx.y * TILE;
+    const uint64_t q = tab.q[pi];
+    const int rbase = blockIdx.y * ROWS;
+    for (int e = threadIdx.x; e < TILE; e += kThreads) sm[e] = a[e];
+    __syncthreads();
+    const ulonglong2* tw = INV ? tab.itw[pi] : tab.tw[pi];
+    if (!INV) {
+        for (int sp = 0; sp < LB; sp++) {
+            const int half = N2 >> (sp + 1);
+            for (int b = threadIdx.x; b < TILE / 2; b += kThreads) {
+                const int rr = b / (N2 / 2), bi = b % (N2 / 2), il = bi / half, j = bi % half;
+                const int c0 = il * 2 * half + j, c1 = c0 + half;
+                const ulonglong2 w = tw[(1 << (LA + sp)) + (rbase + rr) * (1 << sp) + il];
+                const uint64_t u = sm[rr * N2 + c0];
+                const uint64_t v = shoup(sm[rr * N2 + c1], w.x, w.y, q);
+                sm[rr * N2 + c0] = addm(u, v, q);
+                sm[rr * N2 + c1] = subm(u, v, q);
+            }
+            __syncthreads();
+        }
+    } else {
+        for (int sp = LB - 1; sp >= 0; sp--) {
+            const int half = N2 >> (sp + 1);
+            for (int b = threadIdx.x; b < TILE / 2; b += kThreads) {
+                const int rr = b / (N2 / 2), bi = b % (N2 / 2), il = bi / half, j = bi % half;
+                const int c0 = il * 2 * half + j, c1 = c0 + half;
+                const ulonglong2 w = tw[(1 << (LA + sp)) + (rbase + rr) * (1 << sp) + il];
+                const uint64_t u = sm[rr * N2 + c0], v = sm[rr * N2 + c1];
+                sm[rr * N2 + c0] = addm(u, v, q);
+                sm[rr * N2 + c1] = shoup(subm(u, v, q), w.x, w.y, q);
+            }
+            __syncthreads();
+        }
+    }
+    for (int e = threadIdx.x; e < TILE; e += kThreads) a[e] = sm[e];
+}
+
+template <int LA, int LB>
+cudaError_t ntt_launch(const LimbBatch& b, const DevTables& tab, bool inv, cudaStream_t s) {
+    constexpr int COLS = 8, ROWS = 8;
+    const uint32_t limbs = b.n_polys * b.nl;
+    if (limbs == 0) return cudaSuccess;
+    const dim3 gc(limbs, (1 << LB) / COLS), gr(limbs, (1 << LA) / ROWS);
+    if (!inv) {
+        k_ntt_cols<LA, LB, COLS, false><<<gc, kThreads, 0, s>>>(b, tab);
+        k_ntt_rows<LA, LB, ROWS, false><<<gr, kThreads, 0, s>>>(b, tab);
+    } else {
+        k_ntt_rows<LA, LB, ROWS, true><<<gr, kThreads, 0, s>>>(b, tab);
+        k_ntt_cols<LA, LB, COLS, true><<<gc, kThreads, 0, s>>>(b, tab);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t ntt_dispatch(const Context& c, const LimbBatch& b, bool inv, cudaStream_t s) {
+    switch (c.log_n) {
+        case 12: return ntt_launch<6, 6>(b, c.tab, inv, s);
+        case 13: return ntt_launch<7, 6>(b, c.tab, inv, s);
+        case 14: return ntt_launch<7, 7>(b, c.tab, inv, s);
+        case 15: return ntt_launch<8, 7>(b, c.tab, inv, s);
+        case 16: return ntt_launch<8, 8>(b, c.tab, inv, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// elementwise limb kernels
+// ---------------------------------------------------------------------------
+
+// x * 2^-64 mod q (leave Montgomery form)
+__global__ void k_from_mont(LimbBatch lb, DevTables tab, uint32_t n) {
+    const uint32_t limb = blockIdx.y;
+    const int pi = lb.pi[limb % lb.nl];
+    uint64_t* a = limb_ptr(lb, limb, n);
+    const uint64_t q = tab.q[pi], qn = tab.qneg[pi];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        a[i] = mont(a[i], 1, q, qn);
+}
+
+// x * 2^64 mod q (enter Montgomery form): mont(x, 2^128 mod q)
+__global__ void k_to_mont(LimbBatch lb, DevTables tab, uint32_t n) {
+    const uint32_t limb = blockIdx.y;
+    const int pi = lb.pi[limb % lb.nl];
+    uint64_t* a = limb_ptr(lb, limb, n);
+    const uint64_t q = tab.q[pi], qn = tab.qneg[pi], f = tab.r2[pi];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        a[i] = mont(a[i], f, q, qn);
+}
+
+__global__ void k_lift_signed(const int64_t* v, LimbBatch lb, DevTables tab, uint32_t n) {
+    const uint32_t limb = blockIdx.y;
+    const int pi = lb.pi[limb % lb.nl];
+    uint64_t* a = limb_ptr(lb, limb, n);
+    const uint64_t q = tab.q[pi];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int64_t x = v[i];
+        const uint64_t m = x >= 0 ? (uint64_t)x : (uint64_t)(-x);
+        const uint64_t r = reduce2(shoup_lazy(m, 1, tab.rsh[pi], q), q);
+        a[i] = x >= 0 ? r : negm(r, q);
+    }
+}
+
+__global__ void k_pointwise(LimbBatch A, LimbBatch B, LimbBatch O, DevTables tab, uint32_t n, int op) {
+    const uint32_t limb = blockIdx.y;
+    const int pi = A.pi[limb % A.nl];
+    const uint64_t* a = limb_ptr(A, limb, n);
+    const uint64_t* b = limb_ptr(B, limb, n);
+    uint64_t* o = limb_ptr(O, limb, n);
+    const uint64_t q = tab.q[pi], qn = tab.qneg[pi];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (op == 0) o[i] = mont(a[i], b[i], q, qn);
+        else if (op == 1) o[i] = addm(a[i], b[i], q);
+        else o[i] = subm(a[i], b[i], q);
+    }
+}
+
+__global__ void k_permute(LimbBatch I, LimbBatch O, uint32_t log_n, uint64_t galois) {
+    const uint32_t n = 1u << log_n, limb = blockIdx.y;
+    const uint64_t* a = limb_ptr(I, limb, n);
+    uint64_t* o = limb_ptr(O, limb, n);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        o[i] = a[ntt_perm_src(i, log_n, galois)];
+}
+
+struct ScalarK {
+    uint64_t w[MAXB], wsh[MAXB];
+};
+
+__global__ void k_scalar(LimbBatch I, LimbBatch O, ScalarK sk, DevTables tab, uint32_t n) {
+    const uint32_t limb = blockIdx.y, k = limb % I.nl;
+    const int pi = I.pi[k];
+    const uint64_t* a = limb_ptr(I, limb, n);
+    uint64_t* o = limb_ptr(O, limb, n);
+    const uint64_t q = tab.q[pi];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        o[i] = shoup(a[i], sk.w[k], sk.wsh[k], q);
+}
+
+// ---------------------------------------------------------------------------
+// key switching
+// ---------------------------------------------------------------------------
+
+struct ModUpPlan {
+    uint32_t lvl, nd, nlx;
+    uint8_t xpi[MAXB];                      // prime of extended limb jj (Q_l then P)
+    uint8_t dstart[MAXD], dsz[MAXD];        // Q-limb range of digit d
+    uint64_t hinv[MAXD][MAXDS], hinv_sh[MAXD][MAXDS];              // (D/d_i)^-1 mod d_i
+    uint64_t hat[MAXD][MAXDS][MAXB], hat_sh[MAXD][MAXDS][MAXB];    // (D/d_i) mod t_jj
+};
+
+// X: [B][2][l+1][N] copy of the inputs, poly 0 in NTT form, poly 1 in coefficient form.
+// ext[b][d][jj][p]: ModUp of digit d of sigma_k(c1), coefficient form.
+__global__ void __launch_bounds__(kThreads) k_modup(const uint64_t* __restrict__ X, uint64_t* __restrict__ ext,
+                                                    ModUpPlan pl, DevTables tab, uint32_t log_n, uint32_t kinv) {
+    const uint32_t n = 1u << log_n;
+    const uint32_t b = blockIdx.y / pl.nd, d = blockIdx.y % pl.nd;
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const uint32_t e = (p * kinv) & ((2u << log_n) - 1);   // sigma_k gather: X^p <- +-X^(p k^-1)
+    const bool neg = e >= n;
+    const uint32_t src = e & (n - 1);
+    const uint64_t* c1 = X + ((size_t)b * 2 + 1) * (pl.lvl + 1) * n;
+    uint64_t* out = ext + ((size_t)b * pl.nd + d) * pl.nlx * n;
+    uint64_t v[MAXDS];
+    const uint32_t ds = pl.dsz[d], d0 = pl.dstart[d];
+    for (uint32_t i = 0; i < ds; i++) {
+        const uint32_t jq = d0 + i;
+        const uint64_t q = tab.q[jq];
+        uint64_t x = c1[(size_t)jq * n + src];
+        if (neg) x = negm(x, q);
+        out[(size_t)jq * n + p] = x;
+        v[i] = shoup(x, pl.hinv[d][i], pl.hinv_sh[d][i], q);
+    }
+    for (uint32_t jj = 0; jj < pl.nlx; jj++) {
+        if (jj >= d0 && jj < d0 + ds) continue;
+        const uint64_t t = tab.q[pl.xpi[jj]];
+        uint64_t acc = 0;
+        for (uint32_t i = 0; i < ds; i++) acc += shoup_lazy(v[i], pl.hat[d][i][jj], pl.hat_sh[d][i][jj], t);
+        // acc < 2*ds*t <= 6t
+        if (acc >= 4 * t) acc -= 4 * t;
+        if (acc >= 2 * t) acc -= 2 * t;
+        out[(size_t)jj * n + p] = reduce2(acc, t);
+    }
+}
+
+struct IPPlan {
+    uint32_t nd, nlx, nb;
+    uint8_t xpi[MAXB];
+    uint8_t kidx[MAXB];   // key limb (full-basis index) of extended limb jj
+};
+
+// acc[b][c][jj] = sum_d ext[b][d][jj] * key[d][c][kidx[jj]]   (NTT domain, key Montgomery)
+__global__ void __launch_bounds__(kThreads) k_ks_ip(const uint64_t* __restrict__ ext, const uint64_t* __restrict__ key,
+                                                    uint64_t* __restrict__ acc, IPPlan pl, DevTables tab,
+                                                    uint32_t log_n) {
+    const uint32_t n = 1u << log_n;
+    const uint32_t b = blockIdx.y / pl.nlx, jj = blockIdx.y % pl.nlx;
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int pi = pl.xpi[jj];
+    const uint64_t q = tab.q[pi], qn = tab.qneg[pi];
+    uint64_t s0 = 0, s1 = 0;
+    for (uint32_t d = 0; d < pl.nd; d++) {
+        const uint64_t x = ext[(((size_t)b * pl.nd + d) * pl.nlx + jj) * n + p];
+        const uint64_t k0 = key[(((size_t)d * 2 + 0) * pl.nb + pl.kidx[jj]) * n + p];
+        const uint64_t k1 = key[(((size_t)d * 2 + 1) * pl.nb + pl.kidx[jj]) * n + p];
+        s0 = reduce2(s0 + mont(x, k0, q, qn), q);
+        s1 = reduce2(s1 + mont(x, k1, q, qn), q);
+    }
+    acc[(((size_t)b * 2 + 0) * pl.nlx + jj) * n + p] = s0;
+    acc[(((size_t)b * 2 + 1) * pl.nlx + jj) * n + p] = s1;
+}
+
+struct BConvPlan {
+    uint32_t ns, nt;
+    uint8_t spi[MAXDS], tpi[MAXB];
+    uint64_t hinv[MAXDS], hinv_sh[MAXDS];
+    uint64_t hat[MAXDS][MAXB], hat_sh[MAXDS][MAXB];
+};
+
+// dst[poly][dst_off + j] = Conv_{S -> t_j}(src[poly][src_off + 0..ns-1])   (coefficient form)
+__global__ void __launch_bounds__(kThreads) k_bconv(const uint64_t* __restrict__ src, size_t src_stride,
+                                                    uint32_t src_off, uint64_t* __restrict__ dst,
+                                                    size_t dst_stride, uint32_t dst_off, BConvPlan pl,
+                                                    DevTables tab, uint32_t log_n) {
+    const uint32_t n = 1u << log_n, poly = blockIdx.y;
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    uint64_t v[MAXDS];
+    for (uint32_t i = 0; i < pl.ns; i++) {
+        const uint64_t x = src[poly * src_stride + (size_t)(src_off + i) * n + p];
+        v[i] = shoup(x, pl.hinv[i], pl.hinv_sh[i], tab.q[pl.spi[i]]);
+    }
+    for (uint32_t j = 0; j < pl.nt; j++) {
+        const uint64_t t = tab.q[pl.tpi[j]];
+        uint64_t acc = 0;
+        for (uint32_t i = 0; i < pl.ns; i++) acc += shoup_lazy(v[i], pl.hat[i][j], pl.hat_sh[i][j], t);
+        if (acc >= 4 * t) acc -= 4 * t;
+        if (acc >= 2 * t) acc -= 2 * t;
+        dst[poly * dst_stride + (size_t)(dst_off + j) * n + p] = reduce2(acc, t);
+    }
+}
+
+struct CombinePlan {
+    uint32_t lvl, nlx;
+    uint64_t pinv[MAXB], pinv_sh[MAXB];   // P^-1 mod q_j
+};
+
+// out[b][c][j] = (acc[b][c][j] - conv[b][c][j]) * P^-1 (+ sigma_k(c0) for c = 0) (+ add[b][c][j])
+__global__ void __launch_bounds__(kThreads) k_ks_combine(const uint64_t* __restrict__ acc,
+                                                         const uint64_t* __restrict__ conv,
+                                                         const uint64_t* __restrict__ X,
+                                                         uint64_t* const* out, uint64_t* const* add,
+                                                         CombinePlan pl, DevTables tab, uint32_t log_n,
+                                                         uint64_t galois) {
+    const uint32_t n = 1u << log_n, l1 = pl.lvl + 1;
+    const uint32_t b = blockIdx.y / l1, j = blockIdx.y % l1;
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const uint64_t q = tab.q[j];
+    const uint64_t a0 = acc[(((size_t)b * 2 + 0) * pl.nlx + j) * n + p];
+    const uint64_t a1 = acc[(((size_t)b * 2 + 1) * pl.nlx + j) * n + p];
+    const uint64_t v0 = conv[(((size_t)b * 2 + 0) * l1 + j) * n + p];
+    const uint64_t v1 = conv[(((size_t)b * 2 + 1) * l1 + j) * n + p];
+    uint64_t o0 = shoup(subm(a0, v0, q), pl.pinv[j], pl.pinv_sh[j], q);
+    uint64_t o1 = shoup(subm(a1, v1, q), pl.pinv[j], pl.pinv_sh[j], q);
+    const uint64_t c0 = X[((size_t)b * 2 * l1 + j) * n + ntt_perm_src(p, log_n, galois)];
+    o0 = addm(o0, c0, q);
+    if (add != nullptr) {
+        const uint64_t* ad = add[b];
+        o0 = addm(o0, ad[(size_t)j * n + p], q);
+        o1 = addm(o1, ad[((size_t)l1 + j) * n + p], q);
+    }
+    uint64_t* o = out[b];
+    o[(size_t)j * n + p] = o0;
+    o[((size_t)l1 + j) * n + p] = o1;
+}
+
+// X[b] = in[b] (both polys, limbs 0..l)
+__global__ void k_gather_cts(uint64_t* const* in, uint64_t* X, uint32_t words_per_ct) {
+    const uint32_t b = blockIdx.y;
+    const uint64_t* s = in[b];
+    uint64_t* d = X + (size_t)b * words_per_ct;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < words_per_ct; i += gridDim.x * blockDim.x)
+        d[i] = s[i];
+}
+
+// ---------------------------------------------------------------------------
+// rescale
+// ---------------------------------------------------------------------------
+
+// Y[b*2 + c] = limb l of poly c of in[b]
+__global__ void k_gather_last(uint64_t* const* in, uint64_t* Y, uint32_t lvl, uint32_t n) {
+    const uint32_t bc = blockIdx.y, b = bc / 2, c = bc % 2;
+    const uint64_t* s = in[b] + ((size_t)c * (lvl + 1) + lvl) * n;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        Y[(size_t)bc * n + i] = s[i];
+}
+
+// Rl[bc][j] = centred(Y[bc]) mod q_j for j < l (Y: coefficient form mod q_l)
+__global__ void k_rescale_lift(const uint64_t* Y, uint64_t* Rl, uint32_t lvl, DevTables tab, uint32_t n) {
+    const uint32_t bc = blockIdx.y;
+    const uint64_t ql = tab.q[lvl];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint64_t v = Y[(size_t)bc * n + i];
+        const bool neg = v > (ql >> 1);
+        const uint64_t mag = neg ? ql - v : v;
+        for (uint32_t j = 0; j < lvl; j++) {
+            const uint64_t qj = tab.q[j];
+            const uint64_t r = reduce2(shoup_lazy(mag, 1, tab.rsh[j], qj), qj);
+            Rl[((size_t)bc * lvl + j) * n + i] = neg ? negm(r, qj) : r;
+        }
+    }
+}
+
+struct RescalePlan {
+    uint32_t lvl;
+    uint64_t inv[MAXB], inv_sh[MAXB];   // q_l^-1 mod q_j
+};
+
+// out[b][c][j] = (in[b][c][j] - Rl[b*2+c][j]) * q_l^-1
+__global__ void k_rescale_combine(uint64_t* const* in, const uint64_t* Rl, uint64_t* const* out,
+                                  RescalePlan pl, DevTables tab, uint32_t n) {
+    const uint32_t l = pl.lvl;
+    const uint32_t y = blockIdx.y, b = y / (2 * l), c = (y / l) % 2, j = y % l;
+    const uint64_t q = tab.q[j];
+    const uint64_t* s = in[b] + ((size_t)c * (l + 1) + j) * n;
+    const uint64_t* r = Rl + (((size_t)b * 2 + c) * l + j) * n;
+    uint64_t* o = out[b] + ((size_t)c * l + j) * n;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        o[i] = shoup(subm(s[i], r[i], q), pl.inv[j], pl.inv_sh[j], q);
+}
+
+// ---------------------------------------------------------------------------
+// products
+// ---------------------------------------------------------------------------
+
+__global__ void k_mul_plain(uint64_t* const* in, const uint64_t* const* pt, uint64_t* const* out,
+                            uint32_t lvl, DevTables tab, uint32_t n) {
+    const uint32_t l1 = lvl + 1;
+    const uint32_t y = blockIdx.y, b = y / (2 * l1), c = (y / l1) % 2, j = y % l1;
+    const uint64_t q = tab.q[j], qn = tab.qneg[j];
+    const uint64_t* s = in[b] + ((size_t)c * l1 + j) * n;
+    const uint64_t* m = pt[b] + (size_t)j * n;
+    uint64_t* o = out[b] + ((size_t)c * l1 + j) * n;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        o[i] = mont(s[i], m[i], q, qn);
+}
+
+// acc[q][g][c][j] = sum_i T[q][i][c][j] * P[g][i][j]; each thread: one coefficient, QT queries
+template <int QT>
+__global__ void __launch_bounds__(kThreads) k_mac(const uint64_t* __restrict__ T, const uint64_t* __restrict__ P,
+                                                  uint64_t* __restrict__ acc, uint32_t Qn, uint32_t G,
+                                                  uint32_t n_in, uint32_t lvl, DevTables tab, uint32_t log_n) {
+    const uint32_t n = 1u << log_n, l1 = lvl + 1;
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t j = blockIdx.y % l1, g = blockIdx.y / l1;
+    const uint32_t q0 = blockIdx.z * QT;
+    if (p >= n) return;
+    const uint64_t q = tab.q[j], qn = tab.qneg[j];
+    uint64_t s0[QT], s1[QT];
+#pragma unroll
+    for (int k = 0; k < QT; k++) s0[k] = s1[k] = 0;
+    for (uint32_t i = 0; i < n_in; i++) {
+        const uint64_t pv = P[(((size_t)g * n_in + i) * l1 + j) * n + p];
+#pragma unroll
+        for (int k = 0; k < QT; k++) {
+            if (q0 + k >= Qn) break;
+            const size_t tb = ((((size_t)(q0 + k) * n_in + i) * 2) * l1 + j) * n + p;
+            s0[k] = addm(s0[k], mont(T[tb], pv, q, qn), q);
+            s1[k] = addm(s1[k], mont(T[tb + (size_t)l1 * n], pv, q, qn), q);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < QT; k++) {
+        if (q0 + k >= Qn) break;
+        const size_t ob = ((((size_t)(q0 + k) * G + g) * 2) * l1 + j) * n + p;
+        acc[ob] = s0[k];
+        acc[ob + (size_t)l1 * n] = s1[k];
+    }
+}
+
+inline dim3 elem_grid(uint32_t n, uint32_t y) { return dim3((n + kThreads - 1) / kThreads, y); }
+
+}  // namespace
+
+// ===========================================================================
+// launchers
+// ===========================================================================
+
+cudaError_t ntt_forward(const Context& c, const LimbBatch& b, cudaStream_t s) { return ntt_dispatch(c, b, false, s); }
+cudaError_t ntt_inverse(const Context& c, const LimbBatch& b, cudaStream_t s) { return ntt_dispatch(c, b, true, s); }
+
+cudaError_t to_montgomery(const Context& c, const LimbBatch& b, bool inverse, cudaStream_t s) {
+    const uint32_t limbs = b.n_polys * b.nl;
+    if (!limbs) return cudaSuccess;
+    const dim3 g(c.n / kThreads / 4, limbs);
+    if (inverse) k_from_mont<<<g, kThreads, 0, s>>>(b, c.tab, c.n);
+    else k_to_mont<<<g, kThreads, 0, s>>>(b, c.tab, c.n);
+    return cudaGetLastError();
+}
+
+cudaError_t lift_signed(const Context& c, const int64_t* d_v, const LimbBatch& out, cudaStream_t s) {
+    const uint32_t limbs = out.n_polys * out.nl;
+    k_lift_signed<<<dim3(c.n / kThreads / 4, limbs), kThreads, 0, s>>>(d_v, out, c.tab, c.n);
+    return cudaGetLastError();
+}
+
+cudaError_t pointwise_mul(const Context& c, const LimbBatch& a, const LimbBatch& b, const LimbBatch& out,
+                          cudaStream_t s) {
+    k_pointwise<<<dim3(c.n / kThreads / 4, a.n_polys * a.nl), kThreads, 0, s>>>(a, b, out, c.tab, c.n, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t pointwise_addsub(const Context& c, const LimbBatch& a, const LimbBatch& b, const LimbBatch& out,
+                             bool sub, cudaStream_t s) {
+    k_pointwise<<<dim3(c.n / kThreads / 4, a.n_polys * a.nl), kThreads, 0, s>>>(a, b, out, c.tab, c.n,
+                                                                                 sub ? 2 : 1);
+    return cudaGetLastError();
+}
+
+cudaError_t permute_ntt(const Context& c, const LimbBatch& in, const LimbBatch& out, uint64_t galois,
+                        cudaStream_t s) {
+    k_permute<<<dim3(c.n / kThreads / 4, in.n_polys * in.nl), kThreads, 0, s>>>(in, out, c.log_n, galois);
+    return cudaGetLastError();
+}
+
+cudaError_t scalar_mul(const Context& c, const LimbBatch& in, const uint64_t* cst, const LimbBatch& out,
+                       cudaStream_t s) {
+    ScalarK sk{};
+    for (uint32_t k = 0; k < in.nl; k++) {
+        const uint64_t q = c.primes[in.pi[k]];
+        sk.w[k] = cst[k] % q;
+        sk.wsh[k] = h_shoup_companion(sk.w[k], q);
+    }
+    k_scalar<<<dim3(c.n / kThreads / 4, in.n_polys * in.nl), kThreads, 0, s>>>(in, out, sk, c.tab, c.n);
+    return cudaGetLastError();
+}
+
+// ---- key switching ----
+
+size_t ks_scratch_words(const Context& c, uint32_t level, uint32_t B) {
+    const size_t n = c.n, l1 = level + 1, nlx = l1 + c.alpha;
+    size_t nd = 0;
+    for (auto& d : c.digits) nd += (!d.empty() && d[0] <= level);
+    return (size_t)B * n * (2 * l1 + nd * nlx + 2 * nlx + 2 * l1);
+}
+
+cudaError_t ks_rotate(const Context& c, const uint64_t* key, uint64_t galois, uint32_t level, uint32_t B,
+                      uint64_t* const* d_in, uint64_t* const* d_out, uint64_t* const* d_add, uint64_t* scratch,
+                      cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    const uint32_t n = c.n, l1 = level + 1, nlx = l1 + c.alpha;
+    // digits present at this level
+    ModUpPlan mu{};
+    mu.lvl = level;
+    mu.nlx = nlx;
+    for (uint32_t jj = 0; jj < nlx; jj++) mu.xpi[jj] = (uint8_t)(jj < l1 ? jj : c.L + 1 + (jj - l1));
+    uint32_t nd = 0;
+    for (auto& dg : c.digits) {
+        if (dg.empty() || dg[0] > level) continue;
+        uint32_t ds = 0;
+        for (uint32_t x : dg) ds += (x <= level);
+        mu.dstart[nd] = (uint8_t)dg[0];
+        mu.dsz[nd] = (uint8_t)ds;
+        for (uint32_t i = 0; i < ds; i++) {
+            const uint64_t qi = c.primes[dg[0] + i];
+            uint64_t hat = 1;
+            for (uint32_t k = 0; k < ds; k++)
+                if (k != i) hat = h_mulmod(hat, c.primes[dg[0] + k] % qi, qi);
+            mu.hinv[nd][i] = h_invmod(hat, qi);
+            mu.hinv_sh[nd][i] = h_shoup_companion(mu.hinv[nd][i], qi);
+            for (uint32_t jj = 0; jj < nlx; jj++) {
+                const uint64_t t = c.primes[mu.xpi[jj]];
+                uint64_t ht = 1;
+                for (uint32_t k = 0; k < ds; k++)
+                    if (k != i) ht = h_mulmod(ht, c.primes[dg[0] + k] % t, t);
+                mu.hat[nd][i][jj] = ht;
+                mu.hat_sh[nd][i][jj] = h_shoup_companion(ht, t);
+            }
+        }
+        nd++;
+    }
+    mu.nd = nd;
+
+    uint64_t* X = scratch;                                 // [B][2][l1][N]
+    uint64_t* ext = X + (size_t)B * 2 * l1 * n;            // [B][nd][nlx][N]
+    uint64_t* acc = ext + (size_t)B * nd * nlx * n;        // [B][2][nlx][N]
+    uint64_t* conv = acc + (size_t)B * 2 * nlx * n;        // [B][2][l1][N]
+
+    k_gather_cts<<<dim3(64, B), kThreads, 0, s>>>(d_in, X, 2 * l1 * n);
+    // c1 -> coefficient form
+    LimbBatch c1b{X + (size_t)l1 * n, B, (uint64_t)2 * l1 * n, 0, l1, {}};
+    for (uint32_t k = 0; k < l1; k++) c1b.pi[k] = (uint8_t)k;
+    cudaError_t e = ntt_inverse(c, c1b, s);
+    if (e != cudaSuccess) return e;
+    const uint32_t kinv = (uint32_t)h_invmod_pow2(galois, 2ull * n);
+    k_modup<<<elem_grid(n, B * nd), kThreads, 0, s>>>(X, ext, mu, c.tab, c.log_n, kinv);
+    LimbBatch eb{ext, B * nd, (uint64_t)nlx * n, 0, nlx, {}};
+    for (uint32_t jj = 0; jj < nlx; jj++) eb.pi[jj] = mu.xpi[jj];
+    if ((e = ntt_forward(c, eb, s)) != cudaSuccess) return e;
+    IPPlan ip{};
+    ip.nd = nd;
+    ip.nlx = nlx;
+    ip.nb = c.nb;
+    for (uint32_t jj = 0; jj < nlx; jj++) {
+        ip.xpi[jj] = mu.xpi[jj];
+        ip.kidx[jj] = mu.xpi[jj];
+    }
+    k_ks_ip<<<elem_grid(n, B * nlx), kThreads, 0, s>>>(ext, key, acc, ip, c.tab, c.log_n);
+    // ModDown: P limbs -> coefficient form -> convert to Q_l -> NTT
+    LimbBatch pb{acc, B * 2, (uint64_t)nlx * n, l1, c.alpha, {}};
+    for (uint32_t k = 0; k < c.alpha; k++) pb.pi[k] = (uint8_t)(c.L + 1 + k);
+    if ((e = ntt_inverse(c, pb, s)) != cudaSuccess) return e;
+    BConvPlan bp{};
+    bp.ns = c.alpha;
+    bp.nt = l1;
+    for (uint32_t i = 0; i < c.alpha; i++) {
+        bp.spi[i] = (uint8_t)(c.L + 1 + i);
+        const uint64_t pi_ = c.primes[c.L + 1 + i];
+        uint64_t hat = 1;
+        for (uint32_t k = 0; k < c.alpha; k++)
+            if (k != i) hat = h_mulmod(hat, c.primes[c.L + 1 + k] % pi_, pi_);
+        bp.hinv[i] = h_invmod(hat, pi_);
+        bp.hinv_sh[i] = h_shoup_companion(bp.hinv[i], pi_);
+        for (uint32_t j = 0; j < l1; j++) {
+            const uint64_t t = c.primes[j];
+            uint64_t ht = 1;
+            for (uint32_t k = 0; k < c.alpha; k++)
+                if (k != i) ht = h_mulmod(ht, c.primes[c.L + 1 + k] % t, t);
+            bp.hat[i][j] = ht;
+            bp.hat_sh[i][j] = h_shoup_companion(ht, t);
+        }
+    }
+    for (uint32_t j = 0; j < l1; j++) bp.tpi[j] = (uint8_t)j;
+    k_bconv<<<elem_grid(n, B * 2), kThreads, 0, s>>>(acc, (size_t)nlx * n, l1, conv, (size_t)l1 * n, 0, bp, c.tab,
+                                                     c.log_n);
+    LimbBatch cb{conv, B * 2, (uint64_t)l1 * n, 0, l1, {}};
+    for (uint32_t j = 0; j < l1; j++) cb.pi[j] = (uint8_t)j;
+    if ((e = ntt_forward(c, cb, s)) != cudaSuccess) return e;
+    CombinePlan cp{};
+    cp.lvl = level;
+    cp.nlx = nlx;
+    for (uint32_t j = 0; j < l1; j++) {
+        const uint64_t q = c.primes[j];
+        cp.pinv[j] = h_invmod(c.P_mod[j], q);
+        cp.pinv_sh[j] = h_shoup_companion(cp.pinv[j], q);
+    }
+    k_ks_combine<<<elem_grid(n, B * l1), kThreads, 0, s>>>(acc, conv, X, d_out, d_add, cp, c.tab, c.log_n, galois);
+    return cudaGetLastError();
+}
+
+// ---- rescale ----
+
+size_t rescale_scratch_words(const Context& c, uint32_t level, uint32_t B) {
+    return (size_t)B * 2 * c.n * (1 + level);
+}
+
+cudaError_t rescale(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in, uint64_t* const* d_out,
+                    uint64_t* scratch, cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    const uint32_t n = c.n;
+    uint64_t* Y = scratch;                         // [B*2][N]
+    uint64_t* Rl = Y + (size_t)B * 2 * n;          // [B*2][level][N]
+    k_gather_last<<<dim3(n / kThreads / 4, B * 2), kThreads, 0, s>>>(d_in, Y, level, n);
+    LimbBatch yb{Y, B * 2, n, 0, 1, {}};
+    yb.pi[0] = (uint8_t)level;
+    cudaError_t e = ntt_inverse(c, yb, s);
+    if (e != cudaSuccess) return e;
+    k_rescale_lift<<<dim3(n / kThreads / 4, B * 2), kThreads, 0, s>>>(Y, Rl, level, c.tab, n);
+    LimbBatch rb{Rl, B * 2, (uint64_t)level * n, 0, level, {}};
+    for (uint32_t j = 0; j < level; j++) rb.pi[j] = (uint8_t)j;
+    if ((e = ntt_forward(c, rb, s)) != cudaSuccess) return e;
+    RescalePlan rp{};
+    rp.lvl = level;
+    for (uint32_t j = 0; j < level; j++) {
+        const uint64_t q = c.primes[j];
+        rp.inv[j] = h_invmod(c.primes[level] % q, q);
+        rp.inv_sh[j] = h_shoup_companion(rp.inv[j], q);
+    }
+    k_rescale_combine<<<dim3(n / kThreads / 4, B * 2 * level), kThreads, 0, s>>>(d_in, Rl, d_out, rp, c.tab, n);
+    return cudaGetLastError();
+}
+
+cudaError_t mul_plain(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,
+                      const uint64_t* const* d_pt, uint64_t* const* d_out, cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    k_mul_plain<<<dim3(c.n / kThreads / 4, B * 2 * (level + 1)), kThreads, 0, s>>>(d_in, d_pt, d_out, level, c.tab,
+                                                                                   c.n);
+    return cudaGetLastError();
+}
+
+cudaError_t mac(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32_t n_in, const uint64_t* T,
+                const uint64_t* P, uint64_t* acc, cudaStream_t s) {
+    constexpr int QT = 4;
+    const dim3 g((c.n + kThreads - 1) / kThreads, G * (level + 1), (Q + QT - 1) / QT);
+    k_mac<QT><<<g, kThreads, 0, s>>>(T, P, acc, Q, G, n_in, level, c.tab, c.log_n);
+    return cudaGetLastError();
+}
+
+}  // namespace bm

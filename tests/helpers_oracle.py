@@ -1,0 +1,96 @@
+"""Oracle-side construction of match inputs and expected outputs for the parity tests.
+
+Everything here comes from `oracle/` and the seeded generator in
+paper_2408_06167_gb300.workload; nothing is read back from the GPU library.
+"""
+import numpy as np
+
+from oracle import ckks
+from oracle import schedule as sch
+from paper_2408_06167_gb300 import workload as wl
+
+KEY_SEED = 3
+ENC_SEED = 4
+
+_CTX = {}
+
+
+def octx(name):
+    if name not in _CTX:
+        _CTX[name] = ckks.Context(name)
+    return _CTX[name]
+
+
+def schedule_rotations(ctx, m, s):
+    """Left rotations the tiled/expanded schedule needs (negative = right)."""
+    n_in = m // s
+    tiled = ctx.L >= 3
+    level = ctx.L - 1 if tiled else ctx.L
+    rots = []
+    if tiled:
+        rots += [s << j for j in range(sch.log2i(n_in))]
+    rots += [1 << t for t in range(sch.log2i(s))]
+    if level >= 2:
+        rots += [-(1 << t) for t in range(sch.log2i(s))]
+    return rots
+
+
+class OracleMatch:
+    """Keys, gallery plaintexts, query ciphertexts and match outputs from the oracle."""
+
+    def __init__(self, name, m, s, R, n_queries, feats=None, seed=KEY_SEED):
+        self.ctx = ctx = octx(name)
+        self.m, self.s, self.R = m, s, R
+        self.n_in = m // s
+        self.tiled = ctx.L >= 3
+        self.level = ctx.L - 1 if self.tiled else ctx.L
+        self.compress = self.level >= 2
+        self.feats = wl.gallery(R, m) if feats is None else feats
+        self.queries, self.true_ids = wl.queries(self.feats, n_queries)
+        self.sk, self.pk, self.rks = ckks.keygen(ctx, seed, schedule_rotations(ctx, m, s))
+        self.ev = ckks.Evaluator(ctx, self.rks)
+        S, L = ctx.slots, ctx.L
+        self.groups = sch.n_groups(R, s, S)
+        self.gal = [[ctx.encode(sch.gallery_slots(self.feats, g, i, s, S), ctx.q[self.level], self.level)
+                     for i in range(self.n_in)] for g in range(self.groups)]
+        self.masks = ([ctx.encode(sch.alg1_mask_slots(m, s, i, S), ctx.q[L], L) for i in range(self.n_in)]
+                      if self.tiled else None)
+        self.cmask = (ctx.encode(sch.compression_mask_slots(s, S), ctx.q[self.level - 1], self.level - 1)
+                      if self.compress else None)
+
+    # arrays in the library's import layouts
+    def pts_array(self):
+        return np.stack([np.stack([p.limbs for p in row]) for row in self.gal])
+
+    def masks_array(self):
+        return None if self.masks is None else np.stack([p.limbs for p in self.masks])
+
+    def cmask_array(self):
+        return None if self.cmask is None else self.cmask.limbs
+
+    def encrypt(self, qi):
+        ctx, S, L = self.ctx, self.ctx.slots, self.ctx.L
+        q = self.queries[qi]
+        if self.tiled:
+            pts = [ctx.encode(sch.tiled_query_slots(q, S), ctx.scale, L)]
+        else:
+            pts = [ctx.encode(sch.expanded_query_slots(q, self.s, i, S), ctx.scale, L) for i in range(self.n_in)]
+        return [ckks.encrypt(ctx, self.pk, pt, ENC_SEED, qi * 256 + k) for k, pt in enumerate(pts)]
+
+    @staticmethod
+    def ct_array(cts):
+        return np.stack([np.stack([c.c0, c.c1]) for c in cts])
+
+    def match(self, cts):
+        outs, packed = sch.match(self.ev, cts, self.gal, self.masks, self.cmask, self.m, self.s,
+                                 expanded=not self.tiled)
+        return self.ct_array(outs), packed
+
+    def scores(self, outs_array, packed):
+        ctx, S = self.ctx, self.ctx.slots
+        dec = []
+        for o in outs_array:
+            ct = ckks.Ciphertext(o[0], o[1], 0, ctx.scale)
+            dec.append(ckks.decrypt_decode(ctx, ct, self.sk).real)
+        return np.array([dec[o][slot] for o, slot in (sch.identity_slot(i, self.s, S, packed)
+                                                      for i in range(self.R))])
