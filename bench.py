@@ -1,0 +1,303 @@
+#!/usr/bin/env python
+"""Benchmark of the encrypted 1:N match (Blind-Match, Sec. 3.3) on the GPU.
+
+One step = one bm_match call: Algorithm 1 on the encrypted query, HE-C^3 over
+every gallery group, compression, score ciphertexts resident on the device.
+Default workload: ring 2^16 RNS-CKKS, 6,144 identities x 128-dim features in
+parts of 16, one tiled query (the paper's Table 2 gallery size).  Features are
+seeded synthetic L2-normalised Gaussians (paper_2408_06167_gb300.workload).
+
+Prints one JSON line: matches/s with the query resident in HBM (`value`),
+the same through host buffers (`e2e`), p50/p99 step latency, the roofline of
+the dominant kernel class, and the CPU oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--no-cpu-baseline]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encrypted 1:N template matches/sec @128-dim, ring 2^16; p50/p99 query latency"
+UNIT = "matches/s"
+KEY_SEED, ENC_SEED = 3, 4
+L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2, written between timed steps
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="face-128d-6144")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+class OracleRun:
+    """The oracle's match of one query of the workload (keys, gallery and query prepared once)."""
+
+    def __init__(self, wname):
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from helpers_oracle import OracleMatch
+        from paper_2408_06167_gb300 import workload as wl
+        W = wl.WORKLOADS[wname]
+        self.W = W
+        self.om = OracleMatch(W.preset, W.dim, W.part, W.n_ids, 1)
+        self.cts = self.om.encrypt(0)
+
+    def step(self):
+        t0 = time.perf_counter()
+        out, _ = self.om.match(self.cts)
+        return time.perf_counter() - t0
+
+
+def cpu_baseline(wname):
+    run = OracleRun(wname)
+    t = run.step()
+    return {"value": run.W.n_ids / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one query x {run.W.n_ids} identities ({run.W.name}), full match, "
+                      f"{t:.1f} s single-threaded"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    run = OracleRun(args.workload)
+    for _ in range(args.warmup):
+        run.step()
+    times = [run.step() for _ in range(args.steps)]
+    total = sum(times)
+    value = args.steps * run.W.n_ids / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": run.W.name, "ring": "2^16" if run.W.preset == "ring16" else run.W.preset,
+                   "n_ids": run.W.n_ids, "dim": run.W.dim, "part": run.W.part, "queries_per_step": 1},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: one query x {run.W.n_ids} identities, full oracle match"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "latency_ms": {"p50": 1e3 * statistics.median(times), "p99": 1e3 * max(times)},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p["hbm_gbs"], "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def percentile(xs, p):
+    xs = sorted(xs)
+    k = min(len(xs) - 1, max(0, int(round(p / 100.0 * (len(xs) - 1)))))
+    return xs[k]
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2408_06167_gb300 import binding as bm
+    from paper_2408_06167_gb300 import workload as wl
+
+    W = wl.WORKLOADS[args.workload]
+    ctx = bm.bm_context_create(W.preset, local)
+    sk, pk, ek = bm.bm_keygen(ctx, KEY_SEED, W.dim, W.part)
+    feats = wl.gallery(W.n_ids, W.dim)
+    gal = bm.bm_encode_gallery(ctx, feats, W.dim, W.part)
+    qs, _ = wl.queries(feats, W.n_queries)
+    mode = bm.BM_QUERY_TILED if W.query_mode == "tiled" else bm.BM_QUERY_EXPANDED
+    cts = [bm.bm_encrypt_query(ctx, pk, q, W.dim, W.part, mode, ENC_SEED, i) for i, q in enumerate(qs)]
+    host_cts = [bm.bm_encrypt_query(ctx, pk, q, W.dim, W.part, mode, ENC_SEED, i) for i, q in enumerate(qs)]
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    for ct in cts:
+        bm.bm_ciphertext_upload(ct, sptr)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    matches_per_step = W.n_ids * W.n_queries
+
+    # correctness guard on the benchmarked configuration: decrypted Rank-1 vs FP64
+    r = bm.bm_match(ctx, ek, gal, cts, sptr)
+    scores, rank1, _ = bm.bm_decrypt_scores(ctx, sk, r, 0, W.n_ids)
+    ref = wl.plaintext_scores(feats, qs[0])
+    max_err = float(abs(scores - ref).max())
+    assert max_err < 1e-5, max_err
+    del r
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    for _ in range(args.warmup):
+        r = bm.bm_match(ctx, ek, gal, cts, sptr)
+        del r
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    bm.bm_profile_control(0, 1)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        r = bm.bm_match(ctx, ek, gal, cts, sptr)
+        ev[k][1].record(stream)
+        del r
+    torch.cuda.synchronize()
+    launches_timed = sum(bm.bm_profile_read(kind)[0] for kind in bm.KERNEL_KINDS)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * matches_per_step * args.steps / (total_ms / 1e3)
+
+    # per-class device time over the same number of steps (event pair per launch)
+    bm.bm_profile_control(1, 1)
+    for k in range(args.steps):
+        flush.zero_()
+        r = bm.bm_match(ctx, ek, gal, cts, sptr)
+        del r
+    torch.cuda.synchronize()
+    prof = {kind: bm.bm_profile_read(kind) for kind in bm.KERNEL_KINDS}
+    bm.bm_profile_control(0, 1)
+    dom = max(prof, key=lambda k: prof[k][1])
+    n_l, ms_l, by_l = prof[dom]
+    peak, peak_src = load_peaks()
+    achieved = by_l / (ms_l / 1e3) / 1e9 if ms_l > 0 else 0.0
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                "launches_per_step": n_l / args.steps, "avg_launch_us": 1e3 * ms_l / max(n_l, 1),
+                "alg_bytes_per_launch": by_l / max(n_l, 1),
+                "share_of_kernel_time": ms_l / max(sum(v[1] for v in prof.values()), 1e-12)}
+    breakdown = {k: {"launches": v[0] // args.steps, "ms_per_step": v[1] / args.steps,
+                     "alg_GB_per_step": v[2] / args.steps / 1e9} for k, v in prof.items() if v[0]}
+
+    # end to end: host ciphertexts in, score ciphertexts out to the host, every step
+    e2e_s = []
+    for k in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = bm.bm_match(ctx, ek, gal, host_cts, sptr)
+        for qi in range(W.n_queries):
+            bm.bm_result_export(r, qi)
+        torch.cuda.synchronize()
+        e2e_s.append(time.perf_counter() - t0)
+        del r
+    n_q, n_out, _ = bm.bm_result_info(bm.bm_match(ctx, ek, gal, cts, sptr))
+    ncts, lvl = bm.bm_ciphertext_info(host_cts[0])
+    h2d = W.n_queries * ncts * 2 * (lvl + 1) * ctx.n * 8
+    d2h = W.n_queries * n_out * 2 * ctx.n * 8
+    e2e_total = sum(e2e_s)
+    if world > 1:
+        t = torch.tensor([e2e_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": W.name, "ring": "2^16", "n_ids": W.n_ids, "dim": W.dim, "part": W.part,
+                   "queries_per_step": W.n_queries, "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "latency_ms": {"p50": percentile(step_ms, 50), "p99": percentile(step_ms, 99)},
+        "e2e": {"value": world * matches_per_step * args.steps / e2e_total, "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_timed,
+        "roofline": roofline,
+        "kernel_breakdown": breakdown,
+        "clocks": clocks,
+        "check": {"max_abs_score_err_vs_fp64": max_err, "rank1": rank1, "rank1_fp64": int(ref.argmax())},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

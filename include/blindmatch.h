@@ -219,6 +219,30 @@ bm_status bm_ntt_forward(bm_context* ctx, uint64_t* d_data, uint32_t n_polys, ui
 bm_status bm_ntt_inverse(bm_context* ctx, uint64_t* d_data, uint32_t n_polys, uint32_t n_limbs,
                          void* stream);
 
+/* ---- launch accounting (measurement support; no counterpart in the paper) ---- */
+
+/* Kernel classes of the match path. */
+enum {
+    BM_KERNEL_NTT = 0,        /* forward/inverse NTT passes (column and row pass each count) */
+    BM_KERNEL_MODUP = 1,      /* automorphism gather + fast base conversion of one digit */
+    BM_KERNEL_KS_IP = 2,      /* inner product with the rotation key */
+    BM_KERNEL_MODDOWN = 3,    /* base conversion of the special-prime limbs back to Q */
+    BM_KERNEL_KS_COMBINE = 4, /* (x - conv) * P^-1 + sigma(c0) (+ addend) */
+    BM_KERNEL_RESCALE = 5,    /* rescale gather, lift and combine */
+    BM_KERNEL_MAC = 6,        /* HE-C^3 multiply-accumulate over the parts */
+    BM_KERNEL_MUL_PLAIN = 7,  /* ct x pt products (masks) */
+    BM_KERNEL_OTHER = 8,      /* copies, conversions, client-side helpers */
+    BM_KERNEL_KINDS = 9
+};
+
+/* Process-wide counters of kernel launches and of their algorithmic bytes (the
+ * reads and writes each launch must make, counted per kernel from its operand
+ * sizes), per class.  With timing != 0 every later launch is bracketed by a CUDA
+ * event pair on its stream and its device time accumulated.  reset != 0 zeroes
+ * the counters.  Reading waits for the recorded events. */
+bm_status bm_profile_control(uint32_t timing, uint32_t reset);
+bm_status bm_profile_read(uint32_t kind, uint64_t* launches, double* device_ms, double* alg_bytes);
+
 #ifdef __cplusplus
 }
 #endif

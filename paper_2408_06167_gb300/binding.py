@@ -71,6 +71,8 @@ _SIGS = {
     "bm_ct_rescale": (ctypes.c_int, [_vp, _vp, _PP]),
     "bm_ntt_forward": (ctypes.c_int, [_vp, _vp, _u32, _u32, _vp]),
     "bm_ntt_inverse": (ctypes.c_int, [_vp, _vp, _u32, _u32, _vp]),
+    "bm_profile_control": (ctypes.c_int, [_u32, _u32]),
+    "bm_profile_read": (ctypes.c_int, [_u32, _U64P, _DP, _DP]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_L, _name)
@@ -325,3 +327,18 @@ def bm_ntt_forward(ctx, d_ptr, n_polys, n_limbs, stream=None):
 
 def bm_ntt_inverse(ctx, d_ptr, n_polys, n_limbs, stream=None):
     _check(_L.bm_ntt_inverse(ctx.ptr, d_ptr, n_polys, n_limbs, stream))
+
+
+KERNEL_KINDS = ["ntt", "modup", "ks_ip", "moddown", "ks_combine", "rescale", "mac", "mul_plain", "other"]
+
+
+def bm_profile_control(timing, reset):
+    _check(_L.bm_profile_control(int(timing), int(reset)))
+
+
+def bm_profile_read(kind):
+    """(launches, device_ms, algorithmic_bytes) of one kernel class."""
+    k = KERNEL_KINDS.index(kind) if isinstance(kind, str) else kind
+    n, ms, by = _u64(), _dbl(), _dbl()
+    _check(_L.bm_profile_read(k, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
+    return n.value, ms.value, by.value

@@ -13,9 +13,17 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "bm_internal.h"
 
 namespace bm {
+
+// NVTX range for profilers (no-op unless a tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
@@ -788,6 +796,7 @@ struct MatchRun {
     // The whole schedule; with arena.live == false only the pointer arrays are collected.
     void schedule() {
         const uint32_t n_in = g.n_in, part = g.part, lg = g.level;
+        NvtxRange whole(arena.live ? "bm_match_launch" : "bm_match_plan");
         // Algorithm 1: C_out,i = Res(Mul(P)(C_in, mask_i)), then log2(N_in) rotate-and-add by part*2^(j-1)
         if (g.tiled) {
             std::vector<uint64_t*> in, pt, o0, o1;
@@ -820,8 +829,11 @@ struct MatchRun {
                 // per-group outputs at level 0: copy into the result
                 if (arena.live)
                     for (uint32_t q = 0; q < Q; q++)
+                    {
+                        ProfScope ps(BM_KERNEL_OTHER, s, 16.0 * G * cw(0));
                         check(cudaMemcpyAsync(result + ((size_t)q * n_out + g0) * cw(0), accB + (size_t)q * G * cw(0),
                                               (size_t)G * cw(0) * 8, cudaMemcpyDeviceToDevice, s));
+                    }
                 continue;
             }
             const uint32_t lc = lg - 1;
@@ -875,6 +887,7 @@ bm_status bm_match(bm_context* ctxh, const bm_eval_keys* evk, const bm_gallery* 
     BM_CUDA_TRY(cudaSetDevice(c.device));
     cudaStream_t s = (cudaStream_t)stream;
 
+    NvtxRange range("bm_match");
     MatchRun run(c, g, evk->k, s);
     run.Q = n_queries;
     run.ncts = ncts;

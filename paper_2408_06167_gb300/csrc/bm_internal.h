@@ -132,6 +132,18 @@ void encode_real(const Context& ctx, const double* z, double scale, int64_t* out
 // slots of integer coefficients / scale (real parts)
 void decode_real(const Context& ctx, const double* coeffs, double scale, double* z);
 
+// ---- launch accounting (profile.cpp) ----
+// Every launcher brackets its kernel with a ProfScope: launches and algorithmic
+// bytes are always counted per kernel class; with timing enabled a CUDA event
+// pair is recorded around the launch on its stream.
+struct ProfScope {
+    ProfScope(int kind, cudaStream_t s, double alg_bytes, uint32_t launches = 1);
+    ~ProfScope();
+    int kind;
+    cudaStream_t s;
+    int slot;
+};
+
 // ---- kernel launchers (kernels.cu) ----
 cudaError_t ntt_forward(const Context& c, const LimbBatch& b, cudaStream_t s);
 cudaError_t ntt_inverse(const Context& c, const LimbBatch& b, cudaStream_t s);

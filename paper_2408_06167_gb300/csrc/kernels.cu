@@ -139,12 +139,13 @@ cudaError_t ntt_launch(const LimbBatch& b, const DevTables& tab, bool inv, cudaS
     const uint32_t limbs = b.n_polys * b.nl;
     if (limbs == 0) return cudaSuccess;
     const dim3 gc(limbs, (1 << LB) / COLS), gr(limbs, (1 << LA) / ROWS);
+    const double bytes = 16.0 * (1 << (LA + LB)) * limbs;   // each pass reads and writes every limb once
     if (!inv) {
-        k_ntt_cols<LA, LB, COLS, false><<<gc, kThreads, 0, s>>>(b, tab);
-        k_ntt_rows<LA, LB, ROWS, false><<<gr, kThreads, 0, s>>>(b, tab);
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes); k_ntt_cols<LA, LB, COLS, false><<<gc, kThreads, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes); k_ntt_rows<LA, LB, ROWS, false><<<gr, kThreads, 0, s>>>(b, tab); }
     } else {
-        k_ntt_rows<LA, LB, ROWS, true><<<gr, kThreads, 0, s>>>(b, tab);
-        k_ntt_cols<LA, LB, COLS, true><<<gc, kThreads, 0, s>>>(b, tab);
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes); k_ntt_rows<LA, LB, ROWS, true><<<gr, kThreads, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes); k_ntt_cols<LA, LB, COLS, true><<<gc, kThreads, 0, s>>>(b, tab); }
     }
     return cudaGetLastError();
 }
@@ -492,6 +493,7 @@ cudaError_t to_montgomery(const Context& c, const LimbBatch& b, bool inverse, cu
     const uint32_t limbs = b.n_polys * b.nl;
     if (!limbs) return cudaSuccess;
     const dim3 g(c.n / kThreads / 4, limbs);
+    ProfScope ps(BM_KERNEL_OTHER, s, 16.0 * c.n * limbs);
     if (inverse) k_from_mont<<<g, kThreads, 0, s>>>(b, c.tab, c.n);
     else k_to_mont<<<g, kThreads, 0, s>>>(b, c.tab, c.n);
     return cudaGetLastError();
@@ -499,18 +501,21 @@ cudaError_t to_montgomery(const Context& c, const LimbBatch& b, bool inverse, cu
 
 cudaError_t lift_signed(const Context& c, const int64_t* d_v, const LimbBatch& out, cudaStream_t s) {
     const uint32_t limbs = out.n_polys * out.nl;
+    ProfScope ps(BM_KERNEL_OTHER, s, 8.0 * c.n * (limbs + 1));
     k_lift_signed<<<dim3(c.n / kThreads / 4, limbs), kThreads, 0, s>>>(d_v, out, c.tab, c.n);
     return cudaGetLastError();
 }
 
 cudaError_t pointwise_mul(const Context& c, const LimbBatch& a, const LimbBatch& b, const LimbBatch& out,
                           cudaStream_t s) {
+    ProfScope ps(BM_KERNEL_OTHER, s, 24.0 * c.n * a.n_polys * a.nl);
     k_pointwise<<<dim3(c.n / kThreads / 4, a.n_polys * a.nl), kThreads, 0, s>>>(a, b, out, c.tab, c.n, 0);
     return cudaGetLastError();
 }
 
 cudaError_t pointwise_addsub(const Context& c, const LimbBatch& a, const LimbBatch& b, const LimbBatch& out,
                              bool sub, cudaStream_t s) {
+    ProfScope ps(BM_KERNEL_OTHER, s, 24.0 * c.n * a.n_polys * a.nl);
     k_pointwise<<<dim3(c.n / kThreads / 4, a.n_polys * a.nl), kThreads, 0, s>>>(a, b, out, c.tab, c.n,
                                                                                  sub ? 2 : 1);
     return cudaGetLastError();
@@ -518,6 +523,7 @@ cudaError_t pointwise_addsub(const Context& c, const LimbBatch& a, const LimbBat
 
 cudaError_t permute_ntt(const Context& c, const LimbBatch& in, const LimbBatch& out, uint64_t galois,
                         cudaStream_t s) {
+    ProfScope ps(BM_KERNEL_OTHER, s, 16.0 * c.n * in.n_polys * in.nl);
     k_permute<<<dim3(c.n / kThreads / 4, in.n_polys * in.nl), kThreads, 0, s>>>(in, out, c.log_n, galois);
     return cudaGetLastError();
 }
@@ -530,6 +536,7 @@ cudaError_t scalar_mul(const Context& c, const LimbBatch& in, const uint64_t* cs
         sk.w[k] = cst[k] % q;
         sk.wsh[k] = h_shoup_companion(sk.w[k], q);
     }
+    ProfScope ps(BM_KERNEL_OTHER, s, 16.0 * c.n * in.n_polys * in.nl);
     k_scalar<<<dim3(c.n / kThreads / 4, in.n_polys * in.nl), kThreads, 0, s>>>(in, out, sk, c.tab, c.n);
     return cudaGetLastError();
 }
@@ -585,14 +592,22 @@ cudaError_t ks_rotate(const Context& c, const uint64_t* key, uint64_t galois, ui
     uint64_t* acc = ext + (size_t)B * nd * nlx * n;        // [B][2][nlx][N]
     uint64_t* conv = acc + (size_t)B * 2 * nlx * n;        // [B][2][l1][N]
 
-    k_gather_cts<<<dim3(64, B), kThreads, 0, s>>>(d_in, X, 2 * l1 * n);
+    {
+        ProfScope ps(BM_KERNEL_OTHER, s, 32.0 * B * l1 * n);
+        k_gather_cts<<<dim3(64, B), kThreads, 0, s>>>(d_in, X, 2 * l1 * n);
+    }
     // c1 -> coefficient form
     LimbBatch c1b{X + (size_t)l1 * n, B, (uint64_t)2 * l1 * n, 0, l1, {}};
     for (uint32_t k = 0; k < l1; k++) c1b.pi[k] = (uint8_t)k;
     cudaError_t e = ntt_inverse(c, c1b, s);
     if (e != cudaSuccess) return e;
     const uint32_t kinv = (uint32_t)h_invmod_pow2(galois, 2ull * n);
-    k_modup<<<elem_grid(n, B * nd), kThreads, 0, s>>>(X, ext, mu, c.tab, c.log_n, kinv);
+    {
+        double bytes = 0;
+        for (uint32_t d = 0; d < nd; d++) bytes += 8.0 * n * B * (mu.dsz[d] + nlx);
+        ProfScope ps(BM_KERNEL_MODUP, s, bytes);
+        k_modup<<<elem_grid(n, B * nd), kThreads, 0, s>>>(X, ext, mu, c.tab, c.log_n, kinv);
+    }
     LimbBatch eb{ext, B * nd, (uint64_t)nlx * n, 0, nlx, {}};
     for (uint32_t jj = 0; jj < nlx; jj++) eb.pi[jj] = mu.xpi[jj];
     if ((e = ntt_forward(c, eb, s)) != cudaSuccess) return e;
@@ -604,7 +619,10 @@ cudaError_t ks_rotate(const Context& c, const uint64_t* key, uint64_t galois, ui
         ip.xpi[jj] = mu.xpi[jj];
         ip.kidx[jj] = mu.xpi[jj];
     }
-    k_ks_ip<<<elem_grid(n, B * nlx), kThreads, 0, s>>>(ext, key, acc, ip, c.tab, c.log_n);
+    {
+        ProfScope ps(BM_KERNEL_KS_IP, s, 8.0 * n * nlx * ((double)B * nd + 2.0 * nd + 2.0 * B));
+        k_ks_ip<<<elem_grid(n, B * nlx), kThreads, 0, s>>>(ext, key, acc, ip, c.tab, c.log_n);
+    }
     // ModDown: P limbs -> coefficient form -> convert to Q_l -> NTT
     LimbBatch pb{acc, B * 2, (uint64_t)nlx * n, l1, c.alpha, {}};
     for (uint32_t k = 0; k < c.alpha; k++) pb.pi[k] = (uint8_t)(c.L + 1 + k);
@@ -630,8 +648,11 @@ cudaError_t ks_rotate(const Context& c, const uint64_t* key, uint64_t galois, ui
         }
     }
     for (uint32_t j = 0; j < l1; j++) bp.tpi[j] = (uint8_t)j;
-    k_bconv<<<elem_grid(n, B * 2), kThreads, 0, s>>>(acc, (size_t)nlx * n, l1, conv, (size_t)l1 * n, 0, bp, c.tab,
-                                                     c.log_n);
+    {
+        ProfScope ps(BM_KERNEL_MODDOWN, s, 8.0 * n * B * 2 * (c.alpha + l1));
+        k_bconv<<<elem_grid(n, B * 2), kThreads, 0, s>>>(acc, (size_t)nlx * n, l1, conv, (size_t)l1 * n, 0, bp,
+                                                         c.tab, c.log_n);
+    }
     LimbBatch cb{conv, B * 2, (uint64_t)l1 * n, 0, l1, {}};
     for (uint32_t j = 0; j < l1; j++) cb.pi[j] = (uint8_t)j;
     if ((e = ntt_forward(c, cb, s)) != cudaSuccess) return e;
@@ -643,6 +664,7 @@ cudaError_t ks_rotate(const Context& c, const uint64_t* key, uint64_t galois, ui
         cp.pinv[j] = h_invmod(c.P_mod[j], q);
         cp.pinv_sh[j] = h_shoup_companion(cp.pinv[j], q);
     }
+    ProfScope ps(BM_KERNEL_KS_COMBINE, s, 8.0 * n * B * l1 * (2 + 2 + 1 + 2 + (d_add ? 2 : 0)));
     k_ks_combine<<<elem_grid(n, B * l1), kThreads, 0, s>>>(acc, conv, X, d_out, d_add, cp, c.tab, c.log_n, galois);
     return cudaGetLastError();
 }
@@ -659,12 +681,18 @@ cudaError_t rescale(const Context& c, uint32_t level, uint32_t B, uint64_t* cons
     const uint32_t n = c.n;
     uint64_t* Y = scratch;                         // [B*2][N]
     uint64_t* Rl = Y + (size_t)B * 2 * n;          // [B*2][level][N]
-    k_gather_last<<<dim3(n / kThreads / 4, B * 2), kThreads, 0, s>>>(d_in, Y, level, n);
+    {
+        ProfScope ps(BM_KERNEL_RESCALE, s, 16.0 * n * B * 2);
+        k_gather_last<<<dim3(n / kThreads / 4, B * 2), kThreads, 0, s>>>(d_in, Y, level, n);
+    }
     LimbBatch yb{Y, B * 2, n, 0, 1, {}};
     yb.pi[0] = (uint8_t)level;
     cudaError_t e = ntt_inverse(c, yb, s);
     if (e != cudaSuccess) return e;
-    k_rescale_lift<<<dim3(n / kThreads / 4, B * 2), kThreads, 0, s>>>(Y, Rl, level, c.tab, n);
+    {
+        ProfScope ps(BM_KERNEL_RESCALE, s, 8.0 * n * B * 2 * (1 + level));
+        k_rescale_lift<<<dim3(n / kThreads / 4, B * 2), kThreads, 0, s>>>(Y, Rl, level, c.tab, n);
+    }
     LimbBatch rb{Rl, B * 2, (uint64_t)level * n, 0, level, {}};
     for (uint32_t j = 0; j < level; j++) rb.pi[j] = (uint8_t)j;
     if ((e = ntt_forward(c, rb, s)) != cudaSuccess) return e;
@@ -675,6 +703,7 @@ cudaError_t rescale(const Context& c, uint32_t level, uint32_t B, uint64_t* cons
         rp.inv[j] = h_invmod(c.primes[level] % q, q);
         rp.inv_sh[j] = h_shoup_companion(rp.inv[j], q);
     }
+    ProfScope ps(BM_KERNEL_RESCALE, s, 24.0 * n * B * 2 * level);
     k_rescale_combine<<<dim3(n / kThreads / 4, B * 2 * level), kThreads, 0, s>>>(d_in, Rl, d_out, rp, c.tab, n);
     return cudaGetLastError();
 }
@@ -682,6 +711,7 @@ cudaError_t rescale(const Context& c, uint32_t level, uint32_t B, uint64_t* cons
 cudaError_t mul_plain(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,
                       const uint64_t* const* d_pt, uint64_t* const* d_out, cudaStream_t s) {
     if (B == 0) return cudaSuccess;
+    ProfScope ps(BM_KERNEL_MUL_PLAIN, s, 8.0 * c.n * B * (level + 1) * 5);
     k_mul_plain<<<dim3(c.n / kThreads / 4, B * 2 * (level + 1)), kThreads, 0, s>>>(d_in, d_pt, d_out, level, c.tab,
                                                                                    c.n);
     return cudaGetLastError();
@@ -691,6 +721,7 @@ cudaError_t mac(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32
                 const uint64_t* P, uint64_t* acc, cudaStream_t s) {
     constexpr int QT = 4;
     const dim3 g((c.n + kThreads - 1) / kThreads, G * (level + 1), (Q + QT - 1) / QT);
+    ProfScope ps(BM_KERNEL_MAC, s, 8.0 * c.n * (level + 1) * ((double)Q * n_in * 2 + (double)G * n_in + 2.0 * Q * G));
     k_mac<QT><<<g, kThreads, 0, s>>>(T, P, acc, Q, G, n_in, level, c.tab, c.log_n);
     return cudaGetLastError();
 }
