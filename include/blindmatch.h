@@ -219,6 +219,29 @@ bm_status bm_ntt_forward(bm_context* ctx, uint64_t* d_data, uint32_t n_polys, ui
 bm_status bm_ntt_inverse(bm_context* ctx, uint64_t* d_data, uint32_t n_polys, uint32_t n_limbs,
                          void* stream);
 
+/* Rot(ct, rotation) like bm_ct_rotate, for callers that cannot let the library
+ * allocate device memory (a host whose device memory belongs to its own pool
+ * allocator, or a serving loop that forbids allocation after start-up).  The
+ * paper has no counterpart to this call.
+ *   d_in:  n_cts ciphertexts at `level`, coefficient form, device memory,
+ *          layout [n_cts][2][level+1][N]; read only.
+ *   d_out: device memory of the same size; receives the rotated ciphertexts in
+ *          coefficient form.  Must not overlap d_in.
+ * Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default stream)
+ * and the call returns without waiting for it.  Temporaries live in one
+ * file-scope device array of 32 MiB that every GPU loading the library holds
+ * until the process exits; the call performs no cudaMalloc/cudaFree.  Requests
+ * needing more (input copy + key-switch temporaries, e.g. more than one ring-2^16
+ * ciphertext at level 3) or more than 64 ciphertexts fail with BM_E_ARG and a
+ * message giving the limit.  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  All calls
+ * share the array: calls whose work overlaps on one GPU (issued on different
+ * streams or from different threads) race and must be serialised by the
+ * caller.  BM_E_KEY_MISSING if evk has no key for the rotation. */
+bm_status bm_ct_rotate_noalloc(bm_context* ctx, const bm_eval_keys* evk, const uint64_t* d_in,
+                               uint32_t n_cts, uint32_t level, int32_t rotation, uint64_t* d_out,
+                               void* stream);
+
 /* ---- launch accounting (measurement support; no counterpart in the paper) ---- */
 
 /* Kernel classes of the match path. */

@@ -71,6 +71,7 @@ _SIGS = {
     "bm_ct_rescale": (ctypes.c_int, [_vp, _vp, _PP]),
     "bm_ntt_forward": (ctypes.c_int, [_vp, _vp, _u32, _u32, _vp]),
     "bm_ntt_inverse": (ctypes.c_int, [_vp, _vp, _u32, _u32, _vp]),
+    "bm_ct_rotate_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _u32, _u32, _i32, _vp, _vp]),
     "bm_profile_control": (ctypes.c_int, [_u32, _u32]),
     "bm_profile_read": (ctypes.c_int, [_u32, _U64P, _DP, _DP]),
 }
@@ -319,6 +320,11 @@ def bm_ct_rescale(ctx, ct):
     h = _out()
     _check(_L.bm_ct_rescale(ctx.ptr, ct.ptr, ctypes.byref(h)))
     return Ciphertext(h.value, ctx)
+
+
+def bm_ct_rotate_noalloc(ctx, evk, d_in, n_cts, level, rotation, d_out, stream=None):
+    """Rotation on caller-provided device buffers (integer device pointers), no device allocation."""
+    _check(_L.bm_ct_rotate_noalloc(ctx.ptr, evk.ptr, d_in, n_cts, level, rotation, d_out, stream))
 
 
 def bm_ntt_forward(ctx, d_ptr, n_polys, n_limbs, stream=None):

@@ -45,7 +45,6 @@ static uint32_t ilog2(uint64_t x) {
     while ((1ull << r) < x) r++;
     return r;
 }
-static size_t ct_words(const Context& c, uint32_t level) { return (size_t)2 * (level + 1) * c.n; }
 
 // RAII device buffer
 struct DevBuf {
@@ -114,12 +113,6 @@ static std::vector<int32_t> schedule_rotations(const Context& c, const Layout& l
     return r;
 }
 
-static uint64_t galois_of(const Context& c, int32_t rot) {
-    const uint64_t two_n = 2ull * c.n;
-    int64_t r = rot % (int64_t)c.slots;
-    if (r < 0) r += c.slots;
-    return h_powmod(5, (uint64_t)r, two_n);
-}
 
 // ---------------------------------------------------------------------------
 // context

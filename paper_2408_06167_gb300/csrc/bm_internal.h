@@ -101,6 +101,15 @@ struct Result {
     ~Result();
 };
 
+// Galois element 5^r mod 2N of a left rotation by r slots (negative r: right).
+inline uint64_t galois_of(const Context& c, int32_t rot) {
+    int64_t r = rot % (int64_t)c.slots;
+    if (r < 0) r += c.slots;
+    return h_powmod(5, (uint64_t)r, 2ull * c.n);
+}
+// words of one ciphertext at `level`: [2][level+1][N]
+inline size_t ct_words(const Context& c, uint32_t level) { return (size_t)2 * (level + 1) * c.n; }
+
 // ---- error reporting ----
 void set_error(const std::string& msg);
 #define BM_CUDA_TRY(expr)                                                              \
