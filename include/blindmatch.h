@@ -168,12 +168,17 @@ bm_status bm_ciphertext_import(bm_context* ctx, const uint64_t* data, uint32_t n
                                uint32_t level, bm_ciphertext** out);
 bm_status bm_ciphertext_info(const bm_ciphertext* ct, uint32_t* n_cts, uint32_t* level);
 bm_status bm_ciphertext_export(const bm_ciphertext* ct, uint64_t* out, size_t capacity);
-/* Stages the ciphertext on the device (H2D + NTT) on `stream` (a cudaStream_t, NULL
- * for the legacy default stream); later bm_match calls skip their own upload. */
+/* Stages the ciphertext on the device (H2D, coefficient form) on `stream` (a
+ * cudaStream_t, NULL for the legacy default stream) and waits for the copy; later
+ * bm_match calls copy it device-to-device instead of from the host. */
 bm_status bm_ciphertext_upload(bm_ciphertext* ct, void* stream);
 void bm_ciphertext_destroy(bm_ciphertext* ct);
 
-/* Sec. 3.3, the server side, on the GPU: for each query, Algorithm 1 (tiled
+/* Sec. 3.3, the server side, on the GPU.  The first call for a (gallery, key set,
+ * n_queries) triple builds a plan -- persistent device buffers and the whole
+ * schedule captured as a CUDA graph -- kept until the gallery, the key set or the
+ * context is destroyed; later calls copy the queries in, replay the graph and
+ * copy the score ciphertexts into a new result.  For each query, Algorithm 1 (tiled
  * queries), then for every group HE-C^3 (Algorithm 2: ct x pt products summed
  * over the parts, one rescale, log2(part) rotate-and-add steps), then the
  * compression step (mask, pack `part` groups per ciphertext by a tree of right
@@ -190,6 +195,7 @@ bm_status bm_result_info(const bm_result* r, uint32_t* n_queries, uint32_t* n_ou
 /* Score ciphertexts of one query: [n_out][2][N] coefficient form at level 0. */
 bm_status bm_result_export(const bm_result* r, uint32_t query_index, uint64_t* out,
                            size_t capacity);
+/* Frees the result; call it before destroying the result's context. */
 void bm_result_destroy(bm_result* r);
 /* Sec. 3.3 Decryption: decrypts the score ciphertexts of one query with sk and maps
  * slots back to identities: scores[u] ~ <q, g_u> (the cosine similarity of unit

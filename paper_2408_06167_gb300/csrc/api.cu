@@ -155,6 +155,14 @@ static bm_status context_init(Context& c, const bm_params& p, int device) {
     }
     BM_CUDA_TRY(cudaSetDevice(device));
     BM_CUDA_TRY(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+    {
+        // keep freed stream-ordered allocations (results, temporaries) in the pool
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    }
     // twiddles: per prime, N forward pairs then N inverse pairs
     const size_t per = (size_t)2 * c.n;
     std::vector<ulonglong2> tw(per * c.nb);
@@ -256,6 +264,8 @@ bm_status bm_context_create(const bm_params* params, int device, bm_context** ou
 
 void bm_context_destroy(bm_context* ctx) {
     if (!ctx) return;
+    for (Plan* p : ctx->c.plans) destroy_plan(p);
+    ctx->c.plans.clear();
     if (ctx->c.d_twiddles) cudaFree(ctx->c.d_twiddles);
     if (ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
     delete ctx;
@@ -321,6 +331,7 @@ bm_status bm_keygen(bm_context* ctxh, uint64_t seed, uint32_t dim, uint32_t part
     // rotation keys: per digit d, b_d = e_d - a_d*s + P*[limb in digit d]*sigma_k(s) over Q_L u P
     auto* evh = new bm_eval_keys();
     evh->k.ctx = &c;
+    evh->k.id = c.next_id++;
     evh->k.dim = dim;
     evh->k.part = part_size;
     const uint32_t nd = (uint32_t)c.digits.size();
@@ -445,18 +456,22 @@ bm_status bm_eval_keys_export(const bm_eval_keys* evk, int32_t rotation, uint64_
 }  // extern "C"
 
 bm::EvalKeys::~EvalKeys() {
+    if (ctx) drop_plans(*ctx, id);
     for (auto& kv : keys) cudaFree(kv.second);
 }
 bm::Gallery::~Gallery() {
+    if (ctx) drop_plans(*ctx, id);
     if (d_pts) cudaFree(d_pts);
     if (d_masks) cudaFree(d_masks);
     if (d_cmask) cudaFree(d_cmask);
 }
 bm::Ciphertext::~Ciphertext() {
-    if (d_ntt) cudaFree(d_ntt);
+    if (d_coef) cudaFree(d_coef);
 }
 bm::Result::~Result() {
-    if (d_data) cudaFree(d_data);
+    if (d_data) {
+        cudaFreeAsync(d_data, ctx->stream);   // allocated from the stream-ordered pool
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -470,6 +485,7 @@ static bm_status gallery_alloc(Context& c, const Layout& lo, uint64_t n_ids, uin
     gh = new bm_gallery();
     Gallery& g = gh->g;
     g.ctx = &c;
+    g.id = c.next_id++;
     g.n_ids = n_ids;
     g.dim = dim;
     g.part = part;
@@ -698,9 +714,8 @@ bm_status bm_ciphertext_upload(bm_ciphertext* cth, void* stream) {
     const Context& c = *ct.ctx;
     cudaStream_t s = (cudaStream_t)stream;
     BM_CUDA_TRY(cudaSetDevice(c.device));
-    if (!ct.d_ntt) BM_CUDA_TRY(cudaMalloc(&ct.d_ntt, ct.host.size() * 8));
-    BM_CUDA_TRY(cudaMemcpyAsync(ct.d_ntt, ct.host.data(), ct.host.size() * 8, cudaMemcpyHostToDevice, s));
-    BM_CUDA_TRY(ntt_forward(c, packed(c, ct.d_ntt, ct.n_cts * 2, ct.level + 1), s));
+    if (!ct.d_coef) BM_CUDA_TRY(cudaMalloc(&ct.d_coef, ct.host.size() * 8));
+    BM_CUDA_TRY(cudaMemcpyAsync(ct.d_coef, ct.host.data(), ct.host.size() * 8, cudaMemcpyHostToDevice, s));
     BM_CUDA_TRY(cudaStreamSynchronize(s));
     return BM_OK;
 }
@@ -715,8 +730,9 @@ void bm_ciphertext_destroy(bm_ciphertext* ct) { delete ct; }
 
 namespace bm {
 
-// Device arrays of ciphertext pointers for one schedule.  The schedule runs twice:
-// a dry pass that only collects the arrays, then (after one upload) the launch pass.
+// Device arrays of ciphertext pointers for one schedule.  The schedule runs first
+// as a dry pass that only collects the arrays (and sizes the scratch), then
+// (after one upload) as the launch pass.
 struct PtrArena {
     std::vector<uint64_t*> host;
     uint64_t** dev = nullptr;
@@ -733,19 +749,53 @@ struct PtrArena {
     }
 };
 
+// A match schedule for one (gallery, key set, batch size): persistent device
+// buffers, the pointer arrays, and the whole schedule captured as a CUDA graph.
+struct Plan {
+    Context* c = nullptr;
+    uint64_t gid = 0, kid = 0;
+    uint32_t Q = 0, ncts = 0, chunk = 0, n_out = 0;
+    std::vector<void*> bufs;
+    uint64_t *qin = nullptr, *t0 = nullptr, *T = nullptr, *accA = nullptr, *accB = nullptr;
+    uint64_t *scratch = nullptr, *result = nullptr;
+    size_t scratch_words = 0, result_words = 0, qin_words = 0;
+    PtrArena arena;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ProfSink counts;                       // launches per replay
+    ~Plan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (void* p : bufs) cudaFree(p);
+    }
+    bool alloc(uint64_t*& p, size_t words) {
+        if (cudaMalloc((void**)&p, std::max<size_t>(words, 1) * 8) != cudaSuccess) return false;
+        bufs.push_back(p);
+        return true;
+    }
+};
+
+void destroy_plan(Plan* p) { delete p; }
+
+void drop_plans(Context& c, uint64_t id) {
+    std::vector<Plan*> keep;
+    for (Plan* p : c.plans) {
+        if (p->gid == id || p->kid == id) delete p;
+        else keep.push_back(p);
+    }
+    c.plans.swap(keep);
+}
+
 struct MatchRun {
     Context& c;
     const Gallery& g;
     const EvalKeys& ek;
-    cudaStream_t s;
-    PtrArena arena;
-    uint32_t Q = 0, ncts = 0, chunk = 0, ksb = 128;
-    uint64_t *qin = nullptr, *t0 = nullptr, *T = nullptr, *accA = nullptr, *accB = nullptr, *scratch = nullptr;
-    uint64_t* result = nullptr;
-    uint32_t n_out = 0;
+    Plan& pl;
+    cudaStream_t s = nullptr;
+    uint32_t ksb = 128;
     cudaError_t err = cudaSuccess;
 
-    MatchRun(Context& c_, const Gallery& g_, const EvalKeys& ek_, cudaStream_t s_) : c(c_), g(g_), ek(ek_), s(s_) {}
+    MatchRun(Context& c_, const Gallery& g_, const EvalKeys& ek_, Plan& p_) : c(c_), g(g_), ek(ek_), pl(p_) {}
 
     void check(cudaError_t e) {
         if (err == cudaSuccess && e != cudaSuccess) err = e;
@@ -755,77 +805,90 @@ struct MatchRun {
         auto it = ek.keys.find(galois_of(c, rot));
         return it == ek.keys.end() ? nullptr : it->second;
     }
+    void need_scratch(size_t words) { pl.scratch_words = std::max(pl.scratch_words, words); }
 
     void rotate_batch(uint32_t level, int32_t rot, const std::vector<uint64_t*>& in,
                       const std::vector<uint64_t*>& out, const std::vector<uint64_t*>* add) {
-        auto din = arena.list(in);
-        auto dout = arena.list(out);
-        auto dadd = add ? arena.list(*add) : nullptr;
-        if (!arena.live) return;
+        auto din = pl.arena.list(in);
+        auto dout = pl.arena.list(out);
+        auto dadd = add ? pl.arena.list(*add) : nullptr;
+        if (!pl.arena.live) {
+            need_scratch(ks_scratch_words(c, level, (uint32_t)std::min<size_t>(ksb, in.size())));
+            return;
+        }
         const uint64_t gk = galois_of(c, rot);
         for (size_t b0 = 0; b0 < in.size(); b0 += ksb) {
             const uint32_t B = (uint32_t)std::min<size_t>(ksb, in.size() - b0);
-            check(ks_rotate(c, key(rot), gk, level, B, din + b0, dout + b0, dadd ? dadd + b0 : nullptr, scratch, s));
+            check(ks_rotate(c, key(rot), gk, level, B, din + b0, dout + b0, dadd ? dadd + b0 : nullptr, pl.scratch,
+                            s));
         }
     }
     void rescale_batch(uint32_t level, const std::vector<uint64_t*>& in, const std::vector<uint64_t*>& out) {
-        auto din = arena.list(in);
-        auto dout = arena.list(out);
-        if (!arena.live) return;
+        auto din = pl.arena.list(in);
+        auto dout = pl.arena.list(out);
+        if (!pl.arena.live) {
+            need_scratch(rescale_scratch_words(c, level, (uint32_t)std::min<size_t>(ksb, in.size())));
+            return;
+        }
         for (size_t b0 = 0; b0 < in.size(); b0 += ksb) {
             const uint32_t B = (uint32_t)std::min<size_t>(ksb, in.size() - b0);
-            check(rescale(c, level, B, din + b0, dout + b0, scratch, s));
+            check(rescale(c, level, B, din + b0, dout + b0, pl.scratch, s));
         }
     }
     void mulplain_batch(uint32_t level, const std::vector<uint64_t*>& in, const std::vector<uint64_t*>& pt,
                         const std::vector<uint64_t*>& out) {
-        auto din = arena.list(in);
-        auto dpt = arena.list(pt);
-        auto dout = arena.list(out);
-        if (!arena.live) return;
+        auto din = pl.arena.list(in);
+        auto dpt = pl.arena.list(pt);
+        auto dout = pl.arena.list(out);
+        if (!pl.arena.live) return;
         check(mul_plain(c, level, (uint32_t)in.size(), din, dpt, dout, s));
     }
 
-    // The whole schedule; with arena.live == false only the pointer arrays are collected.
+    // a0..a6 on the plan's buffers; with arena.live == false only the pointer
+    // arrays are collected and the scratch sized.
     void schedule() {
-        const uint32_t n_in = g.n_in, part = g.part, lg = g.level;
-        NvtxRange whole(arena.live ? "bm_match_launch" : "bm_match_plan");
+        const uint32_t Q = pl.Q, n_in = g.n_in, part = g.part, lg = g.level, n_out = pl.n_out;
+        pl.arena.cursor = 0;
+        NvtxRange whole(pl.arena.live ? "bm_match_launch" : "bm_match_plan");
+        // a0: queries into the NTT domain
+        if (pl.arena.live) check(ntt_forward(c, packed(c, pl.qin, Q * pl.ncts * 2, c.L + 1), s));
         // Algorithm 1: C_out,i = Res(Mul(P)(C_in, mask_i)), then log2(N_in) rotate-and-add by part*2^(j-1)
         if (g.tiled) {
             std::vector<uint64_t*> in, pt, o0, o1;
             for (uint32_t q = 0; q < Q; q++)
                 for (uint32_t i = 0; i < n_in; i++) {
-                    in.push_back(qin + (size_t)q * cw(c.L));
+                    in.push_back(pl.qin + (size_t)q * cw(c.L));
                     pt.push_back(g.d_masks + (size_t)i * (c.L + 1) * c.n);
-                    o0.push_back(t0 + ((size_t)q * n_in + i) * cw(c.L));
-                    o1.push_back(T + ((size_t)q * n_in + i) * cw(lg));
+                    o0.push_back(pl.t0 + ((size_t)q * n_in + i) * cw(c.L));
+                    o1.push_back(pl.T + ((size_t)q * n_in + i) * cw(lg));
                 }
             mulplain_batch(c.L, in, pt, o0);
             rescale_batch(c.L, o0, o1);
             for (uint32_t j = 1; (1u << (j - 1)) < n_in; j++) rotate_batch(lg, (int32_t)(part << (j - 1)), o1, o1, &o1);
         }
-        const uint64_t* Tsrc = g.tiled ? T : qin;
+        const uint64_t* Tsrc = g.tiled ? pl.T : pl.qin;
         // HE-C^3 per chunk of groups, then compression
-        for (uint32_t g0 = 0; g0 < g.groups; g0 += chunk) {
-            const uint32_t G = std::min(chunk, g.groups - g0);
-            if (arena.live)
-                check(mac(c, lg, Q, G, n_in, Tsrc, g.d_pts + (size_t)g0 * n_in * (lg + 1) * c.n, accA, s));
+        for (uint32_t g0 = 0; g0 < g.groups; g0 += pl.chunk) {
+            const uint32_t G = std::min(pl.chunk, g.groups - g0);
+            if (pl.arena.live) {
+                check(mac(c, lg, Q, G, n_in, Tsrc, g.d_pts + (size_t)g0 * n_in * (lg + 1) * c.n, pl.accA, s));
+            }
             std::vector<uint64_t*> a, b;
             for (uint32_t q = 0; q < Q; q++)
                 for (uint32_t k = 0; k < G; k++) {
-                    a.push_back(accA + ((size_t)q * G + k) * cw(lg));
-                    b.push_back(accB + ((size_t)q * G + k) * cw(lg - 1));
+                    a.push_back(pl.accA + ((size_t)q * G + k) * cw(lg));
+                    b.push_back(pl.accB + ((size_t)q * G + k) * cw(lg - 1));
                 }
             rescale_batch(lg, a, b);
             for (uint32_t t = 1; (1u << (t - 1)) < part; t++) rotate_batch(lg - 1, (int32_t)(1u << (t - 1)), b, b, &b);
             if (!g.compress) {
                 // per-group outputs at level 0: copy into the result
-                if (arena.live)
-                    for (uint32_t q = 0; q < Q; q++)
-                    {
+                if (pl.arena.live)
+                    for (uint32_t q = 0; q < Q; q++) {
                         ProfScope ps(BM_KERNEL_OTHER, s, 16.0 * G * cw(0));
-                        check(cudaMemcpyAsync(result + ((size_t)q * n_out + g0) * cw(0), accB + (size_t)q * G * cw(0),
-                                              (size_t)G * cw(0) * 8, cudaMemcpyDeviceToDevice, s));
+                        check(cudaMemcpyAsync(pl.result + ((size_t)q * n_out + g0) * cw(0),
+                                              pl.accB + (size_t)q * G * cw(0), (size_t)G * cw(0) * 8,
+                                              cudaMemcpyDeviceToDevice, s));
                     }
                 continue;
             }
@@ -838,24 +901,81 @@ struct MatchRun {
                 for (uint32_t q = 0; q < Q; q++)
                     for (uint32_t k = 0; k < G; k += (2u << bb)) {
                         const uint32_t gl = g0 + k;                 // global group of the even element
-                        const uint32_t r = gl % part;
-                        const uint32_t go = gl + (1u << bb);
-                        if (r + (1u << bb) >= part || go >= g.groups || k + (1u << bb) >= G) continue;
-                        even.push_back(accB + ((size_t)q * G + k) * cw(lc));
-                        odd.push_back(accB + ((size_t)q * G + k + (1u << bb)) * cw(lc));
+                        if (gl + (1u << bb) >= g.groups || k + (1u << bb) >= G) continue;
+                        even.push_back(pl.accB + ((size_t)q * G + k) * cw(lc));
+                        odd.push_back(pl.accB + ((size_t)q * G + k + (1u << bb)) * cw(lc));
                     }
                 if (!odd.empty()) rotate_batch(lc, -(int32_t)(1u << bb), odd, even, &even);
             }
             std::vector<uint64_t*> heads, outs;
             for (uint32_t q = 0; q < Q; q++)
                 for (uint32_t k = 0; k < G; k += part) {
-                    heads.push_back(accB + ((size_t)q * G + k) * cw(lc));
-                    outs.push_back(result + ((size_t)q * n_out + (g0 + k) / part) * cw(0));
+                    heads.push_back(pl.accB + ((size_t)q * G + k) * cw(lc));
+                    outs.push_back(pl.result + ((size_t)q * n_out + (g0 + k) / part) * cw(0));
                 }
             rescale_batch(lc, heads, outs);
         }
+        // a6: score ciphertexts back to coefficient form
+        if (pl.arena.live) check(ntt_inverse(c, limbs_of(pl.result, Q * n_out * 2, 1, c.n), s));
     }
 };
+
+static bm_status build_plan(Context& c, const Gallery& g, const EvalKeys& ek, uint32_t Q, Plan*& out) {
+    auto* pl = new Plan();
+    std::unique_ptr<Plan> guard(pl);
+    Layout lo;
+    BM_TRY(make_layout(c, g.n_ids, g.dim, g.part, lo));
+    pl->c = &c;
+    pl->gid = g.id;
+    pl->kid = ek.id;
+    pl->Q = Q;
+    pl->ncts = g.tiled ? 1 : g.n_in;
+    pl->n_out = lo.n_out;
+    const uint32_t lg = g.level;
+    // group chunk: whole packs, bounded by a temporary-memory budget
+    const size_t per_group = (size_t)Q * (ct_words(c, lg) + ct_words(c, lg - 1)) * 8;
+    const size_t budget = (size_t)8 << 30;
+    uint32_t chunk = (uint32_t)std::max<size_t>(1, budget / std::max<size_t>(per_group, 1));
+    if (g.compress) chunk = std::max(g.part, chunk / g.part * g.part);
+    pl->chunk = std::min(chunk, g.groups);
+    pl->qin_words = (size_t)Q * pl->ncts * ct_words(c, c.L);
+    pl->result_words = (size_t)Q * lo.n_out * ct_words(c, 0);
+    bool ok = pl->alloc(pl->qin, pl->qin_words) && pl->alloc(pl->result, pl->result_words);
+    if (g.tiled) {
+        ok = ok && pl->alloc(pl->t0, (size_t)Q * g.n_in * ct_words(c, c.L));
+        ok = ok && pl->alloc(pl->T, (size_t)Q * g.n_in * ct_words(c, lg));
+    }
+    ok = ok && pl->alloc(pl->accA, (size_t)Q * pl->chunk * ct_words(c, lg));
+    ok = ok && pl->alloc(pl->accB, (size_t)Q * pl->chunk * ct_words(c, lg - 1));
+    if (!ok) return fail(BM_E_OOM, "match workspace allocation failed");
+    MatchRun run(c, g, ek, *pl);
+    run.schedule();                                     // dry pass
+    uint64_t* arr = nullptr;
+    ok = pl->alloc(pl->scratch, pl->scratch_words) && pl->alloc(arr, std::max<size_t>(pl->arena.host.size(), 1));
+    if (!ok) return fail(BM_E_OOM, "match scratch allocation failed");
+    pl->arena.dev = (uint64_t**)arr;
+    BM_CUDA_TRY(cudaMemcpy(arr, pl->arena.host.data(), pl->arena.host.size() * sizeof(void*), cudaMemcpyHostToDevice));
+    pl->arena.live = true;
+    // capture the launch pass once
+    cudaStream_t cs = c.stream;
+    BM_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    prof_set_sink(&pl->counts);
+    run.s = cs;
+    run.schedule();
+    prof_set_sink(nullptr);
+    cudaError_t e = cudaStreamEndCapture(cs, &pl->graph);
+    if (run.err != cudaSuccess) return fail(BM_E_CUDA, std::string("match capture: ") + cudaGetErrorString(run.err));
+    BM_CUDA_TRY(e);
+    BM_CUDA_TRY(cudaGraphInstantiate(&pl->exec, pl->graph, 0));
+    out = guard.release();
+    return BM_OK;
+}
+
+static Plan* find_plan(Context& c, uint64_t gid, uint64_t kid, uint32_t Q) {
+    for (Plan* p : c.plans)
+        if (p->gid == gid && p->kid == kid && p->Q == Q) return p;
+    return nullptr;
+}
 
 }  // namespace bm
 
@@ -878,27 +998,30 @@ bm_status bm_match(bm_context* ctxh, const bm_eval_keys* evk, const bm_gallery* 
     for (int32_t r : schedule_rotations(c, lo, g.part))
         if (!evk->k.keys.count(galois_of(c, r))) return fail(BM_E_KEY_MISSING, "missing rotation key");
     BM_CUDA_TRY(cudaSetDevice(c.device));
-    cudaStream_t s = (cudaStream_t)stream;
-
     NvtxRange range("bm_match");
-    MatchRun run(c, g, evk->k, s);
-    run.Q = n_queries;
-    run.ncts = ncts;
-    run.n_out = lo.n_out;
-    const uint32_t lg = g.level;
-    // group chunk: whole packs, bounded by a temporary-memory budget
-    const size_t per_group = (size_t)n_queries * (ct_words(c, lg) + ct_words(c, lg - 1)) * 8;
-    const size_t budget = (size_t)8 << 30;
-    uint32_t chunk = (uint32_t)std::max<size_t>(1, budget / std::max<size_t>(per_group, 1));
-    if (g.compress) chunk = std::max(g.part, chunk / g.part * g.part);
-    run.chunk = std::min(chunk, g.groups);
-    if (g.compress && run.chunk < g.groups) run.chunk = std::max(g.part, run.chunk / g.part * g.part);
-
-    const size_t qwords = (size_t)n_queries * ncts * ct_words(c, c.L);
-    size_t scratch = 0;
-    for (uint32_t lvl = 0; lvl <= c.L; lvl++) {
-        scratch = std::max(scratch, ks_scratch_words(c, lvl, run.ksb));
-        if (lvl) scratch = std::max(scratch, rescale_scratch_words(c, lvl, run.ksb));
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan* pl = find_plan(c, g.id, evk->k.id, n_queries);
+    if (!pl) {
+        BM_TRY(build_plan(c, g, evk->k, n_queries, pl));
+        c.plans.push_back(pl);
+    }
+    // a0: the queries' coefficient-form limbs into the plan's input buffer
+    const size_t per_q = (size_t)ncts * ct_words(c, c.L);
+    for (uint32_t i = 0; i < n_queries; i++) {
+        const Ciphertext& ct = queries[i]->ct;
+        uint64_t* dst = pl->qin + (size_t)i * per_q;
+        if (ct.d_coef) BM_CUDA_TRY(cudaMemcpyAsync(dst, ct.d_coef, per_q * 8, cudaMemcpyDeviceToDevice, s));
+        else BM_CUDA_TRY(cudaMemcpyAsync(dst, ct.host.data(), per_q * 8, cudaMemcpyHostToDevice, s));
+    }
+    if (prof_timing()) {
+        // per-launch timing: run the same launches eagerly so each gets its event pair
+        MatchRun run(c, g, evk->k, *pl);
+        run.s = s;
+        run.schedule();
+        if (run.err != cudaSuccess) return fail(BM_E_CUDA, std::string("match: ") + cudaGetErrorString(run.err));
+    } else {
+        BM_CUDA_TRY(cudaGraphLaunch(pl->exec, s));
+        prof_add(pl->counts);
     }
     auto* rh = new bm_result();
     Result& res = rh->r;
@@ -909,60 +1032,13 @@ bm_status bm_match(bm_context* ctxh, const bm_eval_keys* evk, const bm_gallery* 
     res.dim = g.dim;
     res.part = g.part;
     res.packed = g.compress;
-    std::vector<void*> temps;
-    auto talloc = [&](uint64_t*& p, size_t words) -> bool {
-        if (cudaMallocAsync((void**)&p, std::max<size_t>(words, 1) * 8, s) != cudaSuccess) return false;
-        temps.push_back(p);
-        return true;
-    };
-    auto cleanup = [&]() {
-        for (void* p : temps) cudaFreeAsync(p, s);
-        temps.clear();
-    };
-    bool ok = cudaMalloc(&res.d_data, (size_t)n_queries * lo.n_out * ct_words(c, 0) * 8) == cudaSuccess;
-    ok = ok && talloc(run.qin, qwords);
-    if (g.tiled) {
-        ok = ok && talloc(run.t0, (size_t)n_queries * g.n_in * ct_words(c, c.L));
-        ok = ok && talloc(run.T, (size_t)n_queries * g.n_in * ct_words(c, lg));
-    }
-    ok = ok && talloc(run.accA, (size_t)n_queries * run.chunk * ct_words(c, lg));
-    ok = ok && talloc(run.accB, (size_t)n_queries * run.chunk * ct_words(c, lg - 1));
-    ok = ok && talloc(run.scratch, scratch);
-    if (!ok) {
-        cleanup();
+    cudaError_t e = cudaMallocAsync((void**)&res.d_data, pl->result_words * 8, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(res.d_data, pl->result, pl->result_words * 8, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
         delete rh;
-        return fail(BM_E_OOM, "match workspace allocation failed");
-    }
-    run.result = res.d_data;
-    // a0: queries to the device (H2D unless staged) and into the NTT domain
-    for (uint32_t i = 0; i < n_queries; i++) {
-        const Ciphertext& ct = queries[i]->ct;
-        uint64_t* dst = run.qin + (size_t)i * ncts * ct_words(c, c.L);
-        if (ct.d_ntt) {
-            run.check(cudaMemcpyAsync(dst, ct.d_ntt, ct.host.size() * 8, cudaMemcpyDeviceToDevice, s));
-        } else {
-            run.check(cudaMemcpyAsync(dst, ct.host.data(), ct.host.size() * 8, cudaMemcpyHostToDevice, s));
-            run.check(ntt_forward(c, packed(c, dst, ncts * 2, c.L + 1), s));
-        }
-    }
-    run.schedule();   // dry pass: pointer arrays
-    if (!run.arena.host.empty()) {
-        uint64_t* arr = nullptr;
-        ok = talloc(arr, run.arena.host.size());
-        run.arena.dev = (uint64_t**)arr;
-        if (ok)
-            run.check(cudaMemcpyAsync(run.arena.dev, run.arena.host.data(), run.arena.host.size() * sizeof(void*),
-                                      cudaMemcpyHostToDevice, s));
-    }
-    run.arena.live = true;
-    run.schedule();
-    // a6: score ciphertexts back to coefficient form
-    run.check(ntt_inverse(c, limbs_of(res.d_data, n_queries * lo.n_out * 2, 1, c.n), s));
-    cleanup();
-    run.check(cudaStreamSynchronize(s));
-    if (!ok || run.err != cudaSuccess) {
-        delete rh;
-        return fail(ok ? BM_E_CUDA : BM_E_OOM, std::string("match: ") + cudaGetErrorString(run.err));
+        return fail(BM_E_CUDA, std::string("match: ") + cudaGetErrorString(e));
     }
     *out = rh;
     return BM_OK;

@@ -39,6 +39,9 @@ struct LimbBatch {
     uint8_t pi[MAXB];
 };
 
+struct Plan;                                   // cached match schedule (api.cu)
+void destroy_plan(Plan* p);
+
 struct Context {
     bm_params params{};
     int device = 0;
@@ -51,7 +54,11 @@ struct Context {
     cudaStream_t stream = nullptr;            // for client-side helpers (keygen, encrypt)
     uint64_t P_mod[MAXB]{};                   // P mod each prime
     double scale = 0;
+    uint64_t next_id = 1;                     // ids of galleries and key sets (plan cache keys)
+    std::vector<Plan*> plans;
 };
+// destroys every cached plan that uses the gallery or key set `id`
+void drop_plans(Context& c, uint64_t id);
 
 struct SecretKey {
     Context* ctx;
@@ -66,6 +73,7 @@ struct PublicKey {
 
 struct EvalKeys {
     Context* ctx;
+    uint64_t id = 0;
     uint32_t dim = 0, part = 0;
     std::map<uint64_t, uint64_t*> keys;       // galois element -> [dnum][2][nb][N] NTT + Montgomery
     ~EvalKeys();
@@ -73,6 +81,7 @@ struct EvalKeys {
 
 struct Gallery {
     Context* ctx;
+    uint64_t id = 0;
     uint64_t n_ids = 0;
     uint32_t dim = 0, part = 0, n_in = 0, groups = 0, level = 0;  // level of the gallery pts
     bool tiled = true;                        // queries arrive tiled (Algorithm 1 on the server)
@@ -87,7 +96,7 @@ struct Ciphertext {
     Context* ctx;
     uint32_t n_cts = 1, level = 0;
     std::vector<uint64_t> host;               // [n_cts][2][level+1][N] coefficient form
-    uint64_t* d_ntt = nullptr;                // optional staged device copy, NTT form
+    uint64_t* d_coef = nullptr;               // optional staged device copy, coefficient form
     ~Ciphertext();
 };
 
@@ -152,6 +161,16 @@ struct ProfScope {
     cudaStream_t s;
     int slot;
 };
+// Launch counts of a captured graph: while a sink is set on this thread, ProfScope
+// adds to it instead of the global counters (and records no events); each replay
+// of the graph then adds the sink's counts with prof_add.
+struct ProfSink {
+    uint64_t launches[BM_KERNEL_KINDS] = {};
+    double bytes[BM_KERNEL_KINDS] = {};
+};
+void prof_set_sink(ProfSink* sink);
+void prof_add(const ProfSink& counts);
+bool prof_timing();
 
 // ---- kernel launchers (kernels.cu) ----
 cudaError_t ntt_forward(const Context& c, const LimbBatch& b, cudaStream_t s);
