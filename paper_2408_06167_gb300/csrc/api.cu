@@ -70,7 +70,7 @@ struct DevBuf {
 static LimbBatch limbs_of(uint64_t* base, uint32_t n_polys, uint32_t nl, uint64_t poly_stride,
                           uint32_t first_prime = 0, uint32_t limb_off = 0) {
     LimbBatch b{base, n_polys, poly_stride, limb_off, nl, {}};
-    for (uint32_t k = 0; k < nl; k++) b.pi[k] = (uint8_t)(first_prime + k);
+    for (uint32_t k = 0; k < nl; k++) b.set(k, (uint8_t)(first_prime + k));
     return b;
 }
 // polys of `nl` consecutive limbs starting at prime 0, packed

@@ -29,14 +29,19 @@ struct DevTables {
 };
 
 // A set of limbs: n_polys polynomials at base + poly*poly_stride (words); limb k of
-// each (k < nl) starts at (limb_off + k) * N and uses prime pi[k].
+// each (k < nl) starts at (limb_off + k) * N and uses prime prime(k) (4-bit fields
+// of `pk`, so kernels read them with shifts instead of indexing an array).
 struct LimbBatch {
     uint64_t* base;
     uint32_t n_polys;
     uint64_t poly_stride;
     uint32_t limb_off;
     uint32_t nl;
-    uint8_t pi[MAXB];
+    uint64_t pk;
+    __host__ __device__ __forceinline__ int prime(uint32_t k) const { return (int)((pk >> (4 * k)) & 15); }
+    __host__ __device__ __forceinline__ void set(uint32_t k, uint32_t p) {
+        pk = (pk & ~(15ull << (4 * k))) | ((uint64_t)p << (4 * k));
+    }
 };
 
 struct Plan;                                   // cached match schedule (api.cu)

@@ -49,7 +49,7 @@ template <int LA, int LB, int COLS, bool INV>
 __global__ void __launch_bounds__(kThreads) k_ntt_cols(LimbBatch lb, DevTables tab) {
     constexpr int N1 = 1 << LA, N2 = 1 << LB, TILE = N1 * COLS;
     __shared__ uint64_t sm[TILE];
-    const int pi = lb.pi[blockIdx.x % lb.nl];
+    const int pi = lb.prime(blockIdx.x % lb.nl);
     uint64_t* a = limb_ptr(lb, blockIdx.x, N1 * N2);
     const uint64_t q = tab.q[pi];
     const int c0 = blockIdx.y * COLS;
@@ -95,7 +95,7 @@ template <int LA, int LB, int ROWS, bool INV>
 __global__ void __launch_bounds__(kThreads) k_ntt_rows(LimbBatch lb, DevTables tab) {
     constexpr int N2 = 1 << LB, TILE = ROWS * N2;
     __shared__ uint64_t sm[TILE];
-    const int pi = lb.pi[blockIdx.x % lb.nl];
+    const int pi = lb.prime(blockIdx.x % lb.nl);
     uint64_t* a = limb_ptr(lb, blockIdx.x, (1 << LA) * N2) + (size_t)blockIdx.y * TILE;
     const uint64_t q = tab.q[pi];
     const int rbase = blockIdx.y * ROWS;
@@ -150,13 +150,39 @@ cudaError_t ntt_launch(const LimbBatch& b, const DevTables& tab, bool inv, cudaS
     return cudaGetLastError();
 }
 
+}  // namespace
+}  // namespace bm
+
+#include "ntt_reg.cuh"
+
+namespace bm {
+namespace {
+
+// register-resident passes for even pass sizes (ring 2^12: 64 x 64, ring 2^16: 256 x 256)
+template <int LA, int LB, int C, int R>
+cudaError_t ntt_launch_reg(const LimbBatch& b, const DevTables& tab, bool inv, cudaStream_t s) {
+    const uint32_t limbs = b.n_polys * b.nl;
+    if (limbs == 0) return cudaSuccess;
+    const dim3 gc(limbs, (1 << LB) / C), gr(limbs, (1 << LA) / R);
+    const int tc = C * (1 << (LA / 2)), tr = R * (1 << (LB / 2));
+    const double bytes = 16.0 * (1 << (LA + LB)) * limbs;   // each pass reads and writes every limb once
+    if (!inv) {
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes); nttr::k_col_fwd<LA, LB, C><<<gc, tc, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes); nttr::k_row_fwd<LA, LB, R><<<gr, tr, 0, s>>>(b, tab); }
+    } else {
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes); nttr::k_row_inv<LA, LB, R><<<gr, tr, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes); nttr::k_col_inv<LA, LB, C><<<gc, tc, 0, s>>>(b, tab); }
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t ntt_dispatch(const Context& c, const LimbBatch& b, bool inv, cudaStream_t s) {
     switch (c.log_n) {
-        case 12: return ntt_launch<6, 6>(b, c.tab, inv, s);
+        case 12: return ntt_launch_reg<6, 6, 16, 16>(b, c.tab, inv, s);
         case 13: return ntt_launch<7, 6>(b, c.tab, inv, s);
         case 14: return ntt_launch<7, 7>(b, c.tab, inv, s);
         case 15: return ntt_launch<8, 7>(b, c.tab, inv, s);
-        case 16: return ntt_launch<8, 8>(b, c.tab, inv, s);
+        case 16: return ntt_launch_reg<8, 8, 8, 8>(b, c.tab, inv, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -168,7 +194,7 @@ cudaError_t ntt_dispatch(const Context& c, const LimbBatch& b, bool inv, cudaStr
 // x * 2^-64 mod q (leave Montgomery form)
 __global__ void k_from_mont(LimbBatch lb, DevTables tab, uint32_t n) {
     const uint32_t limb = blockIdx.y;
-    const int pi = lb.pi[limb % lb.nl];
+    const int pi = lb.prime(limb % lb.nl);
     uint64_t* a = limb_ptr(lb, limb, n);
     const uint64_t q = tab.q[pi], qn = tab.qneg[pi];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -178,7 +204,7 @@ __global__ void k_from_mont(LimbBatch lb, DevTables tab, uint32_t n) {
 // x * 2^64 mod q (enter Montgomery form): mont(x, 2^128 mod q)
 __global__ void k_to_mont(LimbBatch lb, DevTables tab, uint32_t n) {
     const uint32_t limb = blockIdx.y;
-    const int pi = lb.pi[limb % lb.nl];
+    const int pi = lb.prime(limb % lb.nl);
     uint64_t* a = limb_ptr(lb, limb, n);
     const uint64_t q = tab.q[pi], qn = tab.qneg[pi], f = tab.r2[pi];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -187,7 +213,7 @@ __global__ void k_to_mont(LimbBatch lb, DevTables tab, uint32_t n) {
 
 __global__ void k_lift_signed(const int64_t* v, LimbBatch lb, DevTables tab, uint32_t n) {
     const uint32_t limb = blockIdx.y;
-    const int pi = lb.pi[limb % lb.nl];
+    const int pi = lb.prime(limb % lb.nl);
     uint64_t* a = limb_ptr(lb, limb, n);
     const uint64_t q = tab.q[pi];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -200,7 +226,7 @@ __global__ void k_lift_signed(const int64_t* v, LimbBatch lb, DevTables tab, uin
 
 __global__ void k_pointwise(LimbBatch A, LimbBatch B, LimbBatch O, DevTables tab, uint32_t n, int op) {
     const uint32_t limb = blockIdx.y;
-    const int pi = A.pi[limb % A.nl];
+    const int pi = A.prime(limb % A.nl);
     const uint64_t* a = limb_ptr(A, limb, n);
     const uint64_t* b = limb_ptr(B, limb, n);
     uint64_t* o = limb_ptr(O, limb, n);
@@ -226,7 +252,7 @@ struct ScalarK {
 
 __global__ void k_scalar(LimbBatch I, LimbBatch O, ScalarK sk, DevTables tab, uint32_t n) {
     const uint32_t limb = blockIdx.y, k = limb % I.nl;
-    const int pi = I.pi[k];
+    const int pi = I.prime(k);
     const uint64_t* a = limb_ptr(I, limb, n);
     uint64_t* o = limb_ptr(O, limb, n);
     const uint64_t q = tab.q[pi];
@@ -532,7 +558,7 @@ cudaError_t scalar_mul(const Context& c, const LimbBatch& in, const uint64_t* cs
                        cudaStream_t s) {
     ScalarK sk{};
     for (uint32_t k = 0; k < in.nl; k++) {
-        const uint64_t q = c.primes[in.pi[k]];
+        const uint64_t q = c.primes[in.prime(k)];
         sk.w[k] = cst[k] % q;
         sk.wsh[k] = h_shoup_companion(sk.w[k], q);
     }
@@ -598,7 +624,7 @@ cudaError_t ks_rotate(const Context& c, const uint64_t* key, uint64_t galois, ui
     }
     // c1 -> coefficient form
     LimbBatch c1b{X + (size_t)l1 * n, B, (uint64_t)2 * l1 * n, 0, l1, {}};
-    for (uint32_t k = 0; k < l1; k++) c1b.pi[k] = (uint8_t)k;
+    for (uint32_t k = 0; k < l1; k++) c1b.set(k, (uint8_t)k);
     cudaError_t e = ntt_inverse(c, c1b, s);
     if (e != cudaSuccess) return e;
     const uint32_t kinv = (uint32_t)h_invmod_pow2(galois, 2ull * n);
@@ -609,7 +635,7 @@ cudaError_t ks_rotate(const Context& c, const uint64_t* key, uint64_t galois, ui
         k_modup<<<elem_grid(n, B * nd), kThreads, 0, s>>>(X, ext, mu, c.tab, c.log_n, kinv);
     }
     LimbBatch eb{ext, B * nd, (uint64_t)nlx * n, 0, nlx, {}};
-    for (uint32_t jj = 0; jj < nlx; jj++) eb.pi[jj] = mu.xpi[jj];
+    for (uint32_t jj = 0; jj < nlx; jj++) eb.set(jj, mu.xpi[jj]);
     if ((e = ntt_forward(c, eb, s)) != cudaSuccess) return e;
     IPPlan ip{};
     ip.nd = nd;
@@ -625,7 +651,7 @@ cudaError_t ks_rotate(const Context& c, const uint64_t* key, uint64_t galois, ui
     }
     // ModDown: P limbs -> coefficient form -> convert to Q_l -> NTT
     LimbBatch pb{acc, B * 2, (uint64_t)nlx * n, l1, c.alpha, {}};
-    for (uint32_t k = 0; k < c.alpha; k++) pb.pi[k] = (uint8_t)(c.L + 1 + k);
+    for (uint32_t k = 0; k < c.alpha; k++) pb.set(k, (uint8_t)(c.L + 1 + k));
     if ((e = ntt_inverse(c, pb, s)) != cudaSuccess) return e;
     BConvPlan bp{};
     bp.ns = c.alpha;
@@ -654,7 +680,7 @@ cudaError_t ks_rotate(const Context& c, const uint64_t* key, uint64_t galois, ui
                                                          c.tab, c.log_n);
     }
     LimbBatch cb{conv, B * 2, (uint64_t)l1 * n, 0, l1, {}};
-    for (uint32_t j = 0; j < l1; j++) cb.pi[j] = (uint8_t)j;
+    for (uint32_t j = 0; j < l1; j++) cb.set(j, (uint8_t)j);
     if ((e = ntt_forward(c, cb, s)) != cudaSuccess) return e;
     CombinePlan cp{};
     cp.lvl = level;
@@ -686,7 +712,7 @@ cudaError_t rescale(const Context& c, uint32_t level, uint32_t B, uint64_t* cons
         k_gather_last<<<dim3(n / kThreads / 4, B * 2), kThreads, 0, s>>>(d_in, Y, level, n);
     }
     LimbBatch yb{Y, B * 2, n, 0, 1, {}};
-    yb.pi[0] = (uint8_t)level;
+    yb.set(0, (uint8_t)level);
     cudaError_t e = ntt_inverse(c, yb, s);
     if (e != cudaSuccess) return e;
     {
@@ -694,7 +720,7 @@ cudaError_t rescale(const Context& c, uint32_t level, uint32_t B, uint64_t* cons
         k_rescale_lift<<<dim3(n / kThreads / 4, B * 2), kThreads, 0, s>>>(Y, Rl, level, c.tab, n);
     }
     LimbBatch rb{Rl, B * 2, (uint64_t)level * n, 0, level, {}};
-    for (uint32_t j = 0; j < level; j++) rb.pi[j] = (uint8_t)j;
+    for (uint32_t j = 0; j < level; j++) rb.set(j, (uint8_t)j);
     if ((e = ntt_forward(c, rb, s)) != cudaSuccess) return e;
     RescalePlan rp{};
     rp.lvl = level;

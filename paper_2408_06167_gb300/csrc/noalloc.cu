@@ -90,7 +90,7 @@ extern "C" bm_status bm_ct_rotate_noalloc(bm_context* ctxh, const bm_eval_keys* 
     BM_CUDA_TRY(cudaMemcpyAsync(lists, h, sizeof(h), cudaMemcpyHostToDevice, s));
     BM_CUDA_TRY(cudaMemcpyAsync(work, d_in, n_cts * cw * 8, cudaMemcpyDeviceToDevice, s));
     LimbBatch all{work, n_cts * 2, (uint64_t)(level + 1) * c.n, 0, level + 1, {}};
-    for (uint32_t k = 0; k <= level; k++) all.pi[k] = (uint8_t)k;
+    for (uint32_t k = 0; k <= level; k++) all.set(k, (uint8_t)k);
     BM_CUDA_TRY(ntt_forward(c, all, s));
     BM_CUDA_TRY(ks_rotate(c, it->second, galois_of(c, rotation), level, n_cts, lists, lists + kMaxCts, nullptr, ks, s));
     LimbBatch outb = all;

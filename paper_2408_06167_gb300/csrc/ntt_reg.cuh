@@ -1,0 +1,226 @@
+// ntt_reg.cuh -- register-resident NTT passes (included by kernels.cu).
+//
+// The negacyclic NTT of one limb (N = N1 * N2, N1 = 2^LA, N2 = 2^LB) is the
+// Cooley-Tukey network with bit-reversed psi twiddles; stage s pairs indices
+// j and j + N/2^(s+1) with twiddle W[2^s + j / (N/2^s)].  Stages 0..LA-1 act on
+// columns of the N1 x N2 view (a "column pass"), stages LA..log N-1 on rows (a
+// "row pass").  Inside a pass each sub-transform has M = 2^P points (P even) and
+// is handled by E = 2^(P/2) threads holding E coefficients each:
+//   phase 1 (first P/2 stages, pair distance >= E): thread t holds the
+//            coefficients t + E*k, k < E ("stride" layout);
+//   phase 2 (last P/2 stages, distance < E): thread t holds E*t + k
+//            ("consecutive" layout);
+// so each pass needs a single exchange through shared memory (padded by one
+// word per E so both layouts are bank-conflict free) instead of a barrier per
+// stage.  Butterflies are Harvey's lazy forms: forward keeps values in [0, 4q),
+// inverse in [0, 2q); the last pass of each transform reduces to [0, q).
+#pragma once
+
+namespace bm {
+namespace nttr {
+
+// x, y in [0, 4q) -> x + w y, x - w y in [0, 4q)
+__device__ __forceinline__ void ct_bfly(uint64_t& x, uint64_t& y, const ulonglong2 w, uint64_t q, uint64_t q2) {
+    const uint64_t a = x >= q2 ? x - q2 : x;
+    const uint64_t t = shoup_lazy(y, w.x, w.y, q);
+    x = a + t;
+    y = a - t + q2;
+}
+
+// x, y in [0, 2q) -> x + y, (x - y) w in [0, 2q)
+__device__ __forceinline__ void gs_bfly(uint64_t& x, uint64_t& y, const ulonglong2 w, uint64_t q, uint64_t q2) {
+    uint64_t a = x + y;
+    a = a >= q2 ? a - q2 : a;
+    const uint64_t t = x - y + q2;
+    x = a;
+    y = shoup_lazy(t, w.x, w.y, q);
+}
+
+__device__ __forceinline__ uint64_t reduce4(uint64_t x, uint64_t q, uint64_t q2) {
+    x = x >= q2 ? x - q2 : x;
+    return x >= q ? x - q : x;
+}
+
+// One stage, compile-time: pairs (k, k + hk) within blocks of 2*hk registers;
+// block blk uses twiddle tw[first + blk].
+template <int E, int HK, bool FWD>
+__device__ __forceinline__ void stage(uint64_t (&v)[E], const ulonglong2* __restrict__ tw, int first, uint64_t q,
+                                      uint64_t q2) {
+#pragma unroll
+    for (int blk = 0; blk < E / (2 * HK); blk++) {
+        const ulonglong2 w = tw[first + blk];
+#pragma unroll
+        for (int j = 0; j < HK; j++) {
+            if constexpr (FWD) ct_bfly(v[blk * 2 * HK + j], v[blk * 2 * HK + j + HK], w, q, q2);
+            else gs_bfly(v[blk * 2 * HK + j], v[blk * 2 * HK + j + HK], w, q, q2);
+        }
+    }
+}
+
+// Forward stages S..P/2-1 of a sub-transform, stride layout (thread holds t + E*k):
+// stage s pairs k and k + 2^(P/2-1-s); block blk of stage s uses W[base(s) + blk].
+template <int P, int S = 0, typename BaseF>
+__device__ __forceinline__ void fwd_stride(uint64_t (&v)[1 << (P / 2)], const ulonglong2* __restrict__ tw, BaseF base,
+                                           uint64_t q, uint64_t q2) {
+    constexpr int H = P / 2;
+    if constexpr (S < H) {
+        stage<1 << H, (1 << (H - 1 - S)), true>(v, tw, base(S), q, q2);
+        fwd_stride<P, S + 1>(v, tw, base, q, q2);
+    }
+}
+
+// Forward stages S..P-1 (S >= P/2), consecutive layout (thread t holds E*t + k):
+// stage s pairs k and k + 2^(P-1-s); the first block's twiddle is W[base(s) + (E*t >> (P-s))].
+template <int P, int S = P / 2, typename BaseF>
+__device__ __forceinline__ void fwd_consec(uint64_t (&v)[1 << (P / 2)], const ulonglong2* __restrict__ tw, BaseF base,
+                                           int t, uint64_t q, uint64_t q2) {
+    constexpr int E = 1 << (P / 2);
+    if constexpr (S < P) {
+        stage<E, (1 << (P - 1 - S)), true>(v, tw, base(S) + ((E * t) >> (P - S)), q, q2);
+        fwd_consec<P, S + 1>(v, tw, base, t, q, q2);
+    }
+}
+
+// Inverse stages S..P/2 downwards, consecutive layout.
+template <int P, int S = P - 1, typename BaseF>
+__device__ __forceinline__ void inv_consec(uint64_t (&v)[1 << (P / 2)], const ulonglong2* __restrict__ tw, BaseF base,
+                                           int t, uint64_t q, uint64_t q2) {
+    constexpr int E = 1 << (P / 2);
+    if constexpr (S >= P / 2) {
+        stage<E, (1 << (P - 1 - S)), false>(v, tw, base(S) + ((E * t) >> (P - S)), q, q2);
+        inv_consec<P, S - 1>(v, tw, base, t, q, q2);
+    }
+}
+
+// Inverse stages S..0 downwards, stride layout.
+template <int P, int S = P / 2 - 1, typename BaseF>
+__device__ __forceinline__ void inv_stride(uint64_t (&v)[1 << (P / 2)], const ulonglong2* __restrict__ tw, BaseF base,
+                                           uint64_t q, uint64_t q2) {
+    constexpr int H = P / 2;
+    if constexpr (S >= 0) {
+        stage<1 << H, (1 << (H - 1 - S)), false>(v, tw, base(S), q, q2);
+        inv_stride<P, S - 1>(v, tw, base, q, q2);
+    }
+}
+
+// padded shared-memory index of sub-transform element r (one spare word per E)
+template <int H>
+__device__ __forceinline__ int pad(int r) { return r + (r >> H); }
+
+// ---------------------------------------------------------------------------
+// pass kernels on a LimbBatch; grid (limbs, tiles)
+// ---------------------------------------------------------------------------
+
+// Column pass, forward: global stages 0..LA-1 on C columns.  Output lazy [0, 4q).
+template <int LA, int LB, int C>
+__global__ void __launch_bounds__(C * (1 << (LA / 2))) k_col_fwd(LimbBatch lb, DevTables tab) {
+    constexpr int H = LA / 2, E = 1 << H, M = 1 << LA, N2 = 1 << LB;
+    __shared__ uint64_t sm[(M + M / E) * C];
+    const int tid = threadIdx.x, t = tid / C, j = tid % C;
+    const int pi = lb.prime(blockIdx.x % lb.nl);
+    uint64_t* a = limb_ptr(lb, blockIdx.x, M * N2) + blockIdx.y * C + j;
+    const uint64_t q = tab.q[pi], q2 = 2 * q;
+    const ulonglong2* tw = tab.tw[pi];
+    const auto base = [](int s) { return 1 << s; };
+    uint64_t v[E];
+#pragma unroll
+    for (int k = 0; k < E; k++) v[k] = a[(size_t)(t + E * k) * N2];
+    fwd_stride<LA>(v, tw, base, q, q2);
+#pragma unroll
+    for (int k = 0; k < E; k++) sm[pad<H>(t + E * k) * C + j] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < E; k++) v[k] = sm[pad<H>(E * t + k) * C + j];
+    fwd_consec<LA>(v, tw, base, t, q, q2);
+#pragma unroll
+    for (int k = 0; k < E; k++) a[(size_t)(E * t + k) * N2] = v[k];
+}
+
+// Row pass, forward: global stages LA..LA+LB-1 on R rows.  Input [0, 4q), output [0, q).
+template <int LA, int LB, int R>
+__global__ void __launch_bounds__(R * (1 << (LB / 2))) k_row_fwd(LimbBatch lb, DevTables tab) {
+    constexpr int H = LB / 2, E = 1 << H, M = 1 << LB, S = M + M / E;
+    __shared__ uint64_t sm[R * S];
+    const int tid = threadIdx.x, j = tid / E, t = tid % E;
+    const int row = blockIdx.y * R + j;
+    const int pi = lb.prime(blockIdx.x % lb.nl);
+    uint64_t* a = limb_ptr(lb, blockIdx.x, (1 << LA) * M) + (size_t)row * M;
+    const uint64_t q = tab.q[pi], q2 = 2 * q;
+    const ulonglong2* tw = tab.tw[pi];
+    const auto base = [row](int s) { return (1 << (LA + s)) + row * (1 << s); };
+    uint64_t* sr = sm + j * S;
+    uint64_t v[E];
+#pragma unroll
+    for (int k = 0; k < E; k++) v[k] = a[t + E * k];
+    fwd_stride<LB>(v, tw, base, q, q2);
+#pragma unroll
+    for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < E; k++) v[k] = sr[pad<H>(E * t + k)];
+    fwd_consec<LB>(v, tw, base, t, q, q2);
+#pragma unroll
+    for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = reduce4(v[k], q, q2);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < E; k++) a[t + E * k] = sr[pad<H>(t + E * k)];
+}
+
+// Row pass, inverse: global stages LA+LB-1..LA on R rows.  Input [0, 2q), output [0, 2q).
+template <int LA, int LB, int R>
+__global__ void __launch_bounds__(R * (1 << (LB / 2))) k_row_inv(LimbBatch lb, DevTables tab) {
+    constexpr int H = LB / 2, E = 1 << H, M = 1 << LB, S = M + M / E;
+    __shared__ uint64_t sm[R * S];
+    const int tid = threadIdx.x, j = tid / E, t = tid % E;
+    const int row = blockIdx.y * R + j;
+    const int pi = lb.prime(blockIdx.x % lb.nl);
+    uint64_t* a = limb_ptr(lb, blockIdx.x, (1 << LA) * M) + (size_t)row * M;
+    const uint64_t q = tab.q[pi], q2 = 2 * q;
+    const ulonglong2* tw = tab.itw[pi];
+    const auto base = [row](int s) { return (1 << (LA + s)) + row * (1 << s); };
+    uint64_t* sr = sm + j * S;
+    uint64_t v[E];
+#pragma unroll
+    for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = a[t + E * k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < E; k++) v[k] = sr[pad<H>(E * t + k)];
+    inv_consec<LB>(v, tw, base, t, q, q2);
+#pragma unroll
+    for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < E; k++) v[k] = sr[pad<H>(t + E * k)];
+    inv_stride<LB>(v, tw, base, q, q2);
+#pragma unroll
+    for (int k = 0; k < E; k++) a[t + E * k] = v[k];
+}
+
+// Column pass, inverse: global stages LA-1..0 on C columns, then * N^-1.  Output [0, q).
+template <int LA, int LB, int C>
+__global__ void __launch_bounds__(C * (1 << (LA / 2))) k_col_inv(LimbBatch lb, DevTables tab) {
+    constexpr int H = LA / 2, E = 1 << H, M = 1 << LA, N2 = 1 << LB;
+    __shared__ uint64_t sm[(M + M / E) * C];
+    const int tid = threadIdx.x, t = tid / C, j = tid % C;
+    const int pi = lb.prime(blockIdx.x % lb.nl);
+    uint64_t* a = limb_ptr(lb, blockIdx.x, M * N2) + blockIdx.y * C + j;
+    const uint64_t q = tab.q[pi], q2 = 2 * q;
+    const ulonglong2* tw = tab.itw[pi];
+    const auto base = [](int s) { return 1 << s; };
+    uint64_t v[E];
+#pragma unroll
+    for (int k = 0; k < E; k++) v[k] = a[(size_t)(E * t + k) * N2];
+    inv_consec<LA>(v, tw, base, t, q, q2);
+#pragma unroll
+    for (int k = 0; k < E; k++) sm[pad<H>(E * t + k) * C + j] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < E; k++) v[k] = sm[pad<H>(t + E * k) * C + j];
+    inv_stride<LA>(v, tw, base, q, q2);
+    const uint64_t ni = tab.ninv[pi], nis = tab.ninv_sh[pi];
+#pragma unroll
+    for (int k = 0; k < E; k++) a[(size_t)(t + E * k) * N2] = shoup(v[k], ni, nis, q);
+}
+
+}  // namespace nttr
+}  // namespace bm
