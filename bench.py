@@ -160,6 +160,38 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+# Integer-multiply peak of the NTT passes: 152 SMs x 64 32-bit multiply results per
+# clock per SM (the integer multiply-add rate of the SM, half its 128 FP32 lanes)
+# x the maximum SM clock.  A 64-bit Shoup butterfly needs 16 such results: the
+# high 64 bits of x*w' (four 32x32-bit products, low and high halves) and the low
+# 64 bits of x*w and of floor(x*w'/2^64)*q (four each).
+SM_COUNT = 152
+INT32_MUL_PER_CLK_PER_SM = 64
+
+
+def alu_peak_tops():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        mhz = 2070.0
+    return SM_COUNT * INT32_MUL_PER_CLK_PER_SM * mhz * 1e6 / 1e12
+
+
+def across_ranks(total_s, work, world):
+    """Whole-job rate: work summed over ranks / the slowest rank's time.  Returns (rate, max_time)."""
+    if world == 1:
+        return work / total_s, total_s
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+    w = torch.tensor([work], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(w.item()) / float(t.item()), float(t.item())
+
+
 def percentile(xs, p):
     xs = sorted(xs)
     k = min(len(xs) - 1, max(0, int(round(p / 100.0 * (len(xs) - 1)))))
@@ -227,12 +259,8 @@ def main():
     torch.cuda.synchronize()
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * matches_per_step * args.steps / (total_ms / 1e3)
+    value, total_s = across_ranks(sum(step_ms) / 1e3, matches_per_step * args.steps, world)
+    total_ms = total_s * 1e3
 
     # per-class device time over the same number of steps (event pair per launch)
     bm.bm_profile_control(1, 1)
@@ -244,14 +272,23 @@ def main():
     prof = {kind: bm.bm_profile_read(kind) for kind in bm.KERNEL_KINDS}
     bm.bm_profile_control(0, 1)
     dom = max(prof, key=lambda k: prof[k][1])
-    n_l, ms_l, by_l = prof[dom]
-    peak, peak_src = load_peaks()
-    achieved = by_l / (ms_l / 1e3) / 1e9 if ms_l > 0 else 0.0
-    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
-                "launches_per_step": n_l / args.steps, "avg_launch_us": 1e3 * ms_l / max(n_l, 1),
-                "alg_bytes_per_launch": by_l / max(n_l, 1),
-                "share_of_kernel_time": ms_l / max(sum(v[1] for v in prof.values()), 1e-12)}
+    n_l, ms_l, by_l, ops_l = prof[dom]
+    peak_hbm, peak_src = load_peaks()
+    hbm_gbs = by_l / (ms_l / 1e3) / 1e9 if ms_l > 0 else 0.0
+    if ops_l > 0:
+        achieved = ops_l / (ms_l / 1e3) / 1e12
+        peak = alu_peak_tops()
+        roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmul32/s",
+                    "frac": achieved / peak, "peak_source": "derived: 152 SMs x 64 int32 mul/clk x max SM clock",
+                    "traffic": None}
+    else:
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": hbm_gbs, "peak": peak_hbm, "unit": "GB/s",
+                    "frac": hbm_gbs / peak_hbm, "peak_source": peak_src, "traffic": None}
+    roofline.update({"hbm_view": {"achieved_gbs": hbm_gbs, "peak_gbs": peak_hbm, "frac": hbm_gbs / peak_hbm,
+                                  "peak_source": peak_src},
+                     "launches_per_step": n_l / args.steps, "avg_launch_us": 1e3 * ms_l / max(n_l, 1),
+                     "alg_bytes_per_launch": by_l / max(n_l, 1), "alg_mul32_per_launch": ops_l / max(n_l, 1),
+                     "share_of_kernel_time": ms_l / max(sum(v[1] for v in prof.values()), 1e-12)})
     breakdown = {k: {"launches": v[0] // args.steps, "ms_per_step": v[1] / args.steps,
                      "alg_GB_per_step": v[2] / args.steps / 1e9} for k, v in prof.items() if v[0]}
 
@@ -270,11 +307,7 @@ def main():
     ncts, lvl = bm.bm_ciphertext_info(host_cts[0])
     h2d = W.n_queries * ncts * 2 * (lvl + 1) * ctx.n * 8
     d2h = W.n_queries * n_out * 2 * ctx.n * 8
-    e2e_total = sum(e2e_s)
-    if world > 1:
-        t = torch.tensor([e2e_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_value, _ = across_ranks(sum(e2e_s), matches_per_step * args.steps, world)
 
     if rank != 0:
         return
@@ -286,7 +319,7 @@ def main():
                    "queries_per_step": W.n_queries, "l2": "flushed between steps (512 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "latency_ms": {"p50": percentile(step_ms, 50), "p99": percentile(step_ms, 99)},
-        "e2e": {"value": world * matches_per_step * args.steps / e2e_total, "unit": UNIT,
+        "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_timed,
         "roofline": roofline,

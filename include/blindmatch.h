@@ -264,13 +264,17 @@ enum {
     BM_KERNEL_KINDS = 9
 };
 
-/* Process-wide counters of kernel launches and of their algorithmic bytes (the
- * reads and writes each launch must make, counted per kernel from its operand
- * sizes), per class.  With timing != 0 every later launch is bracketed by a CUDA
- * event pair on its stream and its device time accumulated.  reset != 0 zeroes
- * the counters.  Reading waits for the recorded events. */
+/* Process-wide counters of kernel launches and of their algorithmic work, per
+ * class: bytes (the reads and writes each launch must make, from its operand
+ * sizes) and 32-bit multiply operations (for the NTT passes: 16 per 64-bit
+ * modular butterfly -- the 32x32-bit partial products of the three 64-bit
+ * products of a Shoup multiplication, counting low and high halves).  With
+ * timing != 0 every later launch is bracketed by a CUDA event pair on its stream
+ * and its device time accumulated (bm_match then runs its plan without the graph).
+ * reset != 0 zeroes the counters.  Reading waits for the recorded events. */
 bm_status bm_profile_control(uint32_t timing, uint32_t reset);
-bm_status bm_profile_read(uint32_t kind, uint64_t* launches, double* device_ms, double* alg_bytes);
+bm_status bm_profile_read(uint32_t kind, uint64_t* launches, double* device_ms, double* alg_bytes,
+                          double* alg_mulops);
 
 #ifdef __cplusplus
 }

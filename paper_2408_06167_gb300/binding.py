@@ -73,7 +73,7 @@ _SIGS = {
     "bm_ntt_inverse": (ctypes.c_int, [_vp, _vp, _u32, _u32, _vp]),
     "bm_ct_rotate_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _u32, _u32, _i32, _vp, _vp]),
     "bm_profile_control": (ctypes.c_int, [_u32, _u32]),
-    "bm_profile_read": (ctypes.c_int, [_u32, _U64P, _DP, _DP]),
+    "bm_profile_read": (ctypes.c_int, [_u32, _U64P, _DP, _DP, _DP]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_L, _name)
@@ -343,8 +343,8 @@ def bm_profile_control(timing, reset):
 
 
 def bm_profile_read(kind):
-    """(launches, device_ms, algorithmic_bytes) of one kernel class."""
+    """(launches, device_ms, algorithmic_bytes, algorithmic_32bit_mul_ops) of one kernel class."""
     k = KERNEL_KINDS.index(kind) if isinstance(kind, str) else kind
-    n, ms, by = _u64(), _dbl(), _dbl()
-    _check(_L.bm_profile_read(k, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
-    return n.value, ms.value, by.value
+    n, ms, by, ops = _u64(), _dbl(), _dbl(), _dbl()
+    _check(_L.bm_profile_read(k, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by), ctypes.byref(ops)))
+    return n.value, ms.value, by.value, ops.value

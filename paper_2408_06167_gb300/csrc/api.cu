@@ -197,6 +197,7 @@ static bm_status context_init(Context& c, const bm_params& p, int device) {
         c.tab.tw[j] = (const ulonglong2*)c.d_twiddles + j * per;
         c.tab.itw[j] = (const ulonglong2*)c.d_twiddles + j * per + c.n;
     }
+    BM_CUDA_TRY(build_ks_constants(c));
     return BM_OK;
 }
 
@@ -267,6 +268,7 @@ void bm_context_destroy(bm_context* ctx) {
     for (Plan* p : ctx->c.plans) destroy_plan(p);
     ctx->c.plans.clear();
     if (ctx->c.d_twiddles) cudaFree(ctx->c.d_twiddles);
+    if (ctx->c.d_ksc) cudaFree(ctx->c.d_ksc);
     if (ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
     delete ctx;
 }

@@ -44,6 +44,17 @@ struct LimbBatch {
     }
 };
 
+// Constants of key switching at one level (device table, one entry per level).
+struct KsLevelConst {
+    uint32_t nd, nlx;                          // digits present; limbs of Q_l u P
+    uint32_t dstart[MAXD], dsz[MAXD];          // Q-limb range of each digit at this level
+    ulonglong2 up_hinv[MAXD][MAXDS];           // (D/d_i)^-1 mod d_i            (Shoup pairs)
+    ulonglong2 up_hat[MAXD][MAXDS][MAXB];      // (D/d_i) mod t_jj, jj over Q_l u P
+    ulonglong2 dn_hinv[BM_MAX_P];              // N^-1 (P/p_i)^-1 mod p_i
+    ulonglong2 dn_hat[BM_MAX_P][MAXB];         // (P/p_i) mod q_j
+    ulonglong2 pinv[MAXB];                     // P^-1 mod q_j
+};
+
 struct Plan;                                   // cached match schedule (api.cu)
 void destroy_plan(Plan* p);
 
@@ -59,6 +70,8 @@ struct Context {
     cudaStream_t stream = nullptr;            // for client-side helpers (keygen, encrypt)
     uint64_t P_mod[MAXB]{};                   // P mod each prime
     double scale = 0;
+    std::vector<KsLevelConst> h_ksc;          // key-switching constants per level (host copy)
+    KsLevelConst* d_ksc = nullptr;            // ... and on the device
     uint64_t next_id = 1;                     // ids of galleries and key sets (plan cache keys)
     std::vector<Plan*> plans;
 };
@@ -160,7 +173,7 @@ void decode_real(const Context& ctx, const double* coeffs, double scale, double*
 // bytes are always counted per kernel class; with timing enabled a CUDA event
 // pair is recorded around the launch on its stream.
 struct ProfScope {
-    ProfScope(int kind, cudaStream_t s, double alg_bytes, uint32_t launches = 1);
+    ProfScope(int kind, cudaStream_t s, double alg_bytes, double alg_ops = 0, uint32_t launches = 1);
     ~ProfScope();
     int kind;
     cudaStream_t s;
@@ -172,6 +185,7 @@ struct ProfScope {
 struct ProfSink {
     uint64_t launches[BM_KERNEL_KINDS] = {};
     double bytes[BM_KERNEL_KINDS] = {};
+    double ops[BM_KERNEL_KINDS] = {};
 };
 void prof_set_sink(ProfSink* sink);
 void prof_add(const ProfSink& counts);
@@ -192,6 +206,15 @@ cudaError_t ks_rotate(const Context& c, const uint64_t* key, uint64_t galois, ui
                       uint32_t B, uint64_t* const* d_in, uint64_t* const* d_out,
                       uint64_t* const* d_add, uint64_t* scratch, cudaStream_t s);
 size_t ks_scratch_words(const Context& c, uint32_t level, uint32_t B);
+// the same rotation in six fused kernels (ks_fused.cu), for rings 2^12 and 2^16
+bool ks_fused_supported(const Context& c);
+cudaError_t ks_rotate_fused(const Context& c, const uint64_t* key, uint64_t galois, uint32_t level,
+                            uint32_t B, uint64_t* const* d_in, uint64_t* const* d_out,
+                            uint64_t* const* d_add, uint64_t* scratch, cudaStream_t s);
+// inverse column pass alone (the second half of an inverse NTT)
+cudaError_t ntt_col_inverse(const Context& c, const LimbBatch& b, cudaStream_t s);
+// fills c.h_ksc / c.d_ksc
+cudaError_t build_ks_constants(Context& c);
 // out[b] = Res(in[b]); in at level, out at level-1 (no aliasing)
 cudaError_t rescale(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,
                     uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s);

@@ -140,12 +140,13 @@ cudaError_t ntt_launch(const LimbBatch& b, const DevTables& tab, bool inv, cudaS
     if (limbs == 0) return cudaSuccess;
     const dim3 gc(limbs, (1 << LB) / COLS), gr(limbs, (1 << LA) / ROWS);
     const double bytes = 16.0 * (1 << (LA + LB)) * limbs;   // each pass reads and writes every limb once
+    const double ops_c = 16.0 * (1 << (LA + LB - 1)) * LA * limbs, ops_r = 16.0 * (1 << (LA + LB - 1)) * LB * limbs;
     if (!inv) {
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes); k_ntt_cols<LA, LB, COLS, false><<<gc, kThreads, 0, s>>>(b, tab); }
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes); k_ntt_rows<LA, LB, ROWS, false><<<gr, kThreads, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_c); k_ntt_cols<LA, LB, COLS, false><<<gc, kThreads, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_r); k_ntt_rows<LA, LB, ROWS, false><<<gr, kThreads, 0, s>>>(b, tab); }
     } else {
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes); k_ntt_rows<LA, LB, ROWS, true><<<gr, kThreads, 0, s>>>(b, tab); }
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes); k_ntt_cols<LA, LB, COLS, true><<<gc, kThreads, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_r); k_ntt_rows<LA, LB, ROWS, true><<<gr, kThreads, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_c); k_ntt_cols<LA, LB, COLS, true><<<gc, kThreads, 0, s>>>(b, tab); }
     }
     return cudaGetLastError();
 }
@@ -166,12 +167,14 @@ cudaError_t ntt_launch_reg(const LimbBatch& b, const DevTables& tab, bool inv, c
     const dim3 gc(limbs, (1 << LB) / C), gr(limbs, (1 << LA) / R);
     const int tc = C * (1 << (LA / 2)), tr = R * (1 << (LB / 2));
     const double bytes = 16.0 * (1 << (LA + LB)) * limbs;   // each pass reads and writes every limb once
+    const double ops_c = 16.0 * (1 << (LA + LB - 1)) * LA * limbs;   // 16 mul ops per butterfly
+    const double ops_r = 16.0 * (1 << (LA + LB - 1)) * LB * limbs;
     if (!inv) {
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes); nttr::k_col_fwd<LA, LB, C><<<gc, tc, 0, s>>>(b, tab); }
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes); nttr::k_row_fwd<LA, LB, R><<<gr, tr, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_c); nttr::k_col_fwd<LA, LB, C><<<gc, tc, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_r); nttr::k_row_fwd<LA, LB, R><<<gr, tr, 0, s>>>(b, tab); }
     } else {
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes); nttr::k_row_inv<LA, LB, R><<<gr, tr, 0, s>>>(b, tab); }
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes); nttr::k_col_inv<LA, LB, C><<<gc, tc, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_r); nttr::k_row_inv<LA, LB, R><<<gr, tr, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_c); nttr::k_col_inv<LA, LB, C><<<gc, tc, 0, s>>>(b, tab); }
     }
     return cudaGetLastError();
 }
@@ -513,6 +516,71 @@ inline dim3 elem_grid(uint32_t n, uint32_t y) { return dim3((n + kThreads - 1) /
 // ===========================================================================
 
 cudaError_t ntt_forward(const Context& c, const LimbBatch& b, cudaStream_t s) { return ntt_dispatch(c, b, false, s); }
+
+cudaError_t ntt_col_inverse(const Context& c, const LimbBatch& b, cudaStream_t s) {
+    const uint32_t limbs = b.n_polys * b.nl;
+    if (limbs == 0) return cudaSuccess;
+    const double lw = 16.0 * c.n * limbs, ops = 16.0 * (c.n / 2) * (c.log_n / 2) * limbs;
+    ProfScope ps(BM_KERNEL_NTT, s, lw, ops);
+    if (c.log_n == 16) nttr::k_col_inv<8, 8, 8><<<dim3(limbs, 256 / 8), 8 * 16, 0, s>>>(b, c.tab);
+    else if (c.log_n == 12) nttr::k_col_inv<6, 6, 16><<<dim3(limbs, 64 / 16), 16 * 8, 0, s>>>(b, c.tab);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t build_ks_constants(Context& c) {
+    auto pair = [](uint64_t w, uint64_t q) { return make_ulonglong2(w % q, h_shoup_companion(w % q, q)); };
+    c.h_ksc.assign(c.L + 1, KsLevelConst{});
+    for (uint32_t l = 0; l <= c.L; l++) {
+        KsLevelConst& K = c.h_ksc[l];
+        const uint32_t l1 = l + 1, nlx = l1 + c.alpha;
+        K.nlx = nlx;
+        auto xprime = [&](uint32_t jj) { return c.primes[jj < l1 ? jj : c.L + 1 + (jj - l1)]; };
+        uint32_t nd = 0;
+        for (const auto& dg : c.digits) {
+            if (dg.empty() || dg[0] > l) continue;
+            uint32_t ds = 0;
+            for (uint32_t x : dg) ds += (x <= l);
+            K.dstart[nd] = dg[0];
+            K.dsz[nd] = ds;
+            for (uint32_t i = 0; i < ds; i++) {
+                const uint64_t qi = c.primes[dg[0] + i];
+                uint64_t hat = 1;
+                for (uint32_t k = 0; k < ds; k++)
+                    if (k != i) hat = h_mulmod(hat, c.primes[dg[0] + k] % qi, qi);
+                K.up_hinv[nd][i] = pair(h_invmod(hat, qi), qi);
+                for (uint32_t jj = 0; jj < nlx; jj++) {
+                    const uint64_t t = xprime(jj);
+                    uint64_t ht = 1;
+                    for (uint32_t k = 0; k < ds; k++)
+                        if (k != i) ht = h_mulmod(ht, c.primes[dg[0] + k] % t, t);
+                    K.up_hat[nd][i][jj] = pair(ht, t);
+                }
+            }
+            nd++;
+        }
+        K.nd = nd;
+        for (uint32_t i = 0; i < c.alpha; i++) {
+            const uint64_t pi = c.primes[c.L + 1 + i];
+            uint64_t hat = 1;
+            for (uint32_t k = 0; k < c.alpha; k++)
+                if (k != i) hat = h_mulmod(hat, c.primes[c.L + 1 + k] % pi, pi);
+            const uint64_t w = h_mulmod(h_invmod(hat, pi), h_invmod(c.n % pi, pi), pi);
+            K.dn_hinv[i] = pair(w, pi);
+            for (uint32_t j = 0; j < l1; j++) {
+                const uint64_t t = c.primes[j];
+                uint64_t ht = 1;
+                for (uint32_t k = 0; k < c.alpha; k++)
+                    if (k != i) ht = h_mulmod(ht, c.primes[c.L + 1 + k] % t, t);
+                K.dn_hat[i][j] = pair(ht, t);
+            }
+        }
+        for (uint32_t j = 0; j < l1; j++) K.pinv[j] = pair(h_invmod(c.P_mod[j], c.primes[j]), c.primes[j]);
+    }
+    cudaError_t e = cudaMalloc(&c.d_ksc, sizeof(KsLevelConst) * c.h_ksc.size());
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(c.d_ksc, c.h_ksc.data(), sizeof(KsLevelConst) * c.h_ksc.size(), cudaMemcpyHostToDevice);
+}
 cudaError_t ntt_inverse(const Context& c, const LimbBatch& b, cudaStream_t s) { return ntt_dispatch(c, b, true, s); }
 
 cudaError_t to_montgomery(const Context& c, const LimbBatch& b, bool inverse, cudaStream_t s) {
@@ -580,6 +648,7 @@ cudaError_t ks_rotate(const Context& c, const uint64_t* key, uint64_t galois, ui
                       uint64_t* const* d_in, uint64_t* const* d_out, uint64_t* const* d_add, uint64_t* scratch,
                       cudaStream_t s) {
     if (B == 0) return cudaSuccess;
+    if (ks_fused_supported(c)) return ks_rotate_fused(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
     const uint32_t n = c.n, l1 = level + 1, nlx = l1 + c.alpha;
     // digits present at this level
     ModUpPlan mu{};

@@ -1,0 +1,420 @@
+// ks_fused.cu -- rotation (Galois automorphism + hybrid key switching) in six
+// fused kernels, for the rings whose NTT passes are register resident (2^12, 2^16).
+//
+// Rot(ct, r) of Sec. 2 on B ciphertexts (c0, c1) at level l, NTT form:
+//   F1  inverse row pass of c1; copy of c0; the digit's own extended limbs as
+//       the NTT-domain automorphism of c1 (no transform needed for them)
+//   F2  inverse column pass of c1 -> coefficient form
+//   F3  per digit: automorphism gather (X^p <- +-X^(p k^-1)) + fast base
+//       conversion to each other limb of Q_l u P + forward column pass
+//   F4  per extended limb: forward row pass, inner product with the rotation
+//       key over the digits, and for the special-prime limbs the inverse row pass
+//   F5  inverse column pass of the special-prime limbs, conversion P -> Q_l,
+//       forward column pass
+//   F6  forward row pass, (acc - conv) * P^-1 + sigma(c0) (+ addend) -> out
+// Each kernel reads and writes every coefficient once; the scratch holds
+// X0, X1, ext, acc and conv (the same words as the staged kernels).
+#include <cuda_runtime.h>
+
+#include "bm_internal.h"
+#include "ntt_reg.cuh"
+
+namespace bm {
+namespace {
+
+using nttr::pad;
+
+__device__ __forceinline__ uint32_t brev_n(uint32_t x, uint32_t bits) { return __brev(x) >> (32 - bits); }
+
+// NTT-domain automorphism: NTT(sigma_k a)[i] = NTT(a)[perm(i)]
+__device__ __forceinline__ uint32_t perm_src(uint32_t i, uint32_t log_n, uint32_t galois) {
+    const uint32_t r = brev_n(i, log_n);
+    const uint32_t e = ((2u * r + 1u) * galois) & ((2u << log_n) - 1);
+    return brev_n((e - 1u) >> 1, log_n);
+}
+
+__device__ __forceinline__ int ext_prime(int jj, int l1, int L) { return jj < l1 ? jj : L + 1 + (jj - l1); }
+
+__device__ __forceinline__ uint64_t red6(uint64_t y, uint64_t t) {   // [0, 6t) -> [0, 4t)
+    return y >= 4 * t ? y - 4 * t : y;
+}
+
+// ---------------------------------------------------------------------------
+// F1: grid (B * l1, N1 / R)
+// ---------------------------------------------------------------------------
+template <int LA, int LB, int R>
+__global__ void __launch_bounds__(R * (1 << (LB / 2)))
+    k_ks_f1(uint64_t* const* in, uint64_t* __restrict__ X0, uint64_t* __restrict__ X1, uint64_t* __restrict__ ext,
+            const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t galois) {
+    constexpr int H = LB / 2, E = 1 << H, M = 1 << LB, S = M + M / E, LOGN = LA + LB, N = 1 << LOGN;
+    __shared__ uint64_t sm[R * S];
+    const int tid = threadIdx.x, jr = tid / E, t = tid % E;
+    const uint32_t b = blockIdx.x / l1, j = blockIdx.x % l1;
+    const int row = blockIdx.y * R + jr;
+    const size_t roff = (size_t)row * M;
+    const uint64_t q = tab.q[j], q2 = 2 * q;
+    const uint64_t* c0 = in[b] + (size_t)j * N;
+    const uint64_t* c1 = in[b] + ((size_t)l1 + j) * N;
+    const uint32_t nd = kc->nd, nlx = kc->nlx;
+    uint32_t d = 0;
+    while (d + 1 < nd && j >= kc->dstart[d + 1]) d++;
+    uint64_t* x0 = X0 + ((size_t)b * l1 + j) * N + roff;
+    uint64_t* eo = ext + (((size_t)b * nd + d) * nlx + j) * N + roff;
+#pragma unroll
+    for (int k = 0; k < E; k++) {
+        const int c = t + E * k;
+        x0[c] = c0[roff + c];
+        eo[c] = c1[perm_src((uint32_t)(roff + c), LOGN, galois)];
+    }
+    uint64_t v[E];
+    uint64_t* sr = sm + jr * S;
+#pragma unroll
+    for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = c1[roff + t + E * k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < E; k++) v[k] = sr[pad<H>(E * t + k)];
+    const auto base = [row](int s) { return (1 << (LA + s)) + row * (1 << s); };
+    nttr::inv_consec<LB>(v, tab.itw[j], base, t, q, q2);
+#pragma unroll
+    for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < E; k++) v[k] = sr[pad<H>(t + E * k)];
+    nttr::inv_stride<LB>(v, tab.itw[j], base, q, q2);
+    uint64_t* x1 = X1 + ((size_t)b * l1 + j) * N + roff;
+#pragma unroll
+    for (int k = 0; k < E; k++) x1[t + E * k] = v[k];
+}
+
+// ---------------------------------------------------------------------------
+// F3: grid (B * nd, N2 / C).  X1 holds c1 in coefficient form.
+// ---------------------------------------------------------------------------
+constexpr int kMaxDigit = 2;   // limbs per digit and special primes handled by the fused kernels
+
+template <int LA, int LB, int C>
+__global__ void __launch_bounds__(C * (1 << (LA / 2)))
+    k_ks_f3(const uint64_t* __restrict__ X1, uint64_t* __restrict__ ext, const KsLevelConst* __restrict__ kc,
+            DevTables tab, uint32_t l1, uint32_t L, uint32_t kinv) {
+    constexpr int H = LA / 2, E = 1 << H, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN;
+    __shared__ uint64_t sm[(M + M / E) * C];
+    const int tid = threadIdx.x, t = tid / C, jc = tid % C;
+    const uint32_t nd = kc->nd, nlx = kc->nlx;
+    const uint32_t b = blockIdx.x / nd, d = blockIdx.x % nd;
+    const int col = blockIdx.y * C + jc;
+    const uint32_t ds = kc->dsz[d], d0 = kc->dstart[d];
+    uint64_t v[kMaxDigit][E];
+#pragma unroll
+    for (int k = 0; k < E; k++) {
+        const uint32_t p = (uint32_t)(t + E * k) * N2 + col;
+        const uint32_t e = (p * kinv) & (2u * N - 1);
+        const uint32_t src = e & (N - 1);
+        const bool neg = e >= (uint32_t)N;
+#pragma unroll
+        for (int i = 0; i < kMaxDigit; i++) {
+            if (i < (int)ds) {
+                const uint64_t qi = tab.q[d0 + i];
+                uint64_t x = X1[((size_t)b * l1 + d0 + i) * N + src];
+                if (neg) x = negm(x, qi);
+                const ulonglong2 h = kc->up_hinv[d][i];
+                v[i][k] = shoup(x, h.x, h.y, qi);
+            }
+        }
+    }
+    const auto base = [](int s) { return 1 << s; };
+    for (uint32_t jj = 0; jj < nlx; jj++) {
+        if (jj >= d0 && jj < d0 + ds) continue;               // the digit's own limbs come from F1
+        const int pi = ext_prime(jj, l1, L);
+        const uint64_t tq = tab.q[pi], tq2 = 2 * tq;
+        uint64_t y[E];
+#pragma unroll
+        for (int k = 0; k < E; k++) {
+            uint64_t acc = 0;
+#pragma unroll
+            for (int i = 0; i < kMaxDigit; i++) {
+                if (i < (int)ds) {
+                    const ulonglong2 h = kc->up_hat[d][i][jj];
+                    acc += shoup_lazy(v[i][k], h.x, h.y, tq);
+                }
+            }
+            y[k] = red6(acc, tq);
+        }
+        nttr::fwd_stride<LA>(y, tab.tw[pi], base, tq, tq2);
+#pragma unroll
+        for (int k = 0; k < E; k++) sm[pad<H>(t + E * k) * C + jc] = y[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < E; k++) y[k] = sm[pad<H>(E * t + k) * C + jc];
+        nttr::fwd_consec<LA>(y, tab.tw[pi], base, t, tq, tq2);
+        uint64_t* o = ext + (((size_t)b * nd + d) * nlx + jj) * N + col;
+#pragma unroll
+        for (int k = 0; k < E; k++) o[(size_t)(E * t + k) * N2] = y[k];
+        __syncthreads();
+    }
+}
+
+// F4 epilogue for one key component: Q limbs are final NTT values (reduced),
+// special-prime limbs get the inverse row pass; stored in the stride layout.
+template <int LA, int LB, typename BaseF>
+__device__ __forceinline__ void f4_store(uint64_t (&a)[1 << (LB / 2)], uint64_t (&v)[1 << (LB / 2)], uint64_t* sr,
+                                         uint64_t* o, bool q_limb, const ulonglong2* itw, BaseF base, int t,
+                                         uint64_t q, uint64_t q2) {
+    constexpr int H = LB / 2, E = 1 << H;
+    if (q_limb) {
+#pragma unroll
+        for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = reduce2(a[k], q);
+    } else {
+        nttr::inv_consec<LB>(a, itw, base, t, q, q2);
+#pragma unroll
+        for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = a[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < E; k++) v[k] = sr[pad<H>(t + E * k)];
+    if (!q_limb) nttr::inv_stride<LB>(v, itw, base, q, q2);
+#pragma unroll
+    for (int k = 0; k < E; k++) o[t + E * k] = v[k];
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// F4: grid (B * nlx, N1 / R).  acc = sum_d ext_d * key_d (both components).
+// ---------------------------------------------------------------------------
+template <int LA, int LB, int R>
+__global__ void __launch_bounds__(R * (1 << (LB / 2)))
+    k_ks_f4(const uint64_t* __restrict__ ext, const uint64_t* __restrict__ key, uint64_t* __restrict__ acc,
+            const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L, uint32_t nb) {
+    constexpr int H = LB / 2, E = 1 << H, M = 1 << LB, S = M + M / E, LOGN = LA + LB, N = 1 << LOGN;
+    __shared__ uint64_t sm[R * S];
+    const int tid = threadIdx.x, jr = tid / E, t = tid % E;
+    const uint32_t nd = kc->nd, nlx = kc->nlx;
+    const uint32_t b = blockIdx.x / nlx, jj = blockIdx.x % nlx;
+    const int pi = ext_prime(jj, l1, L);
+    const uint64_t q = tab.q[pi], qn = tab.qneg[pi], q2 = 2 * q;
+    const int row = blockIdx.y * R + jr;
+    const size_t roff = (size_t)row * M;
+    const auto base = [row](int s) { return (1 << (LA + s)) + row * (1 << s); };
+    uint64_t* sr = sm + jr * S;
+    uint64_t a0[E], a1[E], v[E];
+#pragma unroll
+    for (int k = 0; k < E; k++) a0[k] = a1[k] = 0;
+    for (uint32_t d = 0; d < nd; d++) {
+        const uint64_t* e = ext + (((size_t)b * nd + d) * nlx + jj) * N + roff;
+        const bool own = jj >= kc->dstart[d] && jj < kc->dstart[d] + kc->dsz[d];
+        if (own) {
+#pragma unroll
+            for (int k = 0; k < E; k++) v[k] = e[E * t + k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < E; k++) v[k] = e[t + E * k];
+            nttr::fwd_stride<LB>(v, tab.tw[pi], base, q, q2);
+#pragma unroll
+            for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = v[k];
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < E; k++) v[k] = sr[pad<H>(E * t + k)];
+            nttr::fwd_consec<LB>(v, tab.tw[pi], base, t, q, q2);
+            __syncthreads();
+        }
+        const uint64_t* kb = key + ((size_t)(d * 2 + 0) * nb + pi) * N + roff + E * t;
+        const uint64_t* ka = key + ((size_t)(d * 2 + 1) * nb + pi) * N + roff + E * t;
+#pragma unroll
+        for (int k = 0; k < E; k++) {
+            uint64_t x0 = a0[k] + mont_lazy(v[k], kb[k], q, qn);
+            uint64_t x1 = a1[k] + mont_lazy(v[k], ka[k], q, qn);
+            a0[k] = x0 >= q2 ? x0 - q2 : x0;
+            a1[k] = x1 >= q2 ? x1 - q2 : x1;
+        }
+    }
+    f4_store<LA, LB>(a0, v, sr, acc + (((size_t)b * 2 + 0) * nlx + jj) * N + roff, jj < l1, tab.itw[pi], base, t, q,
+                     q2);
+    f4_store<LA, LB>(a1, v, sr, acc + (((size_t)b * 2 + 1) * nlx + jj) * N + roff, jj < l1, tab.itw[pi], base, t, q,
+                     q2);
+}
+
+// ---------------------------------------------------------------------------
+// F5: grid (B * 2, N2 / C).  conv = Conv_{P -> Q_l}(acc's special-prime limbs).
+// ---------------------------------------------------------------------------
+template <int LA, int LB, int C>
+__global__ void __launch_bounds__(C * (1 << (LA / 2)))
+    k_ks_f5(const uint64_t* __restrict__ acc, uint64_t* __restrict__ conv, const KsLevelConst* __restrict__ kc,
+            DevTables tab, uint32_t l1, uint32_t L, uint32_t alpha) {
+    constexpr int H = LA / 2, E = 1 << H, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN;
+    __shared__ uint64_t sm[(M + M / E) * C];
+    const int tid = threadIdx.x, t = tid / C, jc = tid % C;
+    const uint32_t b = blockIdx.x / 2, comp = blockIdx.x % 2;
+    const int col = blockIdx.y * C + jc;
+    const uint32_t nlx = l1 + alpha;
+    const auto base = [](int s) { return 1 << s; };
+    uint64_t v[kMaxDigit][E];
+#pragma unroll
+    for (int i = 0; i < kMaxDigit; i++) {
+        if (i < (int)alpha) {
+            const int pi = L + 1 + i;
+            const uint64_t p = tab.q[pi], p2 = 2 * p;
+            const uint64_t* src = acc + (((size_t)b * 2 + comp) * nlx + l1 + i) * N + col;
+            uint64_t x[E];
+#pragma unroll
+            for (int k = 0; k < E; k++) x[k] = src[(size_t)(E * t + k) * N2];
+            nttr::inv_consec<LA>(x, tab.itw[pi], base, t, p, p2);
+#pragma unroll
+            for (int k = 0; k < E; k++) sm[pad<H>(E * t + k) * C + jc] = x[k];
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < E; k++) x[k] = sm[pad<H>(t + E * k) * C + jc];
+            nttr::inv_stride<LA>(x, tab.itw[pi], base, p, p2);
+            const ulonglong2 h = kc->dn_hinv[i];          // N^-1 * (P/p_i)^-1 mod p_i
+#pragma unroll
+            for (int k = 0; k < E; k++) v[i][k] = shoup(x[k], h.x, h.y, p);
+            __syncthreads();
+        }
+    }
+    for (uint32_t j = 0; j < l1; j++) {
+        const uint64_t q = tab.q[j], q2 = 2 * q;
+        uint64_t y[E];
+#pragma unroll
+        for (int k = 0; k < E; k++) {
+            uint64_t s = 0;
+#pragma unroll
+            for (int i = 0; i < kMaxDigit; i++) {
+                if (i < (int)alpha) {
+                    const ulonglong2 h = kc->dn_hat[i][j];
+                    s += shoup_lazy(v[i][k], h.x, h.y, q);
+                }
+            }
+            y[k] = red6(s, q);
+        }
+        nttr::fwd_stride<LA>(y, tab.tw[j], base, q, q2);
+#pragma unroll
+        for (int k = 0; k < E; k++) sm[pad<H>(t + E * k) * C + jc] = y[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < E; k++) y[k] = sm[pad<H>(E * t + k) * C + jc];
+        nttr::fwd_consec<LA>(y, tab.tw[j], base, t, q, q2);
+        uint64_t* o = conv + (((size_t)b * 2 + comp) * l1 + j) * N + col;
+#pragma unroll
+        for (int k = 0; k < E; k++) o[(size_t)(E * t + k) * N2] = y[k];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// F6: grid (B * l1, N1 / R).  out = (acc - conv) * P^-1 + sigma(c0) (+ add)
+// ---------------------------------------------------------------------------
+template <int LA, int LB, int R>
+__global__ void __launch_bounds__(R * (1 << (LB / 2)))
+    k_ks_f6(const uint64_t* __restrict__ conv, const uint64_t* __restrict__ acc, const uint64_t* __restrict__ X0,
+            uint64_t* const* out, uint64_t* const* add, const KsLevelConst* __restrict__ kc, DevTables tab,
+            uint32_t l1, uint32_t galois) {
+    constexpr int H = LB / 2, E = 1 << H, M = 1 << LB, S = M + M / E, LOGN = LA + LB, N = 1 << LOGN;
+    __shared__ uint64_t sm[R * S];
+    const int tid = threadIdx.x, jr = tid / E, t = tid % E;
+    const uint32_t b = blockIdx.x / l1, j = blockIdx.x % l1;
+    const uint32_t nlx = kc->nlx;
+    const int row = blockIdx.y * R + jr;
+    const size_t roff = (size_t)row * M;
+    const uint64_t q = tab.q[j], q2 = 2 * q;
+    const ulonglong2 pinv = kc->pinv[j];
+    const auto base = [row](int s) { return (1 << (LA + s)) + row * (1 << s); };
+    uint64_t* sr = sm + jr * S;
+    uint64_t v[E];
+#pragma unroll
+    for (int comp = 0; comp < 2; comp++) {
+        const uint64_t* cv = conv + (((size_t)b * 2 + comp) * l1 + j) * N + roff;
+#pragma unroll
+        for (int k = 0; k < E; k++) v[k] = cv[t + E * k];
+        nttr::fwd_stride<LB>(v, tab.tw[j], base, q, q2);
+#pragma unroll
+        for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = v[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < E; k++) v[k] = sr[pad<H>(E * t + k)];
+        nttr::fwd_consec<LB>(v, tab.tw[j], base, t, q, q2);
+        const uint64_t* av = acc + (((size_t)b * 2 + comp) * nlx + j) * N + roff + E * t;
+        const uint64_t* ad = add ? add[b] + ((size_t)comp * l1 + j) * N + roff + E * t : nullptr;
+#pragma unroll
+        for (int k = 0; k < E; k++) {
+            uint64_t o = shoup(subm(av[k], nttr::reduce4(v[k], q, q2), q), pinv.x, pinv.y, q);
+            if (comp == 0)
+                o = addm(o, X0[((size_t)b * l1 + j) * N + perm_src((uint32_t)(roff + E * t + k), LOGN, galois)], q);
+            if (ad) o = addm(o, ad[k], q);
+            sr[pad<H>(E * t + k)] = o;
+        }
+        __syncthreads();
+        uint64_t* o = out[b] + ((size_t)comp * l1 + j) * N + roff;
+#pragma unroll
+        for (int k = 0; k < E; k++) o[t + E * k] = sr[pad<H>(t + E * k)];
+        __syncthreads();
+    }
+}
+
+template <int LA, int LB, int C, int R>
+cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galois, uint32_t level, uint32_t B,
+                            uint64_t* const* d_in, uint64_t* const* d_out, uint64_t* const* d_add, uint64_t* scratch,
+                            cudaStream_t s) {
+    constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
+    const KsLevelConst& K = c.h_ksc[level];
+    const uint32_t l1 = level + 1, nd = K.nd, nlx = K.nlx, alpha = c.alpha;
+    const KsLevelConst* kc = c.d_ksc + level;
+    uint64_t* X0 = scratch;
+    uint64_t* X1 = X0 + (size_t)B * l1 * N;
+    uint64_t* ext = X1 + (size_t)B * l1 * N;
+    uint64_t* acc = ext + (size_t)B * nd * nlx * N;
+    uint64_t* conv = acc + (size_t)B * 2 * nlx * N;
+    const int tr = R * (1 << (LB / 2)), tc = C * (1 << (LA / 2));
+    const double lw = 8.0 * N;                                  // bytes of one limb
+    const double bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;   // mul ops of one limb pass
+    uint32_t targets = 0, gathers = 0;
+    for (uint32_t d = 0; d < nd; d++) {
+        targets += nlx - K.dsz[d];
+        gathers += K.dsz[d] * (nlx - K.dsz[d]);
+    }
+    {
+        ProfScope ps(BM_KERNEL_NTT, s, lw * B * l1 * 6, bf_r * B * l1);
+        k_ks_f1<LA, LB, R><<<dim3(B * l1, N1 / R), tr, 0, s>>>(d_in, X0, X1, ext, kc, c.tab, l1, (uint32_t)galois);
+    }
+    LimbBatch xb{X1, B, (uint64_t)l1 * N, 0, l1, 0};
+    for (uint32_t k = 0; k < l1; k++) xb.set(k, k);
+    cudaError_t e = ntt_col_inverse(c, xb, s);
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope ps(BM_KERNEL_MODUP, s, lw * B * (gathers + targets), bf_c * B * targets);
+        const uint32_t kinv = (uint32_t)h_invmod_pow2(galois, 2ull * N);
+        k_ks_f3<LA, LB, C><<<dim3(B * nd, N2 / C), tc, 0, s>>>(X1, ext, kc, c.tab, l1, c.L, kinv);
+    }
+    {
+        ProfScope ps(BM_KERNEL_KS_IP, s, lw * nlx * ((double)B * nd + 2.0 * nd + 2.0 * B),
+                     bf_r * B * (targets + 2.0 * alpha));
+        k_ks_f4<LA, LB, R><<<dim3(B * nlx, N1 / R), tr, 0, s>>>(ext, key, acc, kc, c.tab, l1, c.L, c.nb);
+    }
+    {
+        ProfScope ps(BM_KERNEL_MODDOWN, s, lw * B * 2 * (alpha + l1), bf_c * B * 2 * (alpha + l1));
+        k_ks_f5<LA, LB, C><<<dim3(B * 2, N2 / C), tc, 0, s>>>(acc, conv, kc, c.tab, l1, c.L, alpha);
+    }
+    {
+        ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * B * l1 * (2 + 2 + 1 + 2 + (d_add ? 2 : 0)), bf_r * B * 2 * l1);
+        k_ks_f6<LA, LB, R><<<dim3(B * l1, N1 / R), tr, 0, s>>>(conv, acc, X0, d_out, d_add, kc, c.tab, l1,
+                                                                 (uint32_t)galois);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool ks_fused_supported(const Context& c) {
+    if (c.log_n != 12 && c.log_n != 16) return false;
+    if (c.alpha > (uint32_t)kMaxDigit) return false;
+    for (const auto& d : c.digits)
+        if (d.size() > (size_t)kMaxDigit) return false;
+    return true;
+}
+
+cudaError_t ks_rotate_fused(const Context& c, const uint64_t* key, uint64_t galois, uint32_t level, uint32_t B,
+                            uint64_t* const* d_in, uint64_t* const* d_out, uint64_t* const* d_add, uint64_t* scratch,
+                            cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    if (c.log_n == 16) return ks_fused_launch<8, 8, 8, 8>(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
+    if (c.log_n == 12) return ks_fused_launch<6, 6, 16, 16>(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace bm

@@ -19,6 +19,11 @@
 namespace bm {
 namespace nttr {
 
+__device__ __forceinline__ uint64_t* limb_at(const LimbBatch& b, uint32_t limb, uint32_t n) {
+    const uint32_t poly = limb / b.nl, k = limb % b.nl;
+    return b.base + (size_t)poly * b.poly_stride + (size_t)(b.limb_off + k) * n;
+}
+
 // x, y in [0, 4q) -> x + w y, x - w y in [0, 4q)
 __device__ __forceinline__ void ct_bfly(uint64_t& x, uint64_t& y, const ulonglong2 w, uint64_t q, uint64_t q2) {
     const uint64_t a = x >= q2 ? x - q2 : x;
@@ -118,7 +123,7 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2))) k_col_fwd(LimbBatch lb, D
     __shared__ uint64_t sm[(M + M / E) * C];
     const int tid = threadIdx.x, t = tid / C, j = tid % C;
     const int pi = lb.prime(blockIdx.x % lb.nl);
-    uint64_t* a = limb_ptr(lb, blockIdx.x, M * N2) + blockIdx.y * C + j;
+    uint64_t* a = limb_at(lb, blockIdx.x, M * N2) + blockIdx.y * C + j;
     const uint64_t q = tab.q[pi], q2 = 2 * q;
     const ulonglong2* tw = tab.tw[pi];
     const auto base = [](int s) { return 1 << s; };
@@ -144,7 +149,7 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2))) k_row_fwd(LimbBatch lb, D
     const int tid = threadIdx.x, j = tid / E, t = tid % E;
     const int row = blockIdx.y * R + j;
     const int pi = lb.prime(blockIdx.x % lb.nl);
-    uint64_t* a = limb_ptr(lb, blockIdx.x, (1 << LA) * M) + (size_t)row * M;
+    uint64_t* a = limb_at(lb, blockIdx.x, (1 << LA) * M) + (size_t)row * M;
     const uint64_t q = tab.q[pi], q2 = 2 * q;
     const ulonglong2* tw = tab.tw[pi];
     const auto base = [row](int s) { return (1 << (LA + s)) + row * (1 << s); };
@@ -174,7 +179,7 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2))) k_row_inv(LimbBatch lb, D
     const int tid = threadIdx.x, j = tid / E, t = tid % E;
     const int row = blockIdx.y * R + j;
     const int pi = lb.prime(blockIdx.x % lb.nl);
-    uint64_t* a = limb_ptr(lb, blockIdx.x, (1 << LA) * M) + (size_t)row * M;
+    uint64_t* a = limb_at(lb, blockIdx.x, (1 << LA) * M) + (size_t)row * M;
     const uint64_t q = tab.q[pi], q2 = 2 * q;
     const ulonglong2* tw = tab.itw[pi];
     const auto base = [row](int s) { return (1 << (LA + s)) + row * (1 << s); };
@@ -203,7 +208,7 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2))) k_col_inv(LimbBatch lb, D
     __shared__ uint64_t sm[(M + M / E) * C];
     const int tid = threadIdx.x, t = tid / C, j = tid % C;
     const int pi = lb.prime(blockIdx.x % lb.nl);
-    uint64_t* a = limb_ptr(lb, blockIdx.x, M * N2) + blockIdx.y * C + j;
+    uint64_t* a = limb_at(lb, blockIdx.x, M * N2) + blockIdx.y * C + j;
     const uint64_t q = tab.q[pi], q2 = 2 * q;
     const ulonglong2* tw = tab.itw[pi];
     const auto base = [](int s) { return 1 << s; };

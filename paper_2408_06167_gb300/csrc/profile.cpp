@@ -24,6 +24,7 @@ struct Profiler {
     bool timing = false;
     uint64_t launches[BM_KERNEL_KINDS] = {};
     double bytes[BM_KERNEL_KINDS] = {};
+    double ops[BM_KERNEL_KINDS] = {};
     double ms[BM_KERNEL_KINDS] = {};
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> pool;
@@ -67,6 +68,7 @@ void prof_add(const ProfSink& counts) {
     for (int k = 0; k < BM_KERNEL_KINDS; k++) {
         p.launches[k] += counts.launches[k];
         p.bytes[k] += counts.bytes[k];
+        p.ops[k] += counts.ops[k];
     }
 }
 
@@ -76,16 +78,19 @@ bool prof_timing() {
     return p.timing;
 }
 
-ProfScope::ProfScope(int k, cudaStream_t st, double alg_bytes, uint32_t n) : kind(k), s(st), slot(-1) {
+ProfScope::ProfScope(int k, cudaStream_t st, double alg_bytes, double alg_ops, uint32_t n)
+    : kind(k), s(st), slot(-1) {
     if (t_sink) {
         t_sink->launches[kind] += n;
         t_sink->bytes[kind] += alg_bytes;
+        t_sink->ops[kind] += alg_ops;
         return;
     }
     Profiler& p = prof();
     std::lock_guard<std::mutex> g(p.mu);
     p.launches[kind] += n;
     p.bytes[kind] += alg_bytes;
+    p.ops[kind] += alg_ops;
     if (p.timing) {
         Pending e{kind, p.get_event(), p.get_event()};
         cudaEventRecord(e.a, s);
@@ -113,6 +118,7 @@ bm_status bm_profile_control(uint32_t timing, uint32_t reset) {
         for (int k = 0; k < BM_KERNEL_KINDS; k++) {
             p.launches[k] = 0;
             p.bytes[k] = 0;
+            p.ops[k] = 0;
             p.ms[k] = 0;
         }
     }
@@ -120,7 +126,8 @@ bm_status bm_profile_control(uint32_t timing, uint32_t reset) {
     return BM_OK;
 }
 
-bm_status bm_profile_read(uint32_t kind, uint64_t* launches, double* device_ms, double* alg_bytes) {
+bm_status bm_profile_read(uint32_t kind, uint64_t* launches, double* device_ms, double* alg_bytes,
+                          double* alg_mulops) {
     if (kind >= BM_KERNEL_KINDS) return BM_E_ARG;
     bm::Profiler& p = bm::prof();
     std::lock_guard<std::mutex> g(p.mu);
@@ -128,6 +135,7 @@ bm_status bm_profile_read(uint32_t kind, uint64_t* launches, double* device_ms, 
     if (launches) *launches = p.launches[kind];
     if (device_ms) *device_ms = p.ms[kind];
     if (alg_bytes) *alg_bytes = p.bytes[kind];
+    if (alg_mulops) *alg_mulops = p.ops[kind];
     return BM_OK;
 }
 
