@@ -91,53 +91,61 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
 // ---------------------------------------------------------------------------
 constexpr int kMaxDigit = 2;   // limbs per digit and special primes handled by the fused kernels
 
+// Dynamic shared memory of the column kernels: the exchange tile plus kMaxDigit
+// thread-private staging tiles (each thread reads back only what it wrote).
+template <int LA, int C>
+constexpr size_t col_smem_bytes() {
+    return sizeof(uint64_t) * ((size_t)((1 << LA) + (1 << LA) / (1 << (LA / 2))) * C + (size_t)kMaxDigit * (1 << LA) * C);
+}
+template <int LB, int R>
+constexpr size_t row_smem_bytes() {
+    return sizeof(uint64_t) * ((size_t)R * ((1 << LB) + (1 << LB) / (1 << (LB / 2))) + (size_t)kMaxDigit * R * (1 << LB));
+}
+
 template <int LA, int LB, int C>
 __global__ void __launch_bounds__(C * (1 << (LA / 2)))
     k_ks_f3(const uint64_t* __restrict__ X1, uint64_t* __restrict__ ext, const KsLevelConst* __restrict__ kc,
             DevTables tab, uint32_t l1, uint32_t L, uint32_t kinv) {
     constexpr int H = LA / 2, E = 1 << H, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN;
-    __shared__ uint64_t sm[(M + M / E) * C];
+    extern __shared__ uint64_t dsm[];
+    uint64_t* sm = dsm;                                   // exchange tile
+    uint64_t* st = dsm + (M + M / E) * C;                 // staging: [i][row][col]
     const int tid = threadIdx.x, t = tid / C, jc = tid % C;
     const uint32_t nd = kc->nd, nlx = kc->nlx;
     const uint32_t b = blockIdx.x / nd, d = blockIdx.x % nd;
     const int col = blockIdx.y * C + jc;
     const uint32_t ds = kc->dsz[d], d0 = kc->dstart[d];
-    uint64_t v[kMaxDigit][E];
+#pragma unroll 1
+    for (uint32_t i = 0; i < ds; i++) {
+        const uint64_t qi = tab.q[d0 + i];
+        const ulonglong2 h = kc->up_hinv[d][i];
+        const uint64_t* src = X1 + ((size_t)b * l1 + d0 + i) * N;
 #pragma unroll
-    for (int k = 0; k < E; k++) {
-        const uint32_t p = (uint32_t)(t + E * k) * N2 + col;
-        const uint32_t e = (p * kinv) & (2u * N - 1);
-        const uint32_t src = e & (N - 1);
-        const bool neg = e >= (uint32_t)N;
-#pragma unroll
-        for (int i = 0; i < kMaxDigit; i++) {
-            if (i < (int)ds) {
-                const uint64_t qi = tab.q[d0 + i];
-                uint64_t x = X1[((size_t)b * l1 + d0 + i) * N + src];
-                if (neg) x = negm(x, qi);
-                const ulonglong2 h = kc->up_hinv[d][i];
-                v[i][k] = shoup(x, h.x, h.y, qi);
-            }
+        for (int k = 0; k < E; k++) {
+            const uint32_t p = (uint32_t)(t + E * k) * N2 + col;
+            const uint32_t e = (p * kinv) & (2u * N - 1);
+            uint64_t x = src[e & (N - 1)];
+            if (e >= (uint32_t)N) x = negm(x, qi);
+            st[(i * M + t + E * k) * C + jc] = shoup(x, h.x, h.y, qi);
         }
     }
     const auto base = [](int s) { return 1 << s; };
+#pragma unroll 1
     for (uint32_t jj = 0; jj < nlx; jj++) {
         if (jj >= d0 && jj < d0 + ds) continue;               // the digit's own limbs come from F1
         const int pi = ext_prime(jj, l1, L);
         const uint64_t tq = tab.q[pi], tq2 = 2 * tq;
         uint64_t y[E];
 #pragma unroll
-        for (int k = 0; k < E; k++) {
-            uint64_t acc = 0;
+        for (int k = 0; k < E; k++) y[k] = 0;
+#pragma unroll 1
+        for (uint32_t i = 0; i < ds; i++) {
+            const ulonglong2 h = kc->up_hat[d][i][jj];
 #pragma unroll
-            for (int i = 0; i < kMaxDigit; i++) {
-                if (i < (int)ds) {
-                    const ulonglong2 h = kc->up_hat[d][i][jj];
-                    acc += shoup_lazy(v[i][k], h.x, h.y, tq);
-                }
-            }
-            y[k] = red6(acc, tq);
+            for (int k = 0; k < E; k++) y[k] += shoup_lazy(st[(i * M + t + E * k) * C + jc], h.x, h.y, tq);
         }
+#pragma unroll
+        for (int k = 0; k < E; k++) y[k] = red6(y[k], tq);
         nttr::fwd_stride<LA>(y, tab.tw[pi], base, tq, tq2);
 #pragma unroll
         for (int k = 0; k < E; k++) sm[pad<H>(t + E * k) * C + jc] = y[k];
@@ -152,30 +160,6 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
     }
 }
 
-// F4 epilogue for one key component: Q limbs are final NTT values (reduced),
-// special-prime limbs get the inverse row pass; stored in the stride layout.
-template <int LA, int LB, typename BaseF>
-__device__ __forceinline__ void f4_store(uint64_t (&a)[1 << (LB / 2)], uint64_t (&v)[1 << (LB / 2)], uint64_t* sr,
-                                         uint64_t* o, bool q_limb, const ulonglong2* itw, BaseF base, int t,
-                                         uint64_t q, uint64_t q2) {
-    constexpr int H = LB / 2, E = 1 << H;
-    if (q_limb) {
-#pragma unroll
-        for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = reduce2(a[k], q);
-    } else {
-        nttr::inv_consec<LB>(a, itw, base, t, q, q2);
-#pragma unroll
-        for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = a[k];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < E; k++) v[k] = sr[pad<H>(t + E * k)];
-    if (!q_limb) nttr::inv_stride<LB>(v, itw, base, q, q2);
-#pragma unroll
-    for (int k = 0; k < E; k++) o[t + E * k] = v[k];
-    __syncthreads();
-}
-
 // ---------------------------------------------------------------------------
 // F4: grid (B * nlx, N1 / R).  acc = sum_d ext_d * key_d (both components).
 // ---------------------------------------------------------------------------
@@ -184,8 +168,10 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
     k_ks_f4(const uint64_t* __restrict__ ext, const uint64_t* __restrict__ key, uint64_t* __restrict__ acc,
             const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L, uint32_t nb) {
     constexpr int H = LB / 2, E = 1 << H, M = 1 << LB, S = M + M / E, LOGN = LA + LB, N = 1 << LOGN;
-    __shared__ uint64_t sm[R * S];
+    extern __shared__ uint64_t dsm[];
     const int tid = threadIdx.x, jr = tid / E, t = tid % E;
+    uint64_t* sr = dsm + jr * S;                             // exchange row
+    uint64_t* st = dsm + R * S + jr * M + E * t;             // staging: digit d at st[d * R * M + k]
     const uint32_t nd = kc->nd, nlx = kc->nlx;
     const uint32_t b = blockIdx.x / nlx, jj = blockIdx.x % nlx;
     const int pi = ext_prime(jj, l1, L);
@@ -193,14 +179,12 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
     const int row = blockIdx.y * R + jr;
     const size_t roff = (size_t)row * M;
     const auto base = [row](int s) { return (1 << (LA + s)) + row * (1 << s); };
-    uint64_t* sr = sm + jr * S;
-    uint64_t a0[E], a1[E], v[E];
-#pragma unroll
-    for (int k = 0; k < E; k++) a0[k] = a1[k] = 0;
+    uint64_t v[E];
+    // extended limb jj of every digit, NTT form, consecutive layout, staged
+#pragma unroll 1
     for (uint32_t d = 0; d < nd; d++) {
         const uint64_t* e = ext + (((size_t)b * nd + d) * nlx + jj) * N + roff;
-        const bool own = jj >= kc->dstart[d] && jj < kc->dstart[d] + kc->dsz[d];
-        if (own) {
+        if (jj >= kc->dstart[d] && jj < kc->dstart[d] + kc->dsz[d]) {
 #pragma unroll
             for (int k = 0; k < E; k++) v[k] = e[E * t + k];
         } else {
@@ -215,20 +199,40 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
             nttr::fwd_consec<LB>(v, tab.tw[pi], base, t, q, q2);
             __syncthreads();
         }
-        const uint64_t* kb = key + ((size_t)(d * 2 + 0) * nb + pi) * N + roff + E * t;
-        const uint64_t* ka = key + ((size_t)(d * 2 + 1) * nb + pi) * N + roff + E * t;
 #pragma unroll
-        for (int k = 0; k < E; k++) {
-            uint64_t x0 = a0[k] + mont_lazy(v[k], kb[k], q, qn);
-            uint64_t x1 = a1[k] + mont_lazy(v[k], ka[k], q, qn);
-            a0[k] = x0 >= q2 ? x0 - q2 : x0;
-            a1[k] = x1 >= q2 ? x1 - q2 : x1;
-        }
+        for (int k = 0; k < E; k++) st[d * R * M + k] = v[k];
     }
-    f4_store<LA, LB>(a0, v, sr, acc + (((size_t)b * 2 + 0) * nlx + jj) * N + roff, jj < l1, tab.itw[pi], base, t, q,
-                     q2);
-    f4_store<LA, LB>(a1, v, sr, acc + (((size_t)b * 2 + 1) * nlx + jj) * N + roff, jj < l1, tab.itw[pi], base, t, q,
-                     q2);
+    // inner product per key component, then store (special primes: inverse row pass)
+#pragma unroll 1
+    for (uint32_t comp = 0; comp < 2; comp++) {
+#pragma unroll
+        for (int k = 0; k < E; k++) v[k] = 0;
+#pragma unroll 1
+        for (uint32_t d = 0; d < nd; d++) {
+            const uint64_t* kk = key + ((size_t)(d * 2 + comp) * nb + pi) * N + roff + E * t;
+#pragma unroll
+            for (int k = 0; k < E; k++) {
+                const uint64_t x = v[k] + mont_lazy(st[d * R * M + k], kk[k], q, qn);
+                v[k] = x >= q2 ? x - q2 : x;
+            }
+        }
+        if (jj < l1) {
+#pragma unroll
+            for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = reduce2(v[k], q);
+        } else {
+            nttr::inv_consec<LB>(v, tab.itw[pi], base, t, q, q2);
+#pragma unroll
+            for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = v[k];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < E; k++) v[k] = sr[pad<H>(t + E * k)];
+        if (jj >= l1) nttr::inv_stride<LB>(v, tab.itw[pi], base, q, q2);
+        uint64_t* o = acc + (((size_t)b * 2 + comp) * nlx + jj) * N + roff;
+#pragma unroll
+        for (int k = 0; k < E; k++) o[t + E * k] = v[k];
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -239,50 +243,47 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
     k_ks_f5(const uint64_t* __restrict__ acc, uint64_t* __restrict__ conv, const KsLevelConst* __restrict__ kc,
             DevTables tab, uint32_t l1, uint32_t L, uint32_t alpha) {
     constexpr int H = LA / 2, E = 1 << H, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN;
-    __shared__ uint64_t sm[(M + M / E) * C];
+    extern __shared__ uint64_t dsm[];
+    uint64_t* sm = dsm;
+    uint64_t* st = dsm + (M + M / E) * C;                 // staging: [i][row][col]
     const int tid = threadIdx.x, t = tid / C, jc = tid % C;
     const uint32_t b = blockIdx.x / 2, comp = blockIdx.x % 2;
     const int col = blockIdx.y * C + jc;
     const uint32_t nlx = l1 + alpha;
     const auto base = [](int s) { return 1 << s; };
-    uint64_t v[kMaxDigit][E];
+    uint64_t y[E];
+#pragma unroll 1
+    for (uint32_t i = 0; i < alpha; i++) {
+        const int pi = L + 1 + i;
+        const uint64_t p = tab.q[pi], p2 = 2 * p;
+        const uint64_t* src = acc + (((size_t)b * 2 + comp) * nlx + l1 + i) * N + col;
 #pragma unroll
-    for (int i = 0; i < kMaxDigit; i++) {
-        if (i < (int)alpha) {
-            const int pi = L + 1 + i;
-            const uint64_t p = tab.q[pi], p2 = 2 * p;
-            const uint64_t* src = acc + (((size_t)b * 2 + comp) * nlx + l1 + i) * N + col;
-            uint64_t x[E];
+        for (int k = 0; k < E; k++) y[k] = src[(size_t)(E * t + k) * N2];
+        nttr::inv_consec<LA>(y, tab.itw[pi], base, t, p, p2);
 #pragma unroll
-            for (int k = 0; k < E; k++) x[k] = src[(size_t)(E * t + k) * N2];
-            nttr::inv_consec<LA>(x, tab.itw[pi], base, t, p, p2);
+        for (int k = 0; k < E; k++) sm[pad<H>(E * t + k) * C + jc] = y[k];
+        __syncthreads();
 #pragma unroll
-            for (int k = 0; k < E; k++) sm[pad<H>(E * t + k) * C + jc] = x[k];
-            __syncthreads();
+        for (int k = 0; k < E; k++) y[k] = sm[pad<H>(t + E * k) * C + jc];
+        nttr::inv_stride<LA>(y, tab.itw[pi], base, p, p2);
+        const ulonglong2 h = kc->dn_hinv[i];          // N^-1 * (P/p_i)^-1 mod p_i
 #pragma unroll
-            for (int k = 0; k < E; k++) x[k] = sm[pad<H>(t + E * k) * C + jc];
-            nttr::inv_stride<LA>(x, tab.itw[pi], base, p, p2);
-            const ulonglong2 h = kc->dn_hinv[i];          // N^-1 * (P/p_i)^-1 mod p_i
-#pragma unroll
-            for (int k = 0; k < E; k++) v[i][k] = shoup(x[k], h.x, h.y, p);
-            __syncthreads();
-        }
+        for (int k = 0; k < E; k++) st[(i * M + t + E * k) * C + jc] = shoup(y[k], h.x, h.y, p);
+        __syncthreads();
     }
+#pragma unroll 1
     for (uint32_t j = 0; j < l1; j++) {
         const uint64_t q = tab.q[j], q2 = 2 * q;
-        uint64_t y[E];
 #pragma unroll
-        for (int k = 0; k < E; k++) {
-            uint64_t s = 0;
+        for (int k = 0; k < E; k++) y[k] = 0;
+#pragma unroll 1
+        for (uint32_t i = 0; i < alpha; i++) {
+            const ulonglong2 h = kc->dn_hat[i][j];
 #pragma unroll
-            for (int i = 0; i < kMaxDigit; i++) {
-                if (i < (int)alpha) {
-                    const ulonglong2 h = kc->dn_hat[i][j];
-                    s += shoup_lazy(v[i][k], h.x, h.y, q);
-                }
-            }
-            y[k] = red6(s, q);
+            for (int k = 0; k < E; k++) y[k] += shoup_lazy(st[(i * M + t + E * k) * C + jc], h.x, h.y, q);
         }
+#pragma unroll
+        for (int k = 0; k < E; k++) y[k] = red6(y[k], q);
         nttr::fwd_stride<LA>(y, tab.tw[j], base, q, q2);
 #pragma unroll
         for (int k = 0; k < E; k++) sm[pad<H>(t + E * k) * C + jc] = y[k];
@@ -363,6 +364,16 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
     const int tr = R * (1 << (LB / 2)), tc = C * (1 << (LA / 2));
     const double lw = 8.0 * N;                                  // bytes of one limb
     const double bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;   // mul ops of one limb pass
+    static bool attrs = [] {
+        cudaFuncSetAttribute(k_ks_f3<LA, LB, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)col_smem_bytes<LA, C>());
+        cudaFuncSetAttribute(k_ks_f5<LA, LB, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)col_smem_bytes<LA, C>());
+        cudaFuncSetAttribute(k_ks_f4<LA, LB, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)row_smem_bytes<LB, R>());
+        return true;
+    }();
+    (void)attrs;
     uint32_t targets = 0, gathers = 0;
     for (uint32_t d = 0; d < nd; d++) {
         targets += nlx - K.dsz[d];
@@ -379,16 +390,19 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
     {
         ProfScope ps(BM_KERNEL_MODUP, s, lw * B * (gathers + targets), bf_c * B * targets);
         const uint32_t kinv = (uint32_t)h_invmod_pow2(galois, 2ull * N);
-        k_ks_f3<LA, LB, C><<<dim3(B * nd, N2 / C), tc, 0, s>>>(X1, ext, kc, c.tab, l1, c.L, kinv);
+        k_ks_f3<LA, LB, C><<<dim3(B * nd, N2 / C), tc, col_smem_bytes<LA, C>(), s>>>(X1, ext, kc, c.tab, l1, c.L,
+                                                                                   kinv);
     }
     {
         ProfScope ps(BM_KERNEL_KS_IP, s, lw * nlx * ((double)B * nd + 2.0 * nd + 2.0 * B),
                      bf_r * B * (targets + 2.0 * alpha));
-        k_ks_f4<LA, LB, R><<<dim3(B * nlx, N1 / R), tr, 0, s>>>(ext, key, acc, kc, c.tab, l1, c.L, c.nb);
+        k_ks_f4<LA, LB, R><<<dim3(B * nlx, N1 / R), tr, row_smem_bytes<LB, R>(), s>>>(ext, key, acc, kc, c.tab, l1,
+                                                                                     c.L, c.nb);
     }
     {
         ProfScope ps(BM_KERNEL_MODDOWN, s, lw * B * 2 * (alpha + l1), bf_c * B * 2 * (alpha + l1));
-        k_ks_f5<LA, LB, C><<<dim3(B * 2, N2 / C), tc, 0, s>>>(acc, conv, kc, c.tab, l1, c.L, alpha);
+        k_ks_f5<LA, LB, C><<<dim3(B * 2, N2 / C), tc, col_smem_bytes<LA, C>(), s>>>(acc, conv, kc, c.tab, l1, c.L,
+                                                                                   alpha);
     }
     {
         ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * B * l1 * (2 + 2 + 1 + 2 + (d_add ? 2 : 0)), bf_r * B * 2 * l1);
