@@ -181,11 +181,11 @@ cudaError_t ntt_launch_reg(const LimbBatch& b, const DevTables& tab, bool inv, c
 
 cudaError_t ntt_dispatch(const Context& c, const LimbBatch& b, bool inv, cudaStream_t s) {
     switch (c.log_n) {
-        case 12: return ntt_launch_reg<6, 6, 16, 16>(b, c.tab, inv, s);
+        case 12: return ntt_launch_reg<6, 6, 8, 8>(b, c.tab, inv, s);
         case 13: return ntt_launch<7, 6>(b, c.tab, inv, s);
         case 14: return ntt_launch<7, 7>(b, c.tab, inv, s);
         case 15: return ntt_launch<8, 7>(b, c.tab, inv, s);
-        case 16: return ntt_launch_reg<8, 8, 8, 8>(b, c.tab, inv, s);
+        case 16: return ntt_launch_reg<8, 8, 4, 4>(b, c.tab, inv, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -522,8 +522,8 @@ cudaError_t ntt_col_inverse(const Context& c, const LimbBatch& b, cudaStream_t s
     if (limbs == 0) return cudaSuccess;
     const double lw = 16.0 * c.n * limbs, ops = 16.0 * (c.n / 2) * (c.log_n / 2) * limbs;
     ProfScope ps(BM_KERNEL_NTT, s, lw, ops);
-    if (c.log_n == 16) nttr::k_col_inv<8, 8, 8><<<dim3(limbs, 256 / 8), 8 * 16, 0, s>>>(b, c.tab);
-    else if (c.log_n == 12) nttr::k_col_inv<6, 6, 16><<<dim3(limbs, 64 / 16), 16 * 8, 0, s>>>(b, c.tab);
+    if (c.log_n == 16) nttr::k_col_inv<8, 8, 4><<<dim3(limbs, 256 / 4), 4 * 16, 0, s>>>(b, c.tab);
+    else if (c.log_n == 12) nttr::k_col_inv<6, 6, 8><<<dim3(limbs, 64 / 8), 8 * 8, 0, s>>>(b, c.tab);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

@@ -39,6 +39,29 @@ __device__ __forceinline__ uint64_t red6(uint64_t y, uint64_t t) {   // [0, 6t) 
     return y >= 4 * t ? y - 4 * t : y;
 }
 
+constexpr int kMaxDigit = 2;   // limbs per digit and special primes handled by the fused kernels
+
+using nttr::ColBase;
+using nttr::RowBase;
+using nttr::row_tw_entries;
+using nttr::stage_col_twiddles;
+using nttr::stage_row_twiddles;
+
+// Dynamic shared memory (in words) of the column kernels: exchange tile,
+// kMaxDigit thread-private staging tiles (each thread reads back only what it
+// wrote), staged twiddles.
+template <int LA, int C>
+__host__ __device__ constexpr size_t col_smem_words() {
+    return (size_t)((1 << LA) + (1 << LA) / (1 << (LA / 2))) * C + (size_t)kMaxDigit * (1 << LA) * C +
+           2 * (size_t)(1 << LA);
+}
+// ... and of F4: exchange rows, staging, forward and inverse row twiddles.
+template <int LB, int R>
+__host__ __device__ constexpr size_t f4_smem_words() {
+    return (size_t)R * ((1 << LB) + (1 << LB) / (1 << (LB / 2))) + (size_t)kMaxDigit * R * (1 << LB) +
+           4 * (size_t)row_tw_entries<LB, R>();
+}
+
 // ---------------------------------------------------------------------------
 // F1: grid (B * l1, N1 / R)
 // ---------------------------------------------------------------------------
@@ -48,6 +71,7 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
             const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t galois) {
     constexpr int H = LB / 2, E = 1 << H, M = 1 << LB, S = M + M / E, LOGN = LA + LB, N = 1 << LOGN;
     __shared__ uint64_t sm[R * S];
+    __shared__ ulonglong2 tws[row_tw_entries<LB, R>()];
     const int tid = threadIdx.x, jr = tid / E, t = tid % E;
     const uint32_t b = blockIdx.x / l1, j = blockIdx.x % l1;
     const int row = blockIdx.y * R + jr;
@@ -60,48 +84,52 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
     while (d + 1 < nd && j >= kc->dstart[d + 1]) d++;
     uint64_t* x0 = X0 + ((size_t)b * l1 + j) * N + roff;
     uint64_t* eo = ext + (((size_t)b * nd + d) * nlx + j) * N + roff;
+    uint64_t* sr = sm + jr * S;
+    uint64_t v[E];
+#pragma unroll
+    for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = c1[roff + t + E * k];
+    stage_row_twiddles<LA, LB, R>(tws, tab.itw[j], blockIdx.y * R);
 #pragma unroll
     for (int k = 0; k < E; k++) {
         const int c = t + E * k;
         x0[c] = c0[roff + c];
         eo[c] = c1[perm_src((uint32_t)(roff + c), LOGN, galois)];
     }
-    uint64_t v[E];
-    uint64_t* sr = sm + jr * S;
-#pragma unroll
-    for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = c1[roff + t + E * k];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < E; k++) v[k] = sr[pad<H>(E * t + k)];
-    const auto base = [row](int s) { return (1 << (LA + s)) + row * (1 << s); };
-    nttr::inv_consec<LB>(v, tab.itw[j], base, t, q, q2);
+    const RowBase<R> base{jr};
+    nttr::inv_consec<LB>(v, tws, base, t, q, q2);
 #pragma unroll
     for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = v[k];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < E; k++) v[k] = sr[pad<H>(t + E * k)];
-    nttr::inv_stride<LB>(v, tab.itw[j], base, q, q2);
+    nttr::inv_stride<LB>(v, tws, base, q, q2);
     uint64_t* x1 = X1 + ((size_t)b * l1 + j) * N + roff;
 #pragma unroll
     for (int k = 0; k < E; k++) x1[t + E * k] = v[k];
 }
 
+// forward column pass of y (stride layout in, consecutive-layout rows stored to o)
+template <int LA, int LB, int C>
+__device__ __forceinline__ void col_fwd_store(uint64_t (&y)[1 << (LA / 2)], uint64_t* sm, const ulonglong2* tws, int t,
+                                              int jc, uint64_t q, uint64_t* o) {
+    constexpr int H = LA / 2, E = 1 << H, N2 = 1 << LB;
+    nttr::fwd_stride<LA>(y, tws, ColBase{}, q, 2 * q);
+#pragma unroll
+    for (int k = 0; k < E; k++) sm[pad<H>(t + E * k) * C + jc] = y[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < E; k++) y[k] = sm[pad<H>(E * t + k) * C + jc];
+    nttr::fwd_consec<LA>(y, tws, ColBase{}, t, q, 2 * q);
+#pragma unroll
+    for (int k = 0; k < E; k++) o[(size_t)(E * t + k) * N2] = y[k];
+}
+
 // ---------------------------------------------------------------------------
 // F3: grid (B * nd, N2 / C).  X1 holds c1 in coefficient form.
 // ---------------------------------------------------------------------------
-constexpr int kMaxDigit = 2;   // limbs per digit and special primes handled by the fused kernels
-
-// Dynamic shared memory of the column kernels: the exchange tile plus kMaxDigit
-// thread-private staging tiles (each thread reads back only what it wrote).
-template <int LA, int C>
-constexpr size_t col_smem_bytes() {
-    return sizeof(uint64_t) * ((size_t)((1 << LA) + (1 << LA) / (1 << (LA / 2))) * C + (size_t)kMaxDigit * (1 << LA) * C);
-}
-template <int LB, int R>
-constexpr size_t row_smem_bytes() {
-    return sizeof(uint64_t) * ((size_t)R * ((1 << LB) + (1 << LB) / (1 << (LB / 2))) + (size_t)kMaxDigit * R * (1 << LB));
-}
-
 template <int LA, int LB, int C>
 __global__ void __launch_bounds__(C * (1 << (LA / 2)))
     k_ks_f3(const uint64_t* __restrict__ X1, uint64_t* __restrict__ ext, const KsLevelConst* __restrict__ kc,
@@ -109,7 +137,8 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
     constexpr int H = LA / 2, E = 1 << H, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN;
     extern __shared__ uint64_t dsm[];
     uint64_t* sm = dsm;                                   // exchange tile
-    uint64_t* st = dsm + (M + M / E) * C;                 // staging: [i][row][col]
+    uint64_t* st = sm + (M + M / E) * C;                  // staging: [i][row][col]
+    ulonglong2* tws = (ulonglong2*)(st + kMaxDigit * M * C);
     const int tid = threadIdx.x, t = tid / C, jc = tid % C;
     const uint32_t nd = kc->nd, nlx = kc->nlx;
     const uint32_t b = blockIdx.x / nd, d = blockIdx.x % nd;
@@ -129,12 +158,12 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
             st[(i * M + t + E * k) * C + jc] = shoup(x, h.x, h.y, qi);
         }
     }
-    const auto base = [](int s) { return 1 << s; };
 #pragma unroll 1
     for (uint32_t jj = 0; jj < nlx; jj++) {
         if (jj >= d0 && jj < d0 + ds) continue;               // the digit's own limbs come from F1
         const int pi = ext_prime(jj, l1, L);
-        const uint64_t tq = tab.q[pi], tq2 = 2 * tq;
+        const uint64_t tq = tab.q[pi];
+        stage_col_twiddles<LA>(tws, tab.tw[pi]);
         uint64_t y[E];
 #pragma unroll
         for (int k = 0; k < E; k++) y[k] = 0;
@@ -146,16 +175,8 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
         }
 #pragma unroll
         for (int k = 0; k < E; k++) y[k] = red6(y[k], tq);
-        nttr::fwd_stride<LA>(y, tab.tw[pi], base, tq, tq2);
-#pragma unroll
-        for (int k = 0; k < E; k++) sm[pad<H>(t + E * k) * C + jc] = y[k];
         __syncthreads();
-#pragma unroll
-        for (int k = 0; k < E; k++) y[k] = sm[pad<H>(E * t + k) * C + jc];
-        nttr::fwd_consec<LA>(y, tab.tw[pi], base, t, tq, tq2);
-        uint64_t* o = ext + (((size_t)b * nd + d) * nlx + jj) * N + col;
-#pragma unroll
-        for (int k = 0; k < E; k++) o[(size_t)(E * t + k) * N2] = y[k];
+        col_fwd_store<LA, LB, C>(y, sm, tws, t, jc, tq, ext + (((size_t)b * nd + d) * nlx + jj) * N + col);
         __syncthreads();
     }
 }
@@ -168,17 +189,23 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
     k_ks_f4(const uint64_t* __restrict__ ext, const uint64_t* __restrict__ key, uint64_t* __restrict__ acc,
             const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L, uint32_t nb) {
     constexpr int H = LB / 2, E = 1 << H, M = 1 << LB, S = M + M / E, LOGN = LA + LB, N = 1 << LOGN;
+    constexpr int TWN = row_tw_entries<LB, R>();
     extern __shared__ uint64_t dsm[];
     const int tid = threadIdx.x, jr = tid / E, t = tid % E;
     uint64_t* sr = dsm + jr * S;                             // exchange row
     uint64_t* st = dsm + R * S + jr * M + E * t;             // staging: digit d at st[d * R * M + k]
+    ulonglong2* twf = (ulonglong2*)(dsm + R * S + kMaxDigit * R * M);
+    ulonglong2* twi = twf + TWN;
     const uint32_t nd = kc->nd, nlx = kc->nlx;
     const uint32_t b = blockIdx.x / nlx, jj = blockIdx.x % nlx;
     const int pi = ext_prime(jj, l1, L);
     const uint64_t q = tab.q[pi], qn = tab.qneg[pi], q2 = 2 * q;
     const int row = blockIdx.y * R + jr;
     const size_t roff = (size_t)row * M;
-    const auto base = [row](int s) { return (1 << (LA + s)) + row * (1 << s); };
+    const RowBase<R> base{jr};
+    stage_row_twiddles<LA, LB, R>(twf, tab.tw[pi], blockIdx.y * R);
+    if (jj >= l1) stage_row_twiddles<LA, LB, R>(twi, tab.itw[pi], blockIdx.y * R);
+    __syncthreads();
     uint64_t v[E];
     // extended limb jj of every digit, NTT form, consecutive layout, staged
 #pragma unroll 1
@@ -190,13 +217,13 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
         } else {
 #pragma unroll
             for (int k = 0; k < E; k++) v[k] = e[t + E * k];
-            nttr::fwd_stride<LB>(v, tab.tw[pi], base, q, q2);
+            nttr::fwd_stride<LB>(v, twf, base, q, q2);
 #pragma unroll
             for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = v[k];
             __syncthreads();
 #pragma unroll
             for (int k = 0; k < E; k++) v[k] = sr[pad<H>(E * t + k)];
-            nttr::fwd_consec<LB>(v, tab.tw[pi], base, t, q, q2);
+            nttr::fwd_consec<LB>(v, twf, base, t, q, q2);
             __syncthreads();
         }
 #pragma unroll
@@ -220,14 +247,14 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
 #pragma unroll
             for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = reduce2(v[k], q);
         } else {
-            nttr::inv_consec<LB>(v, tab.itw[pi], base, t, q, q2);
+            nttr::inv_consec<LB>(v, twi, base, t, q, q2);
 #pragma unroll
             for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = v[k];
         }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < E; k++) v[k] = sr[pad<H>(t + E * k)];
-        if (jj >= l1) nttr::inv_stride<LB>(v, tab.itw[pi], base, q, q2);
+        if (jj >= l1) nttr::inv_stride<LB>(v, twi, base, q, q2);
         uint64_t* o = acc + (((size_t)b * 2 + comp) * nlx + jj) * N + roff;
 #pragma unroll
         for (int k = 0; k < E; k++) o[t + E * k] = v[k];
@@ -245,12 +272,12 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
     constexpr int H = LA / 2, E = 1 << H, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN;
     extern __shared__ uint64_t dsm[];
     uint64_t* sm = dsm;
-    uint64_t* st = dsm + (M + M / E) * C;                 // staging: [i][row][col]
+    uint64_t* st = sm + (M + M / E) * C;                  // staging: [i][row][col]
+    ulonglong2* tws = (ulonglong2*)(st + kMaxDigit * M * C);
     const int tid = threadIdx.x, t = tid / C, jc = tid % C;
     const uint32_t b = blockIdx.x / 2, comp = blockIdx.x % 2;
     const int col = blockIdx.y * C + jc;
     const uint32_t nlx = l1 + alpha;
-    const auto base = [](int s) { return 1 << s; };
     uint64_t y[E];
 #pragma unroll 1
     for (uint32_t i = 0; i < alpha; i++) {
@@ -259,13 +286,15 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
         const uint64_t* src = acc + (((size_t)b * 2 + comp) * nlx + l1 + i) * N + col;
 #pragma unroll
         for (int k = 0; k < E; k++) y[k] = src[(size_t)(E * t + k) * N2];
-        nttr::inv_consec<LA>(y, tab.itw[pi], base, t, p, p2);
+        stage_col_twiddles<LA>(tws, tab.itw[pi]);
+        __syncthreads();
+        nttr::inv_consec<LA>(y, tws, ColBase{}, t, p, p2);
 #pragma unroll
         for (int k = 0; k < E; k++) sm[pad<H>(E * t + k) * C + jc] = y[k];
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < E; k++) y[k] = sm[pad<H>(t + E * k) * C + jc];
-        nttr::inv_stride<LA>(y, tab.itw[pi], base, p, p2);
+        nttr::inv_stride<LA>(y, tws, ColBase{}, p, p2);
         const ulonglong2 h = kc->dn_hinv[i];          // N^-1 * (P/p_i)^-1 mod p_i
 #pragma unroll
         for (int k = 0; k < E; k++) st[(i * M + t + E * k) * C + jc] = shoup(y[k], h.x, h.y, p);
@@ -273,7 +302,8 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
     }
 #pragma unroll 1
     for (uint32_t j = 0; j < l1; j++) {
-        const uint64_t q = tab.q[j], q2 = 2 * q;
+        const uint64_t q = tab.q[j];
+        stage_col_twiddles<LA>(tws, tab.tw[j]);
 #pragma unroll
         for (int k = 0; k < E; k++) y[k] = 0;
 #pragma unroll 1
@@ -284,16 +314,8 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
         }
 #pragma unroll
         for (int k = 0; k < E; k++) y[k] = red6(y[k], q);
-        nttr::fwd_stride<LA>(y, tab.tw[j], base, q, q2);
-#pragma unroll
-        for (int k = 0; k < E; k++) sm[pad<H>(t + E * k) * C + jc] = y[k];
         __syncthreads();
-#pragma unroll
-        for (int k = 0; k < E; k++) y[k] = sm[pad<H>(E * t + k) * C + jc];
-        nttr::fwd_consec<LA>(y, tab.tw[j], base, t, q, q2);
-        uint64_t* o = conv + (((size_t)b * 2 + comp) * l1 + j) * N + col;
-#pragma unroll
-        for (int k = 0; k < E; k++) o[(size_t)(E * t + k) * N2] = y[k];
+        col_fwd_store<LA, LB, C>(y, sm, tws, t, jc, q, conv + (((size_t)b * 2 + comp) * l1 + j) * N + col);
         __syncthreads();
     }
 }
@@ -308,6 +330,7 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
             uint32_t l1, uint32_t galois) {
     constexpr int H = LB / 2, E = 1 << H, M = 1 << LB, S = M + M / E, LOGN = LA + LB, N = 1 << LOGN;
     __shared__ uint64_t sm[R * S];
+    __shared__ ulonglong2 tws[row_tw_entries<LB, R>()];
     const int tid = threadIdx.x, jr = tid / E, t = tid % E;
     const uint32_t b = blockIdx.x / l1, j = blockIdx.x % l1;
     const uint32_t nlx = kc->nlx;
@@ -315,21 +338,23 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
     const size_t roff = (size_t)row * M;
     const uint64_t q = tab.q[j], q2 = 2 * q;
     const ulonglong2 pinv = kc->pinv[j];
-    const auto base = [row](int s) { return (1 << (LA + s)) + row * (1 << s); };
+    const RowBase<R> base{jr};
     uint64_t* sr = sm + jr * S;
+    stage_row_twiddles<LA, LB, R>(tws, tab.tw[j], blockIdx.y * R);
     uint64_t v[E];
 #pragma unroll
     for (int comp = 0; comp < 2; comp++) {
         const uint64_t* cv = conv + (((size_t)b * 2 + comp) * l1 + j) * N + roff;
 #pragma unroll
         for (int k = 0; k < E; k++) v[k] = cv[t + E * k];
-        nttr::fwd_stride<LB>(v, tab.tw[j], base, q, q2);
+        __syncthreads();
+        nttr::fwd_stride<LB>(v, tws, base, q, q2);
 #pragma unroll
         for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = v[k];
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < E; k++) v[k] = sr[pad<H>(E * t + k)];
-        nttr::fwd_consec<LB>(v, tab.tw[j], base, t, q, q2);
+        nttr::fwd_consec<LB>(v, tws, base, t, q, q2);
         const uint64_t* av = acc + (((size_t)b * 2 + comp) * nlx + j) * N + roff + E * t;
         const uint64_t* ad = add ? add[b] + ((size_t)comp * l1 + j) * N + roff + E * t : nullptr;
 #pragma unroll
@@ -344,7 +369,6 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
         uint64_t* o = out[b] + ((size_t)comp * l1 + j) * N + roff;
 #pragma unroll
         for (int k = 0; k < E; k++) o[t + E * k] = sr[pad<H>(t + E * k)];
-        __syncthreads();
     }
 }
 
@@ -366,11 +390,11 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
     const double bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;   // mul ops of one limb pass
     static bool attrs = [] {
         cudaFuncSetAttribute(k_ks_f3<LA, LB, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)col_smem_bytes<LA, C>());
+                             (int)(8 * col_smem_words<LA, C>()));
         cudaFuncSetAttribute(k_ks_f5<LA, LB, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)col_smem_bytes<LA, C>());
+                             (int)(8 * col_smem_words<LA, C>()));
         cudaFuncSetAttribute(k_ks_f4<LA, LB, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)row_smem_bytes<LB, R>());
+                             (int)(8 * f4_smem_words<LB, R>()));
         return true;
     }();
     (void)attrs;
@@ -390,18 +414,18 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
     {
         ProfScope ps(BM_KERNEL_MODUP, s, lw * B * (gathers + targets), bf_c * B * targets);
         const uint32_t kinv = (uint32_t)h_invmod_pow2(galois, 2ull * N);
-        k_ks_f3<LA, LB, C><<<dim3(B * nd, N2 / C), tc, col_smem_bytes<LA, C>(), s>>>(X1, ext, kc, c.tab, l1, c.L,
+        k_ks_f3<LA, LB, C><<<dim3(B * nd, N2 / C), tc, 8 * col_smem_words<LA, C>(), s>>>(X1, ext, kc, c.tab, l1, c.L,
                                                                                    kinv);
     }
     {
         ProfScope ps(BM_KERNEL_KS_IP, s, lw * nlx * ((double)B * nd + 2.0 * nd + 2.0 * B),
                      bf_r * B * (targets + 2.0 * alpha));
-        k_ks_f4<LA, LB, R><<<dim3(B * nlx, N1 / R), tr, row_smem_bytes<LB, R>(), s>>>(ext, key, acc, kc, c.tab, l1,
+        k_ks_f4<LA, LB, R><<<dim3(B * nlx, N1 / R), tr, 8 * f4_smem_words<LB, R>(), s>>>(ext, key, acc, kc, c.tab, l1,
                                                                                      c.L, c.nb);
     }
     {
         ProfScope ps(BM_KERNEL_MODDOWN, s, lw * B * 2 * (alpha + l1), bf_c * B * 2 * (alpha + l1));
-        k_ks_f5<LA, LB, C><<<dim3(B * 2, N2 / C), tc, col_smem_bytes<LA, C>(), s>>>(acc, conv, kc, c.tab, l1, c.L,
+        k_ks_f5<LA, LB, C><<<dim3(B * 2, N2 / C), tc, 8 * col_smem_words<LA, C>(), s>>>(acc, conv, kc, c.tab, l1, c.L,
                                                                                    alpha);
     }
     {
@@ -426,8 +450,8 @@ cudaError_t ks_rotate_fused(const Context& c, const uint64_t* key, uint64_t galo
                             uint64_t* const* d_in, uint64_t* const* d_out, uint64_t* const* d_add, uint64_t* scratch,
                             cudaStream_t s) {
     if (B == 0) return cudaSuccess;
-    if (c.log_n == 16) return ks_fused_launch<8, 8, 8, 8>(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
-    if (c.log_n == 12) return ks_fused_launch<6, 6, 16, 16>(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
+    if (c.log_n == 16) return ks_fused_launch<8, 8, 4, 4>(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
+    if (c.log_n == 12) return ks_fused_launch<6, 6, 8, 8>(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
     return cudaErrorInvalidValue;
 }
 

@@ -112,6 +112,38 @@ __device__ __forceinline__ void inv_stride(uint64_t (&v)[1 << (P / 2)], const ul
 template <int H>
 __device__ __forceinline__ int pad(int r) { return r + (r >> H); }
 
+// Twiddles a column pass uses: entries 1 .. 2^LA - 1 of the table, staged in
+// shared memory (index unchanged).
+template <int LA>
+__device__ __forceinline__ void stage_col_twiddles(ulonglong2* dst, const ulonglong2* __restrict__ tw) {
+    for (int i = threadIdx.x; i < (1 << LA); i += blockDim.x) dst[i] = tw[i];
+}
+
+// Twiddles of a row pass over rows r0 .. r0+R-1: stage s uses the global entries
+// 2^(LA+s) + r*2^s + [0, 2^s), contiguous over the R rows; staged at
+// R*(2^s - 1) + (r - r0)*2^s + [0, 2^s).
+template <int LA, int LB, int R>
+__device__ __forceinline__ void stage_row_twiddles(ulonglong2* dst, const ulonglong2* __restrict__ tw, int r0) {
+#pragma unroll 1
+    for (int s = 0; s < LB; s++) {
+        const ulonglong2* src = tw + (1 << (LA + s)) + r0 * (1 << s);
+        ulonglong2* d = dst + R * ((1 << s) - 1);
+        for (int i = threadIdx.x; i < (R << s); i += blockDim.x) d[i] = src[i];
+    }
+}
+template <int LB, int R>
+__host__ __device__ constexpr int row_tw_entries() { return R * ((1 << LB) - 1); }
+
+// base(s) of a row pass on staged twiddles, local row jr
+template <int R>
+struct RowBase {
+    int jr;
+    __device__ __forceinline__ int operator()(int s) const { return R * ((1 << s) - 1) + jr * (1 << s); }
+};
+struct ColBase {
+    __device__ __forceinline__ int operator()(int s) const { return 1 << s; }
+};
+
 // ---------------------------------------------------------------------------
 // pass kernels on a LimbBatch; grid (limbs, tiles)
 // ---------------------------------------------------------------------------
@@ -121,22 +153,23 @@ template <int LA, int LB, int C>
 __global__ void __launch_bounds__(C * (1 << (LA / 2))) k_col_fwd(LimbBatch lb, DevTables tab) {
     constexpr int H = LA / 2, E = 1 << H, M = 1 << LA, N2 = 1 << LB;
     __shared__ uint64_t sm[(M + M / E) * C];
+    __shared__ ulonglong2 tws[M];
     const int tid = threadIdx.x, t = tid / C, j = tid % C;
     const int pi = lb.prime(blockIdx.x % lb.nl);
     uint64_t* a = limb_at(lb, blockIdx.x, M * N2) + blockIdx.y * C + j;
     const uint64_t q = tab.q[pi], q2 = 2 * q;
-    const ulonglong2* tw = tab.tw[pi];
-    const auto base = [](int s) { return 1 << s; };
     uint64_t v[E];
 #pragma unroll
     for (int k = 0; k < E; k++) v[k] = a[(size_t)(t + E * k) * N2];
-    fwd_stride<LA>(v, tw, base, q, q2);
+    stage_col_twiddles<LA>(tws, tab.tw[pi]);
+    __syncthreads();
+    fwd_stride<LA>(v, tws, ColBase{}, q, q2);
 #pragma unroll
     for (int k = 0; k < E; k++) sm[pad<H>(t + E * k) * C + j] = v[k];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < E; k++) v[k] = sm[pad<H>(E * t + k) * C + j];
-    fwd_consec<LA>(v, tw, base, t, q, q2);
+    fwd_consec<LA>(v, tws, ColBase{}, t, q, q2);
 #pragma unroll
     for (int k = 0; k < E; k++) a[(size_t)(E * t + k) * N2] = v[k];
 }
@@ -146,24 +179,26 @@ template <int LA, int LB, int R>
 __global__ void __launch_bounds__(R * (1 << (LB / 2))) k_row_fwd(LimbBatch lb, DevTables tab) {
     constexpr int H = LB / 2, E = 1 << H, M = 1 << LB, S = M + M / E;
     __shared__ uint64_t sm[R * S];
-    const int tid = threadIdx.x, j = tid / E, t = tid % E;
-    const int row = blockIdx.y * R + j;
+    __shared__ ulonglong2 tws[row_tw_entries<LB, R>()];
+    const int tid = threadIdx.x, jr = tid / E, t = tid % E;
+    const int row = blockIdx.y * R + jr;
     const int pi = lb.prime(blockIdx.x % lb.nl);
     uint64_t* a = limb_at(lb, blockIdx.x, (1 << LA) * M) + (size_t)row * M;
     const uint64_t q = tab.q[pi], q2 = 2 * q;
-    const ulonglong2* tw = tab.tw[pi];
-    const auto base = [row](int s) { return (1 << (LA + s)) + row * (1 << s); };
-    uint64_t* sr = sm + j * S;
+    const RowBase<R> base{jr};
+    uint64_t* sr = sm + jr * S;
     uint64_t v[E];
 #pragma unroll
     for (int k = 0; k < E; k++) v[k] = a[t + E * k];
-    fwd_stride<LB>(v, tw, base, q, q2);
+    stage_row_twiddles<LA, LB, R>(tws, tab.tw[pi], blockIdx.y * R);
+    __syncthreads();
+    fwd_stride<LB>(v, tws, base, q, q2);
 #pragma unroll
     for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = v[k];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < E; k++) v[k] = sr[pad<H>(E * t + k)];
-    fwd_consec<LB>(v, tw, base, t, q, q2);
+    fwd_consec<LB>(v, tws, base, t, q, q2);
 #pragma unroll
     for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = reduce4(v[k], q, q2);
     __syncthreads();
@@ -176,27 +211,28 @@ template <int LA, int LB, int R>
 __global__ void __launch_bounds__(R * (1 << (LB / 2))) k_row_inv(LimbBatch lb, DevTables tab) {
     constexpr int H = LB / 2, E = 1 << H, M = 1 << LB, S = M + M / E;
     __shared__ uint64_t sm[R * S];
-    const int tid = threadIdx.x, j = tid / E, t = tid % E;
-    const int row = blockIdx.y * R + j;
+    __shared__ ulonglong2 tws[row_tw_entries<LB, R>()];
+    const int tid = threadIdx.x, jr = tid / E, t = tid % E;
+    const int row = blockIdx.y * R + jr;
     const int pi = lb.prime(blockIdx.x % lb.nl);
     uint64_t* a = limb_at(lb, blockIdx.x, (1 << LA) * M) + (size_t)row * M;
     const uint64_t q = tab.q[pi], q2 = 2 * q;
-    const ulonglong2* tw = tab.itw[pi];
-    const auto base = [row](int s) { return (1 << (LA + s)) + row * (1 << s); };
-    uint64_t* sr = sm + j * S;
+    const RowBase<R> base{jr};
+    uint64_t* sr = sm + jr * S;
     uint64_t v[E];
 #pragma unroll
     for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = a[t + E * k];
+    stage_row_twiddles<LA, LB, R>(tws, tab.itw[pi], blockIdx.y * R);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < E; k++) v[k] = sr[pad<H>(E * t + k)];
-    inv_consec<LB>(v, tw, base, t, q, q2);
+    inv_consec<LB>(v, tws, base, t, q, q2);
 #pragma unroll
     for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = v[k];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < E; k++) v[k] = sr[pad<H>(t + E * k)];
-    inv_stride<LB>(v, tw, base, q, q2);
+    inv_stride<LB>(v, tws, base, q, q2);
 #pragma unroll
     for (int k = 0; k < E; k++) a[t + E * k] = v[k];
 }
@@ -206,22 +242,23 @@ template <int LA, int LB, int C>
 __global__ void __launch_bounds__(C * (1 << (LA / 2))) k_col_inv(LimbBatch lb, DevTables tab) {
     constexpr int H = LA / 2, E = 1 << H, M = 1 << LA, N2 = 1 << LB;
     __shared__ uint64_t sm[(M + M / E) * C];
+    __shared__ ulonglong2 tws[M];
     const int tid = threadIdx.x, t = tid / C, j = tid % C;
     const int pi = lb.prime(blockIdx.x % lb.nl);
     uint64_t* a = limb_at(lb, blockIdx.x, M * N2) + blockIdx.y * C + j;
     const uint64_t q = tab.q[pi], q2 = 2 * q;
-    const ulonglong2* tw = tab.itw[pi];
-    const auto base = [](int s) { return 1 << s; };
     uint64_t v[E];
 #pragma unroll
     for (int k = 0; k < E; k++) v[k] = a[(size_t)(E * t + k) * N2];
-    inv_consec<LA>(v, tw, base, t, q, q2);
+    stage_col_twiddles<LA>(tws, tab.itw[pi]);
+    __syncthreads();
+    inv_consec<LA>(v, tws, ColBase{}, t, q, q2);
 #pragma unroll
     for (int k = 0; k < E; k++) sm[pad<H>(E * t + k) * C + j] = v[k];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < E; k++) v[k] = sm[pad<H>(t + E * k) * C + j];
-    inv_stride<LA>(v, tw, base, q, q2);
+    inv_stride<LA>(v, tws, ColBase{}, q, q2);
     const uint64_t ni = tab.ninv[pi], nis = tab.ninv_sh[pi];
 #pragma unroll
     for (int k = 0; k < E; k++) a[(size_t)(t + E * k) * N2] = shoup(v[k], ni, nis, q);
