@@ -46,6 +46,7 @@ using nttr::RowBase;
 using nttr::row_tw_entries;
 using nttr::stage_col_twiddles;
 using nttr::stage_row_twiddles;
+using nttr::tw_wait;
 
 // Dynamic shared memory (in words) of the column kernels: exchange tile,
 // kMaxDigit thread-private staging tiles (each thread reads back only what it
@@ -85,17 +86,17 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
     uint64_t* x0 = X0 + ((size_t)b * l1 + j) * N + roff;
     uint64_t* eo = ext + (((size_t)b * nd + d) * nlx + j) * N + roff;
     uint64_t* sr = sm + jr * S;
+    stage_row_twiddles<LA, LB, R, R * E>(tws, tab.itw[j], blockIdx.y * R);
     uint64_t v[E];
 #pragma unroll
     for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = c1[roff + t + E * k];
-    stage_row_twiddles<LA, LB, R>(tws, tab.itw[j], blockIdx.y * R);
 #pragma unroll
     for (int k = 0; k < E; k++) {
         const int c = t + E * k;
         x0[c] = c0[roff + c];
         eo[c] = c1[perm_src((uint32_t)(roff + c), LOGN, galois)];
     }
-    __syncthreads();
+    tw_wait();
 #pragma unroll
     for (int k = 0; k < E; k++) v[k] = sr[pad<H>(E * t + k)];
     const RowBase<R> base{jr};
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
         if (jj >= d0 && jj < d0 + ds) continue;               // the digit's own limbs come from F1
         const int pi = ext_prime(jj, l1, L);
         const uint64_t tq = tab.q[pi];
-        stage_col_twiddles<LA>(tws, tab.tw[pi]);
+        stage_col_twiddles<LA, C * E>(tws, tab.tw[pi]);
         uint64_t y[E];
 #pragma unroll
         for (int k = 0; k < E; k++) y[k] = 0;
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
         }
 #pragma unroll
         for (int k = 0; k < E; k++) y[k] = red6(y[k], tq);
-        __syncthreads();
+        tw_wait();
         col_fwd_store<LA, LB, C>(y, sm, tws, t, jc, tq, ext + (((size_t)b * nd + d) * nlx + jj) * N + col);
         __syncthreads();
     }
@@ -203,9 +204,9 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
     const int row = blockIdx.y * R + jr;
     const size_t roff = (size_t)row * M;
     const RowBase<R> base{jr};
-    stage_row_twiddles<LA, LB, R>(twf, tab.tw[pi], blockIdx.y * R);
-    if (jj >= l1) stage_row_twiddles<LA, LB, R>(twi, tab.itw[pi], blockIdx.y * R);
-    __syncthreads();
+    stage_row_twiddles<LA, LB, R, R * E>(twf, tab.tw[pi], blockIdx.y * R);
+    if (jj >= l1) stage_row_twiddles<LA, LB, R, R * E>(twi, tab.itw[pi], blockIdx.y * R);
+    tw_wait();
     uint64_t v[E];
     // extended limb jj of every digit, NTT form, consecutive layout, staged
 #pragma unroll 1
@@ -284,10 +285,10 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
         const int pi = L + 1 + i;
         const uint64_t p = tab.q[pi], p2 = 2 * p;
         const uint64_t* src = acc + (((size_t)b * 2 + comp) * nlx + l1 + i) * N + col;
+        stage_col_twiddles<LA, C * E>(tws, tab.itw[pi]);
 #pragma unroll
         for (int k = 0; k < E; k++) y[k] = src[(size_t)(E * t + k) * N2];
-        stage_col_twiddles<LA>(tws, tab.itw[pi]);
-        __syncthreads();
+        tw_wait();
         nttr::inv_consec<LA>(y, tws, ColBase{}, t, p, p2);
 #pragma unroll
         for (int k = 0; k < E; k++) sm[pad<H>(E * t + k) * C + jc] = y[k];
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
 #pragma unroll 1
     for (uint32_t j = 0; j < l1; j++) {
         const uint64_t q = tab.q[j];
-        stage_col_twiddles<LA>(tws, tab.tw[j]);
+        stage_col_twiddles<LA, C * E>(tws, tab.tw[j]);
 #pragma unroll
         for (int k = 0; k < E; k++) y[k] = 0;
 #pragma unroll 1
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
         }
 #pragma unroll
         for (int k = 0; k < E; k++) y[k] = red6(y[k], q);
-        __syncthreads();
+        tw_wait();
         col_fwd_store<LA, LB, C>(y, sm, tws, t, jc, q, conv + (((size_t)b * 2 + comp) * l1 + j) * N + col);
         __syncthreads();
     }
@@ -340,14 +341,15 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
     const ulonglong2 pinv = kc->pinv[j];
     const RowBase<R> base{jr};
     uint64_t* sr = sm + jr * S;
-    stage_row_twiddles<LA, LB, R>(tws, tab.tw[j], blockIdx.y * R);
+    stage_row_twiddles<LA, LB, R, R * E>(tws, tab.tw[j], blockIdx.y * R);
     uint64_t v[E];
 #pragma unroll
     for (int comp = 0; comp < 2; comp++) {
         const uint64_t* cv = conv + (((size_t)b * 2 + comp) * l1 + j) * N + roff;
 #pragma unroll
         for (int k = 0; k < E; k++) v[k] = cv[t + E * k];
-        __syncthreads();
+        if (comp == 0) tw_wait();
+        else __syncthreads();
         nttr::fwd_stride<LB>(v, tws, base, q, q2);
 #pragma unroll
         for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = v[k];

@@ -16,6 +16,8 @@
 // inverse in [0, 2q); the last pass of each transform reduces to [0, q).
 #pragma once
 
+#include <cuda_pipeline.h>
+
 namespace bm {
 namespace nttr {
 
@@ -112,25 +114,43 @@ __device__ __forceinline__ void inv_stride(uint64_t (&v)[1 << (P / 2)], const ul
 template <int H>
 __device__ __forceinline__ int pad(int r) { return r + (r >> H); }
 
-// Twiddles a column pass uses: entries 1 .. 2^LA - 1 of the table, staged in
-// shared memory (index unchanged).
-template <int LA>
+// Twiddles a column pass uses: entries 1 .. 2^LA - 1 of the table, copied to
+// shared memory (index unchanged) with asynchronous copies issued all at once by
+// the T threads of the CTA; wait with tw_wait() before use.
+template <int LA, int T>
 __device__ __forceinline__ void stage_col_twiddles(ulonglong2* dst, const ulonglong2* __restrict__ tw) {
-    for (int i = threadIdx.x; i < (1 << LA); i += blockDim.x) dst[i] = tw[i];
+#pragma unroll
+    for (int i0 = 0; i0 < (1 << LA); i0 += T) {
+        const int i = i0 + (int)threadIdx.x;
+        if (i < (1 << LA)) __pipeline_memcpy_async(dst + i, tw + i, sizeof(ulonglong2));
+    }
+    __pipeline_commit();
 }
 
 // Twiddles of a row pass over rows r0 .. r0+R-1: stage s uses the global entries
-// 2^(LA+s) + r*2^s + [0, 2^s), contiguous over the R rows; staged at
+// 2^(LA+s) + r*2^s + [0, 2^s), contiguous over the R rows; copied to
 // R*(2^s - 1) + (r - r0)*2^s + [0, 2^s).
-template <int LA, int LB, int R>
+template <int LA, int LB, int R, int T>
 __device__ __forceinline__ void stage_row_twiddles(ulonglong2* dst, const ulonglong2* __restrict__ tw, int r0) {
-#pragma unroll 1
+#pragma unroll
     for (int s = 0; s < LB; s++) {
         const ulonglong2* src = tw + (1 << (LA + s)) + r0 * (1 << s);
         ulonglong2* d = dst + R * ((1 << s) - 1);
-        for (int i = threadIdx.x; i < (R << s); i += blockDim.x) d[i] = src[i];
+#pragma unroll
+        for (int i0 = 0; i0 < (R << s); i0 += T) {
+            const int i = i0 + (int)threadIdx.x;
+            if (i < (R << s)) __pipeline_memcpy_async(d + i, src + i, sizeof(ulonglong2));
+        }
     }
+    __pipeline_commit();
 }
+
+// completes this thread's staged copies and makes every thread's visible
+__device__ __forceinline__ void tw_wait() {
+    __pipeline_wait_prior(0);
+    __syncthreads();
+}
+
 template <int LB, int R>
 __host__ __device__ constexpr int row_tw_entries() { return R * ((1 << LB) - 1); }
 
@@ -158,11 +178,11 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2))) k_col_fwd(LimbBatch lb, D
     const int pi = lb.prime(blockIdx.x % lb.nl);
     uint64_t* a = limb_at(lb, blockIdx.x, M * N2) + blockIdx.y * C + j;
     const uint64_t q = tab.q[pi], q2 = 2 * q;
+    stage_col_twiddles<LA, C * E>(tws, tab.tw[pi]);
     uint64_t v[E];
 #pragma unroll
     for (int k = 0; k < E; k++) v[k] = a[(size_t)(t + E * k) * N2];
-    stage_col_twiddles<LA>(tws, tab.tw[pi]);
-    __syncthreads();
+    tw_wait();
     fwd_stride<LA>(v, tws, ColBase{}, q, q2);
 #pragma unroll
     for (int k = 0; k < E; k++) sm[pad<H>(t + E * k) * C + j] = v[k];
@@ -187,11 +207,11 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2))) k_row_fwd(LimbBatch lb, D
     const uint64_t q = tab.q[pi], q2 = 2 * q;
     const RowBase<R> base{jr};
     uint64_t* sr = sm + jr * S;
+    stage_row_twiddles<LA, LB, R, R * E>(tws, tab.tw[pi], blockIdx.y * R);
     uint64_t v[E];
 #pragma unroll
     for (int k = 0; k < E; k++) v[k] = a[t + E * k];
-    stage_row_twiddles<LA, LB, R>(tws, tab.tw[pi], blockIdx.y * R);
-    __syncthreads();
+    tw_wait();
     fwd_stride<LB>(v, tws, base, q, q2);
 #pragma unroll
     for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = v[k];
@@ -219,11 +239,11 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2))) k_row_inv(LimbBatch lb, D
     const uint64_t q = tab.q[pi], q2 = 2 * q;
     const RowBase<R> base{jr};
     uint64_t* sr = sm + jr * S;
+    stage_row_twiddles<LA, LB, R, R * E>(tws, tab.itw[pi], blockIdx.y * R);
     uint64_t v[E];
 #pragma unroll
     for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = a[t + E * k];
-    stage_row_twiddles<LA, LB, R>(tws, tab.itw[pi], blockIdx.y * R);
-    __syncthreads();
+    tw_wait();
 #pragma unroll
     for (int k = 0; k < E; k++) v[k] = sr[pad<H>(E * t + k)];
     inv_consec<LB>(v, tws, base, t, q, q2);
@@ -247,11 +267,11 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2))) k_col_inv(LimbBatch lb, D
     const int pi = lb.prime(blockIdx.x % lb.nl);
     uint64_t* a = limb_at(lb, blockIdx.x, M * N2) + blockIdx.y * C + j;
     const uint64_t q = tab.q[pi], q2 = 2 * q;
+    stage_col_twiddles<LA, C * E>(tws, tab.itw[pi]);
     uint64_t v[E];
 #pragma unroll
     for (int k = 0; k < E; k++) v[k] = a[(size_t)(E * t + k) * N2];
-    stage_col_twiddles<LA>(tws, tab.itw[pi]);
-    __syncthreads();
+    tw_wait();
     inv_consec<LA>(v, tws, ColBase{}, t, q, q2);
 #pragma unroll
     for (int k = 0; k < E; k++) sm[pad<H>(E * t + k) * C + j] = v[k];
