@@ -160,32 +160,32 @@ namespace bm {
 namespace {
 
 // register-resident passes for even pass sizes (ring 2^12: 64 x 64, ring 2^16: 256 x 256)
-template <int LA, int LB, int C, int R>
+template <int LA, int LB, int LT, int C, int R>
 cudaError_t ntt_launch_reg(const LimbBatch& b, const DevTables& tab, bool inv, cudaStream_t s) {
     const uint32_t limbs = b.n_polys * b.nl;
     if (limbs == 0) return cudaSuccess;
     const dim3 gc(limbs, (1 << LB) / C), gr(limbs, (1 << LA) / R);
-    const int tc = C * (1 << (LA / 2)), tr = R * (1 << (LB / 2));
+    const int tc = C * (1 << (LA - LT)), tr = R * (1 << (LB - LT));
     const double bytes = 16.0 * (1 << (LA + LB)) * limbs;   // each pass reads and writes every limb once
     const double ops_c = 16.0 * (1 << (LA + LB - 1)) * LA * limbs;   // 16 mul ops per butterfly
     const double ops_r = 16.0 * (1 << (LA + LB - 1)) * LB * limbs;
     if (!inv) {
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_c); nttr::k_col_fwd<LA, LB, C><<<gc, tc, 0, s>>>(b, tab); }
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_r); nttr::k_row_fwd<LA, LB, R><<<gr, tr, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_c); nttr::k_col_fwd<LA, LB, LT, C><<<gc, tc, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_r); nttr::k_row_fwd<LA, LB, LT, R><<<gr, tr, 0, s>>>(b, tab); }
     } else {
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_r); nttr::k_row_inv<LA, LB, R><<<gr, tr, 0, s>>>(b, tab); }
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_c); nttr::k_col_inv<LA, LB, C><<<gc, tc, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_r); nttr::k_row_inv<LA, LB, LT, R><<<gr, tr, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_c); nttr::k_col_inv<LA, LB, LT, C><<<gc, tc, 0, s>>>(b, tab); }
     }
     return cudaGetLastError();
 }
 
 cudaError_t ntt_dispatch(const Context& c, const LimbBatch& b, bool inv, cudaStream_t s) {
     switch (c.log_n) {
-        case 12: return ntt_launch_reg<6, 6, 8, 8>(b, c.tab, inv, s);
+        case 12: return ntt_launch_reg<6, 6, 2, 8, 8>(b, c.tab, inv, s);
         case 13: return ntt_launch<7, 6>(b, c.tab, inv, s);
         case 14: return ntt_launch<7, 7>(b, c.tab, inv, s);
         case 15: return ntt_launch<8, 7>(b, c.tab, inv, s);
-        case 16: return ntt_launch_reg<8, 8, 4, 4>(b, c.tab, inv, s);
+        case 16: return ntt_launch_reg<8, 8, 2, 2, 2>(b, c.tab, inv, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -522,8 +522,8 @@ cudaError_t ntt_col_inverse(const Context& c, const LimbBatch& b, cudaStream_t s
     if (limbs == 0) return cudaSuccess;
     const double lw = 16.0 * c.n * limbs, ops = 16.0 * (c.n / 2) * (c.log_n / 2) * limbs;
     ProfScope ps(BM_KERNEL_NTT, s, lw, ops);
-    if (c.log_n == 16) nttr::k_col_inv<8, 8, 4><<<dim3(limbs, 256 / 4), 4 * 16, 0, s>>>(b, c.tab);
-    else if (c.log_n == 12) nttr::k_col_inv<6, 6, 8><<<dim3(limbs, 64 / 8), 8 * 8, 0, s>>>(b, c.tab);
+    if (c.log_n == 16) nttr::k_col_inv<8, 8, 2, 2><<<dim3(limbs, 256 / 2), 2 * 64, 0, s>>>(b, c.tab);
+    else if (c.log_n == 12) nttr::k_col_inv<6, 6, 2, 8><<<dim3(limbs, 64 / 8), 8 * 16, 0, s>>>(b, c.tab);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

@@ -22,7 +22,6 @@
 namespace bm {
 namespace {
 
-using nttr::pad;
 
 __device__ __forceinline__ uint32_t brev_n(uint32_t x, uint32_t bits) { return __brev(x) >> (32 - bits); }
 
@@ -42,103 +41,90 @@ __device__ __forceinline__ uint64_t red6(uint64_t y, uint64_t t) {   // [0, 6t) 
 constexpr int kMaxDigit = 2;   // limbs per digit and special primes handled by the fused kernels
 
 using nttr::ColBase;
+using nttr::first_idx;
+using nttr::last_idx;
 using nttr::RowBase;
 using nttr::row_tw_entries;
 using nttr::stage_col_twiddles;
 using nttr::stage_row_twiddles;
+using nttr::sub_words;
+using nttr::SubMem;
 using nttr::tw_wait;
 
-// Dynamic shared memory (in words) of the column kernels: exchange tile,
+// Dynamic shared memory (words) of the column kernels F3/F5: exchange tiles,
 // kMaxDigit thread-private staging tiles (each thread reads back only what it
 // wrote), staged twiddles.
-template <int LA, int C>
+template <int LA, int LT, int C>
 __host__ __device__ constexpr size_t col_smem_words() {
-    return (size_t)((1 << LA) + (1 << LA) / (1 << (LA / 2))) * C + (size_t)kMaxDigit * (1 << LA) * C +
-           2 * (size_t)(1 << LA);
+    return (size_t)sub_words<LA, LT>() * C + (size_t)kMaxDigit * (1 << LA) * C + 2 * (size_t)(1 << LA);
 }
 // ... and of F4: exchange rows, staging, forward and inverse row twiddles.
-template <int LB, int R>
+template <int LB, int LT, int R>
 __host__ __device__ constexpr size_t f4_smem_words() {
-    return (size_t)R * ((1 << LB) + (1 << LB) / (1 << (LB / 2))) + (size_t)kMaxDigit * R * (1 << LB) +
-           4 * (size_t)row_tw_entries<LB, R>();
+    return (size_t)R * sub_words<LB, LT>() + (size_t)kMaxDigit * R * (1 << LB) + 4 * (size_t)row_tw_entries<LB, R>();
 }
 
 // ---------------------------------------------------------------------------
 // F1: grid (B * l1, N1 / R)
 // ---------------------------------------------------------------------------
-template <int LA, int LB, int R>
-__global__ void __launch_bounds__(R * (1 << (LB / 2)))
+template <int LA, int LB, int LT, int R>
+__global__ void __launch_bounds__(R * (1 << (LB - LT)))
     k_ks_f1(uint64_t* const* in, uint64_t* __restrict__ X0, uint64_t* __restrict__ X1, uint64_t* __restrict__ ext,
             const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t galois) {
-    constexpr int H = LB / 2, E = 1 << H, M = 1 << LB, S = M + M / E, LOGN = LA + LB, N = 1 << LOGN;
+    constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>(), LOGN = LA + LB, N = 1 << LOGN;
     __shared__ uint64_t sm[R * S];
     __shared__ ulonglong2 tws[row_tw_entries<LB, R>()];
-    const int tid = threadIdx.x, jr = tid / E, t = tid % E;
+    const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
     const uint32_t b = blockIdx.x / l1, j = blockIdx.x % l1;
     const int row = blockIdx.y * R + jr;
     const size_t roff = (size_t)row * M;
     const uint64_t q = tab.q[j], q2 = 2 * q;
-    const uint64_t* c0 = in[b] + (size_t)j * N;
+    const uint64_t* c0 = in[b] + (size_t)j * N + roff;
     const uint64_t* c1 = in[b] + ((size_t)l1 + j) * N;
     const uint32_t nd = kc->nd, nlx = kc->nlx;
     uint32_t d = 0;
     while (d + 1 < nd && j >= kc->dstart[d + 1]) d++;
     uint64_t* x0 = X0 + ((size_t)b * l1 + j) * N + roff;
     uint64_t* eo = ext + (((size_t)b * nd + d) * nlx + j) * N + roff;
-    uint64_t* sr = sm + jr * S;
-    stage_row_twiddles<LA, LB, R, R * E>(tws, tab.itw[j], blockIdx.y * R);
-    uint64_t v[E];
+    const SubMem sr{sm + jr * S, 1};
+    stage_row_twiddles<LA, LB, R, R * TH>(tws, tab.itw[j], blockIdx.y * R);
+    uint64_t v[K];
 #pragma unroll
-    for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = c1[roff + t + E * k];
-#pragma unroll
-    for (int k = 0; k < E; k++) {
-        const int c = t + E * k;
-        x0[c] = c0[roff + c];
+    for (int k = 0; k < K; k++) {
+        const int c = first_idx<LB, LT>(t, k);
+        v[k] = c1[roff + c];
+        x0[c] = c0[c];
         eo[c] = c1[perm_src((uint32_t)(roff + c), LOGN, galois)];
     }
+    nttr::relayout<LB, LT, 0, LB / LT - 1>(v, sr, t);
     tw_wait();
-#pragma unroll
-    for (int k = 0; k < E; k++) v[k] = sr[pad<H>(E * t + k)];
-    const RowBase<R> base{jr};
-    nttr::inv_consec<LB>(v, tws, base, t, q, q2);
-#pragma unroll
-    for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = v[k];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < E; k++) v[k] = sr[pad<H>(t + E * k)];
-    nttr::inv_stride<LB>(v, tws, base, q, q2);
+    nttr::inv_pass<LB, LT>(v, sr, tws, RowBase<R>{jr}, t, q, q2);
     uint64_t* x1 = X1 + ((size_t)b * l1 + j) * N + roff;
 #pragma unroll
-    for (int k = 0; k < E; k++) x1[t + E * k] = v[k];
+    for (int k = 0; k < K; k++) x1[first_idx<LB, LT>(t, k)] = v[k];
 }
 
-// forward column pass of y (stride layout in, consecutive-layout rows stored to o)
-template <int LA, int LB, int C>
-__device__ __forceinline__ void col_fwd_store(uint64_t (&y)[1 << (LA / 2)], uint64_t* sm, const ulonglong2* tws, int t,
+// forward column pass of y (phase-0 layout in) stored in the last layout to o
+template <int LA, int LB, int LT, int C>
+__device__ __forceinline__ void col_fwd_store(uint64_t (&y)[1 << LT], uint64_t* sm, const ulonglong2* tws, int t,
                                               int jc, uint64_t q, uint64_t* o) {
-    constexpr int H = LA / 2, E = 1 << H, N2 = 1 << LB;
-    nttr::fwd_stride<LA>(y, tws, ColBase{}, q, 2 * q);
+    constexpr int N2 = 1 << LB;
+    nttr::fwd_pass<LA, LT>(y, SubMem{sm + jc, C}, tws, ColBase{}, t, q, 2 * q);
 #pragma unroll
-    for (int k = 0; k < E; k++) sm[pad<H>(t + E * k) * C + jc] = y[k];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < E; k++) y[k] = sm[pad<H>(E * t + k) * C + jc];
-    nttr::fwd_consec<LA>(y, tws, ColBase{}, t, q, 2 * q);
-#pragma unroll
-    for (int k = 0; k < E; k++) o[(size_t)(E * t + k) * N2] = y[k];
+    for (int k = 0; k < (1 << LT); k++) o[(size_t)last_idx<LA, LT>(t, k) * N2] = y[k];
 }
 
 // ---------------------------------------------------------------------------
 // F3: grid (B * nd, N2 / C).  X1 holds c1 in coefficient form.
 // ---------------------------------------------------------------------------
-template <int LA, int LB, int C>
-__global__ void __launch_bounds__(C * (1 << (LA / 2)))
+template <int LA, int LB, int LT, int C>
+__global__ void __launch_bounds__(C * (1 << (LA - LT)))
     k_ks_f3(const uint64_t* __restrict__ X1, uint64_t* __restrict__ ext, const KsLevelConst* __restrict__ kc,
             DevTables tab, uint32_t l1, uint32_t L, uint32_t kinv) {
-    constexpr int H = LA / 2, E = 1 << H, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN;
+    constexpr int K = 1 << LT, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN;
     extern __shared__ uint64_t dsm[];
-    uint64_t* sm = dsm;                                   // exchange tile
-    uint64_t* st = sm + (M + M / E) * C;                  // staging: [i][row][col]
+    uint64_t* sm = dsm;                                   // exchange tiles
+    uint64_t* st = sm + sub_words<LA, LT>() * C;          // staging: [i][row][col]
     ulonglong2* tws = (ulonglong2*)(st + kMaxDigit * M * C);
     const int tid = threadIdx.x, t = tid / C, jc = tid % C;
     const uint32_t nd = kc->nd, nlx = kc->nlx;
@@ -151,12 +137,12 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
         const ulonglong2 h = kc->up_hinv[d][i];
         const uint64_t* src = X1 + ((size_t)b * l1 + d0 + i) * N;
 #pragma unroll
-        for (int k = 0; k < E; k++) {
-            const uint32_t p = (uint32_t)(t + E * k) * N2 + col;
-            const uint32_t e = (p * kinv) & (2u * N - 1);
+        for (int k = 0; k < K; k++) {
+            const int r = first_idx<LA, LT>(t, k);
+            const uint32_t e = ((uint32_t)r * N2 + col) * kinv & (2u * N - 1);
             uint64_t x = src[e & (N - 1)];
             if (e >= (uint32_t)N) x = negm(x, qi);
-            st[(i * M + t + E * k) * C + jc] = shoup(x, h.x, h.y, qi);
+            st[(i * M + r) * C + jc] = shoup(x, h.x, h.y, qi);
         }
     }
 #pragma unroll 1
@@ -164,20 +150,21 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
         if (jj >= d0 && jj < d0 + ds) continue;               // the digit's own limbs come from F1
         const int pi = ext_prime(jj, l1, L);
         const uint64_t tq = tab.q[pi];
-        stage_col_twiddles<LA, C * E>(tws, tab.tw[pi]);
-        uint64_t y[E];
+        stage_col_twiddles<LA, C * (M >> LT)>(tws, tab.tw[pi]);
+        uint64_t y[K];
 #pragma unroll
-        for (int k = 0; k < E; k++) y[k] = 0;
+        for (int k = 0; k < K; k++) y[k] = 0;
 #pragma unroll 1
         for (uint32_t i = 0; i < ds; i++) {
             const ulonglong2 h = kc->up_hat[d][i][jj];
 #pragma unroll
-            for (int k = 0; k < E; k++) y[k] += shoup_lazy(st[(i * M + t + E * k) * C + jc], h.x, h.y, tq);
+            for (int k = 0; k < K; k++)
+                y[k] += shoup_lazy(st[(i * M + first_idx<LA, LT>(t, k)) * C + jc], h.x, h.y, tq);
         }
 #pragma unroll
-        for (int k = 0; k < E; k++) y[k] = red6(y[k], tq);
+        for (int k = 0; k < K; k++) y[k] = red6(y[k], tq);
         tw_wait();
-        col_fwd_store<LA, LB, C>(y, sm, tws, t, jc, tq, ext + (((size_t)b * nd + d) * nlx + jj) * N + col);
+        col_fwd_store<LA, LB, LT, C>(y, sm, tws, t, jc, tq, ext + (((size_t)b * nd + d) * nlx + jj) * N + col);
         __syncthreads();
     }
 }
@@ -185,16 +172,16 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
 // ---------------------------------------------------------------------------
 // F4: grid (B * nlx, N1 / R).  acc = sum_d ext_d * key_d (both components).
 // ---------------------------------------------------------------------------
-template <int LA, int LB, int R>
-__global__ void __launch_bounds__(R * (1 << (LB / 2)))
+template <int LA, int LB, int LT, int R>
+__global__ void __launch_bounds__(R * (1 << (LB - LT)))
     k_ks_f4(const uint64_t* __restrict__ ext, const uint64_t* __restrict__ key, uint64_t* __restrict__ acc,
             const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L, uint32_t nb) {
-    constexpr int H = LB / 2, E = 1 << H, M = 1 << LB, S = M + M / E, LOGN = LA + LB, N = 1 << LOGN;
+    constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>(), LOGN = LA + LB, N = 1 << LOGN;
     constexpr int TWN = row_tw_entries<LB, R>();
     extern __shared__ uint64_t dsm[];
-    const int tid = threadIdx.x, jr = tid / E, t = tid % E;
-    uint64_t* sr = dsm + jr * S;                             // exchange row
-    uint64_t* st = dsm + R * S + jr * M + E * t;             // staging: digit d at st[d * R * M + k]
+    const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
+    const SubMem sr{dsm + jr * S, 1};                        // exchange row
+    uint64_t* st = dsm + R * S + jr * M;                     // staging: digit d at st[d * R * M + last_idx]
     ulonglong2* twf = (ulonglong2*)(dsm + R * S + kMaxDigit * R * M);
     ulonglong2* twi = twf + TWN;
     const uint32_t nd = kc->nd, nlx = kc->nlx;
@@ -204,61 +191,51 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
     const int row = blockIdx.y * R + jr;
     const size_t roff = (size_t)row * M;
     const RowBase<R> base{jr};
-    stage_row_twiddles<LA, LB, R, R * E>(twf, tab.tw[pi], blockIdx.y * R);
-    if (jj >= l1) stage_row_twiddles<LA, LB, R, R * E>(twi, tab.itw[pi], blockIdx.y * R);
+    stage_row_twiddles<LA, LB, R, R * TH>(twf, tab.tw[pi], blockIdx.y * R);
+    if (jj >= l1) stage_row_twiddles<LA, LB, R, R * TH>(twi, tab.itw[pi], blockIdx.y * R);
     tw_wait();
-    uint64_t v[E];
-    // extended limb jj of every digit, NTT form, consecutive layout, staged
+    uint64_t v[K];
+    // extended limb jj of every digit, NTT form, last-phase layout, staged
 #pragma unroll 1
     for (uint32_t d = 0; d < nd; d++) {
         const uint64_t* e = ext + (((size_t)b * nd + d) * nlx + jj) * N + roff;
         if (jj >= kc->dstart[d] && jj < kc->dstart[d] + kc->dsz[d]) {
 #pragma unroll
-            for (int k = 0; k < E; k++) v[k] = e[E * t + k];
+            for (int k = 0; k < K; k++) v[k] = e[last_idx<LB, LT>(t, k)];
         } else {
 #pragma unroll
-            for (int k = 0; k < E; k++) v[k] = e[t + E * k];
-            nttr::fwd_stride<LB>(v, twf, base, q, q2);
-#pragma unroll
-            for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = v[k];
-            __syncthreads();
-#pragma unroll
-            for (int k = 0; k < E; k++) v[k] = sr[pad<H>(E * t + k)];
-            nttr::fwd_consec<LB>(v, twf, base, t, q, q2);
+            for (int k = 0; k < K; k++) v[k] = e[first_idx<LB, LT>(t, k)];
+            nttr::fwd_pass<LB, LT>(v, sr, twf, base, t, q, q2);
             __syncthreads();
         }
 #pragma unroll
-        for (int k = 0; k < E; k++) st[d * R * M + k] = v[k];
+        for (int k = 0; k < K; k++) st[d * R * M + last_idx<LB, LT>(t, k)] = v[k];
     }
     // inner product per key component, then store (special primes: inverse row pass)
 #pragma unroll 1
     for (uint32_t comp = 0; comp < 2; comp++) {
 #pragma unroll
-        for (int k = 0; k < E; k++) v[k] = 0;
+        for (int k = 0; k < K; k++) v[k] = 0;
 #pragma unroll 1
         for (uint32_t d = 0; d < nd; d++) {
-            const uint64_t* kk = key + ((size_t)(d * 2 + comp) * nb + pi) * N + roff + E * t;
+            const uint64_t* kk = key + ((size_t)(d * 2 + comp) * nb + pi) * N + roff;
 #pragma unroll
-            for (int k = 0; k < E; k++) {
-                const uint64_t x = v[k] + mont_lazy(st[d * R * M + k], kk[k], q, qn);
+            for (int k = 0; k < K; k++) {
+                const int c = last_idx<LB, LT>(t, k);
+                const uint64_t x = v[k] + mont_lazy(st[d * R * M + c], kk[c], q, qn);
                 v[k] = x >= q2 ? x - q2 : x;
             }
         }
         if (jj < l1) {
 #pragma unroll
-            for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = reduce2(v[k], q);
+            for (int k = 0; k < K; k++) v[k] = reduce2(v[k], q);
+            nttr::relayout<LB, LT, LB / LT - 1, 0>(v, sr, t);
         } else {
-            nttr::inv_consec<LB>(v, twi, base, t, q, q2);
-#pragma unroll
-            for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = v[k];
+            nttr::inv_pass<LB, LT>(v, sr, twi, base, t, q, q2);
         }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < E; k++) v[k] = sr[pad<H>(t + E * k)];
-        if (jj >= l1) nttr::inv_stride<LB>(v, twi, base, q, q2);
         uint64_t* o = acc + (((size_t)b * 2 + comp) * nlx + jj) * N + roff;
 #pragma unroll
-        for (int k = 0; k < E; k++) o[t + E * k] = v[k];
+        for (int k = 0; k < K; k++) o[first_idx<LB, LT>(t, k)] = v[k];
         __syncthreads();
     }
 }
@@ -266,57 +243,52 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
 // ---------------------------------------------------------------------------
 // F5: grid (B * 2, N2 / C).  conv = Conv_{P -> Q_l}(acc's special-prime limbs).
 // ---------------------------------------------------------------------------
-template <int LA, int LB, int C>
-__global__ void __launch_bounds__(C * (1 << (LA / 2)))
+template <int LA, int LB, int LT, int C>
+__global__ void __launch_bounds__(C * (1 << (LA - LT)))
     k_ks_f5(const uint64_t* __restrict__ acc, uint64_t* __restrict__ conv, const KsLevelConst* __restrict__ kc,
             DevTables tab, uint32_t l1, uint32_t L, uint32_t alpha) {
-    constexpr int H = LA / 2, E = 1 << H, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN;
+    constexpr int K = 1 << LT, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN;
     extern __shared__ uint64_t dsm[];
     uint64_t* sm = dsm;
-    uint64_t* st = sm + (M + M / E) * C;                  // staging: [i][row][col]
+    uint64_t* st = sm + sub_words<LA, LT>() * C;          // staging: [i][row][col]
     ulonglong2* tws = (ulonglong2*)(st + kMaxDigit * M * C);
     const int tid = threadIdx.x, t = tid / C, jc = tid % C;
     const uint32_t b = blockIdx.x / 2, comp = blockIdx.x % 2;
     const int col = blockIdx.y * C + jc;
     const uint32_t nlx = l1 + alpha;
-    uint64_t y[E];
+    uint64_t y[K];
 #pragma unroll 1
     for (uint32_t i = 0; i < alpha; i++) {
         const int pi = L + 1 + i;
         const uint64_t p = tab.q[pi], p2 = 2 * p;
         const uint64_t* src = acc + (((size_t)b * 2 + comp) * nlx + l1 + i) * N + col;
-        stage_col_twiddles<LA, C * E>(tws, tab.itw[pi]);
+        stage_col_twiddles<LA, C * (M >> LT)>(tws, tab.itw[pi]);
 #pragma unroll
-        for (int k = 0; k < E; k++) y[k] = src[(size_t)(E * t + k) * N2];
+        for (int k = 0; k < K; k++) y[k] = src[(size_t)last_idx<LA, LT>(t, k) * N2];
         tw_wait();
-        nttr::inv_consec<LA>(y, tws, ColBase{}, t, p, p2);
-#pragma unroll
-        for (int k = 0; k < E; k++) sm[pad<H>(E * t + k) * C + jc] = y[k];
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < E; k++) y[k] = sm[pad<H>(t + E * k) * C + jc];
-        nttr::inv_stride<LA>(y, tws, ColBase{}, p, p2);
+        nttr::inv_pass<LA, LT>(y, SubMem{sm + jc, C}, tws, ColBase{}, t, p, p2);
         const ulonglong2 h = kc->dn_hinv[i];          // N^-1 * (P/p_i)^-1 mod p_i
 #pragma unroll
-        for (int k = 0; k < E; k++) st[(i * M + t + E * k) * C + jc] = shoup(y[k], h.x, h.y, p);
+        for (int k = 0; k < K; k++) st[(i * M + first_idx<LA, LT>(t, k)) * C + jc] = shoup(y[k], h.x, h.y, p);
         __syncthreads();
     }
 #pragma unroll 1
     for (uint32_t j = 0; j < l1; j++) {
         const uint64_t q = tab.q[j];
-        stage_col_twiddles<LA, C * E>(tws, tab.tw[j]);
+        stage_col_twiddles<LA, C * (M >> LT)>(tws, tab.tw[j]);
 #pragma unroll
-        for (int k = 0; k < E; k++) y[k] = 0;
+        for (int k = 0; k < K; k++) y[k] = 0;
 #pragma unroll 1
         for (uint32_t i = 0; i < alpha; i++) {
             const ulonglong2 h = kc->dn_hat[i][j];
 #pragma unroll
-            for (int k = 0; k < E; k++) y[k] += shoup_lazy(st[(i * M + t + E * k) * C + jc], h.x, h.y, q);
+            for (int k = 0; k < K; k++)
+                y[k] += shoup_lazy(st[(i * M + first_idx<LA, LT>(t, k)) * C + jc], h.x, h.y, q);
         }
 #pragma unroll
-        for (int k = 0; k < E; k++) y[k] = red6(y[k], q);
+        for (int k = 0; k < K; k++) y[k] = red6(y[k], q);
         tw_wait();
-        col_fwd_store<LA, LB, C>(y, sm, tws, t, jc, q, conv + (((size_t)b * 2 + comp) * l1 + j) * N + col);
+        col_fwd_store<LA, LB, LT, C>(y, sm, tws, t, jc, q, conv + (((size_t)b * 2 + comp) * l1 + j) * N + col);
         __syncthreads();
     }
 }
@@ -324,15 +296,15 @@ __global__ void __launch_bounds__(C * (1 << (LA / 2)))
 // ---------------------------------------------------------------------------
 // F6: grid (B * l1, N1 / R).  out = (acc - conv) * P^-1 + sigma(c0) (+ add)
 // ---------------------------------------------------------------------------
-template <int LA, int LB, int R>
-__global__ void __launch_bounds__(R * (1 << (LB / 2)))
+template <int LA, int LB, int LT, int R>
+__global__ void __launch_bounds__(R * (1 << (LB - LT)))
     k_ks_f6(const uint64_t* __restrict__ conv, const uint64_t* __restrict__ acc, const uint64_t* __restrict__ X0,
             uint64_t* const* out, uint64_t* const* add, const KsLevelConst* __restrict__ kc, DevTables tab,
             uint32_t l1, uint32_t galois) {
-    constexpr int H = LB / 2, E = 1 << H, M = 1 << LB, S = M + M / E, LOGN = LA + LB, N = 1 << LOGN;
+    constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>(), LOGN = LA + LB, N = 1 << LOGN;
     __shared__ uint64_t sm[R * S];
     __shared__ ulonglong2 tws[row_tw_entries<LB, R>()];
-    const int tid = threadIdx.x, jr = tid / E, t = tid % E;
+    const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
     const uint32_t b = blockIdx.x / l1, j = blockIdx.x % l1;
     const uint32_t nlx = kc->nlx;
     const int row = blockIdx.y * R + jr;
@@ -340,41 +312,36 @@ __global__ void __launch_bounds__(R * (1 << (LB / 2)))
     const uint64_t q = tab.q[j], q2 = 2 * q;
     const ulonglong2 pinv = kc->pinv[j];
     const RowBase<R> base{jr};
-    uint64_t* sr = sm + jr * S;
-    stage_row_twiddles<LA, LB, R, R * E>(tws, tab.tw[j], blockIdx.y * R);
-    uint64_t v[E];
-#pragma unroll
+    const SubMem sr{sm + jr * S, 1};
+    stage_row_twiddles<LA, LB, R, R * TH>(tws, tab.tw[j], blockIdx.y * R);
+    uint64_t v[K];
+#pragma unroll 1
     for (int comp = 0; comp < 2; comp++) {
         const uint64_t* cv = conv + (((size_t)b * 2 + comp) * l1 + j) * N + roff;
 #pragma unroll
-        for (int k = 0; k < E; k++) v[k] = cv[t + E * k];
+        for (int k = 0; k < K; k++) v[k] = cv[first_idx<LB, LT>(t, k)];
         if (comp == 0) tw_wait();
         else __syncthreads();
-        nttr::fwd_stride<LB>(v, tws, base, q, q2);
+        nttr::fwd_pass<LB, LT>(v, sr, tws, base, t, q, q2);
+        const uint64_t* av = acc + (((size_t)b * 2 + comp) * nlx + j) * N + roff;
+        const uint64_t* ad = add ? add[b] + ((size_t)comp * l1 + j) * N + roff : nullptr;
 #pragma unroll
-        for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = v[k];
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < E; k++) v[k] = sr[pad<H>(E * t + k)];
-        nttr::fwd_consec<LB>(v, tws, base, t, q, q2);
-        const uint64_t* av = acc + (((size_t)b * 2 + comp) * nlx + j) * N + roff + E * t;
-        const uint64_t* ad = add ? add[b] + ((size_t)comp * l1 + j) * N + roff + E * t : nullptr;
-#pragma unroll
-        for (int k = 0; k < E; k++) {
-            uint64_t o = shoup(subm(av[k], nttr::reduce4(v[k], q, q2), q), pinv.x, pinv.y, q);
+        for (int k = 0; k < K; k++) {
+            const int c = last_idx<LB, LT>(t, k);
+            uint64_t o = shoup(subm(av[c], nttr::reduce4(v[k], q, q2), q), pinv.x, pinv.y, q);
             if (comp == 0)
-                o = addm(o, X0[((size_t)b * l1 + j) * N + perm_src((uint32_t)(roff + E * t + k), LOGN, galois)], q);
-            if (ad) o = addm(o, ad[k], q);
-            sr[pad<H>(E * t + k)] = o;
+                o = addm(o, X0[((size_t)b * l1 + j) * N + perm_src((uint32_t)(roff + c), LOGN, galois)], q);
+            if (ad) o = addm(o, ad[c], q);
+            v[k] = o;
         }
-        __syncthreads();
+        nttr::relayout<LB, LT, LB / LT - 1, 0>(v, sr, t);
         uint64_t* o = out[b] + ((size_t)comp * l1 + j) * N + roff;
 #pragma unroll
-        for (int k = 0; k < E; k++) o[t + E * k] = sr[pad<H>(t + E * k)];
+        for (int k = 0; k < K; k++) o[first_idx<LB, LT>(t, k)] = v[k];
     }
 }
 
-template <int LA, int LB, int C, int R>
+template <int LA, int LB, int LT, int C, int R>
 cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galois, uint32_t level, uint32_t B,
                             uint64_t* const* d_in, uint64_t* const* d_out, uint64_t* const* d_add, uint64_t* scratch,
                             cudaStream_t s) {
@@ -387,19 +354,17 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
     uint64_t* ext = X1 + (size_t)B * l1 * N;
     uint64_t* acc = ext + (size_t)B * nd * nlx * N;
     uint64_t* conv = acc + (size_t)B * 2 * nlx * N;
-    const int tr = R * (1 << (LB / 2)), tc = C * (1 << (LA / 2));
-    const double lw = 8.0 * N;                                  // bytes of one limb
-    const double bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;   // mul ops of one limb pass
-    static bool attrs = [] {
-        cudaFuncSetAttribute(k_ks_f3<LA, LB, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(8 * col_smem_words<LA, C>()));
-        cudaFuncSetAttribute(k_ks_f5<LA, LB, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(8 * col_smem_words<LA, C>()));
-        cudaFuncSetAttribute(k_ks_f4<LA, LB, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(8 * f4_smem_words<LB, R>()));
+    const int tr = R * (1 << (LB - LT)), tc = C * (1 << (LA - LT));
+    const size_t col_smem = 8 * col_smem_words<LA, LT, C>(), f4_smem = 8 * f4_smem_words<LB, LT, R>();
+    static bool attrs = [&] {
+        cudaFuncSetAttribute(k_ks_f3<LA, LB, LT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem);
+        cudaFuncSetAttribute(k_ks_f5<LA, LB, LT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem);
+        cudaFuncSetAttribute(k_ks_f4<LA, LB, LT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f4_smem);
         return true;
     }();
     (void)attrs;
+    const double lw = 8.0 * N;                                              // bytes of one limb
+    const double bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;    // mul ops of one limb pass
     uint32_t targets = 0, gathers = 0;
     for (uint32_t d = 0; d < nd; d++) {
         targets += nlx - K.dsz[d];
@@ -407,7 +372,8 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
     }
     {
         ProfScope ps(BM_KERNEL_NTT, s, lw * B * l1 * 6, bf_r * B * l1);
-        k_ks_f1<LA, LB, R><<<dim3(B * l1, N1 / R), tr, 0, s>>>(d_in, X0, X1, ext, kc, c.tab, l1, (uint32_t)galois);
+        k_ks_f1<LA, LB, LT, R><<<dim3(B * l1, N1 / R), tr, 0, s>>>(d_in, X0, X1, ext, kc, c.tab, l1,
+                                                                     (uint32_t)galois);
     }
     LimbBatch xb{X1, B, (uint64_t)l1 * N, 0, l1, 0};
     for (uint32_t k = 0; k < l1; k++) xb.set(k, k);
@@ -416,24 +382,21 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
     {
         ProfScope ps(BM_KERNEL_MODUP, s, lw * B * (gathers + targets), bf_c * B * targets);
         const uint32_t kinv = (uint32_t)h_invmod_pow2(galois, 2ull * N);
-        k_ks_f3<LA, LB, C><<<dim3(B * nd, N2 / C), tc, 8 * col_smem_words<LA, C>(), s>>>(X1, ext, kc, c.tab, l1, c.L,
-                                                                                   kinv);
+        k_ks_f3<LA, LB, LT, C><<<dim3(B * nd, N2 / C), tc, col_smem, s>>>(X1, ext, kc, c.tab, l1, c.L, kinv);
     }
     {
         ProfScope ps(BM_KERNEL_KS_IP, s, lw * nlx * ((double)B * nd + 2.0 * nd + 2.0 * B),
                      bf_r * B * (targets + 2.0 * alpha));
-        k_ks_f4<LA, LB, R><<<dim3(B * nlx, N1 / R), tr, 8 * f4_smem_words<LB, R>(), s>>>(ext, key, acc, kc, c.tab, l1,
-                                                                                     c.L, c.nb);
+        k_ks_f4<LA, LB, LT, R><<<dim3(B * nlx, N1 / R), tr, f4_smem, s>>>(ext, key, acc, kc, c.tab, l1, c.L, c.nb);
     }
     {
         ProfScope ps(BM_KERNEL_MODDOWN, s, lw * B * 2 * (alpha + l1), bf_c * B * 2 * (alpha + l1));
-        k_ks_f5<LA, LB, C><<<dim3(B * 2, N2 / C), tc, 8 * col_smem_words<LA, C>(), s>>>(acc, conv, kc, c.tab, l1, c.L,
-                                                                                   alpha);
+        k_ks_f5<LA, LB, LT, C><<<dim3(B * 2, N2 / C), tc, col_smem, s>>>(acc, conv, kc, c.tab, l1, c.L, alpha);
     }
     {
         ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * B * l1 * (2 + 2 + 1 + 2 + (d_add ? 2 : 0)), bf_r * B * 2 * l1);
-        k_ks_f6<LA, LB, R><<<dim3(B * l1, N1 / R), tr, 0, s>>>(conv, acc, X0, d_out, d_add, kc, c.tab, l1,
-                                                                 (uint32_t)galois);
+        k_ks_f6<LA, LB, LT, R><<<dim3(B * l1, N1 / R), tr, 0, s>>>(conv, acc, X0, d_out, d_add, kc, c.tab, l1,
+                                                                     (uint32_t)galois);
     }
     return cudaGetLastError();
 }
@@ -452,8 +415,8 @@ cudaError_t ks_rotate_fused(const Context& c, const uint64_t* key, uint64_t galo
                             uint64_t* const* d_in, uint64_t* const* d_out, uint64_t* const* d_add, uint64_t* scratch,
                             cudaStream_t s) {
     if (B == 0) return cudaSuccess;
-    if (c.log_n == 16) return ks_fused_launch<8, 8, 4, 4>(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
-    if (c.log_n == 12) return ks_fused_launch<6, 6, 8, 8>(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
+    if (c.log_n == 16) return ks_fused_launch<8, 8, 2, 2, 2>(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
+    if (c.log_n == 12) return ks_fused_launch<6, 6, 2, 8, 8>(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
     return cudaErrorInvalidValue;
 }
 

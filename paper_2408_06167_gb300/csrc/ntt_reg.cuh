@@ -64,55 +64,90 @@ __device__ __forceinline__ void stage(uint64_t (&v)[E], const ulonglong2* __rest
     }
 }
 
-// Forward stages S..P/2-1 of a sub-transform, stride layout (thread holds t + E*k):
-// stage s pairs k and k + 2^(P/2-1-s); block blk of stage s uses W[base(s) + blk].
-template <int P, int S = 0, typename BaseF>
-__device__ __forceinline__ void fwd_stride(uint64_t (&v)[1 << (P / 2)], const ulonglong2* __restrict__ tw, BaseF base,
-                                           uint64_t q, uint64_t q2) {
-    constexpr int H = P / 2;
-    if constexpr (S < H) {
-        stage<1 << H, (1 << (H - 1 - S)), true>(v, tw, base(S), q, q2);
-        fwd_stride<P, S + 1>(v, tw, base, q, q2);
+// A 2^P-point sub-transform is processed by 2^(P-LT) threads holding 2^LT
+// registers each, in P/LT phases of LT stages.  In phase h thread t holds the
+// elements pidx(h, t, k) = ((t >> lb) << (lb + LT)) | (k << lb) | (t mod 2^lb),
+// lb = P - LT*(h+1), so stage s = LT*h + s' pairs registers k and k + 2^(LT-1-s')
+// and its block blk (= k >> (LT - s')) uses twiddle W[base(s) + ((t >> lb) << s') + blk].
+// Phase 0 is the "stride" layout (t + 2^(P-LT) k), the last phase the
+// "consecutive" one (2^LT t + k).
+template <int P, int LT, int h>
+__device__ __forceinline__ int pidx(int t, int k) {
+    constexpr int lb = P - LT * (h + 1);
+    return ((t >> lb) << (lb + LT)) | (k << lb) | (t & ((1 << lb) - 1));
+}
+
+// padded shared-memory index (one spare word per 2^LT): keeps every phase layout
+// within two wavefronts per warp access
+template <int LT>
+__device__ __forceinline__ int padx(int x) { return x + (x >> LT); }
+template <int P, int LT>
+__host__ __device__ constexpr int sub_words() { return (1 << P) + ((1 << P) >> LT); }
+
+// Shared-memory view of one sub-transform: element x at base[padx(x) * stride].
+struct SubMem {
+    uint64_t* base;
+    int stride;
+    __device__ __forceinline__ uint64_t& operator[](int px) const { return base[px * stride]; }
+};
+
+template <int P, int LT, int h, int S = 0, typename BaseF>
+__device__ __forceinline__ void fwd_phase(uint64_t (&v)[1 << LT], const ulonglong2* __restrict__ tw, BaseF base,
+                                          int t, uint64_t q, uint64_t q2) {
+    if constexpr (S < LT) {
+        constexpr int lb = P - LT * (h + 1);
+        stage<1 << LT, (1 << (LT - 1 - S)), true>(v, tw, base(LT * h + S) + ((t >> lb) << S), q, q2);
+        fwd_phase<P, LT, h, S + 1>(v, tw, base, t, q, q2);
     }
 }
 
-// Forward stages S..P-1 (S >= P/2), consecutive layout (thread t holds E*t + k):
-// stage s pairs k and k + 2^(P-1-s); the first block's twiddle is W[base(s) + (E*t >> (P-s))].
-template <int P, int S = P / 2, typename BaseF>
-__device__ __forceinline__ void fwd_consec(uint64_t (&v)[1 << (P / 2)], const ulonglong2* __restrict__ tw, BaseF base,
-                                           int t, uint64_t q, uint64_t q2) {
-    constexpr int E = 1 << (P / 2);
-    if constexpr (S < P) {
-        stage<E, (1 << (P - 1 - S)), true>(v, tw, base(S) + ((E * t) >> (P - S)), q, q2);
-        fwd_consec<P, S + 1>(v, tw, base, t, q, q2);
-    }
-}
-
-// Inverse stages S..P/2 downwards, consecutive layout.
-template <int P, int S = P - 1, typename BaseF>
-__device__ __forceinline__ void inv_consec(uint64_t (&v)[1 << (P / 2)], const ulonglong2* __restrict__ tw, BaseF base,
-                                           int t, uint64_t q, uint64_t q2) {
-    constexpr int E = 1 << (P / 2);
-    if constexpr (S >= P / 2) {
-        stage<E, (1 << (P - 1 - S)), false>(v, tw, base(S) + ((E * t) >> (P - S)), q, q2);
-        inv_consec<P, S - 1>(v, tw, base, t, q, q2);
-    }
-}
-
-// Inverse stages S..0 downwards, stride layout.
-template <int P, int S = P / 2 - 1, typename BaseF>
-__device__ __forceinline__ void inv_stride(uint64_t (&v)[1 << (P / 2)], const ulonglong2* __restrict__ tw, BaseF base,
-                                           uint64_t q, uint64_t q2) {
-    constexpr int H = P / 2;
+template <int P, int LT, int h, int S = LT - 1, typename BaseF>
+__device__ __forceinline__ void inv_phase(uint64_t (&v)[1 << LT], const ulonglong2* __restrict__ tw, BaseF base,
+                                          int t, uint64_t q, uint64_t q2) {
     if constexpr (S >= 0) {
-        stage<1 << H, (1 << (H - 1 - S)), false>(v, tw, base(S), q, q2);
-        inv_stride<P, S - 1>(v, tw, base, q, q2);
+        constexpr int lb = P - LT * (h + 1);
+        stage<1 << LT, (1 << (LT - 1 - S)), false>(v, tw, base(LT * h + S) + ((t >> lb) << S), q, q2);
+        inv_phase<P, LT, h, S - 1>(v, tw, base, t, q, q2);
     }
 }
 
-// padded shared-memory index of sub-transform element r (one spare word per E)
-template <int H>
-__device__ __forceinline__ int pad(int r) { return r + (r >> H); }
+// Moves v from phase-h1 layout to phase-h2 layout through shared memory (one
+// barrier).  Safe back to back: each thread only overwrites positions it read.
+template <int P, int LT, int h1, int h2>
+__device__ __forceinline__ void relayout(uint64_t (&v)[1 << LT], const SubMem& sm, int t) {
+#pragma unroll
+    for (int k = 0; k < (1 << LT); k++) sm[padx<LT>(pidx<P, LT, h1>(t, k))] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < (1 << LT); k++) v[k] = sm[padx<LT>(pidx<P, LT, h2>(t, k))];
+}
+
+// All forward stages: v in phase-0 layout on entry, last-phase layout on exit.
+template <int P, int LT, int h = 0, typename BaseF>
+__device__ __forceinline__ void fwd_pass(uint64_t (&v)[1 << LT], const SubMem& sm, const ulonglong2* __restrict__ tw,
+                                         BaseF base, int t, uint64_t q, uint64_t q2) {
+    fwd_phase<P, LT, h>(v, tw, base, t, q, q2);
+    if constexpr (h + 1 < P / LT) {
+        relayout<P, LT, h, h + 1>(v, sm, t);
+        fwd_pass<P, LT, h + 1>(v, sm, tw, base, t, q, q2);
+    }
+}
+
+// All inverse stages: v in last-phase layout on entry, phase-0 layout on exit.
+template <int P, int LT, int h = P / LT - 1, typename BaseF>
+__device__ __forceinline__ void inv_pass(uint64_t (&v)[1 << LT], const SubMem& sm, const ulonglong2* __restrict__ tw,
+                                         BaseF base, int t, uint64_t q, uint64_t q2) {
+    inv_phase<P, LT, h>(v, tw, base, t, q, q2);
+    if constexpr (h > 0) {
+        relayout<P, LT, h, h - 1>(v, sm, t);
+        inv_pass<P, LT, h - 1>(v, sm, tw, base, t, q, q2);
+    }
+}
+
+template <int P, int LT>
+__device__ __forceinline__ int first_idx(int t, int k) { return pidx<P, LT, 0>(t, k); }
+template <int P, int LT>
+__device__ __forceinline__ int last_idx(int t, int k) { return pidx<P, LT, P / LT - 1>(t, k); }
 
 // Twiddles a column pass uses: entries 1 .. 2^LA - 1 of the table, copied to
 // shared memory (index unchanged) with asynchronous copies issued all at once by
@@ -169,119 +204,92 @@ struct ColBase {
 // ---------------------------------------------------------------------------
 
 // Column pass, forward: global stages 0..LA-1 on C columns.  Output lazy [0, 4q).
-template <int LA, int LB, int C>
-__global__ void __launch_bounds__(C * (1 << (LA / 2))) k_col_fwd(LimbBatch lb, DevTables tab) {
-    constexpr int H = LA / 2, E = 1 << H, M = 1 << LA, N2 = 1 << LB;
-    __shared__ uint64_t sm[(M + M / E) * C];
+template <int LA, int LB, int LT, int C>
+__global__ void __launch_bounds__(C * (1 << (LA - LT))) k_col_fwd(LimbBatch lb, DevTables tab) {
+    constexpr int K = 1 << LT, M = 1 << LA, N2 = 1 << LB;
+    __shared__ uint64_t sm[sub_words<LA, LT>() * C];
     __shared__ ulonglong2 tws[M];
     const int tid = threadIdx.x, t = tid / C, j = tid % C;
     const int pi = lb.prime(blockIdx.x % lb.nl);
     uint64_t* a = limb_at(lb, blockIdx.x, M * N2) + blockIdx.y * C + j;
     const uint64_t q = tab.q[pi], q2 = 2 * q;
-    stage_col_twiddles<LA, C * E>(tws, tab.tw[pi]);
-    uint64_t v[E];
+    stage_col_twiddles<LA, C * (M >> LT)>(tws, tab.tw[pi]);
+    uint64_t v[K];
 #pragma unroll
-    for (int k = 0; k < E; k++) v[k] = a[(size_t)(t + E * k) * N2];
+    for (int k = 0; k < K; k++) v[k] = a[(size_t)first_idx<LA, LT>(t, k) * N2];
     tw_wait();
-    fwd_stride<LA>(v, tws, ColBase{}, q, q2);
+    fwd_pass<LA, LT>(v, SubMem{sm + j, C}, tws, ColBase{}, t, q, q2);
 #pragma unroll
-    for (int k = 0; k < E; k++) sm[pad<H>(t + E * k) * C + j] = v[k];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < E; k++) v[k] = sm[pad<H>(E * t + k) * C + j];
-    fwd_consec<LA>(v, tws, ColBase{}, t, q, q2);
-#pragma unroll
-    for (int k = 0; k < E; k++) a[(size_t)(E * t + k) * N2] = v[k];
+    for (int k = 0; k < K; k++) a[(size_t)last_idx<LA, LT>(t, k) * N2] = v[k];
 }
 
 // Row pass, forward: global stages LA..LA+LB-1 on R rows.  Input [0, 4q), output [0, q).
-template <int LA, int LB, int R>
-__global__ void __launch_bounds__(R * (1 << (LB / 2))) k_row_fwd(LimbBatch lb, DevTables tab) {
-    constexpr int H = LB / 2, E = 1 << H, M = 1 << LB, S = M + M / E;
+template <int LA, int LB, int LT, int R>
+__global__ void __launch_bounds__(R * (1 << (LB - LT))) k_row_fwd(LimbBatch lb, DevTables tab) {
+    constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>();
     __shared__ uint64_t sm[R * S];
     __shared__ ulonglong2 tws[row_tw_entries<LB, R>()];
-    const int tid = threadIdx.x, jr = tid / E, t = tid % E;
+    const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
     const int row = blockIdx.y * R + jr;
     const int pi = lb.prime(blockIdx.x % lb.nl);
     uint64_t* a = limb_at(lb, blockIdx.x, (1 << LA) * M) + (size_t)row * M;
     const uint64_t q = tab.q[pi], q2 = 2 * q;
-    const RowBase<R> base{jr};
-    uint64_t* sr = sm + jr * S;
-    stage_row_twiddles<LA, LB, R, R * E>(tws, tab.tw[pi], blockIdx.y * R);
-    uint64_t v[E];
+    const SubMem sr{sm + jr * S, 1};
+    stage_row_twiddles<LA, LB, R, R * TH>(tws, tab.tw[pi], blockIdx.y * R);
+    uint64_t v[K];
 #pragma unroll
-    for (int k = 0; k < E; k++) v[k] = a[t + E * k];
+    for (int k = 0; k < K; k++) v[k] = a[first_idx<LB, LT>(t, k)];
     tw_wait();
-    fwd_stride<LB>(v, tws, base, q, q2);
+    fwd_pass<LB, LT>(v, sr, tws, RowBase<R>{jr}, t, q, q2);
 #pragma unroll
-    for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = v[k];
-    __syncthreads();
+    for (int k = 0; k < K; k++) v[k] = reduce4(v[k], q, q2);
+    relayout<LB, LT, LB / LT - 1, 0>(v, sr, t);
 #pragma unroll
-    for (int k = 0; k < E; k++) v[k] = sr[pad<H>(E * t + k)];
-    fwd_consec<LB>(v, tws, base, t, q, q2);
-#pragma unroll
-    for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = reduce4(v[k], q, q2);
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < E; k++) a[t + E * k] = sr[pad<H>(t + E * k)];
+    for (int k = 0; k < K; k++) a[first_idx<LB, LT>(t, k)] = v[k];
 }
 
 // Row pass, inverse: global stages LA+LB-1..LA on R rows.  Input [0, 2q), output [0, 2q).
-template <int LA, int LB, int R>
-__global__ void __launch_bounds__(R * (1 << (LB / 2))) k_row_inv(LimbBatch lb, DevTables tab) {
-    constexpr int H = LB / 2, E = 1 << H, M = 1 << LB, S = M + M / E;
+template <int LA, int LB, int LT, int R>
+__global__ void __launch_bounds__(R * (1 << (LB - LT))) k_row_inv(LimbBatch lb, DevTables tab) {
+    constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>();
     __shared__ uint64_t sm[R * S];
     __shared__ ulonglong2 tws[row_tw_entries<LB, R>()];
-    const int tid = threadIdx.x, jr = tid / E, t = tid % E;
+    const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
     const int row = blockIdx.y * R + jr;
     const int pi = lb.prime(blockIdx.x % lb.nl);
     uint64_t* a = limb_at(lb, blockIdx.x, (1 << LA) * M) + (size_t)row * M;
     const uint64_t q = tab.q[pi], q2 = 2 * q;
-    const RowBase<R> base{jr};
-    uint64_t* sr = sm + jr * S;
-    stage_row_twiddles<LA, LB, R, R * E>(tws, tab.itw[pi], blockIdx.y * R);
-    uint64_t v[E];
+    const SubMem sr{sm + jr * S, 1};
+    stage_row_twiddles<LA, LB, R, R * TH>(tws, tab.itw[pi], blockIdx.y * R);
+    uint64_t v[K];
 #pragma unroll
-    for (int k = 0; k < E; k++) sr[pad<H>(t + E * k)] = a[t + E * k];
+    for (int k = 0; k < K; k++) v[k] = a[first_idx<LB, LT>(t, k)];
+    relayout<LB, LT, 0, LB / LT - 1>(v, sr, t);
     tw_wait();
+    inv_pass<LB, LT>(v, sr, tws, RowBase<R>{jr}, t, q, q2);
 #pragma unroll
-    for (int k = 0; k < E; k++) v[k] = sr[pad<H>(E * t + k)];
-    inv_consec<LB>(v, tws, base, t, q, q2);
-#pragma unroll
-    for (int k = 0; k < E; k++) sr[pad<H>(E * t + k)] = v[k];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < E; k++) v[k] = sr[pad<H>(t + E * k)];
-    inv_stride<LB>(v, tws, base, q, q2);
-#pragma unroll
-    for (int k = 0; k < E; k++) a[t + E * k] = v[k];
+    for (int k = 0; k < K; k++) a[first_idx<LB, LT>(t, k)] = v[k];
 }
 
 // Column pass, inverse: global stages LA-1..0 on C columns, then * N^-1.  Output [0, q).
-template <int LA, int LB, int C>
-__global__ void __launch_bounds__(C * (1 << (LA / 2))) k_col_inv(LimbBatch lb, DevTables tab) {
-    constexpr int H = LA / 2, E = 1 << H, M = 1 << LA, N2 = 1 << LB;
-    __shared__ uint64_t sm[(M + M / E) * C];
+template <int LA, int LB, int LT, int C>
+__global__ void __launch_bounds__(C * (1 << (LA - LT))) k_col_inv(LimbBatch lb, DevTables tab) {
+    constexpr int K = 1 << LT, M = 1 << LA, N2 = 1 << LB;
+    __shared__ uint64_t sm[sub_words<LA, LT>() * C];
     __shared__ ulonglong2 tws[M];
     const int tid = threadIdx.x, t = tid / C, j = tid % C;
     const int pi = lb.prime(blockIdx.x % lb.nl);
     uint64_t* a = limb_at(lb, blockIdx.x, M * N2) + blockIdx.y * C + j;
     const uint64_t q = tab.q[pi], q2 = 2 * q;
-    stage_col_twiddles<LA, C * E>(tws, tab.itw[pi]);
-    uint64_t v[E];
+    stage_col_twiddles<LA, C * (M >> LT)>(tws, tab.itw[pi]);
+    uint64_t v[K];
 #pragma unroll
-    for (int k = 0; k < E; k++) v[k] = a[(size_t)(E * t + k) * N2];
+    for (int k = 0; k < K; k++) v[k] = a[(size_t)last_idx<LA, LT>(t, k) * N2];
     tw_wait();
-    inv_consec<LA>(v, tws, ColBase{}, t, q, q2);
-#pragma unroll
-    for (int k = 0; k < E; k++) sm[pad<H>(E * t + k) * C + j] = v[k];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < E; k++) v[k] = sm[pad<H>(t + E * k) * C + j];
-    inv_stride<LA>(v, tws, ColBase{}, q, q2);
+    inv_pass<LA, LT>(v, SubMem{sm + j, C}, tws, ColBase{}, t, q, q2);
     const uint64_t ni = tab.ninv[pi], nis = tab.ninv_sh[pi];
 #pragma unroll
-    for (int k = 0; k < E; k++) a[(size_t)(t + E * k) * N2] = shoup(v[k], ni, nis, q);
+    for (int k = 0; k < K; k++) a[(size_t)first_idx<LA, LT>(t, k) * N2] = shoup(v[k], ni, nis, q);
 }
 
 }  // namespace nttr
