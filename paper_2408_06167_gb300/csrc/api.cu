@@ -269,6 +269,7 @@ void bm_context_destroy(bm_context* ctx) {
     ctx->c.plans.clear();
     if (ctx->c.d_twiddles) cudaFree(ctx->c.d_twiddles);
     if (ctx->c.d_ksc) cudaFree(ctx->c.d_ksc);
+    if (ctx->c.d_qlinv) cudaFree(ctx->c.d_qlinv);
     if (ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
     delete ctx;
 }

@@ -72,6 +72,7 @@ struct Context {
     double scale = 0;
     std::vector<KsLevelConst> h_ksc;          // key-switching constants per level (host copy)
     KsLevelConst* d_ksc = nullptr;            // ... and on the device
+    ulonglong2* d_qlinv = nullptr;            // [level][j]: q_level^-1 mod q_j (Shoup pairs), for rescale
     uint64_t next_id = 1;                     // ids of galleries and key sets (plan cache keys)
     std::vector<Plan*> plans;
 };
@@ -211,6 +212,9 @@ bool ks_fused_supported(const Context& c);
 cudaError_t ks_rotate_fused(const Context& c, const uint64_t* key, uint64_t galois, uint32_t level,
                             uint32_t B, uint64_t* const* d_in, uint64_t* const* d_out,
                             uint64_t* const* d_add, uint64_t* scratch, cudaStream_t s);
+// rescale in three fused kernels (rings 2^12 and 2^16)
+cudaError_t rescale_fused(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,
+                          uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s);
 // inverse column pass alone (the second half of an inverse NTT)
 cudaError_t ntt_col_inverse(const Context& c, const LimbBatch& b, cudaStream_t s);
 // fills c.h_ksc / c.d_ksc

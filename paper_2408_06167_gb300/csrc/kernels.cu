@@ -579,7 +579,14 @@ cudaError_t build_ks_constants(Context& c) {
     }
     cudaError_t e = cudaMalloc(&c.d_ksc, sizeof(KsLevelConst) * c.h_ksc.size());
     if (e != cudaSuccess) return e;
-    return cudaMemcpy(c.d_ksc, c.h_ksc.data(), sizeof(KsLevelConst) * c.h_ksc.size(), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(c.d_ksc, c.h_ksc.data(), sizeof(KsLevelConst) * c.h_ksc.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    std::vector<ulonglong2> qi((size_t)(c.L + 1) * MAXB, make_ulonglong2(0, 0));
+    for (uint32_t l = 1; l <= c.L; l++)
+        for (uint32_t j = 0; j < l; j++) qi[(size_t)l * MAXB + j] = pair(h_invmod(c.primes[l] % c.primes[j], c.primes[j]), c.primes[j]);
+    e = cudaMalloc(&c.d_qlinv, sizeof(ulonglong2) * qi.size());
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(c.d_qlinv, qi.data(), sizeof(ulonglong2) * qi.size(), cudaMemcpyHostToDevice);
 }
 cudaError_t ntt_inverse(const Context& c, const LimbBatch& b, cudaStream_t s) { return ntt_dispatch(c, b, true, s); }
 
@@ -773,6 +780,7 @@ size_t rescale_scratch_words(const Context& c, uint32_t level, uint32_t B) {
 cudaError_t rescale(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in, uint64_t* const* d_out,
                     uint64_t* scratch, cudaStream_t s) {
     if (B == 0) return cudaSuccess;
+    if (ks_fused_supported(c)) return rescale_fused(c, level, B, d_in, d_out, scratch, s);
     const uint32_t n = c.n;
     uint64_t* Y = scratch;                         // [B*2][N]
     uint64_t* Rl = Y + (size_t)B * 2 * n;          // [B*2][level][N]

@@ -341,6 +341,131 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)))
     }
 }
 
+// ---------------------------------------------------------------------------
+// Rescale (Res of Sec. 2) in three kernels: out_j = (c_j - [c_l]_centred) * q_l^-1.
+// R1: grid (B * 2, N1 / R): inverse row pass of limb l of each polynomial -> Y
+// ---------------------------------------------------------------------------
+template <int LA, int LB, int LT, int R>
+__global__ void __launch_bounds__(R * (1 << (LB - LT)))
+    k_rs_r1(uint64_t* const* in, uint64_t* __restrict__ Y, DevTables tab, uint32_t lvl) {
+    constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>(), N = 1 << (LA + LB);
+    __shared__ uint64_t sm[R * S];
+    __shared__ ulonglong2 tws[row_tw_entries<LB, R>()];
+    const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
+    const uint32_t b = blockIdx.x / 2, comp = blockIdx.x % 2;
+    const int row = blockIdx.y * R + jr;
+    const size_t roff = (size_t)row * M;
+    const uint64_t q = tab.q[lvl], q2 = 2 * q;
+    const uint64_t* src = in[b] + ((size_t)comp * (lvl + 1) + lvl) * N + roff;
+    const SubMem sr{sm + jr * S, 1};
+    stage_row_twiddles<LA, LB, R, R * TH>(tws, tab.itw[lvl], blockIdx.y * R);
+    uint64_t v[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = src[first_idx<LB, LT>(t, k)];
+    nttr::relayout<LB, LT, 0, LB / LT - 1>(v, sr, t);
+    tw_wait();
+    nttr::inv_pass<LB, LT>(v, sr, tws, RowBase<R>{jr}, t, q, q2);
+    uint64_t* o = Y + (size_t)blockIdx.x * N + roff;
+#pragma unroll
+    for (int k = 0; k < K; k++) o[first_idx<LB, LT>(t, k)] = v[k];
+}
+
+// R2: grid (B * 2, N2 / C): inverse column pass -> centred lift -> forward column
+// pass on every q_j, j < l -> Rl[b*2+comp][j]
+template <int LA, int LB, int LT, int C>
+__global__ void __launch_bounds__(C * (1 << (LA - LT)))
+    k_rs_r2(const uint64_t* __restrict__ Y, uint64_t* __restrict__ Rl, DevTables tab, uint32_t lvl) {
+    constexpr int K = 1 << LT, M = 1 << LA, N2 = 1 << LB, N = 1 << (LA + LB);
+    __shared__ uint64_t sm[sub_words<LA, LT>() * C];
+    __shared__ ulonglong2 tws[M];
+    const int tid = threadIdx.x, t = tid / C, jc = tid % C;
+    const int col = blockIdx.y * C + jc;
+    const uint64_t ql = tab.q[lvl];
+    const uint64_t* src = Y + (size_t)blockIdx.x * N + col;
+    stage_col_twiddles<LA, C * (M >> LT)>(tws, tab.itw[lvl]);
+    uint64_t c[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) c[k] = src[(size_t)last_idx<LA, LT>(t, k) * N2];
+    tw_wait();
+    nttr::inv_pass<LA, LT>(c, SubMem{sm + jc, C}, tws, ColBase{}, t, ql, 2 * ql);
+    const uint64_t ni = tab.ninv[lvl], nis = tab.ninv_sh[lvl];
+#pragma unroll
+    for (int k = 0; k < K; k++) c[k] = shoup(c[k], ni, nis, ql);      // coefficients of limb l, [0, q_l)
+    __syncthreads();
+#pragma unroll 1
+    for (uint32_t j = 0; j < lvl; j++) {
+        const uint64_t qj = tab.q[j];
+        stage_col_twiddles<LA, C * (M >> LT)>(tws, tab.tw[j]);
+        uint64_t y[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const bool neg = c[k] > (ql >> 1);
+            const uint64_t mag = neg ? ql - c[k] : c[k];
+            const uint64_t r = reduce2(shoup_lazy(mag, 1, tab.rsh[j], qj), qj);
+            y[k] = neg ? negm(r, qj) : r;
+        }
+        tw_wait();
+        col_fwd_store<LA, LB, LT, C>(y, sm, tws, t, jc, qj, Rl + ((size_t)blockIdx.x * lvl + j) * N + col);
+        __syncthreads();
+    }
+}
+
+// R3: grid (B * 2 * l, N1 / R): forward row pass of Rl, out_j = (in_j - r_j) * q_l^-1
+template <int LA, int LB, int LT, int R>
+__global__ void __launch_bounds__(R * (1 << (LB - LT)))
+    k_rs_r3(uint64_t* const* in, const uint64_t* __restrict__ Rl, uint64_t* const* out, DevTables tab, uint32_t lvl,
+            const ulonglong2* __restrict__ qlinv) {
+    constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>(), N = 1 << (LA + LB);
+    __shared__ uint64_t sm[R * S];
+    __shared__ ulonglong2 tws[row_tw_entries<LB, R>()];
+    const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
+    const uint32_t y = blockIdx.x, b = y / (2 * lvl), comp = (y / lvl) % 2, j = y % lvl;
+    const int row = blockIdx.y * R + jr;
+    const size_t roff = (size_t)row * M;
+    const uint64_t q = tab.q[j], q2 = 2 * q;
+    const SubMem sr{sm + jr * S, 1};
+    stage_row_twiddles<LA, LB, R, R * TH>(tws, tab.tw[j], blockIdx.y * R);
+    const uint64_t* r = Rl + ((size_t)(b * 2 + comp) * lvl + j) * N + roff;
+    uint64_t v[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = r[first_idx<LB, LT>(t, k)];
+    tw_wait();
+    nttr::fwd_pass<LB, LT>(v, sr, tws, RowBase<R>{jr}, t, q, q2);
+    const uint64_t* x = in[b] + ((size_t)comp * (lvl + 1) + j) * N + roff;
+    const ulonglong2 w = qlinv[j];
+#pragma unroll
+    for (int k = 0; k < K; k++)
+        v[k] = shoup(subm(x[last_idx<LB, LT>(t, k)], nttr::reduce4(v[k], q, q2), q), w.x, w.y, q);
+    nttr::relayout<LB, LT, LB / LT - 1, 0>(v, sr, t);
+    uint64_t* o = out[b] + ((size_t)comp * lvl + j) * N + roff;
+#pragma unroll
+    for (int k = 0; k < K; k++) o[first_idx<LB, LT>(t, k)] = v[k];
+}
+
+template <int LA, int LB, int LT, int C, int R>
+cudaError_t rescale_fused_launch(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,
+                                 uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s) {
+    constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
+    uint64_t* Y = scratch;                          // [B*2][N]
+    uint64_t* Rl = Y + (size_t)B * 2 * N;           // [B*2][level][N]
+    const int tr = R * (1 << (LB - LT)), tc = C * (1 << (LA - LT));
+    const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;
+    {
+        ProfScope ps(BM_KERNEL_RESCALE, s, lw * B * 2 * 2, bf_r * B * 2);
+        k_rs_r1<LA, LB, LT, R><<<dim3(B * 2, N1 / R), tr, 0, s>>>(d_in, Y, c.tab, level);
+    }
+    {
+        ProfScope ps(BM_KERNEL_RESCALE, s, lw * B * 2 * (1 + level), bf_c * B * 2 * (1 + level));
+        k_rs_r2<LA, LB, LT, C><<<dim3(B * 2, N2 / C), tc, 0, s>>>(Y, Rl, c.tab, level);
+    }
+    {
+        ProfScope ps(BM_KERNEL_RESCALE, s, lw * B * 2 * level * 3, bf_r * B * 2 * level);
+        k_rs_r3<LA, LB, LT, R><<<dim3(B * 2 * level, N1 / R), tr, 0, s>>>(d_in, Rl, d_out, c.tab, level,
+                                                                          c.d_qlinv + (size_t)level * MAXB);
+    }
+    return cudaGetLastError();
+}
+
 template <int LA, int LB, int LT, int C, int R>
 cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galois, uint32_t level, uint32_t B,
                             uint64_t* const* d_in, uint64_t* const* d_out, uint64_t* const* d_add, uint64_t* scratch,
@@ -402,6 +527,14 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
 }
 
 }  // namespace
+
+cudaError_t rescale_fused(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,
+                          uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    if (c.log_n == 16) return rescale_fused_launch<8, 8, 2, 2, 2>(c, level, B, d_in, d_out, scratch, s);
+    if (c.log_n == 12) return rescale_fused_launch<6, 6, 2, 8, 8>(c, level, B, d_in, d_out, scratch, s);
+    return cudaErrorInvalidValue;
+}
 
 bool ks_fused_supported(const Context& c) {
     if (c.log_n != 12 && c.log_n != 16) return false;
