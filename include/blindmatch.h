@@ -205,6 +205,49 @@ bm_status bm_decrypt_scores(bm_context* ctx, const bm_secret_key* sk, const bm_r
                             uint32_t query_index, double* scores, uint64_t n_ids,
                             int64_t* rank1, double* rank1_score);
 
+/* ---- serving: continuous batching over resident galleries ---- */
+
+typedef struct bm_server bm_server;
+typedef struct bm_server_stats_t {
+    uint64_t submitted, completed, failed, cancelled;
+    uint64_t batches;         /* batched matches executed */
+    double mean_batch;        /* queries per executed batch */
+    double p50_ms, p99_ms;    /* submit-to-completion latency of the completed requests */
+    double matches_per_s;     /* identities scored per second, first submit to last completion */
+    uint64_t workspace_bytes; /* device memory held by the executors' match plans */
+} bm_server_stats_t;
+
+/* A match server on ctx (Sec. 3.3 recognition, many clients at once).  Requests
+ * wait in arrival order; `executors` threads (1..16), each with its own CUDA
+ * stream and match plans, repeatedly take the oldest request together with the
+ * other pending requests for the same gallery (at most max_batch) and run them as
+ * one batched bm_match, so requests that arrive while others run join the next
+ * batch and batches of different executors overlap on the GPU.  Match workspaces
+ * are admitted against hbm_budget_bytes of device memory: an executor evicts its
+ * own idle plans first, then halves its batch; a single query that does not fit
+ * fails with BM_E_HBM_BUDGET.  Galleries and key sets are borrowed and must
+ * outlive the server. */
+bm_status bm_server_create(bm_context* ctx, uint64_t hbm_budget_bytes, uint32_t max_batch, uint32_t executors,
+                           bm_server** out);
+/* Stops the executors after their current batch; pending requests are cancelled
+ * and uncollected results freed. */
+void bm_server_destroy(bm_server* srv);
+/* Registers a resident gallery with the rotation keys generated for its
+ * (dim, part) (BM_E_KEY_MISSING otherwise); *gid identifies it in submissions. */
+bm_status bm_server_add_gallery(bm_server* srv, const bm_gallery* gallery, const bm_eval_keys* evk,
+                                uint32_t* gid);
+/* Queues one query (copied) against gallery gid; BM_E_LEVEL if its layout does
+ * not match the gallery's schedule.  *ticket identifies the request. */
+bm_status bm_server_submit(bm_server* srv, uint32_t gid, const bm_ciphertext* query, uint64_t* ticket);
+/* Waits up to timeout_ms for the request; BM_E_TIMEOUT leaves it in flight (wait
+ * again later).  On completion the ticket is consumed: *out receives the
+ * request's result (one query; free it with bm_result_destroy), or the request's
+ * own error is returned (BM_E_HBM_BUDGET, BM_E_CANCELLED, ...). */
+bm_status bm_server_wait(bm_server* srv, uint64_t ticket, uint32_t timeout_ms, bm_result** out);
+/* Cancels a request that has not started; BM_E_ARG if it is running or done. */
+bm_status bm_server_cancel(bm_server* srv, uint64_t ticket);
+bm_status bm_server_stats(bm_server* srv, bm_server_stats_t* out);
+
 /* ---- single operations, for checking the kernels against a reference ---- */
 
 /* Negacyclic products out = a * b in Z_q[X]/(X^N+1), limb k on prime k of the full

@@ -31,6 +31,12 @@ STATUS = ["BM_OK", "BM_E_ARG", "BM_E_PARAM", "BM_E_LEVEL", "BM_E_KEY_MISSING", "
           "BM_E_HBM_BUDGET", "BM_E_CUDA", "BM_E_TIMEOUT", "BM_E_CANCELLED", "BM_E_FORMAT"]
 
 
+class bm_server_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", _u64), ("completed", _u64), ("failed", _u64), ("cancelled", _u64),
+                ("batches", _u64), ("mean_batch", _dbl), ("p50_ms", _dbl), ("p99_ms", _dbl),
+                ("matches_per_s", _dbl), ("workspace_bytes", _u64)]
+
+
 class bm_params(ctypes.Structure):
     _fields_ = [("log_n", _u32), ("n_q", _u32), ("q_bits", _u32 * 6), ("n_p", _u32), ("p_bits", _u32 * 3),
                 ("dnum", _u32), ("log_scale", _u32), ("secret_hw", _u32), ("sigma", _dbl)]
@@ -72,6 +78,13 @@ _SIGS = {
     "bm_ntt_forward": (ctypes.c_int, [_vp, _vp, _u32, _u32, _vp]),
     "bm_ntt_inverse": (ctypes.c_int, [_vp, _vp, _u32, _u32, _vp]),
     "bm_ct_rotate_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _u32, _u32, _i32, _vp, _vp]),
+    "bm_server_create": (ctypes.c_int, [_vp, _u64, _u32, _u32, _PP]),
+    "bm_server_destroy": (None, [_vp]),
+    "bm_server_add_gallery": (ctypes.c_int, [_vp, _vp, _vp, _U32P]),
+    "bm_server_submit": (ctypes.c_int, [_vp, _u32, _vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "bm_server_wait": (ctypes.c_int, [_vp, _u64, _u32, _PP]),
+    "bm_server_cancel": (ctypes.c_int, [_vp, _u64]),
+    "bm_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(bm_server_stats_t)]),
     "bm_profile_control": (ctypes.c_int, [_u32, _u32]),
     "bm_profile_read": (ctypes.c_int, [_u32, _U64P, _DP, _DP, _DP]),
 }
@@ -138,6 +151,10 @@ class Ciphertext(_Handle):
 
 class Result(_Handle):
     _destroy = "bm_result_destroy"
+
+
+class Server(_Handle):
+    _destroy = "bm_server_destroy"
 
 
 def _out():
@@ -348,3 +365,38 @@ def bm_profile_read(kind):
     n, ms, by, ops = _u64(), _dbl(), _dbl(), _dbl()
     _check(_L.bm_profile_read(k, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by), ctypes.byref(ops)))
     return n.value, ms.value, by.value, ops.value
+
+
+def bm_server_create(ctx, hbm_budget_bytes, max_batch=64, executors=2):
+    h = _out()
+    _check(_L.bm_server_create(ctx.ptr, hbm_budget_bytes, max_batch, executors, ctypes.byref(h)))
+    return Server(h.value, ctx)
+
+
+def bm_server_add_gallery(srv, gallery, evk):
+    gid = _u32()
+    _check(_L.bm_server_add_gallery(srv.ptr, gallery.ptr, evk.ptr, ctypes.byref(gid)))
+    srv.keep = getattr(srv, "keep", []) + [gallery, evk]      # borrowed by the server: keep alive
+    return gid.value
+
+
+def bm_server_submit(srv, gid, query):
+    t = ctypes.c_uint64()
+    _check(_L.bm_server_submit(srv.ptr, gid, query.ptr, ctypes.byref(t)))
+    return t.value
+
+
+def bm_server_wait(srv, ticket, timeout_ms=60000):
+    h = _out()
+    _check(_L.bm_server_wait(srv.ptr, ticket, timeout_ms, ctypes.byref(h)))
+    return Result(h.value, srv.owner)
+
+
+def bm_server_cancel(srv, ticket):
+    _check(_L.bm_server_cancel(srv.ptr, ticket))
+
+
+def bm_server_stats(srv):
+    st = bm_server_stats_t()
+    _check(_L.bm_server_stats(srv.ptr, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in bm_server_stats_t._fields_}

@@ -766,6 +766,7 @@ struct Plan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     ProfSink counts;                       // launches per replay
+    size_t bytes = 0;                      // device memory held
     ~Plan() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
@@ -774,6 +775,7 @@ struct Plan {
     bool alloc(uint64_t*& p, size_t words) {
         if (cudaMalloc((void**)&p, std::max<size_t>(words, 1) * 8) != cudaSuccess) return false;
         bufs.push_back(p);
+        bytes += std::max<size_t>(words, 1) * 8;
         return true;
     }
 };
@@ -923,7 +925,7 @@ struct MatchRun {
     }
 };
 
-static bm_status build_plan(Context& c, const Gallery& g, const EvalKeys& ek, uint32_t Q, Plan*& out) {
+bm_status plan_build(Context& c, const Gallery& g, const EvalKeys& ek, uint32_t Q, cudaStream_t cs, Plan*& out) {
     auto* pl = new Plan();
     std::unique_ptr<Plan> guard(pl);
     Layout lo;
@@ -960,7 +962,6 @@ static bm_status build_plan(Context& c, const Gallery& g, const EvalKeys& ek, ui
     BM_CUDA_TRY(cudaMemcpy(arr, pl->arena.host.data(), pl->arena.host.size() * sizeof(void*), cudaMemcpyHostToDevice));
     pl->arena.live = true;
     // capture the launch pass once
-    cudaStream_t cs = c.stream;
     BM_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     prof_set_sink(&pl->counts);
     run.s = cs;
@@ -971,6 +972,35 @@ static bm_status build_plan(Context& c, const Gallery& g, const EvalKeys& ek, ui
     BM_CUDA_TRY(e);
     BM_CUDA_TRY(cudaGraphInstantiate(&pl->exec, pl->graph, 0));
     out = guard.release();
+    return BM_OK;
+}
+
+size_t plan_bytes(const Plan* p) { return p->bytes; }
+uint32_t plan_queries(const Plan* p) { return p->Q; }
+uint32_t plan_outputs(const Plan* p) { return p->n_out; }
+const uint64_t* plan_result(const Plan* p) { return p->result; }
+
+bm_status plan_run(Context& c, const Gallery& g, const EvalKeys& ek, Plan* pl, const Ciphertext* const* queries,
+                   uint32_t nq, cudaStream_t s) {
+    if (nq == 0 || nq > pl->Q) return fail(BM_E_ARG, "batch larger than the plan");
+    // a0: the queries' coefficient-form limbs into the plan's input buffer (padded with the last)
+    const size_t per_q = (size_t)pl->ncts * ct_words(c, c.L);
+    for (uint32_t i = 0; i < pl->Q; i++) {
+        const Ciphertext& ct = *queries[std::min(i, nq - 1)];
+        uint64_t* dst = pl->qin + (size_t)i * per_q;
+        if (ct.d_coef) BM_CUDA_TRY(cudaMemcpyAsync(dst, ct.d_coef, per_q * 8, cudaMemcpyDeviceToDevice, s));
+        else BM_CUDA_TRY(cudaMemcpyAsync(dst, ct.host.data(), per_q * 8, cudaMemcpyHostToDevice, s));
+    }
+    if (prof_timing()) {
+        // per-launch timing: run the same launches eagerly so each gets its event pair
+        MatchRun run(c, g, ek, *pl);
+        run.s = s;
+        run.schedule();
+        if (run.err != cudaSuccess) return fail(BM_E_CUDA, std::string("match: ") + cudaGetErrorString(run.err));
+    } else {
+        BM_CUDA_TRY(cudaGraphLaunch(pl->exec, s));
+        prof_add(pl->counts);
+    }
     return BM_OK;
 }
 
@@ -1005,27 +1035,12 @@ bm_status bm_match(bm_context* ctxh, const bm_eval_keys* evk, const bm_gallery* 
     cudaStream_t s = (cudaStream_t)stream;
     Plan* pl = find_plan(c, g.id, evk->k.id, n_queries);
     if (!pl) {
-        BM_TRY(build_plan(c, g, evk->k, n_queries, pl));
+        BM_TRY(plan_build(c, g, evk->k, n_queries, c.stream, pl));
         c.plans.push_back(pl);
     }
-    // a0: the queries' coefficient-form limbs into the plan's input buffer
-    const size_t per_q = (size_t)ncts * ct_words(c, c.L);
-    for (uint32_t i = 0; i < n_queries; i++) {
-        const Ciphertext& ct = queries[i]->ct;
-        uint64_t* dst = pl->qin + (size_t)i * per_q;
-        if (ct.d_coef) BM_CUDA_TRY(cudaMemcpyAsync(dst, ct.d_coef, per_q * 8, cudaMemcpyDeviceToDevice, s));
-        else BM_CUDA_TRY(cudaMemcpyAsync(dst, ct.host.data(), per_q * 8, cudaMemcpyHostToDevice, s));
-    }
-    if (prof_timing()) {
-        // per-launch timing: run the same launches eagerly so each gets its event pair
-        MatchRun run(c, g, evk->k, *pl);
-        run.s = s;
-        run.schedule();
-        if (run.err != cudaSuccess) return fail(BM_E_CUDA, std::string("match: ") + cudaGetErrorString(run.err));
-    } else {
-        BM_CUDA_TRY(cudaGraphLaunch(pl->exec, s));
-        prof_add(pl->counts);
-    }
+    std::vector<const Ciphertext*> qs(n_queries);
+    for (uint32_t i = 0; i < n_queries; i++) qs[i] = &queries[i]->ct;
+    BM_TRY(plan_run(c, g, evk->k, pl, qs.data(), n_queries, s));
     auto* rh = new bm_result();
     Result& res = rh->r;
     res.ctx = &c;

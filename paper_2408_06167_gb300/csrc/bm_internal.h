@@ -55,7 +55,9 @@ struct KsLevelConst {
     ulonglong2 pinv[MAXB];                     // P^-1 mod q_j
 };
 
-struct Plan;                                   // cached match schedule (api.cu)
+// A match schedule for one (gallery, key set, batch size): persistent device
+// buffers and the whole schedule captured as a CUDA graph (api.cu).
+struct Plan;
 void destroy_plan(Plan* p);
 
 struct Context {
@@ -78,6 +80,19 @@ struct Context {
 };
 // destroys every cached plan that uses the gallery or key set `id`
 void drop_plans(Context& c, uint64_t id);
+struct Gallery;
+struct EvalKeys;
+struct Ciphertext;
+bm_status plan_build(Context& c, const Gallery& g, const EvalKeys& ek, uint32_t Q, cudaStream_t capture,
+                     Plan*& out);
+// enqueues the match of nq <= Q queries on s (graph replay; eager when profiling
+// with timing); the score ciphertexts land in plan_result(), [Q][n_out][2][N]
+bm_status plan_run(Context& c, const Gallery& g, const EvalKeys& ek, Plan* p, const Ciphertext* const* queries,
+                   uint32_t nq, cudaStream_t s);
+size_t plan_bytes(const Plan* p);
+uint32_t plan_queries(const Plan* p);
+uint32_t plan_outputs(const Plan* p);
+const uint64_t* plan_result(const Plan* p);
 
 struct SecretKey {
     Context* ctx;
