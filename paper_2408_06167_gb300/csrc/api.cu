@@ -254,6 +254,7 @@ bm_status bm_params_preset(int preset, bm_params* out) {
 bm_status bm_context_create(const bm_params* params, int device, bm_context** out) {
     if (!params || !out) return fail(BM_E_ARG, "null argument");
     auto* h = new bm_context();
+    h->c.owner = h;
     bm_status s = context_init(h->c, *params, device);
     if (s != BM_OK) {
         bm_context_destroy(h);
@@ -265,6 +266,18 @@ bm_status bm_context_create(const bm_params* params, int device, bm_context** ou
 
 void bm_context_destroy(bm_context* ctx) {
     if (!ctx) return;
+    ctx->c.destroy_requested = true;
+    if (ctx->c.refs.load() == 0) bm::context_free(ctx);
+}
+
+}  // extern "C"
+
+namespace bm {
+void ctx_retain(Context* c) { c->refs++; }
+void ctx_release(Context* c) {
+    if (--c->refs == 0 && c->destroy_requested.load()) context_free(c->owner);
+}
+void context_free(bm_context* ctx) {
     for (Plan* p : ctx->c.plans) destroy_plan(p);
     ctx->c.plans.clear();
     if (ctx->c.d_twiddles) cudaFree(ctx->c.d_twiddles);
@@ -273,6 +286,9 @@ void bm_context_destroy(bm_context* ctx) {
     if (ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
     delete ctx;
 }
+}  // namespace bm
+
+extern "C" {
 
 bm_status bm_context_primes(const bm_context* ctx, uint64_t* primes_out, size_t capacity) {
     if (!ctx || !primes_out) return fail(BM_E_ARG, "null argument");
@@ -296,6 +312,7 @@ bm_status bm_keygen(bm_context* ctxh, uint64_t seed, uint32_t dim, uint32_t part
     const size_t n = c.n, nb = c.nb, L1 = c.L + 1;
 
     auto* skh = new bm_secret_key();
+    skh->ref.attach(&c);
     skh->k.ctx = &c;
     skh->k.coeffs.resize(n);
     sample_secret(seed, c.params.secret_hw, c.log_n, skh->k.coeffs.data());
@@ -312,6 +329,7 @@ bm_status bm_keygen(bm_context* ctxh, uint64_t seed, uint32_t dim, uint32_t part
 
     // public key (b, a) over Q_L: b = e - a*s
     auto* pkh = new bm_public_key();
+    pkh->ref.attach(&c);
     pkh->k.ctx = &c;
     DevBuf pkb, tmp;
     pkb.alloc(2 * L1 * n);
@@ -333,6 +351,7 @@ bm_status bm_keygen(bm_context* ctxh, uint64_t seed, uint32_t dim, uint32_t part
 
     // rotation keys: per digit d, b_d = e_d - a_d*s + P*[limb in digit d]*sigma_k(s) over Q_L u P
     auto* evh = new bm_eval_keys();
+    evh->ref.attach(&c);
     evh->k.ctx = &c;
     evh->k.id = c.next_id++;
     evh->k.dim = dim;
@@ -486,6 +505,7 @@ namespace bm {
 static bm_status gallery_alloc(Context& c, const Layout& lo, uint64_t n_ids, uint32_t dim, uint32_t part,
                                bm_gallery** out, bm_gallery*& gh) {
     gh = new bm_gallery();
+    gh->ref.attach(&c);
     Gallery& g = gh->g;
     g.ctx = &c;
     g.id = c.next_id++;
@@ -639,6 +659,7 @@ bm_status bm_encrypt_query(bm_context* ctxh, const bm_public_key* pk, const doub
     const size_t n = c.n, S = c.slots, L1 = c.L + 1;
     const uint32_t n_cts = mode == BM_QUERY_TILED ? 1 : lo.n_in;
     auto* ch = new bm_ciphertext();
+    ch->ref.attach(&c);
     Ciphertext& ct = ch->ct;
     ct.ctx = &c;
     ct.n_cts = n_cts;
@@ -689,6 +710,7 @@ bm_status bm_ciphertext_import(bm_context* ctxh, const uint64_t* data, uint32_t 
     Context& c = ctxh->c;
     if (level > c.L) return fail(BM_E_FORMAT, "level above the chain");
     auto* ch = new bm_ciphertext();
+    ch->ref.attach(&c);
     ch->ct.ctx = &c;
     ch->ct.n_cts = n_cts;
     ch->ct.level = level;
@@ -1042,6 +1064,7 @@ bm_status bm_match(bm_context* ctxh, const bm_eval_keys* evk, const bm_gallery* 
     for (uint32_t i = 0; i < n_queries; i++) qs[i] = &queries[i]->ct;
     BM_TRY(plan_run(c, g, evk->k, pl, qs.data(), n_queries, s));
     auto* rh = new bm_result();
+    rh->ref.attach(&c);
     Result& res = rh->r;
     res.ctx = &c;
     res.n_queries = n_queries;
@@ -1197,6 +1220,7 @@ static bm_status ct_op(bm_context* ctxh, const bm_ciphertext* in, int op, const 
     else BM_CUDA_TRY(rescale(c, l, B, lin, lout, scr.p, s));
     BM_CUDA_TRY(ntt_inverse(c, packed(c, dout.p, B * 2, lo + 1), s));
     auto* ch = new bm_ciphertext();
+    ch->ref.attach(&c);
     ch->ct.ctx = &c;
     ch->ct.n_cts = B;
     ch->ct.level = lo;

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -77,6 +78,30 @@ struct Context {
     ulonglong2* d_qlinv = nullptr;            // [level][j]: q_level^-1 mod q_j (Shoup pairs), for rescale
     uint64_t next_id = 1;                     // ids of galleries and key sets (plan cache keys)
     std::vector<Plan*> plans;
+    // lifetime: every handle made from the context holds a reference; the context
+    // is freed when it was destroyed and its last handle is gone
+    std::atomic<int> refs{0};
+    std::atomic<bool> destroy_requested{false};
+    struct bm_context* owner = nullptr;
+};
+void ctx_retain(Context* c);
+void context_free(struct bm_context* ctx);
+void ctx_release(Context* c);   // frees a destroyed context with its last handle
+
+// Reference to the context a handle was made from; declared first in each
+// handle so that it is released after the handle's own resources.
+struct CtxRef {
+    Context* c = nullptr;
+    CtxRef() = default;
+    CtxRef(const CtxRef&) = delete;
+    CtxRef& operator=(const CtxRef&) = delete;
+    void attach(Context* x) {
+        c = x;
+        ctx_retain(c);
+    }
+    ~CtxRef() {
+        if (c) ctx_release(c);
+    }
 };
 // destroys every cached plan that uses the gallery or key set `id`
 void drop_plans(Context& c, uint64_t id);
@@ -261,9 +286,9 @@ cudaError_t scalar_mul(const Context& c, const LimbBatch& in, const uint64_t* cs
 
 // opaque handle types of the C-ABI
 struct bm_context { bm::Context c; };
-struct bm_secret_key { bm::SecretKey k; };
-struct bm_public_key { bm::PublicKey k; };
-struct bm_eval_keys { bm::EvalKeys k; };
-struct bm_gallery { bm::Gallery g; };
-struct bm_ciphertext { bm::Ciphertext ct; };
-struct bm_result { bm::Result r; };
+struct bm_secret_key { bm::CtxRef ref; bm::SecretKey k; };
+struct bm_public_key { bm::CtxRef ref; bm::PublicKey k; };
+struct bm_eval_keys { bm::CtxRef ref; bm::EvalKeys k; };
+struct bm_gallery { bm::CtxRef ref; bm::Gallery g; };
+struct bm_ciphertext { bm::CtxRef ref; bm::Ciphertext ct; };
+struct bm_result { bm::CtxRef ref; bm::Result r; };

@@ -180,6 +180,7 @@ void run_batch(Executor& E, std::vector<Request*>& batch) {
         const size_t words = (size_t)n_out * ct_words(c, 0);
         for (size_t i = 0; i < batch.size() && st == BM_OK; i++) {
             auto* rh = new bm_result();
+            rh->ref.attach(&c);
             Result& r = rh->r;
             r.ctx = &c;
             r.n_queries = 1;
@@ -248,7 +249,7 @@ void executor_loop(Executor* E) {
 }  // namespace
 }  // namespace bm
 
-struct bm_server { bm::Server s; };
+struct bm_server { bm::CtxRef ref; bm::Server s; };
 
 using namespace bm;
 
@@ -261,6 +262,7 @@ bm_status bm_server_create(bm_context* ctx, uint64_t hbm_budget_bytes, uint32_t 
         return BM_E_ARG;
     }
     auto* h = new bm_server();
+    h->ref.attach(&ctx->c);
     Server& S = h->s;
     S.c = &ctx->c;
     S.budget = hbm_budget_bytes;
