@@ -40,6 +40,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="face-128d-6144")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving mix: Poisson arrivals against four resident galleries through bm_server_*")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
+    ap.add_argument("--executors", type=int, default=2)
+    ap.add_argument("--max-batch", type=int, default=256)
     return ap.parse_args()
 
 
@@ -198,10 +204,95 @@ def percentile(xs, p):
     return xs[k]
 
 
+SERVE_GALLERIES = [("finger-1k", 1024, 16, 4), ("face-6k", 6144, 128, 16), ("finger-64k", 65536, 16, 4),
+                   ("face-1m", 1 << 20, 128, 16)]
+ARRIVAL_SEED = 5
+
+
+def run_serving(args):
+    """Poisson arrivals (seed 5) at --rate for --duration seconds, each query against a
+    uniformly chosen resident gallery; requests are served by the continuous-batching
+    server.  Reports p50/p99 submit-to-completion latency and matches/s, beside the same
+    mix served one query per bm_match call (the plain unbatched form)."""
+    import numpy as np
+    import torch
+    from paper_2408_06167_gb300 import binding as bm
+    from paper_2408_06167_gb300 import workload as wl
+    ctx = bm.bm_context_create("ring16", 0)
+    keys, gals = {}, []
+    for gi, (name, R, m, s) in enumerate(SERVE_GALLERIES):
+        if (m, s) not in keys:
+            keys[(m, s)] = bm.bm_keygen(ctx, KEY_SEED, m, s)
+        feats = wl.gallery(R, m, seed=10 + gi)
+        qs, _ = wl.queries(feats, 64, seed=20 + gi)
+        sk, pk, ek = keys[(m, s)]
+        cts = [bm.bm_encrypt_query(ctx, pk, q, m, s, bm.BM_QUERY_TILED, ENC_SEED, i) for i, q in enumerate(qs)]
+        gals.append(dict(name=name, R=R, g=bm.bm_encode_gallery(ctx, feats, m, s), ek=ek, cts=cts))
+    # plain unbatched form: one query per bm_match, per gallery
+    stream = torch.cuda.current_stream()
+    single_ms = []
+    for G in gals:
+        bm.bm_match(ctx, G["ek"], G["g"], [G["cts"][0]], stream.cuda_stream)
+        t = []
+        for i in range(3):
+            t0 = time.perf_counter()
+            bm.bm_match(ctx, G["ek"], G["g"], [G["cts"][i]], stream.cuda_stream)
+            t.append(time.perf_counter() - t0)
+        single_ms.append(1e3 * min(t))
+    mean_single_s = sum(single_ms) / len(single_ms) / 1e3        # uniform gallery choice
+    unbatched_rate = 1.0 / mean_single_s
+    unbatched_mps = sum(G["R"] for G in gals) / len(gals) * unbatched_rate
+    srv = bm.bm_server_create(ctx, 160 << 30, max_batch=args.max_batch, executors=args.executors)
+    gids = [bm.bm_server_add_gallery(srv, G["g"], G["ek"]) for G in gals]
+    rng = np.random.default_rng(ARRIVAL_SEED)
+    n = int(args.rate * args.duration)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=n))
+    choice = rng.integers(0, len(gals), size=n)
+    errors = []
+    pending = []
+    start = time.perf_counter()
+    sampler = ClockSampler(0)
+    sampler.start()
+    for k in range(n):
+        delay = start + arrivals[k] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        G = gals[choice[k]]
+        pending.append((choice[k], bm.bm_server_submit(srv, gids[choice[k]], G["cts"][k % len(G["cts"])])))
+    for gi, t in pending:
+        try:
+            bm.bm_server_wait(srv, t, 3600 * 1000)
+        except bm.BlindMatchError as e:
+            errors.append(str(e))
+    wall = time.perf_counter() - start
+    clocks = sampler.stop()
+    st = bm.bm_server_stats(srv)
+    matches = sum(gals[c]["R"] for c in choice)
+    line = {
+        "metric": METRIC, "value": st["matches_per_s"], "unit": UNIT, "n_gpus": 1, "steps": n, "warmup": 0,
+        "ms_per_step": 1e3 * wall / n, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "serving-mix", "ring": "2^16", "arrivals_per_s": args.rate,
+                   "duration_s": args.duration, "galleries": [g[0] for g in SERVE_GALLERIES],
+                   "executors": args.executors, "max_batch": args.max_batch},
+        "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]},
+        "server": {k: st[k] for k in ("submitted", "completed", "failed", "batches", "mean_batch",
+                                      "workspace_bytes")},
+        "errors": errors[:3],
+        "wall_s": wall, "matches": matches,
+        "unbatched": {"single_query_ms": dict(zip([g[0] for g in SERVE_GALLERIES], single_ms)),
+                      "sustainable_queries_per_s": unbatched_rate, "matches_per_s": unbatched_mps},
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serving(args)
     rank, world, local = dist_env()
     import torch
     torch.cuda.set_device(local)

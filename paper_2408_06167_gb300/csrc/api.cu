@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -141,6 +142,7 @@ static bm_status context_init(Context& c, const bm_params& p, int device) {
     c.alpha = p.n_p;
     c.nb = p.n_q + p.n_p;
     c.scale = std::ldexp(1.0, (int)p.log_scale);
+    encoder_tables(c);
     if (!gen_primes(c.log_n, bits, c.primes)) return fail(BM_E_PARAM, "prime search failed");
     c.digits.clear();
     for (uint32_t d = 0; d < p.dnum; d++) {
@@ -198,6 +200,7 @@ static bm_status context_init(Context& c, const bm_params& p, int device) {
         c.tab.itw[j] = (const ulonglong2*)c.d_twiddles + j * per + c.n;
     }
     BM_CUDA_TRY(build_ks_constants(c));
+    if (const char* w = std::getenv("BM_KS_WIDE_BATCH")) c.ks_wide_batch = (uint32_t)std::strtoul(w, nullptr, 10);
     return BM_OK;
 }
 
@@ -568,20 +571,45 @@ bm_status bm_encode_gallery(bm_context* ctxh, const double* feats, uint64_t n_id
     BM_TRY(gallery_alloc(c, lo, n_ids, dim, part_size, out, gh));
     Gallery& g = gh->g;
     const size_t n = c.n, S = c.slots;
-    std::vector<double> z(S);
-    for (uint32_t grp = 0; grp < lo.groups; grp++) {
-        for (uint32_t i = 0; i < lo.n_in; i++) {
-            std::fill(z.begin(), z.end(), 0.0);
+    // plaintexts in chunks: encode on the host cores in parallel, then one upload,
+    // lift, NTT and Montgomery conversion per chunk
+    const uint32_t total = lo.groups * lo.n_in, chunk = 64;
+    std::vector<int64_t> coeffs((size_t)chunk * n);
+    int64_t* d_coeffs = nullptr;
+    if (cudaMalloc(&d_coeffs, coeffs.size() * sizeof(int64_t)) != cudaSuccess) {
+        delete gh;
+        return fail(BM_E_OOM, "gallery staging allocation failed");
+    }
+    const double pscale = (double)c.primes[lo.level];
+    bm_status st = BM_OK;
+    for (uint32_t p0 = 0; p0 < total && st == BM_OK; p0 += chunk) {
+        const uint32_t np = std::min(chunk, total - p0);
+#pragma omp parallel for schedule(dynamic)
+        for (int pp = 0; pp < (int)np; pp++) {
+            const uint32_t grp = (p0 + pp) / lo.n_in, i = (p0 + pp) % lo.n_in;
+            std::vector<double> zz(S, 0.0);
             for (uint32_t u = 0; u < lo.G; u++) {
                 const uint64_t id = (uint64_t)grp * lo.G + u;
                 if (id >= n_ids) break;
-                for (uint32_t t = 0; t < part_size; t++) z[u * part_size + t] = feats[id * dim + i * part_size + t];
+                for (uint32_t t = 0; t < part_size; t++) zz[u * part_size + t] = feats[id * dim + i * part_size + t];
             }
-            uint64_t* dst = g.d_pts + ((size_t)grp * lo.n_in + i) * (lo.level + 1) * n;
-            bm_status st = encode_to_device(c, z, (double)c.primes[lo.level], lo.level, dst);
-            if (st != BM_OK) { delete gh; return st; }
+            encode_real(c, zz.data(), pscale, coeffs.data() + (size_t)pp * n);
         }
+        uint64_t* dst = g.d_pts + (size_t)p0 * (lo.level + 1) * n;
+        LimbBatch out = packed(c, dst, np, lo.level + 1);
+        cudaError_t e = cudaMemcpyAsync(d_coeffs, coeffs.data(), (size_t)np * n * 8, cudaMemcpyHostToDevice, c.stream);
+        if (e == cudaSuccess) e = lift_signed(c, d_coeffs, out, c.stream);
+        if (e == cudaSuccess) e = ntt_forward(c, out, c.stream);
+        if (e == cudaSuccess) e = to_montgomery(c, out, false, c.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);   // coeffs is reused
+        if (e != cudaSuccess) st = fail(BM_E_CUDA, std::string("gallery encode: ") + cudaGetErrorString(e));
     }
+    cudaFree(d_coeffs);
+    if (st != BM_OK) {
+        delete gh;
+        return st;
+    }
+    std::vector<double> z(S);
     if (lo.tiled) {
         for (uint32_t i = 0; i < lo.n_in; i++) {
             for (size_t k = 0; k < S; k++) z[k] = ((k % dim) / part_size == i) ? 1.0 : 0.0;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <complex>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -61,6 +62,14 @@ struct KsLevelConst {
 struct Plan;
 void destroy_plan(Plan* p);
 
+// Precomputed tables of the canonical-embedding encoder (host.cpp).
+struct EncoderTables {
+    std::vector<std::complex<double>> root;   // exp(2 pi i k / N), k < N/2
+    std::vector<uint32_t> brv;                // bit reversal of log N bits
+    std::vector<std::complex<double>> zeta;   // exp(i pi k / N), k < N
+    std::vector<uint32_t> pos, cpos;          // slot j -> index t of 5^j = 2t+1, and of -5^j
+};
+
 struct Context {
     bm_params params{};
     int device = 0;
@@ -73,9 +82,12 @@ struct Context {
     cudaStream_t stream = nullptr;            // for client-side helpers (keygen, encrypt)
     uint64_t P_mod[MAXB]{};                   // P mod each prime
     double scale = 0;
+    EncoderTables enc;
     std::vector<KsLevelConst> h_ksc;          // key-switching constants per level (host copy)
     KsLevelConst* d_ksc = nullptr;            // ... and on the device
     ulonglong2* d_qlinv = nullptr;            // [level][j]: q_level^-1 mod q_j (Shoup pairs), for rescale
+    uint32_t ks_wide_batch = 1u << 30;        // key-switch batches of at least this many ciphertexts use
+                                              // 16 coefficients per thread (BM_KS_WIDE_BATCH)
     uint64_t next_id = 1;                     // ids of galleries and key sets (plan cache keys)
     std::vector<Plan*> plans;
     // lifetime: every handle made from the context holds a reference; the context
@@ -204,6 +216,7 @@ void sample_gauss(uint64_t seed, uint64_t tag, uint64_t obj, double sigma, int64
 void sample_zo(uint64_t seed, uint64_t tag, uint64_t obj, int64_t* out, uint32_t n);
 void sample_secret(uint64_t seed, uint32_t hw, uint32_t log_n, int64_t* out);
 void cdt_table(double sigma, uint32_t kmax, uint64_t* table);
+void encoder_tables(Context& ctx);
 // round(scale * tau^{-1}(z)) for real slot values z[slots]; coefficients out[N]
 void encode_real(const Context& ctx, const double* z, double scale, int64_t* out);
 // slots of integer coefficients / scale (real parts)
@@ -237,7 +250,7 @@ cudaError_t ntt_forward(const Context& c, const LimbBatch& b, cudaStream_t s);
 cudaError_t ntt_inverse(const Context& c, const LimbBatch& b, cudaStream_t s);
 // x -> x * 2^64 mod q (Montgomery form) / back, on a limb batch
 cudaError_t to_montgomery(const Context& c, const LimbBatch& b, bool inverse, cudaStream_t s);
-// out[i] = signed v[i] mod q on each limb (v: device int64[N])
+// out[poly][k][i] = signed v[poly][i] mod q_k on each limb (v: device int64[n_polys][N])
 cudaError_t lift_signed(const Context& c, const int64_t* d_v, const LimbBatch& out, cudaStream_t s);
 
 // Rotation (automorphism + hybrid key switch) of B ciphertexts at `level`, NTT form:

@@ -168,71 +168,70 @@ void sample_secret(uint64_t seed, uint32_t hw, uint32_t log_n, int64_t* out) {
 
 using cplx = std::complex<double>;
 
-// In-place iterative radix-2 DFT: X[k] = sum_t x[t] exp(sign * 2 pi i t k / n).
-static void fft(std::vector<cplx>& a, int sign) {
-    const size_t n = a.size();
-    for (size_t i = 1, j = 0; i < n; i++) {
-        size_t bit = n >> 1;
-        for (; j & bit; bit >>= 1) j ^= bit;
-        j ^= bit;
-        if (i < j) std::swap(a[i], a[j]);
+void encoder_tables(Context& ctx) {
+    const uint32_t n = ctx.n;
+    EncoderTables& T = ctx.enc;
+    T.root.resize(n / 2);
+    for (uint32_t k = 0; k < n / 2; k++) T.root[k] = std::polar(1.0, 2.0 * M_PI * double(k) / double(n));
+    T.brv.resize(n);
+    for (uint32_t i = 0; i < n; i++) {
+        uint32_t r = 0;
+        for (uint32_t b = 0; b < ctx.log_n; b++) r |= ((i >> b) & 1u) << (ctx.log_n - 1 - b);
+        T.brv[i] = r;
     }
-    for (size_t len = 2; len <= n; len <<= 1) {
-        const double ang = sign * 2.0 * M_PI / double(len);
-        std::vector<cplx> w(len / 2);
-        for (size_t k = 0; k < len / 2; k++) w[k] = cplx(std::cos(ang * k), std::sin(ang * k));
-        for (size_t i = 0; i < n; i += len)
-            for (size_t k = 0; k < len / 2; k++) {
-                cplx u = a[i + k], v = a[i + k + len / 2] * w[k];
-                a[i + k] = u + v;
-                a[i + k + len / 2] = u - v;
-            }
+    T.zeta.resize(n);
+    for (uint32_t k = 0; k < n; k++) T.zeta[k] = std::polar(1.0, M_PI * double(k) / double(n));
+    // slot j <-> odd exponent 5^j mod 2N = 2t+1 (and its conjugate -5^j)
+    T.pos.resize(ctx.slots);
+    T.cpos.resize(ctx.slots);
+    const uint64_t two_n = 2ull * n;
+    uint64_t e = 1;
+    for (uint32_t j = 0; j < ctx.slots; j++) {
+        T.pos[j] = (uint32_t)((e - 1) / 2);
+        T.cpos[j] = (uint32_t)((two_n - e - 1) / 2);
+        e = (e * 5) % two_n;
     }
 }
 
-// index t of the odd exponent 2t+1 = 5^j mod 2N (and of its conjugate -5^j)
-static void slot_positions(const Context& ctx, std::vector<uint32_t>& pos, std::vector<uint32_t>& cpos) {
-    const uint64_t two_n = 2ull * ctx.n;
-    pos.resize(ctx.slots);
-    cpos.resize(ctx.slots);
-    uint64_t e = 1;
-    for (uint32_t j = 0; j < ctx.slots; j++) {
-        pos[j] = (uint32_t)((e - 1) / 2);
-        cpos[j] = (uint32_t)((two_n - e - 1) / 2);
-        e = (e * 5) % two_n;
+// In-place iterative radix-2 DFT: X[k] = sum_t x[t] exp(sign * 2 pi i t k / n).
+static void fft(const EncoderTables& T, cplx* a, uint32_t n, int sign) {
+    for (uint32_t i = 0; i < n; i++)
+        if (i < T.brv[i]) std::swap(a[i], a[T.brv[i]]);
+    for (uint32_t len = 2; len <= n; len <<= 1) {
+        const uint32_t half = len / 2, step = n / len;
+        for (uint32_t i = 0; i < n; i += len)
+            for (uint32_t k = 0; k < half; k++) {
+                const cplx w = sign > 0 ? T.root[k * step] : std::conj(T.root[k * step]);
+                const cplx u = a[i + k], v = a[i + k + half] * w;
+                a[i + k] = u + v;
+                a[i + k + half] = u - v;
+            }
     }
 }
 
 void encode_real(const Context& ctx, const double* z, double scale, int64_t* out) {
     const uint32_t n = ctx.n;
-    std::vector<uint32_t> pos, cpos;
-    slot_positions(ctx, pos, cpos);
+    const EncoderTables& T = ctx.enc;
     // values at zeta^(2t+1): m(zeta^(2t+1)) = sum_k (m_k zeta^k) w^(tk), w = exp(2 pi i / N)
     std::vector<cplx> v(n);
     for (uint32_t j = 0; j < ctx.slots; j++) {
-        v[pos[j]] = cplx(z[j], 0.0);
-        v[cpos[j]] = cplx(z[j], 0.0);   // conjugate of a real value
+        v[T.pos[j]] = cplx(z[j], 0.0);
+        v[T.cpos[j]] = cplx(z[j], 0.0);   // conjugate of a real value
     }
-    fft(v, -1);   // sum_t v_t w^(-tk) = N * m_k zeta^k
+    fft(T, v.data(), n, -1);   // sum_t v_t w^(-tk) = N * m_k zeta^k
     for (uint32_t k = 0; k < n; k++) {
-        const double ang = -M_PI * double(k) / double(n);
-        const double mk = (v[k] * cplx(std::cos(ang), std::sin(ang))).real() / double(n);
-        const double x = mk * scale;
+        const double x = (v[k] * std::conj(T.zeta[k])).real() / double(n) * scale;
         out[k] = (int64_t)(x >= 0 ? std::floor(x + 0.5) : -std::floor(-x + 0.5));
     }
 }
 
 void decode_real(const Context& ctx, const double* coeffs, double scale, double* z) {
     const uint32_t n = ctx.n;
+    const EncoderTables& T = ctx.enc;
     std::vector<cplx> w(n);
-    for (uint32_t k = 0; k < n; k++) {
-        const double ang = M_PI * double(k) / double(n);
-        w[k] = cplx(std::cos(ang), std::sin(ang)) * (coeffs[k] / scale);
-    }
-    fft(w, +1);   // value at zeta^(2t+1)
-    std::vector<uint32_t> pos, cpos;
-    slot_positions(ctx, pos, cpos);
-    for (uint32_t j = 0; j < ctx.slots; j++) z[j] = w[pos[j]].real();
+    for (uint32_t k = 0; k < n; k++) w[k] = T.zeta[k] * (coeffs[k] / scale);
+    fft(T, w.data(), n, +1);   // value at zeta^(2t+1)
+    for (uint32_t j = 0; j < ctx.slots; j++) z[j] = w[T.pos[j]].real();
 }
 
 }  // namespace bm

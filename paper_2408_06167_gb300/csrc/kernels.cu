@@ -219,8 +219,9 @@ __global__ void k_lift_signed(const int64_t* v, LimbBatch lb, DevTables tab, uin
     const int pi = lb.prime(limb % lb.nl);
     uint64_t* a = limb_ptr(lb, limb, n);
     const uint64_t q = tab.q[pi];
+    const int64_t* src = v + (size_t)(limb / lb.nl) * n;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int64_t x = v[i];
+        const int64_t x = src[i];
         const uint64_t m = x >= 0 ? (uint64_t)x : (uint64_t)(-x);
         const uint64_t r = reduce2(shoup_lazy(m, 1, tab.rsh[pi], q), q);
         a[i] = x >= 0 ? r : negm(r, q);

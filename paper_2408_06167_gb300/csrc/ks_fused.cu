@@ -548,7 +548,12 @@ cudaError_t ks_rotate_fused(const Context& c, const uint64_t* key, uint64_t galo
                             uint64_t* const* d_in, uint64_t* const* d_out, uint64_t* const* d_add, uint64_t* scratch,
                             cudaStream_t s) {
     if (B == 0) return cudaSuccess;
-    if (c.log_n == 16) return ks_fused_launch<8, 8, 2, 2, 2>(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
+    // few ciphertexts: 4 coefficients per thread (more warps hide the latency);
+    // many: 16 per thread (fewer shared-memory exchanges)
+    const bool wide = B >= c.ks_wide_batch;
+    if (c.log_n == 16)
+        return wide ? ks_fused_launch<8, 8, 4, 8, 8>(c, key, galois, level, B, d_in, d_out, d_add, scratch, s)
+                    : ks_fused_launch<8, 8, 2, 2, 2>(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
     if (c.log_n == 12) return ks_fused_launch<6, 6, 2, 8, 8>(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
     return cudaErrorInvalidValue;
 }
