@@ -184,6 +184,25 @@ def alu_peak_tops():
     return SM_COUNT * INT32_MUL_PER_CLK_PER_SM * mhz * 1e6 / 1e12
 
 
+def measured_traffic(kernel_class, workload):
+    """DRAM bytes per launch of the dominant kernel class from the committed ncu
+    record, or None when the record is for another class or workload, or when
+    the kernel sources have changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            rec = json.load(f)
+        if rec["kernel_class"] != kernel_class or not rec["workload"].startswith(workload):
+            return None
+        h = hashlib.sha1()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        return float(rec["dram_bytes_per_launch"]) if h.hexdigest() == rec["sources_sha1"] else None
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def across_ranks(total_s, work, world):
     """Whole-job rate: work summed over ranks / the slowest rank's time.  Returns (rate, max_time)."""
     if world == 1:
@@ -371,10 +390,10 @@ def main():
         peak = alu_peak_tops()
         roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmul32/s",
                     "frac": achieved / peak, "peak_source": "derived: 152 SMs x 64 int32 mul/clk x max SM clock",
-                    "traffic": None}
+                    "traffic": measured_traffic(dom, W.name)}
     else:
         roofline = {"kernel": dom, "bound": "hbm", "achieved": hbm_gbs, "peak": peak_hbm, "unit": "GB/s",
-                    "frac": hbm_gbs / peak_hbm, "peak_source": peak_src, "traffic": None}
+                    "frac": hbm_gbs / peak_hbm, "peak_source": peak_src, "traffic": measured_traffic(dom, W.name)}
     roofline.update({"hbm_view": {"achieved_gbs": hbm_gbs, "peak_gbs": peak_hbm, "frac": hbm_gbs / peak_hbm,
                                   "peak_source": peak_src},
                      "launches_per_step": n_l / args.steps, "avg_launch_us": 1e3 * ms_l / max(n_l, 1),
