@@ -12,7 +12,9 @@ the same through host buffers (`e2e`), p50/p99 step latency, the roofline of
 the dominant kernel class, and the CPU oracle timed on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload NAME] [--no-cpu-baseline]
+                  [--workload NAME] [--part S] [--no-cpu-baseline] [--no-tune]
+  python bench.py --sweep-part [--workload NAME]      N_in sweep vs the cost model
+  python bench.py --serve [--auto-part] [--rate R]    serving mix
 """
 import argparse
 import json
@@ -35,7 +37,7 @@ L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2, written between timed steps
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="face-128d-6144")
@@ -46,6 +48,14 @@ def parse():
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--executors", type=int, default=2)
     ap.add_argument("--max-batch", type=int, default=256)
+    ap.add_argument("--part", type=int, default=0, help="part size (default: the workload's)")
+    ap.add_argument("--sweep-part", action="store_true",
+                    help="N_in sweep: every part size of the workload, measured beside the cost model's prediction")
+    ap.add_argument("--sweep-limit", type=float, default=4.0,
+                    help="sweep: measure only part sizes predicted within this factor of the best")
+    ap.add_argument("--auto-part", action="store_true",
+                    help="serving: each gallery's part size chosen by the cost model (bm_choose_part)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the rotation kernel-shape tuner")
     return ap.parse_args()
 
 
@@ -238,8 +248,14 @@ def run_serving(args):
     from paper_2408_06167_gb300 import binding as bm
     from paper_2408_06167_gb300 import workload as wl
     ctx = bm.bm_context_create("ring16", 0)
-    keys, gals = {}, []
+    wide = None if args.no_tune else bm.bm_autotune_keyswitch(ctx)
+    costs = bm.bm_measure_op_costs(ctx) if args.auto_part else None
+    keys, gals, parts = {}, [], {}
     for gi, (name, R, m, s) in enumerate(SERVE_GALLERIES):
+        if costs is not None:
+            # the cost model's part size for a typical batch of 16 queries
+            s, _ = bm.bm_choose_part("ring16", costs, R, m, 16, 32 << 30)
+        parts[name] = s
         if (m, s) not in keys:
             keys[(m, s)] = bm.bm_keygen(ctx, KEY_SEED, m, s)
         feats = wl.gallery(R, m, seed=10 + gi)
@@ -293,7 +309,9 @@ def run_serving(args):
         "dtype": "u64", "data": "synthetic",
         "config": {"workload": "serving-mix", "ring": "2^16", "arrivals_per_s": args.rate,
                    "duration_s": args.duration, "galleries": [g[0] for g in SERVE_GALLERIES],
-                   "executors": args.executors, "max_batch": args.max_batch},
+                   "executors": args.executors, "max_batch": args.max_batch, "parts": parts,
+                   "part_choice": "cost model (bm_choose_part, 16 queries)" if costs is not None else "fixed",
+                   "ks_wide_batch": wide},
         "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]},
         "server": {k: st[k] for k in ("submitted", "completed", "failed", "batches", "mean_batch",
                                       "workspace_bytes")},
@@ -306,12 +324,103 @@ def run_serving(args):
     print(json.dumps(line))
 
 
+def run_sweep(args):
+    """Sec. 4 on this GPU: the match of the workload at every part size (N_in =
+    dim / part), each measured (CUDA events, L2 flushed between steps) beside
+    the time the cost model predicts from per-launch times measured on the same
+    GPU, and the model's choice (bm_choose_part).  Part sizes whose plan does not
+    fit in 80% of free device memory, or predicted slower than --sweep-limit x
+    the best prediction, are listed with their prediction only."""
+    import torch
+    from paper_2408_06167_gb300 import binding as bm
+    from paper_2408_06167_gb300 import workload as wl
+    W = wl.WORKLOADS[args.workload]
+    ctx = bm.bm_context_create(W.preset, 0)
+    wide = None if args.no_tune else bm.bm_autotune_keyswitch(ctx)
+    costs = bm.bm_measure_op_costs(ctx)
+    budget = int(0.8 * torch.cuda.mem_get_info()[0])
+    feats = wl.gallery(W.n_ids, W.dim)
+    qs, _ = wl.queries(feats, W.n_queries)
+    ref0 = wl.plaintext_scores(feats, qs[0])
+    mode = bm.BM_QUERY_TILED if W.query_mode == "tiled" else bm.BM_QUERY_EXPANDED
+    parts = [p for p in (128, 64, 32, 16, 8, 4, 2, 1) if p <= W.dim]
+    pred = {p: bm.bm_predict_match(W.preset, costs, W.n_ids, W.dim, p, W.n_queries) for p in parts}
+    fitting = [p for p in parts if pred[p][1] <= budget]
+    best_pred = min(pred[p][0] for p in fitting)
+    model_part, _ = bm.bm_choose_part(W.preset, costs, W.n_ids, W.dim, W.n_queries, budget)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    sampler = ClockSampler(0)
+    sampler.start()
+    rows = []
+    for p in parts:
+        ops, nbytes = bm.bm_plan_estimate(W.preset, W.n_ids, W.dim, p, W.n_queries)
+        rot = {}
+        for o in ops:
+            if o["op"] == "rotate":
+                rot[o["level"]] = rot.get(o["level"], 0) + o["count"] / W.n_queries
+        row = {"part": p, "n_in": W.dim // p, "predicted_ms": pred[p][0], "plan_GB": nbytes / 1e9,
+               "rotations_per_query": {f"level{k}": v for k, v in sorted(rot.items())}}
+        if nbytes > budget:
+            row["skipped"] = "plan larger than 80% of free device memory"
+        elif pred[p][0] > args.sweep_limit * best_pred:
+            row["skipped"] = f"predicted over {args.sweep_limit:g}x the best"
+        if "skipped" in row:
+            rows.append(row)
+            continue
+        sk, pk, ek = bm.bm_keygen(ctx, KEY_SEED, W.dim, p)
+        gal = bm.bm_encode_gallery(ctx, feats, W.dim, p)
+        cts = [bm.bm_encrypt_query(ctx, pk, q, W.dim, p, mode, ENC_SEED, i) for i, q in enumerate(qs)]
+        for ct in cts:
+            bm.bm_ciphertext_upload(ct, sptr)
+        r = bm.bm_match(ctx, ek, gal, cts, sptr)
+        scores, rank1, _ = bm.bm_decrypt_scores(ctx, sk, r, 0, W.n_ids)
+        del r
+        steps = max(2, min(args.steps, int(2000.0 / max(pred[p][0], 1e-3))))
+        for _ in range(max(1, min(args.warmup, steps))):
+            bm.bm_match(ctx, ek, gal, cts, sptr)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            r = bm.bm_match(ctx, ek, gal, cts, sptr)
+            ev[k][1].record(stream)
+            del r
+        torch.cuda.synchronize()
+        ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+        row.update({"measured_ms": ms, "steps": steps, "matches_per_s": W.n_ids * W.n_queries / (ms / 1e3),
+                    "predicted_over_measured": pred[p][0] / ms,
+                    "max_abs_score_err_vs_fp64": float(abs(scores - ref0).max()),
+                    "rank1_equal_fp64": int(rank1) == int(ref0.argmax())})
+        rows.append(row)
+        del gal, ek, sk, pk, cts
+    clocks = sampler.stop()
+    measured = [r for r in rows if "measured_ms" in r]
+    best = min(measured, key=lambda r: r["measured_ms"])
+    line = {
+        "metric": METRIC, "value": best["matches_per_s"], "unit": UNIT, "n_gpus": 1, "steps": best["steps"],
+        "warmup": args.warmup, "ms_per_step": best["measured_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": W.name, "mode": "part-sweep", "ring": "2^16" if W.preset == "ring16" else W.preset,
+                   "n_ids": W.n_ids, "dim": W.dim, "queries_per_step": W.n_queries,
+                   "l2": "flushed between steps (512 MiB write)", "ks_wide_batch": wide},
+        "sweep": rows, "model_part": model_part, "measured_best_part": best["part"],
+        "model_part_measured_ms": next((r.get("measured_ms") for r in rows if r["part"] == model_part), None),
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.serve:
         return run_serving(args)
+    if args.sweep_part:
+        return run_sweep(args)
     rank, world, local = dist_env()
     import torch
     torch.cuda.set_device(local)
@@ -322,14 +431,16 @@ def main():
     from paper_2408_06167_gb300 import workload as wl
 
     W = wl.WORKLOADS[args.workload]
+    part = args.part or W.part
     ctx = bm.bm_context_create(W.preset, local)
-    sk, pk, ek = bm.bm_keygen(ctx, KEY_SEED, W.dim, W.part)
+    wide = None if args.no_tune else bm.bm_autotune_keyswitch(ctx)
+    sk, pk, ek = bm.bm_keygen(ctx, KEY_SEED, W.dim, part)
     feats = wl.gallery(W.n_ids, W.dim)
-    gal = bm.bm_encode_gallery(ctx, feats, W.dim, W.part)
+    gal = bm.bm_encode_gallery(ctx, feats, W.dim, part)
     qs, _ = wl.queries(feats, W.n_queries)
     mode = bm.BM_QUERY_TILED if W.query_mode == "tiled" else bm.BM_QUERY_EXPANDED
-    cts = [bm.bm_encrypt_query(ctx, pk, q, W.dim, W.part, mode, ENC_SEED, i) for i, q in enumerate(qs)]
-    host_cts = [bm.bm_encrypt_query(ctx, pk, q, W.dim, W.part, mode, ENC_SEED, i) for i, q in enumerate(qs)]
+    cts = [bm.bm_encrypt_query(ctx, pk, q, W.dim, part, mode, ENC_SEED, i) for i, q in enumerate(qs)]
+    host_cts = [bm.bm_encrypt_query(ctx, pk, q, W.dim, part, mode, ENC_SEED, i) for i, q in enumerate(qs)]
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
     for ct in cts:
@@ -425,9 +536,11 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": W.name, "ring": "2^16", "n_ids": W.n_ids, "dim": W.dim, "part": W.part,
-                   "queries_per_step": W.n_queries, "l2": "flushed between steps (512 MiB write)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": {"workload": W.name, "ring": "2^16" if W.preset == "ring16" else W.preset, "n_ids": W.n_ids,
+                   "dim": W.dim, "part": part, "queries_per_step": W.n_queries,
+                   "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "ks_wide_batch": wide},
         "latency_ms": {"p50": percentile(step_ms, 50), "p99": percentile(step_ms, 99)},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -319,6 +319,87 @@ bm_status bm_profile_control(uint32_t timing, uint32_t reset);
 bm_status bm_profile_read(uint32_t kind, uint64_t* launches, double* device_ms, double* alg_bytes,
                           double* alg_mulops);
 
+/* ---------------------------------------------------------------------------
+ * Schedule model and part-size choice (Sec. 4: the cost F(N_in) of the match is
+ * a sum over its homomorphic operations -- Propositions 1-3 -- of measured
+ * per-operation times, and N_in = dim/part is picked where F is smallest).
+ * Here the operations are the library's own launches, each timed on this GPU
+ * as a + b * count.
+ * ------------------------------------------------------------------------- */
+enum {
+    BM_OP_ROTATE = 0,     /* rotation (automorphism + key switch) of `count` ciphertexts at `level` */
+    BM_OP_RESCALE = 1,    /* rescale of `count` ciphertexts from `level` */
+    BM_OP_MUL_PLAIN = 2,  /* ct x pt product of `count` ciphertexts at `level` (masks) */
+    BM_OP_MAC = 3,        /* HE-C^3 products: `queries` x `count` groups, `parts` products summed each */
+    BM_OP_NTT = 4,        /* forward NTT of `count` limbs (query ingest) */
+    BM_OP_INTT = 5,       /* inverse NTT of `count` limbs (score egress) */
+    BM_OP_COPY = 6,       /* device copy of `count` level-0 ciphertexts (uncompressed outputs) */
+    BM_OP_KINDS = 7
+};
+
+/* One kernel launch (or launch group) of a match schedule. */
+typedef struct bm_op_launch {
+    uint32_t op;          /* BM_OP_* */
+    uint32_t level;       /* level of the input ciphertexts (0 for NTT / INTT / COPY) */
+    uint32_t count;       /* ciphertexts, limbs or groups, as listed above */
+    uint32_t queries;     /* BM_OP_MAC: queries per product set; else 0 */
+    uint32_t parts;       /* BM_OP_MAC: N_in; else 0 */
+} bm_op_launch;
+
+/* Per-launch device time of each op kind and input level, sampled at
+ * BM_COST_POINTS sizes: t_us[op][level][k] is the time (microseconds) of one
+ * launch of units[op][k] units, units increasing.  Units are `count`, except for
+ * BM_OP_MAC: ceil(queries / 4) * count * parts (one read of a gallery
+ * plaintext serves a tile of four queries).  Between points the time is
+ * interpolated linearly, above the last point extrapolated from the last two,
+ * below the first taken as the first.  NTT, INTT and COPY use level 0. */
+#define BM_COST_POINTS 8
+typedef struct bm_op_costs {
+    double units[BM_OP_KINDS][BM_COST_POINTS];
+    double t_us[BM_OP_KINDS][BM_MAX_Q][BM_COST_POINTS];
+} bm_op_costs;
+
+/* Host only (no device needed): the launches of the match of `n_queries`
+ * queries against a gallery of n_ids identities in (dim, part_size) under
+ * `params` -- exactly the launches bm_match's plan makes, in order -- and the
+ * device memory its plan holds.  Writes up to ops_cap launches to ops (ops may
+ * be NULL) and the total to *n_ops; *plan_bytes gets the plan's bytes.
+ * BM_E_PARAM / BM_E_DIM / BM_E_LEVEL as for bm_context_create / bm_gallery_layout. */
+bm_status bm_plan_estimate(const bm_params* params, uint64_t n_ids, uint32_t dim, uint32_t part_size,
+                           uint32_t n_queries, bm_op_launch* ops, size_t ops_cap, size_t* n_ops,
+                           uint64_t* plan_bytes);
+
+/* Host only: the predicted device time (ms) of that match: the sum over its
+ * launches of the time `costs` gives each launch. */
+bm_status bm_predict_match(const bm_params* params, const bm_op_costs* costs, uint64_t n_ids, uint32_t dim,
+                           uint32_t part_size, uint32_t n_queries, double* ms, uint64_t* plan_bytes);
+
+/* Host only: the part size (N_in = dim / part) of smallest predicted time among
+ * the powers of two 1..dim whose plan fits in `hbm_budget` bytes (0 = no limit);
+ * ties go to the larger part (fewer keys).  BM_E_HBM_BUDGET if none fits. */
+bm_status bm_choose_part(const bm_params* params, const bm_op_costs* costs, uint64_t n_ids, uint32_t dim,
+                         uint32_t n_queries, uint64_t hbm_budget, uint32_t* part_size, double* ms);
+
+/* Times every op kind on this context's device at BM_COST_POINTS sizes per
+ * level (1, 2, 4, ..., 128 ciphertexts or limbs; MAC: 4 queries x 8 parts x
+ * 1..128 groups), with seeded random residues as operands (the values do not
+ * change the time).  Rotations use the kernel shape the context currently picks
+ * for each batch size, so run bm_autotune_keyswitch first.  Takes a few seconds
+ * and up to ~4 GB of device memory at ring 2^16.  Levels an op cannot take
+ * (rescale from level 0) stay 0. */
+bm_status bm_measure_op_costs(bm_context* ctx, bm_op_costs* out);
+
+/* Rotation kernels come in two shapes: 4 coefficients per thread (radix-4
+ * register phases, 2 NTT rows per block) and 16 (radix-16 phases, 8 rows per
+ * block).  bm_autotune_keyswitch times both at every level for batches of
+ * 1, 2, 4, ..., 128 ciphertexts and keeps, per level, the smallest batch size
+ * from which the 16-coefficient shape is faster at every larger size
+ * (wide_batch_out[level], 2^30 = never; pass NULL to skip).
+ * bm_set_ks_wide_batch sets one level's threshold by hand.  Plans built before
+ * the change keep their kernels. */
+bm_status bm_autotune_keyswitch(bm_context* ctx, uint32_t* wide_batch_out, size_t capacity);
+bm_status bm_set_ks_wide_batch(bm_context* ctx, uint32_t level, uint32_t batch);
+
 #ifdef __cplusplus
 }
 #endif

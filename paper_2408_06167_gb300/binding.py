@@ -42,6 +42,35 @@ class bm_params(ctypes.Structure):
                 ("dnum", _u32), ("log_scale", _u32), ("secret_hw", _u32), ("sigma", _dbl)]
 
 
+OPS = {"rotate": 0, "rescale": 1, "mul_plain": 2, "mac": 3, "ntt": 4, "intt": 5, "copy": 6}
+OP_NAMES = {v: k for k, v in OPS.items()}
+BM_OP_KINDS = 7
+BM_MAX_Q = 6
+BM_COST_POINTS = 8
+
+
+class bm_op_launch(ctypes.Structure):
+    _fields_ = [("op", _u32), ("level", _u32), ("count", _u32), ("queries", _u32), ("parts", _u32)]
+
+
+class bm_op_costs(ctypes.Structure):
+    _fields_ = [("units", (_dbl * BM_COST_POINTS) * BM_OP_KINDS),
+                ("t_us", ((_dbl * BM_COST_POINTS) * BM_MAX_Q) * BM_OP_KINDS)]
+
+    def as_arrays(self):
+        """(units[op][k], t_us[op][level][k]) as numpy arrays."""
+        u = np.ctypeslib.as_array(self.units).copy()
+        t = np.ctypeslib.as_array(self.t_us).copy()
+        return u, t
+
+    @classmethod
+    def from_arrays(cls, units, t_us):
+        c = cls()
+        np.ctypeslib.as_array(c.units)[...] = units
+        np.ctypeslib.as_array(c.t_us)[...] = t_us
+        return c
+
+
 _SIGS = {
     "bm_last_error": (ctypes.c_char_p, []),
     "bm_params_preset": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(bm_params)]),
@@ -85,6 +114,16 @@ _SIGS = {
     "bm_server_wait": (ctypes.c_int, [_vp, _u64, _u32, _PP]),
     "bm_server_cancel": (ctypes.c_int, [_vp, _u64]),
     "bm_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(bm_server_stats_t)]),
+    "bm_plan_estimate": (ctypes.c_int, [ctypes.POINTER(bm_params), _u64, _u32, _u32, _u32,
+                                        ctypes.POINTER(bm_op_launch), ctypes.c_size_t,
+                                        ctypes.POINTER(ctypes.c_size_t), _U64P]),
+    "bm_predict_match": (ctypes.c_int, [ctypes.POINTER(bm_params), ctypes.POINTER(bm_op_costs), _u64, _u32, _u32,
+                                        _u32, _DP, _U64P]),
+    "bm_choose_part": (ctypes.c_int, [ctypes.POINTER(bm_params), ctypes.POINTER(bm_op_costs), _u64, _u32, _u32,
+                                      _u64, _U32P, _DP]),
+    "bm_measure_op_costs": (ctypes.c_int, [_vp, ctypes.POINTER(bm_op_costs)]),
+    "bm_autotune_keyswitch": (ctypes.c_int, [_vp, _U32P, ctypes.c_size_t]),
+    "bm_set_ks_wide_batch": (ctypes.c_int, [_vp, _u32, _u32]),
     "bm_profile_control": (ctypes.c_int, [_u32, _u32]),
     "bm_profile_read": (ctypes.c_int, [_u32, _U64P, _DP, _DP, _DP]),
 }
@@ -400,3 +439,58 @@ def bm_server_stats(srv):
     st = bm_server_stats_t()
     _check(_L.bm_server_stats(srv.ptr, ctypes.byref(st)))
     return {f: getattr(st, f) for f, _ in bm_server_stats_t._fields_}
+
+
+# ---- schedule model, part-size choice, kernel-shape tuning ----
+
+def _params(p):
+    return bm_params_preset(p) if isinstance(p, (str, int)) else p
+
+
+def bm_plan_estimate(params, n_ids, dim, part, n_queries):
+    """(launches as a list of dicts, plan bytes) of the match; host only."""
+    p = _params(params)
+    n = ctypes.c_size_t()
+    _check(_L.bm_plan_estimate(ctypes.byref(p), n_ids, dim, part, n_queries, None, 0, ctypes.byref(n), None))
+    arr = (bm_op_launch * max(n.value, 1))()
+    nbytes = _u64()
+    _check(_L.bm_plan_estimate(ctypes.byref(p), n_ids, dim, part, n_queries, arr, n.value, ctypes.byref(n),
+                               ctypes.byref(nbytes)))
+    ops = [dict(op=OP_NAMES[a.op], level=a.level, count=a.count, queries=a.queries, parts=a.parts)
+           for a in arr[:n.value]]
+    return ops, nbytes.value
+
+
+def bm_predict_match(params, costs, n_ids, dim, part, n_queries):
+    """(predicted ms, plan bytes); host only."""
+    p = _params(params)
+    ms, nbytes = _dbl(), _u64()
+    _check(_L.bm_predict_match(ctypes.byref(p), ctypes.byref(costs), n_ids, dim, part, n_queries,
+                               ctypes.byref(ms), ctypes.byref(nbytes)))
+    return ms.value, nbytes.value
+
+
+def bm_choose_part(params, costs, n_ids, dim, n_queries, hbm_budget=0):
+    """(part size, predicted ms); host only."""
+    p = _params(params)
+    part, ms = _u32(), _dbl()
+    _check(_L.bm_choose_part(ctypes.byref(p), ctypes.byref(costs), n_ids, dim, n_queries, hbm_budget,
+                             ctypes.byref(part), ctypes.byref(ms)))
+    return part.value, ms.value
+
+
+def bm_measure_op_costs(ctx):
+    c = bm_op_costs()
+    _check(_L.bm_measure_op_costs(ctx.ptr, ctypes.byref(c)))
+    return c
+
+
+def bm_autotune_keyswitch(ctx):
+    """Per-level batch size from which rotations use 16 coefficients per thread (2^30 = never)."""
+    out = (_u32 * ctx.n_q)()
+    _check(_L.bm_autotune_keyswitch(ctx.ptr, out, ctx.n_q))
+    return list(out)
+
+
+def bm_set_ks_wide_batch(ctx, level, batch):
+    _check(_L.bm_set_ks_wide_batch(ctx.ptr, level, batch))

@@ -47,38 +47,6 @@ static uint32_t ilog2(uint64_t x) {
     return r;
 }
 
-// RAII device buffer
-struct DevBuf {
-    uint64_t* p = nullptr;
-    size_t words = 0;
-    DevBuf() = default;
-    DevBuf(const DevBuf&) = delete;
-    DevBuf& operator=(const DevBuf&) = delete;
-    ~DevBuf() {
-        if (p) cudaFree(p);
-    }
-    cudaError_t alloc(size_t w) {
-        words = w;
-        return cudaMalloc(&p, std::max<size_t>(w, 1) * sizeof(uint64_t));
-    }
-    uint64_t* release() {
-        uint64_t* r = p;
-        p = nullptr;
-        return r;
-    }
-};
-
-static LimbBatch limbs_of(uint64_t* base, uint32_t n_polys, uint32_t nl, uint64_t poly_stride,
-                          uint32_t first_prime = 0, uint32_t limb_off = 0) {
-    LimbBatch b{base, n_polys, poly_stride, limb_off, nl, {}};
-    for (uint32_t k = 0; k < nl; k++) b.set(k, (uint8_t)(first_prime + k));
-    return b;
-}
-// polys of `nl` consecutive limbs starting at prime 0, packed
-static LimbBatch packed(const Context& c, uint64_t* base, uint32_t n_polys, uint32_t nl) {
-    return limbs_of(base, n_polys, nl, (uint64_t)nl * c.n);
-}
-
 // ---------------------------------------------------------------------------
 // schedule layout for (n_ids, dim, part) under a context
 // ---------------------------------------------------------------------------
@@ -119,7 +87,9 @@ static std::vector<int32_t> schedule_rotations(const Context& c, const Layout& l
 // context
 // ---------------------------------------------------------------------------
 
-static bm_status context_init(Context& c, const bm_params& p, int device) {
+// Validates the parameters and fills the context's sizes, digits and scale
+// (host only: the schedule model uses it without a device).
+static bm_status context_shape(Context& c, const bm_params& p) {
     if (p.log_n < 12 || p.log_n > 16) return fail(BM_E_PARAM, "log_n must be in [12, 16]");
     if (p.n_q < 2 || p.n_q > BM_MAX_Q || p.n_p < 1 || p.n_p > BM_MAX_P)
         return fail(BM_E_PARAM, "n_q must be in [2, 6] and n_p in [1, 3]");
@@ -134,7 +104,6 @@ static bm_status context_init(Context& c, const bm_params& p, int device) {
         return fail(BM_E_PARAM, "digits must be non-empty and hold at most 3 primes");
     if (p.log_scale < 20 || p.log_scale > 50) return fail(BM_E_PARAM, "log_scale must be in [20, 50]");
     c.params = p;
-    c.device = device;
     c.log_n = p.log_n;
     c.n = 1u << p.log_n;
     c.slots = c.n / 2;
@@ -142,14 +111,23 @@ static bm_status context_init(Context& c, const bm_params& p, int device) {
     c.alpha = p.n_p;
     c.nb = p.n_q + p.n_p;
     c.scale = std::ldexp(1.0, (int)p.log_scale);
-    encoder_tables(c);
-    if (!gen_primes(c.log_n, bits, c.primes)) return fail(BM_E_PARAM, "prime search failed");
     c.digits.clear();
     for (uint32_t d = 0; d < p.dnum; d++) {
         std::vector<uint32_t> dg;
         for (uint32_t j = d * dsize; j < std::min(p.n_q, (d + 1) * dsize); j++) dg.push_back(j);
         c.digits.push_back(dg);
     }
+    return BM_OK;
+}
+
+static bm_status context_init(Context& c, const bm_params& p, int device) {
+    BM_TRY(context_shape(c, p));
+    c.device = device;
+    std::vector<uint32_t> bits;
+    for (uint32_t i = 0; i < p.n_q; i++) bits.push_back(p.q_bits[i]);
+    for (uint32_t i = 0; i < p.n_p; i++) bits.push_back(p.p_bits[i]);
+    encoder_tables(c);
+    if (!gen_primes(c.log_n, bits, c.primes)) return fail(BM_E_PARAM, "prime search failed");
     for (uint32_t j = 0; j < c.nb; j++) {
         uint64_t P = 1;
         for (uint32_t k = 0; k < c.alpha; k++) P = h_mulmod(P, c.primes[c.L + 1 + k] % c.primes[j], c.primes[j]);
@@ -200,7 +178,8 @@ static bm_status context_init(Context& c, const bm_params& p, int device) {
         c.tab.itw[j] = (const ulonglong2*)c.d_twiddles + j * per + c.n;
     }
     BM_CUDA_TRY(build_ks_constants(c));
-    if (const char* w = std::getenv("BM_KS_WIDE_BATCH")) c.ks_wide_batch = (uint32_t)std::strtoul(w, nullptr, 10);
+    if (const char* w = std::getenv("BM_KS_WIDE_BATCH"))
+        for (uint32_t& t : c.ks_wide_batch) t = (uint32_t)std::strtoul(w, nullptr, 10);
     return BM_OK;
 }
 
@@ -841,24 +820,63 @@ void drop_plans(Context& c, uint64_t id) {
     c.plans.swap(keep);
 }
 
+// What the schedule needs to know about a gallery: its layout and, for the
+// launch pass, where its plaintexts live.
+struct SchedView {
+    uint32_t n_in = 0, part = 0, level = 0, groups = 0;
+    bool tiled = true, compress = true;
+    const uint64_t* d_pts = nullptr;
+    const uint64_t* d_masks = nullptr;
+    const uint64_t* d_cmask = nullptr;
+};
+
+static SchedView view_of(const Gallery& g) {
+    SchedView v;
+    v.n_in = g.n_in;
+    v.part = g.part;
+    v.level = g.level;
+    v.groups = g.groups;
+    v.tiled = g.tiled;
+    v.compress = g.compress;
+    v.d_pts = g.d_pts;
+    v.d_masks = g.d_masks;
+    v.d_cmask = g.d_cmask;
+    return v;
+}
+
+static SchedView view_of(const Layout& lo, uint32_t part) {
+    SchedView v;
+    v.n_in = lo.n_in;
+    v.part = part;
+    v.level = lo.level;
+    v.groups = lo.groups;
+    v.tiled = lo.tiled;
+    v.compress = lo.compress;
+    return v;
+}
+
 struct MatchRun {
-    Context& c;
-    const Gallery& g;
-    const EvalKeys& ek;
+    const Context& c;
+    const SchedView g;
+    const EvalKeys* ek;
     Plan& pl;
     cudaStream_t s = nullptr;
     uint32_t ksb = 128;
     cudaError_t err = cudaSuccess;
+    std::vector<bm_op_launch>* rec = nullptr;   // dry pass: the launches, in order
 
-    MatchRun(Context& c_, const Gallery& g_, const EvalKeys& ek_, Plan& p_) : c(c_), g(g_), ek(ek_), pl(p_) {}
+    MatchRun(const Context& c_, const SchedView& g_, const EvalKeys* ek_, Plan& p_) : c(c_), g(g_), ek(ek_), pl(p_) {}
 
     void check(cudaError_t e) {
         if (err == cudaSuccess && e != cudaSuccess) err = e;
     }
+    void record(uint32_t op, uint32_t level, size_t count, uint32_t queries = 0, uint32_t parts = 0) {
+        if (rec && !pl.arena.live) rec->push_back({op, level, (uint32_t)count, queries, parts});
+    }
     size_t cw(uint32_t level) const { return ct_words(c, level); }
     const uint64_t* key(int32_t rot) const {
-        auto it = ek.keys.find(galois_of(c, rot));
-        return it == ek.keys.end() ? nullptr : it->second;
+        auto it = ek->keys.find(galois_of(c, rot));
+        return it == ek->keys.end() ? nullptr : it->second;
     }
     void need_scratch(size_t words) { pl.scratch_words = std::max(pl.scratch_words, words); }
 
@@ -869,6 +887,7 @@ struct MatchRun {
         auto dadd = add ? pl.arena.list(*add) : nullptr;
         if (!pl.arena.live) {
             need_scratch(ks_scratch_words(c, level, (uint32_t)std::min<size_t>(ksb, in.size())));
+            for (size_t b0 = 0; b0 < in.size(); b0 += ksb) record(BM_OP_ROTATE, level, std::min<size_t>(ksb, in.size() - b0));
             return;
         }
         const uint64_t gk = galois_of(c, rot);
@@ -883,6 +902,7 @@ struct MatchRun {
         auto dout = pl.arena.list(out);
         if (!pl.arena.live) {
             need_scratch(rescale_scratch_words(c, level, (uint32_t)std::min<size_t>(ksb, in.size())));
+            for (size_t b0 = 0; b0 < in.size(); b0 += ksb) record(BM_OP_RESCALE, level, std::min<size_t>(ksb, in.size() - b0));
             return;
         }
         for (size_t b0 = 0; b0 < in.size(); b0 += ksb) {
@@ -895,17 +915,19 @@ struct MatchRun {
         auto din = pl.arena.list(in);
         auto dpt = pl.arena.list(pt);
         auto dout = pl.arena.list(out);
+        record(BM_OP_MUL_PLAIN, level, in.size());
         if (!pl.arena.live) return;
         check(mul_plain(c, level, (uint32_t)in.size(), din, dpt, dout, s));
     }
 
     // a0..a6 on the plan's buffers; with arena.live == false only the pointer
-    // arrays are collected and the scratch sized.
+    // arrays are collected, the scratch sized and (with rec) the launches listed.
     void schedule() {
         const uint32_t Q = pl.Q, n_in = g.n_in, part = g.part, lg = g.level, n_out = pl.n_out;
         pl.arena.cursor = 0;
         NvtxRange whole(pl.arena.live ? "bm_match_launch" : "bm_match_plan");
         // a0: queries into the NTT domain
+        record(BM_OP_NTT, 0, (size_t)Q * pl.ncts * 2 * (c.L + 1));
         if (pl.arena.live) check(ntt_forward(c, packed(c, pl.qin, Q * pl.ncts * 2, c.L + 1), s));
         // Algorithm 1: C_out,i = Res(Mul(P)(C_in, mask_i)), then log2(N_in) rotate-and-add by part*2^(j-1)
         if (g.tiled) {
@@ -913,7 +935,7 @@ struct MatchRun {
             for (uint32_t q = 0; q < Q; q++)
                 for (uint32_t i = 0; i < n_in; i++) {
                     in.push_back(pl.qin + (size_t)q * cw(c.L));
-                    pt.push_back(g.d_masks + (size_t)i * (c.L + 1) * c.n);
+                    pt.push_back(const_cast<uint64_t*>(g.d_masks) + (size_t)i * (c.L + 1) * c.n);
                     o0.push_back(pl.t0 + ((size_t)q * n_in + i) * cw(c.L));
                     o1.push_back(pl.T + ((size_t)q * n_in + i) * cw(lg));
                 }
@@ -925,6 +947,7 @@ struct MatchRun {
         // HE-C^3 per chunk of groups, then compression
         for (uint32_t g0 = 0; g0 < g.groups; g0 += pl.chunk) {
             const uint32_t G = std::min(pl.chunk, g.groups - g0);
+            record(BM_OP_MAC, lg, G, Q, n_in);
             if (pl.arena.live) {
                 check(mac(c, lg, Q, G, n_in, Tsrc, g.d_pts + (size_t)g0 * n_in * (lg + 1) * c.n, pl.accA, s));
             }
@@ -938,17 +961,18 @@ struct MatchRun {
             for (uint32_t t = 1; (1u << (t - 1)) < part; t++) rotate_batch(lg - 1, (int32_t)(1u << (t - 1)), b, b, &b);
             if (!g.compress) {
                 // per-group outputs at level 0: copy into the result
-                if (pl.arena.live)
-                    for (uint32_t q = 0; q < Q; q++) {
-                        ProfScope ps(BM_KERNEL_OTHER, s, 16.0 * G * cw(0));
-                        check(cudaMemcpyAsync(pl.result + ((size_t)q * n_out + g0) * cw(0),
-                                              pl.accB + (size_t)q * G * cw(0), (size_t)G * cw(0) * 8,
-                                              cudaMemcpyDeviceToDevice, s));
-                    }
+                for (uint32_t q = 0; q < Q; q++) {
+                    record(BM_OP_COPY, 0, G);
+                    if (!pl.arena.live) continue;
+                    ProfScope ps(BM_KERNEL_OTHER, s, 16.0 * G * cw(0));
+                    check(cudaMemcpyAsync(pl.result + ((size_t)q * n_out + g0) * cw(0),
+                                          pl.accB + (size_t)q * G * cw(0), (size_t)G * cw(0) * 8,
+                                          cudaMemcpyDeviceToDevice, s));
+                }
                 continue;
             }
             const uint32_t lc = lg - 1;
-            std::vector<uint64_t*> mp(b.size(), g.d_cmask);
+            std::vector<uint64_t*> mp(b.size(), const_cast<uint64_t*>(g.d_cmask));
             mulplain_batch(lc, b, mp, b);
             // tree of right rotations: level bb pairs r and r + 2^bb (r = 0 mod 2^(bb+1)) inside each pack
             for (uint32_t bb = 0; (1u << bb) < part; bb++) {
@@ -971,30 +995,74 @@ struct MatchRun {
             rescale_batch(lc, heads, outs);
         }
         // a6: score ciphertexts back to coefficient form
+        record(BM_OP_INTT, 0, (size_t)Q * n_out * 2);
         if (pl.arena.live) check(ntt_inverse(c, limbs_of(pl.result, Q * n_out * 2, 1, c.n), s));
     }
 };
+
+// Buffer sizes of a plan (words) and its group chunk: whole packs, bounded by
+// an 8 GiB temporary budget.
+static void plan_dims(const Context& c, const SchedView& g, uint32_t n_out, uint32_t Q, Plan& pl) {
+    pl.Q = Q;
+    pl.ncts = g.tiled ? 1 : g.n_in;
+    pl.n_out = n_out;
+    const uint32_t lg = g.level;
+    const size_t per_group = (size_t)Q * (ct_words(c, lg) + ct_words(c, lg - 1)) * 8;
+    const size_t budget = (size_t)8 << 30;
+    uint32_t chunk = (uint32_t)std::max<size_t>(1, budget / std::max<size_t>(per_group, 1));
+    if (g.compress) chunk = std::max(g.part, chunk / g.part * g.part);
+    pl.chunk = std::min(chunk, g.groups);
+    pl.qin_words = (size_t)Q * pl.ncts * ct_words(c, c.L);
+    pl.result_words = (size_t)Q * n_out * ct_words(c, 0);
+}
+
+static size_t words_bytes(size_t w) { return std::max<size_t>(w, 1) * 8; }
+
+// Device bytes of every buffer the plan allocates (the same sizes, in the same
+// roles, as plan_build), with the launches of its schedule when rec != nullptr.
+static size_t plan_shape(const Context& c, const SchedView& g, uint32_t n_out, uint32_t Q,
+                         std::vector<bm_op_launch>* rec) {
+    Plan pl;
+    plan_dims(c, g, n_out, Q, pl);
+    MatchRun run(c, g, nullptr, pl);
+    run.rec = rec;
+    run.schedule();
+    size_t bytes = words_bytes(pl.qin_words) + words_bytes(pl.result_words);
+    if (g.tiled) bytes += words_bytes((size_t)Q * g.n_in * ct_words(c, c.L)) + words_bytes((size_t)Q * g.n_in * ct_words(c, g.level));
+    bytes += words_bytes((size_t)Q * pl.chunk * ct_words(c, g.level)) + words_bytes((size_t)Q * pl.chunk * ct_words(c, g.level - 1));
+    bytes += words_bytes(pl.scratch_words) + words_bytes(pl.arena.host.size());
+    return bytes;
+}
+
+size_t plan_estimate_bytes(const Context& c, const Gallery& g, uint32_t Q) {
+    Layout lo;
+    if (make_layout(c, g.n_ids, g.dim, g.part, lo) != BM_OK) return 0;
+    return plan_shape(c, view_of(g), lo.n_out, Q, nullptr);
+}
+
+bm_status schedule_launches(const bm_params& p, uint64_t n_ids, uint32_t dim, uint32_t part, uint32_t Q,
+                            std::vector<bm_op_launch>* ops, size_t* bytes) {
+    if (Q == 0 || n_ids == 0) return fail(BM_E_ARG, "empty gallery or batch");
+    Context c;
+    BM_TRY(context_shape(c, p));
+    Layout lo;
+    BM_TRY(make_layout(c, n_ids, dim, part, lo));
+    const size_t b = plan_shape(c, view_of(lo, part), lo.n_out, Q, ops);
+    if (bytes) *bytes = b;
+    return BM_OK;
+}
 
 bm_status plan_build(Context& c, const Gallery& g, const EvalKeys& ek, uint32_t Q, cudaStream_t cs, Plan*& out) {
     auto* pl = new Plan();
     std::unique_ptr<Plan> guard(pl);
     Layout lo;
     BM_TRY(make_layout(c, g.n_ids, g.dim, g.part, lo));
+    const SchedView v = view_of(g);
     pl->c = &c;
     pl->gid = g.id;
     pl->kid = ek.id;
-    pl->Q = Q;
-    pl->ncts = g.tiled ? 1 : g.n_in;
-    pl->n_out = lo.n_out;
+    plan_dims(c, v, lo.n_out, Q, *pl);
     const uint32_t lg = g.level;
-    // group chunk: whole packs, bounded by a temporary-memory budget
-    const size_t per_group = (size_t)Q * (ct_words(c, lg) + ct_words(c, lg - 1)) * 8;
-    const size_t budget = (size_t)8 << 30;
-    uint32_t chunk = (uint32_t)std::max<size_t>(1, budget / std::max<size_t>(per_group, 1));
-    if (g.compress) chunk = std::max(g.part, chunk / g.part * g.part);
-    pl->chunk = std::min(chunk, g.groups);
-    pl->qin_words = (size_t)Q * pl->ncts * ct_words(c, c.L);
-    pl->result_words = (size_t)Q * lo.n_out * ct_words(c, 0);
     bool ok = pl->alloc(pl->qin, pl->qin_words) && pl->alloc(pl->result, pl->result_words);
     if (g.tiled) {
         ok = ok && pl->alloc(pl->t0, (size_t)Q * g.n_in * ct_words(c, c.L));
@@ -1003,7 +1071,7 @@ bm_status plan_build(Context& c, const Gallery& g, const EvalKeys& ek, uint32_t 
     ok = ok && pl->alloc(pl->accA, (size_t)Q * pl->chunk * ct_words(c, lg));
     ok = ok && pl->alloc(pl->accB, (size_t)Q * pl->chunk * ct_words(c, lg - 1));
     if (!ok) return fail(BM_E_OOM, "match workspace allocation failed");
-    MatchRun run(c, g, ek, *pl);
+    MatchRun run(c, v, &ek, *pl);
     run.schedule();                                     // dry pass
     uint64_t* arr = nullptr;
     ok = pl->alloc(pl->scratch, pl->scratch_words) && pl->alloc(arr, std::max<size_t>(pl->arena.host.size(), 1));
@@ -1043,7 +1111,7 @@ bm_status plan_run(Context& c, const Gallery& g, const EvalKeys& ek, Plan* pl, c
     }
     if (prof_timing()) {
         // per-launch timing: run the same launches eagerly so each gets its event pair
-        MatchRun run(c, g, ek, *pl);
+        MatchRun run(c, view_of(g), &ek, *pl);
         run.s = s;
         run.schedule();
         if (run.err != cudaSuccess) return fail(BM_E_CUDA, std::string("match: ") + cudaGetErrorString(run.err));
@@ -1063,6 +1131,19 @@ static Plan* find_plan(Context& c, uint64_t gid, uint64_t kid, uint32_t Q) {
 }  // namespace bm
 
 extern "C" {
+
+bm_status bm_plan_estimate(const bm_params* params, uint64_t n_ids, uint32_t dim, uint32_t part_size,
+                           uint32_t n_queries, bm_op_launch* ops, size_t ops_cap, size_t* n_ops,
+                           uint64_t* plan_bytes_out) {
+    if (!params) return fail(BM_E_ARG, "null parameters");
+    std::vector<bm_op_launch> v;
+    size_t bytes = 0;
+    BM_TRY(schedule_launches(*params, n_ids, dim, part_size, n_queries, &v, &bytes));
+    if (ops) std::copy(v.begin(), v.begin() + std::min(ops_cap, v.size()), ops);
+    if (n_ops) *n_ops = v.size();
+    if (plan_bytes_out) *plan_bytes_out = bytes;
+    return BM_OK;
+}
 
 bm_status bm_match(bm_context* ctxh, const bm_eval_keys* evk, const bm_gallery* gal, bm_ciphertext* const* queries,
                    uint32_t n_queries, void* stream, bm_result** out) {

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <complex>
 #include <cstdint>
@@ -86,8 +87,10 @@ struct Context {
     std::vector<KsLevelConst> h_ksc;          // key-switching constants per level (host copy)
     KsLevelConst* d_ksc = nullptr;            // ... and on the device
     ulonglong2* d_qlinv = nullptr;            // [level][j]: q_level^-1 mod q_j (Shoup pairs), for rescale
-    uint32_t ks_wide_batch = 1u << 30;        // key-switch batches of at least this many ciphertexts use
-                                              // 16 coefficients per thread (BM_KS_WIDE_BATCH)
+    uint32_t ks_wide_batch[BM_MAX_Q] = {1u << 30, 1u << 30, 1u << 30, 1u << 30, 1u << 30, 1u << 30};
+                                              // per level: key-switch batches of at least this many
+                                              // ciphertexts use 16 coefficients per thread (set by
+                                              // bm_autotune_keyswitch / bm_set_ks_wide_batch / BM_KS_WIDE_BATCH)
     uint64_t next_id = 1;                     // ids of galleries and key sets (plan cache keys)
     std::vector<Plan*> plans;
     // lifetime: every handle made from the context holds a reference; the context
@@ -127,6 +130,11 @@ bm_status plan_build(Context& c, const Gallery& g, const EvalKeys& ek, uint32_t 
 bm_status plan_run(Context& c, const Gallery& g, const EvalKeys& ek, Plan* p, const Ciphertext* const* queries,
                    uint32_t nq, cudaStream_t s);
 size_t plan_bytes(const Plan* p);
+// device bytes the plan of Q queries for this gallery will hold (host only)
+size_t plan_estimate_bytes(const Context& c, const Gallery& g, uint32_t Q);
+// host only: the launches and plan bytes of a match for (params, n_ids, dim, part, Q)
+bm_status schedule_launches(const bm_params& p, uint64_t n_ids, uint32_t dim, uint32_t part, uint32_t Q,
+                            std::vector<bm_op_launch>* ops, size_t* bytes);
 uint32_t plan_queries(const Plan* p);
 uint32_t plan_outputs(const Plan* p);
 const uint64_t* plan_result(const Plan* p);
@@ -189,6 +197,39 @@ inline uint64_t galois_of(const Context& c, int32_t rot) {
 }
 // words of one ciphertext at `level`: [2][level+1][N]
 inline size_t ct_words(const Context& c, uint32_t level) { return (size_t)2 * (level + 1) * c.n; }
+
+// RAII device buffer
+struct DevBuf {
+    uint64_t* p = nullptr;
+    size_t words = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t alloc(size_t w) {
+        words = w;
+        return cudaMalloc(&p, std::max<size_t>(w, 1) * sizeof(uint64_t));
+    }
+    uint64_t* release() {
+        uint64_t* r = p;
+        p = nullptr;
+        return r;
+    }
+};
+
+inline LimbBatch limbs_of(uint64_t* base, uint32_t n_polys, uint32_t nl, uint64_t poly_stride,
+                          uint32_t first_prime = 0, uint32_t limb_off = 0) {
+    LimbBatch b{base, n_polys, poly_stride, limb_off, nl, {}};
+    for (uint32_t k = 0; k < nl; k++) b.set(k, (uint8_t)(first_prime + k));
+    return b;
+}
+// polys of `nl` consecutive limbs starting at prime 0, packed
+inline LimbBatch packed(const Context& c, uint64_t* base, uint32_t n_polys, uint32_t nl) {
+    return limbs_of(base, n_polys, nl, (uint64_t)nl * c.n);
+}
+
 
 // ---- error reporting ----
 void set_error(const std::string& msg);
@@ -265,6 +306,12 @@ bool ks_fused_supported(const Context& c);
 cudaError_t ks_rotate_fused(const Context& c, const uint64_t* key, uint64_t galois, uint32_t level,
                             uint32_t B, uint64_t* const* d_in, uint64_t* const* d_out,
                             uint64_t* const* d_add, uint64_t* scratch, cudaStream_t s);
+// the same with the kernel shape forced: wide = 16 coefficients per thread
+// (only where ks_has_wide), else 4
+bool ks_has_wide(const Context& c);
+cudaError_t ks_rotate_fused_shape(const Context& c, bool wide, const uint64_t* key, uint64_t galois,
+                                  uint32_t level, uint32_t B, uint64_t* const* d_in, uint64_t* const* d_out,
+                                  uint64_t* const* d_add, uint64_t* scratch, cudaStream_t s);
 // rescale in three fused kernels (rings 2^12 and 2^16)
 cudaError_t rescale_fused(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,
                           uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s);

@@ -61,7 +61,8 @@ __host__ __device__ constexpr size_t col_smem_words() {
 // ... and of F4: exchange rows, staging, forward and inverse row twiddles.
 template <int LB, int LT, int R>
 __host__ __device__ constexpr size_t f4_smem_words() {
-    return (size_t)R * sub_words<LB, LT>() + (size_t)kMaxDigit * R * (1 << LB) + 4 * (size_t)row_tw_entries<LB, R>();
+    return (size_t)R * sub_words<LB, LT>() + (LT > 2 ? (size_t)kMaxDigit * R * (1 << LB) : 0) +
+           4 * (size_t)row_tw_entries<LB, R>();
 }
 
 // ---------------------------------------------------------------------------
@@ -173,16 +174,18 @@ __global__ void __launch_bounds__(C * (1 << (LA - LT)))
 // F4: grid (B * nlx, N1 / R).  acc = sum_d ext_d * key_d (both components).
 // ---------------------------------------------------------------------------
 template <int LA, int LB, int LT, int R>
-__global__ void __launch_bounds__(R * (1 << (LB - LT)))
+__global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
     k_ks_f4(const uint64_t* __restrict__ ext, const uint64_t* __restrict__ key, uint64_t* __restrict__ acc,
             const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L, uint32_t nb) {
     constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>(), LOGN = LA + LB, N = 1 << LOGN;
     constexpr int TWN = row_tw_entries<LB, R>();
+    constexpr bool REG = LT <= 2;                            // digits held in registers (else shared memory)
+    constexpr int NT = R * TH;
     extern __shared__ uint64_t dsm[];
     const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
     const SubMem sr{dsm + jr * S, 1};                        // exchange row
-    uint64_t* st = dsm + R * S + jr * M;                     // staging: digit d at st[d * R * M + last_idx]
-    ulonglong2* twf = (ulonglong2*)(dsm + R * S + kMaxDigit * R * M);
+    uint64_t* st = dsm + R * S;                              // staging (16-coefficient shape): [d][k][tid]
+    ulonglong2* twf = (ulonglong2*)(dsm + R * S + (REG ? 0 : kMaxDigit * R * M));
     ulonglong2* twi = twf + TWN;
     const uint32_t nd = kc->nd, nlx = kc->nlx;
     const uint32_t b = blockIdx.x / nlx, jj = blockIdx.x % nlx;
@@ -194,22 +197,29 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)))
     stage_row_twiddles<LA, LB, R, R * TH>(twf, tab.tw[pi], blockIdx.y * R);
     if (jj >= l1) stage_row_twiddles<LA, LB, R, R * TH>(twi, tab.itw[pi], blockIdx.y * R);
     tw_wait();
-    uint64_t v[K];
-    // extended limb jj of every digit, NTT form, last-phase layout, staged
+    uint64_t v[K], s0[REG ? K : 1], s1[REG ? K : 1];
+    // extended limb jj of every digit, NTT form, last-phase layout
 #pragma unroll 1
     for (uint32_t d = 0; d < nd; d++) {
         const uint64_t* e = ext + (((size_t)b * nd + d) * nlx + jj) * N + roff;
         if (jj >= kc->dstart[d] && jj < kc->dstart[d] + kc->dsz[d]) {
-#pragma unroll
-            for (int k = 0; k < K; k++) v[k] = e[last_idx<LB, LT>(t, k)];
+            nttr::load_last<LB, LT>(v, e, t);
         } else {
 #pragma unroll
             for (int k = 0; k < K; k++) v[k] = e[first_idx<LB, LT>(t, k)];
             nttr::fwd_pass<LB, LT>(v, sr, twf, base, t, q, q2);
             __syncthreads();
         }
+        if constexpr (REG) {
 #pragma unroll
-        for (int k = 0; k < K; k++) st[d * R * M + last_idx<LB, LT>(t, k)] = v[k];
+            for (int k = 0; k < K; k++) {
+                if (d == 0) s0[k] = v[k];
+                else s1[k] = v[k];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; k++) st[(d * K + k) * NT + tid] = v[k];
+        }
     }
     // inner product per key component, then store (special primes: inverse row pass)
 #pragma unroll 1
@@ -218,11 +228,14 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)))
         for (int k = 0; k < K; k++) v[k] = 0;
 #pragma unroll 1
         for (uint32_t d = 0; d < nd; d++) {
-            const uint64_t* kk = key + ((size_t)(d * 2 + comp) * nb + pi) * N + roff;
+            uint64_t kv[K];
+            nttr::load_last<LB, LT>(kv, key + ((size_t)(d * 2 + comp) * nb + pi) * N + roff, t);
 #pragma unroll
             for (int k = 0; k < K; k++) {
-                const int c = last_idx<LB, LT>(t, k);
-                const uint64_t x = v[k] + mont_lazy(st[d * R * M + c], kk[c], q, qn);
+                uint64_t e;
+                if constexpr (REG) e = d == 0 ? s0[k] : s1[k];
+                else e = st[(d * K + k) * NT + tid];
+                const uint64_t x = v[k] + mont_lazy(e, kv[k], q, qn);
                 v[k] = x >= q2 ? x - q2 : x;
             }
         }
@@ -297,7 +310,7 @@ __global__ void __launch_bounds__(C * (1 << (LA - LT)))
 // F6: grid (B * l1, N1 / R).  out = (acc - conv) * P^-1 + sigma(c0) (+ add)
 // ---------------------------------------------------------------------------
 template <int LA, int LB, int LT, int R>
-__global__ void __launch_bounds__(R * (1 << (LB - LT)))
+__global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 3)
     k_ks_f6(const uint64_t* __restrict__ conv, const uint64_t* __restrict__ acc, const uint64_t* __restrict__ X0,
             uint64_t* const* out, uint64_t* const* add, const KsLevelConst* __restrict__ kc, DevTables tab,
             uint32_t l1, uint32_t galois) {
@@ -323,15 +336,16 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)))
         if (comp == 0) tw_wait();
         else __syncthreads();
         nttr::fwd_pass<LB, LT>(v, sr, tws, base, t, q, q2);
-        const uint64_t* av = acc + (((size_t)b * 2 + comp) * nlx + j) * N + roff;
-        const uint64_t* ad = add ? add[b] + ((size_t)comp * l1 + j) * N + roff : nullptr;
+        uint64_t av[K], ad[K];
+        nttr::load_last<LB, LT>(av, acc + (((size_t)b * 2 + comp) * nlx + j) * N + roff, t);
+        if (add) nttr::load_last<LB, LT>(ad, add[b] + ((size_t)comp * l1 + j) * N + roff, t);
 #pragma unroll
         for (int k = 0; k < K; k++) {
             const int c = last_idx<LB, LT>(t, k);
-            uint64_t o = shoup(subm(av[c], nttr::reduce4(v[k], q, q2), q), pinv.x, pinv.y, q);
+            uint64_t o = shoup(subm(av[k], nttr::reduce4(v[k], q, q2), q), pinv.x, pinv.y, q);
             if (comp == 0)
                 o = addm(o, X0[((size_t)b * l1 + j) * N + perm_src((uint32_t)(roff + c), LOGN, galois)], q);
-            if (ad) o = addm(o, ad[c], q);
+            if (add) o = addm(o, ad[k], q);
             v[k] = o;
         }
         nttr::relayout<LB, LT, LB / LT - 1, 0>(v, sr, t);
@@ -431,11 +445,11 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)))
     for (int k = 0; k < K; k++) v[k] = r[first_idx<LB, LT>(t, k)];
     tw_wait();
     nttr::fwd_pass<LB, LT>(v, sr, tws, RowBase<R>{jr}, t, q, q2);
-    const uint64_t* x = in[b] + ((size_t)comp * (lvl + 1) + j) * N + roff;
+    uint64_t x[K];
+    nttr::load_last<LB, LT>(x, in[b] + ((size_t)comp * (lvl + 1) + j) * N + roff, t);
     const ulonglong2 w = qlinv[j];
 #pragma unroll
-    for (int k = 0; k < K; k++)
-        v[k] = shoup(subm(x[last_idx<LB, LT>(t, k)], nttr::reduce4(v[k], q, q2), q), w.x, w.y, q);
+    for (int k = 0; k < K; k++) v[k] = shoup(subm(x[k], nttr::reduce4(v[k], q, q2), q), w.x, w.y, q);
     nttr::relayout<LB, LT, LB / LT - 1, 0>(v, sr, t);
     uint64_t* o = out[b] + ((size_t)comp * lvl + j) * N + roff;
 #pragma unroll
@@ -544,18 +558,27 @@ bool ks_fused_supported(const Context& c) {
     return true;
 }
 
-cudaError_t ks_rotate_fused(const Context& c, const uint64_t* key, uint64_t galois, uint32_t level, uint32_t B,
-                            uint64_t* const* d_in, uint64_t* const* d_out, uint64_t* const* d_add, uint64_t* scratch,
-                            cudaStream_t s) {
+bool ks_has_wide(const Context& c) { return c.log_n == 16; }
+
+cudaError_t ks_rotate_fused_shape(const Context& c, bool wide, const uint64_t* key, uint64_t galois,
+                                  uint32_t level, uint32_t B, uint64_t* const* d_in, uint64_t* const* d_out,
+                                  uint64_t* const* d_add, uint64_t* scratch, cudaStream_t s) {
     if (B == 0) return cudaSuccess;
-    // few ciphertexts: 4 coefficients per thread (more warps hide the latency);
-    // many: 16 per thread (fewer shared-memory exchanges)
-    const bool wide = B >= c.ks_wide_batch;
     if (c.log_n == 16)
         return wide ? ks_fused_launch<8, 8, 4, 8, 8>(c, key, galois, level, B, d_in, d_out, d_add, scratch, s)
                     : ks_fused_launch<8, 8, 2, 2, 2>(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
     if (c.log_n == 12) return ks_fused_launch<6, 6, 2, 8, 8>(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t ks_rotate_fused(const Context& c, const uint64_t* key, uint64_t galois, uint32_t level, uint32_t B,
+                            uint64_t* const* d_in, uint64_t* const* d_out, uint64_t* const* d_add, uint64_t* scratch,
+                            cudaStream_t s) {
+    // few ciphertexts: 4 coefficients per thread (more warps hide the latency);
+    // many: 16 per thread (fewer shared-memory exchanges) -- the per-level
+    // threshold is the tuner's (or the caller's) choice
+    const bool wide = level < BM_MAX_Q && B >= c.ks_wide_batch[level];
+    return ks_rotate_fused_shape(c, wide, key, galois, level, B, d_in, d_out, d_add, scratch, s);
 }
 
 }  // namespace bm

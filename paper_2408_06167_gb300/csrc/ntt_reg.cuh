@@ -149,6 +149,21 @@ __device__ __forceinline__ int first_idx(int t, int k) { return pidx<P, LT, 0>(t
 template <int P, int LT>
 __device__ __forceinline__ int last_idx(int t, int k) { return pidx<P, LT, P / LT - 1>(t, k); }
 
+// In the last-phase layout of a pass over 2^P contiguous words (P a multiple of
+// LT), thread t holds the 2^LT consecutive words at t * 2^LT: moved as 16-byte
+// vectors (the row is 256-byte aligned, so every vector is 16-byte aligned).
+template <int P, int LT>
+__device__ __forceinline__ void load_last(uint64_t (&v)[1 << LT], const uint64_t* __restrict__ row, int t) {
+    static_assert(P % LT == 0, "last phase must start at a multiple of the thread's run");
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(row + (t << LT));
+#pragma unroll
+    for (int k = 0; k < (1 << LT) / 2; k++) {
+        const ulonglong2 w = p[k];
+        v[2 * k] = w.x;
+        v[2 * k + 1] = w.y;
+    }
+}
+
 // Twiddles a column pass uses: entries 1 .. 2^LA - 1 of the table, copied to
 // shared memory (index unchanged) with asynchronous copies issued all at once by
 // the T threads of the CTA; wait with tw_wait() before use.

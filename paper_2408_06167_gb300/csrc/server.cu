@@ -113,13 +113,8 @@ bm_status get_plan(Executor& E, uint32_t gid, uint32_t Q, Plan*& out, std::strin
             return BM_OK;
         }
     const Entry& en = S.galleries[gid];
-    Plan* pl = nullptr;
-    bm_status st = plan_build(*S.c, *en.g, *en.ek, Q, E.s, pl);
-    if (st != BM_OK) {
-        err = bm_last_error();
-        return st;
-    }
-    const size_t need = plan_bytes(pl);
+    // admission: the plan's bytes are known before anything is allocated
+    const size_t need = plan_estimate_bytes(*S.c, *en.g, Q);
     for (;;) {
         {
             std::lock_guard<std::mutex> lk(S.mu);
@@ -130,7 +125,6 @@ bm_status get_plan(Executor& E, uint32_t gid, uint32_t Q, Plan*& out, std::strin
         }
         // evict this executor's least recently used plan, if any
         if (E.plans.empty()) {
-            destroy_plan(pl);
             err = "the match workspace (" + std::to_string(need) + " bytes) exceeds the device-memory budget";
             return BM_E_HBM_BUDGET;
         }
@@ -141,6 +135,17 @@ bm_status get_plan(Executor& E, uint32_t gid, uint32_t Q, Plan*& out, std::strin
         E.plans.erase(lru);
         std::lock_guard<std::mutex> lk(S.mu);
         S.plan_bytes_total -= freed;
+    }
+    Plan* pl = nullptr;
+    bm_status st = plan_build(*S.c, *en.g, *en.ek, Q, E.s, pl);
+    {
+        std::lock_guard<std::mutex> lk(S.mu);
+        S.plan_bytes_total -= need;
+        if (st == BM_OK) S.plan_bytes_total += plan_bytes(pl);
+    }
+    if (st != BM_OK) {
+        err = bm_last_error();
+        return st;
     }
     E.plans.push_back({gid, Q, pl, ++E.clock});
     out = pl;

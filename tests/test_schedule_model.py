@@ -1,0 +1,217 @@
+"""The library's schedule model (host only, no GPU): the launches bm_plan_estimate
+lists are the operations of the oracle's schedule (Algorithm 1, HE-C^3,
+compression) counted by its CountingEvaluator, per op and level; the plan's
+bytes are its buffers; the predicted time is the sum the cost table gives each
+launch; and the part-size choice is the argmin over the powers of two (Sec. 4's
+choice of N_in by the cost model F)."""
+import collections
+import math
+
+import numpy as np
+import pytest
+
+bm = pytest.importorskip("paper_2408_06167_gb300.binding")
+from oracle import schedule as sch  # noqa: E402
+
+PRESET = {"toy": (12, 2), "small4": (12, 4), "ring16": (16, 4)}   # log_n, n_q
+
+
+def oracle_counts(preset, R, dim, part):
+    """(op, level) -> count for one query, from the oracle's schedule."""
+    log_n, n_q = PRESET[preset]
+    L, slots = n_q - 1, 1 << (log_n - 1)
+    tiled = L >= 3
+    n_in = dim // part
+    groups = sch.n_groups(R, part, slots)
+    ev = sch.CountingEvaluator()
+    q = [sch.SymCt(L)] if tiled else [sch.SymCt(L) for _ in range(n_in)]
+    lg = L - 1 if tiled else L
+    compress_mask = object() if lg >= 2 else None
+    sch.match(ev, q, [[None] * n_in for _ in range(groups)], [None] * n_in, compress_mask, dim, part,
+              expanded=not tiled)
+    return ev.counts(), lg, tiled, groups
+
+
+def library_counts(ops):
+    c = collections.Counter()
+    for o in ops:
+        if o["op"] == "mac":
+            c[("MAC", o["level"])] += o["queries"] * o["count"] * o["parts"]
+        else:
+            c[(o["op"], o["level"])] += o["count"]
+    return c
+
+
+CASES = [
+    ("toy", 512, 16, 4, 1), ("toy", 700, 16, 4, 3), ("toy", 5000, 16, 2, 2),
+    ("small4", 2500, 128, 16, 1), ("small4", 2500, 128, 16, 5), ("small4", 9000, 16, 4, 2),
+    ("small4", 100, 8, 1, 1), ("small4", 1, 16, 16, 1), ("small4", 3000, 32, 32, 2),
+    ("ring16", 6144, 128, 16, 1), ("ring16", 65536, 16, 4, 64), ("ring16", 1 << 20, 128, 16, 256),
+    ("ring16", 1 << 20, 128, 4, 7), ("ring16", 1 << 20, 128, 1, 1), ("ring16", 1024, 16, 4, 3),
+]
+
+
+@pytest.mark.parametrize("preset,R,dim,part,Q", CASES)
+def test_launches_are_the_oracle_schedule_operations(preset, R, dim, part, Q):
+    ops, _ = bm.bm_plan_estimate(preset, R, dim, part, Q)
+    lib = library_counts(ops)
+    orc, lg, tiled, groups = oracle_counts(preset, R, dim, part)
+    log_n, n_q = PRESET[preset]
+    L = n_q - 1
+    for (op, level), k in orc.items():
+        if op == "Rot":
+            assert lib[("rotate", level)] == Q * k, (op, level)
+        elif op == "Res":
+            assert lib[("rescale", level)] == Q * k, (op, level)
+        elif op == "MulP" and level == lg:
+            assert lib[("MAC", level)] == Q * k, (op, level)      # HE-C^3 products
+        elif op == "MulP":
+            assert lib[("mul_plain", level)] == Q * k, (op, level)   # Algorithm-1 and compression masks
+    # nothing the oracle does not do
+    kinds = {("rotate", "Rot"), ("rescale", "Res"), ("mul_plain", "MulP")}
+    for (op, level), k in lib.items():
+        if op in ("ntt", "intt", "copy", "MAC"):
+            continue
+        oname = dict(kinds)[op]
+        assert orc.get((oname, level), 0) * Q == k, (op, level)
+    # ingest and egress transforms: every limb of the queries, both limbs of every output
+    n_in = dim // part
+    n_out = -(-groups // part) if lg >= 2 else groups
+    assert lib[("ntt", 0)] == Q * (1 if tiled else n_in) * 2 * (L + 1)
+    assert lib[("intt", 0)] == Q * n_out * 2
+    # rotations and rescales run in batches of at most 128 ciphertexts
+    assert all(o["count"] <= 128 for o in ops if o["op"] in ("rotate", "rescale"))
+
+
+def test_plan_bytes_are_its_buffers():
+    # face gallery, one query: query ct (L = 3), Algorithm-1 outputs at 3 and 2, accumulators
+    # at 2 and 1 for 3 groups, one score ct, key-switch scratch for 8 ciphertexts at level 2
+    ops, nbytes = bm.bm_plan_estimate("ring16", 6144, 128, 16, 1)
+    limb = 8 << 16
+    buffers = (8 + 8 * 8 + 8 * 6 + 3 * 6 + 3 * 4 + 2) * limb
+    ks_scratch = 8 * (2 * 3 + 2 * 5 + 2 * 5 + 2 * 3) * limb
+    pointers = nbytes - buffers - ks_scratch
+    assert 0 < pointers < 4096, pointers
+
+
+def synthetic_costs(a, b):
+    """t = a[op] + b[op][level] * units at every sample point."""
+    units = np.array([[(8.0 if op == bm.OPS["mac"] else 1.0) * (1 << k) for k in range(bm.BM_COST_POINTS)]
+                      for op in range(bm.BM_OP_KINDS)])
+    t = np.zeros((bm.BM_OP_KINDS, bm.BM_MAX_Q, bm.BM_COST_POINTS))
+    for op in range(bm.BM_OP_KINDS):
+        for lv in range(bm.BM_MAX_Q):
+            t[op, lv] = a[op] + b[op][lv] * units[op]
+    return bm.bm_op_costs.from_arrays(units, t)
+
+
+@pytest.mark.parametrize("preset,R,dim,part,Q", CASES[:12])
+def test_prediction_is_the_sum_over_launches(preset, R, dim, part, Q):
+    rng = np.random.default_rng(R + dim + part + Q)
+    b = rng.uniform(0.5, 5.0, size=(bm.BM_OP_KINDS, bm.BM_MAX_Q))
+    # per-unit costs only: the prediction is units x cost summed over the oracle's operations
+    costs = synthetic_costs(np.zeros(bm.BM_OP_KINDS), b)
+    ms, _ = bm.bm_predict_match(preset, costs, R, dim, part, Q)
+    orc, lg, tiled, groups = oracle_counts(preset, R, dim, part)
+    L = PRESET[preset][1] - 1
+    n_in = dim // part
+    want = 0.0
+    for (op, level), k in orc.items():
+        if op == "Rot":
+            want += b[bm.OPS["rotate"], level] * Q * k
+        elif op == "Res":
+            want += b[bm.OPS["rescale"], level] * Q * k
+        elif op == "MulP" and level != lg:
+            want += b[bm.OPS["mul_plain"], level] * Q * k
+    # HE-C^3 products, per launch (one per chunk of groups): one gallery read serves 4
+    # queries, units = ceil(Q/4) x groups x parts, and below the first sample point
+    # (8 units) a launch costs the first point's time
+    ops, _ = bm.bm_plan_estimate(preset, R, dim, part, Q)
+    macs = [o for o in ops if o["op"] == "mac"]
+    assert sum(o["count"] for o in macs) == groups
+    for o in macs:
+        want += b[bm.OPS["mac"], lg] * max(8, math.ceil(Q / 4) * o["count"] * n_in)
+    n_out = -(-groups // part) if lg >= 2 else groups
+    want += b[bm.OPS["ntt"], 0] * Q * (1 if tiled else n_in) * 2 * (L + 1)
+    want += b[bm.OPS["intt"], 0] * Q * n_out * 2
+    if lg < 2:
+        want += b[bm.OPS["copy"], 0] * Q * groups
+    assert ms * 1000 == pytest.approx(want, rel=1e-9)
+    # a fixed cost per launch only: the prediction counts the launches
+    a = rng.uniform(1.0, 3.0, size=bm.BM_OP_KINDS)
+    costs = synthetic_costs(a, np.zeros((bm.BM_OP_KINDS, bm.BM_MAX_Q)))
+    ms, _ = bm.bm_predict_match(preset, costs, R, dim, part, Q)
+    assert ms * 1000 == pytest.approx(sum(a[bm.OPS[o["op"]]] for o in ops), rel=1e-9)
+
+
+def test_interpolation_between_and_beyond_the_sample_points():
+    # rotation launches of 1..128 ciphertexts (on and between the points) and a
+    # mask-product launch of 160 (beyond the last point)
+    units = np.array([[(1 << k) for k in range(bm.BM_COST_POINTS)]] * bm.BM_OP_KINDS, dtype=float)
+    t = np.zeros((bm.BM_OP_KINDS, bm.BM_MAX_Q, bm.BM_COST_POINTS))
+    t[bm.OPS["rotate"], 1] = [10, 11, 13, 17, 25, 41, 73, 137]     # 9 + units, but 10 at one
+    costs = bm.bm_op_costs.from_arrays(units, t)
+    # small4, one identity, dim = part = 2: 1 rotation at level 1 per query (a4), no compression
+    # rotation (groups = 1 < 2 to pair); Q queries -> one launch of Q ciphertexts
+    for Q, want in [(1, 10.0), (3, 12.0), (100, 109.0), (128, 137.0)]:
+        ops, _ = bm.bm_plan_estimate("small4", 1, 2, 2, Q)
+        rot = [o for o in ops if o["op"] == "rotate"]
+        assert [(o["level"], o["count"]) for o in rot] == [(1, Q)]
+        ms, _ = bm.bm_predict_match("small4", costs, 1, 2, 2, Q)
+        assert ms * 1000 == pytest.approx(want)
+    t = np.zeros((bm.BM_OP_KINDS, bm.BM_MAX_Q, bm.BM_COST_POINTS))
+    t[bm.OPS["mul_plain"], 3] = [5, 6, 8, 12, 20, 36, 68, 132]     # 4 + units: 164 at 160
+    costs = bm.bm_op_costs.from_arrays(units, t)
+    ops, _ = bm.bm_plan_estimate("small4", 1, 16, 1, 10)        # Algorithm 1: 10 queries x 16 masks
+    assert [(o["level"], o["count"]) for o in ops if o["op"] == "mul_plain"][0] == (3, 160)
+    ms, _ = bm.bm_predict_match("small4", costs, 1, 16, 1, 10)
+    compression = [o for o in ops if o["op"] == "mul_plain" and o["level"] != 3]
+    assert all(o["level"] == 1 for o in compression)                # costs 0 at level 1
+    assert ms * 1000 == pytest.approx(164.0)
+
+
+@pytest.mark.parametrize("R,dim,Q", [(6144, 128, 1), (1 << 20, 128, 256), (65536, 16, 64), (1024, 16, 1)])
+def test_choice_is_the_argmin_within_the_budget(R, dim, Q):
+    rng = np.random.default_rng(7)
+    b = rng.uniform(0.5, 5.0, size=(bm.BM_OP_KINDS, bm.BM_MAX_Q))
+    b[bm.OPS["rotate"]] *= 40                                      # rotations dominate, as on the GPU
+    costs = synthetic_costs(np.full(bm.BM_OP_KINDS, 2.0), b)
+    parts = [p for p in (1, 2, 4, 8, 16, 32, 64, 128) if p <= dim]
+    pred = {p: bm.bm_predict_match("ring16", costs, R, dim, p, Q) for p in parts}
+    best = min(parts, key=lambda p: (pred[p][0], -p))
+    part, ms = bm.bm_choose_part("ring16", costs, R, dim, Q)
+    assert part == best and ms == pytest.approx(pred[best][0])
+    # a budget just below the best plan's bytes excludes it
+    budget = pred[best][1] - 1
+    fits = [p for p in parts if pred[p][1] <= budget]
+    if fits:
+        part2, _ = bm.bm_choose_part("ring16", costs, R, dim, Q, budget)
+        assert part2 == min(fits, key=lambda p: (pred[p][0], -p))
+    with pytest.raises(bm.BlindMatchError) as e:
+        bm.bm_choose_part("ring16", costs, R, dim, Q, 1 << 20)
+    assert e.value.status == 7
+
+
+def test_large_gallery_trade_off_matches_sec4():
+    # Sec. 4: more parts cost more expansion rotations (N_in log N_in) and fewer
+    # per-group rotations (log s per group plus s - 1 per pack); at a million
+    # identities the minimum moves far below parts of 16
+    rot = {}
+    for part in (1, 2, 4, 8, 16, 32, 64, 128):
+        ops, _ = bm.bm_plan_estimate("ring16", 1 << 20, 128, part, 1)
+        rot[part] = sum(o["count"] for o in ops if o["op"] == "rotate")
+        n_in = 128 // part
+        groups = (1 << 20) * part // (1 << 15)
+        packs = -(-groups // part)
+        s_log = int(math.log2(part))
+        assert rot[part] == n_in * int(math.log2(n_in)) + groups * s_log + packs * (part - 1)
+    assert min(rot, key=rot.get) == 2 and rot[4] < rot[16] / 4
+
+
+def test_errors():
+    with pytest.raises(bm.BlindMatchError) as e:
+        bm.bm_plan_estimate("ring16", 100, 128, 3, 1)
+    assert e.value.status == 5
+    with pytest.raises(bm.BlindMatchError) as e:
+        bm.bm_plan_estimate("ring16", 100, 128, 16, 0)
+    assert e.value.status == 1
