@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--auto-part", action="store_true",
                     help="serving: each gallery's part size chosen by the cost model (bm_choose_part)")
     ap.add_argument("--no-tune", action="store_true", help="skip the rotation kernel-shape tuner")
+    ap.add_argument("--packing", default="real", choices=["real", "complex"],
+                    help="gallery slot packing (complex: a second identity in the imaginary parts)")
     return ap.parse_args()
 
 
@@ -251,10 +253,11 @@ def run_serving(args):
     wide = None if args.no_tune else bm.bm_autotune_keyswitch(ctx)
     costs = bm.bm_measure_op_costs(ctx) if args.auto_part else None
     keys, gals, parts = {}, [], {}
+    packing = bm.BM_PACK_COMPLEX if args.packing == "complex" else bm.BM_PACK_REAL
     for gi, (name, R, m, s) in enumerate(SERVE_GALLERIES):
         if costs is not None:
             # the cost model's part size for a typical batch of 16 queries
-            s, _ = bm.bm_choose_part("ring16", costs, R, m, 16, 32 << 30)
+            s, _ = bm.bm_choose_part("ring16", costs, R, m, 16, 32 << 30, packing)
         parts[name] = s
         if (m, s) not in keys:
             keys[(m, s)] = bm.bm_keygen(ctx, KEY_SEED, m, s)
@@ -262,7 +265,8 @@ def run_serving(args):
         qs, _ = wl.queries(feats, 64, seed=20 + gi)
         sk, pk, ek = keys[(m, s)]
         cts = [bm.bm_encrypt_query(ctx, pk, q, m, s, bm.BM_QUERY_TILED, ENC_SEED, i) for i, q in enumerate(qs)]
-        gals.append(dict(name=name, R=R, g=bm.bm_encode_gallery(ctx, feats, m, s), ek=ek, cts=cts))
+        gals.append(dict(name=name, R=R, g=bm.bm_encode_gallery_packed(ctx, feats, m, s, packing), ek=ek,
+                         cts=cts))
     # plain unbatched form: one query per bm_match, per gallery
     stream = torch.cuda.current_stream()
     single_ms = []
@@ -311,6 +315,7 @@ def run_serving(args):
                    "duration_s": args.duration, "galleries": [g[0] for g in SERVE_GALLERIES],
                    "executors": args.executors, "max_batch": args.max_batch, "parts": parts,
                    "part_choice": "cost model (bm_choose_part, 16 queries)" if costs is not None else "fixed",
+                   "packing": args.packing,
                    "ks_wide_batch": wide},
         "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]},
         "server": {k: st[k] for k in ("submitted", "completed", "failed", "batches", "mean_batch",
@@ -344,10 +349,11 @@ def run_sweep(args):
     ref0 = wl.plaintext_scores(feats, qs[0])
     mode = bm.BM_QUERY_TILED if W.query_mode == "tiled" else bm.BM_QUERY_EXPANDED
     parts = [p for p in (128, 64, 32, 16, 8, 4, 2, 1) if p <= W.dim]
-    pred = {p: bm.bm_predict_match(W.preset, costs, W.n_ids, W.dim, p, W.n_queries) for p in parts}
+    packing = bm.BM_PACK_COMPLEX if args.packing == "complex" else bm.BM_PACK_REAL
+    pred = {p: bm.bm_predict_match(W.preset, costs, W.n_ids, W.dim, p, W.n_queries, packing) for p in parts}
     fitting = [p for p in parts if pred[p][1] <= budget]
     best_pred = min(pred[p][0] for p in fitting)
-    model_part, _ = bm.bm_choose_part(W.preset, costs, W.n_ids, W.dim, W.n_queries, budget)
+    model_part, _ = bm.bm_choose_part(W.preset, costs, W.n_ids, W.dim, W.n_queries, budget, packing)
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -355,7 +361,7 @@ def run_sweep(args):
     sampler.start()
     rows = []
     for p in parts:
-        ops, nbytes = bm.bm_plan_estimate(W.preset, W.n_ids, W.dim, p, W.n_queries)
+        ops, nbytes = bm.bm_plan_estimate(W.preset, W.n_ids, W.dim, p, W.n_queries, packing)
         rot = {}
         for o in ops:
             if o["op"] == "rotate":
@@ -370,7 +376,7 @@ def run_sweep(args):
             rows.append(row)
             continue
         sk, pk, ek = bm.bm_keygen(ctx, KEY_SEED, W.dim, p)
-        gal = bm.bm_encode_gallery(ctx, feats, W.dim, p)
+        gal = bm.bm_encode_gallery_packed(ctx, feats, W.dim, p, packing)
         cts = [bm.bm_encrypt_query(ctx, pk, q, W.dim, p, mode, ENC_SEED, i) for i, q in enumerate(qs)]
         for ct in cts:
             bm.bm_ciphertext_upload(ct, sptr)
@@ -405,7 +411,8 @@ def run_sweep(args):
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": W.name, "mode": "part-sweep", "ring": "2^16" if W.preset == "ring16" else W.preset,
                    "n_ids": W.n_ids, "dim": W.dim, "queries_per_step": W.n_queries,
-                   "l2": "flushed between steps (512 MiB write)", "ks_wide_batch": wide},
+                   "l2": "flushed between steps (512 MiB write)", "packing": args.packing,
+                   "ks_wide_batch": wide},
         "sweep": rows, "model_part": model_part, "measured_best_part": best["part"],
         "model_part_measured_ms": next((r.get("measured_ms") for r in rows if r["part"] == model_part), None),
         "clocks": clocks,
@@ -434,9 +441,10 @@ def main():
     part = args.part or W.part
     ctx = bm.bm_context_create(W.preset, local)
     wide = None if args.no_tune else bm.bm_autotune_keyswitch(ctx)
+    packing = bm.BM_PACK_COMPLEX if args.packing == "complex" else bm.BM_PACK_REAL
     sk, pk, ek = bm.bm_keygen(ctx, KEY_SEED, W.dim, part)
     feats = wl.gallery(W.n_ids, W.dim)
-    gal = bm.bm_encode_gallery(ctx, feats, W.dim, part)
+    gal = bm.bm_encode_gallery_packed(ctx, feats, W.dim, part, packing)
     qs, _ = wl.queries(feats, W.n_queries)
     mode = bm.BM_QUERY_TILED if W.query_mode == "tiled" else bm.BM_QUERY_EXPANDED
     cts = [bm.bm_encrypt_query(ctx, pk, q, W.dim, part, mode, ENC_SEED, i) for i, q in enumerate(qs)]
@@ -540,7 +548,7 @@ def main():
                    "dim": W.dim, "part": part, "queries_per_step": W.n_queries,
                    "l2": "flushed between steps (512 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single",
-                   "ks_wide_batch": wide},
+                   "packing": args.packing, "ks_wide_batch": wide},
         "latency_ms": {"p50": percentile(step_ms, 50), "p99": percentile(step_ms, 99)},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -126,6 +126,18 @@ bm_status bm_public_key_export(const bm_public_key* pk, uint64_t* out, size_t ca
 bm_status bm_eval_keys_export(const bm_eval_keys* evk, int32_t rotation, uint64_t* out,
                               size_t capacity);
 
+/* Slot packing of a gallery.  Sec. 3.2 gives each identity of a group one window
+ * of `part` slots; CKKS slots are complex and the query is real, so a second
+ * identity can ride in the imaginary parts of the same window: every product,
+ * sum, rotation and mask of the match acts on both parts alike, and the score of
+ * identity u sits in the real part and that of identity G+u in the imaginary
+ * part of the same output slot.  Groups (and all per-group work) halve. */
+enum {
+    BM_PACK_REAL = 0,     /* G = (N/2)/part identities per group, real parts only */
+    BM_PACK_COMPLEX = 1   /* 2G per group: identity u (u < G) in the real parts of window u,
+                             identity G+u in its imaginary parts */
+};
+
 /* Sec. 3.2 (enrollment, with a plaintext gallery): feats is n_ids x dim row-major
  * float64, L2-normalised.  Identities are grouped G = (N/2)/part_size per group;
  * identity u of group g fills slots [u*part, u*part+part) of the group's plaintext
@@ -136,6 +148,10 @@ bm_status bm_eval_keys_export(const bm_eval_keys* evk, int32_t rotation, uint64_
  * is too short for any schedule (n_q < 2). */
 bm_status bm_encode_gallery(bm_context* ctx, const double* feats, uint64_t n_ids, uint32_t dim,
                             uint32_t part_size, bm_gallery** out);
+/* The same with a slot packing (BM_PACK_*); bm_encode_gallery is BM_PACK_REAL.
+ * BM_E_ARG for an unknown packing. */
+bm_status bm_encode_gallery_packed(bm_context* ctx, const double* feats, uint64_t n_ids, uint32_t dim,
+                                   uint32_t part_size, uint32_t packing, bm_gallery** out);
 /* Same gallery from coefficient-form plaintexts produced elsewhere:
  * pts [groups][dim/part][level+1][N], masks [dim/part][n_q][N] (tiled schedule; NULL
  * otherwise), cmask [level][N] (when compressing; NULL otherwise), where `level`
@@ -143,12 +159,19 @@ bm_status bm_encode_gallery(bm_context* ctx, const double* feats, uint64_t n_ids
 bm_status bm_gallery_import(bm_context* ctx, const uint64_t* pts, const uint64_t* masks,
                             const uint64_t* cmask, uint64_t n_ids, uint32_t dim,
                             uint32_t part_size, bm_gallery** out);
+bm_status bm_gallery_import_packed(bm_context* ctx, const uint64_t* pts, const uint64_t* masks,
+                                   const uint64_t* cmask, uint64_t n_ids, uint32_t dim,
+                                   uint32_t part_size, uint32_t packing, bm_gallery** out);
 /* Layout of a gallery for (n_ids, dim, part_size) under this context: number of
  * groups, level of the gallery plaintexts, tiled (1) or expanded (0) queries,
  * compressed (1) or per-group (0) outputs, output ciphertexts per query. */
 bm_status bm_gallery_layout(const bm_context* ctx, uint64_t n_ids, uint32_t dim,
                             uint32_t part_size, uint32_t* groups, uint32_t* level,
                             uint32_t* tiled, uint32_t* compressed, uint32_t* n_out);
+bm_status bm_gallery_layout_packed(const bm_context* ctx, uint64_t n_ids, uint32_t dim,
+                                   uint32_t part_size, uint32_t packing, uint32_t* groups,
+                                   uint32_t* level, uint32_t* tiled, uint32_t* compressed,
+                                   uint32_t* n_out);
 /* Coefficient-form copies of the resident plaintexts (layouts as in the import;
  * pass NULL to skip a part). */
 bm_status bm_gallery_export(const bm_gallery* g, uint64_t* pts, uint64_t* masks, uint64_t* cmask);
@@ -199,7 +222,8 @@ bm_status bm_result_export(const bm_result* r, uint32_t query_index, uint64_t* o
 void bm_result_destroy(bm_result* r);
 /* Sec. 3.3 Decryption: decrypts the score ciphertexts of one query with sk and maps
  * slots back to identities: scores[u] ~ <q, g_u> (the cosine similarity of unit
- * vectors).  rank1 = argmax (lowest id on ties), rank1_score its score; the caller
+ * vectors; with BM_PACK_COMPLEX galleries the real or imaginary part of the
+ * identity's slot).  rank1 = argmax (lowest id on ties), rank1_score its score; the caller
  * applies its own threshold to reject unenrolled users. */
 bm_status bm_decrypt_scores(bm_context* ctx, const bm_secret_key* sk, const bm_result* r,
                             uint32_t query_index, double* scores, uint64_t n_ids,
@@ -360,25 +384,27 @@ typedef struct bm_op_costs {
 } bm_op_costs;
 
 /* Host only (no device needed): the launches of the match of `n_queries`
- * queries against a gallery of n_ids identities in (dim, part_size) under
+ * queries against a gallery of n_ids identities in (dim, part_size, packing) under
  * `params` -- exactly the launches bm_match's plan makes, in order -- and the
  * device memory its plan holds.  Writes up to ops_cap launches to ops (ops may
  * be NULL) and the total to *n_ops; *plan_bytes gets the plan's bytes.
  * BM_E_PARAM / BM_E_DIM / BM_E_LEVEL as for bm_context_create / bm_gallery_layout. */
 bm_status bm_plan_estimate(const bm_params* params, uint64_t n_ids, uint32_t dim, uint32_t part_size,
-                           uint32_t n_queries, bm_op_launch* ops, size_t ops_cap, size_t* n_ops,
-                           uint64_t* plan_bytes);
+                           uint32_t packing, uint32_t n_queries, bm_op_launch* ops, size_t ops_cap,
+                           size_t* n_ops, uint64_t* plan_bytes);
 
 /* Host only: the predicted device time (ms) of that match: the sum over its
  * launches of the time `costs` gives each launch. */
 bm_status bm_predict_match(const bm_params* params, const bm_op_costs* costs, uint64_t n_ids, uint32_t dim,
-                           uint32_t part_size, uint32_t n_queries, double* ms, uint64_t* plan_bytes);
+                           uint32_t part_size, uint32_t packing, uint32_t n_queries, double* ms,
+                           uint64_t* plan_bytes);
 
 /* Host only: the part size (N_in = dim / part) of smallest predicted time among
  * the powers of two 1..dim whose plan fits in `hbm_budget` bytes (0 = no limit);
  * ties go to the larger part (fewer keys).  BM_E_HBM_BUDGET if none fits. */
 bm_status bm_choose_part(const bm_params* params, const bm_op_costs* costs, uint64_t n_ids, uint32_t dim,
-                         uint32_t n_queries, uint64_t hbm_budget, uint32_t* part_size, double* ms);
+                         uint32_t packing, uint32_t n_queries, uint64_t hbm_budget, uint32_t* part_size,
+                         double* ms);
 
 /* Times every op kind on this context's device at BM_COST_POINTS sizes per
  * level (1, 2, 4, ..., 128 ciphertexts or limbs; MAC: 4 queries x 8 parts x

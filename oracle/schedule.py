@@ -67,6 +67,25 @@ def gallery_slots(feats, g, i, s, slots):
     return z
 
 
+def gallery_slots_complex(feats, g, i, s, slots):
+    """Complex slot packing: group g holds 2G identities; identity u < G of the
+    group fills the real parts of slots [u*s, u*s+s), identity G+u the imaginary
+    parts of the same slots (the slots of CKKS are complex; the query is real, so
+    each part of every product, sum and rotation carries its own identity)."""
+    G = slots // s
+    R = len(feats)
+    z = [0j] * slots
+    for u in range(2 * G):
+        idx = g * 2 * G + u
+        if idx >= R:
+            break
+        w = u % G
+        for t in range(s):
+            x = float(feats[idx][i * s + t])
+            z[w * s + t] += 1j * x if u >= G else x
+    return z
+
+
 def alg1_mask_slots(m, s, i, slots):
     """mask_i[k] = 1 iff floor((k mod m)/s) = i."""
     return [1.0 if (k % m) // s == i else 0.0 for k in range(slots)]
@@ -77,18 +96,20 @@ def compression_mask_slots(s, slots):
     return [1.0 if k % s == 0 else 0.0 for k in range(slots)]
 
 
-def n_groups(R, s, slots):
-    return -(-R // (slots // s))
+def n_groups(R, s, slots, complex_pack=False):
+    return -(-R // ((2 if complex_pack else 1) * (slots // s)))
 
 
-def identity_slot(idx, s, slots, packed):
-    """(output ciphertext, slot) holding the score of identity idx."""
+def identity_slot(idx, s, slots, packed, complex_pack=False):
+    """(output ciphertext, slot, imaginary part?) holding the score of identity idx."""
     G = slots // s
-    g, u = divmod(idx, G)
+    per = 2 * G if complex_pack else G
+    g, w = divmod(idx, per)
+    u, im = w % G, w >= G
     if packed:
         p, r = divmod(g, s)
-        return p, u * s + r
-    return g, u * s
+        return p, u * s + r, im
+    return g, u * s, im
 
 
 # ---------------------------------------------------------------------------

@@ -26,6 +26,8 @@ _PP = ctypes.POINTER(ctypes.c_void_p)
 
 BM_QUERY_TILED = 0
 BM_QUERY_EXPANDED = 1
+BM_PACK_REAL = 0
+BM_PACK_COMPLEX = 1
 PRESETS = {"toy": 0, "ring16": 1, "small4": 2}
 STATUS = ["BM_OK", "BM_E_ARG", "BM_E_PARAM", "BM_E_LEVEL", "BM_E_KEY_MISSING", "BM_E_DIM", "BM_E_OOM",
           "BM_E_HBM_BUDGET", "BM_E_CUDA", "BM_E_TIMEOUT", "BM_E_CANCELLED", "BM_E_FORMAT"]
@@ -88,6 +90,9 @@ _SIGS = {
     "bm_encode_gallery": (ctypes.c_int, [_vp, _DP, _u64, _u32, _u32, _PP]),
     "bm_gallery_import": (ctypes.c_int, [_vp, _U64P, _U64P, _U64P, _u64, _u32, _u32, _PP]),
     "bm_gallery_layout": (ctypes.c_int, [_vp, _u64, _u32, _u32, _U32P, _U32P, _U32P, _U32P, _U32P]),
+    "bm_gallery_layout_packed": (ctypes.c_int, [_vp, _u64, _u32, _u32, _u32, _U32P, _U32P, _U32P, _U32P, _U32P]),
+    "bm_encode_gallery_packed": (ctypes.c_int, [_vp, _DP, _u64, _u32, _u32, _u32, _PP]),
+    "bm_gallery_import_packed": (ctypes.c_int, [_vp, _U64P, _U64P, _U64P, _u64, _u32, _u32, _u32, _PP]),
     "bm_gallery_export": (ctypes.c_int, [_vp, _U64P, _U64P, _U64P]),
     "bm_gallery_destroy": (None, [_vp]),
     "bm_encrypt_query": (ctypes.c_int, [_vp, _vp, _DP, _u32, _u32, _u32, _u64, _u64, _PP]),
@@ -114,13 +119,13 @@ _SIGS = {
     "bm_server_wait": (ctypes.c_int, [_vp, _u64, _u32, _PP]),
     "bm_server_cancel": (ctypes.c_int, [_vp, _u64]),
     "bm_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(bm_server_stats_t)]),
-    "bm_plan_estimate": (ctypes.c_int, [ctypes.POINTER(bm_params), _u64, _u32, _u32, _u32,
+    "bm_plan_estimate": (ctypes.c_int, [ctypes.POINTER(bm_params), _u64, _u32, _u32, _u32, _u32,
                                         ctypes.POINTER(bm_op_launch), ctypes.c_size_t,
                                         ctypes.POINTER(ctypes.c_size_t), _U64P]),
     "bm_predict_match": (ctypes.c_int, [ctypes.POINTER(bm_params), ctypes.POINTER(bm_op_costs), _u64, _u32, _u32,
-                                        _u32, _DP, _U64P]),
+                                        _u32, _u32, _DP, _U64P]),
     "bm_choose_part": (ctypes.c_int, [ctypes.POINTER(bm_params), ctypes.POINTER(bm_op_costs), _u64, _u32, _u32,
-                                      _u64, _U32P, _DP]),
+                                      _u32, _u64, _U32P, _DP]),
     "bm_measure_op_costs": (ctypes.c_int, [_vp, ctypes.POINTER(bm_op_costs)]),
     "bm_autotune_keyswitch": (ctypes.c_int, [_vp, _U32P, ctypes.c_size_t]),
     "bm_set_ks_wide_batch": (ctypes.c_int, [_vp, _u32, _u32]),
@@ -267,28 +272,43 @@ def bm_gallery_layout(ctx, n_ids, dim, part):
     return dict(zip(["groups", "level", "tiled", "compressed", "n_out"], [x.value for x in v]))
 
 
+def bm_gallery_layout_packed(ctx, n_ids, dim, part, packing):
+    v = [_u32() for _ in range(5)]
+    _check(_L.bm_gallery_layout_packed(ctx.ptr, n_ids, dim, part, packing, *[ctypes.byref(x) for x in v]))
+    return dict(zip(["groups", "level", "tiled", "compressed", "n_out"], [x.value for x in v]))
+
+
 def bm_encode_gallery(ctx, feats, dim, part):
+    return bm_encode_gallery_packed(ctx, feats, dim, part, BM_PACK_REAL)
+
+
+def bm_encode_gallery_packed(ctx, feats, dim, part, packing):
     f = np.ascontiguousarray(feats, dtype=np.float64)
     h = _out()
-    _check(_L.bm_encode_gallery(ctx.ptr, f.ctypes.data_as(_DP), f.shape[0], dim, part, ctypes.byref(h)))
+    _check(_L.bm_encode_gallery_packed(ctx.ptr, f.ctypes.data_as(_DP), f.shape[0], dim, part, packing,
+                                       ctypes.byref(h)))
     g = Gallery(h.value, ctx)
-    g.n_ids, g.dim, g.part = f.shape[0], dim, part
+    g.n_ids, g.dim, g.part, g.packing = f.shape[0], dim, part, packing
     return g
 
 
 def bm_gallery_import(ctx, pts, masks, cmask, n_ids, dim, part):
+    return bm_gallery_import_packed(ctx, pts, masks, cmask, n_ids, dim, part, BM_PACK_REAL)
+
+
+def bm_gallery_import_packed(ctx, pts, masks, cmask, n_ids, dim, part, packing):
     arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.uint64) for a in (pts, masks, cmask)]
     ptrs = [None if a is None else _u64p(a) for a in arrs]
     h = _out()
-    _check(_L.bm_gallery_import(ctx.ptr, *ptrs, n_ids, dim, part, ctypes.byref(h)))
+    _check(_L.bm_gallery_import_packed(ctx.ptr, *ptrs, n_ids, dim, part, packing, ctypes.byref(h)))
     g = Gallery(h.value, ctx)
-    g.n_ids, g.dim, g.part = n_ids, dim, part
+    g.n_ids, g.dim, g.part, g.packing = n_ids, dim, part, packing
     return g
 
 
 def bm_gallery_export(g):
     ctx = g.owner
-    lo = bm_gallery_layout(ctx, g.n_ids, g.dim, g.part)
+    lo = bm_gallery_layout_packed(ctx, g.n_ids, g.dim, g.part, g.packing)
     n_in, lvl = g.dim // g.part, lo["level"]
     pts = np.zeros((lo["groups"], n_in, lvl + 1, ctx.n), dtype=np.uint64)
     masks = np.zeros((n_in, ctx.n_q, ctx.n), dtype=np.uint64) if lo["tiled"] else None
@@ -447,34 +467,35 @@ def _params(p):
     return bm_params_preset(p) if isinstance(p, (str, int)) else p
 
 
-def bm_plan_estimate(params, n_ids, dim, part, n_queries):
+def bm_plan_estimate(params, n_ids, dim, part, n_queries, packing=BM_PACK_REAL):
     """(launches as a list of dicts, plan bytes) of the match; host only."""
     p = _params(params)
     n = ctypes.c_size_t()
-    _check(_L.bm_plan_estimate(ctypes.byref(p), n_ids, dim, part, n_queries, None, 0, ctypes.byref(n), None))
+    _check(_L.bm_plan_estimate(ctypes.byref(p), n_ids, dim, part, packing, n_queries, None, 0, ctypes.byref(n),
+                               None))
     arr = (bm_op_launch * max(n.value, 1))()
     nbytes = _u64()
-    _check(_L.bm_plan_estimate(ctypes.byref(p), n_ids, dim, part, n_queries, arr, n.value, ctypes.byref(n),
-                               ctypes.byref(nbytes)))
+    _check(_L.bm_plan_estimate(ctypes.byref(p), n_ids, dim, part, packing, n_queries, arr, n.value,
+                               ctypes.byref(n), ctypes.byref(nbytes)))
     ops = [dict(op=OP_NAMES[a.op], level=a.level, count=a.count, queries=a.queries, parts=a.parts)
            for a in arr[:n.value]]
     return ops, nbytes.value
 
 
-def bm_predict_match(params, costs, n_ids, dim, part, n_queries):
+def bm_predict_match(params, costs, n_ids, dim, part, n_queries, packing=BM_PACK_REAL):
     """(predicted ms, plan bytes); host only."""
     p = _params(params)
     ms, nbytes = _dbl(), _u64()
-    _check(_L.bm_predict_match(ctypes.byref(p), ctypes.byref(costs), n_ids, dim, part, n_queries,
+    _check(_L.bm_predict_match(ctypes.byref(p), ctypes.byref(costs), n_ids, dim, part, packing, n_queries,
                                ctypes.byref(ms), ctypes.byref(nbytes)))
     return ms.value, nbytes.value
 
 
-def bm_choose_part(params, costs, n_ids, dim, n_queries, hbm_budget=0):
+def bm_choose_part(params, costs, n_ids, dim, n_queries, hbm_budget=0, packing=BM_PACK_REAL):
     """(part size, predicted ms); host only."""
     p = _params(params)
     part, ms = _u32(), _dbl()
-    _check(_L.bm_choose_part(ctypes.byref(p), ctypes.byref(costs), n_ids, dim, n_queries, hbm_budget,
+    _check(_L.bm_choose_part(ctypes.byref(p), ctypes.byref(costs), n_ids, dim, packing, n_queries, hbm_budget,
                              ctypes.byref(part), ctypes.byref(ms)))
     return part.value, ms.value
 

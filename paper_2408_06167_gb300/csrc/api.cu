@@ -53,16 +53,20 @@ static uint32_t ilog2(uint64_t x) {
 
 struct Layout {
     uint32_t n_in, G, groups, level, n_out;
+    uint32_t per_group;                     // identities per group: G, or 2G with complex packing
     bool tiled, compress;
 };
 
-static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uint32_t part, Layout& lo) {
+static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uint32_t part, Layout& lo,
+                             uint32_t packing = BM_PACK_REAL) {
     if (!is_pow2(dim) || !is_pow2(part) || part > dim || dim > c.slots)
         return fail(BM_E_DIM, "dim and part size must be powers of two with part <= dim <= N/2");
+    if (packing != BM_PACK_REAL && packing != BM_PACK_COMPLEX) return fail(BM_E_ARG, "unknown slot packing");
     if (c.L < 1) return fail(BM_E_LEVEL, "the modulus chain needs at least one rescale prime");
     lo.n_in = dim / part;
     lo.G = c.slots / part;
-    lo.groups = (uint32_t)((n_ids + lo.G - 1) / lo.G);
+    lo.per_group = packing == BM_PACK_COMPLEX ? 2 * lo.G : lo.G;
+    lo.groups = (uint32_t)((n_ids + lo.per_group - 1) / lo.per_group);
     lo.tiled = c.L >= 3;                    // Algorithm 1 (1 level) + HE-C^3 (1) + compression (1)
     lo.level = lo.tiled ? c.L - 1 : c.L;    // level of the query parts entering HE-C^3
     lo.compress = lo.level >= 2;            // a level left after HE-C^3 for the mask
@@ -485,11 +489,12 @@ bm::Result::~Result() {
 namespace bm {
 
 static bm_status gallery_alloc(Context& c, const Layout& lo, uint64_t n_ids, uint32_t dim, uint32_t part,
-                               bm_gallery** out, bm_gallery*& gh) {
+                               uint32_t packing, bm_gallery*& gh) {
     gh = new bm_gallery();
     gh->ref.attach(&c);
     Gallery& g = gh->g;
     g.ctx = &c;
+    g.packing = packing;
     g.id = c.next_id++;
     g.n_ids = n_ids;
     g.dim = dim;
@@ -508,7 +513,6 @@ static bm_status gallery_alloc(Context& c, const Layout& lo, uint64_t n_ids, uin
         gh = nullptr;
         return fail(BM_E_OOM, "gallery allocation failed");
     }
-    (void)out;
     return BM_OK;
 }
 
@@ -528,9 +532,16 @@ extern "C" {
 
 bm_status bm_gallery_layout(const bm_context* ctx, uint64_t n_ids, uint32_t dim, uint32_t part_size, uint32_t* groups,
                             uint32_t* level, uint32_t* tiled, uint32_t* compressed, uint32_t* n_out) {
+    return bm_gallery_layout_packed(ctx, n_ids, dim, part_size, BM_PACK_REAL, groups, level, tiled, compressed,
+                                    n_out);
+}
+
+bm_status bm_gallery_layout_packed(const bm_context* ctx, uint64_t n_ids, uint32_t dim, uint32_t part_size,
+                                   uint32_t packing, uint32_t* groups, uint32_t* level, uint32_t* tiled,
+                                   uint32_t* compressed, uint32_t* n_out) {
     if (!ctx) return fail(BM_E_ARG, "null context");
     Layout lo;
-    BM_TRY(make_layout(ctx->c, n_ids, dim, part_size, lo));
+    BM_TRY(make_layout(ctx->c, n_ids, dim, part_size, lo, packing));
     if (groups) *groups = lo.groups;
     if (level) *level = lo.level;
     if (tiled) *tiled = lo.tiled;
@@ -541,13 +552,18 @@ bm_status bm_gallery_layout(const bm_context* ctx, uint64_t n_ids, uint32_t dim,
 
 bm_status bm_encode_gallery(bm_context* ctxh, const double* feats, uint64_t n_ids, uint32_t dim, uint32_t part_size,
                             bm_gallery** out) {
+    return bm_encode_gallery_packed(ctxh, feats, n_ids, dim, part_size, BM_PACK_REAL, out);
+}
+
+bm_status bm_encode_gallery_packed(bm_context* ctxh, const double* feats, uint64_t n_ids, uint32_t dim,
+                                   uint32_t part_size, uint32_t packing, bm_gallery** out) {
     if (!ctxh || !feats || !out || n_ids == 0) return fail(BM_E_ARG, "null argument or empty gallery");
     Context& c = ctxh->c;
     Layout lo;
-    BM_TRY(make_layout(c, n_ids, dim, part_size, lo));
+    BM_TRY(make_layout(c, n_ids, dim, part_size, lo, packing));
     BM_CUDA_TRY(cudaSetDevice(c.device));
     bm_gallery* gh;
-    BM_TRY(gallery_alloc(c, lo, n_ids, dim, part_size, out, gh));
+    BM_TRY(gallery_alloc(c, lo, n_ids, dim, part_size, packing, gh));
     Gallery& g = gh->g;
     const size_t n = c.n, S = c.slots;
     // plaintexts in chunks: encode on the host cores in parallel, then one upload,
@@ -566,13 +582,21 @@ bm_status bm_encode_gallery(bm_context* ctxh, const double* feats, uint64_t n_id
 #pragma omp parallel for schedule(dynamic)
         for (int pp = 0; pp < (int)np; pp++) {
             const uint32_t grp = (p0 + pp) / lo.n_in, i = (p0 + pp) % lo.n_in;
-            std::vector<double> zz(S, 0.0);
-            for (uint32_t u = 0; u < lo.G; u++) {
-                const uint64_t id = (uint64_t)grp * lo.G + u;
+            // identity u of the group in window u (real parts); with complex packing
+            // identity G + u in the imaginary parts of the same window
+            std::vector<std::complex<double>> zz(S, 0.0);
+            for (uint32_t u = 0; u < lo.per_group; u++) {
+                const uint64_t id = (uint64_t)grp * lo.per_group + u;
                 if (id >= n_ids) break;
-                for (uint32_t t = 0; t < part_size; t++) zz[u * part_size + t] = feats[id * dim + i * part_size + t];
+                const uint32_t w = u % lo.G;
+                const bool im = u >= lo.G;
+                for (uint32_t t = 0; t < part_size; t++) {
+                    const double x = feats[id * dim + i * part_size + t];
+                    if (im) zz[w * part_size + t].imag(x);
+                    else zz[w * part_size + t].real(x);
+                }
             }
-            encode_real(c, zz.data(), pscale, coeffs.data() + (size_t)pp * n);
+            encode_complex(c, zz.data(), pscale, coeffs.data() + (size_t)pp * n);
         }
         uint64_t* dst = g.d_pts + (size_t)p0 * (lo.level + 1) * n;
         LimbBatch out = packed(c, dst, np, lo.level + 1);
@@ -607,14 +631,20 @@ bm_status bm_encode_gallery(bm_context* ctxh, const double* feats, uint64_t n_id
 
 bm_status bm_gallery_import(bm_context* ctxh, const uint64_t* pts, const uint64_t* masks, const uint64_t* cmask,
                             uint64_t n_ids, uint32_t dim, uint32_t part_size, bm_gallery** out) {
+    return bm_gallery_import_packed(ctxh, pts, masks, cmask, n_ids, dim, part_size, BM_PACK_REAL, out);
+}
+
+bm_status bm_gallery_import_packed(bm_context* ctxh, const uint64_t* pts, const uint64_t* masks,
+                                   const uint64_t* cmask, uint64_t n_ids, uint32_t dim, uint32_t part_size,
+                                   uint32_t packing, bm_gallery** out) {
     if (!ctxh || !pts || !out || n_ids == 0) return fail(BM_E_ARG, "null argument or empty gallery");
     Context& c = ctxh->c;
     Layout lo;
-    BM_TRY(make_layout(c, n_ids, dim, part_size, lo));
+    BM_TRY(make_layout(c, n_ids, dim, part_size, lo, packing));
     if ((lo.tiled && !masks) || (lo.compress && !cmask)) return fail(BM_E_ARG, "masks required by this layout");
     BM_CUDA_TRY(cudaSetDevice(c.device));
     bm_gallery* gh;
-    BM_TRY(gallery_alloc(c, lo, n_ids, dim, part_size, out, gh));
+    BM_TRY(gallery_alloc(c, lo, n_ids, dim, part_size, packing, gh));
     Gallery& g = gh->g;
     cudaStream_t s = c.stream;
     const size_t n = c.n;
@@ -1036,17 +1066,17 @@ static size_t plan_shape(const Context& c, const SchedView& g, uint32_t n_out, u
 
 size_t plan_estimate_bytes(const Context& c, const Gallery& g, uint32_t Q) {
     Layout lo;
-    if (make_layout(c, g.n_ids, g.dim, g.part, lo) != BM_OK) return 0;
+    if (make_layout(c, g.n_ids, g.dim, g.part, lo, g.packing) != BM_OK) return 0;
     return plan_shape(c, view_of(g), lo.n_out, Q, nullptr);
 }
 
-bm_status schedule_launches(const bm_params& p, uint64_t n_ids, uint32_t dim, uint32_t part, uint32_t Q,
-                            std::vector<bm_op_launch>* ops, size_t* bytes) {
+bm_status schedule_launches(const bm_params& p, uint64_t n_ids, uint32_t dim, uint32_t part, uint32_t packing,
+                            uint32_t Q, std::vector<bm_op_launch>* ops, size_t* bytes) {
     if (Q == 0 || n_ids == 0) return fail(BM_E_ARG, "empty gallery or batch");
     Context c;
     BM_TRY(context_shape(c, p));
     Layout lo;
-    BM_TRY(make_layout(c, n_ids, dim, part, lo));
+    BM_TRY(make_layout(c, n_ids, dim, part, lo, packing));
     const size_t b = plan_shape(c, view_of(lo, part), lo.n_out, Q, ops);
     if (bytes) *bytes = b;
     return BM_OK;
@@ -1056,7 +1086,7 @@ bm_status plan_build(Context& c, const Gallery& g, const EvalKeys& ek, uint32_t 
     auto* pl = new Plan();
     std::unique_ptr<Plan> guard(pl);
     Layout lo;
-    BM_TRY(make_layout(c, g.n_ids, g.dim, g.part, lo));
+    BM_TRY(make_layout(c, g.n_ids, g.dim, g.part, lo, g.packing));
     const SchedView v = view_of(g);
     pl->c = &c;
     pl->gid = g.id;
@@ -1133,12 +1163,12 @@ static Plan* find_plan(Context& c, uint64_t gid, uint64_t kid, uint32_t Q) {
 extern "C" {
 
 bm_status bm_plan_estimate(const bm_params* params, uint64_t n_ids, uint32_t dim, uint32_t part_size,
-                           uint32_t n_queries, bm_op_launch* ops, size_t ops_cap, size_t* n_ops,
-                           uint64_t* plan_bytes_out) {
+                           uint32_t packing, uint32_t n_queries, bm_op_launch* ops, size_t ops_cap,
+                           size_t* n_ops, uint64_t* plan_bytes_out) {
     if (!params) return fail(BM_E_ARG, "null parameters");
     std::vector<bm_op_launch> v;
     size_t bytes = 0;
-    BM_TRY(schedule_launches(*params, n_ids, dim, part_size, n_queries, &v, &bytes));
+    BM_TRY(schedule_launches(*params, n_ids, dim, part_size, packing, n_queries, &v, &bytes));
     if (ops) std::copy(v.begin(), v.begin() + std::min(ops_cap, v.size()), ops);
     if (n_ops) *n_ops = v.size();
     if (plan_bytes_out) *plan_bytes_out = bytes;
@@ -1158,7 +1188,7 @@ bm_status bm_match(bm_context* ctxh, const bm_eval_keys* evk, const bm_gallery* 
             return fail(BM_E_LEVEL, "query layout does not match the gallery's schedule");
     }
     Layout lo;
-    BM_TRY(make_layout(c, g.n_ids, g.dim, g.part, lo));
+    BM_TRY(make_layout(c, g.n_ids, g.dim, g.part, lo, g.packing));
     for (int32_t r : schedule_rotations(c, lo, g.part))
         if (!evk->k.keys.count(galois_of(c, r))) return fail(BM_E_KEY_MISSING, "missing rotation key");
     BM_CUDA_TRY(cudaSetDevice(c.device));
@@ -1182,6 +1212,7 @@ bm_status bm_match(bm_context* ctxh, const bm_eval_keys* evk, const bm_gallery* 
     res.dim = g.dim;
     res.part = g.part;
     res.packed = g.compress;
+    res.packing = g.packing;
     cudaError_t e = cudaMallocAsync((void**)&res.d_data, pl->result_words * 8, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(res.d_data, pl->result, pl->result_words * 8, cudaMemcpyDeviceToDevice, s);
@@ -1242,23 +1273,28 @@ bm_status bm_decrypt_scores(bm_context* ctxh, const bm_secret_key* sk, const bm_
     BM_CUDA_TRY(cudaStreamSynchronize(s));
     const uint64_t q0 = c.primes[0];
     const uint32_t part = res.part, G = c.slots / part;
-    std::vector<double> coef(n), slots(c.slots);
-    std::vector<std::vector<double>> dec(nout);
+    const bool cplx = res.packing == BM_PACK_COMPLEX;
+    const uint64_t per_group = cplx ? 2ull * G : G;
+    std::vector<double> coef(n);
+    std::vector<std::complex<double>> slots(c.slots);
+    std::vector<std::vector<std::complex<double>>> dec(nout);
     for (size_t o = 0; o < nout; o++) {
         for (size_t i = 0; i < n; i++) {
             const uint64_t v = h[o * 2 * n + i];
             coef[i] = v > q0 / 2 ? -(double)(q0 - v) : (double)v;
         }
-        decode_real(c, coef.data(), c.scale, slots.data());
+        decode_complex(c, coef.data(), c.scale, slots.data());
         dec[o] = slots;
     }
     int64_t best = -1;
     double best_score = -INFINITY;
     for (uint64_t id = 0; id < n_ids; id++) {
-        const uint64_t grp = id / G, u = id % G;
-        double v;
-        if (res.packed) v = dec[grp / part][u * part + grp % part];
-        else v = dec[grp][u * part];
+        // group, window and part (real / imaginary) of the identity; packed outputs
+        // hold group g at offset g mod part of pack g / part
+        const uint64_t grp = id / per_group, w = id % per_group, u = w % G;
+        const bool im = w >= G;
+        const std::complex<double> z = res.packed ? dec[grp / part][u * part + grp % part] : dec[grp][u * part];
+        const double v = im ? z.imag() : z.real();
         scores[id] = v;
         if (v > best_score) {
             best_score = v;

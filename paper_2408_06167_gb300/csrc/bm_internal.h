@@ -133,8 +133,8 @@ size_t plan_bytes(const Plan* p);
 // device bytes the plan of Q queries for this gallery will hold (host only)
 size_t plan_estimate_bytes(const Context& c, const Gallery& g, uint32_t Q);
 // host only: the launches and plan bytes of a match for (params, n_ids, dim, part, Q)
-bm_status schedule_launches(const bm_params& p, uint64_t n_ids, uint32_t dim, uint32_t part, uint32_t Q,
-                            std::vector<bm_op_launch>* ops, size_t* bytes);
+bm_status schedule_launches(const bm_params& p, uint64_t n_ids, uint32_t dim, uint32_t part, uint32_t packing,
+                            uint32_t Q, std::vector<bm_op_launch>* ops, size_t* bytes);
 uint32_t plan_queries(const Plan* p);
 uint32_t plan_outputs(const Plan* p);
 const uint64_t* plan_result(const Plan* p);
@@ -165,6 +165,7 @@ struct Gallery {
     uint32_t dim = 0, part = 0, n_in = 0, groups = 0, level = 0;  // level of the gallery pts
     bool tiled = true;                        // queries arrive tiled (Algorithm 1 on the server)
     bool compress = true;                     // outputs are masked and packed
+    uint32_t packing = BM_PACK_REAL;          // BM_PACK_COMPLEX: a second identity in the imaginary parts
     uint64_t* d_pts = nullptr;                // [groups][n_in][level+1][N] NTT + Montgomery
     uint64_t* d_masks = nullptr;              // [n_in][L+1][N] Algorithm-1 masks (tiled only)
     uint64_t* d_cmask = nullptr;              // [level][N] compression mask at level-1
@@ -185,6 +186,7 @@ struct Result {
     uint64_t n_ids = 0;
     uint32_t dim = 0, part = 0;
     bool packed = true;
+    uint32_t packing = BM_PACK_REAL;          // slot packing of the gallery the result came from
     uint64_t* d_data = nullptr;               // [n_queries][n_out][2][N] coefficient form, level 0
     ~Result();
 };
@@ -262,6 +264,9 @@ void encoder_tables(Context& ctx);
 void encode_real(const Context& ctx, const double* z, double scale, int64_t* out);
 // slots of integer coefficients / scale (real parts)
 void decode_real(const Context& ctx, const double* coeffs, double scale, double* z);
+// the same for complex slot values
+void encode_complex(const Context& ctx, const std::complex<double>* z, double scale, int64_t* out);
+void decode_complex(const Context& ctx, const double* coeffs, double scale, std::complex<double>* z);
 
 // ---- launch accounting (profile.cpp) ----
 // Every launcher brackets its kernel with a ProfScope: launches and algorithmic

@@ -9,7 +9,7 @@
 //    samplers on top of it: uniform residues (128 bits reduced mod q), discrete
 //    Gaussian by cumulative table on 63 bits with a sign bit, ZO(1/2) ternary,
 //    ternary of fixed Hamming weight by rejection of occupied positions.
-//  * CKKS canonical embedding (Sec. 2: batches of real values in the slots):
+//  * CKKS canonical embedding (Sec. 2: batches of real -- or complex -- values in the slots):
 //    slot j is the evaluation at zeta^(5^j), zeta = exp(i*pi/N).  Encoding maps
 //    the slots to the N odd powers of zeta and applies one length-N inverse DFT,
 //    computed by an iterative radix-2 FFT.
@@ -223,6 +223,30 @@ void encode_real(const Context& ctx, const double* z, double scale, int64_t* out
         const double x = (v[k] * std::conj(T.zeta[k])).real() / double(n) * scale;
         out[k] = (int64_t)(x >= 0 ? std::floor(x + 0.5) : -std::floor(-x + 0.5));
     }
+}
+
+void encode_complex(const Context& ctx, const std::complex<double>* z, double scale, int64_t* out) {
+    const uint32_t n = ctx.n;
+    const EncoderTables& T = ctx.enc;
+    std::vector<cplx> v(n);
+    for (uint32_t j = 0; j < ctx.slots; j++) {
+        v[T.pos[j]] = z[j];
+        v[T.cpos[j]] = std::conj(z[j]);   // the conjugate root takes the conjugate value: real coefficients
+    }
+    fft(T, v.data(), n, -1);
+    for (uint32_t k = 0; k < n; k++) {
+        const double x = (v[k] * std::conj(T.zeta[k])).real() / double(n) * scale;
+        out[k] = (int64_t)(x >= 0 ? std::floor(x + 0.5) : -std::floor(-x + 0.5));
+    }
+}
+
+void decode_complex(const Context& ctx, const double* coeffs, double scale, std::complex<double>* z) {
+    const uint32_t n = ctx.n;
+    const EncoderTables& T = ctx.enc;
+    std::vector<cplx> w(n);
+    for (uint32_t k = 0; k < n; k++) w[k] = T.zeta[k] * (coeffs[k] / scale);
+    fft(T, w.data(), n, +1);
+    for (uint32_t j = 0; j < ctx.slots; j++) z[j] = w[T.pos[j]];
 }
 
 void decode_real(const Context& ctx, const double* coeffs, double scale, double* z) {

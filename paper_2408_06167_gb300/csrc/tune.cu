@@ -118,11 +118,12 @@ using namespace bm;
 extern "C" {
 
 bm_status bm_predict_match(const bm_params* params, const bm_op_costs* costs, uint64_t n_ids, uint32_t dim,
-                           uint32_t part_size, uint32_t n_queries, double* ms, uint64_t* plan_bytes) {
+                           uint32_t part_size, uint32_t packing, uint32_t n_queries, double* ms,
+                           uint64_t* plan_bytes) {
     if (!params || !costs) return fail(BM_E_ARG, "null argument");
     std::vector<bm_op_launch> ops;
     size_t bytes = 0;
-    bm_status st = schedule_launches(*params, n_ids, dim, part_size, n_queries, &ops, &bytes);
+    bm_status st = schedule_launches(*params, n_ids, dim, part_size, packing, n_queries, &ops, &bytes);
     if (st != BM_OK) return st;
     double us = 0;
     for (const auto& l : ops) us += launch_us(*costs, l);
@@ -132,7 +133,8 @@ bm_status bm_predict_match(const bm_params* params, const bm_op_costs* costs, ui
 }
 
 bm_status bm_choose_part(const bm_params* params, const bm_op_costs* costs, uint64_t n_ids, uint32_t dim,
-                         uint32_t n_queries, uint64_t hbm_budget, uint32_t* part_size, double* ms) {
+                         uint32_t packing, uint32_t n_queries, uint64_t hbm_budget, uint32_t* part_size,
+                         double* ms) {
     if (!params || !costs || !part_size) return fail(BM_E_ARG, "null argument");
     if (!dim || (dim & (dim - 1))) return fail(BM_E_DIM, "dim must be a power of two");
     double best = 0;
@@ -140,7 +142,7 @@ bm_status bm_choose_part(const bm_params* params, const bm_op_costs* costs, uint
     for (uint32_t part = dim; part >= 1; part /= 2) {
         double t = 0;
         uint64_t bytes = 0;
-        bm_status st = bm_predict_match(params, costs, n_ids, dim, part, n_queries, &t, &bytes);
+        bm_status st = bm_predict_match(params, costs, n_ids, dim, part, packing, n_queries, &t, &bytes);
         if (st != BM_OK) return st;
         if (hbm_budget && bytes > hbm_budget) continue;
         if (!best_part || t < best) {

@@ -38,9 +38,10 @@ def schedule_rotations(ctx, m, s):
 class OracleMatch:
     """Keys, gallery plaintexts, query ciphertexts and match outputs from the oracle."""
 
-    def __init__(self, name, m, s, R, n_queries, feats=None, seed=KEY_SEED):
+    def __init__(self, name, m, s, R, n_queries, feats=None, seed=KEY_SEED, complex_pack=False):
         self.ctx = ctx = octx(name)
         self.m, self.s, self.R = m, s, R
+        self.complex_pack = complex_pack
         self.n_in = m // s
         self.tiled = ctx.L >= 3
         self.level = ctx.L - 1 if self.tiled else ctx.L
@@ -50,8 +51,9 @@ class OracleMatch:
         self.sk, self.pk, self.rks = ckks.keygen(ctx, seed, schedule_rotations(ctx, m, s))
         self.ev = ckks.Evaluator(ctx, self.rks)
         S, L = ctx.slots, ctx.L
-        self.groups = sch.n_groups(R, s, S)
-        self.gal = [[ctx.encode(sch.gallery_slots(self.feats, g, i, s, S), ctx.q[self.level], self.level)
+        self.groups = sch.n_groups(R, s, S, complex_pack)
+        slots_of = sch.gallery_slots_complex if complex_pack else sch.gallery_slots
+        self.gal = [[ctx.encode(slots_of(self.feats, g, i, s, S), ctx.q[self.level], self.level)
                      for i in range(self.n_in)] for g in range(self.groups)]
         self.masks = ([ctx.encode(sch.alg1_mask_slots(m, s, i, S), ctx.q[L], L) for i in range(self.n_in)]
                       if self.tiled else None)
@@ -91,6 +93,7 @@ class OracleMatch:
         dec = []
         for o in outs_array:
             ct = ckks.Ciphertext(o[0], o[1], 0, ctx.scale)
-            dec.append(ckks.decrypt_decode(ctx, ct, self.sk).real)
-        return np.array([dec[o][slot] for o, slot in (sch.identity_slot(i, self.s, S, packed)
-                                                      for i in range(self.R))])
+            dec.append(ckks.decrypt_decode(ctx, ct, self.sk))
+        return np.array([dec[o][slot].imag if im else dec[o][slot].real
+                         for o, slot, im in (sch.identity_slot(i, self.s, S, packed, self.complex_pack)
+                                             for i in range(self.R))])

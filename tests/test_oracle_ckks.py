@@ -100,7 +100,7 @@ def test_match_invariants_and_scores_small4(m, s, R):
     packs = sch.compress(ev, accs, mm, s)
     assert len(packs) == -(-ng // s) and packs[0].level == 0
     dec = [ckks.decrypt_decode(ctx, p, sk).real for p in packs]
-    got = np.array([dec[o][slot] for o, slot in (sch.identity_slot(i, s, S, True) for i in range(R))])
+    got = np.array([dec[o][slot] for o, slot, _ in (sch.identity_slot(i, s, S, True) for i in range(R))])
     assert np.abs(got - ref).max() < 1e-5
     top2 = np.sort(ref)[-2:]
     if top2[1] - top2[0] > 2e-5:
@@ -124,8 +124,37 @@ def test_linear_compression_and_per_part_rescale_agree_with_default():
     for kw in [dict(tree=False), dict(rescale_each_part=True)]:
         outs, packed = sch.match(ev, [ct], gal, masks, mm, m, s, **kw)
         dec = [ckks.decrypt_decode(ctx, p, sk).real for p in outs]
-        got = np.array([dec[o][slot] for o, slot in (sch.identity_slot(i, s, S, packed) for i in range(R))])
+        got = np.array([dec[o][slot] for o, slot, _ in (sch.identity_slot(i, s, S, packed) for i in range(R))])
         assert np.abs(got - ref).max() < 1e-5, kw
+
+
+@pytest.mark.parametrize("m,s,R", [(16, 4, 3000), (128, 16, 5000), (16, 16, 2100)])
+def test_complex_slot_packing_scores(m, s, R):
+    """Complex packing: identities u and G+u of a group share slot window u (real and
+    imaginary parts); every score is still the FP64 cosine within 1e-5, the real and
+    imaginary parts carry their own identities, and the groups halve."""
+    ctx, sk, pk, ev = _setup("small4", m, s, R)
+    S, L, n_in = ctx.slots, ctx.L, m // s
+    feats = wl.gallery(R, m)
+    q = wl.queries(feats, 1)[0][0]
+    ct = ckks.encrypt(ctx, pk, ctx.encode(sch.tiled_query_slots(q, S), ctx.scale, L), 4, 0)
+    masks = [ctx.encode(sch.alg1_mask_slots(m, s, i, S), ctx.q[L], L) for i in range(n_in)]
+    ng = sch.n_groups(R, s, S, complex_pack=True)
+    assert ng == -(-R // (2 * (S // s)))
+    gal = [[ctx.encode(sch.gallery_slots_complex(feats, g, i, s, S), ctx.q[L - 1], L - 1) for i in range(n_in)]
+           for g in range(ng)]
+    # the plaintext of group 0, part 0 evaluates to A + iB at the slot roots
+    z = ctx.decode(ctx.crt(gal[0][0].limbs, ctx.q[:L]), ctx.q[L - 1])
+    G = S // s
+    assert abs(z[0].real - feats[0][0]) < 1e-9 and abs(z[0].imag - feats[G][0]) < 1e-9
+    mm = ctx.encode(sch.compression_mask_slots(s, S), ctx.q[L - 2], L - 2)
+    outs, packed = sch.match(ev, [ct], gal, masks, mm, m, s)
+    dec = [ckks.decrypt_decode(ctx, p, sk) for p in outs]
+    got = np.array([dec[o][slot].imag if im else dec[o][slot].real
+                    for o, slot, im in (sch.identity_slot(i, s, S, packed, complex_pack=True) for i in range(R))])
+    ref = wl.plaintext_scores(feats, q)
+    assert np.abs(got - ref).max() < 1e-5
+    assert got.argmax() == ref.argmax() or np.sort(ref)[-1] - np.sort(ref)[-2] < 2e-5
 
 
 def test_toy_expanded_queries_match_plaintext_cosine():

@@ -215,3 +215,13 @@ def test_errors():
     with pytest.raises(bm.BlindMatchError) as e:
         bm.bm_plan_estimate("ring16", 100, 128, 16, 0)
     assert e.value.status == 1
+
+
+def test_model_counts_halve_with_complex_packing():
+    # Algorithm 1 is per query; HE-C^3 rotations and compression are per group and pack
+    ops_r, _ = bm.bm_plan_estimate("ring16", 1 << 20, 128, 16, 1)
+    ops_c, _ = bm.bm_plan_estimate("ring16", 1 << 20, 128, 16, 1, packing=bm.BM_PACK_COMPLEX)
+    def rot(ops, lv):
+        return sum(o["count"] for o in ops if o["op"] == "rotate" and o["level"] == lv)
+    assert rot(ops_c, 2) == rot(ops_r, 2) == 24
+    assert rot(ops_c, 1) == 256 * 4 + 16 * 15 and rot(ops_r, 1) == 512 * 4 + 32 * 15
