@@ -191,36 +191,37 @@ cudaError_t ntt_dispatch(const Context& c, const LimbBatch& b, bool inv, cudaStr
 }
 
 // ---------------------------------------------------------------------------
-// elementwise limb kernels
+// elementwise limb kernels: grid (limbs, chunks of a limb), the limb on x so
+// that any number of limbs fits (gridDim.y is limited to 65535)
 // ---------------------------------------------------------------------------
 
 // x * 2^-64 mod q (leave Montgomery form)
 __global__ void k_from_mont(LimbBatch lb, DevTables tab, uint32_t n) {
-    const uint32_t limb = blockIdx.y;
+    const uint32_t limb = blockIdx.x;
     const int pi = lb.prime(limb % lb.nl);
     uint64_t* a = limb_ptr(lb, limb, n);
     const uint64_t q = tab.q[pi], qn = tab.qneg[pi];
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x)
         a[i] = mont(a[i], 1, q, qn);
 }
 
 // x * 2^64 mod q (enter Montgomery form): mont(x, 2^128 mod q)
 __global__ void k_to_mont(LimbBatch lb, DevTables tab, uint32_t n) {
-    const uint32_t limb = blockIdx.y;
+    const uint32_t limb = blockIdx.x;
     const int pi = lb.prime(limb % lb.nl);
     uint64_t* a = limb_ptr(lb, limb, n);
     const uint64_t q = tab.q[pi], qn = tab.qneg[pi], f = tab.r2[pi];
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x)
         a[i] = mont(a[i], f, q, qn);
 }
 
 __global__ void k_lift_signed(const int64_t* v, LimbBatch lb, DevTables tab, uint32_t n) {
-    const uint32_t limb = blockIdx.y;
+    const uint32_t limb = blockIdx.x;
     const int pi = lb.prime(limb % lb.nl);
     uint64_t* a = limb_ptr(lb, limb, n);
     const uint64_t q = tab.q[pi];
     const int64_t* src = v + (size_t)(limb / lb.nl) * n;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x) {
         const int64_t x = src[i];
         const uint64_t m = x >= 0 ? (uint64_t)x : (uint64_t)(-x);
         const uint64_t r = reduce2(shoup_lazy(m, 1, tab.rsh[pi], q), q);
@@ -229,13 +230,13 @@ __global__ void k_lift_signed(const int64_t* v, LimbBatch lb, DevTables tab, uin
 }
 
 __global__ void k_pointwise(LimbBatch A, LimbBatch B, LimbBatch O, DevTables tab, uint32_t n, int op) {
-    const uint32_t limb = blockIdx.y;
+    const uint32_t limb = blockIdx.x;
     const int pi = A.prime(limb % A.nl);
     const uint64_t* a = limb_ptr(A, limb, n);
     const uint64_t* b = limb_ptr(B, limb, n);
     uint64_t* o = limb_ptr(O, limb, n);
     const uint64_t q = tab.q[pi], qn = tab.qneg[pi];
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x) {
         if (op == 0) o[i] = mont(a[i], b[i], q, qn);
         else if (op == 1) o[i] = addm(a[i], b[i], q);
         else o[i] = subm(a[i], b[i], q);
@@ -243,10 +244,10 @@ __global__ void k_pointwise(LimbBatch A, LimbBatch B, LimbBatch O, DevTables tab
 }
 
 __global__ void k_permute(LimbBatch I, LimbBatch O, uint32_t log_n, uint64_t galois) {
-    const uint32_t n = 1u << log_n, limb = blockIdx.y;
+    const uint32_t n = 1u << log_n, limb = blockIdx.x;
     const uint64_t* a = limb_ptr(I, limb, n);
     uint64_t* o = limb_ptr(O, limb, n);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x)
         o[i] = a[ntt_perm_src(i, log_n, galois)];
 }
 
@@ -255,12 +256,12 @@ struct ScalarK {
 };
 
 __global__ void k_scalar(LimbBatch I, LimbBatch O, ScalarK sk, DevTables tab, uint32_t n) {
-    const uint32_t limb = blockIdx.y, k = limb % I.nl;
+    const uint32_t limb = blockIdx.x, k = limb % I.nl;
     const int pi = I.prime(k);
     const uint64_t* a = limb_ptr(I, limb, n);
     uint64_t* o = limb_ptr(O, limb, n);
     const uint64_t q = tab.q[pi];
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x)
         o[i] = shoup(a[i], sk.w[k], sk.wsh[k], q);
 }
 
@@ -463,15 +464,17 @@ __global__ void k_rescale_combine(uint64_t* const* in, const uint64_t* Rl, uint6
 // products
 // ---------------------------------------------------------------------------
 
+// grid (B * 2 * (lvl + 1), chunks of a limb): one limb of one ciphertext per x index
+// (gridDim.x has room for any batch; gridDim.y is limited to 65535)
 __global__ void k_mul_plain(uint64_t* const* in, const uint64_t* const* pt, uint64_t* const* out,
                             uint32_t lvl, DevTables tab, uint32_t n) {
     const uint32_t l1 = lvl + 1;
-    const uint32_t y = blockIdx.y, b = y / (2 * l1), c = (y / l1) % 2, j = y % l1;
+    const uint32_t y = blockIdx.x, b = y / (2 * l1), c = (y / l1) % 2, j = y % l1;
     const uint64_t q = tab.q[j], qn = tab.qneg[j];
     const uint64_t* s = in[b] + ((size_t)c * l1 + j) * n;
     const uint64_t* m = pt[b] + (size_t)j * n;
     uint64_t* o = out[b] + ((size_t)c * l1 + j) * n;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x)
         o[i] = mont(s[i], m[i], q, qn);
 }
 
@@ -594,7 +597,7 @@ cudaError_t ntt_inverse(const Context& c, const LimbBatch& b, cudaStream_t s) { 
 cudaError_t to_montgomery(const Context& c, const LimbBatch& b, bool inverse, cudaStream_t s) {
     const uint32_t limbs = b.n_polys * b.nl;
     if (!limbs) return cudaSuccess;
-    const dim3 g(c.n / kThreads / 4, limbs);
+    const dim3 g(limbs, c.n / kThreads / 4);
     ProfScope ps(BM_KERNEL_OTHER, s, 16.0 * c.n * limbs);
     if (inverse) k_from_mont<<<g, kThreads, 0, s>>>(b, c.tab, c.n);
     else k_to_mont<<<g, kThreads, 0, s>>>(b, c.tab, c.n);
@@ -604,21 +607,21 @@ cudaError_t to_montgomery(const Context& c, const LimbBatch& b, bool inverse, cu
 cudaError_t lift_signed(const Context& c, const int64_t* d_v, const LimbBatch& out, cudaStream_t s) {
     const uint32_t limbs = out.n_polys * out.nl;
     ProfScope ps(BM_KERNEL_OTHER, s, 8.0 * c.n * (limbs + 1));
-    k_lift_signed<<<dim3(c.n / kThreads / 4, limbs), kThreads, 0, s>>>(d_v, out, c.tab, c.n);
+    k_lift_signed<<<dim3(limbs, c.n / kThreads / 4), kThreads, 0, s>>>(d_v, out, c.tab, c.n);
     return cudaGetLastError();
 }
 
 cudaError_t pointwise_mul(const Context& c, const LimbBatch& a, const LimbBatch& b, const LimbBatch& out,
                           cudaStream_t s) {
     ProfScope ps(BM_KERNEL_OTHER, s, 24.0 * c.n * a.n_polys * a.nl);
-    k_pointwise<<<dim3(c.n / kThreads / 4, a.n_polys * a.nl), kThreads, 0, s>>>(a, b, out, c.tab, c.n, 0);
+    k_pointwise<<<dim3(a.n_polys * a.nl, c.n / kThreads / 4), kThreads, 0, s>>>(a, b, out, c.tab, c.n, 0);
     return cudaGetLastError();
 }
 
 cudaError_t pointwise_addsub(const Context& c, const LimbBatch& a, const LimbBatch& b, const LimbBatch& out,
                              bool sub, cudaStream_t s) {
     ProfScope ps(BM_KERNEL_OTHER, s, 24.0 * c.n * a.n_polys * a.nl);
-    k_pointwise<<<dim3(c.n / kThreads / 4, a.n_polys * a.nl), kThreads, 0, s>>>(a, b, out, c.tab, c.n,
+    k_pointwise<<<dim3(a.n_polys * a.nl, c.n / kThreads / 4), kThreads, 0, s>>>(a, b, out, c.tab, c.n,
                                                                                  sub ? 2 : 1);
     return cudaGetLastError();
 }
@@ -626,7 +629,7 @@ cudaError_t pointwise_addsub(const Context& c, const LimbBatch& a, const LimbBat
 cudaError_t permute_ntt(const Context& c, const LimbBatch& in, const LimbBatch& out, uint64_t galois,
                         cudaStream_t s) {
     ProfScope ps(BM_KERNEL_OTHER, s, 16.0 * c.n * in.n_polys * in.nl);
-    k_permute<<<dim3(c.n / kThreads / 4, in.n_polys * in.nl), kThreads, 0, s>>>(in, out, c.log_n, galois);
+    k_permute<<<dim3(in.n_polys * in.nl, c.n / kThreads / 4), kThreads, 0, s>>>(in, out, c.log_n, galois);
     return cudaGetLastError();
 }
 
@@ -639,7 +642,7 @@ cudaError_t scalar_mul(const Context& c, const LimbBatch& in, const uint64_t* cs
         sk.wsh[k] = h_shoup_companion(sk.w[k], q);
     }
     ProfScope ps(BM_KERNEL_OTHER, s, 16.0 * c.n * in.n_polys * in.nl);
-    k_scalar<<<dim3(c.n / kThreads / 4, in.n_polys * in.nl), kThreads, 0, s>>>(in, out, sk, c.tab, c.n);
+    k_scalar<<<dim3(in.n_polys * in.nl, c.n / kThreads / 4), kThreads, 0, s>>>(in, out, sk, c.tab, c.n);
     return cudaGetLastError();
 }
 
@@ -816,7 +819,7 @@ cudaError_t mul_plain(const Context& c, uint32_t level, uint32_t B, uint64_t* co
                       const uint64_t* const* d_pt, uint64_t* const* d_out, cudaStream_t s) {
     if (B == 0) return cudaSuccess;
     ProfScope ps(BM_KERNEL_MUL_PLAIN, s, 8.0 * c.n * B * (level + 1) * 5);
-    k_mul_plain<<<dim3(c.n / kThreads / 4, B * 2 * (level + 1)), kThreads, 0, s>>>(d_in, d_pt, d_out, level, c.tab,
+    k_mul_plain<<<dim3(B * 2 * (level + 1), c.n / kThreads / 4), kThreads, 0, s>>>(d_in, d_pt, d_out, level, c.tab,
                                                                                    c.n);
     return cudaGetLastError();
 }
