@@ -78,8 +78,10 @@ enum {
 /* Query layouts of bm_encrypt_query (Sec. 3.3). */
 enum {
     BM_QUERY_TILED = 0,    /* one ciphertext, q tiled with period dim; the server runs Algorithm 1 */
-    BM_QUERY_EXPANDED = 1  /* dim/part ciphertexts, part i tiled with period part (client-side
+    BM_QUERY_EXPANDED = 1, /* dim/part ciphertexts, part i tiled with period part (client-side
                               expansion; required when the chain has fewer than 3 rescale primes) */
+    BM_QUERY_TEMPLATE = 2  /* one ciphertext, the vector in the first dim slots and zeros after:
+                              an enrollment template (Sec. 3.2) for bm_enroll_encrypted */
 };
 
 typedef struct bm_context bm_context;
@@ -111,6 +113,18 @@ bm_status bm_context_primes(const bm_context* ctx, uint64_t* primes_out, size_t 
  * BM_E_DIM for an invalid (dim, part_size). */
 bm_status bm_keygen(bm_context* ctx, uint64_t seed, uint32_t dim, uint32_t part_size,
                     bm_secret_key** sk, bm_public_key** pk, bm_eval_keys** evk);
+/* Key sets beyond the plaintext-gallery schedule. */
+enum {
+    BM_KEYS_ENCRYPTED_GALLERY = 1   /* also the relinearisation key (the key-switching key from s^2
+                                       to s, for Mul of two ciphertexts, Sec. 3.1) and the right
+                                       rotations by every power of two from part_size below N/2
+                                       that enrollment uses (Sec. 3.2) */
+};
+/* bm_keygen with extra key sets (BM_KEYS_* flags); flags = 0 is bm_keygen.  The
+ * relinearisation key is sampled like a rotation key with s^2 in place of
+ * sigma_k(s) (Philox tags 9 and 10, object = digit). */
+bm_status bm_keygen_ex(bm_context* ctx, uint64_t seed, uint32_t dim, uint32_t part_size, uint32_t flags,
+                       bm_secret_key** sk, bm_public_key** pk, bm_eval_keys** evk);
 void bm_secret_key_destroy(bm_secret_key* sk);
 void bm_public_key_destroy(bm_public_key* pk);
 void bm_eval_keys_destroy(bm_eval_keys* evk);
@@ -173,8 +187,31 @@ bm_status bm_gallery_layout_packed(const bm_context* ctx, uint64_t n_ids, uint32
                                    uint32_t* level, uint32_t* tiled, uint32_t* compressed,
                                    uint32_t* n_out);
 /* Coefficient-form copies of the resident plaintexts (layouts as in the import;
- * pass NULL to skip a part). */
+ * pass NULL to skip a part).  For an encrypted gallery `pts` receives its
+ * ciphertexts [groups][dim/part][2][level+1][N]. */
 bm_status bm_gallery_export(const bm_gallery* g, uint64_t* pts, uint64_t* masks, uint64_t* cmask);
+
+/* Encrypted gallery (Sec. 3.2 as the paper runs it: the server never sees a
+ * template in the clear).  templates[k] is identity k's BM_QUERY_TEMPLATE
+ * ciphertext at the top level.  Identity k goes to group g = k / G, window
+ * w = k mod G (G = (N/2)/part_size); for each part i the server multiplies the
+ * template by mask_i (ones at slots [i*part, (i+1)*part)), rescales, rotates the
+ * product right by (w - i)*part slots -- as one rotation per set bit of that
+ * amount mod N/2, lowest bit first -- and adds it into the group ciphertext
+ * C[g][i].  The gallery ciphertexts sit at level L-1 (the Algorithm-2 level) and
+ * HE-C^3 multiplies them with the expanded query (ciphertext x ciphertext), sums
+ * the tensor products over the parts and relinearises once per group.  Needs
+ * evk from bm_keygen_ex(..., BM_KEYS_ENCRYPTED_GALLERY) and a chain with at
+ * least three rescale primes (BM_E_LEVEL otherwise); real packing only. */
+bm_status bm_enroll_encrypted(bm_context* ctx, const bm_eval_keys* evk, bm_ciphertext* const* templates,
+                              uint64_t n_ids, uint32_t dim, uint32_t part_size, bm_gallery** out);
+/* The same gallery from ciphertexts made elsewhere: cts [groups][dim/part][2][L][N]
+ * (level L-1, scale 2^log_scale), masks and cmask as in bm_gallery_import. */
+bm_status bm_gallery_import_encrypted(bm_context* ctx, const uint64_t* cts, const uint64_t* masks,
+                                      const uint64_t* cmask, uint64_t n_ids, uint32_t dim,
+                                      uint32_t part_size, bm_gallery** out);
+/* 1 if the gallery holds ciphertexts, 0 if plaintexts; its packing. */
+bm_status bm_gallery_info(const bm_gallery* g, uint32_t* encrypted, uint32_t* packing);
 void bm_gallery_destroy(bm_gallery* g);
 
 /* Sec. 3.3: encrypts the L2-normalised query q[dim] under pk at the top level
@@ -187,6 +224,16 @@ bm_status bm_encrypt_query(bm_context* ctx, const bm_public_key* pk, const doubl
                            bm_ciphertext** out);
 /* Wraps n_cts coefficient-form ciphertexts [n_cts][2][level+1][N].  BM_E_FORMAT for
  * a level above L. */
+/* Batched encryption: vectors is n_vec x dim row-major; out[k] (n_vec handles)
+ * is vectors[k] encrypted as bm_encrypt_query(..., mode, seed, first_id + k)
+ * would encrypt it -- bit for bit: the noise is drawn from the same counter-based
+ * Philox words, on the GPU, and the encoding runs on the host cores in parallel.
+ * flags BM_ENC_KEEP_DEVICE also keeps a device copy of each ciphertext (as after
+ * bm_ciphertext_upload). */
+#define BM_ENC_KEEP_DEVICE 1u
+bm_status bm_encrypt_batch(bm_context* ctx, const bm_public_key* pk, const double* vectors, uint64_t n_vec,
+                           uint32_t dim, uint32_t part_size, uint32_t mode, uint64_t seed, uint64_t first_id,
+                           uint32_t flags, bm_ciphertext** out);
 bm_status bm_ciphertext_import(bm_context* ctx, const uint64_t* data, uint32_t n_cts,
                                uint32_t level, bm_ciphertext** out);
 bm_status bm_ciphertext_info(const bm_ciphertext* ct, uint32_t* n_cts, uint32_t* level);
@@ -358,7 +405,8 @@ enum {
     BM_OP_NTT = 4,        /* forward NTT of `count` limbs (query ingest) */
     BM_OP_INTT = 5,       /* inverse NTT of `count` limbs (score egress) */
     BM_OP_COPY = 6,       /* device copy of `count` level-0 ciphertexts (uncompressed outputs) */
-    BM_OP_KINDS = 7
+    BM_OP_MAC_CT = 7,     /* HE-C^3 tensor products with an encrypted gallery, as BM_OP_MAC */
+    BM_OP_KINDS = 8
 };
 
 /* One kernel launch (or launch group) of a match schedule. */
@@ -374,7 +422,7 @@ typedef struct bm_op_launch {
  * BM_COST_POINTS sizes: t_us[op][level][k] is the time (microseconds) of one
  * launch of units[op][k] units, units increasing.  Units are `count`, except for
  * BM_OP_MAC: ceil(queries / 4) * count * parts (one read of a gallery
- * plaintext serves a tile of four queries).  Between points the time is
+ * plaintext serves a tile of four queries; the same for BM_OP_MAC_CT).  Between points the time is
  * interpolated linearly, above the last point extrapolated from the last two,
  * below the first taken as the first.  NTT, INTT and COPY use level 0. */
 #define BM_COST_POINTS 8
@@ -382,6 +430,10 @@ typedef struct bm_op_costs {
     double units[BM_OP_KINDS][BM_COST_POINTS];
     double t_us[BM_OP_KINDS][BM_MAX_Q][BM_COST_POINTS];
 } bm_op_costs;
+
+/* Gallery kinds for the schedule model: a BM_PACK_* value, or'ed with
+ * BM_LAYOUT_ENCRYPTED for a gallery of ciphertexts (bm_enroll_encrypted). */
+#define BM_LAYOUT_ENCRYPTED 0x100u
 
 /* Host only (no device needed): the launches of the match of `n_queries`
  * queries against a gallery of n_ids identities in (dim, part_size, packing) under
@@ -411,7 +463,7 @@ bm_status bm_choose_part(const bm_params* params, const bm_op_costs* costs, uint
  * 1..128 groups), with seeded random residues as operands (the values do not
  * change the time).  Rotations use the kernel shape the context currently picks
  * for each batch size, so run bm_autotune_keyswitch first.  Takes a few seconds
- * and up to ~4 GB of device memory at ring 2^16.  Levels an op cannot take
+ * and up to ~9 GB of device memory at ring 2^16.  Levels an op cannot take
  * (rescale from level 0) stay 0. */
 bm_status bm_measure_op_costs(bm_context* ctx, bm_op_costs* out);
 

@@ -36,6 +36,8 @@ TAG_RK_E = 5
 TAG_ENC_V = 6
 TAG_ENC_E0 = 7
 TAG_ENC_E1 = 8
+TAG_RLK_A = 9
+TAG_RLK_E = 10
 
 _U64P = ctypes.POINTER(ctypes.c_uint64)
 _I64P = ctypes.POINTER(ctypes.c_int64)
@@ -446,6 +448,29 @@ def keygen_rotation(ctx, seed, sk, galois):
     return key
 
 
+def keygen_relin(ctx, seed, sk):
+    """Relinearisation key (the evaluation key of Mul, Sec. 3.1): the hybrid
+    key-switching key from s^2 to s -- the rotation-key construction with
+    sigma_k(s) replaced by s^2 (tags RLK_A / RLK_E, object = digit)."""
+    nb = ctx.L + 1 + ctx.alpha
+    data = _u64((ctx.dnum, 2, nb, ctx.n))
+    for d, dl in enumerate(ctx.digits):
+        e = sample_gauss(ctx, seed, TAG_RLK_E, d)
+        for gi in range(nb):
+            t = ctx.primes[gi]
+            s_t = sk.limb(t)
+            a = sample_uniform(ctx, seed, TAG_RLK_A, d, gi)
+            b = add_mod(neg_mod(ctx.mul(a, s_t, gi), t), signed_to_mod(e, t), t)
+            if gi in dl:
+                b = add_mod(b, scalar_mul(ctx.mul(s_t, s_t, gi), ctx.P % t, t), t)
+            data[d, 0, gi] = b
+            data[d, 1, gi] = a
+    key = RotationKey(1, data)
+    key.ntt_data = np.stack([np.stack([np.stack([ctx.ntt(data[d, c, gi], gi) for gi in range(nb)])
+                                       for c in range(2)]) for d in range(ctx.dnum)])
+    return key
+
+
 def keygen(ctx, seed, rotations):
     """sk, pk and the rotation keys for the given left-rotation amounts (negative = right)."""
     sk = sample_secret(ctx, seed)
@@ -491,12 +516,23 @@ def decrypt_decode(ctx, ct, sk):
 # evaluator: Add, Mul(P), Res, Rot (Sec. 2)
 # ---------------------------------------------------------------------------
 
+@dataclass
+class Ciphertext3:
+    """Tensor product (d0, d1, d2) of two ciphertexts: decrypts as d0 + d1*s + d2*s^2."""
+    d0: np.ndarray
+    d1: np.ndarray
+    d2: np.ndarray
+    level: int
+    scale: float
+
+
 class Evaluator:
     """Exact RNS-CKKS evaluator on coefficient-form ciphertexts."""
 
-    def __init__(self, ctx, rot_keys):
+    def __init__(self, ctx, rot_keys, relin_key=None):
         self.ctx = ctx
         self.keys = rot_keys
+        self.relin_key = relin_key
 
     def zero_like(self, ct, level=None):
         """Encryption of zero: the identity of add (Algorithm 2 starts from it)."""
@@ -517,6 +553,35 @@ class Evaluator:
         c0 = np.stack([self.ctx.mul(ct.c0[j], pt.limbs[j], j) for j in range(ct.level + 1)])
         c1 = np.stack([self.ctx.mul(ct.c1[j], pt.limbs[j], j) for j in range(ct.level + 1)])
         return Ciphertext(c0, c1, ct.level, ct.scale * pt.scale)
+
+    def tensor(self, a, b):
+        """(a0 + a1 s)(b0 + b1 s) = a0 b0 + (a0 b1 + a1 b0) s + a1 b1 s^2, per limb."""
+        assert a.level == b.level
+        m = self.ctx.mul
+        lv, q = a.level, self.ctx.q
+        d0 = np.stack([m(a.c0[j], b.c0[j], j) for j in range(lv + 1)])
+        d1 = np.stack([add_mod(m(a.c0[j], b.c1[j], j), m(a.c1[j], b.c0[j], j), q[j]) for j in range(lv + 1)])
+        d2 = np.stack([m(a.c1[j], b.c1[j], j) for j in range(lv + 1)])
+        return Ciphertext3(d0, d1, d2, lv, a.scale * b.scale)
+
+    def add3(self, x, y):
+        if x is None:
+            return y
+        q = self.ctx.q
+        f = lambda u, v: np.stack([add_mod(u[j], v[j], q[j]) for j in range(x.level + 1)])
+        return Ciphertext3(f(x.d0, y.d0), f(x.d1, y.d1), f(x.d2, y.d2), x.level, x.scale)
+
+    def relinearize(self, t):
+        """(d0, d1, d2) -> (d0 + KS(d2)_0, d1 + KS(d2)_1) with the key from s^2 to s."""
+        ctx, lv = self.ctx, t.level
+        k0, k1 = keyswitch(ctx, t.d2, lv, self.relin_key)
+        c0 = np.stack([add_mod(t.d0[j], k0[j], ctx.q[j]) for j in range(lv + 1)])
+        c1 = np.stack([add_mod(t.d1[j], k1[j], ctx.q[j]) for j in range(lv + 1)])
+        return Ciphertext(c0, c1, lv, t.scale)
+
+    def mul_cipher(self, a, b):
+        """Mul of two ciphertexts (Sec. 2): tensor product, then relinearisation."""
+        return self.relinearize(self.tensor(a, b))
 
     def rescale(self, ct):
         assert ct.level >= 1

@@ -86,6 +86,19 @@ def gallery_slots_complex(feats, g, i, s, slots):
     return z
 
 
+def template_slots(feat, slots):
+    """Enrollment ciphertext layout (Sec. 3.2): the vector in the first slots, zeros after."""
+    z = [0.0] * slots
+    for k, x in enumerate(feat):
+        z[k] = float(x)
+    return z
+
+
+def enroll_mask_slots(s, i, slots):
+    """Enrollment mask_i (Sec. 3.2): ones at the s slots starting at i*s."""
+    return [1.0 if i * s <= k < (i + 1) * s else 0.0 for k in range(slots)]
+
+
 def alg1_mask_slots(m, s, i, slots):
     """mask_i[k] = 1 iff floor((k mod m)/s) = i."""
     return [1.0 if (k % m) // s == i else 0.0 for k in range(slots)]
@@ -128,10 +141,53 @@ def expand_query(ev, ct, masks, m, s):
     return out
 
 
-def hec3(ev, cu, cs, s, rescale_each_part=False, encrypted_gallery=False):
+def enroll(ev, templates, emasks, s, slots):
+    """Sec. 3.2, server side: the encrypted template of identity idx (group g,
+    window w) is multiplied by each mask_i (part i), rescaled, rotated right by
+    (w - i)*s slots so that part i lands in window w, and added into the group
+    ciphertext C[g][i].  The printed shift (Index - i + 1)*m/N_in is read with
+    0-based indices.  A right rotation by t is applied as rotations by the powers
+    of two of t's binary digits, lowest first (keys for powers of two only).
+    Returns C[g][i] for every group that holds an identity."""
+    G = slots // s
+    n_in = len(emasks)
+    groups = -(-len(templates) // G)
+    out = [[None] * n_in for _ in range(groups)]
+    for idx, ct in enumerate(templates):
+        g, w = divmod(idx, G)
+        for i in range(n_in):
+            x = ev.rescale(ev.mul_plain(ct, emasks[i]))
+            t, b = ((w - i) * s) % slots, 0
+            while t:
+                if t & 1:
+                    x = ev.rotate(x, -(1 << b))
+                t >>= 1
+                b += 1
+            out[g][i] = ev.add(out[g][i], x)
+    return out
+
+
+def enroll_rotations(s, slots):
+    """Right rotations enrollment uses: every power of two from s below the slot count."""
+    return [-(1 << b) for b in range(log2i(s), log2i(slots))]
+
+
+def hec3(ev, cu, cs, s, rescale_each_part=False, encrypted_gallery=False, lazy_relin=True):
     """Algorithm 2 for one group: sum_i Mul(C_u,i, C_s,i), then log2(s) rotate-and-add steps.
 
-    Slot u*s of the result holds <q, g_u> for every identity u of the group."""
+    Slot u*s of the result holds <q, g_u> for every identity u of the group.
+    With an encrypted gallery the products are ciphertext x ciphertext; by
+    default the tensor products are summed and relinearised once (same
+    message, one key switch instead of N_in); lazy_relin=False relinearises
+    every product."""
+    if encrypted_gallery and lazy_relin and not rescale_each_part:
+        acc3 = None
+        for i in range(len(cu)):
+            acc3 = ev.add3(acc3, ev.tensor(cu[i], cs[i]))
+        acc = ev.rescale(ev.relinearize(acc3))
+        for t in range(1, log2i(s) + 1):
+            acc = ev.add(ev.rotate(acc, 1 << (t - 1)), acc)
+        return acc
     mul = ev.mul_cipher if encrypted_gallery else ev.mul_plain
     if rescale_each_part:
         acc = ev.zero_like(cu[0], level=cu[0].level - 1)
@@ -174,14 +230,14 @@ def compress(ev, accs, mask_m, s, tree=True, final_rescale=True):
 
 
 def match(ev, query_cts, gallery_pts, masks, mask_m, m, s, expanded=False,
-          rescale_each_part=False, tree=True):
+          rescale_each_part=False, tree=True, encrypted_gallery=False):
     """Full server-side match for one query.
 
     query_cts: [ct] (tiled, run through Algorithm 1) or the N_in client-expanded cts.
     gallery_pts[g][i]: plaintext of group g, part i.
     Returns (outputs, packed): the score ciphertexts and whether they are packed."""
     cu = query_cts if expanded else expand_query(ev, query_cts[0], masks, m, s)
-    accs = [hec3(ev, cu, gallery_pts[g], s, rescale_each_part) for g in range(len(gallery_pts))]
+    accs = [hec3(ev, cu, gallery_pts[g], s, rescale_each_part, encrypted_gallery) for g in range(len(gallery_pts))]
     if accs[0].level >= 1 and mask_m is not None:
         return compress(ev, accs, mask_m, s, tree=tree), True
     return accs, False
@@ -216,6 +272,19 @@ class CountingEvaluator:
     def mul_cipher(self, a, b):
         self._rec("MulC", a.level)
         return SymCt(a.level)
+
+    def tensor(self, a, b):
+        self._rec("Tensor", a.level)
+        return SymCt(a.level)
+
+    def add3(self, x, y):
+        if x is not None:
+            self._rec("Add", x.level)
+        return y
+
+    def relinearize(self, t):
+        self._rec("Relin", t.level)
+        return SymCt(t.level)
 
     def rescale(self, ct):
         self._rec("Res", ct.level)

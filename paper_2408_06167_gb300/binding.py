@@ -26,8 +26,12 @@ _PP = ctypes.POINTER(ctypes.c_void_p)
 
 BM_QUERY_TILED = 0
 BM_QUERY_EXPANDED = 1
+BM_QUERY_TEMPLATE = 2
 BM_PACK_REAL = 0
 BM_PACK_COMPLEX = 1
+BM_LAYOUT_ENCRYPTED = 0x100
+BM_KEYS_ENCRYPTED_GALLERY = 1
+BM_ENC_KEEP_DEVICE = 1
 PRESETS = {"toy": 0, "ring16": 1, "small4": 2}
 STATUS = ["BM_OK", "BM_E_ARG", "BM_E_PARAM", "BM_E_LEVEL", "BM_E_KEY_MISSING", "BM_E_DIM", "BM_E_OOM",
           "BM_E_HBM_BUDGET", "BM_E_CUDA", "BM_E_TIMEOUT", "BM_E_CANCELLED", "BM_E_FORMAT"]
@@ -44,9 +48,9 @@ class bm_params(ctypes.Structure):
                 ("dnum", _u32), ("log_scale", _u32), ("secret_hw", _u32), ("sigma", _dbl)]
 
 
-OPS = {"rotate": 0, "rescale": 1, "mul_plain": 2, "mac": 3, "ntt": 4, "intt": 5, "copy": 6}
+OPS = {"rotate": 0, "rescale": 1, "mul_plain": 2, "mac": 3, "ntt": 4, "intt": 5, "copy": 6, "mac_ct": 7}
 OP_NAMES = {v: k for k, v in OPS.items()}
-BM_OP_KINDS = 7
+BM_OP_KINDS = 8
 BM_MAX_Q = 6
 BM_COST_POINTS = 8
 
@@ -80,6 +84,11 @@ _SIGS = {
     "bm_context_destroy": (None, [_vp]),
     "bm_context_primes": (ctypes.c_int, [_vp, _U64P, ctypes.c_size_t]),
     "bm_keygen": (ctypes.c_int, [_vp, _u64, _u32, _u32, _PP, _PP, _PP]),
+    "bm_keygen_ex": (ctypes.c_int, [_vp, _u64, _u32, _u32, _u32, _PP, _PP, _PP]),
+    "bm_enroll_encrypted": (ctypes.c_int, [_vp, _vp, _PP, _u64, _u32, _u32, _PP]),
+    "bm_encrypt_batch": (ctypes.c_int, [_vp, _vp, _DP, _u64, _u32, _u32, _u32, _u64, _u64, _u32, _PP]),
+    "bm_gallery_import_encrypted": (ctypes.c_int, [_vp, _U64P, _U64P, _U64P, _u64, _u32, _u32, _PP]),
+    "bm_gallery_info": (ctypes.c_int, [_vp, _U32P, _U32P]),
     "bm_secret_key_destroy": (None, [_vp]),
     "bm_public_key_destroy": (None, [_vp]),
     "bm_eval_keys_destroy": (None, [_vp]),
@@ -232,8 +241,12 @@ def bm_context_primes(ctx):
 
 
 def bm_keygen(ctx, seed, dim, part):
+    return bm_keygen_ex(ctx, seed, dim, part, 0)
+
+
+def bm_keygen_ex(ctx, seed, dim, part, flags):
     sk, pk, ek = _out(), _out(), _out()
-    _check(_L.bm_keygen(ctx.ptr, seed, dim, part, ctypes.byref(sk), ctypes.byref(pk), ctypes.byref(ek)))
+    _check(_L.bm_keygen_ex(ctx.ptr, seed, dim, part, flags, ctypes.byref(sk), ctypes.byref(pk), ctypes.byref(ek)))
     return SecretKey(sk.value, ctx), PublicKey(pk.value, ctx), EvalKeys(ek.value, ctx)
 
 
@@ -306,11 +319,48 @@ def bm_gallery_import_packed(ctx, pts, masks, cmask, n_ids, dim, part, packing):
     return g
 
 
+def bm_encrypt_batch(ctx, pk, vectors, dim, part, mode, seed, first_id=0, flags=0):
+    """Ciphertext handles of every row of `vectors` (as bm_encrypt_query with query ids first_id + k)."""
+    v = np.ascontiguousarray(vectors, dtype=np.float64)
+    n = v.shape[0]
+    arr = (ctypes.c_void_p * n)()
+    _check(_L.bm_encrypt_batch(ctx.ptr, pk.ptr, v.ctypes.data_as(_DP), n, dim, part, mode, seed, first_id, flags,
+                               arr))
+    return [Ciphertext(arr[k], ctx) for k in range(n)]
+
+
+def bm_enroll_encrypted(ctx, evk, templates, dim, part):
+    arr = (ctypes.c_void_p * len(templates))(*[t.ptr for t in templates])
+    h = _out()
+    _check(_L.bm_enroll_encrypted(ctx.ptr, evk.ptr, arr, len(templates), dim, part, ctypes.byref(h)))
+    g = Gallery(h.value, ctx)
+    g.n_ids, g.dim, g.part, g.packing, g.encrypted = len(templates), dim, part, BM_PACK_REAL, True
+    return g
+
+
+def bm_gallery_import_encrypted(ctx, cts, masks, cmask, n_ids, dim, part):
+    arrs = [np.ascontiguousarray(a, dtype=np.uint64) for a in (cts, masks, cmask)]
+    h = _out()
+    _check(_L.bm_gallery_import_encrypted(ctx.ptr, *[_u64p(a) for a in arrs], n_ids, dim, part, ctypes.byref(h)))
+    g = Gallery(h.value, ctx)
+    g.n_ids, g.dim, g.part, g.packing, g.encrypted = n_ids, dim, part, BM_PACK_REAL, True
+    return g
+
+
+def bm_gallery_info(g):
+    """(encrypted, packing)."""
+    e, p = _u32(), _u32()
+    _check(_L.bm_gallery_info(g.ptr, ctypes.byref(e), ctypes.byref(p)))
+    return bool(e.value), p.value
+
+
 def bm_gallery_export(g):
     ctx = g.owner
-    lo = bm_gallery_layout_packed(ctx, g.n_ids, g.dim, g.part, g.packing)
+    enc = getattr(g, "encrypted", False)
+    lo = bm_gallery_layout_packed(ctx, g.n_ids, g.dim, g.part, g.packing | (BM_LAYOUT_ENCRYPTED if enc else 0))
     n_in, lvl = g.dim // g.part, lo["level"]
-    pts = np.zeros((lo["groups"], n_in, lvl + 1, ctx.n), dtype=np.uint64)
+    shape = (lo["groups"], n_in, 2, lvl + 1, ctx.n) if enc else (lo["groups"], n_in, lvl + 1, ctx.n)
+    pts = np.zeros(shape, dtype=np.uint64)
     masks = np.zeros((n_in, ctx.n_q, ctx.n), dtype=np.uint64) if lo["tiled"] else None
     cmask = np.zeros((lvl, ctx.n), dtype=np.uint64) if lo["compressed"] else None
     _check(_L.bm_gallery_export(g.ptr, _u64p(pts), None if masks is None else _u64p(masks),

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libblindmatch.so")
-SOURCES = ["api.cu", "kernels.cu", "ks_fused.cu", "server.cu", "host.cpp", "profile.cpp", "noalloc.cu", "tune.cu"]
+SOURCES = ["api.cu", "kernels.cu", "ks_fused.cu", "server.cu", "host.cpp", "profile.cpp", "noalloc.cu", "tune.cu", "encrypt.cu"]
 HEADERS = ["bm_internal.h", "bm_math.cuh", "ntt_reg.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")

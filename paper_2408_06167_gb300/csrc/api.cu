@@ -55,14 +55,30 @@ struct Layout {
     uint32_t n_in, G, groups, level, n_out;
     uint32_t per_group;                     // identities per group: G, or 2G with complex packing
     bool tiled, compress;
+    bool encrypted;                         // gallery of ciphertexts (HE-C^3 products ct x ct)
 };
 
+// Scale of the score ciphertexts: 2^log_scale with a plaintext gallery (every
+// plaintext scale is the prime its rescale drops); Delta^2 / q_level with an
+// encrypted one (one ct x ct product, one rescale by the gallery level's prime).
+double result_scale(const Context& c, const Gallery& g) {
+    return g.encrypted ? c.scale * c.scale / (double)c.primes[g.level] : c.scale;
+}
+
+static uint32_t gallery_kind(const Gallery& g) { return g.packing | (g.encrypted ? BM_LAYOUT_ENCRYPTED : 0u); }
+
+// `kind`: a BM_PACK_* value, or'ed with BM_LAYOUT_ENCRYPTED for a gallery of ciphertexts
 static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uint32_t part, Layout& lo,
-                             uint32_t packing = BM_PACK_REAL) {
+                             uint32_t kind = BM_PACK_REAL) {
+    const uint32_t packing = kind & ~BM_LAYOUT_ENCRYPTED;
+    lo.encrypted = (kind & BM_LAYOUT_ENCRYPTED) != 0;
     if (!is_pow2(dim) || !is_pow2(part) || part > dim || dim > c.slots)
         return fail(BM_E_DIM, "dim and part size must be powers of two with part <= dim <= N/2");
     if (packing != BM_PACK_REAL && packing != BM_PACK_COMPLEX) return fail(BM_E_ARG, "unknown slot packing");
+    if (lo.encrypted && packing != BM_PACK_REAL) return fail(BM_E_ARG, "encrypted galleries use real packing");
     if (c.L < 1) return fail(BM_E_LEVEL, "the modulus chain needs at least one rescale prime");
+    if (lo.encrypted && c.L < 3)
+        return fail(BM_E_LEVEL, "an encrypted gallery needs three rescale primes (enrollment, HE-C^3, compression)");
     lo.n_in = dim / part;
     lo.G = c.slots / part;
     lo.per_group = packing == BM_PACK_COMPLEX ? 2 * lo.G : lo.G;
@@ -289,7 +305,13 @@ bm_status bm_context_primes(const bm_context* ctx, uint64_t* primes_out, size_t 
 
 bm_status bm_keygen(bm_context* ctxh, uint64_t seed, uint32_t dim, uint32_t part_size, bm_secret_key** sk_out,
                     bm_public_key** pk_out, bm_eval_keys** evk_out) {
+    return bm_keygen_ex(ctxh, seed, dim, part_size, 0, sk_out, pk_out, evk_out);
+}
+
+bm_status bm_keygen_ex(bm_context* ctxh, uint64_t seed, uint32_t dim, uint32_t part_size, uint32_t flags,
+                       bm_secret_key** sk_out, bm_public_key** pk_out, bm_eval_keys** evk_out) {
     if (!ctxh || !sk_out || !pk_out || !evk_out) return fail(BM_E_ARG, "null argument");
+    if (flags & ~(uint32_t)BM_KEYS_ENCRYPTED_GALLERY) return fail(BM_E_ARG, "unknown key-set flags");
     Context& c = ctxh->c;
     Layout lo;
     BM_TRY(make_layout(c, 1, dim, part_size, lo));
@@ -346,28 +368,24 @@ bm_status bm_keygen(bm_context* ctxh, uint64_t seed, uint32_t dim, uint32_t part
     DevBuf srot, prod;
     srot.alloc(nb * n);
     prod.alloc(nb * n);
-    for (int32_t rot : schedule_rotations(c, lo, part_size)) {
-        const uint64_t k = galois_of(c, rot);
-        if (evh->k.keys.count(k)) continue;
+    // one key-switching key from the NTT-form polynomial t (every limb of Q_L u P) to s:
+    // per digit d, b_d = e_d - a_d*s + P*[limb in digit d]*t, a_d uniform (Philox objects obj0 + d)
+    auto switch_key = [&](const uint64_t* t, uint64_t tag_a, uint64_t tag_e, uint64_t obj0, uint64_t*& out) -> bool {
         DevBuf key;
-        if (key.alloc((size_t)nd * 2 * nb * n) != cudaSuccess) {
-            delete skh; delete pkh; delete evh;
-            return fail(BM_E_OOM, "rotation key allocation failed");
-        }
-        permute_ntt(c, packed(c, s_plain.p, 1, nb), packed(c, srot.p, 1, nb), k, s);
+        if (key.alloc((size_t)nd * 2 * nb * n) != cudaSuccess) return false;
         for (uint32_t d = 0; d < nd; d++) {
-            const uint64_t obj = k * 16 + d;
+            const uint64_t obj = obj0 + d;
             uint64_t* kb = key.p + ((size_t)d * 2 + 0) * nb * n;
             uint64_t* ka = key.p + ((size_t)d * 2 + 1) * nb * n;
-            for (uint32_t j = 0; j < nb; j++) sample_uniform(seed, TAG_RK_A, obj, j, c.primes[j], host.data() + j * n, c.n);
-            sample_gauss(seed, TAG_RK_E, obj, c.params.sigma, e.data(), c.n);
+            for (uint32_t j = 0; j < nb; j++) sample_uniform(seed, tag_a, obj, j, c.primes[j], host.data() + j * n, c.n);
+            sample_gauss(seed, tag_e, obj, c.params.sigma, e.data(), c.n);
             cudaMemcpyAsync(ka, host.data(), nb * n * 8, cudaMemcpyHostToDevice, s);
             ntt_forward(c, packed(c, ka, 1, nb), s);
             upload_signed_ntt(c, e.data(), kb, nb, 0, s, false);
             pointwise_mul(c, packed(c, ka, 1, nb), packed(c, skh->k.d_ntt, 1, nb), packed(c, prod.p, 1, nb), s);
             pointwise_addsub(c, packed(c, kb, 1, nb), packed(c, prod.p, 1, nb), packed(c, kb, 1, nb), true, s);
             for (uint32_t j : c.digits[d]) {
-                LimbBatch one = limbs_of(srot.p + (size_t)j * n, 1, 1, n, j);
+                LimbBatch one = limbs_of(const_cast<uint64_t*>(t) + (size_t)j * n, 1, 1, n, j);
                 LimbBatch dst = limbs_of(prod.p + (size_t)j * n, 1, 1, n, j);
                 scalar_mul(c, one, &c.P_mod[j], dst, s);
                 LimbBatch kbj = limbs_of(kb + (size_t)j * n, 1, 1, n, j);
@@ -377,7 +395,31 @@ bm_status bm_keygen(bm_context* ctxh, uint64_t seed, uint32_t dim, uint32_t part
             cudaStreamSynchronize(s);
         }
         to_montgomery(c, packed(c, key.p, nd * 2, nb), false, s);
-        evh->k.keys[k] = key.release();
+        out = key.release();
+        return true;
+    };
+    std::vector<int32_t> rots = schedule_rotations(c, lo, part_size);
+    if (flags & BM_KEYS_ENCRYPTED_GALLERY)
+        for (uint32_t b = 0; (1u << b) < c.slots; b++)
+            if ((1u << b) >= part_size) rots.push_back(-(int32_t)(1u << b));   // enrollment shifts
+    for (int32_t rot : rots) {
+        const uint64_t k = galois_of(c, rot);
+        if (evh->k.keys.count(k)) continue;
+        permute_ntt(c, packed(c, s_plain.p, 1, nb), packed(c, srot.p, 1, nb), k, s);
+        uint64_t* key = nullptr;
+        if (!switch_key(srot.p, TAG_RK_A, TAG_RK_E, k * 16, key)) {
+            delete skh; delete pkh; delete evh;
+            return fail(BM_E_OOM, "rotation key allocation failed");
+        }
+        evh->k.keys[k] = key;
+    }
+    if (flags & BM_KEYS_ENCRYPTED_GALLERY) {
+        // relinearisation key: the target is s^2 (NTT domain: s times s, Montgomery times plain)
+        pointwise_mul(c, packed(c, s_plain.p, 1, nb), packed(c, skh->k.d_ntt, 1, nb), packed(c, srot.p, 1, nb), s);
+        if (!switch_key(srot.p, TAG_RLK_A, TAG_RLK_E, 0, evh->k.relin)) {
+            delete skh; delete pkh; delete evh;
+            return fail(BM_E_OOM, "relinearisation key allocation failed");
+        }
     }
     cudaError_t ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) {
@@ -466,6 +508,7 @@ bm_status bm_eval_keys_export(const bm_eval_keys* evk, int32_t rotation, uint64_
 bm::EvalKeys::~EvalKeys() {
     if (ctx) drop_plans(*ctx, id);
     for (auto& kv : keys) cudaFree(kv.second);
+    if (relin) cudaFree(relin);
 }
 bm::Gallery::~Gallery() {
     if (ctx) drop_plans(*ctx, id);
@@ -494,7 +537,8 @@ static bm_status gallery_alloc(Context& c, const Layout& lo, uint64_t n_ids, uin
     gh->ref.attach(&c);
     Gallery& g = gh->g;
     g.ctx = &c;
-    g.packing = packing;
+    g.packing = packing & ~BM_LAYOUT_ENCRYPTED;
+    g.encrypted = lo.encrypted;
     g.id = c.next_id++;
     g.n_ids = n_ids;
     g.dim = dim;
@@ -505,7 +549,8 @@ static bm_status gallery_alloc(Context& c, const Layout& lo, uint64_t n_ids, uin
     g.tiled = lo.tiled;
     g.compress = lo.compress;
     const size_t n = c.n;
-    cudaError_t e = cudaMalloc(&g.d_pts, (size_t)lo.groups * lo.n_in * (lo.level + 1) * n * 8);
+    const size_t polys = lo.encrypted ? 2 : 1;
+    cudaError_t e = cudaMalloc(&g.d_pts, (size_t)lo.groups * lo.n_in * polys * (lo.level + 1) * n * 8);
     if (e == cudaSuccess && lo.tiled) e = cudaMalloc(&g.d_masks, (size_t)lo.n_in * (c.L + 1) * n * 8);
     if (e == cudaSuccess && lo.compress) e = cudaMalloc(&g.d_cmask, (size_t)lo.level * n * 8);
     if (e != cudaSuccess) {
@@ -523,6 +568,25 @@ static bm_status encode_to_device(Context& c, const std::vector<double>& z, doub
     encode_real(c, z.data(), scale, m.data());
     BM_TRY(upload_signed_ntt(c, m.data(), dst, level + 1, 0, c.stream, true));
     BM_CUDA_TRY(cudaStreamSynchronize(c.stream));   // m is a host temporary
+    return BM_OK;
+}
+
+// The Algorithm-1 masks (mask_i[k] = 1 iff floor((k mod dim)/part) = i, at the top
+// level, scale q_L) and the compression mask (M[k] = 1 iff k = 0 mod part, scale
+// of the prime its rescale drops) of a gallery.
+static bm_status encode_gallery_masks(Context& c, const Layout& lo, uint32_t dim, uint32_t part, Gallery& g) {
+    const size_t n = c.n, S = c.slots;
+    std::vector<double> z(S);
+    if (lo.tiled) {
+        for (uint32_t i = 0; i < lo.n_in; i++) {
+            for (size_t k = 0; k < S; k++) z[k] = ((k % dim) / part == i) ? 1.0 : 0.0;
+            BM_TRY(encode_to_device(c, z, (double)c.primes[c.L], c.L, g.d_masks + (size_t)i * (c.L + 1) * n));
+        }
+    }
+    if (lo.compress) {
+        for (size_t k = 0; k < S; k++) z[k] = (k % part == 0) ? 1.0 : 0.0;
+        BM_TRY(encode_to_device(c, z, (double)c.primes[lo.level - 1], lo.level - 1, g.d_cmask));
+    }
     return BM_OK;
 }
 
@@ -612,18 +676,10 @@ bm_status bm_encode_gallery_packed(bm_context* ctxh, const double* feats, uint64
         delete gh;
         return st;
     }
-    std::vector<double> z(S);
-    if (lo.tiled) {
-        for (uint32_t i = 0; i < lo.n_in; i++) {
-            for (size_t k = 0; k < S; k++) z[k] = ((k % dim) / part_size == i) ? 1.0 : 0.0;
-            bm_status st = encode_to_device(c, z, (double)c.primes[c.L], c.L, g.d_masks + (size_t)i * (c.L + 1) * n);
-            if (st != BM_OK) { delete gh; return st; }
-        }
-    }
-    if (lo.compress) {
-        for (size_t k = 0; k < S; k++) z[k] = (k % part_size == 0) ? 1.0 : 0.0;
-        bm_status st = encode_to_device(c, z, (double)c.primes[lo.level - 1], lo.level - 1, g.d_cmask);
-        if (st != BM_OK) { delete gh; return st; }
+    st = encode_gallery_masks(c, lo, dim, part_size, g);
+    if (st != BM_OK) {
+        delete gh;
+        return st;
     }
     *out = gh;
     return BM_OK;
@@ -666,12 +722,202 @@ bm_status bm_gallery_import_packed(bm_context* ctxh, const uint64_t* pts, const 
     return BM_OK;
 }
 
+bm_status bm_enroll_encrypted(bm_context* ctxh, const bm_eval_keys* evk, bm_ciphertext* const* templates,
+                              uint64_t n_ids, uint32_t dim, uint32_t part_size, bm_gallery** out) {
+    if (!ctxh || !evk || !templates || !out || n_ids == 0) return fail(BM_E_ARG, "null argument or empty gallery");
+    Context& c = ctxh->c;
+    if (evk->k.ctx != &c) return fail(BM_E_ARG, "keys belong to another context");
+    const uint32_t kind = BM_PACK_REAL | BM_LAYOUT_ENCRYPTED;
+    Layout lo;
+    BM_TRY(make_layout(c, n_ids, dim, part_size, lo, kind));
+    if (!evk->k.relin) return fail(BM_E_KEY_MISSING, "no relinearisation key (bm_keygen_ex, BM_KEYS_ENCRYPTED_GALLERY)");
+    const uint32_t lb0 = ilog2(part_size), lbS = ilog2(c.slots);
+    std::vector<const uint64_t*> rkey(lbS, nullptr);
+    for (uint32_t b = lb0; b < lbS; b++) {
+        auto it = evk->k.keys.find(galois_of(c, -(int32_t)(1u << b)));
+        if (it == evk->k.keys.end()) return fail(BM_E_KEY_MISSING, "missing enrollment rotation key");
+        rkey[b] = it->second;
+    }
+    for (uint64_t k = 0; k < n_ids; k++) {
+        if (!templates[k]) return fail(BM_E_ARG, "null template");
+        const Ciphertext& t = templates[k]->ct;
+        if (t.ctx != &c) return fail(BM_E_ARG, "template from another context");
+        if (t.n_cts != 1 || t.level != c.L) return fail(BM_E_LEVEL, "templates are single top-level ciphertexts");
+    }
+    BM_CUDA_TRY(cudaSetDevice(c.device));
+    bm_gallery* gh;
+    BM_TRY(gallery_alloc(c, lo, n_ids, dim, part_size, kind, gh));
+    std::unique_ptr<bm_gallery> guard(gh);
+    Gallery& g = gh->g;
+    cudaStream_t s = c.stream;
+    const size_t n = c.n, L = c.L, lg = lo.level, S = c.slots;
+    const uint32_t n_in = lo.n_in, G = lo.G;
+    const size_t cwL = ct_words(c, (uint32_t)L), cwg = ct_words(c, (uint32_t)lg);
+    BM_CUDA_TRY(cudaMemsetAsync(g.d_pts, 0, (size_t)lo.groups * n_in * cwg * 8, s));
+    // enrollment masks: ones at slots [i*part, (i+1)*part), top level, scale q_L
+    DevBuf emask;
+    BM_CUDA_TRY(emask.alloc((size_t)n_in * (L + 1) * n));
+    {
+        std::vector<double> z(S);
+        for (uint32_t i = 0; i < n_in; i++) {
+            for (size_t k = 0; k < S; k++) z[k] = (k >= (size_t)i * part_size && k < (size_t)(i + 1) * part_size);
+            BM_TRY(encode_to_device(c, z, (double)c.primes[L], (uint32_t)L, emask.p + (size_t)i * (L + 1) * n));
+        }
+    }
+    // identities in chunks: templates -> masked, rescaled parts -> rotations -> sums into C[g][i]
+    const uint32_t CH = 32, maxB = 128;
+    const size_t P = (size_t)CH * n_in;
+    DevBuf tin, x0, xa, xb, scratch, plist, olist;
+    BM_CUDA_TRY(tin.alloc(CH * cwL));
+    BM_CUDA_TRY(x0.alloc(P * cwL));
+    BM_CUDA_TRY(xa.alloc(P * cwg));
+    BM_CUDA_TRY(xb.alloc(P * cwg));
+    BM_CUDA_TRY(scratch.alloc(std::max(ks_scratch_words(c, (uint32_t)lg, maxB), rescale_scratch_words(c, (uint32_t)L, maxB))));
+    // pointer lists per chunk: 5P (products, rescales) + 2P per shift bit + at most P
+    // group targets + P sums; offsets: one per target and one more (u32, two per word)
+    const size_t list_cap = P * (7 + 2 * (lbS - lb0)) + 16;
+    BM_CUDA_TRY(plist.alloc(list_cap));
+    BM_CUDA_TRY(olist.alloc(P / 2 + 2));
+    std::vector<uint64_t*> hl;
+    std::vector<uint32_t> hoff;
+    hl.reserve(list_cap);
+    uint64_t** dl = (uint64_t**)plist.p;
+    for (uint64_t u0 = 0; u0 < n_ids; u0 += CH) {
+        const uint32_t nu = (uint32_t)std::min<uint64_t>(CH, n_ids - u0);
+        const uint32_t np = nu * n_in;
+        hl.clear();
+        hoff.clear();
+        auto put = [&](uint64_t* p) { hl.push_back(p); };
+        for (uint32_t u = 0; u < nu; u++) {
+            const Ciphertext& t = templates[u0 + u]->ct;
+            if (t.d_coef)
+                BM_CUDA_TRY(cudaMemcpyAsync(tin.p + u * cwL, t.d_coef, cwL * 8, cudaMemcpyDeviceToDevice, s));
+            else
+                BM_CUDA_TRY(cudaMemcpyAsync(tin.p + u * cwL, t.host.data(), cwL * 8, cudaMemcpyHostToDevice, s));
+        }
+        BM_CUDA_TRY(ntt_forward(c, packed(c, tin.p, nu * 2, (uint32_t)L + 1), s));
+        // X[u][i] = Res(template_u * mask_i): lists in, pt, out (mul_plain), in, out (rescale)
+        const size_t o_mp = hl.size();
+        for (uint32_t k = 0; k < np; k++) put(tin.p + (k / n_in) * cwL);
+        for (uint32_t k = 0; k < np; k++) put(emask.p + (size_t)(k % n_in) * (L + 1) * n);
+        for (uint32_t k = 0; k < np; k++) put(x0.p + k * cwL);
+        const size_t o_rs = hl.size();
+        for (uint32_t k = 0; k < np; k++) put(x0.p + k * cwL);
+        for (uint32_t k = 0; k < np; k++) put(xa.p + k * cwg);
+        // rotations: the right shift of part i of identity u is ((w - i) * part) mod N/2,
+        // one rotation per set bit, lowest first; each rotation moves a ciphertext between
+        // its two buffers
+        std::vector<uint32_t> shift(np);
+        std::vector<uint8_t> cur(np, 0);
+        for (uint32_t k = 0; k < np; k++) {
+            const uint64_t w = (u0 + k / n_in) % G, i = k % n_in;
+            shift[k] = (uint32_t)((((int64_t)w - (int64_t)i) * (int64_t)part_size % (int64_t)S + (int64_t)S) % (int64_t)S);
+        }
+        struct RotLaunch { uint32_t b; size_t off, cnt; };
+        std::vector<RotLaunch> rl;
+        for (uint32_t b = lb0; b < lbS; b++) {
+            std::vector<uint32_t> ks;
+            for (uint32_t k = 0; k < np; k++)
+                if (shift[k] >> b & 1u) ks.push_back(k);
+            if (ks.empty()) continue;
+            const size_t off = hl.size();
+            for (uint32_t k : ks) put((cur[k] ? xb.p : xa.p) + k * cwg);
+            for (uint32_t k : ks) put((cur[k] ? xa.p : xb.p) + k * cwg);
+            for (uint32_t k : ks) cur[k] ^= 1;
+            rl.push_back({b, off, ks.size()});
+        }
+        // sums: target (group, part) <- its identities of this chunk, in identity order
+        const size_t o_dst = hl.size();
+        std::vector<std::pair<uint64_t, uint32_t>> targets;
+        for (uint32_t u = 0; u < nu; u++) {
+            const uint64_t grp = (u0 + u) / G;
+            if (targets.empty() || targets.back().first != grp) targets.push_back({grp, u});
+        }
+        for (auto& tg : targets)
+            for (uint32_t i = 0; i < n_in; i++) put(g.d_pts + (tg.first * n_in + i) * cwg);
+        const size_t o_src = hl.size();
+        hoff.push_back(0);
+        for (size_t ti = 0; ti < targets.size(); ti++) {
+            const uint32_t ub = targets[ti].second;
+            const uint32_t ue = ti + 1 < targets.size() ? targets[ti + 1].second : nu;
+            for (uint32_t i = 0; i < n_in; i++) {
+                for (uint32_t u = ub; u < ue; u++) {
+                    const uint32_t k = u * n_in + i;
+                    put((cur[k] ? xb.p : xa.p) + k * cwg);
+                }
+                hoff.push_back((uint32_t)(hl.size() - o_src));
+            }
+        }
+        if (hl.size() > list_cap || hoff.size() > olist.words * 2) return fail(BM_E_ARG, "enrollment list overflow");
+        BM_CUDA_TRY(cudaMemcpyAsync(plist.p, hl.data(), hl.size() * sizeof(void*), cudaMemcpyHostToDevice, s));
+        BM_CUDA_TRY(cudaMemcpyAsync(olist.p, hoff.data(), hoff.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+        BM_CUDA_TRY(mul_plain(c, (uint32_t)L, np, dl + o_mp, (const uint64_t* const*)(dl + o_mp + np),
+                              dl + o_mp + 2 * np, s));
+        for (uint32_t b0 = 0; b0 < np; b0 += maxB)
+            BM_CUDA_TRY(rescale(c, (uint32_t)L, std::min(maxB, np - b0), dl + o_rs + b0, dl + o_rs + np + b0,
+                                scratch.p, s));
+        for (const RotLaunch& r : rl) {
+            const uint64_t gk = galois_of(c, -(int32_t)(1u << r.b));
+            for (size_t b0 = 0; b0 < r.cnt; b0 += maxB) {
+                const uint32_t B = (uint32_t)std::min<size_t>(maxB, r.cnt - b0);
+                BM_CUDA_TRY(ks_rotate(c, rkey[r.b], gk, (uint32_t)lg, B, dl + r.off + b0, dl + r.off + r.cnt + b0,
+                                      nullptr, scratch.p, s));
+            }
+        }
+        BM_CUDA_TRY(accumulate(c, (uint32_t)lg, (uint32_t)(targets.size() * n_in), dl + o_dst,
+                               (const uint64_t* const*)(dl + o_src), (const uint32_t*)olist.p, np, s));
+        BM_CUDA_TRY(cudaStreamSynchronize(s));           // the host lists are rebuilt for the next chunk
+    }
+    BM_CUDA_TRY(to_montgomery(c, packed(c, g.d_pts, lo.groups * n_in * 2, (uint32_t)lg + 1), false, s));
+    BM_TRY(encode_gallery_masks(c, lo, dim, part_size, g));
+    BM_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = guard.release();
+    return BM_OK;
+}
+
+bm_status bm_gallery_import_encrypted(bm_context* ctxh, const uint64_t* cts, const uint64_t* masks,
+                                      const uint64_t* cmask, uint64_t n_ids, uint32_t dim, uint32_t part_size,
+                                      bm_gallery** out) {
+    if (!ctxh || !cts || !masks || !cmask || !out || n_ids == 0) return fail(BM_E_ARG, "null argument or empty gallery");
+    Context& c = ctxh->c;
+    const uint32_t kind = BM_PACK_REAL | BM_LAYOUT_ENCRYPTED;
+    Layout lo;
+    BM_TRY(make_layout(c, n_ids, dim, part_size, lo, kind));
+    BM_CUDA_TRY(cudaSetDevice(c.device));
+    bm_gallery* gh;
+    BM_TRY(gallery_alloc(c, lo, n_ids, dim, part_size, kind, gh));
+    std::unique_ptr<bm_gallery> guard(gh);
+    Gallery& g = gh->g;
+    cudaStream_t s = c.stream;
+    const size_t n = c.n;
+    auto up = [&](uint64_t* dst, const uint64_t* src, uint32_t polys, uint32_t nl) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(dst, src, (size_t)polys * nl * n * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = ntt_forward(c, packed(c, dst, polys, nl), s);
+        if (e == cudaSuccess) e = to_montgomery(c, packed(c, dst, polys, nl), false, s);
+        return e;
+    };
+    cudaError_t e = up(g.d_pts, cts, lo.groups * lo.n_in * 2, lo.level + 1);
+    if (e == cudaSuccess) e = up(g.d_masks, masks, lo.n_in, c.L + 1);
+    if (e == cudaSuccess) e = up(g.d_cmask, cmask, 1, lo.level);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(BM_E_CUDA, std::string("gallery import: ") + cudaGetErrorString(e));
+    *out = guard.release();
+    return BM_OK;
+}
+
+bm_status bm_gallery_info(const bm_gallery* gh, uint32_t* encrypted, uint32_t* packing) {
+    if (!gh) return fail(BM_E_ARG, "null gallery");
+    if (encrypted) *encrypted = gh->g.encrypted;
+    if (packing) *packing = gh->g.packing;
+    return BM_OK;
+}
+
 bm_status bm_gallery_export(const bm_gallery* gh, uint64_t* pts, uint64_t* masks, uint64_t* cmask) {
     if (!gh) return fail(BM_E_ARG, "null gallery");
     const Gallery& g = gh->g;
     const Context& c = *g.ctx;
     BM_CUDA_TRY(cudaSetDevice(c.device));
-    if (pts) BM_TRY(download_coeff(c, g.d_pts, g.groups * g.n_in, g.level + 1, true, pts));
+    if (pts) BM_TRY(download_coeff(c, g.d_pts, g.groups * g.n_in * (g.encrypted ? 2 : 1), g.level + 1, true, pts));
     if (masks && g.tiled) BM_TRY(download_coeff(c, g.d_masks, g.n_in, c.L + 1, true, masks));
     if (cmask && g.compress) BM_TRY(download_coeff(c, g.d_cmask, 1, g.level, true, cmask));
     return BM_OK;
@@ -687,14 +933,15 @@ bm_status bm_encrypt_query(bm_context* ctxh, const bm_public_key* pk, const doub
                            uint32_t part_size, uint32_t mode, uint64_t seed, uint64_t query_id,
                            bm_ciphertext** out) {
     if (!ctxh || !pk || !q || !out) return fail(BM_E_ARG, "null argument");
-    if (mode != BM_QUERY_TILED && mode != BM_QUERY_EXPANDED) return fail(BM_E_ARG, "unknown query mode");
+    if (mode != BM_QUERY_TILED && mode != BM_QUERY_EXPANDED && mode != BM_QUERY_TEMPLATE)
+        return fail(BM_E_ARG, "unknown query mode");
     Context& c = ctxh->c;
     Layout lo;
     BM_TRY(make_layout(c, 1, dim, part_size, lo));
     BM_CUDA_TRY(cudaSetDevice(c.device));
     cudaStream_t s = c.stream;
     const size_t n = c.n, S = c.slots, L1 = c.L + 1;
-    const uint32_t n_cts = mode == BM_QUERY_TILED ? 1 : lo.n_in;
+    const uint32_t n_cts = mode == BM_QUERY_EXPANDED ? lo.n_in : 1;
     auto* ch = new bm_ciphertext();
     ch->ref.attach(&c);
     Ciphertext& ct = ch->ct;
@@ -710,8 +957,11 @@ bm_status bm_encrypt_query(bm_context* ctxh, const bm_public_key* pk, const doub
     std::vector<double> z(S);
     std::vector<int64_t> m(n), vv(n), e0(n), e1(n);
     for (uint32_t k = 0; k < n_cts; k++) {
-        for (size_t j = 0; j < S; j++)
-            z[j] = mode == BM_QUERY_TILED ? q[j % dim] : q[k * part_size + (j % part_size)];
+        for (size_t j = 0; j < S; j++) {
+            if (mode == BM_QUERY_TILED) z[j] = q[j % dim];
+            else if (mode == BM_QUERY_EXPANDED) z[j] = q[k * part_size + (j % part_size)];
+            else z[j] = j < dim ? q[j] : 0.0;                 // template: first slots, zero padding
+        }
         encode_real(c, z.data(), c.scale, m.data());
         const uint64_t obj = query_id * 256 + k;
         sample_zo(seed, TAG_ENC_V, obj, vv.data(), c.n);
@@ -818,7 +1068,7 @@ struct Plan {
     uint64_t gid = 0, kid = 0;
     uint32_t Q = 0, ncts = 0, chunk = 0, n_out = 0;
     std::vector<void*> bufs;
-    uint64_t *qin = nullptr, *t0 = nullptr, *T = nullptr, *accA = nullptr, *accB = nullptr;
+    uint64_t *qin = nullptr, *t0 = nullptr, *T = nullptr, *accA = nullptr, *accB = nullptr, *accT = nullptr;
     uint64_t *scratch = nullptr, *result = nullptr;
     size_t scratch_words = 0, result_words = 0, qin_words = 0;
     PtrArena arena;
@@ -854,7 +1104,7 @@ void drop_plans(Context& c, uint64_t id) {
 // launch pass, where its plaintexts live.
 struct SchedView {
     uint32_t n_in = 0, part = 0, level = 0, groups = 0;
-    bool tiled = true, compress = true;
+    bool tiled = true, compress = true, encrypted = false;
     const uint64_t* d_pts = nullptr;
     const uint64_t* d_masks = nullptr;
     const uint64_t* d_cmask = nullptr;
@@ -868,6 +1118,7 @@ static SchedView view_of(const Gallery& g) {
     v.groups = g.groups;
     v.tiled = g.tiled;
     v.compress = g.compress;
+    v.encrypted = g.encrypted;
     v.d_pts = g.d_pts;
     v.d_masks = g.d_masks;
     v.d_cmask = g.d_cmask;
@@ -882,6 +1133,7 @@ static SchedView view_of(const Layout& lo, uint32_t part) {
     v.groups = lo.groups;
     v.tiled = lo.tiled;
     v.compress = lo.compress;
+    v.encrypted = lo.encrypted;
     return v;
 }
 
@@ -910,8 +1162,10 @@ struct MatchRun {
     }
     void need_scratch(size_t words) { pl.scratch_words = std::max(pl.scratch_words, words); }
 
+    // key switch of a batch: rotation by `rot`, or (relin) relinearisation -- the key
+    // from s^2 to s with the identity automorphism
     void rotate_batch(uint32_t level, int32_t rot, const std::vector<uint64_t*>& in,
-                      const std::vector<uint64_t*>& out, const std::vector<uint64_t*>* add) {
+                      const std::vector<uint64_t*>& out, const std::vector<uint64_t*>* add, bool relin = false) {
         auto din = pl.arena.list(in);
         auto dout = pl.arena.list(out);
         auto dadd = add ? pl.arena.list(*add) : nullptr;
@@ -920,11 +1174,11 @@ struct MatchRun {
             for (size_t b0 = 0; b0 < in.size(); b0 += ksb) record(BM_OP_ROTATE, level, std::min<size_t>(ksb, in.size() - b0));
             return;
         }
-        const uint64_t gk = galois_of(c, rot);
+        const uint64_t gk = relin ? 1 : galois_of(c, rot);
+        const uint64_t* kp = relin ? ek->relin : key(rot);
         for (size_t b0 = 0; b0 < in.size(); b0 += ksb) {
             const uint32_t B = (uint32_t)std::min<size_t>(ksb, in.size() - b0);
-            check(ks_rotate(c, key(rot), gk, level, B, din + b0, dout + b0, dadd ? dadd + b0 : nullptr, pl.scratch,
-                            s));
+            check(ks_rotate(c, kp, gk, level, B, din + b0, dout + b0, dadd ? dadd + b0 : nullptr, pl.scratch, s));
         }
     }
     void rescale_batch(uint32_t level, const std::vector<uint64_t*>& in, const std::vector<uint64_t*>& out) {
@@ -977,16 +1231,24 @@ struct MatchRun {
         // HE-C^3 per chunk of groups, then compression
         for (uint32_t g0 = 0; g0 < g.groups; g0 += pl.chunk) {
             const uint32_t G = std::min(pl.chunk, g.groups - g0);
-            record(BM_OP_MAC, lg, G, Q, n_in);
+            record(g.encrypted ? BM_OP_MAC_CT : BM_OP_MAC, lg, G, Q, n_in);
             if (pl.arena.live) {
-                check(mac(c, lg, Q, G, n_in, Tsrc, g.d_pts + (size_t)g0 * n_in * (lg + 1) * c.n, pl.accA, s));
+                if (g.encrypted)
+                    check(mac_ct(c, lg, Q, G, n_in, Tsrc, g.d_pts + (size_t)g0 * n_in * 2 * (lg + 1) * c.n, pl.accT,
+                                 pl.accA, s));
+                else
+                    check(mac(c, lg, Q, G, n_in, Tsrc, g.d_pts + (size_t)g0 * n_in * (lg + 1) * c.n, pl.accA, s));
             }
-            std::vector<uint64_t*> a, b;
+            std::vector<uint64_t*> a, b, t;
             for (uint32_t q = 0; q < Q; q++)
                 for (uint32_t k = 0; k < G; k++) {
                     a.push_back(pl.accA + ((size_t)q * G + k) * cw(lg));
                     b.push_back(pl.accB + ((size_t)q * G + k) * cw(lg - 1));
+                    if (g.encrypted) t.push_back(pl.accT + ((size_t)q * G + k) * cw(lg));
                 }
+            // encrypted gallery: one relinearisation of the summed tensor products,
+            // (d0, d1, d2) -> (d0 + KS(d2)_0, d1 + KS(d2)_1) with t = (d0, d2), a = (0, d1)
+            if (g.encrypted) rotate_batch(lg, 0, t, a, &a, true);
             rescale_batch(lg, a, b);
             for (uint32_t t = 1; (1u << (t - 1)) < part; t++) rotate_batch(lg - 1, (int32_t)(1u << (t - 1)), b, b, &b);
             if (!g.compress) {
@@ -1037,7 +1299,7 @@ static void plan_dims(const Context& c, const SchedView& g, uint32_t n_out, uint
     pl.ncts = g.tiled ? 1 : g.n_in;
     pl.n_out = n_out;
     const uint32_t lg = g.level;
-    const size_t per_group = (size_t)Q * (ct_words(c, lg) + ct_words(c, lg - 1)) * 8;
+    const size_t per_group = (size_t)Q * ((g.encrypted ? 2 : 1) * ct_words(c, lg) + ct_words(c, lg - 1)) * 8;
     const size_t budget = (size_t)8 << 30;
     uint32_t chunk = (uint32_t)std::max<size_t>(1, budget / std::max<size_t>(per_group, 1));
     if (g.compress) chunk = std::max(g.part, chunk / g.part * g.part);
@@ -1060,13 +1322,14 @@ static size_t plan_shape(const Context& c, const SchedView& g, uint32_t n_out, u
     size_t bytes = words_bytes(pl.qin_words) + words_bytes(pl.result_words);
     if (g.tiled) bytes += words_bytes((size_t)Q * g.n_in * ct_words(c, c.L)) + words_bytes((size_t)Q * g.n_in * ct_words(c, g.level));
     bytes += words_bytes((size_t)Q * pl.chunk * ct_words(c, g.level)) + words_bytes((size_t)Q * pl.chunk * ct_words(c, g.level - 1));
+    if (g.encrypted) bytes += words_bytes((size_t)Q * pl.chunk * ct_words(c, g.level));
     bytes += words_bytes(pl.scratch_words) + words_bytes(pl.arena.host.size());
     return bytes;
 }
 
 size_t plan_estimate_bytes(const Context& c, const Gallery& g, uint32_t Q) {
     Layout lo;
-    if (make_layout(c, g.n_ids, g.dim, g.part, lo, g.packing) != BM_OK) return 0;
+    if (make_layout(c, g.n_ids, g.dim, g.part, lo, gallery_kind(g)) != BM_OK) return 0;
     return plan_shape(c, view_of(g), lo.n_out, Q, nullptr);
 }
 
@@ -1086,7 +1349,7 @@ bm_status plan_build(Context& c, const Gallery& g, const EvalKeys& ek, uint32_t 
     auto* pl = new Plan();
     std::unique_ptr<Plan> guard(pl);
     Layout lo;
-    BM_TRY(make_layout(c, g.n_ids, g.dim, g.part, lo, g.packing));
+    BM_TRY(make_layout(c, g.n_ids, g.dim, g.part, lo, gallery_kind(g)));
     const SchedView v = view_of(g);
     pl->c = &c;
     pl->gid = g.id;
@@ -1100,6 +1363,7 @@ bm_status plan_build(Context& c, const Gallery& g, const EvalKeys& ek, uint32_t 
     }
     ok = ok && pl->alloc(pl->accA, (size_t)Q * pl->chunk * ct_words(c, lg));
     ok = ok && pl->alloc(pl->accB, (size_t)Q * pl->chunk * ct_words(c, lg - 1));
+    if (g.encrypted) ok = ok && pl->alloc(pl->accT, (size_t)Q * pl->chunk * ct_words(c, lg));
     if (!ok) return fail(BM_E_OOM, "match workspace allocation failed");
     MatchRun run(c, v, &ek, *pl);
     run.schedule();                                     // dry pass
@@ -1188,7 +1452,7 @@ bm_status bm_match(bm_context* ctxh, const bm_eval_keys* evk, const bm_gallery* 
             return fail(BM_E_LEVEL, "query layout does not match the gallery's schedule");
     }
     Layout lo;
-    BM_TRY(make_layout(c, g.n_ids, g.dim, g.part, lo, g.packing));
+    BM_TRY(make_layout(c, g.n_ids, g.dim, g.part, lo, gallery_kind(g)));
     for (int32_t r : schedule_rotations(c, lo, g.part))
         if (!evk->k.keys.count(galois_of(c, r))) return fail(BM_E_KEY_MISSING, "missing rotation key");
     BM_CUDA_TRY(cudaSetDevice(c.device));
@@ -1213,6 +1477,7 @@ bm_status bm_match(bm_context* ctxh, const bm_eval_keys* evk, const bm_gallery* 
     res.part = g.part;
     res.packed = g.compress;
     res.packing = g.packing;
+    res.scale = result_scale(c, g);
     cudaError_t e = cudaMallocAsync((void**)&res.d_data, pl->result_words * 8, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(res.d_data, pl->result, pl->result_words * 8, cudaMemcpyDeviceToDevice, s);
@@ -1283,7 +1548,7 @@ bm_status bm_decrypt_scores(bm_context* ctxh, const bm_secret_key* sk, const bm_
             const uint64_t v = h[o * 2 * n + i];
             coef[i] = v > q0 / 2 ? -(double)(q0 - v) : (double)v;
         }
-        decode_complex(c, coef.data(), c.scale, slots.data());
+        decode_complex(c, coef.data(), res.scale > 0 ? res.scale : c.scale, slots.data());
         dec[o] = slots;
     }
     int64_t best = -1;

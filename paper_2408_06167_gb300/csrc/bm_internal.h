@@ -130,6 +130,8 @@ bm_status plan_build(Context& c, const Gallery& g, const EvalKeys& ek, uint32_t 
 bm_status plan_run(Context& c, const Gallery& g, const EvalKeys& ek, Plan* p, const Ciphertext* const* queries,
                    uint32_t nq, cudaStream_t s);
 size_t plan_bytes(const Plan* p);
+// scale of the score ciphertexts of a match against g
+double result_scale(const Context& c, const Gallery& g);
 // device bytes the plan of Q queries for this gallery will hold (host only)
 size_t plan_estimate_bytes(const Context& c, const Gallery& g, uint32_t Q);
 // host only: the launches and plan bytes of a match for (params, n_ids, dim, part, Q)
@@ -155,6 +157,7 @@ struct EvalKeys {
     uint64_t id = 0;
     uint32_t dim = 0, part = 0;
     std::map<uint64_t, uint64_t*> keys;       // galois element -> [dnum][2][nb][N] NTT + Montgomery
+    uint64_t* relin = nullptr;                // key from s^2 to s, same layout (encrypted galleries)
     ~EvalKeys();
 };
 
@@ -166,6 +169,7 @@ struct Gallery {
     bool tiled = true;                        // queries arrive tiled (Algorithm 1 on the server)
     bool compress = true;                     // outputs are masked and packed
     uint32_t packing = BM_PACK_REAL;          // BM_PACK_COMPLEX: a second identity in the imaginary parts
+    bool encrypted = false;                   // d_pts holds ciphertexts [groups][n_in][2][level+1][N]
     uint64_t* d_pts = nullptr;                // [groups][n_in][level+1][N] NTT + Montgomery
     uint64_t* d_masks = nullptr;              // [n_in][L+1][N] Algorithm-1 masks (tiled only)
     uint64_t* d_cmask = nullptr;              // [level][N] compression mask at level-1
@@ -187,6 +191,7 @@ struct Result {
     uint32_t dim = 0, part = 0;
     bool packed = true;
     uint32_t packing = BM_PACK_REAL;          // slot packing of the gallery the result came from
+    double scale = 0;                         // scale of the score ciphertexts
     uint64_t* d_data = nullptr;               // [n_queries][n_out][2][N] coefficient form, level 0
     ~Result();
 };
@@ -251,7 +256,7 @@ uint64_t find_psi(uint64_t q, uint32_t log_n);
 void philox4x64_10(uint64_t k0, uint64_t k1, const uint64_t ctr[4], uint64_t out[4]);
 enum : uint64_t {
     TAG_SECRET = 1, TAG_PK_A = 2, TAG_PK_E = 3, TAG_RK_A = 4, TAG_RK_E = 5,
-    TAG_ENC_V = 6, TAG_ENC_E0 = 7, TAG_ENC_E1 = 8
+    TAG_ENC_V = 6, TAG_ENC_E0 = 7, TAG_ENC_E1 = 8, TAG_RLK_A = 9, TAG_RLK_E = 10
 };
 void sample_uniform(uint64_t seed, uint64_t tag, uint64_t obj, uint64_t limb, uint64_t q,
                     uint64_t* out, uint32_t n);
@@ -334,6 +339,13 @@ cudaError_t mul_plain(const Context& c, uint32_t level, uint32_t B, uint64_t* co
 // acc[q][g] = sum_i T[q][i] * P[g][i]  (T: [Q][n_in][2][level+1][N], P: [G][n_in][level+1][N])
 cudaError_t mac(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32_t n_in,
                 const uint64_t* T, const uint64_t* P, uint64_t* acc, cudaStream_t s);
+// dst[t] += sum of src[off[t] .. off[t+1]) (ciphertexts at `level`; off and the lists on the device)
+cudaError_t accumulate(const Context& c, uint32_t level, uint32_t n_targets, uint64_t* const* dst,
+                       const uint64_t* const* src, const uint32_t* off, uint32_t n_src, cudaStream_t s);
+// encrypted gallery: A[q][g] = (d0, d2), B[q][g] = (0, d1) of sum_i T[q][i] (x) C[g][i]
+// (C: [G][n_in][2][level+1][N] Montgomery form)
+cudaError_t mac_ct(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32_t n_in, const uint64_t* T,
+                   const uint64_t* C, uint64_t* A, uint64_t* B, cudaStream_t s);
 // plain products a*b on each limb (NTT form, b Montgomery)
 cudaError_t pointwise_mul(const Context& c, const LimbBatch& a, const LimbBatch& b,
                           const LimbBatch& out, cudaStream_t s);

@@ -511,6 +511,64 @@ __global__ void __launch_bounds__(kThreads) k_mac(const uint64_t* __restrict__ T
     }
 }
 
+// HE-C^3 with an encrypted gallery: the tensor products of the expanded query
+// parts T[q][i] with the gallery ciphertexts C[g][i] summed over the parts,
+//   d0 = sum T0*C0,  d1 = sum T0*C1 + T1*C0,  d2 = sum T1*C1   (C in Montgomery form),
+// written as A[q][g] = (d0, d2) -- the input of the relinearising key switch --
+// and B[q][g] = (0, d1) -- its addend.  Grid and tiling as k_mac.
+template <int QT>
+__global__ void __launch_bounds__(kThreads) k_mac_ct(const uint64_t* __restrict__ T, const uint64_t* __restrict__ C,
+                                                     uint64_t* __restrict__ A, uint64_t* __restrict__ B,
+                                                     uint32_t Qn, uint32_t G, uint32_t n_in, uint32_t lvl,
+                                                     DevTables tab, uint32_t log_n) {
+    const uint32_t n = 1u << log_n, l1 = lvl + 1;
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t j = blockIdx.y % l1, g = blockIdx.y / l1;
+    const uint32_t q0 = blockIdx.z * QT;
+    if (p >= n) return;
+    const uint64_t q = tab.q[j], qn = tab.qneg[j];
+    uint64_t d0[QT], d1[QT], d2[QT];
+#pragma unroll
+    for (int k = 0; k < QT; k++) d0[k] = d1[k] = d2[k] = 0;
+    for (uint32_t i = 0; i < n_in; i++) {
+        const size_t cb = ((((size_t)g * n_in + i) * 2) * l1 + j) * n + p;
+        const uint64_t c0 = C[cb], c1 = C[cb + (size_t)l1 * n];
+#pragma unroll
+        for (int k = 0; k < QT; k++) {
+            if (q0 + k >= Qn) break;
+            const size_t tb = ((((size_t)(q0 + k) * n_in + i) * 2) * l1 + j) * n + p;
+            const uint64_t t0 = T[tb], t1 = T[tb + (size_t)l1 * n];
+            d0[k] = addm(d0[k], mont(t0, c0, q, qn), q);
+            d1[k] = addm(d1[k], addm(mont(t0, c1, q, qn), mont(t1, c0, q, qn), q), q);
+            d2[k] = addm(d2[k], mont(t1, c1, q, qn), q);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < QT; k++) {
+        if (q0 + k >= Qn) break;
+        const size_t ob = ((((size_t)(q0 + k) * G + g) * 2) * l1 + j) * n + p;
+        A[ob] = d0[k];
+        A[ob + (size_t)l1 * n] = d2[k];
+        B[ob] = 0;
+        B[ob + (size_t)l1 * n] = d1[k];
+    }
+}
+
+// dst[t] += sum of src[k], k in [off[t], off[t+1]): ciphertexts [2][l1][N] at one
+// level; grid (targets * 2 * l1, chunks of a limb)
+__global__ void k_accumulate(uint64_t* const* dst, const uint64_t* const* src, const uint32_t* off, uint32_t l1,
+                             DevTables tab, uint32_t n) {
+    const uint32_t t = blockIdx.x / (2 * l1), r = blockIdx.x % (2 * l1), j = r % l1;
+    const uint64_t q = tab.q[j];
+    uint64_t* d = dst[t] + (size_t)r * n;
+    const uint32_t k0 = off[t], k1 = off[t + 1];
+    for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x) {
+        uint64_t acc = d[i];
+        for (uint32_t k = k0; k < k1; k++) acc = addm(acc, src[k][(size_t)r * n + i], q);
+        d[i] = acc;
+    }
+}
+
 inline dim3 elem_grid(uint32_t n, uint32_t y) { return dim3((n + kThreads - 1) / kThreads, y); }
 
 }  // namespace
@@ -830,6 +888,25 @@ cudaError_t mac(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32
     const dim3 g((c.n + kThreads - 1) / kThreads, G * (level + 1), (Q + QT - 1) / QT);
     ProfScope ps(BM_KERNEL_MAC, s, 8.0 * c.n * (level + 1) * ((double)Q * n_in * 2 + (double)G * n_in + 2.0 * Q * G));
     k_mac<QT><<<g, kThreads, 0, s>>>(T, P, acc, Q, G, n_in, level, c.tab, c.log_n);
+    return cudaGetLastError();
+}
+
+cudaError_t mac_ct(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32_t n_in, const uint64_t* T,
+                   const uint64_t* C, uint64_t* A, uint64_t* B, cudaStream_t s) {
+    constexpr int QT = 4;
+    const dim3 g((c.n + kThreads - 1) / kThreads, G * (level + 1), (Q + QT - 1) / QT);
+    ProfScope ps(BM_KERNEL_MAC, s,
+                 8.0 * c.n * (level + 1) * ((double)Q * n_in * 2 + 2.0 * G * n_in + 4.0 * Q * G));
+    k_mac_ct<QT><<<g, kThreads, 0, s>>>(T, C, A, B, Q, G, n_in, level, c.tab, c.log_n);
+    return cudaGetLastError();
+}
+
+cudaError_t accumulate(const Context& c, uint32_t level, uint32_t n_targets, uint64_t* const* dst,
+                       const uint64_t* const* src, const uint32_t* off, uint32_t n_src, cudaStream_t s) {
+    if (!n_targets) return cudaSuccess;
+    ProfScope ps(BM_KERNEL_OTHER, s, 16.0 * c.n * (level + 1) * (n_targets + n_src));
+    k_accumulate<<<dim3(n_targets * 2 * (level + 1), c.n / kThreads / 4), kThreads, 0, s>>>(dst, src, off, level + 1,
+                                                                                            c.tab, c.n);
     return cudaGetLastError();
 }
 

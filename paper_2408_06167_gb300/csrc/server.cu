@@ -195,6 +195,7 @@ void run_batch(Executor& E, std::vector<Request*>& batch) {
             r.part = en.g->part;
             r.packed = en.g->compress;
             r.packing = en.g->packing;
+            r.scale = result_scale(c, *en.g);
             cudaError_t e = cudaMallocAsync((void**)&r.d_data, words * 8, E.s);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(r.d_data, plan_result(pl) + i * words, words * 8, cudaMemcpyDeviceToDevice, E.s);

@@ -104,7 +104,7 @@ double interp(const double* u, const double* t, double x) {
 double launch_us(const bm_op_costs& k, const bm_op_launch& l) {
     double units = l.count;
     uint32_t level = l.level;
-    if (l.op == BM_OP_MAC) units = std::ceil(l.queries / 4.0) * l.count * l.parts;
+    if (l.op == BM_OP_MAC || l.op == BM_OP_MAC_CT) units = std::ceil(l.queries / 4.0) * l.count * l.parts;
     if (l.op == BM_OP_NTT || l.op == BM_OP_INTT || l.op == BM_OP_COPY) level = 0;
     if (l.op >= BM_OP_KINDS || level >= BM_MAX_Q) return 0.0;
     return interp(k.units[l.op], k.t_us[l.op][level], units);
@@ -214,7 +214,7 @@ bm_status bm_measure_op_costs(bm_context* ctxh, bm_op_costs* out) {
     std::memset(out, 0, sizeof(*out));
     for (int op = 0; op < BM_OP_KINDS; op++)
         for (int k = 0; k < BM_COST_POINTS; k++)
-            out->units[op][k] = (op == BM_OP_MAC ? (double)kMacParts : 1.0) * (double)(1u << k);
+            out->units[op][k] = (op == BM_OP_MAC || op == BM_OP_MAC_CT ? (double)kMacParts : 1.0) * (double)(1u << k);
     cudaStream_t s = c.stream;
     Timer tm(s);
     const uint32_t L = c.L;
@@ -269,18 +269,22 @@ bm_status bm_measure_op_costs(bm_context* ctxh, bm_op_costs* out) {
     {
         // HE-C^3 products: 4 queries x 8 parts x 1..128 groups, at the levels a
         // gallery can sit (L - 1 with Algorithm 1 on the server, L without)
+        // (and the same with a gallery of ciphertexts: tensor products, two outputs)
         const uint32_t Gmax = kMaxB;
-        DevBuf T, P, acc;
+        DevBuf T, P, acc, acc2;
         BM_CUDA_TRY(T.alloc((size_t)kMacQ * kMacParts * ct_words(c, L)));
-        BM_CUDA_TRY(P.alloc((size_t)Gmax * kMacParts * (L + 1) * c.n));
+        BM_CUDA_TRY(P.alloc((size_t)Gmax * kMacParts * ct_words(c, L)));
         BM_CUDA_TRY(acc.alloc((size_t)kMacQ * Gmax * ct_words(c, L)));
+        BM_CUDA_TRY(acc2.alloc((size_t)kMacQ * Gmax * ct_words(c, L)));
         for (uint32_t level = (L ? L - 1 : 0); level <= L; level++) {
             BM_CUDA_TRY(fill(c, T.p, (size_t)kMacQ * kMacParts * ct_words(c, level), level + 1, 41 + level, s));
-            BM_CUDA_TRY(fill(c, P.p, (size_t)Gmax * kMacParts * (level + 1) * c.n, level + 1, 51 + level, s));
+            BM_CUDA_TRY(fill(c, P.p, (size_t)Gmax * kMacParts * ct_words(c, level), level + 1, 51 + level, s));
             for (int k = 0; k < BM_COST_POINTS; k++) {
                 const uint32_t G = 1u << k;
                 out->t_us[BM_OP_MAC][level][k] =
                     tm.us([&] { return mac(c, level, kMacQ, G, kMacParts, T.p, P.p, acc.p, s); }, 2, reps_for(G));
+                out->t_us[BM_OP_MAC_CT][level][k] = tm.us(
+                    [&] { return mac_ct(c, level, kMacQ, G, kMacParts, T.p, P.p, acc.p, acc2.p, s); }, 2, reps_for(G));
             }
             BM_CUDA_TRY(tm.err);
         }

@@ -38,10 +38,11 @@ def schedule_rotations(ctx, m, s):
 class OracleMatch:
     """Keys, gallery plaintexts, query ciphertexts and match outputs from the oracle."""
 
-    def __init__(self, name, m, s, R, n_queries, feats=None, seed=KEY_SEED, complex_pack=False):
+    def __init__(self, name, m, s, R, n_queries, feats=None, seed=KEY_SEED, complex_pack=False, encrypted=False):
         self.ctx = ctx = octx(name)
         self.m, self.s, self.R = m, s, R
         self.complex_pack = complex_pack
+        self.encrypted = encrypted
         self.n_in = m // s
         self.tiled = ctx.L >= 3
         self.level = ctx.L - 1 if self.tiled else ctx.L
@@ -49,12 +50,24 @@ class OracleMatch:
         self.feats = wl.gallery(R, m) if feats is None else feats
         self.queries, self.true_ids = wl.queries(self.feats, n_queries)
         self.sk, self.pk, self.rks = ckks.keygen(ctx, seed, schedule_rotations(ctx, m, s))
-        self.ev = ckks.Evaluator(ctx, self.rks)
+        self.ev = ckks.Evaluator(ctx, self.rks, ckks.keygen_relin(ctx, seed, self.sk) if encrypted else None)
         S, L = ctx.slots, ctx.L
         self.groups = sch.n_groups(R, s, S, complex_pack)
         slots_of = sch.gallery_slots_complex if complex_pack else sch.gallery_slots
-        self.gal = [[ctx.encode(slots_of(self.feats, g, i, s, S), ctx.q[self.level], self.level)
-                     for i in range(self.n_in)] for g in range(self.groups)]
+        if encrypted:
+            # a gallery of ciphertexts at the HE-C^3 level with scale Delta: the packed
+            # layout encrypted at the top level (seed 7), top limbs dropped
+            def enc(g, i):
+                ct = ckks.encrypt(ctx, self.pk, ctx.encode(slots_of(self.feats, g, i, s, S), ctx.scale, L), 7,
+                                  g * 256 + i)
+                return ckks.Ciphertext(ct.c0[: self.level + 1].copy(), ct.c1[: self.level + 1].copy(), self.level,
+                                       ct.scale)
+            self.gal = [[enc(g, i) for i in range(self.n_in)] for g in range(self.groups)]
+        else:
+            self.gal = [[ctx.encode(slots_of(self.feats, g, i, s, S), ctx.q[self.level], self.level)
+                         for i in range(self.n_in)] for g in range(self.groups)]
+        # scale of the score ciphertexts: one ct x ct product and one rescale with a gallery of ciphertexts
+        self.out_scale = ctx.scale ** 2 / ctx.q[self.level] if encrypted else ctx.scale
         self.masks = ([ctx.encode(sch.alg1_mask_slots(m, s, i, S), ctx.q[L], L) for i in range(self.n_in)]
                       if self.tiled else None)
         self.cmask = (ctx.encode(sch.compression_mask_slots(s, S), ctx.q[self.level - 1], self.level - 1)
@@ -62,6 +75,8 @@ class OracleMatch:
 
     # arrays in the library's import layouts
     def pts_array(self):
+        if self.encrypted:
+            return np.stack([np.stack([np.stack([c.c0, c.c1]) for c in row]) for row in self.gal])
         return np.stack([np.stack([p.limbs for p in row]) for row in self.gal])
 
     def masks_array(self):
@@ -85,14 +100,14 @@ class OracleMatch:
 
     def match(self, cts):
         outs, packed = sch.match(self.ev, cts, self.gal, self.masks, self.cmask, self.m, self.s,
-                                 expanded=not self.tiled)
+                                 expanded=not self.tiled, encrypted_gallery=self.encrypted)
         return self.ct_array(outs), packed
 
     def scores(self, outs_array, packed):
         ctx, S = self.ctx, self.ctx.slots
         dec = []
         for o in outs_array:
-            ct = ckks.Ciphertext(o[0], o[1], 0, ctx.scale)
+            ct = ckks.Ciphertext(o[0], o[1], 0, self.out_scale)
             dec.append(ckks.decrypt_decode(ctx, ct, self.sk))
         return np.array([dec[o][slot].imag if im else dec[o][slot].real
                          for o, slot, im in (sch.identity_slot(i, self.s, S, packed, self.complex_pack)

@@ -287,3 +287,50 @@ def test_keyswitch_output_decrypts_to_c_times_rotated_secret(level):
     err = ctx.crt(diff, ctx.q[: level + 1])
     # noise: ModDown rounding (<= alpha*(1 + ||s||_1)) + digit*e/P terms, far below 2^20
     assert max(abs(e) for e in err) < 2**20, max(abs(e) for e in err)
+
+
+@pytest.mark.parametrize("level", [1, 2, 3])
+def test_relinearisation_output_decrypts_to_c_times_s_squared(level):
+    """KS with the relinearisation key: d0 + d1*s = c * s^2 + (small) mod Q_level."""
+    ctx = ckks.Context("small4")
+    sk = ckks.sample_secret(ctx, 3)
+    key = ckks.keygen_relin(ctx, 3, sk)
+    rng = np.random.default_rng(10 + level)
+    c = np.stack([rng.integers(0, ctx.q[j], size=ctx.n, dtype=np.uint64) for j in range(level + 1)])
+    d0, d1 = ckks.keyswitch(ctx, c, level, key)
+    diff = np.zeros((level + 1, ctx.n), dtype=np.uint64)
+    for j in range(level + 1):
+        qj = ctx.q[j]
+        s_j = sk.limb(qj)
+        lhs = ckks.add_mod(d0[j], ctx.mul(d1[j], s_j, j), qj)
+        diff[j] = ckks.sub_mod(lhs, ctx.mul(c[j], ctx.mul(s_j, s_j, j), j), qj)
+    err = ctx.crt(diff, ctx.q[: level + 1])
+    assert max(abs(e) for e in err) < 2**20, max(abs(e) for e in err)
+
+
+def test_tensor_product_decrypts_to_the_product_of_messages():
+    """(d0 + d1 s + d2 s^2) = (a0 + a1 s)(b0 + b1 s) exactly in Z_Q[X]/(X^N + 1):
+    both sides as centred integers, the right side a schoolbook negacyclic product."""
+    ctx = ckks.Context(ckks.Params(6, (50, 40, 40), (50,), dnum=1))
+    sk = ckks.sample_secret(ctx, 5)
+    ev = ckks.Evaluator(ctx, {})
+    rng = np.random.default_rng(3)
+    lv = 2
+    rnd = lambda: np.stack([rng.integers(0, ctx.q[j], size=ctx.n, dtype=np.uint64) for j in range(lv + 1)])
+    a = ckks.Ciphertext(rnd(), rnd(), lv, 1.0)
+    b = ckks.Ciphertext(rnd(), rnd(), lv, 1.0)
+    t = ev.tensor(a, b)
+    Q = math.prod(ctx.q[: lv + 1])
+    s = [int(x) for x in sk.coeffs]
+    dec = lambda c0, c1: [x % Q for x in ctx.crt(np.stack([ckks.add_mod(c0[j], ctx.mul(c1[j], sk.limb(ctx.q[j]), j),
+                                                                        ctx.q[j]) for j in range(lv + 1)]),
+                                               ctx.q[: lv + 1])]
+    ma, mb = dec(a.c0, a.c1), dec(b.c0, b.c1)
+    want = micro.schoolbook_negacyclic(ma, mb, Q)
+    # d0 + d1 s + d2 s^2 with big integers
+    ci = lambda x: [v % Q for v in ctx.crt(x, ctx.q[: lv + 1])]
+    d0, d1, d2 = ci(t.d0), ci(t.d1), ci(t.d2)
+    s2 = micro.schoolbook_negacyclic(s, s, Q)
+    got = [(x + y + z) % Q for x, y, z in zip(d0, micro.schoolbook_negacyclic(d1, s, Q),
+                                              micro.schoolbook_negacyclic(d2, s2, Q))]
+    assert got == want

@@ -199,3 +199,52 @@ def test_identities_per_ciphertext_example():
     ex = _golden()["vectors_per_ciphertext_example"]
     s = ex["m"] // ex["n_in"]
     assert ex["n_slots"] // s == ex["value"]        # (N * N_in) / m vectors per ciphertext
+
+
+@pytest.fixture(scope="module")
+def enrolled():
+    """small4, 16-dim parts of 4: 12 encrypted templates placed by the server-side
+    enrollment of Sec. 3.2 (mask, rescale, right rotation by powers of two, add)."""
+    m, s, R = 16, 4, 12
+    ctx = ckks.Context("small4")
+    S, L, n_in = ctx.slots, ctx.L, m // s
+    rots = ([s << j for j in range(sch.log2i(n_in))] + [1 << t for t in range(sch.log2i(s))]
+            + [-(1 << t) for t in range(sch.log2i(s))] + sch.enroll_rotations(s, S))
+    sk, pk, rks = ckks.keygen(ctx, 3, rots)
+    ev = ckks.Evaluator(ctx, rks, ckks.keygen_relin(ctx, 3, sk))
+    feats = wl.gallery(R, m)
+    temps = [ckks.encrypt(ctx, pk, ctx.encode(sch.template_slots(f, S), ctx.scale, L), 6, k)
+             for k, f in enumerate(feats)]
+    emasks = [ctx.encode(sch.enroll_mask_slots(s, i, S), ctx.q[L], L) for i in range(n_in)]
+    gal = sch.enroll(ev, temps, emasks, s, S)
+    return dict(ctx=ctx, sk=sk, pk=pk, ev=ev, feats=feats, gal=gal, m=m, s=s, R=R)
+
+
+def test_enrollment_places_each_template_in_its_window(enrolled):
+    ctx, gal, s = enrolled["ctx"], enrolled["gal"], enrolled["s"]
+    S, L = ctx.slots, ctx.L
+    assert len(gal) == 1 and all(c.level == L - 1 and c.scale == ctx.scale for c in gal[0])
+    for i, c in enumerate(gal[0]):
+        d = ckks.decrypt_decode(ctx, c, enrolled["sk"]).real
+        want = np.array(sch.gallery_slots(enrolled["feats"], 0, i, s, S))
+        assert np.abs(d - want).max() < 1e-6, i
+
+
+def test_encrypted_gallery_match_scores(enrolled):
+    ctx, ev, s, m = enrolled["ctx"], enrolled["ev"], enrolled["s"], enrolled["m"]
+    S, L, n_in = ctx.slots, ctx.L, m // s
+    feats = enrolled["feats"]
+    q = wl.queries(feats, 1)[0][0]
+    ct = ckks.encrypt(ctx, enrolled["pk"], ctx.encode(sch.tiled_query_slots(q, S), ctx.scale, L), 4, 0)
+    masks = [ctx.encode(sch.alg1_mask_slots(m, s, i, S), ctx.q[L], L) for i in range(n_in)]
+    mm = ctx.encode(sch.compression_mask_slots(s, S), ctx.q[L - 2], L - 2)
+    ref = wl.plaintext_scores(feats, q)
+    for lazy in (True, False):
+        cu = sch.expand_query(ev, ct, masks, m, s)
+        accs = [sch.hec3(ev, cu, g, s, encrypted_gallery=True, lazy_relin=lazy) for g in enrolled["gal"]]
+        outs = sch.compress(ev, accs, mm, s)
+        # ct x ct at level L-1 then one rescale: the output scale is Delta^2 / q_(L-1)
+        assert outs[0].level == 0 and outs[0].scale == pytest.approx(ctx.scale ** 2 / ctx.q[L - 1], rel=1e-15)
+        dec = [ckks.decrypt_decode(ctx, o, enrolled["sk"]).real for o in outs]
+        got = np.array([dec[o][slot] for o, slot, _ in (sch.identity_slot(i, s, S, True) for i in range(len(feats)))])
+        assert np.abs(got - ref).max() < 1e-5, lazy
