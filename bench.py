@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "encrypted 1:N template matches/sec @128-dim, ring 2^16; p50/p99 query latency"
 UNIT = "matches/s"
-KEY_SEED, ENC_SEED = 3, 4
+KEY_SEED, ENC_SEED, TEMPLATE_SEED = 3, 4, 6
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2, written between timed steps
 
 
@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--auto-part", action="store_true",
                     help="serving: each gallery's part size chosen by the cost model (bm_choose_part)")
     ap.add_argument("--no-tune", action="store_true", help="skip the rotation kernel-shape tuner")
+    ap.add_argument("--gallery", default="plain", choices=["plain", "encrypted"],
+                    help="gallery of plaintexts, or of ciphertexts enrolled on the server (Sec. 3.2)")
     ap.add_argument("--packing", default="real", choices=["real", "complex"],
                     help="gallery slot packing (complex: a second identity in the imaginary parts)")
     return ap.parse_args()
@@ -442,9 +444,22 @@ def main():
     ctx = bm.bm_context_create(W.preset, local)
     wide = None if args.no_tune else bm.bm_autotune_keyswitch(ctx)
     packing = bm.BM_PACK_COMPLEX if args.packing == "complex" else bm.BM_PACK_REAL
-    sk, pk, ek = bm.bm_keygen(ctx, KEY_SEED, W.dim, part)
     feats = wl.gallery(W.n_ids, W.dim)
-    gal = bm.bm_encode_gallery_packed(ctx, feats, W.dim, part, packing)
+    enroll = None
+    if args.gallery == "encrypted":
+        # the client encrypts every template (one GPU batch), the server enrolls them
+        sk, pk, ek = bm.bm_keygen_ex(ctx, KEY_SEED, W.dim, part, bm.BM_KEYS_ENCRYPTED_GALLERY)
+        t0 = time.perf_counter()
+        temps = bm.bm_encrypt_batch(ctx, pk, feats, W.dim, part, bm.BM_QUERY_TEMPLATE, TEMPLATE_SEED, 0,
+                                    bm.BM_ENC_KEEP_DEVICE)
+        t1 = time.perf_counter()
+        gal = bm.bm_enroll_encrypted(ctx, ek, temps, W.dim, part)
+        t2 = time.perf_counter()
+        del temps
+        enroll = {"encrypt_templates_s": t1 - t0, "enroll_s": t2 - t1}
+    else:
+        sk, pk, ek = bm.bm_keygen(ctx, KEY_SEED, W.dim, part)
+        gal = bm.bm_encode_gallery_packed(ctx, feats, W.dim, part, packing)
     qs, _ = wl.queries(feats, W.n_queries)
     mode = bm.BM_QUERY_TILED if W.query_mode == "tiled" else bm.BM_QUERY_EXPANDED
     cts = [bm.bm_encrypt_query(ctx, pk, q, W.dim, part, mode, ENC_SEED, i) for i, q in enumerate(qs)]
@@ -548,7 +563,7 @@ def main():
                    "dim": W.dim, "part": part, "queries_per_step": W.n_queries,
                    "l2": "flushed between steps (512 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single",
-                   "packing": args.packing, "ks_wide_batch": wide},
+                   "packing": args.packing, "gallery": args.gallery, "ks_wide_batch": wide},
         "latency_ms": {"p50": percentile(step_ms, 50), "p99": percentile(step_ms, 99)},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -558,6 +573,8 @@ def main():
         "clocks": clocks,
         "check": {"max_abs_score_err_vs_fp64": max_err, "rank1": rank1, "rank1_fp64": int(ref.argmax())},
     }
+    if enroll:
+        line["enrollment"] = enroll
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(line))
