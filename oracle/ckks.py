@@ -596,6 +596,36 @@ class Evaluator:
             return ct.copy()
         return self.apply_galois(ct, self.ctx.galois_left(r))
 
+    def rotate_hoisted(self, ct, rs):
+        """Rot(ct, r) for every r in rs, sharing one basis extension of c1: the
+        extended limbs of c1 (ModUp, NTT form) are computed once; each rotation
+        takes their Galois image (an exact permutation of the NTT slots,
+        computed here as NTT(sigma_k(INTT(.)))), the inner product with its key,
+        ModDown, and adds sigma_k(c0).  Same messages as rotate(); the bits
+        differ from it because ModUp runs before the automorphism."""
+        ctx, lvl = self.ctx, ct.level
+        ext_idx = ctx.ext_index(lvl)
+        ext = modup_ntt(ctx, ct.c1, lvl)
+        outs = []
+        for r in rs:
+            if r % ctx.slots == 0:
+                outs.append(ct.copy())
+                continue
+            k = ctx.galois_left(r)
+            key = self.keys[k]
+            acc = np.zeros((2, len(ext_idx), ctx.n), dtype=np.uint64)
+            for d, f_d in ext.items():
+                for jj, gi in enumerate(ext_idx):
+                    t = ctx.primes[gi]
+                    fk = ctx.ntt(automorphism(ctx.intt(f_d[jj], gi), ctx.log_n, k, t), gi)
+                    for comp in range(2):
+                        acc[comp, jj] = add_mod(acc[comp, jj], pointwise_mul(fk, key.ntt_data[d, comp, gi], t), t)
+            d0, d1 = moddown(ctx, acc, lvl)
+            c0s = np.stack([automorphism(ct.c0[j], ctx.log_n, k, ctx.q[j]) for j in range(lvl + 1)])
+            c0 = np.stack([add_mod(c0s[j], d0[j], ctx.q[j]) for j in range(lvl + 1)])
+            outs.append(Ciphertext(c0, d1, lvl, ct.scale))
+        return outs
+
     def apply_galois(self, ct, k):
         ctx, lvl = self.ctx, ct.level
         key = self.keys[k]
@@ -606,28 +636,26 @@ class Evaluator:
         return Ciphertext(c0, d1, lvl, ct.scale)
 
 
-def keyswitch(ctx, c, level, key):
-    """Hybrid key switching of the polynomial c (limbs q_0..q_level, coefficient form).
-
-    ModUp: per digit d (limbs of Q_d at or below `level`), the digit's own limbs
-    are kept and every other limb of Q_level u P is the fast base conversion
-    of those limbs.  Inner product with the key's digit-d pair in the NTT
-    domain, summed over digits.  ModDown: out_j = (x_j - Conv_P->q_j([x]_P)) * P^{-1}.
-    Returns the two output polynomials (limbs q_0..q_level)."""
-    ext = ctx.ext_index(level)                     # global basis indices
-    acc = np.zeros((2, len(ext), ctx.n), dtype=np.uint64)
+def modup_ntt(ctx, c, level):
+    """ModUp of c (limbs q_0..q_level, coefficient form) per digit, NTT form:
+    {digit: [limb of Q_level u P]} -- the digit's own limbs kept, every other limb
+    the fast base conversion of them (as in keyswitch)."""
+    ext = ctx.ext_index(level)
+    out = {}
     for d, dl in enumerate(ctx.digits):
         dl = [j for j in dl if j <= level]
         if not dl:
             continue
         src_primes = [ctx.q[j] for j in dl]
         src = np.stack([c[j] for j in dl])
-        for jj, gi in enumerate(ext):
-            t = ctx.primes[gi]
-            limb = c[gi] if gi in dl else bconv(src, src_primes, t)
-            f = ctx.ntt(limb, gi)
-            for comp in range(2):
-                acc[comp, jj] = add_mod(acc[comp, jj], pointwise_mul(f, key.ntt_data[d, comp, gi], t), t)
+        out[d] = [ctx.ntt(c[gi] if gi in dl else bconv(src, src_primes, ctx.primes[gi]), gi) for gi in ext]
+    return out
+
+
+def moddown(ctx, acc, level):
+    """(x - Conv_P->q_j([x]_P)) * P^{-1} mod q_j for both components of the inner
+    product acc[comp][limb of Q_level u P] (NTT form); coefficient-form outputs."""
+    ext = ctx.ext_index(level)
     out = []
     for comp in range(2):
         x = np.stack([ctx.intt(acc[comp, jj], gi) for jj, gi in enumerate(ext)])
@@ -640,3 +668,21 @@ def keyswitch(ctx, c, level, key):
             res[j] = scalar_mul(sub_mod(x[j], conv, qj), p_inv, qj)
         out.append(res)
     return out[0], out[1]
+
+
+def keyswitch(ctx, c, level, key):
+    """Hybrid key switching of the polynomial c (limbs q_0..q_level, coefficient form).
+
+    ModUp: per digit d (limbs of Q_d at or below `level`), the digit's own limbs
+    are kept and every other limb of Q_level u P is the fast base conversion
+    of those limbs.  Inner product with the key's digit-d pair in the NTT
+    domain, summed over digits.  ModDown: out_j = (x_j - Conv_P->q_j([x]_P)) * P^{-1}.
+    Returns the two output polynomials (limbs q_0..q_level)."""
+    ext = ctx.ext_index(level)                     # global basis indices
+    acc = np.zeros((2, len(ext), ctx.n), dtype=np.uint64)
+    for d, f_d in modup_ntt(ctx, c, level).items():
+        for jj, gi in enumerate(ext):
+            t = ctx.primes[gi]
+            for comp in range(2):
+                acc[comp, jj] = add_mod(acc[comp, jj], pointwise_mul(f_d[jj], key.ntt_data[d, comp, gi], t), t)
+    return moddown(ctx, acc, level)

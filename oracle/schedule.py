@@ -143,11 +143,15 @@ def expand_query(ev, ct, masks, m, s):
 
 def enroll(ev, templates, emasks, s, slots):
     """Sec. 3.2, server side: the encrypted template of identity idx (group g,
-    window w) is multiplied by each mask_i (part i), rescaled, rotated right by
-    (w - i)*s slots so that part i lands in window w, and added into the group
-    ciphertext C[g][i].  The printed shift (Index - i + 1)*m/N_in is read with
-    0-based indices.  A right rotation by t is applied as rotations by the powers
-    of two of t's binary digits, lowest first (keys for powers of two only).
+    window w) is multiplied by each mask_i (part i), rotated right by (w - i)*s
+    slots so that part i lands in window w, and added into the group ciphertext
+    C[g][i]; each C[g][i] is rescaled once, after its last identity.  The printed
+    shift (Index - i + 1)*m/N_in is read with 0-based indices.  A right rotation
+    by t is applied as rotations by the powers of two of t's binary digits,
+    lowest first (keys for powers of two only).  Rotating and summing before the
+    rescale keeps the key-switching noise of every identity at the product's
+    scale Delta*q_L, where it vanishes in the rescale, and adds one rescale's
+    rounding per group instead of one per identity.
     Returns C[g][i] for every group that holds an identity."""
     G = slots // s
     n_in = len(emasks)
@@ -156,7 +160,7 @@ def enroll(ev, templates, emasks, s, slots):
     for idx, ct in enumerate(templates):
         g, w = divmod(idx, G)
         for i in range(n_in):
-            x = ev.rescale(ev.mul_plain(ct, emasks[i]))
+            x = ev.mul_plain(ct, emasks[i])
             t, b = ((w - i) * s) % slots, 0
             while t:
                 if t & 1:
@@ -164,12 +168,31 @@ def enroll(ev, templates, emasks, s, slots):
                 t >>= 1
                 b += 1
             out[g][i] = ev.add(out[g][i], x)
-    return out
+    return [[ev.rescale(c) for c in row] for row in out]
 
 
 def enroll_rotations(s, slots):
     """Right rotations enrollment uses: every power of two from s below the slot count."""
     return [-(1 << b) for b in range(log2i(s), log2i(slots))]
+
+
+def expand_query_hoisted(ev, ct, masks, m, s):
+    """Algorithm 1's outputs by hoisted rotations (a reordering of the same sum):
+    T_i = sum_j Rot(ct (x) mask_i, j*s) over j < N_in, and
+    Rot(ct (x) mask_i, j*s) = Rot(ct, j*s) (x) mask_((i-j) mod N_in) because
+    shifting by j parts moves part index p to p - j (mod N_in) in every
+    length-m window of the tiled query.  The N_in - 1 rotations of the one
+    query ciphertext share a basis extension; each T_i is then N_in plaintext
+    products summed and rescaled once."""
+    n_in = m // s
+    rots = [ct] + ev.rotate_hoisted(ct, [j * s for j in range(1, n_in)])
+    out = []
+    for i in range(n_in):
+        acc = None
+        for j in range(n_in):
+            acc = ev.add(acc, ev.mul_plain(rots[j], masks[(i - j) % n_in]))
+        out.append(ev.rescale(acc))
+    return out
 
 
 def hec3(ev, cu, cs, s, rescale_each_part=False, encrypted_gallery=False, lazy_relin=True):
@@ -230,13 +253,18 @@ def compress(ev, accs, mask_m, s, tree=True, final_rescale=True):
 
 
 def match(ev, query_cts, gallery_pts, masks, mask_m, m, s, expanded=False,
-          rescale_each_part=False, tree=True, encrypted_gallery=False):
+          rescale_each_part=False, tree=True, encrypted_gallery=False, hoisted=False):
     """Full server-side match for one query.
 
     query_cts: [ct] (tiled, run through Algorithm 1) or the N_in client-expanded cts.
     gallery_pts[g][i]: plaintext of group g, part i.
     Returns (outputs, packed): the score ciphertexts and whether they are packed."""
-    cu = query_cts if expanded else expand_query(ev, query_cts[0], masks, m, s)
+    if expanded:
+        cu = query_cts
+    elif hoisted:
+        cu = expand_query_hoisted(ev, query_cts[0], masks, m, s)
+    else:
+        cu = expand_query(ev, query_cts[0], masks, m, s)
     accs = [hec3(ev, cu, gallery_pts[g], s, rescale_each_part, encrypted_gallery) for g in range(len(gallery_pts))]
     if accs[0].level >= 1 and mask_m is not None:
         return compress(ev, accs, mask_m, s, tree=tree), True
@@ -293,6 +321,12 @@ class CountingEvaluator:
     def rotate(self, ct, r):
         self._rec("Rot", ct.level)
         return SymCt(ct.level)
+
+    def rotate_hoisted(self, ct, rs):
+        self._rec("ModUp", ct.level)
+        for r in rs:
+            self._rec("RotH", ct.level)
+        return [SymCt(ct.level) for _ in rs]
 
     def zero_like(self, ct, level=None):
         return SymCt(ct.level if level is None else level)

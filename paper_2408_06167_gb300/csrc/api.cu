@@ -753,7 +753,13 @@ bm_status bm_enroll_encrypted(bm_context* ctxh, const bm_eval_keys* evk, bm_ciph
     const size_t n = c.n, L = c.L, lg = lo.level, S = c.slots;
     const uint32_t n_in = lo.n_in, G = lo.G;
     const size_t cwL = ct_words(c, (uint32_t)L), cwg = ct_words(c, (uint32_t)lg);
-    BM_CUDA_TRY(cudaMemsetAsync(g.d_pts, 0, (size_t)lo.groups * n_in * cwg * 8, s));
+    // the group ciphertexts are summed at the top level (scale Delta * q_L) and
+    // rescaled once at the end: the key-switching noise of every identity stays
+    // far below that scale and each group gets one rescale's rounding
+    const size_t n_grp = (size_t)lo.groups * n_in;
+    DevBuf acc_top;
+    BM_CUDA_TRY(acc_top.alloc(n_grp * cwL));
+    BM_CUDA_TRY(cudaMemsetAsync(acc_top.p, 0, n_grp * cwL * 8, s));
     // enrollment masks: ones at slots [i*part, (i+1)*part), top level, scale q_L
     DevBuf emask;
     BM_CUDA_TRY(emask.alloc((size_t)n_in * (L + 1) * n));
@@ -764,18 +770,17 @@ bm_status bm_enroll_encrypted(bm_context* ctxh, const bm_eval_keys* evk, bm_ciph
             BM_TRY(encode_to_device(c, z, (double)c.primes[L], (uint32_t)L, emask.p + (size_t)i * (L + 1) * n));
         }
     }
-    // identities in chunks: templates -> masked, rescaled parts -> rotations -> sums into C[g][i]
+    // identities in chunks: templates -> masked parts -> rotations -> sums into the group ciphertexts
     const uint32_t CH = 32, maxB = 128;
     const size_t P = (size_t)CH * n_in;
-    DevBuf tin, x0, xa, xb, scratch, plist, olist;
+    DevBuf tin, xa, xb, scratch, plist, olist;
     BM_CUDA_TRY(tin.alloc(CH * cwL));
-    BM_CUDA_TRY(x0.alloc(P * cwL));
-    BM_CUDA_TRY(xa.alloc(P * cwg));
-    BM_CUDA_TRY(xb.alloc(P * cwg));
-    BM_CUDA_TRY(scratch.alloc(std::max(ks_scratch_words(c, (uint32_t)lg, maxB), rescale_scratch_words(c, (uint32_t)L, maxB))));
-    // pointer lists per chunk: 5P (products, rescales) + 2P per shift bit + at most P
-    // group targets + P sums; offsets: one per target and one more (u32, two per word)
-    const size_t list_cap = P * (7 + 2 * (lbS - lb0)) + 16;
+    BM_CUDA_TRY(xa.alloc(P * cwL));
+    BM_CUDA_TRY(xb.alloc(P * cwL));
+    BM_CUDA_TRY(scratch.alloc(std::max(ks_scratch_words(c, (uint32_t)L, maxB), rescale_scratch_words(c, (uint32_t)L, maxB))));
+    // pointer lists per chunk: 3P (products) + 2P per shift bit + at most P group
+    // targets + P sums; offsets: one per target and one more (u32, two per word)
+    const size_t list_cap = std::max<size_t>(P * (5 + 2 * (lbS - lb0)) + 16, 2 * n_grp + 16);
     BM_CUDA_TRY(plist.alloc(list_cap));
     BM_CUDA_TRY(olist.alloc(P / 2 + 2));
     std::vector<uint64_t*> hl;
@@ -796,14 +801,11 @@ bm_status bm_enroll_encrypted(bm_context* ctxh, const bm_eval_keys* evk, bm_ciph
                 BM_CUDA_TRY(cudaMemcpyAsync(tin.p + u * cwL, t.host.data(), cwL * 8, cudaMemcpyHostToDevice, s));
         }
         BM_CUDA_TRY(ntt_forward(c, packed(c, tin.p, nu * 2, (uint32_t)L + 1), s));
-        // X[u][i] = Res(template_u * mask_i): lists in, pt, out (mul_plain), in, out (rescale)
+        // X[u][i] = template_u * mask_i: lists in, pt, out
         const size_t o_mp = hl.size();
         for (uint32_t k = 0; k < np; k++) put(tin.p + (k / n_in) * cwL);
         for (uint32_t k = 0; k < np; k++) put(emask.p + (size_t)(k % n_in) * (L + 1) * n);
-        for (uint32_t k = 0; k < np; k++) put(x0.p + k * cwL);
-        const size_t o_rs = hl.size();
-        for (uint32_t k = 0; k < np; k++) put(x0.p + k * cwL);
-        for (uint32_t k = 0; k < np; k++) put(xa.p + k * cwg);
+        for (uint32_t k = 0; k < np; k++) put(xa.p + k * cwL);
         // rotations: the right shift of part i of identity u is ((w - i) * part) mod N/2,
         // one rotation per set bit, lowest first; each rotation moves a ciphertext between
         // its two buffers
@@ -821,8 +823,8 @@ bm_status bm_enroll_encrypted(bm_context* ctxh, const bm_eval_keys* evk, bm_ciph
                 if (shift[k] >> b & 1u) ks.push_back(k);
             if (ks.empty()) continue;
             const size_t off = hl.size();
-            for (uint32_t k : ks) put((cur[k] ? xb.p : xa.p) + k * cwg);
-            for (uint32_t k : ks) put((cur[k] ? xa.p : xb.p) + k * cwg);
+            for (uint32_t k : ks) put((cur[k] ? xb.p : xa.p) + k * cwL);
+            for (uint32_t k : ks) put((cur[k] ? xa.p : xb.p) + k * cwL);
             for (uint32_t k : ks) cur[k] ^= 1;
             rl.push_back({b, off, ks.size()});
         }
@@ -834,7 +836,7 @@ bm_status bm_enroll_encrypted(bm_context* ctxh, const bm_eval_keys* evk, bm_ciph
             if (targets.empty() || targets.back().first != grp) targets.push_back({grp, u});
         }
         for (auto& tg : targets)
-            for (uint32_t i = 0; i < n_in; i++) put(g.d_pts + (tg.first * n_in + i) * cwg);
+            for (uint32_t i = 0; i < n_in; i++) put(acc_top.p + (tg.first * n_in + i) * cwL);
         const size_t o_src = hl.size();
         hoff.push_back(0);
         for (size_t ti = 0; ti < targets.size(); ti++) {
@@ -843,7 +845,7 @@ bm_status bm_enroll_encrypted(bm_context* ctxh, const bm_eval_keys* evk, bm_ciph
             for (uint32_t i = 0; i < n_in; i++) {
                 for (uint32_t u = ub; u < ue; u++) {
                     const uint32_t k = u * n_in + i;
-                    put((cur[k] ? xb.p : xa.p) + k * cwg);
+                    put((cur[k] ? xb.p : xa.p) + k * cwL);
                 }
                 hoff.push_back((uint32_t)(hl.size() - o_src));
             }
@@ -853,20 +855,31 @@ bm_status bm_enroll_encrypted(bm_context* ctxh, const bm_eval_keys* evk, bm_ciph
         BM_CUDA_TRY(cudaMemcpyAsync(olist.p, hoff.data(), hoff.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
         BM_CUDA_TRY(mul_plain(c, (uint32_t)L, np, dl + o_mp, (const uint64_t* const*)(dl + o_mp + np),
                               dl + o_mp + 2 * np, s));
-        for (uint32_t b0 = 0; b0 < np; b0 += maxB)
-            BM_CUDA_TRY(rescale(c, (uint32_t)L, std::min(maxB, np - b0), dl + o_rs + b0, dl + o_rs + np + b0,
-                                scratch.p, s));
         for (const RotLaunch& r : rl) {
             const uint64_t gk = galois_of(c, -(int32_t)(1u << r.b));
             for (size_t b0 = 0; b0 < r.cnt; b0 += maxB) {
                 const uint32_t B = (uint32_t)std::min<size_t>(maxB, r.cnt - b0);
-                BM_CUDA_TRY(ks_rotate(c, rkey[r.b], gk, (uint32_t)lg, B, dl + r.off + b0, dl + r.off + r.cnt + b0,
+                BM_CUDA_TRY(ks_rotate(c, rkey[r.b], gk, (uint32_t)L, B, dl + r.off + b0, dl + r.off + r.cnt + b0,
                                       nullptr, scratch.p, s));
             }
         }
-        BM_CUDA_TRY(accumulate(c, (uint32_t)lg, (uint32_t)(targets.size() * n_in), dl + o_dst,
+        BM_CUDA_TRY(accumulate(c, (uint32_t)L, (uint32_t)(targets.size() * n_in), dl + o_dst,
                                (const uint64_t* const*)(dl + o_src), (const uint32_t*)olist.p, np, s));
         BM_CUDA_TRY(cudaStreamSynchronize(s));           // the host lists are rebuilt for the next chunk
+    }
+    // one rescale per group ciphertext: top level -> the gallery level
+    hl.clear();
+    for (size_t k = 0; k < n_grp; k++) hl.push_back(acc_top.p + k * cwL);
+    for (size_t k = 0; k < n_grp; k++) hl.push_back(g.d_pts + k * cwg);
+    for (size_t b0 = 0; b0 < n_grp; b0 += maxB) {
+        const uint32_t B = (uint32_t)std::min<size_t>(maxB, n_grp - b0);
+        std::vector<uint64_t*> part_list;
+        for (uint32_t k = 0; k < B; k++) part_list.push_back(hl[b0 + k]);
+        for (uint32_t k = 0; k < B; k++) part_list.push_back(hl[n_grp + b0 + k]);
+        BM_CUDA_TRY(cudaMemcpyAsync(plist.p, part_list.data(), part_list.size() * sizeof(void*),
+                                    cudaMemcpyHostToDevice, s));
+        BM_CUDA_TRY(rescale(c, (uint32_t)L, B, dl, dl + B, scratch.p, s));
+        BM_CUDA_TRY(cudaStreamSynchronize(s));           // the list buffer is reused
     }
     BM_CUDA_TRY(to_montgomery(c, packed(c, g.d_pts, lo.groups * n_in * 2, (uint32_t)lg + 1), false, s));
     BM_TRY(encode_gallery_masks(c, lo, dim, part_size, g));

@@ -248,3 +248,36 @@ def test_encrypted_gallery_match_scores(enrolled):
         dec = [ckks.decrypt_decode(ctx, o, enrolled["sk"]).real for o in outs]
         got = np.array([dec[o][slot] for o, slot, _ in (sch.identity_slot(i, s, S, True) for i in range(len(feats)))])
         assert np.abs(got - ref).max() < 1e-5, lazy
+
+
+@pytest.mark.parametrize("m,s", [(16, 4), (128, 16), (16, 1)])
+def test_hoisted_expansion_gives_algorithm1_outputs(m, s):
+    """The hoisted form of Algorithm 1 (N_in - 1 rotations of the query sharing one
+    basis extension, products with the rotated masks) decrypts to the same parts as
+    the printed doubling form: part i replicated with period s in every slot."""
+    ctx, sk, pk, ev = _setup("small4", m, s, 1, extra_rots=[j * s for j in range(1, m // s)])
+    S, L, n_in = ctx.slots, ctx.L, m // s
+    q = wl.queries(wl.gallery(3, m), 1)[0][0]
+    ct = ckks.encrypt(ctx, pk, ctx.encode(sch.tiled_query_slots(q, S), ctx.scale, L), 4, 0)
+    masks = [ctx.encode(sch.alg1_mask_slots(m, s, i, S), ctx.q[L], L) for i in range(n_in)]
+    hoisted = sch.expand_query_hoisted(ev, ct, masks, m, s)
+    for i in range(n_in):
+        assert hoisted[i].level == L - 1 and hoisted[i].scale == ctx.scale
+        d = ckks.decrypt_decode(ctx, hoisted[i], sk).real
+        assert np.abs(d - np.array(sch.expanded_query_slots(q, s, i, S))).max() < 1e-6, i
+
+
+def test_hoisted_rotation_permutes_slots():
+    ctx = ckks.Context("small4")
+    sk, pk, rks = ckks.keygen(ctx, 3, [1, 5, -3, 100])
+    ev = ckks.Evaluator(ctx, rks)
+    rng = np.random.default_rng(4)
+    z = rng.uniform(-1, 1, ctx.slots)
+    for level in (3, 2):
+        ct = ckks.encrypt(ctx, pk, ctx.encode(z, ctx.scale, ctx.L), 5, 0)
+        while ct.level > level:
+            ct = ckks.Ciphertext(ct.c0[:-1].copy(), ct.c1[:-1].copy(), ct.level - 1, ct.scale)
+        outs = ev.rotate_hoisted(ct, [1, 5, -3, 100])
+        for r, o in zip([1, 5, -3, 100], outs):
+            d = ckks.decrypt_decode(ctx, o, sk).real
+            assert np.abs(d - np.roll(z, -r)).max() < 1e-6, (level, r)
