@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--auto-part", action="store_true",
                     help="serving: each gallery's part size chosen by the cost model (bm_choose_part)")
     ap.add_argument("--no-tune", action="store_true", help="skip the rotation kernel-shape tuner")
+    ap.add_argument("--expansion", default="doubling", choices=["doubling", "hoisted", "auto"],
+                    help="form of Algorithm 1 (auto: serving picks per gallery by the cost model)")
     ap.add_argument("--gallery", default="plain", choices=["plain", "encrypted"],
                     help="gallery of plaintexts, or of ciphertexts enrolled on the server (Sec. 3.2)")
     ap.add_argument("--packing", default="real", choices=["real", "complex"],
@@ -256,19 +258,31 @@ def run_serving(args):
     costs = bm.bm_measure_op_costs(ctx) if args.auto_part else None
     keys, gals, parts = {}, [], {}
     packing = bm.BM_PACK_COMPLEX if args.packing == "complex" else bm.BM_PACK_REAL
+    expansions = {}
     for gi, (name, R, m, s) in enumerate(SERVE_GALLERIES):
+        hoist = args.expansion == "hoisted"
         if costs is not None:
-            # the cost model's part size for a typical batch of 16 queries
-            s, _ = bm.bm_choose_part("ring16", costs, R, m, 16, 32 << 30, packing)
+            # the cost model's part size (and, with --expansion auto, form of Algorithm 1)
+            # for a typical batch of 16 queries
+            forms = [False, True] if args.expansion == "auto" else [hoist]
+            best = min(((bm.bm_choose_part("ring16", costs, R, m, 16, 32 << 30,
+                                           packing | (bm.BM_LAYOUT_HOISTED if h else 0)), h) for h in forms),
+                       key=lambda x: x[0][1])
+            (s, _), hoist = best
+        elif args.expansion == "auto":
+            hoist = False
         parts[name] = s
+        expansions[name] = "hoisted" if hoist else "doubling"
         if (m, s) not in keys:
-            keys[(m, s)] = bm.bm_keygen(ctx, KEY_SEED, m, s)
+            keys[(m, s)] = bm.bm_keygen_ex(ctx, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
         feats = wl.gallery(R, m, seed=10 + gi)
         qs, _ = wl.queries(feats, 64, seed=20 + gi)
         sk, pk, ek = keys[(m, s)]
         cts = [bm.bm_encrypt_query(ctx, pk, q, m, s, bm.BM_QUERY_TILED, ENC_SEED, i) for i, q in enumerate(qs)]
-        gals.append(dict(name=name, R=R, g=bm.bm_encode_gallery_packed(ctx, feats, m, s, packing), ek=ek,
-                         cts=cts))
+        g = bm.bm_encode_gallery_packed(ctx, feats, m, s, packing)
+        if hoist:
+            bm.bm_gallery_set_expansion(g, bm.BM_EXPAND_HOISTED)
+        gals.append(dict(name=name, R=R, g=g, ek=ek, cts=cts))
     # plain unbatched form: one query per bm_match, per gallery
     stream = torch.cuda.current_stream()
     single_ms = []
@@ -317,7 +331,7 @@ def run_serving(args):
                    "duration_s": args.duration, "galleries": [g[0] for g in SERVE_GALLERIES],
                    "executors": args.executors, "max_batch": args.max_batch, "parts": parts,
                    "part_choice": "cost model (bm_choose_part, 16 queries)" if costs is not None else "fixed",
-                   "packing": args.packing,
+                   "packing": args.packing, "expansion": expansions,
                    "ks_wide_batch": wide},
         "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]},
         "server": {k: st[k] for k in ("submitted", "completed", "failed", "batches", "mean_batch",
@@ -352,6 +366,9 @@ def run_sweep(args):
     mode = bm.BM_QUERY_TILED if W.query_mode == "tiled" else bm.BM_QUERY_EXPANDED
     parts = [p for p in (128, 64, 32, 16, 8, 4, 2, 1) if p <= W.dim]
     packing = bm.BM_PACK_COMPLEX if args.packing == "complex" else bm.BM_PACK_REAL
+    hoisted = args.expansion == "hoisted"
+    if hoisted:
+        packing |= bm.BM_LAYOUT_HOISTED
     pred = {p: bm.bm_predict_match(W.preset, costs, W.n_ids, W.dim, p, W.n_queries, packing) for p in parts}
     fitting = [p for p in parts if pred[p][1] <= budget]
     best_pred = min(pred[p][0] for p in fitting)
@@ -377,8 +394,10 @@ def run_sweep(args):
         if "skipped" in row:
             rows.append(row)
             continue
-        sk, pk, ek = bm.bm_keygen(ctx, KEY_SEED, W.dim, p)
-        gal = bm.bm_encode_gallery_packed(ctx, feats, W.dim, p, packing)
+        sk, pk, ek = bm.bm_keygen_ex(ctx, KEY_SEED, W.dim, p, bm.BM_KEYS_HOISTED if hoisted else 0)
+        gal = bm.bm_encode_gallery_packed(ctx, feats, W.dim, p, packing & ~bm.BM_LAYOUT_HOISTED)
+        if hoisted:
+            bm.bm_gallery_set_expansion(gal, bm.BM_EXPAND_HOISTED)
         cts = [bm.bm_encrypt_query(ctx, pk, q, W.dim, p, mode, ENC_SEED, i) for i, q in enumerate(qs)]
         for ct in cts:
             bm.bm_ciphertext_upload(ct, sptr)
@@ -414,7 +433,7 @@ def run_sweep(args):
         "config": {"workload": W.name, "mode": "part-sweep", "ring": "2^16" if W.preset == "ring16" else W.preset,
                    "n_ids": W.n_ids, "dim": W.dim, "queries_per_step": W.n_queries,
                    "l2": "flushed between steps (512 MiB write)", "packing": args.packing,
-                   "ks_wide_batch": wide},
+                   "expansion": args.expansion, "ks_wide_batch": wide},
         "sweep": rows, "model_part": model_part, "measured_best_part": best["part"],
         "model_part_measured_ms": next((r.get("measured_ms") for r in rows if r["part"] == model_part), None),
         "clocks": clocks,
@@ -458,8 +477,11 @@ def main():
         del temps
         enroll = {"encrypt_templates_s": t1 - t0, "enroll_s": t2 - t1}
     else:
-        sk, pk, ek = bm.bm_keygen(ctx, KEY_SEED, W.dim, part)
+        sk, pk, ek = bm.bm_keygen_ex(ctx, KEY_SEED, W.dim, part,
+                                     bm.BM_KEYS_HOISTED if args.expansion == "hoisted" else 0)
         gal = bm.bm_encode_gallery_packed(ctx, feats, W.dim, part, packing)
+        if args.expansion == "hoisted" and W.query_mode == "tiled":
+            bm.bm_gallery_set_expansion(gal, bm.BM_EXPAND_HOISTED)
     qs, _ = wl.queries(feats, W.n_queries)
     mode = bm.BM_QUERY_TILED if W.query_mode == "tiled" else bm.BM_QUERY_EXPANDED
     cts = [bm.bm_encrypt_query(ctx, pk, q, W.dim, part, mode, ENC_SEED, i) for i, q in enumerate(qs)]
@@ -563,7 +585,8 @@ def main():
                    "dim": W.dim, "part": part, "queries_per_step": W.n_queries,
                    "l2": "flushed between steps (512 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single",
-                   "packing": args.packing, "gallery": args.gallery, "ks_wide_batch": wide},
+                   "packing": args.packing, "gallery": args.gallery, "expansion": args.expansion,
+                   "ks_wide_batch": wide},
         "latency_ms": {"p50": percentile(step_ms, 50), "p99": percentile(step_ms, 99)},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -115,10 +115,12 @@ bm_status bm_keygen(bm_context* ctx, uint64_t seed, uint32_t dim, uint32_t part_
                     bm_secret_key** sk, bm_public_key** pk, bm_eval_keys** evk);
 /* Key sets beyond the plaintext-gallery schedule. */
 enum {
-    BM_KEYS_ENCRYPTED_GALLERY = 1   /* also the relinearisation key (the key-switching key from s^2
+    BM_KEYS_ENCRYPTED_GALLERY = 1,  /* also the relinearisation key (the key-switching key from s^2
                                        to s, for Mul of two ciphertexts, Sec. 3.1) and the right
                                        rotations by every power of two from part_size below N/2
                                        that enrollment uses (Sec. 3.2) */
+    BM_KEYS_HOISTED = 2             /* also the left rotations by j*part_size, 0 < j < dim/part_size,
+                                       of the hoisted Algorithm 1 (BM_EXPAND_HOISTED) */
 };
 /* bm_keygen with extra key sets (BM_KEYS_* flags); flags = 0 is bm_keygen.  The
  * relinearisation key is sampled like a rotation key with s^2 in place of
@@ -212,6 +214,25 @@ bm_status bm_gallery_import_encrypted(bm_context* ctx, const uint64_t* cts, cons
                                       uint32_t part_size, bm_gallery** out);
 /* 1 if the gallery holds ciphertexts, 0 if plaintexts; its packing. */
 bm_status bm_gallery_info(const bm_gallery* g, uint32_t* encrypted, uint32_t* packing);
+
+/* How the server runs Algorithm 1 (Input Ciphertext Expansion) for this gallery:
+ *  BM_EXPAND_DOUBLING  the printed form: per part i, mask, rescale, then log2(N_in)
+ *                      rotate-and-add steps by part*2^(j-1) (N_in log2 N_in rotations)
+ *  BM_EXPAND_HOISTED   the same sum reordered: T_i = Res(sum_j Rot(ct, j*part) *
+ *                      mask_((i-j) mod N_in)) -- since rotating a masked ciphertext by j
+ *                      parts equals rotating the ciphertext and using the mask of part
+ *                      i-j -- so N_in - 1 rotations of the one query ciphertext, which
+ *                      share its basis extension (hoisting), and N_in^2 plaintext products.
+ * Both decrypt to the same parts; the ciphertext bits differ.  Needs the rotation
+ * keys by j*part for j < N_in (bm_keygen_ex with BM_KEYS_HOISTED).  Plans of the
+ * gallery built before the call are dropped; call it before registering the
+ * gallery with a server.  BM_E_ARG for an unknown mode or a gallery without
+ * Algorithm 1 (client-expanded queries). */
+enum {
+    BM_EXPAND_DOUBLING = 0,
+    BM_EXPAND_HOISTED = 1
+};
+bm_status bm_gallery_set_expansion(bm_gallery* g, uint32_t mode);
 void bm_gallery_destroy(bm_gallery* g);
 
 /* Sec. 3.3: encrypts the L2-normalised query q[dim] under pk at the top level
@@ -406,7 +427,10 @@ enum {
     BM_OP_INTT = 5,       /* inverse NTT of `count` limbs (score egress) */
     BM_OP_COPY = 6,       /* device copy of `count` level-0 ciphertexts (uncompressed outputs) */
     BM_OP_MAC_CT = 7,     /* HE-C^3 tensor products with an encrypted gallery, as BM_OP_MAC */
-    BM_OP_KINDS = 8
+    BM_OP_MODUP = 8,      /* hoisted Algorithm 1: basis extension of `count` query ciphertexts */
+    BM_OP_ROT_HOISTED = 9,/* hoisted Algorithm 1: `count` rotations from extended ciphertexts */
+    BM_OP_MAC_CIRC = 10,  /* hoisted Algorithm 1: `queries` x `count` outputs of `parts` mask products */
+    BM_OP_KINDS = 11
 };
 
 /* One kernel launch (or launch group) of a match schedule. */
@@ -422,7 +446,7 @@ typedef struct bm_op_launch {
  * BM_COST_POINTS sizes: t_us[op][level][k] is the time (microseconds) of one
  * launch of units[op][k] units, units increasing.  Units are `count`, except for
  * BM_OP_MAC: ceil(queries / 4) * count * parts (one read of a gallery
- * plaintext serves a tile of four queries; the same for BM_OP_MAC_CT).  Between points the time is
+ * plaintext serves a tile of four queries; the same for BM_OP_MAC_CT and BM_OP_MAC_CIRC).  Between points the time is
  * interpolated linearly, above the last point extrapolated from the last two,
  * below the first taken as the first.  NTT, INTT and COPY use level 0. */
 #define BM_COST_POINTS 8
@@ -434,6 +458,8 @@ typedef struct bm_op_costs {
 /* Gallery kinds for the schedule model: a BM_PACK_* value, or'ed with
  * BM_LAYOUT_ENCRYPTED for a gallery of ciphertexts (bm_enroll_encrypted). */
 #define BM_LAYOUT_ENCRYPTED 0x100u
+/* ... or'ed with BM_LAYOUT_HOISTED for the hoisted form of Algorithm 1 (bm_gallery_set_expansion). */
+#define BM_LAYOUT_HOISTED 0x200u
 
 /* Host only (no device needed): the launches of the match of `n_queries`
  * queries against a gallery of n_ids identities in (dim, part_size, packing) under
@@ -459,7 +485,7 @@ bm_status bm_choose_part(const bm_params* params, const bm_op_costs* costs, uint
                          double* ms);
 
 /* Times every op kind on this context's device at BM_COST_POINTS sizes per
- * level (1, 2, 4, ..., 128 ciphertexts or limbs; MAC: 4 queries x 8 parts x
+ * level (1, 2, 4, ..., 128 ciphertexts or limbs; MAC_CIRC: 4 queries x 2^k parts; MAC: 4 queries x 8 parts x
  * 1..128 groups), with seeded random residues as operands (the values do not
  * change the time).  Rotations use the kernel shape the context currently picks
  * for each batch size, so run bm_autotune_keyswitch first.  Takes a few seconds

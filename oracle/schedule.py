@@ -185,7 +185,7 @@ def expand_query_hoisted(ev, ct, masks, m, s):
     query ciphertext share a basis extension; each T_i is then N_in plaintext
     products summed and rescaled once."""
     n_in = m // s
-    rots = [ct] + ev.rotate_hoisted(ct, [j * s for j in range(1, n_in)])
+    rots = [ct] + (ev.rotate_hoisted(ct, [j * s for j in range(1, n_in)]) if n_in > 1 else [])
     out = []
     for i in range(n_in):
         acc = None
@@ -290,6 +290,8 @@ class CountingEvaluator:
         self.ops.append((op, level))
 
     def add(self, a, b):
+        if a is None or b is None:          # the identity of add (as Evaluator.add)
+            return b if a is None else a
         self._rec("Add", a.level)
         return SymCt(a.level)
 

@@ -30,7 +30,11 @@ BM_QUERY_TEMPLATE = 2
 BM_PACK_REAL = 0
 BM_PACK_COMPLEX = 1
 BM_LAYOUT_ENCRYPTED = 0x100
+BM_LAYOUT_HOISTED = 0x200
 BM_KEYS_ENCRYPTED_GALLERY = 1
+BM_KEYS_HOISTED = 2
+BM_EXPAND_DOUBLING = 0
+BM_EXPAND_HOISTED = 1
 BM_ENC_KEEP_DEVICE = 1
 PRESETS = {"toy": 0, "ring16": 1, "small4": 2}
 STATUS = ["BM_OK", "BM_E_ARG", "BM_E_PARAM", "BM_E_LEVEL", "BM_E_KEY_MISSING", "BM_E_DIM", "BM_E_OOM",
@@ -48,9 +52,10 @@ class bm_params(ctypes.Structure):
                 ("dnum", _u32), ("log_scale", _u32), ("secret_hw", _u32), ("sigma", _dbl)]
 
 
-OPS = {"rotate": 0, "rescale": 1, "mul_plain": 2, "mac": 3, "ntt": 4, "intt": 5, "copy": 6, "mac_ct": 7}
+OPS = {"rotate": 0, "rescale": 1, "mul_plain": 2, "mac": 3, "ntt": 4, "intt": 5, "copy": 6, "mac_ct": 7,
+       "modup": 8, "rot_hoisted": 9, "mac_circ": 10}
 OP_NAMES = {v: k for k, v in OPS.items()}
-BM_OP_KINDS = 8
+BM_OP_KINDS = 11
 BM_MAX_Q = 6
 BM_COST_POINTS = 8
 
@@ -89,6 +94,7 @@ _SIGS = {
     "bm_encrypt_batch": (ctypes.c_int, [_vp, _vp, _DP, _u64, _u32, _u32, _u32, _u64, _u64, _u32, _PP]),
     "bm_gallery_import_encrypted": (ctypes.c_int, [_vp, _U64P, _U64P, _U64P, _u64, _u32, _u32, _PP]),
     "bm_gallery_info": (ctypes.c_int, [_vp, _U32P, _U32P]),
+    "bm_gallery_set_expansion": (ctypes.c_int, [_vp, _u32]),
     "bm_secret_key_destroy": (None, [_vp]),
     "bm_public_key_destroy": (None, [_vp]),
     "bm_eval_keys_destroy": (None, [_vp]),
@@ -345,6 +351,11 @@ def bm_gallery_import_encrypted(ctx, cts, masks, cmask, n_ids, dim, part):
     g = Gallery(h.value, ctx)
     g.n_ids, g.dim, g.part, g.packing, g.encrypted = n_ids, dim, part, BM_PACK_REAL, True
     return g
+
+
+def bm_gallery_set_expansion(g, mode):
+    _check(_L.bm_gallery_set_expansion(g.ptr, mode))
+    g.hoisted = mode == BM_EXPAND_HOISTED
 
 
 def bm_gallery_info(g):

@@ -56,6 +56,7 @@ struct Layout {
     uint32_t per_group;                     // identities per group: G, or 2G with complex packing
     bool tiled, compress;
     bool encrypted;                         // gallery of ciphertexts (HE-C^3 products ct x ct)
+    bool hoisted;                           // Algorithm 1 by hoisted rotations
 };
 
 // Scale of the score ciphertexts: 2^log_scale with a plaintext gallery (every
@@ -65,13 +66,17 @@ double result_scale(const Context& c, const Gallery& g) {
     return g.encrypted ? c.scale * c.scale / (double)c.primes[g.level] : c.scale;
 }
 
-static uint32_t gallery_kind(const Gallery& g) { return g.packing | (g.encrypted ? BM_LAYOUT_ENCRYPTED : 0u); }
+static uint32_t gallery_kind(const Gallery& g) {
+    return g.packing | (g.encrypted ? BM_LAYOUT_ENCRYPTED : 0u) |
+           (g.expansion == BM_EXPAND_HOISTED ? BM_LAYOUT_HOISTED : 0u);
+}
 
 // `kind`: a BM_PACK_* value, or'ed with BM_LAYOUT_ENCRYPTED for a gallery of ciphertexts
 static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uint32_t part, Layout& lo,
                              uint32_t kind = BM_PACK_REAL) {
-    const uint32_t packing = kind & ~BM_LAYOUT_ENCRYPTED;
+    const uint32_t packing = kind & ~(BM_LAYOUT_ENCRYPTED | BM_LAYOUT_HOISTED);
     lo.encrypted = (kind & BM_LAYOUT_ENCRYPTED) != 0;
+    lo.hoisted = (kind & BM_LAYOUT_HOISTED) != 0;
     if (!is_pow2(dim) || !is_pow2(part) || part > dim || dim > c.slots)
         return fail(BM_E_DIM, "dim and part size must be powers of two with part <= dim <= N/2");
     if (packing != BM_PACK_REAL && packing != BM_PACK_COMPLEX) return fail(BM_E_ARG, "unknown slot packing");
@@ -86,6 +91,7 @@ static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uin
     lo.tiled = c.L >= 3;                    // Algorithm 1 (1 level) + HE-C^3 (1) + compression (1)
     lo.level = lo.tiled ? c.L - 1 : c.L;    // level of the query parts entering HE-C^3
     lo.compress = lo.level >= 2;            // a level left after HE-C^3 for the mask
+    if (!lo.tiled) lo.hoisted = false;      // no Algorithm 1 on the server
     lo.n_out = lo.compress ? (lo.groups + part - 1) / part : lo.groups;
     return BM_OK;
 }
@@ -93,7 +99,9 @@ static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uin
 // left-rotation amounts the schedule uses (negative = right)
 static std::vector<int32_t> schedule_rotations(const Context& c, const Layout& lo, uint32_t part) {
     std::vector<int32_t> r;
-    if (lo.tiled)
+    if (lo.tiled && lo.hoisted)
+        for (uint32_t j = 1; j < lo.n_in; j++) r.push_back((int32_t)(part * j));
+    else if (lo.tiled)
         for (uint32_t j = 0; (1u << j) < lo.n_in; j++) r.push_back((int32_t)(part << j));
     for (uint32_t t = 0; (1u << t) < part; t++) r.push_back((int32_t)(1u << t));
     if (lo.compress)
@@ -311,7 +319,7 @@ bm_status bm_keygen(bm_context* ctxh, uint64_t seed, uint32_t dim, uint32_t part
 bm_status bm_keygen_ex(bm_context* ctxh, uint64_t seed, uint32_t dim, uint32_t part_size, uint32_t flags,
                        bm_secret_key** sk_out, bm_public_key** pk_out, bm_eval_keys** evk_out) {
     if (!ctxh || !sk_out || !pk_out || !evk_out) return fail(BM_E_ARG, "null argument");
-    if (flags & ~(uint32_t)BM_KEYS_ENCRYPTED_GALLERY) return fail(BM_E_ARG, "unknown key-set flags");
+    if (flags & ~(uint32_t)(BM_KEYS_ENCRYPTED_GALLERY | BM_KEYS_HOISTED)) return fail(BM_E_ARG, "unknown key-set flags");
     Context& c = ctxh->c;
     Layout lo;
     BM_TRY(make_layout(c, 1, dim, part_size, lo));
@@ -399,6 +407,8 @@ bm_status bm_keygen_ex(bm_context* ctxh, uint64_t seed, uint32_t dim, uint32_t p
         return true;
     };
     std::vector<int32_t> rots = schedule_rotations(c, lo, part_size);
+    if ((flags & BM_KEYS_HOISTED) && lo.tiled)
+        for (uint32_t j = 1; j < lo.n_in; j++) rots.push_back((int32_t)(part_size * j));   // hoisted Algorithm 1
     if (flags & BM_KEYS_ENCRYPTED_GALLERY)
         for (uint32_t b = 0; (1u << b) < c.slots; b++)
             if ((1u << b) >= part_size) rots.push_back(-(int32_t)(1u << b));   // enrollment shifts
@@ -537,8 +547,9 @@ static bm_status gallery_alloc(Context& c, const Layout& lo, uint64_t n_ids, uin
     gh->ref.attach(&c);
     Gallery& g = gh->g;
     g.ctx = &c;
-    g.packing = packing & ~BM_LAYOUT_ENCRYPTED;
+    g.packing = packing & ~(BM_LAYOUT_ENCRYPTED | BM_LAYOUT_HOISTED);
     g.encrypted = lo.encrypted;
+    g.expansion = lo.hoisted ? BM_EXPAND_HOISTED : BM_EXPAND_DOUBLING;
     g.id = c.next_id++;
     g.n_ids = n_ids;
     g.dim = dim;
@@ -918,6 +929,18 @@ bm_status bm_gallery_import_encrypted(bm_context* ctxh, const uint64_t* cts, con
     return BM_OK;
 }
 
+bm_status bm_gallery_set_expansion(bm_gallery* gh, uint32_t mode) {
+    if (!gh) return fail(BM_E_ARG, "null gallery");
+    if (mode != BM_EXPAND_DOUBLING && mode != BM_EXPAND_HOISTED) return fail(BM_E_ARG, "unknown expansion");
+    Gallery& g = gh->g;
+    if (!g.tiled) return fail(BM_E_ARG, "the gallery's queries arrive expanded (no Algorithm 1 on the server)");
+    if (g.expansion != mode) {
+        drop_plans(*g.ctx, g.id);
+        g.expansion = mode;
+    }
+    return BM_OK;
+}
+
 bm_status bm_gallery_info(const bm_gallery* gh, uint32_t* encrypted, uint32_t* packing) {
     if (!gh) return fail(BM_E_ARG, "null gallery");
     if (encrypted) *encrypted = gh->g.encrypted;
@@ -1080,8 +1103,10 @@ struct Plan {
     Context* c = nullptr;
     uint64_t gid = 0, kid = 0;
     uint32_t Q = 0, ncts = 0, chunk = 0, n_out = 0;
+    uint32_t qe = 0;                       // queries per Algorithm-1 chunk (hoisted form)
     std::vector<void*> bufs;
     uint64_t *qin = nullptr, *t0 = nullptr, *T = nullptr, *accA = nullptr, *accB = nullptr, *accT = nullptr;
+    uint64_t *ext = nullptr, *R = nullptr; // hoisted Algorithm 1: query extensions, rotated queries
     uint64_t *scratch = nullptr, *result = nullptr;
     size_t scratch_words = 0, result_words = 0, qin_words = 0;
     PtrArena arena;
@@ -1117,7 +1142,7 @@ void drop_plans(Context& c, uint64_t id) {
 // launch pass, where its plaintexts live.
 struct SchedView {
     uint32_t n_in = 0, part = 0, level = 0, groups = 0;
-    bool tiled = true, compress = true, encrypted = false;
+    bool tiled = true, compress = true, encrypted = false, hoisted = false;
     const uint64_t* d_pts = nullptr;
     const uint64_t* d_masks = nullptr;
     const uint64_t* d_cmask = nullptr;
@@ -1132,6 +1157,7 @@ static SchedView view_of(const Gallery& g) {
     v.tiled = g.tiled;
     v.compress = g.compress;
     v.encrypted = g.encrypted;
+    v.hoisted = g.tiled && g.expansion == BM_EXPAND_HOISTED;
     v.d_pts = g.d_pts;
     v.d_masks = g.d_masks;
     v.d_cmask = g.d_cmask;
@@ -1147,6 +1173,7 @@ static SchedView view_of(const Layout& lo, uint32_t part) {
     v.tiled = lo.tiled;
     v.compress = lo.compress;
     v.encrypted = lo.encrypted;
+    v.hoisted = lo.hoisted;
     return v;
 }
 
@@ -1170,6 +1197,7 @@ struct MatchRun {
     }
     size_t cw(uint32_t level) const { return ct_words(c, level); }
     const uint64_t* key(int32_t rot) const {
+        if (!ek) return nullptr;                // schedule model: no keys
         auto it = ek->keys.find(galois_of(c, rot));
         return it == ek->keys.end() ? nullptr : it->second;
     }
@@ -1217,6 +1245,38 @@ struct MatchRun {
         check(mul_plain(c, level, (uint32_t)in.size(), din, dpt, dout, s));
     }
 
+    // hoisted Algorithm 1: basis extension of the queries' c1 into pl.ext
+    void modup_batch(uint32_t level, const std::vector<uint64_t*>& in) {
+        auto din = pl.arena.list(in);
+        record(BM_OP_MODUP, level, in.size());
+        if (!pl.arena.live) {
+            need_scratch(ks_modup_scratch_words(c, level, (uint32_t)in.size()));
+            return;
+        }
+        check(ks_modup_hoisted(c, level, (uint32_t)in.size(), din, pl.ext, pl.scratch, s));
+    }
+    // ... rotations of the extended queries (per element: extension, source, key, Galois element)
+    void hoisted_batch(uint32_t level, const std::vector<uint64_t*>& ext_of, const std::vector<uint64_t*>& src,
+                       const std::vector<uint64_t*>& keys, const std::vector<uint64_t*>& gal,
+                       const std::vector<uint64_t*>& out) {
+        auto de = pl.arena.list(ext_of);
+        auto ds = pl.arena.list(src);
+        auto dk = pl.arena.list(keys);
+        auto dg = pl.arena.list(gal);
+        auto dout = pl.arena.list(out);
+        for (size_t b0 = 0; b0 < out.size(); b0 += ksb) {
+            const uint32_t E = (uint32_t)std::min<size_t>(ksb, out.size() - b0);
+            record(BM_OP_ROT_HOISTED, level, E);
+            if (!pl.arena.live) {
+                need_scratch(ks_hoisted_scratch_words(c, level, E));
+                continue;
+            }
+            check(ks_rotate_hoisted(c, level, E, (const uint64_t* const*)(de + b0), (const uint64_t* const*)(ds + b0),
+                                    (const uint64_t* const*)(dk + b0), (const uint64_t*)(dg + b0), dout + b0,
+                                    pl.scratch, s));
+        }
+    }
+
     // a0..a6 on the plan's buffers; with arena.live == false only the pointer
     // arrays are collected, the scratch sized and (with rec) the launches listed.
     void schedule() {
@@ -1226,8 +1286,39 @@ struct MatchRun {
         // a0: queries into the NTT domain
         record(BM_OP_NTT, 0, (size_t)Q * pl.ncts * 2 * (c.L + 1));
         if (pl.arena.live) check(ntt_forward(c, packed(c, pl.qin, Q * pl.ncts * 2, c.L + 1), s));
-        // Algorithm 1: C_out,i = Res(Mul(P)(C_in, mask_i)), then log2(N_in) rotate-and-add by part*2^(j-1)
-        if (g.tiled) {
+        // Algorithm 1, hoisted form: T_i = Res(sum_j Rot(ct, j*part) * mask_((i-j) mod N_in)),
+        // the N_in - 1 rotations of each query sharing one basis extension; queries in chunks of pl.qe
+        if (g.tiled && g.hoisted) {
+            const size_t ew = ks_ext_words(c, c.L);
+            for (uint32_t qb = 0; qb < Q; qb += pl.qe) {
+                const uint32_t nq = std::min(pl.qe, Q - qb);
+                std::vector<uint64_t*> qs, ext_of, src, keys, gal, out, R, o0, o1;
+                for (uint32_t q = 0; q < nq; q++) qs.push_back(pl.qin + (size_t)(qb + q) * cw(c.L));
+                if (n_in > 1) modup_batch(c.L, qs);
+                for (uint32_t q = 0; q < nq; q++)
+                    for (uint32_t j = 1; j < n_in; j++) {
+                        ext_of.push_back(pl.ext + (size_t)q * ew);
+                        src.push_back(qs[q]);
+                        keys.push_back(const_cast<uint64_t*>(key((int32_t)(part * j))));
+                        gal.push_back(reinterpret_cast<uint64_t*>((uintptr_t)galois_of(c, (int32_t)(part * j))));
+                        out.push_back(pl.R + ((size_t)q * n_in + j) * cw(c.L));
+                    }
+                hoisted_batch(c.L, ext_of, src, keys, gal, out);
+                for (uint32_t q = 0; q < nq; q++)
+                    for (uint32_t j = 0; j < n_in; j++)
+                        R.push_back(j == 0 ? qs[q] : pl.R + ((size_t)q * n_in + j) * cw(c.L));
+                auto dR = pl.arena.list(R);
+                record(BM_OP_MAC_CIRC, c.L, n_in, nq, n_in);
+                if (pl.arena.live) check(mac_circ(c, c.L, nq, n_in, (const uint64_t* const*)dR, g.d_masks, pl.t0, s));
+                for (uint32_t q = 0; q < nq; q++)
+                    for (uint32_t i = 0; i < n_in; i++) {
+                        o0.push_back(pl.t0 + ((size_t)q * n_in + i) * cw(c.L));
+                        o1.push_back(pl.T + ((size_t)(qb + q) * n_in + i) * cw(lg));
+                    }
+                rescale_batch(c.L, o0, o1);
+            }
+        } else if (g.tiled) {
+            // Algorithm 1: C_out,i = Res(Mul(P)(C_in, mask_i)), then log2(N_in) rotate-and-add by part*2^(j-1)
             std::vector<uint64_t*> in, pt, o0, o1;
             for (uint32_t q = 0; q < Q; q++)
                 for (uint32_t i = 0; i < n_in; i++) {
@@ -1319,6 +1410,35 @@ static void plan_dims(const Context& c, const SchedView& g, uint32_t n_out, uint
     pl.chunk = std::min(chunk, g.groups);
     pl.qin_words = (size_t)Q * pl.ncts * ct_words(c, c.L);
     pl.result_words = (size_t)Q * n_out * ct_words(c, 0);
+    // hoisted Algorithm 1: rotated copies and products of a chunk of queries within ~4 GiB
+    pl.qe = Q;
+    if (g.tiled && g.hoisted) {
+        const size_t per_q = ((size_t)2 * g.n_in * ct_words(c, c.L) + ks_ext_words(c, c.L)) * 8;
+        pl.qe = (uint32_t)std::min<size_t>(Q, std::max<size_t>(1, ((size_t)4 << 30) / per_q));
+    }
+}
+
+// The plan's device buffers: field and words, the same list for the allocation
+// (plan_build) and the host-side estimate (plan_shape).
+struct BufSpec {
+    uint64_t** field;
+    size_t words;
+};
+static std::vector<BufSpec> plan_buffers(const Context& c, const SchedView& g, Plan& pl) {
+    const uint32_t Q = pl.Q, lg = g.level;
+    std::vector<BufSpec> b{{&pl.qin, pl.qin_words}, {&pl.result, pl.result_words}};
+    if (g.tiled) {
+        b.push_back({&pl.t0, (size_t)pl.qe * g.n_in * ct_words(c, c.L)});
+        b.push_back({&pl.T, (size_t)Q * g.n_in * ct_words(c, lg)});
+        if (g.hoisted) {
+            b.push_back({&pl.ext, (size_t)pl.qe * ks_ext_words(c, c.L)});
+            b.push_back({&pl.R, (size_t)pl.qe * g.n_in * ct_words(c, c.L)});
+        }
+    }
+    b.push_back({&pl.accA, (size_t)Q * pl.chunk * ct_words(c, lg)});
+    b.push_back({&pl.accB, (size_t)Q * pl.chunk * ct_words(c, lg - 1)});
+    if (g.encrypted) b.push_back({&pl.accT, (size_t)Q * pl.chunk * ct_words(c, lg)});
+    return b;
 }
 
 static size_t words_bytes(size_t w) { return std::max<size_t>(w, 1) * 8; }
@@ -1332,10 +1452,8 @@ static size_t plan_shape(const Context& c, const SchedView& g, uint32_t n_out, u
     MatchRun run(c, g, nullptr, pl);
     run.rec = rec;
     run.schedule();
-    size_t bytes = words_bytes(pl.qin_words) + words_bytes(pl.result_words);
-    if (g.tiled) bytes += words_bytes((size_t)Q * g.n_in * ct_words(c, c.L)) + words_bytes((size_t)Q * g.n_in * ct_words(c, g.level));
-    bytes += words_bytes((size_t)Q * pl.chunk * ct_words(c, g.level)) + words_bytes((size_t)Q * pl.chunk * ct_words(c, g.level - 1));
-    if (g.encrypted) bytes += words_bytes((size_t)Q * pl.chunk * ct_words(c, g.level));
+    size_t bytes = 0;
+    for (const BufSpec& b : plan_buffers(c, g, pl)) bytes += words_bytes(b.words);
     bytes += words_bytes(pl.scratch_words) + words_bytes(pl.arena.host.size());
     return bytes;
 }
@@ -1368,15 +1486,8 @@ bm_status plan_build(Context& c, const Gallery& g, const EvalKeys& ek, uint32_t 
     pl->gid = g.id;
     pl->kid = ek.id;
     plan_dims(c, v, lo.n_out, Q, *pl);
-    const uint32_t lg = g.level;
-    bool ok = pl->alloc(pl->qin, pl->qin_words) && pl->alloc(pl->result, pl->result_words);
-    if (g.tiled) {
-        ok = ok && pl->alloc(pl->t0, (size_t)Q * g.n_in * ct_words(c, c.L));
-        ok = ok && pl->alloc(pl->T, (size_t)Q * g.n_in * ct_words(c, lg));
-    }
-    ok = ok && pl->alloc(pl->accA, (size_t)Q * pl->chunk * ct_words(c, lg));
-    ok = ok && pl->alloc(pl->accB, (size_t)Q * pl->chunk * ct_words(c, lg - 1));
-    if (g.encrypted) ok = ok && pl->alloc(pl->accT, (size_t)Q * pl->chunk * ct_words(c, lg));
+    bool ok = true;
+    for (const BufSpec& b : plan_buffers(c, v, *pl)) ok = ok && pl->alloc(*b.field, b.words);
     if (!ok) return fail(BM_E_OOM, "match workspace allocation failed");
     MatchRun run(c, v, &ek, *pl);
     run.schedule();                                     // dry pass

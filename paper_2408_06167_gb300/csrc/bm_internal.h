@@ -170,6 +170,7 @@ struct Gallery {
     bool compress = true;                     // outputs are masked and packed
     uint32_t packing = BM_PACK_REAL;          // BM_PACK_COMPLEX: a second identity in the imaginary parts
     bool encrypted = false;                   // d_pts holds ciphertexts [groups][n_in][2][level+1][N]
+    uint32_t expansion = BM_EXPAND_DOUBLING;  // form of Algorithm 1 (BM_EXPAND_*)
     uint64_t* d_pts = nullptr;                // [groups][n_in][level+1][N] NTT + Montgomery
     uint64_t* d_masks = nullptr;              // [n_in][L+1][N] Algorithm-1 masks (tiled only)
     uint64_t* d_cmask = nullptr;              // [level][N] compression mask at level-1
@@ -322,6 +323,20 @@ bool ks_has_wide(const Context& c);
 cudaError_t ks_rotate_fused_shape(const Context& c, bool wide, const uint64_t* key, uint64_t galois,
                                   uint32_t level, uint32_t B, uint64_t* const* d_in, uint64_t* const* d_out,
                                   uint64_t* const* d_add, uint64_t* scratch, cudaStream_t s);
+// Hoisted rotations (rings 2^12 and 2^16): the basis extension of c1 of B ciphertexts
+// at `level`, every extended limb in NTT order -- ext [B][nd][nlx][N] (ks_ext_words
+// per ciphertext; scratch ks_modup_scratch_words) -- then E rotations, element e
+// rotating src[e] by Galois element gal_of[e] with key key_of[e] from its
+// extension ext_of[e] into out[e] (scratch ks_hoisted_scratch_words).  The same
+// messages as ks_rotate; the bits differ (the automorphism follows ModUp).
+size_t ks_ext_words(const Context& c, uint32_t level);
+size_t ks_modup_scratch_words(const Context& c, uint32_t level, uint32_t B);
+size_t ks_hoisted_scratch_words(const Context& c, uint32_t level, uint32_t E);
+cudaError_t ks_modup_hoisted(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in, uint64_t* ext,
+                             uint64_t* scratch, cudaStream_t s);
+cudaError_t ks_rotate_hoisted(const Context& c, uint32_t level, uint32_t E, const uint64_t* const* ext_of,
+                              const uint64_t* const* src, const uint64_t* const* key_of, const uint64_t* gal_of,
+                              uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s);
 // rescale in three fused kernels (rings 2^12 and 2^16)
 cudaError_t rescale_fused(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,
                           uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s);
@@ -339,6 +354,9 @@ cudaError_t mul_plain(const Context& c, uint32_t level, uint32_t B, uint64_t* co
 // acc[q][g] = sum_i T[q][i] * P[g][i]  (T: [Q][n_in][2][level+1][N], P: [G][n_in][level+1][N])
 cudaError_t mac(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32_t n_in,
                 const uint64_t* T, const uint64_t* P, uint64_t* acc, cudaStream_t s);
+// hoisted Algorithm 1: t0[q][i] = sum_j R[q*n_in + j] * masks[(i - j) mod n_in] (t0 [Q][n_in] cts)
+cudaError_t mac_circ(const Context& c, uint32_t level, uint32_t Q, uint32_t n_in, const uint64_t* const* R,
+                     const uint64_t* masks, uint64_t* t0, cudaStream_t s);
 // dst[t] += sum of src[off[t] .. off[t+1]) (ciphertexts at `level`; off and the lists on the device)
 cudaError_t accumulate(const Context& c, uint32_t level, uint32_t n_targets, uint64_t* const* dst,
                        const uint64_t* const* src, const uint32_t* off, uint32_t n_src, cudaStream_t s);

@@ -254,6 +254,95 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
 }
 
 // ---------------------------------------------------------------------------
+// Hoisted rotations (several rotations of one ciphertext share its basis
+// extension).  F3r: grid (B * nd * nlx, N1 / R): forward row pass, in place, of
+// the converted limbs F3 left column-transformed, so that every extended limb
+// of ext is in NTT order (the digit's own limbs already are, from F1).
+// ---------------------------------------------------------------------------
+template <int LA, int LB, int LT, int R>
+__global__ void __launch_bounds__(R * (1 << (LB - LT)))
+    k_ks_f3r(uint64_t* __restrict__ ext, const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L) {
+    constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>(), LOGN = LA + LB, N = 1 << LOGN;
+    __shared__ uint64_t sm[R * S];
+    __shared__ ulonglong2 tws[row_tw_entries<LB, R>()];
+    const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
+    const uint32_t nd = kc->nd, nlx = kc->nlx;
+    const uint32_t jj = blockIdx.x % nlx, d = (blockIdx.x / nlx) % nd;
+    if (jj >= kc->dstart[d] && jj < kc->dstart[d] + kc->dsz[d]) return;   // own limb: NTT form already
+    const int pi = ext_prime(jj, l1, L);
+    const uint64_t q = tab.q[pi], q2 = 2 * q;
+    const int row = blockIdx.y * R + jr;
+    uint64_t* e = ext + (size_t)blockIdx.x * N + (size_t)row * M;
+    stage_row_twiddles<LA, LB, R, R * TH>(tws, tab.tw[pi], blockIdx.y * R);
+    uint64_t v[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = e[first_idx<LB, LT>(t, k)];
+    tw_wait();
+    nttr::fwd_pass<LB, LT>(v, SubMem{sm + jr * S, 1}, tws, RowBase<R>{jr}, t, q, q2);
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = nttr::reduce4(v[k], q, q2);
+    nttr::store_last<LB, LT>(v, e, t);
+}
+
+// F4h: grid (E * nlx, N1 / R).  Element e: acc[e] = sum_d sigma_e(ext_of[e]_d) * key_e,d
+// -- the Galois image of an extended limb is a permutation of its NTT slots --
+// then, for the special-prime limbs, the inverse row pass (as F4).
+template <int LA, int LB, int LT, int R>
+__global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
+    k_ks_f4h(const uint64_t* const* ext_of, const uint64_t* const* key_of, const uint64_t* gal_of,
+             uint64_t* __restrict__ acc, const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L,
+             uint32_t nb) {
+    constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>(), LOGN = LA + LB, N = 1 << LOGN;
+    constexpr int TWN = row_tw_entries<LB, R>();
+    __shared__ uint64_t sm[R * S];
+    __shared__ ulonglong2 twi[TWN];
+    const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
+    const SubMem sr{sm + jr * S, 1};
+    const uint32_t nd = kc->nd, nlx = kc->nlx;
+    const uint32_t e = blockIdx.x / nlx, jj = blockIdx.x % nlx;
+    const int pi = ext_prime(jj, l1, L);
+    const uint64_t q = tab.q[pi], qn = tab.qneg[pi], q2 = 2 * q;
+    const uint32_t galois = (uint32_t)gal_of[e];
+    const uint64_t* key = key_of[e];
+    const uint64_t* ext = ext_of[e];
+    const int row = blockIdx.y * R + jr;
+    const size_t roff = (size_t)row * M;
+    if (jj >= l1) stage_row_twiddles<LA, LB, R, R * TH>(twi, tab.itw[pi], blockIdx.y * R);
+    uint32_t src[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) src[k] = perm_src((uint32_t)(roff + last_idx<LB, LT>(t, k)), LOGN, galois);
+    uint64_t v[K];
+#pragma unroll 1
+    for (uint32_t comp = 0; comp < 2; comp++) {
+#pragma unroll
+        for (int k = 0; k < K; k++) v[k] = 0;
+#pragma unroll 1
+        for (uint32_t d = 0; d < nd; d++) {
+            const uint64_t* x = ext + ((size_t)d * nlx + jj) * N;
+            uint64_t kv[K];
+            nttr::load_last<LB, LT>(kv, key + ((size_t)(d * 2 + comp) * nb + pi) * N + roff, t);
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const uint64_t y = v[k] + mont_lazy(x[src[k]], kv[k], q, qn);
+                v[k] = y >= q2 ? y - q2 : y;
+            }
+        }
+        if (jj < l1) {
+#pragma unroll
+            for (int k = 0; k < K; k++) v[k] = reduce2(v[k], q);
+            nttr::relayout<LB, LT, LB / LT - 1, 0>(v, sr, t);
+        } else {
+            if (comp == 0) tw_wait();
+            nttr::inv_pass<LB, LT>(v, sr, twi, RowBase<R>{jr}, t, q, q2);
+        }
+        uint64_t* o = acc + (((size_t)e * 2 + comp) * nlx + jj) * N + roff;
+#pragma unroll
+        for (int k = 0; k < K; k++) o[first_idx<LB, LT>(t, k)] = v[k];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // F5: grid (B * 2, N2 / C).  conv = Conv_{P -> Q_l}(acc's special-prime limbs).
 // ---------------------------------------------------------------------------
 template <int LA, int LB, int LT, int C>
@@ -313,12 +402,16 @@ template <int LA, int LB, int LT, int R>
 __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 3)
     k_ks_f6(const uint64_t* __restrict__ conv, const uint64_t* __restrict__ acc, const uint64_t* __restrict__ X0,
             uint64_t* const* out, uint64_t* const* add, const KsLevelConst* __restrict__ kc, DevTables tab,
-            uint32_t l1, uint32_t galois) {
+            uint32_t l1, uint32_t galois, const uint64_t* const* c0_of, const uint64_t* gal_of) {
     constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>(), LOGN = LA + LB, N = 1 << LOGN;
     __shared__ uint64_t sm[R * S];
     __shared__ ulonglong2 tws[row_tw_entries<LB, R>()];
     const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
     const uint32_t b = blockIdx.x / l1, j = blockIdx.x % l1;
+    // hoisted rotations: each element has its own Galois element and reads sigma(c0)
+    // from its source ciphertext (NTT form) instead of the copy X0
+    if (gal_of) galois = (uint32_t)gal_of[b];
+    const uint64_t* x0 = c0_of ? c0_of[b] + (size_t)j * N : X0 + ((size_t)b * l1 + j) * N;
     const uint32_t nlx = kc->nlx;
     const int row = blockIdx.y * R + jr;
     const size_t roff = (size_t)row * M;
@@ -343,8 +436,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 3)
         for (int k = 0; k < K; k++) {
             const int c = last_idx<LB, LT>(t, k);
             uint64_t o = shoup(subm(av[k], nttr::reduce4(v[k], q, q2), q), pinv.x, pinv.y, q);
-            if (comp == 0)
-                o = addm(o, X0[((size_t)b * l1 + j) * N + perm_src((uint32_t)(roff + c), LOGN, galois)], q);
+            if (comp == 0) o = addm(o, x0[perm_src((uint32_t)(roff + c), LOGN, galois)], q);
             if (add) o = addm(o, ad[k], q);
             v[k] = o;
         }
@@ -535,12 +627,124 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
     {
         ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * B * l1 * (2 + 2 + 1 + 2 + (d_add ? 2 : 0)), bf_r * B * 2 * l1);
         k_ks_f6<LA, LB, LT, R><<<dim3(B * l1, N1 / R), tr, 0, s>>>(conv, acc, X0, d_out, d_add, kc, c.tab, l1,
-                                                                     (uint32_t)galois);
+                                                                     (uint32_t)galois, nullptr, nullptr);
+    }
+    return cudaGetLastError();
+}
+
+// ModUp of c1 for B ciphertexts, every extended limb in NTT order: ext [B][nd][nlx][N].
+// Scratch: X0, X1 ([B][l1][N] each; X0 receives an unused copy of c0).
+template <int LA, int LB, int LT, int C, int R>
+cudaError_t ks_modup_launch(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in, uint64_t* ext,
+                            uint64_t* scratch, cudaStream_t s) {
+    constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
+    const KsLevelConst& K = c.h_ksc[level];
+    const uint32_t l1 = level + 1, nd = K.nd, nlx = K.nlx;
+    const KsLevelConst* kc = c.d_ksc + level;
+    uint64_t* X0 = scratch;
+    uint64_t* X1 = X0 + (size_t)B * l1 * N;
+    const int tr = R * (1 << (LB - LT)), tc = C * (1 << (LA - LT));
+    const size_t col_smem = 8 * col_smem_words<LA, LT, C>();
+    static bool attrs = [&] {
+        cudaFuncSetAttribute(k_ks_f3<LA, LB, LT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem);
+        return true;
+    }();
+    (void)attrs;
+    const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;
+    uint32_t targets = 0, gathers = 0;
+    for (uint32_t d = 0; d < nd; d++) {
+        targets += nlx - K.dsz[d];
+        gathers += K.dsz[d] * (nlx - K.dsz[d]);
+    }
+    {
+        ProfScope ps(BM_KERNEL_NTT, s, lw * B * l1 * 6, bf_r * B * l1);
+        k_ks_f1<LA, LB, LT, R><<<dim3(B * l1, N1 / R), tr, 0, s>>>(d_in, X0, X1, ext, kc, c.tab, l1, 1u);
+    }
+    LimbBatch xb{X1, B, (uint64_t)l1 * N, 0, l1, 0};
+    for (uint32_t k = 0; k < l1; k++) xb.set(k, k);
+    cudaError_t e = ntt_col_inverse(c, xb, s);
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope ps(BM_KERNEL_MODUP, s, lw * B * (gathers + targets), bf_c * B * targets);
+        k_ks_f3<LA, LB, LT, C><<<dim3(B * nd, N2 / C), tc, col_smem, s>>>(X1, ext, kc, c.tab, l1, c.L, 1u);
+    }
+    {
+        ProfScope ps(BM_KERNEL_MODUP, s, lw * B * targets * 2, bf_r * B * targets);
+        k_ks_f3r<LA, LB, LT, R><<<dim3(B * nd * nlx, N1 / R), tr, 0, s>>>(ext, kc, c.tab, l1, c.L);
+    }
+    return cudaGetLastError();
+}
+
+// E hoisted rotations: out[e] = Rot(src[e]) by Galois element gal_of[e] with key key_of[e],
+// from the extension ext_of[e] of src[e]'s c1.  Scratch: acc, conv.
+template <int LA, int LB, int LT, int C, int R>
+cudaError_t ks_hoisted_launch(const Context& c, uint32_t level, uint32_t E, const uint64_t* const* ext_of,
+                              const uint64_t* const* src, const uint64_t* const* key_of, const uint64_t* gal_of,
+                              uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s) {
+    constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
+    const KsLevelConst& K = c.h_ksc[level];
+    const uint32_t l1 = level + 1, nd = K.nd, nlx = K.nlx, alpha = c.alpha;
+    const KsLevelConst* kc = c.d_ksc + level;
+    uint64_t* acc = scratch;
+    uint64_t* conv = acc + (size_t)E * 2 * nlx * N;
+    const int tr = R * (1 << (LB - LT)), tc = C * (1 << (LA - LT));
+    const size_t col_smem = 8 * col_smem_words<LA, LT, C>();
+    static bool attrs = [&] {
+        cudaFuncSetAttribute(k_ks_f5<LA, LB, LT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem);
+        return true;
+    }();
+    (void)attrs;
+    const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;
+    {
+        ProfScope ps(BM_KERNEL_KS_IP, s, lw * nlx * ((double)E * nd + 2.0 * nd * E + 2.0 * E), bf_r * E * 2.0 * alpha);
+        k_ks_f4h<LA, LB, LT, R><<<dim3(E * nlx, N1 / R), tr, 0, s>>>(ext_of, key_of, gal_of, acc, kc, c.tab, l1, c.L,
+                                                                       c.nb);
+    }
+    {
+        ProfScope ps(BM_KERNEL_MODDOWN, s, lw * E * 2 * (alpha + l1), bf_c * E * 2 * (alpha + l1));
+        k_ks_f5<LA, LB, LT, C><<<dim3(E * 2, N2 / C), tc, col_smem, s>>>(acc, conv, kc, c.tab, l1, c.L, alpha);
+    }
+    {
+        ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * E * l1 * 7, bf_r * E * 2 * l1);
+        k_ks_f6<LA, LB, LT, R><<<dim3(E * l1, N1 / R), tr, 0, s>>>(conv, acc, nullptr, d_out, nullptr, kc, c.tab, l1,
+                                                                     0u, src, gal_of);
     }
     return cudaGetLastError();
 }
 
 }  // namespace
+
+size_t ks_modup_scratch_words(const Context& c, uint32_t level, uint32_t B) {
+    return (size_t)2 * B * (level + 1) * c.n;
+}
+size_t ks_ext_words(const Context& c, uint32_t level) {
+    size_t nd = 0;   // digits with a limb at or below the level (host-only contexts have no constants)
+    for (auto& d : c.digits) nd += (!d.empty() && d[0] <= level);
+    return nd * (level + 1 + c.alpha) * c.n;
+}
+size_t ks_hoisted_scratch_words(const Context& c, uint32_t level, uint32_t E) {
+    const size_t nlx = level + 1 + c.alpha;
+    return (size_t)E * c.n * (2 * nlx + 2 * (level + 1));
+}
+
+cudaError_t ks_modup_hoisted(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in, uint64_t* ext,
+                             uint64_t* scratch, cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    if (c.log_n == 16) return ks_modup_launch<8, 8, 2, 2, 2>(c, level, B, d_in, ext, scratch, s);
+    if (c.log_n == 12) return ks_modup_launch<6, 6, 2, 8, 8>(c, level, B, d_in, ext, scratch, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t ks_rotate_hoisted(const Context& c, uint32_t level, uint32_t E, const uint64_t* const* ext_of,
+                              const uint64_t* const* src, const uint64_t* const* key_of, const uint64_t* gal_of,
+                              uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s) {
+    if (E == 0) return cudaSuccess;
+    if (c.log_n == 16)
+        return ks_hoisted_launch<8, 8, 2, 2, 2>(c, level, E, ext_of, src, key_of, gal_of, d_out, scratch, s);
+    if (c.log_n == 12)
+        return ks_hoisted_launch<6, 6, 2, 8, 8>(c, level, E, ext_of, src, key_of, gal_of, d_out, scratch, s);
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t rescale_fused(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,
                           uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s) {

@@ -153,6 +153,14 @@ __device__ __forceinline__ int last_idx(int t, int k) { return pidx<P, LT, P / L
 // LT), thread t holds the 2^LT consecutive words at t * 2^LT: moved as 16-byte
 // vectors (the row is 256-byte aligned, so every vector is 16-byte aligned).
 template <int P, int LT>
+__device__ __forceinline__ void store_last(const uint64_t (&v)[1 << LT], uint64_t* __restrict__ row, int t) {
+    static_assert(P % LT == 0, "last phase must start at a multiple of the thread's run");
+    ulonglong2* p = reinterpret_cast<ulonglong2*>(row + (t << LT));
+#pragma unroll
+    for (int k = 0; k < (1 << LT) / 2; k++) p[k] = make_ulonglong2(v[2 * k], v[2 * k + 1]);
+}
+
+template <int P, int LT>
 __device__ __forceinline__ void load_last(uint64_t (&v)[1 << LT], const uint64_t* __restrict__ row, int t) {
     static_assert(P % LT == 0, "last phase must start at a multiple of the thread's run");
     const ulonglong2* p = reinterpret_cast<const ulonglong2*>(row + (t << LT));

@@ -104,7 +104,8 @@ double interp(const double* u, const double* t, double x) {
 double launch_us(const bm_op_costs& k, const bm_op_launch& l) {
     double units = l.count;
     uint32_t level = l.level;
-    if (l.op == BM_OP_MAC || l.op == BM_OP_MAC_CT) units = std::ceil(l.queries / 4.0) * l.count * l.parts;
+    if (l.op == BM_OP_MAC || l.op == BM_OP_MAC_CT || l.op == BM_OP_MAC_CIRC)
+        units = std::ceil(l.queries / 4.0) * l.count * l.parts;
     if (l.op == BM_OP_NTT || l.op == BM_OP_INTT || l.op == BM_OP_COPY) level = 0;
     if (l.op >= BM_OP_KINDS || level >= BM_MAX_Q) return 0.0;
     return interp(k.units[l.op], k.t_us[l.op][level], units);
@@ -214,7 +215,8 @@ bm_status bm_measure_op_costs(bm_context* ctxh, bm_op_costs* out) {
     std::memset(out, 0, sizeof(*out));
     for (int op = 0; op < BM_OP_KINDS; op++)
         for (int k = 0; k < BM_COST_POINTS; k++)
-            out->units[op][k] = (op == BM_OP_MAC || op == BM_OP_MAC_CT ? (double)kMacParts : 1.0) * (double)(1u << k);
+            out->units[op][k] = op == BM_OP_MAC_CIRC ? (double)(1u << k) * (double)(1u << k)   // 4 queries x (2^k)^2
+                                : (op == BM_OP_MAC || op == BM_OP_MAC_CT ? (double)kMacParts : 1.0) * (double)(1u << k);
     cudaStream_t s = c.stream;
     Timer tm(s);
     const uint32_t L = c.L;
@@ -265,6 +267,51 @@ bm_status bm_measure_op_costs(bm_context* ctxh, bm_op_costs* out) {
             }
             BM_CUDA_TRY(tm.err);
         }
+    }
+    if (ks_fused_supported(c)) {
+        // hoisted Algorithm 1 at the top level: basis extension of 1..128 ciphertexts,
+        // 1..128 rotations from extensions, circulant products of 4 queries x 2^k parts
+        const size_t cw = ct_words(c, L), ew = ks_ext_words(c, L);
+        DevBuf in, outb, ext, scratch, key, masks, t0, plist;
+        BM_CUDA_TRY(in.alloc(cw * kMaxB));
+        BM_CUDA_TRY(outb.alloc(cw * kMaxB));
+        BM_CUDA_TRY(ext.alloc(ew * kMaxB));
+        BM_CUDA_TRY(scratch.alloc(std::max(ks_modup_scratch_words(c, L, kMaxB), ks_hoisted_scratch_words(c, L, kMaxB))));
+        BM_CUDA_TRY(key.alloc((size_t)c.digits.size() * 2 * c.nb * c.n));
+        BM_CUDA_TRY(masks.alloc((size_t)kMaxB * (L + 1) * c.n));
+        BM_CUDA_TRY(t0.alloc((size_t)kMacQ * kMaxB * cw));
+        BM_CUDA_TRY(fill(c, in.p, cw * kMaxB, L + 1, 61, s));
+        BM_CUDA_TRY(fill(c, key.p, key.words, c.nb, 62, s));
+        BM_CUDA_TRY(fill(c, masks.p, masks.words, L + 1, 63, s));
+        // element lists: extension, source, key, Galois element (rotation by one slot), output
+        std::vector<uint64_t*> h;
+        for (uint32_t k = 0; k < kMaxB; k++) h.push_back(ext.p + k * ew);
+        for (uint32_t k = 0; k < kMaxB; k++) h.push_back(in.p + k * cw);
+        for (uint32_t k = 0; k < kMaxB; k++) h.push_back(key.p);
+        for (uint32_t k = 0; k < kMaxB; k++) h.push_back(reinterpret_cast<uint64_t*>((uintptr_t)galois_of(c, 1)));
+        for (uint32_t k = 0; k < kMaxB; k++) h.push_back(outb.p + k * cw);
+        for (uint32_t k = 0; k < kMacQ * kMaxB; k++) h.push_back(in.p + (k % kMaxB) * cw);   // R lists
+        BM_CUDA_TRY(plist.alloc(h.size()));
+        BM_CUDA_TRY(cudaMemcpy(plist.p, h.data(), h.size() * sizeof(void*), cudaMemcpyHostToDevice));
+        uint64_t* const* dl = (uint64_t* const*)plist.p;
+        for (int k = 0; k < BM_COST_POINTS; k++) {
+            const uint32_t B = 1u << k;
+            const int r = reps_for(B);
+            out->t_us[BM_OP_MODUP][L][k] =
+                tm.us([&] { return ks_modup_hoisted(c, L, B, (uint64_t* const*)(dl + kMaxB), ext.p, scratch.p, s); },
+                      2, r);
+            out->t_us[BM_OP_ROT_HOISTED][L][k] = tm.us(
+                [&] {
+                    return ks_rotate_hoisted(c, L, B, (const uint64_t* const*)dl, (const uint64_t* const*)(dl + kMaxB),
+                                             (const uint64_t* const*)(dl + 2 * kMaxB),
+                                             (const uint64_t*)(dl + 3 * kMaxB), dl + 4 * kMaxB, scratch.p, s);
+                },
+                2, r);
+            out->t_us[BM_OP_MAC_CIRC][L][k] = tm.us(
+                [&] { return mac_circ(c, L, kMacQ, B, (const uint64_t* const*)(dl + 5 * kMaxB), masks.p, t0.p, s); },
+                2, r);
+        }
+        BM_CUDA_TRY(tm.err);
     }
     {
         // HE-C^3 products: 4 queries x 8 parts x 1..128 groups, at the levels a

@@ -21,13 +21,15 @@ def octx(name):
     return _CTX[name]
 
 
-def schedule_rotations(ctx, m, s):
+def schedule_rotations(ctx, m, s, hoisted=False):
     """Left rotations the tiled/expanded schedule needs (negative = right)."""
     n_in = m // s
     tiled = ctx.L >= 3
     level = ctx.L - 1 if tiled else ctx.L
     rots = []
-    if tiled:
+    if tiled and hoisted:
+        rots += [s * j for j in range(1, n_in)]
+    elif tiled:
         rots += [s << j for j in range(sch.log2i(n_in))]
     rots += [1 << t for t in range(sch.log2i(s))]
     if level >= 2:
@@ -38,18 +40,20 @@ def schedule_rotations(ctx, m, s):
 class OracleMatch:
     """Keys, gallery plaintexts, query ciphertexts and match outputs from the oracle."""
 
-    def __init__(self, name, m, s, R, n_queries, feats=None, seed=KEY_SEED, complex_pack=False, encrypted=False):
+    def __init__(self, name, m, s, R, n_queries, feats=None, seed=KEY_SEED, complex_pack=False, encrypted=False,
+                 hoisted=False):
         self.ctx = ctx = octx(name)
         self.m, self.s, self.R = m, s, R
         self.complex_pack = complex_pack
         self.encrypted = encrypted
+        self.hoisted = hoisted
         self.n_in = m // s
         self.tiled = ctx.L >= 3
         self.level = ctx.L - 1 if self.tiled else ctx.L
         self.compress = self.level >= 2
         self.feats = wl.gallery(R, m) if feats is None else feats
         self.queries, self.true_ids = wl.queries(self.feats, n_queries)
-        self.sk, self.pk, self.rks = ckks.keygen(ctx, seed, schedule_rotations(ctx, m, s))
+        self.sk, self.pk, self.rks = ckks.keygen(ctx, seed, schedule_rotations(ctx, m, s, hoisted))
         self.ev = ckks.Evaluator(ctx, self.rks, ckks.keygen_relin(ctx, seed, self.sk) if encrypted else None)
         S, L = ctx.slots, ctx.L
         self.groups = sch.n_groups(R, s, S, complex_pack)
@@ -100,7 +104,8 @@ class OracleMatch:
 
     def match(self, cts):
         outs, packed = sch.match(self.ev, cts, self.gal, self.masks, self.cmask, self.m, self.s,
-                                 expanded=not self.tiled, encrypted_gallery=self.encrypted)
+                                 expanded=not self.tiled, encrypted_gallery=self.encrypted,
+                                 hoisted=self.hoisted)
         return self.ct_array(outs), packed
 
     def scores(self, outs_array, packed):

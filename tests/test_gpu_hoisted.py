@@ -1,0 +1,84 @@
+"""Algorithm 1 in hoisted form on the GPU against the oracle: the basis
+extension of each query's c1 computed once, N_in - 1 rotations taken from it
+(the Galois image of each extended limb is a permutation of its NTT slots),
+the circulant mask products and one rescale per part -- bit-exact against the
+oracle's hoisted expansion, then the same HE-C^3 and compression; end to end,
+the scores equal those of the printed (doubling) form within the tolerance."""
+import numpy as np
+import pytest
+
+from helpers_oracle import KEY_SEED, OracleMatch
+from paper_2408_06167_gb300 import workload as wl
+
+pytestmark = pytest.mark.gpu
+
+bm = pytest.importorskip("paper_2408_06167_gb300.binding")
+
+_CTX = {}
+
+
+def gctx(name):
+    if name not in _CTX:
+        _CTX[name] = bm.bm_context_create(name)
+    return _CTX[name]
+
+
+@pytest.mark.parametrize("name,m,s,R,nq", [
+    ("small4", 128, 16, 2500, 2),     # N_in = 8: 7 hoisted rotations per query
+    ("small4", 16, 4, 3000, 3),       # N_in = 4, three queries in one chunk
+    ("small4", 16, 1, 2100, 1),       # N_in = 16, part size 1
+    ("small4", 16, 16, 100, 1),       # N_in = 1: no rotations, the query times its mask
+])
+def test_hoisted_match_is_bit_exact(name, m, s, R, nq):
+    c = gctx(name)
+    om = OracleMatch(name, m, s, R, nq, hoisted=True)
+    _, _, ek = bm.bm_keygen_ex(c, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
+    g = bm.bm_gallery_import(c, om.pts_array(), om.masks_array(), om.cmask_array(), R, m, s)
+    bm.bm_gallery_set_expansion(g, bm.BM_EXPAND_HOISTED)
+    ocs = [om.encrypt(qi) for qi in range(nq)]
+    qs = [bm.bm_ciphertext_import(c, om.ct_array(cts), om.ctx.L) for cts in ocs]
+    res = bm.bm_match(c, ek, g, qs)
+    for qi in range(nq):
+        want, opacked = om.match(ocs[qi])
+        got = bm.bm_result_export(res, qi)
+        assert np.array_equal(got, want), f"query {qi}: ciphertexts differ"
+        ref = wl.plaintext_scores(om.feats, om.queries[qi])
+        assert np.abs(om.scores(got, opacked) - ref).max() < 1e-5
+
+
+@pytest.mark.parametrize("m,s,R,nq", [(128, 16, 6144, 1), (128, 4, 20000, 3)])
+def test_hoisted_and_doubling_forms_give_the_same_scores_ring16(m, s, R, nq):
+    c = gctx("ring16")
+    feats = wl.gallery(R, m)
+    qs, _ = wl.queries(feats, nq)
+    sk, pk, ek = bm.bm_keygen_ex(c, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
+    gd = bm.bm_encode_gallery(c, feats, m, s)
+    gh = bm.bm_encode_gallery(c, feats, m, s)
+    bm.bm_gallery_set_expansion(gh, bm.BM_EXPAND_HOISTED)
+    cts = bm.bm_encrypt_batch(c, pk, qs, m, s, bm.BM_QUERY_TILED, 4, 0)
+    rd, rh = bm.bm_match(c, ek, gd, cts), bm.bm_match(c, ek, gh, cts)
+    for qi in range(nq):
+        ref = wl.plaintext_scores(feats, qs[qi])
+        sd, r1d, _ = bm.bm_decrypt_scores(c, sk, rd, qi, R)
+        sh, r1h, _ = bm.bm_decrypt_scores(c, sk, rh, qi, R)
+        assert np.abs(sh - ref).max() < 1e-5 and np.abs(sd - ref).max() < 1e-5
+        assert r1h == r1d
+        assert not np.array_equal(bm.bm_result_export(rd, qi), bm.bm_result_export(rh, qi))
+
+
+def test_expansion_errors():
+    c = gctx("toy")
+    g = bm.bm_encode_gallery(c, wl.gallery(100, 16), 16, 4)
+    with pytest.raises(bm.BlindMatchError) as e:
+        bm.bm_gallery_set_expansion(g, bm.BM_EXPAND_HOISTED)    # client-expanded queries: no Algorithm 1
+    assert e.value.status == 1
+    c4 = gctx("small4")
+    _, pk, ek = bm.bm_keygen(c4, KEY_SEED, 16, 4)                 # doubling keys only
+    g4 = bm.bm_encode_gallery(c4, wl.gallery(100, 16), 16, 4)
+    bm.bm_gallery_set_expansion(g4, bm.BM_EXPAND_HOISTED)
+    ct = bm.bm_encrypt_query(c4, pk, wl.gallery(1, 16)[0], 16, 4, bm.BM_QUERY_TILED, 4, 0)
+    with pytest.raises(bm.BlindMatchError) as e:
+        bm.bm_match(c4, ek, g4, [ct])                             # rotation by 3 parts has no key
+    assert e.value.status == 4
+    with pytest.raises(bm.BlindMatchError):
+        bm.bm_gallery_set_expansion(g4, 7)

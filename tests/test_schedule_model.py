@@ -225,3 +225,29 @@ def test_model_counts_halve_with_complex_packing():
         return sum(o["count"] for o in ops if o["op"] == "rotate" and o["level"] == lv)
     assert rot(ops_c, 2) == rot(ops_r, 2) == 24
     assert rot(ops_c, 1) == 256 * 4 + 16 * 15 and rot(ops_r, 1) == 512 * 4 + 32 * 15
+
+
+@pytest.mark.parametrize("preset,R,dim,part,Q", [("small4", 2500, 128, 16, 3), ("ring16", 1 << 20, 128, 4, 40),
+                                                 ("ring16", 6144, 128, 32, 1), ("small4", 300, 16, 1, 2),
+                                                 ("small4", 300, 16, 16, 2)])
+def test_hoisted_launches_are_the_oracle_hoisted_schedule(preset, R, dim, part, Q):
+    """Algorithm 1 in hoisted form: one basis extension per query, N_in - 1 rotations
+    from it, N_in x N_in mask products per query, then the same HE-C^3 and compression."""
+    ops, _ = bm.bm_plan_estimate(preset, R, dim, part, Q, packing=bm.BM_LAYOUT_HOISTED)
+    log_n, n_q = PRESET[preset]
+    L, slots = n_q - 1, 1 << (log_n - 1)
+    n_in = dim // part
+    ev = sch.CountingEvaluator()
+    groups = sch.n_groups(R, part, slots)
+    sch.match(ev, [sch.SymCt(L)], [[None] * n_in for _ in range(groups)], [None] * n_in, object(), dim, part,
+              hoisted=True)
+    orc = ev.counts()
+    lib = library_counts(ops)
+    assert lib[("modup", L)] == Q * orc.get(("ModUp", L), 0) == (Q if n_in > 1 else 0)
+    assert lib[("rot_hoisted", L)] == Q * orc.get(("RotH", L), 0) == Q * (n_in - 1)
+    circ = sum(o["queries"] * o["count"] * o["parts"] for o in ops if o["op"] == "mac_circ")
+    assert circ == Q * n_in * n_in == Q * orc.get(("MulP", L), 0)
+    assert lib[("rescale", L)] == Q * orc[("Res", L)] == Q * n_in
+    assert lib[("rotate", L - 1)] == 0                     # no doubling rotations at the Algorithm-2 level
+    for lv in range(L - 1):
+        assert lib[("rotate", lv)] == Q * orc.get(("Rot", lv), 0)
