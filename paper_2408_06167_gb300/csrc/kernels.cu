@@ -170,11 +170,11 @@ cudaError_t ntt_launch_reg(const LimbBatch& b, const DevTables& tab, bool inv, c
     const double ops_c = 16.0 * (1 << (LA + LB - 1)) * LA * limbs;   // 16 mul ops per butterfly
     const double ops_r = 16.0 * (1 << (LA + LB - 1)) * LB * limbs;
     if (!inv) {
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_c); nttr::k_col_fwd<LA, LB, LT, C><<<gc, tc, 0, s>>>(b, tab); }
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_r); nttr::k_row_fwd<LA, LB, LT, R><<<gr, tr, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_c); pdl_launch(nttr::k_col_fwd<LA, LB, LT, C>, gc, tc, 0, s, b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_r); pdl_launch(nttr::k_row_fwd<LA, LB, LT, R>, gr, tr, 0, s, b, tab); }
     } else {
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_r); nttr::k_row_inv<LA, LB, LT, R><<<gr, tr, 0, s>>>(b, tab); }
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_c); nttr::k_col_inv<LA, LB, LT, C><<<gc, tc, 0, s>>>(b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_r); pdl_launch(nttr::k_row_inv<LA, LB, LT, R>, gr, tr, 0, s, b, tab); }
+        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_c); pdl_launch(nttr::k_col_inv<LA, LB, LT, C>, gc, tc, 0, s, b, tab); }
     }
     return cudaGetLastError();
 }
@@ -471,6 +471,7 @@ __global__ void k_mul_plain(uint64_t* const* in, const uint64_t* const* pt, uint
     const uint32_t l1 = lvl + 1;
     const uint32_t y = blockIdx.x, b = y / (2 * l1), c = (y / l1) % 2, j = y % l1;
     const uint64_t q = tab.q[j], qn = tab.qneg[j];
+    pdl_wait();
     const uint64_t* s = in[b] + ((size_t)c * l1 + j) * n;
     const uint64_t* m = pt[b] + (size_t)j * n;
     uint64_t* o = out[b] + ((size_t)c * l1 + j) * n;
@@ -487,6 +488,7 @@ __global__ void __launch_bounds__(kThreads) k_mac(const uint64_t* __restrict__ T
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t j = blockIdx.y % l1, g = blockIdx.y / l1;
     const uint32_t q0 = blockIdx.z * QT;
+    pdl_wait();
     if (p >= n) return;
     const uint64_t q = tab.q[j], qn = tab.qneg[j];
     uint64_t s0[QT], s1[QT];
@@ -525,6 +527,7 @@ __global__ void __launch_bounds__(kThreads) k_mac_ct(const uint64_t* __restrict_
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t j = blockIdx.y % l1, g = blockIdx.y / l1;
     const uint32_t q0 = blockIdx.z * QT;
+    pdl_wait();
     if (p >= n) return;
     const uint64_t q = tab.q[j], qn = tab.qneg[j];
     uint64_t d0[QT], d1[QT], d2[QT];
@@ -566,6 +569,7 @@ __global__ void __launch_bounds__(kThreads) k_mac_circ(const uint64_t* const* R,
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t j = blockIdx.y % l1, i = blockIdx.y / l1;
     const uint32_t q0 = blockIdx.z * QT;
+    pdl_wait();
     if (p >= n) return;
     const uint64_t q = tab.q[j], qn = tab.qneg[j];
     uint64_t s0[QT], s1[QT];
@@ -614,6 +618,14 @@ inline dim3 elem_grid(uint32_t n, uint32_t y) { return dim3((n + kThreads - 1) /
 // launchers
 // ===========================================================================
 
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("BM_PDL");
+        return !e || std::atoi(e) != 0;
+    }();
+    return on;
+}
+
 cudaError_t ntt_forward(const Context& c, const LimbBatch& b, cudaStream_t s) { return ntt_dispatch(c, b, false, s); }
 
 cudaError_t ntt_col_inverse(const Context& c, const LimbBatch& b, cudaStream_t s) {
@@ -621,8 +633,8 @@ cudaError_t ntt_col_inverse(const Context& c, const LimbBatch& b, cudaStream_t s
     if (limbs == 0) return cudaSuccess;
     const double lw = 16.0 * c.n * limbs, ops = 16.0 * (c.n / 2) * (c.log_n / 2) * limbs;
     ProfScope ps(BM_KERNEL_NTT, s, lw, ops);
-    if (c.log_n == 16) nttr::k_col_inv<8, 8, 2, 2><<<dim3(limbs, 256 / 2), 2 * 64, 0, s>>>(b, c.tab);
-    else if (c.log_n == 12) nttr::k_col_inv<6, 6, 2, 8><<<dim3(limbs, 64 / 8), 8 * 16, 0, s>>>(b, c.tab);
+    if (c.log_n == 16) pdl_launch(nttr::k_col_inv<8, 8, 2, 2>, dim3(limbs, 256 / 2), 2 * 64, 0, s, b, c.tab);
+    else if (c.log_n == 12) pdl_launch(nttr::k_col_inv<6, 6, 2, 8>, dim3(limbs, 64 / 8), 8 * 16, 0, s, b, c.tab);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -914,7 +926,7 @@ cudaError_t mul_plain(const Context& c, uint32_t level, uint32_t B, uint64_t* co
                       const uint64_t* const* d_pt, uint64_t* const* d_out, cudaStream_t s) {
     if (B == 0) return cudaSuccess;
     ProfScope ps(BM_KERNEL_MUL_PLAIN, s, 8.0 * c.n * B * (level + 1) * 5);
-    k_mul_plain<<<dim3(B * 2 * (level + 1), c.n / kThreads / 4), kThreads, 0, s>>>(d_in, d_pt, d_out, level, c.tab,
+    pdl_launch(k_mul_plain, dim3(B * 2 * (level + 1), c.n / kThreads / 4), kThreads, 0, s, d_in, d_pt, d_out, level, c.tab,
                                                                                    c.n);
     return cudaGetLastError();
 }
@@ -924,7 +936,7 @@ cudaError_t mac(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32
     constexpr int QT = 4;
     const dim3 g((c.n + kThreads - 1) / kThreads, G * (level + 1), (Q + QT - 1) / QT);
     ProfScope ps(BM_KERNEL_MAC, s, 8.0 * c.n * (level + 1) * ((double)Q * n_in * 2 + (double)G * n_in + 2.0 * Q * G));
-    k_mac<QT><<<g, kThreads, 0, s>>>(T, P, acc, Q, G, n_in, level, c.tab, c.log_n);
+    pdl_launch(k_mac<QT>, g, kThreads, 0, s, T, P, acc, Q, G, n_in, level, c.tab, c.log_n);
     return cudaGetLastError();
 }
 
@@ -934,7 +946,7 @@ cudaError_t mac_ct(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uin
     const dim3 g((c.n + kThreads - 1) / kThreads, G * (level + 1), (Q + QT - 1) / QT);
     ProfScope ps(BM_KERNEL_MAC, s,
                  8.0 * c.n * (level + 1) * ((double)Q * n_in * 2 + 2.0 * G * n_in + 4.0 * Q * G));
-    k_mac_ct<QT><<<g, kThreads, 0, s>>>(T, C, A, B, Q, G, n_in, level, c.tab, c.log_n);
+    pdl_launch(k_mac_ct<QT>, g, kThreads, 0, s, T, C, A, B, Q, G, n_in, level, c.tab, c.log_n);
     return cudaGetLastError();
 }
 
@@ -952,7 +964,7 @@ cudaError_t mac_circ(const Context& c, uint32_t level, uint32_t Q, uint32_t n_in
     constexpr int QT = 4;
     const dim3 g((c.n + kThreads - 1) / kThreads, n_in * (level + 1), (Q + QT - 1) / QT);
     ProfScope ps(BM_KERNEL_MAC, s, 8.0 * c.n * (level + 1) * ((double)Q * n_in * 2 + (double)n_in + 2.0 * Q * n_in));
-    k_mac_circ<QT><<<g, kThreads, 0, s>>>(R, masks, t0, Q, n_in, level, c.tab, c.log_n);
+    pdl_launch(k_mac_circ<QT>, g, kThreads, 0, s, R, masks, t0, Q, n_in, level, c.tab, c.log_n);
     return cudaGetLastError();
 }
 

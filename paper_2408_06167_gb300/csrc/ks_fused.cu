@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)))
     uint64_t* eo = ext + (((size_t)b * nd + d) * nlx + j) * N + roff;
     const SubMem sr{sm + jr * S, 1};
     stage_row_twiddles<LA, LB, R, R * TH>(tws, tab.itw[j], blockIdx.y * R);
+    pdl_wait();
     uint64_t v[K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)))
     nttr::relayout<LB, LT, 0, LB / LT - 1>(v, sr, t);
     tw_wait();
     nttr::inv_pass<LB, LT>(v, sr, tws, RowBase<R>{jr}, t, q, q2);
+    pdl_trigger();
     uint64_t* x1 = X1 + ((size_t)b * l1 + j) * N + roff;
 #pragma unroll
     for (int k = 0; k < K; k++) x1[first_idx<LB, LT>(t, k)] = v[k];
@@ -132,6 +134,7 @@ __global__ void __launch_bounds__(C * (1 << (LA - LT)))
     const uint32_t b = blockIdx.x / nd, d = blockIdx.x % nd;
     const int col = blockIdx.y * C + jc;
     const uint32_t ds = kc->dsz[d], d0 = kc->dstart[d];
+    pdl_wait();
 #pragma unroll 1
     for (uint32_t i = 0; i < ds; i++) {
         const uint64_t qi = tab.q[d0 + i];
@@ -197,6 +200,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
     stage_row_twiddles<LA, LB, R, R * TH>(twf, tab.tw[pi], blockIdx.y * R);
     if (jj >= l1) stage_row_twiddles<LA, LB, R, R * TH>(twi, tab.itw[pi], blockIdx.y * R);
     tw_wait();
+    pdl_wait();
     uint64_t v[K], s0[REG ? K : 1], s1[REG ? K : 1];
     // extended limb jj of every digit, NTT form, last-phase layout
 #pragma unroll 1
@@ -274,6 +278,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)))
     const int row = blockIdx.y * R + jr;
     uint64_t* e = ext + (size_t)blockIdx.x * N + (size_t)row * M;
     stage_row_twiddles<LA, LB, R, R * TH>(tws, tab.tw[pi], blockIdx.y * R);
+    pdl_wait();
     uint64_t v[K];
 #pragma unroll
     for (int k = 0; k < K; k++) v[k] = e[first_idx<LB, LT>(t, k)];
@@ -281,6 +286,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)))
     nttr::fwd_pass<LB, LT>(v, SubMem{sm + jr * S, 1}, tws, RowBase<R>{jr}, t, q, q2);
 #pragma unroll
     for (int k = 0; k < K; k++) v[k] = nttr::reduce4(v[k], q, q2);
+    pdl_trigger();
     nttr::store_last<LB, LT>(v, e, t);
 }
 
@@ -308,6 +314,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
     const int row = blockIdx.y * R + jr;
     const size_t roff = (size_t)row * M;
     if (jj >= l1) stage_row_twiddles<LA, LB, R, R * TH>(twi, tab.itw[pi], blockIdx.y * R);
+    pdl_wait();
     uint32_t src[K];
 #pragma unroll
     for (int k = 0; k < K; k++) src[k] = perm_src((uint32_t)(roff + last_idx<LB, LT>(t, k)), LOGN, galois);
@@ -358,6 +365,7 @@ __global__ void __launch_bounds__(C * (1 << (LA - LT)))
     const uint32_t b = blockIdx.x / 2, comp = blockIdx.x % 2;
     const int col = blockIdx.y * C + jc;
     const uint32_t nlx = l1 + alpha;
+    pdl_wait();
     uint64_t y[K];
 #pragma unroll 1
     for (uint32_t i = 0; i < alpha; i++) {
@@ -420,6 +428,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 3)
     const RowBase<R> base{jr};
     const SubMem sr{sm + jr * S, 1};
     stage_row_twiddles<LA, LB, R, R * TH>(tws, tab.tw[j], blockIdx.y * R);
+    pdl_wait();
     uint64_t v[K];
 #pragma unroll 1
     for (int comp = 0; comp < 2; comp++) {
@@ -465,12 +474,14 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)))
     const uint64_t* src = in[b] + ((size_t)comp * (lvl + 1) + lvl) * N + roff;
     const SubMem sr{sm + jr * S, 1};
     stage_row_twiddles<LA, LB, R, R * TH>(tws, tab.itw[lvl], blockIdx.y * R);
+    pdl_wait();
     uint64_t v[K];
 #pragma unroll
     for (int k = 0; k < K; k++) v[k] = src[first_idx<LB, LT>(t, k)];
     nttr::relayout<LB, LT, 0, LB / LT - 1>(v, sr, t);
     tw_wait();
     nttr::inv_pass<LB, LT>(v, sr, tws, RowBase<R>{jr}, t, q, q2);
+    pdl_trigger();
     uint64_t* o = Y + (size_t)blockIdx.x * N + roff;
 #pragma unroll
     for (int k = 0; k < K; k++) o[first_idx<LB, LT>(t, k)] = v[k];
@@ -489,6 +500,7 @@ __global__ void __launch_bounds__(C * (1 << (LA - LT)))
     const uint64_t ql = tab.q[lvl];
     const uint64_t* src = Y + (size_t)blockIdx.x * N + col;
     stage_col_twiddles<LA, C * (M >> LT)>(tws, tab.itw[lvl]);
+    pdl_wait();
     uint64_t c[K];
 #pragma unroll
     for (int k = 0; k < K; k++) c[k] = src[(size_t)last_idx<LA, LT>(t, k) * N2];
@@ -531,6 +543,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)))
     const uint64_t q = tab.q[j], q2 = 2 * q;
     const SubMem sr{sm + jr * S, 1};
     stage_row_twiddles<LA, LB, R, R * TH>(tws, tab.tw[j], blockIdx.y * R);
+    pdl_wait();
     const uint64_t* r = Rl + ((size_t)(b * 2 + comp) * lvl + j) * N + roff;
     uint64_t v[K];
 #pragma unroll
@@ -543,6 +556,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)))
 #pragma unroll
     for (int k = 0; k < K; k++) v[k] = shoup(subm(x[k], nttr::reduce4(v[k], q, q2), q), w.x, w.y, q);
     nttr::relayout<LB, LT, LB / LT - 1, 0>(v, sr, t);
+    pdl_trigger();
     uint64_t* o = out[b] + ((size_t)comp * lvl + j) * N + roff;
 #pragma unroll
     for (int k = 0; k < K; k++) o[first_idx<LB, LT>(t, k)] = v[k];
@@ -558,15 +572,15 @@ cudaError_t rescale_fused_launch(const Context& c, uint32_t level, uint32_t B, u
     const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;
     {
         ProfScope ps(BM_KERNEL_RESCALE, s, lw * B * 2 * 2, bf_r * B * 2);
-        k_rs_r1<LA, LB, LT, R><<<dim3(B * 2, N1 / R), tr, 0, s>>>(d_in, Y, c.tab, level);
+        pdl_launch(k_rs_r1<LA, LB, LT, R>, dim3(B * 2, N1 / R), tr, 0, s, d_in, Y, c.tab, level);
     }
     {
         ProfScope ps(BM_KERNEL_RESCALE, s, lw * B * 2 * (1 + level), bf_c * B * 2 * (1 + level));
-        k_rs_r2<LA, LB, LT, C><<<dim3(B * 2, N2 / C), tc, 0, s>>>(Y, Rl, c.tab, level);
+        pdl_launch(k_rs_r2<LA, LB, LT, C>, dim3(B * 2, N2 / C), tc, 0, s, Y, Rl, c.tab, level);
     }
     {
         ProfScope ps(BM_KERNEL_RESCALE, s, lw * B * 2 * level * 3, bf_r * B * 2 * level);
-        k_rs_r3<LA, LB, LT, R><<<dim3(B * 2 * level, N1 / R), tr, 0, s>>>(d_in, Rl, d_out, c.tab, level,
+        pdl_launch(k_rs_r3<LA, LB, LT, R>, dim3(B * 2 * level, N1 / R), tr, 0, s, d_in, Rl, d_out, c.tab, level,
                                                                           c.d_qlinv + (size_t)level * MAXB);
     }
     return cudaGetLastError();
@@ -603,7 +617,7 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
     }
     {
         ProfScope ps(BM_KERNEL_NTT, s, lw * B * l1 * 6, bf_r * B * l1);
-        k_ks_f1<LA, LB, LT, R><<<dim3(B * l1, N1 / R), tr, 0, s>>>(d_in, X0, X1, ext, kc, c.tab, l1,
+        pdl_launch(k_ks_f1<LA, LB, LT, R>, dim3(B * l1, N1 / R), tr, 0, s, d_in, X0, X1, ext, kc, c.tab, l1,
                                                                      (uint32_t)galois);
     }
     LimbBatch xb{X1, B, (uint64_t)l1 * N, 0, l1, 0};
@@ -613,20 +627,20 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
     {
         ProfScope ps(BM_KERNEL_MODUP, s, lw * B * (gathers + targets), bf_c * B * targets);
         const uint32_t kinv = (uint32_t)h_invmod_pow2(galois, 2ull * N);
-        k_ks_f3<LA, LB, LT, C><<<dim3(B * nd, N2 / C), tc, col_smem, s>>>(X1, ext, kc, c.tab, l1, c.L, kinv);
+        pdl_launch(k_ks_f3<LA, LB, LT, C>, dim3(B * nd, N2 / C), tc, col_smem, s, X1, ext, kc, c.tab, l1, c.L, kinv);
     }
     {
         ProfScope ps(BM_KERNEL_KS_IP, s, lw * nlx * ((double)B * nd + 2.0 * nd + 2.0 * B),
                      bf_r * B * (targets + 2.0 * alpha));
-        k_ks_f4<LA, LB, LT, R><<<dim3(B * nlx, N1 / R), tr, f4_smem, s>>>(ext, key, acc, kc, c.tab, l1, c.L, c.nb);
+        pdl_launch(k_ks_f4<LA, LB, LT, R>, dim3(B * nlx, N1 / R), tr, f4_smem, s, ext, key, acc, kc, c.tab, l1, c.L, c.nb);
     }
     {
         ProfScope ps(BM_KERNEL_MODDOWN, s, lw * B * 2 * (alpha + l1), bf_c * B * 2 * (alpha + l1));
-        k_ks_f5<LA, LB, LT, C><<<dim3(B * 2, N2 / C), tc, col_smem, s>>>(acc, conv, kc, c.tab, l1, c.L, alpha);
+        pdl_launch(k_ks_f5<LA, LB, LT, C>, dim3(B * 2, N2 / C), tc, col_smem, s, acc, conv, kc, c.tab, l1, c.L, alpha);
     }
     {
         ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * B * l1 * (2 + 2 + 1 + 2 + (d_add ? 2 : 0)), bf_r * B * 2 * l1);
-        k_ks_f6<LA, LB, LT, R><<<dim3(B * l1, N1 / R), tr, 0, s>>>(conv, acc, X0, d_out, d_add, kc, c.tab, l1,
+        pdl_launch(k_ks_f6<LA, LB, LT, R>, dim3(B * l1, N1 / R), tr, 0, s, conv, acc, X0, d_out, d_add, kc, c.tab, l1,
                                                                      (uint32_t)galois, nullptr, nullptr);
     }
     return cudaGetLastError();
@@ -658,7 +672,7 @@ cudaError_t ks_modup_launch(const Context& c, uint32_t level, uint32_t B, uint64
     }
     {
         ProfScope ps(BM_KERNEL_NTT, s, lw * B * l1 * 6, bf_r * B * l1);
-        k_ks_f1<LA, LB, LT, R><<<dim3(B * l1, N1 / R), tr, 0, s>>>(d_in, X0, X1, ext, kc, c.tab, l1, 1u);
+        pdl_launch(k_ks_f1<LA, LB, LT, R>, dim3(B * l1, N1 / R), tr, 0, s, d_in, X0, X1, ext, kc, c.tab, l1, 1u);
     }
     LimbBatch xb{X1, B, (uint64_t)l1 * N, 0, l1, 0};
     for (uint32_t k = 0; k < l1; k++) xb.set(k, k);
@@ -666,11 +680,11 @@ cudaError_t ks_modup_launch(const Context& c, uint32_t level, uint32_t B, uint64
     if (e != cudaSuccess) return e;
     {
         ProfScope ps(BM_KERNEL_MODUP, s, lw * B * (gathers + targets), bf_c * B * targets);
-        k_ks_f3<LA, LB, LT, C><<<dim3(B * nd, N2 / C), tc, col_smem, s>>>(X1, ext, kc, c.tab, l1, c.L, 1u);
+        pdl_launch(k_ks_f3<LA, LB, LT, C>, dim3(B * nd, N2 / C), tc, col_smem, s, X1, ext, kc, c.tab, l1, c.L, 1u);
     }
     {
         ProfScope ps(BM_KERNEL_MODUP, s, lw * B * targets * 2, bf_r * B * targets);
-        k_ks_f3r<LA, LB, LT, R><<<dim3(B * nd * nlx, N1 / R), tr, 0, s>>>(ext, kc, c.tab, l1, c.L);
+        pdl_launch(k_ks_f3r<LA, LB, LT, R>, dim3(B * nd * nlx, N1 / R), tr, 0, s, ext, kc, c.tab, l1, c.L);
     }
     return cudaGetLastError();
 }
@@ -697,16 +711,16 @@ cudaError_t ks_hoisted_launch(const Context& c, uint32_t level, uint32_t E, cons
     const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;
     {
         ProfScope ps(BM_KERNEL_KS_IP, s, lw * nlx * ((double)E * nd + 2.0 * nd * E + 2.0 * E), bf_r * E * 2.0 * alpha);
-        k_ks_f4h<LA, LB, LT, R><<<dim3(E * nlx, N1 / R), tr, 0, s>>>(ext_of, key_of, gal_of, acc, kc, c.tab, l1, c.L,
+        pdl_launch(k_ks_f4h<LA, LB, LT, R>, dim3(E * nlx, N1 / R), tr, 0, s, ext_of, key_of, gal_of, acc, kc, c.tab, l1, c.L,
                                                                        c.nb);
     }
     {
         ProfScope ps(BM_KERNEL_MODDOWN, s, lw * E * 2 * (alpha + l1), bf_c * E * 2 * (alpha + l1));
-        k_ks_f5<LA, LB, LT, C><<<dim3(E * 2, N2 / C), tc, col_smem, s>>>(acc, conv, kc, c.tab, l1, c.L, alpha);
+        pdl_launch(k_ks_f5<LA, LB, LT, C>, dim3(E * 2, N2 / C), tc, col_smem, s, acc, conv, kc, c.tab, l1, c.L, alpha);
     }
     {
         ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * E * l1 * 7, bf_r * E * 2 * l1);
-        k_ks_f6<LA, LB, LT, R><<<dim3(E * l1, N1 / R), tr, 0, s>>>(conv, acc, nullptr, d_out, nullptr, kc, c.tab, l1,
+        pdl_launch(k_ks_f6<LA, LB, LT, R>, dim3(E * l1, N1 / R), tr, 0, s, conv, acc, nullptr, d_out, nullptr, kc, c.tab, l1,
                                                                      0u, src, gal_of);
     }
     return cudaGetLastError();

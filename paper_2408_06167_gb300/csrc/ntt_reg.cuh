@@ -19,6 +19,36 @@
 #include <cuda_pipeline.h>
 
 namespace bm {
+
+// Programmatic dependent launch (the kernels of the match path are launched with
+// pdl_launch): a kernel may be scheduled while the previous kernel of its stream
+// drains.  pdl_wait() blocks until that kernel has completed and its writes are
+// visible -- every such kernel calls it before its first read of data the
+// previous kernels wrote and before its first global write; only constant
+// context tables (twiddles, primes) are read before it.  pdl_trigger() lets the
+// next kernel be scheduled once every block of this one has reached it; both
+// are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// launch with the programmatic-serialization attribute (off with BM_PDL=0)
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 namespace nttr {
 
 __device__ __forceinline__ uint64_t* limb_at(const LimbBatch& b, uint32_t limb, uint32_t n) {
@@ -237,11 +267,13 @@ __global__ void __launch_bounds__(C * (1 << (LA - LT))) k_col_fwd(LimbBatch lb, 
     uint64_t* a = limb_at(lb, blockIdx.x, M * N2) + blockIdx.y * C + j;
     const uint64_t q = tab.q[pi], q2 = 2 * q;
     stage_col_twiddles<LA, C * (M >> LT)>(tws, tab.tw[pi]);
+    pdl_wait();
     uint64_t v[K];
 #pragma unroll
     for (int k = 0; k < K; k++) v[k] = a[(size_t)first_idx<LA, LT>(t, k) * N2];
     tw_wait();
     fwd_pass<LA, LT>(v, SubMem{sm + j, C}, tws, ColBase{}, t, q, q2);
+    pdl_trigger();
 #pragma unroll
     for (int k = 0; k < K; k++) a[(size_t)last_idx<LA, LT>(t, k) * N2] = v[k];
 }
@@ -259,6 +291,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT))) k_row_fwd(LimbBatch lb, 
     const uint64_t q = tab.q[pi], q2 = 2 * q;
     const SubMem sr{sm + jr * S, 1};
     stage_row_twiddles<LA, LB, R, R * TH>(tws, tab.tw[pi], blockIdx.y * R);
+    pdl_wait();
     uint64_t v[K];
 #pragma unroll
     for (int k = 0; k < K; k++) v[k] = a[first_idx<LB, LT>(t, k)];
@@ -267,6 +300,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT))) k_row_fwd(LimbBatch lb, 
 #pragma unroll
     for (int k = 0; k < K; k++) v[k] = reduce4(v[k], q, q2);
     relayout<LB, LT, LB / LT - 1, 0>(v, sr, t);
+    pdl_trigger();
 #pragma unroll
     for (int k = 0; k < K; k++) a[first_idx<LB, LT>(t, k)] = v[k];
 }
@@ -284,12 +318,14 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT))) k_row_inv(LimbBatch lb, 
     const uint64_t q = tab.q[pi], q2 = 2 * q;
     const SubMem sr{sm + jr * S, 1};
     stage_row_twiddles<LA, LB, R, R * TH>(tws, tab.itw[pi], blockIdx.y * R);
+    pdl_wait();
     uint64_t v[K];
 #pragma unroll
     for (int k = 0; k < K; k++) v[k] = a[first_idx<LB, LT>(t, k)];
     relayout<LB, LT, 0, LB / LT - 1>(v, sr, t);
     tw_wait();
     inv_pass<LB, LT>(v, sr, tws, RowBase<R>{jr}, t, q, q2);
+    pdl_trigger();
 #pragma unroll
     for (int k = 0; k < K; k++) a[first_idx<LB, LT>(t, k)] = v[k];
 }
@@ -305,11 +341,13 @@ __global__ void __launch_bounds__(C * (1 << (LA - LT))) k_col_inv(LimbBatch lb, 
     uint64_t* a = limb_at(lb, blockIdx.x, M * N2) + blockIdx.y * C + j;
     const uint64_t q = tab.q[pi], q2 = 2 * q;
     stage_col_twiddles<LA, C * (M >> LT)>(tws, tab.itw[pi]);
+    pdl_wait();
     uint64_t v[K];
 #pragma unroll
     for (int k = 0; k < K; k++) v[k] = a[(size_t)last_idx<LA, LT>(t, k) * N2];
     tw_wait();
     inv_pass<LA, LT>(v, SubMem{sm + j, C}, tws, ColBase{}, t, q, q2);
+    pdl_trigger();
     const uint64_t ni = tab.ninv[pi], nis = tab.ninv_sh[pi];
 #pragma unroll
     for (int k = 0; k < K; k++) a[(size_t)first_idx<LA, LT>(t, k) * N2] = shoup(v[k], ni, nis, q);
