@@ -40,6 +40,13 @@ __device__ __forceinline__ uint64_t red6(uint64_t y, uint64_t t) {   // [0, 6t) 
 
 constexpr int kMaxDigit = 2;   // limbs per digit and special primes handled by the fused kernels
 
+// 32-bit multiply results of one 64-bit modular product (the accounting of the
+// roofline): Shoup with a precomputed companion = the high half of x*w' (four
+// 32x32 partial products, both halves: 8) and the low halves of x*w and of the
+// quotient times q (4 each) = 16, as one butterfly; Montgomery = the full
+// product a*b (8), the low half of t*(-q^-1) (4) and the high half of m*q (8) = 20.
+constexpr double kShoupMul = 16, kMontMul = 20;
+
 using nttr::ColBase;
 using nttr::first_idx;
 using nttr::last_idx;
@@ -625,21 +632,24 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
     cudaError_t e = ntt_col_inverse(c, xb, s);
     if (e != cudaSuccess) return e;
     {
-        ProfScope ps(BM_KERNEL_MODUP, s, lw * B * (gathers + targets), bf_c * B * targets);
+        ProfScope ps(BM_KERNEL_MODUP, s, lw * B * (gathers + targets),
+                     bf_c * B * targets + kShoupMul * N * B * (l1 + gathers));
         const uint32_t kinv = (uint32_t)h_invmod_pow2(galois, 2ull * N);
         pdl_launch(k_ks_f3<LA, LB, LT, C>, dim3(B * nd, N2 / C), tc, col_smem, s, X1, ext, kc, c.tab, l1, c.L, kinv);
     }
     {
         ProfScope ps(BM_KERNEL_KS_IP, s, lw * nlx * ((double)B * nd + 2.0 * nd + 2.0 * B),
-                     bf_r * B * (targets + 2.0 * alpha));
+                     bf_r * B * (targets + 2.0 * alpha) + kMontMul * N * B * nlx * 2.0 * nd);
         pdl_launch(k_ks_f4<LA, LB, LT, R>, dim3(B * nlx, N1 / R), tr, f4_smem, s, ext, key, acc, kc, c.tab, l1, c.L, c.nb);
     }
     {
-        ProfScope ps(BM_KERNEL_MODDOWN, s, lw * B * 2 * (alpha + l1), bf_c * B * 2 * (alpha + l1));
+        ProfScope ps(BM_KERNEL_MODDOWN, s, lw * B * 2 * (alpha + l1),
+                     bf_c * B * 2 * (alpha + l1) + kShoupMul * N * B * 2 * (alpha + (double)l1 * alpha));
         pdl_launch(k_ks_f5<LA, LB, LT, C>, dim3(B * 2, N2 / C), tc, col_smem, s, acc, conv, kc, c.tab, l1, c.L, alpha);
     }
     {
-        ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * B * l1 * (2 + 2 + 1 + 2 + (d_add ? 2 : 0)), bf_r * B * 2 * l1);
+        ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * B * l1 * (2 + 2 + 1 + 2 + (d_add ? 2 : 0)),
+                     bf_r * B * 2 * l1 + kShoupMul * N * B * 2 * l1);
         pdl_launch(k_ks_f6<LA, LB, LT, R>, dim3(B * l1, N1 / R), tr, 0, s, conv, acc, X0, d_out, d_add, kc, c.tab, l1,
                                                                      (uint32_t)galois, nullptr, nullptr);
     }
@@ -679,7 +689,8 @@ cudaError_t ks_modup_launch(const Context& c, uint32_t level, uint32_t B, uint64
     cudaError_t e = ntt_col_inverse(c, xb, s);
     if (e != cudaSuccess) return e;
     {
-        ProfScope ps(BM_KERNEL_MODUP, s, lw * B * (gathers + targets), bf_c * B * targets);
+        ProfScope ps(BM_KERNEL_MODUP, s, lw * B * (gathers + targets),
+                     bf_c * B * targets + kShoupMul * N * B * (l1 + gathers));
         pdl_launch(k_ks_f3<LA, LB, LT, C>, dim3(B * nd, N2 / C), tc, col_smem, s, X1, ext, kc, c.tab, l1, c.L, 1u);
     }
     {
@@ -710,16 +721,18 @@ cudaError_t ks_hoisted_launch(const Context& c, uint32_t level, uint32_t E, cons
     (void)attrs;
     const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;
     {
-        ProfScope ps(BM_KERNEL_KS_IP, s, lw * nlx * ((double)E * nd + 2.0 * nd * E + 2.0 * E), bf_r * E * 2.0 * alpha);
+        ProfScope ps(BM_KERNEL_KS_IP, s, lw * nlx * ((double)E * nd + 2.0 * nd * E + 2.0 * E),
+                     bf_r * E * 2.0 * alpha + kMontMul * N * E * nlx * 2.0 * nd);
         pdl_launch(k_ks_f4h<LA, LB, LT, R>, dim3(E * nlx, N1 / R), tr, 0, s, ext_of, key_of, gal_of, acc, kc, c.tab, l1, c.L,
                                                                        c.nb);
     }
     {
-        ProfScope ps(BM_KERNEL_MODDOWN, s, lw * E * 2 * (alpha + l1), bf_c * E * 2 * (alpha + l1));
+        ProfScope ps(BM_KERNEL_MODDOWN, s, lw * E * 2 * (alpha + l1),
+                     bf_c * E * 2 * (alpha + l1) + kShoupMul * N * E * 2 * (alpha + (double)l1 * alpha));
         pdl_launch(k_ks_f5<LA, LB, LT, C>, dim3(E * 2, N2 / C), tc, col_smem, s, acc, conv, kc, c.tab, l1, c.L, alpha);
     }
     {
-        ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * E * l1 * 7, bf_r * E * 2 * l1);
+        ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * E * l1 * 7, bf_r * E * 2 * l1 + kShoupMul * N * E * 2 * l1);
         pdl_launch(k_ks_f6<LA, LB, LT, R>, dim3(E * l1, N1 / R), tr, 0, s, conv, acc, nullptr, d_out, nullptr, kc, c.tab, l1,
                                                                      0u, src, gal_of);
     }
