@@ -56,8 +56,9 @@ def parse():
     ap.add_argument("--auto-part", action="store_true",
                     help="serving: each gallery's part size chosen by the cost model (bm_choose_part)")
     ap.add_argument("--no-tune", action="store_true", help="skip the rotation kernel-shape tuner")
-    ap.add_argument("--expansion", default="doubling", choices=["doubling", "hoisted", "auto"],
-                    help="form of Algorithm 1 (auto: serving picks per gallery by the cost model)")
+    ap.add_argument("--expansion", default="hoisted", choices=["doubling", "hoisted", "auto"],
+                    help="form of Algorithm 1: the printed doubling order or the hoisted sum "
+                         "(auto: serving picks per gallery by the cost model)")
     ap.add_argument("--gallery", default="plain", choices=["plain", "encrypted"],
                     help="gallery of plaintexts, or of ciphertexts enrolled on the server (Sec. 3.2)")
     ap.add_argument("--packing", default="real", choices=["real", "complex"],
@@ -200,22 +201,24 @@ def alu_peak_tops():
     return SM_COUNT * INT32_MUL_PER_CLK_PER_SM * mhz * 1e6 / 1e12
 
 
-def measured_traffic(kernel_class, workload):
-    """DRAM bytes per launch of the dominant kernel class from the committed ncu
-    record, or None when the record is for another class or workload, or when
-    the kernel sources have changed since the counters were taken."""
+def measured_traffic(kernel_class, workload, config):
+    """DRAM bytes per launch of a kernel class from the committed ncu record, or
+    None when the record is for another workload or schedule, or when the kernel
+    sources have changed since the counters were taken."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
             rec = json.load(f)
-        if rec["kernel_class"] != kernel_class or not rec["workload"].startswith(workload):
+        if rec["workload"] != workload or any(rec["config"].get(k) != config.get(k) for k in rec["config"]):
             return None
         h = hashlib.sha1()
         for src in rec["sources"]:
             with open(os.path.join(ROOT, src), "rb") as f:
                 h.update(f.read())
-        return float(rec["dram_bytes_per_launch"]) if h.hexdigest() == rec["sources_sha1"] else None
-    except (OSError, KeyError, ValueError):
+        if h.hexdigest() != rec["sources_sha1"]:
+            return None
+        return float(rec["dram_bytes_per_launch"][kernel_class])
+    except (OSError, KeyError, ValueError, TypeError):
         return None
 
 
@@ -540,16 +543,18 @@ def main():
     dom = max(prof, key=lambda k: prof[k][1])
     n_l, ms_l, by_l, ops_l = prof[dom]
     peak_hbm, peak_src = load_peaks()
+    traffic_cfg = {"part": part, "packing": args.packing, "gallery": args.gallery, "expansion": args.expansion}
     hbm_gbs = by_l / (ms_l / 1e3) / 1e9 if ms_l > 0 else 0.0
     if ops_l > 0:
         achieved = ops_l / (ms_l / 1e3) / 1e12
         peak = alu_peak_tops()
         roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmul32/s",
                     "frac": achieved / peak, "peak_source": "derived: 152 SMs x 64 int32 mul/clk x max SM clock",
-                    "traffic": measured_traffic(dom, W.name)}
+                    "traffic": measured_traffic(dom, W.name, traffic_cfg)}
     else:
         roofline = {"kernel": dom, "bound": "hbm", "achieved": hbm_gbs, "peak": peak_hbm, "unit": "GB/s",
-                    "frac": hbm_gbs / peak_hbm, "peak_source": peak_src, "traffic": measured_traffic(dom, W.name)}
+                    "frac": hbm_gbs / peak_hbm, "peak_source": peak_src,
+                    "traffic": measured_traffic(dom, W.name, traffic_cfg)}
     roofline.update({"hbm_view": {"achieved_gbs": hbm_gbs, "peak_gbs": peak_hbm, "frac": hbm_gbs / peak_hbm,
                                   "peak_source": peak_src},
                      "launches_per_step": n_l / args.steps, "avg_launch_us": 1e3 * ms_l / max(n_l, 1),

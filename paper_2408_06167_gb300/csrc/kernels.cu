@@ -559,39 +559,43 @@ __global__ void __launch_bounds__(kThreads) k_mac_ct(const uint64_t* __restrict_
 
 // Algorithm 1 in hoisted form: t0[q][i] = sum_j R[q][j] * mask[(i - j) mod n_in] with
 // R[q][j] = Rot(query q, j*part) given by pointer (R[q][0] the query itself),
-// masks [n_in][l1][N] Montgomery, t0 [Q][n_in][2][l1][N]; grid (chunks of N,
-// n_in * l1, queries / QT), QT queries per thread (one read of each mask word)
-template <int QT>
+// masks [n_in][l1][N] Montgomery, t0 [Q][n_in][2][l1][N].  Grid (chunks of N, l1,
+// Q * ceil(n_in / OC)): a thread computes OC outputs i of one query, limb and
+// coefficient, reading each rotated query once per OC outputs.
+template <int OC>
 __global__ void __launch_bounds__(kThreads) k_mac_circ(const uint64_t* const* R, const uint64_t* __restrict__ masks,
-                                                       uint64_t* __restrict__ t0, uint32_t Qn, uint32_t n_in,
-                                                       uint32_t lvl, DevTables tab, uint32_t log_n) {
+                                                       uint64_t* __restrict__ t0, uint32_t n_in, uint32_t lvl,
+                                                       DevTables tab, uint32_t log_n) {
     const uint32_t n = 1u << log_n, l1 = lvl + 1;
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t j = blockIdx.y % l1, i = blockIdx.y / l1;
-    const uint32_t q0 = blockIdx.z * QT;
+    const uint32_t j = blockIdx.y;
+    const uint32_t chunks = (n_in + OC - 1) / OC;
+    const uint32_t qi = blockIdx.z / chunks, i0 = (blockIdx.z % chunks) * OC;
     pdl_wait();
     if (p >= n) return;
     const uint64_t q = tab.q[j], qn = tab.qneg[j];
-    uint64_t s0[QT], s1[QT];
+    uint64_t s0[OC], s1[OC];
 #pragma unroll
-    for (int k = 0; k < QT; k++) s0[k] = s1[k] = 0;
+    for (int o = 0; o < OC; o++) s0[o] = s1[o] = 0;
     for (uint32_t jj = 0; jj < n_in; jj++) {
-        const uint32_t mi = (i + n_in - jj) % n_in;
-        const uint64_t mk = masks[((size_t)mi * l1 + j) * n + p];
+        const uint64_t* r = R[(size_t)qi * n_in + jj];
+        const uint64_t r0 = r[(size_t)j * n + p], r1 = r[((size_t)l1 + j) * n + p];
 #pragma unroll
-        for (int k = 0; k < QT; k++) {
-            if (q0 + k >= Qn) break;
-            const uint64_t* r = R[(size_t)(q0 + k) * n_in + jj];
-            s0[k] = addm(s0[k], mont(r[(size_t)j * n + p], mk, q, qn), q);
-            s1[k] = addm(s1[k], mont(r[((size_t)l1 + j) * n + p], mk, q, qn), q);
+        for (int o = 0; o < OC; o++) {
+            const uint32_t i = i0 + o;
+            if (i >= n_in) break;
+            const uint64_t mk = masks[((size_t)((i + n_in - jj) % n_in) * l1 + j) * n + p];
+            s0[o] = addm(s0[o], mont(r0, mk, q, qn), q);
+            s1[o] = addm(s1[o], mont(r1, mk, q, qn), q);
         }
     }
 #pragma unroll
-    for (int k = 0; k < QT; k++) {
-        if (q0 + k >= Qn) break;
-        const size_t ob = ((((size_t)(q0 + k) * n_in + i) * 2) * l1 + j) * n + p;
-        t0[ob] = s0[k];
-        t0[ob + (size_t)l1 * n] = s1[k];
+    for (int o = 0; o < OC; o++) {
+        const uint32_t i = i0 + o;
+        if (i >= n_in) break;
+        const size_t ob = ((((size_t)qi * n_in + i) * 2) * l1 + j) * n + p;
+        t0[ob] = s0[o];
+        t0[ob + (size_t)l1 * n] = s1[o];
     }
 }
 
@@ -961,10 +965,10 @@ cudaError_t accumulate(const Context& c, uint32_t level, uint32_t n_targets, uin
 
 cudaError_t mac_circ(const Context& c, uint32_t level, uint32_t Q, uint32_t n_in, const uint64_t* const* R,
                      const uint64_t* masks, uint64_t* t0, cudaStream_t s) {
-    constexpr int QT = 4;
-    const dim3 g((c.n + kThreads - 1) / kThreads, n_in * (level + 1), (Q + QT - 1) / QT);
+    constexpr int OC = 8;
+    const dim3 g((c.n + kThreads - 1) / kThreads, level + 1, Q * ((n_in + OC - 1) / OC));
     ProfScope ps(BM_KERNEL_MAC, s, 8.0 * c.n * (level + 1) * ((double)Q * n_in * 2 + (double)n_in + 2.0 * Q * n_in));
-    pdl_launch(k_mac_circ<QT>, g, kThreads, 0, s, R, masks, t0, Q, n_in, level, c.tab, c.log_n);
+    pdl_launch(k_mac_circ<OC>, g, kThreads, 0, s, R, masks, t0, n_in, level, c.tab, c.log_n);
     return cudaGetLastError();
 }
 
