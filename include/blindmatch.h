@@ -119,8 +119,10 @@ enum {
                                        to s, for Mul of two ciphertexts, Sec. 3.1) and the right
                                        rotations by every power of two from part_size below N/2
                                        that enrollment uses (Sec. 3.2) */
-    BM_KEYS_HOISTED = 2             /* also the left rotations by j*part_size, 0 < j < dim/part_size,
-                                       of the hoisted Algorithm 1 (BM_EXPAND_HOISTED) */
+    BM_KEYS_HOISTED = 2             /* also the rotations of the hoisted forms (BM_SCHED_*): left by
+                                       j*part_size, 0 < j < dim/part_size (Algorithm 1), left by the
+                                       baby and giant steps of the rotate-and-sum, right by 1 .. part_size-1
+                                       (linear compression) */
 };
 /* bm_keygen with extra key sets (BM_KEYS_* flags); flags = 0 is bm_keygen.  The
  * relinearisation key is sampled like a rotation key with s^2 in place of
@@ -233,6 +235,30 @@ enum {
     BM_EXPAND_HOISTED = 1
 };
 bm_status bm_gallery_set_expansion(bm_gallery* g, uint32_t mode);
+
+/* The schedule's hoisted forms, as a set of flags (the same messages as the
+ * printed forms; the ciphertext bits differ, and each is bit-exact against the
+ * oracle's evaluation in the same order):
+ *  BM_SCHED_HOISTED_EXPANSION    Algorithm 1 as above (= BM_EXPAND_HOISTED)
+ *  BM_SCHED_HOISTED_ROTSUM       Algorithm 2's rotate-and-sum over a part of s
+ *                                slots, sum_{r<s} Rot(acc, r), as two rounds of
+ *                                hoisted rotations: acc += Rot(acc, r) for 0 < r < b,
+ *                                then acc += Rot(acc, b*k) for 0 < k < s/b, with
+ *                                b = 2^ceil(log2(s)/2) (log2(s) sequential
+ *                                rotations otherwise)
+ *  BM_SCHED_HOISTED_COMPRESSION  the compression in its linear form, every group
+ *                                r > 0 of a pack rotated right by r in one round of
+ *                                hoisted rotations (a radix-2 tree otherwise)
+ * Needs the keys of bm_keygen_ex(..., BM_KEYS_HOISTED).  Plans of the gallery
+ * built before the call are dropped; call it before registering the gallery
+ * with a server.  BM_E_ARG for unknown flags, or the expansion flag on a gallery
+ * without Algorithm 1. */
+enum {
+    BM_SCHED_HOISTED_EXPANSION = 1,
+    BM_SCHED_HOISTED_ROTSUM = 2,
+    BM_SCHED_HOISTED_COMPRESSION = 4
+};
+bm_status bm_gallery_set_schedule(bm_gallery* g, uint32_t flags);
 void bm_gallery_destroy(bm_gallery* g);
 
 /* Sec. 3.3: encrypts the L2-normalised query q[dim] under pk at the top level
@@ -427,10 +453,11 @@ enum {
     BM_OP_INTT = 5,       /* inverse NTT of `count` limbs (score egress) */
     BM_OP_COPY = 6,       /* device copy of `count` level-0 ciphertexts (uncompressed outputs) */
     BM_OP_MAC_CT = 7,     /* HE-C^3 tensor products with an encrypted gallery, as BM_OP_MAC */
-    BM_OP_MODUP = 8,      /* hoisted Algorithm 1: basis extension of `count` query ciphertexts */
-    BM_OP_ROT_HOISTED = 9,/* hoisted Algorithm 1: `count` rotations from extended ciphertexts */
+    BM_OP_MODUP = 8,      /* hoisted rotations: basis extension of `count` ciphertexts at `level` */
+    BM_OP_ROT_HOISTED = 9,/* hoisted rotations: `count` rotations from extended ciphertexts */
     BM_OP_MAC_CIRC = 10,  /* hoisted Algorithm 1: `queries` x `count` outputs of `parts` mask products */
-    BM_OP_KINDS = 11
+    BM_OP_ACCUM = 11,     /* sums of `count` ciphertexts at `level` into their targets (hoisted rounds) */
+    BM_OP_KINDS = 12
 };
 
 /* One kernel launch (or launch group) of a match schedule. */
@@ -458,8 +485,11 @@ typedef struct bm_op_costs {
 /* Gallery kinds for the schedule model: a BM_PACK_* value, or'ed with
  * BM_LAYOUT_ENCRYPTED for a gallery of ciphertexts (bm_enroll_encrypted). */
 #define BM_LAYOUT_ENCRYPTED 0x100u
-/* ... or'ed with BM_LAYOUT_HOISTED for the hoisted form of Algorithm 1 (bm_gallery_set_expansion). */
+/* ... or'ed with BM_LAYOUT_HOISTED for the hoisted form of Algorithm 1 (bm_gallery_set_expansion),
+ * BM_LAYOUT_HOISTED_ROTSUM and BM_LAYOUT_HOISTED_COMPRESSION for the other hoisted forms. */
 #define BM_LAYOUT_HOISTED 0x200u
+#define BM_LAYOUT_HOISTED_ROTSUM 0x400u
+#define BM_LAYOUT_HOISTED_COMPRESSION 0x800u
 
 /* Host only (no device needed): the launches of the match of `n_queries`
  * queries against a gallery of n_ids identities in (dim, part_size, packing) under

@@ -195,7 +195,27 @@ def expand_query_hoisted(ev, ct, masks, m, s):
     return out
 
 
-def hec3(ev, cu, cs, s, rescale_each_part=False, encrypted_gallery=False, lazy_relin=True):
+def bsgs_split(s):
+    """(baby, giant) step counts of the hoisted rotate-and-sum over s (a power of
+    two): baby = 2^ceil(log2(s)/2), giant = s / baby."""
+    lb = log2i(s)
+    b = 1 << ((lb + 1) // 2)
+    return b, s // b
+
+
+def rotsum_hoisted(ev, acc, s):
+    """sum_{r<s} Rot(acc, r) -- the message of Algorithm 2's log2(s)
+    rotate-and-add steps -- in two rounds of hoisted rotations: baby steps
+    acc + sum_{r<b} Rot(acc, r), then giant steps over multiples of b."""
+    b, g = bsgs_split(s)
+    for step, count in ((1, b), (b, g)):
+        if count > 1:
+            for x in ev.rotate_hoisted(acc, [step * k for k in range(1, count)]):
+                acc = ev.add(acc, x)
+    return acc
+
+
+def hec3(ev, cu, cs, s, rescale_each_part=False, encrypted_gallery=False, lazy_relin=True, rotsum="doubling"):
     """Algorithm 2 for one group: sum_i Mul(C_u,i, C_s,i), then log2(s) rotate-and-add steps.
 
     Slot u*s of the result holds <q, g_u> for every identity u of the group.
@@ -208,6 +228,8 @@ def hec3(ev, cu, cs, s, rescale_each_part=False, encrypted_gallery=False, lazy_r
         for i in range(len(cu)):
             acc3 = ev.add3(acc3, ev.tensor(cu[i], cs[i]))
         acc = ev.rescale(ev.relinearize(acc3))
+        if rotsum == "hoisted":
+            return rotsum_hoisted(ev, acc, s)
         for t in range(1, log2i(s) + 1):
             acc = ev.add(ev.rotate(acc, 1 << (t - 1)), acc)
         return acc
@@ -221,18 +243,26 @@ def hec3(ev, cu, cs, s, rescale_each_part=False, encrypted_gallery=False, lazy_r
         for i in range(1, len(cu)):
             acc = ev.add(acc, mul(cu[i], cs[i]))
         acc = ev.rescale(acc)
+    if rotsum == "hoisted":
+        return rotsum_hoisted(ev, acc, s)
     for t in range(1, log2i(s) + 1):
         acc = ev.add(ev.rotate(acc, 1 << (t - 1)), acc)
     return acc
 
 
-def compress(ev, accs, mask_m, s, tree=True, final_rescale=True):
-    """Compression: mask each group output and pack s groups per ciphertext."""
+def compress(ev, accs, mask_m, s, tree=True, final_rescale=True, hoisted=False):
+    """Compression: mask each group output and pack s groups per ciphertext.
+    hoisted=True: the linear form with every group's rotation taken in one
+    round (each rotation hoisted: ModUp before the automorphism)."""
     xs = [ev.mul_plain(a, mask_m) for a in accs]
     packs = []
     for p in range(-(-len(xs) // s)):
         ys = xs[p * s:(p + 1) * s]
-        if tree:
+        if hoisted:
+            y = ys[0]
+            for r in range(1, len(ys)):
+                y = ev.add(y, ev.rotate_hoisted(ys[r], [-r])[0])
+        elif tree:
             b = 0
             while len(ys) > 1:
                 nxt = []
@@ -253,7 +283,8 @@ def compress(ev, accs, mask_m, s, tree=True, final_rescale=True):
 
 
 def match(ev, query_cts, gallery_pts, masks, mask_m, m, s, expanded=False,
-          rescale_each_part=False, tree=True, encrypted_gallery=False, hoisted=False):
+          rescale_each_part=False, tree=True, encrypted_gallery=False, hoisted=False,
+          hoisted_rotsum=False, hoisted_compress=False):
     """Full server-side match for one query.
 
     query_cts: [ct] (tiled, run through Algorithm 1) or the N_in client-expanded cts.
@@ -265,9 +296,11 @@ def match(ev, query_cts, gallery_pts, masks, mask_m, m, s, expanded=False,
         cu = expand_query_hoisted(ev, query_cts[0], masks, m, s)
     else:
         cu = expand_query(ev, query_cts[0], masks, m, s)
-    accs = [hec3(ev, cu, gallery_pts[g], s, rescale_each_part, encrypted_gallery) for g in range(len(gallery_pts))]
+    rotsum = "hoisted" if hoisted_rotsum else "doubling"
+    accs = [hec3(ev, cu, gallery_pts[g], s, rescale_each_part, encrypted_gallery, rotsum=rotsum)
+            for g in range(len(gallery_pts))]
     if accs[0].level >= 1 and mask_m is not None:
-        return compress(ev, accs, mask_m, s, tree=tree), True
+        return compress(ev, accs, mask_m, s, tree=tree, hoisted=hoisted_compress), True
     return accs, False
 
 

@@ -31,6 +31,12 @@ BM_PACK_REAL = 0
 BM_PACK_COMPLEX = 1
 BM_LAYOUT_ENCRYPTED = 0x100
 BM_LAYOUT_HOISTED = 0x200
+BM_LAYOUT_HOISTED_ROTSUM = 0x400
+BM_LAYOUT_HOISTED_COMPRESSION = 0x800
+BM_SCHED_HOISTED_EXPANSION = 1
+BM_SCHED_HOISTED_ROTSUM = 2
+BM_SCHED_HOISTED_COMPRESSION = 4
+BM_SCHED_ALL = 7
 BM_KEYS_ENCRYPTED_GALLERY = 1
 BM_KEYS_HOISTED = 2
 BM_EXPAND_DOUBLING = 0
@@ -53,9 +59,9 @@ class bm_params(ctypes.Structure):
 
 
 OPS = {"rotate": 0, "rescale": 1, "mul_plain": 2, "mac": 3, "ntt": 4, "intt": 5, "copy": 6, "mac_ct": 7,
-       "modup": 8, "rot_hoisted": 9, "mac_circ": 10}
+       "modup": 8, "rot_hoisted": 9, "mac_circ": 10, "accum": 11}
 OP_NAMES = {v: k for k, v in OPS.items()}
-BM_OP_KINDS = 11
+BM_OP_KINDS = 12
 BM_MAX_Q = 6
 BM_COST_POINTS = 8
 
@@ -95,6 +101,7 @@ _SIGS = {
     "bm_gallery_import_encrypted": (ctypes.c_int, [_vp, _U64P, _U64P, _U64P, _u64, _u32, _u32, _PP]),
     "bm_gallery_info": (ctypes.c_int, [_vp, _U32P, _U32P]),
     "bm_gallery_set_expansion": (ctypes.c_int, [_vp, _u32]),
+    "bm_gallery_set_schedule": (ctypes.c_int, [_vp, _u32]),
     "bm_secret_key_destroy": (None, [_vp]),
     "bm_public_key_destroy": (None, [_vp]),
     "bm_eval_keys_destroy": (None, [_vp]),
@@ -356,6 +363,11 @@ def bm_gallery_import_encrypted(ctx, cts, masks, cmask, n_ids, dim, part):
 def bm_gallery_set_expansion(g, mode):
     _check(_L.bm_gallery_set_expansion(g.ptr, mode))
     g.hoisted = mode == BM_EXPAND_HOISTED
+
+
+def bm_gallery_set_schedule(g, flags):
+    _check(_L.bm_gallery_set_schedule(g.ptr, flags))
+    g.hoisted = bool(flags & BM_SCHED_HOISTED_EXPANSION)
 
 
 def bm_gallery_info(g):

@@ -57,6 +57,7 @@ struct Layout {
     bool tiled, compress;
     bool encrypted;                         // gallery of ciphertexts (HE-C^3 products ct x ct)
     bool hoisted;                           // Algorithm 1 by hoisted rotations
+    bool hrotsum, hcomp;                    // rotate-and-sum / compression by hoisted rounds
 };
 
 // Scale of the score ciphertexts: 2^log_scale with a plaintext gallery (every
@@ -68,15 +69,27 @@ double result_scale(const Context& c, const Gallery& g) {
 
 static uint32_t gallery_kind(const Gallery& g) {
     return g.packing | (g.encrypted ? BM_LAYOUT_ENCRYPTED : 0u) |
-           (g.expansion == BM_EXPAND_HOISTED ? BM_LAYOUT_HOISTED : 0u);
+           ((g.sched & BM_SCHED_HOISTED_EXPANSION) ? BM_LAYOUT_HOISTED : 0u) |
+           ((g.sched & BM_SCHED_HOISTED_ROTSUM) ? BM_LAYOUT_HOISTED_ROTSUM : 0u) |
+           ((g.sched & BM_SCHED_HOISTED_COMPRESSION) ? BM_LAYOUT_HOISTED_COMPRESSION : 0u);
+}
+
+// baby and giant steps of the hoisted rotate-and-sum over s slots: b = 2^ceil(log2(s)/2)
+static void bsgs_split(uint32_t s, uint32_t& b, uint32_t& g) {
+    const uint32_t lb = ilog2(s);
+    b = 1u << ((lb + 1) / 2);
+    g = s / b;
 }
 
 // `kind`: a BM_PACK_* value, or'ed with BM_LAYOUT_ENCRYPTED for a gallery of ciphertexts
 static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uint32_t part, Layout& lo,
                              uint32_t kind = BM_PACK_REAL) {
-    const uint32_t packing = kind & ~(BM_LAYOUT_ENCRYPTED | BM_LAYOUT_HOISTED);
+    const uint32_t packing = kind & ~(BM_LAYOUT_ENCRYPTED | BM_LAYOUT_HOISTED | BM_LAYOUT_HOISTED_ROTSUM |
+                                      BM_LAYOUT_HOISTED_COMPRESSION);
     lo.encrypted = (kind & BM_LAYOUT_ENCRYPTED) != 0;
     lo.hoisted = (kind & BM_LAYOUT_HOISTED) != 0;
+    lo.hrotsum = (kind & BM_LAYOUT_HOISTED_ROTSUM) != 0;
+    lo.hcomp = (kind & BM_LAYOUT_HOISTED_COMPRESSION) != 0;
     if (!is_pow2(dim) || !is_pow2(part) || part > dim || dim > c.slots)
         return fail(BM_E_DIM, "dim and part size must be powers of two with part <= dim <= N/2");
     if (packing != BM_PACK_REAL && packing != BM_PACK_COMPLEX) return fail(BM_E_ARG, "unknown slot packing");
@@ -92,6 +105,7 @@ static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uin
     lo.level = lo.tiled ? c.L - 1 : c.L;    // level of the query parts entering HE-C^3
     lo.compress = lo.level >= 2;            // a level left after HE-C^3 for the mask
     if (!lo.tiled) lo.hoisted = false;      // no Algorithm 1 on the server
+    if (!lo.compress) lo.hcomp = false;
     lo.n_out = lo.compress ? (lo.groups + part - 1) / part : lo.groups;
     return BM_OK;
 }
@@ -103,8 +117,17 @@ static std::vector<int32_t> schedule_rotations(const Context& c, const Layout& l
         for (uint32_t j = 1; j < lo.n_in; j++) r.push_back((int32_t)(part * j));
     else if (lo.tiled)
         for (uint32_t j = 0; (1u << j) < lo.n_in; j++) r.push_back((int32_t)(part << j));
-    for (uint32_t t = 0; (1u << t) < part; t++) r.push_back((int32_t)(1u << t));
-    if (lo.compress)
+    if (lo.hrotsum) {
+        uint32_t b, g;
+        bsgs_split(part, b, g);
+        for (uint32_t k = 1; k < b; k++) r.push_back((int32_t)k);
+        for (uint32_t k = 1; k < g; k++) r.push_back((int32_t)(b * k));
+    } else {
+        for (uint32_t t = 0; (1u << t) < part; t++) r.push_back((int32_t)(1u << t));
+    }
+    if (lo.compress && lo.hcomp)
+        for (uint32_t k = 1; k < part; k++) r.push_back(-(int32_t)k);
+    else if (lo.compress)
         for (uint32_t t = 0; (1u << t) < part; t++) r.push_back(-(int32_t)(1u << t));
     (void)c;
     return r;
@@ -407,8 +430,13 @@ bm_status bm_keygen_ex(bm_context* ctxh, uint64_t seed, uint32_t dim, uint32_t p
         return true;
     };
     std::vector<int32_t> rots = schedule_rotations(c, lo, part_size);
-    if ((flags & BM_KEYS_HOISTED) && lo.tiled)
-        for (uint32_t j = 1; j < lo.n_in; j++) rots.push_back((int32_t)(part_size * j));   // hoisted Algorithm 1
+    if (flags & BM_KEYS_HOISTED) {
+        Layout all = lo;                                  // every hoisted form
+        all.hoisted = lo.tiled;
+        all.hrotsum = true;
+        all.hcomp = lo.compress;
+        for (int32_t r : schedule_rotations(c, all, part_size)) rots.push_back(r);
+    }
     if (flags & BM_KEYS_ENCRYPTED_GALLERY)
         for (uint32_t b = 0; (1u << b) < c.slots; b++)
             if ((1u << b) >= part_size) rots.push_back(-(int32_t)(1u << b));   // enrollment shifts
@@ -547,9 +575,11 @@ static bm_status gallery_alloc(Context& c, const Layout& lo, uint64_t n_ids, uin
     gh->ref.attach(&c);
     Gallery& g = gh->g;
     g.ctx = &c;
-    g.packing = packing & ~(BM_LAYOUT_ENCRYPTED | BM_LAYOUT_HOISTED);
+    g.packing = packing & ~(BM_LAYOUT_ENCRYPTED | BM_LAYOUT_HOISTED | BM_LAYOUT_HOISTED_ROTSUM |
+                            BM_LAYOUT_HOISTED_COMPRESSION);
     g.encrypted = lo.encrypted;
-    g.expansion = lo.hoisted ? BM_EXPAND_HOISTED : BM_EXPAND_DOUBLING;
+    g.sched = (lo.hoisted ? BM_SCHED_HOISTED_EXPANSION : 0u) | (lo.hrotsum ? BM_SCHED_HOISTED_ROTSUM : 0u) |
+              (lo.hcomp ? BM_SCHED_HOISTED_COMPRESSION : 0u);
     g.id = c.next_id++;
     g.n_ids = n_ids;
     g.dim = dim;
@@ -790,12 +820,12 @@ bm_status bm_enroll_encrypted(bm_context* ctxh, const bm_eval_keys* evk, bm_ciph
     BM_CUDA_TRY(xb.alloc(P * cwL));
     BM_CUDA_TRY(scratch.alloc(std::max(ks_scratch_words(c, (uint32_t)L, maxB), rescale_scratch_words(c, (uint32_t)L, maxB))));
     // pointer lists per chunk: 3P (products) + 2P per shift bit + at most P group
-    // targets + P sums; offsets: one per target and one more (u32, two per word)
+    // targets + P sums; offsets: one per target and one more
     const size_t list_cap = std::max<size_t>(P * (5 + 2 * (lbS - lb0)) + 16, 2 * n_grp + 16);
     BM_CUDA_TRY(plist.alloc(list_cap));
-    BM_CUDA_TRY(olist.alloc(P / 2 + 2));
+    BM_CUDA_TRY(olist.alloc(P + 2));
     std::vector<uint64_t*> hl;
-    std::vector<uint32_t> hoff;
+    std::vector<uint64_t> hoff;
     hl.reserve(list_cap);
     uint64_t** dl = (uint64_t**)plist.p;
     for (uint64_t u0 = 0; u0 < n_ids; u0 += CH) {
@@ -858,12 +888,12 @@ bm_status bm_enroll_encrypted(bm_context* ctxh, const bm_eval_keys* evk, bm_ciph
                     const uint32_t k = u * n_in + i;
                     put((cur[k] ? xb.p : xa.p) + k * cwL);
                 }
-                hoff.push_back((uint32_t)(hl.size() - o_src));
+                hoff.push_back(hl.size() - o_src);
             }
         }
-        if (hl.size() > list_cap || hoff.size() > olist.words * 2) return fail(BM_E_ARG, "enrollment list overflow");
+        if (hl.size() > list_cap || hoff.size() > olist.words) return fail(BM_E_ARG, "enrollment list overflow");
         BM_CUDA_TRY(cudaMemcpyAsync(plist.p, hl.data(), hl.size() * sizeof(void*), cudaMemcpyHostToDevice, s));
-        BM_CUDA_TRY(cudaMemcpyAsync(olist.p, hoff.data(), hoff.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+        BM_CUDA_TRY(cudaMemcpyAsync(olist.p, hoff.data(), hoff.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
         BM_CUDA_TRY(mul_plain(c, (uint32_t)L, np, dl + o_mp, (const uint64_t* const*)(dl + o_mp + np),
                               dl + o_mp + 2 * np, s));
         for (const RotLaunch& r : rl) {
@@ -875,7 +905,7 @@ bm_status bm_enroll_encrypted(bm_context* ctxh, const bm_eval_keys* evk, bm_ciph
             }
         }
         BM_CUDA_TRY(accumulate(c, (uint32_t)L, (uint32_t)(targets.size() * n_in), dl + o_dst,
-                               (const uint64_t* const*)(dl + o_src), (const uint32_t*)olist.p, np, s));
+                               (const uint64_t* const*)(dl + o_src), olist.p, np, s));
         BM_CUDA_TRY(cudaStreamSynchronize(s));           // the host lists are rebuilt for the next chunk
     }
     // one rescale per group ciphertext: top level -> the gallery level
@@ -929,16 +959,25 @@ bm_status bm_gallery_import_encrypted(bm_context* ctxh, const uint64_t* cts, con
     return BM_OK;
 }
 
+bm_status bm_gallery_set_schedule(bm_gallery* gh, uint32_t flags) {
+    if (!gh) return fail(BM_E_ARG, "null gallery");
+    const uint32_t all = BM_SCHED_HOISTED_EXPANSION | BM_SCHED_HOISTED_ROTSUM | BM_SCHED_HOISTED_COMPRESSION;
+    if (flags & ~all) return fail(BM_E_ARG, "unknown schedule flags");
+    Gallery& g = gh->g;
+    if ((flags & BM_SCHED_HOISTED_EXPANSION) && !g.tiled)
+        return fail(BM_E_ARG, "the gallery's queries arrive expanded (no Algorithm 1 on the server)");
+    if (g.sched != flags) {
+        drop_plans(*g.ctx, g.id);
+        g.sched = flags;
+    }
+    return BM_OK;
+}
+
 bm_status bm_gallery_set_expansion(bm_gallery* gh, uint32_t mode) {
     if (!gh) return fail(BM_E_ARG, "null gallery");
     if (mode != BM_EXPAND_DOUBLING && mode != BM_EXPAND_HOISTED) return fail(BM_E_ARG, "unknown expansion");
-    Gallery& g = gh->g;
-    if (!g.tiled) return fail(BM_E_ARG, "the gallery's queries arrive expanded (no Algorithm 1 on the server)");
-    if (g.expansion != mode) {
-        drop_plans(*g.ctx, g.id);
-        g.expansion = mode;
-    }
-    return BM_OK;
+    const uint32_t rest = gh->g.sched & ~(uint32_t)BM_SCHED_HOISTED_EXPANSION;
+    return bm_gallery_set_schedule(gh, rest | (mode == BM_EXPAND_HOISTED ? BM_SCHED_HOISTED_EXPANSION : 0u));
 }
 
 bm_status bm_gallery_info(const bm_gallery* gh, uint32_t* encrypted, uint32_t* packing) {
@@ -1107,6 +1146,8 @@ struct Plan {
     std::vector<void*> bufs;
     uint64_t *qin = nullptr, *t0 = nullptr, *T = nullptr, *accA = nullptr, *accB = nullptr, *accT = nullptr;
     uint64_t *ext = nullptr, *R = nullptr; // hoisted Algorithm 1: query extensions, rotated queries
+    uint64_t *ext2 = nullptr, *rot = nullptr; // hoisted rounds after HE-C^3: extensions, rotated copies
+    size_t hsrc = 0, helem = 0;            // ... their capacities (ciphertexts)
     uint64_t *scratch = nullptr, *result = nullptr;
     size_t scratch_words = 0, result_words = 0, qin_words = 0;
     PtrArena arena;
@@ -1142,7 +1183,7 @@ void drop_plans(Context& c, uint64_t id) {
 // launch pass, where its plaintexts live.
 struct SchedView {
     uint32_t n_in = 0, part = 0, level = 0, groups = 0;
-    bool tiled = true, compress = true, encrypted = false, hoisted = false;
+    bool tiled = true, compress = true, encrypted = false, hoisted = false, hrotsum = false, hcomp = false;
     const uint64_t* d_pts = nullptr;
     const uint64_t* d_masks = nullptr;
     const uint64_t* d_cmask = nullptr;
@@ -1157,7 +1198,9 @@ static SchedView view_of(const Gallery& g) {
     v.tiled = g.tiled;
     v.compress = g.compress;
     v.encrypted = g.encrypted;
-    v.hoisted = g.tiled && g.expansion == BM_EXPAND_HOISTED;
+    v.hoisted = g.tiled && (g.sched & BM_SCHED_HOISTED_EXPANSION);
+    v.hrotsum = (g.sched & BM_SCHED_HOISTED_ROTSUM) != 0;
+    v.hcomp = g.compress && (g.sched & BM_SCHED_HOISTED_COMPRESSION);
     v.d_pts = g.d_pts;
     v.d_masks = g.d_masks;
     v.d_cmask = g.d_cmask;
@@ -1174,6 +1217,8 @@ static SchedView view_of(const Layout& lo, uint32_t part) {
     v.compress = lo.compress;
     v.encrypted = lo.encrypted;
     v.hoisted = lo.hoisted;
+    v.hrotsum = lo.hrotsum;
+    v.hcomp = lo.hcomp;
     return v;
 }
 
@@ -1245,15 +1290,58 @@ struct MatchRun {
         check(mul_plain(c, level, (uint32_t)in.size(), din, dpt, dout, s));
     }
 
-    // hoisted Algorithm 1: basis extension of the queries' c1 into pl.ext
-    void modup_batch(uint32_t level, const std::vector<uint64_t*>& in) {
+    // hoisted rotations: basis extension of the ciphertexts' c1 into ext (per ciphertext ks_ext_words)
+    void modup_batch(uint32_t level, const std::vector<uint64_t*>& in, uint64_t* ext) {
         auto din = pl.arena.list(in);
         record(BM_OP_MODUP, level, in.size());
         if (!pl.arena.live) {
             need_scratch(ks_modup_scratch_words(c, level, (uint32_t)in.size()));
             return;
         }
-        check(ks_modup_hoisted(c, level, (uint32_t)in.size(), din, pl.ext, pl.scratch, s));
+        check(ks_modup_hoisted(c, level, (uint32_t)in.size(), din, ext, pl.scratch, s));
+    }
+    // dst[t] += the ciphertexts of srcs[t] (one launch)
+    void accumulate_batch(uint32_t level, const std::vector<uint64_t*>& dst,
+                          const std::vector<std::vector<uint64_t*>>& srcs) {
+        std::vector<uint64_t*> flat, off{reinterpret_cast<uint64_t*>((uintptr_t)0)};
+        for (const auto& l : srcs) {
+            flat.insert(flat.end(), l.begin(), l.end());
+            off.push_back(reinterpret_cast<uint64_t*>((uintptr_t)flat.size()));
+        }
+        auto dd = pl.arena.list(dst);
+        auto ds = pl.arena.list(flat);
+        auto doff = pl.arena.list(off);
+        record(BM_OP_ACCUM, level, flat.size());
+        if (!pl.arena.live || flat.empty()) return;
+        check(accumulate(c, level, (uint32_t)dst.size(), dd, (const uint64_t* const*)ds, (const uint64_t*)doff,
+                         (uint32_t)flat.size(), s));
+    }
+    // One round of hoisted rotations: every source is extended once; element e rotates
+    // source e_src[e] by e_rot[e]; target t then gains the rotated elements t_elems[t]
+    // (dst[t] += sum).  Targets may be sources: the sums follow every rotation.
+    void hoisted_round(uint32_t level, const std::vector<uint64_t*>& srcs, const std::vector<uint32_t>& e_src,
+                       const std::vector<int32_t>& e_rot, const std::vector<uint64_t*>& tgts,
+                       const std::vector<std::vector<uint32_t>>& t_elems) {
+        const size_t ew = ks_ext_words(c, level), cwl = cw(level);
+        for (size_t s0 = 0; s0 < srcs.size(); s0 += ksb) {
+            std::vector<uint64_t*> chunk(srcs.begin() + s0, srcs.begin() + std::min(srcs.size(), s0 + ksb));
+            modup_batch(level, chunk, pl.ext2 + s0 * ew);
+        }
+        std::vector<uint64_t*> ext_of, src, keys, gal, out;
+        for (size_t e = 0; e < e_src.size(); e++) {
+            ext_of.push_back(pl.ext2 + (size_t)e_src[e] * ew);
+            src.push_back(srcs[e_src[e]]);
+            keys.push_back(const_cast<uint64_t*>(key(e_rot[e])));
+            gal.push_back(reinterpret_cast<uint64_t*>((uintptr_t)galois_of(c, e_rot[e])));
+            out.push_back(pl.rot + e * cwl);
+        }
+        hoisted_batch(level, ext_of, src, keys, gal, out);
+        std::vector<std::vector<uint64_t*>> lists;
+        for (const auto& te : t_elems) {
+            lists.emplace_back();
+            for (uint32_t e : te) lists.back().push_back(pl.rot + (size_t)e * cwl);
+        }
+        accumulate_batch(level, tgts, lists);
     }
     // ... rotations of the extended queries (per element: extension, source, key, Galois element)
     void hoisted_batch(uint32_t level, const std::vector<uint64_t*>& ext_of, const std::vector<uint64_t*>& src,
@@ -1294,7 +1382,7 @@ struct MatchRun {
                 const uint32_t nq = std::min(pl.qe, Q - qb);
                 std::vector<uint64_t*> qs, ext_of, src, keys, gal, out, R, o0, o1;
                 for (uint32_t q = 0; q < nq; q++) qs.push_back(pl.qin + (size_t)(qb + q) * cw(c.L));
-                if (n_in > 1) modup_batch(c.L, qs);
+                if (n_in > 1) modup_batch(c.L, qs, pl.ext);
                 for (uint32_t q = 0; q < nq; q++)
                     for (uint32_t j = 1; j < n_in; j++) {
                         ext_of.push_back(pl.ext + (size_t)q * ew);
@@ -1354,7 +1442,28 @@ struct MatchRun {
             // (d0, d1, d2) -> (d0 + KS(d2)_0, d1 + KS(d2)_1) with t = (d0, d2), a = (0, d1)
             if (g.encrypted) rotate_batch(lg, 0, t, a, &a, true);
             rescale_batch(lg, a, b);
-            for (uint32_t t = 1; (1u << (t - 1)) < part; t++) rotate_batch(lg - 1, (int32_t)(1u << (t - 1)), b, b, &b);
+            if (g.hrotsum) {
+                // sum_{r<part} Rot(acc, r) in two hoisted rounds: baby steps 1..bs-1, giant steps bs*k
+                uint32_t bs, gs;
+                bsgs_split(part, bs, gs);
+                const uint32_t rounds[2][2] = {{1, bs}, {bs, gs}};
+                for (const auto& rd : rounds) {
+                    if (rd[1] <= 1) continue;
+                    std::vector<uint32_t> e_src;
+                    std::vector<int32_t> e_rot;
+                    std::vector<std::vector<uint32_t>> t_elems(b.size());
+                    for (uint32_t k = 0; k < b.size(); k++)
+                        for (uint32_t r = 1; r < rd[1]; r++) {
+                            t_elems[k].push_back((uint32_t)e_src.size());
+                            e_src.push_back(k);
+                            e_rot.push_back((int32_t)(rd[0] * r));
+                        }
+                    hoisted_round(lg - 1, b, e_src, e_rot, b, t_elems);
+                }
+            } else {
+                for (uint32_t t = 1; (1u << (t - 1)) < part; t++)
+                    rotate_batch(lg - 1, (int32_t)(1u << (t - 1)), b, b, &b);
+            }
             if (!g.compress) {
                 // per-group outputs at level 0: copy into the result
                 for (uint32_t q = 0; q < Q; q++) {
@@ -1370,8 +1479,28 @@ struct MatchRun {
             const uint32_t lc = lg - 1;
             std::vector<uint64_t*> mp(b.size(), const_cast<uint64_t*>(g.d_cmask));
             mulplain_batch(lc, b, mp, b);
+            if (g.hcomp) {
+                // linear form: every group r > 0 of a pack rotated right by r in one hoisted round,
+                // summed into the pack's first group
+                std::vector<uint64_t*> srcs, heads;
+                std::vector<uint32_t> e_src;
+                std::vector<int32_t> e_rot;
+                std::vector<std::vector<uint32_t>> t_elems;
+                for (uint32_t q = 0; q < Q; q++)
+                    for (uint32_t k = 0; k < G; k += part) {
+                        heads.push_back(pl.accB + ((size_t)q * G + k) * cw(lc));
+                        t_elems.emplace_back();
+                        for (uint32_t r = 1; r < part && k + r < G && g0 + k + r < g.groups; r++) {
+                            t_elems.back().push_back((uint32_t)e_src.size());
+                            e_src.push_back((uint32_t)srcs.size());
+                            e_rot.push_back(-(int32_t)r);
+                            srcs.push_back(pl.accB + ((size_t)q * G + k + r) * cw(lc));
+                        }
+                    }
+                if (!srcs.empty()) hoisted_round(lc, srcs, e_src, e_rot, heads, t_elems);
+            }
             // tree of right rotations: level bb pairs r and r + 2^bb (r = 0 mod 2^(bb+1)) inside each pack
-            for (uint32_t bb = 0; (1u << bb) < part; bb++) {
+            for (uint32_t bb = 0; !g.hcomp && (1u << bb) < part; bb++) {
                 std::vector<uint64_t*> odd, even;
                 for (uint32_t q = 0; q < Q; q++)
                     for (uint32_t k = 0; k < G; k += (2u << bb)) {
@@ -1403,11 +1532,23 @@ static void plan_dims(const Context& c, const SchedView& g, uint32_t n_out, uint
     pl.ncts = g.tiled ? 1 : g.n_in;
     pl.n_out = n_out;
     const uint32_t lg = g.level;
-    const size_t per_group = (size_t)Q * ((g.encrypted ? 2 : 1) * ct_words(c, lg) + ct_words(c, lg - 1)) * 8;
+    // hoisted rounds after HE-C^3: sources and rotated copies per group of a query
+    uint32_t per_src = 0;
+    if (g.hrotsum) {
+        uint32_t bs, gs;
+        bsgs_split(g.part, bs, gs);
+        per_src = std::max(bs, gs) - 1;
+    }
+    if (g.hcomp) per_src = std::max<uint32_t>(per_src, 1);
+    const size_t hold = per_src ? ks_ext_words(c, lg - 1) + (size_t)per_src * ct_words(c, lg - 1) : 0;
+    const size_t per_group =
+        (size_t)Q * ((g.encrypted ? 2 : 1) * ct_words(c, lg) + ct_words(c, lg - 1) + hold) * 8;
     const size_t budget = (size_t)8 << 30;
     uint32_t chunk = (uint32_t)std::max<size_t>(1, budget / std::max<size_t>(per_group, 1));
     if (g.compress) chunk = std::max(g.part, chunk / g.part * g.part);
     pl.chunk = std::min(chunk, g.groups);
+    pl.hsrc = per_src ? (size_t)Q * pl.chunk : 0;
+    pl.helem = pl.hsrc * per_src;
     pl.qin_words = (size_t)Q * pl.ncts * ct_words(c, c.L);
     pl.result_words = (size_t)Q * n_out * ct_words(c, 0);
     // hoisted Algorithm 1: rotated copies and products of a chunk of queries within ~4 GiB
@@ -1438,6 +1579,10 @@ static std::vector<BufSpec> plan_buffers(const Context& c, const SchedView& g, P
     b.push_back({&pl.accA, (size_t)Q * pl.chunk * ct_words(c, lg)});
     b.push_back({&pl.accB, (size_t)Q * pl.chunk * ct_words(c, lg - 1)});
     if (g.encrypted) b.push_back({&pl.accT, (size_t)Q * pl.chunk * ct_words(c, lg)});
+    if (pl.hsrc) {
+        b.push_back({&pl.ext2, pl.hsrc * ks_ext_words(c, lg - 1)});
+        b.push_back({&pl.rot, pl.helem * ct_words(c, lg - 1)});
+    }
     return b;
 }
 

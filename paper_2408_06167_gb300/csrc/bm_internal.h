@@ -170,7 +170,7 @@ struct Gallery {
     bool compress = true;                     // outputs are masked and packed
     uint32_t packing = BM_PACK_REAL;          // BM_PACK_COMPLEX: a second identity in the imaginary parts
     bool encrypted = false;                   // d_pts holds ciphertexts [groups][n_in][2][level+1][N]
-    uint32_t expansion = BM_EXPAND_DOUBLING;  // form of Algorithm 1 (BM_EXPAND_*)
+    uint32_t sched = 0;                       // hoisted forms of the schedule (BM_SCHED_* flags)
     uint64_t* d_pts = nullptr;                // [groups][n_in][level+1][N] NTT + Montgomery
     uint64_t* d_masks = nullptr;              // [n_in][L+1][N] Algorithm-1 masks (tiled only)
     uint64_t* d_cmask = nullptr;              // [level][N] compression mask at level-1
@@ -359,7 +359,7 @@ cudaError_t mac_circ(const Context& c, uint32_t level, uint32_t Q, uint32_t n_in
                      const uint64_t* masks, uint64_t* t0, cudaStream_t s);
 // dst[t] += sum of src[off[t] .. off[t+1]) (ciphertexts at `level`; off and the lists on the device)
 cudaError_t accumulate(const Context& c, uint32_t level, uint32_t n_targets, uint64_t* const* dst,
-                       const uint64_t* const* src, const uint32_t* off, uint32_t n_src, cudaStream_t s);
+                       const uint64_t* const* src, const uint64_t* off, uint32_t n_src, cudaStream_t s);
 // encrypted gallery: A[q][g] = (d0, d2), B[q][g] = (0, d1) of sum_i T[q][i] (x) C[g][i]
 // (C: [G][n_in][2][level+1][N] Montgomery form)
 cudaError_t mac_ct(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32_t n_in, const uint64_t* T,

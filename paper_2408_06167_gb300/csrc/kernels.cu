@@ -601,15 +601,16 @@ __global__ void __launch_bounds__(kThreads) k_mac_circ(const uint64_t* const* R,
 
 // dst[t] += sum of src[k], k in [off[t], off[t+1]): ciphertexts [2][l1][N] at one
 // level; grid (targets * 2 * l1, chunks of a limb)
-__global__ void k_accumulate(uint64_t* const* dst, const uint64_t* const* src, const uint32_t* off, uint32_t l1,
+__global__ void k_accumulate(uint64_t* const* dst, const uint64_t* const* src, const uint64_t* off, uint32_t l1,
                              DevTables tab, uint32_t n) {
     const uint32_t t = blockIdx.x / (2 * l1), r = blockIdx.x % (2 * l1), j = r % l1;
     const uint64_t q = tab.q[j];
+    pdl_wait();
     uint64_t* d = dst[t] + (size_t)r * n;
-    const uint32_t k0 = off[t], k1 = off[t + 1];
+    const uint64_t k0 = off[t], k1 = off[t + 1];
     for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x) {
         uint64_t acc = d[i];
-        for (uint32_t k = k0; k < k1; k++) acc = addm(acc, src[k][(size_t)r * n + i], q);
+        for (uint64_t k = k0; k < k1; k++) acc = addm(acc, src[k][(size_t)r * n + i], q);
         d[i] = acc;
     }
 }
@@ -955,12 +956,11 @@ cudaError_t mac_ct(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uin
 }
 
 cudaError_t accumulate(const Context& c, uint32_t level, uint32_t n_targets, uint64_t* const* dst,
-                       const uint64_t* const* src, const uint32_t* off, uint32_t n_src, cudaStream_t s) {
+                       const uint64_t* const* src, const uint64_t* off, uint32_t n_src, cudaStream_t s) {
     if (!n_targets) return cudaSuccess;
     ProfScope ps(BM_KERNEL_OTHER, s, 16.0 * c.n * (level + 1) * (n_targets + n_src));
-    k_accumulate<<<dim3(n_targets * 2 * (level + 1), c.n / kThreads / 4), kThreads, 0, s>>>(dst, src, off, level + 1,
-                                                                                            c.tab, c.n);
-    return cudaGetLastError();
+    return pdl_launch(k_accumulate, dim3(n_targets * 2 * (level + 1), c.n / kThreads / 4), kThreads, 0, s, dst, src,
+                      off, level + 1, c.tab, c.n);
 }
 
 cudaError_t mac_circ(const Context& c, uint32_t level, uint32_t Q, uint32_t n_in, const uint64_t* const* R,

@@ -269,8 +269,9 @@ bm_status bm_measure_op_costs(bm_context* ctxh, bm_op_costs* out) {
         }
     }
     if (ks_fused_supported(c)) {
-        // hoisted Algorithm 1 at the top level: basis extension of 1..128 ciphertexts,
-        // 1..128 rotations from extensions, circulant products of 4 queries x 2^k parts
+        // hoisted rotations at every level: basis extension of 1..128 ciphertexts, 1..128
+        // rotations from extensions, sums of 1..128 ciphertexts; at the top level the
+        // circulant products of hoisted Algorithm 1, 4 queries x 2^k parts
         const size_t cw = ct_words(c, L), ew = ks_ext_words(c, L);
         DevBuf in, outb, ext, scratch, key, masks, t0, plist;
         BM_CUDA_TRY(in.alloc(cw * kMaxB));
@@ -294,24 +295,42 @@ bm_status bm_measure_op_costs(bm_context* ctxh, bm_op_costs* out) {
         BM_CUDA_TRY(plist.alloc(h.size()));
         BM_CUDA_TRY(cudaMemcpy(plist.p, h.data(), h.size() * sizeof(void*), cudaMemcpyHostToDevice));
         uint64_t* const* dl = (uint64_t* const*)plist.p;
-        for (int k = 0; k < BM_COST_POINTS; k++) {
-            const uint32_t B = 1u << k;
-            const int r = reps_for(B);
-            out->t_us[BM_OP_MODUP][L][k] =
-                tm.us([&] { return ks_modup_hoisted(c, L, B, (uint64_t* const*)(dl + kMaxB), ext.p, scratch.p, s); },
-                      2, r);
-            out->t_us[BM_OP_ROT_HOISTED][L][k] = tm.us(
-                [&] {
-                    return ks_rotate_hoisted(c, L, B, (const uint64_t* const*)dl, (const uint64_t* const*)(dl + kMaxB),
-                                             (const uint64_t* const*)(dl + 2 * kMaxB),
-                                             (const uint64_t*)(dl + 3 * kMaxB), dl + 4 * kMaxB, scratch.p, s);
-                },
-                2, r);
-            out->t_us[BM_OP_MAC_CIRC][L][k] = tm.us(
-                [&] { return mac_circ(c, L, kMacQ, B, (const uint64_t* const*)(dl + 5 * kMaxB), masks.p, t0.p, s); },
-                2, r);
+        // accumulation lists: B targets, one source each (offsets 0..B)
+        DevBuf offs;
+        std::vector<uint64_t> ho(kMaxB + 1);
+        for (uint32_t k = 0; k <= kMaxB; k++) ho[k] = k;
+        BM_CUDA_TRY(offs.alloc(kMaxB + 1));
+        BM_CUDA_TRY(cudaMemcpy(offs.p, ho.data(), (kMaxB + 1) * 8, cudaMemcpyHostToDevice));
+        for (uint32_t level = 0; level <= L; level++) {
+            for (int k = 0; k < BM_COST_POINTS; k++) {
+                const uint32_t B = 1u << k;
+                const int r = reps_for(B);
+                out->t_us[BM_OP_MODUP][level][k] = tm.us(
+                    [&] { return ks_modup_hoisted(c, level, B, (uint64_t* const*)(dl + kMaxB), ext.p, scratch.p, s); },
+                    2, r);
+                out->t_us[BM_OP_ROT_HOISTED][level][k] = tm.us(
+                    [&] {
+                        return ks_rotate_hoisted(c, level, B, (const uint64_t* const*)dl,
+                                                 (const uint64_t* const*)(dl + kMaxB),
+                                                 (const uint64_t* const*)(dl + 2 * kMaxB),
+                                                 (const uint64_t*)(dl + 3 * kMaxB), dl + 4 * kMaxB, scratch.p, s);
+                    },
+                    2, r);
+                out->t_us[BM_OP_ACCUM][level][k] = tm.us(
+                    [&] {
+                        return accumulate(c, level, B, dl + 4 * kMaxB, (const uint64_t* const*)(dl + kMaxB), offs.p,
+                                          B, s);
+                    },
+                    2, r);
+                if (level == L)
+                    out->t_us[BM_OP_MAC_CIRC][L][k] = tm.us(
+                        [&] {
+                            return mac_circ(c, L, kMacQ, B, (const uint64_t* const*)(dl + 5 * kMaxB), masks.p, t0.p, s);
+                        },
+                        2, r);
+            }
+            BM_CUDA_TRY(tm.err);
         }
-        BM_CUDA_TRY(tm.err);
     }
     {
         // HE-C^3 products: 4 queries x 8 parts x 1..128 groups, at the levels a

@@ -34,6 +34,11 @@ def schedule_rotations(ctx, m, s, hoisted=False):
     rots += [1 << t for t in range(sch.log2i(s))]
     if level >= 2:
         rots += [-(1 << t) for t in range(sch.log2i(s))]
+    if hoisted:
+        b, g = sch.bsgs_split(s)
+        rots += list(range(1, b)) + [b * k for k in range(1, g)]
+        if level >= 2:
+            rots += [-r for r in range(1, s)]
     return rots
 
 
@@ -41,19 +46,20 @@ class OracleMatch:
     """Keys, gallery plaintexts, query ciphertexts and match outputs from the oracle."""
 
     def __init__(self, name, m, s, R, n_queries, feats=None, seed=KEY_SEED, complex_pack=False, encrypted=False,
-                 hoisted=False):
+                 hoisted=False, hoisted_tail=False):
         self.ctx = ctx = octx(name)
         self.m, self.s, self.R = m, s, R
         self.complex_pack = complex_pack
         self.encrypted = encrypted
         self.hoisted = hoisted
+        self.hoisted_tail = hoisted_tail
         self.n_in = m // s
         self.tiled = ctx.L >= 3
         self.level = ctx.L - 1 if self.tiled else ctx.L
         self.compress = self.level >= 2
         self.feats = wl.gallery(R, m) if feats is None else feats
         self.queries, self.true_ids = wl.queries(self.feats, n_queries)
-        self.sk, self.pk, self.rks = ckks.keygen(ctx, seed, schedule_rotations(ctx, m, s, hoisted))
+        self.sk, self.pk, self.rks = ckks.keygen(ctx, seed, schedule_rotations(ctx, m, s, hoisted or hoisted_tail))
         self.ev = ckks.Evaluator(ctx, self.rks, ckks.keygen_relin(ctx, seed, self.sk) if encrypted else None)
         S, L = ctx.slots, ctx.L
         self.groups = sch.n_groups(R, s, S, complex_pack)
@@ -105,7 +111,8 @@ class OracleMatch:
     def match(self, cts):
         outs, packed = sch.match(self.ev, cts, self.gal, self.masks, self.cmask, self.m, self.s,
                                  expanded=not self.tiled, encrypted_gallery=self.encrypted,
-                                 hoisted=self.hoisted)
+                                 hoisted=self.hoisted, hoisted_rotsum=self.hoisted_tail,
+                                 hoisted_compress=self.hoisted_tail)
         return self.ct_array(outs), packed
 
     def scores(self, outs_array, packed):

@@ -46,6 +46,33 @@ def test_hoisted_match_is_bit_exact(name, m, s, R, nq):
         assert np.abs(om.scores(got, opacked) - ref).max() < 1e-5
 
 
+@pytest.mark.parametrize("name,m,s,R,nq,tail_only", [
+    ("small4", 128, 16, 2500, 2, False),   # every hoisted form: rotate-and-sum 4 x 4, compression 15 rotations
+    ("small4", 16, 4, 3000, 3, False),     # rotate-and-sum 2 x 2, partial packs
+    ("small4", 32, 32, 700, 1, True),      # rotate-and-sum 8 x 4 after the printed Algorithm 1
+    ("small4", 16, 8, 2100, 1, False),     # rotate-and-sum 4 x 2
+    ("toy", 16, 4, 1500, 2, True),         # client-expanded queries, per-group outputs (no compression)
+])
+def test_hoisted_schedule_is_bit_exact(name, m, s, R, nq, tail_only):
+    c = gctx(name)
+    om = OracleMatch(name, m, s, R, nq, hoisted=not tail_only and name != "toy", hoisted_tail=True)
+    _, _, ek = bm.bm_keygen_ex(c, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
+    g = bm.bm_gallery_import(c, om.pts_array(), om.masks_array(), om.cmask_array(), R, m, s)
+    flags = bm.BM_SCHED_HOISTED_ROTSUM | bm.BM_SCHED_HOISTED_COMPRESSION
+    if om.hoisted:
+        flags |= bm.BM_SCHED_HOISTED_EXPANSION
+    bm.bm_gallery_set_schedule(g, flags)
+    ocs = [om.encrypt(qi) for qi in range(nq)]
+    qs = [bm.bm_ciphertext_import(c, om.ct_array(cts), om.ctx.L) for cts in ocs]
+    res = bm.bm_match(c, ek, g, qs)
+    for qi in range(nq):
+        want, opacked = om.match(ocs[qi])
+        got = bm.bm_result_export(res, qi)
+        assert np.array_equal(got, want), f"query {qi}: ciphertexts differ"
+        ref = wl.plaintext_scores(om.feats, om.queries[qi])
+        assert np.abs(om.scores(got, opacked) - ref).max() < 1e-5
+
+
 @pytest.mark.parametrize("m,s,R,nq", [(128, 16, 6144, 1), (128, 4, 20000, 3)])
 def test_hoisted_and_doubling_forms_give_the_same_scores_ring16(m, s, R, nq):
     c = gctx("ring16")
@@ -54,7 +81,7 @@ def test_hoisted_and_doubling_forms_give_the_same_scores_ring16(m, s, R, nq):
     sk, pk, ek = bm.bm_keygen_ex(c, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
     gd = bm.bm_encode_gallery(c, feats, m, s)
     gh = bm.bm_encode_gallery(c, feats, m, s)
-    bm.bm_gallery_set_expansion(gh, bm.BM_EXPAND_HOISTED)
+    bm.bm_gallery_set_schedule(gh, bm.BM_SCHED_ALL)
     cts = bm.bm_encrypt_batch(c, pk, qs, m, s, bm.BM_QUERY_TILED, 4, 0)
     rd, rh = bm.bm_match(c, ek, gd, cts), bm.bm_match(c, ek, gh, cts)
     for qi in range(nq):

@@ -281,3 +281,25 @@ def test_hoisted_rotation_permutes_slots():
         for r, o in zip([1, 5, -3, 100], outs):
             d = ckks.decrypt_decode(ctx, o, sk).real
             assert np.abs(d - np.roll(z, -r)).max() < 1e-6, (level, r)
+
+
+@pytest.mark.parametrize("m,s,R", [(128, 16, 2500), (16, 4, 3000), (32, 32, 700), (16, 8, 3000)])
+def test_hoisted_rotate_and_sum_and_compression_scores(m, s, R):
+    """Algorithm 2's rotate-and-sum as two rounds of hoisted rotations and the
+    linear compression with hoisted rotations give the FP64 scores."""
+    b, g = sch.bsgs_split(s)
+    extra = [k for k in range(1, b)] + [b * k for k in range(1, g)] + [-r for r in range(1, s)]
+    ctx, sk, pk, ev = _setup("small4", m, s, R, extra_rots=extra)
+    S, L, n_in = ctx.slots, ctx.L, m // s
+    feats = wl.gallery(R, m)
+    q = wl.queries(feats, 1)[0][0]
+    ct = ckks.encrypt(ctx, pk, ctx.encode(sch.tiled_query_slots(q, S), ctx.scale, L), 4, 0)
+    masks = [ctx.encode(sch.alg1_mask_slots(m, s, i, S), ctx.q[L], L) for i in range(n_in)]
+    gal = [[ctx.encode(sch.gallery_slots(feats, gg, i, s, S), ctx.q[L - 1], L - 1) for i in range(n_in)]
+           for gg in range(sch.n_groups(R, s, S))]
+    mm = ctx.encode(sch.compression_mask_slots(s, S), ctx.q[L - 2], L - 2)
+    ref = wl.plaintext_scores(feats, q)
+    outs, packed = sch.match(ev, [ct], gal, masks, mm, m, s, hoisted_rotsum=True, hoisted_compress=True)
+    dec = [ckks.decrypt_decode(ctx, o, sk).real for o in outs]
+    got = np.array([dec[o][slot] for o, slot, _ in (sch.identity_slot(i, s, S, packed) for i in range(R))])
+    assert np.abs(got - ref).max() < 1e-5
