@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--expansion", default="hoisted", choices=["doubling", "hoisted", "auto"],
                     help="form of Algorithm 1: the printed doubling order or the hoisted sum "
                          "(auto: serving picks per gallery by the cost model)")
+    ap.add_argument("--tail", default="printed", choices=["printed", "hoisted"],
+                    help="Algorithm 2's rotate-and-sum and the compression: the printed sequential forms or "
+                         "rounds of hoisted rotations")
     ap.add_argument("--gallery", default="plain", choices=["plain", "encrypted"],
                     help="gallery of plaintexts, or of ciphertexts enrolled on the server (Sec. 3.2)")
     ap.add_argument("--packing", default="real", choices=["real", "complex"],
@@ -263,19 +266,22 @@ def run_serving(args):
     packing = bm.BM_PACK_COMPLEX if args.packing == "complex" else bm.BM_PACK_REAL
     expansions = {}
     for gi, (name, R, m, s) in enumerate(SERVE_GALLERIES):
-        hoist = args.expansion == "hoisted"
+        if args.expansion == "auto":
+            forms = [(e, t) for e in ("doubling", "hoisted") for t in ("printed", "hoisted")]
+        else:
+            forms = [(args.expansion, args.tail)]
         if costs is not None:
-            # the cost model's part size (and, with --expansion auto, form of Algorithm 1)
-            # for a typical batch of 16 queries
-            forms = [False, True] if args.expansion == "auto" else [hoist]
-            best = min(((bm.bm_choose_part("ring16", costs, R, m, 16, 32 << 30,
-                                           packing | (bm.BM_LAYOUT_HOISTED if h else 0)), h) for h in forms),
-                       key=lambda x: x[0][1])
-            (s, _), hoist = best
-        elif args.expansion == "auto":
-            hoist = False
+            # the cost model's part size (and, with --expansion auto, hoisted forms) for a
+            # typical batch of 16 queries
+            best = min(((bm.bm_choose_part("ring16", costs, R, m, 16, 32 << 30, packing | sched_flags(bm, *f)[1]), f)
+                        for f in forms), key=lambda x: x[0][1])
+            (s, _), form = best
+        else:
+            form = forms[0] if args.expansion != "auto" else ("doubling", "printed")
+        flags, _ = sched_flags(bm, *form)
         parts[name] = s
-        expansions[name] = "hoisted" if hoist else "doubling"
+        expansions[name] = "+".join(x for x, on in (("hoisted-expansion", flags & 1), ("hoisted-rotsum", flags & 2),
+                                                    ("hoisted-compression", flags & 4)) if on) or "printed"
         if (m, s) not in keys:
             keys[(m, s)] = bm.bm_keygen_ex(ctx, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
         feats = wl.gallery(R, m, seed=10 + gi)
@@ -283,8 +289,7 @@ def run_serving(args):
         sk, pk, ek = keys[(m, s)]
         cts = [bm.bm_encrypt_query(ctx, pk, q, m, s, bm.BM_QUERY_TILED, ENC_SEED, i) for i, q in enumerate(qs)]
         g = bm.bm_encode_gallery_packed(ctx, feats, m, s, packing)
-        if hoist:
-            bm.bm_gallery_set_expansion(g, bm.BM_EXPAND_HOISTED)
+        bm.bm_gallery_set_schedule(g, flags)
         gals.append(dict(name=name, R=R, g=g, ek=ek, cts=cts))
     # plain unbatched form: one query per bm_match, per gallery
     stream = torch.cuda.current_stream()
@@ -348,6 +353,16 @@ def run_serving(args):
     print(json.dumps(line))
 
 
+def sched_flags(bm, expansion, tail):
+    """(gallery schedule flags, model layout flags) of the chosen forms."""
+    f = bm.BM_SCHED_HOISTED_EXPANSION if expansion == "hoisted" else 0
+    if tail == "hoisted":
+        f |= bm.BM_SCHED_HOISTED_ROTSUM | bm.BM_SCHED_HOISTED_COMPRESSION
+    lay = ((bm.BM_LAYOUT_HOISTED if f & 1 else 0) | (bm.BM_LAYOUT_HOISTED_ROTSUM if f & 2 else 0)
+           | (bm.BM_LAYOUT_HOISTED_COMPRESSION if f & 4 else 0))
+    return f, lay
+
+
 def run_sweep(args):
     """Sec. 4 on this GPU: the match of the workload at every part size (N_in =
     dim / part), each measured (CUDA events, L2 flushed between steps) beside
@@ -369,9 +384,9 @@ def run_sweep(args):
     mode = bm.BM_QUERY_TILED if W.query_mode == "tiled" else bm.BM_QUERY_EXPANDED
     parts = [p for p in (128, 64, 32, 16, 8, 4, 2, 1) if p <= W.dim]
     packing = bm.BM_PACK_COMPLEX if args.packing == "complex" else bm.BM_PACK_REAL
-    hoisted = args.expansion == "hoisted"
-    if hoisted:
-        packing |= bm.BM_LAYOUT_HOISTED
+    flags, lay = sched_flags(bm, args.expansion, args.tail)
+    hoisted = flags != 0
+    packing |= lay
     pred = {p: bm.bm_predict_match(W.preset, costs, W.n_ids, W.dim, p, W.n_queries, packing) for p in parts}
     fitting = [p for p in parts if pred[p][1] <= budget]
     best_pred = min(pred[p][0] for p in fitting)
@@ -398,9 +413,8 @@ def run_sweep(args):
             rows.append(row)
             continue
         sk, pk, ek = bm.bm_keygen_ex(ctx, KEY_SEED, W.dim, p, bm.BM_KEYS_HOISTED if hoisted else 0)
-        gal = bm.bm_encode_gallery_packed(ctx, feats, W.dim, p, packing & ~bm.BM_LAYOUT_HOISTED)
-        if hoisted:
-            bm.bm_gallery_set_expansion(gal, bm.BM_EXPAND_HOISTED)
+        gal = bm.bm_encode_gallery_packed(ctx, feats, W.dim, p, packing & 0xff)
+        bm.bm_gallery_set_schedule(gal, flags)
         cts = [bm.bm_encrypt_query(ctx, pk, q, W.dim, p, mode, ENC_SEED, i) for i, q in enumerate(qs)]
         for ct in cts:
             bm.bm_ciphertext_upload(ct, sptr)
@@ -436,7 +450,7 @@ def run_sweep(args):
         "config": {"workload": W.name, "mode": "part-sweep", "ring": "2^16" if W.preset == "ring16" else W.preset,
                    "n_ids": W.n_ids, "dim": W.dim, "queries_per_step": W.n_queries,
                    "l2": "flushed between steps (512 MiB write)", "packing": args.packing,
-                   "expansion": args.expansion, "ks_wide_batch": wide},
+                   "expansion": args.expansion, "tail": args.tail, "ks_wide_batch": wide},
         "sweep": rows, "model_part": model_part, "measured_best_part": best["part"],
         "model_part_measured_ms": next((r.get("measured_ms") for r in rows if r["part"] == model_part), None),
         "clocks": clocks,
@@ -480,11 +494,10 @@ def main():
         del temps
         enroll = {"encrypt_templates_s": t1 - t0, "enroll_s": t2 - t1}
     else:
-        sk, pk, ek = bm.bm_keygen_ex(ctx, KEY_SEED, W.dim, part,
-                                     bm.BM_KEYS_HOISTED if args.expansion == "hoisted" else 0)
+        flags, _ = sched_flags(bm, args.expansion if W.query_mode == "tiled" else "doubling", args.tail)
+        sk, pk, ek = bm.bm_keygen_ex(ctx, KEY_SEED, W.dim, part, bm.BM_KEYS_HOISTED if flags else 0)
         gal = bm.bm_encode_gallery_packed(ctx, feats, W.dim, part, packing)
-        if args.expansion == "hoisted" and W.query_mode == "tiled":
-            bm.bm_gallery_set_expansion(gal, bm.BM_EXPAND_HOISTED)
+        bm.bm_gallery_set_schedule(gal, flags)
     qs, _ = wl.queries(feats, W.n_queries)
     mode = bm.BM_QUERY_TILED if W.query_mode == "tiled" else bm.BM_QUERY_EXPANDED
     cts = [bm.bm_encrypt_query(ctx, pk, q, W.dim, part, mode, ENC_SEED, i) for i, q in enumerate(qs)]
@@ -543,7 +556,8 @@ def main():
     dom = max(prof, key=lambda k: prof[k][1])
     n_l, ms_l, by_l, ops_l = prof[dom]
     peak_hbm, peak_src = load_peaks()
-    traffic_cfg = {"part": part, "packing": args.packing, "gallery": args.gallery, "expansion": args.expansion}
+    traffic_cfg = {"part": part, "packing": args.packing, "gallery": args.gallery, "expansion": args.expansion,
+                   "tail": args.tail}
     hbm_gbs = by_l / (ms_l / 1e3) / 1e9 if ms_l > 0 else 0.0
     if ops_l > 0:
         achieved = ops_l / (ms_l / 1e3) / 1e12
@@ -591,7 +605,7 @@ def main():
                    "l2": "flushed between steps (512 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single",
                    "packing": args.packing, "gallery": args.gallery, "expansion": args.expansion,
-                   "ks_wide_batch": wide},
+                   "tail": args.tail, "ks_wide_batch": wide},
         "latency_ms": {"p50": percentile(step_ms, 50), "p99": percentile(step_ms, 99)},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
