@@ -48,6 +48,27 @@ BM_HD uint64_t mont(uint64_t a, uint64_t b, uint64_t q, uint64_t qneg) {
     return r >= q ? r - q : r;
 }
 
+// Sums of products, reduced once: the 128-bit sum t of products a*b (a < 4q, b < q,
+// q < 2^62, so the high word of a*b is below q) is
+// kept below q * 2^64 by subtracting q from its high word whenever that word
+// reaches q (t changes by a multiple of q * 2^64, so t mod q does not); one
+// Montgomery reduction then gives t * 2^-64 mod q -- the same residue as the sum
+// of the Montgomery products, for one reduction instead of one per product.
+struct Acc128 {
+    uint64_t lo = 0, hi = 0;
+};
+BM_HD void mul_acc(Acc128& t, uint64_t a, uint64_t b, uint64_t q) {
+    const uint64_t lo = a * b, hi = mulhi64(a, b);   // hi < 4q^2 / 2^64 < q
+    t.lo += lo;
+    t.hi += hi + (t.lo < lo);                        // < 2q
+    if (t.hi >= q) t.hi -= q;
+}
+BM_HD uint64_t redc(const Acc128& t, uint64_t q, uint64_t qneg) {   // t < q * 2^64
+    const uint64_t m = t.lo * qneg;
+    const uint64_t r = t.hi + mulhi64(m, q) + (t.lo != 0);         // (t + m q) / 2^64 < 2q
+    return r >= q ? r - q : r;
+}
+
 BM_HD uint64_t reduce2(uint64_t x, uint64_t q) { return x >= q ? x - q : x; }
 BM_HD uint64_t addm(uint64_t a, uint64_t b, uint64_t q) { return reduce2(a + b, q); }
 BM_HD uint64_t subm(uint64_t a, uint64_t b, uint64_t q) { return a >= b ? a - b : a + q - b; }

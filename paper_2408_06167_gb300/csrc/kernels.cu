@@ -491,25 +491,23 @@ __global__ void __launch_bounds__(kThreads) k_mac(const uint64_t* __restrict__ T
     pdl_wait();
     if (p >= n) return;
     const uint64_t q = tab.q[j], qn = tab.qneg[j];
-    uint64_t s0[QT], s1[QT];
-#pragma unroll
-    for (int k = 0; k < QT; k++) s0[k] = s1[k] = 0;
+    Acc128 s0[QT], s1[QT];
     for (uint32_t i = 0; i < n_in; i++) {
         const uint64_t pv = P[(((size_t)g * n_in + i) * l1 + j) * n + p];
 #pragma unroll
         for (int k = 0; k < QT; k++) {
             if (q0 + k >= Qn) break;
             const size_t tb = ((((size_t)(q0 + k) * n_in + i) * 2) * l1 + j) * n + p;
-            s0[k] = addm(s0[k], mont(T[tb], pv, q, qn), q);
-            s1[k] = addm(s1[k], mont(T[tb + (size_t)l1 * n], pv, q, qn), q);
+            mul_acc(s0[k], T[tb], pv, q);
+            mul_acc(s1[k], T[tb + (size_t)l1 * n], pv, q);
         }
     }
 #pragma unroll
     for (int k = 0; k < QT; k++) {
         if (q0 + k >= Qn) break;
         const size_t ob = ((((size_t)(q0 + k) * G + g) * 2) * l1 + j) * n + p;
-        acc[ob] = s0[k];
-        acc[ob + (size_t)l1 * n] = s1[k];
+        acc[ob] = redc(s0[k], q, qn);
+        acc[ob + (size_t)l1 * n] = redc(s1[k], q, qn);
     }
 }
 
@@ -530,9 +528,7 @@ __global__ void __launch_bounds__(kThreads) k_mac_ct(const uint64_t* __restrict_
     pdl_wait();
     if (p >= n) return;
     const uint64_t q = tab.q[j], qn = tab.qneg[j];
-    uint64_t d0[QT], d1[QT], d2[QT];
-#pragma unroll
-    for (int k = 0; k < QT; k++) d0[k] = d1[k] = d2[k] = 0;
+    Acc128 d0[QT], d1[QT], d2[QT];
     for (uint32_t i = 0; i < n_in; i++) {
         const size_t cb = ((((size_t)g * n_in + i) * 2) * l1 + j) * n + p;
         const uint64_t c0 = C[cb], c1 = C[cb + (size_t)l1 * n];
@@ -541,19 +537,20 @@ __global__ void __launch_bounds__(kThreads) k_mac_ct(const uint64_t* __restrict_
             if (q0 + k >= Qn) break;
             const size_t tb = ((((size_t)(q0 + k) * n_in + i) * 2) * l1 + j) * n + p;
             const uint64_t t0 = T[tb], t1 = T[tb + (size_t)l1 * n];
-            d0[k] = addm(d0[k], mont(t0, c0, q, qn), q);
-            d1[k] = addm(d1[k], addm(mont(t0, c1, q, qn), mont(t1, c0, q, qn), q), q);
-            d2[k] = addm(d2[k], mont(t1, c1, q, qn), q);
+            mul_acc(d0[k], t0, c0, q);
+            mul_acc(d1[k], t0, c1, q);
+            mul_acc(d1[k], t1, c0, q);
+            mul_acc(d2[k], t1, c1, q);
         }
     }
 #pragma unroll
     for (int k = 0; k < QT; k++) {
         if (q0 + k >= Qn) break;
         const size_t ob = ((((size_t)(q0 + k) * G + g) * 2) * l1 + j) * n + p;
-        A[ob] = d0[k];
-        A[ob + (size_t)l1 * n] = d2[k];
+        A[ob] = redc(d0[k], q, qn);
+        A[ob + (size_t)l1 * n] = redc(d2[k], q, qn);
         B[ob] = 0;
-        B[ob + (size_t)l1 * n] = d1[k];
+        B[ob + (size_t)l1 * n] = redc(d1[k], q, qn);
     }
 }
 
@@ -574,9 +571,7 @@ __global__ void __launch_bounds__(kThreads) k_mac_circ(const uint64_t* const* R,
     pdl_wait();
     if (p >= n) return;
     const uint64_t q = tab.q[j], qn = tab.qneg[j];
-    uint64_t s0[OC], s1[OC];
-#pragma unroll
-    for (int o = 0; o < OC; o++) s0[o] = s1[o] = 0;
+    Acc128 s0[OC], s1[OC];
     for (uint32_t jj = 0; jj < n_in; jj++) {
         const uint64_t* r = R[(size_t)qi * n_in + jj];
         const uint64_t r0 = r[(size_t)j * n + p], r1 = r[((size_t)l1 + j) * n + p];
@@ -585,8 +580,8 @@ __global__ void __launch_bounds__(kThreads) k_mac_circ(const uint64_t* const* R,
             const uint32_t i = i0 + o;
             if (i >= n_in) break;
             const uint64_t mk = masks[((size_t)((i + n_in - jj) % n_in) * l1 + j) * n + p];
-            s0[o] = addm(s0[o], mont(r0, mk, q, qn), q);
-            s1[o] = addm(s1[o], mont(r1, mk, q, qn), q);
+            mul_acc(s0[o], r0, mk, q);
+            mul_acc(s1[o], r1, mk, q);
         }
     }
 #pragma unroll
@@ -594,8 +589,8 @@ __global__ void __launch_bounds__(kThreads) k_mac_circ(const uint64_t* const* R,
         const uint32_t i = i0 + o;
         if (i >= n_in) break;
         const size_t ob = ((((size_t)qi * n_in + i) * 2) * l1 + j) * n + p;
-        t0[ob] = s0[o];
-        t0[ob + (size_t)l1 * n] = s1[o];
+        t0[ob] = redc(s0[o], q, qn);
+        t0[ob + (size_t)l1 * n] = redc(s1[o], q, qn);
     }
 }
 

@@ -40,12 +40,13 @@ __device__ __forceinline__ uint64_t red6(uint64_t y, uint64_t t) {   // [0, 6t) 
 
 constexpr int kMaxDigit = 2;   // limbs per digit and special primes handled by the fused kernels
 
-// 32-bit multiply results of one 64-bit modular product (the accounting of the
-// roofline): Shoup with a precomputed companion = the high half of x*w' (four
-// 32x32 partial products, both halves: 8) and the low halves of x*w and of the
-// quotient times q (4 each) = 16, as one butterfly; Montgomery = the full
-// product a*b (8), the low half of t*(-q^-1) (4) and the high half of m*q (8) = 20.
-constexpr double kShoupMul = 16, kMontMul = 20;
+// 32-bit multiply results of the modular arithmetic (the accounting of the
+// roofline): a Shoup product with a precomputed companion = the high half of
+// x*w' (four 32x32 partial products, both halves: 8) and the low halves of x*w
+// and of the quotient times q (4 each) = 16, as one butterfly; a sum of products
+// reduced once = 8 per full 128-bit product plus one Montgomery reduction (the
+// low half of t*(-q^-1), 4, and the high half of m*q, 8) = 12.
+constexpr double kShoupMul = 16, kProdMul = 8, kRedcMul = 12;
 
 using nttr::ColBase;
 using nttr::first_idx;
@@ -232,11 +233,11 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
             for (int k = 0; k < K; k++) st[(d * K + k) * NT + tid] = v[k];
         }
     }
-    // inner product per key component, then store (special primes: inverse row pass)
+    // inner product per key component (summed at 128 bits, one reduction), then
+    // store (special primes: inverse row pass)
 #pragma unroll 1
     for (uint32_t comp = 0; comp < 2; comp++) {
-#pragma unroll
-        for (int k = 0; k < K; k++) v[k] = 0;
+        Acc128 a[K];
 #pragma unroll 1
         for (uint32_t d = 0; d < nd; d++) {
             uint64_t kv[K];
@@ -246,13 +247,12 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
                 uint64_t e;
                 if constexpr (REG) e = d == 0 ? s0[k] : s1[k];
                 else e = st[(d * K + k) * NT + tid];
-                const uint64_t x = v[k] + mont_lazy(e, kv[k], q, qn);
-                v[k] = x >= q2 ? x - q2 : x;
+                mul_acc(a[k], e, kv[k], q);              // e < 4q after the row pass: allowed
             }
         }
-        if (jj < l1) {
 #pragma unroll
-            for (int k = 0; k < K; k++) v[k] = reduce2(v[k], q);
+        for (int k = 0; k < K; k++) v[k] = redc(a[k], q, qn);
+        if (jj < l1) {
             nttr::relayout<LB, LT, LB / LT - 1, 0>(v, sr, t);
         } else {
             nttr::inv_pass<LB, LT>(v, sr, twi, base, t, q, q2);
@@ -328,22 +328,18 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
     uint64_t v[K];
 #pragma unroll 1
     for (uint32_t comp = 0; comp < 2; comp++) {
-#pragma unroll
-        for (int k = 0; k < K; k++) v[k] = 0;
+        Acc128 a[K];
 #pragma unroll 1
         for (uint32_t d = 0; d < nd; d++) {
             const uint64_t* x = ext + ((size_t)d * nlx + jj) * N;
             uint64_t kv[K];
             nttr::load_last<LB, LT>(kv, key + ((size_t)(d * 2 + comp) * nb + pi) * N + roff, t);
 #pragma unroll
-            for (int k = 0; k < K; k++) {
-                const uint64_t y = v[k] + mont_lazy(x[src[k]], kv[k], q, qn);
-                v[k] = y >= q2 ? y - q2 : y;
-            }
+            for (int k = 0; k < K; k++) mul_acc(a[k], x[src[k]], kv[k], q);
         }
-        if (jj < l1) {
 #pragma unroll
-            for (int k = 0; k < K; k++) v[k] = reduce2(v[k], q);
+        for (int k = 0; k < K; k++) v[k] = redc(a[k], q, qn);
+        if (jj < l1) {
             nttr::relayout<LB, LT, LB / LT - 1, 0>(v, sr, t);
         } else {
             if (comp == 0) tw_wait();
@@ -639,7 +635,7 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
     }
     {
         ProfScope ps(BM_KERNEL_KS_IP, s, lw * nlx * ((double)B * nd + 2.0 * nd + 2.0 * B),
-                     bf_r * B * (targets + 2.0 * alpha) + kMontMul * N * B * nlx * 2.0 * nd);
+                     bf_r * B * (targets + 2.0 * alpha) + N * B * nlx * 2.0 * (kProdMul * nd + kRedcMul));
         pdl_launch(k_ks_f4<LA, LB, LT, R>, dim3(B * nlx, N1 / R), tr, f4_smem, s, ext, key, acc, kc, c.tab, l1, c.L, c.nb);
     }
     {
@@ -722,7 +718,7 @@ cudaError_t ks_hoisted_launch(const Context& c, uint32_t level, uint32_t E, cons
     const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;
     {
         ProfScope ps(BM_KERNEL_KS_IP, s, lw * nlx * ((double)E * nd + 2.0 * nd * E + 2.0 * E),
-                     bf_r * E * 2.0 * alpha + kMontMul * N * E * nlx * 2.0 * nd);
+                     bf_r * E * 2.0 * alpha + N * E * nlx * 2.0 * (kProdMul * nd + kRedcMul));
         pdl_launch(k_ks_f4h<LA, LB, LT, R>, dim3(E * nlx, N1 / R), tr, 0, s, ext_of, key_of, gal_of, acc, kc, c.tab, l1, c.L,
                                                                        c.nb);
     }
