@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--expansion", default="hoisted", choices=["doubling", "hoisted", "auto"],
                     help="form of Algorithm 1: the printed doubling order or the hoisted sum "
                          "(auto: serving picks per gallery by the cost model)")
-    ap.add_argument("--tail", default="printed", choices=["printed", "hoisted"],
+    ap.add_argument("--tail", default="hoisted", choices=["printed", "hoisted"],
                     help="Algorithm 2's rotate-and-sum and the compression: the printed sequential forms or "
                          "rounds of hoisted rotations")
     ap.add_argument("--gallery", default="plain", choices=["plain", "encrypted"],
