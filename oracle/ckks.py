@@ -626,6 +626,52 @@ class Evaluator:
             outs.append(Ciphertext(c0, d1, lvl, ct.scale))
         return outs
 
+    def rotate_sum_hoisted(self, base, terms):
+        """base + sum over terms (ct, r) of Rot(ct, r), every ciphertext at one
+        level, with ONE ModDown for the whole sum (double hoisting, Bossuat,
+        Mouchet, Troncoso-Pastoriza and Hubaux, Eurocrypt 2021): the c1 of each
+        distinct ciphertext is extended once (ModUp, NTT form); the Galois image
+        of a term's extension times the term's key is summed over all terms in
+        Q_l u P; that sum is moved down once; then base and every term's
+        sigma_k(c0) are added.  Adding sigma_k(c0) after ModDown gives the same
+        residues as adding P * sigma_k(c0) to the q-limbs before it, since
+        ModDown(P*x + y) = x + ModDown(y) exactly.  A term with r = 0 (mod slots)
+        adds its ciphertext unrotated.  Same message as base plus the single
+        rotations; the bits differ from those by the roundings saved."""
+        ctx, lvl = self.ctx, base.level
+        ext_idx = ctx.ext_index(lvl)
+        c0 = [base.c0[j].copy() for j in range(lvl + 1)]
+        c1 = [base.c1[j].copy() for j in range(lvl + 1)]
+        acc = np.zeros((2, len(ext_idx), ctx.n), dtype=np.uint64)
+        exts = {}
+        rotated = False
+        for ct, r in terms:
+            assert ct.level == lvl
+            if r % ctx.slots == 0:
+                for j in range(lvl + 1):
+                    c0[j] = add_mod(c0[j], ct.c0[j], ctx.q[j])
+                    c1[j] = add_mod(c1[j], ct.c1[j], ctx.q[j])
+                continue
+            rotated = True
+            k = ctx.galois_left(r)
+            key = self.keys[k]
+            if id(ct) not in exts:
+                exts[id(ct)] = modup_ntt(ctx, ct.c1, lvl)
+            for d, f_d in exts[id(ct)].items():
+                for jj, gi in enumerate(ext_idx):
+                    t = ctx.primes[gi]
+                    fk = ctx.ntt(automorphism(ctx.intt(f_d[jj], gi), ctx.log_n, k, t), gi)
+                    for comp in range(2):
+                        acc[comp, jj] = add_mod(acc[comp, jj], pointwise_mul(fk, key.ntt_data[d, comp, gi], t), t)
+            for j in range(lvl + 1):
+                c0[j] = add_mod(c0[j], automorphism(ct.c0[j], ctx.log_n, k, ctx.q[j]), ctx.q[j])
+        if rotated:
+            d0, d1 = moddown(ctx, acc, lvl)
+            for j in range(lvl + 1):
+                c0[j] = add_mod(c0[j], d0[j], ctx.q[j])
+                c1[j] = add_mod(c1[j], d1[j], ctx.q[j])
+        return Ciphertext(np.stack(c0), np.stack(c1), lvl, base.scale)
+
     def apply_galois(self, ct, k):
         ctx, lvl = self.ctx, ct.level
         key = self.keys[k]

@@ -203,15 +203,21 @@ def bsgs_split(s):
     return b, s // b
 
 
-def rotsum_hoisted(ev, acc, s):
+def rotsum_hoisted(ev, acc, s, double=False):
     """sum_{r<s} Rot(acc, r) -- the message of Algorithm 2's log2(s)
     rotate-and-add steps -- in two rounds of hoisted rotations: baby steps
-    acc + sum_{r<b} Rot(acc, r), then giant steps over multiples of b."""
+    acc + sum_{r<b} Rot(acc, r), then giant steps over multiples of b.
+    double=True: each round's rotations summed before one ModDown
+    (Evaluator.rotate_sum_hoisted)."""
     b, g = bsgs_split(s)
     for step, count in ((1, b), (b, g)):
         if count > 1:
-            for x in ev.rotate_hoisted(acc, [step * k for k in range(1, count)]):
-                acc = ev.add(acc, x)
+            rs = [step * k for k in range(1, count)]
+            if double:
+                acc = ev.rotate_sum_hoisted(acc, [(acc, r) for r in rs])
+            else:
+                for x in ev.rotate_hoisted(acc, rs):
+                    acc = ev.add(acc, x)
     return acc
 
 
@@ -228,8 +234,8 @@ def hec3(ev, cu, cs, s, rescale_each_part=False, encrypted_gallery=False, lazy_r
         for i in range(len(cu)):
             acc3 = ev.add3(acc3, ev.tensor(cu[i], cs[i]))
         acc = ev.rescale(ev.relinearize(acc3))
-        if rotsum == "hoisted":
-            return rotsum_hoisted(ev, acc, s)
+        if rotsum in ("hoisted", "double"):
+            return rotsum_hoisted(ev, acc, s, double=rotsum == "double")
         for t in range(1, log2i(s) + 1):
             acc = ev.add(ev.rotate(acc, 1 << (t - 1)), acc)
         return acc
@@ -243,8 +249,8 @@ def hec3(ev, cu, cs, s, rescale_each_part=False, encrypted_gallery=False, lazy_r
         for i in range(1, len(cu)):
             acc = ev.add(acc, mul(cu[i], cs[i]))
         acc = ev.rescale(acc)
-    if rotsum == "hoisted":
-        return rotsum_hoisted(ev, acc, s)
+    if rotsum in ("hoisted", "double"):
+        return rotsum_hoisted(ev, acc, s, double=rotsum == "double")
     for t in range(1, log2i(s) + 1):
         acc = ev.add(ev.rotate(acc, 1 << (t - 1)), acc)
     return acc
@@ -253,12 +259,15 @@ def hec3(ev, cu, cs, s, rescale_each_part=False, encrypted_gallery=False, lazy_r
 def compress(ev, accs, mask_m, s, tree=True, final_rescale=True, hoisted=False):
     """Compression: mask each group output and pack s groups per ciphertext.
     hoisted=True: the linear form with every group's rotation taken in one
-    round (each rotation hoisted: ModUp before the automorphism)."""
+    round (each rotation hoisted: ModUp before the automorphism);
+    hoisted="double": the same rotations summed before one ModDown per pack."""
     xs = [ev.mul_plain(a, mask_m) for a in accs]
     packs = []
     for p in range(-(-len(xs) // s)):
         ys = xs[p * s:(p + 1) * s]
-        if hoisted:
+        if hoisted == "double":
+            y = ev.rotate_sum_hoisted(ys[0], [(ys[r], -r) for r in range(1, len(ys))])
+        elif hoisted:
             y = ys[0]
             for r in range(1, len(ys)):
                 y = ev.add(y, ev.rotate_hoisted(ys[r], [-r])[0])
@@ -284,7 +293,7 @@ def compress(ev, accs, mask_m, s, tree=True, final_rescale=True, hoisted=False):
 
 def match(ev, query_cts, gallery_pts, masks, mask_m, m, s, expanded=False,
           rescale_each_part=False, tree=True, encrypted_gallery=False, hoisted=False,
-          hoisted_rotsum=False, hoisted_compress=False):
+          hoisted_rotsum=False, hoisted_compress=False, double_hoisted=False):
     """Full server-side match for one query.
 
     query_cts: [ct] (tiled, run through Algorithm 1) or the N_in client-expanded cts.
@@ -296,7 +305,9 @@ def match(ev, query_cts, gallery_pts, masks, mask_m, m, s, expanded=False,
         cu = expand_query_hoisted(ev, query_cts[0], masks, m, s)
     else:
         cu = expand_query(ev, query_cts[0], masks, m, s)
-    rotsum = "hoisted" if hoisted_rotsum else "doubling"
+    rotsum = ("double" if double_hoisted else "hoisted") if hoisted_rotsum else "doubling"
+    if hoisted_compress and double_hoisted:
+        hoisted_compress = "double"
     accs = [hec3(ev, cu, gallery_pts[g], s, rescale_each_part, encrypted_gallery, rotsum=rotsum)
             for g in range(len(gallery_pts))]
     if accs[0].level >= 1 and mask_m is not None:
@@ -362,6 +373,21 @@ class CountingEvaluator:
         for r in rs:
             self._rec("RotH", ct.level)
         return [SymCt(ct.level) for _ in rs]
+
+    def rotate_sum_hoisted(self, base, terms):
+        seen = set()
+        rotated = False
+        for ct, r in terms:
+            if id(ct) not in seen:
+                seen.add(id(ct))
+                self._rec("ModUp", ct.level)
+            self._rec("IPH", ct.level)
+            rotated = True
+        if rotated:
+            self._rec("ModDown", base.level)
+        for _ in terms:
+            self._rec("Add", base.level)
+        return SymCt(base.level)
 
     def zero_like(self, ct, level=None):
         return SymCt(ct.level if level is None else level)

@@ -46,13 +46,14 @@ class OracleMatch:
     """Keys, gallery plaintexts, query ciphertexts and match outputs from the oracle."""
 
     def __init__(self, name, m, s, R, n_queries, feats=None, seed=KEY_SEED, complex_pack=False, encrypted=False,
-                 hoisted=False, hoisted_tail=False):
+                 hoisted=False, hoisted_tail=False, double_hoisted=False):
         self.ctx = ctx = octx(name)
         self.m, self.s, self.R = m, s, R
         self.complex_pack = complex_pack
         self.encrypted = encrypted
         self.hoisted = hoisted
         self.hoisted_tail = hoisted_tail
+        self.double_hoisted = double_hoisted
         self.n_in = m // s
         self.tiled = ctx.L >= 3
         self.level = ctx.L - 1 if self.tiled else ctx.L
@@ -112,7 +113,7 @@ class OracleMatch:
         outs, packed = sch.match(self.ev, cts, self.gal, self.masks, self.cmask, self.m, self.s,
                                  expanded=not self.tiled, encrypted_gallery=self.encrypted,
                                  hoisted=self.hoisted, hoisted_rotsum=self.hoisted_tail,
-                                 hoisted_compress=self.hoisted_tail)
+                                 hoisted_compress=self.hoisted_tail, double_hoisted=self.double_hoisted)
         return self.ct_array(outs), packed
 
     def scores(self, outs_array, packed):

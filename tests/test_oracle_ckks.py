@@ -303,3 +303,88 @@ def test_hoisted_rotate_and_sum_and_compression_scores(m, s, R):
     dec = [ckks.decrypt_decode(ctx, o, sk).real for o in outs]
     got = np.array([dec[o][slot] for o, slot, _ in (sch.identity_slot(i, s, S, packed) for i in range(R))])
     assert np.abs(got - ref).max() < 1e-5
+
+
+def _centred(x, q):
+    x = x.astype(object) % q
+    return np.where(x > q // 2, x - q, x).astype(np.int64)
+
+
+def test_double_hoisted_single_term_is_the_hoisted_rotation():
+    """With one rotated term the sum before ModDown is that term's inner product,
+    so rotate_sum_hoisted(base, [(ct, r)]) is base + rotate_hoisted(ct, [r]) bit
+    for bit; an unrotated term adds its ciphertext exactly."""
+    ctx = ckks.Context("small4")
+    sk, pk, rks = ckks.keygen(ctx, 3, [1, -5, 7])
+    ev = ckks.Evaluator(ctx, rks)
+    rng = np.random.default_rng(8)
+    a = ckks.encrypt(ctx, pk, ctx.encode(rng.uniform(-1, 1, ctx.slots), ctx.scale, ctx.L), 5, 0)
+    b = ckks.encrypt(ctx, pk, ctx.encode(rng.uniform(-1, 1, ctx.slots), ctx.scale, ctx.L), 5, 1)
+    zero = ckks.Ciphertext(np.zeros_like(a.c0), np.zeros_like(a.c1), a.level, a.scale)
+    for r in (1, -5, 7):
+        want = ev.rotate_hoisted(a, [r])[0]
+        got = ev.rotate_sum_hoisted(zero, [(a, r)])
+        assert np.array_equal(got.c0, want.c0) and np.array_equal(got.c1, want.c1), r
+        got_b = ev.rotate_sum_hoisted(b, [(a, r), (a, 0)])
+        want_b = ev.add(ev.add(b, want), a)
+        assert np.array_equal(got_b.c0, want_b.c0) and np.array_equal(got_b.c1, want_b.c1), r
+
+
+@pytest.mark.parametrize("level", [3, 1])
+def test_double_hoisted_sum_decrypts_and_differs_only_by_rounding(level):
+    """Several terms over two ciphertexts: the message is base + the rotated
+    messages, and the ciphertext differs from base + the single hoisted
+    rotations by a small integer polynomial -- the same integer in every limb --
+    bounded by the roundings of ModDown: floor(sum Y/P) - sum floor(Y/P) lies in
+    [0, T) for T terms, and each fast base conversion adds e in [0, alpha)."""
+    ctx = ckks.Context("small4")
+    rots = [1, 2, 3, -4, 9]
+    sk, pk, rks = ckks.keygen(ctx, 3, rots)
+    ev = ckks.Evaluator(ctx, rks)
+    rng = np.random.default_rng(9)
+    zs = [rng.uniform(-1, 1, ctx.slots) for _ in range(3)]
+    cts = []
+    for k, z in enumerate(zs):
+        ct = ckks.encrypt(ctx, pk, ctx.encode(z, ctx.scale, ctx.L), 5, k)
+        cts.append(ckks.Ciphertext(ct.c0[:level + 1].copy(), ct.c1[:level + 1].copy(), level, ct.scale))
+    base, a, b = cts
+    terms = [(a, 1), (a, 2), (a, 3), (b, -4), (b, 9), (b, 0)]
+    got = ev.rotate_sum_hoisted(base, terms)
+    d = ckks.decrypt_decode(ctx, got, sk).real
+    want_z = zs[0] + np.roll(zs[1], -1) + np.roll(zs[1], -2) + np.roll(zs[1], -3) + np.roll(zs[2], 4) \
+        + np.roll(zs[2], -9) + zs[2]
+    assert np.abs(d - want_z).max() < 1e-6
+    single = base
+    for ct, r in terms:
+        single = ev.add(single, ev.rotate_hoisted(ct, [r])[0] if r else ct)
+    T, alpha = sum(1 for _, r in terms if r), len(ctx.p)
+    for comp in ("c0", "c1"):
+        diffs = [_centred(getattr(got, comp)[j].astype(object) - getattr(single, comp)[j].astype(object), ctx.q[j])
+                 for j in range(level + 1)]
+        for j in range(1, level + 1):
+            assert np.array_equal(diffs[j], diffs[0]), (comp, j)
+        assert np.abs(diffs[0]).max() <= T * (alpha + 1) + alpha, comp
+        assert np.abs(diffs[0]).max() > 0, comp          # the roundings saved change the bits
+
+
+@pytest.mark.parametrize("m,s,R", [(128, 16, 2500), (16, 4, 3000), (16, 8, 3000)])
+def test_double_hoisted_tail_scores(m, s, R):
+    """Rotate-and-sum and linear compression with one ModDown per round output
+    give the FP64 scores."""
+    b, g = sch.bsgs_split(s)
+    extra = [k for k in range(1, b)] + [b * k for k in range(1, g)] + [-r for r in range(1, s)]
+    ctx, sk, pk, ev = _setup("small4", m, s, R, extra_rots=extra)
+    S, L, n_in = ctx.slots, ctx.L, m // s
+    feats = wl.gallery(R, m)
+    q = wl.queries(feats, 1)[0][0]
+    ct = ckks.encrypt(ctx, pk, ctx.encode(sch.tiled_query_slots(q, S), ctx.scale, L), 4, 0)
+    masks = [ctx.encode(sch.alg1_mask_slots(m, s, i, S), ctx.q[L], L) for i in range(n_in)]
+    gal = [[ctx.encode(sch.gallery_slots(feats, gg, i, s, S), ctx.q[L - 1], L - 1) for i in range(n_in)]
+           for gg in range(sch.n_groups(R, s, S))]
+    mm = ctx.encode(sch.compression_mask_slots(s, S), ctx.q[L - 2], L - 2)
+    ref = wl.plaintext_scores(feats, q)
+    outs, packed = sch.match(ev, [ct], gal, masks, mm, m, s, hoisted_rotsum=True, hoisted_compress=True,
+                             double_hoisted=True)
+    dec = [ckks.decrypt_decode(ctx, o, sk).real for o in outs]
+    got = np.array([dec[o][slot] for o, slot, _ in (sch.identity_slot(i, s, S, packed) for i in range(R))])
+    assert np.abs(got - ref).max() < 1e-5
