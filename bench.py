@@ -59,9 +59,10 @@ def parse():
     ap.add_argument("--expansion", default="hoisted", choices=["doubling", "hoisted", "auto"],
                     help="form of Algorithm 1: the printed doubling order or the hoisted sum "
                          "(auto: serving picks per gallery by the cost model)")
-    ap.add_argument("--tail", default="hoisted", choices=["printed", "hoisted"],
-                    help="Algorithm 2's rotate-and-sum and the compression: the printed sequential forms or "
-                         "rounds of hoisted rotations")
+    ap.add_argument("--tail", default="hoisted", choices=["printed", "hoisted", "double"],
+                    help="Algorithm 2's rotate-and-sum and the compression: the printed sequential forms, "
+                         "rounds of hoisted rotations, or the same rounds with one ModDown per output "
+                         "(double hoisting)")
     ap.add_argument("--gallery", default="plain", choices=["plain", "encrypted"],
                     help="gallery of plaintexts, or of ciphertexts enrolled on the server (Sec. 3.2)")
     ap.add_argument("--packing", default="real", choices=["real", "complex"],
@@ -267,7 +268,7 @@ def run_serving(args):
     expansions = {}
     for gi, (name, R, m, s) in enumerate(SERVE_GALLERIES):
         if args.expansion == "auto":
-            forms = [(e, t) for e in ("doubling", "hoisted") for t in ("printed", "hoisted")]
+            forms = [(e, t) for e in ("doubling", "hoisted") for t in ("printed", "hoisted", "double")]
         else:
             forms = [(args.expansion, args.tail)]
         if costs is not None:
@@ -281,7 +282,8 @@ def run_serving(args):
         flags, _ = sched_flags(bm, *form)
         parts[name] = s
         expansions[name] = "+".join(x for x, on in (("hoisted-expansion", flags & 1), ("hoisted-rotsum", flags & 2),
-                                                    ("hoisted-compression", flags & 4)) if on) or "printed"
+                                                    ("hoisted-compression", flags & 4), ("double-hoisted", flags & 8))
+                                    if on) or "printed"
         if (m, s) not in keys:
             keys[(m, s)] = bm.bm_keygen_ex(ctx, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
         feats = wl.gallery(R, m, seed=10 + gi)
@@ -356,10 +358,12 @@ def run_serving(args):
 def sched_flags(bm, expansion, tail):
     """(gallery schedule flags, model layout flags) of the chosen forms."""
     f = bm.BM_SCHED_HOISTED_EXPANSION if expansion == "hoisted" else 0
-    if tail == "hoisted":
+    if tail in ("hoisted", "double"):
         f |= bm.BM_SCHED_HOISTED_ROTSUM | bm.BM_SCHED_HOISTED_COMPRESSION
+    if tail == "double":
+        f |= bm.BM_SCHED_DOUBLE_HOISTED
     lay = ((bm.BM_LAYOUT_HOISTED if f & 1 else 0) | (bm.BM_LAYOUT_HOISTED_ROTSUM if f & 2 else 0)
-           | (bm.BM_LAYOUT_HOISTED_COMPRESSION if f & 4 else 0))
+           | (bm.BM_LAYOUT_HOISTED_COMPRESSION if f & 4 else 0) | (bm.BM_LAYOUT_DOUBLE_HOISTED if f & 8 else 0))
     return f, lay
 
 

@@ -249,6 +249,11 @@ bm_status bm_gallery_set_expansion(bm_gallery* g, uint32_t mode);
  *  BM_SCHED_HOISTED_COMPRESSION  the compression in its linear form, every group
  *                                r > 0 of a pack rotated right by r in one round of
  *                                hoisted rotations (a radix-2 tree otherwise)
+ *  BM_SCHED_DOUBLE_HOISTED       with either of the two above: each round's
+ *                                rotations into one output summed in the extended
+ *                                basis Q_l u P and moved down once (one ModDown per
+ *                                output instead of one per rotation; double
+ *                                hoisting, Bossuat et al., Eurocrypt 2021)
  * Needs the keys of bm_keygen_ex(..., BM_KEYS_HOISTED).  Plans of the gallery
  * built before the call are dropped; call it before registering the gallery
  * with a server.  BM_E_ARG for unknown flags, or the expansion flag on a gallery
@@ -256,7 +261,8 @@ bm_status bm_gallery_set_expansion(bm_gallery* g, uint32_t mode);
 enum {
     BM_SCHED_HOISTED_EXPANSION = 1,
     BM_SCHED_HOISTED_ROTSUM = 2,
-    BM_SCHED_HOISTED_COMPRESSION = 4
+    BM_SCHED_HOISTED_COMPRESSION = 4,
+    BM_SCHED_DOUBLE_HOISTED = 8
 };
 bm_status bm_gallery_set_schedule(bm_gallery* g, uint32_t flags);
 void bm_gallery_destroy(bm_gallery* g);
@@ -457,7 +463,10 @@ enum {
     BM_OP_ROT_HOISTED = 9,/* hoisted rotations: `count` rotations from extended ciphertexts */
     BM_OP_MAC_CIRC = 10,  /* hoisted Algorithm 1: `queries` x `count` outputs of `parts` mask products */
     BM_OP_ACCUM = 11,     /* sums of `count` ciphertexts at `level` into their targets (hoisted rounds) */
-    BM_OP_KINDS = 12
+    BM_OP_IP_SUM = 12,    /* double-hoisted rounds: key-switch products of `count` rotations summed
+                             into `parts` targets before ModDown */
+    BM_OP_MODDOWN = 13,   /* double-hoisted rounds: ModDown of `count` sums, added to their targets */
+    BM_OP_KINDS = 14
 };
 
 /* One kernel launch (or launch group) of a match schedule. */
@@ -466,7 +475,7 @@ typedef struct bm_op_launch {
     uint32_t level;       /* level of the input ciphertexts (0 for NTT / INTT / COPY) */
     uint32_t count;       /* ciphertexts, limbs or groups, as listed above */
     uint32_t queries;     /* BM_OP_MAC: queries per product set; else 0 */
-    uint32_t parts;       /* BM_OP_MAC: N_in; else 0 */
+    uint32_t parts;       /* BM_OP_MAC: N_in; BM_OP_IP_SUM: targets; else 0 */
 } bm_op_launch;
 
 /* Per-launch device time of each op kind and input level, sampled at
@@ -490,6 +499,8 @@ typedef struct bm_op_costs {
 #define BM_LAYOUT_HOISTED 0x200u
 #define BM_LAYOUT_HOISTED_ROTSUM 0x400u
 #define BM_LAYOUT_HOISTED_COMPRESSION 0x800u
+/* ... and BM_LAYOUT_DOUBLE_HOISTED for BM_SCHED_DOUBLE_HOISTED. */
+#define BM_LAYOUT_DOUBLE_HOISTED 0x1000u
 
 /* Host only (no device needed): the launches of the match of `n_queries`
  * queries against a gallery of n_ids identities in (dim, part_size, packing) under

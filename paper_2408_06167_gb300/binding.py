@@ -33,10 +33,12 @@ BM_LAYOUT_ENCRYPTED = 0x100
 BM_LAYOUT_HOISTED = 0x200
 BM_LAYOUT_HOISTED_ROTSUM = 0x400
 BM_LAYOUT_HOISTED_COMPRESSION = 0x800
+BM_LAYOUT_DOUBLE_HOISTED = 0x1000
 BM_SCHED_HOISTED_EXPANSION = 1
 BM_SCHED_HOISTED_ROTSUM = 2
 BM_SCHED_HOISTED_COMPRESSION = 4
-BM_SCHED_ALL = 7
+BM_SCHED_ALL = 7                      # every hoisted form, one ModDown per rotation
+BM_SCHED_DOUBLE_HOISTED = 8
 BM_KEYS_ENCRYPTED_GALLERY = 1
 BM_KEYS_HOISTED = 2
 BM_EXPAND_DOUBLING = 0
@@ -59,9 +61,9 @@ class bm_params(ctypes.Structure):
 
 
 OPS = {"rotate": 0, "rescale": 1, "mul_plain": 2, "mac": 3, "ntt": 4, "intt": 5, "copy": 6, "mac_ct": 7,
-       "modup": 8, "rot_hoisted": 9, "mac_circ": 10, "accum": 11}
+       "modup": 8, "rot_hoisted": 9, "mac_circ": 10, "accum": 11, "ip_sum": 12, "moddown": 13}
 OP_NAMES = {v: k for k, v in OPS.items()}
-BM_OP_KINDS = 12
+BM_OP_KINDS = 14
 BM_MAX_Q = 6
 BM_COST_POINTS = 8
 

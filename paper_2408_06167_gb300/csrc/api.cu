@@ -58,6 +58,7 @@ struct Layout {
     bool encrypted;                         // gallery of ciphertexts (HE-C^3 products ct x ct)
     bool hoisted;                           // Algorithm 1 by hoisted rotations
     bool hrotsum, hcomp;                    // rotate-and-sum / compression by hoisted rounds
+    bool dhoist;                            // ... with one ModDown per round output
 };
 
 // Scale of the score ciphertexts: 2^log_scale with a plaintext gallery (every
@@ -71,7 +72,8 @@ static uint32_t gallery_kind(const Gallery& g) {
     return g.packing | (g.encrypted ? BM_LAYOUT_ENCRYPTED : 0u) |
            ((g.sched & BM_SCHED_HOISTED_EXPANSION) ? BM_LAYOUT_HOISTED : 0u) |
            ((g.sched & BM_SCHED_HOISTED_ROTSUM) ? BM_LAYOUT_HOISTED_ROTSUM : 0u) |
-           ((g.sched & BM_SCHED_HOISTED_COMPRESSION) ? BM_LAYOUT_HOISTED_COMPRESSION : 0u);
+           ((g.sched & BM_SCHED_HOISTED_COMPRESSION) ? BM_LAYOUT_HOISTED_COMPRESSION : 0u) |
+           ((g.sched & BM_SCHED_DOUBLE_HOISTED) ? BM_LAYOUT_DOUBLE_HOISTED : 0u);
 }
 
 // baby and giant steps of the hoisted rotate-and-sum over s slots: b = 2^ceil(log2(s)/2)
@@ -85,11 +87,12 @@ static void bsgs_split(uint32_t s, uint32_t& b, uint32_t& g) {
 static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uint32_t part, Layout& lo,
                              uint32_t kind = BM_PACK_REAL) {
     const uint32_t packing = kind & ~(BM_LAYOUT_ENCRYPTED | BM_LAYOUT_HOISTED | BM_LAYOUT_HOISTED_ROTSUM |
-                                      BM_LAYOUT_HOISTED_COMPRESSION);
+                                      BM_LAYOUT_HOISTED_COMPRESSION | BM_LAYOUT_DOUBLE_HOISTED);
     lo.encrypted = (kind & BM_LAYOUT_ENCRYPTED) != 0;
     lo.hoisted = (kind & BM_LAYOUT_HOISTED) != 0;
     lo.hrotsum = (kind & BM_LAYOUT_HOISTED_ROTSUM) != 0;
     lo.hcomp = (kind & BM_LAYOUT_HOISTED_COMPRESSION) != 0;
+    lo.dhoist = (kind & BM_LAYOUT_DOUBLE_HOISTED) != 0;
     if (!is_pow2(dim) || !is_pow2(part) || part > dim || dim > c.slots)
         return fail(BM_E_DIM, "dim and part size must be powers of two with part <= dim <= N/2");
     if (packing != BM_PACK_REAL && packing != BM_PACK_COMPLEX) return fail(BM_E_ARG, "unknown slot packing");
@@ -106,6 +109,7 @@ static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uin
     lo.compress = lo.level >= 2;            // a level left after HE-C^3 for the mask
     if (!lo.tiled) lo.hoisted = false;      // no Algorithm 1 on the server
     if (!lo.compress) lo.hcomp = false;
+    if (!lo.hrotsum && !lo.hcomp) lo.dhoist = false;
     lo.n_out = lo.compress ? (lo.groups + part - 1) / part : lo.groups;
     return BM_OK;
 }
@@ -576,10 +580,10 @@ static bm_status gallery_alloc(Context& c, const Layout& lo, uint64_t n_ids, uin
     Gallery& g = gh->g;
     g.ctx = &c;
     g.packing = packing & ~(BM_LAYOUT_ENCRYPTED | BM_LAYOUT_HOISTED | BM_LAYOUT_HOISTED_ROTSUM |
-                            BM_LAYOUT_HOISTED_COMPRESSION);
+                            BM_LAYOUT_HOISTED_COMPRESSION | BM_LAYOUT_DOUBLE_HOISTED);
     g.encrypted = lo.encrypted;
     g.sched = (lo.hoisted ? BM_SCHED_HOISTED_EXPANSION : 0u) | (lo.hrotsum ? BM_SCHED_HOISTED_ROTSUM : 0u) |
-              (lo.hcomp ? BM_SCHED_HOISTED_COMPRESSION : 0u);
+              (lo.hcomp ? BM_SCHED_HOISTED_COMPRESSION : 0u) | (lo.dhoist ? BM_SCHED_DOUBLE_HOISTED : 0u);
     g.id = c.next_id++;
     g.n_ids = n_ids;
     g.dim = dim;
@@ -961,7 +965,8 @@ bm_status bm_gallery_import_encrypted(bm_context* ctxh, const uint64_t* cts, con
 
 bm_status bm_gallery_set_schedule(bm_gallery* gh, uint32_t flags) {
     if (!gh) return fail(BM_E_ARG, "null gallery");
-    const uint32_t all = BM_SCHED_HOISTED_EXPANSION | BM_SCHED_HOISTED_ROTSUM | BM_SCHED_HOISTED_COMPRESSION;
+    const uint32_t all = BM_SCHED_HOISTED_EXPANSION | BM_SCHED_HOISTED_ROTSUM | BM_SCHED_HOISTED_COMPRESSION |
+                         BM_SCHED_DOUBLE_HOISTED;
     if (flags & ~all) return fail(BM_E_ARG, "unknown schedule flags");
     Gallery& g = gh->g;
     if ((flags & BM_SCHED_HOISTED_EXPANSION) && !g.tiled)
@@ -1184,6 +1189,7 @@ void drop_plans(Context& c, uint64_t id) {
 struct SchedView {
     uint32_t n_in = 0, part = 0, level = 0, groups = 0;
     bool tiled = true, compress = true, encrypted = false, hoisted = false, hrotsum = false, hcomp = false;
+    bool dhoist = false;                   // hoisted rounds with one ModDown per output
     const uint64_t* d_pts = nullptr;
     const uint64_t* d_masks = nullptr;
     const uint64_t* d_cmask = nullptr;
@@ -1201,6 +1207,7 @@ static SchedView view_of(const Gallery& g) {
     v.hoisted = g.tiled && (g.sched & BM_SCHED_HOISTED_EXPANSION);
     v.hrotsum = (g.sched & BM_SCHED_HOISTED_ROTSUM) != 0;
     v.hcomp = g.compress && (g.sched & BM_SCHED_HOISTED_COMPRESSION);
+    v.dhoist = (v.hrotsum || v.hcomp) && (g.sched & BM_SCHED_DOUBLE_HOISTED);
     v.d_pts = g.d_pts;
     v.d_masks = g.d_masks;
     v.d_cmask = g.d_cmask;
@@ -1219,6 +1226,7 @@ static SchedView view_of(const Layout& lo, uint32_t part) {
     v.hoisted = lo.hoisted;
     v.hrotsum = lo.hrotsum;
     v.hcomp = lo.hcomp;
+    v.dhoist = lo.dhoist;
     return v;
 }
 
@@ -1327,6 +1335,10 @@ struct MatchRun {
             std::vector<uint64_t*> chunk(srcs.begin() + s0, srcs.begin() + std::min(srcs.size(), s0 + ksb));
             modup_batch(level, chunk, pl.ext2 + s0 * ew);
         }
+        if (g.dhoist) {
+            double_hoisted_sums(level, srcs, e_src, e_rot, tgts, t_elems);
+            return;
+        }
         std::vector<uint64_t*> ext_of, src, keys, gal, out;
         for (size_t e = 0; e < e_src.size(); e++) {
             ext_of.push_back(pl.ext2 + (size_t)e_src[e] * ew);
@@ -1342,6 +1354,48 @@ struct MatchRun {
             for (uint32_t e : te) lists.back().push_back(pl.rot + (size_t)e * cwl);
         }
         accumulate_batch(level, tgts, lists);
+    }
+    // ... with one ModDown per target (double hoisting): target t gains the sum of
+    // its elements' rotations, their key-switch products (and P * sigma(c0)) summed
+    // in Q_l u P and moved down once, in place; targets in chunks of ksb
+    void double_hoisted_sums(uint32_t level, const std::vector<uint64_t*>& srcs, const std::vector<uint32_t>& e_src,
+                             const std::vector<int32_t>& e_rot, const std::vector<uint64_t*>& tgts,
+                             const std::vector<std::vector<uint32_t>>& t_elems) {
+        const size_t ew = ks_ext_words(c, level);
+        std::vector<uint64_t*> ext_of, src, keys, gal, tg, off{reinterpret_cast<uint64_t*>((uintptr_t)0)};
+        std::vector<uint32_t> t_off{0};
+        for (size_t t = 0; t < tgts.size(); t++) {
+            if (t_elems[t].empty()) continue;
+            for (uint32_t e : t_elems[t]) {
+                ext_of.push_back(pl.ext2 + (size_t)e_src[e] * ew);
+                src.push_back(srcs[e_src[e]]);
+                keys.push_back(const_cast<uint64_t*>(key(e_rot[e])));
+                gal.push_back(reinterpret_cast<uint64_t*>((uintptr_t)galois_of(c, e_rot[e])));
+            }
+            tg.push_back(tgts[t]);
+            off.push_back(reinterpret_cast<uint64_t*>((uintptr_t)ext_of.size()));
+            t_off.push_back((uint32_t)ext_of.size());
+        }
+        auto de = pl.arena.list(ext_of);
+        auto ds = pl.arena.list(src);
+        auto dk = pl.arena.list(keys);
+        auto dg = pl.arena.list(gal);
+        auto dt = pl.arena.list(tg);
+        auto doff = pl.arena.list(off);
+        for (size_t t0 = 0; t0 < tg.size(); t0 += ksb) {
+            const uint32_t T = (uint32_t)std::min<size_t>(ksb, tg.size() - t0);
+            const uint32_t E = t_off[t0 + T] - t_off[t0];
+            record(BM_OP_IP_SUM, level, E, 0, T);
+            record(BM_OP_MODDOWN, level, T);
+            if (!pl.arena.live) {
+                need_scratch(ks_hoisted_scratch_words(c, level, T));
+                continue;
+            }
+            check(ks_ipsum_hoisted(c, level, T, (const uint64_t*)(doff + t0), E, (const uint64_t* const*)de,
+                                   (const uint64_t* const*)ds, (const uint64_t* const*)dk, (const uint64_t*)dg,
+                                   pl.scratch, s));
+            check(ks_moddown_add(c, level, T, dt + t0, pl.scratch, s));
+        }
     }
     // ... rotations of the extended queries (per element: extension, source, key, Galois element)
     void hoisted_batch(uint32_t level, const std::vector<uint64_t*>& ext_of, const std::vector<uint64_t*>& src,
@@ -1540,7 +1594,9 @@ static void plan_dims(const Context& c, const SchedView& g, uint32_t n_out, uint
         per_src = std::max(bs, gs) - 1;
     }
     if (g.hcomp) per_src = std::max<uint32_t>(per_src, 1);
-    const size_t hold = per_src ? ks_ext_words(c, lg - 1) + (size_t)per_src * ct_words(c, lg - 1) : 0;
+    // double hoisting sums the rotations in the key-switch scratch: no rotated copies
+    const uint32_t copies = g.dhoist ? 0 : per_src;
+    const size_t hold = per_src ? ks_ext_words(c, lg - 1) + (size_t)copies * ct_words(c, lg - 1) : 0;
     const size_t per_group =
         (size_t)Q * ((g.encrypted ? 2 : 1) * ct_words(c, lg) + ct_words(c, lg - 1) + hold) * 8;
     const size_t budget = (size_t)8 << 30;
@@ -1548,7 +1604,7 @@ static void plan_dims(const Context& c, const SchedView& g, uint32_t n_out, uint
     if (g.compress) chunk = std::max(g.part, chunk / g.part * g.part);
     pl.chunk = std::min(chunk, g.groups);
     pl.hsrc = per_src ? (size_t)Q * pl.chunk : 0;
-    pl.helem = pl.hsrc * per_src;
+    pl.helem = pl.hsrc * copies;
     pl.qin_words = (size_t)Q * pl.ncts * ct_words(c, c.L);
     pl.result_words = (size_t)Q * n_out * ct_words(c, 0);
     // hoisted Algorithm 1: rotated copies and products of a chunk of queries within ~4 GiB

@@ -56,6 +56,7 @@ struct KsLevelConst {
     ulonglong2 dn_hinv[BM_MAX_P];              // N^-1 (P/p_i)^-1 mod p_i
     ulonglong2 dn_hat[BM_MAX_P][MAXB];         // (P/p_i) mod q_j
     ulonglong2 pinv[MAXB];                     // P^-1 mod q_j
+    uint64_t pmont[MAXB];                      // P * 2^64 mod q_j (Montgomery form of P)
 };
 
 // A match schedule for one (gallery, key set, batch size): persistent device
@@ -337,6 +338,19 @@ cudaError_t ks_modup_hoisted(const Context& c, uint32_t level, uint32_t B, uint6
 cudaError_t ks_rotate_hoisted(const Context& c, uint32_t level, uint32_t E, const uint64_t* const* ext_of,
                               const uint64_t* const* src, const uint64_t* const* key_of, const uint64_t* gal_of,
                               uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s);
+// Sums of hoisted rotations with one ModDown each (double hoisting), in two
+// calls on the same scratch (ks_hoisted_scratch_words(c, level, T)):
+// ks_ipsum_hoisted sums, for each of T targets, the key-switch products of its
+// elements e in [off[t], off[t+1]) (rotation of src_of[e] by gal_of[e] with key
+// key_of[e] from the extension ext_of[e]; off on the device, absolute element
+// indices) with P * sigma(c0); ks_moddown_add moves the sums down and adds them
+// to tgt[t] in place.  Targets may be sources.
+cudaError_t ks_ipsum_hoisted(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
+                             const uint64_t* const* ext_of, const uint64_t* const* src_of,
+                             const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch,
+                             cudaStream_t s);
+cudaError_t ks_moddown_add(const Context& c, uint32_t level, uint32_t T, uint64_t* const* d_tgt, uint64_t* scratch,
+                           cudaStream_t s);
 // rescale in three fused kernels (rings 2^12 and 2^16)
 cudaError_t rescale_fused(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,
                           uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s);

@@ -63,10 +63,64 @@ BM_HD void mul_acc(Acc128& t, uint64_t a, uint64_t b, uint64_t q) {
     t.hi += hi + (t.lo < lo);                        // < 2q
     if (t.hi >= q) t.hi -= q;
 }
+// The same sum with the reduction of the high word batched: for a, b < q < 2^60
+// the high word of a*b is below q/16, so kFoldEvery = 8 products (each adding at
+// most q/16 + 1 with its carry) keep a high word that started below q under 2q,
+// and one fold brings it back below q.
+constexpr int kFoldEvery = 8;
+BM_HD void mul_add(Acc128& t, uint64_t a, uint64_t b) {
+    const uint64_t lo = a * b, hi = mulhi64(a, b);
+    t.lo += lo;
+    t.hi += hi + (t.lo < lo);
+}
+BM_HD void fold(Acc128& t, uint64_t q) {
+    if (t.hi >= q) t.hi -= q;
+}
 BM_HD uint64_t redc(const Acc128& t, uint64_t q, uint64_t qneg) {   // t < q * 2^64
     const uint64_t m = t.lo * qneg;
     const uint64_t r = t.hi + mulhi64(m, q) + (t.lo != 0);         // (t + m q) / 2^64 < 2q
     return r >= q ? r - q : r;
+}
+
+// Sums of products by 31-bit pieces, for a, b < q < 2^60: a = a1 * 2^31 + a0 with
+// a0 < 2^31, a1 < q / 2^31, and the sum t = hi * 2^62 + mid * 2^31 + lo held as three
+// 64-bit sums of 32 x 32-bit products, one multiply-add each: lo gains a0*b0 < 2^62,
+// mid a0*b1 + a1*b0 < 2q, hi a1*b1 < q^2 / 2^62 < q/4 per product.  fold62 every
+// kFold62Every = 4 products moves lo's and mid's bits above 31 up a sum (lo stays
+// below 2^64, mid below 2^63) and keeps hi below 4q by subtracting 4q from it, i.e.
+// q * 2^64 from t, which leaves t mod q unchanged.
+constexpr int kFold62Every = 4;
+struct Piece31 {
+    uint32_t l, h;
+};
+BM_HD Piece31 piece31(uint64_t a) { return {(uint32_t)a & 0x7fffffffu, (uint32_t)(a >> 31)}; }
+struct Acc62 {
+    uint64_t lo = 0, mid = 0, hi = 0;
+};
+BM_HD void mul_add(Acc62& t, Piece31 a, Piece31 b) {
+    t.lo += (uint64_t)a.l * b.l;
+    t.mid += (uint64_t)a.l * b.h;
+    t.mid += (uint64_t)a.h * b.l;
+    t.hi += (uint64_t)a.h * b.h;
+}
+BM_HD void fold62(Acc62& t, uint64_t q4) {
+    t.mid += t.lo >> 31;
+    t.lo &= 0x7fffffffull;
+    t.hi += t.mid >> 31;
+    t.mid &= 0x7fffffffull;
+    if (t.hi >= q4) t.hi -= q4;
+}
+// t * 2^-64 mod q: after a fold, t < 4q * 2^62 + 2^62 + 2^31, so the high word of
+// the 128-bit value is at most q and one subtraction brings it below q
+BM_HD uint64_t redc(Acc62 t, uint64_t q, uint64_t qneg) {
+    fold62(t, 4 * q);
+    Acc128 r;
+    const uint64_t top = t.hi << 62;
+    r.lo = t.lo + (t.mid << 31);                 // < 2^62 + 2^31: no carry
+    r.lo += top;
+    r.hi = (t.hi >> 2) + (r.lo < top);
+    if (r.hi >= q) r.hi -= q;
+    return redc(r, q, qneg);
 }
 
 BM_HD uint64_t reduce2(uint64_t x, uint64_t q) { return x >= q ? x - q : x; }

@@ -15,6 +15,9 @@
 //  * ct x pt products and the HE-C^3 multiply-accumulate over the parts.
 #include <cuda_runtime.h>
 
+#include <cstdio>
+#include <cstdlib>
+
 #include "bm_internal.h"
 
 namespace bm {
@@ -479,118 +482,218 @@ __global__ void k_mul_plain(uint64_t* const* in, const uint64_t* const* pt, uint
         o[i] = mont(s[i], m[i], q, qn);
 }
 
-// acc[q][g][c][j] = sum_i T[q][i][c][j] * P[g][i][j]; each thread: one coefficient, QT queries
-template <int QT>
-__global__ void __launch_bounds__(kThreads) k_mac(const uint64_t* __restrict__ T, const uint64_t* __restrict__ P,
-                                                  uint64_t* __restrict__ acc, uint32_t Qn, uint32_t G,
-                                                  uint32_t n_in, uint32_t lvl, DevTables tab, uint32_t log_n) {
+// ---------------------------------------------------------------------------
+// HE-C^3 products (Algorithm 2's Mul and the sum over the parts).  For one
+// coefficient of one limb the products of Q queries with G groups over N_in parts
+// form a small Q x N_in by N_in x G product; a thread keeps QT x GT of its sums in
+// registers, so each part of a query is read once per GT groups and each gallery
+// plaintext once per QT queries.  Blocks are numbered tiles fastest, then
+// coefficient chunks, then limbs: the blocks in flight share one coefficient range
+// of one limb, and the slices they read stay in L2 while the expanded queries
+// stream from HBM once per GT groups.
+// ---------------------------------------------------------------------------
+
+constexpr int kMacThreads = 128;
+
+struct MacTile {
+    uint32_t q0, g0, j;
+    uint32_t p;
+};
+__device__ __forceinline__ MacTile mac_tile(uint32_t n_qt, uint32_t n_gt, uint32_t chunks, int QT, int GT) {
+    uint32_t b = blockIdx.x;
+    MacTile t;
+    t.g0 = (b % n_gt) * GT;
+    b /= n_gt;
+    t.q0 = (b % n_qt) * QT;
+    b /= n_qt;
+    t.p = (b % chunks) * kMacThreads + threadIdx.x;
+    t.j = b / chunks;
+    return t;
+}
+
+// acc[q][g][c][j] = sum_i T[q][i][c][j] * P[g][i][j] (P in Montgomery form, so the
+// single reduction of each sum gives the product in normal form; every operand is
+// reduced below q)
+template <int QT, int GT>
+__global__ void __launch_bounds__(kMacThreads) k_mac(const uint64_t* __restrict__ T, const uint64_t* __restrict__ P,
+                                                     uint64_t* __restrict__ acc, uint32_t Qn, uint32_t G,
+                                                     uint32_t n_in, uint32_t lvl, DevTables tab, uint32_t log_n,
+                                                     uint32_t n_qt, uint32_t n_gt) {
     const uint32_t n = 1u << log_n, l1 = lvl + 1;
-    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t j = blockIdx.y % l1, g = blockIdx.y / l1;
-    const uint32_t q0 = blockIdx.z * QT;
+    const MacTile t = mac_tile(n_qt, n_gt, n / kMacThreads, QT, GT);
     pdl_wait();
-    if (p >= n) return;
-    const uint64_t q = tab.q[j], qn = tab.qneg[j];
-    Acc128 s0[QT], s1[QT];
-    for (uint32_t i = 0; i < n_in; i++) {
-        const uint64_t pv = P[(((size_t)g * n_in + i) * l1 + j) * n + p];
+    const uint32_t nq = min((uint32_t)QT, Qn - t.q0), ng = min((uint32_t)GT, G - t.g0);
+    const uint64_t q = tab.q[t.j], qn = tab.qneg[t.j], q4 = 4 * q;
+    const size_t ln = (size_t)l1 * n;                        // one polynomial at this level
+    const size_t t_i = 2 * ln, t_q = (size_t)n_in * t_i;     // strides of T: part, query
+    const size_t p_g = (size_t)n_in * ln;                    // stride of P: group (part: ln)
+    const uint64_t* tp = T + (size_t)t.q0 * t_q + (size_t)t.j * n + t.p;
+    const uint64_t* pp = P + (size_t)t.g0 * p_g + (size_t)t.j * n + t.p;
+    Acc62 a0[QT][GT], a1[QT][GT];
+    for (uint32_t i0 = 0; i0 < n_in; i0 += kFold62Every) {
+        const uint32_t i1 = min(n_in, i0 + kFold62Every);
+        for (uint32_t i = i0; i < i1; i++) {
+            Piece31 x0[QT], x1[QT], y[GT];
 #pragma unroll
-        for (int k = 0; k < QT; k++) {
-            if (q0 + k >= Qn) break;
-            const size_t tb = ((((size_t)(q0 + k) * n_in + i) * 2) * l1 + j) * n + p;
-            mul_acc(s0[k], T[tb], pv, q);
-            mul_acc(s1[k], T[tb + (size_t)l1 * n], pv, q);
+            for (int k = 0; k < QT; k++) {
+                const uint64_t* r = tp + k * t_q + i * t_i;
+                x0[k] = piece31((uint32_t)k < nq ? r[0] : 0);
+                x1[k] = piece31((uint32_t)k < nq ? r[ln] : 0);
+            }
+#pragma unroll
+            for (int h = 0; h < GT; h++) y[h] = piece31((uint32_t)h < ng ? pp[h * p_g + i * ln] : 0);
+#pragma unroll
+            for (int k = 0; k < QT; k++)
+#pragma unroll
+                for (int h = 0; h < GT; h++) {
+                    mul_add(a0[k][h], x0[k], y[h]);
+                    mul_add(a1[k][h], x1[k], y[h]);
+                }
         }
+#pragma unroll
+        for (int k = 0; k < QT; k++)
+#pragma unroll
+            for (int h = 0; h < GT; h++) {
+                fold62(a0[k][h], q4);
+                fold62(a1[k][h], q4);
+            }
     }
 #pragma unroll
-    for (int k = 0; k < QT; k++) {
-        if (q0 + k >= Qn) break;
-        const size_t ob = ((((size_t)(q0 + k) * G + g) * 2) * l1 + j) * n + p;
-        acc[ob] = redc(s0[k], q, qn);
-        acc[ob + (size_t)l1 * n] = redc(s1[k], q, qn);
-    }
+    for (int k = 0; k < QT; k++)
+#pragma unroll
+        for (int h = 0; h < GT; h++) {
+            if ((uint32_t)k >= nq || (uint32_t)h >= ng) continue;
+            const size_t ob = ((size_t)(t.q0 + k) * G + t.g0 + h) * t_i + (size_t)t.j * n + t.p;
+            acc[ob] = redc(a0[k][h], q, qn);
+            acc[ob + ln] = redc(a1[k][h], q, qn);
+        }
 }
 
 // HE-C^3 with an encrypted gallery: the tensor products of the expanded query
 // parts T[q][i] with the gallery ciphertexts C[g][i] summed over the parts,
 //   d0 = sum T0*C0,  d1 = sum T0*C1 + T1*C0,  d2 = sum T1*C1   (C in Montgomery form),
 // written as A[q][g] = (d0, d2) -- the input of the relinearising key switch --
-// and B[q][g] = (0, d1) -- its addend.  Grid and tiling as k_mac.
-template <int QT>
-__global__ void __launch_bounds__(kThreads) k_mac_ct(const uint64_t* __restrict__ T, const uint64_t* __restrict__ C,
-                                                     uint64_t* __restrict__ A, uint64_t* __restrict__ B,
-                                                     uint32_t Qn, uint32_t G, uint32_t n_in, uint32_t lvl,
-                                                     DevTables tab, uint32_t log_n) {
+// and B[q][g] = (0, d1) -- its addend.  Tiles and block order as k_mac; d1 takes
+// two products a part, so the sums are folded every kFold62Every / 2 parts.
+template <int QT, int GT>
+__global__ void __launch_bounds__(kMacThreads) k_mac_ct(const uint64_t* __restrict__ T, const uint64_t* __restrict__ C,
+                                                        uint64_t* __restrict__ A, uint64_t* __restrict__ B,
+                                                        uint32_t Qn, uint32_t G, uint32_t n_in, uint32_t lvl,
+                                                        DevTables tab, uint32_t log_n, uint32_t n_qt, uint32_t n_gt) {
     const uint32_t n = 1u << log_n, l1 = lvl + 1;
-    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t j = blockIdx.y % l1, g = blockIdx.y / l1;
-    const uint32_t q0 = blockIdx.z * QT;
+    const MacTile t = mac_tile(n_qt, n_gt, n / kMacThreads, QT, GT);
     pdl_wait();
-    if (p >= n) return;
-    const uint64_t q = tab.q[j], qn = tab.qneg[j];
-    Acc128 d0[QT], d1[QT], d2[QT];
-    for (uint32_t i = 0; i < n_in; i++) {
-        const size_t cb = ((((size_t)g * n_in + i) * 2) * l1 + j) * n + p;
-        const uint64_t c0 = C[cb], c1 = C[cb + (size_t)l1 * n];
+    const uint32_t nq = min((uint32_t)QT, Qn - t.q0), ng = min((uint32_t)GT, G - t.g0);
+    const uint64_t q = tab.q[t.j], qn = tab.qneg[t.j], q4 = 4 * q;
+    const size_t ln = (size_t)l1 * n;
+    const size_t t_i = 2 * ln, t_q = (size_t)n_in * t_i;     // strides of T and C: part; query / group
+    const uint64_t* tp = T + (size_t)t.q0 * t_q + (size_t)t.j * n + t.p;
+    const uint64_t* cp = C + (size_t)t.g0 * t_q + (size_t)t.j * n + t.p;
+    Acc62 d0[QT][GT], d1[QT][GT], d2[QT][GT];
+    for (uint32_t i0 = 0; i0 < n_in; i0 += kFold62Every / 2) {
+        const uint32_t i1 = min(n_in, i0 + kFold62Every / 2);
+        for (uint32_t i = i0; i < i1; i++) {
+            Piece31 x0[QT], x1[QT], y0[GT], y1[GT];
 #pragma unroll
-        for (int k = 0; k < QT; k++) {
-            if (q0 + k >= Qn) break;
-            const size_t tb = ((((size_t)(q0 + k) * n_in + i) * 2) * l1 + j) * n + p;
-            const uint64_t t0 = T[tb], t1 = T[tb + (size_t)l1 * n];
-            mul_acc(d0[k], t0, c0, q);
-            mul_acc(d1[k], t0, c1, q);
-            mul_acc(d1[k], t1, c0, q);
-            mul_acc(d2[k], t1, c1, q);
+            for (int k = 0; k < QT; k++) {
+                const uint64_t* r = tp + k * t_q + i * t_i;
+                x0[k] = piece31((uint32_t)k < nq ? r[0] : 0);
+                x1[k] = piece31((uint32_t)k < nq ? r[ln] : 0);
+            }
+#pragma unroll
+            for (int h = 0; h < GT; h++) {
+                const uint64_t* r = cp + h * t_q + i * t_i;
+                y0[h] = piece31((uint32_t)h < ng ? r[0] : 0);
+                y1[h] = piece31((uint32_t)h < ng ? r[ln] : 0);
+            }
+#pragma unroll
+            for (int k = 0; k < QT; k++)
+#pragma unroll
+                for (int h = 0; h < GT; h++) {
+                    mul_add(d0[k][h], x0[k], y0[h]);
+                    mul_add(d1[k][h], x0[k], y1[h]);
+                    mul_add(d1[k][h], x1[k], y0[h]);
+                    mul_add(d2[k][h], x1[k], y1[h]);
+                }
         }
+#pragma unroll
+        for (int k = 0; k < QT; k++)
+#pragma unroll
+            for (int h = 0; h < GT; h++) {
+                fold62(d0[k][h], q4);
+                fold62(d1[k][h], q4);
+                fold62(d2[k][h], q4);
+            }
     }
 #pragma unroll
-    for (int k = 0; k < QT; k++) {
-        if (q0 + k >= Qn) break;
-        const size_t ob = ((((size_t)(q0 + k) * G + g) * 2) * l1 + j) * n + p;
-        A[ob] = redc(d0[k], q, qn);
-        A[ob + (size_t)l1 * n] = redc(d2[k], q, qn);
-        B[ob] = 0;
-        B[ob + (size_t)l1 * n] = redc(d1[k], q, qn);
-    }
+    for (int k = 0; k < QT; k++)
+#pragma unroll
+        for (int h = 0; h < GT; h++) {
+            if ((uint32_t)k >= nq || (uint32_t)h >= ng) continue;
+            const size_t ob = ((size_t)(t.q0 + k) * G + t.g0 + h) * t_i + (size_t)t.j * n + t.p;
+            A[ob] = redc(d0[k][h], q, qn);
+            A[ob + ln] = redc(d2[k][h], q, qn);
+            B[ob] = 0;
+            B[ob + ln] = redc(d1[k][h], q, qn);
+        }
 }
 
 // Algorithm 1 in hoisted form: t0[q][i] = sum_j R[q][j] * mask[(i - j) mod n_in] with
 // R[q][j] = Rot(query q, j*part) given by pointer (R[q][0] the query itself),
-// masks [n_in][l1][N] Montgomery, t0 [Q][n_in][2][l1][N].  Grid (chunks of N, l1,
-// Q * ceil(n_in / OC)): a thread computes OC outputs i of one query, limb and
-// coefficient, reading each rotated query once per OC outputs.
+// masks [n_in][l1][N] Montgomery, t0 [Q][n_in][2][l1][N], n_in a power of two.
+// Grid (ceil(n_in / OC) * N / kMacThreads, l1, Q), output chunks fastest so that
+// the passes over one coefficient range run together and share its rotated
+// copies in L2: a thread computes OC outputs i of one query, limb and
+// coefficient, reading each rotated query once per OC outputs; the block stages
+// the query's pointer list in shared memory.
 template <int OC>
-__global__ void __launch_bounds__(kThreads) k_mac_circ(const uint64_t* const* R, const uint64_t* __restrict__ masks,
-                                                       uint64_t* __restrict__ t0, uint32_t n_in, uint32_t lvl,
-                                                       DevTables tab, uint32_t log_n) {
-    const uint32_t n = 1u << log_n, l1 = lvl + 1;
-    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t j = blockIdx.y;
+__global__ void __launch_bounds__(kMacThreads) k_mac_circ(const uint64_t* const* R, const uint64_t* __restrict__ masks,
+                                                          uint64_t* __restrict__ t0, uint32_t n_in, uint32_t lvl,
+                                                          DevTables tab, uint32_t log_n) {
+    __shared__ const uint64_t* sR[kMacThreads];
+    const uint32_t n = 1u << log_n, l1 = lvl + 1, nm = n_in - 1;
     const uint32_t chunks = (n_in + OC - 1) / OC;
-    const uint32_t qi = blockIdx.z / chunks, i0 = (blockIdx.z % chunks) * OC;
+    const uint32_t i0 = (blockIdx.x % chunks) * OC;
+    const uint32_t p = (blockIdx.x / chunks) * kMacThreads + threadIdx.x;   // < n: the grid covers N exactly
+    const uint32_t j = blockIdx.y, qi = blockIdx.z;
     pdl_wait();
-    if (p >= n) return;
-    const uint64_t q = tab.q[j], qn = tab.qneg[j];
-    Acc128 s0[OC], s1[OC];
-    for (uint32_t jj = 0; jj < n_in; jj++) {
-        const uint64_t* r = R[(size_t)qi * n_in + jj];
-        const uint64_t r0 = r[(size_t)j * n + p], r1 = r[((size_t)l1 + j) * n + p];
+    const uint64_t q = tab.q[j], qn = tab.qneg[j], q4 = 4 * q;
+    const size_t ln = (size_t)l1 * n;
+    const uint64_t* mj = masks + (size_t)j * n + p;               // mask k at mj + k * ln
+    Acc62 s0[OC], s1[OC];
+    for (uint32_t b0 = 0; b0 < n_in; b0 += kMacThreads) {
+        const uint32_t nb = min(n_in - b0, (uint32_t)kMacThreads);
+        __syncthreads();
+        if (threadIdx.x < nb) sR[threadIdx.x] = R[(size_t)qi * n_in + b0 + threadIdx.x];
+        __syncthreads();
+        for (uint32_t u0 = 0; u0 < nb; u0 += kFold62Every) {
+            const uint32_t u1 = min(nb, u0 + kFold62Every);
+            for (uint32_t u = u0; u < u1; u++) {
+                const uint32_t jj = b0 + u;
+                const uint64_t* r = sR[u] + (size_t)j * n + p;
+                const Piece31 r0 = piece31(r[0]), r1 = piece31(r[ln]);
 #pragma unroll
-        for (int o = 0; o < OC; o++) {
-            const uint32_t i = i0 + o;
-            if (i >= n_in) break;
-            const uint64_t mk = masks[((size_t)((i + n_in - jj) % n_in) * l1 + j) * n + p];
-            mul_acc(s0[o], r0, mk, q);
-            mul_acc(s1[o], r1, mk, q);
+                for (int o = 0; o < OC; o++) {
+                    if (i0 + o >= n_in) break;
+                    const Piece31 mk = piece31(mj[(size_t)((i0 + o - jj) & nm) * ln]);
+                    mul_add(s0[o], r0, mk);
+                    mul_add(s1[o], r1, mk);
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < OC; o++) {
+                fold62(s0[o], q4);
+                fold62(s1[o], q4);
+            }
         }
     }
 #pragma unroll
     for (int o = 0; o < OC; o++) {
         const uint32_t i = i0 + o;
         if (i >= n_in) break;
-        const size_t ob = ((((size_t)qi * n_in + i) * 2) * l1 + j) * n + p;
+        const size_t ob = ((size_t)qi * n_in + i) * 2 * ln + (size_t)j * n + p;
         t0[ob] = redc(s0[o], q, qn);
-        t0[ob + (size_t)l1 * n] = redc(s1[o], q, qn);
+        t0[ob + ln] = redc(s1[o], q, qn);
     }
 }
 
@@ -686,7 +789,10 @@ cudaError_t build_ks_constants(Context& c) {
                 K.dn_hat[i][j] = pair(ht, t);
             }
         }
-        for (uint32_t j = 0; j < l1; j++) K.pinv[j] = pair(h_invmod(c.P_mod[j], c.primes[j]), c.primes[j]);
+        for (uint32_t j = 0; j < l1; j++) {
+            K.pinv[j] = pair(h_invmod(c.P_mod[j], c.primes[j]), c.primes[j]);
+            K.pmont[j] = (uint64_t)(((unsigned __int128)c.P_mod[j] << 64) % c.primes[j]);
+        }
     }
     cudaError_t e = cudaMalloc(&c.d_ksc, sizeof(KsLevelConst) * c.h_ksc.size());
     if (e != cudaSuccess) return e;
@@ -931,23 +1037,86 @@ cudaError_t mul_plain(const Context& c, uint32_t level, uint32_t B, uint64_t* co
     return cudaGetLastError();
 }
 
+// Largest tile of the HE-C^3 products: BM_MAC_TILE="QxG" (each 1, 2 or 4) caps
+// the queries and groups a thread takes (within the per-kernel limits below).
+static void mac_tile_cap(int& qt, int& gt) {
+    static const int cap = [] {
+        int a = 4, b = 4;
+        if (const char* e = std::getenv("BM_MAC_TILE")) {
+            if (std::sscanf(e, "%dx%d", &a, &b) != 2) a = b = 4;
+        }
+        auto pow2 = [](int v) { return v >= 4 ? 4 : (v >= 2 ? 2 : 1); };
+        return pow2(a) * 8 + pow2(b);
+    }();
+    qt = std::min(qt, cap / 8);
+    gt = std::min(gt, cap % 8);
+}
+
+// tile shape of the HE-C^3 products: up to 4 queries and 4 (ct x pt) or 2
+// (ct x ct) groups a thread; blocks = tiles x chunks x limbs
+static bool mac_grid(const Context& c, uint32_t level, uint32_t Q, uint32_t G, int QT, int GT, uint32_t& n_qt,
+                     uint32_t& n_gt, uint32_t& blocks) {
+    n_qt = (Q + QT - 1) / QT;
+    n_gt = (G + GT - 1) / GT;
+    const uint64_t b = (uint64_t)n_qt * n_gt * (c.n / kMacThreads) * (level + 1);
+    blocks = (uint32_t)b;
+    return b > 0 && b <= 0x7fffffffull;
+}
+
+template <int QT, int GT>
+static cudaError_t launch_mac(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32_t n_in,
+                              const uint64_t* T, const uint64_t* P, uint64_t* acc, cudaStream_t s) {
+    uint32_t n_qt, n_gt, blocks;
+    if (!mac_grid(c, level, Q, G, QT, GT, n_qt, n_gt, blocks)) return cudaErrorInvalidConfiguration;
+    return pdl_launch(k_mac<QT, GT>, dim3(blocks), kMacThreads, 0, s, T, P, acc, Q, G, n_in, level, c.tab, c.log_n,
+                      n_qt, n_gt);
+}
+
+template <int QT, int GT>
+static cudaError_t launch_mac_ct(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32_t n_in,
+                                 const uint64_t* T, const uint64_t* C, uint64_t* A, uint64_t* B, cudaStream_t s) {
+    uint32_t n_qt, n_gt, blocks;
+    if (!mac_grid(c, level, Q, G, QT, GT, n_qt, n_gt, blocks)) return cudaErrorInvalidConfiguration;
+    return pdl_launch(k_mac_ct<QT, GT>, dim3(blocks), kMacThreads, 0, s, T, C, A, B, Q, G, n_in, level, c.tab,
+                      c.log_n, n_qt, n_gt);
+}
+
 cudaError_t mac(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32_t n_in, const uint64_t* T,
                 const uint64_t* P, uint64_t* acc, cudaStream_t s) {
-    constexpr int QT = 4;
-    const dim3 g((c.n + kThreads - 1) / kThreads, G * (level + 1), (Q + QT - 1) / QT);
+    if (!Q || !G) return cudaSuccess;
     ProfScope ps(BM_KERNEL_MAC, s, 8.0 * c.n * (level + 1) * ((double)Q * n_in * 2 + (double)G * n_in + 2.0 * Q * G));
-    pdl_launch(k_mac<QT>, g, kThreads, 0, s, T, P, acc, Q, G, n_in, level, c.tab, c.log_n);
-    return cudaGetLastError();
+    // at most 8 (query, group) sums a thread (six registers each)
+    int qt = Q >= 4 ? 4 : (Q >= 2 ? 2 : 1), gt = G >= 3 ? (qt == 4 ? 2 : 4) : (G == 2 ? 2 : 1);
+    mac_tile_cap(qt, gt);
+    switch (qt * 8 + gt) {
+        case 4 * 8 + 4:
+        case 4 * 8 + 2: return launch_mac<4, 2>(c, level, Q, G, n_in, T, P, acc, s);
+        case 4 * 8 + 1: return launch_mac<4, 1>(c, level, Q, G, n_in, T, P, acc, s);
+        case 2 * 8 + 4: return launch_mac<2, 4>(c, level, Q, G, n_in, T, P, acc, s);
+        case 2 * 8 + 2: return launch_mac<2, 2>(c, level, Q, G, n_in, T, P, acc, s);
+        case 2 * 8 + 1: return launch_mac<2, 1>(c, level, Q, G, n_in, T, P, acc, s);
+        case 1 * 8 + 4: return launch_mac<1, 4>(c, level, Q, G, n_in, T, P, acc, s);
+        case 1 * 8 + 2: return launch_mac<1, 2>(c, level, Q, G, n_in, T, P, acc, s);
+        default: return launch_mac<1, 1>(c, level, Q, G, n_in, T, P, acc, s);
+    }
 }
 
 cudaError_t mac_ct(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32_t n_in, const uint64_t* T,
                    const uint64_t* C, uint64_t* A, uint64_t* B, cudaStream_t s) {
-    constexpr int QT = 4;
-    const dim3 g((c.n + kThreads - 1) / kThreads, G * (level + 1), (Q + QT - 1) / QT);
+    if (!Q || !G) return cudaSuccess;
     ProfScope ps(BM_KERNEL_MAC, s,
                  8.0 * c.n * (level + 1) * ((double)Q * n_in * 2 + 2.0 * G * n_in + 4.0 * Q * G));
-    pdl_launch(k_mac_ct<QT>, g, kThreads, 0, s, T, C, A, B, Q, G, n_in, level, c.tab, c.log_n);
-    return cudaGetLastError();
+    // at most 4 (query, group) triples of sums a thread
+    int qt = Q >= 4 ? 4 : (Q >= 2 ? 2 : 1), gt = G >= 2 && qt < 4 ? 2 : 1;
+    mac_tile_cap(qt, gt);
+    switch (qt * 8 + gt) {
+        case 4 * 8 + 2:
+        case 4 * 8 + 1: return launch_mac_ct<4, 1>(c, level, Q, G, n_in, T, C, A, B, s);
+        case 2 * 8 + 2: return launch_mac_ct<2, 2>(c, level, Q, G, n_in, T, C, A, B, s);
+        case 2 * 8 + 1: return launch_mac_ct<2, 1>(c, level, Q, G, n_in, T, C, A, B, s);
+        case 1 * 8 + 2: return launch_mac_ct<1, 2>(c, level, Q, G, n_in, T, C, A, B, s);
+        default: return launch_mac_ct<1, 1>(c, level, Q, G, n_in, T, C, A, B, s);
+    }
 }
 
 cudaError_t accumulate(const Context& c, uint32_t level, uint32_t n_targets, uint64_t* const* dst,
@@ -961,9 +1130,11 @@ cudaError_t accumulate(const Context& c, uint32_t level, uint32_t n_targets, uin
 cudaError_t mac_circ(const Context& c, uint32_t level, uint32_t Q, uint32_t n_in, const uint64_t* const* R,
                      const uint64_t* masks, uint64_t* t0, cudaStream_t s) {
     constexpr int OC = 8;
-    const dim3 g((c.n + kThreads - 1) / kThreads, level + 1, Q * ((n_in + OC - 1) / OC));
+    if (!Q) return cudaSuccess;
+    if (Q > 65535) return cudaErrorInvalidConfiguration;
+    const dim3 g((c.n / kMacThreads) * ((n_in + OC - 1) / OC), level + 1, Q);
     ProfScope ps(BM_KERNEL_MAC, s, 8.0 * c.n * (level + 1) * ((double)Q * n_in * 2 + (double)n_in + 2.0 * Q * n_in));
-    pdl_launch(k_mac_circ<OC>, g, kThreads, 0, s, R, masks, t0, n_in, level, c.tab, c.log_n);
+    pdl_launch(k_mac_circ<OC>, g, kMacThreads, 0, s, R, masks, t0, n_in, level, c.tab, c.log_n);
     return cudaGetLastError();
 }
 

@@ -352,6 +352,74 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
     }
 }
 
+// F4s: grid (T * nlx, N1 / R).  Target t sums its elements e in [off[t], off[t+1])
+// before a single ModDown (double hoisting):
+//   acc[t] = sum_e ( sum_d sigma_e(ext_of[e]_d) * key_e,d  +  P * sigma_e(c0 of src_of[e]) )
+// the last term on the q-limbs of the first component only (ModDown returns it
+// exactly: P * x has no special-prime residue and (P * x) * P^-1 = x); then, for
+// the special-prime limbs, the inverse row pass (as F4).
+template <int LA, int LB, int LT, int R>
+__global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
+    k_ks_f4s(const uint64_t* const* ext_of, const uint64_t* const* src_of, const uint64_t* const* key_of,
+             const uint64_t* gal_of, const uint64_t* off, uint64_t* __restrict__ acc,
+             const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L, uint32_t nb) {
+    constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>(), LOGN = LA + LB, N = 1 << LOGN;
+    constexpr int TWN = row_tw_entries<LB, R>();
+    __shared__ uint64_t sm[R * S];
+    __shared__ ulonglong2 twi[TWN];
+    const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
+    const SubMem sr{sm + jr * S, 1};
+    const uint32_t nd = kc->nd, nlx = kc->nlx;
+    const uint32_t tg = blockIdx.x / nlx, jj = blockIdx.x % nlx;
+    const int pi = ext_prime(jj, l1, L);
+    const uint64_t q = tab.q[pi], qn = tab.qneg[pi], q2 = 2 * q;
+    const uint64_t pm = jj < l1 ? kc->pmont[jj] : 0;
+    const int row = blockIdx.y * R + jr;
+    const size_t roff = (size_t)row * M;
+    if (jj >= l1) stage_row_twiddles<LA, LB, R, R * TH>(twi, tab.itw[pi], blockIdx.y * R);
+    pdl_wait();
+    const uint64_t e0 = off[tg], e1 = off[tg + 1];
+    uint64_t v[K];
+#pragma unroll 1
+    for (uint32_t comp = 0; comp < 2; comp++) {
+        Acc128 a[K];
+#pragma unroll 1
+        for (uint64_t e = e0; e < e1; e++) {
+            const uint32_t galois = (uint32_t)gal_of[e];
+            const uint64_t* key = key_of[e];
+            const uint64_t* ext = ext_of[e];
+            uint32_t src[K];
+#pragma unroll
+            for (int k = 0; k < K; k++) src[k] = perm_src((uint32_t)(roff + last_idx<LB, LT>(t, k)), LOGN, galois);
+#pragma unroll 1
+            for (uint32_t d = 0; d < nd; d++) {
+                const uint64_t* x = ext + ((size_t)d * nlx + jj) * N;
+                uint64_t kv[K];
+                nttr::load_last<LB, LT>(kv, key + ((size_t)(d * 2 + comp) * nb + pi) * N + roff, t);
+#pragma unroll
+                for (int k = 0; k < K; k++) mul_acc(a[k], x[src[k]], kv[k], q);
+            }
+            if (comp == 0 && jj < l1) {
+                const uint64_t* c0 = src_of[e] + (size_t)jj * N;
+#pragma unroll
+                for (int k = 0; k < K; k++) mul_acc(a[k], c0[src[k]], pm, q);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; k++) v[k] = redc(a[k], q, qn);
+        if (jj < l1) {
+            nttr::relayout<LB, LT, LB / LT - 1, 0>(v, sr, t);
+        } else {
+            if (comp == 0) tw_wait();
+            nttr::inv_pass<LB, LT>(v, sr, twi, RowBase<R>{jr}, t, q, q2);
+        }
+        uint64_t* o = acc + (((size_t)tg * 2 + comp) * nlx + jj) * N + roff;
+#pragma unroll
+        for (int k = 0; k < K; k++) o[first_idx<LB, LT>(t, k)] = v[k];
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // F5: grid (B * 2, N2 / C).  conv = Conv_{P -> Q_l}(acc's special-prime limbs).
 // ---------------------------------------------------------------------------
@@ -407,7 +475,8 @@ __global__ void __launch_bounds__(C * (1 << (LA - LT)))
 }
 
 // ---------------------------------------------------------------------------
-// F6: grid (B * l1, N1 / R).  out = (acc - conv) * P^-1 + sigma(c0) (+ add)
+// F6: grid (B * l1, N1 / R).  out = (acc - conv) * P^-1 + sigma(c0) (+ add); without
+// X0 and c0_of no sigma(c0) term (the sums of F4s hold it)
 // ---------------------------------------------------------------------------
 template <int LA, int LB, int LT, int R>
 __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 3)
@@ -422,7 +491,8 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 3)
     // hoisted rotations: each element has its own Galois element and reads sigma(c0)
     // from its source ciphertext (NTT form) instead of the copy X0
     if (gal_of) galois = (uint32_t)gal_of[b];
-    const uint64_t* x0 = c0_of ? c0_of[b] + (size_t)j * N : X0 + ((size_t)b * l1 + j) * N;
+    // sums of hoisted rotations (F4s) carry their sigma(c0) terms already: no X0, no c0_of
+    const uint64_t* x0 = c0_of ? c0_of[b] + (size_t)j * N : (X0 ? X0 + ((size_t)b * l1 + j) * N : nullptr);
     const uint32_t nlx = kc->nlx;
     const int row = blockIdx.y * R + jr;
     const size_t roff = (size_t)row * M;
@@ -448,7 +518,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 3)
         for (int k = 0; k < K; k++) {
             const int c = last_idx<LB, LT>(t, k);
             uint64_t o = shoup(subm(av[k], nttr::reduce4(v[k], q, q2), q), pinv.x, pinv.y, q);
-            if (comp == 0) o = addm(o, x0[perm_src((uint32_t)(roff + c), LOGN, galois)], q);
+            if (comp == 0 && x0) o = addm(o, x0[perm_src((uint32_t)(roff + c), LOGN, galois)], q);
             if (add) o = addm(o, ad[k], q);
             v[k] = o;
         }
@@ -735,6 +805,61 @@ cudaError_t ks_hoisted_launch(const Context& c, uint32_t level, uint32_t E, cons
     return cudaGetLastError();
 }
 
+// Sums of hoisted rotations before ModDown (double hoisting), F4s: acc[t] for T
+// targets, the elements of target t in [off[t], off[t+1]) rotating src_of[e] by
+// gal_of[e] with key key_of[e] from the extension ext_of[e] of src_of[e]'s c1.
+// Scratch: acc, then conv (ks_moddown_add), of T targets.
+template <int LA, int LB, int LT, int C, int R>
+cudaError_t ks_ipsum_launch(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
+                            const uint64_t* const* ext_of, const uint64_t* const* src_of,
+                            const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch, cudaStream_t s) {
+    constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
+    (void)N2;
+    const KsLevelConst& K = c.h_ksc[level];
+    const uint32_t l1 = level + 1, nd = K.nd, nlx = K.nlx, alpha = c.alpha;
+    const KsLevelConst* kc = c.d_ksc + level;
+    const int tr = R * (1 << (LB - LT));
+    const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB;
+    ProfScope ps(BM_KERNEL_KS_IP, s, lw * (nlx * ((double)E * nd + 2.0 * nd * E + 2.0 * T) + (double)E * l1),
+                 bf_r * T * 2.0 * alpha + N * (double)nlx * (2.0 * kProdMul * nd * E + 2.0 * kRedcMul * T) +
+                     (double)N * l1 * E * kProdMul);
+    pdl_launch(k_ks_f4s<LA, LB, LT, R>, dim3(T * nlx, N1 / R), tr, 0, s, ext_of, src_of, key_of, gal_of, off, scratch,
+               kc, c.tab, l1, c.L, c.nb);
+    return cudaGetLastError();
+}
+
+// ModDown of the T sums in scratch and tgt[t] += the result, F5 + F6 (in place: F6
+// reads each target word before writing it, and no sigma(c0) term -- F4s holds it).
+template <int LA, int LB, int LT, int C, int R>
+cudaError_t ks_moddown_add_launch(const Context& c, uint32_t level, uint32_t T, uint64_t* const* d_tgt,
+                                  uint64_t* scratch, cudaStream_t s) {
+    constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
+    const KsLevelConst& K = c.h_ksc[level];
+    const uint32_t l1 = level + 1, nlx = K.nlx, alpha = c.alpha;
+    const KsLevelConst* kc = c.d_ksc + level;
+    uint64_t* acc = scratch;
+    uint64_t* conv = acc + (size_t)T * 2 * nlx * N;
+    const int tr = R * (1 << (LB - LT)), tc = C * (1 << (LA - LT));
+    const size_t col_smem = 8 * col_smem_words<LA, LT, C>();
+    static bool attrs = [&] {
+        cudaFuncSetAttribute(k_ks_f5<LA, LB, LT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem);
+        return true;
+    }();
+    (void)attrs;
+    const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;
+    {
+        ProfScope ps(BM_KERNEL_MODDOWN, s, lw * T * 2 * (alpha + l1),
+                     bf_c * T * 2 * (alpha + l1) + kShoupMul * N * T * 2 * (alpha + (double)l1 * alpha));
+        pdl_launch(k_ks_f5<LA, LB, LT, C>, dim3(T * 2, N2 / C), tc, col_smem, s, acc, conv, kc, c.tab, l1, c.L, alpha);
+    }
+    {
+        ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * T * l1 * 8, bf_r * T * 2 * l1 + kShoupMul * N * T * 2 * l1);
+        pdl_launch(k_ks_f6<LA, LB, LT, R>, dim3(T * l1, N1 / R), tr, 0, s, conv, acc, nullptr, d_tgt, d_tgt, kc, c.tab,
+                   l1, 0u, nullptr, nullptr);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t ks_modup_scratch_words(const Context& c, uint32_t level, uint32_t B) {
@@ -766,6 +891,24 @@ cudaError_t ks_rotate_hoisted(const Context& c, uint32_t level, uint32_t E, cons
         return ks_hoisted_launch<8, 8, 2, 2, 2>(c, level, E, ext_of, src, key_of, gal_of, d_out, scratch, s);
     if (c.log_n == 12)
         return ks_hoisted_launch<6, 6, 2, 8, 8>(c, level, E, ext_of, src, key_of, gal_of, d_out, scratch, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t ks_ipsum_hoisted(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
+                             const uint64_t* const* ext_of, const uint64_t* const* src_of,
+                             const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch,
+                             cudaStream_t s) {
+    if (T == 0) return cudaSuccess;
+    if (c.log_n == 16) return ks_ipsum_launch<8, 8, 2, 2, 2>(c, level, T, off, E, ext_of, src_of, key_of, gal_of, scratch, s);
+    if (c.log_n == 12) return ks_ipsum_launch<6, 6, 2, 8, 8>(c, level, T, off, E, ext_of, src_of, key_of, gal_of, scratch, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t ks_moddown_add(const Context& c, uint32_t level, uint32_t T, uint64_t* const* d_tgt, uint64_t* scratch,
+                           cudaStream_t s) {
+    if (T == 0) return cudaSuccess;
+    if (c.log_n == 16) return ks_moddown_add_launch<8, 8, 2, 2, 2>(c, level, T, d_tgt, scratch, s);
+    if (c.log_n == 12) return ks_moddown_add_launch<6, 6, 2, 8, 8>(c, level, T, d_tgt, scratch, s);
     return cudaErrorInvalidValue;
 }
 

@@ -270,8 +270,9 @@ bm_status bm_measure_op_costs(bm_context* ctxh, bm_op_costs* out) {
     }
     if (ks_fused_supported(c)) {
         // hoisted rotations at every level: basis extension of 1..128 ciphertexts, 1..128
-        // rotations from extensions, sums of 1..128 ciphertexts; at the top level the
-        // circulant products of hoisted Algorithm 1, 4 queries x 2^k parts
+        // rotations from extensions, sums of 1..128 ciphertexts, 1..128 rotations summed
+        // before ModDown (four to a target) and 1..128 such ModDowns; at the top level
+        // the circulant products of hoisted Algorithm 1, 4 queries x 2^k parts
         const size_t cw = ct_words(c, L), ew = ks_ext_words(c, L);
         DevBuf in, outb, ext, scratch, key, masks, t0, plist;
         BM_CUDA_TRY(in.alloc(cw * kMaxB));
@@ -301,6 +302,13 @@ bm_status bm_measure_op_costs(bm_context* ctxh, bm_op_costs* out) {
         for (uint32_t k = 0; k <= kMaxB; k++) ho[k] = k;
         BM_CUDA_TRY(offs.alloc(kMaxB + 1));
         BM_CUDA_TRY(cudaMemcpy(offs.p, ho.data(), (kMaxB + 1) * 8, cudaMemcpyHostToDevice));
+        // double-hoisted rounds: 2^k rotations summed four to a target (row k of offs4)
+        DevBuf offs4;
+        std::vector<uint64_t> h4((size_t)BM_COST_POINTS * (kMaxB + 1));
+        for (int k = 0; k < BM_COST_POINTS; k++)
+            for (uint32_t t = 0; t <= kMaxB; t++) h4[(size_t)k * (kMaxB + 1) + t] = std::min<uint64_t>(4ull * t, 1ull << k);
+        BM_CUDA_TRY(offs4.alloc(h4.size()));
+        BM_CUDA_TRY(cudaMemcpy(offs4.p, h4.data(), h4.size() * 8, cudaMemcpyHostToDevice));
         for (uint32_t level = 0; level <= L; level++) {
             for (int k = 0; k < BM_COST_POINTS; k++) {
                 const uint32_t B = 1u << k;
@@ -322,6 +330,16 @@ bm_status bm_measure_op_costs(bm_context* ctxh, bm_op_costs* out) {
                                           B, s);
                     },
                     2, r);
+                out->t_us[BM_OP_IP_SUM][level][k] = tm.us(
+                    [&] {
+                        return ks_ipsum_hoisted(c, level, (B + 3) / 4, offs4.p + (size_t)k * (kMaxB + 1), B,
+                                                (const uint64_t* const*)dl, (const uint64_t* const*)(dl + kMaxB),
+                                                (const uint64_t* const*)(dl + 2 * kMaxB),
+                                                (const uint64_t*)(dl + 3 * kMaxB), scratch.p, s);
+                    },
+                    2, r);
+                out->t_us[BM_OP_MODDOWN][level][k] =
+                    tm.us([&] { return ks_moddown_add(c, level, B, dl + 4 * kMaxB, scratch.p, s); }, 2, r);
                 if (level == L)
                     out->t_us[BM_OP_MAC_CIRC][L][k] = tm.us(
                         [&] {

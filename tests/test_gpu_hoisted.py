@@ -46,6 +46,7 @@ def test_hoisted_match_is_bit_exact(name, m, s, R, nq):
         assert np.abs(om.scores(got, opacked) - ref).max() < 1e-5
 
 
+@pytest.mark.parametrize("double", [False, True])
 @pytest.mark.parametrize("name,m,s,R,nq,tail_only", [
     ("small4", 128, 16, 2500, 2, False),   # every hoisted form: rotate-and-sum 4 x 4, compression 15 rotations
     ("small4", 16, 4, 3000, 3, False),     # rotate-and-sum 2 x 2, partial packs
@@ -53,12 +54,17 @@ def test_hoisted_match_is_bit_exact(name, m, s, R, nq):
     ("small4", 16, 8, 2100, 1, False),     # rotate-and-sum 4 x 2
     ("toy", 16, 4, 1500, 2, True),         # client-expanded queries, per-group outputs (no compression)
 ])
-def test_hoisted_schedule_is_bit_exact(name, m, s, R, nq, tail_only):
+def test_hoisted_schedule_is_bit_exact(name, m, s, R, nq, tail_only, double):
+    """Every hoisted form; double=True: each round's rotations into one output
+    summed before a single ModDown (double hoisting)."""
     c = gctx(name)
-    om = OracleMatch(name, m, s, R, nq, hoisted=not tail_only and name != "toy", hoisted_tail=True)
+    om = OracleMatch(name, m, s, R, nq, hoisted=not tail_only and name != "toy", hoisted_tail=True,
+                     double_hoisted=double)
     _, _, ek = bm.bm_keygen_ex(c, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
     g = bm.bm_gallery_import(c, om.pts_array(), om.masks_array(), om.cmask_array(), R, m, s)
     flags = bm.BM_SCHED_HOISTED_ROTSUM | bm.BM_SCHED_HOISTED_COMPRESSION
+    if double:
+        flags |= bm.BM_SCHED_DOUBLE_HOISTED
     if om.hoisted:
         flags |= bm.BM_SCHED_HOISTED_EXPANSION
     bm.bm_gallery_set_schedule(g, flags)
@@ -73,15 +79,16 @@ def test_hoisted_schedule_is_bit_exact(name, m, s, R, nq, tail_only):
         assert np.abs(om.scores(got, opacked) - ref).max() < 1e-5
 
 
+@pytest.mark.parametrize("double", [False, True])
 @pytest.mark.parametrize("m,s,R,nq", [(128, 16, 6144, 1), (128, 4, 20000, 3)])
-def test_hoisted_and_doubling_forms_give_the_same_scores_ring16(m, s, R, nq):
+def test_hoisted_and_doubling_forms_give_the_same_scores_ring16(m, s, R, nq, double):
     c = gctx("ring16")
     feats = wl.gallery(R, m)
     qs, _ = wl.queries(feats, nq)
     sk, pk, ek = bm.bm_keygen_ex(c, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
     gd = bm.bm_encode_gallery(c, feats, m, s)
     gh = bm.bm_encode_gallery(c, feats, m, s)
-    bm.bm_gallery_set_schedule(gh, bm.BM_SCHED_ALL)
+    bm.bm_gallery_set_schedule(gh, bm.BM_SCHED_ALL | (bm.BM_SCHED_DOUBLE_HOISTED if double else 0))
     cts = bm.bm_encrypt_batch(c, pk, qs, m, s, bm.BM_QUERY_TILED, 4, 0)
     rd, rh = bm.bm_match(c, ek, gd, cts), bm.bm_match(c, ek, gh, cts)
     for qi in range(nq):

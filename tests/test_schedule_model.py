@@ -278,3 +278,33 @@ def test_every_hoisted_form_matches_the_oracle_counts(preset, R, dim, part, Q):
     # every rotated copy is summed into its target
     assert sum(o["count"] for o in ops if o["op"] == "accum") == sum(
         o["count"] for o in ops if o["op"] == "rot_hoisted" and o["level"] < lg)
+
+
+@pytest.mark.parametrize("preset,R,dim,part,Q", [("small4", 2500, 128, 16, 3), ("ring16", 1 << 20, 128, 4, 40),
+                                                 ("ring16", 6144, 128, 16, 1), ("small4", 3000, 32, 32, 2),
+                                                 ("toy", 1500, 16, 4, 2)])
+def test_double_hoisted_forms_match_the_oracle_counts(preset, R, dim, part, Q):
+    """One ModDown per round output: the plan's key-switch products and ModDowns
+    are the oracle's and no rotated copies are summed afterwards."""
+    single = bm.BM_LAYOUT_HOISTED | bm.BM_LAYOUT_HOISTED_ROTSUM | bm.BM_LAYOUT_HOISTED_COMPRESSION
+    ops, _ = bm.bm_plan_estimate(preset, R, dim, part, Q, packing=single | bm.BM_LAYOUT_DOUBLE_HOISTED)
+    log_n, n_q = PRESET[preset]
+    L, slots = n_q - 1, 1 << (log_n - 1)
+    tiled = L >= 3
+    lg = L - 1 if tiled else L
+    n_in = dim // part
+    groups = sch.n_groups(R, part, slots)
+    ev = sch.CountingEvaluator()
+    q = [sch.SymCt(L)] if tiled else [sch.SymCt(L) for _ in range(n_in)]
+    sch.match(ev, q, [[None] * n_in for _ in range(groups)], [None] * n_in, object() if lg >= 2 else None, dim, part,
+              expanded=not tiled, hoisted=tiled, hoisted_rotsum=True, hoisted_compress=True, double_hoisted=True)
+    orc = ev.counts()
+    lib = library_counts(ops)
+    for lv in range(L + 1):
+        assert lib[("modup", lv)] == Q * orc.get(("ModUp", lv), 0), lv
+        assert lib[("ip_sum", lv)] == Q * orc.get(("IPH", lv), 0), lv
+        assert lib[("moddown", lv)] == Q * orc.get(("ModDown", lv), 0), lv
+        assert lib[("rotate", lv)] == 0, lv
+        if lv < lg:
+            assert lib[("rot_hoisted", lv)] == 0, lv          # the tail's rotations are all summed
+    assert not any(o["op"] == "accum" for o in ops)
