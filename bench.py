@@ -59,13 +59,13 @@ def parse():
     ap.add_argument("--expansion", default="hoisted", choices=["doubling", "hoisted", "auto"],
                     help="form of Algorithm 1: the printed doubling order or the hoisted sum "
                          "(auto: serving picks per gallery by the cost model)")
-    ap.add_argument("--tail", default="hoisted", choices=["printed", "hoisted", "double"],
+    ap.add_argument("--tail", default="double", choices=["printed", "hoisted", "double"],
                     help="Algorithm 2's rotate-and-sum and the compression: the printed sequential forms, "
                          "rounds of hoisted rotations, or the same rounds with one ModDown per output "
                          "(double hoisting)")
     ap.add_argument("--gallery", default="plain", choices=["plain", "encrypted"],
                     help="gallery of plaintexts, or of ciphertexts enrolled on the server (Sec. 3.2)")
-    ap.add_argument("--packing", default="real", choices=["real", "complex"],
+    ap.add_argument("--packing", default="complex", choices=["real", "complex"],
                     help="gallery slot packing (complex: a second identity in the imaginary parts)")
     return ap.parse_args()
 
