@@ -556,6 +556,8 @@ bm::Gallery::~Gallery() {
     if (ctx) drop_plans(*ctx, id);
     if (d_pts) cudaFree(d_pts);
     if (d_masks) cudaFree(d_masks);
+    if (d_masks_hat) cudaFree(d_masks_hat);
+    if (d_circ_tw) cudaFree(d_circ_tw);
     if (d_cmask) cudaFree(d_cmask);
 }
 bm::Ciphertext::~Ciphertext() {
@@ -597,6 +599,10 @@ static bm_status gallery_alloc(Context& c, const Layout& lo, uint64_t n_ids, uin
     const size_t polys = lo.encrypted ? 2 : 1;
     cudaError_t e = cudaMalloc(&g.d_pts, (size_t)lo.groups * lo.n_in * polys * (lo.level + 1) * n * 8);
     if (e == cudaSuccess && lo.tiled) e = cudaMalloc(&g.d_masks, (size_t)lo.n_in * (c.L + 1) * n * 8);
+    if (e == cudaSuccess && lo.tiled && lo.n_in >= 2 && lo.n_in <= kMaxCircParts) {
+        e = cudaMalloc(&g.d_masks_hat, (size_t)lo.n_in * (c.L + 1) * n * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&g.d_circ_tw, (size_t)lo.n_in * (c.L + 1) * sizeof(ulonglong2));
+    }
     if (e == cudaSuccess && lo.compress) e = cudaMalloc(&g.d_cmask, (size_t)lo.level * n * 8);
     if (e != cudaSuccess) {
         delete gh;
@@ -627,12 +633,21 @@ static bm_status encode_gallery_masks(Context& c, const Layout& lo, uint32_t dim
             for (size_t k = 0; k < S; k++) z[k] = ((k % dim) / part == i) ? 1.0 : 0.0;
             BM_TRY(encode_to_device(c, z, (double)c.primes[c.L], c.L, g.d_masks + (size_t)i * (c.L + 1) * n));
         }
+        if (g.d_masks_hat)
+            BM_CUDA_TRY(circ_prepare(c, g.n_in, g.d_masks, g.d_masks_hat, g.d_circ_tw, c.stream));
     }
     if (lo.compress) {
         for (size_t k = 0; k < S; k++) z[k] = (k % part == 0) ? 1.0 : 0.0;
         BM_TRY(encode_to_device(c, z, (double)c.primes[lo.level - 1], lo.level - 1, g.d_cmask));
     }
     return BM_OK;
+}
+
+// the masks' side of hoisted Algorithm 1 as a convolution over the parts
+// (mac_circ), once the masks are on the device
+static cudaError_t gallery_circ(Context& c, Gallery& g) {
+    if (!g.d_masks_hat) return cudaSuccess;
+    return circ_prepare(c, g.n_in, g.d_masks, g.d_masks_hat, g.d_circ_tw, c.stream);
 }
 
 }  // namespace bm
@@ -758,6 +773,7 @@ bm_status bm_gallery_import_packed(bm_context* ctxh, const uint64_t* pts, const 
     cudaError_t e = up(g.d_pts, pts, lo.groups * lo.n_in, lo.level + 1);
     if (e == cudaSuccess && lo.tiled) e = up(g.d_masks, masks, lo.n_in, c.L + 1);
     if (e == cudaSuccess && lo.compress) e = up(g.d_cmask, cmask, 1, lo.level);
+    if (e == cudaSuccess) e = gallery_circ(c, g);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         delete gh;
@@ -957,6 +973,7 @@ bm_status bm_gallery_import_encrypted(bm_context* ctxh, const uint64_t* cts, con
     cudaError_t e = up(g.d_pts, cts, lo.groups * lo.n_in * 2, lo.level + 1);
     if (e == cudaSuccess) e = up(g.d_masks, masks, lo.n_in, c.L + 1);
     if (e == cudaSuccess) e = up(g.d_cmask, cmask, 1, lo.level);
+    if (e == cudaSuccess) e = gallery_circ(c, g);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(BM_E_CUDA, std::string("gallery import: ") + cudaGetErrorString(e));
     *out = guard.release();
@@ -1192,6 +1209,8 @@ struct SchedView {
     bool dhoist = false;                   // hoisted rounds with one ModDown per output
     const uint64_t* d_pts = nullptr;
     const uint64_t* d_masks = nullptr;
+    const uint64_t* d_masks_hat = nullptr;
+    const ulonglong2* d_circ_tw = nullptr;
     const uint64_t* d_cmask = nullptr;
 };
 
@@ -1210,6 +1229,8 @@ static SchedView view_of(const Gallery& g) {
     v.dhoist = (v.hrotsum || v.hcomp) && (g.sched & BM_SCHED_DOUBLE_HOISTED);
     v.d_pts = g.d_pts;
     v.d_masks = g.d_masks;
+    v.d_masks_hat = g.d_masks_hat;
+    v.d_circ_tw = g.d_circ_tw;
     v.d_cmask = g.d_cmask;
     return v;
 }
@@ -1451,7 +1472,9 @@ struct MatchRun {
                         R.push_back(j == 0 ? qs[q] : pl.R + ((size_t)q * n_in + j) * cw(c.L));
                 auto dR = pl.arena.list(R);
                 record(BM_OP_MAC_CIRC, c.L, n_in, nq, n_in);
-                if (pl.arena.live) check(mac_circ(c, c.L, nq, n_in, (const uint64_t* const*)dR, g.d_masks, pl.t0, s));
+                if (pl.arena.live)
+                    check(mac_circ(c, c.L, nq, n_in, (const uint64_t* const*)dR, g.d_masks, g.d_masks_hat,
+                                   g.d_circ_tw, pl.t0, s));
                 for (uint32_t q = 0; q < nq; q++)
                     for (uint32_t i = 0; i < n_in; i++) {
                         o0.push_back(pl.t0 + ((size_t)q * n_in + i) * cw(c.L));

@@ -174,6 +174,8 @@ struct Gallery {
     uint32_t sched = 0;                       // hoisted forms of the schedule (BM_SCHED_* flags)
     uint64_t* d_pts = nullptr;                // [groups][n_in][level+1][N] NTT + Montgomery
     uint64_t* d_masks = nullptr;              // [n_in][L+1][N] Algorithm-1 masks (tiled only)
+    uint64_t* d_masks_hat = nullptr;          // [n_in][L+1][N] their transform over the parts (circ_prepare)
+    ulonglong2* d_circ_tw = nullptr;          // [L+1][n_in] twiddles of that transform
     uint64_t* d_cmask = nullptr;              // [level][N] compression mask at level-1
     ~Gallery();
 };
@@ -279,6 +281,15 @@ void decode_complex(const Context& ctx, const double* coeffs, double scale, std:
 // Every launcher brackets its kernel with a ProfScope: launches and algorithmic
 // bytes are always counted per kernel class; with timing enabled a CUDA event
 // pair is recorded around the launch on its stream.
+// 32-bit multiply results of the modular arithmetic (the accounting of the
+// roofline): a Shoup product with a precomputed companion = the high half of
+// x*w' (four 32x32 partial products, both halves: 8) and the low halves of x*w
+// and of the quotient times q (4 each) = 16, as one butterfly; a sum of products
+// reduced once = 8 per product (the full 128-bit product, or four 32 x 32 -> 64
+// multiply-adds of 31-bit pieces, two multiplies each) plus one Montgomery
+// reduction per sum (the low half of t*(-q^-1), 4, and the high half of m*q, 8) = 12.
+constexpr double kShoupMul = 16, kProdMul = 8, kRedcMul = 12;
+
 struct ProfScope {
     ProfScope(int kind, cudaStream_t s, double alg_bytes, double alg_ops = 0, uint32_t launches = 1);
     ~ProfScope();
@@ -368,9 +379,17 @@ cudaError_t mul_plain(const Context& c, uint32_t level, uint32_t B, uint64_t* co
 // acc[q][g] = sum_i T[q][i] * P[g][i]  (T: [Q][n_in][2][level+1][N], P: [G][n_in][level+1][N])
 cudaError_t mac(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32_t n_in,
                 const uint64_t* T, const uint64_t* P, uint64_t* acc, cudaStream_t s);
-// hoisted Algorithm 1: t0[q][i] = sum_j R[q*n_in + j] * masks[(i - j) mod n_in] (t0 [Q][n_in] cts)
+// hoisted Algorithm 1: t0[q][i] = sum_j R[q*n_in + j] * masks[(i - j) mod n_in] (t0 [Q][n_in] cts);
+// with hat and tw from circ_prepare (2 <= n_in <= kMaxCircParts) as a cyclic
+// convolution over the parts by length-n_in transforms, else the direct sum
+constexpr uint32_t kMaxCircParts = 32;
 cudaError_t mac_circ(const Context& c, uint32_t level, uint32_t Q, uint32_t n_in, const uint64_t* const* R,
-                     const uint64_t* masks, uint64_t* t0, cudaStream_t s);
+                     const uint64_t* masks, const uint64_t* hat, const ulonglong2* tw, uint64_t* t0,
+                     cudaStream_t s);
+// the masks' side of that convolution: tw [L+1][n_in] twiddles (host-built, copied),
+// hat [n_in][L+1][N] = transformed masks / n_in (Montgomery form); synchronises s
+cudaError_t circ_prepare(const Context& c, uint32_t n_in, const uint64_t* masks, uint64_t* hat, ulonglong2* tw,
+                         cudaStream_t s);
 // dst[t] += sum of src[off[t] .. off[t+1]) (ciphertexts at `level`; off and the lists on the device)
 cudaError_t accumulate(const Context& c, uint32_t level, uint32_t n_targets, uint64_t* const* dst,
                        const uint64_t* const* src, const uint64_t* off, uint32_t n_src, cudaStream_t s);

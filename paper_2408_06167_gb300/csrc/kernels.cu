@@ -496,12 +496,17 @@ __global__ void k_mul_plain(uint64_t* const* in, const uint64_t* const* pt, uint
 constexpr int kMacThreads = 128;
 
 struct MacTile {
-    uint32_t q0, g0, j;
+    uint32_t q0, g0, j, c;
     uint32_t p;
 };
-__device__ __forceinline__ MacTile mac_tile(uint32_t n_qt, uint32_t n_gt, uint32_t chunks, int QT, int GT) {
+// block order: ciphertext component (kMacPolys of them a block's tile set) fastest,
+// then group tiles, query tiles, coefficient chunks, limbs
+__device__ __forceinline__ MacTile mac_tile(uint32_t n_qt, uint32_t n_gt, uint32_t chunks, int QT, int GT,
+                                            uint32_t n_c) {
     uint32_t b = blockIdx.x;
     MacTile t;
+    t.c = b % n_c;
+    b /= n_c;
     t.g0 = (b % n_gt) * GT;
     b /= n_gt;
     t.q0 = (b % n_qt) * QT;
@@ -520,7 +525,7 @@ __global__ void __launch_bounds__(kMacThreads) k_mac(const uint64_t* __restrict_
                                                      uint32_t n_in, uint32_t lvl, DevTables tab, uint32_t log_n,
                                                      uint32_t n_qt, uint32_t n_gt) {
     const uint32_t n = 1u << log_n, l1 = lvl + 1;
-    const MacTile t = mac_tile(n_qt, n_gt, n / kMacThreads, QT, GT);
+    const MacTile t = mac_tile(n_qt, n_gt, n / kMacThreads, QT, GT, 1);
     pdl_wait();
     const uint32_t nq = min((uint32_t)QT, Qn - t.q0), ng = min((uint32_t)GT, G - t.g0);
     const uint64_t q = tab.q[t.j], qn = tab.qneg[t.j], q4 = 4 * q;
@@ -529,26 +534,45 @@ __global__ void __launch_bounds__(kMacThreads) k_mac(const uint64_t* __restrict_
     const size_t p_g = (size_t)n_in * ln;                    // stride of P: group (part: ln)
     const uint64_t* tp = T + (size_t)t.q0 * t_q + (size_t)t.j * n + t.p;
     const uint64_t* pp = P + (size_t)t.g0 * p_g + (size_t)t.j * n + t.p;
+    // the words of U parts are loaded before their products (U by the tile's registers)
+    constexpr int W = 2 * QT + GT, U = W * 4 <= 24 ? 4 : (W * 2 <= 12 ? 2 : 1);
     Acc62 a0[QT][GT], a1[QT][GT];
     for (uint32_t i0 = 0; i0 < n_in; i0 += kFold62Every) {
-        const uint32_t i1 = min(n_in, i0 + kFold62Every);
-        for (uint32_t i = i0; i < i1; i++) {
-            Piece31 x0[QT], x1[QT], y[GT];
 #pragma unroll
-            for (int k = 0; k < QT; k++) {
-                const uint64_t* r = tp + k * t_q + i * t_i;
-                x0[k] = piece31((uint32_t)k < nq ? r[0] : 0);
-                x1[k] = piece31((uint32_t)k < nq ? r[ln] : 0);
+        for (int v0 = 0; v0 < kFold62Every; v0 += U) {
+            uint64_t xr0[U][QT], xr1[U][QT], yr[U][GT];
+#pragma unroll
+            for (int v = 0; v < U; v++) {
+                const uint32_t i = i0 + v0 + v;
+                const bool ok = i < n_in;
+#pragma unroll
+                for (int k = 0; k < QT; k++) {
+                    const uint64_t* r = tp + k * t_q + i * t_i;
+                    xr0[v][k] = ok && (uint32_t)k < nq ? r[0] : 0;
+                    xr1[v][k] = ok && (uint32_t)k < nq ? r[ln] : 0;
+                }
+#pragma unroll
+                for (int h = 0; h < GT; h++) yr[v][h] = ok && (uint32_t)h < ng ? pp[h * p_g + i * ln] : 0;
             }
 #pragma unroll
-            for (int h = 0; h < GT; h++) y[h] = piece31((uint32_t)h < ng ? pp[h * p_g + i * ln] : 0);
+            for (int v = 0; v < U; v++) {
+                if (i0 + v0 + v >= n_in) break;
+                Piece31 x0[QT], x1[QT], y[GT];
 #pragma unroll
-            for (int k = 0; k < QT; k++)
-#pragma unroll
-                for (int h = 0; h < GT; h++) {
-                    mul_add(a0[k][h], x0[k], y[h]);
-                    mul_add(a1[k][h], x1[k], y[h]);
+                for (int k = 0; k < QT; k++) {
+                    x0[k] = piece31(xr0[v][k]);
+                    x1[k] = piece31(xr1[v][k]);
                 }
+#pragma unroll
+                for (int h = 0; h < GT; h++) y[h] = piece31(yr[v][h]);
+#pragma unroll
+                for (int k = 0; k < QT; k++)
+#pragma unroll
+                    for (int h = 0; h < GT; h++) {
+                        mul_add(a0[k][h], x0[k], y[h]);
+                        mul_add(a1[k][h], x1[k], y[h]);
+                    }
+            }
         }
 #pragma unroll
         for (int k = 0; k < QT; k++)
@@ -581,7 +605,7 @@ __global__ void __launch_bounds__(kMacThreads) k_mac_ct(const uint64_t* __restri
                                                         uint32_t Qn, uint32_t G, uint32_t n_in, uint32_t lvl,
                                                         DevTables tab, uint32_t log_n, uint32_t n_qt, uint32_t n_gt) {
     const uint32_t n = 1u << log_n, l1 = lvl + 1;
-    const MacTile t = mac_tile(n_qt, n_gt, n / kMacThreads, QT, GT);
+    const MacTile t = mac_tile(n_qt, n_gt, n / kMacThreads, QT, GT, 1);
     pdl_wait();
     const uint32_t nq = min((uint32_t)QT, Qn - t.q0), ng = min((uint32_t)GT, G - t.g0);
     const uint64_t q = tab.q[t.j], qn = tab.qneg[t.j], q4 = 4 * q;
@@ -644,22 +668,27 @@ __global__ void __launch_bounds__(kMacThreads) k_mac_ct(const uint64_t* __restri
 // Grid (ceil(n_in / OC) * N / kMacThreads, l1, Q), output chunks fastest so that
 // the passes over one coefficient range run together and share its rotated
 // copies in L2: a thread computes OC outputs i of one query, limb and
-// coefficient, reading each rotated query once per OC outputs; the block stages
-// the query's pointer list in shared memory.
-template <int OC>
+// coefficient, reading each rotated query once per OC outputs.  The block
+// stages the query's pointer list and, with SM, its words of every mask (split
+// into 31-bit pieces; n_in * kMacThreads words of dynamic shared memory) --
+// static gallery data, staged before the wait on the previous kernel.
+template <int OC, bool SM>
 __global__ void __launch_bounds__(kMacThreads) k_mac_circ(const uint64_t* const* R, const uint64_t* __restrict__ masks,
                                                           uint64_t* __restrict__ t0, uint32_t n_in, uint32_t lvl,
                                                           DevTables tab, uint32_t log_n) {
+    extern __shared__ uint64_t sm_mask[];                       // [n_in][kMacThreads] (SM)
     __shared__ const uint64_t* sR[kMacThreads];
     const uint32_t n = 1u << log_n, l1 = lvl + 1, nm = n_in - 1;
     const uint32_t chunks = (n_in + OC - 1) / OC;
     const uint32_t i0 = (blockIdx.x % chunks) * OC;
     const uint32_t p = (blockIdx.x / chunks) * kMacThreads + threadIdx.x;   // < n: the grid covers N exactly
     const uint32_t j = blockIdx.y, qi = blockIdx.z;
-    pdl_wait();
-    const uint64_t q = tab.q[j], qn = tab.qneg[j], q4 = 4 * q;
     const size_t ln = (size_t)l1 * n;
     const uint64_t* mj = masks + (size_t)j * n + p;               // mask k at mj + k * ln
+    if (SM)
+        for (uint32_t k = 0; k < n_in; k++) sm_mask[k * kMacThreads + threadIdx.x] = pack31(mj[k * ln]);
+    pdl_wait();
+    const uint64_t q = tab.q[j], qn = tab.qneg[j], q4 = 4 * q;
     Acc62 s0[OC], s1[OC];
     for (uint32_t b0 = 0; b0 < n_in; b0 += kMacThreads) {
         const uint32_t nb = min(n_in - b0, (uint32_t)kMacThreads);
@@ -667,15 +696,25 @@ __global__ void __launch_bounds__(kMacThreads) k_mac_circ(const uint64_t* const*
         if (threadIdx.x < nb) sR[threadIdx.x] = R[(size_t)qi * n_in + b0 + threadIdx.x];
         __syncthreads();
         for (uint32_t u0 = 0; u0 < nb; u0 += kFold62Every) {
-            const uint32_t u1 = min(nb, u0 + kFold62Every);
-            for (uint32_t u = u0; u < u1; u++) {
-                const uint32_t jj = b0 + u;
-                const uint64_t* r = sR[u] + (size_t)j * n + p;
-                const Piece31 r0 = piece31(r[0]), r1 = piece31(r[ln]);
+            uint64_t rv0[kFold62Every], rv1[kFold62Every];
+#pragma unroll
+            for (int v = 0; v < kFold62Every; v++) {
+                if (u0 + v < nb) {
+                    const uint64_t* r = sR[u0 + v] + (size_t)j * n + p;
+                    rv0[v] = r[0];
+                    rv1[v] = r[ln];
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < kFold62Every; v++) {
+                if (u0 + v >= nb) break;
+                const uint32_t jj = b0 + u0 + v;
+                const Piece31 r0 = piece31(rv0[v]), r1 = piece31(rv1[v]);
 #pragma unroll
                 for (int o = 0; o < OC; o++) {
                     if (i0 + o >= n_in) break;
-                    const Piece31 mk = piece31(mj[(size_t)((i0 + o - jj) & nm) * ln]);
+                    const uint32_t k = (i0 + o - jj) & nm;
+                    const Piece31 mk = SM ? unpack31(sm_mask[k * kMacThreads + threadIdx.x]) : piece31(mj[k * ln]);
                     mul_add(s0[o], r0, mk);
                     mul_add(s1[o], r1, mk);
                 }
@@ -695,6 +734,117 @@ __global__ void __launch_bounds__(kMacThreads) k_mac_circ(const uint64_t* const*
         t0[ob] = redc(s0[o], q, qn);
         t0[ob + ln] = redc(s1[o], q, qn);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1's hoisted sum as a cyclic convolution over the parts.  For one
+// coefficient of one limb, t0[i] = sum_j R[j] * M[(i - j) mod n] is the length-n
+// cyclic convolution of the rotated copies with the masks.  With w a primitive
+// n-th root of unity mod q (n divides q - 1: every prime is 1 mod 2N) it equals
+// DIT_{w^-1}(DIF_w(R) * DIF_w(M) / n): Gentleman-Sande forward (natural order in,
+// bit-reversed out), the products in that order, Cooley-Tukey inverse
+// (bit-reversed in, natural out).  The masks' side DIF_w(M) / n is computed once
+// per gallery (k_circ_prep, kept in Montgomery form); the result has the same
+// residues as the direct sum, for (n/2) log2 n butterflies a side -- those with
+// twiddle 1 without a product -- and n products instead of n^2.
+// Twiddle table per limb j: [j][e] = w^e for e < n/2, then [j][n/2 + e] = w^-e (Shoup pairs).
+// ---------------------------------------------------------------------------
+template <int NIN>
+__device__ __forceinline__ void circ_dif(uint64_t (&x)[NIN], const ulonglong2* fw, uint64_t q) {
+#pragma unroll
+    for (int len = NIN / 2; len >= 1; len >>= 1)
+#pragma unroll
+        for (int st = 0; st < NIN; st += 2 * len)
+#pragma unroll
+            for (int k = 0; k < len; k++) {
+                const uint64_t u = x[st + k], v = x[st + k + len];
+                x[st + k] = addm(u, v, q);
+                const uint64_t d = subm(u, v, q);
+                if (k == 0) {
+                    x[st + k + len] = d;
+                } else {
+                    const ulonglong2 w = fw[k * (NIN / (2 * len))];
+                    x[st + k + len] = shoup(d, w.x, w.y, q);
+                }
+            }
+}
+template <int NIN>
+__device__ __forceinline__ void circ_dit(uint64_t (&x)[NIN], const ulonglong2* iw, uint64_t q) {
+#pragma unroll
+    for (int len = 1; len < NIN; len <<= 1)
+#pragma unroll
+        for (int st = 0; st < NIN; st += 2 * len)
+#pragma unroll
+            for (int k = 0; k < len; k++) {
+                const uint64_t u = x[st + k];
+                uint64_t v = x[st + k + len];
+                if (k != 0) {
+                    const ulonglong2 w = iw[k * (NIN / (2 * len))];
+                    v = shoup(v, w.x, w.y, q);
+                }
+                x[st + k] = addm(u, v, q);
+                x[st + k + len] = subm(u, v, q);
+            }
+}
+
+struct CircNinv {
+    ulonglong2 v[MAXB];   // n^-1 mod q_j (Shoup pairs)
+};
+
+// hat[k][j][p] = (DIF_w(masks[.][j][p]))[k] / n; the masks are in Montgomery form
+// and so is hat.  Grid (N / kMacThreads, l1).
+template <int NIN>
+__global__ void __launch_bounds__(kMacThreads) k_circ_prep(const uint64_t* __restrict__ masks,
+                                                           uint64_t* __restrict__ hat,
+                                                           const ulonglong2* __restrict__ tw, CircNinv ninv,
+                                                           uint32_t l1, DevTables tab, uint32_t log_n) {
+    __shared__ ulonglong2 stw[NIN];
+    const uint32_t n = 1u << log_n, j = blockIdx.y, p = blockIdx.x * kMacThreads + threadIdx.x;
+    const size_t ln = (size_t)l1 * n;
+    if (threadIdx.x < NIN) stw[threadIdx.x] = tw[(size_t)j * NIN + threadIdx.x];
+    __syncthreads();
+    const uint64_t q = tab.q[j];
+    uint64_t x[NIN];
+#pragma unroll
+    for (int k = 0; k < NIN; k++) x[k] = masks[k * ln + (size_t)j * n + p];
+    circ_dif<NIN>(x, stw, q);
+    const ulonglong2 ni = ninv.v[j];
+#pragma unroll
+    for (int k = 0; k < NIN; k++) hat[k * ln + (size_t)j * n + p] = shoup(x[k], ni.x, ni.y, q);
+}
+
+// t0[q][i][c][j][p] = sum_jj R[q][jj][c][j][p] * mask[(i - jj) mod NIN][j][p], by the
+// convolution above.  Grid (2 * N / kMacThreads, l1, Q): a thread takes one
+// coefficient of one component of one limb of one query (component fastest).
+template <int NIN>
+__global__ void __launch_bounds__(kMacThreads) k_mac_circ_ntt(const uint64_t* const* R,
+                                                              const uint64_t* __restrict__ hat,
+                                                              const ulonglong2* __restrict__ tw,
+                                                              uint64_t* __restrict__ t0, uint32_t lvl, DevTables tab,
+                                                              uint32_t log_n) {
+    __shared__ ulonglong2 stw[NIN];
+    __shared__ const uint64_t* sR[NIN];
+    const uint32_t n = 1u << log_n, l1 = lvl + 1;
+    const uint32_t c = blockIdx.x & 1, p = (blockIdx.x >> 1) * kMacThreads + threadIdx.x;
+    const uint32_t j = blockIdx.y, qi = blockIdx.z;
+    const size_t ln = (size_t)l1 * n;
+    if (threadIdx.x < NIN) stw[threadIdx.x] = tw[(size_t)j * NIN + threadIdx.x];   // gallery data: before the wait
+    pdl_wait();
+    if (threadIdx.x < NIN) sR[threadIdx.x] = R[(size_t)qi * NIN + threadIdx.x];
+    __syncthreads();
+    const uint64_t q = tab.q[j], qn = tab.qneg[j];
+    const size_t off = (size_t)c * ln + (size_t)j * n + p;
+    uint64_t x[NIN];
+#pragma unroll
+    for (int k = 0; k < NIN; k++) x[k] = sR[k][off];
+    circ_dif<NIN>(x, stw, q);
+    const uint64_t* h = hat + (size_t)j * n + p;
+#pragma unroll
+    for (int k = 0; k < NIN; k++) x[k] = mont(x[k], h[k * ln], q, qn);
+    circ_dit<NIN>(x, stw + NIN / 2, q);
+    uint64_t* o = t0 + (size_t)qi * NIN * 2 * ln + off;
+#pragma unroll
+    for (int i = 0; i < NIN; i++) o[(size_t)i * 2 * ln] = x[i];
 }
 
 // dst[t] += sum of src[k], k in [off[t], off[t+1]): ciphertexts [2][l1][N] at one
@@ -1054,11 +1204,11 @@ static void mac_tile_cap(int& qt, int& gt) {
 
 // tile shape of the HE-C^3 products: up to 4 queries and 4 (ct x pt) or 2
 // (ct x ct) groups a thread; blocks = tiles x chunks x limbs
-static bool mac_grid(const Context& c, uint32_t level, uint32_t Q, uint32_t G, int QT, int GT, uint32_t& n_qt,
-                     uint32_t& n_gt, uint32_t& blocks) {
+static bool mac_grid(const Context& c, uint32_t level, uint32_t Q, uint32_t G, int QT, int GT, uint32_t n_c,
+                     uint32_t& n_qt, uint32_t& n_gt, uint32_t& blocks) {
     n_qt = (Q + QT - 1) / QT;
     n_gt = (G + GT - 1) / GT;
-    const uint64_t b = (uint64_t)n_qt * n_gt * (c.n / kMacThreads) * (level + 1);
+    const uint64_t b = (uint64_t)n_c * n_qt * n_gt * (c.n / kMacThreads) * (level + 1);
     blocks = (uint32_t)b;
     return b > 0 && b <= 0x7fffffffull;
 }
@@ -1067,7 +1217,7 @@ template <int QT, int GT>
 static cudaError_t launch_mac(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32_t n_in,
                               const uint64_t* T, const uint64_t* P, uint64_t* acc, cudaStream_t s) {
     uint32_t n_qt, n_gt, blocks;
-    if (!mac_grid(c, level, Q, G, QT, GT, n_qt, n_gt, blocks)) return cudaErrorInvalidConfiguration;
+    if (!mac_grid(c, level, Q, G, QT, GT, 1, n_qt, n_gt, blocks)) return cudaErrorInvalidConfiguration;
     return pdl_launch(k_mac<QT, GT>, dim3(blocks), kMacThreads, 0, s, T, P, acc, Q, G, n_in, level, c.tab, c.log_n,
                       n_qt, n_gt);
 }
@@ -1076,7 +1226,7 @@ template <int QT, int GT>
 static cudaError_t launch_mac_ct(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32_t n_in,
                                  const uint64_t* T, const uint64_t* C, uint64_t* A, uint64_t* B, cudaStream_t s) {
     uint32_t n_qt, n_gt, blocks;
-    if (!mac_grid(c, level, Q, G, QT, GT, n_qt, n_gt, blocks)) return cudaErrorInvalidConfiguration;
+    if (!mac_grid(c, level, Q, G, QT, GT, 1, n_qt, n_gt, blocks)) return cudaErrorInvalidConfiguration;
     return pdl_launch(k_mac_ct<QT, GT>, dim3(blocks), kMacThreads, 0, s, T, C, A, B, Q, G, n_in, level, c.tab,
                       c.log_n, n_qt, n_gt);
 }
@@ -1084,9 +1234,14 @@ static cudaError_t launch_mac_ct(const Context& c, uint32_t level, uint32_t Q, u
 cudaError_t mac(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32_t n_in, const uint64_t* T,
                 const uint64_t* P, uint64_t* acc, cudaStream_t s) {
     if (!Q || !G) return cudaSuccess;
-    ProfScope ps(BM_KERNEL_MAC, s, 8.0 * c.n * (level + 1) * ((double)Q * n_in * 2 + (double)G * n_in + 2.0 * Q * G));
-    // at most 8 (query, group) sums a thread (six registers each)
-    int qt = Q >= 4 ? 4 : (Q >= 2 ? 2 : 1), gt = G >= 3 ? (qt == 4 ? 2 : 4) : (G == 2 ? 2 : 1);
+    const double lim = (double)c.n * (level + 1);   // coefficients of a polynomial at this level
+    ProfScope ps(BM_KERNEL_MAC, s, 8.0 * lim * ((double)Q * n_in * 2 + (double)G * n_in + 2.0 * Q * G),
+                 lim * 2.0 * Q * G * (kProdMul * n_in + kRedcMul));
+    // (query, group) sums of both components a thread, six registers each: a tile of 4
+    // queries x 1 group with many queries (measured best on the batched workloads:
+    // the group tiles re-read the query words from L2), else up to 2 x 2 / 1 x 4
+    int qt = Q >= 4 ? 4 : (Q >= 2 ? 2 : 1);
+    int gt = qt == 4 ? 1 : (qt == 2 ? (G >= 2 ? 2 : 1) : (G >= 3 ? 4 : (G == 2 ? 2 : 1)));
     mac_tile_cap(qt, gt);
     switch (qt * 8 + gt) {
         case 4 * 8 + 4:
@@ -1104,8 +1259,9 @@ cudaError_t mac(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32
 cudaError_t mac_ct(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32_t n_in, const uint64_t* T,
                    const uint64_t* C, uint64_t* A, uint64_t* B, cudaStream_t s) {
     if (!Q || !G) return cudaSuccess;
-    ProfScope ps(BM_KERNEL_MAC, s,
-                 8.0 * c.n * (level + 1) * ((double)Q * n_in * 2 + 2.0 * G * n_in + 4.0 * Q * G));
+    const double lim = (double)c.n * (level + 1);
+    ProfScope ps(BM_KERNEL_MAC, s, 8.0 * lim * ((double)Q * n_in * 2 + 2.0 * G * n_in + 4.0 * Q * G),
+                 lim * (double)Q * G * (4.0 * kProdMul * n_in + 3.0 * kRedcMul));
     // at most 4 (query, group) triples of sums a thread
     int qt = Q >= 4 ? 4 : (Q >= 2 ? 2 : 1), gt = G >= 2 && qt < 4 ? 2 : 1;
     mac_tile_cap(qt, gt);
@@ -1127,15 +1283,88 @@ cudaError_t accumulate(const Context& c, uint32_t level, uint32_t n_targets, uin
                       off, level + 1, c.tab, c.n);
 }
 
+// non-trivial twiddle products of one length-n transform (butterflies with k > 0)
+static double circ_products(uint32_t n) {
+    double t = 0;
+    for (uint32_t len = n / 2; len >= 1; len >>= 1) t += (double)(n / (2 * len)) * (len - 1);
+    return t;
+}
+
+template <int NIN>
+static cudaError_t launch_circ_ntt(const Context& c, uint32_t level, uint32_t Q, const uint64_t* const* R,
+                                   const uint64_t* hat, const ulonglong2* tw, uint64_t* t0, cudaStream_t s) {
+    return pdl_launch(k_mac_circ_ntt<NIN>, dim3(2 * (c.n / kMacThreads), level + 1, Q), kMacThreads, 0, s, R, hat, tw,
+                      t0, level, c.tab, c.log_n);
+}
+
 cudaError_t mac_circ(const Context& c, uint32_t level, uint32_t Q, uint32_t n_in, const uint64_t* const* R,
-                     const uint64_t* masks, uint64_t* t0, cudaStream_t s) {
+                     const uint64_t* masks, const uint64_t* hat, const ulonglong2* tw, uint64_t* t0,
+                     cudaStream_t s) {
     constexpr int OC = 8;
     if (!Q) return cudaSuccess;
     if (Q > 65535) return cudaErrorInvalidConfiguration;
+    const double lim = (double)c.n * (level + 1);
+    if (hat && tw && n_in >= 2 && n_in <= kMaxCircParts) {
+        // two transforms of n_in words and n_in Montgomery products per coefficient,
+        // component and query
+        ProfScope ps(BM_KERNEL_MAC, s, 8.0 * lim * ((double)Q * n_in * 2 + (double)n_in + 2.0 * Q * n_in),
+                     lim * 2.0 * Q * (2.0 * kShoupMul * circ_products(n_in) + (kProdMul + kRedcMul) * n_in));
+        switch (n_in) {
+            case 2: return launch_circ_ntt<2>(c, level, Q, R, hat, tw, t0, s);
+            case 4: return launch_circ_ntt<4>(c, level, Q, R, hat, tw, t0, s);
+            case 8: return launch_circ_ntt<8>(c, level, Q, R, hat, tw, t0, s);
+            case 16: return launch_circ_ntt<16>(c, level, Q, R, hat, tw, t0, s);
+            default: return launch_circ_ntt<32>(c, level, Q, R, hat, tw, t0, s);
+        }
+    }
     const dim3 g((c.n / kMacThreads) * ((n_in + OC - 1) / OC), level + 1, Q);
-    ProfScope ps(BM_KERNEL_MAC, s, 8.0 * c.n * (level + 1) * ((double)Q * n_in * 2 + (double)n_in + 2.0 * Q * n_in));
-    pdl_launch(k_mac_circ<OC>, g, kMacThreads, 0, s, R, masks, t0, n_in, level, c.tab, c.log_n);
+    // masks in shared memory up to 64 parts (64 KiB a block)
+    constexpr uint32_t kMaxSmParts = 64;
+    static const bool attr = [] {
+        return cudaFuncSetAttribute(k_mac_circ<OC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(kMaxSmParts * kMacThreads * 8)) == cudaSuccess;
+    }();
+    ProfScope ps(BM_KERNEL_MAC, s, 8.0 * lim * ((double)Q * n_in * 2 + (double)n_in + 2.0 * Q * n_in),
+                 lim * 2.0 * Q * n_in * (kProdMul * n_in + kRedcMul));
+    if (attr && n_in <= kMaxSmParts)
+        pdl_launch(k_mac_circ<OC, true>, g, kMacThreads, (size_t)n_in * kMacThreads * 8, s, R, masks, t0, n_in, level,
+                   c.tab, c.log_n);
+    else
+        pdl_launch(k_mac_circ<OC, false>, g, kMacThreads, 0, s, R, masks, t0, n_in, level, c.tab, c.log_n);
     return cudaGetLastError();
+}
+
+cudaError_t circ_prepare(const Context& c, uint32_t n_in, const uint64_t* masks, uint64_t* hat, ulonglong2* tw,
+                         cudaStream_t s) {
+    if (n_in < 2 || n_in > kMaxCircParts || (n_in & (n_in - 1))) return cudaErrorInvalidValue;
+    const uint32_t l1 = c.L + 1;
+    std::vector<ulonglong2> h((size_t)l1 * n_in);
+    CircNinv ninv{};
+    for (uint32_t j = 0; j < l1; j++) {
+        const uint64_t q = c.primes[j];
+        const uint64_t w = h_powmod(c.psi[j], (2ull << c.log_n) / n_in, q), wi = h_invmod(w, q);
+        for (uint32_t e = 0; e < n_in / 2; e++) {
+            const uint64_t a = h_powmod(w, e, q), b = h_powmod(wi, e, q);
+            h[(size_t)j * n_in + e] = make_ulonglong2(a, h_shoup_companion(a, q));
+            h[(size_t)j * n_in + n_in / 2 + e] = make_ulonglong2(b, h_shoup_companion(b, q));
+        }
+        const uint64_t ni = h_invmod(n_in % q, q);
+        ninv.v[j] = make_ulonglong2(ni, h_shoup_companion(ni, q));
+    }
+    cudaError_t e = cudaMemcpyAsync(tw, h.data(), h.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    const dim3 g(c.n / kMacThreads, l1);
+    switch (n_in) {
+        case 2: k_circ_prep<2><<<g, kMacThreads, 0, s>>>(masks, hat, tw, ninv, l1, c.tab, c.log_n); break;
+        case 4: k_circ_prep<4><<<g, kMacThreads, 0, s>>>(masks, hat, tw, ninv, l1, c.tab, c.log_n); break;
+        case 8: k_circ_prep<8><<<g, kMacThreads, 0, s>>>(masks, hat, tw, ninv, l1, c.tab, c.log_n); break;
+        case 16: k_circ_prep<16><<<g, kMacThreads, 0, s>>>(masks, hat, tw, ninv, l1, c.tab, c.log_n); break;
+        default: k_circ_prep<32><<<g, kMacThreads, 0, s>>>(masks, hat, tw, ninv, l1, c.tab, c.log_n); break;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the host table must outlive the copy
+    return cudaStreamSynchronize(s);
 }
 
 }  // namespace bm

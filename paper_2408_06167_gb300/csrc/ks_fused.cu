@@ -40,13 +40,6 @@ __device__ __forceinline__ uint64_t red6(uint64_t y, uint64_t t) {   // [0, 6t) 
 
 constexpr int kMaxDigit = 2;   // limbs per digit and special primes handled by the fused kernels
 
-// 32-bit multiply results of the modular arithmetic (the accounting of the
-// roofline): a Shoup product with a precomputed companion = the high half of
-// x*w' (four 32x32 partial products, both halves: 8) and the low halves of x*w
-// and of the quotient times q (4 each) = 16, as one butterfly; a sum of products
-// reduced once = 8 per full 128-bit product plus one Montgomery reduction (the
-// low half of t*(-q^-1), 4, and the high half of m*q, 8) = 12.
-constexpr double kShoupMul = 16, kProdMul = 8, kRedcMul = 12;
 
 using nttr::ColBase;
 using nttr::first_idx;

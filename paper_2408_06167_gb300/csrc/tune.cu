@@ -274,17 +274,21 @@ bm_status bm_measure_op_costs(bm_context* ctxh, bm_op_costs* out) {
         // before ModDown (four to a target) and 1..128 such ModDowns; at the top level
         // the circulant products of hoisted Algorithm 1, 4 queries x 2^k parts
         const size_t cw = ct_words(c, L), ew = ks_ext_words(c, L);
-        DevBuf in, outb, ext, scratch, key, masks, t0, plist;
+        DevBuf in, outb, ext, scratch, key, masks, hat, ctw, t0, plist;
         BM_CUDA_TRY(in.alloc(cw * kMaxB));
         BM_CUDA_TRY(outb.alloc(cw * kMaxB));
         BM_CUDA_TRY(ext.alloc(ew * kMaxB));
         BM_CUDA_TRY(scratch.alloc(std::max(ks_modup_scratch_words(c, L, kMaxB), ks_hoisted_scratch_words(c, L, kMaxB))));
         BM_CUDA_TRY(key.alloc((size_t)c.digits.size() * 2 * c.nb * c.n));
         BM_CUDA_TRY(masks.alloc((size_t)kMaxB * (L + 1) * c.n));
+        BM_CUDA_TRY(hat.alloc((size_t)kMaxB * (L + 1) * c.n));
+        BM_CUDA_TRY(ctw.alloc((size_t)(L + 1) * kMaxCircParts * 2));   // twiddle pairs of up to 32 parts
         BM_CUDA_TRY(t0.alloc((size_t)kMacQ * kMaxB * cw));
         BM_CUDA_TRY(fill(c, in.p, cw * kMaxB, L + 1, 61, s));
         BM_CUDA_TRY(fill(c, key.p, key.words, c.nb, 62, s));
         BM_CUDA_TRY(fill(c, masks.p, masks.words, L + 1, 63, s));
+        BM_CUDA_TRY(fill(c, hat.p, hat.words, L + 1, 64, s));
+        BM_CUDA_TRY(fill(c, ctw.p, ctw.words, L + 1, 65, s));
         // element lists: extension, source, key, Galois element (rotation by one slot), output
         std::vector<uint64_t*> h;
         for (uint32_t k = 0; k < kMaxB; k++) h.push_back(ext.p + k * ew);
@@ -343,7 +347,9 @@ bm_status bm_measure_op_costs(bm_context* ctxh, bm_op_costs* out) {
                 if (level == L)
                     out->t_us[BM_OP_MAC_CIRC][L][k] = tm.us(
                         [&] {
-                            return mac_circ(c, L, kMacQ, B, (const uint64_t* const*)(dl + 5 * kMaxB), masks.p, t0.p, s);
+                            // the schedule's form: the convolution over the parts up to 32 parts
+                            return mac_circ(c, L, kMacQ, B, (const uint64_t* const*)(dl + 5 * kMaxB), masks.p, hat.p,
+                                            (const ulonglong2*)ctw.p, t0.p, s);
                         },
                         2, r);
             }

@@ -1,9 +1,11 @@
 """Algorithm 1 in hoisted form on the GPU against the oracle: the basis
 extension of each query's c1 computed once, N_in - 1 rotations taken from it
 (the Galois image of each extended limb is a permutation of its NTT slots),
-the circulant mask products and one rescale per part -- bit-exact against the
-oracle's hoisted expansion, then the same HE-C^3 and compression; end to end,
-the scores equal those of the printed (doubling) form within the tolerance."""
+the circulant mask products (up to 32 parts as a cyclic convolution by
+transforms over the parts, beyond that the direct sum) and one rescale per part
+-- bit-exact against the oracle's hoisted expansion, then the same HE-C^3 and
+compression; end to end, the scores equal those of the printed (doubling) form
+within the tolerance."""
 import numpy as np
 import pytest
 
@@ -28,6 +30,8 @@ def gctx(name):
     ("small4", 16, 4, 3000, 3),       # N_in = 4, three queries in one chunk
     ("small4", 16, 1, 2100, 1),       # N_in = 16, part size 1
     ("small4", 16, 16, 100, 1),       # N_in = 1: no rotations, the query times its mask
+    ("small4", 128, 4, 600, 1),       # N_in = 32: the largest convolution by transforms over the parts
+    ("small4", 128, 2, 300, 1),       # N_in = 64: the direct circulant sum (masks in shared memory)
 ])
 def test_hoisted_match_is_bit_exact(name, m, s, R, nq):
     c = gctx(name)
