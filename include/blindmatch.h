@@ -253,7 +253,9 @@ bm_status bm_gallery_set_expansion(bm_gallery* g, uint32_t mode);
  *                                rotations into one output summed in the extended
  *                                basis Q_l u P and moved down once (one ModDown per
  *                                output instead of one per rotation; double
- *                                hoisting, Bossuat et al., Eurocrypt 2021)
+ *                                hoisting, Bossuat et al., Eurocrypt 2021); the
+ *                                rotate-and-sum over s <= 8 slots then takes a
+ *                                single round of the s - 1 rotations
  * Needs the keys of bm_keygen_ex(..., BM_KEYS_HOISTED).  Plans of the gallery
  * built before the call are dropped; call it before registering the gallery
  * with a server.  BM_E_ARG for unknown flags, or the expansion flag on a gallery

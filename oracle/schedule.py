@@ -195,9 +195,14 @@ def expand_query_hoisted(ev, ct, masks, m, s):
     return out
 
 
-def bsgs_split(s):
+def bsgs_split(s, double=False):
     """(baby, giant) step counts of the hoisted rotate-and-sum over s (a power of
-    two): baby = 2^ceil(log2(s)/2), giant = s / baby."""
+    two): baby = 2^ceil(log2(s)/2), giant = s / baby.  With one ModDown per
+    round output (double=True) a round costs one basis extension, one key-switch
+    product per rotation and one ModDown, so up to s = 8 a single round of s - 1
+    rotations (baby = s, giant = 1) is cheaper than two."""
+    if double and s <= 8:
+        return s, 1
     lb = log2i(s)
     b = 1 << ((lb + 1) // 2)
     return b, s // b
@@ -209,7 +214,7 @@ def rotsum_hoisted(ev, acc, s, double=False):
     acc + sum_{r<b} Rot(acc, r), then giant steps over multiples of b.
     double=True: each round's rotations summed before one ModDown
     (Evaluator.rotate_sum_hoisted)."""
-    b, g = bsgs_split(s)
+    b, g = bsgs_split(s, double)
     for step, count in ((1, b), (b, g)):
         if count > 1:
             rs = [step * k for k in range(1, count)]

@@ -76,8 +76,15 @@ static uint32_t gallery_kind(const Gallery& g) {
            ((g.sched & BM_SCHED_DOUBLE_HOISTED) ? BM_LAYOUT_DOUBLE_HOISTED : 0u);
 }
 
-// baby and giant steps of the hoisted rotate-and-sum over s slots: b = 2^ceil(log2(s)/2)
-static void bsgs_split(uint32_t s, uint32_t& b, uint32_t& g) {
+// baby and giant steps of the hoisted rotate-and-sum over s slots: b = 2^ceil(log2(s)/2);
+// with one ModDown per round output (double hoisting) a single round of s - 1
+// rotations up to s = 8 (a round: one extension, a product per rotation, one ModDown)
+static void bsgs_split(uint32_t s, bool dhoist, uint32_t& b, uint32_t& g) {
+    if (dhoist && s <= 8) {
+        b = s;
+        g = 1;
+        return;
+    }
     const uint32_t lb = ilog2(s);
     b = 1u << ((lb + 1) / 2);
     g = s / b;
@@ -123,7 +130,7 @@ static std::vector<int32_t> schedule_rotations(const Context& c, const Layout& l
         for (uint32_t j = 0; (1u << j) < lo.n_in; j++) r.push_back((int32_t)(part << j));
     if (lo.hrotsum) {
         uint32_t b, g;
-        bsgs_split(part, b, g);
+        bsgs_split(part, lo.dhoist, b, g);
         for (uint32_t k = 1; k < b; k++) r.push_back((int32_t)k);
         for (uint32_t k = 1; k < g; k++) r.push_back((int32_t)(b * k));
     } else {
@@ -435,11 +442,14 @@ bm_status bm_keygen_ex(bm_context* ctxh, uint64_t seed, uint32_t dim, uint32_t p
     };
     std::vector<int32_t> rots = schedule_rotations(c, lo, part_size);
     if (flags & BM_KEYS_HOISTED) {
-        Layout all = lo;                                  // every hoisted form
+        Layout all = lo;                                  // every hoisted form, both rotate-and-sum splits
         all.hoisted = lo.tiled;
         all.hrotsum = true;
         all.hcomp = lo.compress;
-        for (int32_t r : schedule_rotations(c, all, part_size)) rots.push_back(r);
+        for (bool dh : {false, true}) {
+            all.dhoist = dh;
+            for (int32_t r : schedule_rotations(c, all, part_size)) rots.push_back(r);
+        }
     }
     if (flags & BM_KEYS_ENCRYPTED_GALLERY)
         for (uint32_t b = 0; (1u << b) < c.slots; b++)
@@ -1522,7 +1532,7 @@ struct MatchRun {
             if (g.hrotsum) {
                 // sum_{r<part} Rot(acc, r) in two hoisted rounds: baby steps 1..bs-1, giant steps bs*k
                 uint32_t bs, gs;
-                bsgs_split(part, bs, gs);
+                bsgs_split(part, g.dhoist, bs, gs);
                 const uint32_t rounds[2][2] = {{1, bs}, {bs, gs}};
                 for (const auto& rd : rounds) {
                     if (rd[1] <= 1) continue;
@@ -1613,7 +1623,7 @@ static void plan_dims(const Context& c, const SchedView& g, uint32_t n_out, uint
     uint32_t per_src = 0;
     if (g.hrotsum) {
         uint32_t bs, gs;
-        bsgs_split(g.part, bs, gs);
+        bsgs_split(g.part, g.dhoist, bs, gs);
         per_src = std::max(bs, gs) - 1;
     }
     if (g.hcomp) per_src = std::max<uint32_t>(per_src, 1);

@@ -35,8 +35,9 @@ def schedule_rotations(ctx, m, s, hoisted=False):
     if level >= 2:
         rots += [-(1 << t) for t in range(sch.log2i(s))]
     if hoisted:
+        # both splits of the hoisted rotate-and-sum: one round of 1..s-1, or baby and giant steps
         b, g = sch.bsgs_split(s)
-        rots += list(range(1, b)) + [b * k for k in range(1, g)]
+        rots += list(range(1, s)) + [b * k for k in range(1, g)]
         if level >= 2:
             rots += [-r for r in range(1, s)]
     return rots
