@@ -1187,19 +1187,21 @@ cudaError_t mul_plain(const Context& c, uint32_t level, uint32_t B, uint64_t* co
     return cudaGetLastError();
 }
 
-// Largest tile of the HE-C^3 products: BM_MAC_TILE="QxG" (each 1, 2 or 4) caps
-// the queries and groups a thread takes (within the per-kernel limits below).
-static void mac_tile_cap(int& qt, int& gt) {
-    static const int cap = [] {
-        int a = 4, b = 4;
-        if (const char* e = std::getenv("BM_MAC_TILE")) {
-            if (std::sscanf(e, "%dx%d", &a, &b) != 2) a = b = 4;
-        }
+// Tile of the HE-C^3 products for measurements: BM_MAC_TILE="QxG" (each 1, 2 or 4)
+// sets the queries and groups a thread takes (at most 4 pairs for the ct x ct form),
+// in place of the default choice.
+static void mac_tile_env(int& qt, int& gt, int max_pairs) {
+    static const int env = [] {
+        int a = 0, b = 0;
+        if (const char* e = std::getenv("BM_MAC_TILE"))
+            if (std::sscanf(e, "%dx%d", &a, &b) != 2) a = b = 0;
         auto pow2 = [](int v) { return v >= 4 ? 4 : (v >= 2 ? 2 : 1); };
-        return pow2(a) * 8 + pow2(b);
+        return a > 0 && b > 0 ? pow2(a) * 8 + pow2(b) : 0;
     }();
-    qt = std::min(qt, cap / 8);
-    gt = std::min(gt, cap % 8);
+    if (!env) return;
+    qt = env / 8;
+    gt = env % 8;
+    while (qt * gt > max_pairs) (gt > 1 ? gt : qt) /= 2;
 }
 
 // tile shape of the HE-C^3 products: up to 4 queries and 4 (ct x pt) or 2
@@ -1242,7 +1244,7 @@ cudaError_t mac(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uint32
     // the group tiles re-read the query words from L2), else up to 2 x 2 / 1 x 4
     int qt = Q >= 4 ? 4 : (Q >= 2 ? 2 : 1);
     int gt = qt == 4 ? 1 : (qt == 2 ? (G >= 2 ? 2 : 1) : (G >= 3 ? 4 : (G == 2 ? 2 : 1)));
-    mac_tile_cap(qt, gt);
+    mac_tile_env(qt, gt, 8);
     switch (qt * 8 + gt) {
         case 4 * 8 + 4:
         case 4 * 8 + 2: return launch_mac<4, 2>(c, level, Q, G, n_in, T, P, acc, s);
@@ -1264,7 +1266,7 @@ cudaError_t mac_ct(const Context& c, uint32_t level, uint32_t Q, uint32_t G, uin
                  lim * (double)Q * G * (4.0 * kProdMul * n_in + 3.0 * kRedcMul));
     // at most 4 (query, group) triples of sums a thread
     int qt = Q >= 4 ? 4 : (Q >= 2 ? 2 : 1), gt = G >= 2 && qt < 4 ? 2 : 1;
-    mac_tile_cap(qt, gt);
+    mac_tile_env(qt, gt, 4);
     switch (qt * 8 + gt) {
         case 4 * 8 + 2:
         case 4 * 8 + 1: return launch_mac_ct<4, 1>(c, level, Q, G, n_in, T, C, A, B, s);
