@@ -672,6 +672,67 @@ class Evaluator:
                 c1[j] = add_mod(c1[j], d1[j], ctx.q[j])
         return Ciphertext(np.stack(c0), np.stack(c1), lvl, base.scale)
 
+    def hoisted_products_ext(self, ct, rs):
+        """The rotations of ct by every r in rs kept in the extended basis Q_l u P,
+        before ModDown, NTT form: {r: E_r} with E_r[comp] of shape (|Q_l u P|, N).
+        E_r = (sum_d sigma_k(ext_d) * key_k,d) + (P * sigma_k(c0) on the q-limbs of
+        the first component), so that ModDown(E_r) is Rot(ct, r) of rotate_hoisted;
+        r = 0 gives P * ct on the q-limbs and 0 on the special limbs.  One basis
+        extension of c1 serves every r."""
+        ctx, lvl = self.ctx, ct.level
+        ext_idx = ctx.ext_index(lvl)
+        ext = modup_ntt(ctx, ct.c1, lvl)
+        out = {}
+        for r in rs:
+            E = np.zeros((2, len(ext_idx), ctx.n), dtype=np.uint64)
+            if r % ctx.slots == 0:
+                for jj, gi in enumerate(ext_idx[: lvl + 1]):
+                    t = ctx.primes[gi]
+                    E[0, jj] = ctx.ntt(scalar_mul(ct.c0[gi], ctx.P % t, t), gi)
+                    E[1, jj] = ctx.ntt(scalar_mul(ct.c1[gi], ctx.P % t, t), gi)
+                out[r] = E
+                continue
+            k = ctx.galois_left(r)
+            key = self.keys[k]
+            for d, f_d in ext.items():
+                for jj, gi in enumerate(ext_idx):
+                    t = ctx.primes[gi]
+                    fk = ctx.ntt(automorphism(ctx.intt(f_d[jj], gi), ctx.log_n, k, t), gi)
+                    for comp in range(2):
+                        E[comp, jj] = add_mod(E[comp, jj], pointwise_mul(fk, key.ntt_data[d, comp, gi], t), t)
+            for jj, gi in enumerate(ext_idx[: lvl + 1]):
+                t = ctx.primes[gi]
+                c0k = automorphism(ct.c0[gi], ctx.log_n, k, t)
+                E[0, jj] = add_mod(E[0, jj], ctx.ntt(scalar_mul(c0k, ctx.P % t, t), gi), t)
+            out[r] = E
+        return out
+
+    def expand_query_fused(self, ct, n_in, s, mask_slots):
+        """Algorithm 1 with its key switches and rescale fused: E_j =
+        hoisted_products_ext(ct, j*s) for j < n_in, the masks mask_slots(i) encoded
+        at scale q_L with their integer coefficients reduced on every prime of
+        Q_L u P, e_i = sum_j E_j * mask_((i-j) mod n_in) there, and
+        T_i = moddown_rescale(e_i): the parts of Algorithm 1 at level L - 1."""
+        ctx, L = self.ctx, ct.level
+        ext_idx = ctx.ext_index(L)
+        E = self.hoisted_products_ext(ct, [s * j for j in range(n_in)])
+        masks = []
+        for i in range(n_in):
+            c = ctx.encode_int(mask_slots(i), ctx.q[L])
+            masks.append([ctx.ntt(signed_to_mod(c, ctx.primes[gi]), gi) for gi in ext_idx])
+        outs = []
+        for i in range(n_in):
+            e = np.zeros((2, len(ext_idx), ctx.n), dtype=np.uint64)
+            for j in range(n_in):
+                M = masks[(i - j) % n_in]
+                for jj, gi in enumerate(ext_idx):
+                    t = ctx.primes[gi]
+                    for comp in range(2):
+                        e[comp, jj] = add_mod(e[comp, jj], pointwise_mul(E[s * j][comp, jj], M[jj], t), t)
+            c0, c1 = moddown_rescale(ctx, e, L)
+            outs.append(Ciphertext(c0, c1, L - 1, ct.scale))
+        return outs
+
     def apply_galois(self, ct, k):
         ctx, lvl = self.ctx, ct.level
         key = self.keys[k]
@@ -712,6 +773,29 @@ def moddown(ctx, acc, level):
             conv = bconv(xp, ctx.p, qj)
             p_inv = pow(ctx.P % qj, -1, qj)
             res[j] = scalar_mul(sub_mod(x[j], conv, qj), p_inv, qj)
+        out.append(res)
+    return out[0], out[1]
+
+
+def moddown_rescale(ctx, e, level):
+    """ModDown and Rescale in one step: e[comp] (limbs of Q_level u P, NTT form) divided
+    by S = q_level * P with the special set {q_level} u P, out_j = (x_j - Conv_S->q_j([x]_S))
+    * S^{-1} mod q_j for j < level (coefficient form).  The same fast base conversion
+    as moddown; e / S carries the message of e / P rescaled by q_level."""
+    ext = ctx.ext_index(level)
+    spec = [level] + list(range(level + 1, level + 1 + ctx.alpha))          # positions in ext
+    sp_primes = [ctx.primes[ext[j]] for j in spec]
+    S = math.prod(sp_primes)
+    out = []
+    for comp in range(2):
+        x = np.stack([ctx.intt(e[comp, jj], gi) for jj, gi in enumerate(ext)])
+        xs = np.stack([x[j] for j in spec])
+        res = _u64((level, ctx.n))
+        for j in range(level):
+            qj = ctx.q[j]
+            conv = bconv(xs, sp_primes, qj)
+            s_inv = pow(S % qj, -1, qj)
+            res[j] = scalar_mul(sub_mod(x[j], conv, qj), s_inv, qj)
         out.append(res)
     return out[0], out[1]
 

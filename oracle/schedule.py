@@ -195,6 +195,19 @@ def expand_query_hoisted(ev, ct, masks, m, s):
     return out
 
 
+def expand_query_fused(ev, ct, m, s):
+    """Algorithm 1 with its key switches and rescale fused (same parts as
+    expand_query; the bits differ by the roundings saved): the N_in - 1 rotations
+    of the query stay in the extended basis Q_L u P before ModDown, the circulant
+    mask products run there, and each part is divided once by q_L * P
+    (Evaluator.expand_query_fused)."""
+    return ev.expand_query_fused(ct, m // s, s, lambda i: alg1_mask_slots(m, s, i, ct_slots(ev)))
+
+
+def ct_slots(ev):
+    return ev.ctx.slots
+
+
 def bsgs_split(s, double=False):
     """(baby, giant) step counts of the hoisted rotate-and-sum over s (a power of
     two): baby = 2^ceil(log2(s)/2), giant = s / baby.  With one ModDown per
@@ -302,10 +315,14 @@ def match(ev, query_cts, gallery_pts, masks, mask_m, m, s, expanded=False,
     """Full server-side match for one query.
 
     query_cts: [ct] (tiled, run through Algorithm 1) or the N_in client-expanded cts.
+    hoisted: False (the printed doubling order), True (hoisted rotations) or
+    "fused" (hoisted rotations with their ModDown and the rescale fused).
     gallery_pts[g][i]: plaintext of group g, part i.
     Returns (outputs, packed): the score ciphertexts and whether they are packed."""
     if expanded:
         cu = query_cts
+    elif hoisted == "fused":
+        cu = expand_query_fused(ev, query_cts[0], m, s)
     elif hoisted:
         cu = expand_query_hoisted(ev, query_cts[0], masks, m, s)
     else:
@@ -334,6 +351,7 @@ class CountingEvaluator:
 
     def __init__(self):
         self.ops = []
+        self.ctx = None
 
     def _rec(self, op, level):
         self.ops.append((op, level))
@@ -378,6 +396,17 @@ class CountingEvaluator:
         for r in rs:
             self._rec("RotH", ct.level)
         return [SymCt(ct.level) for _ in rs]
+
+    def expand_query_fused(self, ct, n_in, s, mask_slots):
+        L = ct.level
+        if n_in > 1:
+            self._rec("ModUp", L)
+        for _ in range(n_in - 1):
+            self._rec("IPH", L)
+        self._rec("CircExt", L)
+        for _ in range(n_in):
+            self._rec("ModDownRes", L)
+        return [SymCt(L - 1) for _ in range(n_in)]
 
     def rotate_sum_hoisted(self, base, terms):
         seen = set()

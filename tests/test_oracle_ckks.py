@@ -389,3 +389,55 @@ def test_double_hoisted_tail_scores(m, s, R):
     dec = [ckks.decrypt_decode(ctx, o, sk).real for o in outs]
     got = np.array([dec[o][slot] for o, slot, _ in (sch.identity_slot(i, s, S, packed) for i in range(R))])
     assert np.abs(got - ref).max() < 1e-5
+
+
+def test_moddown_rescale_is_the_floor_up_to_the_conversion_error():
+    """Big-integer pin of the fused ModDown + Rescale: for the integer E (CRT over
+    Q_L u P) of each coefficient and S = q_L * P, the output is floor(E / S) - u
+    with the same u in {0, ..., |S| - 1} on every target prime (the fast base
+    conversion returns [E]_S + u S)."""
+    ctx = ckks.Context("small4")
+    L = ctx.L
+    ext = ctx.ext_index(L)
+    rng = np.random.default_rng(21)
+    e = np.stack([np.stack([rng.integers(0, ctx.primes[gi], ctx.n, dtype=np.uint64) for gi in ext])
+                  for _ in range(2)])
+    c0, c1 = ckks.moddown_rescale(ctx, e, L)
+    prims = [ctx.primes[gi] for gi in ext]
+    S = ctx.q[L] * ctx.P
+    spec = 1 + len(ctx.p)
+    for comp, out in enumerate((c0, c1)):
+        x = np.stack([ctx.intt(e[comp, jj], gi) for jj, gi in enumerate(ext)])
+        Q = math.prod(prims)
+        E = [v % Q for v in ctx.crt(x, prims)]
+        fl = [v // S for v in E]
+        for k in range(0, ctx.n, 97):
+            us = {(fl[k] - int(out[j][k])) % ctx.q[j] for j in range(L)}
+            assert len(us) == 1 and us.pop() < spec, (comp, k)
+
+
+@pytest.mark.parametrize("m,s", [(16, 4), (128, 16), (16, 1)])
+def test_fused_expansion_gives_algorithm1_outputs(m, s):
+    """Algorithm 1 with the key switches and the rescale fused decrypts to the same
+    parts as the printed form, and differs from the hoisted form by a small integer
+    polynomial -- the same in every limb -- bounded by the roundings moved:
+    3 * N_in * N * max|mask| / q_L + 4."""
+    ctx, sk, pk, ev = _setup("small4", m, s, 1, extra_rots=[j * s for j in range(1, m // s)])
+    S, L, n_in = ctx.slots, ctx.L, m // s
+    q = wl.queries(wl.gallery(3, m), 1)[0][0]
+    ct = ckks.encrypt(ctx, pk, ctx.encode(sch.tiled_query_slots(q, S), ctx.scale, L), 4, 0)
+    masks = [ctx.encode(sch.alg1_mask_slots(m, s, i, S), ctx.q[L], L) for i in range(n_in)]
+    fused = sch.expand_query_fused(ev, ct, m, s)
+    hoisted = sch.expand_query_hoisted(ev, ct, masks, m, s)
+    mmax = max(int(np.abs(ctx.encode_int(sch.alg1_mask_slots(m, s, i, S), ctx.q[L])).max()) for i in range(n_in))
+    bound = 3 * n_in * ctx.n * mmax // ctx.q[L] + 4
+    for i in range(n_in):
+        assert fused[i].level == L - 1 and fused[i].scale == ctx.scale
+        d = ckks.decrypt_decode(ctx, fused[i], sk).real
+        assert np.abs(d - np.array(sch.expanded_query_slots(q, s, i, S))).max() < 1e-6, i
+        for comp in ("c0", "c1"):
+            diffs = [_centred(getattr(fused[i], comp)[j].astype(object) - getattr(hoisted[i], comp)[j].astype(object),
+                              ctx.q[j]) for j in range(L)]
+            for j in range(1, L):
+                assert np.array_equal(diffs[j], diffs[0]), (i, comp, j)
+            assert np.abs(diffs[0]).max() <= bound, (i, comp, int(np.abs(diffs[0]).max()), bound)
