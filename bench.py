@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--auto-part", action="store_true",
                     help="serving: each gallery's part size chosen by the cost model (bm_choose_part)")
     ap.add_argument("--no-tune", action="store_true", help="skip the rotation kernel-shape tuner")
-    ap.add_argument("--expansion", default="hoisted", choices=["doubling", "hoisted", "auto"],
+    ap.add_argument("--expansion", default="fused", choices=["doubling", "hoisted", "fused", "auto"],
                     help="form of Algorithm 1: the printed doubling order or the hoisted sum "
                          "(auto: serving picks per gallery by the cost model)")
     ap.add_argument("--tail", default="double", choices=["printed", "hoisted", "double"],
@@ -268,7 +268,7 @@ def run_serving(args):
     expansions = {}
     for gi, (name, R, m, s) in enumerate(SERVE_GALLERIES):
         if args.expansion == "auto":
-            forms = [(e, t) for e in ("doubling", "hoisted") for t in ("printed", "hoisted", "double")]
+            forms = [(e, t) for e in ("doubling", "hoisted", "fused") for t in ("printed", "hoisted", "double")]
         else:
             forms = [(args.expansion, args.tail)]
         if costs is not None:
@@ -282,7 +282,8 @@ def run_serving(args):
         flags, _ = sched_flags(bm, *form)
         parts[name] = s
         expansions[name] = "+".join(x for x, on in (("hoisted-expansion", flags & 1), ("hoisted-rotsum", flags & 2),
-                                                    ("hoisted-compression", flags & 4), ("double-hoisted", flags & 8))
+                                                    ("hoisted-compression", flags & 4), ("double-hoisted", flags & 8),
+                                                    ("fused-expansion", flags & 16))
                                     if on) or "printed"
         if (m, s) not in keys:
             keys[(m, s)] = bm.bm_keygen_ex(ctx, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
@@ -357,13 +358,16 @@ def run_serving(args):
 
 def sched_flags(bm, expansion, tail):
     """(gallery schedule flags, model layout flags) of the chosen forms."""
-    f = bm.BM_SCHED_HOISTED_EXPANSION if expansion == "hoisted" else 0
+    f = bm.BM_SCHED_HOISTED_EXPANSION if expansion in ("hoisted", "fused") else 0
+    if expansion == "fused":
+        f |= bm.BM_SCHED_FUSED_EXPANSION
     if tail in ("hoisted", "double"):
         f |= bm.BM_SCHED_HOISTED_ROTSUM | bm.BM_SCHED_HOISTED_COMPRESSION
     if tail == "double":
         f |= bm.BM_SCHED_DOUBLE_HOISTED
     lay = ((bm.BM_LAYOUT_HOISTED if f & 1 else 0) | (bm.BM_LAYOUT_HOISTED_ROTSUM if f & 2 else 0)
-           | (bm.BM_LAYOUT_HOISTED_COMPRESSION if f & 4 else 0) | (bm.BM_LAYOUT_DOUBLE_HOISTED if f & 8 else 0))
+           | (bm.BM_LAYOUT_HOISTED_COMPRESSION if f & 4 else 0) | (bm.BM_LAYOUT_DOUBLE_HOISTED if f & 8 else 0)
+           | (bm.BM_LAYOUT_FUSED_EXPANSION if f & 16 else 0))
     return f, lay
 
 

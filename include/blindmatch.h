@@ -232,7 +232,8 @@ bm_status bm_gallery_info(const bm_gallery* g, uint32_t* encrypted, uint32_t* pa
  * Algorithm 1 (client-expanded queries). */
 enum {
     BM_EXPAND_DOUBLING = 0,
-    BM_EXPAND_HOISTED = 1
+    BM_EXPAND_HOISTED = 1,
+    BM_EXPAND_FUSED = 2      /* hoisted, with the key switches and the rescale fused (below) */
 };
 bm_status bm_gallery_set_expansion(bm_gallery* g, uint32_t mode);
 
@@ -249,6 +250,12 @@ bm_status bm_gallery_set_expansion(bm_gallery* g, uint32_t mode);
  *  BM_SCHED_HOISTED_COMPRESSION  the compression in its linear form, every group
  *                                r > 0 of a pack rotated right by r in one round of
  *                                hoisted rotations (a radix-2 tree otherwise)
+ *  BM_SCHED_FUSED_EXPANSION      with the hoisted expansion: the N_in - 1 rotations
+ *                                kept in the extended basis Q_L u P (before ModDown),
+ *                                the circulant mask products there, and each part
+ *                                divided once by q_L * P -- one fused ModDown and
+ *                                Rescale per part instead of a ModDown per rotation
+ *                                and a rescale per part (2 <= N_in <= 32)
  *  BM_SCHED_DOUBLE_HOISTED       with either of the two above: each round's
  *                                rotations into one output summed in the extended
  *                                basis Q_l u P and moved down once (one ModDown per
@@ -264,7 +271,8 @@ enum {
     BM_SCHED_HOISTED_EXPANSION = 1,
     BM_SCHED_HOISTED_ROTSUM = 2,
     BM_SCHED_HOISTED_COMPRESSION = 4,
-    BM_SCHED_DOUBLE_HOISTED = 8
+    BM_SCHED_DOUBLE_HOISTED = 8,
+    BM_SCHED_FUSED_EXPANSION = 16
 };
 bm_status bm_gallery_set_schedule(bm_gallery* g, uint32_t flags);
 void bm_gallery_destroy(bm_gallery* g);
@@ -501,8 +509,10 @@ typedef struct bm_op_costs {
 #define BM_LAYOUT_HOISTED 0x200u
 #define BM_LAYOUT_HOISTED_ROTSUM 0x400u
 #define BM_LAYOUT_HOISTED_COMPRESSION 0x800u
-/* ... and BM_LAYOUT_DOUBLE_HOISTED for BM_SCHED_DOUBLE_HOISTED. */
+/* ... and BM_LAYOUT_DOUBLE_HOISTED for BM_SCHED_DOUBLE_HOISTED, BM_LAYOUT_FUSED_EXPANSION for
+ * BM_SCHED_FUSED_EXPANSION. */
 #define BM_LAYOUT_DOUBLE_HOISTED 0x1000u
+#define BM_LAYOUT_FUSED_EXPANSION 0x2000u
 
 /* Host only (no device needed): the launches of the match of `n_queries`
  * queries against a gallery of n_ids identities in (dim, part_size, packing) under

@@ -59,6 +59,7 @@ struct Layout {
     bool hoisted;                           // Algorithm 1 by hoisted rotations
     bool hrotsum, hcomp;                    // rotate-and-sum / compression by hoisted rounds
     bool dhoist;                            // ... with one ModDown per round output
+    bool fused;                             // hoisted Algorithm 1 with ModDown and Rescale fused
 };
 
 // Scale of the score ciphertexts: 2^log_scale with a plaintext gallery (every
@@ -73,7 +74,8 @@ static uint32_t gallery_kind(const Gallery& g) {
            ((g.sched & BM_SCHED_HOISTED_EXPANSION) ? BM_LAYOUT_HOISTED : 0u) |
            ((g.sched & BM_SCHED_HOISTED_ROTSUM) ? BM_LAYOUT_HOISTED_ROTSUM : 0u) |
            ((g.sched & BM_SCHED_HOISTED_COMPRESSION) ? BM_LAYOUT_HOISTED_COMPRESSION : 0u) |
-           ((g.sched & BM_SCHED_DOUBLE_HOISTED) ? BM_LAYOUT_DOUBLE_HOISTED : 0u);
+           ((g.sched & BM_SCHED_DOUBLE_HOISTED) ? BM_LAYOUT_DOUBLE_HOISTED : 0u) |
+           ((g.sched & BM_SCHED_FUSED_EXPANSION) ? BM_LAYOUT_FUSED_EXPANSION : 0u);
 }
 
 // baby and giant steps of the hoisted rotate-and-sum over s slots: b = 2^ceil(log2(s)/2);
@@ -94,12 +96,14 @@ static void bsgs_split(uint32_t s, bool dhoist, uint32_t& b, uint32_t& g) {
 static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uint32_t part, Layout& lo,
                              uint32_t kind = BM_PACK_REAL) {
     const uint32_t packing = kind & ~(BM_LAYOUT_ENCRYPTED | BM_LAYOUT_HOISTED | BM_LAYOUT_HOISTED_ROTSUM |
-                                      BM_LAYOUT_HOISTED_COMPRESSION | BM_LAYOUT_DOUBLE_HOISTED);
+                                      BM_LAYOUT_HOISTED_COMPRESSION | BM_LAYOUT_DOUBLE_HOISTED |
+                                      BM_LAYOUT_FUSED_EXPANSION);
     lo.encrypted = (kind & BM_LAYOUT_ENCRYPTED) != 0;
     lo.hoisted = (kind & BM_LAYOUT_HOISTED) != 0;
     lo.hrotsum = (kind & BM_LAYOUT_HOISTED_ROTSUM) != 0;
     lo.hcomp = (kind & BM_LAYOUT_HOISTED_COMPRESSION) != 0;
     lo.dhoist = (kind & BM_LAYOUT_DOUBLE_HOISTED) != 0;
+    lo.fused = (kind & BM_LAYOUT_FUSED_EXPANSION) != 0;
     if (!is_pow2(dim) || !is_pow2(part) || part > dim || dim > c.slots)
         return fail(BM_E_DIM, "dim and part size must be powers of two with part <= dim <= N/2");
     if (packing != BM_PACK_REAL && packing != BM_PACK_COMPLEX) return fail(BM_E_ARG, "unknown slot packing");
@@ -117,6 +121,8 @@ static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uin
     if (!lo.tiled) lo.hoisted = false;      // no Algorithm 1 on the server
     if (!lo.compress) lo.hcomp = false;
     if (!lo.hrotsum && !lo.hcomp) lo.dhoist = false;
+    if (lo.fused) lo.hoisted = lo.tiled;    // the fused form is a form of the hoisted expansion
+    if (!lo.hoisted || lo.n_in < 2 || lo.n_in > kMaxCircParts || !ks_mdr_supported(c)) lo.fused = false;
     lo.n_out = lo.compress ? (lo.groups + part - 1) / part : lo.groups;
     return BM_OK;
 }
@@ -326,6 +332,7 @@ void context_free(bm_context* ctx) {
     ctx->c.plans.clear();
     if (ctx->c.d_twiddles) cudaFree(ctx->c.d_twiddles);
     if (ctx->c.d_ksc) cudaFree(ctx->c.d_ksc);
+    if (ctx->c.d_ksc_mdr) cudaFree(ctx->c.d_ksc_mdr);
     if (ctx->c.d_qlinv) cudaFree(ctx->c.d_qlinv);
     if (ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
     delete ctx;
@@ -568,6 +575,8 @@ bm::Gallery::~Gallery() {
     if (d_masks) cudaFree(d_masks);
     if (d_masks_hat) cudaFree(d_masks_hat);
     if (d_circ_tw) cudaFree(d_circ_tw);
+    if (d_masks_hat_ext) cudaFree(d_masks_hat_ext);
+    if (d_circ_tw_ext) cudaFree(d_circ_tw_ext);
     if (d_cmask) cudaFree(d_cmask);
 }
 bm::Ciphertext::~Ciphertext() {
@@ -592,10 +601,11 @@ static bm_status gallery_alloc(Context& c, const Layout& lo, uint64_t n_ids, uin
     Gallery& g = gh->g;
     g.ctx = &c;
     g.packing = packing & ~(BM_LAYOUT_ENCRYPTED | BM_LAYOUT_HOISTED | BM_LAYOUT_HOISTED_ROTSUM |
-                            BM_LAYOUT_HOISTED_COMPRESSION | BM_LAYOUT_DOUBLE_HOISTED);
+                            BM_LAYOUT_HOISTED_COMPRESSION | BM_LAYOUT_DOUBLE_HOISTED | BM_LAYOUT_FUSED_EXPANSION);
     g.encrypted = lo.encrypted;
     g.sched = (lo.hoisted ? BM_SCHED_HOISTED_EXPANSION : 0u) | (lo.hrotsum ? BM_SCHED_HOISTED_ROTSUM : 0u) |
-              (lo.hcomp ? BM_SCHED_HOISTED_COMPRESSION : 0u) | (lo.dhoist ? BM_SCHED_DOUBLE_HOISTED : 0u);
+              (lo.hcomp ? BM_SCHED_HOISTED_COMPRESSION : 0u) | (lo.dhoist ? BM_SCHED_DOUBLE_HOISTED : 0u) |
+              (lo.fused ? BM_SCHED_FUSED_EXPANSION : 0u);
     g.id = c.next_id++;
     g.n_ids = n_ids;
     g.dim = dim;
@@ -612,6 +622,11 @@ static bm_status gallery_alloc(Context& c, const Layout& lo, uint64_t n_ids, uin
     if (e == cudaSuccess && lo.tiled && lo.n_in >= 2 && lo.n_in <= kMaxCircParts) {
         e = cudaMalloc(&g.d_masks_hat, (size_t)lo.n_in * (c.L + 1) * n * 8);
         if (e == cudaSuccess) e = cudaMalloc(&g.d_circ_tw, (size_t)lo.n_in * (c.L + 1) * sizeof(ulonglong2));
+        if (e == cudaSuccess && ks_mdr_supported(c)) {
+            const size_t nlx = c.L + 1 + c.alpha;
+            e = cudaMalloc(&g.d_masks_hat_ext, (size_t)lo.n_in * nlx * n * 8);
+            if (e == cudaSuccess) e = cudaMalloc(&g.d_circ_tw_ext, (size_t)lo.n_in * nlx * sizeof(ulonglong2));
+        }
     }
     if (e == cudaSuccess && lo.compress) e = cudaMalloc(&g.d_cmask, (size_t)lo.level * n * 8);
     if (e != cudaSuccess) {
@@ -632,6 +647,23 @@ static bm_status encode_to_device(Context& c, const std::vector<double>& z, doub
     return BM_OK;
 }
 
+// the masks' side of hoisted Algorithm 1 as a convolution over the parts
+// (mac_circ), once the masks are on the device
+static cudaError_t gallery_circ(Context& c, Gallery& g) {
+    if (!g.d_masks_hat) return cudaSuccess;
+    cudaError_t e = circ_prepare(c, g.n_in, c.L + 1, g.d_masks, g.d_masks_hat, g.d_circ_tw, c.stream);
+    if (e != cudaSuccess || !g.d_masks_hat_ext) return e;
+    // the fused Algorithm 1: masks and their transform on Q_L u P (the buffer of the
+    // extended masks is reused for nothing else: it is freed after the transform)
+    const uint32_t nlx = c.L + 1 + c.alpha;
+    uint64_t* ext = nullptr;
+    e = cudaMalloc(&ext, (size_t)g.n_in * nlx * c.n * 8);
+    if (e == cudaSuccess) e = masks_extend(c, g.n_in, g.d_masks, ext, c.stream);
+    if (e == cudaSuccess) e = circ_prepare(c, g.n_in, nlx, ext, g.d_masks_hat_ext, g.d_circ_tw_ext, c.stream);
+    if (ext) cudaFree(ext);
+    return e;
+}
+
 // The Algorithm-1 masks (mask_i[k] = 1 iff floor((k mod dim)/part) = i, at the top
 // level, scale q_L) and the compression mask (M[k] = 1 iff k = 0 mod part, scale
 // of the prime its rescale drops) of a gallery.
@@ -644,7 +676,7 @@ static bm_status encode_gallery_masks(Context& c, const Layout& lo, uint32_t dim
             BM_TRY(encode_to_device(c, z, (double)c.primes[c.L], c.L, g.d_masks + (size_t)i * (c.L + 1) * n));
         }
         if (g.d_masks_hat)
-            BM_CUDA_TRY(circ_prepare(c, g.n_in, g.d_masks, g.d_masks_hat, g.d_circ_tw, c.stream));
+            BM_CUDA_TRY(gallery_circ(c, g));
     }
     if (lo.compress) {
         for (size_t k = 0; k < S; k++) z[k] = (k % part == 0) ? 1.0 : 0.0;
@@ -653,12 +685,6 @@ static bm_status encode_gallery_masks(Context& c, const Layout& lo, uint32_t dim
     return BM_OK;
 }
 
-// the masks' side of hoisted Algorithm 1 as a convolution over the parts
-// (mac_circ), once the masks are on the device
-static cudaError_t gallery_circ(Context& c, Gallery& g) {
-    if (!g.d_masks_hat) return cudaSuccess;
-    return circ_prepare(c, g.n_in, g.d_masks, g.d_masks_hat, g.d_circ_tw, c.stream);
-}
 
 }  // namespace bm
 
@@ -993,11 +1019,13 @@ bm_status bm_gallery_import_encrypted(bm_context* ctxh, const uint64_t* cts, con
 bm_status bm_gallery_set_schedule(bm_gallery* gh, uint32_t flags) {
     if (!gh) return fail(BM_E_ARG, "null gallery");
     const uint32_t all = BM_SCHED_HOISTED_EXPANSION | BM_SCHED_HOISTED_ROTSUM | BM_SCHED_HOISTED_COMPRESSION |
-                         BM_SCHED_DOUBLE_HOISTED;
+                         BM_SCHED_DOUBLE_HOISTED | BM_SCHED_FUSED_EXPANSION;
     if (flags & ~all) return fail(BM_E_ARG, "unknown schedule flags");
     Gallery& g = gh->g;
     if ((flags & BM_SCHED_HOISTED_EXPANSION) && !g.tiled)
         return fail(BM_E_ARG, "the gallery's queries arrive expanded (no Algorithm 1 on the server)");
+    if ((flags & BM_SCHED_FUSED_EXPANSION) && (!(flags & BM_SCHED_HOISTED_EXPANSION) || !g.d_masks_hat_ext))
+        return fail(BM_E_ARG, "the fused expansion needs the hoisted expansion and 2..32 parts");
     if (g.sched != flags) {
         drop_plans(*g.ctx, g.id);
         g.sched = flags;
@@ -1007,9 +1035,13 @@ bm_status bm_gallery_set_schedule(bm_gallery* gh, uint32_t flags) {
 
 bm_status bm_gallery_set_expansion(bm_gallery* gh, uint32_t mode) {
     if (!gh) return fail(BM_E_ARG, "null gallery");
-    if (mode != BM_EXPAND_DOUBLING && mode != BM_EXPAND_HOISTED) return fail(BM_E_ARG, "unknown expansion");
-    const uint32_t rest = gh->g.sched & ~(uint32_t)BM_SCHED_HOISTED_EXPANSION;
-    return bm_gallery_set_schedule(gh, rest | (mode == BM_EXPAND_HOISTED ? BM_SCHED_HOISTED_EXPANSION : 0u));
+    if (mode != BM_EXPAND_DOUBLING && mode != BM_EXPAND_HOISTED && mode != BM_EXPAND_FUSED)
+        return fail(BM_E_ARG, "unknown expansion");
+    const uint32_t rest = gh->g.sched & ~(uint32_t)(BM_SCHED_HOISTED_EXPANSION | BM_SCHED_FUSED_EXPANSION);
+    const uint32_t form = mode == BM_EXPAND_FUSED ? BM_SCHED_HOISTED_EXPANSION | BM_SCHED_FUSED_EXPANSION
+                          : mode == BM_EXPAND_HOISTED ? BM_SCHED_HOISTED_EXPANSION
+                                                      : 0u;
+    return bm_gallery_set_schedule(gh, rest | form);
 }
 
 bm_status bm_gallery_info(const bm_gallery* gh, uint32_t* encrypted, uint32_t* packing) {
@@ -1217,10 +1249,13 @@ struct SchedView {
     uint32_t n_in = 0, part = 0, level = 0, groups = 0;
     bool tiled = true, compress = true, encrypted = false, hoisted = false, hrotsum = false, hcomp = false;
     bool dhoist = false;                   // hoisted rounds with one ModDown per output
+    bool fused = false;                    // hoisted Algorithm 1 with ModDown and Rescale fused
     const uint64_t* d_pts = nullptr;
     const uint64_t* d_masks = nullptr;
     const uint64_t* d_masks_hat = nullptr;
     const ulonglong2* d_circ_tw = nullptr;
+    const uint64_t* d_masks_hat_ext = nullptr;
+    const ulonglong2* d_circ_tw_ext = nullptr;
     const uint64_t* d_cmask = nullptr;
 };
 
@@ -1237,10 +1272,13 @@ static SchedView view_of(const Gallery& g) {
     v.hrotsum = (g.sched & BM_SCHED_HOISTED_ROTSUM) != 0;
     v.hcomp = g.compress && (g.sched & BM_SCHED_HOISTED_COMPRESSION);
     v.dhoist = (v.hrotsum || v.hcomp) && (g.sched & BM_SCHED_DOUBLE_HOISTED);
+    v.fused = v.hoisted && (g.sched & BM_SCHED_FUSED_EXPANSION) && g.d_masks_hat_ext;
     v.d_pts = g.d_pts;
     v.d_masks = g.d_masks;
     v.d_masks_hat = g.d_masks_hat;
     v.d_circ_tw = g.d_circ_tw;
+    v.d_masks_hat_ext = g.d_masks_hat_ext;
+    v.d_circ_tw_ext = g.d_circ_tw_ext;
     v.d_cmask = g.d_cmask;
     return v;
 }
@@ -1258,6 +1296,7 @@ static SchedView view_of(const Layout& lo, uint32_t part) {
     v.hrotsum = lo.hrotsum;
     v.hcomp = lo.hcomp;
     v.dhoist = lo.dhoist;
+    v.fused = lo.fused;
     return v;
 }
 
@@ -1461,7 +1500,66 @@ struct MatchRun {
         if (pl.arena.live) check(ntt_forward(c, packed(c, pl.qin, Q * pl.ncts * 2, c.L + 1), s));
         // Algorithm 1, hoisted form: T_i = Res(sum_j Rot(ct, j*part) * mask_((i-j) mod N_in)),
         // the N_in - 1 rotations of each query sharing one basis extension; queries in chunks of pl.qe
-        if (g.tiled && g.hoisted) {
+        if (g.tiled && g.hoisted && g.fused) {
+            // fused form: E_j = the rotation by j parts before ModDown (sums left in NTT
+            // form on Q_L u P, P * sigma(c0) included), E_0 = P * query; e_i = sum_j E_j *
+            // mask_((i-j) mod N_in) on Q_L u P; T_i = e_i / (q_L P) (ModDown and Rescale fused)
+            const size_t ew = ks_ext_words(c, c.L);
+            const uint32_t nlx = c.L + 1 + c.alpha;
+            const size_t xw = (size_t)2 * nlx * c.n;             // one sum on Q_L u P
+            for (uint32_t qb = 0; qb < Q; qb += pl.qe) {
+                const uint32_t nq = std::min(pl.qe, Q - qb);
+                uint64_t* E0 = pl.R + (size_t)pl.qe * (n_in - 1) * xw;       // after the rotated sums
+                std::vector<uint64_t*> qs, ext_of, src, keys, gal, off{reinterpret_cast<uint64_t*>((uintptr_t)0)}, R, outs;
+                for (uint32_t q = 0; q < nq; q++) qs.push_back(pl.qin + (size_t)(qb + q) * cw(c.L));
+                modup_batch(c.L, qs, pl.ext);
+                for (uint32_t q = 0; q < nq; q++)
+                    for (uint32_t j = 1; j < n_in; j++) {
+                        ext_of.push_back(pl.ext + (size_t)q * ew);
+                        src.push_back(qs[q]);
+                        keys.push_back(const_cast<uint64_t*>(key((int32_t)(part * j))));
+                        gal.push_back(reinterpret_cast<uint64_t*>((uintptr_t)galois_of(c, (int32_t)(part * j))));
+                        off.push_back(reinterpret_cast<uint64_t*>((uintptr_t)ext_of.size()));
+                    }
+                auto de = pl.arena.list(ext_of);
+                auto ds = pl.arena.list(src);
+                auto dk = pl.arena.list(keys);
+                auto dg = pl.arena.list(gal);
+                auto doff = pl.arena.list(off);
+                auto dq = pl.arena.list(qs);
+                const uint32_t nt = (uint32_t)ext_of.size();
+                for (uint32_t t0 = 0; t0 < nt; t0 += ksb) {
+                    const uint32_t T = std::min(ksb, nt - t0);
+                    record(BM_OP_IP_SUM, c.L, T, 0, T);
+                    if (pl.arena.live)
+                        check(ks_ipsum_hoisted(c, c.L, T, (const uint64_t*)(doff + t0), T, (const uint64_t* const*)de,
+                                               (const uint64_t* const*)ds, (const uint64_t* const*)dk,
+                                               (const uint64_t*)dg, pl.R + (size_t)t0 * xw, s, true));
+                }
+                record(BM_OP_COPY, 0, nq);
+                if (pl.arena.live) check(lift_p(c, nq, dq, E0, s));
+                for (uint32_t q = 0; q < nq; q++)
+                    for (uint32_t j = 0; j < n_in; j++)
+                        R.push_back(j == 0 ? E0 + (size_t)q * xw : pl.R + ((size_t)q * (n_in - 1) + j - 1) * xw);
+                auto dR = pl.arena.list(R);
+                record(BM_OP_MAC_CIRC, c.L, n_in, nq, n_in);
+                if (pl.arena.live)
+                    check(mac_circ(c, nlx - 1, nq, n_in, (const uint64_t* const*)dR, nullptr, g.d_masks_hat_ext,
+                                   g.d_circ_tw_ext, pl.t0, s));
+                for (uint32_t q = 0; q < nq; q++)
+                    for (uint32_t i = 0; i < n_in; i++) outs.push_back(pl.T + ((size_t)(qb + q) * n_in + i) * cw(lg));
+                auto dout = pl.arena.list(outs);
+                for (uint32_t o0 = 0; o0 < (uint32_t)outs.size(); o0 += ksb) {
+                    const uint32_t T = std::min<uint32_t>(ksb, (uint32_t)outs.size() - o0);
+                    record(BM_OP_MODDOWN, c.L, T);
+                    if (!pl.arena.live) {
+                        need_scratch(ks_mdr_scratch_words(c, T));
+                        continue;
+                    }
+                    check(ks_moddown_rescale(c, T, pl.t0 + (size_t)o0 * xw, dout + o0, pl.scratch, s));
+                }
+            }
+        } else if (g.tiled && g.hoisted) {
             const size_t ew = ks_ext_words(c, c.L);
             for (uint32_t qb = 0; qb < Q; qb += pl.qe) {
                 const uint32_t nq = std::min(pl.qe, Q - qb);
@@ -1643,7 +1741,8 @@ static void plan_dims(const Context& c, const SchedView& g, uint32_t n_out, uint
     // hoisted Algorithm 1: rotated copies and products of a chunk of queries within ~4 GiB
     pl.qe = Q;
     if (g.tiled && g.hoisted) {
-        const size_t per_q = ((size_t)2 * g.n_in * ct_words(c, c.L) + ks_ext_words(c, c.L)) * 8;
+        const size_t sw = g.fused ? (size_t)2 * (c.L + 1 + c.alpha) * c.n : ct_words(c, c.L);
+        const size_t per_q = ((size_t)2 * g.n_in * sw + ks_ext_words(c, c.L)) * 8;
         pl.qe = (uint32_t)std::min<size_t>(Q, std::max<size_t>(1, ((size_t)4 << 30) / per_q));
     }
 }
@@ -1658,11 +1757,13 @@ static std::vector<BufSpec> plan_buffers(const Context& c, const SchedView& g, P
     const uint32_t Q = pl.Q, lg = g.level;
     std::vector<BufSpec> b{{&pl.qin, pl.qin_words}, {&pl.result, pl.result_words}};
     if (g.tiled) {
-        b.push_back({&pl.t0, (size_t)pl.qe * g.n_in * ct_words(c, c.L)});
+        // the fused Algorithm 1 keeps its sums on Q_L u P
+        const size_t sw = g.fused ? (size_t)2 * (c.L + 1 + c.alpha) * c.n : ct_words(c, c.L);
+        b.push_back({&pl.t0, (size_t)pl.qe * g.n_in * sw});
         b.push_back({&pl.T, (size_t)Q * g.n_in * ct_words(c, lg)});
         if (g.hoisted) {
             b.push_back({&pl.ext, (size_t)pl.qe * ks_ext_words(c, c.L)});
-            b.push_back({&pl.R, (size_t)pl.qe * g.n_in * ct_words(c, c.L)});
+            b.push_back({&pl.R, (size_t)pl.qe * g.n_in * sw});
         }
     }
     b.push_back({&pl.accA, (size_t)Q * pl.chunk * ct_words(c, lg)});

@@ -87,6 +87,8 @@ struct Context {
     EncoderTables enc;
     std::vector<KsLevelConst> h_ksc;          // key-switching constants per level (host copy)
     KsLevelConst* d_ksc = nullptr;            // ... and on the device
+    KsLevelConst h_ksc_mdr{};                 // ModDown + Rescale at the top level (special set {q_L} u P)
+    KsLevelConst* d_ksc_mdr = nullptr;        //   (only nlx, dn_hinv, dn_hat and pinv are set)
     ulonglong2* d_qlinv = nullptr;            // [level][j]: q_level^-1 mod q_j (Shoup pairs), for rescale
     uint32_t ks_wide_batch[BM_MAX_Q] = {1u << 30, 1u << 30, 1u << 30, 1u << 30, 1u << 30, 1u << 30};
                                               // per level: key-switch batches of at least this many
@@ -176,6 +178,8 @@ struct Gallery {
     uint64_t* d_masks = nullptr;              // [n_in][L+1][N] Algorithm-1 masks (tiled only)
     uint64_t* d_masks_hat = nullptr;          // [n_in][L+1][N] their transform over the parts (circ_prepare)
     ulonglong2* d_circ_tw = nullptr;          // [L+1][n_in] twiddles of that transform
+    uint64_t* d_masks_hat_ext = nullptr;      // [n_in][L+1+alpha][N] the same on Q_L u P (fused Algorithm 1)
+    ulonglong2* d_circ_tw_ext = nullptr;      // [L+1+alpha][n_in]
     uint64_t* d_cmask = nullptr;              // [level][N] compression mask at level-1
     ~Gallery();
 };
@@ -356,10 +360,18 @@ cudaError_t ks_rotate_hoisted(const Context& c, uint32_t level, uint32_t E, cons
 // key_of[e] from the extension ext_of[e]; off on the device, absolute element
 // indices) with P * sigma(c0); ks_moddown_add moves the sums down and adds them
 // to tgt[t] in place.  Targets may be sources.
+// (ntt_out: the sums left in NTT form on every limb, written to scratch as [T][2][nlx][N])
 cudaError_t ks_ipsum_hoisted(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
                              const uint64_t* const* ext_of, const uint64_t* const* src_of,
                              const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch,
-                             cudaStream_t s);
+                             cudaStream_t s, bool ntt_out = false);
+// ModDown and Rescale fused at the top level: e [T][2][L+1+alpha][N] (NTT form, every
+// limb; the special limbs are transformed in place) divided by q_L * P into out[t]
+// (level L - 1); scratch ks_mdr_scratch_words(c, T); needs ks_mdr_supported(c)
+bool ks_mdr_supported(const Context& c);
+size_t ks_mdr_scratch_words(const Context& c, uint32_t T);
+cudaError_t ks_moddown_rescale(const Context& c, uint32_t T, uint64_t* e, uint64_t* const* d_out, uint64_t* scratch,
+                               cudaStream_t s);
 cudaError_t ks_moddown_add(const Context& c, uint32_t level, uint32_t T, uint64_t* const* d_tgt, uint64_t* scratch,
                            cudaStream_t s);
 // rescale in three fused kernels (rings 2^12 and 2^16)
@@ -386,10 +398,16 @@ constexpr uint32_t kMaxCircParts = 32;
 cudaError_t mac_circ(const Context& c, uint32_t level, uint32_t Q, uint32_t n_in, const uint64_t* const* R,
                      const uint64_t* masks, const uint64_t* hat, const ulonglong2* tw, uint64_t* t0,
                      cudaStream_t s);
-// the masks' side of that convolution: tw [L+1][n_in] twiddles (host-built, copied),
-// hat [n_in][L+1][N] = transformed masks / n_in (Montgomery form); synchronises s
-cudaError_t circ_prepare(const Context& c, uint32_t n_in, const uint64_t* masks, uint64_t* hat, ulonglong2* tw,
-                         cudaStream_t s);
+// the masks' side of that convolution on the first l1 primes of the basis: tw
+// [l1][n_in] twiddles (host-built, copied), hat [n_in][l1][N] = transformed masks /
+// n_in (Montgomery form); synchronises s
+cudaError_t circ_prepare(const Context& c, uint32_t n_in, uint32_t l1, const uint64_t* masks, uint64_t* hat,
+                         ulonglong2* tw, cudaStream_t s);
+// masks [n_in][L+1][N] (NTT + Montgomery) extended to Q_L u P: ext [n_in][L+1+alpha][N],
+// the special limbs from the centred integer coefficients of the q_0 limb; synchronises s
+cudaError_t masks_extend(const Context& c, uint32_t n_in, const uint64_t* masks, uint64_t* ext, cudaStream_t s);
+// E0[q] = P * in[q] on Q_L u P (special limbs 0): in[q] [2][L+1][N], E0 [Q][2][L+1+alpha][N], NTT form
+cudaError_t lift_p(const Context& c, uint32_t Q, uint64_t* const* in, uint64_t* E0, cudaStream_t s);
 // dst[t] += sum of src[off[t] .. off[t+1]) (ciphertexts at `level`; off and the lists on the device)
 cudaError_t accumulate(const Context& c, uint32_t level, uint32_t n_targets, uint64_t* const* dst,
                        const uint64_t* const* src, const uint64_t* off, uint32_t n_src, cudaStream_t s);

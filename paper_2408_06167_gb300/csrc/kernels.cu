@@ -736,6 +736,38 @@ __global__ void __launch_bounds__(kMacThreads) k_mac_circ(const uint64_t* const*
     }
 }
 
+// E0[q] = P * query q in the extended basis Q_L u P: the q-limbs times P (Montgomery
+// product with P * 2^64), the special limbs 0.  in[q]: [2][L+1][N] NTT form; E0
+// [Q][2][nlx][N].  Grid (Q * 2 * nlx, chunks of a limb).
+__global__ void k_lift_p(const uint64_t* const* in, uint64_t* __restrict__ E0, const KsLevelConst* __restrict__ kc,
+                         DevTables tab, uint32_t l1, uint32_t nlx, uint32_t n) {
+    const uint32_t y = blockIdx.x, b = y / (2 * nlx), comp = (y / nlx) % 2, jj = y % nlx;
+    pdl_wait();
+    uint64_t* o = E0 + ((size_t)b * 2 * nlx + (size_t)comp * nlx + jj) * n;
+    if (jj >= l1) {
+        for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x) o[i] = 0;
+        return;
+    }
+    const uint64_t q = tab.q[jj], qn = tab.qneg[jj], pm = kc->pmont[jj];
+    const uint64_t* a = in[b] + ((size_t)comp * l1 + jj) * n;
+    for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x)
+        o[i] = mont(a[i], pm, q, qn);
+}
+
+// The residues of integer coefficients x on the special primes, from their q_0
+// residue v (coefficient form): the centred x = v or v - q_0 (|x| < q_0 / 2 and
+// below every special prime), out[k][i] = x mod p_k.  Grid (alpha, chunks).
+__global__ void k_centred_to_p(const uint64_t* __restrict__ v0, uint64_t* __restrict__ out, size_t out_stride,
+                               uint64_t q0, uint32_t L, DevTables tab, uint32_t n) {
+    const uint32_t k = blockIdx.x;
+    const uint64_t p = tab.q[L + 1 + k], half = q0 / 2;
+    uint64_t* o = out + (size_t)k * out_stride;
+    for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x) {
+        const uint64_t v = v0[i];
+        o[i] = v <= half ? v : p - (q0 - v);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Algorithm 1's hoisted sum as a cyclic convolution over the parts.  For one
 // coefficient of one limb, t0[i] = sum_j R[j] * M[(i - j) mod n] is the length-n
@@ -948,6 +980,37 @@ cudaError_t build_ks_constants(Context& c) {
     if (e != cudaSuccess) return e;
     e = cudaMemcpy(c.d_ksc, c.h_ksc.data(), sizeof(KsLevelConst) * c.h_ksc.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
+    // ModDown and Rescale fused at the top level: special set S = {q_L} u P (primes
+    // L..L+alpha), targets q_0..q_(L-1); the F5 / F6 fields with S in place of P
+    if (c.alpha + 1 <= BM_MAX_P && c.L >= 1) {
+        KsLevelConst M{};
+        const uint32_t L = c.L, ns = c.alpha + 1;
+        M.nlx = L + 1 + c.alpha;
+        for (uint32_t i = 0; i < ns; i++) {
+            const uint64_t si = c.primes[L + i];
+            uint64_t hat = 1;                                     // (S / s_i) mod s_i
+            for (uint32_t k = 0; k < ns; k++)
+                if (k != i) hat = h_mulmod(hat, c.primes[L + k] % si, si);
+            M.dn_hinv[i] = pair(h_mulmod(h_invmod(hat, si), h_invmod(c.n % si, si), si), si);
+            for (uint32_t j = 0; j < L; j++) {
+                const uint64_t t = c.primes[j];
+                uint64_t ht = 1;
+                for (uint32_t k = 0; k < ns; k++)
+                    if (k != i) ht = h_mulmod(ht, c.primes[L + k] % t, t);
+                M.dn_hat[i][j] = pair(ht, t);
+            }
+        }
+        for (uint32_t j = 0; j < L; j++) {
+            const uint64_t t = c.primes[j];
+            const uint64_t smod = h_mulmod(c.P_mod[j], c.primes[L] % t, t);   // S mod q_j
+            M.pinv[j] = pair(h_invmod(smod, t), t);
+        }
+        c.h_ksc_mdr = M;
+        e = cudaMalloc(&c.d_ksc_mdr, sizeof(KsLevelConst));
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpy(c.d_ksc_mdr, &c.h_ksc_mdr, sizeof(KsLevelConst), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+    }
     std::vector<ulonglong2> qi((size_t)(c.L + 1) * MAXB, make_ulonglong2(0, 0));
     for (uint32_t l = 1; l <= c.L; l++)
         for (uint32_t j = 0; j < l; j++) qi[(size_t)l * MAXB + j] = pair(h_invmod(c.primes[l] % c.primes[j], c.primes[j]), c.primes[j]);
@@ -1336,10 +1399,50 @@ cudaError_t mac_circ(const Context& c, uint32_t level, uint32_t Q, uint32_t n_in
     return cudaGetLastError();
 }
 
-cudaError_t circ_prepare(const Context& c, uint32_t n_in, const uint64_t* masks, uint64_t* hat, ulonglong2* tw,
-                         cudaStream_t s) {
-    if (n_in < 2 || n_in > kMaxCircParts || (n_in & (n_in - 1))) return cudaErrorInvalidValue;
-    const uint32_t l1 = c.L + 1;
+cudaError_t lift_p(const Context& c, uint32_t Q, uint64_t* const* in, uint64_t* E0, cudaStream_t s) {
+    if (!Q) return cudaSuccess;
+    const uint32_t l1 = c.L + 1, nlx = l1 + c.alpha;
+    ProfScope ps(BM_KERNEL_OTHER, s, 8.0 * c.n * Q * 2 * (l1 + nlx), 20.0 * c.n * Q * 2 * l1);
+    return pdl_launch(k_lift_p, dim3(Q * 2 * nlx, c.n / kThreads / 4), kThreads, 0, s, (const uint64_t* const*)in, E0,
+                      c.d_ksc + c.L, c.tab, l1, nlx, c.n);
+}
+
+cudaError_t masks_extend(const Context& c, uint32_t n_in, const uint64_t* masks, uint64_t* ext, cudaStream_t s) {
+    // ext [n_in][nlx][N]: the q-limbs copied, the special limbs from the q_0 limb's
+    // integer coefficients (NTT + Montgomery like the q-limbs)
+    const uint32_t l1 = c.L + 1, nlx = l1 + c.alpha;
+    const size_t n = c.n;
+    uint64_t* tmp = nullptr;
+    cudaError_t e = cudaMalloc(&tmp, n * 8);
+    if (e != cudaSuccess) return e;
+    for (uint32_t k = 0; k < n_in && e == cudaSuccess; k++) {
+        const uint64_t* src = masks + (size_t)k * l1 * n;
+        uint64_t* dst = ext + (size_t)k * nlx * n;
+        e = cudaMemcpyAsync(dst, src, l1 * n * 8, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, src, n * 8, cudaMemcpyDeviceToDevice, s);
+        LimbBatch t0{tmp, 1, n, 0, 1, 0};
+        t0.set(0, 0);
+        if (e == cudaSuccess) e = to_montgomery(c, t0, true, s);
+        if (e == cudaSuccess) e = ntt_inverse(c, t0, s);
+        if (e == cudaSuccess) {
+            k_centred_to_p<<<dim3(c.alpha, (uint32_t)(n / kThreads / 4)), kThreads, 0, s>>>(tmp, dst + l1 * n, n,
+                                                                                           c.primes[0], c.L, c.tab,
+                                                                                           (uint32_t)n);
+            e = cudaGetLastError();
+        }
+        LimbBatch pb{dst, 1, (uint64_t)nlx * n, l1, c.alpha, 0};
+        for (uint32_t i = 0; i < c.alpha; i++) pb.set(i, c.L + 1 + i);
+        if (e == cudaSuccess) e = ntt_forward(c, pb, s);
+        if (e == cudaSuccess) e = to_montgomery(c, pb, false, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(tmp);
+    return e;
+}
+
+cudaError_t circ_prepare(const Context& c, uint32_t n_in, uint32_t l1, const uint64_t* masks, uint64_t* hat,
+                         ulonglong2* tw, cudaStream_t s) {
+    if (n_in < 2 || n_in > kMaxCircParts || (n_in & (n_in - 1)) || l1 > MAXB) return cudaErrorInvalidValue;
     std::vector<ulonglong2> h((size_t)l1 * n_in);
     CircNinv ninv{};
     for (uint32_t j = 0; j < l1; j++) {

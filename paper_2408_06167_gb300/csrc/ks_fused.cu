@@ -55,9 +55,9 @@ using nttr::tw_wait;
 // Dynamic shared memory (words) of the column kernels F3/F5: exchange tiles,
 // kMaxDigit thread-private staging tiles (each thread reads back only what it
 // wrote), staged twiddles.
-template <int LA, int LT, int C>
+template <int LA, int LT, int C, int MAXS = kMaxDigit>
 __host__ __device__ constexpr size_t col_smem_words() {
-    return (size_t)sub_words<LA, LT>() * C + (size_t)kMaxDigit * (1 << LA) * C + 2 * (size_t)(1 << LA);
+    return (size_t)sub_words<LA, LT>() * C + (size_t)MAXS * (1 << LA) * C + 2 * (size_t)(1 << LA);
 }
 // ... and of F4: exchange rows, staging, forward and inverse row twiddles.
 template <int LB, int LT, int R>
@@ -350,12 +350,14 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
 //   acc[t] = sum_e ( sum_d sigma_e(ext_of[e]_d) * key_e,d  +  P * sigma_e(c0 of src_of[e]) )
 // the last term on the q-limbs of the first component only (ModDown returns it
 // exactly: P * x has no special-prime residue and (P * x) * P^-1 = x); then, for
-// the special-prime limbs, the inverse row pass (as F4).
+// the special-prime limbs, the inverse row pass (as F4) -- or, with ntt_out, every
+// limb left in NTT form (the fused Algorithm 1 multiplies them by the masks first).
 template <int LA, int LB, int LT, int R>
 __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
     k_ks_f4s(const uint64_t* const* ext_of, const uint64_t* const* src_of, const uint64_t* const* key_of,
              const uint64_t* gal_of, const uint64_t* off, uint64_t* __restrict__ acc,
-             const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L, uint32_t nb) {
+             const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L, uint32_t nb,
+             bool ntt_out) {
     constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>(), LOGN = LA + LB, N = 1 << LOGN;
     constexpr int TWN = row_tw_entries<LB, R>();
     __shared__ uint64_t sm[R * S];
@@ -369,7 +371,8 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
     const uint64_t pm = jj < l1 ? kc->pmont[jj] : 0;
     const int row = blockIdx.y * R + jr;
     const size_t roff = (size_t)row * M;
-    if (jj >= l1) stage_row_twiddles<LA, LB, R, R * TH>(twi, tab.itw[pi], blockIdx.y * R);
+    const bool inv = jj >= l1 && !ntt_out;      // special limbs for F5: inverse row pass
+    if (inv) stage_row_twiddles<LA, LB, R, R * TH>(twi, tab.itw[pi], blockIdx.y * R);
     pdl_wait();
     const uint64_t e0 = off[tg], e1 = off[tg + 1];
     uint64_t v[K];
@@ -400,7 +403,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
         }
 #pragma unroll
         for (int k = 0; k < K; k++) v[k] = redc(a[k], q, qn);
-        if (jj < l1) {
+        if (!inv) {
             nttr::relayout<LB, LT, LB / LT - 1, 0>(v, sr, t);
         } else {
             if (comp == 0) tw_wait();
@@ -415,8 +418,10 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
 
 // ---------------------------------------------------------------------------
 // F5: grid (B * 2, N2 / C).  conv = Conv_{P -> Q_l}(acc's special-prime limbs).
+// (MAXS: the most special limbs, the staging depth; the fused ModDown + Rescale
+// calls it with the special set {q_L} u P, l1 = L and L - 1 in place of L.)
 // ---------------------------------------------------------------------------
-template <int LA, int LB, int LT, int C>
+template <int LA, int LB, int LT, int C, int MAXS = kMaxDigit>
 __global__ void __launch_bounds__(C * (1 << (LA - LT)))
     k_ks_f5(const uint64_t* __restrict__ acc, uint64_t* __restrict__ conv, const KsLevelConst* __restrict__ kc,
             DevTables tab, uint32_t l1, uint32_t L, uint32_t alpha) {
@@ -424,7 +429,7 @@ __global__ void __launch_bounds__(C * (1 << (LA - LT)))
     extern __shared__ uint64_t dsm[];
     uint64_t* sm = dsm;
     uint64_t* st = sm + sub_words<LA, LT>() * C;          // staging: [i][row][col]
-    ulonglong2* tws = (ulonglong2*)(st + kMaxDigit * M * C);
+    ulonglong2* tws = (ulonglong2*)(st + MAXS * M * C);
     const int tid = threadIdx.x, t = tid / C, jc = tid % C;
     const uint32_t b = blockIdx.x / 2, comp = blockIdx.x % 2;
     const int col = blockIdx.y * C + jc;
@@ -805,7 +810,8 @@ cudaError_t ks_hoisted_launch(const Context& c, uint32_t level, uint32_t E, cons
 template <int LA, int LB, int LT, int C, int R>
 cudaError_t ks_ipsum_launch(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
                             const uint64_t* const* ext_of, const uint64_t* const* src_of,
-                            const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch, cudaStream_t s) {
+                            const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch, bool ntt_out,
+                            cudaStream_t s) {
     constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
     (void)N2;
     const KsLevelConst& K = c.h_ksc[level];
@@ -814,10 +820,10 @@ cudaError_t ks_ipsum_launch(const Context& c, uint32_t level, uint32_t T, const 
     const int tr = R * (1 << (LB - LT));
     const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB;
     ProfScope ps(BM_KERNEL_KS_IP, s, lw * (nlx * ((double)E * nd + 2.0 * nd * E + 2.0 * T) + (double)E * l1),
-                 bf_r * T * 2.0 * alpha + N * (double)nlx * (2.0 * kProdMul * nd * E + 2.0 * kRedcMul * T) +
-                     (double)N * l1 * E * kProdMul);
+                 (ntt_out ? 0.0 : bf_r * T * 2.0 * alpha) +
+                     N * (double)nlx * (2.0 * kProdMul * nd * E + 2.0 * kRedcMul * T) + (double)N * l1 * E * kProdMul);
     pdl_launch(k_ks_f4s<LA, LB, LT, R>, dim3(T * nlx, N1 / R), tr, 0, s, ext_of, src_of, key_of, gal_of, off, scratch,
-               kc, c.tab, l1, c.L, c.nb);
+               kc, c.tab, l1, c.L, c.nb, ntt_out);
     return cudaGetLastError();
 }
 
@@ -849,6 +855,47 @@ cudaError_t ks_moddown_add_launch(const Context& c, uint32_t level, uint32_t T, 
         ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * T * l1 * 8, bf_r * T * 2 * l1 + kShoupMul * N * T * 2 * l1);
         pdl_launch(k_ks_f6<LA, LB, LT, R>, dim3(T * l1, N1 / R), tr, 0, s, conv, acc, nullptr, d_tgt, d_tgt, kc, c.tab,
                    l1, 0u, nullptr, nullptr);
+    }
+    return cudaGetLastError();
+}
+
+// ModDown and Rescale fused on T sums in the extended basis: e [T][2][nlx][N] (NTT
+// form, every limb) divided by S = q_L * P into out[t] (level L - 1): the inverse row
+// pass of the special limbs {q_L} u P, F5 with that special set (l1 = L, q_L as the
+// first special prime) and F6 with S^-1 (constants c.d_ksc_mdr).  Scratch: conv of T.
+template <int LA, int LB, int LT, int C, int R>
+cudaError_t ks_mdr_launch(const Context& c, uint32_t T, uint64_t* e, uint64_t* const* d_out, uint64_t* scratch,
+                          cudaStream_t s) {
+    constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
+    constexpr int MAXS = BM_MAX_P;
+    const uint32_t L = c.L, nlx = L + 1 + c.alpha, ns = c.alpha + 1;
+    const KsLevelConst* kc = c.d_ksc_mdr;
+    uint64_t* conv = scratch;
+    const int tr = R * (1 << (LB - LT)), tc = C * (1 << (LA - LT));
+    const size_t col_smem = 8 * col_smem_words<LA, LT, C, MAXS>();
+    static bool attrs = [&] {
+        cudaFuncSetAttribute(k_ks_f5<LA, LB, LT, C, MAXS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)col_smem);
+        return true;
+    }();
+    (void)attrs;
+    const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;
+    {
+        LimbBatch sb{e, T * 2, (uint64_t)nlx * N, L, ns, 0};
+        for (uint32_t k = 0; k < ns; k++) sb.set(k, L + k);
+        ProfScope ps(BM_KERNEL_MODDOWN, s, 2 * lw * T * 2 * ns, bf_r * T * 2 * ns);
+        pdl_launch(nttr::k_row_inv<LA, LB, LT, R>, dim3(T * 2 * ns, N1 / R), tr, 0, s, sb, c.tab);
+    }
+    {
+        ProfScope ps(BM_KERNEL_MODDOWN, s, lw * T * 2 * (ns + L),
+                     bf_c * T * 2 * (ns + L) + kShoupMul * N * T * 2 * (ns + (double)L * ns));
+        pdl_launch(k_ks_f5<LA, LB, LT, C, MAXS>, dim3(T * 2, N2 / C), tc, col_smem, s, e, conv, kc, c.tab, L, L - 1,
+                   ns);
+    }
+    {
+        ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * T * L * 6, bf_r * T * 2 * L + kShoupMul * N * T * 2 * L);
+        pdl_launch(k_ks_f6<LA, LB, LT, R>, dim3(T * L, N1 / R), tr, 0, s, conv, e, nullptr, d_out, nullptr, kc, c.tab,
+                   L, 0u, nullptr, nullptr);
     }
     return cudaGetLastError();
 }
@@ -890,10 +937,24 @@ cudaError_t ks_rotate_hoisted(const Context& c, uint32_t level, uint32_t E, cons
 cudaError_t ks_ipsum_hoisted(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
                              const uint64_t* const* ext_of, const uint64_t* const* src_of,
                              const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool ntt_out) {
     if (T == 0) return cudaSuccess;
-    if (c.log_n == 16) return ks_ipsum_launch<8, 8, 2, 2, 2>(c, level, T, off, E, ext_of, src_of, key_of, gal_of, scratch, s);
-    if (c.log_n == 12) return ks_ipsum_launch<6, 6, 2, 8, 8>(c, level, T, off, E, ext_of, src_of, key_of, gal_of, scratch, s);
+    if (c.log_n == 16)
+        return ks_ipsum_launch<8, 8, 2, 2, 2>(c, level, T, off, E, ext_of, src_of, key_of, gal_of, scratch, ntt_out, s);
+    if (c.log_n == 12)
+        return ks_ipsum_launch<6, 6, 2, 8, 8>(c, level, T, off, E, ext_of, src_of, key_of, gal_of, scratch, ntt_out, s);
+    return cudaErrorInvalidValue;
+}
+
+bool ks_mdr_supported(const Context& c) { return ks_fused_supported(c) && c.alpha + 1 <= BM_MAX_P && c.L >= 1; }
+size_t ks_mdr_scratch_words(const Context& c, uint32_t T) { return (size_t)T * 2 * c.L * c.n; }
+
+cudaError_t ks_moddown_rescale(const Context& c, uint32_t T, uint64_t* e, uint64_t* const* d_out, uint64_t* scratch,
+                               cudaStream_t s) {
+    if (T == 0) return cudaSuccess;
+    if (!ks_mdr_supported(c)) return cudaErrorInvalidValue;
+    if (c.log_n == 16) return ks_mdr_launch<8, 8, 2, 2, 2>(c, T, e, d_out, scratch, s);
+    if (c.log_n == 12) return ks_mdr_launch<6, 6, 2, 8, 8>(c, T, e, d_out, scratch, s);
     return cudaErrorInvalidValue;
 }
 

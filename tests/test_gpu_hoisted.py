@@ -50,6 +50,52 @@ def test_hoisted_match_is_bit_exact(name, m, s, R, nq):
         assert np.abs(om.scores(got, opacked) - ref).max() < 1e-5
 
 
+@pytest.mark.parametrize("name,m,s,R,nq", [
+    ("small4", 128, 16, 2500, 2),     # N_in = 8
+    ("small4", 16, 4, 3000, 3),       # N_in = 4, three queries
+    ("small4", 16, 1, 2100, 1),       # N_in = 16
+    ("small4", 128, 4, 600, 1),       # N_in = 32
+])
+def test_fused_expansion_match_is_bit_exact(name, m, s, R, nq):
+    """Algorithm 1 with ModDown and Rescale fused (rotations kept on Q_L u P, the
+    circulant there, one division by q_L P per part), then every hoisted tail
+    form: bit-exact against the oracle's same-order evaluation."""
+    c = gctx(name)
+    om = OracleMatch(name, m, s, R, nq, hoisted="fused", hoisted_tail=True, double_hoisted=True)
+    _, _, ek = bm.bm_keygen_ex(c, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
+    g = bm.bm_gallery_import(c, om.pts_array(), om.masks_array(), om.cmask_array(), R, m, s)
+    bm.bm_gallery_set_schedule(g, bm.BM_SCHED_ALL | bm.BM_SCHED_DOUBLE_HOISTED | bm.BM_SCHED_FUSED_EXPANSION)
+    ocs = [om.encrypt(qi) for qi in range(nq)]
+    qs = [bm.bm_ciphertext_import(c, om.ct_array(cts), om.ctx.L) for cts in ocs]
+    res = bm.bm_match(c, ek, g, qs)
+    for qi in range(nq):
+        want, opacked = om.match(ocs[qi])
+        got = bm.bm_result_export(res, qi)
+        assert np.array_equal(got, want), f"query {qi}: ciphertexts differ"
+        ref = wl.plaintext_scores(om.feats, om.queries[qi])
+        assert np.abs(om.scores(got, opacked) - ref).max() < 1e-5
+
+
+def test_fused_expansion_pipeline_ring16():
+    """Ring 2^16 end to end with the fused Algorithm 1: scores within 1e-5 of FP64,
+    the same Rank-1 as the hoisted form."""
+    c = gctx("ring16")
+    m, s, R = 128, 16, 6144
+    feats = wl.gallery(R, m)
+    qs, _ = wl.queries(feats, 2)
+    sk, pk, ek = bm.bm_keygen_ex(c, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
+    g = bm.bm_encode_gallery_packed(c, feats, m, s, bm.BM_PACK_COMPLEX)
+    bm.bm_gallery_set_expansion(g, bm.BM_EXPAND_FUSED)
+    cts = bm.bm_encrypt_batch(c, pk, qs, m, s, bm.BM_QUERY_TILED, 4, 0)
+    res = bm.bm_match(c, ek, g, cts)
+    for qi in range(2):
+        ref = wl.plaintext_scores(feats, qs[qi])
+        scores, rank1, _ = bm.bm_decrypt_scores(c, sk, res, qi, R)
+        assert np.abs(scores - ref).max() < 1e-5
+        if np.sort(ref)[-1] - np.sort(ref)[-2] > 2e-5:
+            assert rank1 == int(ref.argmax())
+
+
 @pytest.mark.parametrize("double", [False, True])
 @pytest.mark.parametrize("name,m,s,R,nq,tail_only", [
     ("small4", 128, 16, 2500, 2, False),   # every hoisted form: rotate-and-sum 4 x 4, compression 15 rotations
@@ -120,3 +166,7 @@ def test_expansion_errors():
     assert e.value.status == 4
     with pytest.raises(bm.BlindMatchError):
         bm.bm_gallery_set_expansion(g4, 7)
+    g1 = bm.bm_encode_gallery(c4, wl.gallery(100, 16), 16, 16)   # one part: no rotations to fuse
+    with pytest.raises(bm.BlindMatchError) as e:
+        bm.bm_gallery_set_expansion(g1, bm.BM_EXPAND_FUSED)
+    assert e.value.status == 1

@@ -308,3 +308,27 @@ def test_double_hoisted_forms_match_the_oracle_counts(preset, R, dim, part, Q):
         if lv < lg:
             assert lib[("rot_hoisted", lv)] == 0, lv          # the tail's rotations are all summed
     assert not any(o["op"] == "accum" for o in ops)
+
+
+@pytest.mark.parametrize("preset,R,dim,part,Q", [("small4", 2500, 128, 16, 3), ("ring16", 6144, 128, 16, 1),
+                                                 ("ring16", 1 << 20, 128, 4, 40), ("small4", 3000, 16, 4, 2)])
+def test_fused_expansion_matches_the_oracle_counts(preset, R, dim, part, Q):
+    """Algorithm 1 with ModDown and Rescale fused: one basis extension and N_in - 1
+    key-switch products per query, N_in fused divisions, no rescale at the top level."""
+    kind = (bm.BM_LAYOUT_HOISTED | bm.BM_LAYOUT_FUSED_EXPANSION | bm.BM_LAYOUT_HOISTED_ROTSUM
+            | bm.BM_LAYOUT_HOISTED_COMPRESSION | bm.BM_LAYOUT_DOUBLE_HOISTED)
+    ops, _ = bm.bm_plan_estimate(preset, R, dim, part, Q, packing=kind)
+    log_n, n_q = PRESET[preset]
+    L, slots = n_q - 1, 1 << (log_n - 1)
+    n_in = dim // part
+    groups = sch.n_groups(R, part, slots)
+    ev = sch.CountingEvaluator()
+    sch.match(ev, [sch.SymCt(L)], [[None] * n_in for _ in range(groups)], [None] * n_in, object(), dim, part,
+              hoisted="fused", hoisted_rotsum=True, hoisted_compress=True, double_hoisted=True)
+    orc = ev.counts()
+    lib = library_counts(ops)
+    assert lib[("modup", L)] == Q * orc[("ModUp", L)] == Q
+    assert lib[("ip_sum", L)] == Q * orc[("IPH", L)] == Q * (n_in - 1)
+    assert lib[("moddown", L)] == Q * orc[("ModDownRes", L)] == Q * n_in
+    assert lib[("rescale", L)] == 0 and ("Res", L) not in orc
+    assert lib[("rot_hoisted", L)] == 0
