@@ -57,8 +57,8 @@ def parse():
                     help="serving: each gallery's part size chosen by the cost model (bm_choose_part)")
     ap.add_argument("--no-tune", action="store_true", help="skip the rotation kernel-shape tuner")
     ap.add_argument("--expansion", default="fused", choices=["doubling", "hoisted", "fused", "auto"],
-                    help="form of Algorithm 1: the printed doubling order or the hoisted sum "
-                         "(auto: serving picks per gallery by the cost model)")
+                    help="form of Algorithm 1: the printed doubling order, the hoisted sum, or the hoisted sum "
+                         "with its key switches and rescale fused (auto: serving picks per gallery by the cost model)")
     ap.add_argument("--tail", default="double", choices=["printed", "hoisted", "double"],
                     help="Algorithm 2's rotate-and-sum and the compression: the printed sequential forms, "
                          "rounds of hoisted rotations, or the same rounds with one ModDown per output "
