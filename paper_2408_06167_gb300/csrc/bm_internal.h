@@ -290,7 +290,7 @@ void decode_complex(const Context& ctx, const double* coeffs, double scale, std:
 // x*w' (four 32x32 partial products, both halves: 8) and the low halves of x*w
 // and of the quotient times q (4 each) = 16, as one butterfly; a sum of products
 // reduced once = 8 per product (the full 128-bit product, or four 32 x 32 -> 64
-// multiply-adds of 31-bit pieces, two multiplies each) plus one Montgomery
+// multiply-adds of 30-bit pieces, two multiplies each) plus one Montgomery
 // reduction per sum (the low half of t*(-q^-1), 4, and the high half of m*q, 8) = 12.
 constexpr double kShoupMul = 16, kProdMul = 8, kRedcMul = 12;
 

@@ -69,22 +69,23 @@ BM_HD uint64_t redc(const Acc128& t, uint64_t q, uint64_t qneg) {   // t < q * 2
     return r >= q ? r - q : r;
 }
 
-// Sums of products by 31-bit pieces, for a, b < q < 2^60: a = a1 * 2^31 + a0 with
-// a0 < 2^31, a1 < q / 2^31, and the sum t = hi * 2^62 + mid * 2^31 + lo held as three
-// 64-bit sums of 32 x 32-bit products, one multiply-add each: lo gains a0*b0 < 2^62,
-// mid a0*b1 + a1*b0 < 2q, hi a1*b1 < q^2 / 2^62 < q/4 per product.  fold62 every
-// kFold62Every = 4 products moves lo's and mid's bits above 31 up a sum (lo stays
-// below 2^64, mid below 2^63) and keeps hi below 4q by subtracting 4q from it, i.e.
-// q * 2^64 from t, which leaves t mod q unchanged.
-constexpr int kFold62Every = 4;
-struct Piece31 {
+// Sums of products by 30-bit pieces, for a, b < q < 2^60: a = a1 * 2^30 + a0 with
+// a0, a1 < 2^30, and the sum t = hi * 2^60 + mid * 2^30 + lo held as three 64-bit
+// sums of 32 x 32-bit products, one multiply-add each: lo gains a0*b0 < 2^60, mid
+// a0*b1 + a1*b0 < 2^61, hi a1*b1 < q^2 / 2^60 < q per product.  fold60 every
+// kFold60Every = 8 products moves lo's and mid's bits above 30 up a sum (lo then
+// stays below 2^63, mid below 2^64 - 2^34) and keeps hi below 8q by subtracting 8q
+// (hi below 16q < 2^64 before the fold), i.e. q * 2^63 from t, which leaves t mod q
+// unchanged.
+constexpr int kFold60Every = 8;
+struct Piece30 {
     uint32_t l, h;
 };
-BM_HD Piece31 piece31(uint64_t a) { return {(uint32_t)a & 0x7fffffffu, (uint32_t)(a >> 31)}; }
-// the pieces stored in one word (low piece in bits 0..30, high piece in bits 32..63)
-BM_HD uint64_t pack31(uint64_t a) { return ((a >> 31) << 32) | (a & 0x7fffffffull); }
-BM_HD Piece31 unpack31(uint64_t w) { return {(uint32_t)w, (uint32_t)(w >> 32)}; }
-struct Acc62 {
+BM_HD Piece30 piece30(uint64_t a) { return {(uint32_t)a & 0x3fffffffu, (uint32_t)(a >> 30)}; }
+// the pieces stored in one word (low piece in bits 0..29, high piece in bits 32..63)
+BM_HD uint64_t pack30(uint64_t a) { return ((a >> 30) << 32) | (a & 0x3fffffffull); }
+BM_HD Piece30 unpack30(uint64_t w) { return {(uint32_t)w, (uint32_t)(w >> 32)}; }
+struct Acc60 {
     uint64_t lo = 0, mid = 0, hi = 0;
 };
 // acc += a * b (32 x 32 -> 64 bits).  On the device as the low and high halves of
@@ -99,29 +100,28 @@ BM_HD void mac32(uint64_t& acc, uint32_t a, uint32_t b) {
     acc += (uint64_t)a * b;
 #endif
 }
-BM_HD void mul_add(Acc62& t, Piece31 a, Piece31 b) {
+BM_HD void mul_add(Acc60& t, Piece30 a, Piece30 b) {
     mac32(t.lo, a.l, b.l);
     mac32(t.mid, a.l, b.h);
     mac32(t.mid, a.h, b.l);
     mac32(t.hi, a.h, b.h);
 }
-BM_HD void fold62(Acc62& t, uint64_t q4) {
-    t.mid += t.lo >> 31;
-    t.lo &= 0x7fffffffull;
-    t.hi += t.mid >> 31;
-    t.mid &= 0x7fffffffull;
-    if (t.hi >= q4) t.hi -= q4;
+BM_HD void fold60(Acc60& t, uint64_t q8) {
+    t.mid += t.lo >> 30;
+    t.lo &= 0x3fffffffull;
+    t.hi += t.mid >> 30;
+    t.mid &= 0x3fffffffull;
+    if (t.hi >= q8) t.hi -= q8;
 }
-// t * 2^-64 mod q: after a fold, t < 4q * 2^62 + 2^62 + 2^31, so the high word of
-// the 128-bit value is at most q and one subtraction brings it below q
-BM_HD uint64_t redc(Acc62 t, uint64_t q, uint64_t qneg) {
-    fold62(t, 4 * q);
+// t * 2^-64 mod q: after a fold, t < 8q * 2^60 + 2^60 + 2^30, so the high word of the
+// 128-bit value is below q
+BM_HD uint64_t redc(Acc60 t, uint64_t q, uint64_t qneg) {
+    fold60(t, 8 * q);
     Acc128 r;
-    const uint64_t top = t.hi << 62;
-    r.lo = t.lo + (t.mid << 31);                 // < 2^62 + 2^31: no carry
+    const uint64_t top = t.hi << 60;
+    r.lo = t.lo + (t.mid << 30);                 // < 2^60 + 2^30: no carry
     r.lo += top;
-    r.hi = (t.hi >> 2) + (r.lo < top);
-    if (r.hi >= q) r.hi -= q;
+    r.hi = (t.hi >> 4) + (r.lo < top);
     return redc(r, q, qneg);
 }
 

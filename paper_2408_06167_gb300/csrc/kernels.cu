@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(kMacThreads) k_mac(const uint64_t* __restrict_
     const MacTile t = mac_tile(n_qt, n_gt, n / kMacThreads, QT, GT, 1);
     pdl_wait();
     const uint32_t nq = min((uint32_t)QT, Qn - t.q0), ng = min((uint32_t)GT, G - t.g0);
-    const uint64_t q = tab.q[t.j], qn = tab.qneg[t.j], q4 = 4 * q;
+    const uint64_t q = tab.q[t.j], qn = tab.qneg[t.j], q8 = 8 * q;
     const size_t ln = (size_t)l1 * n;                        // one polynomial at this level
     const size_t t_i = 2 * ln, t_q = (size_t)n_in * t_i;     // strides of T: part, query
     const size_t p_g = (size_t)n_in * ln;                    // stride of P: group (part: ln)
@@ -536,10 +536,10 @@ __global__ void __launch_bounds__(kMacThreads) k_mac(const uint64_t* __restrict_
     const uint64_t* pp = P + (size_t)t.g0 * p_g + (size_t)t.j * n + t.p;
     // the words of U parts are loaded before their products (U by the tile's registers)
     constexpr int W = 2 * QT + GT, U = W * 4 <= 24 ? 4 : (W * 2 <= 12 ? 2 : 1);
-    Acc62 a0[QT][GT], a1[QT][GT];
-    for (uint32_t i0 = 0; i0 < n_in; i0 += kFold62Every) {
+    Acc60 a0[QT][GT], a1[QT][GT];
+    for (uint32_t i0 = 0; i0 < n_in; i0 += kFold60Every) {
 #pragma unroll
-        for (int v0 = 0; v0 < kFold62Every; v0 += U) {
+        for (int v0 = 0; v0 < kFold60Every; v0 += U) {
             uint64_t xr0[U][QT], xr1[U][QT], yr[U][GT];
 #pragma unroll
             for (int v = 0; v < U; v++) {
@@ -557,14 +557,14 @@ __global__ void __launch_bounds__(kMacThreads) k_mac(const uint64_t* __restrict_
 #pragma unroll
             for (int v = 0; v < U; v++) {
                 if (i0 + v0 + v >= n_in) break;
-                Piece31 x0[QT], x1[QT], y[GT];
+                Piece30 x0[QT], x1[QT], y[GT];
 #pragma unroll
                 for (int k = 0; k < QT; k++) {
-                    x0[k] = piece31(xr0[v][k]);
-                    x1[k] = piece31(xr1[v][k]);
+                    x0[k] = piece30(xr0[v][k]);
+                    x1[k] = piece30(xr1[v][k]);
                 }
 #pragma unroll
-                for (int h = 0; h < GT; h++) y[h] = piece31(yr[v][h]);
+                for (int h = 0; h < GT; h++) y[h] = piece30(yr[v][h]);
 #pragma unroll
                 for (int k = 0; k < QT; k++)
 #pragma unroll
@@ -578,8 +578,8 @@ __global__ void __launch_bounds__(kMacThreads) k_mac(const uint64_t* __restrict_
         for (int k = 0; k < QT; k++)
 #pragma unroll
             for (int h = 0; h < GT; h++) {
-                fold62(a0[k][h], q4);
-                fold62(a1[k][h], q4);
+                fold60(a0[k][h], q8);
+                fold60(a1[k][h], q8);
             }
     }
 #pragma unroll
@@ -598,7 +598,7 @@ __global__ void __launch_bounds__(kMacThreads) k_mac(const uint64_t* __restrict_
 //   d0 = sum T0*C0,  d1 = sum T0*C1 + T1*C0,  d2 = sum T1*C1   (C in Montgomery form),
 // written as A[q][g] = (d0, d2) -- the input of the relinearising key switch --
 // and B[q][g] = (0, d1) -- its addend.  Tiles and block order as k_mac; d1 takes
-// two products a part, so the sums are folded every kFold62Every / 2 parts.
+// two products a part, so the sums are folded every kFold60Every / 2 parts.
 template <int QT, int GT>
 __global__ void __launch_bounds__(kMacThreads) k_mac_ct(const uint64_t* __restrict__ T, const uint64_t* __restrict__ C,
                                                         uint64_t* __restrict__ A, uint64_t* __restrict__ B,
@@ -608,27 +608,27 @@ __global__ void __launch_bounds__(kMacThreads) k_mac_ct(const uint64_t* __restri
     const MacTile t = mac_tile(n_qt, n_gt, n / kMacThreads, QT, GT, 1);
     pdl_wait();
     const uint32_t nq = min((uint32_t)QT, Qn - t.q0), ng = min((uint32_t)GT, G - t.g0);
-    const uint64_t q = tab.q[t.j], qn = tab.qneg[t.j], q4 = 4 * q;
+    const uint64_t q = tab.q[t.j], qn = tab.qneg[t.j], q8 = 8 * q;
     const size_t ln = (size_t)l1 * n;
     const size_t t_i = 2 * ln, t_q = (size_t)n_in * t_i;     // strides of T and C: part; query / group
     const uint64_t* tp = T + (size_t)t.q0 * t_q + (size_t)t.j * n + t.p;
     const uint64_t* cp = C + (size_t)t.g0 * t_q + (size_t)t.j * n + t.p;
-    Acc62 d0[QT][GT], d1[QT][GT], d2[QT][GT];
-    for (uint32_t i0 = 0; i0 < n_in; i0 += kFold62Every / 2) {
-        const uint32_t i1 = min(n_in, i0 + kFold62Every / 2);
+    Acc60 d0[QT][GT], d1[QT][GT], d2[QT][GT];
+    for (uint32_t i0 = 0; i0 < n_in; i0 += kFold60Every / 2) {
+        const uint32_t i1 = min(n_in, i0 + kFold60Every / 2);
         for (uint32_t i = i0; i < i1; i++) {
-            Piece31 x0[QT], x1[QT], y0[GT], y1[GT];
+            Piece30 x0[QT], x1[QT], y0[GT], y1[GT];
 #pragma unroll
             for (int k = 0; k < QT; k++) {
                 const uint64_t* r = tp + k * t_q + i * t_i;
-                x0[k] = piece31((uint32_t)k < nq ? r[0] : 0);
-                x1[k] = piece31((uint32_t)k < nq ? r[ln] : 0);
+                x0[k] = piece30((uint32_t)k < nq ? r[0] : 0);
+                x1[k] = piece30((uint32_t)k < nq ? r[ln] : 0);
             }
 #pragma unroll
             for (int h = 0; h < GT; h++) {
                 const uint64_t* r = cp + h * t_q + i * t_i;
-                y0[h] = piece31((uint32_t)h < ng ? r[0] : 0);
-                y1[h] = piece31((uint32_t)h < ng ? r[ln] : 0);
+                y0[h] = piece30((uint32_t)h < ng ? r[0] : 0);
+                y1[h] = piece30((uint32_t)h < ng ? r[ln] : 0);
             }
 #pragma unroll
             for (int k = 0; k < QT; k++)
@@ -644,9 +644,9 @@ __global__ void __launch_bounds__(kMacThreads) k_mac_ct(const uint64_t* __restri
         for (int k = 0; k < QT; k++)
 #pragma unroll
             for (int h = 0; h < GT; h++) {
-                fold62(d0[k][h], q4);
-                fold62(d1[k][h], q4);
-                fold62(d2[k][h], q4);
+                fold60(d0[k][h], q8);
+                fold60(d1[k][h], q8);
+                fold60(d2[k][h], q8);
             }
     }
 #pragma unroll
@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(kMacThreads) k_mac_ct(const uint64_t* __restri
 // copies in L2: a thread computes OC outputs i of one query, limb and
 // coefficient, reading each rotated query once per OC outputs.  The block
 // stages the query's pointer list and, with SM, its words of every mask (split
-// into 31-bit pieces; n_in * kMacThreads words of dynamic shared memory) --
+// into 30-bit pieces; n_in * kMacThreads words of dynamic shared memory) --
 // static gallery data, staged before the wait on the previous kernel.
 template <int OC, bool SM>
 __global__ void __launch_bounds__(kMacThreads) k_mac_circ(const uint64_t* const* R, const uint64_t* __restrict__ masks,
@@ -686,19 +686,19 @@ __global__ void __launch_bounds__(kMacThreads) k_mac_circ(const uint64_t* const*
     const size_t ln = (size_t)l1 * n;
     const uint64_t* mj = masks + (size_t)j * n + p;               // mask k at mj + k * ln
     if (SM)
-        for (uint32_t k = 0; k < n_in; k++) sm_mask[k * kMacThreads + threadIdx.x] = pack31(mj[k * ln]);
+        for (uint32_t k = 0; k < n_in; k++) sm_mask[k * kMacThreads + threadIdx.x] = pack30(mj[k * ln]);
     pdl_wait();
-    const uint64_t q = tab.q[j], qn = tab.qneg[j], q4 = 4 * q;
-    Acc62 s0[OC], s1[OC];
+    const uint64_t q = tab.q[j], qn = tab.qneg[j], q8 = 8 * q;
+    Acc60 s0[OC], s1[OC];
     for (uint32_t b0 = 0; b0 < n_in; b0 += kMacThreads) {
         const uint32_t nb = min(n_in - b0, (uint32_t)kMacThreads);
         __syncthreads();
         if (threadIdx.x < nb) sR[threadIdx.x] = R[(size_t)qi * n_in + b0 + threadIdx.x];
         __syncthreads();
-        for (uint32_t u0 = 0; u0 < nb; u0 += kFold62Every) {
-            uint64_t rv0[kFold62Every], rv1[kFold62Every];
+        for (uint32_t u0 = 0; u0 < nb; u0 += kFold60Every) {
+            uint64_t rv0[kFold60Every], rv1[kFold60Every];
 #pragma unroll
-            for (int v = 0; v < kFold62Every; v++) {
+            for (int v = 0; v < kFold60Every; v++) {
                 if (u0 + v < nb) {
                     const uint64_t* r = sR[u0 + v] + (size_t)j * n + p;
                     rv0[v] = r[0];
@@ -706,23 +706,23 @@ __global__ void __launch_bounds__(kMacThreads) k_mac_circ(const uint64_t* const*
                 }
             }
 #pragma unroll
-            for (int v = 0; v < kFold62Every; v++) {
+            for (int v = 0; v < kFold60Every; v++) {
                 if (u0 + v >= nb) break;
                 const uint32_t jj = b0 + u0 + v;
-                const Piece31 r0 = piece31(rv0[v]), r1 = piece31(rv1[v]);
+                const Piece30 r0 = piece30(rv0[v]), r1 = piece30(rv1[v]);
 #pragma unroll
                 for (int o = 0; o < OC; o++) {
                     if (i0 + o >= n_in) break;
                     const uint32_t k = (i0 + o - jj) & nm;
-                    const Piece31 mk = SM ? unpack31(sm_mask[k * kMacThreads + threadIdx.x]) : piece31(mj[k * ln]);
+                    const Piece30 mk = SM ? unpack30(sm_mask[k * kMacThreads + threadIdx.x]) : piece30(mj[k * ln]);
                     mul_add(s0[o], r0, mk);
                     mul_add(s1[o], r1, mk);
                 }
             }
 #pragma unroll
             for (int o = 0; o < OC; o++) {
-                fold62(s0[o], q4);
-                fold62(s1[o], q4);
+                fold60(s0[o], q8);
+                fold60(s1[o], q8);
             }
         }
     }

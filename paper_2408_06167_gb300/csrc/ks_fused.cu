@@ -883,6 +883,7 @@ cudaError_t ks_mdr_launch(const Context& c, uint32_t T, uint64_t* e, uint64_t* c
     {
         LimbBatch sb{e, T * 2, (uint64_t)nlx * N, L, ns, 0};
         for (uint32_t k = 0; k < ns; k++) sb.set(k, L + k);
+        // the prelude of the fused ModDown (the part F4 does for a plain key switch): moddown class
         ProfScope ps(BM_KERNEL_MODDOWN, s, 2 * lw * T * 2 * ns, bf_r * T * 2 * ns);
         pdl_launch(nttr::k_row_inv<LA, LB, LT, R>, dim3(T * 2 * ns, N1 / R), tr, 0, s, sb, c.tab);
     }
