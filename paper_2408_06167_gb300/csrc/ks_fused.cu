@@ -128,8 +128,11 @@ __global__ void __launch_bounds__(C * (1 << (LA - LT)))
     constexpr int K = 1 << LT, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN;
     extern __shared__ uint64_t dsm[];
     uint64_t* sm = dsm;                                   // exchange tiles
-    uint64_t* st = sm + sub_words<LA, LT>() * C;          // staging: [i][row][col]
+    // staging [i][k][thread]: thread-private (each thread reads back only what it
+    // wrote), thread index fastest so a warp's accesses are free of bank conflicts
+    uint64_t* st = sm + sub_words<LA, LT>() * C;
     ulonglong2* tws = (ulonglong2*)(st + kMaxDigit * M * C);
+    constexpr int NT = C * (M >> LT);
     const int tid = threadIdx.x, t = tid / C, jc = tid % C;
     const uint32_t nd = kc->nd, nlx = kc->nlx;
     const uint32_t b = blockIdx.x / nd, d = blockIdx.x % nd;
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(C * (1 << (LA - LT)))
             const uint32_t e = ((uint32_t)r * N2 + col) * kinv & (2u * N - 1);
             uint64_t x = src[e & (N - 1)];
             if (e >= (uint32_t)N) x = negm(x, qi);
-            st[(i * M + r) * C + jc] = shoup(x, h.x, h.y, qi);
+            st[(i * K + k) * NT + tid] = shoup(x, h.x, h.y, qi);
         }
     }
 #pragma unroll 1
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(C * (1 << (LA - LT)))
             const ulonglong2 h = kc->up_hat[d][i][jj];
 #pragma unroll
             for (int k = 0; k < K; k++)
-                y[k] += shoup_lazy(st[(i * M + first_idx<LA, LT>(t, k)) * C + jc], h.x, h.y, tq);
+                y[k] += shoup_lazy(st[(i * K + k) * NT + tid], h.x, h.y, tq);
         }
 #pragma unroll
         for (int k = 0; k < K; k++) y[k] = red6(y[k], tq);
@@ -425,10 +428,10 @@ template <int LA, int LB, int LT, int C, int MAXS = kMaxDigit>
 __global__ void __launch_bounds__(C * (1 << (LA - LT)))
     k_ks_f5(const uint64_t* __restrict__ acc, uint64_t* __restrict__ conv, const KsLevelConst* __restrict__ kc,
             DevTables tab, uint32_t l1, uint32_t L, uint32_t alpha) {
-    constexpr int K = 1 << LT, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN;
+    constexpr int K = 1 << LT, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN, NT = C * (M >> LT);
     extern __shared__ uint64_t dsm[];
     uint64_t* sm = dsm;
-    uint64_t* st = sm + sub_words<LA, LT>() * C;          // staging: [i][row][col]
+    uint64_t* st = sm + sub_words<LA, LT>() * C;          // staging [i][k][thread] (thread-private, as F3)
     ulonglong2* tws = (ulonglong2*)(st + MAXS * M * C);
     const int tid = threadIdx.x, t = tid / C, jc = tid % C;
     const uint32_t b = blockIdx.x / 2, comp = blockIdx.x % 2;
@@ -448,7 +451,7 @@ __global__ void __launch_bounds__(C * (1 << (LA - LT)))
         nttr::inv_pass<LA, LT>(y, SubMem{sm + jc, C}, tws, ColBase{}, t, p, p2);
         const ulonglong2 h = kc->dn_hinv[i];          // N^-1 * (P/p_i)^-1 mod p_i
 #pragma unroll
-        for (int k = 0; k < K; k++) st[(i * M + first_idx<LA, LT>(t, k)) * C + jc] = shoup(y[k], h.x, h.y, p);
+        for (int k = 0; k < K; k++) st[(i * K + k) * NT + tid] = shoup(y[k], h.x, h.y, p);
         __syncthreads();
     }
 #pragma unroll 1
@@ -462,7 +465,7 @@ __global__ void __launch_bounds__(C * (1 << (LA - LT)))
             const ulonglong2 h = kc->dn_hat[i][j];
 #pragma unroll
             for (int k = 0; k < K; k++)
-                y[k] += shoup_lazy(st[(i * M + first_idx<LA, LT>(t, k)) * C + jc], h.x, h.y, q);
+                y[k] += shoup_lazy(st[(i * K + k) * NT + tid], h.x, h.y, q);
         }
 #pragma unroll
         for (int k = 0; k < K; k++) y[k] = red6(y[k], q);
