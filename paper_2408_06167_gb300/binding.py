@@ -441,11 +441,17 @@ def bm_result_info(r):
     return a.value, b.value, bool(c.value)
 
 
-def bm_result_export(r, query_index):
+def bm_result_export(r, query_index, out=None):
+    """Score ciphertexts of one query, [n_out][2][1][N] uint64; into `out` when given
+    (a C-contiguous uint64 array of that size, e.g. a view of page-locked memory)."""
     _, n_out, _ = bm_result_info(r)
-    out = np.zeros((n_out, 2, 1, r.owner.n), dtype=np.uint64)
+    shape = (n_out, 2, 1, r.owner.n)
+    if out is None:
+        out = np.empty(shape, dtype=np.uint64)
+    elif out.dtype != np.uint64 or not out.flags.c_contiguous or out.size != int(np.prod(shape)):
+        raise ValueError(f"out must be a C-contiguous uint64 array of {shape}")
     _check(_L.bm_result_export(r.ptr, query_index, _u64p(out), out.size))
-    return out
+    return out.reshape(shape)
 
 
 def bm_decrypt_scores(ctx, sk, r, query_index, n_ids):

@@ -1212,6 +1212,7 @@ struct Plan {
     uint64_t *ext = nullptr, *R = nullptr; // hoisted Algorithm 1: query extensions, rotated queries
     uint64_t *ext2 = nullptr, *rot = nullptr; // hoisted rounds after HE-C^3: extensions, rotated copies
     size_t hsrc = 0, helem = 0;            // ... their capacities (ciphertexts)
+    uint64_t *packs = nullptr;             // compression outputs before the coefficient-domain rescale
     uint64_t *scratch = nullptr, *result = nullptr;
     size_t scratch_words = 0, result_words = 0, qin_words = 0;
     PtrArena arena;
@@ -1258,6 +1259,12 @@ struct SchedView {
     const ulonglong2* d_circ_tw_ext = nullptr;
     const uint64_t* d_cmask = nullptr;
 };
+
+// The double-hoisted linear compression at level 1 writes its packs to a buffer of
+// their own and ends with the rescale in the coefficient domain.
+static bool coef_tail(const Context& c, const SchedView& g) {
+    return g.compress && g.hcomp && g.dhoist && g.level == 2 && rescale_coef_supported(c);
+}
 
 static SchedView view_of(const Gallery& g) {
     SchedView v;
@@ -1399,14 +1406,15 @@ struct MatchRun {
     // (dst[t] += sum).  Targets may be sources: the sums follow every rotation.
     void hoisted_round(uint32_t level, const std::vector<uint64_t*>& srcs, const std::vector<uint32_t>& e_src,
                        const std::vector<int32_t>& e_rot, const std::vector<uint64_t*>& tgts,
-                       const std::vector<std::vector<uint32_t>>& t_elems) {
+                       const std::vector<std::vector<uint32_t>>& t_elems,
+                       const std::vector<uint64_t*>* outs = nullptr) {
         const size_t ew = ks_ext_words(c, level), cwl = cw(level);
         for (size_t s0 = 0; s0 < srcs.size(); s0 += ksb) {
             std::vector<uint64_t*> chunk(srcs.begin() + s0, srcs.begin() + std::min(srcs.size(), s0 + ksb));
             modup_batch(level, chunk, pl.ext2 + s0 * ew);
         }
         if (g.dhoist) {
-            double_hoisted_sums(level, srcs, e_src, e_rot, tgts, t_elems);
+            double_hoisted_sums(level, srcs, e_src, e_rot, tgts, t_elems, outs);
             return;
         }
         std::vector<uint64_t*> ext_of, src, keys, gal, out;
@@ -1430,12 +1438,15 @@ struct MatchRun {
     // in Q_l u P and moved down once, in place; targets in chunks of ksb
     void double_hoisted_sums(uint32_t level, const std::vector<uint64_t*>& srcs, const std::vector<uint32_t>& e_src,
                              const std::vector<int32_t>& e_rot, const std::vector<uint64_t*>& tgts,
-                             const std::vector<std::vector<uint32_t>>& t_elems) {
+                             const std::vector<std::vector<uint32_t>>& t_elems,
+                             const std::vector<uint64_t*>* outs = nullptr) {
+        // with outs, target t + its sum goes to outs[t] (every target, a zero sum for
+        // those without elements); else the targets are updated in place
         const size_t ew = ks_ext_words(c, level);
-        std::vector<uint64_t*> ext_of, src, keys, gal, tg, off{reinterpret_cast<uint64_t*>((uintptr_t)0)};
+        std::vector<uint64_t*> ext_of, src, keys, gal, tg, to, off{reinterpret_cast<uint64_t*>((uintptr_t)0)};
         std::vector<uint32_t> t_off{0};
         for (size_t t = 0; t < tgts.size(); t++) {
-            if (t_elems[t].empty()) continue;
+            if (t_elems[t].empty() && !outs) continue;
             for (uint32_t e : t_elems[t]) {
                 ext_of.push_back(pl.ext2 + (size_t)e_src[e] * ew);
                 src.push_back(srcs[e_src[e]]);
@@ -1443,6 +1454,7 @@ struct MatchRun {
                 gal.push_back(reinterpret_cast<uint64_t*>((uintptr_t)galois_of(c, e_rot[e])));
             }
             tg.push_back(tgts[t]);
+            if (outs) to.push_back((*outs)[t]);
             off.push_back(reinterpret_cast<uint64_t*>((uintptr_t)ext_of.size()));
             t_off.push_back((uint32_t)ext_of.size());
         }
@@ -1451,6 +1463,7 @@ struct MatchRun {
         auto dk = pl.arena.list(keys);
         auto dg = pl.arena.list(gal);
         auto dt = pl.arena.list(tg);
+        auto dto = outs ? pl.arena.list(to) : nullptr;
         auto doff = pl.arena.list(off);
         for (size_t t0 = 0; t0 < tg.size(); t0 += ksb) {
             const uint32_t T = (uint32_t)std::min<size_t>(ksb, tg.size() - t0);
@@ -1464,7 +1477,7 @@ struct MatchRun {
             check(ks_ipsum_hoisted(c, level, T, (const uint64_t*)(doff + t0), E, (const uint64_t* const*)de,
                                    (const uint64_t* const*)ds, (const uint64_t* const*)dk, (const uint64_t*)dg,
                                    pl.scratch, s));
-            check(ks_moddown_add(c, level, T, dt + t0, pl.scratch, s));
+            check(ks_moddown_add(c, level, T, dt + t0, pl.scratch, s, dto ? dto + t0 : nullptr));
         }
     }
     // ... rotations of the extended queries (per element: extension, source, key, Galois element)
@@ -1664,6 +1677,7 @@ struct MatchRun {
             const uint32_t lc = lg - 1;
             std::vector<uint64_t*> mp(b.size(), const_cast<uint64_t*>(g.d_cmask));
             mulplain_batch(lc, b, mp, b);
+            std::vector<uint64_t*> packs;
             if (g.hcomp) {
                 // linear form: every group r > 0 of a pack rotated right by r in one hoisted round,
                 // summed into the pack's first group
@@ -1682,7 +1696,13 @@ struct MatchRun {
                             srcs.push_back(pl.accB + ((size_t)q * G + k + r) * cw(lc));
                         }
                     }
-                if (!srcs.empty()) hoisted_round(lc, srcs, e_src, e_rot, heads, t_elems);
+                if (coef_tail()) {
+                    // the packs to a contiguous buffer for the coefficient-domain rescale below
+                    for (size_t p = 0; p < heads.size(); p++) packs.push_back(pl.packs + p * cw(lc));
+                    hoisted_round(lc, srcs, e_src, e_rot, heads, t_elems, &packs);
+                } else if (!srcs.empty()) {
+                    hoisted_round(lc, srcs, e_src, e_rot, heads, t_elems);
+                }
             }
             // tree of right rotations: level bb pairs r and r + 2^bb (r = 0 mod 2^(bb+1)) inside each pack
             for (uint32_t bb = 0; !g.hcomp && (1u << bb) < part; bb++) {
@@ -1702,12 +1722,27 @@ struct MatchRun {
                     heads.push_back(pl.accB + ((size_t)q * G + k) * cw(lc));
                     outs.push_back(pl.result + ((size_t)q * n_out + (g0 + k) / part) * cw(0));
                 }
-            rescale_batch(lc, heads, outs);
+            if (coef_tail()) {
+                // the last rescale in the coefficient domain: an inverse NTT of both limbs of
+                // each pack, then (c_0 - [c_1]) * q_1^-1 into the result (the residues of the
+                // NTT-domain rescale and the inverse NTT of a6)
+                record(BM_OP_INTT, 0, packs.size() * 2 * (lc + 1));
+                if (pl.arena.live) check(ntt_inverse(c, packed(c, pl.packs, (uint32_t)packs.size() * 2, lc + 1), s));
+                auto din = pl.arena.list(packs);
+                auto dout = pl.arena.list(outs);
+                record(BM_OP_RESCALE, lc, packs.size());
+                if (pl.arena.live) check(rescale_coef(c, (uint32_t)packs.size(), din, dout, s));
+            } else {
+                rescale_batch(lc, heads, outs);
+            }
         }
-        // a6: score ciphertexts back to coefficient form
-        record(BM_OP_INTT, 0, (size_t)Q * n_out * 2);
-        if (pl.arena.live) check(ntt_inverse(c, limbs_of(pl.result, Q * n_out * 2, 1, c.n), s));
+        // a6: score ciphertexts back to coefficient form (done above with the coefficient-domain rescale)
+        if (!coef_tail()) {
+            record(BM_OP_INTT, 0, (size_t)Q * n_out * 2);
+            if (pl.arena.live) check(ntt_inverse(c, limbs_of(pl.result, Q * n_out * 2, 1, c.n), s));
+        }
     }
+    bool coef_tail() const { return bm::coef_tail(c, g); }
 };
 
 // Buffer sizes of a plan (words) and its group chunk: whole packs, bounded by
@@ -1769,6 +1804,7 @@ static std::vector<BufSpec> plan_buffers(const Context& c, const SchedView& g, P
     b.push_back({&pl.accA, (size_t)Q * pl.chunk * ct_words(c, lg)});
     b.push_back({&pl.accB, (size_t)Q * pl.chunk * ct_words(c, lg - 1)});
     if (g.encrypted) b.push_back({&pl.accT, (size_t)Q * pl.chunk * ct_words(c, lg)});
+    if (coef_tail(c, g)) b.push_back({&pl.packs, (size_t)Q * ((pl.chunk + g.part - 1) / g.part) * ct_words(c, 1)});
     if (pl.hsrc) {
         b.push_back({&pl.ext2, pl.hsrc * ks_ext_words(c, lg - 1)});
         b.push_back({&pl.rot, pl.helem * ct_words(c, lg - 1)});

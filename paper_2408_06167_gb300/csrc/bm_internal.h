@@ -16,6 +16,28 @@
 
 namespace bm {
 
+// Page-locked host memory from a caching pool: cudaMallocHost on a miss, freed
+// blocks kept by exact size (up to 2 GiB in all) for the next request of that
+// size, so a host ciphertext is copied to and from the device by DMA without a
+// page-locking call per object.  Pageable memory when page-locking fails (no
+// device).  Thread-safe.
+void* pinned_alloc(size_t bytes);
+void pinned_free(void* p, size_t bytes);
+template <class T>
+struct PinnedAlloc {
+    using value_type = T;
+    PinnedAlloc() = default;
+    template <class U>
+    PinnedAlloc(const PinnedAlloc<U>&) {}
+    T* allocate(size_t n) { return static_cast<T*>(pinned_alloc(n * sizeof(T))); }
+    void deallocate(T* p, size_t n) { pinned_free(p, n * sizeof(T)); }
+    template <class U>
+    bool operator==(const PinnedAlloc<U>&) const { return true; }
+    template <class U>
+    bool operator!=(const PinnedAlloc<U>&) const { return false; }
+};
+using HostWords = std::vector<uint64_t, PinnedAlloc<uint64_t>>;
+
 constexpr int MAXB = BM_MAX_Q + BM_MAX_P;   // primes in the full basis Q_L u P
 constexpr int MAXD = 4;                     // key-switching digits
 constexpr int MAXDS = 3;                    // limbs per digit
@@ -187,7 +209,7 @@ struct Gallery {
 struct Ciphertext {
     Context* ctx;
     uint32_t n_cts = 1, level = 0;
-    std::vector<uint64_t> host;               // [n_cts][2][level+1][N] coefficient form
+    HostWords host;                           // [n_cts][2][level+1][N] coefficient form, page-locked
     uint64_t* d_coef = nullptr;               // optional staged device copy, coefficient form
     ~Ciphertext();
 };
@@ -359,7 +381,7 @@ cudaError_t ks_rotate_hoisted(const Context& c, uint32_t level, uint32_t E, cons
 // elements e in [off[t], off[t+1]) (rotation of src_of[e] by gal_of[e] with key
 // key_of[e] from the extension ext_of[e]; off on the device, absolute element
 // indices) with P * sigma(c0); ks_moddown_add moves the sums down and adds them
-// to tgt[t] in place.  Targets may be sources.
+// to tgt[t] in place (or writes tgt[t] + the result to d_out[t]).  Targets may be sources.
 // (ntt_out: the sums left in NTT form on every limb, written to scratch as [T][2][nlx][N])
 cudaError_t ks_ipsum_hoisted(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
                              const uint64_t* const* ext_of, const uint64_t* const* src_of,
@@ -373,7 +395,7 @@ size_t ks_mdr_scratch_words(const Context& c, uint32_t T);
 cudaError_t ks_moddown_rescale(const Context& c, uint32_t T, uint64_t* e, uint64_t* const* d_out, uint64_t* scratch,
                                cudaStream_t s);
 cudaError_t ks_moddown_add(const Context& c, uint32_t level, uint32_t T, uint64_t* const* d_tgt, uint64_t* scratch,
-                           cudaStream_t s);
+                           cudaStream_t s, uint64_t* const* d_out = nullptr);
 // rescale in three fused kernels (rings 2^12 and 2^16)
 cudaError_t rescale_fused(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,
                           uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s);
@@ -406,6 +428,10 @@ cudaError_t circ_prepare(const Context& c, uint32_t n_in, uint32_t l1, const uin
 // masks [n_in][L+1][N] (NTT + Montgomery) extended to Q_L u P: ext [n_in][L+1+alpha][N],
 // the special limbs from the centred integer coefficients of the q_0 limb; synchronises s
 cudaError_t masks_extend(const Context& c, uint32_t n_in, const uint64_t* masks, uint64_t* ext, cudaStream_t s);
+// the last rescale in the coefficient domain: in[b] level-1 ciphertexts (coefficient
+// form) -> out[b] at level 0, the residues of rescale + inverse NTT (needs q_1 < q_0)
+bool rescale_coef_supported(const Context& c);
+cudaError_t rescale_coef(const Context& c, uint32_t B, uint64_t* const* in, uint64_t* const* out, cudaStream_t s);
 // E0[q] = P * in[q] on Q_L u P (special limbs 0): in[q] [2][L+1][N], E0 [Q][2][L+1+alpha][N], NTT form
 cudaError_t lift_p(const Context& c, uint32_t Q, uint64_t* const* in, uint64_t* E0, cudaStream_t s);
 // dst[t] += sum of src[off[t] .. off[t+1]) (ciphertexts at `level`; off and the lists on the device)

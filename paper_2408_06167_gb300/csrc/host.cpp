@@ -15,7 +15,11 @@
 //    computed by an iterative radix-2 FFT.
 #include <cmath>
 #include <complex>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "bm_internal.h"
@@ -256,6 +260,65 @@ void decode_real(const Context& ctx, const double* coeffs, double scale, double*
     for (uint32_t k = 0; k < n; k++) w[k] = T.zeta[k] * (coeffs[k] / scale);
     fft(T, w.data(), n, +1);   // value at zeta^(2t+1)
     for (uint32_t j = 0; j < ctx.slots; j++) z[j] = w[T.pos[j]].real();
+}
+
+// ---- page-locked host memory (caching pool) ----
+namespace {
+struct PinnedPool {
+    std::mutex mu;
+    std::unordered_map<size_t, std::vector<void*>> free_blocks;   // exact size -> blocks
+    std::unordered_map<void*, bool> pageable;                     // fallback blocks from malloc
+    size_t cached = 0;
+    static constexpr size_t kMaxCached = (size_t)2 << 30;
+};
+PinnedPool& pool() {
+    static PinnedPool* p = new PinnedPool();   // never destroyed: blocks may be freed during exit
+    return *p;
+}
+}  // namespace
+
+void* pinned_alloc(size_t bytes) {
+    if (bytes == 0) bytes = 1;
+    PinnedPool& P = pool();
+    {
+        std::lock_guard<std::mutex> g(P.mu);
+        auto it = P.free_blocks.find(bytes);
+        if (it != P.free_blocks.end() && !it->second.empty()) {
+            void* p = it->second.back();
+            it->second.pop_back();
+            P.cached -= bytes;
+            return p;
+        }
+    }
+    void* p = nullptr;
+    if (cudaMallocHost(&p, bytes) == cudaSuccess) return p;
+    cudaGetLastError();   // clear the failed call's error
+    p = std::malloc(bytes);
+    if (!p) throw std::bad_alloc();
+    std::lock_guard<std::mutex> g(P.mu);
+    P.pageable[p] = true;
+    return p;
+}
+
+void pinned_free(void* p, size_t bytes) {
+    if (!p) return;
+    if (bytes == 0) bytes = 1;
+    PinnedPool& P = pool();
+    {
+        std::lock_guard<std::mutex> g(P.mu);
+        auto pg = P.pageable.find(p);
+        if (pg != P.pageable.end()) {
+            P.pageable.erase(pg);
+            std::free(p);
+            return;
+        }
+        if (P.cached + bytes <= PinnedPool::kMaxCached) {
+            P.free_blocks[bytes].push_back(p);
+            P.cached += bytes;
+            return;
+        }
+    }
+    cudaFreeHost(p);
 }
 
 }  // namespace bm

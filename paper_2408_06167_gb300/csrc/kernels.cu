@@ -534,7 +534,8 @@ __global__ void __launch_bounds__(kMacThreads) k_mac(const uint64_t* __restrict_
     const size_t p_g = (size_t)n_in * ln;                    // stride of P: group (part: ln)
     const uint64_t* tp = T + (size_t)t.q0 * t_q + (size_t)t.j * n + t.p;
     const uint64_t* pp = P + (size_t)t.g0 * p_g + (size_t)t.j * n + t.p;
-    // the words of U parts are loaded before their products (U by the tile's registers)
+    // the words of U parts are loaded before their products (U by the tile's registers;
+    // deeper prefetch of the 4 x 1 tile measured slower)
     constexpr int W = 2 * QT + GT, U = W * 4 <= 24 ? 4 : (W * 2 <= 12 ? 2 : 1);
     Acc60 a0[QT][GT], a1[QT][GT];
     for (uint32_t i0 = 0; i0 < n_in; i0 += kFold60Every) {
@@ -733,6 +734,24 @@ __global__ void __launch_bounds__(kMacThreads) k_mac_circ(const uint64_t* const*
         const size_t ob = ((size_t)qi * n_in + i) * 2 * ln + (size_t)j * n + p;
         t0[ob] = redc(s0[o], q, qn);
         t0[ob + ln] = redc(s1[o], q, qn);
+    }
+}
+
+// The last rescale of the match in the coefficient domain: in[b] a level-1 ciphertext
+// [2][2][N] in coefficient form, out[b] its rescale [2][N] at level 0:
+// out = (c_0 - [c_1]_centred) * q_1^-1 mod q_0 -- the residues of the NTT-domain
+// rescale followed by the inverse NTT.  Grid (B * 2, chunks of a limb).
+__global__ void k_rescale_coef(uint64_t* const* in, uint64_t* const* out, uint64_t q0, uint64_t q1, ulonglong2 q1inv,
+                               uint32_t n) {
+    const uint32_t b = blockIdx.x / 2, comp = blockIdx.x % 2;
+    pdl_wait();
+    const uint64_t* c = in[b] + (size_t)comp * 2 * n;
+    uint64_t* o = out[b] + (size_t)comp * n;
+    const uint64_t half = q1 >> 1;
+    for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x) {
+        const uint64_t r = c[n + i];                              // [0, q_1), q_1 < q_0
+        const uint64_t lift = r > half ? q0 - (q1 - r) : r;       // the centred representative mod q_0
+        o[i] = shoup(subm(c[i], lift, q0), q1inv.x, q1inv.y, q0);
     }
 }
 
@@ -1397,6 +1416,20 @@ cudaError_t mac_circ(const Context& c, uint32_t level, uint32_t Q, uint32_t n_in
     else
         pdl_launch(k_mac_circ<OC, false>, g, kMacThreads, 0, s, R, masks, t0, n_in, level, c.tab, c.log_n);
     return cudaGetLastError();
+}
+
+// q_1 < q_0 follows from the bit sizes (a b-bit prime lies in [2^(b-1), 2^b)); the
+// host-only plan estimate has the sizes but no primes
+bool rescale_coef_supported(const Context& c) { return c.L >= 1 && c.params.q_bits[1] < c.params.q_bits[0]; }
+
+cudaError_t rescale_coef(const Context& c, uint32_t B, uint64_t* const* in, uint64_t* const* out, cudaStream_t s) {
+    if (!B) return cudaSuccess;
+    if (!rescale_coef_supported(c)) return cudaErrorInvalidValue;
+    const uint64_t q0 = c.primes[0], q1 = c.primes[1];
+    const uint64_t inv = h_invmod(q1 % q0, q0);
+    ProfScope ps(BM_KERNEL_RESCALE, s, 8.0 * c.n * B * 2 * 3, 16.0 * c.n * B * 2);
+    return pdl_launch(k_rescale_coef, dim3(B * 2, c.n / kThreads / 4), kThreads, 0, s, in, out, q0, q1,
+                      make_ulonglong2(inv, h_shoup_companion(inv, q0)), (uint32_t)c.n);
 }
 
 cudaError_t lift_p(const Context& c, uint32_t Q, uint64_t* const* in, uint64_t* E0, cudaStream_t s) {

@@ -831,10 +831,11 @@ cudaError_t ks_ipsum_launch(const Context& c, uint32_t level, uint32_t T, const 
 }
 
 // ModDown of the T sums in scratch and tgt[t] += the result, F5 + F6 (in place: F6
-// reads each target word before writing it, and no sigma(c0) term -- F4s holds it).
+// reads each target word before writing it, and no sigma(c0) term -- F4s holds it);
+// with d_out the sum tgt[t] + result goes to out[t] instead.
 template <int LA, int LB, int LT, int C, int R>
 cudaError_t ks_moddown_add_launch(const Context& c, uint32_t level, uint32_t T, uint64_t* const* d_tgt,
-                                  uint64_t* scratch, cudaStream_t s) {
+                                  uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s) {
     constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
     const KsLevelConst& K = c.h_ksc[level];
     const uint32_t l1 = level + 1, nlx = K.nlx, alpha = c.alpha;
@@ -856,8 +857,8 @@ cudaError_t ks_moddown_add_launch(const Context& c, uint32_t level, uint32_t T, 
     }
     {
         ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * T * l1 * 8, bf_r * T * 2 * l1 + kShoupMul * N * T * 2 * l1);
-        pdl_launch(k_ks_f6<LA, LB, LT, R>, dim3(T * l1, N1 / R), tr, 0, s, conv, acc, nullptr, d_tgt, d_tgt, kc, c.tab,
-                   l1, 0u, nullptr, nullptr);
+        pdl_launch(k_ks_f6<LA, LB, LT, R>, dim3(T * l1, N1 / R), tr, 0, s, conv, acc, nullptr, d_out ? d_out : d_tgt,
+                   d_tgt, kc, c.tab, l1, 0u, nullptr, nullptr);
     }
     return cudaGetLastError();
 }
@@ -963,10 +964,10 @@ cudaError_t ks_moddown_rescale(const Context& c, uint32_t T, uint64_t* e, uint64
 }
 
 cudaError_t ks_moddown_add(const Context& c, uint32_t level, uint32_t T, uint64_t* const* d_tgt, uint64_t* scratch,
-                           cudaStream_t s) {
+                           cudaStream_t s, uint64_t* const* d_out) {
     if (T == 0) return cudaSuccess;
-    if (c.log_n == 16) return ks_moddown_add_launch<8, 8, 2, 2, 2>(c, level, T, d_tgt, scratch, s);
-    if (c.log_n == 12) return ks_moddown_add_launch<6, 6, 2, 8, 8>(c, level, T, d_tgt, scratch, s);
+    if (c.log_n == 16) return ks_moddown_add_launch<8, 8, 2, 2, 2>(c, level, T, d_tgt, d_out, scratch, s);
+    if (c.log_n == 12) return ks_moddown_add_launch<6, 6, 2, 8, 8>(c, level, T, d_tgt, d_out, scratch, s);
     return cudaErrorInvalidValue;
 }
 
