@@ -708,11 +708,19 @@ class Evaluator:
         return out
 
     def expand_query_fused(self, ct, n_in, s, mask_slots):
-        """Algorithm 1 with its key switches and rescale fused: E_j =
+        """Algorithm 1 with its key switches and rescale fused: T_i =
+        moddown_rescale(e_i) for the e_i of expand_query_ext, the parts of Algorithm 1
+        at level L - 1."""
+        L = ct.level
+        return [Ciphertext(*moddown_rescale(self.ctx, e, L), L - 1, ct.scale)
+                for e in self.expand_query_ext(ct, n_in, s, mask_slots)]
+
+    def expand_query_ext(self, ct, n_in, s, mask_slots):
+        """Algorithm 1 up to its division, in the extended basis: E_j =
         hoisted_products_ext(ct, j*s) for j < n_in, the masks mask_slots(i) encoded
         at scale q_L with their integer coefficients reduced on every prime of
-        Q_L u P, e_i = sum_j E_j * mask_((i-j) mod n_in) there, and
-        T_i = moddown_rescale(e_i): the parts of Algorithm 1 at level L - 1."""
+        Q_L u P, and e_i = sum_j E_j * mask_((i-j) mod n_in) there (NTT form,
+        e_i[comp] of shape (|Q_L u P|, N)); e_i / (q_L * P) is part i."""
         ctx, L = self.ctx, ct.level
         ext_idx = ctx.ext_index(L)
         E = self.hoisted_products_ext(ct, [s * j for j in range(n_in)])
@@ -729,9 +737,26 @@ class Evaluator:
                     t = ctx.primes[gi]
                     for comp in range(2):
                         e[comp, jj] = add_mod(e[comp, jj], pointwise_mul(E[s * j][comp, jj], M[jj], t), t)
-            c0, c1 = moddown_rescale(ctx, e, L)
-            outs.append(Ciphertext(c0, c1, L - 1, ct.scale))
+            outs.append(e)
         return outs
+
+    def hec3_deferred(self, e_parts, pts, ct):
+        """HE-C^3's sum of products on the parts of Algorithm 1 before their division:
+        sum_i e_i * pt_i on Q_L u P (L = ct.level; the plaintexts' integer
+        coefficients reduced on every prime there, extend_plaintext), divided once by
+        q_(L-1) * q_L * P (moddown_rescale with two q-primes dropped): the product of
+        Algorithm 2 and its rescale, at level L - 2."""
+        ctx, L = self.ctx, ct.level
+        ext_idx = ctx.ext_index(L)
+        acc = np.zeros((2, len(ext_idx), ctx.n), dtype=np.uint64)
+        for e, pt in zip(e_parts, pts):
+            X = extend_plaintext(ctx, pt, L)
+            for jj, gi in enumerate(ext_idx):
+                t = ctx.primes[gi]
+                for comp in range(2):
+                    acc[comp, jj] = add_mod(acc[comp, jj], pointwise_mul(e[comp, jj], X[jj], t), t)
+        c0, c1 = moddown_rescale(ctx, acc, L, drop=2)
+        return Ciphertext(c0, c1, L - 2, ct.scale * pts[0].scale / ctx.q[L - 1])
 
     def apply_galois(self, ct, k):
         ctx, lvl = self.ctx, ct.level
@@ -777,27 +802,40 @@ def moddown(ctx, acc, level):
     return out[0], out[1]
 
 
-def moddown_rescale(ctx, e, level):
+def moddown_rescale(ctx, e, level, drop=1):
     """ModDown and Rescale in one step: e[comp] (limbs of Q_level u P, NTT form) divided
-    by S = q_level * P with the special set {q_level} u P, out_j = (x_j - Conv_S->q_j([x]_S))
-    * S^{-1} mod q_j for j < level (coefficient form).  The same fast base conversion
-    as moddown; e / S carries the message of e / P rescaled by q_level."""
+    by S = q_(level-drop+1) * ... * q_level * P with the special set {q_(level-drop+1),
+    ..., q_level} u P, out_j = (x_j - Conv_S->q_j([x]_S)) * S^{-1} mod q_j for
+    j <= level - drop (coefficient form).  The same fast base conversion as moddown;
+    e / S carries the message of e / P rescaled by the dropped q-primes."""
     ext = ctx.ext_index(level)
-    spec = [level] + list(range(level + 1, level + 1 + ctx.alpha))          # positions in ext
+    nt = level + 1 - drop                                                    # target limbs
+    spec = list(range(nt, level + 1 + ctx.alpha))                            # positions in ext
     sp_primes = [ctx.primes[ext[j]] for j in spec]
     S = math.prod(sp_primes)
     out = []
     for comp in range(2):
         x = np.stack([ctx.intt(e[comp, jj], gi) for jj, gi in enumerate(ext)])
         xs = np.stack([x[j] for j in spec])
-        res = _u64((level, ctx.n))
-        for j in range(level):
+        res = _u64((nt, ctx.n))
+        for j in range(nt):
             qj = ctx.q[j]
             conv = bconv(xs, sp_primes, qj)
             s_inv = pow(S % qj, -1, qj)
             res[j] = scalar_mul(sub_mod(x[j], conv, qj), s_inv, qj)
         out.append(res)
     return out[0], out[1]
+
+
+def extend_plaintext(ctx, pt, level):
+    """The integer coefficients of pt -- the centred residues of its q_0 limb, exact
+    while they lie within q_0 / 2 -- reduced on every prime of Q_level u P, NTT form
+    (one row per prime of ctx.ext_index(level))."""
+    q0 = ctx.q[0]
+    v = np.asarray(pt.limbs[0], dtype=np.uint64)
+    c = v.astype(np.int64)
+    c[v > np.uint64(q0 // 2)] -= np.int64(q0)
+    return [ctx.ntt(signed_to_mod(c, ctx.primes[gi]), gi) for gi in ctx.ext_index(level)]
 
 
 def keyswitch(ctx, c, level, key):

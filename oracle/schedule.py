@@ -204,6 +204,12 @@ def expand_query_fused(ev, ct, m, s):
     return ev.expand_query_fused(ct, m // s, s, lambda i: alg1_mask_slots(m, s, i, ct_slots(ev)))
 
 
+def expand_query_ext(ev, ct, m, s):
+    """The fused Algorithm 1 up to its division: the N_in sums e_i on Q_L u P
+    (Evaluator.expand_query_ext); e_i / (q_L * P) is part i of expand_query_fused."""
+    return ev.expand_query_ext(ct, m // s, s, lambda i: alg1_mask_slots(m, s, i, ct_slots(ev)))
+
+
 def ct_slots(ev):
     return ev.ctx.slots
 
@@ -274,6 +280,20 @@ def hec3(ev, cu, cs, s, rescale_each_part=False, encrypted_gallery=False, lazy_r
     return acc
 
 
+def hec3_deferred(ev, e_parts, cs, s, query_ct, rotsum="doubling"):
+    """Algorithm 2 for one group on the undivided parts of the fused Algorithm 1:
+    the sum of products on Q_L u P with one division by q_(L-1) * q_L * P
+    (Evaluator.hec3_deferred), then the rotate-and-sum as in hec3.  The same
+    message as hec3 on expand_query_fused's parts; one division per group in place
+    of one per part and the rescale."""
+    acc = ev.hec3_deferred(e_parts, cs, query_ct)
+    if rotsum in ("hoisted", "double"):
+        return rotsum_hoisted(ev, acc, s, double=rotsum == "double")
+    for t in range(1, log2i(s) + 1):
+        acc = ev.add(ev.rotate(acc, 1 << (t - 1)), acc)
+    return acc
+
+
 def compress(ev, accs, mask_m, s, tree=True, final_rescale=True, hoisted=False):
     """Compression: mask each group output and pack s groups per ciphertext.
     hoisted=True: the linear form with every group's rotation taken in one
@@ -315,10 +335,21 @@ def match(ev, query_cts, gallery_pts, masks, mask_m, m, s, expanded=False,
     """Full server-side match for one query.
 
     query_cts: [ct] (tiled, run through Algorithm 1) or the N_in client-expanded cts.
-    hoisted: False (the printed doubling order), True (hoisted rotations) or
-    "fused" (hoisted rotations with their ModDown and the rescale fused).
+    hoisted: False (the printed doubling order), True (hoisted rotations),
+    "fused" (hoisted rotations with their ModDown and the rescale fused) or
+    "deferred" (the fused form with its division moved past HE-C^3's products).
     gallery_pts[g][i]: plaintext of group g, part i.
     Returns (outputs, packed): the score ciphertexts and whether they are packed."""
+    rotsum = ("double" if double_hoisted else "hoisted") if hoisted_rotsum else "doubling"
+    if hoisted_compress and double_hoisted:
+        hoisted_compress = "double"
+    if hoisted == "deferred" and not expanded:
+        e_parts = expand_query_ext(ev, query_cts[0], m, s)
+        accs = [hec3_deferred(ev, e_parts, gallery_pts[g], s, query_cts[0], rotsum=rotsum)
+                for g in range(len(gallery_pts))]
+        if accs[0].level >= 1 and mask_m is not None:
+            return compress(ev, accs, mask_m, s, tree=tree, hoisted=hoisted_compress), True
+        return accs, False
     if expanded:
         cu = query_cts
     elif hoisted == "fused":
@@ -327,9 +358,6 @@ def match(ev, query_cts, gallery_pts, masks, mask_m, m, s, expanded=False,
         cu = expand_query_hoisted(ev, query_cts[0], masks, m, s)
     else:
         cu = expand_query(ev, query_cts[0], masks, m, s)
-    rotsum = ("double" if double_hoisted else "hoisted") if hoisted_rotsum else "doubling"
-    if hoisted_compress and double_hoisted:
-        hoisted_compress = "double"
     accs = [hec3(ev, cu, gallery_pts[g], s, rescale_each_part, encrypted_gallery, rotsum=rotsum)
             for g in range(len(gallery_pts))]
     if accs[0].level >= 1 and mask_m is not None:
@@ -407,6 +435,21 @@ class CountingEvaluator:
         for _ in range(n_in):
             self._rec("ModDownRes", L)
         return [SymCt(L - 1) for _ in range(n_in)]
+
+    def expand_query_ext(self, ct, n_in, s, mask_slots):
+        L = ct.level
+        if n_in > 1:
+            self._rec("ModUp", L)
+        for _ in range(n_in - 1):
+            self._rec("IPH", L)
+        self._rec("CircExt", L)
+        return [SymCt(L) for _ in range(n_in)]
+
+    def hec3_deferred(self, e_parts, pts, ct):
+        for _ in e_parts:
+            self._rec("MulPExt", ct.level)
+        self._rec("ModDownRes2", ct.level)
+        return SymCt(ct.level - 2)
 
     def rotate_sum_hoisted(self, base, terms):
         seen = set()

@@ -416,6 +416,89 @@ def test_moddown_rescale_is_the_floor_up_to_the_conversion_error():
             assert len(us) == 1 and us.pop() < spec, (comp, k)
 
 
+def test_moddown_rescale_two_primes_is_the_floor_up_to_the_conversion_error():
+    """Big-integer pin of the division by S = q_(L-1) * q_L * P (two q-primes and P
+    dropped): for the integer E (CRT over Q_L u P) of each coefficient the output on
+    q_0..q_(L-2) is floor(E / S) - u, with the same u in {0, ..., |S| - 1} on every
+    target prime."""
+    ctx = ckks.Context("small4")
+    L = ctx.L
+    ext = ctx.ext_index(L)
+    rng = np.random.default_rng(22)
+    e = np.stack([np.stack([rng.integers(0, ctx.primes[gi], ctx.n, dtype=np.uint64) for gi in ext])
+                  for _ in range(2)])
+    c0, c1 = ckks.moddown_rescale(ctx, e, L, drop=2)
+    assert c0.shape == (L - 1, ctx.n) and c1.shape == (L - 1, ctx.n)
+    prims = [ctx.primes[gi] for gi in ext]
+    S = ctx.q[L - 1] * ctx.q[L] * ctx.P
+    spec = 2 + len(ctx.p)
+    for comp, out in enumerate((c0, c1)):
+        x = np.stack([ctx.intt(e[comp, jj], gi) for jj, gi in enumerate(ext)])
+        E = [v % math.prod(prims) for v in ctx.crt(x, prims)]
+        fl = [v // S for v in E]
+        for k in range(0, ctx.n, 89):
+            us = {(fl[k] - int(out[j][k])) % ctx.q[j] for j in range(L - 1)}
+            assert len(us) == 1 and us.pop() < spec, (comp, k)
+
+
+def test_extend_plaintext_reduces_the_same_integers():
+    """A gallery plaintext at level L - 1 extended to Q_L u P: its own limbs come back
+    unchanged (so the centred q_0 residues are its integer coefficients), and every
+    limb, brought back to coefficient form, holds those integers mod its prime."""
+    ctx = ckks.Context("small4")
+    L, S, m, s = ctx.L, ctx.slots, 128, 16
+    feats = wl.gallery(300, m)
+    pt = ctx.encode(sch.gallery_slots_complex(feats, 0, 3, s, S), ctx.q[L - 1], L - 1)
+    X = ckks.extend_plaintext(ctx, pt, L)
+    ext = ctx.ext_index(L)
+    assert len(X) == L + 1 + len(ctx.p)
+    ints = [_centred(pt.limbs[0].astype(object), ctx.q[0])[k] for k in range(ctx.n)]
+    assert max(abs(v) for v in ints) < ctx.q[0] // 4
+    for jj, gi in enumerate(ext):
+        coef = ctx.intt(X[jj], gi)
+        if jj < L:
+            assert np.array_equal(coef, pt.limbs[jj]), jj
+        t = ctx.primes[gi]
+        assert all(int(coef[k]) == ints[k] % t for k in range(0, ctx.n, 61)), jj
+
+
+@pytest.mark.parametrize("m,s,R", [(16, 4, 3000), (128, 16, 2500)])
+def test_deferred_division_gives_the_fused_hec3_outputs(m, s, R):
+    """HE-C^3 on the undivided parts of the fused Algorithm 1, divided once by
+    q_(L-1) q_L P, decrypts to the same group sums as HE-C^3 on the fused parts
+    (level L - 2, the same scale), and differs from it by a small integer polynomial,
+    the same in every limb, bounded by the roundings moved:
+    3 * N_in * N * max|pt| / q_(L-1) + 4."""
+    ctx, sk, pk, ev = _setup("small4", m, s, R, extra_rots=[j * s for j in range(1, m // s)])
+    S, L, n_in = ctx.slots, ctx.L, m // s
+    feats = wl.gallery(R, m)
+    q = wl.queries(feats, 1)[0][0]
+    ct = ckks.encrypt(ctx, pk, ctx.encode(sch.tiled_query_slots(q, S), ctx.scale, L), 4, 0)
+    gal = [ctx.encode(sch.gallery_slots_complex(feats, 0, i, s, S), ctx.q[L - 1], L - 1) for i in range(n_in)]
+    e_parts = sch.expand_query_ext(ev, ct, m, s)
+    fused = sch.expand_query_fused(ev, ct, m, s)
+    want = sch.hec3(ev, fused, gal, s)
+    got = sch.hec3_deferred(ev, e_parts, gal, s, ct)
+    assert got.level == want.level == L - 2 and got.scale == want.scale
+    dw = ckks.decrypt_decode(ctx, want, sk)
+    dg = ckks.decrypt_decode(ctx, got, sk)
+    assert np.abs(dg - dw).max() < 1e-6
+    pmax = max(int(np.abs(_centred(p.limbs[0].astype(object), ctx.q[0])).max()) for p in gal)
+    bound = 3 * n_in * ctx.n * pmax // ctx.q[L - 1] + 4
+    # before the rotate-and-sum: the products and the division alone
+    a_w = ev.mul_plain(fused[0], gal[0])
+    for i in range(1, n_in):
+        a_w = ev.add(a_w, ev.mul_plain(fused[i], gal[i]))
+    a_w = ev.rescale(a_w)
+    a_g = ev.hec3_deferred(e_parts, gal, ct)
+    for comp in ("c0", "c1"):
+        diffs = [_centred(getattr(a_g, comp)[j].astype(object) - getattr(a_w, comp)[j].astype(object), ctx.q[j])
+                 for j in range(L - 1)]
+        for j in range(1, L - 1):
+            assert np.array_equal(diffs[j], diffs[0]), (comp, j)
+        assert np.abs(diffs[0]).max() <= bound, (comp, int(np.abs(diffs[0]).max()), bound)
+
+
 @pytest.mark.parametrize("m,s", [(16, 4), (128, 16), (16, 1)])
 def test_fused_expansion_gives_algorithm1_outputs(m, s):
     """Algorithm 1 with the key switches and the rescale fused decrypts to the same
