@@ -56,9 +56,12 @@ def parse():
     ap.add_argument("--auto-part", action="store_true",
                     help="serving: each gallery's part size chosen by the cost model (bm_choose_part)")
     ap.add_argument("--no-tune", action="store_true", help="skip the rotation kernel-shape tuner")
-    ap.add_argument("--expansion", default="fused", choices=["doubling", "hoisted", "fused", "auto"],
-                    help="form of Algorithm 1: the printed doubling order, the hoisted sum, or the hoisted sum "
-                         "with its key switches and rescale fused (auto: serving picks per gallery by the cost model)")
+    ap.add_argument("--expansion", default="best",
+                    choices=["doubling", "hoisted", "fused", "deferred", "best", "auto"],
+                    help="form of Algorithm 1: the printed doubling order, the hoisted sum, the hoisted sum "
+                         "with its key switches and rescale fused, or that with its division moved past HE-C^3's "
+                         "products (best: deferred when the gallery has fewer groups than parts, else fused; "
+                         "auto: serving picks per gallery by the cost model)")
     ap.add_argument("--tail", default="double", choices=["printed", "hoisted", "double"],
                     help="Algorithm 2's rotate-and-sum and the compression: the printed sequential forms, "
                          "rounds of hoisted rotations, or the same rounds with one ModDown per output "
@@ -268,9 +271,12 @@ def run_serving(args):
     expansions = {}
     for gi, (name, R, m, s) in enumerate(SERVE_GALLERIES):
         if args.expansion == "auto":
-            forms = [(e, t) for e in ("doubling", "hoisted", "fused") for t in ("printed", "hoisted", "double")]
+            forms = [(e, t) for e in ("doubling", "hoisted", "fused", "deferred") for t in ("printed", "hoisted", "double")]
+        elif args.expansion == "best" and costs is not None:
+            forms = [("fused", args.tail), ("deferred", args.tail)]   # the part size decides: the model picks
         else:
-            forms = [(args.expansion, args.tail)]
+            forms = [(resolve_expansion(args.expansion, R, m, s, packing == bm.BM_PACK_COMPLEX, ctx.n // 2),
+                      args.tail)]
         if costs is not None:
             # the cost model's part size (and, with --expansion auto, hoisted forms) for a
             # typical batch of 16 queries
@@ -283,7 +289,7 @@ def run_serving(args):
         parts[name] = s
         expansions[name] = "+".join(x for x, on in (("hoisted-expansion", flags & 1), ("hoisted-rotsum", flags & 2),
                                                     ("hoisted-compression", flags & 4), ("double-hoisted", flags & 8),
-                                                    ("fused-expansion", flags & 16))
+                                                    ("fused-expansion", flags & 16), ("deferred-division", flags & 32))
                                     if on) or "printed"
         if (m, s) not in keys:
             keys[(m, s)] = bm.bm_keygen_ex(ctx, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
@@ -356,18 +362,31 @@ def run_serving(args):
     print(json.dumps(line))
 
 
+def resolve_expansion(expansion, n_ids, dim, part, complex_pack, slots):
+    """'best': the deferred division when the gallery has fewer groups than parts (one
+    division per group instead of one per part), else the fused expansion."""
+    if expansion != "best":
+        return expansion
+    groups = -(-n_ids // ((2 if complex_pack else 1) * (slots // part)))
+    return "deferred" if groups < dim // part else "fused"
+
+
 def sched_flags(bm, expansion, tail):
     """(gallery schedule flags, model layout flags) of the chosen forms."""
-    f = bm.BM_SCHED_HOISTED_EXPANSION if expansion in ("hoisted", "fused") else 0
-    if expansion == "fused":
+    if expansion == "best":       # resolved per gallery where its size is known
+        expansion = "fused"
+    f = bm.BM_SCHED_HOISTED_EXPANSION if expansion in ("hoisted", "fused", "deferred") else 0
+    if expansion in ("fused", "deferred"):
         f |= bm.BM_SCHED_FUSED_EXPANSION
+    if expansion == "deferred":
+        f |= bm.BM_SCHED_DEFERRED_DIVISION
     if tail in ("hoisted", "double"):
         f |= bm.BM_SCHED_HOISTED_ROTSUM | bm.BM_SCHED_HOISTED_COMPRESSION
     if tail == "double":
         f |= bm.BM_SCHED_DOUBLE_HOISTED
     lay = ((bm.BM_LAYOUT_HOISTED if f & 1 else 0) | (bm.BM_LAYOUT_HOISTED_ROTSUM if f & 2 else 0)
            | (bm.BM_LAYOUT_HOISTED_COMPRESSION if f & 4 else 0) | (bm.BM_LAYOUT_DOUBLE_HOISTED if f & 8 else 0)
-           | (bm.BM_LAYOUT_FUSED_EXPANSION if f & 16 else 0))
+           | (bm.BM_LAYOUT_FUSED_EXPANSION if f & 16 else 0) | (bm.BM_LAYOUT_DEFERRED_DIVISION if f & 32 else 0))
     return f, lay
 
 
@@ -487,6 +506,7 @@ def main():
     W = wl.WORKLOADS[args.workload]
     part = args.part or W.part
     ctx = bm.bm_context_create(W.preset, local)
+    args.expansion = resolve_expansion(args.expansion, W.n_ids, W.dim, part, args.packing == "complex", ctx.n // 2)
     wide = None if args.no_tune else bm.bm_autotune_keyswitch(ctx)
     packing = bm.BM_PACK_COMPLEX if args.packing == "complex" else bm.BM_PACK_REAL
     feats = wl.gallery(W.n_ids, W.dim)

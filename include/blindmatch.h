@@ -233,7 +233,8 @@ bm_status bm_gallery_info(const bm_gallery* g, uint32_t* encrypted, uint32_t* pa
 enum {
     BM_EXPAND_DOUBLING = 0,
     BM_EXPAND_HOISTED = 1,
-    BM_EXPAND_FUSED = 2      /* hoisted, with the key switches and the rescale fused (below) */
+    BM_EXPAND_FUSED = 2,     /* hoisted, with the key switches and the rescale fused (below) */
+    BM_EXPAND_DEFERRED = 3   /* fused, with the division moved past HE-C^3's products (below) */
 };
 bm_status bm_gallery_set_expansion(bm_gallery* g, uint32_t mode);
 
@@ -256,6 +257,15 @@ bm_status bm_gallery_set_expansion(bm_gallery* g, uint32_t mode);
  *                                divided once by q_L * P -- one fused ModDown and
  *                                Rescale per part instead of a ModDown per rotation
  *                                and a rescale per part (2 <= N_in <= 32)
+ *  BM_SCHED_DEFERRED_DIVISION    with the fused expansion: the parts kept undivided
+ *                                on Q_L u P, HE-C^3's products summed there against
+ *                                the gallery plaintexts extended to Q_L u P, and each
+ *                                (query, group) sum divided once by q_(L-1) q_L P --
+ *                                one division per group instead of one per part and
+ *                                the rescale after the products; the gallery keeps a
+ *                                second copy of its plaintexts on Q_L u P (twice the
+ *                                limbs).  Fewer divisions when a gallery has fewer
+ *                                groups than parts.
  *  BM_SCHED_DOUBLE_HOISTED       with either of the two above: each round's
  *                                rotations into one output summed in the extended
  *                                basis Q_l u P and moved down once (one ModDown per
@@ -272,7 +282,8 @@ enum {
     BM_SCHED_HOISTED_ROTSUM = 2,
     BM_SCHED_HOISTED_COMPRESSION = 4,
     BM_SCHED_DOUBLE_HOISTED = 8,
-    BM_SCHED_FUSED_EXPANSION = 16
+    BM_SCHED_FUSED_EXPANSION = 16,
+    BM_SCHED_DEFERRED_DIVISION = 32
 };
 bm_status bm_gallery_set_schedule(bm_gallery* g, uint32_t flags);
 void bm_gallery_destroy(bm_gallery* g);
@@ -510,9 +521,10 @@ typedef struct bm_op_costs {
 #define BM_LAYOUT_HOISTED_ROTSUM 0x400u
 #define BM_LAYOUT_HOISTED_COMPRESSION 0x800u
 /* ... and BM_LAYOUT_DOUBLE_HOISTED for BM_SCHED_DOUBLE_HOISTED, BM_LAYOUT_FUSED_EXPANSION for
- * BM_SCHED_FUSED_EXPANSION. */
+ * BM_SCHED_FUSED_EXPANSION, BM_LAYOUT_DEFERRED_DIVISION for BM_SCHED_DEFERRED_DIVISION. */
 #define BM_LAYOUT_DOUBLE_HOISTED 0x1000u
 #define BM_LAYOUT_FUSED_EXPANSION 0x2000u
+#define BM_LAYOUT_DEFERRED_DIVISION 0x4000u
 
 /* Host only (no device needed): the launches of the match of `n_queries`
  * queries against a gallery of n_ids identities in (dim, part_size, packing) under

@@ -35,17 +35,20 @@ BM_LAYOUT_HOISTED_ROTSUM = 0x400
 BM_LAYOUT_HOISTED_COMPRESSION = 0x800
 BM_LAYOUT_DOUBLE_HOISTED = 0x1000
 BM_LAYOUT_FUSED_EXPANSION = 0x2000
+BM_LAYOUT_DEFERRED_DIVISION = 0x4000
 BM_SCHED_HOISTED_EXPANSION = 1
 BM_SCHED_HOISTED_ROTSUM = 2
 BM_SCHED_HOISTED_COMPRESSION = 4
 BM_SCHED_ALL = 7                      # every hoisted form, one ModDown per rotation
 BM_SCHED_DOUBLE_HOISTED = 8
 BM_SCHED_FUSED_EXPANSION = 16
+BM_SCHED_DEFERRED_DIVISION = 32
 BM_KEYS_ENCRYPTED_GALLERY = 1
 BM_KEYS_HOISTED = 2
 BM_EXPAND_DOUBLING = 0
 BM_EXPAND_HOISTED = 1
 BM_EXPAND_FUSED = 2
+BM_EXPAND_DEFERRED = 3
 BM_ENC_KEEP_DEVICE = 1
 PRESETS = {"toy": 0, "ring16": 1, "small4": 2}
 STATUS = ["BM_OK", "BM_E_ARG", "BM_E_PARAM", "BM_E_LEVEL", "BM_E_KEY_MISSING", "BM_E_DIM", "BM_E_OOM",
@@ -367,7 +370,7 @@ def bm_gallery_import_encrypted(ctx, cts, masks, cmask, n_ids, dim, part):
 
 def bm_gallery_set_expansion(g, mode):
     _check(_L.bm_gallery_set_expansion(g.ptr, mode))
-    g.hoisted = mode in (BM_EXPAND_HOISTED, BM_EXPAND_FUSED)
+    g.hoisted = mode in (BM_EXPAND_HOISTED, BM_EXPAND_FUSED, BM_EXPAND_DEFERRED)
 
 
 def bm_gallery_set_schedule(g, flags):

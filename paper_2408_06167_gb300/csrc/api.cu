@@ -60,6 +60,7 @@ struct Layout {
     bool hrotsum, hcomp;                    // rotate-and-sum / compression by hoisted rounds
     bool dhoist;                            // ... with one ModDown per round output
     bool fused;                             // hoisted Algorithm 1 with ModDown and Rescale fused
+    bool deferred;                          // ... with the division moved past HE-C^3's products
 };
 
 // Scale of the score ciphertexts: 2^log_scale with a plaintext gallery (every
@@ -75,7 +76,8 @@ static uint32_t gallery_kind(const Gallery& g) {
            ((g.sched & BM_SCHED_HOISTED_ROTSUM) ? BM_LAYOUT_HOISTED_ROTSUM : 0u) |
            ((g.sched & BM_SCHED_HOISTED_COMPRESSION) ? BM_LAYOUT_HOISTED_COMPRESSION : 0u) |
            ((g.sched & BM_SCHED_DOUBLE_HOISTED) ? BM_LAYOUT_DOUBLE_HOISTED : 0u) |
-           ((g.sched & BM_SCHED_FUSED_EXPANSION) ? BM_LAYOUT_FUSED_EXPANSION : 0u);
+           ((g.sched & BM_SCHED_FUSED_EXPANSION) ? BM_LAYOUT_FUSED_EXPANSION : 0u) |
+           ((g.sched & BM_SCHED_DEFERRED_DIVISION) ? BM_LAYOUT_DEFERRED_DIVISION : 0u);
 }
 
 // baby and giant steps of the hoisted rotate-and-sum over s slots: b = 2^ceil(log2(s)/2);
@@ -97,13 +99,14 @@ static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uin
                              uint32_t kind = BM_PACK_REAL) {
     const uint32_t packing = kind & ~(BM_LAYOUT_ENCRYPTED | BM_LAYOUT_HOISTED | BM_LAYOUT_HOISTED_ROTSUM |
                                       BM_LAYOUT_HOISTED_COMPRESSION | BM_LAYOUT_DOUBLE_HOISTED |
-                                      BM_LAYOUT_FUSED_EXPANSION);
+                                      BM_LAYOUT_FUSED_EXPANSION | BM_LAYOUT_DEFERRED_DIVISION);
     lo.encrypted = (kind & BM_LAYOUT_ENCRYPTED) != 0;
     lo.hoisted = (kind & BM_LAYOUT_HOISTED) != 0;
     lo.hrotsum = (kind & BM_LAYOUT_HOISTED_ROTSUM) != 0;
     lo.hcomp = (kind & BM_LAYOUT_HOISTED_COMPRESSION) != 0;
     lo.dhoist = (kind & BM_LAYOUT_DOUBLE_HOISTED) != 0;
     lo.fused = (kind & BM_LAYOUT_FUSED_EXPANSION) != 0;
+    lo.deferred = (kind & BM_LAYOUT_DEFERRED_DIVISION) != 0;
     if (!is_pow2(dim) || !is_pow2(part) || part > dim || dim > c.slots)
         return fail(BM_E_DIM, "dim and part size must be powers of two with part <= dim <= N/2");
     if (packing != BM_PACK_REAL && packing != BM_PACK_COMPLEX) return fail(BM_E_ARG, "unknown slot packing");
@@ -122,7 +125,9 @@ static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uin
     if (!lo.compress) lo.hcomp = false;
     if (!lo.hrotsum && !lo.hcomp) lo.dhoist = false;
     if (lo.fused) lo.hoisted = lo.tiled;    // the fused form is a form of the hoisted expansion
+    if (lo.deferred) lo.fused = true;       // the deferred division is a form of the fused expansion
     if (!lo.hoisted || lo.n_in < 2 || lo.n_in > kMaxCircParts || !ks_mdr_supported(c)) lo.fused = false;
+    if (!lo.fused || lo.encrypted || !ks_mdr_supported(c, 2)) lo.deferred = false;
     lo.n_out = lo.compress ? (lo.groups + part - 1) / part : lo.groups;
     return BM_OK;
 }
@@ -577,6 +582,7 @@ bm::Gallery::~Gallery() {
     if (d_circ_tw) cudaFree(d_circ_tw);
     if (d_masks_hat_ext) cudaFree(d_masks_hat_ext);
     if (d_circ_tw_ext) cudaFree(d_circ_tw_ext);
+    if (d_pts_ext) cudaFree(d_pts_ext);
     if (d_cmask) cudaFree(d_cmask);
 }
 bm::Ciphertext::~Ciphertext() {
@@ -601,7 +607,8 @@ static bm_status gallery_alloc(Context& c, const Layout& lo, uint64_t n_ids, uin
     Gallery& g = gh->g;
     g.ctx = &c;
     g.packing = packing & ~(BM_LAYOUT_ENCRYPTED | BM_LAYOUT_HOISTED | BM_LAYOUT_HOISTED_ROTSUM |
-                            BM_LAYOUT_HOISTED_COMPRESSION | BM_LAYOUT_DOUBLE_HOISTED | BM_LAYOUT_FUSED_EXPANSION);
+                            BM_LAYOUT_HOISTED_COMPRESSION | BM_LAYOUT_DOUBLE_HOISTED | BM_LAYOUT_FUSED_EXPANSION |
+                            BM_LAYOUT_DEFERRED_DIVISION);
     g.encrypted = lo.encrypted;
     g.sched = (lo.hoisted ? BM_SCHED_HOISTED_EXPANSION : 0u) | (lo.hrotsum ? BM_SCHED_HOISTED_ROTSUM : 0u) |
               (lo.hcomp ? BM_SCHED_HOISTED_COMPRESSION : 0u) | (lo.dhoist ? BM_SCHED_DOUBLE_HOISTED : 0u) |
@@ -1019,13 +1026,34 @@ bm_status bm_gallery_import_encrypted(bm_context* ctxh, const uint64_t* cts, con
 bm_status bm_gallery_set_schedule(bm_gallery* gh, uint32_t flags) {
     if (!gh) return fail(BM_E_ARG, "null gallery");
     const uint32_t all = BM_SCHED_HOISTED_EXPANSION | BM_SCHED_HOISTED_ROTSUM | BM_SCHED_HOISTED_COMPRESSION |
-                         BM_SCHED_DOUBLE_HOISTED | BM_SCHED_FUSED_EXPANSION;
+                         BM_SCHED_DOUBLE_HOISTED | BM_SCHED_FUSED_EXPANSION | BM_SCHED_DEFERRED_DIVISION;
     if (flags & ~all) return fail(BM_E_ARG, "unknown schedule flags");
     Gallery& g = gh->g;
     if ((flags & BM_SCHED_HOISTED_EXPANSION) && !g.tiled)
         return fail(BM_E_ARG, "the gallery's queries arrive expanded (no Algorithm 1 on the server)");
     if ((flags & BM_SCHED_FUSED_EXPANSION) && (!(flags & BM_SCHED_HOISTED_EXPANSION) || !g.d_masks_hat_ext))
         return fail(BM_E_ARG, "the fused expansion needs the hoisted expansion and 2..32 parts");
+    if (flags & BM_SCHED_DEFERRED_DIVISION) {
+        Context& c = *g.ctx;
+        if (!(flags & BM_SCHED_FUSED_EXPANSION) || g.encrypted || !ks_mdr_supported(c, 2))
+            return fail(BM_E_ARG, "the deferred division needs the fused expansion and a plaintext gallery");
+        if (!g.d_pts_ext) {
+            // the plaintexts' integer coefficients on every prime of Q_L u P, once
+            const size_t nlx = c.L + 1 + c.alpha, count = (size_t)g.groups * g.n_in;
+            BM_CUDA_TRY(cudaSetDevice(c.device));
+            if (cudaMalloc(&g.d_pts_ext, count * nlx * c.n * 8) != cudaSuccess) {
+                cudaGetLastError();
+                g.d_pts_ext = nullptr;
+                return fail(BM_E_OOM, "extended gallery allocation failed");
+            }
+            const cudaError_t e = extend_to_ext_basis(c, count, g.d_pts, g.level + 1, g.d_pts_ext, c.stream);
+            if (e != cudaSuccess) {
+                cudaFree(g.d_pts_ext);
+                g.d_pts_ext = nullptr;
+                return fail(BM_E_CUDA, std::string("gallery extension: ") + cudaGetErrorString(e));
+            }
+        }
+    }
     if (g.sched != flags) {
         drop_plans(*g.ctx, g.id);
         g.sched = flags;
@@ -1035,12 +1063,16 @@ bm_status bm_gallery_set_schedule(bm_gallery* gh, uint32_t flags) {
 
 bm_status bm_gallery_set_expansion(bm_gallery* gh, uint32_t mode) {
     if (!gh) return fail(BM_E_ARG, "null gallery");
-    if (mode != BM_EXPAND_DOUBLING && mode != BM_EXPAND_HOISTED && mode != BM_EXPAND_FUSED)
+    if (mode != BM_EXPAND_DOUBLING && mode != BM_EXPAND_HOISTED && mode != BM_EXPAND_FUSED &&
+        mode != BM_EXPAND_DEFERRED)
         return fail(BM_E_ARG, "unknown expansion");
-    const uint32_t rest = gh->g.sched & ~(uint32_t)(BM_SCHED_HOISTED_EXPANSION | BM_SCHED_FUSED_EXPANSION);
-    const uint32_t form = mode == BM_EXPAND_FUSED ? BM_SCHED_HOISTED_EXPANSION | BM_SCHED_FUSED_EXPANSION
-                          : mode == BM_EXPAND_HOISTED ? BM_SCHED_HOISTED_EXPANSION
-                                                      : 0u;
+    const uint32_t rest = gh->g.sched & ~(uint32_t)(BM_SCHED_HOISTED_EXPANSION | BM_SCHED_FUSED_EXPANSION |
+                                                    BM_SCHED_DEFERRED_DIVISION);
+    const uint32_t form =
+        mode == BM_EXPAND_DEFERRED ? BM_SCHED_HOISTED_EXPANSION | BM_SCHED_FUSED_EXPANSION | BM_SCHED_DEFERRED_DIVISION
+        : mode == BM_EXPAND_FUSED  ? BM_SCHED_HOISTED_EXPANSION | BM_SCHED_FUSED_EXPANSION
+        : mode == BM_EXPAND_HOISTED ? BM_SCHED_HOISTED_EXPANSION
+                                    : 0u;
     return bm_gallery_set_schedule(gh, rest | form);
 }
 
@@ -1251,7 +1283,9 @@ struct SchedView {
     bool tiled = true, compress = true, encrypted = false, hoisted = false, hrotsum = false, hcomp = false;
     bool dhoist = false;                   // hoisted rounds with one ModDown per output
     bool fused = false;                    // hoisted Algorithm 1 with ModDown and Rescale fused
+    bool deferred = false;                 // ... divided after HE-C^3's products (one division per group)
     const uint64_t* d_pts = nullptr;
+    const uint64_t* d_pts_ext = nullptr;   // the plaintexts on Q_L u P (deferred division)
     const uint64_t* d_masks = nullptr;
     const uint64_t* d_masks_hat = nullptr;
     const ulonglong2* d_circ_tw = nullptr;
@@ -1280,6 +1314,8 @@ static SchedView view_of(const Gallery& g) {
     v.hcomp = g.compress && (g.sched & BM_SCHED_HOISTED_COMPRESSION);
     v.dhoist = (v.hrotsum || v.hcomp) && (g.sched & BM_SCHED_DOUBLE_HOISTED);
     v.fused = v.hoisted && (g.sched & BM_SCHED_FUSED_EXPANSION) && g.d_masks_hat_ext;
+    v.deferred = v.fused && (g.sched & BM_SCHED_DEFERRED_DIVISION) && g.d_pts_ext;
+    v.d_pts_ext = g.d_pts_ext;
     v.d_pts = g.d_pts;
     v.d_masks = g.d_masks;
     v.d_masks_hat = g.d_masks_hat;
@@ -1304,6 +1340,7 @@ static SchedView view_of(const Layout& lo, uint32_t part) {
     v.hcomp = lo.hcomp;
     v.dhoist = lo.dhoist;
     v.fused = lo.fused;
+    v.deferred = lo.deferred;
     return v;
 }
 
@@ -1556,9 +1593,12 @@ struct MatchRun {
                         R.push_back(j == 0 ? E0 + (size_t)q * xw : pl.R + ((size_t)q * (n_in - 1) + j - 1) * xw);
                 auto dR = pl.arena.list(R);
                 record(BM_OP_MAC_CIRC, c.L, n_in, nq, n_in);
+                // deferred division: the undivided parts e_i go to T (on Q_L u P) for HE-C^3
+                uint64_t* circ_out = g.deferred ? pl.T + (size_t)qb * n_in * xw : pl.t0;
                 if (pl.arena.live)
                     check(mac_circ(c, nlx - 1, nq, n_in, (const uint64_t* const*)dR, nullptr, g.d_masks_hat_ext,
-                                   g.d_circ_tw_ext, pl.t0, s));
+                                   g.d_circ_tw_ext, circ_out, s));
+                if (g.deferred) continue;
                 for (uint32_t q = 0; q < nq; q++)
                     for (uint32_t i = 0; i < n_in; i++) outs.push_back(pl.T + ((size_t)(qb + q) * n_in + i) * cw(lg));
                 auto dout = pl.arena.list(outs);
@@ -1618,12 +1658,16 @@ struct MatchRun {
             for (uint32_t j = 1; (1u << (j - 1)) < n_in; j++) rotate_batch(lg, (int32_t)(part << (j - 1)), o1, o1, &o1);
         }
         const uint64_t* Tsrc = g.tiled ? pl.T : pl.qin;
+        const uint32_t nlx = c.L + 1 + c.alpha;
+        const size_t xw = (size_t)2 * nlx * c.n;
         // HE-C^3 per chunk of groups, then compression
         for (uint32_t g0 = 0; g0 < g.groups; g0 += pl.chunk) {
             const uint32_t G = std::min(pl.chunk, g.groups - g0);
-            record(g.encrypted ? BM_OP_MAC_CT : BM_OP_MAC, lg, G, Q, n_in);
+            record(g.encrypted ? BM_OP_MAC_CT : BM_OP_MAC, g.deferred ? c.L : lg, G, Q, n_in);
             if (pl.arena.live) {
-                if (g.encrypted)
+                if (g.deferred)   // the undivided parts times the plaintexts on Q_L u P
+                    check(mac(c, nlx - 1, Q, G, n_in, Tsrc, g.d_pts_ext + (size_t)g0 * n_in * nlx * c.n, pl.accA, s));
+                else if (g.encrypted)
                     check(mac_ct(c, lg, Q, G, n_in, Tsrc, g.d_pts + (size_t)g0 * n_in * 2 * (lg + 1) * c.n, pl.accT,
                                  pl.accA, s));
                 else
@@ -1639,7 +1683,21 @@ struct MatchRun {
             // encrypted gallery: one relinearisation of the summed tensor products,
             // (d0, d1, d2) -> (d0 + KS(d2)_0, d1 + KS(d2)_1) with t = (d0, d2), a = (0, d1)
             if (g.encrypted) rotate_batch(lg, 0, t, a, &a, true);
-            rescale_batch(lg, a, b);
+            if (g.deferred) {
+                // each (query, group) sum divided once by q_(L-1) q_L P (accA: [Q][G][2][nlx][N])
+                auto db = pl.arena.list(b);
+                for (uint32_t o0 = 0; o0 < (uint32_t)b.size(); o0 += ksb) {
+                    const uint32_t T = std::min<uint32_t>(ksb, (uint32_t)b.size() - o0);
+                    record(BM_OP_MODDOWN, c.L, T);
+                    if (!pl.arena.live) {
+                        need_scratch(ks_mdr_scratch_words(c, T));
+                        continue;
+                    }
+                    check(ks_moddown_rescale(c, T, pl.accA + (size_t)o0 * xw, db + o0, pl.scratch, s, 2));
+                }
+            } else {
+                rescale_batch(lg, a, b);
+            }
             if (g.hrotsum) {
                 // sum_{r<part} Rot(acc, r) in two hoisted rounds: baby steps 1..bs-1, giant steps bs*k
                 uint32_t bs, gs;
@@ -1763,8 +1821,8 @@ static void plan_dims(const Context& c, const SchedView& g, uint32_t n_out, uint
     // double hoisting sums the rotations in the key-switch scratch: no rotated copies
     const uint32_t copies = g.dhoist ? 0 : per_src;
     const size_t hold = per_src ? ks_ext_words(c, lg - 1) + (size_t)copies * ct_words(c, lg - 1) : 0;
-    const size_t per_group =
-        (size_t)Q * ((g.encrypted ? 2 : 1) * ct_words(c, lg) + ct_words(c, lg - 1) + hold) * 8;
+    const size_t acc_words = g.deferred ? (size_t)2 * (c.L + 1 + c.alpha) * c.n : ct_words(c, lg);
+    const size_t per_group = (size_t)Q * ((g.encrypted ? 2 : 1) * acc_words + ct_words(c, lg - 1) + hold) * 8;
     const size_t budget = (size_t)8 << 30;
     uint32_t chunk = (uint32_t)std::max<size_t>(1, budget / std::max<size_t>(per_group, 1));
     if (g.compress) chunk = std::max(g.part, chunk / g.part * g.part);
@@ -1794,14 +1852,16 @@ static std::vector<BufSpec> plan_buffers(const Context& c, const SchedView& g, P
     if (g.tiled) {
         // the fused Algorithm 1 keeps its sums on Q_L u P
         const size_t sw = g.fused ? (size_t)2 * (c.L + 1 + c.alpha) * c.n : ct_words(c, c.L);
-        b.push_back({&pl.t0, (size_t)pl.qe * g.n_in * sw});
-        b.push_back({&pl.T, (size_t)Q * g.n_in * ct_words(c, lg)});
+        // deferred division: the undivided parts of every query in T, no t0
+        b.push_back({&pl.t0, g.deferred ? 0 : (size_t)pl.qe * g.n_in * sw});
+        b.push_back({&pl.T, (size_t)Q * g.n_in * (g.deferred ? sw : ct_words(c, lg))});
         if (g.hoisted) {
             b.push_back({&pl.ext, (size_t)pl.qe * ks_ext_words(c, c.L)});
             b.push_back({&pl.R, (size_t)pl.qe * g.n_in * sw});
         }
     }
-    b.push_back({&pl.accA, (size_t)Q * pl.chunk * ct_words(c, lg)});
+    b.push_back({&pl.accA, (size_t)Q * pl.chunk *
+                               (g.deferred ? (size_t)2 * (c.L + 1 + c.alpha) * c.n : ct_words(c, lg))});
     b.push_back({&pl.accB, (size_t)Q * pl.chunk * ct_words(c, lg - 1)});
     if (g.encrypted) b.push_back({&pl.accT, (size_t)Q * pl.chunk * ct_words(c, lg)});
     if (coef_tail(c, g)) b.push_back({&pl.packs, (size_t)Q * ((pl.chunk + g.part - 1) / g.part) * ct_words(c, 1)});

@@ -41,6 +41,8 @@ using HostWords = std::vector<uint64_t, PinnedAlloc<uint64_t>>;
 constexpr int MAXB = BM_MAX_Q + BM_MAX_P;   // primes in the full basis Q_L u P
 constexpr int MAXD = 4;                     // key-switching digits
 constexpr int MAXDS = 3;                    // limbs per digit
+constexpr int MAXSP = BM_MAX_P + 1;         // special limbs of a fused division (P and up to two q-primes)
+constexpr int kMdrDrops = 2;                // fused divisions: by q_L P, and by q_(L-1) q_L P
 
 // Per-prime constants and twiddle tables, passed to kernels by value.
 struct DevTables {
@@ -75,8 +77,8 @@ struct KsLevelConst {
     uint32_t dstart[MAXD], dsz[MAXD];          // Q-limb range of each digit at this level
     ulonglong2 up_hinv[MAXD][MAXDS];           // (D/d_i)^-1 mod d_i            (Shoup pairs)
     ulonglong2 up_hat[MAXD][MAXDS][MAXB];      // (D/d_i) mod t_jj, jj over Q_l u P
-    ulonglong2 dn_hinv[BM_MAX_P];              // N^-1 (P/p_i)^-1 mod p_i
-    ulonglong2 dn_hat[BM_MAX_P][MAXB];         // (P/p_i) mod q_j
+    ulonglong2 dn_hinv[MAXSP];                 // N^-1 (P/p_i)^-1 mod p_i
+    ulonglong2 dn_hat[MAXSP][MAXB];            // (P/p_i) mod q_j
     ulonglong2 pinv[MAXB];                     // P^-1 mod q_j
     uint64_t pmont[MAXB];                      // P * 2^64 mod q_j (Montgomery form of P)
 };
@@ -109,8 +111,8 @@ struct Context {
     EncoderTables enc;
     std::vector<KsLevelConst> h_ksc;          // key-switching constants per level (host copy)
     KsLevelConst* d_ksc = nullptr;            // ... and on the device
-    KsLevelConst h_ksc_mdr{};                 // ModDown + Rescale at the top level (special set {q_L} u P)
-    KsLevelConst* d_ksc_mdr = nullptr;        //   (only nlx, dn_hinv, dn_hat and pinv are set)
+    KsLevelConst h_ksc_mdr[kMdrDrops]{};      // ModDown + Rescale at the top level, [d - 1]: special set
+    KsLevelConst* d_ksc_mdr = nullptr;        //   {q_(L-d+1)..q_L} u P (only nlx, dn_hinv, dn_hat, pinv set)
     ulonglong2* d_qlinv = nullptr;            // [level][j]: q_level^-1 mod q_j (Shoup pairs), for rescale
     uint32_t ks_wide_batch[BM_MAX_Q] = {1u << 30, 1u << 30, 1u << 30, 1u << 30, 1u << 30, 1u << 30};
                                               // per level: key-switch batches of at least this many
@@ -201,6 +203,7 @@ struct Gallery {
     uint64_t* d_masks_hat = nullptr;          // [n_in][L+1][N] their transform over the parts (circ_prepare)
     ulonglong2* d_circ_tw = nullptr;          // [L+1][n_in] twiddles of that transform
     uint64_t* d_masks_hat_ext = nullptr;      // [n_in][L+1+alpha][N] the same on Q_L u P (fused Algorithm 1)
+    uint64_t* d_pts_ext = nullptr;            // [groups][n_in][L+1+alpha][N] d_pts on Q_L u P (deferred division)
     ulonglong2* d_circ_tw_ext = nullptr;      // [L+1+alpha][n_in]
     uint64_t* d_cmask = nullptr;              // [level][N] compression mask at level-1
     ~Gallery();
@@ -388,12 +391,13 @@ cudaError_t ks_ipsum_hoisted(const Context& c, uint32_t level, uint32_t T, const
                              const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch,
                              cudaStream_t s, bool ntt_out = false);
 // ModDown and Rescale fused at the top level: e [T][2][L+1+alpha][N] (NTT form, every
-// limb; the special limbs are transformed in place) divided by q_L * P into out[t]
-// (level L - 1); scratch ks_mdr_scratch_words(c, T); needs ks_mdr_supported(c)
-bool ks_mdr_supported(const Context& c);
+// limb; the special limbs are transformed in place) divided by q_(L-drop+1)..q_L * P
+// into out[t] (level L - drop, drop 1 or 2); scratch ks_mdr_scratch_words(c, T);
+// needs ks_mdr_supported(c, drop)
+bool ks_mdr_supported(const Context& c, uint32_t drop = 1);
 size_t ks_mdr_scratch_words(const Context& c, uint32_t T);
 cudaError_t ks_moddown_rescale(const Context& c, uint32_t T, uint64_t* e, uint64_t* const* d_out, uint64_t* scratch,
-                               cudaStream_t s);
+                               cudaStream_t s, uint32_t drop = 1);
 cudaError_t ks_moddown_add(const Context& c, uint32_t level, uint32_t T, uint64_t* const* d_tgt, uint64_t* scratch,
                            cudaStream_t s, uint64_t* const* d_out = nullptr);
 // rescale in three fused kernels (rings 2^12 and 2^16)
@@ -428,6 +432,11 @@ cudaError_t circ_prepare(const Context& c, uint32_t n_in, uint32_t l1, const uin
 // masks [n_in][L+1][N] (NTT + Montgomery) extended to Q_L u P: ext [n_in][L+1+alpha][N],
 // the special limbs from the centred integer coefficients of the q_0 limb; synchronises s
 cudaError_t masks_extend(const Context& c, uint32_t n_in, const uint64_t* masks, uint64_t* ext, cudaStream_t s);
+// plaintexts in [count][l_in][N] (NTT + Montgomery, primes q_0..q_(l_in-1)) extended to
+// Q_L u P: out [count][L+1+alpha][N], limbs l_in.. from the centred integer
+// coefficients of the q_0 limb (exact while they lie within q_0 / 2); synchronises s
+cudaError_t extend_to_ext_basis(const Context& c, size_t count, const uint64_t* in, uint32_t l_in, uint64_t* out,
+                                cudaStream_t s);
 // the last rescale in the coefficient domain: in[b] level-1 ciphertexts (coefficient
 // form) -> out[b] at level 0, the residues of rescale + inverse NTT (needs q_1 < q_0)
 bool rescale_coef_supported(const Context& c);

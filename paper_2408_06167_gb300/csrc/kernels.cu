@@ -777,9 +777,9 @@ __global__ void k_lift_p(const uint64_t* const* in, uint64_t* __restrict__ E0, c
 // residue v (coefficient form): the centred x = v or v - q_0 (|x| < q_0 / 2 and
 // below every special prime), out[k][i] = x mod p_k.  Grid (alpha, chunks).
 __global__ void k_centred_to_p(const uint64_t* __restrict__ v0, uint64_t* __restrict__ out, size_t out_stride,
-                               uint64_t q0, uint32_t L, DevTables tab, uint32_t n) {
+                               uint64_t q0, uint32_t first, DevTables tab, uint32_t n) {
     const uint32_t k = blockIdx.x;
-    const uint64_t p = tab.q[L + 1 + k], half = q0 / 2;
+    const uint64_t p = tab.q[first + k], half = q0 / 2;
     uint64_t* o = out + (size_t)k * out_stride;
     for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x) {
         const uint64_t v = v0[i];
@@ -999,35 +999,40 @@ cudaError_t build_ks_constants(Context& c) {
     if (e != cudaSuccess) return e;
     e = cudaMemcpy(c.d_ksc, c.h_ksc.data(), sizeof(KsLevelConst) * c.h_ksc.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
-    // ModDown and Rescale fused at the top level: special set S = {q_L} u P (primes
-    // L..L+alpha), targets q_0..q_(L-1); the F5 / F6 fields with S in place of P
-    if (c.alpha + 1 <= BM_MAX_P && c.L >= 1) {
+    // ModDown and Rescale fused at the top level, dropping d = 1 or 2 q-primes: special
+    // set S = {q_(L-d+1), .., q_L} u P (primes L-d+1 .. L+alpha, contiguous in the
+    // basis), targets q_0..q_(L-d); the F5 / F6 fields with S in place of P
+    for (uint32_t d = 1; d <= (uint32_t)kMdrDrops; d++) {
         KsLevelConst M{};
-        const uint32_t L = c.L, ns = c.alpha + 1;
+        const uint32_t L = c.L, ns = c.alpha + d, nt = L + 1 - d, s0 = nt;
+        if (ns > (uint32_t)MAXSP || L < d) break;
         M.nlx = L + 1 + c.alpha;
         for (uint32_t i = 0; i < ns; i++) {
-            const uint64_t si = c.primes[L + i];
+            const uint64_t si = c.primes[s0 + i];
             uint64_t hat = 1;                                     // (S / s_i) mod s_i
             for (uint32_t k = 0; k < ns; k++)
-                if (k != i) hat = h_mulmod(hat, c.primes[L + k] % si, si);
+                if (k != i) hat = h_mulmod(hat, c.primes[s0 + k] % si, si);
             M.dn_hinv[i] = pair(h_mulmod(h_invmod(hat, si), h_invmod(c.n % si, si), si), si);
-            for (uint32_t j = 0; j < L; j++) {
+            for (uint32_t j = 0; j < nt; j++) {
                 const uint64_t t = c.primes[j];
                 uint64_t ht = 1;
                 for (uint32_t k = 0; k < ns; k++)
-                    if (k != i) ht = h_mulmod(ht, c.primes[L + k] % t, t);
+                    if (k != i) ht = h_mulmod(ht, c.primes[s0 + k] % t, t);
                 M.dn_hat[i][j] = pair(ht, t);
             }
         }
-        for (uint32_t j = 0; j < L; j++) {
+        for (uint32_t j = 0; j < nt; j++) {
             const uint64_t t = c.primes[j];
-            const uint64_t smod = h_mulmod(c.P_mod[j], c.primes[L] % t, t);   // S mod q_j
+            uint64_t smod = c.P_mod[j];                           // S mod q_j
+            for (uint32_t k = 0; k < d; k++) smod = h_mulmod(smod, c.primes[s0 + k] % t, t);
             M.pinv[j] = pair(h_invmod(smod, t), t);
         }
-        c.h_ksc_mdr = M;
-        e = cudaMalloc(&c.d_ksc_mdr, sizeof(KsLevelConst));
+        c.h_ksc_mdr[d - 1] = M;
+    }
+    if (c.L >= 1 && c.alpha + 1 <= (uint32_t)BM_MAX_P) {
+        e = cudaMalloc(&c.d_ksc_mdr, sizeof(KsLevelConst) * kMdrDrops);
         if (e != cudaSuccess) return e;
-        e = cudaMemcpy(c.d_ksc_mdr, &c.h_ksc_mdr, sizeof(KsLevelConst), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(c.d_ksc_mdr, c.h_ksc_mdr, sizeof(KsLevelConst) * kMdrDrops, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return e;
     }
     std::vector<ulonglong2> qi((size_t)(c.L + 1) * MAXB, make_ulonglong2(0, 0));
@@ -1440,37 +1445,45 @@ cudaError_t lift_p(const Context& c, uint32_t Q, uint64_t* const* in, uint64_t* 
                       c.d_ksc + c.L, c.tab, l1, nlx, c.n);
 }
 
-cudaError_t masks_extend(const Context& c, uint32_t n_in, const uint64_t* masks, uint64_t* ext, cudaStream_t s) {
-    // ext [n_in][nlx][N]: the q-limbs copied, the special limbs from the q_0 limb's
-    // integer coefficients (NTT + Montgomery like the q-limbs)
-    const uint32_t l1 = c.L + 1, nlx = l1 + c.alpha;
+cudaError_t extend_to_ext_basis(const Context& c, size_t count, const uint64_t* in, uint32_t l_in, uint64_t* out,
+                                cudaStream_t s) {
+    // out [count][nlx][N]: the l_in limbs of in copied, limbs l_in..nlx-1 (primes of the
+    // same index in the basis q_0..q_L, p_0..) from the q_0 limb's integer
+    // coefficients, centred (NTT + Montgomery like the copied limbs)
+    const uint32_t nlx = c.L + 1 + c.alpha;
+    if (l_in == 0 || l_in >= nlx) return cudaErrorInvalidValue;
+    const uint32_t nx = nlx - l_in;
     const size_t n = c.n;
     uint64_t* tmp = nullptr;
     cudaError_t e = cudaMalloc(&tmp, n * 8);
     if (e != cudaSuccess) return e;
-    for (uint32_t k = 0; k < n_in && e == cudaSuccess; k++) {
-        const uint64_t* src = masks + (size_t)k * l1 * n;
-        uint64_t* dst = ext + (size_t)k * nlx * n;
-        e = cudaMemcpyAsync(dst, src, l1 * n * 8, cudaMemcpyDeviceToDevice, s);
+    for (size_t k = 0; k < count && e == cudaSuccess; k++) {
+        const uint64_t* src = in + k * l_in * n;
+        uint64_t* dst = out + k * nlx * n;
+        e = cudaMemcpyAsync(dst, src, l_in * n * 8, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, src, n * 8, cudaMemcpyDeviceToDevice, s);
         LimbBatch t0{tmp, 1, n, 0, 1, 0};
         t0.set(0, 0);
         if (e == cudaSuccess) e = to_montgomery(c, t0, true, s);
         if (e == cudaSuccess) e = ntt_inverse(c, t0, s);
         if (e == cudaSuccess) {
-            k_centred_to_p<<<dim3(c.alpha, (uint32_t)(n / kThreads / 4)), kThreads, 0, s>>>(tmp, dst + l1 * n, n,
-                                                                                           c.primes[0], c.L, c.tab,
-                                                                                           (uint32_t)n);
+            k_centred_to_p<<<dim3(nx, (uint32_t)(n / kThreads / 4)), kThreads, 0, s>>>(tmp, dst + l_in * n, n,
+                                                                                     c.primes[0], l_in, c.tab,
+                                                                                     (uint32_t)n);
             e = cudaGetLastError();
         }
-        LimbBatch pb{dst, 1, (uint64_t)nlx * n, l1, c.alpha, 0};
-        for (uint32_t i = 0; i < c.alpha; i++) pb.set(i, c.L + 1 + i);
+        LimbBatch pb{dst, 1, (uint64_t)nlx * n, l_in, nx, 0};
+        for (uint32_t i = 0; i < nx; i++) pb.set(i, l_in + i);
         if (e == cudaSuccess) e = ntt_forward(c, pb, s);
         if (e == cudaSuccess) e = to_montgomery(c, pb, false, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(tmp);
     return e;
+}
+
+cudaError_t masks_extend(const Context& c, uint32_t n_in, const uint64_t* masks, uint64_t* ext, cudaStream_t s) {
+    return extend_to_ext_basis(c, n_in, masks, c.L + 1, ext, s);
 }
 
 cudaError_t circ_prepare(const Context& c, uint32_t n_in, uint32_t l1, const uint64_t* masks, uint64_t* hat,

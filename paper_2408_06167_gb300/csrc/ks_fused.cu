@@ -864,16 +864,18 @@ cudaError_t ks_moddown_add_launch(const Context& c, uint32_t level, uint32_t T, 
 }
 
 // ModDown and Rescale fused on T sums in the extended basis: e [T][2][nlx][N] (NTT
-// form, every limb) divided by S = q_L * P into out[t] (level L - 1): the inverse row
-// pass of the special limbs {q_L} u P, F5 with that special set (l1 = L, q_L as the
-// first special prime) and F6 with S^-1 (constants c.d_ksc_mdr).  Scratch: conv of T.
-template <int LA, int LB, int LT, int C, int R>
+// form, every limb) divided by S = q_(L-drop+1) .. q_L * P into out[t] (level
+// L - drop): the inverse row pass of the special limbs {q_(L-drop+1) .. q_L} u P, F5
+// with that special set (l1 = L + 1 - drop targets, the dropped q-primes first among
+// the specials) and F6 with S^-1 (constants c.d_ksc_mdr[drop - 1]).  Scratch: conv of T.
+// (MAXS: F5's staging depth, alpha + drop <= MAXS; the smaller depth of one dropped
+// prime keeps that division's occupancy)
+template <int LA, int LB, int LT, int C, int R, int MAXS>
 cudaError_t ks_mdr_launch(const Context& c, uint32_t T, uint64_t* e, uint64_t* const* d_out, uint64_t* scratch,
-                          cudaStream_t s) {
+                          uint32_t drop, cudaStream_t s) {
     constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
-    constexpr int MAXS = BM_MAX_P;
-    const uint32_t L = c.L, nlx = L + 1 + c.alpha, ns = c.alpha + 1;
-    const KsLevelConst* kc = c.d_ksc_mdr;
+    const uint32_t nlx = c.L + 1 + c.alpha, ns = c.alpha + drop, L = c.L + 1 - drop;   // L: target limbs
+    const KsLevelConst* kc = c.d_ksc_mdr + (drop - 1);
     uint64_t* conv = scratch;
     const int tr = R * (1 << (LB - LT)), tc = C * (1 << (LA - LT));
     const size_t col_smem = 8 * col_smem_words<LA, LT, C, MAXS>();
@@ -895,7 +897,7 @@ cudaError_t ks_mdr_launch(const Context& c, uint32_t T, uint64_t* e, uint64_t* c
         ProfScope ps(BM_KERNEL_MODDOWN, s, lw * T * 2 * (ns + L),
                      bf_c * T * 2 * (ns + L) + kShoupMul * N * T * 2 * (ns + (double)L * ns));
         pdl_launch(k_ks_f5<LA, LB, LT, C, MAXS>, dim3(T * 2, N2 / C), tc, col_smem, s, e, conv, kc, c.tab, L, L - 1,
-                   ns);
+                   ns);   // special i at prime (L - 1) + 1 + i
     }
     {
         ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * T * L * 6, bf_r * T * 2 * L + kShoupMul * N * T * 2 * L);
@@ -951,15 +953,23 @@ cudaError_t ks_ipsum_hoisted(const Context& c, uint32_t level, uint32_t T, const
     return cudaErrorInvalidValue;
 }
 
-bool ks_mdr_supported(const Context& c) { return ks_fused_supported(c) && c.alpha + 1 <= BM_MAX_P && c.L >= 1; }
+bool ks_mdr_supported(const Context& c, uint32_t drop) {
+    // staging depth BM_MAX_P for one dropped prime, MAXSP = BM_MAX_P + 1 for two
+    return ks_fused_supported(c) && drop >= 1 && drop <= (uint32_t)kMdrDrops && c.alpha + 1 <= BM_MAX_P &&
+           c.L >= drop;
+}
 size_t ks_mdr_scratch_words(const Context& c, uint32_t T) { return (size_t)T * 2 * c.L * c.n; }
 
 cudaError_t ks_moddown_rescale(const Context& c, uint32_t T, uint64_t* e, uint64_t* const* d_out, uint64_t* scratch,
-                               cudaStream_t s) {
+                               cudaStream_t s, uint32_t drop) {
     if (T == 0) return cudaSuccess;
-    if (!ks_mdr_supported(c)) return cudaErrorInvalidValue;
-    if (c.log_n == 16) return ks_mdr_launch<8, 8, 2, 2, 2>(c, T, e, d_out, scratch, s);
-    if (c.log_n == 12) return ks_mdr_launch<6, 6, 2, 8, 8>(c, T, e, d_out, scratch, s);
+    if (!ks_mdr_supported(c, drop)) return cudaErrorInvalidValue;
+    if (c.log_n == 16)
+        return drop == 1 ? ks_mdr_launch<8, 8, 2, 2, 2, BM_MAX_P>(c, T, e, d_out, scratch, drop, s)
+                         : ks_mdr_launch<8, 8, 2, 2, 2, MAXSP>(c, T, e, d_out, scratch, drop, s);
+    if (c.log_n == 12)
+        return drop == 1 ? ks_mdr_launch<6, 6, 2, 8, 8, BM_MAX_P>(c, T, e, d_out, scratch, drop, s)
+                         : ks_mdr_launch<6, 6, 2, 8, 8, MAXSP>(c, T, e, d_out, scratch, drop, s);
     return cudaErrorInvalidValue;
 }
 

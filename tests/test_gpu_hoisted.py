@@ -50,21 +50,27 @@ def test_hoisted_match_is_bit_exact(name, m, s, R, nq):
         assert np.abs(om.scores(got, opacked) - ref).max() < 1e-5
 
 
+@pytest.mark.parametrize("form", ["fused", "deferred"])
 @pytest.mark.parametrize("name,m,s,R,nq", [
     ("small4", 128, 16, 2500, 2),     # N_in = 8
     ("small4", 16, 4, 3000, 3),       # N_in = 4, three queries
     ("small4", 16, 1, 2100, 1),       # N_in = 16
     ("small4", 128, 4, 600, 1),       # N_in = 32
 ])
-def test_fused_expansion_match_is_bit_exact(name, m, s, R, nq):
+def test_fused_expansion_match_is_bit_exact(name, m, s, R, nq, form):
     """Algorithm 1 with ModDown and Rescale fused (rotations kept on Q_L u P, the
     circulant there, one division by q_L P per part), then every hoisted tail
-    form: bit-exact against the oracle's same-order evaluation."""
+    form: bit-exact against the oracle's same-order evaluation.  form="deferred":
+    the parts left undivided, HE-C^3's products on Q_L u P against the gallery
+    plaintexts extended there, one division by q_(L-1) q_L P per (query, group)."""
     c = gctx(name)
-    om = OracleMatch(name, m, s, R, nq, hoisted="fused", hoisted_tail=True, double_hoisted=True)
+    om = OracleMatch(name, m, s, R, nq, hoisted=form, hoisted_tail=True, double_hoisted=True)
     _, _, ek = bm.bm_keygen_ex(c, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
     g = bm.bm_gallery_import(c, om.pts_array(), om.masks_array(), om.cmask_array(), R, m, s)
-    bm.bm_gallery_set_schedule(g, bm.BM_SCHED_ALL | bm.BM_SCHED_DOUBLE_HOISTED | bm.BM_SCHED_FUSED_EXPANSION)
+    flags = bm.BM_SCHED_ALL | bm.BM_SCHED_DOUBLE_HOISTED | bm.BM_SCHED_FUSED_EXPANSION
+    if form == "deferred":
+        flags |= bm.BM_SCHED_DEFERRED_DIVISION
+    bm.bm_gallery_set_schedule(g, flags)
     ocs = [om.encrypt(qi) for qi in range(nq)]
     qs = [bm.bm_ciphertext_import(c, om.ct_array(cts), om.ctx.L) for cts in ocs]
     res = bm.bm_match(c, ek, g, qs)
@@ -76,16 +82,17 @@ def test_fused_expansion_match_is_bit_exact(name, m, s, R, nq):
         assert np.abs(om.scores(got, opacked) - ref).max() < 1e-5
 
 
-def test_fused_expansion_pipeline_ring16():
-    """Ring 2^16 end to end with the fused Algorithm 1: scores within 1e-5 of FP64,
-    the same Rank-1 as the hoisted form."""
+@pytest.mark.parametrize("mode", ["fused", "deferred"])
+def test_fused_expansion_pipeline_ring16(mode):
+    """Ring 2^16 end to end with the fused Algorithm 1 (and with its division moved
+    past HE-C^3's products): scores within 1e-5 of FP64, the FP64 Rank-1."""
     c = gctx("ring16")
     m, s, R = 128, 16, 6144
     feats = wl.gallery(R, m)
     qs, _ = wl.queries(feats, 2)
     sk, pk, ek = bm.bm_keygen_ex(c, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
     g = bm.bm_encode_gallery_packed(c, feats, m, s, bm.BM_PACK_COMPLEX)
-    bm.bm_gallery_set_expansion(g, bm.BM_EXPAND_FUSED)
+    bm.bm_gallery_set_expansion(g, bm.BM_EXPAND_FUSED if mode == "fused" else bm.BM_EXPAND_DEFERRED)
     cts = bm.bm_encrypt_batch(c, pk, qs, m, s, bm.BM_QUERY_TILED, 4, 0)
     res = bm.bm_match(c, ek, g, cts)
     for qi in range(2):
@@ -169,4 +176,10 @@ def test_expansion_errors():
     g1 = bm.bm_encode_gallery(c4, wl.gallery(100, 16), 16, 16)   # one part: no rotations to fuse
     with pytest.raises(bm.BlindMatchError) as e:
         bm.bm_gallery_set_expansion(g1, bm.BM_EXPAND_FUSED)
+    assert e.value.status == 1
+    with pytest.raises(bm.BlindMatchError) as e:
+        bm.bm_gallery_set_expansion(g1, bm.BM_EXPAND_DEFERRED)
+    assert e.value.status == 1
+    with pytest.raises(bm.BlindMatchError) as e:                # the deferred division without the fused form
+        bm.bm_gallery_set_schedule(g4, bm.BM_SCHED_HOISTED_EXPANSION | bm.BM_SCHED_DEFERRED_DIVISION)
     assert e.value.status == 1

@@ -312,6 +312,37 @@ def test_double_hoisted_forms_match_the_oracle_counts(preset, R, dim, part, Q):
 
 @pytest.mark.parametrize("preset,R,dim,part,Q", [("small4", 2500, 128, 16, 3), ("ring16", 6144, 128, 16, 1),
                                                  ("ring16", 1 << 20, 128, 4, 40), ("small4", 3000, 16, 4, 2)])
+def test_deferred_division_matches_the_oracle_counts(preset, R, dim, part, Q):
+    """The fused Algorithm 1 with its division moved past HE-C^3's products: no
+    division per part, one division by q_(L-1) q_L P per (query, group) and no rescale
+    at the HE-C^3 level; HE-C^3's products run on the L + 1 + alpha limbs of Q_L u P."""
+    kind = (bm.BM_LAYOUT_HOISTED | bm.BM_LAYOUT_FUSED_EXPANSION | bm.BM_LAYOUT_DEFERRED_DIVISION
+            | bm.BM_LAYOUT_HOISTED_ROTSUM | bm.BM_LAYOUT_HOISTED_COMPRESSION | bm.BM_LAYOUT_DOUBLE_HOISTED)
+    ops, plan_bytes = bm.bm_plan_estimate(preset, R, dim, part, Q, packing=kind)
+    _, fused_bytes = bm.bm_plan_estimate(preset, R, dim, part, Q, packing=kind & ~bm.BM_LAYOUT_DEFERRED_DIVISION)
+    log_n, n_q = PRESET[preset]
+    L, slots = n_q - 1, 1 << (log_n - 1)
+    n_in = dim // part
+    groups = sch.n_groups(R, part, slots)
+    ev = sch.CountingEvaluator()
+    sch.match(ev, [sch.SymCt(L)], [[None] * n_in for _ in range(groups)], [None] * n_in, object(), dim, part,
+              hoisted="deferred", hoisted_rotsum=True, hoisted_compress=True, double_hoisted=True)
+    orc = ev.counts()
+    lib = library_counts(ops)
+    assert lib[("modup", L)] == Q * orc[("ModUp", L)] == Q
+    assert lib[("ip_sum", L)] == Q * orc[("IPH", L)] == Q * (n_in - 1)
+    assert ("ModDownRes", L) not in orc
+    assert lib[("moddown", L)] == Q * orc[("ModDownRes2", L)] == Q * groups
+    assert lib[("MAC", L)] == Q * orc[("MulPExt", L)] == Q * groups * n_in
+    assert lib[("rescale", L)] == lib[("rescale", L - 1)] == 0
+    assert ("Res", L - 1) not in orc
+    # the rest of the schedule (rotate-and-sum, compression) is the fused form's
+    assert lib[("ip_sum", L - 2)] == Q * orc[("IPH", L - 2)]
+    assert plan_bytes > 0 and fused_bytes > 0
+
+
+@pytest.mark.parametrize("preset,R,dim,part,Q", [("small4", 2500, 128, 16, 3), ("ring16", 6144, 128, 16, 1),
+                                                 ("ring16", 1 << 20, 128, 4, 40), ("small4", 3000, 16, 4, 2)])
 def test_fused_expansion_matches_the_oracle_counts(preset, R, dim, part, Q):
     """Algorithm 1 with ModDown and Rescale fused: one basis extension and N_in - 1
     key-switch products per query, N_in fused divisions, no rescale at the top level."""
