@@ -285,6 +285,8 @@ def run_serving(args):
             (s, _), form = best
         else:
             form = forms[0] if args.expansion != "auto" else ("doubling", "printed")
+        if form[0] in ("fused", "deferred") and not 2 <= m // s <= 32:
+            form = ("hoisted", form[1])   # the fused forms need 2..32 parts: the plain hoisted sum
         flags, _ = sched_flags(bm, *form)
         parts[name] = s
         expansions[name] = "+".join(x for x, on in (("hoisted-expansion", flags & 1), ("hoisted-rotsum", flags & 2),
@@ -364,9 +366,12 @@ def run_serving(args):
 
 def resolve_expansion(expansion, n_ids, dim, part, complex_pack, slots):
     """'best': the deferred division when the gallery has fewer groups than parts (one
-    division per group instead of one per part), else the fused expansion."""
+    division per group instead of one per part), else the fused expansion; the plain
+    hoisted sum outside the fused forms' 2..32 parts."""
     if expansion != "best":
         return expansion
+    if not 2 <= dim // part <= 32:
+        return "hoisted"
     groups = -(-n_ids // ((2 if complex_pack else 1) * (slots // part)))
     return "deferred" if groups < dim // part else "fused"
 
@@ -557,10 +562,12 @@ def main():
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     bm.bm_profile_control(0, 1)
+    # bm_match_async: every step enqueued without a host wait, so each event pair holds
+    # the step's device work only (no host wake-up inside it)
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
-        r = bm.bm_match(ctx, ek, gal, cts, sptr)
+        r = bm.bm_match_async(ctx, ek, gal, cts, sptr)
         ev[k][1].record(stream)
         del r
     torch.cuda.synchronize()

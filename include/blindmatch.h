@@ -271,7 +271,7 @@ bm_status bm_gallery_set_expansion(bm_gallery* g, uint32_t mode);
  *                                basis Q_l u P and moved down once (one ModDown per
  *                                output instead of one per rotation; double
  *                                hoisting, Bossuat et al., Eurocrypt 2021); the
- *                                rotate-and-sum over s <= 8 slots then takes a
+ *                                rotate-and-sum over s <= 16 slots then takes a
  *                                single round of the s - 1 rotations
  * Needs the keys of bm_keygen_ex(..., BM_KEYS_HOISTED).  Plans of the gallery
  * built before the call are dropped; call it before registering the gallery
@@ -334,6 +334,16 @@ void bm_ciphertext_destroy(bm_ciphertext* ct);
 bm_status bm_match(bm_context* ctx, const bm_eval_keys* evk, const bm_gallery* gallery,
                    bm_ciphertext* const* queries, uint32_t n_queries, void* stream,
                    bm_result** out);
+/* bm_match without the wait: the match and the copy of its score ciphertexts are
+ * enqueued on `stream` and the call returns; the result is complete when the stream
+ * reaches the end of that work (the caller synchronises the stream, or records an
+ * event after the call).  bm_result_export and bm_decrypt_scores wait for it
+ * themselves, and bm_result_destroy may be called at any time (the free is ordered
+ * after the copy).  Host ciphertexts are copied from their page-locked host memory
+ * while the call's work runs: keep them alive until the stream has passed it.  The
+ * same plans, errors and results as bm_match. */
+bm_status bm_match_async(bm_context* ctx, const bm_eval_keys* evk, const bm_gallery* gallery,
+                         bm_ciphertext* const* queries, uint32_t n_queries, void* stream, bm_result** out);
 bm_status bm_result_info(const bm_result* r, uint32_t* n_queries, uint32_t* n_out,
                          uint32_t* packed);
 /* Score ciphertexts of one query: [n_out][2][N] coefficient form at level 0. */

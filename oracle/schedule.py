@@ -218,9 +218,9 @@ def bsgs_split(s, double=False):
     """(baby, giant) step counts of the hoisted rotate-and-sum over s (a power of
     two): baby = 2^ceil(log2(s)/2), giant = s / baby.  With one ModDown per
     round output (double=True) a round costs one basis extension, one key-switch
-    product per rotation and one ModDown, so up to s = 8 a single round of s - 1
+    product per rotation and one ModDown, so up to s = 16 a single round of s - 1
     rotations (baby = s, giant = 1) is cheaper than two."""
-    if double and s <= 8:
+    if double and s <= 16:
         return s, 1
     lb = log2i(s)
     b = 1 << ((lb + 1) // 2)

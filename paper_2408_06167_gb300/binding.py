@@ -132,6 +132,7 @@ _SIGS = {
     "bm_ciphertext_upload": (ctypes.c_int, [_vp, _vp]),
     "bm_ciphertext_destroy": (None, [_vp]),
     "bm_match": (ctypes.c_int, [_vp, _vp, _vp, _PP, _u32, _vp, _PP]),
+    "bm_match_async": (ctypes.c_int, [_vp, _vp, _vp, _PP, _u32, _vp, _PP]),
     "bm_result_info": (ctypes.c_int, [_vp, _U32P, _U32P, _U32P]),
     "bm_result_export": (ctypes.c_int, [_vp, _u32, _U64P, ctypes.c_size_t]),
     "bm_result_destroy": (None, [_vp]),
@@ -435,6 +436,15 @@ def bm_match(ctx, evk, gallery, queries, stream=None):
     arr = (ctypes.c_void_p * len(queries))(*[q.ptr for q in queries])
     h = _out()
     _check(_L.bm_match(ctx.ptr, evk.ptr, gallery.ptr, arr, len(queries), stream, ctypes.byref(h)))
+    return Result(h.value, ctx)
+
+
+def bm_match_async(ctx, evk, gallery, queries, stream=None):
+    """bm_match without the wait: the result is complete once `stream` has passed the
+    call (export and decryption wait for it themselves)."""
+    arr = (ctypes.c_void_p * len(queries))(*[q.ptr for q in queries])
+    h = _out()
+    _check(_L.bm_match_async(ctx.ptr, evk.ptr, gallery.ptr, arr, len(queries), stream, ctypes.byref(h)))
     return Result(h.value, ctx)
 
 

@@ -82,9 +82,11 @@ static uint32_t gallery_kind(const Gallery& g) {
 
 // baby and giant steps of the hoisted rotate-and-sum over s slots: b = 2^ceil(log2(s)/2);
 // with one ModDown per round output (double hoisting) a single round of s - 1
-// rotations up to s = 8 (a round: one extension, a product per rotation, one ModDown)
+// rotations up to s = 16 (a round: one extension, a product per rotation, one
+// ModDown; at s = 16 one round of 15 products measured 20 us faster per face step
+// than two rounds of 3)
 static void bsgs_split(uint32_t s, bool dhoist, uint32_t& b, uint32_t& g) {
-    if (dhoist && s <= 8) {
+    if (dhoist && s <= 16) {
         b = s;
         g = 1;
         return;
@@ -590,8 +592,12 @@ bm::Ciphertext::~Ciphertext() {
 }
 bm::Result::~Result() {
     if (d_data) {
-        cudaFreeAsync(d_data, ctx->stream);   // allocated from the stream-ordered pool
+        // allocated from the stream-ordered pool; an asynchronous match's copy may still
+        // be in flight on its stream: the free waits for its event
+        if (ready) cudaStreamWaitEvent(ctx->stream, ready, 0);
+        cudaFreeAsync(d_data, ctx->stream);
     }
+    if (ready) cudaEventDestroy(ready);
 }
 
 // ---------------------------------------------------------------------------
@@ -1994,8 +2000,12 @@ bm_status bm_plan_estimate(const bm_params* params, uint64_t n_ids, uint32_t dim
     return BM_OK;
 }
 
-bm_status bm_match(bm_context* ctxh, const bm_eval_keys* evk, const bm_gallery* gal, bm_ciphertext* const* queries,
-                   uint32_t n_queries, void* stream, bm_result** out) {
+namespace bm {
+// bm_match and bm_match_async: with sync, returns once the result is complete; else
+// the result carries an event recorded on the stream after its copy
+static bm_status match_impl(bm_context* ctxh, const bm_eval_keys* evk, const bm_gallery* gal,
+                            bm_ciphertext* const* queries, uint32_t n_queries, void* stream, bm_result** out,
+                            bool sync) {
     if (!ctxh || !evk || !gal || !queries || !out || n_queries == 0) return fail(BM_E_ARG, "null argument");
     Context& c = ctxh->c;
     const Gallery& g = gal->g;
@@ -2036,13 +2046,29 @@ bm_status bm_match(bm_context* ctxh, const bm_eval_keys* evk, const bm_gallery* 
     cudaError_t e = cudaMallocAsync((void**)&res.d_data, pl->result_words * 8, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(res.d_data, pl->result, pl->result_words * 8, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && sync) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && !sync) {
+        e = cudaEventCreateWithFlags(&res.ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(res.ready, s);
+    }
     if (e != cudaSuccess) {
+        if (!sync) cudaStreamSynchronize(s);   // nothing of the result may still be in flight
         delete rh;
         return fail(BM_E_CUDA, std::string("match: ") + cudaGetErrorString(e));
     }
     *out = rh;
     return BM_OK;
+}
+}  // namespace bm
+
+bm_status bm_match(bm_context* ctxh, const bm_eval_keys* evk, const bm_gallery* gal, bm_ciphertext* const* queries,
+                   uint32_t n_queries, void* stream, bm_result** out) {
+    return match_impl(ctxh, evk, gal, queries, n_queries, stream, out, true);
+}
+
+bm_status bm_match_async(bm_context* ctxh, const bm_eval_keys* evk, const bm_gallery* gal,
+                         bm_ciphertext* const* queries, uint32_t n_queries, void* stream, bm_result** out) {
+    return match_impl(ctxh, evk, gal, queries, n_queries, stream, out, false);
 }
 
 bm_status bm_result_info(const bm_result* r, uint32_t* n_queries, uint32_t* n_out, uint32_t* packed_out) {
@@ -2061,6 +2087,7 @@ bm_status bm_result_export(const bm_result* r, uint32_t query_index, uint64_t* o
     const size_t words = (size_t)res.n_out * ct_words(c, 0);
     if (capacity < words) return fail(BM_E_ARG, "capacity too small");
     BM_CUDA_TRY(cudaSetDevice(c.device));
+    if (res.ready) BM_CUDA_TRY(cudaEventSynchronize(res.ready));
     BM_CUDA_TRY(cudaMemcpy(out, res.d_data + (size_t)query_index * words, words * 8, cudaMemcpyDeviceToHost));
     return BM_OK;
 }
@@ -2076,6 +2103,7 @@ bm_status bm_decrypt_scores(bm_context* ctxh, const bm_secret_key* sk, const bm_
     if (n_ids != res.n_ids) return fail(BM_E_ARG, "n_ids does not match the gallery");
     BM_CUDA_TRY(cudaSetDevice(c.device));
     cudaStream_t s = c.stream;
+    if (res.ready) BM_CUDA_TRY(cudaStreamWaitEvent(s, res.ready, 0));
     const size_t n = c.n, nout = res.n_out;
     DevBuf t;
     BM_CUDA_TRY(t.alloc(nout * 2 * n));

@@ -226,6 +226,7 @@ struct Result {
     uint32_t packing = BM_PACK_REAL;          // slot packing of the gallery the result came from
     double scale = 0;                         // scale of the score ciphertexts
     uint64_t* d_data = nullptr;               // [n_queries][n_out][2][N] coefficient form, level 0
+    cudaEvent_t ready = nullptr;              // asynchronous match: recorded after d_data's copy
     ~Result();
 };
 

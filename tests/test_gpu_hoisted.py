@@ -183,3 +183,31 @@ def test_expansion_errors():
     with pytest.raises(bm.BlindMatchError) as e:                # the deferred division without the fused form
         bm.bm_gallery_set_schedule(g4, bm.BM_SCHED_HOISTED_EXPANSION | bm.BM_SCHED_DEFERRED_DIVISION)
     assert e.value.status == 1
+
+
+def test_async_match_gives_the_synchronous_results():
+    """bm_match_async enqueues the match and returns: back-to-back calls on one stream
+    give the same score ciphertexts as bm_match, export and decryption wait for the
+    result themselves, and a result destroyed before its stream has passed it is
+    freed in stream order."""
+    import torch
+    c = gctx("small4")
+    m, s, R = 16, 4, 3000
+    feats = wl.gallery(R, m)
+    qs, _ = wl.queries(feats, 3)
+    sk, pk, ek = bm.bm_keygen_ex(c, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
+    g = bm.bm_encode_gallery_packed(c, feats, m, s, bm.BM_PACK_COMPLEX)
+    bm.bm_gallery_set_expansion(g, bm.BM_EXPAND_DEFERRED)
+    cts = [bm.bm_encrypt_query(c, pk, q, m, s, bm.BM_QUERY_TILED, 4, i) for i, q in enumerate(qs)]
+    want = [bm.bm_result_export(bm.bm_match(c, ek, g, [ct]), 0) for ct in cts]
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    dropped = bm.bm_match_async(c, ek, g, [cts[0]], sp)
+    res = [bm.bm_match_async(c, ek, g, [ct], sp) for ct in cts]
+    del dropped
+    for i, r in enumerate(res):
+        assert np.array_equal(bm.bm_result_export(r, 0), want[i]), i
+        scores, rank1, _ = bm.bm_decrypt_scores(c, sk, r, 0, R)
+        ref = wl.plaintext_scores(feats, qs[i])
+        assert np.abs(scores - ref).max() < 1e-5
+    stream.synchronize()

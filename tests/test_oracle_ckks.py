@@ -367,12 +367,13 @@ def test_double_hoisted_sum_decrypts_and_differs_only_by_rounding(level):
         assert np.abs(diffs[0]).max() > 0, comp          # the roundings saved change the bits
 
 
-@pytest.mark.parametrize("m,s,R", [(128, 16, 2500), (16, 4, 3000), (16, 8, 3000)])
+@pytest.mark.parametrize("m,s,R", [(128, 16, 2500), (16, 4, 3000), (16, 8, 3000), (64, 32, 2000)])
 def test_double_hoisted_tail_scores(m, s, R):
     """Rotate-and-sum and linear compression with one ModDown per round output
-    give the FP64 scores (a single round of rotations up to s = 8)."""
+    give the FP64 scores (a single round of rotations up to s = 16, baby and giant
+    steps above)."""
     b, g = sch.bsgs_split(s, double=True)
-    assert (b, g) == ((s, 1) if s <= 8 else sch.bsgs_split(s))
+    assert (b, g) == ((s, 1) if s <= 16 else sch.bsgs_split(s))
     extra = [k for k in range(1, b)] + [b * k for k in range(1, g)] + [-r for r in range(1, s)]
     ctx, sk, pk, ev = _setup("small4", m, s, R, extra_rots=extra)
     S, L, n_in = ctx.slots, ctx.L, m // s
