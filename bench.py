@@ -364,16 +364,16 @@ def run_serving(args):
     print(json.dumps(line))
 
 
-def resolve_expansion(expansion, n_ids, dim, part, complex_pack, slots):
+def resolve_expansion(expansion, n_ids, dim, part, complex_pack, slots, encrypted=False):
     """'best': the deferred division when the gallery has fewer groups than parts (one
-    division per group instead of one per part), else the fused expansion; the plain
-    hoisted sum outside the fused forms' 2..32 parts."""
+    division per group instead of one per part; plaintext galleries only), else the
+    fused expansion; the plain hoisted sum outside the fused forms' 2..32 parts."""
     if expansion != "best":
         return expansion
     if not 2 <= dim // part <= 32:
         return "hoisted"
     groups = -(-n_ids // ((2 if complex_pack else 1) * (slots // part)))
-    return "deferred" if groups < dim // part else "fused"
+    return "deferred" if groups < dim // part and not encrypted else "fused"
 
 
 def sched_flags(bm, expansion, tail):
@@ -511,7 +511,8 @@ def main():
     W = wl.WORKLOADS[args.workload]
     part = args.part or W.part
     ctx = bm.bm_context_create(W.preset, local)
-    args.expansion = resolve_expansion(args.expansion, W.n_ids, W.dim, part, args.packing == "complex", ctx.n // 2)
+    args.expansion = resolve_expansion(args.expansion, W.n_ids, W.dim, part, args.packing == "complex", ctx.n // 2,
+                                       args.gallery == "encrypted")
     wide = None if args.no_tune else bm.bm_autotune_keyswitch(ctx)
     packing = bm.BM_PACK_COMPLEX if args.packing == "complex" else bm.BM_PACK_REAL
     feats = wl.gallery(W.n_ids, W.dim)

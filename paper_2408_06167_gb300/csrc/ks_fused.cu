@@ -16,6 +16,8 @@
 // X0, X1, ext, acc and conv (the same words as the staged kernels).
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+
 #include "bm_internal.h"
 #include "ntt_reg.cuh"
 
@@ -348,7 +350,9 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
     }
 }
 
-// F4s: grid (T * nlx, N1 / R).  Target t sums its elements e in [off[t], off[t+1])
+// F4s: grid (T * nlx * 2, N1 / R), one ciphertext component a block (the two
+// components of a limb share no loads: each gathers the extension words again).
+// Target t sums its elements e in [off[t], off[t+1])
 // before a single ModDown (double hoisting):
 //   acc[t] = sum_e ( sum_d sigma_e(ext_of[e]_d) * key_e,d  +  P * sigma_e(c0 of src_of[e]) )
 // the last term on the q-limbs of the first component only (ModDown returns it
@@ -368,7 +372,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
     const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
     const SubMem sr{sm + jr * S, 1};
     const uint32_t nd = kc->nd, nlx = kc->nlx;
-    const uint32_t tg = blockIdx.x / nlx, jj = blockIdx.x % nlx;
+    const uint32_t comp = blockIdx.x % 2, tg = blockIdx.x / 2 / nlx, jj = blockIdx.x / 2 % nlx;
     const int pi = ext_prime(jj, l1, L);
     const uint64_t q = tab.q[pi], qn = tab.qneg[pi], q2 = 2 * q;
     const uint64_t pm = jj < l1 ? kc->pmont[jj] : 0;
@@ -379,44 +383,83 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
     pdl_wait();
     const uint64_t e0 = off[tg], e1 = off[tg + 1];
     uint64_t v[K];
+    Acc128 a[K];
+    uint64_t e = e0;
+    // two elements a step: the gathers and key words of both in flight together
+    // (latency-bound at the match's batch sizes; the sum mod q does not depend on the
+    // order of its terms)
 #pragma unroll 1
-    for (uint32_t comp = 0; comp < 2; comp++) {
-        Acc128 a[K];
-#pragma unroll 1
-        for (uint64_t e = e0; e < e1; e++) {
-            const uint32_t galois = (uint32_t)gal_of[e];
-            const uint64_t* key = key_of[e];
-            const uint64_t* ext = ext_of[e];
-            uint32_t src[K];
+    for (; e + 1 < e1; e += 2) {
+        const uint32_t ga = (uint32_t)gal_of[e], gb = (uint32_t)gal_of[e + 1];
+        const uint64_t *ka = key_of[e], *kb = key_of[e + 1];
+        const uint64_t *xa = ext_of[e], *xb = ext_of[e + 1];
+        uint32_t sa[K], sb[K];
 #pragma unroll
-            for (int k = 0; k < K; k++) src[k] = perm_src((uint32_t)(roff + last_idx<LB, LT>(t, k)), LOGN, galois);
+        for (int k = 0; k < K; k++) {
+            const uint32_t idx = (uint32_t)(roff + last_idx<LB, LT>(t, k));
+            sa[k] = perm_src(idx, LOGN, ga);
+            sb[k] = perm_src(idx, LOGN, gb);
+        }
 #pragma unroll 1
-            for (uint32_t d = 0; d < nd; d++) {
-                const uint64_t* x = ext + ((size_t)d * nlx + jj) * N;
-                uint64_t kv[K];
-                nttr::load_last<LB, LT>(kv, key + ((size_t)(d * 2 + comp) * nb + pi) * N + roff, t);
+        for (uint32_t d = 0; d < nd; d++) {
+            const size_t xo = ((size_t)d * nlx + jj) * N, ko = ((size_t)(d * 2 + comp) * nb + pi) * N + roff;
+            uint64_t kva[K], kvb[K], gva[K], gvb[K];
+            nttr::load_last<LB, LT>(kva, ka + ko, t);
+            nttr::load_last<LB, LT>(kvb, kb + ko, t);
 #pragma unroll
-                for (int k = 0; k < K; k++) mul_acc(a[k], x[src[k]], kv[k], q);
+            for (int k = 0; k < K; k++) {
+                gva[k] = xa[xo + sa[k]];
+                gvb[k] = xb[xo + sb[k]];
             }
-            if (comp == 0 && jj < l1) {
-                const uint64_t* c0 = src_of[e] + (size_t)jj * N;
 #pragma unroll
-                for (int k = 0; k < K; k++) mul_acc(a[k], c0[src[k]], pm, q);
+            for (int k = 0; k < K; k++) {
+                mul_acc(a[k], gva[k], kva[k], q);
+                mul_acc(a[k], gvb[k], kvb[k], q);
             }
         }
+        if (comp == 0 && jj < l1) {
+            const uint64_t* c0a = src_of[e] + (size_t)jj * N;
+            const uint64_t* c0b = src_of[e + 1] + (size_t)jj * N;
 #pragma unroll
-        for (int k = 0; k < K; k++) v[k] = redc(a[k], q, qn);
-        if (!inv) {
-            nttr::relayout<LB, LT, LB / LT - 1, 0>(v, sr, t);
-        } else {
-            if (comp == 0) tw_wait();
-            nttr::inv_pass<LB, LT>(v, sr, twi, RowBase<R>{jr}, t, q, q2);
+            for (int k = 0; k < K; k++) {
+                mul_acc(a[k], c0a[sa[k]], pm, q);
+                mul_acc(a[k], c0b[sb[k]], pm, q);
+            }
         }
-        uint64_t* o = acc + (((size_t)tg * 2 + comp) * nlx + jj) * N + roff;
-#pragma unroll
-        for (int k = 0; k < K; k++) o[first_idx<LB, LT>(t, k)] = v[k];
-        __syncthreads();
     }
+#pragma unroll 1
+    for (; e < e1; e++) {
+        const uint32_t galois = (uint32_t)gal_of[e];
+        const uint64_t* key = key_of[e];
+        const uint64_t* ext = ext_of[e];
+        uint32_t src[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) src[k] = perm_src((uint32_t)(roff + last_idx<LB, LT>(t, k)), LOGN, galois);
+#pragma unroll 1
+        for (uint32_t d = 0; d < nd; d++) {
+            const uint64_t* x = ext + ((size_t)d * nlx + jj) * N;
+            uint64_t kv[K];
+            nttr::load_last<LB, LT>(kv, key + ((size_t)(d * 2 + comp) * nb + pi) * N + roff, t);
+#pragma unroll
+            for (int k = 0; k < K; k++) mul_acc(a[k], x[src[k]], kv[k], q);
+        }
+        if (comp == 0 && jj < l1) {
+            const uint64_t* c0 = src_of[e] + (size_t)jj * N;
+#pragma unroll
+            for (int k = 0; k < K; k++) mul_acc(a[k], c0[src[k]], pm, q);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = redc(a[k], q, qn);
+    if (!inv) {
+        nttr::relayout<LB, LT, LB / LT - 1, 0>(v, sr, t);
+    } else {
+        tw_wait();
+        nttr::inv_pass<LB, LT>(v, sr, twi, RowBase<R>{jr}, t, q, q2);
+    }
+    uint64_t* o = acc + (((size_t)tg * 2 + comp) * nlx + jj) * N + roff;
+#pragma unroll
+    for (int k = 0; k < K; k++) o[first_idx<LB, LT>(t, k)] = v[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -825,8 +868,8 @@ cudaError_t ks_ipsum_launch(const Context& c, uint32_t level, uint32_t T, const 
     ProfScope ps(BM_KERNEL_KS_IP, s, lw * (nlx * ((double)E * nd + 2.0 * nd * E + 2.0 * T) + (double)E * l1),
                  (ntt_out ? 0.0 : bf_r * T * 2.0 * alpha) +
                      N * (double)nlx * (2.0 * kProdMul * nd * E + 2.0 * kRedcMul * T) + (double)N * l1 * E * kProdMul);
-    pdl_launch(k_ks_f4s<LA, LB, LT, R>, dim3(T * nlx, N1 / R), tr, 0, s, ext_of, src_of, key_of, gal_of, off, scratch,
-               kc, c.tab, l1, c.L, c.nb, ntt_out);
+    pdl_launch(k_ks_f4s<LA, LB, LT, R>, dim3(T * nlx * 2, N1 / R), tr, 0, s, ext_of, src_of, key_of, gal_of, off, scratch, kc, c.tab, l1,
+               c.L, c.nb, ntt_out);
     return cudaGetLastError();
 }
 
