@@ -503,7 +503,9 @@ enum {
 /* One kernel launch (or launch group) of a match schedule. */
 typedef struct bm_op_launch {
     uint32_t op;          /* BM_OP_* */
-    uint32_t level;       /* level of the input ciphertexts (0 for NTT / INTT / COPY) */
+    uint32_t level;       /* level of the input ciphertexts (0 for NTT / INTT / COPY; for
+                             BM_OP_MAC on Q_L u P, the deferred division's products, L + alpha:
+                             the limbs less one) */
     uint32_t count;       /* ciphertexts, limbs or groups, as listed above */
     uint32_t queries;     /* BM_OP_MAC: queries per product set; else 0 */
     uint32_t parts;       /* BM_OP_MAC: N_in; BM_OP_IP_SUM: targets; else 0 */

@@ -1669,7 +1669,8 @@ struct MatchRun {
         // HE-C^3 per chunk of groups, then compression
         for (uint32_t g0 = 0; g0 < g.groups; g0 += pl.chunk) {
             const uint32_t G = std::min(pl.chunk, g.groups - g0);
-            record(g.encrypted ? BM_OP_MAC_CT : BM_OP_MAC, g.deferred ? c.L : lg, G, Q, n_in);
+            // (the deferred division's products run on the L + 1 + alpha limbs of Q_L u P)
+            record(g.encrypted ? BM_OP_MAC_CT : BM_OP_MAC, g.deferred ? nlx - 1 : lg, G, Q, n_in);
             if (pl.arena.live) {
                 if (g.deferred)   // the undivided parts times the plaintexts on Q_L u P
                     check(mac(c, nlx - 1, Q, G, n_in, Tsrc, g.d_pts_ext + (size_t)g0 * n_in * nlx * c.n, pl.accA, s));

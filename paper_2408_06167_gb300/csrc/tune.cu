@@ -104,11 +104,23 @@ double interp(const double* u, const double* t, double x) {
 double launch_us(const bm_op_costs& k, const bm_op_launch& l) {
     double units = l.count;
     uint32_t level = l.level;
-    if (l.op == BM_OP_MAC || l.op == BM_OP_MAC_CT || l.op == BM_OP_MAC_CIRC)
+    double scale = 1.0;
+    if (l.op >= BM_OP_KINDS) return 0.0;
+    if (l.op == BM_OP_MAC || l.op == BM_OP_MAC_CT || l.op == BM_OP_MAC_CIRC) {
         units = std::ceil(l.queries / 4.0) * l.count * l.parts;
+        // products on more limbs than the top measured level (the deferred division's
+        // HE-C^3 on Q_L u P): that level's time scaled by the limbs, a MAC's cost
+        // being proportional to them
+        int top = (int)std::min<uint32_t>(level, BM_MAX_Q - 1);
+        while (top > 0 && k.t_us[l.op][top][BM_COST_POINTS - 1] == 0.0) top--;
+        if ((uint32_t)top < level) {
+            scale = (level + 1.0) / (top + 1.0);
+            level = (uint32_t)top;
+        }
+    }
     if (l.op == BM_OP_NTT || l.op == BM_OP_INTT || l.op == BM_OP_COPY) level = 0;
-    if (l.op >= BM_OP_KINDS || level >= BM_MAX_Q) return 0.0;
-    return interp(k.units[l.op], k.t_us[l.op][level], units);
+    if (level >= BM_MAX_Q) return 0.0;
+    return scale * interp(k.units[l.op], k.t_us[l.op][level], units);
 }
 
 }  // namespace

@@ -333,7 +333,8 @@ def test_deferred_division_matches_the_oracle_counts(preset, R, dim, part, Q):
     assert lib[("ip_sum", L)] == Q * orc[("IPH", L)] == Q * (n_in - 1)
     assert ("ModDownRes", L) not in orc
     assert lib[("moddown", L)] == Q * orc[("ModDownRes2", L)] == Q * groups
-    assert lib[("MAC", L)] == Q * orc[("MulPExt", L)] == Q * groups * n_in
+    alpha = bm.bm_params_preset(preset).n_p
+    assert lib[("MAC", L + alpha)] == Q * orc[("MulPExt", L)] == Q * groups * n_in    # on the limbs of Q_L u P
     assert lib[("rescale", L)] == lib[("rescale", L - 1)] == 0
     assert ("Res", L - 1) not in orc
     # the rest of the schedule (rotate-and-sum, compression) is the fused form's
@@ -363,3 +364,25 @@ def test_fused_expansion_matches_the_oracle_counts(preset, R, dim, part, Q):
     assert lib[("moddown", L)] == Q * orc[("ModDownRes", L)] == Q * n_in
     assert lib[("rescale", L)] == 0 and ("Res", L) not in orc
     assert lib[("rot_hoisted", L)] == 0
+
+
+def test_products_on_more_limbs_than_measured_are_priced_by_their_limbs():
+    """The deferred division's HE-C^3 products run on the L + 1 + alpha limbs of
+    Q_L u P, above the levels the cost model measures: the model prices them at the
+    top measured level's cost scaled by the limbs (a MAC's cost is proportional to
+    them)."""
+    preset, R, dim, part, Q = "ring16", 6144, 128, 16, 1
+    L = PRESET[preset][1] - 1
+    mac = bm.OPS["mac"]
+    c = 0.25
+    b = np.zeros((bm.BM_OP_KINDS, bm.BM_MAX_Q))
+    b[mac, : L + 1] = c * np.arange(1, L + 2)           # proportional to the limbs; nothing above L
+    costs = synthetic_costs(np.zeros(bm.BM_OP_KINDS), b)
+    kind = (bm.BM_PACK_COMPLEX | bm.BM_LAYOUT_HOISTED | bm.BM_LAYOUT_FUSED_EXPANSION | bm.BM_LAYOUT_DEFERRED_DIVISION
+            | bm.BM_LAYOUT_HOISTED_ROTSUM | bm.BM_LAYOUT_HOISTED_COMPRESSION | bm.BM_LAYOUT_DOUBLE_HOISTED)
+    ops, _ = bm.bm_plan_estimate(preset, R, dim, part, Q, packing=kind)
+    macs = [o for o in ops if o["op"] == "mac"]
+    assert macs and all(o["level"] > L for o in macs)
+    want = sum(c * (o["level"] + 1) * math.ceil(o["queries"] / 4) * o["count"] * o["parts"] for o in macs)
+    ms, _ = bm.bm_predict_match(preset, costs, R, dim, part, Q, packing=kind)
+    assert ms * 1000 == pytest.approx(want, rel=1e-9)
