@@ -1251,6 +1251,7 @@ struct Plan {
     uint64_t *ext2 = nullptr, *rot = nullptr; // hoisted rounds after HE-C^3: extensions, rotated copies
     size_t hsrc = 0, helem = 0;            // ... their capacities (ciphertexts)
     uint64_t *packs = nullptr;             // compression outputs before the coefficient-domain rescale
+    uint64_t *qc1 = nullptr;               // hoisted Algorithm 1: the queries' c1 in coefficient form
     uint64_t *scratch = nullptr, *result = nullptr;
     size_t scratch_words = 0, result_words = 0, qin_words = 0;
     PtrArena arena;
@@ -1428,6 +1429,12 @@ struct MatchRun {
         }
         check(ks_modup_hoisted(c, level, (uint32_t)in.size(), din, ext, pl.scratch, s));
     }
+    // the same from the coefficient form of the sources' c1, coef [B][l1][N]
+    void modup_coef_batch(uint32_t level, const std::vector<uint64_t*>& in, const uint64_t* coef, uint64_t* ext) {
+        auto din = pl.arena.list(in);
+        record(BM_OP_MODUP, level, in.size());
+        if (pl.arena.live) check(ks_modup_hoisted_coef(c, level, (uint32_t)in.size(), din, coef, ext, s));
+    }
     // dst[t] += the ciphertexts of srcs[t] (one launch)
     void accumulate_batch(uint32_t level, const std::vector<uint64_t*>& dst,
                           const std::vector<std::vector<uint64_t*>>& srcs) {
@@ -1551,7 +1558,15 @@ struct MatchRun {
         const uint32_t Q = pl.Q, n_in = g.n_in, part = g.part, lg = g.level, n_out = pl.n_out;
         pl.arena.cursor = 0;
         NvtxRange whole(pl.arena.live ? "bm_match_launch" : "bm_match_plan");
-        // a0: queries into the NTT domain
+        // a0: queries into the NTT domain; the hoisted Algorithm 1 first keeps the
+        // coefficient form of each query's c1 for its basis extension (no inverse NTT)
+        const size_t lw = c.n * (size_t)(c.L + 1);
+        if (g.tiled && g.hoisted) {
+            record(BM_OP_COPY, 0, Q);
+            if (pl.arena.live)
+                check(cudaMemcpy2DAsync(pl.qc1, lw * 8, pl.qin + lw, cw(c.L) * 8, lw * 8, Q, cudaMemcpyDeviceToDevice,
+                                        s));
+        }
         record(BM_OP_NTT, 0, (size_t)Q * pl.ncts * 2 * (c.L + 1));
         if (pl.arena.live) check(ntt_forward(c, packed(c, pl.qin, Q * pl.ncts * 2, c.L + 1), s));
         // Algorithm 1, hoisted form: T_i = Res(sum_j Rot(ct, j*part) * mask_((i-j) mod N_in)),
@@ -1568,7 +1583,7 @@ struct MatchRun {
                 uint64_t* E0 = pl.R + (size_t)pl.qe * (n_in - 1) * xw;       // after the rotated sums
                 std::vector<uint64_t*> qs, ext_of, src, keys, gal, off{reinterpret_cast<uint64_t*>((uintptr_t)0)}, R, outs;
                 for (uint32_t q = 0; q < nq; q++) qs.push_back(pl.qin + (size_t)(qb + q) * cw(c.L));
-                modup_batch(c.L, qs, pl.ext);
+                modup_coef_batch(c.L, qs, pl.qc1 + (size_t)qb * lw, pl.ext);
                 for (uint32_t q = 0; q < nq; q++)
                     for (uint32_t j = 1; j < n_in; j++) {
                         ext_of.push_back(pl.ext + (size_t)q * ew);
@@ -1624,7 +1639,7 @@ struct MatchRun {
                 const uint32_t nq = std::min(pl.qe, Q - qb);
                 std::vector<uint64_t*> qs, ext_of, src, keys, gal, out, R, o0, o1;
                 for (uint32_t q = 0; q < nq; q++) qs.push_back(pl.qin + (size_t)(qb + q) * cw(c.L));
-                if (n_in > 1) modup_batch(c.L, qs, pl.ext);
+                if (n_in > 1) modup_coef_batch(c.L, qs, pl.qc1 + (size_t)qb * lw, pl.ext);
                 for (uint32_t q = 0; q < nq; q++)
                     for (uint32_t j = 1; j < n_in; j++) {
                         ext_of.push_back(pl.ext + (size_t)q * ew);
@@ -1863,6 +1878,7 @@ static std::vector<BufSpec> plan_buffers(const Context& c, const SchedView& g, P
         b.push_back({&pl.t0, g.deferred ? 0 : (size_t)pl.qe * g.n_in * sw});
         b.push_back({&pl.T, (size_t)Q * g.n_in * (g.deferred ? sw : ct_words(c, lg))});
         if (g.hoisted) {
+            b.push_back({&pl.qc1, (size_t)Q * (c.L + 1) * c.n});
             b.push_back({&pl.ext, (size_t)pl.qe * ks_ext_words(c, c.L)});
             b.push_back({&pl.R, (size_t)pl.qe * g.n_in * sw});
         }

@@ -376,6 +376,10 @@ size_t ks_modup_scratch_words(const Context& c, uint32_t level, uint32_t B);
 size_t ks_hoisted_scratch_words(const Context& c, uint32_t level, uint32_t E);
 cudaError_t ks_modup_hoisted(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in, uint64_t* ext,
                              uint64_t* scratch, cudaStream_t s);
+// the same extension from c1's coefficient form coef [B][l1][N] (d_in[b]: the NTT-form
+// ciphertexts, for the own-digit limbs); no scratch
+cudaError_t ks_modup_hoisted_coef(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,
+                                  const uint64_t* coef, uint64_t* ext, cudaStream_t s);
 cudaError_t ks_rotate_hoisted(const Context& c, uint32_t level, uint32_t E, const uint64_t* const* ext_of,
                               const uint64_t* const* src, const uint64_t* const* key_of, const uint64_t* gal_of,
                               uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s);

@@ -270,14 +270,31 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
 // ---------------------------------------------------------------------------
 template <int LA, int LB, int LT, int R>
 __global__ void __launch_bounds__(R * (1 << (LB - LT)))
-    k_ks_f3r(uint64_t* __restrict__ ext, const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L) {
+    k_ks_f3r(uint64_t* __restrict__ ext, const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L,
+             const uint64_t* const* own_src) {
     constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>(), LOGN = LA + LB, N = 1 << LOGN;
     __shared__ uint64_t sm[R * S];
     __shared__ ulonglong2 tws[row_tw_entries<LB, R>()];
     const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
     const uint32_t nd = kc->nd, nlx = kc->nlx;
     const uint32_t jj = blockIdx.x % nlx, d = (blockIdx.x / nlx) % nd;
-    if (jj >= kc->dstart[d] && jj < kc->dstart[d] + kc->dsz[d]) return;   // own limb: NTT form already
+    if (jj >= kc->dstart[d] && jj < kc->dstart[d] + kc->dsz[d]) {
+        // own limb: NTT form already (F1 wrote it), or copied here from the NTT-form
+        // input when the extension started from its coefficient form
+        if (!own_src) return;
+        const uint32_t b = blockIdx.x / (nd * nlx);
+        const size_t roff = (size_t)(blockIdx.y * R + jr) * M;
+        const uint64_t* src = own_src[b] + ((size_t)l1 + jj) * N + roff;
+        uint64_t* e = ext + (size_t)blockIdx.x * N + roff;
+        pdl_wait();
+        uint64_t v[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) v[k] = src[first_idx<LB, LT>(t, k)];
+        pdl_trigger();
+#pragma unroll
+        for (int k = 0; k < K; k++) e[first_idx<LB, LT>(t, k)] = v[k];
+        return;
+    }
     const int pi = ext_prime(jj, l1, L);
     const uint64_t q = tab.q[pi], q2 = 2 * q;
     const int row = blockIdx.y * R + jr;
@@ -805,7 +822,44 @@ cudaError_t ks_modup_launch(const Context& c, uint32_t level, uint32_t B, uint64
     }
     {
         ProfScope ps(BM_KERNEL_MODUP, s, lw * B * targets * 2, bf_r * B * targets);
-        pdl_launch(k_ks_f3r<LA, LB, LT, R>, dim3(B * nd * nlx, N1 / R), tr, 0, s, ext, kc, c.tab, l1, c.L);
+        pdl_launch(k_ks_f3r<LA, LB, LT, R>, dim3(B * nd * nlx, N1 / R), tr, 0, s, ext, kc, c.tab, l1, c.L,
+                   (const uint64_t* const*)nullptr);
+    }
+    return cudaGetLastError();
+}
+
+// The same extension from c1 in coefficient form, coef [B][l1][N] (the input before its
+// forward NTT): F3 on coef directly and F3r, whose own-limb blocks copy the
+// NTT-form limbs of d_in[b]'s c1 -- no F1 and no inverse column pass.
+template <int LA, int LB, int LT, int C, int R>
+cudaError_t ks_modup_coef_launch(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,
+                                 const uint64_t* coef, uint64_t* ext, cudaStream_t s) {
+    constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
+    const KsLevelConst& K = c.h_ksc[level];
+    const uint32_t l1 = level + 1, nd = K.nd, nlx = K.nlx;
+    const KsLevelConst* kc = c.d_ksc + level;
+    const int tr = R * (1 << (LB - LT)), tc = C * (1 << (LA - LT));
+    const size_t col_smem = 8 * col_smem_words<LA, LT, C>();
+    static bool attrs = [&] {
+        cudaFuncSetAttribute(k_ks_f3<LA, LB, LT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem);
+        return true;
+    }();
+    (void)attrs;
+    const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;
+    uint32_t targets = 0, gathers = 0;
+    for (uint32_t d = 0; d < nd; d++) {
+        targets += nlx - K.dsz[d];
+        gathers += K.dsz[d] * (nlx - K.dsz[d]);
+    }
+    {
+        ProfScope ps(BM_KERNEL_MODUP, s, lw * B * (gathers + targets),
+                     bf_c * B * targets + kShoupMul * N * B * (l1 + gathers));
+        pdl_launch(k_ks_f3<LA, LB, LT, C>, dim3(B * nd, N2 / C), tc, col_smem, s, coef, ext, kc, c.tab, l1, c.L, 1u);
+    }
+    {
+        ProfScope ps(BM_KERNEL_MODUP, s, lw * B * (targets * 2 + 2 * l1), bf_r * B * targets);
+        pdl_launch(k_ks_f3r<LA, LB, LT, R>, dim3(B * nd * nlx, N1 / R), tr, 0, s, ext, kc, c.tab, l1, c.L,
+                   (const uint64_t* const*)d_in);
     }
     return cudaGetLastError();
 }
@@ -970,6 +1024,14 @@ cudaError_t ks_modup_hoisted(const Context& c, uint32_t level, uint32_t B, uint6
     if (B == 0) return cudaSuccess;
     if (c.log_n == 16) return ks_modup_launch<8, 8, 2, 2, 2>(c, level, B, d_in, ext, scratch, s);
     if (c.log_n == 12) return ks_modup_launch<6, 6, 2, 8, 8>(c, level, B, d_in, ext, scratch, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t ks_modup_hoisted_coef(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,
+                                  const uint64_t* coef, uint64_t* ext, cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    if (c.log_n == 16) return ks_modup_coef_launch<8, 8, 2, 2, 2>(c, level, B, d_in, coef, ext, s);
+    if (c.log_n == 12) return ks_modup_coef_launch<6, 6, 2, 8, 8>(c, level, B, d_in, coef, ext, s);
     return cudaErrorInvalidValue;
 }
 
