@@ -1,8 +1,12 @@
 """Parity at the benchmarked sizes, in the launch configuration the bench times.
 
+* 6,144 identities x 128 dims, parts of 16, one query (the bench's default line,
+  its default forms, through bm_match_async): the score ciphertext is bit-exact
+  against the oracle's evaluation in the same order.
 * 65,536 identities x 16 dims, parts of 4, 64 queries matched in one batched
-  call: the score ciphertexts of sampled queries are bit-exact against the
-  oracle's match of the same plaintexts and query ciphertexts.
+  call, in the printed forms and in the bench's forms: the score ciphertexts of
+  sampled queries are bit-exact against the oracle's match of the same
+  plaintexts and query ciphertexts.
 * 1,048,576 identities x 128 dims, parts of 16, 256 queries in one call (too
   large for the oracle): for sampled queries every one of the million
   decrypted scores is within 1e-5 of the FP64 cosine and Rank-1 is the FP64
@@ -62,3 +66,50 @@ def test_large_batched_full_size_scores(ring16, part, packing, hoisted):
         srt = np.sort(ref)
         if srt[-1] - srt[-2] > 2e-5:
             assert rank1 == int(ref.argmax()), qi
+
+
+def test_face_full_size_default_forms_are_bit_exact(ring16):
+    """The bench's default line: 6,144 identities x 128 dims, parts of 16, one query,
+    complex packing, the fused Algorithm 1 with the deferred division and the
+    double-hoisted tail, matched through bm_match_async as the bench times it: the
+    score ciphertext is bit-exact against the oracle's same-order evaluation."""
+    c = ring16
+    W = wl.WORKLOADS["face-128d-6144"]
+    om = OracleMatch("ring16", W.dim, W.part, W.n_ids, 1, complex_pack=True, hoisted="deferred", hoisted_tail=True,
+                     double_hoisted=True)
+    _, _, ek = bm.bm_keygen_ex(c, KEY_SEED, W.dim, W.part, bm.BM_KEYS_HOISTED)
+    g = bm.bm_gallery_import_packed(c, om.pts_array(), om.masks_array(), om.cmask_array(), W.n_ids, W.dim, W.part,
+                                    bm.BM_PACK_COMPLEX)
+    bm.bm_gallery_set_schedule(g, bm.BM_SCHED_ALL | bm.BM_SCHED_DOUBLE_HOISTED | bm.BM_SCHED_FUSED_EXPANSION
+                               | bm.BM_SCHED_DEFERRED_DIVISION)
+    cts = om.encrypt(0)
+    q = bm.bm_ciphertext_import(c, om.ct_array(cts), om.ctx.L)
+    res = bm.bm_match_async(c, ek, g, [q])
+    got = bm.bm_result_export(res, 0)
+    want, packed = om.match(cts)
+    assert np.array_equal(got, want), "score ciphertexts differ"
+    ref = wl.plaintext_scores(om.feats, om.queries[0])
+    assert np.abs(om.scores(got, packed) - ref).max() < 1e-5
+
+
+def test_finger_full_size_default_forms_are_bit_exact(ring16):
+    """The finger line's forms: 65,536 identities x 16 dims, parts of 4, 64 queries in
+    one call, complex packing, the fused Algorithm 1 (4 groups, 4 parts) and the
+    double-hoisted tail: sampled queries bit-exact against the oracle."""
+    c = ring16
+    W = wl.WORKLOADS["finger-16d-65536-q64"]
+    om = OracleMatch("ring16", W.dim, W.part, W.n_ids, W.n_queries, complex_pack=True, hoisted="fused",
+                     hoisted_tail=True, double_hoisted=True)
+    _, _, ek = bm.bm_keygen_ex(c, KEY_SEED, W.dim, W.part, bm.BM_KEYS_HOISTED)
+    g = bm.bm_gallery_import_packed(c, om.pts_array(), om.masks_array(), om.cmask_array(), W.n_ids, W.dim, W.part,
+                                    bm.BM_PACK_COMPLEX)
+    bm.bm_gallery_set_schedule(g, bm.BM_SCHED_ALL | bm.BM_SCHED_DOUBLE_HOISTED | bm.BM_SCHED_FUSED_EXPANSION)
+    ocs = [om.encrypt(qi) for qi in range(W.n_queries)]
+    qs = [bm.bm_ciphertext_import(c, om.ct_array(cts), om.ctx.L) for cts in ocs]
+    res = bm.bm_match_async(c, ek, g, qs)
+    for qi in (0, W.n_queries - 1):
+        want, packed = om.match(ocs[qi])
+        got = bm.bm_result_export(res, qi)
+        assert np.array_equal(got, want), f"query {qi}: ciphertexts differ"
+        ref = wl.plaintext_scores(om.feats, om.queries[qi])
+        assert np.abs(om.scores(got, packed) - ref).max() < 1e-5
