@@ -623,7 +623,9 @@ def main():
     for k in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = bm.bm_match(ctx, ek, gal, host_cts, sptr)
+        # the match enqueued, then each query's score ciphertexts read back (the export
+        # waits for the match itself: one host wait a step)
+        r = bm.bm_match_async(ctx, ek, gal, host_cts, sptr)
         for qi in range(W.n_queries):
             bm.bm_result_export(r, qi, host_out[qi])
         torch.cuda.synchronize()
