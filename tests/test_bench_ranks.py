@@ -47,3 +47,21 @@ def test_rate_is_total_work_over_slowest_rank():
 def test_single_rank_needs_no_process_group():
     import bench
     assert bench.across_ranks(2.0, 10.0, 1) == (5.0, 2.0)
+
+
+@pytest.mark.parametrize("n_ids,dim,part,complex_pack,encrypted,want", [
+    (6144, 128, 16, True, False, "deferred"),      # face: 2 groups < 8 parts
+    (6144, 128, 16, False, False, "deferred"),     # 3 groups < 8 parts
+    (6144, 128, 16, True, True, "fused"),          # encrypted gallery: no deferred division
+    (65536, 16, 4, True, False, "fused"),          # finger: 4 groups, 4 parts
+    (1 << 20, 128, 4, True, False, "fused"),       # 64 groups, 32 parts
+    (1024, 16, 16, True, False, "hoisted"),        # one part: no fused forms
+    (6144, 128, 2, True, False, "hoisted"),        # 64 parts: beyond the fused forms' 32
+])
+def test_best_expansion_form(n_ids, dim, part, complex_pack, encrypted, want):
+    """bench.py's default form: the deferred division when the gallery has fewer
+    groups than parts (plaintext galleries), else the fused expansion, and the
+    plain hoisted sum outside 2..32 parts; explicit forms pass through."""
+    import bench
+    assert bench.resolve_expansion("best", n_ids, dim, part, complex_pack, 1 << 15, encrypted) == want
+    assert bench.resolve_expansion("fused", n_ids, dim, part, complex_pack, 1 << 15, encrypted) == "fused"
