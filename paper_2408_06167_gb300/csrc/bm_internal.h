@@ -16,7 +16,7 @@
 
 namespace bm {
 
-// Page-locked host memory from a caching pool: cudaMallocHost on a miss, freed
+// Page-locked host memory from a caching pool: cudaHostAlloc (portable) on a miss, freed
 // blocks kept by exact size (up to 2 GiB in all) for the next request of that
 // size, so a host ciphertext is copied to and from the device by DMA without a
 // page-locking call per object.  Pageable memory when page-locking fails (no

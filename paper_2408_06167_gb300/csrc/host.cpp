@@ -291,7 +291,9 @@ void* pinned_alloc(size_t bytes) {
         }
     }
     void* p = nullptr;
-    if (cudaMallocHost(&p, bytes) == cudaSuccess) return p;
+    // portable: page-locked for every device's context of the process, not only the
+    // one current at the allocation
+    if (cudaHostAlloc(&p, bytes, cudaHostAllocPortable) == cudaSuccess) return p;
     cudaGetLastError();   // clear the failed call's error
     p = std::malloc(bytes);
     if (!p) throw std::bad_alloc();
