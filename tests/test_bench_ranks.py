@@ -65,3 +65,19 @@ def test_best_expansion_form(n_ids, dim, part, complex_pack, encrypted, want):
     import bench
     assert bench.resolve_expansion("best", n_ids, dim, part, complex_pack, 1 << 15, encrypted) == want
     assert bench.resolve_expansion("fused", n_ids, dim, part, complex_pack, 1 << 15, encrypted) == "fused"
+
+
+def test_roofline_bound_is_the_binding_roof():
+    """The line's roofline takes the roof the dominant class is closer to: HBM for a
+    class moving bytes at a larger fraction of the copy bandwidth than its multiplies
+    reach of the integer peak, the ALU otherwise; both views are reported."""
+    import bench
+    # 3 launches of 1 ms: 8 GB and 10 T mul32 in total -> 2.67 TB/s, 3.33 T mul32/s
+    r = bench.roofline_of("ks_ip", 3.0, 8e9, 10e12 / 1e3, 6669.5, "measured", 20.137, 68.6e6)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] == 68.6e6
+    assert abs(r["frac"] - (8e9 / 3e-3 / 1e9) / 6669.5) < 1e-12
+    assert r["alu_view"]["frac"] < r["frac"] == r["hbm_view"]["frac"]
+    r = bench.roofline_of("moddown", 1.0, 1e9, 15e9, 6669.5, "measured", 20.137, None)
+    assert r["bound"] == "alu" and r["unit"] == "Tmul32/s" and abs(r["frac"] - 15.0 / 20.137) < 1e-12
+    r = bench.roofline_of("copy", 1.0, 5e9, 0, 6669.5, "measured", 20.137, None)
+    assert r["bound"] == "hbm" and "alu_view" not in r
