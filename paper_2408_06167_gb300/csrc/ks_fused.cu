@@ -481,8 +481,10 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
 
 // ---------------------------------------------------------------------------
 // F5: grid (B * 2, N2 / C).  conv = Conv_{P -> Q_l}(acc's special-prime limbs).
-// (MAXS: the most special limbs, the staging depth; the fused ModDown + Rescale
-// calls it with the special set {q_L} u P, l1 = L and L - 1 in place of L.)
+// (MAXS: the most special limbs, the staging depth; the fused divisions call it with
+// the special set {q_L} u P -- l1 = L, L - 1 in place of L -- or {q_(L-1), q_L} u P
+// -- l1 = L - 1, L - 2 in place of L; the special limbs follow the targets in the
+// basis order either way.)
 // ---------------------------------------------------------------------------
 template <int LA, int LB, int LT, int C, int MAXS = kMaxDigit>
 __global__ void __launch_bounds__(C * (1 << (LA - LT)))
