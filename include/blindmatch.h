@@ -438,10 +438,15 @@ bm_status bm_ntt_inverse(bm_context* ctx, uint64_t* d_data, uint32_t n_polys, ui
  * needing more (input copy + key-switch temporaries, e.g. more than one ring-2^16
  * ciphertext at level 3) or more than 64 ciphertexts fail with BM_E_ARG and a
  * message giving the limit.  The first call on a device looks up the array's
- * device address; make that first call before any stream capture.  All calls
- * share the array: calls whose work overlaps on one GPU (issued on different
- * streams or from different threads) race and must be serialised by the
- * caller.  BM_E_KEY_MISSING if evk has no key for the rotation. */
+ * device address (cudaGetSymbolAddress, cached per device for the life of the
+ * process: calls after a cudaDeviceReset of that device are not supported);
+ * make that first call before any stream capture.  Every call writes its
+ * pointer lists on the device with a kernel (no host staging buffer and no
+ * host-to-device copy), restores the caller's current device before
+ * returning, and does not wait on the stream.
+ * All calls share the array: calls whose work overlaps on one GPU (issued on
+ * different streams or from different threads) race and must be serialised by
+ * the caller.  BM_E_KEY_MISSING if evk has no key for the rotation. */
 bm_status bm_ct_rotate_noalloc(bm_context* ctx, const bm_eval_keys* evk, const uint64_t* d_in,
                                uint32_t n_cts, uint32_t level, int32_t rotation, uint64_t* d_out,
                                void* stream);

@@ -253,6 +253,14 @@ static bm_status context_init(Context& c, const bm_params& p, int device) {
         c.tab.itw[j] = (const ulonglong2*)c.d_twiddles + j * per + c.n;
     }
     BM_CUDA_TRY(build_ks_constants(c));
+    {
+        int sms = 0;
+        BM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+        c.sm_count = (uint32_t)sms;
+        BM_CUDA_TRY(cudaHostAlloc((void**)&c.h_ks_err, sizeof(int), cudaHostAllocMapped | cudaHostAllocPortable));
+        *c.h_ks_err = 0;
+        BM_CUDA_TRY(cudaHostGetDevicePointer((void**)&c.d_ks_err, c.h_ks_err, 0));
+    }
     if (const char* w = std::getenv("BM_KS_WIDE_BATCH"))
         for (uint32_t& t : c.ks_wide_batch) t = (uint32_t)std::strtoul(w, nullptr, 10);
     return BM_OK;
@@ -341,6 +349,7 @@ void context_free(bm_context* ctx) {
     if (ctx->c.d_ksc) cudaFree(ctx->c.d_ksc);
     if (ctx->c.d_ksc_mdr) cudaFree(ctx->c.d_ksc_mdr);
     if (ctx->c.d_qlinv) cudaFree(ctx->c.d_qlinv);
+    if (ctx->c.h_ks_err) cudaFreeHost(ctx->c.h_ks_err);
     if (ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
     delete ctx;
 }
@@ -1377,6 +1386,17 @@ struct MatchRun {
     }
     void need_scratch(size_t words) { pl.scratch_words = std::max(pl.scratch_words, words); }
 
+    // the shape of a launch of hoisted sums: the distinct extensions, sources and keys
+    // of its elements [b, e) and the most elements of one of its targets
+    static KsSumInfo sum_info(const std::vector<uint64_t*>& ext_of, const std::vector<uint64_t*>& src,
+                              const std::vector<uint64_t*>& keys, size_t b, size_t e, uint32_t max_elems) {
+        auto count = [&](const std::vector<uint64_t*>& v) {
+            std::vector<uint64_t*> u(v.begin() + b, v.begin() + e);
+            std::sort(u.begin(), u.end());
+            return (uint32_t)(std::unique(u.begin(), u.end()) - u.begin());
+        };
+        return {count(ext_of), count(keys), count(src), max_elems};
+    }
     // key switch of a batch: rotation by `rot`, or (relin) relinearisation -- the key
     // from s^2 to s with the identity automorphism
     void rotate_batch(uint32_t level, int32_t rot, const std::vector<uint64_t*>& in,
@@ -1518,6 +1538,8 @@ struct MatchRun {
         for (size_t t0 = 0; t0 < tg.size(); t0 += ksb) {
             const uint32_t T = (uint32_t)std::min<size_t>(ksb, tg.size() - t0);
             const uint32_t E = t_off[t0 + T] - t_off[t0];
+            uint32_t mx = 0;
+            for (uint32_t t = t0; t < t0 + T; t++) mx = std::max(mx, t_off[t + 1] - t_off[t]);
             record(BM_OP_IP_SUM, level, E, 0, T);
             record(BM_OP_MODDOWN, level, T);
             if (!pl.arena.live) {
@@ -1526,7 +1548,7 @@ struct MatchRun {
             }
             check(ks_ipsum_hoisted(c, level, T, (const uint64_t*)(doff + t0), E, (const uint64_t* const*)de,
                                    (const uint64_t* const*)ds, (const uint64_t* const*)dk, (const uint64_t*)dg,
-                                   pl.scratch, s));
+                                   pl.scratch, s, false, sum_info(ext_of, src, keys, t_off[t0], t_off[t0 + T], mx)));
             check(ks_moddown_add(c, level, T, dt + t0, pl.scratch, s, dto ? dto + t0 : nullptr));
         }
     }
@@ -1605,7 +1627,8 @@ struct MatchRun {
                     if (pl.arena.live)
                         check(ks_ipsum_hoisted(c, c.L, T, (const uint64_t*)(doff + t0), T, (const uint64_t* const*)de,
                                                (const uint64_t* const*)ds, (const uint64_t* const*)dk,
-                                               (const uint64_t*)dg, pl.R + (size_t)t0 * xw, s, true));
+                                               (const uint64_t*)dg, pl.R + (size_t)t0 * xw, s, true,
+                                               sum_info(ext_of, src, keys, t0, t0 + T, 1)));
                 }
                 record(BM_OP_COPY, 0, nq);
                 if (pl.arena.live) check(lift_p(c, nq, dq, E0, s));

@@ -118,6 +118,9 @@ struct Context {
                                               // per level: key-switch batches of at least this many
                                               // ciphertexts use 16 coefficients per thread (set by
                                               // bm_autotune_keyswitch / bm_set_ks_wide_batch / BM_KS_WIDE_BATCH)
+    uint32_t sm_count = 0;                    // SMs of the device (persistent kernels: one block each)
+    int* h_ks_err = nullptr;                  // bounded device waits that expired (page-locked, mapped;
+    int* d_ks_err = nullptr;                  //   the kernels set it, the host reads and clears it)
     uint64_t next_id = 1;                     // ids of galleries and key sets (plan cache keys)
     std::vector<Plan*> plans;
     // lifetime: every handle made from the context holds a reference; the context
@@ -391,10 +394,18 @@ cudaError_t ks_rotate_hoisted(const Context& c, uint32_t level, uint32_t E, cons
 // indices) with P * sigma(c0); ks_moddown_add moves the sums down and adds them
 // to tgt[t] in place (or writes tgt[t] + the result to d_out[t]).  Targets may be sources.
 // (ntt_out: the sums left in NTT form on every limb, written to scratch as [T][2][nlx][N])
+// The shape of one such launch as the schedule knows it on the host: the distinct
+// extensions, keys and source ciphertexts of its elements (for the algorithmic byte
+// count: each is read once, its other uses are re-reads of the same words) and the
+// most elements of one target (the depth of the kernel's copy pipeline); zero =
+// unknown (every element its own operands; a deep pipeline).
+struct KsSumInfo {
+    uint32_t ext = 0, keys = 0, srcs = 0, max_elems = 0;
+};
 cudaError_t ks_ipsum_hoisted(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
                              const uint64_t* const* ext_of, const uint64_t* const* src_of,
                              const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch,
-                             cudaStream_t s, bool ntt_out = false);
+                             cudaStream_t s, bool ntt_out = false, KsSumInfo u = {});
 // ModDown and Rescale fused at the top level: e [T][2][L+1+alpha][N] (NTT form, every
 // limb; the special limbs are transformed in place) divided by q_(L-drop+1)..q_L * P
 // into out[t] (level L - drop, drop 1 or 2); scratch ks_mdr_scratch_words(c, T);

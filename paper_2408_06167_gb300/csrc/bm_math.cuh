@@ -69,6 +69,50 @@ BM_HD uint64_t redc(const Acc128& t, uint64_t q, uint64_t qneg) {   // t < q * 2
     return r >= q ? r - q : r;
 }
 
+// Sums of products without a reduction per product: t += a * b as a 128-bit sum
+// (a, b < 2^61, so each product is below 2^122 and 64 of them stay below 2^128).
+// On the device the full 64 x 64 -> 128-bit product is added by three carry
+// chains of 32 x 32-bit multiply-adds (eight multiply-adds, two carry adds);
+// reduce_hi keeps longer sums in range, redc_wide reduces the sum once.
+BM_HD void mad128(Acc128& t, uint64_t a, uint64_t b) {
+#if defined(__CUDA_ARCH__)
+    uint32_t a0, a1, b0, b1, t0, t1, t2, t3;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(a0), "=r"(a1) : "l"(a));
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(b0), "=r"(b1) : "l"(b));
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(t0), "=r"(t1) : "l"(t.lo));
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(t2), "=r"(t3) : "l"(t.hi));
+    asm("mad.lo.cc.u32 %0, %4, %6, %0;\n\t"     // low halves: a0 b0 @0, a0 b1 @32, a1 b1 @64
+        "madc.lo.cc.u32 %1, %4, %7, %1;\n\t"
+        "madc.lo.cc.u32 %2, %5, %7, %2;\n\t"
+        "addc.u32 %3, %3, 0;\n\t"
+        "mad.hi.cc.u32 %1, %4, %6, %1;\n\t"      // high halves: a0 b0 @32, a0 b1 @64, a1 b1 @96
+        "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+        "madc.hi.u32 %3, %5, %7, %3;\n\t"
+        "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"      // a1 b0: low half @32, high half @64
+        "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3)
+        : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(t.lo) : "r"(t0), "r"(t1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(t.hi) : "r"(t2), "r"(t3));
+#else
+    const unsigned __int128 s = ((unsigned __int128)t.hi << 64 | t.lo) + (unsigned __int128)a * b;
+    t.lo = (uint64_t)s;
+    t.hi = (uint64_t)(s >> 64);
+#endif
+}
+// the high word reduced below q (t changes by a multiple of q * 2^64, so t mod q
+// and its Montgomery reduction do not); rsh = floor(2^64 / q)
+BM_HD void reduce_hi(Acc128& t, uint64_t q, uint64_t rsh) {
+    uint64_t h = t.hi - mulhi64(t.hi, rsh) * q;        // [0, 2q)
+    t.hi = h >= q ? h - q : h;
+}
+// t * 2^-64 mod q for any 128-bit t
+BM_HD uint64_t redc_wide(Acc128 t, uint64_t q, uint64_t qneg, uint64_t rsh) {
+    reduce_hi(t, q, rsh);
+    return redc(t, q, qneg);
+}
+
 // Sums of products by 30-bit pieces, for a, b < q < 2^60: a = a1 * 2^30 + a0 with
 // a0, a1 < 2^30, and the sum t = hi * 2^60 + mid * 2^30 + lo held as three 64-bit
 // sums of 32 x 32-bit products, one multiply-add each: lo gains a0*b0 < 2^60, mid

@@ -367,116 +367,148 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
     }
 }
 
-// F4s: grid (T * nlx * 2, N1 / R), one ciphertext component a block (the two
-// components of a limb share no loads: each gathers the extension words again).
-// Target t sums its elements e in [off[t], off[t+1])
-// before a single ModDown (double hoisting):
+// The Galois image of a limb in NTT form at the four positions i0 .. i0 + 3 (i0 a
+// multiple of 4, thread t of the last row layout): for any odd Galois element the
+// four source positions perm_src(i0 + k) are an aligned group of four words --
+// positions i0 + k and i0 + k + 1 (k even) come from one 16-byte half of the
+// group, in either order, and positions i0 + 2, i0 + 3 from the other half -- so
+// the group is read as one 32-byte vector and its words put in place by selects.
+struct Perm4 {
+    uint32_t gb;        // first source word of the group
+    uint32_t sel;       // bit 1: the half of positions 0, 1; bit 0: they are swapped; bit 2: 2, 3 swapped
+};
+__device__ __forceinline__ Perm4 perm4(uint32_t i0, uint32_t log_n, uint32_t galois) {
+    const uint32_t p0 = perm_src(i0, log_n, galois), p2 = perm_src(i0 + 2, log_n, galois);
+    return {p0 & ~3u, (p0 & 3u) | ((p2 & 1u) << 2)};
+}
+struct W4 {
+    uint64_t w[4];
+};
+// four consecutive words, one 256-bit load (32-byte aligned)
+__device__ __forceinline__ W4 ld256(const uint64_t* p) {
+    W4 r;
+    asm volatile("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+                 : "=l"(r.w[0]), "=l"(r.w[1]), "=l"(r.w[2]), "=l"(r.w[3])
+                 : "l"(p));
+    return r;
+}
+__device__ __forceinline__ void place4(uint64_t (&o)[4], const W4& g, uint32_t sel) {
+    const uint64_t a0 = (sel & 2) ? g.w[2] : g.w[0], a1 = (sel & 2) ? g.w[3] : g.w[1];
+    const uint64_t b0 = (sel & 2) ? g.w[0] : g.w[2], b1 = (sel & 2) ? g.w[1] : g.w[3];
+    o[0] = (sel & 1) ? a1 : a0;
+    o[1] = (sel & 1) ? a0 : a1;
+    o[2] = (sel & 4) ? b1 : b0;
+    o[3] = (sel & 4) ? b0 : b1;
+}
+
+// F4s: grid (T * nlx, N1 / R); a block holds both ciphertext components of R rows of
+// one extended limb of one target, so every gathered extension word serves the
+// products of both.  Target t sums its elements e in [off[t], off[t+1]) before a
+// single ModDown (double hoisting):
 //   acc[t] = sum_e ( sum_d sigma_e(ext_of[e]_d) * key_e,d  +  P * sigma_e(c0 of src_of[e]) )
 // the last term on the q-limbs of the first component only (ModDown returns it
-// exactly: P * x has no special-prime residue and (P * x) * P^-1 = x); then, for
-// the special-prime limbs, the inverse row pass (as F4) -- or, with ntt_out, every
-// limb left in NTT form (the fused Algorithm 1 multiplies them by the masks first).
-template <int LA, int LB, int LT, int R>
-__global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
+// exactly: P * x has no special-prime residue and (P * x) * P^-1 = x), taken as P
+// times the sum of the gathered c0 words (one product per word, not one per
+// element); then, for the special-prime limbs, the inverse row pass (as F4) -- or,
+// with ntt_out, every limb left in NTT form (the fused Algorithm 1 multiplies them
+// by the masks first).  A thread holds four consecutive words of a row (the last
+// row layout) and moves every operand group as one 32-byte vector: its key words of
+// each digit and component, the Galois source group of each extension digit and of
+// c0.  The products are summed at 128 bits without a reduction per product (the
+// high word -- and the c0 sum -- reduced every kFoldElems elements: at most
+// ND * kFoldElems < 64 products and kFoldElems < 16 c0 words between reductions)
+// and reduced once.
+constexpr uint32_t kFoldElems = 12;
+template <int LA, int LB, int R, int ND, int MINB>
+__global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
     k_ks_f4s(const uint64_t* const* ext_of, const uint64_t* const* src_of, const uint64_t* const* key_of,
              const uint64_t* gal_of, const uint64_t* off, uint64_t* __restrict__ acc,
              const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L, uint32_t nb,
              bool ntt_out) {
-    constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>(), LOGN = LA + LB, N = 1 << LOGN;
+    constexpr int LT = 2, K = 4, M = 1 << LB, TH = M >> LT, SW = sub_words<LB, LT>(), LOGN = LA + LB, N = 1 << LOGN;
     constexpr int TWN = row_tw_entries<LB, R>();
-    __shared__ uint64_t sm[R * S];
+    __shared__ uint64_t sm[R * SW];
     __shared__ ulonglong2 twi[TWN];
     const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
-    const SubMem sr{sm + jr * S, 1};
+    const SubMem sr{sm + jr * SW, 1};
     const uint32_t nd = kc->nd, nlx = kc->nlx;
-    const uint32_t comp = blockIdx.x % 2, tg = blockIdx.x / 2 / nlx, jj = blockIdx.x / 2 % nlx;
+    const uint32_t tg = blockIdx.x / nlx, jj = blockIdx.x % nlx;
     const int pi = ext_prime(jj, l1, L);
-    const uint64_t q = tab.q[pi], qn = tab.qneg[pi], q2 = 2 * q;
+    const uint64_t q = tab.q[pi], qn = tab.qneg[pi], rsh = tab.rsh[pi], q2 = 2 * q;
     const uint64_t pm = jj < l1 ? kc->pmont[jj] : 0;
     const int row = blockIdx.y * R + jr;
     const size_t roff = (size_t)row * M;
+    const uint32_t i0 = (uint32_t)roff + (uint32_t)(t << LT);     // last layout: words i0 .. i0 + 3
     const bool inv = jj >= l1 && !ntt_out;      // special limbs for F5: inverse row pass
+    const bool qlimb = jj < l1;
     if (inv) stage_row_twiddles<LA, LB, R, R * TH>(twi, tab.itw[pi], blockIdx.y * R);
     pdl_wait();
-    const uint64_t e0 = off[tg], e1 = off[tg + 1];
-    uint64_t v[K];
-    Acc128 a[K];
-    uint64_t e = e0;
-    // two elements a step: the gathers and key words of both in flight together
-    // (latency-bound at the match's batch sizes; the sum mod q does not depend on the
-    // order of its terms)
+    const uint32_t e0 = (uint32_t)off[tg], e1 = (uint32_t)off[tg + 1];
+    Acc128 a0[K], a1[K];
+    uint64_t cs[K] = {0, 0, 0, 0};
 #pragma unroll 1
-    for (; e + 1 < e1; e += 2) {
-        const uint32_t ga = (uint32_t)gal_of[e], gb = (uint32_t)gal_of[e + 1];
-        const uint64_t *ka = key_of[e], *kb = key_of[e + 1];
-        const uint64_t *xa = ext_of[e], *xb = ext_of[e + 1];
-        uint32_t sa[K], sb[K];
+    for (uint32_t e = e0; e < e1; e++) {
+        const Perm4 pm4 = perm4(i0, LOGN, (uint32_t)gal_of[e]);
+        const uint64_t* key = key_of[e] + (size_t)pi * N + i0;
+        const uint64_t* ext = ext_of[e] + (size_t)jj * N + pm4.gb;
+        W4 xs[ND], k0s[ND], k1s[ND], cw;
 #pragma unroll
-        for (int k = 0; k < K; k++) {
-            const uint32_t idx = (uint32_t)(roff + last_idx<LB, LT>(t, k));
-            sa[k] = perm_src(idx, LOGN, ga);
-            sb[k] = perm_src(idx, LOGN, gb);
-        }
-#pragma unroll 1
-        for (uint32_t d = 0; d < nd; d++) {
-            const size_t xo = ((size_t)d * nlx + jj) * N, ko = ((size_t)(d * 2 + comp) * nb + pi) * N + roff;
-            uint64_t kva[K], kvb[K], gva[K], gvb[K];
-            nttr::load_last<LB, LT>(kva, ka + ko, t);
-            nttr::load_last<LB, LT>(kvb, kb + ko, t);
-#pragma unroll
-            for (int k = 0; k < K; k++) {
-                gva[k] = xa[xo + sa[k]];
-                gvb[k] = xb[xo + sb[k]];
-            }
-#pragma unroll
-            for (int k = 0; k < K; k++) {
-                mul_acc(a[k], gva[k], kva[k], q);
-                mul_acc(a[k], gvb[k], kvb[k], q);
+        for (int d = 0; d < ND; d++) {
+            if (d < (int)nd) {
+                xs[d] = ld256(ext + (size_t)d * nlx * N);
+                k0s[d] = ld256(key + (size_t)(2 * d) * nb * N);
+                k1s[d] = ld256(key + (size_t)(2 * d + 1) * nb * N);
             }
         }
-        if (comp == 0 && jj < l1) {
-            const uint64_t* c0a = src_of[e] + (size_t)jj * N;
-            const uint64_t* c0b = src_of[e + 1] + (size_t)jj * N;
+        if (qlimb) cw = ld256(src_of[e] + (size_t)jj * N + pm4.gb);
+#pragma unroll
+        for (int d = 0; d < ND; d++) {
+            if (d < (int)nd) {
+                uint64_t x[K];
+                place4(x, xs[d], pm4.sel);
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    mad128(a0[k], x[k], k0s[d].w[k]);
+                    mad128(a1[k], x[k], k1s[d].w[k]);
+                }
+            }
+        }
+        if (qlimb) {
+            uint64_t c[K];
+            place4(c, cw, pm4.sel);
+#pragma unroll
+            for (int k = 0; k < K; k++) cs[k] += c[k];
+        }
+        if ((e - e0) % kFoldElems == kFoldElems - 1) {
 #pragma unroll
             for (int k = 0; k < K; k++) {
-                mul_acc(a[k], c0a[sa[k]], pm, q);
-                mul_acc(a[k], c0b[sb[k]], pm, q);
+                reduce_hi(a0[k], q, rsh);
+                reduce_hi(a1[k], q, rsh);
+                const uint64_t r = cs[k] - mulhi64(cs[k], rsh) * q;   // [0, 2q)
+                cs[k] = r >= q ? r - q : r;
             }
         }
     }
+    if (qlimb) {
+#pragma unroll
+        for (int k = 0; k < K; k++) mad128(a0[k], cs[k], pm);
+    }
 #pragma unroll 1
-    for (; e < e1; e++) {
-        const uint32_t galois = (uint32_t)gal_of[e];
-        const uint64_t* key = key_of[e];
-        const uint64_t* ext = ext_of[e];
-        uint32_t src[K];
+    for (uint32_t comp = 0; comp < 2; comp++) {
+        uint64_t v[K];
 #pragma unroll
-        for (int k = 0; k < K; k++) src[k] = perm_src((uint32_t)(roff + last_idx<LB, LT>(t, k)), LOGN, galois);
-#pragma unroll 1
-        for (uint32_t d = 0; d < nd; d++) {
-            const uint64_t* x = ext + ((size_t)d * nlx + jj) * N;
-            uint64_t kv[K];
-            nttr::load_last<LB, LT>(kv, key + ((size_t)(d * 2 + comp) * nb + pi) * N + roff, t);
+        for (int k = 0; k < K; k++) v[k] = redc_wide(comp ? a1[k] : a0[k], q, qn, rsh);
+        uint64_t* o = acc + (((size_t)tg * 2 + comp) * nlx + jj) * N + roff;
+        if (!inv) {
+            nttr::store_last<LB, LT>(v, o, t);
+        } else {
+            if (comp == 0) tw_wait();
+            else __syncthreads();
+            nttr::inv_pass<LB, LT>(v, sr, twi, RowBase<R>{jr}, t, q, q2);
 #pragma unroll
-            for (int k = 0; k < K; k++) mul_acc(a[k], x[src[k]], kv[k], q);
-        }
-        if (comp == 0 && jj < l1) {
-            const uint64_t* c0 = src_of[e] + (size_t)jj * N;
-#pragma unroll
-            for (int k = 0; k < K; k++) mul_acc(a[k], c0[src[k]], pm, q);
+            for (int k = 0; k < K; k++) o[first_idx<LB, LT>(t, k)] = v[k];
         }
     }
-#pragma unroll
-    for (int k = 0; k < K; k++) v[k] = redc(a[k], q, qn);
-    if (!inv) {
-        nttr::relayout<LB, LT, LB / LT - 1, 0>(v, sr, t);
-    } else {
-        tw_wait();
-        nttr::inv_pass<LB, LT>(v, sr, twi, RowBase<R>{jr}, t, q, q2);
-    }
-    uint64_t* o = acc + (((size_t)tg * 2 + comp) * nlx + jj) * N + roff;
-#pragma unroll
-    for (int k = 0; k < K; k++) o[first_idx<LB, LT>(t, k)] = v[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -913,19 +945,31 @@ template <int LA, int LB, int LT, int C, int R>
 cudaError_t ks_ipsum_launch(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
                             const uint64_t* const* ext_of, const uint64_t* const* src_of,
                             const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch, bool ntt_out,
-                            cudaStream_t s) {
+                            KsSumInfo u, cudaStream_t s) {
     constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
     (void)N2;
     const KsLevelConst& K = c.h_ksc[level];
     const uint32_t l1 = level + 1, nd = K.nd, nlx = K.nlx, alpha = c.alpha;
     const KsLevelConst* kc = c.d_ksc + level;
-    const int tr = R * (1 << (LB - LT));
     const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB;
-    ProfScope ps(BM_KERNEL_KS_IP, s, lw * (nlx * ((double)E * nd + 2.0 * nd * E + 2.0 * T) + (double)E * l1),
+    // algorithmic bytes: every distinct extension (nd x nlx limbs), key slice (nd x 2 x
+    // nlx limbs) and source c0 (l1 limbs) once, and the sums (2 x nlx limbs a target)
+    const double ue = u.ext ? u.ext : E, uk = u.keys ? u.keys : E, us = u.srcs ? u.srcs : E;
+    ProfScope ps(BM_KERNEL_KS_IP, s, lw * (nlx * (ue * nd + 2.0 * nd * uk + 2.0 * T) + us * l1),
                  (ntt_out ? 0.0 : bf_r * T * 2.0 * alpha) +
                      N * (double)nlx * (2.0 * kProdMul * nd * E + 2.0 * kRedcMul * T) + (double)N * l1 * E * kProdMul);
-    pdl_launch(k_ks_f4s<LA, LB, LT, R>, dim3(T * nlx * 2, N1 / R), tr, 0, s, ext_of, src_of, key_of, gal_of, off, scratch, kc, c.tab, l1,
-               c.L, c.nb, ntt_out);
+    // R rows a block (64 threads); digits unrolled up to ND
+    constexpr int RF = 256 >> LB;
+    const dim3 g(T * nlx, N1 / RF), b(RF * (1 << (LB - 2)));
+    auto args = [&](auto kernel) {
+        return pdl_launch(kernel, g, b, 0, s, ext_of, src_of, key_of, gal_of, off, scratch, kc, c.tab, l1, c.L, c.nb,
+                          ntt_out);
+    };
+    cudaError_t e = cudaErrorInvalidValue;
+    if (nd <= 1) e = args(k_ks_f4s<LA, LB, RF, 1, 8>);
+    else if (nd <= 2) e = args(k_ks_f4s<LA, LB, RF, 2, 8>);
+    else if (nd <= 4) e = args(k_ks_f4s<LA, LB, RF, 4, 4>);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -1051,12 +1095,14 @@ cudaError_t ks_rotate_hoisted(const Context& c, uint32_t level, uint32_t E, cons
 cudaError_t ks_ipsum_hoisted(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
                              const uint64_t* const* ext_of, const uint64_t* const* src_of,
                              const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch,
-                             cudaStream_t s, bool ntt_out) {
+                             cudaStream_t s, bool ntt_out, KsSumInfo u) {
     if (T == 0) return cudaSuccess;
     if (c.log_n == 16)
-        return ks_ipsum_launch<8, 8, 2, 2, 2>(c, level, T, off, E, ext_of, src_of, key_of, gal_of, scratch, ntt_out, s);
+        return ks_ipsum_launch<8, 8, 2, 2, 2>(c, level, T, off, E, ext_of, src_of, key_of, gal_of, scratch, ntt_out, u,
+                                              s);
     if (c.log_n == 12)
-        return ks_ipsum_launch<6, 6, 2, 8, 8>(c, level, T, off, E, ext_of, src_of, key_of, gal_of, scratch, ntt_out, s);
+        return ks_ipsum_launch<6, 6, 2, 8, 8>(c, level, T, off, E, ext_of, src_of, key_of, gal_of, scratch, ntt_out, u,
+                                              s);
     return cudaErrorInvalidValue;
 }
 

@@ -31,7 +31,9 @@ uint64_t* g_addr[256] = {};
 
 // Device address of g_rotate_scratch on `device` (which must be current); the
 // symbol's name in host code is only a host-side stand-in, so its address is
-// looked up once per device and cached.
+// looked up once per device and cached for the life of the process (a
+// cudaDeviceReset reloads the module and may move the array: calls after one
+// are not supported).
 cudaError_t scratch_address(int device, uint64_t** out) {
     std::lock_guard<std::mutex> g(g_mu);
     if (device < 0 || device >= 256) return cudaErrorInvalidDevice;
@@ -44,6 +46,28 @@ cudaError_t scratch_address(int device, uint64_t** out) {
     *out = g_addr[device];
     return cudaSuccess;
 }
+
+// The in/out pointer lists of the key switch, written on the device from values
+// passed by value (no host staging buffer, so nothing is read from host memory
+// after the call returns).
+__global__ void k_noalloc_lists(uint64_t** lists, uint64_t* work, uint64_t* out, size_t cw, uint32_t n) {
+    const uint32_t b = threadIdx.x;
+    if (b < n) {
+        lists[b] = work + b * cw;
+        lists[kMaxCts + b] = out + b * cw;
+    }
+}
+
+// Restores the caller's current device on every return path.
+struct DeviceGuard {
+    int prev = -1;
+    DeviceGuard() {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 }  // namespace
 }  // namespace bm
@@ -76,18 +100,15 @@ extern "C" bm_status bm_ct_rotate_noalloc(bm_context* ctxh, const bm_eval_keys* 
         return BM_E_KEY_MISSING;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    DeviceGuard keep_device;
     BM_CUDA_TRY(cudaSetDevice(c.device));
     uint64_t* base = nullptr;
     BM_CUDA_TRY(scratch_address(c.device, &base));
     uint64_t** lists = (uint64_t**)base;               // [in pointers][out pointers]
     uint64_t* work = base + kListWords;                // NTT-form copy of the inputs
     uint64_t* ks = work + (size_t)n_cts * cw;          // key-switch temporaries
-    uint64_t* h[kListWords];                           // host staging on the stack
-    for (uint32_t b = 0; b < n_cts; b++) {
-        h[b] = work + b * cw;
-        h[kMaxCts + b] = d_out + b * cw;
-    }
-    BM_CUDA_TRY(cudaMemcpyAsync(lists, h, sizeof(h), cudaMemcpyHostToDevice, s));
+    k_noalloc_lists<<<1, kMaxCts, 0, s>>>(lists, work, d_out, cw, n_cts);
+    BM_CUDA_TRY(cudaGetLastError());
     BM_CUDA_TRY(cudaMemcpyAsync(work, d_in, n_cts * cw * 8, cudaMemcpyDeviceToDevice, s));
     LimbBatch all{work, n_cts * 2, (uint64_t)(level + 1) * c.n, 0, level + 1, {}};
     for (uint32_t k = 0; k <= level; k++) all.set(k, (uint8_t)k);
