@@ -54,12 +54,12 @@ using nttr::sub_words;
 using nttr::SubMem;
 using nttr::tw_wait;
 
-// Dynamic shared memory (words) of the column kernels F3/F5: exchange tiles,
+// Dynamic shared memory (words) of the column kernel F3: exchange tiles,
 // kMaxDigit thread-private staging tiles (each thread reads back only what it
 // wrote), staged twiddles.
-template <int LA, int LT, int C, int MAXS = kMaxDigit>
+template <int LA, int LT, int C>
 __host__ __device__ constexpr size_t col_smem_words() {
-    return (size_t)sub_words<LA, LT>() * C + (size_t)MAXS * (1 << LA) * C + 2 * (size_t)(1 << LA);
+    return (size_t)sub_words<LA, LT>() * C + (size_t)kMaxDigit * (1 << LA) * C + 2 * (size_t)(1 << LA);
 }
 // ... and of F4: exchange rows, staging, forward and inverse row twiddles.
 template <int LB, int LT, int R>
@@ -512,61 +512,116 @@ __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
 }
 
 // ---------------------------------------------------------------------------
-// F5: grid (B * 2, N2 / C).  conv = Conv_{P -> Q_l}(acc's special-prime limbs).
-// (MAXS: the most special limbs, the staging depth; the fused divisions call it with
-// the special set {q_L} u P -- l1 = L, L - 1 in place of L -- or {q_(L-1), q_L} u P
-// -- l1 = L - 1, L - 2 in place of L; the special limbs follow the targets in the
-// basis order either way.)
+// F5: grid (B * 2, N2 / C), GP groups of C columns a block.  conv = Conv_{P -> Q_l}(acc's
+// special-prime limbs): the inverse column pass of the ns special limbs (group g takes
+// limb g: the passes of a column run side by side), each scaled by N^-1 (P/p_i)^-1 and
+// staged in shared memory, then the conversion to the l1 target limbs and their
+// forward column passes (group g takes targets g, g + GP, ...).  Groups without a limb
+// in a phase only meet its barriers.
+// (GP: the most special limbs; the fused divisions call it with the special set
+// {q_L} u P -- l1 = L, L - 1 in place of L -- or {q_(L-1), q_L} u P -- l1 = L - 1, L - 2
+// in place of L; the special limbs follow the targets in the basis order either way.)
 // ---------------------------------------------------------------------------
-template <int LA, int LB, int LT, int C, int MAXS = kMaxDigit>
-__global__ void __launch_bounds__(C * (1 << (LA - LT)))
+// the block barriers of one register pass (one per exchange), without its arithmetic: a
+// group with nothing to transform meets the barriers of the groups that have
+template <int P, int LT>
+__device__ __forceinline__ void pass_barriers() {
+#pragma unroll
+    for (int h = 0; h + 1 < P / LT; h++) __syncthreads();
+}
+template <int LA, int LT, int C, int GP>
+__host__ __device__ constexpr size_t f5_smem_words() {   // exchange, staging, twiddles of each group
+    return (size_t)GP * (sub_words<LA, LT>() * C + (size_t)(1 << LT) * C * ((1 << LA) >> LT) + 2 * (1 << LA));
+}
+template <int LA, int LB, int LT, int C, int GP>
+__global__ void __launch_bounds__(GP * C * (1 << (LA - LT)))
     k_ks_f5(const uint64_t* __restrict__ acc, uint64_t* __restrict__ conv, const KsLevelConst* __restrict__ kc,
-            DevTables tab, uint32_t l1, uint32_t L, uint32_t alpha) {
-    constexpr int K = 1 << LT, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN, NT = C * (M >> LT);
+            DevTables tab, uint32_t l1, uint32_t L, uint32_t ns) {
+    constexpr int K = 1 << LT, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN, TPC = M >> LT, NTG = C * TPC;
+    constexpr int SW = sub_words<LA, LT>() * C;
     extern __shared__ uint64_t dsm[];
-    uint64_t* sm = dsm;
-    uint64_t* st = sm + sub_words<LA, LT>() * C;          // staging [i][k][thread] (thread-private, as F3)
-    ulonglong2* tws = (ulonglong2*)(st + MAXS * M * C);
-    const int tid = threadIdx.x, t = tid / C, jc = tid % C;
+    const int tid = threadIdx.x, g = tid / NTG, r = tid % NTG, t = r / C, jc = r % C;
+    uint64_t* xch = dsm + g * SW;                                   // the group's exchange columns
+    uint64_t* st = dsm + GP * SW;                                   // staging [ns][K][NTG]
+    ulonglong2* tws = reinterpret_cast<ulonglong2*>(st + (size_t)GP * K * NTG) + g * M;   // the group's twiddles
     const uint32_t b = blockIdx.x / 2, comp = blockIdx.x % 2;
     const int col = blockIdx.y * C + jc;
-    const uint32_t nlx = l1 + alpha;
+    const uint32_t nlx = l1 + ns;
+    const SubMem sx{xch + jc, C};
+    auto stage_tw = [&](const ulonglong2* tw) {
+        for (int i = r; i < M; i += NTG) __pipeline_memcpy_async(tws + i, tw + i, sizeof(ulonglong2));
+        __pipeline_commit();
+    };
+    // phase 1: special limb g
+    const bool a1 = (uint32_t)g < ns;
+    const int ps = (int)L + 1 + g;
+    const uint64_t p = a1 ? tab.q[ps] : tab.q[0];
+    if (a1) stage_tw(tab.itw[ps]);
     pdl_wait();
     uint64_t y[K];
-#pragma unroll 1
-    for (uint32_t i = 0; i < alpha; i++) {
-        const int pi = L + 1 + i;
-        const uint64_t p = tab.q[pi], p2 = 2 * p;
-        const uint64_t* src = acc + (((size_t)b * 2 + comp) * nlx + l1 + i) * N + col;
-        stage_col_twiddles<LA, C * (M >> LT)>(tws, tab.itw[pi]);
+    if (a1) {
+        const uint64_t* src = acc + (((size_t)b * 2 + comp) * nlx + l1 + g) * N + col;
 #pragma unroll
         for (int k = 0; k < K; k++) y[k] = src[(size_t)last_idx<LA, LT>(t, k) * N2];
-        tw_wait();
-        nttr::inv_pass<LA, LT>(y, SubMem{sm + jc, C}, tws, ColBase{}, t, p, p2);
-        const ulonglong2 h = kc->dn_hinv[i];          // N^-1 * (P/p_i)^-1 mod p_i
-#pragma unroll
-        for (int k = 0; k < K; k++) st[(i * K + k) * NT + tid] = shoup(y[k], h.x, h.y, p);
-        __syncthreads();
-    }
-#pragma unroll 1
-    for (uint32_t j = 0; j < l1; j++) {
-        const uint64_t q = tab.q[j];
-        stage_col_twiddles<LA, C * (M >> LT)>(tws, tab.tw[j]);
+    } else {
 #pragma unroll
         for (int k = 0; k < K; k++) y[k] = 0;
-#pragma unroll 1
-        for (uint32_t i = 0; i < alpha; i++) {
-            const ulonglong2 h = kc->dn_hat[i][j];
+    }
+    __pipeline_wait_prior(0);
+    __syncthreads();
+    if (a1) nttr::inv_pass<LA, LT>(y, sx, tws, ColBase{}, t, p, 2 * p);
+    else pass_barriers<LA, LT>();
+    if (a1) {
+        const ulonglong2 h = kc->dn_hinv[g];          // N^-1 * (P/p_i)^-1 mod p_i
 #pragma unroll
-            for (int k = 0; k < K; k++)
-                y[k] += shoup_lazy(st[(i * K + k) * NT + tid], h.x, h.y, q);
+        for (int k = 0; k < K; k++) st[(g * K + k) * NTG + r] = shoup(y[k], h.x, h.y, p);
+    }
+    __syncthreads();
+    // phase 2: targets g, g + GP, ...
+#pragma unroll 1
+    for (uint32_t j0 = 0; j0 < l1; j0 += GP) {
+        const uint32_t j = j0 + g;
+        const bool a2 = j < l1;
+        const uint64_t q = tab.q[a2 ? j : 0];
+        if (a2) stage_tw(tab.tw[j]);
+#pragma unroll
+        for (int k = 0; k < K; k++) y[k] = 0;
+        if (a2) {
+#pragma unroll 1
+            for (uint32_t i = 0; i < ns; i++) {
+                const ulonglong2 h = kc->dn_hat[i][j];
+#pragma unroll
+                for (int k = 0; k < K; k++) y[k] += shoup_lazy(st[(i * K + k) * NTG + r], h.x, h.y, q);
+            }
         }
 #pragma unroll
         for (int k = 0; k < K; k++) y[k] = red6(y[k], q);
-        tw_wait();
-        col_fwd_store<LA, LB, LT, C>(y, sm, tws, t, jc, q, conv + (((size_t)b * 2 + comp) * l1 + j) * N + col);
+        __pipeline_wait_prior(0);
         __syncthreads();
+        if (a2) nttr::fwd_pass<LA, LT>(y, sx, tws, ColBase{}, t, q, 2 * q);
+        else pass_barriers<LA, LT>();
+        if (a2) {
+            uint64_t* o = conv + (((size_t)b * 2 + comp) * l1 + j) * N + col;
+#pragma unroll
+            for (int k = 0; k < K; k++) o[(size_t)last_idx<LA, LT>(t, k) * N2] = y[k];
+        }
+        __syncthreads();        // the twiddles are restaged for the next targets
     }
+}
+
+// F5 of nb2 = (ciphertexts x 2 components) with ns special limbs (its shared memory set once)
+template <int LA, int LB, int LT, int C, int GP>
+cudaError_t f5_launch(uint32_t nb2, const uint64_t* acc, uint64_t* conv, const KsLevelConst* kc, const DevTables& tab,
+                      uint32_t l1, uint32_t L, uint32_t ns, cudaStream_t s) {
+    constexpr int threads = GP * C * (1 << (LA - LT));
+    constexpr size_t smem = 8 * f5_smem_words<LA, LT, C, GP>();
+    static const bool attrs =
+        cudaFuncSetAttribute(k_ks_f5<LA, LB, LT, C, GP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+        cudaSuccess;
+    (void)attrs;
+    if (ns > (uint32_t)GP) return cudaErrorInvalidValue;
+    return pdl_launch(k_ks_f5<LA, LB, LT, C, GP>, dim3(nb2, (1 << LB) / C), threads, smem, s, acc, conv, kc, tab, l1, L,
+                      ns);
 }
 
 // ---------------------------------------------------------------------------
@@ -771,7 +826,6 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
     const size_t col_smem = 8 * col_smem_words<LA, LT, C>(), f4_smem = 8 * f4_smem_words<LB, LT, R>();
     static bool attrs = [&] {
         cudaFuncSetAttribute(k_ks_f3<LA, LB, LT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem);
-        cudaFuncSetAttribute(k_ks_f5<LA, LB, LT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem);
         cudaFuncSetAttribute(k_ks_f4<LA, LB, LT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f4_smem);
         return true;
     }();
@@ -806,7 +860,7 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
     {
         ProfScope ps(BM_KERNEL_MODDOWN, s, lw * B * 2 * (alpha + l1),
                      bf_c * B * 2 * (alpha + l1) + kShoupMul * N * B * 2 * (alpha + (double)l1 * alpha));
-        pdl_launch(k_ks_f5<LA, LB, LT, C>, dim3(B * 2, N2 / C), tc, col_smem, s, acc, conv, kc, c.tab, l1, c.L, alpha);
+        f5_launch<LA, LB, LT, C, kMaxDigit>(B * 2, acc, conv, kc, c.tab, l1, c.L, alpha, s);
     }
     {
         ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * B * l1 * (2 + 2 + 1 + 2 + (d_add ? 2 : 0)),
@@ -910,13 +964,7 @@ cudaError_t ks_hoisted_launch(const Context& c, uint32_t level, uint32_t E, cons
     const KsLevelConst* kc = c.d_ksc + level;
     uint64_t* acc = scratch;
     uint64_t* conv = acc + (size_t)E * 2 * nlx * N;
-    const int tr = R * (1 << (LB - LT)), tc = C * (1 << (LA - LT));
-    const size_t col_smem = 8 * col_smem_words<LA, LT, C>();
-    static bool attrs = [&] {
-        cudaFuncSetAttribute(k_ks_f5<LA, LB, LT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem);
-        return true;
-    }();
-    (void)attrs;
+    const int tr = R * (1 << (LB - LT));
     const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;
     {
         ProfScope ps(BM_KERNEL_KS_IP, s, lw * nlx * ((double)E * nd + 2.0 * nd * E + 2.0 * E),
@@ -927,7 +975,7 @@ cudaError_t ks_hoisted_launch(const Context& c, uint32_t level, uint32_t E, cons
     {
         ProfScope ps(BM_KERNEL_MODDOWN, s, lw * E * 2 * (alpha + l1),
                      bf_c * E * 2 * (alpha + l1) + kShoupMul * N * E * 2 * (alpha + (double)l1 * alpha));
-        pdl_launch(k_ks_f5<LA, LB, LT, C>, dim3(E * 2, N2 / C), tc, col_smem, s, acc, conv, kc, c.tab, l1, c.L, alpha);
+        f5_launch<LA, LB, LT, C, kMaxDigit>(E * 2, acc, conv, kc, c.tab, l1, c.L, alpha, s);
     }
     {
         ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * E * l1 * 7, bf_r * E * 2 * l1 + kShoupMul * N * E * 2 * l1);
@@ -985,18 +1033,12 @@ cudaError_t ks_moddown_add_launch(const Context& c, uint32_t level, uint32_t T, 
     const KsLevelConst* kc = c.d_ksc + level;
     uint64_t* acc = scratch;
     uint64_t* conv = acc + (size_t)T * 2 * nlx * N;
-    const int tr = R * (1 << (LB - LT)), tc = C * (1 << (LA - LT));
-    const size_t col_smem = 8 * col_smem_words<LA, LT, C>();
-    static bool attrs = [&] {
-        cudaFuncSetAttribute(k_ks_f5<LA, LB, LT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem);
-        return true;
-    }();
-    (void)attrs;
+    const int tr = R * (1 << (LB - LT));
     const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;
     {
         ProfScope ps(BM_KERNEL_MODDOWN, s, lw * T * 2 * (alpha + l1),
                      bf_c * T * 2 * (alpha + l1) + kShoupMul * N * T * 2 * (alpha + (double)l1 * alpha));
-        pdl_launch(k_ks_f5<LA, LB, LT, C>, dim3(T * 2, N2 / C), tc, col_smem, s, acc, conv, kc, c.tab, l1, c.L, alpha);
+        f5_launch<LA, LB, LT, C, kMaxDigit>(T * 2, acc, conv, kc, c.tab, l1, c.L, alpha, s);
     }
     {
         ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * T * l1 * 8, bf_r * T * 2 * l1 + kShoupMul * N * T * 2 * l1);
@@ -1011,8 +1053,8 @@ cudaError_t ks_moddown_add_launch(const Context& c, uint32_t level, uint32_t T, 
 // L - drop): the inverse row pass of the special limbs {q_(L-drop+1) .. q_L} u P, F5
 // with that special set (l1 = L + 1 - drop targets, the dropped q-primes first among
 // the specials) and F6 with S^-1 (constants c.d_ksc_mdr[drop - 1]).  Scratch: conv of T.
-// (MAXS: F5's staging depth, alpha + drop <= MAXS; the smaller depth of one dropped
-// prime keeps that division's occupancy)
+// (MAXS: F5's groups, one per special limb, alpha + drop <= MAXS; the fewer groups
+// of one dropped prime keep that division's blocks smaller)
 template <int LA, int LB, int LT, int C, int R, int MAXS>
 cudaError_t ks_mdr_launch(const Context& c, uint32_t T, uint64_t* e, uint64_t* const* d_out, uint64_t* scratch,
                           uint32_t drop, cudaStream_t s) {
@@ -1020,14 +1062,7 @@ cudaError_t ks_mdr_launch(const Context& c, uint32_t T, uint64_t* e, uint64_t* c
     const uint32_t nlx = c.L + 1 + c.alpha, ns = c.alpha + drop, L = c.L + 1 - drop;   // L: target limbs
     const KsLevelConst* kc = c.d_ksc_mdr + (drop - 1);
     uint64_t* conv = scratch;
-    const int tr = R * (1 << (LB - LT)), tc = C * (1 << (LA - LT));
-    const size_t col_smem = 8 * col_smem_words<LA, LT, C, MAXS>();
-    static bool attrs = [&] {
-        cudaFuncSetAttribute(k_ks_f5<LA, LB, LT, C, MAXS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)col_smem);
-        return true;
-    }();
-    (void)attrs;
+    const int tr = R * (1 << (LB - LT));
     const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;
     {
         LimbBatch sb{e, T * 2, (uint64_t)nlx * N, L, ns, 0};
@@ -1039,8 +1074,7 @@ cudaError_t ks_mdr_launch(const Context& c, uint32_t T, uint64_t* e, uint64_t* c
     {
         ProfScope ps(BM_KERNEL_MODDOWN, s, lw * T * 2 * (ns + L),
                      bf_c * T * 2 * (ns + L) + kShoupMul * N * T * 2 * (ns + (double)L * ns));
-        pdl_launch(k_ks_f5<LA, LB, LT, C, MAXS>, dim3(T * 2, N2 / C), tc, col_smem, s, e, conv, kc, c.tab, L, L - 1,
-                   ns);   // special i at prime (L - 1) + 1 + i
+        f5_launch<LA, LB, LT, C, MAXS>(T * 2, e, conv, kc, c.tab, L, L - 1, ns, s);   // special i at prime L + i
     }
     {
         ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * T * L * 6, bf_r * T * 2 * L + kShoupMul * N * T * 2 * L);
