@@ -25,6 +25,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -42,6 +44,14 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="face-128d-6144")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--write-traffic", default="",
+                    help="write the DRAM-traffic record of --workload (its default forms) from this ncu CSV "
+                         "(dram__bytes_read.sum, dram__bytes_write.sum per launch) and exit")
+    ap.add_argument("--traffic-command", default="", help="--write-traffic: the ncu command the CSV came from")
+    ap.add_argument("--cpu-extrapolate", action="store_true",
+                    help="the oracle on the batched configurations, sampled and scaled (a labelled extrapolation)")
+    ap.add_argument("--cpu-sample-ids", type=int, default=32768,
+                    help="--cpu-extrapolate: identities of the sampled gallery")
     ap.add_argument("--serve", action="store_true",
                     help="serving mix: Poisson arrivals against four resident galleries through bm_server_*")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
@@ -49,6 +59,9 @@ def parse():
     ap.add_argument("--executors", type=int, default=2)
     ap.add_argument("--max-batch", type=int, default=256)
     ap.add_argument("--part", type=int, default=0, help="part size (default: the workload's)")
+    ap.add_argument("--shard", action="store_true",
+                    help="with N ranks: the gallery split by whole packs over the ranks (strong scaling: each "
+                         "rank matches the same queries against its shard); without: N replicas")
     ap.add_argument("--sweep-part", action="store_true",
                     help="N_in sweep: every part size of the workload, measured beside the cost model's prediction")
     ap.add_argument("--sweep-limit", type=float, default=4.0,
@@ -127,54 +140,208 @@ class ClockSampler:
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
 
-class OracleRun:
-    """The oracle's match of one query of the workload (keys, gallery and query prepared once)."""
+def _oracle_match(wname, form, n_ids=None):
+    """The oracle's match of one query of the workload, in the forms the GPU line runs:
+    Algorithm 1 hoisted with its key switches fused (form "fused"), or also with its
+    division moved past HE-C^3's products ("deferred"); double-hoisted rotate-and-sum
+    and compression; complex packing.  n_ids < the workload's: the first n_ids
+    identities (whole groups), for a sampled run."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from helpers_oracle import OracleMatch
+    from paper_2408_06167_gb300 import workload as wl
+    W = wl.WORKLOADS[wname]
+    return W, OracleMatch(W.preset, W.dim, W.part, n_ids or W.n_ids, 1, complex_pack=True, hoisted=form,
+                          hoisted_tail=True, double_hoisted=True)
 
-    def __init__(self, wname):
-        sys.path.insert(0, os.path.join(ROOT, "tests"))
-        from helpers_oracle import OracleMatch
-        from paper_2408_06167_gb300 import workload as wl
-        W = wl.WORKLOADS[wname]
-        self.W = W
-        self.om = OracleMatch(W.preset, W.dim, W.part, W.n_ids, 1)
+
+def _oracle_expand(om, ct, form):
+    from oracle import schedule as sch
+    return (sch.expand_query_ext if form == "deferred" else sch.expand_query_fused)(om.ev, ct, om.m, om.s)
+
+
+def _oracle_groups(om, ct, parts, groups, form):
+    """HE-C^3 (the products over the parts and their division or rescale) and the
+    rotate-and-sum for the given groups; returns (accs, mac_s, rotsum_s)."""
+    from oracle import schedule as sch
+    ev, accs, tm, tr = om.ev, [], 0.0, 0.0
+    for g in groups:
+        t0 = time.perf_counter()
+        if form == "deferred":
+            acc = ev.hec3_deferred(parts, om.gal[g], ct)
+        else:
+            acc = ev.mul_plain(parts[0], om.gal[g][0])
+            for i in range(1, len(parts)):
+                acc = ev.add(acc, ev.mul_plain(parts[i], om.gal[g][i]))
+            acc = ev.rescale(acc)
+        t1 = time.perf_counter()
+        acc = sch.rotsum_hoisted(ev, acc, om.s, double=True)
+        accs.append(acc)
+        tm += t1 - t0
+        tr += time.perf_counter() - t1
+    return accs, tm, tr
+
+
+_WORKER = {}
+
+
+def _worker_init(wname, form, n_ids):
+    _WORKER["om"] = _oracle_match(wname, form, n_ids)[1]
+
+
+def _worker_groups(ct, parts, groups, form):
+    return _oracle_groups(_WORKER["om"], ct, parts, groups, form)
+
+
+class OracleRun:
+    """The oracle's match of one query (keys, gallery and query prepared once), timed
+    by stage -- expansion (Algorithm 1), HE-C^3 products, rotate-and-sum, compression
+    -- single-threaded, or with the groups spread over `cores` worker processes (each
+    holding its own copy of the keys and gallery; the expanded query goes to them)."""
+
+    def __init__(self, wname, form, cores=1, n_ids=None):
+        from oracle import schedule as sch
+        self.form, self.cores = form, cores
+        self.W, self.om = _oracle_match(wname, form, n_ids)
+        self.n_ids = n_ids or self.W.n_ids
         self.cts = self.om.encrypt(0)
+        self.groups = len(self.om.gal)
+        self.pool = None
+        # the staged composition is the oracle's own match
+        outs = self._run()[0]
+        want, _ = self.om.match(self.cts)
+        assert np.array_equal(self.om.ct_array(outs), want), "staged oracle run differs from its match"
+        if cores > 1 and self.groups > 1:
+            import concurrent.futures
+            import multiprocessing
+            self.pool = concurrent.futures.ProcessPoolExecutor(
+                max_workers=min(cores, self.groups), mp_context=multiprocessing.get_context("spawn"),
+                initializer=_worker_init, initargs=(wname, form, n_ids))
+            list(self.pool.map(_noop, range(min(cores, self.groups))))     # workers set up before timing
+        self._sch = sch
+
+    def _run(self):
+        from oracle import schedule as sch
+        ct = self.cts[0]
+        t0 = time.perf_counter()
+        parts = _oracle_expand(self.om, ct, self.form)
+        t1 = time.perf_counter()
+        if self.pool is None:
+            accs, tm, tr = _oracle_groups(self.om, ct, parts, range(self.groups), self.form)
+        else:
+            w = min(self.cores, self.groups)
+            chunks = [list(range(k, self.groups, w)) for k in range(w)]
+            res = list(self.pool.map(_worker_groups, [ct] * w, [parts] * w, chunks, [self.form] * w))
+            accs = [None] * self.groups
+            for ch, (a, _, _) in zip(chunks, res):
+                for g, x in zip(ch, a):
+                    accs[g] = x
+            tm, tr = max(r[1] for r in res), max(r[2] for r in res)
+        t2 = time.perf_counter()
+        packs = sch.compress(self.om.ev, accs, self.om.cmask, self.om.s, hoisted="double")
+        t3 = time.perf_counter()
+        return packs, {"expansion": t1 - t0, "hec3_products": tm, "rotate_and_sum": tr, "compression": t3 - t2,
+                       "groups_wall": t2 - t1, "total": t3 - t0}
 
     def step(self):
-        t0 = time.perf_counter()
-        out, _ = self.om.match(self.cts)
-        return time.perf_counter() - t0
+        return self._run()[1]
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.shutdown()
+
+
+def _noop(_):
+    return 0
+
+
+def oracle_form(wname):
+    from paper_2408_06167_gb300 import workload as wl
+    W = wl.WORKLOADS[wname]
+    return resolve_expansion("best", W.n_ids, W.dim, W.part, True, (1 << (16 if W.preset == "ring16" else 12)) // 2)
 
 
 def cpu_baseline(wname):
-    run = OracleRun(wname)
-    t = run.step()
-    return {"value": run.W.n_ids / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one query x {run.W.n_ids} identities ({run.W.name}), full match, "
-                      f"{t:.1f} s single-threaded"}
+    """The oracle on the host cores: one query of the workload in the GPU line's forms,
+    by stage single-threaded, then with its groups spread over the host cores."""
+    form = oracle_form(wname)
+    cores = os.cpu_count() or 1
+    single = OracleRun(wname, form)
+    st = single.step()
+    multi = OracleRun(wname, form, cores=cores) if single.groups > 1 and cores > 1 else None
+    mt = multi.step() if multi else st
+    if multi:
+        multi.close()
+    used = min(cores, single.groups) if multi else 1
+    return {"value": single.n_ids / mt["total"], "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"one query x {single.n_ids} identities ({wname}), full match: Algorithm 1, then the "
+                      f"{single.groups} groups' HE-C^3 and rotate-and-sum over {used} processes, then compression",
+            "host_cpus": cores, "forms": f"{form} Algorithm 1, double-hoisted rotate-and-sum and compression, "
+                                        f"complex packing (the GPU line's)",
+            "single_thread_value": single.n_ids / st["total"],
+            "stages_s_single_thread": {k: st[k] for k in ("expansion", "hec3_products", "rotate_and_sum",
+                                                          "compression", "total")},
+            "stages_s": {k: mt[k] for k in ("expansion", "groups_wall", "compression", "total")}}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    run = OracleRun(args.workload)
+    form = oracle_form(args.workload)
+    cores = os.cpu_count() or 1
+    run = OracleRun(args.workload, form, cores=cores)
     for _ in range(args.warmup):
         run.step()
-    times = [run.step() for _ in range(args.steps)]
+    stages = [run.step() for _ in range(args.steps)]
+    run.close()
+    times = [x["total"] for x in stages]
     total = sum(times)
-    value = args.steps * run.W.n_ids / total
+    value = args.steps * run.n_ids / total
+    used = min(cores, run.groups) if run.pool else 1
+    W = run.W
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": run.W.name, "ring": "2^16" if run.W.preset == "ring16" else run.W.preset,
-                   "n_ids": run.W.n_ids, "dim": run.W.dim, "part": run.W.part, "queries_per_step": 1},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"each step: one query x {run.W.n_ids} identities, full oracle match"},
+        "config": {"workload": W.name, "ring": "2^16" if W.preset == "ring16" else W.preset,
+                   "n_ids": W.n_ids, "dim": W.dim, "part": W.part, "queries_per_step": 1, "packing": "complex",
+                   "expansion": form, "tail": "double", "gallery": "plain"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "host_cpus": cores,
+                         "sample": f"each step: one query x {run.n_ids} identities, full oracle match in the GPU "
+                                   f"line's forms, the {run.groups} groups over {used} processes"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "latency_ms": {"p50": 1e3 * statistics.median(times), "p99": 1e3 * max(times)},
+        "stages_s": {k: statistics.median(x[k] for x in stages) for k in stages[0]},
     }
     print(json.dumps(line))
+
+
+def run_cpu_extrapolate(args):
+    """The oracle on the batched configurations, sampled and scaled (a labelled
+    extrapolation, not a run of the whole configuration): per query, Algorithm 1 once;
+    HE-C^3, rotate-and-sum and compression over the first `--cpu-sample-ids`
+    identities (whole groups), scaled by the gallery's groups; x the queries of a
+    batch.  Single-threaded and over the host cores."""
+    out = {}
+    cores = os.cpu_count() or 1
+    for wname in ("finger-16d-65536-q64", "large-128d-1m-q256"):
+        from paper_2408_06167_gb300 import workload as wl
+        W = wl.WORKLOADS[wname]
+        form = oracle_form(wname)
+        n = min(W.n_ids, args.cpu_sample_ids)
+        for c in (1, cores):
+            run = OracleRun(wname, form, cores=c, n_ids=n)
+            st = run.step()
+            run.close()
+            full_groups = -(-W.n_ids // (n // run.groups if run.groups else 1))
+            scale = full_groups / run.groups
+            per_query = st["expansion"] + scale * (st["groups_wall"] + st["compression"])
+            out.setdefault(wname, {})[f"cores_{min(c, run.groups) if c > 1 else 1}"] = {
+                "sampled_ids": n, "sampled_groups": run.groups, "scale_to_groups": full_groups,
+                "stages_s_sample": st, "query_s_extrapolated": per_query,
+                "batch_s_extrapolated": per_query * W.n_queries,
+                "matches_per_s_extrapolated": W.n_ids / per_query, "forms": form}
+    print(json.dumps({"cpu_extrapolation": out, "host_cpus": cores}))
 
 
 # ---------------------------------------------------------------------------
@@ -209,24 +376,90 @@ def alu_peak_tops():
 
 
 def measured_traffic(kernel_class, workload, config):
-    """DRAM bytes per launch of a kernel class from the committed ncu record, or
-    None when the record is for another workload or schedule, or when the kernel
-    sources have changed since the counters were taken."""
-    import hashlib
+    """DRAM bytes per launch of a kernel class from the committed ncu record of the
+    workload, or None when there is none for this schedule, or when the kernel sources
+    have changed since the counters were taken."""
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
-            rec = json.load(f)
-        if rec["workload"] != workload or any(rec["config"].get(k) != config.get(k) for k in rec["config"]):
-            return None
-        h = hashlib.sha1()
-        for src in rec["sources"]:
-            with open(os.path.join(ROOT, src), "rb") as f:
-                h.update(f.read())
-        if h.hexdigest() != rec["sources_sha1"]:
-            return None
-        return float(rec["dram_bytes_per_launch"][kernel_class])
+            doc = json.load(f)
+        for rec in doc["records"]:
+            if rec["workload"] != workload or any(rec["config"].get(k) != config.get(k) for k in rec["config"]):
+                continue
+            if _sources_sha1(rec["sources"]) != rec["sources_sha1"]:
+                return None
+            return float(rec["dram_bytes_per_launch"][kernel_class])
     except (OSError, KeyError, ValueError, TypeError):
-        return None
+        pass
+    return None
+
+
+class L2Flush:
+    """Between timed steps: a 512 MiB write (larger than the 129 MB L2), then a 512 MiB
+    read of another buffer, which writes the dirty lines back before the step starts
+    (so the next step neither finds its data in L2 nor pays for that write-back)."""
+
+    def __init__(self):
+        import torch
+        self.w = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        self.r = torch.ones(L2_FLUSH_BYTES // 8, dtype=torch.int64, device="cuda")
+
+    def __call__(self):
+        self.w.zero_()
+        self.r.sum()
+
+
+# kernel classes of the library's launches by kernel name (the classes the roofline
+# can name as dominant; NTT passes also run inside other classes and are left out)
+TRAFFIC_CLASSES = {"ks_ip": ("k_ks_f4s<", "k_ks_f4h<", "k_ks_f4<"),
+                   "mac": ("k_mac<", "k_mac_ct<", "k_mac_circ<", "k_mac_circ_ntt<"),
+                   "moddown": ("k_ks_f5<",), "modup": ("k_ks_f3<", "k_ks_f3r<"), "ks_combine": ("k_ks_f6<",)}
+TRAFFIC_SOURCES = ["paper_2408_06167_gb300/csrc/kernels.cu", "paper_2408_06167_gb300/csrc/ks_fused.cu",
+                   "paper_2408_06167_gb300/csrc/ntt_reg.cuh", "paper_2408_06167_gb300/csrc/bm_math.cuh"]
+
+
+def _sources_sha1(srcs):
+    import hashlib
+    h = hashlib.sha1()
+    for src in srcs:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def write_traffic_record(csv_path, workload, config, command):
+    """Adds (or replaces) the record of `workload` in profiles/roofline_traffic.json from
+    an ncu CSV with dram__bytes_read.sum and dram__bytes_write.sum per launch: DRAM
+    bytes per launch of each kernel class, keyed by the workload, its schedule config
+    and the SHA-1 of the kernel sources."""
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    hi = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
+    h = rows[hi]
+    ki, mi, ui, vi, ii = (h.index(x) for x in ("Kernel Name", "Metric Name", "Metric Unit", "Metric Value", "ID"))
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    per = {}
+    for r in rows[hi + 1:]:
+        if len(r) > vi and r[mi] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            d = per.setdefault(r[ii], {"k": r[ki], "b": 0.0})
+            d["b"] += float(r[vi].replace(",", "")) * scale[r[ui]]
+    cls = {}
+    for d in per.values():
+        kind = next((c for c, pats in TRAFFIC_CLASSES.items() if any(p in d["k"] for p in pats)), None)
+        if kind:
+            cls.setdefault(kind, []).append(d["b"])
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        doc = json.load(open(path))
+        recs = [r for r in doc.get("records", []) if r.get("workload") != workload]
+    except (OSError, ValueError):
+        recs = []
+    recs.append({"workload": workload, "config": config,
+                 "dram_bytes_per_launch": {k: sum(v) / len(v) for k, v in sorted(cls.items())},
+                 "launches": {k: len(v) for k, v in sorted(cls.items())}, "command": command,
+                 "sources": TRAFFIC_SOURCES, "sources_sha1": _sources_sha1(TRAFFIC_SOURCES)})
+    with open(path, "w") as f:
+        json.dump({"records": recs}, f, indent=1)
+        f.write("\n")
 
 
 def across_ranks(total_s, work, world):
@@ -394,7 +627,10 @@ def roofline_of(kernel, ms, alg_bytes, alg_mul32, peak_gbs, peak_src, peak_tmul,
         views["alu_view"] = {"achieved_tmul32": tmul, "peak_tmul32": peak_tmul, "frac": tmul / peak_tmul}
         if alu["frac"] >= hbm["frac"]:
             best = alu
-    return {"kernel": kernel, **best, "traffic": traffic, **views}
+    # neither roof near: the kernel's time is set by latency (launch ramp, dependent
+    # memory round trips, barriers), which the fraction of the nearer roof states
+    regime = "at a roof" if best["frac"] >= 0.5 else "latency-bound (below half of both roofs)"
+    return {"kernel": kernel, **best, "regime": regime, "traffic": traffic, **views}
 
 
 def sched_flags(bm, expansion, tail):
@@ -432,7 +668,7 @@ def run_sweep(args):
     costs = bm.bm_measure_op_costs(ctx)
     budget = int(0.8 * torch.cuda.mem_get_info()[0])
     feats = wl.gallery(W.n_ids, W.dim)
-    qs, _ = wl.queries(feats, W.n_queries)
+    qs, _ = wl.queries(feats_all, W.n_queries)
     ref0 = wl.plaintext_scores(feats, qs[0])
     mode = bm.BM_QUERY_TILED if W.query_mode == "tiled" else bm.BM_QUERY_EXPANDED
     parts = [p for p in (128, 64, 32, 16, 8, 4, 2, 1) if p <= W.dim]
@@ -446,7 +682,7 @@ def run_sweep(args):
     model_part, _ = bm.bm_choose_part(W.preset, costs, W.n_ids, W.dim, W.n_queries, budget, packing)
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush = L2Flush()
     sampler = ClockSampler(0)
     sampler.start()
     rows = []
@@ -480,7 +716,7 @@ def run_sweep(args):
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         for k in range(steps):
-            flush.zero_()
+            flush()
             ev[k][0].record(stream)
             r = bm.bm_match(ctx, ek, gal, cts, sptr)
             ev[k][1].record(stream)
@@ -502,7 +738,7 @@ def run_sweep(args):
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": W.name, "mode": "part-sweep", "ring": "2^16" if W.preset == "ring16" else W.preset,
                    "n_ids": W.n_ids, "dim": W.dim, "queries_per_step": W.n_queries,
-                   "l2": "flushed between steps (512 MiB write)", "packing": args.packing,
+                   "l2": "flushed between steps (512 MiB write, then 512 MiB read)", "packing": args.packing,
                    "expansion": args.expansion, "tail": args.tail, "ks_wide_batch": wide},
         "sweep": rows, "model_part": model_part, "measured_best_part": best["part"],
         "model_part_measured_ms": next((r.get("measured_ms") for r in rows if r["part"] == model_part), None),
@@ -515,6 +751,16 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.cpu_extrapolate:
+        return run_cpu_extrapolate(args)
+    if args.write_traffic:
+        from paper_2408_06167_gb300 import workload as wl
+        W = wl.WORKLOADS[args.workload]
+        part = args.part or W.part
+        exp = resolve_expansion(args.expansion, W.n_ids, W.dim, part, args.packing == "complex",
+                                (1 << (16 if W.preset == "ring16" else 12)) // 2, args.gallery == "encrypted")
+        cfg = {"part": part, "packing": args.packing, "gallery": args.gallery, "expansion": exp, "tail": args.tail}
+        return write_traffic_record(args.write_traffic, W.name, cfg, args.traffic_command)
     if args.serve:
         return run_serving(args)
     if args.sweep_part:
@@ -536,7 +782,16 @@ def main():
                                        args.gallery == "encrypted")
     wide = None if args.no_tune else bm.bm_autotune_keyswitch(ctx)
     packing = bm.BM_PACK_COMPLEX if args.packing == "complex" else bm.BM_PACK_REAL
-    feats = wl.gallery(W.n_ids, W.dim)
+    feats_all = wl.gallery(W.n_ids, W.dim)
+    lo, hi = 0, W.n_ids
+    if args.shard and world > 1:
+        from paper_2408_06167_gb300 import shard
+        lay = bm.bm_gallery_layout_packed(ctx, W.n_ids, W.dim, part, packing)
+        lo, hi = shard.shard_range(W.n_ids, ctx.n // 2, part, packing == bm.BM_PACK_COMPLEX, bool(lay["compressed"]),
+                                   rank, world)
+        assert hi > lo, "more ranks than packs"
+    feats = feats_all[lo:hi]
+    n_local = hi - lo
     enroll = None
     if args.gallery == "encrypted":
         # the client encrypts every template (one GPU batch), the server enrolls them
@@ -554,7 +809,7 @@ def main():
         sk, pk, ek = bm.bm_keygen_ex(ctx, KEY_SEED, W.dim, part, bm.BM_KEYS_HOISTED if flags else 0)
         gal = bm.bm_encode_gallery_packed(ctx, feats, W.dim, part, packing)
         bm.bm_gallery_set_schedule(gal, flags)
-    qs, _ = wl.queries(feats, W.n_queries)
+    qs, _ = wl.queries(feats_all, W.n_queries)
     mode = bm.BM_QUERY_TILED if W.query_mode == "tiled" else bm.BM_QUERY_EXPANDED
     cts = [bm.bm_encrypt_query(ctx, pk, q, W.dim, part, mode, ENC_SEED, i) for i, q in enumerate(qs)]
     host_cts = [bm.bm_encrypt_query(ctx, pk, q, W.dim, part, mode, ENC_SEED, i) for i, q in enumerate(qs)]
@@ -562,12 +817,12 @@ def main():
     sptr = stream.cuda_stream
     for ct in cts:
         bm.bm_ciphertext_upload(ct, sptr)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    matches_per_step = W.n_ids * W.n_queries
+    flush = L2Flush()
+    matches_per_step = n_local * W.n_queries
 
     # correctness guard on the benchmarked configuration: decrypted Rank-1 vs FP64
     r = bm.bm_match(ctx, ek, gal, cts, sptr)
-    scores, rank1, _ = bm.bm_decrypt_scores(ctx, sk, r, 0, W.n_ids)
+    scores, rank1, _ = bm.bm_decrypt_scores(ctx, sk, r, 0, n_local)
     ref = wl.plaintext_scores(feats, qs[0])
     max_err = float(abs(scores - ref).max())
     assert max_err < 1e-5, max_err
@@ -587,7 +842,7 @@ def main():
     # bm_match_async: every step enqueued without a host wait, so each event pair holds
     # the step's device work only (no host wake-up inside it)
     for k in range(args.steps):
-        flush.zero_()
+        flush()
         ev[k][0].record(stream)
         r = bm.bm_match_async(ctx, ek, gal, cts, sptr)
         ev[k][1].record(stream)
@@ -605,7 +860,7 @@ def main():
     # per-class device time over the same number of steps (event pair per launch)
     bm.bm_profile_control(1, 1)
     for k in range(args.steps):
-        flush.zero_()
+        flush()
         r = bm.bm_match(ctx, ek, gal, cts, sptr)
         del r
     torch.cuda.synchronize()
@@ -652,11 +907,11 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "scaling": "strong" if args.shard else "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": W.name, "ring": "2^16" if W.preset == "ring16" else W.preset, "n_ids": W.n_ids,
                    "dim": W.dim, "part": part, "queries_per_step": W.n_queries,
-                   "l2": "flushed between steps (512 MiB write)",
-                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between steps (512 MiB write, then 512 MiB read)",
+                   "parallelism": ("gallery shards by pack" if args.shard else "replicas") if world > 1 else "single",
                    "packing": args.packing, "gallery": args.gallery, "expansion": args.expansion,
                    "tail": args.tail, "ks_wide_batch": wide},
         "latency_ms": {"p50": percentile(step_ms, 50), "p99": percentile(step_ms, 99)},

@@ -58,12 +58,13 @@ typedef enum bm_status {
  * 2^bits not used before it.  The paper fixes none of this (Sec. 5.1 names only
  * N = 8192, log PQ ~ 158, l = 3, under Lattigo). */
 typedef struct bm_params {
-    uint32_t log_n;               /* ring degree N = 2^log_n, 12 <= log_n <= 16 */
+    uint32_t log_n;               /* ring degree N = 2^log_n: 12 or 16 (the register-resident
+                                     NTT passes: 2^6 x 2^6 or 2^8 x 2^8 points) */
     uint32_t n_q;                 /* primes in Q (L = n_q - 1), 2 <= n_q <= BM_MAX_Q */
     uint32_t q_bits[BM_MAX_Q];    /* q_bits[0]: base prime; then rescale primes; each 30..60 */
-    uint32_t n_p;                 /* special primes, 1 <= n_p <= BM_MAX_P */
+    uint32_t n_p;                 /* special primes, 1 <= n_p <= 2 */
     uint32_t p_bits[BM_MAX_P];    /* 30..60 */
-    uint32_t dnum;                /* key-switching digits (ceil(n_q/dnum) <= 3), 1..4 */
+    uint32_t dnum;                /* key-switching digits (ceil(n_q/dnum) <= 2), 1..4 */
     uint32_t log_scale;           /* encoding scale Delta = 2^log_scale */
     uint32_t secret_hw;           /* 0: ZO(1/2) ternary secret; else ternary of this Hamming weight */
     double sigma;                 /* discrete Gaussian width of the errors (3.2) */

@@ -165,9 +165,12 @@ static std::vector<int32_t> schedule_rotations(const Context& c, const Layout& l
 // Validates the parameters and fills the context's sizes, digits and scale
 // (host only: the schedule model uses it without a device).
 static bm_status context_shape(Context& c, const bm_params& p) {
-    if (p.log_n < 12 || p.log_n > 16) return fail(BM_E_PARAM, "log_n must be in [12, 16]");
-    if (p.n_q < 2 || p.n_q > BM_MAX_Q || p.n_p < 1 || p.n_p > BM_MAX_P)
-        return fail(BM_E_PARAM, "n_q must be in [2, 6] and n_p in [1, 3]");
+    // the key-switching, rescale and NTT kernels are written for these shapes: register-
+    // resident NTT passes of 2^6 x 2^6 or 2^8 x 2^8 points, digits of at most two primes
+    // and at most two special primes
+    if (p.log_n != 12 && p.log_n != 16) return fail(BM_E_PARAM, "log_n must be 12 or 16");
+    if (p.n_q < 2 || p.n_q > BM_MAX_Q || p.n_p < 1 || p.n_p > 2)
+        return fail(BM_E_PARAM, "n_q must be in [2, 6] and n_p in [1, 2]");
     std::vector<uint32_t> bits;
     for (uint32_t i = 0; i < p.n_q; i++) bits.push_back(p.q_bits[i]);
     for (uint32_t i = 0; i < p.n_p; i++) bits.push_back(p.p_bits[i]);
@@ -175,8 +178,8 @@ static bm_status context_shape(Context& c, const bm_params& p) {
         if (b < 30 || b > 60) return fail(BM_E_PARAM, "prime sizes must be in [30, 60] bits");
     if (p.dnum < 1 || p.dnum > MAXD) return fail(BM_E_PARAM, "dnum must be in [1, 4]");
     const uint32_t dsize = (p.n_q + p.dnum - 1) / p.dnum;
-    if (dsize > MAXDS || (p.dnum - 1) * dsize >= p.n_q)
-        return fail(BM_E_PARAM, "digits must be non-empty and hold at most 3 primes");
+    if (dsize > 2 || (p.dnum - 1) * dsize >= p.n_q)
+        return fail(BM_E_PARAM, "digits must be non-empty and hold at most 2 primes");
     if (p.log_scale < 20 || p.log_scale > 50) return fail(BM_E_PARAM, "log_scale must be in [20, 50]");
     c.params = p;
     c.log_n = p.log_n;

@@ -43,117 +43,6 @@ __device__ __forceinline__ uint64_t* limb_ptr(const LimbBatch& b, uint32_t limb,
     return b.base + (size_t)poly * b.poly_stride + (size_t)(b.limb_off + k) * n;
 }
 
-// ---------------------------------------------------------------------------
-// NTT passes.  View a limb as N1 x N2 (index r*N2 + c).  Stages 0..LA-1 pair
-// rows (same column); stages LA..log N-1 pair columns inside a row.
-// ---------------------------------------------------------------------------
-
-template <int LA, int LB, int COLS, bool INV>
-__global__ void __launch_bounds__(kThreads) k_ntt_cols(LimbBatch lb, DevTables tab) {
-    constexpr int N1 = 1 << LA, N2 = 1 << LB, TILE = N1 * COLS;
-    __shared__ uint64_t sm[TILE];
-    const int pi = lb.prime(blockIdx.x % lb.nl);
-    uint64_t* a = limb_ptr(lb, blockIdx.x, N1 * N2);
-    const uint64_t q = tab.q[pi];
-    const int c0 = blockIdx.y * COLS;
-    for (int e = threadIdx.x; e < TILE; e += kThreads) sm[e] = a[(e / COLS) * N2 + c0 + (e % COLS)];
-    __syncthreads();
-    if (!INV) {
-        const ulonglong2* tw = tab.tw[pi];
-        for (int s = 0; s < LA; s++) {
-            const int half = N1 >> (s + 1);
-            for (int b = threadIdx.x; b < TILE / 2; b += kThreads) {
-                const int c = b % COLS, bi = b / COLS, i = bi / half, j = bi % half;
-                const int r0 = i * 2 * half + j, r1 = r0 + half;
-                const ulonglong2 w = tw[(1 << s) + i];
-                const uint64_t u = sm[r0 * COLS + c];
-                const uint64_t v = shoup(sm[r1 * COLS + c], w.x, w.y, q);
-                sm[r0 * COLS + c] = addm(u, v, q);
-                sm[r1 * COLS + c] = subm(u, v, q);
-            }
-            __syncthreads();
-        }
-        for (int e = threadIdx.x; e < TILE; e += kThreads) a[(e / COLS) * N2 + c0 + (e % COLS)] = sm[e];
-    } else {
-        const ulonglong2* tw = tab.itw[pi];
-        for (int s = LA - 1; s >= 0; s--) {
-            const int half = N1 >> (s + 1);
-            for (int b = threadIdx.x; b < TILE / 2; b += kThreads) {
-                const int c = b % COLS, bi = b / COLS, i = bi / half, j = bi % half;
-                const int r0 = i * 2 * half + j, r1 = r0 + half;
-                const ulonglong2 w = tw[(1 << s) + i];
-                const uint64_t u = sm[r0 * COLS + c], v = sm[r1 * COLS + c];
-                sm[r0 * COLS + c] = addm(u, v, q);
-                sm[r1 * COLS + c] = shoup(subm(u, v, q), w.x, w.y, q);
-            }
-            __syncthreads();
-        }
-        const uint64_t ni = tab.ninv[pi], nis = tab.ninv_sh[pi];
-        for (int e = threadIdx.x; e < TILE; e += kThreads)
-            a[(e / COLS) * N2 + c0 + (e % COLS)] = shoup(sm[e], ni, nis, q);
-    }
-}
-
-template <int LA, int LB, int ROWS, bool INV>
-__global__ void __launch_bounds__(kThreads) k_ntt_rows(LimbBatch lb, DevTables tab) {
-    constexpr int N2 = 1 << LB, TILE = ROWS * N2;
-    __shared__ uint64_t sm[TILE];
-    const int pi = lb.prime(blockIdx.x % lb.nl);
-    uint64_t* a = limb_ptr(lb, blockIdx.x, (1 << LA) * N2) + (size_t)blockIdx.y * TILE;
-    const uint64_t q = tab.q[pi];
-    const int rbase = blockIdx.y * ROWS;
-    for (int e = threadIdx.x; e < TILE; e += kThreads) sm[e] = a[e];
-    __syncthreads();
-    const ulonglong2* tw = INV ? tab.itw[pi] : tab.tw[pi];
-    if (!INV) {
-        for (int sp = 0; sp < LB; sp++) {
-            const int half = N2 >> (sp + 1);
-            for (int b = threadIdx.x; b < TILE / 2; b += kThreads) {
-                const int rr = b / (N2 / 2), bi = b % (N2 / 2), il = bi / half, j = bi % half;
-                const int c0 = il * 2 * half + j, c1 = c0 + half;
-                const ulonglong2 w = tw[(1 << (LA + sp)) + (rbase + rr) * (1 << sp) + il];
-                const uint64_t u = sm[rr * N2 + c0];
-                const uint64_t v = shoup(sm[rr * N2 + c1], w.x, w.y, q);
-                sm[rr * N2 + c0] = addm(u, v, q);
-                sm[rr * N2 + c1] = subm(u, v, q);
-            }
-            __syncthreads();
-        }
-    } else {
-        for (int sp = LB - 1; sp >= 0; sp--) {
-            const int half = N2 >> (sp + 1);
-            for (int b = threadIdx.x; b < TILE / 2; b += kThreads) {
-                const int rr = b / (N2 / 2), bi = b % (N2 / 2), il = bi / half, j = bi % half;
-                const int c0 = il * 2 * half + j, c1 = c0 + half;
-                const ulonglong2 w = tw[(1 << (LA + sp)) + (rbase + rr) * (1 << sp) + il];
-                const uint64_t u = sm[rr * N2 + c0], v = sm[rr * N2 + c1];
-                sm[rr * N2 + c0] = addm(u, v, q);
-                sm[rr * N2 + c1] = shoup(subm(u, v, q), w.x, w.y, q);
-            }
-            __syncthreads();
-        }
-    }
-    for (int e = threadIdx.x; e < TILE; e += kThreads) a[e] = sm[e];
-}
-
-template <int LA, int LB>
-cudaError_t ntt_launch(const LimbBatch& b, const DevTables& tab, bool inv, cudaStream_t s) {
-    constexpr int COLS = 8, ROWS = 8;
-    const uint32_t limbs = b.n_polys * b.nl;
-    if (limbs == 0) return cudaSuccess;
-    const dim3 gc(limbs, (1 << LB) / COLS), gr(limbs, (1 << LA) / ROWS);
-    const double bytes = 16.0 * (1 << (LA + LB)) * limbs;   // each pass reads and writes every limb once
-    const double ops_c = 16.0 * (1 << (LA + LB - 1)) * LA * limbs, ops_r = 16.0 * (1 << (LA + LB - 1)) * LB * limbs;
-    if (!inv) {
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_c); k_ntt_cols<LA, LB, COLS, false><<<gc, kThreads, 0, s>>>(b, tab); }
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_r); k_ntt_rows<LA, LB, ROWS, false><<<gr, kThreads, 0, s>>>(b, tab); }
-    } else {
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_r); k_ntt_rows<LA, LB, ROWS, true><<<gr, kThreads, 0, s>>>(b, tab); }
-        { ProfScope ps(BM_KERNEL_NTT, s, bytes, ops_c); k_ntt_cols<LA, LB, COLS, true><<<gc, kThreads, 0, s>>>(b, tab); }
-    }
-    return cudaGetLastError();
-}
-
 }  // namespace
 }  // namespace bm
 
@@ -185,9 +74,6 @@ cudaError_t ntt_launch_reg(const LimbBatch& b, const DevTables& tab, bool inv, c
 cudaError_t ntt_dispatch(const Context& c, const LimbBatch& b, bool inv, cudaStream_t s) {
     switch (c.log_n) {
         case 12: return ntt_launch_reg<6, 6, 2, 8, 8>(b, c.tab, inv, s);
-        case 13: return ntt_launch<7, 6>(b, c.tab, inv, s);
-        case 14: return ntt_launch<7, 7>(b, c.tab, inv, s);
-        case 15: return ntt_launch<8, 7>(b, c.tab, inv, s);
         case 16: return ntt_launch_reg<8, 8, 2, 2, 2>(b, c.tab, inv, s);
         default: return cudaErrorInvalidValue;
     }
@@ -266,201 +152,6 @@ __global__ void k_scalar(LimbBatch I, LimbBatch O, ScalarK sk, DevTables tab, ui
     const uint64_t q = tab.q[pi];
     for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x)
         o[i] = shoup(a[i], sk.w[k], sk.wsh[k], q);
-}
-
-// ---------------------------------------------------------------------------
-// key switching
-// ---------------------------------------------------------------------------
-
-struct ModUpPlan {
-    uint32_t lvl, nd, nlx;
-    uint8_t xpi[MAXB];                      // prime of extended limb jj (Q_l then P)
-    uint8_t dstart[MAXD], dsz[MAXD];        // Q-limb range of digit d
-    uint64_t hinv[MAXD][MAXDS], hinv_sh[MAXD][MAXDS];              // (D/d_i)^-1 mod d_i
-    uint64_t hat[MAXD][MAXDS][MAXB], hat_sh[MAXD][MAXDS][MAXB];    // (D/d_i) mod t_jj
-};
-
-// X: [B][2][l+1][N] copy of the inputs, poly 0 in NTT form, poly 1 in coefficient form.
-// ext[b][d][jj][p]: ModUp of digit d of sigma_k(c1), coefficient form.
-__global__ void __launch_bounds__(kThreads) k_modup(const uint64_t* __restrict__ X, uint64_t* __restrict__ ext,
-                                                    ModUpPlan pl, DevTables tab, uint32_t log_n, uint32_t kinv) {
-    const uint32_t n = 1u << log_n;
-    const uint32_t b = blockIdx.y / pl.nd, d = blockIdx.y % pl.nd;
-    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const uint32_t e = (p * kinv) & ((2u << log_n) - 1);   // sigma_k gather: X^p <- +-X^(p k^-1)
-    const bool neg = e >= n;
-    const uint32_t src = e & (n - 1);
-    const uint64_t* c1 = X + ((size_t)b * 2 + 1) * (pl.lvl + 1) * n;
-    uint64_t* out = ext + ((size_t)b * pl.nd + d) * pl.nlx * n;
-    uint64_t v[MAXDS];
-    const uint32_t ds = pl.dsz[d], d0 = pl.dstart[d];
-    for (uint32_t i = 0; i < ds; i++) {
-        const uint32_t jq = d0 + i;
-        const uint64_t q = tab.q[jq];
-        uint64_t x = c1[(size_t)jq * n + src];
-        if (neg) x = negm(x, q);
-        out[(size_t)jq * n + p] = x;
-        v[i] = shoup(x, pl.hinv[d][i], pl.hinv_sh[d][i], q);
-    }
-    for (uint32_t jj = 0; jj < pl.nlx; jj++) {
-        if (jj >= d0 && jj < d0 + ds) continue;
-        const uint64_t t = tab.q[pl.xpi[jj]];
-        uint64_t acc = 0;
-        for (uint32_t i = 0; i < ds; i++) acc += shoup_lazy(v[i], pl.hat[d][i][jj], pl.hat_sh[d][i][jj], t);
-        // acc < 2*ds*t <= 6t
-        if (acc >= 4 * t) acc -= 4 * t;
-        if (acc >= 2 * t) acc -= 2 * t;
-        out[(size_t)jj * n + p] = reduce2(acc, t);
-    }
-}
-
-struct IPPlan {
-    uint32_t nd, nlx, nb;
-    uint8_t xpi[MAXB];
-    uint8_t kidx[MAXB];   // key limb (full-basis index) of extended limb jj
-};
-
-// acc[b][c][jj] = sum_d ext[b][d][jj] * key[d][c][kidx[jj]]   (NTT domain, key Montgomery)
-__global__ void __launch_bounds__(kThreads) k_ks_ip(const uint64_t* __restrict__ ext, const uint64_t* __restrict__ key,
-                                                    uint64_t* __restrict__ acc, IPPlan pl, DevTables tab,
-                                                    uint32_t log_n) {
-    const uint32_t n = 1u << log_n;
-    const uint32_t b = blockIdx.y / pl.nlx, jj = blockIdx.y % pl.nlx;
-    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const int pi = pl.xpi[jj];
-    const uint64_t q = tab.q[pi], qn = tab.qneg[pi];
-    uint64_t s0 = 0, s1 = 0;
-    for (uint32_t d = 0; d < pl.nd; d++) {
-        const uint64_t x = ext[(((size_t)b * pl.nd + d) * pl.nlx + jj) * n + p];
-        const uint64_t k0 = key[(((size_t)d * 2 + 0) * pl.nb + pl.kidx[jj]) * n + p];
-        const uint64_t k1 = key[(((size_t)d * 2 + 1) * pl.nb + pl.kidx[jj]) * n + p];
-        s0 = reduce2(s0 + mont(x, k0, q, qn), q);
-        s1 = reduce2(s1 + mont(x, k1, q, qn), q);
-    }
-    acc[(((size_t)b * 2 + 0) * pl.nlx + jj) * n + p] = s0;
-    acc[(((size_t)b * 2 + 1) * pl.nlx + jj) * n + p] = s1;
-}
-
-struct BConvPlan {
-    uint32_t ns, nt;
-    uint8_t spi[MAXDS], tpi[MAXB];
-    uint64_t hinv[MAXDS], hinv_sh[MAXDS];
-    uint64_t hat[MAXDS][MAXB], hat_sh[MAXDS][MAXB];
-};
-
-// dst[poly][dst_off + j] = Conv_{S -> t_j}(src[poly][src_off + 0..ns-1])   (coefficient form)
-__global__ void __launch_bounds__(kThreads) k_bconv(const uint64_t* __restrict__ src, size_t src_stride,
-                                                    uint32_t src_off, uint64_t* __restrict__ dst,
-                                                    size_t dst_stride, uint32_t dst_off, BConvPlan pl,
-                                                    DevTables tab, uint32_t log_n) {
-    const uint32_t n = 1u << log_n, poly = blockIdx.y;
-    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    uint64_t v[MAXDS];
-    for (uint32_t i = 0; i < pl.ns; i++) {
-        const uint64_t x = src[poly * src_stride + (size_t)(src_off + i) * n + p];
-        v[i] = shoup(x, pl.hinv[i], pl.hinv_sh[i], tab.q[pl.spi[i]]);
-    }
-    for (uint32_t j = 0; j < pl.nt; j++) {
-        const uint64_t t = tab.q[pl.tpi[j]];
-        uint64_t acc = 0;
-        for (uint32_t i = 0; i < pl.ns; i++) acc += shoup_lazy(v[i], pl.hat[i][j], pl.hat_sh[i][j], t);
-        if (acc >= 4 * t) acc -= 4 * t;
-        if (acc >= 2 * t) acc -= 2 * t;
-        dst[poly * dst_stride + (size_t)(dst_off + j) * n + p] = reduce2(acc, t);
-    }
-}
-
-struct CombinePlan {
-    uint32_t lvl, nlx;
-    uint64_t pinv[MAXB], pinv_sh[MAXB];   // P^-1 mod q_j
-};
-
-// out[b][c][j] = (acc[b][c][j] - conv[b][c][j]) * P^-1 (+ sigma_k(c0) for c = 0) (+ add[b][c][j])
-__global__ void __launch_bounds__(kThreads) k_ks_combine(const uint64_t* __restrict__ acc,
-                                                         const uint64_t* __restrict__ conv,
-                                                         const uint64_t* __restrict__ X,
-                                                         uint64_t* const* out, uint64_t* const* add,
-                                                         CombinePlan pl, DevTables tab, uint32_t log_n,
-                                                         uint64_t galois) {
-    const uint32_t n = 1u << log_n, l1 = pl.lvl + 1;
-    const uint32_t b = blockIdx.y / l1, j = blockIdx.y % l1;
-    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const uint64_t q = tab.q[j];
-    const uint64_t a0 = acc[(((size_t)b * 2 + 0) * pl.nlx + j) * n + p];
-    const uint64_t a1 = acc[(((size_t)b * 2 + 1) * pl.nlx + j) * n + p];
-    const uint64_t v0 = conv[(((size_t)b * 2 + 0) * l1 + j) * n + p];
-    const uint64_t v1 = conv[(((size_t)b * 2 + 1) * l1 + j) * n + p];
-    uint64_t o0 = shoup(subm(a0, v0, q), pl.pinv[j], pl.pinv_sh[j], q);
-    uint64_t o1 = shoup(subm(a1, v1, q), pl.pinv[j], pl.pinv_sh[j], q);
-    const uint64_t c0 = X[((size_t)b * 2 * l1 + j) * n + ntt_perm_src(p, log_n, galois)];
-    o0 = addm(o0, c0, q);
-    if (add != nullptr) {
-        const uint64_t* ad = add[b];
-        o0 = addm(o0, ad[(size_t)j * n + p], q);
-        o1 = addm(o1, ad[((size_t)l1 + j) * n + p], q);
-    }
-    uint64_t* o = out[b];
-    o[(size_t)j * n + p] = o0;
-    o[((size_t)l1 + j) * n + p] = o1;
-}
-
-// X[b] = in[b] (both polys, limbs 0..l)
-__global__ void k_gather_cts(uint64_t* const* in, uint64_t* X, uint32_t words_per_ct) {
-    const uint32_t b = blockIdx.y;
-    const uint64_t* s = in[b];
-    uint64_t* d = X + (size_t)b * words_per_ct;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < words_per_ct; i += gridDim.x * blockDim.x)
-        d[i] = s[i];
-}
-
-// ---------------------------------------------------------------------------
-// rescale
-// ---------------------------------------------------------------------------
-
-// Y[b*2 + c] = limb l of poly c of in[b]
-__global__ void k_gather_last(uint64_t* const* in, uint64_t* Y, uint32_t lvl, uint32_t n) {
-    const uint32_t bc = blockIdx.y, b = bc / 2, c = bc % 2;
-    const uint64_t* s = in[b] + ((size_t)c * (lvl + 1) + lvl) * n;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        Y[(size_t)bc * n + i] = s[i];
-}
-
-// Rl[bc][j] = centred(Y[bc]) mod q_j for j < l (Y: coefficient form mod q_l)
-__global__ void k_rescale_lift(const uint64_t* Y, uint64_t* Rl, uint32_t lvl, DevTables tab, uint32_t n) {
-    const uint32_t bc = blockIdx.y;
-    const uint64_t ql = tab.q[lvl];
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint64_t v = Y[(size_t)bc * n + i];
-        const bool neg = v > (ql >> 1);
-        const uint64_t mag = neg ? ql - v : v;
-        for (uint32_t j = 0; j < lvl; j++) {
-            const uint64_t qj = tab.q[j];
-            const uint64_t r = reduce2(shoup_lazy(mag, 1, tab.rsh[j], qj), qj);
-            Rl[((size_t)bc * lvl + j) * n + i] = neg ? negm(r, qj) : r;
-        }
-    }
-}
-
-struct RescalePlan {
-    uint32_t lvl;
-    uint64_t inv[MAXB], inv_sh[MAXB];   // q_l^-1 mod q_j
-};
-
-// out[b][c][j] = (in[b][c][j] - Rl[b*2+c][j]) * q_l^-1
-__global__ void k_rescale_combine(uint64_t* const* in, const uint64_t* Rl, uint64_t* const* out,
-                                  RescalePlan pl, DevTables tab, uint32_t n) {
-    const uint32_t l = pl.lvl;
-    const uint32_t y = blockIdx.y, b = y / (2 * l), c = (y / l) % 2, j = y % l;
-    const uint64_t q = tab.q[j];
-    const uint64_t* s = in[b] + ((size_t)c * (l + 1) + j) * n;
-    const uint64_t* r = Rl + (((size_t)b * 2 + c) * l + j) * n;
-    uint64_t* o = out[b] + ((size_t)c * l + j) * n;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        o[i] = shoup(subm(s[i], r[i], q), pl.inv[j], pl.inv_sh[j], q);
 }
 
 // ---------------------------------------------------------------------------
@@ -914,7 +605,6 @@ __global__ void k_accumulate(uint64_t* const* dst, const uint64_t* const* src, c
     }
 }
 
-inline dim3 elem_grid(uint32_t n, uint32_t y) { return dim3((n + kThreads - 1) / kThreads, y); }
 
 }  // namespace
 
@@ -1109,120 +799,9 @@ cudaError_t ks_rotate(const Context& c, const uint64_t* key, uint64_t galois, ui
                       uint64_t* const* d_in, uint64_t* const* d_out, uint64_t* const* d_add, uint64_t* scratch,
                       cudaStream_t s) {
     if (B == 0) return cudaSuccess;
-    if (ks_fused_supported(c)) return ks_rotate_fused(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
-    const uint32_t n = c.n, l1 = level + 1, nlx = l1 + c.alpha;
-    // digits present at this level
-    ModUpPlan mu{};
-    mu.lvl = level;
-    mu.nlx = nlx;
-    for (uint32_t jj = 0; jj < nlx; jj++) mu.xpi[jj] = (uint8_t)(jj < l1 ? jj : c.L + 1 + (jj - l1));
-    uint32_t nd = 0;
-    for (auto& dg : c.digits) {
-        if (dg.empty() || dg[0] > level) continue;
-        uint32_t ds = 0;
-        for (uint32_t x : dg) ds += (x <= level);
-        mu.dstart[nd] = (uint8_t)dg[0];
-        mu.dsz[nd] = (uint8_t)ds;
-        for (uint32_t i = 0; i < ds; i++) {
-            const uint64_t qi = c.primes[dg[0] + i];
-            uint64_t hat = 1;
-            for (uint32_t k = 0; k < ds; k++)
-                if (k != i) hat = h_mulmod(hat, c.primes[dg[0] + k] % qi, qi);
-            mu.hinv[nd][i] = h_invmod(hat, qi);
-            mu.hinv_sh[nd][i] = h_shoup_companion(mu.hinv[nd][i], qi);
-            for (uint32_t jj = 0; jj < nlx; jj++) {
-                const uint64_t t = c.primes[mu.xpi[jj]];
-                uint64_t ht = 1;
-                for (uint32_t k = 0; k < ds; k++)
-                    if (k != i) ht = h_mulmod(ht, c.primes[dg[0] + k] % t, t);
-                mu.hat[nd][i][jj] = ht;
-                mu.hat_sh[nd][i][jj] = h_shoup_companion(ht, t);
-            }
-        }
-        nd++;
-    }
-    mu.nd = nd;
-
-    uint64_t* X = scratch;                                 // [B][2][l1][N]
-    uint64_t* ext = X + (size_t)B * 2 * l1 * n;            // [B][nd][nlx][N]
-    uint64_t* acc = ext + (size_t)B * nd * nlx * n;        // [B][2][nlx][N]
-    uint64_t* conv = acc + (size_t)B * 2 * nlx * n;        // [B][2][l1][N]
-
-    {
-        ProfScope ps(BM_KERNEL_OTHER, s, 32.0 * B * l1 * n);
-        k_gather_cts<<<dim3(64, B), kThreads, 0, s>>>(d_in, X, 2 * l1 * n);
-    }
-    // c1 -> coefficient form
-    LimbBatch c1b{X + (size_t)l1 * n, B, (uint64_t)2 * l1 * n, 0, l1, {}};
-    for (uint32_t k = 0; k < l1; k++) c1b.set(k, (uint8_t)k);
-    cudaError_t e = ntt_inverse(c, c1b, s);
-    if (e != cudaSuccess) return e;
-    const uint32_t kinv = (uint32_t)h_invmod_pow2(galois, 2ull * n);
-    {
-        double bytes = 0;
-        for (uint32_t d = 0; d < nd; d++) bytes += 8.0 * n * B * (mu.dsz[d] + nlx);
-        ProfScope ps(BM_KERNEL_MODUP, s, bytes);
-        k_modup<<<elem_grid(n, B * nd), kThreads, 0, s>>>(X, ext, mu, c.tab, c.log_n, kinv);
-    }
-    LimbBatch eb{ext, B * nd, (uint64_t)nlx * n, 0, nlx, {}};
-    for (uint32_t jj = 0; jj < nlx; jj++) eb.set(jj, mu.xpi[jj]);
-    if ((e = ntt_forward(c, eb, s)) != cudaSuccess) return e;
-    IPPlan ip{};
-    ip.nd = nd;
-    ip.nlx = nlx;
-    ip.nb = c.nb;
-    for (uint32_t jj = 0; jj < nlx; jj++) {
-        ip.xpi[jj] = mu.xpi[jj];
-        ip.kidx[jj] = mu.xpi[jj];
-    }
-    {
-        ProfScope ps(BM_KERNEL_KS_IP, s, 8.0 * n * nlx * ((double)B * nd + 2.0 * nd + 2.0 * B));
-        k_ks_ip<<<elem_grid(n, B * nlx), kThreads, 0, s>>>(ext, key, acc, ip, c.tab, c.log_n);
-    }
-    // ModDown: P limbs -> coefficient form -> convert to Q_l -> NTT
-    LimbBatch pb{acc, B * 2, (uint64_t)nlx * n, l1, c.alpha, {}};
-    for (uint32_t k = 0; k < c.alpha; k++) pb.set(k, (uint8_t)(c.L + 1 + k));
-    if ((e = ntt_inverse(c, pb, s)) != cudaSuccess) return e;
-    BConvPlan bp{};
-    bp.ns = c.alpha;
-    bp.nt = l1;
-    for (uint32_t i = 0; i < c.alpha; i++) {
-        bp.spi[i] = (uint8_t)(c.L + 1 + i);
-        const uint64_t pi_ = c.primes[c.L + 1 + i];
-        uint64_t hat = 1;
-        for (uint32_t k = 0; k < c.alpha; k++)
-            if (k != i) hat = h_mulmod(hat, c.primes[c.L + 1 + k] % pi_, pi_);
-        bp.hinv[i] = h_invmod(hat, pi_);
-        bp.hinv_sh[i] = h_shoup_companion(bp.hinv[i], pi_);
-        for (uint32_t j = 0; j < l1; j++) {
-            const uint64_t t = c.primes[j];
-            uint64_t ht = 1;
-            for (uint32_t k = 0; k < c.alpha; k++)
-                if (k != i) ht = h_mulmod(ht, c.primes[c.L + 1 + k] % t, t);
-            bp.hat[i][j] = ht;
-            bp.hat_sh[i][j] = h_shoup_companion(ht, t);
-        }
-    }
-    for (uint32_t j = 0; j < l1; j++) bp.tpi[j] = (uint8_t)j;
-    {
-        ProfScope ps(BM_KERNEL_MODDOWN, s, 8.0 * n * B * 2 * (c.alpha + l1));
-        k_bconv<<<elem_grid(n, B * 2), kThreads, 0, s>>>(acc, (size_t)nlx * n, l1, conv, (size_t)l1 * n, 0, bp,
-                                                         c.tab, c.log_n);
-    }
-    LimbBatch cb{conv, B * 2, (uint64_t)l1 * n, 0, l1, {}};
-    for (uint32_t j = 0; j < l1; j++) cb.set(j, (uint8_t)j);
-    if ((e = ntt_forward(c, cb, s)) != cudaSuccess) return e;
-    CombinePlan cp{};
-    cp.lvl = level;
-    cp.nlx = nlx;
-    for (uint32_t j = 0; j < l1; j++) {
-        const uint64_t q = c.primes[j];
-        cp.pinv[j] = h_invmod(c.P_mod[j], q);
-        cp.pinv_sh[j] = h_shoup_companion(cp.pinv[j], q);
-    }
-    ProfScope ps(BM_KERNEL_KS_COMBINE, s, 8.0 * n * B * l1 * (2 + 2 + 1 + 2 + (d_add ? 2 : 0)));
-    k_ks_combine<<<elem_grid(n, B * l1), kThreads, 0, s>>>(acc, conv, X, d_out, d_add, cp, c.tab, c.log_n, galois);
-    return cudaGetLastError();
+    // every context the library creates is one the fused kernels cover (context_shape)
+    if (!ks_fused_supported(c)) return cudaErrorInvalidValue;
+    return ks_rotate_fused(c, key, galois, level, B, d_in, d_out, d_add, scratch, s);
 }
 
 // ---- rescale ----
@@ -1234,35 +813,8 @@ size_t rescale_scratch_words(const Context& c, uint32_t level, uint32_t B) {
 cudaError_t rescale(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in, uint64_t* const* d_out,
                     uint64_t* scratch, cudaStream_t s) {
     if (B == 0) return cudaSuccess;
-    if (ks_fused_supported(c)) return rescale_fused(c, level, B, d_in, d_out, scratch, s);
-    const uint32_t n = c.n;
-    uint64_t* Y = scratch;                         // [B*2][N]
-    uint64_t* Rl = Y + (size_t)B * 2 * n;          // [B*2][level][N]
-    {
-        ProfScope ps(BM_KERNEL_RESCALE, s, 16.0 * n * B * 2);
-        k_gather_last<<<dim3(n / kThreads / 4, B * 2), kThreads, 0, s>>>(d_in, Y, level, n);
-    }
-    LimbBatch yb{Y, B * 2, n, 0, 1, {}};
-    yb.set(0, (uint8_t)level);
-    cudaError_t e = ntt_inverse(c, yb, s);
-    if (e != cudaSuccess) return e;
-    {
-        ProfScope ps(BM_KERNEL_RESCALE, s, 8.0 * n * B * 2 * (1 + level));
-        k_rescale_lift<<<dim3(n / kThreads / 4, B * 2), kThreads, 0, s>>>(Y, Rl, level, c.tab, n);
-    }
-    LimbBatch rb{Rl, B * 2, (uint64_t)level * n, 0, level, {}};
-    for (uint32_t j = 0; j < level; j++) rb.set(j, (uint8_t)j);
-    if ((e = ntt_forward(c, rb, s)) != cudaSuccess) return e;
-    RescalePlan rp{};
-    rp.lvl = level;
-    for (uint32_t j = 0; j < level; j++) {
-        const uint64_t q = c.primes[j];
-        rp.inv[j] = h_invmod(c.primes[level] % q, q);
-        rp.inv_sh[j] = h_shoup_companion(rp.inv[j], q);
-    }
-    ProfScope ps(BM_KERNEL_RESCALE, s, 24.0 * n * B * 2 * level);
-    k_rescale_combine<<<dim3(n / kThreads / 4, B * 2 * level), kThreads, 0, s>>>(d_in, Rl, d_out, rp, c.tab, n);
-    return cudaGetLastError();
+    if (!ks_fused_supported(c)) return cudaErrorInvalidValue;
+    return rescale_fused(c, level, B, d_in, d_out, scratch, s);
 }
 
 cudaError_t mul_plain(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,

@@ -62,9 +62,9 @@ __host__ __device__ constexpr size_t col_smem_words() {
     return (size_t)sub_words<LA, LT>() * C + (size_t)kMaxDigit * (1 << LA) * C + 2 * (size_t)(1 << LA);
 }
 // ... and of F4: exchange rows, staging, forward and inverse row twiddles.
-template <int LB, int LT, int R>
+template <int LB, int LT, int R, int ND>
 __host__ __device__ constexpr size_t f4_smem_words() {
-    return (size_t)R * sub_words<LB, LT>() + (LT > 2 ? (size_t)kMaxDigit * R * (1 << LB) : 0) +
+    return (size_t)R * sub_words<LB, LT>() + (LT > 2 ? (size_t)ND * R * (1 << LB) : 0) +
            4 * (size_t)row_tw_entries<LB, R>();
 }
 
@@ -180,9 +180,11 @@ __global__ void __launch_bounds__(C * (1 << (LA - LT)))
 }
 
 // ---------------------------------------------------------------------------
-// F4: grid (B * nlx, N1 / R).  acc = sum_d ext_d * key_d (both components).
+// F4: grid (B * nlx, N1 / R).  acc = sum_d ext_d * key_d (both components), up to
+// ND digits (their row-passed extension words in registers, or in shared memory for
+// the 16-coefficient shape).
 // ---------------------------------------------------------------------------
-template <int LA, int LB, int LT, int R>
+template <int LA, int LB, int LT, int R, int ND>
 __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
     k_ks_f4(const uint64_t* __restrict__ ext, const uint64_t* __restrict__ key, uint64_t* __restrict__ acc,
             const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L, uint32_t nb) {
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
     const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
     const SubMem sr{dsm + jr * S, 1};                        // exchange row
     uint64_t* st = dsm + R * S;                              // staging (16-coefficient shape): [d][k][tid]
-    ulonglong2* twf = (ulonglong2*)(dsm + R * S + (REG ? 0 : kMaxDigit * R * M));
+    ulonglong2* twf = (ulonglong2*)(dsm + R * S + (REG ? 0 : ND * R * M));
     ulonglong2* twi = twf + TWN;
     const uint32_t nd = kc->nd, nlx = kc->nlx;
     const uint32_t b = blockIdx.x / nlx, jj = blockIdx.x % nlx;
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
     if (jj >= l1) stage_row_twiddles<LA, LB, R, R * TH>(twi, tab.itw[pi], blockIdx.y * R);
     tw_wait();
     pdl_wait();
-    uint64_t v[K], s0[REG ? K : 1], s1[REG ? K : 1];
+    uint64_t v[K], sv[REG ? ND : 1][REG ? K : 1];
     // extended limb jj of every digit, NTT form, last-phase layout
 #pragma unroll 1
     for (uint32_t d = 0; d < nd; d++) {
@@ -222,10 +224,11 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
         }
         if constexpr (REG) {
 #pragma unroll
-            for (int k = 0; k < K; k++) {
-                if (d == 0) s0[k] = v[k];
-                else s1[k] = v[k];
-            }
+            for (int dd = 0; dd < ND; dd++)
+                if ((uint32_t)dd == d) {
+#pragma unroll
+                    for (int k = 0; k < K; k++) sv[dd][k] = v[k];
+                }
         } else {
 #pragma unroll
             for (int k = 0; k < K; k++) st[(d * K + k) * NT + tid] = v[k];
@@ -236,16 +239,18 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
 #pragma unroll 1
     for (uint32_t comp = 0; comp < 2; comp++) {
         Acc128 a[K];
-#pragma unroll 1
-        for (uint32_t d = 0; d < nd; d++) {
-            uint64_t kv[K];
-            nttr::load_last<LB, LT>(kv, key + ((size_t)(d * 2 + comp) * nb + pi) * N + roff, t);
 #pragma unroll
-            for (int k = 0; k < K; k++) {
-                uint64_t e;
-                if constexpr (REG) e = d == 0 ? s0[k] : s1[k];
-                else e = st[(d * K + k) * NT + tid];
-                mul_acc(a[k], e, kv[k], q);              // e < 4q after the row pass: allowed
+        for (int d = 0; d < ND; d++) {
+            if ((uint32_t)d < nd) {
+                uint64_t kv[K];
+                nttr::load_last<LB, LT>(kv, key + ((size_t)(d * 2 + comp) * nb + pi) * N + roff, t);
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    uint64_t e;
+                    if constexpr (REG) e = sv[d][k];
+                    else e = st[(d * K + k) * NT + tid];
+                    mul_acc(a[k], e, kv[k], q);              // e < 4q after the row pass: allowed
+                }
             }
         }
 #pragma unroll
@@ -823,10 +828,13 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
     uint64_t* acc = ext + (size_t)B * nd * nlx * N;
     uint64_t* conv = acc + (size_t)B * 2 * nlx * N;
     const int tr = R * (1 << (LB - LT)), tc = C * (1 << (LA - LT));
-    const size_t col_smem = 8 * col_smem_words<LA, LT, C>(), f4_smem = 8 * f4_smem_words<LB, LT, R>();
+    const size_t col_smem = 8 * col_smem_words<LA, LT, C>();
+    const size_t f4_smem2 = 8 * f4_smem_words<LB, LT, R, 2>(), f4_smem4 = 8 * f4_smem_words<LB, LT, R, MAXD>();
     static bool attrs = [&] {
         cudaFuncSetAttribute(k_ks_f3<LA, LB, LT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem);
-        cudaFuncSetAttribute(k_ks_f4<LA, LB, LT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f4_smem);
+        cudaFuncSetAttribute(k_ks_f4<LA, LB, LT, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f4_smem2);
+        cudaFuncSetAttribute(k_ks_f4<LA, LB, LT, R, MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)f4_smem4);
         return true;
     }();
     (void)attrs;
@@ -855,7 +863,12 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
     {
         ProfScope ps(BM_KERNEL_KS_IP, s, lw * nlx * ((double)B * nd + 2.0 * nd + 2.0 * B),
                      bf_r * B * (targets + 2.0 * alpha) + N * B * nlx * 2.0 * (kProdMul * nd + kRedcMul));
-        pdl_launch(k_ks_f4<LA, LB, LT, R>, dim3(B * nlx, N1 / R), tr, f4_smem, s, ext, key, acc, kc, c.tab, l1, c.L, c.nb);
+        if (nd <= 2)
+            pdl_launch(k_ks_f4<LA, LB, LT, R, 2>, dim3(B * nlx, N1 / R), tr, f4_smem2, s, ext, key, acc, kc, c.tab, l1,
+                       c.L, c.nb);
+        else
+            pdl_launch(k_ks_f4<LA, LB, LT, R, MAXD>, dim3(B * nlx, N1 / R), tr, f4_smem4, s, ext, key, acc, kc, c.tab,
+                       l1, c.L, c.nb);
     }
     {
         ProfScope ps(BM_KERNEL_MODDOWN, s, lw * B * 2 * (alpha + l1),

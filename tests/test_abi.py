@@ -43,3 +43,28 @@ def test_presets_and_errors_without_gpu():
         assert e.status == 1
     else:
         raise AssertionError("unknown preset accepted")
+
+
+def test_context_refuses_shapes_outside_the_kernels():
+    """The key-switching, rescale and NTT kernels cover rings 2^12 and 2^16, digits
+    of at most two primes and at most two special primes; other parameter sets are
+    refused before any device work (so this runs without a GPU)."""
+    from paper_2408_06167_gb300 import binding as bm
+    cases = []
+    for log_n in (11, 13, 14, 15, 17):
+        p = bm.bm_params_preset("small4")
+        p.log_n = log_n
+        cases.append(p)
+    p = bm.bm_params_preset("small4")
+    p.n_p, p.p_bits[2] = 3, 60
+    cases.append(p)
+    p = bm.bm_params_preset("small4")
+    p.dnum = 1                       # one digit of four primes
+    cases.append(p)
+    for p in cases:
+        try:
+            bm.bm_context_create(p)
+        except bm.BlindMatchError as e:
+            assert e.status == 2, (p.log_n, p.n_p, p.dnum, str(e))
+        else:
+            raise AssertionError(f"accepted log_n={p.log_n} n_p={p.n_p} dnum={p.dnum}")

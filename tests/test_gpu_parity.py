@@ -233,3 +233,51 @@ def test_errors_are_reported():
     with pytest.raises(bm.BlindMatchError) as e:
         bm.bm_match(c, ek2, g, [ct2])
     assert e.value.status == 4           # BM_E_KEY_MISSING
+
+
+DNUM4 = ckks.Params(12, (60, 40, 40, 40), (60, 60), dnum=4, secret_hw=192)
+
+
+def dnum4_ctx():
+    """The 4-prime chain with one prime a key-switching digit (four digits at the top
+    level: the plain and hoisted key switches sum four products a word)."""
+    if "small4-dnum4" not in _CTX:
+        p = bm.bm_params_preset("small4")
+        p.dnum = 4
+        _CTX["small4-dnum4"] = bm.bm_context_create(p)
+    return _CTX["small4-dnum4"]
+
+
+@pytest.mark.parametrize("level,rot", [(0, 1), (1, -8), (2, 16), (3, 16), (3, 64)])
+def test_rotation_four_digits_is_bit_exact(level, rot):
+    c, o = dnum4_ctx(), octx(DNUM4)
+    _, _, ek = bm.bm_keygen(c, KEY_SEED, 128, 16)
+    key = ckks.keygen_rotation(o, KEY_SEED, ckks.sample_secret(o, KEY_SEED), o.galois_left(rot))
+    ev = ckks.Evaluator(o, {key.galois: key})
+    data = _random_ct(o, level, 2, 40 + level)
+    got = bm.bm_ciphertext_export(bm.bm_ct_rotate(c, ek, bm.bm_ciphertext_import(c, data, level), rot))
+    for b in range(2):
+        want = ev.rotate(ckks.Ciphertext(data[b, 0], data[b, 1], level, 1.0), rot)
+        assert np.array_equal(got[b, 0], want.c0) and np.array_equal(got[b, 1], want.c1), b
+
+
+@pytest.mark.parametrize("form", ["fused", "deferred"])
+def test_match_four_digits_is_bit_exact(form):
+    """The bench's forms (fused Algorithm 1 with or without the deferred division,
+    double-hoisted tail, complex packing) with four digits: the hoisted sums of the
+    top level take four digits a word."""
+    c = dnum4_ctx()
+    m, s, R = 128, 16, 700
+    om = OracleMatch(DNUM4, m, s, R, 1, complex_pack=True, hoisted=form, hoisted_tail=True, double_hoisted=True)
+    _, _, ek = bm.bm_keygen_ex(c, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
+    g = bm.bm_gallery_import_packed(c, om.pts_array(), om.masks_array(), om.cmask_array(), R, m, s, bm.BM_PACK_COMPLEX)
+    flags = bm.BM_SCHED_ALL | bm.BM_SCHED_DOUBLE_HOISTED | bm.BM_SCHED_FUSED_EXPANSION
+    if form == "deferred":
+        flags |= bm.BM_SCHED_DEFERRED_DIVISION
+    bm.bm_gallery_set_schedule(g, flags)
+    cts = om.encrypt(0)
+    res = bm.bm_match(c, ek, g, [bm.bm_ciphertext_import(c, om.ct_array(cts), om.ctx.L)])
+    want, packed = om.match(cts)
+    got = bm.bm_result_export(res, 0)
+    assert np.array_equal(got, want)
+    assert np.abs(om.scores(got, packed) - wl.plaintext_scores(om.feats, om.queries[0])).max() < 1e-5
