@@ -54,7 +54,11 @@ def parse():
                     help="--cpu-extrapolate: identities of the sampled gallery")
     ap.add_argument("--serve", action="store_true",
                     help="serving mix: Poisson arrivals against four resident galleries through bm_server_*")
-    ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
+    ap.add_argument("--rate", default="200", help="serving: arrivals per second (comma-separated: one line each)")
+    ap.add_argument("--rate-too", action="store_true", help="serving: the Poisson rates as well as --closed-loop")
+    ap.add_argument("--closed-loop", default="0",
+                    help="serving: K clients, each submitting its next query when its previous result is back "
+                         "(in place of Poisson arrivals)")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--executors", type=int, default=2)
     ap.add_argument("--max-batch", type=int, default=256)
@@ -549,52 +553,104 @@ def run_serving(args):
     mean_single_s = sum(single_ms) / len(single_ms) / 1e3        # uniform gallery choice
     unbatched_rate = 1.0 / mean_single_s
     unbatched_mps = sum(G["R"] for G in gals) / len(gals) * unbatched_rate
-    srv = bm.bm_server_create(ctx, 160 << 30, max_batch=args.max_batch, executors=args.executors)
-    gids = [bm.bm_server_add_gallery(srv, G["g"], G["ek"]) for G in gals]
-    rng = np.random.default_rng(ARRIVAL_SEED)
-    n = int(args.rate * args.duration)
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=n))
-    choice = rng.integers(0, len(gals), size=n)
-    errors = []
-    pending = []
-    start = time.perf_counter()
-    sampler = ClockSampler(0)
-    sampler.start()
-    for k in range(n):
-        delay = start + arrivals[k] - time.perf_counter()
-        if delay > 0:
-            time.sleep(delay)
-        G = gals[choice[k]]
-        pending.append((choice[k], bm.bm_server_submit(srv, gids[choice[k]], G["cts"][k % len(G["cts"])])))
-    for gi, t in pending:
-        try:
-            bm.bm_server_wait(srv, t, 3600 * 1000)
-        except bm.BlindMatchError as e:
-            errors.append(str(e))
-    wall = time.perf_counter() - start
-    clocks = sampler.stop()
-    st = bm.bm_server_stats(srv)
-    matches = sum(gals[c]["R"] for c in choice)
-    line = {
-        "metric": METRIC, "value": st["matches_per_s"], "unit": UNIT, "n_gpus": 1, "steps": n, "warmup": 0,
-        "ms_per_step": 1e3 * wall / n, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "serving-mix", "ring": "2^16", "arrivals_per_s": args.rate,
-                   "duration_s": args.duration, "galleries": [g[0] for g in SERVE_GALLERIES],
-                   "executors": args.executors, "max_batch": args.max_batch, "parts": parts,
-                   "part_choice": "cost model (bm_choose_part, 16 queries)" if costs is not None else "fixed",
-                   "packing": args.packing, "expansion": expansions,
-                   "ks_wide_batch": wide},
-        "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]},
-        "server": {k: st[k] for k in ("submitted", "completed", "failed", "batches", "mean_batch",
-                                      "workspace_bytes")},
-        "errors": errors[:3],
-        "wall_s": wall, "matches": matches,
-        "unbatched": {"single_query_ms": dict(zip([g[0] for g in SERVE_GALLERIES], single_ms)),
-                      "sustainable_queries_per_s": unbatched_rate, "matches_per_s": unbatched_mps},
-        "clocks": clocks,
-    }
-    print(json.dumps(line))
+    closed = [int(k) for k in str(args.closed_loop).split(",") if int(k) > 0]
+    settings = [("closed", k) for k in closed]
+    if not closed or args.rate_too:
+        settings += [("poisson", float(r)) for r in str(args.rate).split(",")]
+    for kind, amount in settings:
+        args.closed_loop_n = amount if kind == "closed" else 0
+        args.rate_v = amount if kind == "poisson" else 0.0
+        srv = bm.bm_server_create(ctx, 160 << 30, max_batch=args.max_batch, executors=args.executors)
+        gids = [bm.bm_server_add_gallery(srv, G["g"], G["ek"]) for G in gals]
+        import queue
+        import threading
+        errors = []
+        start = time.perf_counter()
+        sampler = ClockSampler(0)
+        sampler.start()
+        choice = []
+        if args.closed_loop_n:
+            # K clients, each submitting its next query as soon as its previous result is back
+            lock = threading.Lock()
+
+            def client(k):
+                rng_k = np.random.default_rng([ARRIVAL_SEED, k])
+                i = 0
+                while time.perf_counter() - start < args.duration:
+                    gi = int(rng_k.integers(0, len(gals)))
+                    G = gals[gi]
+                    try:
+                        t = bm.bm_server_submit(srv, gids[gi], G["cts"][(k + i) % len(G["cts"])])
+                        bm.bm_server_wait(srv, t, 3600 * 1000)
+                    except bm.BlindMatchError as e:
+                        with lock:
+                            errors.append(str(e))
+                    with lock:
+                        choice.append(gi)
+                    i += 1
+
+            threads = [threading.Thread(target=client, args=(k,)) for k in range(args.closed_loop_n)]
+            for th in threads:
+                th.start()
+            for th in threads:
+                th.join()
+            n = len(choice)
+        else:
+            # Poisson arrivals; a waiter collects (and drops) each result as it completes
+            rng = np.random.default_rng(ARRIVAL_SEED)
+            n = int(args.rate_v * args.duration)
+            arrivals = np.cumsum(rng.exponential(1.0 / args.rate_v, size=n))
+            choice = list(rng.integers(0, len(gals), size=n))
+            tickets = queue.Queue()
+
+            def waiter():
+                while True:
+                    t = tickets.get()
+                    if t is None:
+                        return
+                    try:
+                        bm.bm_server_wait(srv, t, 3600 * 1000)
+                    except bm.BlindMatchError as e:
+                        errors.append(str(e))
+
+            wt = threading.Thread(target=waiter)
+            wt.start()
+            for k in range(n):
+                delay = start + arrivals[k] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                G = gals[choice[k]]
+                tickets.put(bm.bm_server_submit(srv, gids[choice[k]], G["cts"][k % len(G["cts"])]))
+            tickets.put(None)
+            wt.join()
+        wall = time.perf_counter() - start
+        clocks = sampler.stop()
+        st = bm.bm_server_stats(srv)
+        matches = sum(gals[c]["R"] for c in choice)
+        line = {
+            "metric": METRIC, "value": st["matches_per_s"], "unit": UNIT, "n_gpus": 1, "steps": n, "warmup": 0,
+            "ms_per_step": 1e3 * wall / n, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "serving-mix", "ring": "2^16",
+                       "arrivals": (f"closed loop, {args.closed_loop_n} clients" if args.closed_loop_n
+                                    else f"Poisson, {args.rate_v:g} per s"),
+                       "arrivals_per_s": n / wall,
+                       "duration_s": args.duration, "galleries": [g[0] for g in SERVE_GALLERIES],
+                       "executors": args.executors, "max_batch": args.max_batch, "parts": parts,
+                       "part_choice": "cost model (bm_choose_part, 16 queries)" if costs is not None else "fixed",
+                       "packing": args.packing, "expansion": expansions,
+                       "ks_wide_batch": wide},
+            "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]},
+            "server": {k: st[k] for k in ("submitted", "completed", "failed", "batches", "mean_batch",
+                                          "workspace_bytes")},
+            "errors": errors[:3],
+            "wall_s": wall, "matches": matches,
+            "unbatched": {"single_query_ms": dict(zip([g[0] for g in SERVE_GALLERIES], single_ms)),
+                          "sustainable_queries_per_s": unbatched_rate, "matches_per_s": unbatched_mps},
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+        del srv
 
 
 def resolve_expansion(expansion, n_ids, dim, part, complex_pack, slots, encrypted=False):

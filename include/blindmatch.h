@@ -587,6 +587,34 @@ bm_status bm_measure_op_costs(bm_context* ctx, bm_op_costs* out);
 bm_status bm_autotune_keyswitch(bm_context* ctx, uint32_t* wide_batch_out, size_t capacity);
 bm_status bm_set_ks_wide_batch(bm_context* ctx, uint32_t level, uint32_t batch);
 
+/* The standalone NTT (the match's ingest and egress transforms, and the transforms
+ * of the client-side calls) comes in three shapes: 0 = radix-4 register phases with 2
+ * rows or columns a block (ring 2^12: 8), 1 = radix-4 with 4 a block (ring 2^12: 16),
+ * 2 = radix-16 phases with 8 a block (ring 2^16 only).  A batch of `limbs` limbs
+ * falls in bucket k, the smallest with limbs <= 2^k (the last bucket, k =
+ * BM_NTT_BUCKETS - 1, takes every larger batch).  bm_autotune_ntt times a forward
+ * and an inverse transform of 2^k limbs in every shape for each bucket and keeps,
+ * per bucket, the fastest (shape 0 unless another is 2% faster); shapes_out[k]
+ * receives the choice (NULL to skip).  Every shape gives the same residues.
+ * bm_set_ntt_shape sets one bucket by hand.  Plans built before keep their kernels.
+ * (NTT radix and tile as tuned parameters: no counterpart in the paper, whose cost
+ * model of Sec. 4 measures per-operation times the same way.) */
+#define BM_NTT_BUCKETS 10
+bm_status bm_autotune_ntt(bm_context* ctx, uint8_t* shapes_out, size_t capacity);
+bm_status bm_set_ntt_shape(bm_context* ctx, uint32_t bucket, uint32_t shape);
+
+/* Key-switching digits (dnum) chosen by the cost model of Sec. 4: for each dnum in
+ * 1..4 that bm_context_create accepts with the other fields of *base, a context on
+ * `device` is made, its kernel shapes tuned (bm_autotune_keyswitch, bm_autotune_ntt),
+ * its per-operation costs measured (bm_measure_op_costs) and the match of n_queries
+ * queries against n_ids identities (dim, part_size, packing: as bm_predict_match)
+ * predicted; *dnum_out gets the dnum of least predicted time, ms_out[d - 1] (when not
+ * NULL, capacity >= 4) each prediction in ms (0: dnum not taken).  More digits make
+ * smaller digit products but more extension limbs and larger keys.  Takes about a
+ * minute at ring 2^16.  BM_E_PARAM if no dnum is taken. */
+bm_status bm_choose_dnum(const bm_params* base, int device, uint64_t n_ids, uint32_t dim, uint32_t part_size,
+                         uint32_t packing, uint32_t n_queries, uint32_t* dnum_out, double* ms_out, size_t capacity);
+
 #ifdef __cplusplus
 }
 #endif

@@ -160,6 +160,10 @@ _SIGS = {
     "bm_measure_op_costs": (ctypes.c_int, [_vp, ctypes.POINTER(bm_op_costs)]),
     "bm_autotune_keyswitch": (ctypes.c_int, [_vp, _U32P, ctypes.c_size_t]),
     "bm_set_ks_wide_batch": (ctypes.c_int, [_vp, _u32, _u32]),
+    "bm_autotune_ntt": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint8), ctypes.c_size_t]),
+    "bm_set_ntt_shape": (ctypes.c_int, [_vp, _u32, _u32]),
+    "bm_choose_dnum": (ctypes.c_int, [ctypes.POINTER(bm_params), ctypes.c_int, _u64, _u32, _u32, _u32, _u32, _U32P,
+                                      _DP, ctypes.c_size_t]),
     "bm_profile_control": (ctypes.c_int, [_u32, _u32]),
     "bm_profile_read": (ctypes.c_int, [_u32, _U64P, _DP, _DP, _DP]),
 }
@@ -612,3 +616,26 @@ def bm_autotune_keyswitch(ctx):
 
 def bm_set_ks_wide_batch(ctx, level, batch):
     _check(_L.bm_set_ks_wide_batch(ctx.ptr, level, batch))
+
+
+BM_NTT_BUCKETS = 10
+
+
+def bm_autotune_ntt(ctx):
+    """Per batch bucket (limbs <= 2^k) the standalone NTT shape the tuner keeps (0, 1, 2)."""
+    out = (ctypes.c_uint8 * BM_NTT_BUCKETS)()
+    _check(_L.bm_autotune_ntt(ctx.ptr, out, BM_NTT_BUCKETS))
+    return list(out)
+
+
+def bm_set_ntt_shape(ctx, bucket, shape):
+    _check(_L.bm_set_ntt_shape(ctx.ptr, bucket, shape))
+
+
+def bm_choose_dnum(params, n_ids, dim, part, n_queries, packing=BM_PACK_REAL, device=0):
+    """(dnum of least predicted match time, predicted ms per dnum 1..4 (0: not taken))."""
+    p = _params(params)
+    d = _u32()
+    ms = (ctypes.c_double * 4)()
+    _check(_L.bm_choose_dnum(ctypes.byref(p), device, n_ids, dim, part, packing, n_queries, ctypes.byref(d), ms, 4))
+    return d.value, list(ms)

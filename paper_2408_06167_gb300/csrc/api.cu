@@ -256,14 +256,7 @@ static bm_status context_init(Context& c, const bm_params& p, int device) {
         c.tab.itw[j] = (const ulonglong2*)c.d_twiddles + j * per + c.n;
     }
     BM_CUDA_TRY(build_ks_constants(c));
-    {
-        int sms = 0;
-        BM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
-        c.sm_count = (uint32_t)sms;
-        BM_CUDA_TRY(cudaHostAlloc((void**)&c.h_ks_err, sizeof(int), cudaHostAllocMapped | cudaHostAllocPortable));
-        *c.h_ks_err = 0;
-        BM_CUDA_TRY(cudaHostGetDevicePointer((void**)&c.d_ks_err, c.h_ks_err, 0));
-    }
+
     if (const char* w = std::getenv("BM_KS_WIDE_BATCH"))
         for (uint32_t& t : c.ks_wide_batch) t = (uint32_t)std::strtoul(w, nullptr, 10);
     return BM_OK;
@@ -352,7 +345,6 @@ void context_free(bm_context* ctx) {
     if (ctx->c.d_ksc) cudaFree(ctx->c.d_ksc);
     if (ctx->c.d_ksc_mdr) cudaFree(ctx->c.d_ksc_mdr);
     if (ctx->c.d_qlinv) cudaFree(ctx->c.d_qlinv);
-    if (ctx->c.h_ks_err) cudaFreeHost(ctx->c.h_ks_err);
     if (ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
     delete ctx;
 }

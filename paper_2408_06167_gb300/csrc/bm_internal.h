@@ -96,6 +96,16 @@ struct EncoderTables {
     std::vector<uint32_t> pos, cpos;          // slot j -> index t of 5^j = 2t+1, and of -5^j
 };
 
+// Batch buckets of the standalone NTT: bucket k holds batches of 2^(k-1) + 1 .. 2^k limbs
+// (bucket 0: one limb; the last: 2^(kNttBuckets-2) + 1 limbs and more).
+constexpr int kNttBuckets = BM_NTT_BUCKETS;
+inline int ntt_bucket(uint32_t limbs) {
+    int k = 0;
+    while (k + 1 < kNttBuckets && (1u << k) < limbs) k++;
+    return k;
+}
+constexpr int kNttShapes = 3;
+
 struct Context {
     bm_params params{};
     int device = 0;
@@ -118,9 +128,8 @@ struct Context {
                                               // per level: key-switch batches of at least this many
                                               // ciphertexts use 16 coefficients per thread (set by
                                               // bm_autotune_keyswitch / bm_set_ks_wide_batch / BM_KS_WIDE_BATCH)
-    uint32_t sm_count = 0;                    // SMs of the device (persistent kernels: one block each)
-    int* h_ks_err = nullptr;                  // bounded device waits that expired (page-locked, mapped;
-    int* d_ks_err = nullptr;                  //   the kernels set it, the host reads and clears it)
+    uint8_t ntt_shape[kNttBuckets] = {};      // standalone NTT shape per batch bucket (ntt_bucket):
+                                              // set by bm_autotune_ntt / bm_set_ntt_shape
     uint64_t next_id = 1;                     // ids of galleries and key sets (plan cache keys)
     std::vector<Plan*> plans;
     // lifetime: every handle made from the context holds a reference; the context
@@ -345,6 +354,8 @@ bool prof_timing();
 // ---- kernel launchers (kernels.cu) ----
 cudaError_t ntt_forward(const Context& c, const LimbBatch& b, cudaStream_t s);
 cudaError_t ntt_inverse(const Context& c, const LimbBatch& b, cudaStream_t s);
+// the same in a given shape (0..kNttShapes-1), whatever the context's choice
+cudaError_t ntt_dispatch_shape(const Context& c, const LimbBatch& b, bool inv, int shape, cudaStream_t s);
 // x -> x * 2^64 mod q (Montgomery form) / back, on a limb batch
 cudaError_t to_montgomery(const Context& c, const LimbBatch& b, bool inverse, cudaStream_t s);
 // out[poly][k][i] = signed v[poly][i] mod q_k on each limb (v: device int64[n_polys][N])

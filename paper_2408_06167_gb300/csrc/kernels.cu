@@ -71,12 +71,30 @@ cudaError_t ntt_launch_reg(const LimbBatch& b, const DevTables& tab, bool inv, c
     return cudaGetLastError();
 }
 
-cudaError_t ntt_dispatch(const Context& c, const LimbBatch& b, bool inv, cudaStream_t s) {
+}  // namespace
+
+// The standalone NTT in one of three shapes (the tuner's choice per batch size, see
+// ntt_shape_of): 0 = radix-4 register phases, 2 rows or columns a block (ring 2^12: 8);
+// 1 = radix-4, 4 a block (ring 2^12: 16); 2 = radix-16 phases, 8 a block (ring 2^16
+// only; ring 2^12 keeps shape 0).  Every shape computes the same transform and ends in
+// canonical residues, so the choice never changes a result.
+cudaError_t ntt_dispatch_shape(const Context& c, const LimbBatch& b, bool inv, int shape, cudaStream_t s) {
     switch (c.log_n) {
-        case 12: return ntt_launch_reg<6, 6, 2, 8, 8>(b, c.tab, inv, s);
-        case 16: return ntt_launch_reg<8, 8, 2, 2, 2>(b, c.tab, inv, s);
+        case 12:
+            return shape == 1 ? ntt_launch_reg<6, 6, 2, 16, 16>(b, c.tab, inv, s)
+                              : ntt_launch_reg<6, 6, 2, 8, 8>(b, c.tab, inv, s);
+        case 16:
+            return shape == 2   ? ntt_launch_reg<8, 8, 4, 8, 8>(b, c.tab, inv, s)
+                   : shape == 1 ? ntt_launch_reg<8, 8, 2, 4, 4>(b, c.tab, inv, s)
+                                : ntt_launch_reg<8, 8, 2, 2, 2>(b, c.tab, inv, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+namespace {
+
+cudaError_t ntt_dispatch(const Context& c, const LimbBatch& b, bool inv, cudaStream_t s) {
+    return ntt_dispatch_shape(c, b, inv, c.ntt_shape[ntt_bucket(b.n_polys * b.nl)], s);
 }
 
 // ---------------------------------------------------------------------------

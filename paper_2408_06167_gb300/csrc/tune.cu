@@ -220,6 +220,80 @@ bm_status bm_autotune_keyswitch(bm_context* ctxh, uint32_t* wide_batch_out, size
     return BM_OK;
 }
 
+bm_status bm_set_ntt_shape(bm_context* ctxh, uint32_t bucket, uint32_t shape) {
+    if (!ctxh) return fail(BM_E_ARG, "null context");
+    if (bucket >= (uint32_t)kNttBuckets || shape >= (uint32_t)kNttShapes)
+        return fail(BM_E_ARG, "bucket or shape out of range");
+    ctxh->c.ntt_shape[bucket] = (uint8_t)shape;
+    return BM_OK;
+}
+
+bm_status bm_autotune_ntt(bm_context* ctxh, uint8_t* shapes_out, size_t capacity) {
+    if (!ctxh) return fail(BM_E_ARG, "null context");
+    Context& c = ctxh->c;
+    if (shapes_out && capacity < (size_t)kNttBuckets) return fail(BM_E_ARG, "capacity below BM_NTT_BUCKETS");
+    BM_CUDA_TRY(cudaSetDevice(c.device));
+    const uint32_t max_limbs = 1u << (kNttBuckets - 1);
+    DevBuf buf;
+    BM_CUDA_TRY(buf.alloc((size_t)max_limbs * c.n));
+    cudaStream_t s = c.stream;
+    BM_CUDA_TRY(fill(c, buf.p, buf.words, c.nb, 21, s));
+    Timer tm(s);
+    const int shapes = c.log_n == 16 ? kNttShapes : 2;
+    for (int k = 0; k < kNttBuckets; k++) {
+        const uint32_t limbs = 1u << k;
+        // limbs cycle through the primes of the full basis (a batch of ciphertext limbs)
+        LimbBatch b{buf.p, limbs, (uint64_t)c.n, 0, 1, {}};
+        b.set(0, 0);
+        double t[kNttShapes] = {};
+        for (int sh = 0; sh < shapes; sh++)
+            t[sh] = tm.us([&] {
+                cudaError_t e = ntt_dispatch_shape(c, b, false, sh, s);
+                return e != cudaSuccess ? e : ntt_dispatch_shape(c, b, true, sh, s);
+            }, 2, reps_for(limbs));
+        BM_CUDA_TRY(tm.err);
+        int best = 0;
+        for (int sh = 1; sh < shapes; sh++)
+            if (t[sh] < 0.98 * t[best]) best = sh;
+        c.ntt_shape[k] = (uint8_t)best;
+    }
+    if (shapes_out)
+        for (int k = 0; k < kNttBuckets; k++) shapes_out[k] = c.ntt_shape[k];
+    return BM_OK;
+}
+
+bm_status bm_choose_dnum(const bm_params* base, int device, uint64_t n_ids, uint32_t dim, uint32_t part_size,
+                         uint32_t packing, uint32_t n_queries, uint32_t* dnum_out, double* ms_out, size_t capacity) {
+    if (!base || !dnum_out) return fail(BM_E_ARG, "null argument");
+    if (ms_out && capacity < (size_t)MAXD) return fail(BM_E_ARG, "capacity below 4");
+    double best = 0;
+    uint32_t best_d = 0;
+    for (uint32_t d = 1; d <= (uint32_t)MAXD; d++) {
+        if (ms_out) ms_out[d - 1] = 0;
+        bm_params p = *base;
+        p.dnum = d;
+        bm_context* ctx = nullptr;
+        if (bm_context_create(&p, device, &ctx) != BM_OK) continue;   // digits the kernels do not take
+        bm_op_costs costs{};
+        double ms = 0;
+        uint64_t bytes = 0;
+        bm_status st = bm_autotune_keyswitch(ctx, nullptr, 0);
+        if (st == BM_OK) st = bm_autotune_ntt(ctx, nullptr, 0);
+        if (st == BM_OK) st = bm_measure_op_costs(ctx, &costs);
+        if (st == BM_OK) st = bm_predict_match(&p, &costs, n_ids, dim, part_size, packing, n_queries, &ms, &bytes);
+        bm_context_destroy(ctx);
+        if (st != BM_OK) return st;
+        if (ms_out) ms_out[d - 1] = ms;
+        if (!best_d || ms < best) {
+            best = ms;
+            best_d = d;
+        }
+    }
+    if (!best_d) return fail(BM_E_PARAM, "no digit count the kernels take for these parameters");
+    *dnum_out = best_d;
+    return BM_OK;
+}
+
 bm_status bm_measure_op_costs(bm_context* ctxh, bm_op_costs* out) {
     if (!ctxh || !out) return fail(BM_E_ARG, "null argument");
     Context& c = ctxh->c;

@@ -140,3 +140,55 @@ def test_server_plan_bytes_equal_the_estimate():
         bm.bm_server_wait(srv2, bm.bm_server_submit(srv2, gid2, ct))
     assert e.value.status == 7
     assert bm.bm_server_stats(srv2)["workspace_bytes"] == 0
+
+
+@pytest.mark.parametrize("name,limbs", [("ring16", 1), ("ring16", 24), ("ring16", 300), ("small4", 5), ("small4", 70)])
+def test_every_ntt_shape_gives_the_same_residues(name, limbs):
+    """The three standalone NTT shapes (radix-4 with 2 or 4 rows a block, radix-16
+    with 8) are the same transform: forward outputs equal, inverse returns the input."""
+    c, o = bm.bm_context_create(name), octx(name)
+    rng = np.random.default_rng(limbs)
+    nl = len(o.primes)
+    x = np.stack([rng.integers(0, o.primes[k % nl], size=o.n, dtype=np.uint64) for k in range(limbs)])
+    n_polys = -(-limbs // nl)
+    host = np.zeros((n_polys * nl, o.n), dtype=np.uint64)
+    host[:limbs] = x
+    for k in range(limbs, n_polys * nl):
+        host[k] = rng.integers(0, o.primes[k % nl], size=o.n, dtype=np.uint64)
+    outs = []
+    for shape in range(3):
+        for b in range(bm.BM_NTT_BUCKETS):
+            bm.bm_set_ntt_shape(c, b, shape)
+        d = torch.from_numpy(host.view(np.int64).copy()).cuda()
+        bm.bm_ntt_forward(c, d.data_ptr(), n_polys, nl)
+        torch.cuda.synchronize()
+        outs.append(d.cpu().numpy().view(np.uint64).copy())
+        bm.bm_ntt_inverse(c, d.data_ptr(), n_polys, nl)
+        torch.cuda.synchronize()
+        assert np.array_equal(d.cpu().numpy().view(np.uint64), host), shape
+    assert np.array_equal(outs[1], outs[0]) and np.array_equal(outs[2], outs[0])
+
+
+def test_tuned_ntt_shapes_keep_the_match(ring16):
+    c = ring16
+    m, s, R = 128, 16, 6144
+    feats = wl.gallery(R, m)
+    qs, _ = wl.queries(feats, 1)
+    sk, pk, ek = bm.bm_keygen(c, KEY_SEED, m, s)
+    g = bm.bm_encode_gallery(c, feats, m, s)
+    ct = bm.bm_encrypt_query(c, pk, qs[0], m, s, bm.BM_QUERY_TILED, 4, 0)
+    base = bm.bm_result_export(bm.bm_match(c, ek, g, [ct]), 0)
+    shapes = bm.bm_autotune_ntt(c)
+    assert len(shapes) == bm.BM_NTT_BUCKETS and all(0 <= x <= 2 for x in shapes)
+    for b in range(bm.BM_NTT_BUCKETS):
+        bm.bm_set_ntt_shape(c, b, 2)
+    r = bm.bm_match(c, ek, g, [ct, ct])                   # a new plan in the radix-16 shape
+    assert np.array_equal(bm.bm_result_export(r, 1), base)
+    for b, x in enumerate(shapes):
+        bm.bm_set_ntt_shape(c, b, x)
+
+
+def test_dnum_choice_is_a_taken_digit_count():
+    d, ms = bm.bm_choose_dnum("small4", 3000, 16, 4, 2, bm.BM_PACK_COMPLEX)
+    assert d in (2, 4) and ms[d - 1] > 0 and ms[0] == 0 and ms[2] == 0     # dnum 1 and 3 are refused
+    assert ms[d - 1] == min(x for x in ms if x > 0)
