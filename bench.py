@@ -61,6 +61,8 @@ def parse():
                          "(in place of Poisson arrivals)")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--executors", type=int, default=2)
+    ap.add_argument("--serve-warmup", type=float, default=5.0,
+                    help="serving: seconds of closed-loop requests before each measured window (plans built)")
     ap.add_argument("--max-batch", type=int, default=256)
     ap.add_argument("--part", type=int, default=0, help="part size (default: the workload's)")
     ap.add_argument("--shard", action="store_true",
@@ -73,6 +75,9 @@ def parse():
     ap.add_argument("--auto-part", action="store_true",
                     help="serving: each gallery's part size chosen by the cost model (bm_choose_part)")
     ap.add_argument("--no-tune", action="store_true", help="skip the rotation kernel-shape tuner")
+    ap.add_argument("--tune-dnum", action="store_true",
+                    help="also report the cost model's choice of key-switching digits for the workload (the line "
+                         "itself keeps the configuration's dnum)")
     ap.add_argument("--expansion", default="best",
                     choices=["doubling", "hoisted", "fused", "deferred", "best", "auto"],
                     help="form of Algorithm 1: the printed doubling order, the hoisted sum, the hoisted sum "
@@ -502,6 +507,7 @@ def run_serving(args):
     from paper_2408_06167_gb300 import workload as wl
     ctx = bm.bm_context_create("ring16", 0)
     wide = None if args.no_tune else bm.bm_autotune_keyswitch(ctx)
+    ntt_shapes = None if args.no_tune else bm.bm_autotune_ntt(ctx)
     costs = bm.bm_measure_op_costs(ctx) if args.auto_part else None
     keys, gals, parts = {}, [], {}
     packing = bm.BM_PACK_COMPLEX if args.packing == "complex" else bm.BM_PACK_REAL
@@ -565,18 +571,16 @@ def run_serving(args):
         import queue
         import threading
         errors = []
-        start = time.perf_counter()
-        sampler = ClockSampler(0)
-        sampler.start()
-        choice = []
-        if args.closed_loop_n:
+        lock = threading.Lock()
+
+        def closed_loop(K, dur, choice):
             # K clients, each submitting its next query as soon as its previous result is back
-            lock = threading.Lock()
+            t_end = time.perf_counter() + dur
 
             def client(k):
-                rng_k = np.random.default_rng([ARRIVAL_SEED, k])
+                rng_k = np.random.default_rng([ARRIVAL_SEED, k, int(dur * 1000)])
                 i = 0
-                while time.perf_counter() - start < args.duration:
+                while time.perf_counter() < t_end:
                     gi = int(rng_k.integers(0, len(gals)))
                     G = gals[gi]
                     try:
@@ -589,11 +593,23 @@ def run_serving(args):
                         choice.append(gi)
                     i += 1
 
-            threads = [threading.Thread(target=client, args=(k,)) for k in range(args.closed_loop_n)]
+            threads = [threading.Thread(target=client, args=(k,)) for k in range(K)]
             for th in threads:
                 th.start()
             for th in threads:
                 th.join()
+
+        # untimed warm-up: the plans the setting uses are built before the window opens
+        if args.serve_warmup > 0:
+            closed_loop(max(args.closed_loop_n, 16), args.serve_warmup, [])
+            bm.bm_server_reset_stats(srv)
+            errors.clear()
+        start = time.perf_counter()
+        sampler = ClockSampler(0)
+        sampler.start()
+        choice = []
+        if args.closed_loop_n:
+            closed_loop(args.closed_loop_n, args.duration, choice)
             n = len(choice)
         else:
             # Poisson arrivals; a waiter collects (and drops) each result as it completes
@@ -639,7 +655,7 @@ def run_serving(args):
                        "executors": args.executors, "max_batch": args.max_batch, "parts": parts,
                        "part_choice": "cost model (bm_choose_part, 16 queries)" if costs is not None else "fixed",
                        "packing": args.packing, "expansion": expansions,
-                       "ks_wide_batch": wide},
+                       "ks_wide_batch": wide, "ntt_shapes": ntt_shapes},
             "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]},
             "server": {k: st[k] for k in ("submitted", "completed", "failed", "batches", "mean_batch",
                                           "workspace_bytes")},
@@ -721,6 +737,7 @@ def run_sweep(args):
     W = wl.WORKLOADS[args.workload]
     ctx = bm.bm_context_create(W.preset, 0)
     wide = None if args.no_tune else bm.bm_autotune_keyswitch(ctx)
+    ntt_shapes = None if args.no_tune else bm.bm_autotune_ntt(ctx)
     costs = bm.bm_measure_op_costs(ctx)
     budget = int(0.8 * torch.cuda.mem_get_info()[0])
     feats = wl.gallery(W.n_ids, W.dim)
@@ -795,7 +812,7 @@ def run_sweep(args):
         "config": {"workload": W.name, "mode": "part-sweep", "ring": "2^16" if W.preset == "ring16" else W.preset,
                    "n_ids": W.n_ids, "dim": W.dim, "queries_per_step": W.n_queries,
                    "l2": "flushed between steps (512 MiB write, then 512 MiB read)", "packing": args.packing,
-                   "expansion": args.expansion, "tail": args.tail, "ks_wide_batch": wide},
+                   "expansion": args.expansion, "tail": args.tail, "ks_wide_batch": wide, "ntt_shapes": ntt_shapes},
         "sweep": rows, "model_part": model_part, "measured_best_part": best["part"],
         "model_part_measured_ms": next((r.get("measured_ms") for r in rows if r["part"] == model_part), None),
         "clocks": clocks,
@@ -837,6 +854,7 @@ def main():
     args.expansion = resolve_expansion(args.expansion, W.n_ids, W.dim, part, args.packing == "complex", ctx.n // 2,
                                        args.gallery == "encrypted")
     wide = None if args.no_tune else bm.bm_autotune_keyswitch(ctx)
+    ntt_shapes = None if args.no_tune else bm.bm_autotune_ntt(ctx)
     packing = bm.BM_PACK_COMPLEX if args.packing == "complex" else bm.BM_PACK_REAL
     feats_all = wl.gallery(W.n_ids, W.dim)
     lo, hi = 0, W.n_ids
@@ -969,7 +987,7 @@ def main():
                    "l2": "flushed between steps (512 MiB write, then 512 MiB read)",
                    "parallelism": ("gallery shards by pack" if args.shard else "replicas") if world > 1 else "single",
                    "packing": args.packing, "gallery": args.gallery, "expansion": args.expansion,
-                   "tail": args.tail, "ks_wide_batch": wide},
+                   "tail": args.tail, "ks_wide_batch": wide, "ntt_shapes": ntt_shapes},
         "latency_ms": {"p50": percentile(step_ms, 50), "p99": percentile(step_ms, 99)},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -981,6 +999,11 @@ def main():
     }
     if enroll:
         line["enrollment"] = enroll
+    if args.tune_dnum:
+        flags_l = sched_flags(bm, args.expansion, args.tail)[1] | packing
+        d, ms = bm.bm_choose_dnum(W.preset, W.n_ids, W.dim, part, W.n_queries, flags_l, local)
+        line["dnum_model"] = {"chosen": d, "predicted_ms_by_dnum": {str(k + 1): v for k, v in enumerate(ms) if v > 0},
+                              "line_dnum": ctx.dnum}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(line))

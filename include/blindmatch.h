@@ -378,7 +378,9 @@ typedef struct bm_server_stats_t {
  * stream and match plans, repeatedly take the oldest request together with the
  * other pending requests for the same gallery (at most max_batch) and run them as
  * one batched bm_match, so requests that arrive while others run join the next
- * batch and batches of different executors overlap on the GPU.  Match workspaces
+ * batch and batches of different executors overlap on the GPU.  A batch runs the
+ * plan of the largest power of two of queries it holds (so plans are reused and no
+ * plan runs padding); the rest go back to the front of the queue.  Match workspaces
  * are admitted against hbm_budget_bytes of device memory: an executor evicts its
  * own idle plans first, then halves its batch; a single query that does not fit
  * fails with BM_E_HBM_BUDGET.  Galleries and key sets are borrowed and must
@@ -403,6 +405,9 @@ bm_status bm_server_wait(bm_server* srv, uint64_t ticket, uint32_t timeout_ms, b
 /* Cancels a request that has not started; BM_E_ARG if it is running or done. */
 bm_status bm_server_cancel(bm_server* srv, uint64_t ticket);
 bm_status bm_server_stats(bm_server* srv, bm_server_stats_t* out);
+/* Zeroes the counters and latencies bm_server_stats reports (plans and pending
+ * requests are kept): a measurement window after a warm-up. */
+bm_status bm_server_reset_stats(bm_server* srv);
 
 /* ---- single operations, for checking the kernels against a reference ---- */
 

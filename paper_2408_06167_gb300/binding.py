@@ -150,6 +150,7 @@ _SIGS = {
     "bm_server_wait": (ctypes.c_int, [_vp, _u64, _u32, _PP]),
     "bm_server_cancel": (ctypes.c_int, [_vp, _u64]),
     "bm_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(bm_server_stats_t)]),
+    "bm_server_reset_stats": (ctypes.c_int, [_vp]),
     "bm_plan_estimate": (ctypes.c_int, [ctypes.POINTER(bm_params), _u64, _u32, _u32, _u32, _u32,
                                         ctypes.POINTER(bm_op_launch), ctypes.c_size_t,
                                         ctypes.POINTER(ctypes.c_size_t), _U64P]),
@@ -560,6 +561,10 @@ def bm_server_stats(srv):
     st = bm_server_stats_t()
     _check(_L.bm_server_stats(srv.ptr, ctypes.byref(st)))
     return {f: getattr(st, f) for f, _ in bm_server_stats_t._fields_}
+
+
+def bm_server_reset_stats(srv):
+    _check(_L.bm_server_reset_stats(srv.ptr))
 
 
 # ---- schedule model, part-size choice, kernel-shape tuning ----

@@ -1048,7 +1048,8 @@ bm_status bm_gallery_set_schedule(bm_gallery* gh, uint32_t flags) {
         if (!(flags & BM_SCHED_FUSED_EXPANSION) || g.encrypted || !ks_mdr_supported(c, 2))
             return fail(BM_E_ARG, "the deferred division needs the fused expansion and a plaintext gallery");
         if (!g.d_pts_ext) {
-            // the plaintexts' integer coefficients on every prime of Q_L u P, once
+            // the plaintexts' integer coefficients on every prime of Q_L u P, once, then
+            // folded with the masks
             const size_t nlx = c.L + 1 + c.alpha, count = (size_t)g.groups * g.n_in;
             BM_CUDA_TRY(cudaSetDevice(c.device));
             if (cudaMalloc(&g.d_pts_ext, count * nlx * c.n * 8) != cudaSuccess) {
@@ -1056,11 +1057,22 @@ bm_status bm_gallery_set_schedule(bm_gallery* gh, uint32_t flags) {
                 g.d_pts_ext = nullptr;
                 return fail(BM_E_OOM, "extended gallery allocation failed");
             }
-            const cudaError_t e = extend_to_ext_basis(c, count, g.d_pts, g.level + 1, g.d_pts_ext, c.stream);
+            cudaError_t e = extend_to_ext_basis(c, count, g.d_pts, g.level + 1, g.d_pts_ext, c.stream);
+            // folded with the masks of Algorithm 1 (fold_gallery): HE-C^3 then takes the
+            // query's rotated copies E_j themselves, with no circulant
+            uint64_t *masks_ext = nullptr, *fold = nullptr;
+            if (e == cudaSuccess) e = cudaMalloc(&masks_ext, (size_t)g.n_in * nlx * c.n * 8);
+            if (e == cudaSuccess) e = cudaMalloc(&fold, count * nlx * c.n * 8);
+            if (e == cudaSuccess) e = masks_extend(c, g.n_in, g.d_masks, masks_ext, c.stream);
+            if (e == cudaSuccess) e = fold_gallery(c, g.groups, g.n_in, masks_ext, g.d_pts_ext, fold, c.stream);
+            if (masks_ext) cudaFree(masks_ext);
+            cudaFree(g.d_pts_ext);
+            g.d_pts_ext = e == cudaSuccess ? fold : nullptr;
             if (e != cudaSuccess) {
-                cudaFree(g.d_pts_ext);
-                g.d_pts_ext = nullptr;
-                return fail(BM_E_CUDA, std::string("gallery extension: ") + cudaGetErrorString(e));
+                if (fold) cudaFree(fold);
+                cudaGetLastError();
+                return fail(e == cudaErrorMemoryAllocation ? BM_E_OOM : BM_E_CUDA,
+                            std::string("gallery extension: ") + cudaGetErrorString(e));
             }
         }
     }
@@ -1591,7 +1603,9 @@ struct MatchRun {
         if (g.tiled && g.hoisted && g.fused) {
             // fused form: E_j = the rotation by j parts before ModDown (sums left in NTT
             // form on Q_L u P, P * sigma(c0) included), E_0 = P * query; e_i = sum_j E_j *
-            // mask_((i-j) mod N_in) on Q_L u P; T_i = e_i / (q_L P) (ModDown and Rescale fused)
+            // mask_((i-j) mod N_in) on Q_L u P; T_i = e_i / (q_L P) (ModDown and Rescale fused).
+            // With the deferred division HE-C^3 sums e_i * pts_i, i.e. sum_j E_j * fold_j
+            // (the gallery folded with the masks), and divides after it.
             const size_t ew = ks_ext_words(c, c.L);
             const uint32_t nlx = c.L + 1 + c.alpha;
             const size_t xw = (size_t)2 * nlx * c.n;             // one sum on Q_L u P
@@ -1616,28 +1630,35 @@ struct MatchRun {
                 auto doff = pl.arena.list(off);
                 auto dq = pl.arena.list(qs);
                 const uint32_t nt = (uint32_t)ext_of.size();
-                for (uint32_t t0 = 0; t0 < nt; t0 += ksb) {
-                    const uint32_t T = std::min(ksb, nt - t0);
+                // deferred division: E_0 .. E_(N_in-1) of each query go straight to T (on Q_L u P),
+                // E_j at part j, for HE-C^3 against the gallery folded with the masks
+                // (fold_gallery): no circulant; the sums of a launch are whole queries
+                const uint32_t per = n_in - 1, step = g.deferred ? std::max(1u, ksb / per) * per : ksb;
+                for (uint32_t t0 = 0; t0 < nt; t0 += step) {
+                    const uint32_t T = std::min(step, nt - t0);
                     record(BM_OP_IP_SUM, c.L, T, 0, T);
+                    uint64_t* out = g.deferred ? pl.T + ((size_t)qb * n_in + (size_t)(t0 / per) * n_in) * xw
+                                               : pl.R + (size_t)t0 * xw;
                     if (pl.arena.live)
                         check(ks_ipsum_hoisted(c, c.L, T, (const uint64_t*)(doff + t0), T, (const uint64_t* const*)de,
                                                (const uint64_t* const*)ds, (const uint64_t* const*)dk,
-                                               (const uint64_t*)dg, pl.R + (size_t)t0 * xw, s, true,
-                                               sum_info(ext_of, src, keys, t0, t0 + T, 1)));
+                                               (const uint64_t*)dg, out, s, true,
+                                               sum_info(ext_of, src, keys, t0, t0 + T, 1), g.deferred ? per : 0));
                 }
                 record(BM_OP_COPY, 0, nq);
+                if (g.deferred) {
+                    if (pl.arena.live) check(lift_p(c, nq, dq, pl.T + (size_t)qb * n_in * xw, s, (size_t)n_in * xw));
+                    continue;
+                }
                 if (pl.arena.live) check(lift_p(c, nq, dq, E0, s));
                 for (uint32_t q = 0; q < nq; q++)
                     for (uint32_t j = 0; j < n_in; j++)
                         R.push_back(j == 0 ? E0 + (size_t)q * xw : pl.R + ((size_t)q * (n_in - 1) + j - 1) * xw);
                 auto dR = pl.arena.list(R);
                 record(BM_OP_MAC_CIRC, c.L, n_in, nq, n_in);
-                // deferred division: the undivided parts e_i go to T (on Q_L u P) for HE-C^3
-                uint64_t* circ_out = g.deferred ? pl.T + (size_t)qb * n_in * xw : pl.t0;
                 if (pl.arena.live)
                     check(mac_circ(c, nlx - 1, nq, n_in, (const uint64_t* const*)dR, nullptr, g.d_masks_hat_ext,
-                                   g.d_circ_tw_ext, circ_out, s));
-                if (g.deferred) continue;
+                                   g.d_circ_tw_ext, pl.t0, s));
                 for (uint32_t q = 0; q < nq; q++)
                     for (uint32_t i = 0; i < n_in; i++) outs.push_back(pl.T + ((size_t)(qb + q) * n_in + i) * cw(lg));
                 auto dout = pl.arena.list(outs);

@@ -416,7 +416,7 @@ struct KsSumInfo {
 cudaError_t ks_ipsum_hoisted(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
                              const uint64_t* const* ext_of, const uint64_t* const* src_of,
                              const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch,
-                             cudaStream_t s, bool ntt_out = false, KsSumInfo u = {});
+                             cudaStream_t s, bool ntt_out = false, KsSumInfo u = {}, uint32_t tpad = 0);
 // ModDown and Rescale fused at the top level: e [T][2][L+1+alpha][N] (NTT form, every
 // limb; the special limbs are transformed in place) divided by q_(L-drop+1)..q_L * P
 // into out[t] (level L - drop, drop 1 or 2); scratch ks_mdr_scratch_words(c, T);
@@ -468,8 +468,18 @@ cudaError_t extend_to_ext_basis(const Context& c, size_t count, const uint64_t* 
 // form) -> out[b] at level 0, the residues of rescale + inverse NTT (needs q_1 < q_0)
 bool rescale_coef_supported(const Context& c);
 cudaError_t rescale_coef(const Context& c, uint32_t B, uint64_t* const* in, uint64_t* const* out, cudaStream_t s);
-// E0[q] = P * in[q] on Q_L u P (special limbs 0): in[q] [2][L+1][N], E0 [Q][2][L+1+alpha][N], NTT form
-cudaError_t lift_p(const Context& c, uint32_t Q, uint64_t* const* in, uint64_t* E0, cudaStream_t s);
+// E0[q] = P * in[q] on Q_L u P (special limbs 0): in[q] [2][L+1][N], E0 + q * stride holds
+// [2][L+1+alpha][N] (stride in words; 0 = packed), NTT form
+cudaError_t lift_p(const Context& c, uint32_t Q, uint64_t* const* in, uint64_t* E0, cudaStream_t s,
+                   size_t stride = 0);
+// The gallery of the deferred division folded with the masks of the fused Algorithm 1:
+// fold[g][j] = sum_i mask_((i - j) mod n_in) * pts[g][i] on every limb of Q_L u P (masks
+// and plaintexts NTT + Montgomery; the result Montgomery too), so HE-C^3 on the rotated
+// copies E_j of the query gives the sum over the parts of the circulant's e_i times the
+// plaintexts: sum_j E_j fold_j = sum_i (sum_j E_j mask_(i-j)) pts_i, mod q.
+// pts, fold [groups][n_in][L+1+alpha][N]; masks_ext [n_in][L+1+alpha][N]
+cudaError_t fold_gallery(const Context& c, size_t groups, uint32_t n_in, const uint64_t* masks_ext,
+                         const uint64_t* pts, uint64_t* fold, cudaStream_t s);
 // dst[t] += sum of src[off[t] .. off[t+1]) (ciphertexts at `level`; off and the lists on the device)
 cudaError_t accumulate(const Context& c, uint32_t level, uint32_t n_targets, uint64_t* const* dst,
                        const uint64_t* const* src, const uint64_t* off, uint32_t n_src, cudaStream_t s);

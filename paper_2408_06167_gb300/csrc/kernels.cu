@@ -468,10 +468,10 @@ __global__ void k_rescale_coef(uint64_t* const* in, uint64_t* const* out, uint64
 // product with P * 2^64), the special limbs 0.  in[q]: [2][L+1][N] NTT form; E0
 // [Q][2][nlx][N].  Grid (Q * 2 * nlx, chunks of a limb).
 __global__ void k_lift_p(const uint64_t* const* in, uint64_t* __restrict__ E0, const KsLevelConst* __restrict__ kc,
-                         DevTables tab, uint32_t l1, uint32_t nlx, uint32_t n) {
+                         DevTables tab, uint32_t l1, uint32_t nlx, uint32_t n, size_t stride) {
     const uint32_t y = blockIdx.x, b = y / (2 * nlx), comp = (y / nlx) % 2, jj = y % nlx;
     pdl_wait();
-    uint64_t* o = E0 + ((size_t)b * 2 * nlx + (size_t)comp * nlx + jj) * n;
+    uint64_t* o = E0 + (size_t)b * stride + ((size_t)comp * nlx + jj) * n;
     if (jj >= l1) {
         for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x) o[i] = 0;
         return;
@@ -1007,12 +1007,46 @@ cudaError_t rescale_coef(const Context& c, uint32_t B, uint64_t* const* in, uint
                       make_ulonglong2(inv, h_shoup_companion(inv, q0)), (uint32_t)c.n);
 }
 
-cudaError_t lift_p(const Context& c, uint32_t Q, uint64_t* const* in, uint64_t* E0, cudaStream_t s) {
+cudaError_t lift_p(const Context& c, uint32_t Q, uint64_t* const* in, uint64_t* E0, cudaStream_t s, size_t stride) {
     if (!Q) return cudaSuccess;
     const uint32_t l1 = c.L + 1, nlx = l1 + c.alpha;
+    if (!stride) stride = (size_t)2 * nlx * c.n;
     ProfScope ps(BM_KERNEL_OTHER, s, 8.0 * c.n * Q * 2 * (l1 + nlx), 20.0 * c.n * Q * 2 * l1);
     return pdl_launch(k_lift_p, dim3(Q * 2 * nlx, c.n / kThreads / 4), kThreads, 0, s, (const uint64_t* const*)in, E0,
-                      c.d_ksc + c.L, c.tab, l1, nlx, c.n);
+                      c.d_ksc + c.L, c.tab, l1, nlx, c.n, stride);
+}
+
+// fold [groups][n_in][nlx][N]: grid (groups * n_in * nlx, N / (kThreads * 2)); each thread
+// two words of one limb of one (group, part j), the sum over the parts i of the
+// Montgomery products mask_((i-j) mod n_in) * pts_i, accumulated at 128 bits
+__global__ void k_fold_gallery(const uint64_t* __restrict__ masks, const uint64_t* __restrict__ pts,
+                               uint64_t* __restrict__ fold, DevTables tab, uint32_t n_in, uint32_t nlx, uint32_t n) {
+    const uint32_t y = blockIdx.x, jj = y % nlx, j = (y / nlx) % n_in, g = y / nlx / n_in;
+    const uint64_t q = tab.q[jj], qn = tab.qneg[jj];   // limb jj of Q_L u P: prime jj of the basis
+    const uint64_t* P = pts + (size_t)g * n_in * nlx * n + (size_t)jj * n;
+    for (uint32_t w = blockIdx.y * blockDim.x + threadIdx.x; w < n; w += gridDim.y * blockDim.x) {
+        Acc128 a;
+        for (uint32_t i = 0; i < n_in; i++) {
+            const uint32_t mi = (i + n_in - j) % n_in;
+            mul_acc(a, masks[((size_t)mi * nlx + jj) * n + w], P[(size_t)i * nlx * n + w], q);
+        }
+        fold[(((size_t)g * n_in + j) * nlx + jj) * n + w] = redc(a, q, qn);
+    }
+}
+
+cudaError_t fold_gallery(const Context& c, size_t groups, uint32_t n_in, const uint64_t* masks_ext,
+                         const uint64_t* pts, uint64_t* fold, cudaStream_t s) {
+    const uint32_t nlx = c.L + 1 + c.alpha;
+    // grid x over (group, part, limb) in chunks below the launch limit
+    const size_t per = (size_t)n_in * nlx, max_x = (size_t)1 << 30;
+    for (size_t g0 = 0; g0 < groups; g0 += max_x / per) {
+        const size_t gn = std::min(groups - g0, max_x / per);
+        k_fold_gallery<<<dim3((uint32_t)(gn * per), c.n / kThreads / 2), kThreads, 0, s>>>(
+            masks_ext, pts + g0 * per * c.n, fold + g0 * per * c.n, c.tab, n_in, nlx, c.n);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaStreamSynchronize(s);
 }
 
 cudaError_t extend_to_ext_basis(const Context& c, size_t count, const uint64_t* in, uint32_t l_in, uint64_t* out,

@@ -422,14 +422,16 @@ __device__ __forceinline__ void place4(uint64_t (&o)[4], const W4& g, uint32_t s
 // c0.  The products are summed at 128 bits without a reduction per product (the
 // high word -- and the c0 sum -- reduced every kFoldElems elements: at most
 // ND * kFoldElems < 64 products and kFoldElems < 16 c0 words between reductions)
-// and reduced once.
+// and reduced once.  With tpad, the sums of each run of tpad consecutive targets go
+// to slots 1..tpad of a run of tpad + 1 (slot 0 is another operand's: the fused
+// Algorithm 1 puts E_1..E_(N_in-1) of each query after its E_0).
 constexpr uint32_t kFoldElems = 12;
 template <int LA, int LB, int R, int ND, int MINB>
 __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
     k_ks_f4s(const uint64_t* const* ext_of, const uint64_t* const* src_of, const uint64_t* const* key_of,
              const uint64_t* gal_of, const uint64_t* off, uint64_t* __restrict__ acc,
              const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L, uint32_t nb,
-             bool ntt_out) {
+             bool ntt_out, uint32_t tpad) {
     constexpr int LT = 2, K = 4, M = 1 << LB, TH = M >> LT, SW = sub_words<LB, LT>(), LOGN = LA + LB, N = 1 << LOGN;
     constexpr int TWN = row_tw_entries<LB, R>();
     __shared__ uint64_t sm[R * SW];
@@ -449,6 +451,9 @@ __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
     if (inv) stage_row_twiddles<LA, LB, R, R * TH>(twi, tab.itw[pi], blockIdx.y * R);
     pdl_wait();
     const uint32_t e0 = (uint32_t)off[tg], e1 = (uint32_t)off[tg + 1];
+    // output slot: target tg, or with tpad the slot after every run of tpad targets left
+    // free (slot tpad + 1 of each run's successor holds another operand)
+    const uint32_t tgo = tpad ? tg / tpad * (tpad + 1) + tg % tpad + 1 : tg;
     Acc128 a0[K], a1[K];
     uint64_t cs[K] = {0, 0, 0, 0};
 #pragma unroll 1
@@ -503,7 +508,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
         uint64_t v[K];
 #pragma unroll
         for (int k = 0; k < K; k++) v[k] = redc_wide(comp ? a1[k] : a0[k], q, qn, rsh);
-        uint64_t* o = acc + (((size_t)tg * 2 + comp) * nlx + jj) * N + roff;
+        uint64_t* o = acc + (((size_t)tgo * 2 + comp) * nlx + jj) * N + roff;
         if (!inv) {
             nttr::store_last<LB, LT>(v, o, t);
         } else {
@@ -534,11 +539,11 @@ __device__ __forceinline__ void pass_barriers() {
 #pragma unroll
     for (int h = 0; h + 1 < P / LT; h++) __syncthreads();
 }
-template <int LA, int LT, int C, int GP>
-__host__ __device__ constexpr size_t f5_smem_words() {   // exchange, staging, twiddles of each group
-    return (size_t)GP * (sub_words<LA, LT>() * C + (size_t)(1 << LT) * C * ((1 << LA) >> LT) + 2 * (1 << LA));
+template <int LA, int LT, int C, int GP, int MAXS>
+__host__ __device__ constexpr size_t f5_smem_words() {   // exchange and twiddles of each group, staging
+    return (size_t)GP * (sub_words<LA, LT>() * C + 2 * (1 << LA)) + (size_t)MAXS * (1 << LT) * C * ((1 << LA) >> LT);
 }
-template <int LA, int LB, int LT, int C, int GP>
+template <int LA, int LB, int LT, int C, int GP, int MAXS>
 __global__ void __launch_bounds__(GP * C * (1 << (LA - LT)))
     k_ks_f5(const uint64_t* __restrict__ acc, uint64_t* __restrict__ conv, const KsLevelConst* __restrict__ kc,
             DevTables tab, uint32_t l1, uint32_t L, uint32_t ns) {
@@ -548,7 +553,7 @@ __global__ void __launch_bounds__(GP * C * (1 << (LA - LT)))
     const int tid = threadIdx.x, g = tid / NTG, r = tid % NTG, t = r / C, jc = r % C;
     uint64_t* xch = dsm + g * SW;                                   // the group's exchange columns
     uint64_t* st = dsm + GP * SW;                                   // staging [ns][K][NTG]
-    ulonglong2* tws = reinterpret_cast<ulonglong2*>(st + (size_t)GP * K * NTG) + g * M;   // the group's twiddles
+    ulonglong2* tws = reinterpret_cast<ulonglong2*>(st + (size_t)MAXS * K * NTG) + g * M;   // the group's twiddles
     const uint32_t b = blockIdx.x / 2, comp = blockIdx.x % 2;
     const int col = blockIdx.y * C + jc;
     const uint32_t nlx = l1 + ns;
@@ -557,31 +562,35 @@ __global__ void __launch_bounds__(GP * C * (1 << (LA - LT)))
         for (int i = r; i < M; i += NTG) __pipeline_memcpy_async(tws + i, tw + i, sizeof(ulonglong2));
         __pipeline_commit();
     };
-    // phase 1: special limb g
-    const bool a1 = (uint32_t)g < ns;
-    const int ps = (int)L + 1 + g;
-    const uint64_t p = a1 ? tab.q[ps] : tab.q[0];
-    if (a1) stage_tw(tab.itw[ps]);
-    pdl_wait();
+    // phase 1: special limbs g, g + GP, ...
     uint64_t y[K];
-    if (a1) {
-        const uint64_t* src = acc + (((size_t)b * 2 + comp) * nlx + l1 + g) * N + col;
+#pragma unroll 1
+    for (uint32_t i0 = 0; i0 < ns; i0 += GP) {
+        const uint32_t i = i0 + g;
+        const bool a1 = i < ns;
+        const int ps = (int)L + 1 + (int)i;
+        const uint64_t p = a1 ? tab.q[ps] : tab.q[0];
+        if (a1) stage_tw(tab.itw[ps]);
+        if (i0 == 0) pdl_wait();
+        if (a1) {
+            const uint64_t* src = acc + (((size_t)b * 2 + comp) * nlx + l1 + i) * N + col;
 #pragma unroll
-        for (int k = 0; k < K; k++) y[k] = src[(size_t)last_idx<LA, LT>(t, k) * N2];
-    } else {
+            for (int k = 0; k < K; k++) y[k] = src[(size_t)last_idx<LA, LT>(t, k) * N2];
+        } else {
 #pragma unroll
-        for (int k = 0; k < K; k++) y[k] = 0;
+            for (int k = 0; k < K; k++) y[k] = 0;
+        }
+        __pipeline_wait_prior(0);
+        __syncthreads();
+        if (a1) nttr::inv_pass<LA, LT>(y, sx, tws, ColBase{}, t, p, 2 * p);
+        else pass_barriers<LA, LT>();
+        if (a1) {
+            const ulonglong2 h = kc->dn_hinv[i];          // N^-1 * (P/p_i)^-1 mod p_i
+#pragma unroll
+            for (int k = 0; k < K; k++) st[(i * K + k) * NTG + r] = shoup(y[k], h.x, h.y, p);
+        }
+        __syncthreads();        // the twiddles are restaged, and the staging read, next
     }
-    __pipeline_wait_prior(0);
-    __syncthreads();
-    if (a1) nttr::inv_pass<LA, LT>(y, sx, tws, ColBase{}, t, p, 2 * p);
-    else pass_barriers<LA, LT>();
-    if (a1) {
-        const ulonglong2 h = kc->dn_hinv[g];          // N^-1 * (P/p_i)^-1 mod p_i
-#pragma unroll
-        for (int k = 0; k < K; k++) st[(g * K + k) * NTG + r] = shoup(y[k], h.x, h.y, p);
-    }
-    __syncthreads();
     // phase 2: targets g, g + GP, ...
 #pragma unroll 1
     for (uint32_t j0 = 0; j0 < l1; j0 += GP) {
@@ -614,19 +623,29 @@ __global__ void __launch_bounds__(GP * C * (1 << (LA - LT)))
     }
 }
 
-// F5 of nb2 = (ciphertexts x 2 components) with ns special limbs (its shared memory set once)
-template <int LA, int LB, int LT, int C, int GP>
+// F5 of nb2 = (ciphertexts x 2 components) with ns <= MAXS special limbs: one thread
+// group a special limb for the few column blocks of a small batch (latency-bound: the
+// limbs' passes side by side), a single group looping over them for a batch that
+// already fills the GPU (no idle groups).  Shared memory set once per variant.
+template <int LA, int LB, int LT, int C, int GP, int MAXS>
+cudaError_t f5_variant(uint32_t nb2, const uint64_t* acc, uint64_t* conv, const KsLevelConst* kc,
+                       const DevTables& tab, uint32_t l1, uint32_t L, uint32_t ns, cudaStream_t s) {
+    constexpr int threads = GP * C * (1 << (LA - LT));
+    constexpr size_t smem = 8 * f5_smem_words<LA, LT, C, GP, MAXS>();
+    static const bool attrs = cudaFuncSetAttribute(k_ks_f5<LA, LB, LT, C, GP, MAXS>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                              cudaSuccess;
+    (void)attrs;
+    return pdl_launch(k_ks_f5<LA, LB, LT, C, GP, MAXS>, dim3(nb2, (1 << LB) / C), threads, smem, s, acc, conv, kc,
+                      tab, l1, L, ns);
+}
+constexpr uint32_t kF5SerialFrom = 16;    // ciphertext components from which F5 takes one group
+template <int LA, int LB, int LT, int C, int MAXS>
 cudaError_t f5_launch(uint32_t nb2, const uint64_t* acc, uint64_t* conv, const KsLevelConst* kc, const DevTables& tab,
                       uint32_t l1, uint32_t L, uint32_t ns, cudaStream_t s) {
-    constexpr int threads = GP * C * (1 << (LA - LT));
-    constexpr size_t smem = 8 * f5_smem_words<LA, LT, C, GP>();
-    static const bool attrs =
-        cudaFuncSetAttribute(k_ks_f5<LA, LB, LT, C, GP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
-        cudaSuccess;
-    (void)attrs;
-    if (ns > (uint32_t)GP) return cudaErrorInvalidValue;
-    return pdl_launch(k_ks_f5<LA, LB, LT, C, GP>, dim3(nb2, (1 << LB) / C), threads, smem, s, acc, conv, kc, tab, l1, L,
-                      ns);
+    if (ns > (uint32_t)MAXS) return cudaErrorInvalidValue;
+    if (nb2 >= kF5SerialFrom) return f5_variant<LA, LB, LT, C, 1, MAXS>(nb2, acc, conv, kc, tab, l1, L, ns, s);
+    return f5_variant<LA, LB, LT, C, MAXS, MAXS>(nb2, acc, conv, kc, tab, l1, L, ns, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1006,7 +1025,7 @@ template <int LA, int LB, int LT, int C, int R>
 cudaError_t ks_ipsum_launch(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
                             const uint64_t* const* ext_of, const uint64_t* const* src_of,
                             const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch, bool ntt_out,
-                            KsSumInfo u, cudaStream_t s) {
+                            KsSumInfo u, uint32_t tpad, cudaStream_t s) {
     constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
     (void)N2;
     const KsLevelConst& K = c.h_ksc[level];
@@ -1024,7 +1043,7 @@ cudaError_t ks_ipsum_launch(const Context& c, uint32_t level, uint32_t T, const 
     const dim3 g(T * nlx, N1 / RF), b(RF * (1 << (LB - 2)));
     auto args = [&](auto kernel) {
         return pdl_launch(kernel, g, b, 0, s, ext_of, src_of, key_of, gal_of, off, scratch, kc, c.tab, l1, c.L, c.nb,
-                          ntt_out);
+                          ntt_out, tpad);
     };
     cudaError_t e = cudaErrorInvalidValue;
     if (nd <= 1) e = args(k_ks_f4s<LA, LB, RF, 1, 8>);
@@ -1142,14 +1161,14 @@ cudaError_t ks_rotate_hoisted(const Context& c, uint32_t level, uint32_t E, cons
 cudaError_t ks_ipsum_hoisted(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
                              const uint64_t* const* ext_of, const uint64_t* const* src_of,
                              const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch,
-                             cudaStream_t s, bool ntt_out, KsSumInfo u) {
+                             cudaStream_t s, bool ntt_out, KsSumInfo u, uint32_t tpad) {
     if (T == 0) return cudaSuccess;
     if (c.log_n == 16)
         return ks_ipsum_launch<8, 8, 2, 2, 2>(c, level, T, off, E, ext_of, src_of, key_of, gal_of, scratch, ntt_out, u,
-                                              s);
+                                              tpad, s);
     if (c.log_n == 12)
         return ks_ipsum_launch<6, 6, 2, 8, 8>(c, level, T, off, E, ext_of, src_of, key_of, gal_of, scratch, ntt_out, u,
-                                              s);
+                                              tpad, s);
     return cudaErrorInvalidValue;
 }
 

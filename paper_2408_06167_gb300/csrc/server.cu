@@ -81,9 +81,11 @@ struct Server {
     bool any = false;
 };
 
+// the plan size for n pending queries: the largest power of two not above n (and
+// max_batch), so a plan never runs padding queries; the surplus goes back to the queue
 uint32_t bucket(uint32_t n, uint32_t max_batch) {
     uint32_t b = 1;
-    while (b < n) b <<= 1;
+    while (2 * b <= n) b <<= 1;
     return std::min(b, max_batch);
 }
 
@@ -422,6 +424,21 @@ bm_status bm_server_cancel(bm_server* h, uint64_t ticket) {
     finish(S, *it, BM_E_CANCELLED, "cancelled by the caller");
     S.pending.erase(it);
     S.cv_done.notify_all();
+    return BM_OK;
+}
+
+bm_status bm_server_reset_stats(bm_server* h) {
+    if (!h) {
+        set_error("bm_server_reset_stats: null argument");
+        return BM_E_ARG;
+    }
+    Server& S = h->s;
+    std::lock_guard<std::mutex> lk(S.mu);
+    S.submitted = S.completed = S.failed = S.cancelled = S.batches = 0;
+    S.batched_queries = 0;
+    S.matches = 0;
+    S.latencies_ms.clear();
+    S.any = false;
     return BM_OK;
 }
 
