@@ -1484,14 +1484,14 @@ struct MatchRun {
     void hoisted_round(uint32_t level, const std::vector<uint64_t*>& srcs, const std::vector<uint32_t>& e_src,
                        const std::vector<int32_t>& e_rot, const std::vector<uint64_t*>& tgts,
                        const std::vector<std::vector<uint32_t>>& t_elems,
-                       const std::vector<uint64_t*>* outs = nullptr) {
+                       const std::vector<uint64_t*>* outs = nullptr, const uint64_t* mask = nullptr) {
         const size_t ew = ks_ext_words(c, level), cwl = cw(level);
         for (size_t s0 = 0; s0 < srcs.size(); s0 += ksb) {
             std::vector<uint64_t*> chunk(srcs.begin() + s0, srcs.begin() + std::min(srcs.size(), s0 + ksb));
             modup_batch(level, chunk, pl.ext2 + s0 * ew);
         }
         if (g.dhoist) {
-            double_hoisted_sums(level, srcs, e_src, e_rot, tgts, t_elems, outs);
+            double_hoisted_sums(level, srcs, e_src, e_rot, tgts, t_elems, outs, mask);
             return;
         }
         std::vector<uint64_t*> ext_of, src, keys, gal, out;
@@ -1516,9 +1516,10 @@ struct MatchRun {
     void double_hoisted_sums(uint32_t level, const std::vector<uint64_t*>& srcs, const std::vector<uint32_t>& e_src,
                              const std::vector<int32_t>& e_rot, const std::vector<uint64_t*>& tgts,
                              const std::vector<std::vector<uint32_t>>& t_elems,
-                             const std::vector<uint64_t*>* outs = nullptr) {
+                             const std::vector<uint64_t*>* outs = nullptr, const uint64_t* mask = nullptr) {
         // with outs, target t + its sum goes to outs[t] (every target, a zero sum for
-        // those without elements); else the targets are updated in place
+        // those without elements); else the targets are updated in place; with mask the
+        // result is multiplied by that plaintext (every target must then have elements)
         const size_t ew = ks_ext_words(c, level);
         std::vector<uint64_t*> ext_of, src, keys, gal, tg, to, off{reinterpret_cast<uint64_t*>((uintptr_t)0)};
         std::vector<uint32_t> t_off{0};
@@ -1556,7 +1557,7 @@ struct MatchRun {
             check(ks_ipsum_hoisted(c, level, T, (const uint64_t*)(doff + t0), E, (const uint64_t* const*)de,
                                    (const uint64_t* const*)ds, (const uint64_t* const*)dk, (const uint64_t*)dg,
                                    pl.scratch, s, false, sum_info(ext_of, src, keys, t_off[t0], t_off[t0 + T], mx)));
-            check(ks_moddown_add(c, level, T, dt + t0, pl.scratch, s, dto ? dto + t0 : nullptr));
+            check(ks_moddown_add(c, level, T, dt + t0, pl.scratch, s, dto ? dto + t0 : nullptr, mask));
         }
     }
     // ... rotations of the extended queries (per element: extension, source, key, Galois element)
@@ -1645,11 +1646,8 @@ struct MatchRun {
                                                (const uint64_t*)dg, out, s, true,
                                                sum_info(ext_of, src, keys, t0, t0 + T, 1), g.deferred ? per : 0));
                 }
+                if (g.deferred) continue;          // E_0 written by the same launch (slot 0 of each query)
                 record(BM_OP_COPY, 0, nq);
-                if (g.deferred) {
-                    if (pl.arena.live) check(lift_p(c, nq, dq, pl.T + (size_t)qb * n_in * xw, s, (size_t)n_in * xw));
-                    continue;
-                }
                 if (pl.arena.live) check(lift_p(c, nq, dq, E0, s));
                 for (uint32_t q = 0; q < nq; q++)
                     for (uint32_t j = 0; j < n_in; j++)
@@ -1759,12 +1757,17 @@ struct MatchRun {
             } else {
                 rescale_batch(lg, a, b);
             }
+            // the compression's mask product taken in the ModDown of the last double-hoisted
+            // rotate-and-sum round (one launch less); else its own launch below
+            bool mask_fused = false;
             if (g.hrotsum) {
                 // sum_{r<part} Rot(acc, r) in two hoisted rounds: baby steps 1..bs-1, giant steps bs*k
                 uint32_t bs, gs;
                 bsgs_split(part, g.dhoist, bs, gs);
                 const uint32_t rounds[2][2] = {{1, bs}, {bs, gs}};
-                for (const auto& rd : rounds) {
+                const int last = gs > 1 ? 1 : (bs > 1 ? 0 : -1);
+                for (int ri = 0; ri < 2; ri++) {
+                    const auto& rd = rounds[ri];
                     if (rd[1] <= 1) continue;
                     std::vector<uint32_t> e_src;
                     std::vector<int32_t> e_rot;
@@ -1775,7 +1778,9 @@ struct MatchRun {
                             e_src.push_back(k);
                             e_rot.push_back((int32_t)(rd[0] * r));
                         }
-                    hoisted_round(lg - 1, b, e_src, e_rot, b, t_elems);
+                    const bool fuse = ri == last && g.compress && g.dhoist;
+                    hoisted_round(lg - 1, b, e_src, e_rot, b, t_elems, nullptr, fuse ? g.d_cmask : nullptr);
+                    mask_fused = mask_fused || fuse;
                 }
             } else {
                 for (uint32_t t = 1; (1u << (t - 1)) < part; t++)
@@ -1795,7 +1800,7 @@ struct MatchRun {
             }
             const uint32_t lc = lg - 1;
             std::vector<uint64_t*> mp(b.size(), const_cast<uint64_t*>(g.d_cmask));
-            mulplain_batch(lc, b, mp, b);
+            if (!mask_fused) mulplain_batch(lc, b, mp, b);
             std::vector<uint64_t*> packs;
             if (g.hcomp) {
                 // linear form: every group r > 0 of a pack rotated right by r in one hoisted round,

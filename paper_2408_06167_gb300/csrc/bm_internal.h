@@ -426,7 +426,7 @@ size_t ks_mdr_scratch_words(const Context& c, uint32_t T);
 cudaError_t ks_moddown_rescale(const Context& c, uint32_t T, uint64_t* e, uint64_t* const* d_out, uint64_t* scratch,
                                cudaStream_t s, uint32_t drop = 1);
 cudaError_t ks_moddown_add(const Context& c, uint32_t level, uint32_t T, uint64_t* const* d_tgt, uint64_t* scratch,
-                           cudaStream_t s, uint64_t* const* d_out = nullptr);
+                           cudaStream_t s, uint64_t* const* d_out = nullptr, const uint64_t* mask = nullptr);
 // rescale in three fused kernels (rings 2^12 and 2^16)
 cudaError_t rescale_fused(const Context& c, uint32_t level, uint32_t B, uint64_t* const* d_in,
                           uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s);

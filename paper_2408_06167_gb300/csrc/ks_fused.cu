@@ -422,9 +422,10 @@ __device__ __forceinline__ void place4(uint64_t (&o)[4], const W4& g, uint32_t s
 // c0.  The products are summed at 128 bits without a reduction per product (the
 // high word -- and the c0 sum -- reduced every kFoldElems elements: at most
 // ND * kFoldElems < 64 products and kFoldElems < 16 c0 words between reductions)
-// and reduced once.  With tpad, the sums of each run of tpad consecutive targets go
-// to slots 1..tpad of a run of tpad + 1 (slot 0 is another operand's: the fused
-// Algorithm 1 puts E_1..E_(N_in-1) of each query after its E_0).
+// and reduced once.  With tpad (only with ntt_out), the sums of each run of tpad
+// consecutive targets go to slots 1..tpad of a run of tpad + 1, and slot 0 of the run
+// gets P times the run's source ciphertext: E_0, E_1..E_(N_in-1) of a query of the fused
+// Algorithm 1 in one launch.
 constexpr uint32_t kFoldElems = 12;
 template <int LA, int LB, int R, int ND, int MINB>
 __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
@@ -439,7 +440,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
     const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
     const SubMem sr{sm + jr * SW, 1};
     const uint32_t nd = kc->nd, nlx = kc->nlx;
-    const uint32_t tg = blockIdx.x / nlx, jj = blockIdx.x % nlx;
+    const uint32_t jj = blockIdx.x % nlx, slot = blockIdx.x / nlx;
     const int pi = ext_prime(jj, l1, L);
     const uint64_t q = tab.q[pi], qn = tab.qneg[pi], rsh = tab.rsh[pi], q2 = 2 * q;
     const uint64_t pm = jj < l1 ? kc->pmont[jj] : 0;
@@ -448,12 +449,28 @@ __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
     const uint32_t i0 = (uint32_t)roff + (uint32_t)(t << LT);     // last layout: words i0 .. i0 + 3
     const bool inv = jj >= l1 && !ntt_out;      // special limbs for F5: inverse row pass
     const bool qlimb = jj < l1;
+    // output slot = block's slot; with tpad, slot 0 of each run of tpad + 1 is P * the
+    // run's source ciphertext (E_0 of the fused Algorithm 1: P * c on the q-limbs, 0 on
+    // the special limbs) and slots 1..tpad the run's targets
+    const uint32_t run = tpad ? slot / (tpad + 1) : 0, kk = tpad ? slot % (tpad + 1) : 1;
+    const uint32_t tg = tpad ? run * tpad + kk - 1 : slot, tgo = slot;
     if (inv) stage_row_twiddles<LA, LB, R, R * TH>(twi, tab.itw[pi], blockIdx.y * R);
     pdl_wait();
+    if (kk == 0) {
+        const uint64_t* src = src_of[off[run * tpad]];
+#pragma unroll 1
+        for (uint32_t comp = 0; comp < 2; comp++) {
+            uint64_t v[K] = {0, 0, 0, 0};
+            if (qlimb) {
+                const W4 x = ld256(src + ((size_t)comp * l1 + jj) * N + i0);
+#pragma unroll
+                for (int k = 0; k < K; k++) v[k] = mont(x.w[k], pm, q, qn);
+            }
+            nttr::store_last<LB, LT>(v, acc + (((size_t)tgo * 2 + comp) * nlx + jj) * N + roff, t);
+        }
+        return;
+    }
     const uint32_t e0 = (uint32_t)off[tg], e1 = (uint32_t)off[tg + 1];
-    // output slot: target tg, or with tpad the slot after every run of tpad targets left
-    // free (slot tpad + 1 of each run's successor holds another operand)
-    const uint32_t tgo = tpad ? tg / tpad * (tpad + 1) + tg % tpad + 1 : tg;
     Acc128 a0[K], a1[K];
     uint64_t cs[K] = {0, 0, 0, 0};
 #pragma unroll 1
@@ -650,18 +667,22 @@ cudaError_t f5_launch(uint32_t nb2, const uint64_t* acc, uint64_t* conv, const K
 
 // ---------------------------------------------------------------------------
 // F6: grid (B * l1, N1 / R).  out = (acc - conv) * P^-1 + sigma(c0) (+ add); without
-// X0 and c0_of no sigma(c0) term (the sums of F4s hold it)
+// X0 and c0_of no sigma(c0) term (the sums of F4s hold it); with mask (a plaintext
+// [l1][N], NTT + Montgomery) the result times it, the mask product of the compression
+// taken here instead of in a launch of its own
 // ---------------------------------------------------------------------------
 template <int LA, int LB, int LT, int R>
 __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 3)
     k_ks_f6(const uint64_t* __restrict__ conv, const uint64_t* __restrict__ acc, const uint64_t* __restrict__ X0,
             uint64_t* const* out, uint64_t* const* add, const KsLevelConst* __restrict__ kc, DevTables tab,
-            uint32_t l1, uint32_t galois, const uint64_t* const* c0_of, const uint64_t* gal_of) {
+            uint32_t l1, uint32_t galois, const uint64_t* const* c0_of, const uint64_t* gal_of,
+            const uint64_t* __restrict__ mask) {
     constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>(), LOGN = LA + LB, N = 1 << LOGN;
     __shared__ uint64_t sm[R * S];
     __shared__ ulonglong2 tws[row_tw_entries<LB, R>()];
     const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
     const uint32_t b = blockIdx.x / l1, j = blockIdx.x % l1;
+    const uint64_t qn = tab.qneg[j];
     // hoisted rotations: each element has its own Galois element and reads sigma(c0)
     // from its source ciphertext (NTT form) instead of the copy X0
     if (gal_of) galois = (uint32_t)gal_of[b];
@@ -694,6 +715,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 3)
             uint64_t o = shoup(subm(av[k], nttr::reduce4(v[k], q, q2), q), pinv.x, pinv.y, q);
             if (comp == 0 && x0) o = addm(o, x0[perm_src((uint32_t)(roff + c), LOGN, galois)], q);
             if (add) o = addm(o, ad[k], q);
+            if (mask) o = mont(o, mask[(size_t)j * N + roff + c], q, qn);   // the ct x pt product after it
             v[k] = o;
         }
         nttr::relayout<LB, LT, LB / LT - 1, 0>(v, sr, t);
@@ -898,7 +920,7 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
         ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * B * l1 * (2 + 2 + 1 + 2 + (d_add ? 2 : 0)),
                      bf_r * B * 2 * l1 + kShoupMul * N * B * 2 * l1);
         pdl_launch(k_ks_f6<LA, LB, LT, R>, dim3(B * l1, N1 / R), tr, 0, s, conv, acc, X0, d_out, d_add, kc, c.tab, l1,
-                                                                     (uint32_t)galois, nullptr, nullptr);
+                                                                     (uint32_t)galois, nullptr, nullptr, nullptr);
     }
     return cudaGetLastError();
 }
@@ -1012,7 +1034,7 @@ cudaError_t ks_hoisted_launch(const Context& c, uint32_t level, uint32_t E, cons
     {
         ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * E * l1 * 7, bf_r * E * 2 * l1 + kShoupMul * N * E * 2 * l1);
         pdl_launch(k_ks_f6<LA, LB, LT, R>, dim3(E * l1, N1 / R), tr, 0, s, conv, acc, nullptr, d_out, nullptr, kc, c.tab, l1,
-                                                                     0u, src, gal_of);
+                                                                     0u, src, gal_of, nullptr);
     }
     return cudaGetLastError();
 }
@@ -1035,12 +1057,14 @@ cudaError_t ks_ipsum_launch(const Context& c, uint32_t level, uint32_t T, const 
     // algorithmic bytes: every distinct extension (nd x nlx limbs), key slice (nd x 2 x
     // nlx limbs) and source c0 (l1 limbs) once, and the sums (2 x nlx limbs a target)
     const double ue = u.ext ? u.ext : E, uk = u.keys ? u.keys : E, us = u.srcs ? u.srcs : E;
-    ProfScope ps(BM_KERNEL_KS_IP, s, lw * (nlx * (ue * nd + 2.0 * nd * uk + 2.0 * T) + us * l1),
+    // with tpad the E_0 slots: each source's 2 l1 limbs read, 2 nlx written
+    const double e0 = tpad ? (double)(T / tpad) * (2.0 * l1 + 2.0 * nlx) : 0.0;
+    ProfScope ps(BM_KERNEL_KS_IP, s, lw * (nlx * (ue * nd + 2.0 * nd * uk + 2.0 * T) + us * l1 + e0),
                  (ntt_out ? 0.0 : bf_r * T * 2.0 * alpha) +
                      N * (double)nlx * (2.0 * kProdMul * nd * E + 2.0 * kRedcMul * T) + (double)N * l1 * E * kProdMul);
     // R rows a block (64 threads); digits unrolled up to ND
     constexpr int RF = 256 >> LB;
-    const dim3 g(T * nlx, N1 / RF), b(RF * (1 << (LB - 2)));
+    const dim3 g((T + (tpad ? T / tpad : 0)) * nlx, N1 / RF), b(RF * (1 << (LB - 2)));
     auto args = [&](auto kernel) {
         return pdl_launch(kernel, g, b, 0, s, ext_of, src_of, key_of, gal_of, off, scratch, kc, c.tab, l1, c.L, c.nb,
                           ntt_out, tpad);
@@ -1058,7 +1082,7 @@ cudaError_t ks_ipsum_launch(const Context& c, uint32_t level, uint32_t T, const 
 // with d_out the sum tgt[t] + result goes to out[t] instead.
 template <int LA, int LB, int LT, int C, int R>
 cudaError_t ks_moddown_add_launch(const Context& c, uint32_t level, uint32_t T, uint64_t* const* d_tgt,
-                                  uint64_t* const* d_out, uint64_t* scratch, cudaStream_t s) {
+                                  uint64_t* const* d_out, uint64_t* scratch, const uint64_t* mask, cudaStream_t s) {
     constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
     const KsLevelConst& K = c.h_ksc[level];
     const uint32_t l1 = level + 1, nlx = K.nlx, alpha = c.alpha;
@@ -1073,9 +1097,11 @@ cudaError_t ks_moddown_add_launch(const Context& c, uint32_t level, uint32_t T, 
         f5_launch<LA, LB, LT, C, kMaxDigit>(T * 2, acc, conv, kc, c.tab, l1, c.L, alpha, s);
     }
     {
-        ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * T * l1 * 8, bf_r * T * 2 * l1 + kShoupMul * N * T * 2 * l1);
+        // with the mask: its l1 limbs once more, and a Montgomery product a word (20 mul32)
+        ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * (T * l1 * 8 + (mask ? l1 : 0)),
+                     bf_r * T * 2 * l1 + kShoupMul * N * T * 2 * l1 + (mask ? 20.0 * N * T * 2 * l1 : 0.0));
         pdl_launch(k_ks_f6<LA, LB, LT, R>, dim3(T * l1, N1 / R), tr, 0, s, conv, acc, nullptr, d_out ? d_out : d_tgt,
-                   d_tgt, kc, c.tab, l1, 0u, nullptr, nullptr);
+                   d_tgt, kc, c.tab, l1, 0u, nullptr, nullptr, mask);
     }
     return cudaGetLastError();
 }
@@ -1111,7 +1137,7 @@ cudaError_t ks_mdr_launch(const Context& c, uint32_t T, uint64_t* e, uint64_t* c
     {
         ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * T * L * 6, bf_r * T * 2 * L + kShoupMul * N * T * 2 * L);
         pdl_launch(k_ks_f6<LA, LB, LT, R>, dim3(T * L, N1 / R), tr, 0, s, conv, e, nullptr, d_out, nullptr, kc, c.tab,
-                   L, 0u, nullptr, nullptr);
+                   L, 0u, nullptr, nullptr, nullptr);
     }
     return cudaGetLastError();
 }
@@ -1193,10 +1219,10 @@ cudaError_t ks_moddown_rescale(const Context& c, uint32_t T, uint64_t* e, uint64
 }
 
 cudaError_t ks_moddown_add(const Context& c, uint32_t level, uint32_t T, uint64_t* const* d_tgt, uint64_t* scratch,
-                           cudaStream_t s, uint64_t* const* d_out) {
+                           cudaStream_t s, uint64_t* const* d_out, const uint64_t* mask) {
     if (T == 0) return cudaSuccess;
-    if (c.log_n == 16) return ks_moddown_add_launch<8, 8, 2, 2, 2>(c, level, T, d_tgt, d_out, scratch, s);
-    if (c.log_n == 12) return ks_moddown_add_launch<6, 6, 2, 8, 8>(c, level, T, d_tgt, d_out, scratch, s);
+    if (c.log_n == 16) return ks_moddown_add_launch<8, 8, 2, 2, 2>(c, level, T, d_tgt, d_out, scratch, mask, s);
+    if (c.log_n == 12) return ks_moddown_add_launch<6, 6, 2, 8, 8>(c, level, T, d_tgt, d_out, scratch, mask, s);
     return cudaErrorInvalidValue;
 }
 
