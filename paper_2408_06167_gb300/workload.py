@@ -57,4 +57,7 @@ WORKLOADS = {
     "face-128d-6144": Workload("face-128d-6144", "ring16", 128, 16, 6144, 1),
     "finger-16d-65536-q64": Workload("finger-16d-65536-q64", "ring16", 16, 4, 65536, 64),
     "large-128d-1m-q256": Workload("large-128d-1m-q256", "ring16", 128, 16, 1 << 20, 256),
+    # one 65,536-row pack of the large workload with 32 queries: the same key-switch launch
+    # shapes (128 ciphertexts a launch) on a device footprint small enough for counter captures
+    "large-128d-64k-q32": Workload("large-128d-64k-q32", "ring16", 128, 16, 1 << 16, 32),
 }
