@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
     k_ks_f4s(const uint64_t* const* ext_of, const uint64_t* const* src_of, const uint64_t* const* key_of,
              const uint64_t* gal_of, const uint64_t* off, uint64_t* __restrict__ acc,
              const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L, uint32_t nb,
-             bool ntt_out, uint32_t tpad) {
+             bool ntt_out, uint32_t tpad, bool by_target) {
     constexpr int LT = 2, K = 4, M = 1 << LB, TH = M >> LT, SW = sub_words<LB, LT>(), LOGN = LA + LB, N = 1 << LOGN;
     constexpr int TWN = row_tw_entries<LB, R>();
     __shared__ uint64_t sm[R * SW];
@@ -440,11 +440,17 @@ __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
     const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
     const SubMem sr{sm + jr * SW, 1};
     const uint32_t nd = kc->nd, nlx = kc->nlx;
-    const uint32_t jj = blockIdx.x % nlx, slot = blockIdx.x / nlx;
+    // by_target: blocks taken target by target (limb fastest, then row), so the many
+    // rotations of one source read its permuted extension while it is still in L2;
+    // else row by row over all targets (limb fastest, then target), so targets that share
+    // a key read each key row while it is in L2
+    const uint32_t lin = blockIdx.y * gridDim.x + blockIdx.x, jj = lin % nlx;
+    const uint32_t yb = by_target ? (lin / nlx) % gridDim.y : blockIdx.y;
+    const uint32_t slot = by_target ? lin / (nlx * gridDim.y) : blockIdx.x / nlx;
     const int pi = ext_prime(jj, l1, L);
     const uint64_t q = tab.q[pi], qn = tab.qneg[pi], rsh = tab.rsh[pi], q2 = 2 * q;
     const uint64_t pm = jj < l1 ? kc->pmont[jj] : 0;
-    const int row = blockIdx.y * R + jr;
+    const int row = yb * R + jr;
     const size_t roff = (size_t)row * M;
     const uint32_t i0 = (uint32_t)roff + (uint32_t)(t << LT);     // last layout: words i0 .. i0 + 3
     const bool inv = jj >= l1 && !ntt_out;      // special limbs for F5: inverse row pass
@@ -454,7 +460,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
     // the special limbs) and slots 1..tpad the run's targets
     const uint32_t run = tpad ? slot / (tpad + 1) : 0, kk = tpad ? slot % (tpad + 1) : 1;
     const uint32_t tg = tpad ? run * tpad + kk - 1 : slot, tgo = slot;
-    if (inv) stage_row_twiddles<LA, LB, R, R * TH>(twi, tab.itw[pi], blockIdx.y * R);
+    if (inv) stage_row_twiddles<LA, LB, R, R * TH>(twi, tab.itw[pi], yb * R);
     pdl_wait();
     if (kk == 0) {
         const uint64_t* src = src_of[off[run * tpad]];
@@ -1067,7 +1073,7 @@ cudaError_t ks_ipsum_launch(const Context& c, uint32_t level, uint32_t T, const 
     const dim3 g((T + (tpad ? T / tpad : 0)) * nlx, N1 / RF), b(RF * (1 << (LB - 2)));
     auto args = [&](auto kernel) {
         return pdl_launch(kernel, g, b, 0, s, ext_of, src_of, key_of, gal_of, off, scratch, kc, c.tab, l1, c.L, c.nb,
-                          ntt_out, tpad);
+                          ntt_out, tpad, u.max_elems > 1);
     };
     cudaError_t e = cudaErrorInvalidValue;
     if (nd <= 1) e = args(k_ks_f4s<LA, LB, RF, 1, 8>);
