@@ -672,6 +672,47 @@ class Evaluator:
                 c1[j] = add_mod(c1[j], d1[j], ctx.q[j])
         return Ciphertext(np.stack(c0), np.stack(c1), lvl, base.scale)
 
+    def rotate_plaintext(self, pt, r):
+        return rotate_plaintext(self.ctx, pt, r)
+
+    def masked_rotate_sums(self, groups):
+        """sum over groups (pt, terms) of pt * (sum over terms (ct, r) of Rot(ct, r)),
+        every ciphertext at one level, with ONE ModDown for the whole sum: each group's
+        rotations are taken in the extended basis Q_l u P before ModDown
+        (hoisted_products_ext: sum_d sigma_k(ext_d) * key_k,d + P * sigma_k(c0), a term
+        with r = 0 entering as P * ct), summed, multiplied there by the group's plaintext
+        (its integer coefficients reduced on every prime of Q_l u P, extend_plaintext),
+        summed over the groups and moved down once.  Multiplication by a plaintext is
+        slot-wise and the key-switch sums are linear, so the message is that of
+        sum_g pt_g * (sum of the single rotations); the plaintext multiplies the sum
+        before the rounding of ModDown instead of after it."""
+        ctx = self.ctx
+        lvl = groups[0][1][0][0].level
+        ext_idx = ctx.ext_index(lvl)
+        acc = np.zeros((2, len(ext_idx), ctx.n), dtype=np.uint64)
+        scale = None
+        for pt, terms in groups:
+            by_ct = {}
+            for ct, r in terms:
+                assert ct.level == lvl
+                by_ct.setdefault(id(ct), (ct, []))[1].append(r)
+                scale = ct.scale * pt.scale
+            S = np.zeros_like(acc)
+            for ct, rs in by_ct.values():
+                E = self.hoisted_products_ext(ct, rs)
+                for r in rs:
+                    for jj, gi in enumerate(ext_idx):
+                        t = ctx.primes[gi]
+                        for comp in range(2):
+                            S[comp, jj] = add_mod(S[comp, jj], E[r][comp, jj], t)
+            X = extend_plaintext(ctx, pt, lvl)
+            for jj, gi in enumerate(ext_idx):
+                t = ctx.primes[gi]
+                for comp in range(2):
+                    acc[comp, jj] = add_mod(acc[comp, jj], pointwise_mul(S[comp, jj], X[jj], t), t)
+        d0, d1 = moddown(ctx, acc, lvl)
+        return Ciphertext(d0, d1, lvl, scale)
+
     def hoisted_products_ext(self, ct, rs):
         """The rotations of ct by every r in rs kept in the extended basis Q_l u P,
         before ModDown, NTT form: {r: E_r} with E_r[comp] of shape (|Q_l u P|, N).
@@ -825,6 +866,17 @@ def moddown_rescale(ctx, e, level, drop=1):
             res[j] = scalar_mul(sub_mod(x[j], conv, qj), s_inv, qj)
         out.append(res)
     return out[0], out[1]
+
+
+def rotate_plaintext(ctx, pt, r):
+    """The plaintext of Rot(message, r): the Galois automorphism sigma_(5^r) (left by r,
+    right for r < 0) applied to every limb's coefficients -- an exact signed permutation
+    of the integer coefficients, the same one the rotation of a ciphertext applies."""
+    if r % ctx.slots == 0:
+        return Plaintext(pt.limbs.copy(), pt.level, pt.scale)
+    k = ctx.galois_left(r)
+    limbs = np.stack([automorphism(pt.limbs[j], ctx.log_n, k, ctx.q[j]) for j in range(pt.level + 1)])
+    return Plaintext(limbs, pt.level, pt.scale)
 
 
 def extend_plaintext(ctx, pt, level):

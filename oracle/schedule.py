@@ -258,6 +258,8 @@ def hec3(ev, cu, cs, s, rescale_each_part=False, encrypted_gallery=False, lazy_r
         for i in range(len(cu)):
             acc3 = ev.add3(acc3, ev.tensor(cu[i], cs[i]))
         acc = ev.rescale(ev.relinearize(acc3))
+        if rotsum == "none":
+            return acc
         if rotsum in ("hoisted", "double"):
             return rotsum_hoisted(ev, acc, s, double=rotsum == "double")
         for t in range(1, log2i(s) + 1):
@@ -273,6 +275,8 @@ def hec3(ev, cu, cs, s, rescale_each_part=False, encrypted_gallery=False, lazy_r
         for i in range(1, len(cu)):
             acc = ev.add(acc, mul(cu[i], cs[i]))
         acc = ev.rescale(acc)
+    if rotsum == "none":
+        return acc
     if rotsum in ("hoisted", "double"):
         return rotsum_hoisted(ev, acc, s, double=rotsum == "double")
     for t in range(1, log2i(s) + 1):
@@ -287,6 +291,8 @@ def hec3_deferred(ev, e_parts, cs, s, query_ct, rotsum="doubling"):
     message as hec3 on expand_query_fused's parts; one division per group in place
     of one per part and the rescale."""
     acc = ev.hec3_deferred(e_parts, cs, query_ct)
+    if rotsum == "none":
+        return acc
     if rotsum in ("hoisted", "double"):
         return rotsum_hoisted(ev, acc, s, double=rotsum == "double")
     for t in range(1, log2i(s) + 1):
@@ -329,9 +335,37 @@ def compress(ev, accs, mask_m, s, tree=True, final_rescale=True, hoisted=False):
     return packs
 
 
+def rotsum_compress(ev, accs, mask_m, s):
+    """Algorithm 2's rotate-and-sum and the linear compression in one round of
+    rotations per pack, with one ModDown per pack (Evaluator.masked_rotate_sums).
+    The linear compression puts group o of a pack (o = its offset) at
+    Rot(M * acc_o, -o) = Rot(M, -o) * Rot(acc_o, -o), and the rotate-and-sum's last
+    round makes acc_o = sum over its rotations k < count of Rot(base_o, step * k), base_o
+    the round's input, so Rot(acc_o, -o) = sum_k Rot(base_o, step * k - o): the group's
+    terms are the last round's rotations shifted by -o (one of them the identity when o
+    is a multiple of step), its plaintext the compression mask rotated by -o.  Rounds
+    before the last (the baby steps above s = 16) run as in rotsum_hoisted.  Each pack
+    is then rescaled, as the compression's packs are.  The same messages as
+    compress(..., hoisted="double") on rotsum_hoisted(double=True)'s outputs; the mask
+    multiplies the key-switch sums before ModDown instead of after it, and the groups'
+    rotations by -o are no second round."""
+    b, g = bsgs_split(s, double=True)
+    if g > 1:
+        accs = [ev.rotate_sum_hoisted(a, [(a, r) for r in range(1, b)]) for a in accs]
+        step, count = b, g
+    else:
+        step, count = 1, b
+    packs = []
+    for p in range(-(-len(accs) // s)):
+        groups = [(ev.rotate_plaintext(mask_m, -o), [(a, step * k - o) for k in range(count)])
+                  for o, a in enumerate(accs[p * s:(p + 1) * s])]
+        packs.append(ev.rescale(ev.masked_rotate_sums(groups)))
+    return packs
+
+
 def match(ev, query_cts, gallery_pts, masks, mask_m, m, s, expanded=False,
           rescale_each_part=False, tree=True, encrypted_gallery=False, hoisted=False,
-          hoisted_rotsum=False, hoisted_compress=False, double_hoisted=False):
+          hoisted_rotsum=False, hoisted_compress=False, double_hoisted=False, fused_compress=False):
     """Full server-side match for one query.
 
     query_cts: [ct] (tiled, run through Algorithm 1) or the N_in client-expanded cts.
@@ -339,17 +373,32 @@ def match(ev, query_cts, gallery_pts, masks, mask_m, m, s, expanded=False,
     "fused" (hoisted rotations with their ModDown and the rescale fused) or
     "deferred" (the fused form with its division moved past HE-C^3's products).
     gallery_pts[g][i]: plaintext of group g, part i.
+    fused_compress: the rotate-and-sum's last round and the compression in one round
+    per pack (rotsum_compress; needs the double-hoisted rotate-and-sum and compression).
     Returns (outputs, packed): the score ciphertexts and whether they are packed."""
     rotsum = ("double" if double_hoisted else "hoisted") if hoisted_rotsum else "doubling"
     if hoisted_compress and double_hoisted:
         hoisted_compress = "double"
+    if fused_compress:
+        assert rotsum == "double" and hoisted_compress == "double"
+        if mask_m is None:
+            fused_compress = False
+
+    def tail(accs):
+        if fused_compress and accs[0].level >= 1:
+            return rotsum_compress(ev, accs, mask_m, s), True
+        if fused_compress:
+            accs = [rotsum_hoisted(ev, a, s, double=True) for a in accs]
+        if accs[0].level >= 1 and mask_m is not None:
+            return compress(ev, accs, mask_m, s, tree=tree, hoisted=hoisted_compress), True
+        return accs, False
+    if fused_compress:
+        rotsum = "none"
     if hoisted == "deferred" and not expanded:
         e_parts = expand_query_ext(ev, query_cts[0], m, s)
         accs = [hec3_deferred(ev, e_parts, gallery_pts[g], s, query_cts[0], rotsum=rotsum)
                 for g in range(len(gallery_pts))]
-        if accs[0].level >= 1 and mask_m is not None:
-            return compress(ev, accs, mask_m, s, tree=tree, hoisted=hoisted_compress), True
-        return accs, False
+        return tail(accs)
     if expanded:
         cu = query_cts
     elif hoisted == "fused":
@@ -360,9 +409,7 @@ def match(ev, query_cts, gallery_pts, masks, mask_m, m, s, expanded=False,
         cu = expand_query(ev, query_cts[0], masks, m, s)
     accs = [hec3(ev, cu, gallery_pts[g], s, rescale_each_part, encrypted_gallery, rotsum=rotsum)
             for g in range(len(gallery_pts))]
-    if accs[0].level >= 1 and mask_m is not None:
-        return compress(ev, accs, mask_m, s, tree=tree, hoisted=hoisted_compress), True
-    return accs, False
+    return tail(accs)
 
 
 # ---------------------------------------------------------------------------
@@ -465,6 +512,23 @@ class CountingEvaluator:
         for _ in terms:
             self._rec("Add", base.level)
         return SymCt(base.level)
+
+    def rotate_plaintext(self, pt, r):
+        return pt
+
+    def masked_rotate_sums(self, groups):
+        lvl = groups[0][1][0][0].level
+        seen = set()
+        for _, terms in groups:
+            for ct, r in terms:
+                if r == 0:
+                    continue
+                if id(ct) not in seen:
+                    seen.add(id(ct))
+                    self._rec("ModUp", ct.level)
+                self._rec("IPH", ct.level)
+        self._rec("ModDown", lvl)
+        return SymCt(lvl)
 
     def zero_like(self, ct, level=None):
         return SymCt(ct.level if level is None else level)

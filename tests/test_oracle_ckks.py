@@ -392,6 +392,76 @@ def test_double_hoisted_tail_scores(m, s, R):
     assert np.abs(got - ref).max() < 1e-5
 
 
+def test_rotated_plaintext_decodes_to_the_rotated_message():
+    """The Galois image of a plaintext's coefficients decodes to its message rotated
+    by r slots (left for r > 0, as Sec. 2's Rot), against numpy's roll of the encoded
+    vector."""
+    ctx = ckks.Context("small4")
+    rng = np.random.default_rng(21)
+    z = rng.uniform(-1, 1, ctx.slots)
+    pt = ctx.encode(z, ctx.q[1], 1)
+    for r in (1, -1, 3, -7, 0):
+        rp = ckks.rotate_plaintext(ctx, pt, r)
+        got = ctx.decode(ctx.crt(rp.limbs, ctx.q[:2]), pt.scale).real
+        assert np.abs(got - np.roll(z, -r)).max() < 1e-6, r
+
+
+def test_masked_rotate_sum_with_the_unit_plaintext_is_the_double_hoisted_sum():
+    """With one group and the plaintext 1 (the constant polynomial) the masked sum is
+    rotate_sum_hoisted on a zero base, bit for bit: the terms' products summed in Q_l u P
+    and one ModDown, an unrotated term entering as P * ct (exact under ModDown)."""
+    ctx = ckks.Context("small4")
+    sk, pk, rks = ckks.keygen(ctx, 3, [1, 2, -3])
+    ev = ckks.Evaluator(ctx, rks)
+    rng = np.random.default_rng(22)
+    lvl = 2
+    ct = ckks.encrypt(ctx, pk, ctx.encode(rng.uniform(-1, 1, ctx.slots), ctx.scale, ctx.L), 5, 0)
+    a = ckks.Ciphertext(ct.c0[:lvl + 1].copy(), ct.c1[:lvl + 1].copy(), lvl, ct.scale)
+    one = ckks.Plaintext(np.stack([np.eye(1, ctx.n, 0, dtype=np.uint64)[0] for _ in range(lvl + 1)]), lvl, 1.0)
+    zero = ckks.Ciphertext(np.zeros_like(a.c0), np.zeros_like(a.c1), lvl, a.scale)
+    terms = [(a, 1), (a, 0), (a, 2), (a, -3)]
+    got = ev.masked_rotate_sums([(one, terms)])
+    want = ev.rotate_sum_hoisted(zero, terms)
+    assert np.array_equal(got.c0, want.c0) and np.array_equal(got.c1, want.c1)
+
+
+@pytest.mark.parametrize("m,s,R,complex_pack", [(128, 16, 2500, False), (16, 4, 3000, False),
+                                                (64, 32, 2000, False), (16, 8, 1100, True)])
+def test_fused_rotate_and_sum_and_compression_scores(m, s, R, complex_pack):
+    """The rotate-and-sum's last round and the linear compression in one round per
+    pack (the mask rotated by each group's offset, one ModDown a pack) give the FP64
+    scores, and every pack decrypts to the message of the double-hoisted compression
+    of the double-hoisted rotate-and-sum (ragged last packs, s > 16 with baby steps
+    first, complex packing)."""
+    b, g = sch.bsgs_split(s, double=True)
+    extra = [k for k in range(1, b)] + [b * k for k in range(1, g)] + [-r for r in range(1, s)]
+    extra += [b * k - o for k in range(g) for o in range(s)]
+    ctx, sk, pk, ev = _setup("small4", m, s, R, extra_rots=sorted(set(r for r in extra if r)))
+    S, L, n_in = ctx.slots, ctx.L, m // s
+    feats = wl.gallery(R, m)
+    q = wl.queries(feats, 1)[0][0]
+    ct = ckks.encrypt(ctx, pk, ctx.encode(sch.tiled_query_slots(q, S), ctx.scale, L), 4, 0)
+    masks = [ctx.encode(sch.alg1_mask_slots(m, s, i, S), ctx.q[L], L) for i in range(n_in)]
+    slots_of = sch.gallery_slots_complex if complex_pack else sch.gallery_slots
+    gal = [[ctx.encode(slots_of(feats, gg, i, s, S), ctx.q[L - 1], L - 1) for i in range(n_in)]
+           for gg in range(sch.n_groups(R, s, S, complex_pack))]
+    mm = ctx.encode(sch.compression_mask_slots(s, S), ctx.q[L - 2], L - 2)
+    ref = wl.plaintext_scores(feats, q)
+    kw = dict(hoisted_rotsum=True, hoisted_compress=True, double_hoisted=True)
+    outs, packed = sch.match(ev, [ct], gal, masks, mm, m, s, fused_compress=True, **kw)
+    assert packed and len(outs) == -(-len(gal) // s)
+    dec = [ckks.decrypt_decode(ctx, o, sk) for o in outs]
+    got = []
+    for i in range(R):
+        o, slot, im = sch.identity_slot(i, s, S, packed, complex_pack)
+        got.append(dec[o][slot].imag if im else dec[o][slot].real)
+    assert np.abs(np.array(got) - ref).max() < 1e-5
+    plain, _ = sch.match(ev, [ct], gal, masks, mm, m, s, **kw)
+    for o, p in zip(outs, plain):
+        assert o.level == p.level and o.scale == p.scale
+        assert np.abs(ckks.decrypt_decode(ctx, o, sk) - ckks.decrypt_decode(ctx, p, sk)).max() < 1e-6
+
+
 def test_moddown_rescale_is_the_floor_up_to_the_conversion_error():
     """Big-integer pin of the fused ModDown + Rescale: for the integer E (CRT over
     Q_L u P) of each coefficient and S = q_L * P, the output is floor(E / S) - u
