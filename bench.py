@@ -84,10 +84,11 @@ def parse():
                          "with its key switches and rescale fused, or that with its division moved past HE-C^3's "
                          "products (best: deferred when the gallery has fewer groups than parts, else fused; "
                          "auto: serving picks per gallery by the cost model)")
-    ap.add_argument("--tail", default="double", choices=["printed", "hoisted", "double"],
+    ap.add_argument("--tail", default="fused", choices=["printed", "hoisted", "double", "fused"],
                     help="Algorithm 2's rotate-and-sum and the compression: the printed sequential forms, "
-                         "rounds of hoisted rotations, or the same rounds with one ModDown per output "
-                         "(double hoisting)")
+                         "rounds of hoisted rotations, the same rounds with one ModDown per output "
+                         "(double hoisting), or that with the rotate-and-sum's last round and the "
+                         "compression in one round per pack (one ModDown a pack)")
     ap.add_argument("--gallery", default="plain", choices=["plain", "encrypted"],
                     help="gallery of plaintexts, or of ciphertexts enrolled on the server (Sec. 3.2)")
     ap.add_argument("--packing", default="complex", choices=["real", "complex"],
@@ -149,18 +150,19 @@ class ClockSampler:
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
 
-def _oracle_match(wname, form, n_ids=None):
+def _oracle_match(wname, form, n_ids=None, tail="fused"):
     """The oracle's match of one query of the workload, in the forms the GPU line runs:
     Algorithm 1 hoisted with its key switches fused (form "fused"), or also with its
     division moved past HE-C^3's products ("deferred"); double-hoisted rotate-and-sum
-    and compression; complex packing.  n_ids < the workload's: the first n_ids
+    and compression (tail "fused": the rotate-and-sum's last round and the compression
+    in one round per pack); complex packing.  n_ids < the workload's: the first n_ids
     identities (whole groups), for a sampled run."""
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from helpers_oracle import OracleMatch
     from paper_2408_06167_gb300 import workload as wl
     W = wl.WORKLOADS[wname]
     return W, OracleMatch(W.preset, W.dim, W.part, n_ids or W.n_ids, 1, complex_pack=True, hoisted=form,
-                          hoisted_tail=True, double_hoisted=True)
+                          hoisted_tail=True, double_hoisted=True, fused_compress=tail == "fused")
 
 
 def _oracle_expand(om, ct, form):
@@ -168,9 +170,9 @@ def _oracle_expand(om, ct, form):
     return (sch.expand_query_ext if form == "deferred" else sch.expand_query_fused)(om.ev, ct, om.m, om.s)
 
 
-def _oracle_groups(om, ct, parts, groups, form):
-    """HE-C^3 (the products over the parts and their division or rescale) and the
-    rotate-and-sum for the given groups; returns (accs, mac_s, rotsum_s)."""
+def _oracle_groups(om, ct, parts, groups, form, rotsum=True):
+    """HE-C^3 (the products over the parts and their division or rescale) and (rotsum)
+    the rotate-and-sum for the given groups; returns (accs, mac_s, rotsum_s)."""
     from oracle import schedule as sch
     ev, accs, tm, tr = om.ev, [], 0.0, 0.0
     for g in groups:
@@ -183,7 +185,8 @@ def _oracle_groups(om, ct, parts, groups, form):
                 acc = ev.add(acc, ev.mul_plain(parts[i], om.gal[g][i]))
             acc = ev.rescale(acc)
         t1 = time.perf_counter()
-        acc = sch.rotsum_hoisted(ev, acc, om.s, double=True)
+        if rotsum:
+            acc = sch.rotsum_hoisted(ev, acc, om.s, double=True)
         accs.append(acc)
         tm += t1 - t0
         tr += time.perf_counter() - t1
@@ -193,24 +196,25 @@ def _oracle_groups(om, ct, parts, groups, form):
 _WORKER = {}
 
 
-def _worker_init(wname, form, n_ids):
-    _WORKER["om"] = _oracle_match(wname, form, n_ids)[1]
+def _worker_init(wname, form, n_ids, tail):
+    _WORKER["om"] = _oracle_match(wname, form, n_ids, tail)[1]
 
 
-def _worker_groups(ct, parts, groups, form):
-    return _oracle_groups(_WORKER["om"], ct, parts, groups, form)
+def _worker_groups(ct, parts, groups, form, rotsum):
+    return _oracle_groups(_WORKER["om"], ct, parts, groups, form, rotsum)
 
 
 class OracleRun:
     """The oracle's match of one query (keys, gallery and query prepared once), timed
     by stage -- expansion (Algorithm 1), HE-C^3 products, rotate-and-sum, compression
-    -- single-threaded, or with the groups spread over `cores` worker processes (each
+    (with tail "fused" the last two are one round per pack, timed as compression) --
+    single-threaded, or with the groups spread over `cores` worker processes (each
     holding its own copy of the keys and gallery; the expanded query goes to them)."""
 
-    def __init__(self, wname, form, cores=1, n_ids=None):
+    def __init__(self, wname, form, cores=1, n_ids=None, tail="fused"):
         from oracle import schedule as sch
-        self.form, self.cores = form, cores
-        self.W, self.om = _oracle_match(wname, form, n_ids)
+        self.form, self.cores, self.tail = form, cores, tail
+        self.W, self.om = _oracle_match(wname, form, n_ids, tail)
         self.n_ids = n_ids or self.W.n_ids
         self.cts = self.om.encrypt(0)
         self.groups = len(self.om.gal)
@@ -224,7 +228,7 @@ class OracleRun:
             import multiprocessing
             self.pool = concurrent.futures.ProcessPoolExecutor(
                 max_workers=min(cores, self.groups), mp_context=multiprocessing.get_context("spawn"),
-                initializer=_worker_init, initargs=(wname, form, n_ids))
+                initializer=_worker_init, initargs=(wname, form, n_ids, tail))
             list(self.pool.map(_noop, range(min(cores, self.groups))))     # workers set up before timing
         self._sch = sch
 
@@ -234,19 +238,23 @@ class OracleRun:
         t0 = time.perf_counter()
         parts = _oracle_expand(self.om, ct, self.form)
         t1 = time.perf_counter()
+        rotsum = self.tail != "fused"
         if self.pool is None:
-            accs, tm, tr = _oracle_groups(self.om, ct, parts, range(self.groups), self.form)
+            accs, tm, tr = _oracle_groups(self.om, ct, parts, range(self.groups), self.form, rotsum)
         else:
             w = min(self.cores, self.groups)
             chunks = [list(range(k, self.groups, w)) for k in range(w)]
-            res = list(self.pool.map(_worker_groups, [ct] * w, [parts] * w, chunks, [self.form] * w))
+            res = list(self.pool.map(_worker_groups, [ct] * w, [parts] * w, chunks, [self.form] * w, [rotsum] * w))
             accs = [None] * self.groups
             for ch, (a, _, _) in zip(chunks, res):
                 for g, x in zip(ch, a):
                     accs[g] = x
             tm, tr = max(r[1] for r in res), max(r[2] for r in res)
         t2 = time.perf_counter()
-        packs = sch.compress(self.om.ev, accs, self.om.cmask, self.om.s, hoisted="double")
+        if rotsum:
+            packs = sch.compress(self.om.ev, accs, self.om.cmask, self.om.s, hoisted="double")
+        else:
+            packs = sch.rotsum_compress(self.om.ev, accs, self.om.cmask, self.om.s)
         t3 = time.perf_counter()
         return packs, {"expansion": t1 - t0, "hec3_products": tm, "rotate_and_sum": tr, "compression": t3 - t2,
                        "groups_wall": t2 - t1, "total": t3 - t0}
@@ -269,22 +277,24 @@ def oracle_form(wname):
     return resolve_expansion("best", W.n_ids, W.dim, W.part, True, (1 << (16 if W.preset == "ring16" else 12)) // 2)
 
 
-def cpu_baseline(wname):
+def cpu_baseline(wname, tail="fused"):
     """The oracle on the host cores: one query of the workload in the GPU line's forms,
     by stage single-threaded, then with its groups spread over the host cores."""
     form = oracle_form(wname)
     cores = os.cpu_count() or 1
-    single = OracleRun(wname, form)
+    single = OracleRun(wname, form, tail=tail)
     st = single.step()
-    multi = OracleRun(wname, form, cores=cores) if single.groups > 1 and cores > 1 else None
+    multi = OracleRun(wname, form, cores=cores, tail=tail) if single.groups > 1 and cores > 1 else None
     mt = multi.step() if multi else st
     if multi:
         multi.close()
     used = min(cores, single.groups) if multi else 1
     return {"value": single.n_ids / mt["total"], "unit": UNIT, "cores": used, "kind": "oracle",
             "sample": f"one query x {single.n_ids} identities ({wname}), full match: Algorithm 1, then the "
-                      f"{single.groups} groups' HE-C^3 and rotate-and-sum over {used} processes, then compression",
-            "host_cpus": cores, "forms": f"{form} Algorithm 1, double-hoisted rotate-and-sum and compression, "
+                      f"{single.groups} groups' HE-C^3{'' if tail == 'fused' else ' and rotate-and-sum'} over "
+                      f"{used} processes, then {'rotate-and-sum and ' if tail == 'fused' else ''}compression",
+            "host_cpus": cores, "forms": f"{form} Algorithm 1, double-hoisted rotate-and-sum and compression"
+                                        f"{' in one round per pack' if tail == 'fused' else ''}, "
                                         f"complex packing (the GPU line's)",
             "single_thread_value": single.n_ids / st["total"],
             "stages_s_single_thread": {k: st[k] for k in ("expansion", "hec3_products", "rotate_and_sum",
@@ -298,7 +308,7 @@ def run_reference(args):
         return
     form = oracle_form(args.workload)
     cores = os.cpu_count() or 1
-    run = OracleRun(args.workload, form, cores=cores)
+    run = OracleRun(args.workload, form, cores=cores, tail=args.tail)
     for _ in range(args.warmup):
         run.step()
     stages = [run.step() for _ in range(args.steps)]
@@ -314,7 +324,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": W.name, "ring": "2^16" if W.preset == "ring16" else W.preset,
                    "n_ids": W.n_ids, "dim": W.dim, "part": W.part, "queries_per_step": 1, "packing": "complex",
-                   "expansion": form, "tail": "double", "gallery": "plain"},
+                   "expansion": form, "tail": args.tail, "gallery": "plain"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "host_cpus": cores,
                          "sample": f"each step: one query x {run.n_ids} identities, full oracle match in the GPU "
                                    f"line's forms, the {run.groups} groups over {used} processes"},
@@ -339,7 +349,7 @@ def run_cpu_extrapolate(args):
         form = oracle_form(wname)
         n = min(W.n_ids, args.cpu_sample_ids)
         for c in (1, cores):
-            run = OracleRun(wname, form, cores=c, n_ids=n)
+            run = OracleRun(wname, form, cores=c, n_ids=n, tail=args.tail)
             st = run.step()
             run.close()
             full_groups = -(-W.n_ids // (n // run.groups if run.groups else 1))
@@ -514,7 +524,7 @@ def run_serving(args):
     expansions = {}
     for gi, (name, R, m, s) in enumerate(SERVE_GALLERIES):
         if args.expansion == "auto":
-            forms = [(e, t) for e in ("doubling", "hoisted", "fused", "deferred") for t in ("printed", "hoisted", "double")]
+            forms = [(e, t) for e in ("doubling", "hoisted", "fused", "deferred") for t in ("printed", "hoisted", "double", "fused")]
         elif args.expansion == "best" and costs is not None:
             forms = [("fused", args.tail), ("deferred", args.tail)]   # the part size decides: the model picks
         else:
@@ -714,13 +724,16 @@ def sched_flags(bm, expansion, tail):
         f |= bm.BM_SCHED_FUSED_EXPANSION
     if expansion == "deferred":
         f |= bm.BM_SCHED_DEFERRED_DIVISION
-    if tail in ("hoisted", "double"):
+    if tail in ("hoisted", "double", "fused"):
         f |= bm.BM_SCHED_HOISTED_ROTSUM | bm.BM_SCHED_HOISTED_COMPRESSION
-    if tail == "double":
+    if tail in ("double", "fused"):
         f |= bm.BM_SCHED_DOUBLE_HOISTED
+    if tail == "fused":
+        f |= bm.BM_SCHED_FUSED_COMPRESSION
     lay = ((bm.BM_LAYOUT_HOISTED if f & 1 else 0) | (bm.BM_LAYOUT_HOISTED_ROTSUM if f & 2 else 0)
            | (bm.BM_LAYOUT_HOISTED_COMPRESSION if f & 4 else 0) | (bm.BM_LAYOUT_DOUBLE_HOISTED if f & 8 else 0)
-           | (bm.BM_LAYOUT_FUSED_EXPANSION if f & 16 else 0) | (bm.BM_LAYOUT_DEFERRED_DIVISION if f & 32 else 0))
+           | (bm.BM_LAYOUT_FUSED_EXPANSION if f & 16 else 0) | (bm.BM_LAYOUT_DEFERRED_DIVISION if f & 32 else 0)
+           | (bm.BM_LAYOUT_FUSED_COMPRESSION if f & 64 else 0))
     return f, lay
 
 
@@ -1005,7 +1018,7 @@ def main():
         line["dnum_model"] = {"chosen": d, "predicted_ms_by_dnum": {str(k + 1): v for k, v in enumerate(ms) if v > 0},
                               "line_dnum": ctx.dnum}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload)
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.tail)
     print(json.dumps(line))
 
 

@@ -274,6 +274,20 @@ bm_status bm_gallery_set_expansion(bm_gallery* g, uint32_t mode);
  *                                hoisting, Bossuat et al., Eurocrypt 2021); the
  *                                rotate-and-sum over s <= 16 slots then takes a
  *                                single round of the s - 1 rotations
+ *  BM_SCHED_FUSED_COMPRESSION    with the three above (hoisted rotate-and-sum and
+ *                                compression, double hoisting): the rotate-and-sum's
+ *                                last round and the compression as one round per pack.
+ *                                The compression places group o of a pack (o its
+ *                                offset) at Rot(M * acc_o, -o) = Rot(M, -o) *
+ *                                Rot(acc_o, -o), and Rot(acc_o, -o) is the last
+ *                                round's sum with every rotation shifted by -o, so
+ *                                each pack is the sum over its groups of the mask
+ *                                rotated by -o times the group's shifted rotations,
+ *                                taken in Q_l u P and moved down once: one ModDown per
+ *                                pack instead of one per group plus the compression
+ *                                round.  The mask multiplies the key-switch sums
+ *                                before ModDown's rounding, not after it.  A gallery
+ *                                without compression ignores the flag.
  * Needs the keys of bm_keygen_ex(..., BM_KEYS_HOISTED).  Plans of the gallery
  * built before the call are dropped; call it before registering the gallery
  * with a server.  BM_E_ARG for unknown flags, or the expansion flag on a gallery
@@ -284,7 +298,8 @@ enum {
     BM_SCHED_HOISTED_COMPRESSION = 4,
     BM_SCHED_DOUBLE_HOISTED = 8,
     BM_SCHED_FUSED_EXPANSION = 16,
-    BM_SCHED_DEFERRED_DIVISION = 32
+    BM_SCHED_DEFERRED_DIVISION = 32,
+    BM_SCHED_FUSED_COMPRESSION = 64
 };
 bm_status bm_gallery_set_schedule(bm_gallery* g, uint32_t flags);
 void bm_gallery_destroy(bm_gallery* g);
@@ -544,10 +559,12 @@ typedef struct bm_op_costs {
 #define BM_LAYOUT_HOISTED_ROTSUM 0x400u
 #define BM_LAYOUT_HOISTED_COMPRESSION 0x800u
 /* ... and BM_LAYOUT_DOUBLE_HOISTED for BM_SCHED_DOUBLE_HOISTED, BM_LAYOUT_FUSED_EXPANSION for
- * BM_SCHED_FUSED_EXPANSION, BM_LAYOUT_DEFERRED_DIVISION for BM_SCHED_DEFERRED_DIVISION. */
+ * BM_SCHED_FUSED_EXPANSION, BM_LAYOUT_DEFERRED_DIVISION for BM_SCHED_DEFERRED_DIVISION,
+ * BM_LAYOUT_FUSED_COMPRESSION for BM_SCHED_FUSED_COMPRESSION. */
 #define BM_LAYOUT_DOUBLE_HOISTED 0x1000u
 #define BM_LAYOUT_FUSED_EXPANSION 0x2000u
 #define BM_LAYOUT_DEFERRED_DIVISION 0x4000u
+#define BM_LAYOUT_FUSED_COMPRESSION 0x8000u
 
 /* Host only (no device needed): the launches of the match of `n_queries`
  * queries against a gallery of n_ids identities in (dim, part_size, packing) under

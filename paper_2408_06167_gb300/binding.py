@@ -36,6 +36,7 @@ BM_LAYOUT_HOISTED_COMPRESSION = 0x800
 BM_LAYOUT_DOUBLE_HOISTED = 0x1000
 BM_LAYOUT_FUSED_EXPANSION = 0x2000
 BM_LAYOUT_DEFERRED_DIVISION = 0x4000
+BM_LAYOUT_FUSED_COMPRESSION = 0x8000
 BM_SCHED_HOISTED_EXPANSION = 1
 BM_SCHED_HOISTED_ROTSUM = 2
 BM_SCHED_HOISTED_COMPRESSION = 4
@@ -43,6 +44,7 @@ BM_SCHED_ALL = 7                      # every hoisted form, one ModDown per rota
 BM_SCHED_DOUBLE_HOISTED = 8
 BM_SCHED_FUSED_EXPANSION = 16
 BM_SCHED_DEFERRED_DIVISION = 32
+BM_SCHED_FUSED_COMPRESSION = 64
 BM_KEYS_ENCRYPTED_GALLERY = 1
 BM_KEYS_HOISTED = 2
 BM_EXPAND_DOUBLING = 0

@@ -61,6 +61,7 @@ struct Layout {
     bool dhoist;                            // ... with one ModDown per round output
     bool fused;                             // hoisted Algorithm 1 with ModDown and Rescale fused
     bool deferred;                          // ... with the division moved past HE-C^3's products
+    bool fcomp;                             // rotate-and-sum's last round and compression fused
 };
 
 // Scale of the score ciphertexts: 2^log_scale with a plaintext gallery (every
@@ -77,7 +78,8 @@ static uint32_t gallery_kind(const Gallery& g) {
            ((g.sched & BM_SCHED_HOISTED_COMPRESSION) ? BM_LAYOUT_HOISTED_COMPRESSION : 0u) |
            ((g.sched & BM_SCHED_DOUBLE_HOISTED) ? BM_LAYOUT_DOUBLE_HOISTED : 0u) |
            ((g.sched & BM_SCHED_FUSED_EXPANSION) ? BM_LAYOUT_FUSED_EXPANSION : 0u) |
-           ((g.sched & BM_SCHED_DEFERRED_DIVISION) ? BM_LAYOUT_DEFERRED_DIVISION : 0u);
+           ((g.sched & BM_SCHED_DEFERRED_DIVISION) ? BM_LAYOUT_DEFERRED_DIVISION : 0u) |
+           ((g.sched & BM_SCHED_FUSED_COMPRESSION) ? BM_LAYOUT_FUSED_COMPRESSION : 0u);
 }
 
 // baby and giant steps of the hoisted rotate-and-sum over s slots: b = 2^ceil(log2(s)/2);
@@ -101,7 +103,8 @@ static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uin
                              uint32_t kind = BM_PACK_REAL) {
     const uint32_t packing = kind & ~(BM_LAYOUT_ENCRYPTED | BM_LAYOUT_HOISTED | BM_LAYOUT_HOISTED_ROTSUM |
                                       BM_LAYOUT_HOISTED_COMPRESSION | BM_LAYOUT_DOUBLE_HOISTED |
-                                      BM_LAYOUT_FUSED_EXPANSION | BM_LAYOUT_DEFERRED_DIVISION);
+                                      BM_LAYOUT_FUSED_EXPANSION | BM_LAYOUT_DEFERRED_DIVISION |
+                                      BM_LAYOUT_FUSED_COMPRESSION);
     lo.encrypted = (kind & BM_LAYOUT_ENCRYPTED) != 0;
     lo.hoisted = (kind & BM_LAYOUT_HOISTED) != 0;
     lo.hrotsum = (kind & BM_LAYOUT_HOISTED_ROTSUM) != 0;
@@ -109,6 +112,7 @@ static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uin
     lo.dhoist = (kind & BM_LAYOUT_DOUBLE_HOISTED) != 0;
     lo.fused = (kind & BM_LAYOUT_FUSED_EXPANSION) != 0;
     lo.deferred = (kind & BM_LAYOUT_DEFERRED_DIVISION) != 0;
+    lo.fcomp = (kind & BM_LAYOUT_FUSED_COMPRESSION) != 0;
     if (!is_pow2(dim) || !is_pow2(part) || part > dim || dim > c.slots)
         return fail(BM_E_DIM, "dim and part size must be powers of two with part <= dim <= N/2");
     if (packing != BM_PACK_REAL && packing != BM_PACK_COMPLEX) return fail(BM_E_ARG, "unknown slot packing");
@@ -130,6 +134,7 @@ static bm_status make_layout(const Context& c, uint64_t n_ids, uint32_t dim, uin
     if (lo.deferred) lo.fused = true;       // the deferred division is a form of the fused expansion
     if (!lo.hoisted || lo.n_in < 2 || lo.n_in > kMaxCircParts || !ks_mdr_supported(c)) lo.fused = false;
     if (!lo.fused || lo.encrypted || !ks_mdr_supported(c, 2)) lo.deferred = false;
+    if (!lo.compress || !lo.hrotsum || !lo.hcomp || !lo.dhoist) lo.fcomp = false;
     lo.n_out = lo.compress ? (lo.groups + part - 1) / part : lo.groups;
     return BM_OK;
 }
@@ -141,6 +146,19 @@ static std::vector<int32_t> schedule_rotations(const Context& c, const Layout& l
         for (uint32_t j = 1; j < lo.n_in; j++) r.push_back((int32_t)(part * j));
     else if (lo.tiled)
         for (uint32_t j = 0; (1u << j) < lo.n_in; j++) r.push_back((int32_t)(part << j));
+    if (lo.fcomp) {
+        // rounds before the last as below; the last round's rotations shifted by -o for
+        // every group offset o of a pack (the identity needs no key)
+        uint32_t b, g;
+        bsgs_split(part, true, b, g);
+        const uint32_t step = g > 1 ? b : 1, count = g > 1 ? g : b;
+        if (g > 1)
+            for (uint32_t k = 1; k < b; k++) r.push_back((int32_t)k);
+        for (uint32_t k = 0; k < count; k++)
+            for (uint32_t o = 0; o < part; o++)
+                if (step * k != o) r.push_back((int32_t)(step * k) - (int32_t)o);
+        return r;
+    }
     if (lo.hrotsum) {
         uint32_t b, g;
         bsgs_split(part, lo.dhoist, b, g);
@@ -466,8 +484,11 @@ bm_status bm_keygen_ex(bm_context* ctxh, uint64_t seed, uint32_t dim, uint32_t p
         all.hcomp = lo.compress;
         for (bool dh : {false, true}) {
             all.dhoist = dh;
+            all.fcomp = false;
             for (int32_t r : schedule_rotations(c, all, part_size)) rots.push_back(r);
         }
+        all.fcomp = lo.compress;
+        for (int32_t r : schedule_rotations(c, all, part_size)) rots.push_back(r);
     }
     if (flags & BM_KEYS_ENCRYPTED_GALLERY)
         for (uint32_t b = 0; (1u << b) < c.slots; b++)
@@ -590,6 +611,7 @@ bm::Gallery::~Gallery() {
     if (d_circ_tw_ext) cudaFree(d_circ_tw_ext);
     if (d_pts_ext) cudaFree(d_pts_ext);
     if (d_cmask) cudaFree(d_cmask);
+    if (d_cmask_rot) cudaFree(d_cmask_rot);
 }
 bm::Ciphertext::~Ciphertext() {
     if (d_coef) cudaFree(d_coef);
@@ -618,7 +640,7 @@ static bm_status gallery_alloc(Context& c, const Layout& lo, uint64_t n_ids, uin
     g.ctx = &c;
     g.packing = packing & ~(BM_LAYOUT_ENCRYPTED | BM_LAYOUT_HOISTED | BM_LAYOUT_HOISTED_ROTSUM |
                             BM_LAYOUT_HOISTED_COMPRESSION | BM_LAYOUT_DOUBLE_HOISTED | BM_LAYOUT_FUSED_EXPANSION |
-                            BM_LAYOUT_DEFERRED_DIVISION);
+                            BM_LAYOUT_DEFERRED_DIVISION | BM_LAYOUT_FUSED_COMPRESSION);
     g.encrypted = lo.encrypted;
     g.sched = (lo.hoisted ? BM_SCHED_HOISTED_EXPANSION : 0u) | (lo.hrotsum ? BM_SCHED_HOISTED_ROTSUM : 0u) |
               (lo.hcomp ? BM_SCHED_HOISTED_COMPRESSION : 0u) | (lo.dhoist ? BM_SCHED_DOUBLE_HOISTED : 0u) |
@@ -1036,8 +1058,12 @@ bm_status bm_gallery_import_encrypted(bm_context* ctxh, const uint64_t* cts, con
 bm_status bm_gallery_set_schedule(bm_gallery* gh, uint32_t flags) {
     if (!gh) return fail(BM_E_ARG, "null gallery");
     const uint32_t all = BM_SCHED_HOISTED_EXPANSION | BM_SCHED_HOISTED_ROTSUM | BM_SCHED_HOISTED_COMPRESSION |
-                         BM_SCHED_DOUBLE_HOISTED | BM_SCHED_FUSED_EXPANSION | BM_SCHED_DEFERRED_DIVISION;
+                         BM_SCHED_DOUBLE_HOISTED | BM_SCHED_FUSED_EXPANSION | BM_SCHED_DEFERRED_DIVISION |
+                         BM_SCHED_FUSED_COMPRESSION;
     if (flags & ~all) return fail(BM_E_ARG, "unknown schedule flags");
+    const uint32_t fc_needs = BM_SCHED_HOISTED_ROTSUM | BM_SCHED_HOISTED_COMPRESSION | BM_SCHED_DOUBLE_HOISTED;
+    if ((flags & BM_SCHED_FUSED_COMPRESSION) && (flags & fc_needs) != fc_needs)
+        return fail(BM_E_ARG, "the fused compression needs the double-hoisted rotate-and-sum and compression");
     Gallery& g = gh->g;
     if ((flags & BM_SCHED_HOISTED_EXPANSION) && !g.tiled)
         return fail(BM_E_ARG, "the gallery's queries arrive expanded (no Algorithm 1 on the server)");
@@ -1074,6 +1100,30 @@ bm_status bm_gallery_set_schedule(bm_gallery* gh, uint32_t flags) {
                 return fail(e == cudaErrorMemoryAllocation ? BM_E_OOM : BM_E_CUDA,
                             std::string("gallery extension: ") + cudaGetErrorString(e));
             }
+        }
+    }
+    if ((flags & BM_SCHED_FUSED_COMPRESSION) && g.compress && !g.d_cmask_rot) {
+        // the compression mask on Q_lc u P (lc = g.level - 1), then rotated right by every
+        // group offset o of a pack: part copies
+        Context& c = *g.ctx;
+        const uint32_t l_in = g.level, nlc = l_in + c.alpha;
+        const size_t mw = (size_t)nlc * c.n;
+        BM_CUDA_TRY(cudaSetDevice(c.device));
+        uint64_t* ext = nullptr;
+        cudaError_t e = cudaMalloc(&g.d_cmask_rot, (size_t)g.part * mw * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&ext, mw * 8);
+        if (e == cudaSuccess) e = extend_to_level_ext(c, 1, g.d_cmask, l_in, ext, c.stream);
+        for (uint32_t o = 0; o < g.part && e == cudaSuccess; o++)
+            e = permute_ntt(c, packed(c, ext, 1, nlc), packed(c, g.d_cmask_rot + o * mw, 1, nlc),
+                            galois_of(c, -(int32_t)o), c.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+        if (ext) cudaFree(ext);
+        if (e != cudaSuccess) {
+            if (g.d_cmask_rot) cudaFree(g.d_cmask_rot);
+            g.d_cmask_rot = nullptr;
+            cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? BM_E_OOM : BM_E_CUDA,
+                        std::string("compression masks: ") + cudaGetErrorString(e));
         }
     }
     if (g.sched != flags) {
@@ -1307,6 +1357,7 @@ struct SchedView {
     bool dhoist = false;                   // hoisted rounds with one ModDown per output
     bool fused = false;                    // hoisted Algorithm 1 with ModDown and Rescale fused
     bool deferred = false;                 // ... divided after HE-C^3's products (one division per group)
+    bool fcomp = false;                    // rotate-and-sum's last round and compression in one round
     const uint64_t* d_pts = nullptr;
     const uint64_t* d_pts_ext = nullptr;   // the plaintexts on Q_L u P (deferred division)
     const uint64_t* d_masks = nullptr;
@@ -1315,6 +1366,7 @@ struct SchedView {
     const uint64_t* d_masks_hat_ext = nullptr;
     const ulonglong2* d_circ_tw_ext = nullptr;
     const uint64_t* d_cmask = nullptr;
+    const uint64_t* d_cmask_rot = nullptr; // the compression mask on Q_lc u P rotated by each offset
 };
 
 // The double-hoisted linear compression at level 1 writes its packs to a buffer of
@@ -1338,6 +1390,9 @@ static SchedView view_of(const Gallery& g) {
     v.dhoist = (v.hrotsum || v.hcomp) && (g.sched & BM_SCHED_DOUBLE_HOISTED);
     v.fused = v.hoisted && (g.sched & BM_SCHED_FUSED_EXPANSION) && g.d_masks_hat_ext;
     v.deferred = v.fused && (g.sched & BM_SCHED_DEFERRED_DIVISION) && g.d_pts_ext;
+    v.fcomp = v.compress && v.hrotsum && v.hcomp && v.dhoist && (g.sched & BM_SCHED_FUSED_COMPRESSION) &&
+              g.d_cmask_rot;
+    v.d_cmask_rot = g.d_cmask_rot;
     v.d_pts_ext = g.d_pts_ext;
     v.d_pts = g.d_pts;
     v.d_masks = g.d_masks;
@@ -1364,6 +1419,7 @@ static SchedView view_of(const Layout& lo, uint32_t part) {
     v.dhoist = lo.dhoist;
     v.fused = lo.fused;
     v.deferred = lo.deferred;
+    v.fcomp = lo.fcomp;
     return v;
 }
 
@@ -1398,7 +1454,9 @@ struct MatchRun {
     static KsSumInfo sum_info(const std::vector<uint64_t*>& ext_of, const std::vector<uint64_t*>& src,
                               const std::vector<uint64_t*>& keys, size_t b, size_t e, uint32_t max_elems) {
         auto count = [&](const std::vector<uint64_t*>& v) {
-            std::vector<uint64_t*> u(v.begin() + b, v.begin() + e);
+            std::vector<uint64_t*> u;
+            for (size_t i = b; i < e; i++)
+                if (v[i]) u.push_back(v[i]);
             std::sort(u.begin(), u.end());
             return (uint32_t)(std::unique(u.begin(), u.end()) - u.begin());
         };
@@ -1516,20 +1574,26 @@ struct MatchRun {
     void double_hoisted_sums(uint32_t level, const std::vector<uint64_t*>& srcs, const std::vector<uint32_t>& e_src,
                              const std::vector<int32_t>& e_rot, const std::vector<uint64_t*>& tgts,
                              const std::vector<std::vector<uint32_t>>& t_elems,
-                             const std::vector<uint64_t*>* outs = nullptr, const uint64_t* mask = nullptr) {
+                             const std::vector<uint64_t*>* outs = nullptr, const uint64_t* mask = nullptr,
+                             const std::vector<uint64_t>* e_flag = nullptr, const uint64_t* gmask = nullptr,
+                             uint32_t n_masks = 0) {
         // with outs, target t + its sum goes to outs[t] (every target, a zero sum for
         // those without elements); else the targets are updated in place; with mask the
-        // result is multiplied by that plaintext (every target must then have elements)
+        // result is multiplied by that plaintext (every target must then have elements).
+        // With gmask (group-masked sums, outs required, no target added): the elements'
+        // flags e_flag mark each group's end and plaintext and the unrotated terms
         const size_t ew = ks_ext_words(c, level);
         std::vector<uint64_t*> ext_of, src, keys, gal, tg, to, off{reinterpret_cast<uint64_t*>((uintptr_t)0)};
         std::vector<uint32_t> t_off{0};
         for (size_t t = 0; t < tgts.size(); t++) {
             if (t_elems[t].empty() && !outs) continue;
             for (uint32_t e : t_elems[t]) {
+                const uint64_t f = e_flag ? (*e_flag)[e] : 0;
+                const bool id = (f & kGalIdentity) != 0;
                 ext_of.push_back(pl.ext2 + (size_t)e_src[e] * ew);
                 src.push_back(srcs[e_src[e]]);
-                keys.push_back(const_cast<uint64_t*>(key(e_rot[e])));
-                gal.push_back(reinterpret_cast<uint64_t*>((uintptr_t)galois_of(c, e_rot[e])));
+                keys.push_back(id ? nullptr : const_cast<uint64_t*>(key(e_rot[e])));
+                gal.push_back(reinterpret_cast<uint64_t*>((uintptr_t)((id ? 1u : galois_of(c, e_rot[e])) | f)));
             }
             tg.push_back(tgts[t]);
             if (outs) to.push_back((*outs)[t]);
@@ -1548,16 +1612,22 @@ struct MatchRun {
             const uint32_t E = t_off[t0 + T] - t_off[t0];
             uint32_t mx = 0;
             for (uint32_t t = t0; t < t0 + T; t++) mx = std::max(mx, t_off[t + 1] - t_off[t]);
-            record(BM_OP_IP_SUM, level, E, 0, T);
+            uint32_t n_rot = E;                  // the unrotated terms are no key-switch products
+            for (uint32_t i = t_off[t0]; i < t_off[t0 + T]; i++)
+                if (reinterpret_cast<uintptr_t>(gal[i]) & kGalIdentity) n_rot--;
+            record(BM_OP_IP_SUM, level, n_rot, 0, T);
             record(BM_OP_MODDOWN, level, T);
             if (!pl.arena.live) {
                 need_scratch(ks_hoisted_scratch_words(c, level, T));
                 continue;
             }
+            KsSumInfo u = sum_info(ext_of, src, keys, t_off[t0], t_off[t0 + T], mx);
+            u.masks = n_masks;
             check(ks_ipsum_hoisted(c, level, T, (const uint64_t*)(doff + t0), E, (const uint64_t* const*)de,
                                    (const uint64_t* const*)ds, (const uint64_t* const*)dk, (const uint64_t*)dg,
-                                   pl.scratch, s, false, sum_info(ext_of, src, keys, t_off[t0], t_off[t0 + T], mx)));
-            check(ks_moddown_add(c, level, T, dt + t0, pl.scratch, s, dto ? dto + t0 : nullptr, mask));
+                                   pl.scratch, s, false, u, 0, gmask));
+            check(ks_moddown_add(c, level, T, gmask ? nullptr : dt + t0, pl.scratch, s, dto ? dto + t0 : nullptr,
+                                 mask));
         }
     }
     // ... rotations of the extended queries (per element: extension, source, key, Galois element)
@@ -1769,6 +1839,7 @@ struct MatchRun {
                 for (int ri = 0; ri < 2; ri++) {
                     const auto& rd = rounds[ri];
                     if (rd[1] <= 1) continue;
+                    if (g.fcomp && ri == last) break;          // taken with the compression below
                     std::vector<uint32_t> e_src;
                     std::vector<int32_t> e_rot;
                     std::vector<std::vector<uint32_t>> t_elems(b.size());
@@ -1799,10 +1870,55 @@ struct MatchRun {
                 continue;
             }
             const uint32_t lc = lg - 1;
+            std::vector<uint64_t*> packs;
+            if (g.fcomp) {
+                // the rotate-and-sum's last round and the compression in one round per pack:
+                // group o of a pack contributes Rot(M, -o) * sum_k Rot(acc_o, step * k - o)
+                // (the unrotated term when step * k = o), every pack one group-masked sum
+                // moved down once
+                uint32_t bs, gs;
+                bsgs_split(part, true, bs, gs);
+                const uint32_t step = gs > 1 ? bs : 1, count = gs > 1 ? gs : bs;
+                std::vector<uint64_t*> srcs, heads, fouts;
+                std::vector<uint32_t> e_src;
+                std::vector<int32_t> e_rot;
+                std::vector<uint64_t> e_flag;
+                std::vector<std::vector<uint32_t>> t_elems;
+                for (uint32_t q = 0; q < Q; q++)
+                    for (uint32_t k = 0; k < G; k += part) {
+                        heads.push_back(pl.accB + ((size_t)q * G + k) * cw(lc));
+                        t_elems.emplace_back();
+                        for (uint32_t o = 0; o < part && k + o < G && g0 + k + o < g.groups; o++) {
+                            const uint32_t si = (uint32_t)srcs.size();
+                            srcs.push_back(pl.accB + ((size_t)q * G + k + o) * cw(lc));
+                            for (uint32_t kk = 0; kk < count; kk++) {
+                                const int32_t r = (int32_t)(step * kk) - (int32_t)o;
+                                uint64_t f = r == 0 ? kGalIdentity : 0;
+                                if (kk + 1 == count) f |= kGalGroupEnd | ((uint64_t)o << kGalMaskShift);
+                                t_elems.back().push_back((uint32_t)e_src.size());
+                                e_src.push_back(si);
+                                e_rot.push_back(r);
+                                e_flag.push_back(f);
+                            }
+                        }
+                    }
+                const bool ct = coef_tail();
+                for (size_t p = 0; p < heads.size(); p++) {
+                    if (ct) packs.push_back(pl.packs + p * cw(lc));
+                    fouts.push_back(ct ? packs.back() : heads[p]);
+                }
+                const size_t ew = ks_ext_words(c, lc);
+                for (size_t s0 = 0; s0 < srcs.size(); s0 += ksb) {
+                    std::vector<uint64_t*> chunk(srcs.begin() + s0, srcs.begin() + std::min(srcs.size(), s0 + ksb));
+                    modup_batch(lc, chunk, pl.ext2 + s0 * ew);
+                }
+                double_hoisted_sums(lc, srcs, e_src, e_rot, heads, t_elems, &fouts, nullptr, &e_flag, g.d_cmask_rot,
+                                    std::min(part, G));
+                mask_fused = true;
+            }
             std::vector<uint64_t*> mp(b.size(), const_cast<uint64_t*>(g.d_cmask));
             if (!mask_fused) mulplain_batch(lc, b, mp, b);
-            std::vector<uint64_t*> packs;
-            if (g.hcomp) {
+            if (g.hcomp && !g.fcomp) {
                 // linear form: every group r > 0 of a pack rotated right by r in one hoisted round,
                 // summed into the pack's first group
                 std::vector<uint64_t*> srcs, heads;

@@ -218,6 +218,9 @@ struct Gallery {
     uint64_t* d_pts_ext = nullptr;            // [groups][n_in][L+1+alpha][N] d_pts on Q_L u P (deferred division)
     ulonglong2* d_circ_tw_ext = nullptr;      // [L+1+alpha][n_in]
     uint64_t* d_cmask = nullptr;              // [level][N] compression mask at level-1
+    // [part][level+alpha][N]: the compression mask on Q_(level-1) u P rotated right by each
+    // group offset o of a pack (BM_SCHED_FUSED_COMPRESSION), NTT + Montgomery
+    uint64_t* d_cmask_rot = nullptr;
     ~Gallery();
 };
 
@@ -411,12 +414,20 @@ cudaError_t ks_rotate_hoisted(const Context& c, uint32_t level, uint32_t E, cons
 // most elements of one target (the depth of the kernel's copy pipeline); zero =
 // unknown (every element its own operands; a deep pipeline).
 struct KsSumInfo {
-    uint32_t ext = 0, keys = 0, srcs = 0, max_elems = 0;
+    uint32_t ext = 0, keys = 0, srcs = 0, max_elems = 0, masks = 0;
 };
+// Group-masked sums (gmask != nullptr): a target's elements come group by group, and
+// each group's key-switch sum is multiplied by its own plaintext before the target sums
+// the groups.  Flags in the high bits of gal_of[e] (the low 32 bits are the Galois element):
+constexpr uint64_t kGalGroupEnd = 1ull << 63;  // last element of its group
+constexpr uint64_t kGalIdentity = 1ull << 62;  // the unrotated source: P * (c0, c1) on the q-limbs
+constexpr int kGalMaskShift = 40;              // the group's plaintext: gmask + index * nlx * N
+constexpr uint64_t kGalMaskBits = 0xffffull;
 cudaError_t ks_ipsum_hoisted(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
                              const uint64_t* const* ext_of, const uint64_t* const* src_of,
                              const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch,
-                             cudaStream_t s, bool ntt_out = false, KsSumInfo u = {}, uint32_t tpad = 0);
+                             cudaStream_t s, bool ntt_out = false, KsSumInfo u = {}, uint32_t tpad = 0,
+                             const uint64_t* gmask = nullptr);
 // ModDown and Rescale fused at the top level: e [T][2][L+1+alpha][N] (NTT form, every
 // limb; the special limbs are transformed in place) divided by q_(L-drop+1)..q_L * P
 // into out[t] (level L - drop, drop 1 or 2); scratch ks_mdr_scratch_words(c, T);
@@ -463,6 +474,9 @@ cudaError_t masks_extend(const Context& c, uint32_t n_in, const uint64_t* masks,
 // Q_L u P: out [count][L+1+alpha][N], limbs l_in.. from the centred integer
 // coefficients of the q_0 limb (exact while they lie within q_0 / 2); synchronises s
 cudaError_t extend_to_ext_basis(const Context& c, size_t count, const uint64_t* in, uint32_t l_in, uint64_t* out,
+                                cudaStream_t s);
+// ... to the key-switching basis of their own level, Q_(l_in-1) u P: out [count][l_in+alpha][N]
+cudaError_t extend_to_level_ext(const Context& c, size_t count, const uint64_t* in, uint32_t l_in, uint64_t* out,
                                 cudaStream_t s);
 // the last rescale in the coefficient domain: in[b] level-1 ciphertexts (coefficient
 // form) -> out[b] at level 0, the residues of rescale + inverse NTT (needs q_1 < q_0)

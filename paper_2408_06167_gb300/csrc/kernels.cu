@@ -1049,13 +1049,12 @@ cudaError_t fold_gallery(const Context& c, size_t groups, uint32_t n_in, const u
     return cudaStreamSynchronize(s);
 }
 
-cudaError_t extend_to_ext_basis(const Context& c, size_t count, const uint64_t* in, uint32_t l_in, uint64_t* out,
-                                cudaStream_t s) {
-    // out [count][nlx][N]: the l_in limbs of in copied, limbs l_in..nlx-1 (primes of the
-    // same index in the basis q_0..q_L, p_0..) from the q_0 limb's integer
-    // coefficients, centred (NTT + Montgomery like the copied limbs)
-    const uint32_t nlx = c.L + 1 + c.alpha;
-    if (l_in == 0 || l_in >= nlx) return cudaErrorInvalidValue;
+// out [count][nlx][N]: the l_in limbs of in copied, limbs l_in..nlx-1 (the primes of
+// index first, first + 1, ... in the basis q_0..q_L, p_0..) from the q_0 limb's integer
+// coefficients, centred (NTT + Montgomery like the copied limbs)
+static cudaError_t extend_limbs(const Context& c, size_t count, const uint64_t* in, uint32_t l_in, uint32_t nlx,
+                                uint32_t first, uint64_t* out, cudaStream_t s) {
+    if (l_in == 0 || l_in >= nlx || first + (nlx - l_in) > c.L + 1 + c.alpha) return cudaErrorInvalidValue;
     const uint32_t nx = nlx - l_in;
     const size_t n = c.n;
     uint64_t* tmp = nullptr;
@@ -1072,18 +1071,28 @@ cudaError_t extend_to_ext_basis(const Context& c, size_t count, const uint64_t* 
         if (e == cudaSuccess) e = ntt_inverse(c, t0, s);
         if (e == cudaSuccess) {
             k_centred_to_p<<<dim3(nx, (uint32_t)(n / kThreads / 4)), kThreads, 0, s>>>(tmp, dst + l_in * n, n,
-                                                                                     c.primes[0], l_in, c.tab,
+                                                                                     c.primes[0], first, c.tab,
                                                                                      (uint32_t)n);
             e = cudaGetLastError();
         }
         LimbBatch pb{dst, 1, (uint64_t)nlx * n, l_in, nx, 0};
-        for (uint32_t i = 0; i < nx; i++) pb.set(i, l_in + i);
+        for (uint32_t i = 0; i < nx; i++) pb.set(i, first + i);
         if (e == cudaSuccess) e = ntt_forward(c, pb, s);
         if (e == cudaSuccess) e = to_montgomery(c, pb, false, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(tmp);
     return e;
+}
+
+cudaError_t extend_to_ext_basis(const Context& c, size_t count, const uint64_t* in, uint32_t l_in, uint64_t* out,
+                                cudaStream_t s) {
+    return extend_limbs(c, count, in, l_in, c.L + 1 + c.alpha, l_in, out, s);
+}
+
+cudaError_t extend_to_level_ext(const Context& c, size_t count, const uint64_t* in, uint32_t l_in, uint64_t* out,
+                                cudaStream_t s) {
+    return extend_limbs(c, count, in, l_in, l_in + c.alpha, c.L + 1, out, s);
 }
 
 cudaError_t masks_extend(const Context& c, uint32_t n_in, const uint64_t* masks, uint64_t* ext, cudaStream_t s) {

@@ -427,12 +427,12 @@ __device__ __forceinline__ void place4(uint64_t (&o)[4], const W4& g, uint32_t s
 // gets P times the run's source ciphertext: E_0, E_1..E_(N_in-1) of a query of the fused
 // Algorithm 1 in one launch.
 constexpr uint32_t kFoldElems = 12;
-template <int LA, int LB, int R, int ND, int MINB>
+template <int LA, int LB, int R, int ND, int MINB, bool GM>
 __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
     k_ks_f4s(const uint64_t* const* ext_of, const uint64_t* const* src_of, const uint64_t* const* key_of,
              const uint64_t* gal_of, const uint64_t* off, uint64_t* __restrict__ acc,
              const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L, uint32_t nb,
-             bool ntt_out, uint32_t tpad, bool by_target) {
+             bool ntt_out, uint32_t tpad, bool by_target, const uint64_t* __restrict__ gmask) {
     constexpr int LT = 2, K = 4, M = 1 << LB, TH = M >> LT, SW = sub_words<LB, LT>(), LOGN = LA + LB, N = 1 << LOGN;
     constexpr int TWN = row_tw_entries<LB, R>();
     __shared__ uint64_t sm[R * SW];
@@ -479,9 +479,24 @@ __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
     const uint32_t e0 = (uint32_t)off[tg], e1 = (uint32_t)off[tg + 1];
     Acc128 a0[K], a1[K];
     uint64_t cs[K] = {0, 0, 0, 0};
+    uint64_t pk0[K] = {0, 0, 0, 0}, pk1[K] = {0, 0, 0, 0};   // GM: the target's sum of masked groups
 #pragma unroll 1
     for (uint32_t e = e0; e < e1; e++) {
-        const Perm4 pm4 = perm4(i0, LOGN, (uint32_t)gal_of[e]);
+        const uint64_t gw = gal_of[e];
+        if (GM && (gw & kGalIdentity)) {
+            // the unrotated source: P * c0 joins the c0 sum, P * c1 the second component
+            if (qlimb) {
+                const uint64_t* src = src_of[e];
+                const W4 x0 = ld256(src + (size_t)jj * N + i0);
+                const W4 x1 = ld256(src + ((size_t)l1 + jj) * N + i0);
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    cs[k] += x0.w[k];
+                    mad128(a1[k], x1.w[k], pm);
+                }
+            }
+        } else {
+        const Perm4 pm4 = perm4(i0, LOGN, (uint32_t)gw);
         const uint64_t* key = key_of[e] + (size_t)pi * N + i0;
         const uint64_t* ext = ext_of[e] + (size_t)jj * N + pm4.gb;
         W4 xs[ND], k0s[ND], k1s[ND], cw;
@@ -512,6 +527,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
 #pragma unroll
             for (int k = 0; k < K; k++) cs[k] += c[k];
         }
+        }
         if ((e - e0) % kFoldElems == kFoldElems - 1) {
 #pragma unroll
             for (int k = 0; k < K; k++) {
@@ -521,8 +537,24 @@ __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
                 cs[k] = r >= q ? r - q : r;
             }
         }
+        if (GM && (gw & kGalGroupEnd)) {
+            // the group's sum (with P times its c0 words) reduced, times the group's
+            // plaintext (Montgomery form), added to the target's sum; the group
+            // accumulators start again from zero
+            const uint32_t mi = (uint32_t)((gw >> kGalMaskShift) & kGalMaskBits);
+            const W4 mw = ld256(gmask + ((size_t)mi * nlx + jj) * N + i0);
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                if (qlimb) mad128(a0[k], cs[k], pm);
+                pk0[k] = addm(pk0[k], mont(redc_wide(a0[k], q, qn, rsh), mw.w[k], q, qn), q);
+                pk1[k] = addm(pk1[k], mont(redc_wide(a1[k], q, qn, rsh), mw.w[k], q, qn), q);
+                a0[k] = Acc128{};
+                a1[k] = Acc128{};
+                cs[k] = 0;
+            }
+        }
     }
-    if (qlimb) {
+    if (!GM && qlimb) {
 #pragma unroll
         for (int k = 0; k < K; k++) mad128(a0[k], cs[k], pm);
     }
@@ -530,7 +562,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
     for (uint32_t comp = 0; comp < 2; comp++) {
         uint64_t v[K];
 #pragma unroll
-        for (int k = 0; k < K; k++) v[k] = redc_wide(comp ? a1[k] : a0[k], q, qn, rsh);
+        for (int k = 0; k < K; k++) v[k] = GM ? (comp ? pk1[k] : pk0[k]) : redc_wide(comp ? a1[k] : a0[k], q, qn, rsh);
         uint64_t* o = acc + (((size_t)tgo * 2 + comp) * nlx + jj) * N + roff;
         if (!inv) {
             nttr::store_last<LB, LT>(v, o, t);
@@ -1053,7 +1085,7 @@ template <int LA, int LB, int LT, int C, int R>
 cudaError_t ks_ipsum_launch(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
                             const uint64_t* const* ext_of, const uint64_t* const* src_of,
                             const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch, bool ntt_out,
-                            KsSumInfo u, uint32_t tpad, cudaStream_t s) {
+                            KsSumInfo u, uint32_t tpad, const uint64_t* gmask, cudaStream_t s) {
     constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
     (void)N2;
     const KsLevelConst& K = c.h_ksc[level];
@@ -1063,9 +1095,11 @@ cudaError_t ks_ipsum_launch(const Context& c, uint32_t level, uint32_t T, const 
     // algorithmic bytes: every distinct extension (nd x nlx limbs), key slice (nd x 2 x
     // nlx limbs) and source c0 (l1 limbs) once, and the sums (2 x nlx limbs a target)
     const double ue = u.ext ? u.ext : E, uk = u.keys ? u.keys : E, us = u.srcs ? u.srcs : E;
-    // with tpad the E_0 slots: each source's 2 l1 limbs read, 2 nlx written
+    // with tpad the E_0 slots: each source's 2 l1 limbs read, 2 nlx written; with group
+    // masks each mask's nlx limbs and each source's c1 limbs (its unrotated term)
     const double e0 = tpad ? (double)(T / tpad) * (2.0 * l1 + 2.0 * nlx) : 0.0;
-    ProfScope ps(BM_KERNEL_KS_IP, s, lw * (nlx * (ue * nd + 2.0 * nd * uk + 2.0 * T) + us * l1 + e0),
+    const double gm = gmask ? (double)u.masks * nlx + us * l1 : 0.0;
+    ProfScope ps(BM_KERNEL_KS_IP, s, lw * (nlx * (ue * nd + 2.0 * nd * uk + 2.0 * T) + us * l1 + e0 + gm),
                  (ntt_out ? 0.0 : bf_r * T * 2.0 * alpha) +
                      N * (double)nlx * (2.0 * kProdMul * nd * E + 2.0 * kRedcMul * T) + (double)N * l1 * E * kProdMul);
     // R rows a block (64 threads); digits unrolled up to ND
@@ -1073,12 +1107,18 @@ cudaError_t ks_ipsum_launch(const Context& c, uint32_t level, uint32_t T, const 
     const dim3 g((T + (tpad ? T / tpad : 0)) * nlx, N1 / RF), b(RF * (1 << (LB - 2)));
     auto args = [&](auto kernel) {
         return pdl_launch(kernel, g, b, 0, s, ext_of, src_of, key_of, gal_of, off, scratch, kc, c.tab, l1, c.L, c.nb,
-                          ntt_out, tpad, u.max_elems > 1);
+                          ntt_out, tpad, u.max_elems > 1, gmask);
     };
     cudaError_t e = cudaErrorInvalidValue;
-    if (nd <= 1) e = args(k_ks_f4s<LA, LB, RF, 1, 8>);
-    else if (nd <= 2) e = args(k_ks_f4s<LA, LB, RF, 2, 8>);
-    else if (nd <= 4) e = args(k_ks_f4s<LA, LB, RF, 4, 4>);
+    if (gmask) {
+        if (nd <= 1) e = args(k_ks_f4s<LA, LB, RF, 1, 8, true>);
+        else if (nd <= 2) e = args(k_ks_f4s<LA, LB, RF, 2, 8, true>);
+        else if (nd <= 4) e = args(k_ks_f4s<LA, LB, RF, 4, 4, true>);
+    } else {
+        if (nd <= 1) e = args(k_ks_f4s<LA, LB, RF, 1, 8, false>);
+        else if (nd <= 2) e = args(k_ks_f4s<LA, LB, RF, 2, 8, false>);
+        else if (nd <= 4) e = args(k_ks_f4s<LA, LB, RF, 4, 4, false>);
+    }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -1193,14 +1233,15 @@ cudaError_t ks_rotate_hoisted(const Context& c, uint32_t level, uint32_t E, cons
 cudaError_t ks_ipsum_hoisted(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
                              const uint64_t* const* ext_of, const uint64_t* const* src_of,
                              const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch,
-                             cudaStream_t s, bool ntt_out, KsSumInfo u, uint32_t tpad) {
+                             cudaStream_t s, bool ntt_out, KsSumInfo u, uint32_t tpad, const uint64_t* gmask) {
     if (T == 0) return cudaSuccess;
+    if (gmask && (ntt_out || tpad)) return cudaErrorInvalidValue;
     if (c.log_n == 16)
         return ks_ipsum_launch<8, 8, 2, 2, 2>(c, level, T, off, E, ext_of, src_of, key_of, gal_of, scratch, ntt_out, u,
-                                              tpad, s);
+                                              tpad, gmask, s);
     if (c.log_n == 12)
         return ks_ipsum_launch<6, 6, 2, 8, 8>(c, level, T, off, E, ext_of, src_of, key_of, gal_of, scratch, ntt_out, u,
-                                              tpad, s);
+                                              tpad, gmask, s);
     return cudaErrorInvalidValue;
 }
 
@@ -1227,6 +1268,7 @@ cudaError_t ks_moddown_rescale(const Context& c, uint32_t T, uint64_t* e, uint64
 cudaError_t ks_moddown_add(const Context& c, uint32_t level, uint32_t T, uint64_t* const* d_tgt, uint64_t* scratch,
                            cudaStream_t s, uint64_t* const* d_out, const uint64_t* mask) {
     if (T == 0) return cudaSuccess;
+    if (!d_tgt && !d_out) return cudaErrorInvalidValue;
     if (c.log_n == 16) return ks_moddown_add_launch<8, 8, 2, 2, 2>(c, level, T, d_tgt, d_out, scratch, mask, s);
     if (c.log_n == 12) return ks_moddown_add_launch<6, 6, 2, 8, 8>(c, level, T, d_tgt, d_out, scratch, mask, s);
     return cudaErrorInvalidValue;

@@ -21,7 +21,7 @@ def octx(name):
     return _CTX[name]
 
 
-def schedule_rotations(ctx, m, s, hoisted=False):
+def schedule_rotations(ctx, m, s, hoisted=False, fused_compress=False):
     """Left rotations the tiled/expanded schedule needs (negative = right)."""
     n_in = m // s
     tiled = ctx.L >= 3
@@ -40,14 +40,19 @@ def schedule_rotations(ctx, m, s, hoisted=False):
         rots += list(range(1, s)) + [b * k for k in range(1, g)]
         if level >= 2:
             rots += [-r for r in range(1, s)]
-    return rots
+    if fused_compress and level >= 2:
+        # the last rotate-and-sum round's rotations shifted by every group offset of a pack
+        b, g = sch.bsgs_split(s, double=True)
+        step, count = (b, g) if g > 1 else (1, b)
+        rots += [step * k - o for k in range(count) for o in range(s) if step * k != o]
+    return sorted(set(rots), key=rots.index)
 
 
 class OracleMatch:
     """Keys, gallery plaintexts, query ciphertexts and match outputs from the oracle."""
 
     def __init__(self, name, m, s, R, n_queries, feats=None, seed=KEY_SEED, complex_pack=False, encrypted=False,
-                 hoisted=False, hoisted_tail=False, double_hoisted=False):
+                 hoisted=False, hoisted_tail=False, double_hoisted=False, fused_compress=False):
         self.ctx = ctx = octx(name)
         self.m, self.s, self.R = m, s, R
         self.complex_pack = complex_pack
@@ -55,13 +60,15 @@ class OracleMatch:
         self.hoisted = hoisted
         self.hoisted_tail = hoisted_tail
         self.double_hoisted = double_hoisted
+        self.fused_compress = fused_compress
         self.n_in = m // s
         self.tiled = ctx.L >= 3
         self.level = ctx.L - 1 if self.tiled else ctx.L
         self.compress = self.level >= 2
         self.feats = wl.gallery(R, m) if feats is None else feats
         self.queries, self.true_ids = wl.queries(self.feats, n_queries)
-        self.sk, self.pk, self.rks = ckks.keygen(ctx, seed, schedule_rotations(ctx, m, s, hoisted or hoisted_tail))
+        self.sk, self.pk, self.rks = ckks.keygen(ctx, seed, schedule_rotations(ctx, m, s, hoisted or hoisted_tail,
+                                                                              fused_compress))
         self.ev = ckks.Evaluator(ctx, self.rks, ckks.keygen_relin(ctx, seed, self.sk) if encrypted else None)
         S, L = ctx.slots, ctx.L
         self.groups = sch.n_groups(R, s, S, complex_pack)
@@ -114,7 +121,8 @@ class OracleMatch:
         outs, packed = sch.match(self.ev, cts, self.gal, self.masks, self.cmask, self.m, self.s,
                                  expanded=not self.tiled, encrypted_gallery=self.encrypted,
                                  hoisted=self.hoisted, hoisted_rotsum=self.hoisted_tail,
-                                 hoisted_compress=self.hoisted_tail, double_hoisted=self.double_hoisted)
+                                 hoisted_compress=self.hoisted_tail, double_hoisted=self.double_hoisted,
+                                 fused_compress=self.fused_compress)
         return self.ct_array(outs), packed
 
     def scores(self, outs_array, packed):

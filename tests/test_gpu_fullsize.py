@@ -68,20 +68,23 @@ def test_large_batched_full_size_scores(ring16, part, packing, hoisted):
             assert rank1 == int(ref.argmax()), qi
 
 
-def test_face_full_size_default_forms_are_bit_exact(ring16):
+@pytest.mark.parametrize("fused_compress", [True, False])
+def test_face_full_size_default_forms_are_bit_exact(ring16, fused_compress):
     """The bench's default line: 6,144 identities x 128 dims, parts of 16, one query,
     complex packing, the fused Algorithm 1 with the deferred division and the
-    double-hoisted tail, matched through bm_match_async as the bench times it: the
-    score ciphertext is bit-exact against the oracle's same-order evaluation."""
+    double-hoisted tail (its last round and the compression in one round per pack, or
+    the two rounds), matched through bm_match_async as the bench times it: the score
+    ciphertext is bit-exact against the oracle's same-order evaluation."""
     c = ring16
     W = wl.WORKLOADS["face-128d-6144"]
     om = OracleMatch("ring16", W.dim, W.part, W.n_ids, 1, complex_pack=True, hoisted="deferred", hoisted_tail=True,
-                     double_hoisted=True)
+                     double_hoisted=True, fused_compress=fused_compress)
     _, _, ek = bm.bm_keygen_ex(c, KEY_SEED, W.dim, W.part, bm.BM_KEYS_HOISTED)
     g = bm.bm_gallery_import_packed(c, om.pts_array(), om.masks_array(), om.cmask_array(), W.n_ids, W.dim, W.part,
                                     bm.BM_PACK_COMPLEX)
     bm.bm_gallery_set_schedule(g, bm.BM_SCHED_ALL | bm.BM_SCHED_DOUBLE_HOISTED | bm.BM_SCHED_FUSED_EXPANSION
-                               | bm.BM_SCHED_DEFERRED_DIVISION)
+                               | bm.BM_SCHED_DEFERRED_DIVISION
+                               | (bm.BM_SCHED_FUSED_COMPRESSION if fused_compress else 0))
     cts = om.encrypt(0)
     q = bm.bm_ciphertext_import(c, om.ct_array(cts), om.ctx.L)
     res = bm.bm_match_async(c, ek, g, [q])
@@ -95,15 +98,17 @@ def test_face_full_size_default_forms_are_bit_exact(ring16):
 def test_finger_full_size_default_forms_are_bit_exact(ring16):
     """The finger line's forms: 65,536 identities x 16 dims, parts of 4, 64 queries in
     one call, complex packing, the fused Algorithm 1 (4 groups, 4 parts) and the
-    double-hoisted tail: sampled queries bit-exact against the oracle."""
+    double-hoisted tail with its last round and the compression in one round per pack:
+    sampled queries bit-exact against the oracle."""
     c = ring16
     W = wl.WORKLOADS["finger-16d-65536-q64"]
     om = OracleMatch("ring16", W.dim, W.part, W.n_ids, W.n_queries, complex_pack=True, hoisted="fused",
-                     hoisted_tail=True, double_hoisted=True)
+                     hoisted_tail=True, double_hoisted=True, fused_compress=True)
     _, _, ek = bm.bm_keygen_ex(c, KEY_SEED, W.dim, W.part, bm.BM_KEYS_HOISTED)
     g = bm.bm_gallery_import_packed(c, om.pts_array(), om.masks_array(), om.cmask_array(), W.n_ids, W.dim, W.part,
                                     bm.BM_PACK_COMPLEX)
-    bm.bm_gallery_set_schedule(g, bm.BM_SCHED_ALL | bm.BM_SCHED_DOUBLE_HOISTED | bm.BM_SCHED_FUSED_EXPANSION)
+    bm.bm_gallery_set_schedule(g, bm.BM_SCHED_ALL | bm.BM_SCHED_DOUBLE_HOISTED | bm.BM_SCHED_FUSED_EXPANSION
+                               | bm.BM_SCHED_FUSED_COMPRESSION)
     ocs = [om.encrypt(qi) for qi in range(W.n_queries)]
     qs = [bm.bm_ciphertext_import(c, om.ct_array(cts), om.ctx.L) for cts in ocs]
     res = bm.bm_match_async(c, ek, g, qs)

@@ -136,6 +136,52 @@ def test_hoisted_schedule_is_bit_exact(name, m, s, R, nq, tail_only, double):
         assert np.abs(om.scores(got, opacked) - ref).max() < 1e-5
 
 
+@pytest.mark.parametrize("name,m,s,R,nq,expansion", [
+    ("small4", 128, 16, 2500, 2, "deferred"),  # one round of 16 terms a group, 2 groups in one pack
+    ("small4", 16, 4, 3000, 3, "fused"),       # packs of 4 groups, a ragged last pack, three queries
+    ("small4", 32, 32, 700, 1, "printed"),     # baby steps first, the giant round fused (s > 16)
+    ("small4", 16, 8, 2100, 1, "hoisted"),     # one round of 8 terms a group
+    ("small4", 16, 1, 2100, 1, "hoisted"),     # parts of 1: each pack one group, its masked term alone
+])
+def test_fused_compression_is_bit_exact(name, m, s, R, nq, expansion):
+    """The rotate-and-sum's last round and the compression as one round per pack
+    (each group's rotations shifted by its offset, the rotated compression masks
+    applied before one ModDown a pack): bit-exact against the oracle's same-order
+    evaluation, after each form of Algorithm 1."""
+    c = gctx(name)
+    hoisted = {"printed": False, "hoisted": True}.get(expansion, expansion)
+    om = OracleMatch(name, m, s, R, nq, hoisted=hoisted, hoisted_tail=True, double_hoisted=True,
+                     fused_compress=True)
+    _, _, ek = bm.bm_keygen_ex(c, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
+    g = bm.bm_gallery_import(c, om.pts_array(), om.masks_array(), om.cmask_array(), R, m, s)
+    flags = (bm.BM_SCHED_HOISTED_ROTSUM | bm.BM_SCHED_HOISTED_COMPRESSION | bm.BM_SCHED_DOUBLE_HOISTED
+             | bm.BM_SCHED_FUSED_COMPRESSION)
+    if expansion != "printed":
+        flags |= bm.BM_SCHED_HOISTED_EXPANSION
+    if expansion in ("fused", "deferred"):
+        flags |= bm.BM_SCHED_FUSED_EXPANSION
+    if expansion == "deferred":
+        flags |= bm.BM_SCHED_DEFERRED_DIVISION
+    bm.bm_gallery_set_schedule(g, flags)
+    ocs = [om.encrypt(qi) for qi in range(nq)]
+    qs = [bm.bm_ciphertext_import(c, om.ct_array(cts), om.ctx.L) for cts in ocs]
+    res = bm.bm_match(c, ek, g, qs)
+    for qi in range(nq):
+        want, opacked = om.match(ocs[qi])
+        got = bm.bm_result_export(res, qi)
+        assert np.array_equal(got, want), f"query {qi}: ciphertexts differ"
+        ref = wl.plaintext_scores(om.feats, om.queries[qi])
+        assert np.abs(om.scores(got, opacked) - ref).max() < 1e-5
+
+
+def test_fused_compression_flag_needs_the_double_hoisted_tail():
+    c = gctx("small4")
+    om = OracleMatch("small4", 16, 4, 300, 1)
+    g = bm.bm_gallery_import(c, om.pts_array(), om.masks_array(), om.cmask_array(), 300, 16, 4)
+    with pytest.raises(bm.BlindMatchError):
+        bm.bm_gallery_set_schedule(g, bm.BM_SCHED_HOISTED_ROTSUM | bm.BM_SCHED_FUSED_COMPRESSION)
+
+
 @pytest.mark.parametrize("double", [False, True])
 @pytest.mark.parametrize("m,s,R,nq", [(128, 16, 6144, 1), (128, 4, 20000, 3)])
 def test_hoisted_and_doubling_forms_give_the_same_scores_ring16(m, s, R, nq, double):

@@ -264,14 +264,17 @@ def test_rotation_four_digits_is_bit_exact(level, rot):
 @pytest.mark.parametrize("form", ["fused", "deferred"])
 def test_match_four_digits_is_bit_exact(form):
     """The bench's forms (fused Algorithm 1 with or without the deferred division,
-    double-hoisted tail, complex packing) with four digits: the hoisted sums of the
-    top level take four digits a word."""
+    double-hoisted tail with its last round and the compression in one round per pack,
+    complex packing) with four digits: the hoisted sums of the top level take four
+    digits a word."""
     c = dnum4_ctx()
     m, s, R = 128, 16, 700
-    om = OracleMatch(DNUM4, m, s, R, 1, complex_pack=True, hoisted=form, hoisted_tail=True, double_hoisted=True)
+    om = OracleMatch(DNUM4, m, s, R, 1, complex_pack=True, hoisted=form, hoisted_tail=True, double_hoisted=True,
+                     fused_compress=True)
     _, _, ek = bm.bm_keygen_ex(c, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
     g = bm.bm_gallery_import_packed(c, om.pts_array(), om.masks_array(), om.cmask_array(), R, m, s, bm.BM_PACK_COMPLEX)
-    flags = bm.BM_SCHED_ALL | bm.BM_SCHED_DOUBLE_HOISTED | bm.BM_SCHED_FUSED_EXPANSION
+    flags = (bm.BM_SCHED_ALL | bm.BM_SCHED_DOUBLE_HOISTED | bm.BM_SCHED_FUSED_EXPANSION
+             | bm.BM_SCHED_FUSED_COMPRESSION)
     if form == "deferred":
         flags |= bm.BM_SCHED_DEFERRED_DIVISION
     bm.bm_gallery_set_schedule(g, flags)

@@ -310,6 +310,40 @@ def test_double_hoisted_forms_match_the_oracle_counts(preset, R, dim, part, Q):
     assert not any(o["op"] == "accum" for o in ops)
 
 
+@pytest.mark.parametrize("preset,R,dim,part,Q", [("small4", 2500, 128, 16, 3), ("ring16", 1 << 20, 128, 4, 40),
+                                                 ("ring16", 6144, 128, 16, 1), ("small4", 3000, 32, 32, 2),
+                                                 ("ring16", 65536, 16, 4, 64)])
+def test_fused_compression_matches_the_oracle_counts(preset, R, dim, part, Q):
+    """The rotate-and-sum's last round and the compression in one round per pack: one
+    ModDown per pack at the compression level, one key-switch product per rotated term
+    (the unrotated term of each group is none), no second round and no mask product."""
+    kind = (bm.BM_LAYOUT_HOISTED | bm.BM_LAYOUT_HOISTED_ROTSUM | bm.BM_LAYOUT_HOISTED_COMPRESSION
+            | bm.BM_LAYOUT_DOUBLE_HOISTED | bm.BM_LAYOUT_FUSED_COMPRESSION)
+    ops, _ = bm.bm_plan_estimate(preset, R, dim, part, Q, packing=kind)
+    log_n, n_q = PRESET[preset]
+    L, slots = n_q - 1, 1 << (log_n - 1)
+    lg, n_in = L - 1, dim // part
+    groups = sch.n_groups(R, part, slots)
+    packs = -(-groups // part)
+    ev = sch.CountingEvaluator()
+    sch.match(ev, [sch.SymCt(L)], [[None] * n_in for _ in range(groups)], [None] * n_in, object(), dim, part,
+              hoisted=True, hoisted_rotsum=True, hoisted_compress=True, double_hoisted=True, fused_compress=True)
+    orc = ev.counts()
+    lib = library_counts(ops)
+    lc = lg - 1
+    b, g = sch.bsgs_split(part, double=True)
+    count = g if g > 1 else b
+    assert lib[("moddown", lc)] == Q * orc[("ModDown", lc)] == Q * (packs + (groups if g > 1 else 0))
+    assert lib[("ip_sum", lc)] == Q * orc[("IPH", lc)]
+    rotated = sum(1 for k in range(count) for o in range(part) if (b if g > 1 else 1) * k != o)
+    full = groups // part
+    assert orc[("IPH", lc)] >= full * rotated
+    assert ("MulP", lc) not in orc
+    assert lib[("mul_plain", lc)] == 0
+    for lv in range(L + 1):
+        assert lib[("modup", lv)] == Q * orc.get(("ModUp", lv), 0), lv
+
+
 @pytest.mark.parametrize("preset,R,dim,part,Q", [("small4", 2500, 128, 16, 3), ("ring16", 6144, 128, 16, 1),
                                                  ("ring16", 1 << 20, 128, 4, 40), ("small4", 3000, 16, 4, 2)])
 def test_deferred_division_matches_the_oracle_counts(preset, R, dim, part, Q):
