@@ -1576,12 +1576,14 @@ struct MatchRun {
                              const std::vector<std::vector<uint32_t>>& t_elems,
                              const std::vector<uint64_t*>* outs = nullptr, const uint64_t* mask = nullptr,
                              const std::vector<uint64_t>* e_flag = nullptr, const uint64_t* gmask = nullptr,
-                             uint32_t n_masks = 0) {
+                             uint32_t n_masks = 0, bool rs_coef = false) {
         // with outs, target t + its sum goes to outs[t] (every target, a zero sum for
         // those without elements); else the targets are updated in place; with mask the
         // result is multiplied by that plaintext (every target must then have elements).
         // With gmask (group-masked sums, outs required, no target added): the elements'
-        // flags e_flag mark each group's end and plaintext and the unrotated terms
+        // flags e_flag mark each group's end and plaintext and the unrotated terms; with
+        // rs_coef (level 1) the ModDown is taken in the coefficient domain with the rescale
+        // to level 0, outs then the level-0 results
         const size_t ew = ks_ext_words(c, level);
         std::vector<uint64_t*> ext_of, src, keys, gal, tg, to, off{reinterpret_cast<uint64_t*>((uintptr_t)0)};
         std::vector<uint32_t> t_off{0};
@@ -1625,9 +1627,12 @@ struct MatchRun {
             u.masks = n_masks;
             check(ks_ipsum_hoisted(c, level, T, (const uint64_t*)(doff + t0), E, (const uint64_t* const*)de,
                                    (const uint64_t* const*)ds, (const uint64_t* const*)dk, (const uint64_t*)dg,
-                                   pl.scratch, s, false, u, 0, gmask));
-            check(ks_moddown_add(c, level, T, gmask ? nullptr : dt + t0, pl.scratch, s, dto ? dto + t0 : nullptr,
-                                 mask));
+                                   pl.scratch, s, false, u, 0, gmask, rs_coef));
+            if (rs_coef)
+                check(ks_moddown_rescale_coef(c, T, pl.scratch, dto + t0, s));
+            else
+                check(ks_moddown_add(c, level, T, gmask ? nullptr : dt + t0, pl.scratch, s, dto ? dto + t0 : nullptr,
+                                     mask));
         }
     }
     // ... rotations of the extended queries (per element: extension, source, key, Galois element)
@@ -1871,6 +1876,7 @@ struct MatchRun {
             }
             const uint32_t lc = lg - 1;
             std::vector<uint64_t*> packs;
+            bool tail_done = false;            // the results written by the fused round
             if (g.fcomp) {
                 // the rotate-and-sum's last round and the compression in one round per pack:
                 // group o of a pack contributes Rot(M, -o) * sum_k Rot(acc_o, step * k - o)
@@ -1902,19 +1908,22 @@ struct MatchRun {
                             }
                         }
                     }
+                // with the coefficient-domain tail the packs' ModDown, inverse NTT and rescale
+                // are one kernel writing the level-0 results
                 const bool ct = coef_tail();
-                for (size_t p = 0; p < heads.size(); p++) {
-                    if (ct) packs.push_back(pl.packs + p * cw(lc));
-                    fouts.push_back(ct ? packs.back() : heads[p]);
-                }
+                for (uint32_t q = 0; q < Q && ct; q++)
+                    for (uint32_t k = 0; k < G; k += part)
+                        fouts.push_back(pl.result + ((size_t)q * n_out + (g0 + k) / part) * cw(0));
+                if (!ct) fouts = heads;
                 const size_t ew = ks_ext_words(c, lc);
                 for (size_t s0 = 0; s0 < srcs.size(); s0 += ksb) {
                     std::vector<uint64_t*> chunk(srcs.begin() + s0, srcs.begin() + std::min(srcs.size(), s0 + ksb));
                     modup_batch(lc, chunk, pl.ext2 + s0 * ew);
                 }
                 double_hoisted_sums(lc, srcs, e_src, e_rot, heads, t_elems, &fouts, nullptr, &e_flag, g.d_cmask_rot,
-                                    std::min(part, G));
+                                    std::min(part, G), ct);
                 mask_fused = true;
+                tail_done = ct;
             }
             std::vector<uint64_t*> mp(b.size(), const_cast<uint64_t*>(g.d_cmask));
             if (!mask_fused) mulplain_batch(lc, b, mp, b);
@@ -1962,7 +1971,8 @@ struct MatchRun {
                     heads.push_back(pl.accB + ((size_t)q * G + k) * cw(lc));
                     outs.push_back(pl.result + ((size_t)q * n_out + (g0 + k) / part) * cw(0));
                 }
-            if (coef_tail()) {
+            if (tail_done) {
+            } else if (coef_tail()) {
                 // the last rescale in the coefficient domain: an inverse NTT of both limbs of
                 // each pack, then (c_0 - [c_1]) * q_1^-1 into the result (the residues of the
                 // NTT-domain rescale and the inverse NTT of a6)

@@ -427,7 +427,13 @@ cudaError_t ks_ipsum_hoisted(const Context& c, uint32_t level, uint32_t T, const
                              const uint64_t* const* ext_of, const uint64_t* const* src_of,
                              const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch,
                              cudaStream_t s, bool ntt_out = false, KsSumInfo u = {}, uint32_t tpad = 0,
-                             const uint64_t* gmask = nullptr);
+                             const uint64_t* gmask = nullptr, bool inv_all = false);
+// ModDown of T level-1 sums in scratch (F4s with inv_all: every limb after its inverse
+// row pass) taken in the coefficient domain, with the rescale to level 0 after it:
+// out[t] [2][1][N] coefficient form = Res((x - Conv_P(x)) * P^-1), the residues of F5 + F6,
+// the inverse NTT and rescale_coef (needs rescale_coef_supported)
+cudaError_t ks_moddown_rescale_coef(const Context& c, uint32_t T, uint64_t* scratch, uint64_t* const* d_out,
+                                    cudaStream_t s);
 // ModDown and Rescale fused at the top level: e [T][2][L+1+alpha][N] (NTT form, every
 // limb; the special limbs are transformed in place) divided by q_(L-drop+1)..q_L * P
 // into out[t] (level L - drop, drop 1 or 2); scratch ks_mdr_scratch_words(c, T);

@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
     k_ks_f4s(const uint64_t* const* ext_of, const uint64_t* const* src_of, const uint64_t* const* key_of,
              const uint64_t* gal_of, const uint64_t* off, uint64_t* __restrict__ acc,
              const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L, uint32_t nb,
-             bool ntt_out, uint32_t tpad, bool by_target, const uint64_t* __restrict__ gmask) {
+             bool ntt_out, uint32_t tpad, bool by_target, const uint64_t* __restrict__ gmask, bool inv_all) {
     constexpr int LT = 2, K = 4, M = 1 << LB, TH = M >> LT, SW = sub_words<LB, LT>(), LOGN = LA + LB, N = 1 << LOGN;
     constexpr int TWN = row_tw_entries<LB, R>();
     __shared__ uint64_t sm[R * SW];
@@ -453,7 +453,9 @@ __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
     const int row = yb * R + jr;
     const size_t roff = (size_t)row * M;
     const uint32_t i0 = (uint32_t)roff + (uint32_t)(t << LT);     // last layout: words i0 .. i0 + 3
-    const bool inv = jj >= l1 && !ntt_out;      // special limbs for F5: inverse row pass
+    // special limbs for F5: inverse row pass (inv_all: every limb, for a ModDown taken in
+    // the coefficient domain)
+    const bool inv = (jj >= l1 || inv_all) && !ntt_out;
     const bool qlimb = jj < l1;
     // output slot = block's slot; with tpad, slot 0 of each run of tpad + 1 is P * the
     // run's source ciphertext (E_0 of the fused Algorithm 1: P * c on the q-limbs, 0 on
@@ -594,21 +596,28 @@ __device__ __forceinline__ void pass_barriers() {
 #pragma unroll
     for (int h = 0; h + 1 < P / LT; h++) __syncthreads();
 }
-template <int LA, int LT, int C, int GP, int MAXS>
+template <int LA, int LT, int C, int GP, int MAXS, bool RS = false>
 __host__ __device__ constexpr size_t f5_smem_words() {   // exchange and twiddles of each group, staging
-    return (size_t)GP * (sub_words<LA, LT>() * C + 2 * (1 << LA)) + (size_t)MAXS * (1 << LT) * C * ((1 << LA) >> LT);
+    return (size_t)GP * (sub_words<LA, LT>() * C + 2 * (1 << LA)) +
+           (size_t)(MAXS + (RS ? 2 : 0)) * (1 << LT) * C * ((1 << LA) >> LT);
 }
-template <int LA, int LB, int LT, int C, int GP, int MAXS>
+// the constants of F5's coefficient-domain form (RS): N^-1 and P^-1 mod q_0, q_1 and
+// q_1^-1 mod q_0 (Shoup pairs)
+struct F5Rs {
+    ulonglong2 ninv[2], pinv[2], q1inv;
+};
+template <int LA, int LB, int LT, int C, int GP, int MAXS, bool RS = false>
 __global__ void __launch_bounds__(GP * C * (1 << (LA - LT)))
     k_ks_f5(const uint64_t* __restrict__ acc, uint64_t* __restrict__ conv, const KsLevelConst* __restrict__ kc,
-            DevTables tab, uint32_t l1, uint32_t L, uint32_t ns) {
+            DevTables tab, uint32_t l1, uint32_t L, uint32_t ns, uint64_t* const* rs_out, F5Rs rc) {
     constexpr int K = 1 << LT, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN, TPC = M >> LT, NTG = C * TPC;
     constexpr int SW = sub_words<LA, LT>() * C;
     extern __shared__ uint64_t dsm[];
     const int tid = threadIdx.x, g = tid / NTG, r = tid % NTG, t = r / C, jc = r % C;
     uint64_t* xch = dsm + g * SW;                                   // the group's exchange columns
     uint64_t* st = dsm + GP * SW;                                   // staging [ns][K][NTG]
-    ulonglong2* tws = reinterpret_cast<ulonglong2*>(st + (size_t)MAXS * K * NTG) + g * M;   // the group's twiddles
+    uint64_t* fin = st + (size_t)MAXS * K * NTG;                    // RS: the two targets [2][K][NTG]
+    ulonglong2* tws = reinterpret_cast<ulonglong2*>(fin + (RS ? (size_t)2 * K * NTG : 0)) + g * M;   // the group's twiddles
     const uint32_t b = blockIdx.x / 2, comp = blockIdx.x % 2;
     const int col = blockIdx.y * C + jc;
     const uint32_t nlx = l1 + ns;
@@ -646,13 +655,14 @@ __global__ void __launch_bounds__(GP * C * (1 << (LA - LT)))
         }
         __syncthreads();        // the twiddles are restaged, and the staging read, next
     }
-    // phase 2: targets g, g + GP, ...
+    // phase 2: targets g, g + GP, ...  (RS: the target limb's own inverse column pass
+    // instead of the conversion's forward one, the ModDown in the coefficient domain)
 #pragma unroll 1
     for (uint32_t j0 = 0; j0 < l1; j0 += GP) {
         const uint32_t j = j0 + g;
         const bool a2 = j < l1;
         const uint64_t q = tab.q[a2 ? j : 0];
-        if (a2) stage_tw(tab.tw[j]);
+        if (a2) stage_tw(RS ? tab.itw[j] : tab.tw[j]);
 #pragma unroll
         for (int k = 0; k < K; k++) y[k] = 0;
         if (a2) {
@@ -665,16 +675,54 @@ __global__ void __launch_bounds__(GP * C * (1 << (LA - LT)))
         }
 #pragma unroll
         for (int k = 0; k < K; k++) y[k] = red6(y[k], q);
-        __pipeline_wait_prior(0);
-        __syncthreads();
-        if (a2) nttr::fwd_pass<LA, LT>(y, sx, tws, ColBase{}, t, q, 2 * q);
-        else pass_barriers<LA, LT>();
-        if (a2) {
-            uint64_t* o = conv + (((size_t)b * 2 + comp) * l1 + j) * N + col;
+        if constexpr (RS) {
+            uint64_t x[K];
+            if (a2) {
+                const uint64_t* src = acc + (((size_t)b * 2 + comp) * nlx + j) * N + col;
 #pragma unroll
-            for (int k = 0; k < K; k++) o[(size_t)last_idx<LA, LT>(t, k) * N2] = y[k];
+                for (int k = 0; k < K; k++) x[k] = src[(size_t)last_idx<LA, LT>(t, k) * N2];
+            }
+            __pipeline_wait_prior(0);
+            __syncthreads();
+            if (a2) nttr::inv_pass<LA, LT>(x, sx, tws, ColBase{}, t, q, 2 * q);
+            else pass_barriers<LA, LT>();
+            if (a2) {
+                // (N^-1 x - conv) * P^-1: the coefficient form of F6's output
+                const ulonglong2 ni = rc.ninv[j], pi = rc.pinv[j];
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    uint64_t yr = y[k] >= 2 * q ? y[k] - 2 * q : y[k];           // [0, 4q) -> [0, q)
+                    yr = yr >= q ? yr - q : yr;
+                    fin[(j * K + k) * NTG + r] = shoup(subm(shoup(x[k], ni.x, ni.y, q), yr, q), pi.x, pi.y, q);
+                }
+            }
+        } else {
+            __pipeline_wait_prior(0);
+            __syncthreads();
+            if (a2) nttr::fwd_pass<LA, LT>(y, sx, tws, ColBase{}, t, q, 2 * q);
+            else pass_barriers<LA, LT>();
+            if (a2) {
+                uint64_t* o = conv + (((size_t)b * 2 + comp) * l1 + j) * N + col;
+#pragma unroll
+                for (int k = 0; k < K; k++) o[(size_t)last_idx<LA, LT>(t, k) * N2] = y[k];
+            }
         }
         __syncthreads();        // the twiddles are restaged for the next targets
+    }
+    if constexpr (RS) {
+        // the rescale from level 1: (c_0 - [c_1]_centred) * q_1^-1 mod q_0 (q_1 < q_0), in
+        // natural coefficient order (the inverse pass leaves its first-phase layout)
+        if (g == 0) {
+            const uint64_t q0 = tab.q[0], q1 = tab.q[1], half = q1 >> 1;
+            uint64_t* o = rs_out[b] + (size_t)comp * N + col;
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const uint64_t r1 = fin[(K + k) * NTG + r];
+                const uint64_t lift = r1 > half ? q0 - (q1 - r1) : r1;
+                o[(size_t)first_idx<LA, LT>(t, k) * N2] =
+                    shoup(subm(fin[k * NTG + r], lift, q0), rc.q1inv.x, rc.q1inv.y, q0);
+            }
+        }
     }
 }
 
@@ -682,17 +730,18 @@ __global__ void __launch_bounds__(GP * C * (1 << (LA - LT)))
 // group a special limb for the few column blocks of a small batch (latency-bound: the
 // limbs' passes side by side), a single group looping over them for a batch that
 // already fills the GPU (no idle groups).  Shared memory set once per variant.
-template <int LA, int LB, int LT, int C, int GP, int MAXS>
+template <int LA, int LB, int LT, int C, int GP, int MAXS, bool RS = false>
 cudaError_t f5_variant(uint32_t nb2, const uint64_t* acc, uint64_t* conv, const KsLevelConst* kc,
-                       const DevTables& tab, uint32_t l1, uint32_t L, uint32_t ns, cudaStream_t s) {
+                       const DevTables& tab, uint32_t l1, uint32_t L, uint32_t ns, cudaStream_t s,
+                       uint64_t* const* rs_out = nullptr, F5Rs rc = {}) {
     constexpr int threads = GP * C * (1 << (LA - LT));
-    constexpr size_t smem = 8 * f5_smem_words<LA, LT, C, GP, MAXS>();
-    static const bool attrs = cudaFuncSetAttribute(k_ks_f5<LA, LB, LT, C, GP, MAXS>,
+    constexpr size_t smem = 8 * f5_smem_words<LA, LT, C, GP, MAXS, RS>();
+    static const bool attrs = cudaFuncSetAttribute(k_ks_f5<LA, LB, LT, C, GP, MAXS, RS>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
                               cudaSuccess;
     (void)attrs;
-    return pdl_launch(k_ks_f5<LA, LB, LT, C, GP, MAXS>, dim3(nb2, (1 << LB) / C), threads, smem, s, acc, conv, kc,
-                      tab, l1, L, ns);
+    return pdl_launch(k_ks_f5<LA, LB, LT, C, GP, MAXS, RS>, dim3(nb2, (1 << LB) / C), threads, smem, s, acc, conv, kc,
+                      tab, l1, L, ns, rs_out, rc);
 }
 constexpr uint32_t kF5SerialFrom = 16;    // ciphertext components from which F5 takes one group
 template <int LA, int LB, int LT, int C, int MAXS>
@@ -1085,7 +1134,7 @@ template <int LA, int LB, int LT, int C, int R>
 cudaError_t ks_ipsum_launch(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
                             const uint64_t* const* ext_of, const uint64_t* const* src_of,
                             const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch, bool ntt_out,
-                            KsSumInfo u, uint32_t tpad, const uint64_t* gmask, cudaStream_t s) {
+                            KsSumInfo u, uint32_t tpad, const uint64_t* gmask, bool inv_all, cudaStream_t s) {
     constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
     (void)N2;
     const KsLevelConst& K = c.h_ksc[level];
@@ -1107,7 +1156,7 @@ cudaError_t ks_ipsum_launch(const Context& c, uint32_t level, uint32_t T, const 
     const dim3 g((T + (tpad ? T / tpad : 0)) * nlx, N1 / RF), b(RF * (1 << (LB - 2)));
     auto args = [&](auto kernel) {
         return pdl_launch(kernel, g, b, 0, s, ext_of, src_of, key_of, gal_of, off, scratch, kc, c.tab, l1, c.L, c.nb,
-                          ntt_out, tpad, u.max_elems > 1, gmask);
+                          ntt_out, tpad, u.max_elems > 1, gmask, inv_all);
     };
     cudaError_t e = cudaErrorInvalidValue;
     if (gmask) {
@@ -1233,15 +1282,17 @@ cudaError_t ks_rotate_hoisted(const Context& c, uint32_t level, uint32_t E, cons
 cudaError_t ks_ipsum_hoisted(const Context& c, uint32_t level, uint32_t T, const uint64_t* off, uint32_t E,
                              const uint64_t* const* ext_of, const uint64_t* const* src_of,
                              const uint64_t* const* key_of, const uint64_t* gal_of, uint64_t* scratch,
-                             cudaStream_t s, bool ntt_out, KsSumInfo u, uint32_t tpad, const uint64_t* gmask) {
+                             cudaStream_t s, bool ntt_out, KsSumInfo u, uint32_t tpad, const uint64_t* gmask,
+                             bool inv_all) {
     if (T == 0) return cudaSuccess;
     if (gmask && (ntt_out || tpad)) return cudaErrorInvalidValue;
+    if (inv_all && ntt_out) return cudaErrorInvalidValue;
     if (c.log_n == 16)
         return ks_ipsum_launch<8, 8, 2, 2, 2>(c, level, T, off, E, ext_of, src_of, key_of, gal_of, scratch, ntt_out, u,
-                                              tpad, gmask, s);
+                                              tpad, gmask, inv_all, s);
     if (c.log_n == 12)
         return ks_ipsum_launch<6, 6, 2, 8, 8>(c, level, T, off, E, ext_of, src_of, key_of, gal_of, scratch, ntt_out, u,
-                                              tpad, gmask, s);
+                                              tpad, gmask, inv_all, s);
     return cudaErrorInvalidValue;
 }
 
@@ -1271,6 +1322,41 @@ cudaError_t ks_moddown_add(const Context& c, uint32_t level, uint32_t T, uint64_
     if (!d_tgt && !d_out) return cudaErrorInvalidValue;
     if (c.log_n == 16) return ks_moddown_add_launch<8, 8, 2, 2, 2>(c, level, T, d_tgt, d_out, scratch, mask, s);
     if (c.log_n == 12) return ks_moddown_add_launch<6, 6, 2, 8, 8>(c, level, T, d_tgt, d_out, scratch, mask, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t ks_moddown_rescale_coef(const Context& c, uint32_t T, uint64_t* scratch, uint64_t* const* d_out,
+                                    cudaStream_t s) {
+    if (T == 0) return cudaSuccess;
+    const uint32_t level = 1, l1 = 2, ns = c.alpha;
+    if (!rescale_coef_supported(c) || c.L < level || ns > (uint32_t)kMaxDigit) return cudaErrorInvalidValue;
+    F5Rs rc{};
+    for (uint32_t j = 0; j < 2; j++) {
+        const uint64_t q = c.primes[j], ni = h_invmod(c.n % q, q);
+        rc.ninv[j] = make_ulonglong2(ni, h_shoup_companion(ni, q));
+        rc.pinv[j] = c.h_ksc[level].pinv[j];
+    }
+    const uint64_t q0 = c.primes[0], q1i = h_invmod(c.primes[1] % q0, q0);
+    rc.q1inv = make_ulonglong2(q1i, h_shoup_companion(q1i, q0));
+    const uint32_t nlx = l1 + ns, nb2 = T * 2;
+    const double N = (double)c.n, bf_c = 16.0 * (N / 2) * (c.log_n / 2);
+    // reads every limb of each sum, writes one limb of each component
+    ProfScope ps(BM_KERNEL_MODDOWN, s, 8.0 * N * nb2 * (nlx + 1),
+                 bf_c * nb2 * (ns + l1) + kShoupMul * N * nb2 * (ns + (double)l1 * ns + 2.0 * l1 + 1));
+    if (c.log_n == 16) {
+        if (nb2 >= kF5SerialFrom)
+            return f5_variant<8, 8, 2, 2, 1, kMaxDigit, true>(nb2, scratch, nullptr, c.d_ksc + level, c.tab, l1, c.L,
+                                                             ns, s, d_out, rc);
+        return f5_variant<8, 8, 2, 2, kMaxDigit, kMaxDigit, true>(nb2, scratch, nullptr, c.d_ksc + level, c.tab, l1,
+                                                                 c.L, ns, s, d_out, rc);
+    }
+    if (c.log_n == 12) {
+        if (nb2 >= kF5SerialFrom)
+            return f5_variant<6, 6, 2, 8, 1, kMaxDigit, true>(nb2, scratch, nullptr, c.d_ksc + level, c.tab, l1, c.L,
+                                                             ns, s, d_out, rc);
+        return f5_variant<6, 6, 2, 8, kMaxDigit, kMaxDigit, true>(nb2, scratch, nullptr, c.d_ksc + level, c.tab, l1,
+                                                                 c.L, ns, s, d_out, rc);
+    }
     return cudaErrorInvalidValue;
 }
 
