@@ -48,6 +48,10 @@ def parse():
                     help="write the DRAM-traffic record of --workload (its default forms) from this ncu CSV "
                          "(dram__bytes_read.sum, dram__bytes_write.sum per launch) and exit")
     ap.add_argument("--traffic-command", default="", help="--write-traffic: the ncu command the CSV came from")
+    ap.add_argument("--traffic-plain", default="",
+                    help="--write-traffic: the bench line of the same command without ncu (algorithmic bytes)")
+    ap.add_argument("--traffic-stands-for", default="",
+                    help="--write-traffic: comma-separated larger workloads the record is scaled to")
     ap.add_argument("--cpu-extrapolate", action="store_true",
                     help="the oracle on the batched configurations, sampled and scaled (a labelled extrapolation)")
     ap.add_argument("--cpu-sample-ids", type=int, default=32768,
@@ -394,22 +398,35 @@ def alu_peak_tops():
     return SM_COUNT * INT32_MUL_PER_CLK_PER_SM * mhz * 1e6 / 1e12
 
 
-def measured_traffic(kernel_class, workload, config):
+def measured_traffic(kernel_class, workload, config, alg_bytes_per_launch=None):
     """DRAM bytes per launch of a kernel class from the committed ncu record of the
     workload, or None when there is none for this schedule, or when the kernel sources
-    have changed since the counters were taken."""
+    have changed since the counters were taken.  A workload too large to capture under
+    ncu is covered by the record of a smaller case of the same schedule that names it in
+    `stands_for`: its DRAM bytes per launch scaled by the ratio of algorithmic bytes per
+    launch (traffic taken to grow in proportion to the units a launch processes).
+    Returns (bytes, source) or (None, None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
             doc = json.load(f)
-        for rec in doc["records"]:
-            if rec["workload"] != workload or any(rec["config"].get(k) != config.get(k) for k in rec["config"]):
+        own = [r for r in doc["records"] if r["workload"] == workload]
+        proxy = [r for r in doc["records"] if workload in r.get("stands_for", [])]
+        for rec in own + proxy:
+            if any(rec["config"].get(k) != config.get(k) for k in rec["config"]):
                 continue
             if _sources_sha1(rec["sources"]) != rec["sources_sha1"]:
-                return None
-            return float(rec["dram_bytes_per_launch"][kernel_class])
+                return None, None
+            b = float(rec["dram_bytes_per_launch"][kernel_class])
+            if rec["workload"] == workload:
+                return b, "ncu capture of this workload"
+            ref = rec.get("alg_bytes_per_launch", {}).get(kernel_class)
+            if not ref or not alg_bytes_per_launch:
+                return None, None
+            return b * alg_bytes_per_launch / ref, ("ncu capture of %s scaled by algorithmic bytes per launch"
+                                                    % rec["workload"])
     except (OSError, KeyError, ValueError, TypeError):
         pass
-    return None
+    return None, None
 
 
 class L2Flush:
@@ -445,11 +462,13 @@ def _sources_sha1(srcs):
     return h.hexdigest()
 
 
-def write_traffic_record(csv_path, workload, config, command):
+def write_traffic_record(csv_path, workload, config, command, plain_json=None, stands_for=None):
     """Adds (or replaces) the record of `workload` in profiles/roofline_traffic.json from
     an ncu CSV with dram__bytes_read.sum and dram__bytes_write.sum per launch: DRAM
     bytes per launch of each kernel class, keyed by the workload, its schedule config
-    and the SHA-1 of the kernel sources."""
+    and the SHA-1 of the kernel sources.  With `plain_json` (the bench line of the same
+    command run without ncu) the record keeps the algorithmic bytes per launch of each
+    class, so that it can stand for the larger workloads listed in `stands_for`."""
     import csv
     rows = list(csv.reader(open(csv_path)))
     hi = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
@@ -472,10 +491,17 @@ def write_traffic_record(csv_path, workload, config, command):
         recs = [r for r in doc.get("records", []) if r.get("workload") != workload]
     except (OSError, ValueError):
         recs = []
-    recs.append({"workload": workload, "config": config,
-                 "dram_bytes_per_launch": {k: sum(v) / len(v) for k, v in sorted(cls.items())},
-                 "launches": {k: len(v) for k, v in sorted(cls.items())}, "command": command,
-                 "sources": TRAFFIC_SOURCES, "sources_sha1": _sources_sha1(TRAFFIC_SOURCES)})
+    rec = {"workload": workload, "config": config,
+           "dram_bytes_per_launch": {k: sum(v) / len(v) for k, v in sorted(cls.items())},
+           "launches": {k: len(v) for k, v in sorted(cls.items())}, "command": command,
+           "sources": TRAFFIC_SOURCES, "sources_sha1": _sources_sha1(TRAFFIC_SOURCES)}
+    if plain_json:
+        line = json.loads([x for x in open(plain_json) if x.startswith("{")][-1])
+        rec["alg_bytes_per_launch"] = {k: v["alg_GB_per_step"] * 1e9 / v["launches"]
+                                       for k, v in sorted(line["kernel_breakdown"].items()) if k in cls}
+    if stands_for:
+        rec["stands_for"] = list(stands_for)
+    recs.append(rec)
     with open(path, "w") as f:
         json.dump({"records": recs}, f, indent=1)
         f.write("\n")
@@ -846,7 +872,9 @@ def main():
         exp = resolve_expansion(args.expansion, W.n_ids, W.dim, part, args.packing == "complex",
                                 (1 << (16 if W.preset == "ring16" else 12)) // 2, args.gallery == "encrypted")
         cfg = {"part": part, "packing": args.packing, "gallery": args.gallery, "expansion": exp, "tail": args.tail}
-        return write_traffic_record(args.write_traffic, W.name, cfg, args.traffic_command)
+        return write_traffic_record(args.write_traffic, W.name, cfg, args.traffic_command,
+                                    args.traffic_plain or None,
+                                    [w for w in args.traffic_stands_for.split(",") if w] or None)
     if args.serve:
         return run_serving(args)
     if args.sweep_part:
@@ -958,8 +986,10 @@ def main():
     peak_hbm, peak_src = load_peaks()
     traffic_cfg = {"part": part, "packing": args.packing, "gallery": args.gallery, "expansion": args.expansion,
                    "tail": args.tail}
-    roofline = roofline_of(dom, ms_l, by_l, ops_l, peak_hbm, peak_src, alu_peak_tops(),
-                           measured_traffic(dom, W.name, traffic_cfg))
+    traffic, traffic_src = measured_traffic(dom, W.name, traffic_cfg, by_l / max(n_l, 1))
+    roofline = roofline_of(dom, ms_l, by_l, ops_l, peak_hbm, peak_src, alu_peak_tops(), traffic)
+    if traffic_src:
+        roofline["traffic_source"] = traffic_src
     roofline.update({"launches_per_step": n_l / args.steps, "avg_launch_us": 1e3 * ms_l / max(n_l, 1),
                      "alg_bytes_per_launch": by_l / max(n_l, 1), "alg_mul32_per_launch": ops_l / max(n_l, 1),
                      "share_of_kernel_time": ms_l / max(sum(v[1] for v in prof.values()), 1e-12)})

@@ -81,3 +81,41 @@ def test_roofline_bound_is_the_binding_roof():
     assert r["bound"] == "alu" and r["unit"] == "Tmul32/s" and abs(r["frac"] - 15.0 / 20.137) < 1e-12
     r = bench.roofline_of("copy", 1.0, 5e9, 0, 6669.5, "measured", 20.137, None)
     assert r["bound"] == "hbm" and "alu_view" not in r
+
+
+def test_traffic_record_own_proxy_and_stale(tmp_path, monkeypatch):
+    """The line's `traffic`: the workload's own ncu record; for a workload only a
+    smaller case's record stands for, that record's DRAM bytes per launch scaled by
+    the ratio of algorithmic bytes per launch; nothing for another schedule, and
+    nothing once the kernel sources differ from those the counters were taken on."""
+    import json
+    import bench
+    (tmp_path / "profiles").mkdir()
+    src = tmp_path / "k.cu"
+    src.write_text("kernel v1")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "TRAFFIC_SOURCES", ["k.cu"])
+    csv_path = tmp_path / "l.csv"
+    csv_path.write_text('"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"\n'
+                        '"0","void k_ks_f4s<8>()","dram__bytes_read.sum","Mbyte","80"\n'
+                        '"0","void k_ks_f4s<8>()","dram__bytes_write.sum","Mbyte","20"\n'
+                        '"1","void k_ks_f4s<8>()","dram__bytes_read.sum","Mbyte","200"\n'
+                        '"1","void k_ks_f4s<8>()","dram__bytes_write.sum","byte","0"\n'
+                        '"2","void k_mac<1, 2>()","dram__bytes_read.sum","Gbyte","1"\n'
+                        '"2","void k_mac<1, 2>()","dram__bytes_write.sum","byte","0"\n')
+    plain = tmp_path / "plain.json"
+    plain.write_text(json.dumps({"kernel_breakdown": {"ks_ip": {"launches": 2, "alg_GB_per_step": 0.3},
+                                                      "mac": {"launches": 1, "alg_GB_per_step": 2.0}}}) + "\n")
+    cfg = {"part": 16, "tail": "fused"}
+    bench.write_traffic_record(str(csv_path), "small", cfg, "ncu ...", str(plain), ["big"])
+    rec = json.load(open(tmp_path / "profiles" / "roofline_traffic.json"))["records"][0]
+    assert rec["dram_bytes_per_launch"]["ks_ip"] == pytest.approx(150e6)
+    assert rec["alg_bytes_per_launch"]["ks_ip"] == pytest.approx(150e6)
+    assert bench.measured_traffic("ks_ip", "small", cfg) == (pytest.approx(150e6), "ncu capture of this workload")
+    b, why = bench.measured_traffic("ks_ip", "big", cfg, 600e6)
+    assert b == pytest.approx(600e6) and "scaled" in why
+    assert bench.measured_traffic("mac", "big", cfg, 4e9)[0] == pytest.approx(2e9)
+    assert bench.measured_traffic("ks_ip", "big", {"part": 4, "tail": "fused"}, 600e6) == (None, None)
+    assert bench.measured_traffic("ks_ip", "other", cfg, 600e6) == (None, None)
+    src.write_text("kernel v2")
+    assert bench.measured_traffic("ks_ip", "small", cfg) == (None, None)
