@@ -356,13 +356,22 @@ bm_status bm_match(bm_context* ctx, const bm_eval_keys* evk, const bm_gallery* g
  * event after the call).  bm_result_export and bm_decrypt_scores wait for it
  * themselves, and bm_result_destroy may be called at any time (the free is ordered
  * after the copy).  Host ciphertexts are copied from their page-locked host memory
- * while the call's work runs: keep them alive until the stream has passed it.  The
- * same plans, errors and results as bm_match. */
+ * while the call's work runs: keep them alive until the stream has passed it.  For
+ * plans of up to 256 MiB of queries (64 top-level ring-2^16 queries) that copy runs on
+ * the plan's own stream into one of two staging buffers, waiting only for the call
+ * before the previous one to have moved its queries out: a call issued while the
+ * previous call's match still runs copies its queries during that match, so a client
+ * that enqueues the next match before reading back the last result keeps the copies
+ * off the critical path.  Calls that share a plan (same gallery, key set and
+ * n_queries) must be issued on one stream, or serialised by the caller: the plan's
+ * buffers are reused by every call.  The same plans, errors and results as bm_match. */
 bm_status bm_match_async(bm_context* ctx, const bm_eval_keys* evk, const bm_gallery* gallery,
                          bm_ciphertext* const* queries, uint32_t n_queries, void* stream, bm_result** out);
 bm_status bm_result_info(const bm_result* r, uint32_t* n_queries, uint32_t* n_out,
                          uint32_t* packed);
-/* Score ciphertexts of one query: [n_out][2][N] coefficient form at level 0. */
+/* Score ciphertexts of one query: [n_out][2][N] coefficient form at level 0.  Waits
+ * for the result's match, then copies on the context's own non-blocking stream: work
+ * enqueued after that match (the next bm_match_async) is not waited for. */
 bm_status bm_result_export(const bm_result* r, uint32_t query_index, uint64_t* out,
                            size_t capacity);
 /* Frees the result; call it before destroying the result's context. */

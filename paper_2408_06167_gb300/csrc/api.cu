@@ -1325,9 +1325,22 @@ struct Plan {
     cudaGraphExec_t exec = nullptr;
     ProfSink counts;                       // launches per replay
     size_t bytes = 0;                      // device memory held
+    // host queries: copied into one of two staging buffers on the plan's own copy stream
+    // (so that the copy of a call overlaps the match of the call before it), then moved
+    // into qin on the caller's stream ahead of the graph
+    uint64_t* stg[2] = {nullptr, nullptr};
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+    uint32_t slot = 0;
     ~Plan() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamSynchronize(cs);
+        for (int k = 0; k < 2; k++) {
+            if (ev_ready[k]) cudaEventDestroy(ev_ready[k]);
+            if (ev_free[k]) cudaEventDestroy(ev_free[k]);
+        }
+        if (cs) cudaStreamDestroy(cs);
         for (void* p : bufs) cudaFree(p);
     }
     bool alloc(uint64_t*& p, size_t words) {
@@ -1666,14 +1679,22 @@ struct MatchRun {
         // a0: queries into the NTT domain; the hoisted Algorithm 1 first keeps the
         // coefficient form of each query's c1 for its basis extension (no inverse NTT)
         const size_t lw = c.n * (size_t)(c.L + 1);
+        // a0 and Algorithm 1's extension in two launches (ks_a0_modup) when every query is in
+        // one chunk and the NTT of the batch takes the default shape; else the copy of c1,
+        // the NTT and the extension from the copy
+        const bool front = g.tiled && g.hoisted && g.n_in > 1 && pl.qe == Q &&
+                           c.ntt_shape[ntt_bucket(Q * pl.ncts * 2 * (c.L + 1))] == 0;
         if (g.tiled && g.hoisted) {
             record(BM_OP_COPY, 0, Q);
-            if (pl.arena.live)
+            if (pl.arena.live && !front)
                 check(cudaMemcpy2DAsync(pl.qc1, lw * 8, pl.qin + lw, cw(c.L) * 8, lw * 8, Q, cudaMemcpyDeviceToDevice,
                                         s));
         }
         record(BM_OP_NTT, 0, (size_t)Q * pl.ncts * 2 * (c.L + 1));
-        if (pl.arena.live) check(ntt_forward(c, packed(c, pl.qin, Q * pl.ncts * 2, c.L + 1), s));
+        if (pl.arena.live) {
+            if (front) check(ks_a0_modup(c, Q, pl.qin, pl.ext, s));
+            else check(ntt_forward(c, packed(c, pl.qin, Q * pl.ncts * 2, c.L + 1), s));
+        }
         // Algorithm 1, hoisted form: T_i = Res(sum_j Rot(ct, j*part) * mask_((i-j) mod N_in)),
         // the N_in - 1 rotations of each query sharing one basis extension; queries in chunks of pl.qe
         if (g.tiled && g.hoisted && g.fused) {
@@ -1690,7 +1711,8 @@ struct MatchRun {
                 uint64_t* E0 = pl.R + (size_t)pl.qe * (n_in - 1) * xw;       // after the rotated sums
                 std::vector<uint64_t*> qs, ext_of, src, keys, gal, off{reinterpret_cast<uint64_t*>((uintptr_t)0)}, R, outs;
                 for (uint32_t q = 0; q < nq; q++) qs.push_back(pl.qin + (size_t)(qb + q) * cw(c.L));
-                modup_coef_batch(c.L, qs, pl.qc1 + (size_t)qb * lw, pl.ext);
+                if (front) record(BM_OP_MODUP, c.L, qs.size());          // written by ks_a0_modup
+                else modup_coef_batch(c.L, qs, pl.qc1 + (size_t)qb * lw, pl.ext);
                 for (uint32_t q = 0; q < nq; q++)
                     for (uint32_t j = 1; j < n_in; j++) {
                         ext_of.push_back(pl.ext + (size_t)q * ew);
@@ -1751,7 +1773,8 @@ struct MatchRun {
                 const uint32_t nq = std::min(pl.qe, Q - qb);
                 std::vector<uint64_t*> qs, ext_of, src, keys, gal, out, R, o0, o1;
                 for (uint32_t q = 0; q < nq; q++) qs.push_back(pl.qin + (size_t)(qb + q) * cw(c.L));
-                if (n_in > 1) modup_coef_batch(c.L, qs, pl.qc1 + (size_t)qb * lw, pl.ext);
+                if (front) record(BM_OP_MODUP, c.L, qs.size());           // written by ks_a0_modup
+                else if (n_in > 1) modup_coef_batch(c.L, qs, pl.qc1 + (size_t)qb * lw, pl.ext);
                 for (uint32_t q = 0; q < nq; q++)
                     for (uint32_t j = 1; j < n_in; j++) {
                         ext_of.push_back(pl.ext + (size_t)q * ew);
@@ -1817,9 +1840,16 @@ struct MatchRun {
             // encrypted gallery: one relinearisation of the summed tensor products,
             // (d0, d1, d2) -> (d0 + KS(d2)_0, d1 + KS(d2)_1) with t = (d0, d2), a = (0, d1)
             if (g.encrypted) rotate_batch(lg, 0, t, a, &a, true);
+            // the fused rotate-and-sum + compression extends the group sums first of all (one
+            // round: no hoisted round before it), so the deferred division can hand it the
+            // extension of its quotients from the same kernels (ks_moddown_rescale_modup)
+            uint32_t bs0, gs0;
+            bsgs_split(part, g.dhoist, bs0, gs0);
+            const bool mdru = g.deferred && g.fcomp && gs0 == 1 && lg == c.L - 1 && ks_mdru_supported(c);
             if (g.deferred) {
                 // each (query, group) sum divided once by q_(L-1) q_L P (accA: [Q][G][2][nlx][N])
                 auto db = pl.arena.list(b);
+                const size_t ewc = ks_ext_words(c, lg - 1);
                 for (uint32_t o0 = 0; o0 < (uint32_t)b.size(); o0 += ksb) {
                     const uint32_t T = std::min<uint32_t>(ksb, (uint32_t)b.size() - o0);
                     record(BM_OP_MODDOWN, c.L, T);
@@ -1827,7 +1857,11 @@ struct MatchRun {
                         need_scratch(ks_mdr_scratch_words(c, T));
                         continue;
                     }
-                    check(ks_moddown_rescale(c, T, pl.accA + (size_t)o0 * xw, db + o0, pl.scratch, s, 2));
+                    if (mdru)
+                        check(ks_moddown_rescale_modup(c, T, pl.accA + (size_t)o0 * xw, db + o0,
+                                                       pl.ext2 + (size_t)o0 * ewc, pl.scratch, s));
+                    else
+                        check(ks_moddown_rescale(c, T, pl.accA + (size_t)o0 * xw, db + o0, pl.scratch, s, 2));
                 }
             } else {
                 rescale_batch(lg, a, b);
@@ -1918,7 +1952,9 @@ struct MatchRun {
                 const size_t ew = ks_ext_words(c, lc);
                 for (size_t s0 = 0; s0 < srcs.size(); s0 += ksb) {
                     std::vector<uint64_t*> chunk(srcs.begin() + s0, srcs.begin() + std::min(srcs.size(), s0 + ksb));
-                    modup_batch(lc, chunk, pl.ext2 + s0 * ew);
+                    // (with mdru the division above wrote these extensions: srcs are b, in order)
+                    if (mdru) record(BM_OP_MODUP, lc, chunk.size());
+                    else modup_batch(lc, chunk, pl.ext2 + s0 * ew);
                 }
                 double_hoisted_sums(lc, srcs, e_src, e_rot, heads, t_elems, &fouts, nullptr, &e_flag, g.d_cmask_rot,
                                     std::min(part, G), ct);
@@ -2038,9 +2074,16 @@ struct BufSpec {
     uint64_t** field;
     size_t words;
 };
+// host queries of a plan whose input is at most this many words (256 MiB: 64 top-level
+// ring-2^16 queries) are staged through two buffers of that size (plan_run); larger
+// batches are copied into qin directly
+constexpr size_t kStageWords = (size_t)32 << 20;
 static std::vector<BufSpec> plan_buffers(const Context& c, const SchedView& g, Plan& pl) {
     const uint32_t Q = pl.Q, lg = g.level;
     std::vector<BufSpec> b{{&pl.qin, pl.qin_words}, {&pl.result, pl.result_words}};
+    const size_t stage = pl.qin_words <= kStageWords ? pl.qin_words : 0;
+    b.push_back({&pl.stg[0], stage});
+    b.push_back({&pl.stg[1], stage});
     if (g.tiled) {
         // the fused Algorithm 1 keeps its sums on Q_L u P
         const size_t sw = g.fused ? (size_t)2 * (c.L + 1 + c.alpha) * c.n : ct_words(c, c.L);
@@ -2145,11 +2188,40 @@ bm_status plan_run(Context& c, const Gallery& g, const EvalKeys& ek, Plan* pl, c
     if (nq == 0 || nq > pl->Q) return fail(BM_E_ARG, "batch larger than the plan");
     // a0: the queries' coefficient-form limbs into the plan's input buffer (padded with the last)
     const size_t per_q = (size_t)pl->ncts * ct_words(c, c.L);
-    for (uint32_t i = 0; i < pl->Q; i++) {
-        const Ciphertext& ct = *queries[std::min(i, nq - 1)];
-        uint64_t* dst = pl->qin + (size_t)i * per_q;
-        if (ct.d_coef) BM_CUDA_TRY(cudaMemcpyAsync(dst, ct.d_coef, per_q * 8, cudaMemcpyDeviceToDevice, s));
-        else BM_CUDA_TRY(cudaMemcpyAsync(dst, ct.host.data(), per_q * 8, cudaMemcpyHostToDevice, s));
+    bool from_host = false;
+    for (uint32_t i = 0; i < nq; i++) from_host = from_host || !queries[i]->d_coef;
+    if (!from_host || pl->qin_words > kStageWords) {
+        // device queries (or a batch too large to stage): straight into qin on s
+        for (uint32_t i = 0; i < pl->Q; i++) {
+            const Ciphertext& ct = *queries[std::min(i, nq - 1)];
+            uint64_t* dst = pl->qin + (size_t)i * per_q;
+            if (ct.d_coef) BM_CUDA_TRY(cudaMemcpyAsync(dst, ct.d_coef, per_q * 8, cudaMemcpyDeviceToDevice, s));
+            else BM_CUDA_TRY(cudaMemcpyAsync(dst, ct.host.data(), per_q * 8, cudaMemcpyHostToDevice, s));
+        }
+    } else {
+        // host queries: H2D into a staging buffer on the copy stream, which waits only until
+        // the move out of that buffer two calls ago has run (so this copy overlaps the
+        // previous call's match), then one device-to-device move into qin on s
+        if (!pl->cs) {
+            BM_CUDA_TRY(cudaStreamCreateWithFlags(&pl->cs, cudaStreamNonBlocking));
+            for (int k = 0; k < 2; k++) {
+                BM_CUDA_TRY(cudaEventCreateWithFlags(&pl->ev_ready[k], cudaEventDisableTiming));
+                BM_CUDA_TRY(cudaEventCreateWithFlags(&pl->ev_free[k], cudaEventDisableTiming));
+            }
+        }
+        const uint32_t k = pl->slot;
+        pl->slot ^= 1;
+        BM_CUDA_TRY(cudaStreamWaitEvent(pl->cs, pl->ev_free[k], 0));
+        for (uint32_t i = 0; i < pl->Q; i++) {
+            const Ciphertext& ct = *queries[std::min(i, nq - 1)];
+            uint64_t* dst = pl->stg[k] + (size_t)i * per_q;
+            if (ct.d_coef) BM_CUDA_TRY(cudaMemcpyAsync(dst, ct.d_coef, per_q * 8, cudaMemcpyDeviceToDevice, pl->cs));
+            else BM_CUDA_TRY(cudaMemcpyAsync(dst, ct.host.data(), per_q * 8, cudaMemcpyHostToDevice, pl->cs));
+        }
+        BM_CUDA_TRY(cudaEventRecord(pl->ev_ready[k], pl->cs));
+        BM_CUDA_TRY(cudaStreamWaitEvent(s, pl->ev_ready[k], 0));
+        BM_CUDA_TRY(cudaMemcpyAsync(pl->qin, pl->stg[k], pl->Q * per_q * 8, cudaMemcpyDeviceToDevice, s));
+        BM_CUDA_TRY(cudaEventRecord(pl->ev_free[k], s));
     }
     if (prof_timing()) {
         // per-launch timing: run the same launches eagerly so each gets its event pair
@@ -2275,7 +2347,11 @@ bm_status bm_result_export(const bm_result* r, uint32_t query_index, uint64_t* o
     if (capacity < words) return fail(BM_E_ARG, "capacity too small");
     BM_CUDA_TRY(cudaSetDevice(c.device));
     if (res.ready) BM_CUDA_TRY(cudaEventSynchronize(res.ready));
-    BM_CUDA_TRY(cudaMemcpy(out, res.d_data + (size_t)query_index * words, words * 8, cudaMemcpyDeviceToHost));
+    // on the context's non-blocking stream: the copy does not wait for work the caller
+    // has enqueued since (a later match), as one on the legacy stream would
+    BM_CUDA_TRY(cudaMemcpyAsync(out, res.d_data + (size_t)query_index * words, words * 8, cudaMemcpyDeviceToHost,
+                                c.stream));
+    BM_CUDA_TRY(cudaStreamSynchronize(c.stream));
     return BM_OK;
 }
 

@@ -442,6 +442,18 @@ bool ks_mdr_supported(const Context& c, uint32_t drop = 1);
 size_t ks_mdr_scratch_words(const Context& c, uint32_t T);
 cudaError_t ks_moddown_rescale(const Context& c, uint32_t T, uint64_t* e, uint64_t* const* d_out, uint64_t* scratch,
                                cudaStream_t s, uint32_t drop = 1);
+// The deferred division (drop 2) of T sums e [T][2][L+1+alpha][N] (NTT form, every limb
+// transformed in place) into out[t] at level L - 2, with the quotient's hoisted ModUp at
+// that level written to ext + t * ks_ext_words(c, L - 2) -- the residues of
+// ks_moddown_rescale(drop 2) followed by ks_modup_hoisted, in three launches; scratch
+// ks_mdr_scratch_words(c, T); needs ks_mdru_supported(c)
+bool ks_mdru_supported(const Context& c);
+// a0 and Algorithm 1's extension together: Q top-level queries qin [Q][2][L+1][N] from
+// coefficient to NTT form in place, and the extension of their c1 into ext (the layout
+// and residues of ks_modup_hoisted_coef), in two launches
+cudaError_t ks_a0_modup(const Context& c, uint32_t Q, uint64_t* qin, uint64_t* ext, cudaStream_t s);
+cudaError_t ks_moddown_rescale_modup(const Context& c, uint32_t T, uint64_t* e, uint64_t* const* d_out,
+                                     uint64_t* ext, uint64_t* scratch, cudaStream_t s);
 cudaError_t ks_moddown_add(const Context& c, uint32_t level, uint32_t T, uint64_t* const* d_tgt, uint64_t* scratch,
                            cudaStream_t s, uint64_t* const* d_out = nullptr, const uint64_t* mask = nullptr);
 // rescale in three fused kernels (rings 2^12 and 2^16)

@@ -16,6 +16,7 @@
 // X0, X1, ext, acc and conv (the same words as the staged kernels).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdlib>
 
 #include "bm_internal.h"
@@ -121,12 +122,15 @@ __device__ __forceinline__ void col_fwd_store(uint64_t (&y)[1 << LT], uint64_t* 
 }
 
 // ---------------------------------------------------------------------------
-// F3: grid (B * nd, N2 / C).  X1 holds c1 in coefficient form.
+// F3: grid (B * nd * ts_n, N2 / C).  X1 holds c1 in coefficient form.  The digit's
+// target limbs (every extended limb but its own) are dealt round-robin to ts_n blocks
+// of the same columns, each staging the digit's source limbs itself: ts_n > 1 fills
+// the GPU when B * nd column blocks alone would leave SMs idle (one query).
 // ---------------------------------------------------------------------------
 template <int LA, int LB, int LT, int C>
 __global__ void __launch_bounds__(C * (1 << (LA - LT)))
     k_ks_f3(const uint64_t* __restrict__ X1, uint64_t* __restrict__ ext, const KsLevelConst* __restrict__ kc,
-            DevTables tab, uint32_t l1, uint32_t L, uint32_t kinv) {
+            DevTables tab, uint32_t l1, uint32_t L, uint32_t kinv, uint32_t ts_n) {
     constexpr int K = 1 << LT, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN;
     extern __shared__ uint64_t dsm[];
     uint64_t* sm = dsm;                                   // exchange tiles
@@ -137,7 +141,8 @@ __global__ void __launch_bounds__(C * (1 << (LA - LT)))
     constexpr int NT = C * (M >> LT);
     const int tid = threadIdx.x, t = tid / C, jc = tid % C;
     const uint32_t nd = kc->nd, nlx = kc->nlx;
-    const uint32_t b = blockIdx.x / nd, d = blockIdx.x % nd;
+    const uint32_t ts = blockIdx.x % ts_n, bd = blockIdx.x / ts_n;
+    const uint32_t b = bd / nd, d = bd % nd;
     const int col = blockIdx.y * C + jc;
     const uint32_t ds = kc->dsz[d], d0 = kc->dstart[d];
     pdl_wait();
@@ -155,9 +160,11 @@ __global__ void __launch_bounds__(C * (1 << (LA - LT)))
             st[(i * K + k) * NT + tid] = shoup(x, h.x, h.y, qi);
         }
     }
+    uint32_t ti = 0;                                          // index among the digit's targets
 #pragma unroll 1
     for (uint32_t jj = 0; jj < nlx; jj++) {
         if (jj >= d0 && jj < d0 + ds) continue;               // the digit's own limbs come from F1
+        if (ti++ % ts_n != ts) continue;                      // another block's target
         const int pi = ext_prime(jj, l1, L);
         const uint64_t tq = tab.q[pi];
         stage_col_twiddles<LA, C * (M >> LT)>(tws, tab.tw[pi]);
@@ -265,6 +272,126 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 4)
         for (int k = 0; k < K; k++) o[first_idx<LB, LT>(t, k)] = v[k];
         __syncthreads();
     }
+}
+
+// ---------------------------------------------------------------------------
+// The queries' forward NTT (a0) and the extension of their c1 for the hoisted Algorithm 1
+// in two launches, from the coefficient form in qin ([Q][2][l1][N], qstride words a query):
+// F0c, grid (Q * l1 + Q * nd * ts_n, N2 / C): blocks below Q * l1 the forward column pass
+// of a c0 limb in place; the others, per (query, digit, slice), the digit's targets --
+// every extended limb, its own limbs as they are and the others by the fast base
+// conversion of F3 -- each after its forward column pass into ext (qin's c1 is only
+// read here, so no copy of it is needed).  F0r, grid (Q * l1 + Q * nd * nlx, N1 / R):
+// the forward row pass of the c0 limbs in place and of every limb of ext in place, each
+// own limb of a digit written to qin's c1 as well.  The residues of a0's NTT, F3 and F3r.
+// ---------------------------------------------------------------------------
+template <int LA, int LB, int LT, int C>
+__global__ void __launch_bounds__(C * (1 << (LA - LT)))
+    k_ks_f0c(uint64_t* __restrict__ qin, uint64_t qstride, uint64_t* __restrict__ ext,
+             const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L, uint32_t n0, uint32_t ts_n) {
+    constexpr int K = 1 << LT, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN;
+    extern __shared__ uint64_t dsm[];
+    uint64_t* sm = dsm;
+    uint64_t* st = sm + sub_words<LA, LT>() * C;
+    ulonglong2* tws = (ulonglong2*)(st + kMaxDigit * M * C);
+    constexpr int NT = C * (M >> LT);
+    const int tid = threadIdx.x, t = tid / C, jc = tid % C;
+    const int col = blockIdx.y * C + jc;
+    if (blockIdx.x < n0) {
+        // a0, c0 limb j of query b
+        const uint32_t b = blockIdx.x / l1, j = blockIdx.x % l1;
+        uint64_t* a = qin + (size_t)b * qstride + (size_t)j * N + col;
+        const uint64_t q = tab.q[j];
+        stage_col_twiddles<LA, NT>(tws, tab.tw[j]);
+        pdl_wait();
+        uint64_t v[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) v[k] = a[(size_t)first_idx<LA, LT>(t, k) * N2];
+        tw_wait();
+        nttr::fwd_pass<LA, LT>(v, SubMem{sm + jc, C}, tws, ColBase{}, t, q, 2 * q);
+#pragma unroll
+        for (int k = 0; k < K; k++) a[(size_t)last_idx<LA, LT>(t, k) * N2] = v[k];
+        return;
+    }
+    const uint32_t nd = kc->nd, nlx = kc->nlx;
+    const uint32_t rb = blockIdx.x - n0, ts = rb % ts_n, bd = rb / ts_n;
+    const uint32_t b = bd / nd, d = bd % nd;
+    const uint32_t ds = kc->dsz[d], d0 = kc->dstart[d];
+    const uint64_t* X1 = qin + (size_t)b * qstride + (size_t)l1 * N;      // c1, coefficient form
+    pdl_wait();
+#pragma unroll 1
+    for (uint32_t i = 0; i < ds; i++) {
+        const uint64_t qi = tab.q[d0 + i];
+        const ulonglong2 h = kc->up_hinv[d][i];
+        const uint64_t* src = X1 + (size_t)(d0 + i) * N + col;
+#pragma unroll
+        for (int k = 0; k < K; k++)
+            st[(i * K + k) * NT + tid] = shoup(src[(size_t)first_idx<LA, LT>(t, k) * N2], h.x, h.y, qi);
+    }
+#pragma unroll 1
+    for (uint32_t jj = ts; jj < nlx; jj += ts_n) {
+        const int pi = ext_prime(jj, l1, L);
+        const uint64_t tq = tab.q[pi];
+        stage_col_twiddles<LA, NT>(tws, tab.tw[pi]);
+        uint64_t y[K];
+        if (jj >= d0 && jj < d0 + ds) {
+            const uint64_t* src = X1 + (size_t)jj * N + col;             // own limb: c1 itself
+#pragma unroll
+            for (int k = 0; k < K; k++) y[k] = src[(size_t)first_idx<LA, LT>(t, k) * N2];
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; k++) y[k] = 0;
+#pragma unroll 1
+            for (uint32_t i = 0; i < ds; i++) {
+                const ulonglong2 h = kc->up_hat[d][i][jj];
+#pragma unroll
+                for (int k = 0; k < K; k++) y[k] += shoup_lazy(st[(i * K + k) * NT + tid], h.x, h.y, tq);
+            }
+#pragma unroll
+            for (int k = 0; k < K; k++) y[k] = red6(y[k], tq);
+        }
+        tw_wait();
+        col_fwd_store<LA, LB, LT, C>(y, sm, tws, t, jc, tq, ext + (((size_t)b * nd + d) * nlx + jj) * N + col);
+        __syncthreads();
+    }
+}
+
+template <int LA, int LB, int LT, int R>
+__global__ void __launch_bounds__(R * (1 << (LB - LT)))
+    k_ks_f0r(uint64_t* __restrict__ qin, uint64_t qstride, uint64_t* __restrict__ ext,
+             const KsLevelConst* __restrict__ kc, DevTables tab, uint32_t l1, uint32_t L, uint32_t n0) {
+    constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>(), N = 1 << (LA + LB);
+    __shared__ uint64_t sm[R * S];
+    __shared__ ulonglong2 tws[row_tw_entries<LB, R>()];
+    const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
+    const size_t roff = (size_t)(blockIdx.y * R + jr) * M;
+    uint64_t *e, *also = nullptr;
+    int pi;
+    if (blockIdx.x < n0) {
+        const uint32_t b = blockIdx.x / l1, j = blockIdx.x % l1;
+        e = qin + (size_t)b * qstride + (size_t)j * N + roff;
+        pi = (int)j;
+    } else {
+        const uint32_t nd = kc->nd, nlx = kc->nlx, rb = blockIdx.x - n0;
+        const uint32_t jj = rb % nlx, d = (rb / nlx) % nd, b = rb / (nd * nlx);
+        e = ext + (size_t)rb * N + roff;
+        pi = ext_prime(jj, l1, L);
+        if (jj >= kc->dstart[d] && jj < kc->dstart[d] + kc->dsz[d])
+            also = qin + (size_t)b * qstride + ((size_t)l1 + jj) * N + roff;      // qin's c1 limb jj
+    }
+    const uint64_t q = tab.q[pi], q2 = 2 * q;
+    stage_row_twiddles<LA, LB, R, R * TH>(tws, tab.tw[pi], blockIdx.y * R);
+    pdl_wait();
+    uint64_t v[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = e[first_idx<LB, LT>(t, k)];
+    tw_wait();
+    nttr::fwd_pass<LB, LT>(v, SubMem{sm + jr * S, 1}, tws, RowBase<R>{jr}, t, q, q2);
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = nttr::reduce4(v[k], q, q2);
+    pdl_trigger();
+    nttr::store_last<LB, LT>(v, e, t);
+    if (also) nttr::store_last<LB, LT>(v, also, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -427,6 +554,17 @@ __device__ __forceinline__ void place4(uint64_t (&o)[4], const W4& g, uint32_t s
 // gets P times the run's source ciphertext: E_0, E_1..E_(N_in-1) of a query of the fused
 // Algorithm 1 in one launch.
 constexpr uint32_t kFoldElems = 12;
+
+// F3's target slices: every target limb of a digit in a block of its own while the
+// batch's column blocks (B * nd * column blocks) would not give each SM four, else one
+// block for all of a digit's targets (the source limbs staged once)
+constexpr uint32_t kF3FillBlocks = 4 * 152;
+uint32_t f3_slices(const KsLevelConst& K, uint32_t B, uint32_t col_blocks) {
+    if ((uint64_t)B * K.nd * col_blocks >= kF3FillBlocks) return 1;
+    uint32_t t = 1;
+    for (uint32_t d = 0; d < K.nd; d++) t = std::max(t, K.nlx - K.dsz[d]);
+    return t;
+}
 template <int LA, int LB, int R, int ND, int MINB, bool GM>
 __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
     k_ks_f4s(const uint64_t* const* ext_of, const uint64_t* const* src_of, const uint64_t* const* key_of,
@@ -596,28 +734,40 @@ __device__ __forceinline__ void pass_barriers() {
 #pragma unroll
     for (int h = 0; h + 1 < P / LT; h++) __syncthreads();
 }
-template <int LA, int LT, int C, int GP, int MAXS, bool RS = false>
+template <int LA, int LT, int C, int GP, int MAXS, bool CD = false>
 __host__ __device__ constexpr size_t f5_smem_words() {   // exchange and twiddles of each group, staging
     return (size_t)GP * (sub_words<LA, LT>() * C + 2 * (1 << LA)) +
-           (size_t)(MAXS + (RS ? 2 : 0)) * (1 << LT) * C * ((1 << LA) >> LT);
+           (size_t)(MAXS + (CD ? 2 : 0)) * (1 << LT) * C * ((1 << LA) >> LT);
 }
-// the constants of F5's coefficient-domain form (RS): N^-1 and P^-1 mod q_0, q_1 and
-// q_1^-1 mod q_0 (Shoup pairs)
+// the constants of F5's coefficient-domain forms (RS, MU): N^-1 and the divisor's inverse
+// (P^-1, or S^-1 for the deferred division) mod q_0, q_1, and q_1^-1 mod q_0 (Shoup pairs)
 struct F5Rs {
     ulonglong2 ninv[2], pinv[2], q1inv;
 };
-template <int LA, int LB, int LT, int C, int GP, int MAXS, bool RS = false>
+// MU: the quotient's ModUp for the next level's hoisted key switching, taken in the same
+// kernel: y [B][2][l1][N] receives the quotient's limbs after their forward column pass,
+// ext (stride ext_words a ciphertext) the conversion of its c1 to the level's other
+// extended limbs after theirs (the level has one digit, its l1 q-limbs; kcu its constants)
+struct F5Mu {
+    uint64_t* y;
+    uint64_t* ext;
+    const KsLevelConst* kcu;
+    uint64_t ext_words;
+    uint32_t Lc;                 // the context's top level (the special primes follow it)
+};
+template <int LA, int LB, int LT, int C, int GP, int MAXS, bool RS = false, bool MU = false>
 __global__ void __launch_bounds__(GP * C * (1 << (LA - LT)))
     k_ks_f5(const uint64_t* __restrict__ acc, uint64_t* __restrict__ conv, const KsLevelConst* __restrict__ kc,
-            DevTables tab, uint32_t l1, uint32_t L, uint32_t ns, uint64_t* const* rs_out, F5Rs rc) {
+            DevTables tab, uint32_t l1, uint32_t L, uint32_t ns, uint64_t* const* rs_out, F5Rs rc, F5Mu mu) {
+    constexpr bool CD = RS || MU;     // the ModDown in the coefficient domain
     constexpr int K = 1 << LT, M = 1 << LA, N2 = 1 << LB, LOGN = LA + LB, N = 1 << LOGN, TPC = M >> LT, NTG = C * TPC;
     constexpr int SW = sub_words<LA, LT>() * C;
     extern __shared__ uint64_t dsm[];
     const int tid = threadIdx.x, g = tid / NTG, r = tid % NTG, t = r / C, jc = r % C;
     uint64_t* xch = dsm + g * SW;                                   // the group's exchange columns
     uint64_t* st = dsm + GP * SW;                                   // staging [ns][K][NTG]
-    uint64_t* fin = st + (size_t)MAXS * K * NTG;                    // RS: the two targets [2][K][NTG]
-    ulonglong2* tws = reinterpret_cast<ulonglong2*>(fin + (RS ? (size_t)2 * K * NTG : 0)) + g * M;   // the group's twiddles
+    uint64_t* fin = st + (size_t)MAXS * K * NTG;                    // CD: the two targets [2][K][NTG]
+    ulonglong2* tws = reinterpret_cast<ulonglong2*>(fin + (CD ? (size_t)2 * K * NTG : 0)) + g * M;   // the group's twiddles
     const uint32_t b = blockIdx.x / 2, comp = blockIdx.x % 2;
     const int col = blockIdx.y * C + jc;
     const uint32_t nlx = l1 + ns;
@@ -655,14 +805,14 @@ __global__ void __launch_bounds__(GP * C * (1 << (LA - LT)))
         }
         __syncthreads();        // the twiddles are restaged, and the staging read, next
     }
-    // phase 2: targets g, g + GP, ...  (RS: the target limb's own inverse column pass
+    // phase 2: targets g, g + GP, ...  (CD: the target limb's own inverse column pass
     // instead of the conversion's forward one, the ModDown in the coefficient domain)
 #pragma unroll 1
     for (uint32_t j0 = 0; j0 < l1; j0 += GP) {
         const uint32_t j = j0 + g;
         const bool a2 = j < l1;
         const uint64_t q = tab.q[a2 ? j : 0];
-        if (a2) stage_tw(RS ? tab.itw[j] : tab.tw[j]);
+        if (a2) stage_tw(CD ? tab.itw[j] : tab.tw[j]);
 #pragma unroll
         for (int k = 0; k < K; k++) y[k] = 0;
         if (a2) {
@@ -675,7 +825,7 @@ __global__ void __launch_bounds__(GP * C * (1 << (LA - LT)))
         }
 #pragma unroll
         for (int k = 0; k < K; k++) y[k] = red6(y[k], q);
-        if constexpr (RS) {
+        if constexpr (CD) {
             uint64_t x[K];
             if (a2) {
                 const uint64_t* src = acc + (((size_t)b * 2 + comp) * nlx + j) * N + col;
@@ -709,6 +859,51 @@ __global__ void __launch_bounds__(GP * C * (1 << (LA - LT)))
         }
         __syncthreads();        // the twiddles are restaged for the next targets
     }
+    if constexpr (MU) {
+        // phase 3, jobs g, g + GP, ...: the forward column pass of each quotient limb (both
+        // components) and, for c1, its conversion to each other extended limb of its level
+        // (the fast base conversion of the hoisted ModUp, from the coefficient form held in
+        // fin) and that limb's forward column pass
+        const uint32_t nlu = mu.kcu->nlx, nj = l1 + (comp ? nlu - l1 : 0);
+#pragma unroll 1
+        for (uint32_t o0 = 0; o0 < nj; o0 += GP) {
+            const uint32_t o = o0 + g;
+            const bool a3 = o < nj;
+            const int pi = o < l1 ? (int)o : (int)mu.Lc + 1 + (int)(o - l1);
+            const uint64_t q = tab.q[a3 ? pi : 0];
+            if (a3) stage_tw(tab.tw[pi]);
+            if (a3) {
+                if (o < l1) {
+#pragma unroll
+                    for (int k = 0; k < K; k++) y[k] = fin[(o * K + k) * NTG + r];
+                } else {
+#pragma unroll
+                    for (int k = 0; k < K; k++) y[k] = 0;
+#pragma unroll 1
+                    for (uint32_t i = 0; i < l1; i++) {
+                        const ulonglong2 hi = mu.kcu->up_hinv[0][i], hh = mu.kcu->up_hat[0][i][o];
+                        const uint64_t qi = tab.q[i];
+#pragma unroll
+                        for (int k = 0; k < K; k++)
+                            y[k] += shoup_lazy(shoup(fin[(i * K + k) * NTG + r], hi.x, hi.y, qi), hh.x, hh.y, q);
+                    }
+#pragma unroll
+                    for (int k = 0; k < K; k++) y[k] = red6(y[k], q);
+                }
+            }
+            __pipeline_wait_prior(0);
+            __syncthreads();
+            if (a3) nttr::fwd_pass<LA, LT>(y, sx, tws, ColBase{}, t, q, 2 * q);
+            else pass_barriers<LA, LT>();
+            if (a3) {
+                uint64_t* dst = o < l1 ? mu.y + (((size_t)b * 2 + comp) * l1 + o) * N + col
+                                       : mu.ext + (size_t)b * mu.ext_words + (size_t)o * N + col;
+#pragma unroll
+                for (int k = 0; k < K; k++) dst[(size_t)last_idx<LA, LT>(t, k) * N2] = y[k];
+            }
+            __syncthreads();    // the twiddles are restaged for the next jobs
+        }
+    }
     if constexpr (RS) {
         // the rescale from level 1: (c_0 - [c_1]_centred) * q_1^-1 mod q_0 (q_1 < q_0), in
         // natural coefficient order (the inverse pass leaves its first-phase layout)
@@ -730,18 +925,18 @@ __global__ void __launch_bounds__(GP * C * (1 << (LA - LT)))
 // group a special limb for the few column blocks of a small batch (latency-bound: the
 // limbs' passes side by side), a single group looping over them for a batch that
 // already fills the GPU (no idle groups).  Shared memory set once per variant.
-template <int LA, int LB, int LT, int C, int GP, int MAXS, bool RS = false>
+template <int LA, int LB, int LT, int C, int GP, int MAXS, bool RS = false, bool MU = false>
 cudaError_t f5_variant(uint32_t nb2, const uint64_t* acc, uint64_t* conv, const KsLevelConst* kc,
                        const DevTables& tab, uint32_t l1, uint32_t L, uint32_t ns, cudaStream_t s,
-                       uint64_t* const* rs_out = nullptr, F5Rs rc = {}) {
+                       uint64_t* const* rs_out = nullptr, F5Rs rc = {}, F5Mu mu = {}) {
     constexpr int threads = GP * C * (1 << (LA - LT));
-    constexpr size_t smem = 8 * f5_smem_words<LA, LT, C, GP, MAXS, RS>();
-    static const bool attrs = cudaFuncSetAttribute(k_ks_f5<LA, LB, LT, C, GP, MAXS, RS>,
+    constexpr size_t smem = 8 * f5_smem_words<LA, LT, C, GP, MAXS, RS || MU>();
+    static const bool attrs = cudaFuncSetAttribute(k_ks_f5<LA, LB, LT, C, GP, MAXS, RS, MU>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
                               cudaSuccess;
     (void)attrs;
-    return pdl_launch(k_ks_f5<LA, LB, LT, C, GP, MAXS, RS>, dim3(nb2, (1 << LB) / C), threads, smem, s, acc, conv, kc,
-                      tab, l1, L, ns, rs_out, rc);
+    return pdl_launch(k_ks_f5<LA, LB, LT, C, GP, MAXS, RS, MU>, dim3(nb2, (1 << LB) / C), threads, smem, s, acc, conv,
+                      kc, tab, l1, L, ns, rs_out, rc, mu);
 }
 constexpr uint32_t kF5SerialFrom = 16;    // ciphertext components from which F5 takes one group
 template <int LA, int LB, int LT, int C, int MAXS>
@@ -810,6 +1005,43 @@ __global__ void __launch_bounds__(R * (1 << (LB - LT)), LT <= 2 ? 8 : 3)
 #pragma unroll
         for (int k = 0; k < K; k++) o[first_idx<LB, LT>(t, k)] = v[k];
     }
+}
+
+// ---------------------------------------------------------------------------
+// F6u: grid (T * (2 l1 + nu), N1 / R), after F5's MU form.  Jobs of ciphertext b: the
+// forward row pass of each quotient limb y [b][comp][j] into out[b] (the level-l1-1
+// ciphertext in NTT form, the F6 of a plain division) and, for c1, into ext's digit
+// limbs as well (the extension's own limbs are the ciphertext's NTT form); then the
+// forward row pass of each converted limb of ext in place (as F3r).
+// ---------------------------------------------------------------------------
+template <int LA, int LB, int LT, int R>
+__global__ void __launch_bounds__(R * (1 << (LB - LT)))
+    k_ks_f6u(const uint64_t* __restrict__ Y, uint64_t* const* out, uint64_t* __restrict__ ext, uint64_t ext_words,
+             DevTables tab, uint32_t l1, uint32_t nlu, uint32_t Lc) {
+    constexpr int K = 1 << LT, M = 1 << LB, TH = M >> LT, S = sub_words<LB, LT>(), N = 1 << (LA + LB);
+    __shared__ uint64_t sm[R * S];
+    __shared__ ulonglong2 tws[row_tw_entries<LB, R>()];
+    const int tid = threadIdx.x, jr = tid / TH, t = tid % TH;
+    const uint32_t jobs = 2 * l1 + (nlu - l1), b = blockIdx.x / jobs, job = blockIdx.x % jobs;
+    const bool quot = job < 2 * l1;
+    const uint32_t comp = quot ? job / l1 : 1, j = quot ? job % l1 : l1 + (job - 2 * l1);
+    const int pi = j < l1 ? (int)j : (int)Lc + 1 + (int)(j - l1);
+    const uint64_t q = tab.q[pi], q2 = 2 * q;
+    const size_t roff = (size_t)(blockIdx.y * R + jr) * M;
+    uint64_t* e = ext + (size_t)b * ext_words + (size_t)j * N + roff;
+    const uint64_t* src = quot ? Y + (((size_t)b * 2 + comp) * l1 + j) * N + roff : e;
+    stage_row_twiddles<LA, LB, R, R * TH>(tws, tab.tw[pi], blockIdx.y * R);
+    pdl_wait();
+    uint64_t v[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = src[first_idx<LB, LT>(t, k)];
+    tw_wait();
+    nttr::fwd_pass<LB, LT>(v, SubMem{sm + jr * S, 1}, tws, RowBase<R>{jr}, t, q, q2);
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = nttr::reduce4(v[k], q, q2);
+    pdl_trigger();
+    if (quot) nttr::store_last<LB, LT>(v, out[b] + ((size_t)comp * l1 + j) * N + roff, t);
+    if (!quot || comp == 1) nttr::store_last<LB, LT>(v, e, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -986,7 +1218,9 @@ cudaError_t ks_fused_launch(const Context& c, const uint64_t* key, uint64_t galo
         ProfScope ps(BM_KERNEL_MODUP, s, lw * B * (gathers + targets),
                      bf_c * B * targets + kShoupMul * N * B * (l1 + gathers));
         const uint32_t kinv = (uint32_t)h_invmod_pow2(galois, 2ull * N);
-        pdl_launch(k_ks_f3<LA, LB, LT, C>, dim3(B * nd, N2 / C), tc, col_smem, s, X1, ext, kc, c.tab, l1, c.L, kinv);
+        const uint32_t ts_n = f3_slices(K, B, N2 / C);
+        pdl_launch(k_ks_f3<LA, LB, LT, C>, dim3(B * nd * ts_n, N2 / C), tc, col_smem, s, X1, ext, kc, c.tab, l1, c.L,
+                   kinv, ts_n);
     }
     {
         ProfScope ps(BM_KERNEL_KS_IP, s, lw * nlx * ((double)B * nd + 2.0 * nd + 2.0 * B),
@@ -1047,7 +1281,9 @@ cudaError_t ks_modup_launch(const Context& c, uint32_t level, uint32_t B, uint64
     {
         ProfScope ps(BM_KERNEL_MODUP, s, lw * B * (gathers + targets),
                      bf_c * B * targets + kShoupMul * N * B * (l1 + gathers));
-        pdl_launch(k_ks_f3<LA, LB, LT, C>, dim3(B * nd, N2 / C), tc, col_smem, s, X1, ext, kc, c.tab, l1, c.L, 1u);
+        const uint32_t ts_n = f3_slices(K, B, N2 / C);
+        pdl_launch(k_ks_f3<LA, LB, LT, C>, dim3(B * nd * ts_n, N2 / C), tc, col_smem, s, X1, ext, kc, c.tab, l1, c.L,
+                   1u, ts_n);
     }
     {
         ProfScope ps(BM_KERNEL_MODUP, s, lw * B * targets * 2, bf_r * B * targets);
@@ -1083,7 +1319,9 @@ cudaError_t ks_modup_coef_launch(const Context& c, uint32_t level, uint32_t B, u
     {
         ProfScope ps(BM_KERNEL_MODUP, s, lw * B * (gathers + targets),
                      bf_c * B * targets + kShoupMul * N * B * (l1 + gathers));
-        pdl_launch(k_ks_f3<LA, LB, LT, C>, dim3(B * nd, N2 / C), tc, col_smem, s, coef, ext, kc, c.tab, l1, c.L, 1u);
+        const uint32_t ts_n = f3_slices(K, B, N2 / C);
+        pdl_launch(k_ks_f3<LA, LB, LT, C>, dim3(B * nd * ts_n, N2 / C), tc, col_smem, s, coef, ext, kc, c.tab, l1, c.L,
+                   1u, ts_n);
     }
     {
         ProfScope ps(BM_KERNEL_MODUP, s, lw * B * (targets * 2 + 2 * l1), bf_r * B * targets);
@@ -1237,6 +1475,91 @@ cudaError_t ks_mdr_launch(const Context& c, uint32_t T, uint64_t* e, uint64_t* c
     return cudaGetLastError();
 }
 
+// The deferred division (drop 2: S = q_(L-1) q_L P) and the quotient's hoisted ModUp at
+// its level in three launches: the inverse row pass of every limb of the T sums (in
+// place), F5 in its MU form (the division in the coefficient domain, the quotient's
+// forward column passes and its c1's conversion to the level's special primes) and
+// F6u (the row passes).  out[t] receives the quotient in NTT form -- the residues of
+// ks_moddown_rescale's F5 + F6 -- and ext + t * ks_ext_words(c, L - 2) its extension --
+// those of F1, the inverse column pass, F3 and F3r on out[t].  Scratch: y of T.
+template <int LA, int LB, int LT, int C, int R>
+cudaError_t ks_mdru_launch(const Context& c, uint32_t T, uint64_t* e, uint64_t* const* d_out, uint64_t* ext,
+                           uint64_t* scratch, cudaStream_t s) {
+    constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
+    constexpr uint32_t drop = 2;
+    const uint32_t nlx = c.L + 1 + c.alpha, ns = c.alpha + drop, l1 = c.L + 1 - drop, lc = l1 - 1;
+    const KsLevelConst& KU = c.h_ksc[lc];
+    const uint32_t nlu = KU.nlx;
+    const int tr = R * (1 << (LB - LT));
+    const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;
+    {
+        LimbBatch sb{e, T * 2, (uint64_t)nlx * N, 0, nlx, 0};
+        for (uint32_t k = 0; k < nlx; k++) sb.set(k, (uint8_t)k);
+        ProfScope ps(BM_KERNEL_MODDOWN, s, 2 * lw * T * 2 * nlx, bf_r * T * 2 * nlx);
+        pdl_launch(nttr::k_row_inv<LA, LB, LT, R>, dim3(T * 2 * nlx, N1 / R), tr, 0, s, sb, c.tab);
+    }
+    {
+        F5Rs rc{};
+        for (uint32_t j = 0; j < l1; j++) {
+            const uint64_t q = c.primes[j], ni = h_invmod(c.n % q, q);
+            rc.ninv[j] = make_ulonglong2(ni, h_shoup_companion(ni, q));
+            rc.pinv[j] = c.h_ksc_mdr[drop - 1].pinv[j];
+        }
+        F5Mu mu{scratch, ext, c.d_ksc + lc, ks_ext_words(c, lc), c.L};
+        // reads every limb of the sums; writes the quotient and the converted limbs
+        ProfScope ps(BM_KERNEL_MODDOWN, s, lw * T * (2 * nlx + 2 * l1 + (nlu - l1)),
+                     bf_c * T * (2 * (ns + l1) + 2 * l1 + (nlu - l1)) +
+                         kShoupMul * N * T * (2 * (ns + (double)l1 * ns + 2.0 * l1) + l1 * (1.0 + (nlu - l1))));
+        f5_variant<LA, LB, LT, C, MAXSP, MAXSP, false, true>(T * 2, e, nullptr, c.d_ksc_mdr + (drop - 1), c.tab, l1,
+                                                            l1 - 1, ns, s, nullptr, rc, mu);
+    }
+    {
+        const uint32_t jobs = 2 * l1 + (nlu - l1);
+        ProfScope ps(BM_KERNEL_KS_COMBINE, s, lw * T * (2 * jobs + l1), bf_r * T * jobs);
+        pdl_launch(k_ks_f6u<LA, LB, LT, R>, dim3(T * jobs, N1 / R), tr, 0, s, (const uint64_t*)scratch, d_out, ext,
+                   (uint64_t)ks_ext_words(c, lc), c.tab, l1, nlu, c.L);
+    }
+    return cudaGetLastError();
+}
+
+// a0 and the extension of the top-level queries' c1 (F0c, F0r): qin [Q][2][L+1][N] in
+// coefficient form -> NTT form in place; ext [Q][nd][nlx][N] as ks_modup_hoisted_coef writes it
+template <int LA, int LB, int LT, int C, int R>
+cudaError_t ks_a0_modup_launch(const Context& c, uint32_t Q, uint64_t* qin, uint64_t* ext, cudaStream_t s) {
+    constexpr int N1 = 1 << LA, N2 = 1 << LB, N = N1 * N2;
+    const uint32_t level = c.L, l1 = level + 1;
+    const KsLevelConst& K = c.h_ksc[level];
+    const uint32_t nd = K.nd, nlx = K.nlx, n0 = Q * l1;
+    const KsLevelConst* kc = c.d_ksc + level;
+    const uint64_t qstride = (uint64_t)ct_words(c, level);
+    const int tr = R * (1 << (LB - LT)), tc = C * (1 << (LA - LT));
+    const size_t col_smem = 8 * col_smem_words<LA, LT, C>();
+    static bool attrs = [&] {
+        cudaFuncSetAttribute(k_ks_f0c<LA, LB, LT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem);
+        return true;
+    }();
+    (void)attrs;
+    // every target of a digit in a block of its own while the column blocks alone would
+    // not fill the GPU (as F3)
+    const uint32_t ts_n = (uint64_t)Q * nd * (N2 / C) >= kF3FillBlocks ? 1 : nlx;
+    const double lw = 8.0 * N, bf_r = 16.0 * (N / 2) * LB, bf_c = 16.0 * (N / 2) * LA;
+    uint32_t gathers = 0;
+    for (uint32_t d = 0; d < nd; d++) gathers += K.dsz[d] * (nlx - K.dsz[d]);
+    {
+        // c0's column pass; c1 read once per digit slice, every extended limb written
+        ProfScope ps(BM_KERNEL_MODUP, s, lw * Q * (2.0 * l1 + l1 + nd * nlx),
+                     bf_c * Q * (l1 + (double)nd * nlx) + kShoupMul * N * Q * (l1 + gathers));
+        pdl_launch(k_ks_f0c<LA, LB, LT, C>, dim3(n0 + Q * nd * ts_n, N2 / C), tc, col_smem, s, qin, qstride, ext, kc,
+                   c.tab, l1, c.L, n0, ts_n);
+    }
+    {
+        ProfScope ps(BM_KERNEL_NTT, s, lw * Q * (2.0 * l1 + 2.0 * nd * nlx + l1), bf_r * Q * (l1 + (double)nd * nlx));
+        pdl_launch(k_ks_f0r<LA, LB, LT, R>, dim3(n0 + Q * nd * nlx, N1 / R), tr, 0, s, qin, qstride, ext, kc, c.tab,
+                   l1, c.L, n0);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t ks_modup_scratch_words(const Context& c, uint32_t level, uint32_t B) {
@@ -1313,6 +1636,31 @@ cudaError_t ks_moddown_rescale(const Context& c, uint32_t T, uint64_t* e, uint64
     if (c.log_n == 12)
         return drop == 1 ? ks_mdr_launch<6, 6, 2, 8, 8, BM_MAX_P>(c, T, e, d_out, scratch, drop, s)
                          : ks_mdr_launch<6, 6, 2, 8, 8, MAXSP>(c, T, e, d_out, scratch, drop, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t ks_a0_modup(const Context& c, uint32_t Q, uint64_t* qin, uint64_t* ext, cudaStream_t s) {
+    if (Q == 0) return cudaSuccess;
+    if (c.log_n == 16) return ks_a0_modup_launch<8, 8, 2, 2, 2>(c, Q, qin, ext, s);
+    if (c.log_n == 12) return ks_a0_modup_launch<6, 6, 2, 8, 8>(c, Q, qin, ext, s);
+    return cudaErrorInvalidValue;
+}
+
+bool ks_mdru_supported(const Context& c) {
+    // the quotient's level has one digit, its q-limbs, and at most MAXSP extended limbs
+    // besides them (F5's thread groups take the conversions side by side)
+    if (!ks_mdr_supported(c, 2) || c.L < 2) return false;
+    const KsLevelConst& K = c.h_ksc[c.L - 2];
+    return K.nd == 1 && K.dstart[0] == 0 && K.dsz[0] == c.L - 1 && K.nlx - K.dsz[0] <= (uint32_t)MAXSP &&
+           K.dsz[0] <= 2;
+}
+
+cudaError_t ks_moddown_rescale_modup(const Context& c, uint32_t T, uint64_t* e, uint64_t* const* d_out,
+                                     uint64_t* ext, uint64_t* scratch, cudaStream_t s) {
+    if (T == 0) return cudaSuccess;
+    if (!ks_mdru_supported(c)) return cudaErrorInvalidValue;
+    if (c.log_n == 16) return ks_mdru_launch<8, 8, 2, 2, 2>(c, T, e, d_out, ext, scratch, s);
+    if (c.log_n == 12) return ks_mdru_launch<6, 6, 2, 8, 8>(c, T, e, d_out, ext, scratch, s);
     return cudaErrorInvalidValue;
 }
 

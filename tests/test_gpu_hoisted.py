@@ -143,6 +143,7 @@ def test_hoisted_schedule_is_bit_exact(name, m, s, R, nq, tail_only, double):
     ("small4", 16, 8, 2100, 1, "hoisted"),     # one round of 8 terms a group
     ("small4", 16, 1, 2100, 1, "hoisted"),     # parts of 1: each pack one group, its masked term alone
     ("ring16", 16, 4, 20000, 1, "fused"),      # ring 2^16, one pack of 3 groups split over two thread groups
+    ("ring16", 128, 16, 5000, 2, "deferred"),  # ring 2^16, 3 groups of 2 queries: the division hands the extension on
 ])
 def test_fused_compression_is_bit_exact(name, m, s, R, nq, expansion):
     """The rotate-and-sum's last round and the compression as one round per pack

@@ -84,11 +84,12 @@ def test_launches_are_the_oracle_schedule_operations(preset, R, dim, part, Q):
 
 
 def test_plan_bytes_are_its_buffers():
-    # face gallery, one query: query ct (L = 3), Algorithm-1 outputs at 3 and 2, accumulators
-    # at 2 and 1 for 3 groups, one score ct, key-switch scratch for 8 ciphertexts at level 2
+    # face gallery, one query: query ct (L = 3) and its two staging copies, Algorithm-1 outputs
+    # at 3 and 2, accumulators at 2 and 1 for 3 groups, one score ct, key-switch scratch for 8
+    # ciphertexts at level 2
     ops, nbytes = bm.bm_plan_estimate("ring16", 6144, 128, 16, 1)
     limb = 8 << 16
-    buffers = (8 + 8 * 8 + 8 * 6 + 3 * 6 + 3 * 4 + 2) * limb
+    buffers = (3 * 8 + 8 * 8 + 8 * 6 + 3 * 6 + 3 * 4 + 2) * limb
     ks_scratch = 8 * (2 * 3 + 2 * 5 + 2 * 5 + 2 * 3) * limb
     pointers = nbytes - buffers - ks_scratch
     assert 0 < pointers < 4096, pointers
