@@ -448,7 +448,8 @@ class L2Flush:
 # can name as dominant; NTT passes also run inside other classes and are left out)
 TRAFFIC_CLASSES = {"ks_ip": ("k_ks_f4s<", "k_ks_f4h<", "k_ks_f4<"),
                    "mac": ("k_mac<", "k_mac_ct<", "k_mac_circ<", "k_mac_circ_ntt<"),
-                   "moddown": ("k_ks_f5<",), "modup": ("k_ks_f3<", "k_ks_f3r<"), "ks_combine": ("k_ks_f6<",)}
+                   "moddown": ("k_ks_f5<",), "modup": ("k_ks_f3<", "k_ks_f3r<", "k_ks_f0c<"),
+                   "ks_combine": ("k_ks_f6<", "k_ks_f6u<")}
 TRAFFIC_SOURCES = ["paper_2408_06167_gb300/csrc/kernels.cu", "paper_2408_06167_gb300/csrc/ks_fused.cu",
                    "paper_2408_06167_gb300/csrc/ntt_reg.cuh", "paper_2408_06167_gb300/csrc/bm_math.cuh"]
 
