@@ -20,7 +20,7 @@ NVCC = os.environ.get("NVCC", "nvcc")
 
 
 def _flags():
-    return ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fopenmp",
+    return ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fopenmp", "-Xcompiler", "-D_GLIBCXX_ASSERTIONS",
             "-I", os.path.join(ROOT, "include"), "-I", SRC] + ARCH
 
 

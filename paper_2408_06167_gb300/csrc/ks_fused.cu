@@ -565,7 +565,7 @@ uint32_t f3_slices(const KsLevelConst& K, uint32_t B, uint32_t col_blocks) {
     for (uint32_t d = 0; d < K.nd; d++) t = std::max(t, K.nlx - K.dsz[d]);
     return t;
 }
-template <int LA, int LB, int R, int ND, int MINB, bool GM>
+template <int LA, int LB, int R, int ND, int MINB, bool GM, bool PF = false>
 __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
     k_ks_f4s(const uint64_t* const* ext_of, const uint64_t* const* src_of, const uint64_t* const* key_of,
              const uint64_t* gal_of, const uint64_t* off, uint64_t* __restrict__ acc,
@@ -620,6 +620,89 @@ __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
     Acc128 a0[K], a1[K];
     uint64_t cs[K] = {0, 0, 0, 0};
     uint64_t pk0[K] = {0, 0, 0, 0}, pk1[K] = {0, 0, 0, 0};   // GM: the target's sum of masked groups
+    if constexpr (PF) {
+        // one digit, group-masked sums, elements software-pipelined: the key words and the
+        // extension gather of element e + 1 (keys read from DRAM the first time a launch
+        // uses them) are in flight while element e gathers its c0 words and runs its products
+        static_assert(GM && ND == 1, "the pipelined loop takes one digit and group masks");
+        uint64_t gwn = kGalIdentity;
+        Perm4 pmn{i0, 0};
+        W4 k0n{}, k1n{}, xn{};
+        // element f's words: the unrotated source's c1 for an identity element (its c0 is
+        // read with the products), else the Galois gather of its extension and its key
+        auto issue = [&](uint32_t f) {
+            gwn = gal_of[f];
+            if (gwn & kGalIdentity) {
+                pmn = Perm4{i0, 0};
+                if (qlimb) xn = ld256(src_of[f] + ((size_t)l1 + jj) * N + i0);
+            } else {
+                pmn = perm4(i0, LOGN, (uint32_t)gwn);
+                xn = ld256(ext_of[f] + (size_t)jj * N + pmn.gb);
+                const uint64_t* key = key_of[f] + (size_t)pi * N + i0;
+                k0n = ld256(key);
+                k1n = ld256(key + (size_t)nb * N);
+            }
+        };
+        if (e0 < e1) issue(e0);
+        uint32_t fold = kFoldElems;                     // elements to the next reduction
+#pragma unroll 1
+        for (uint32_t e = e0; e < e1; e++) {
+            const uint64_t gw = gwn;
+            const W4 k0 = k0n, k1 = k1n, xw = xn;
+            const bool ident = (gw & kGalIdentity) != 0;
+            const Perm4 pm4 = pmn;
+            W4 cw;
+            if (qlimb) cw = ld256(src_of[e] + (size_t)jj * N + pm4.gb);
+            if (e + 1 < e1) issue(e + 1);
+            if (ident) {
+                // the unrotated source: P * c0 joins the c0 sum, P * c1 the second component
+                if (qlimb) {
+#pragma unroll
+                    for (int k = 0; k < K; k++) {
+                        cs[k] += cw.w[k];
+                        mad128(a1[k], xw.w[k], pm);
+                    }
+                }
+            } else {
+                uint64_t x[K];
+                place4(x, xw, pm4.sel);
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    mad128(a0[k], x[k], k0.w[k]);
+                    mad128(a1[k], x[k], k1.w[k]);
+                }
+                if (qlimb) {
+                    uint64_t c[K];
+                    place4(c, cw, pm4.sel);
+#pragma unroll
+                    for (int k = 0; k < K; k++) cs[k] += c[k];
+                }
+            }
+            if (--fold == 0) {
+                fold = kFoldElems;
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    reduce_hi(a0[k], q, rsh);
+                    reduce_hi(a1[k], q, rsh);
+                    const uint64_t r = cs[k] - mulhi64(cs[k], rsh) * q;   // [0, 2q)
+                    cs[k] = r >= q ? r - q : r;
+                }
+            }
+            if (gw & kGalGroupEnd) {
+                const uint32_t mi = (uint32_t)((gw >> kGalMaskShift) & kGalMaskBits);
+                const W4 mw = ld256(gmask + ((size_t)mi * nlx + jj) * N + i0);
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    if (qlimb) mad128(a0[k], cs[k], pm);
+                    pk0[k] = addm(pk0[k], mont(redc_wide(a0[k], q, qn, rsh), mw.w[k], q, qn), q);
+                    pk1[k] = addm(pk1[k], mont(redc_wide(a1[k], q, qn, rsh), mw.w[k], q, qn), q);
+                    a0[k] = Acc128{};
+                    a1[k] = Acc128{};
+                    cs[k] = 0;
+                }
+            }
+        }
+    } else {
 #pragma unroll 1
     for (uint32_t e = e0; e < e1; e++) {
         const uint64_t gw = gal_of[e];
@@ -693,6 +776,7 @@ __global__ void __launch_bounds__(R * (1 << (LB - 2)), MINB)
                 cs[k] = 0;
             }
         }
+    }
     }
     if (!GM && qlimb) {
 #pragma unroll
@@ -1397,7 +1481,11 @@ cudaError_t ks_ipsum_launch(const Context& c, uint32_t level, uint32_t T, const 
                           ntt_out, tpad, u.max_elems > 1, gmask, inv_all);
     };
     cudaError_t e = cudaErrorInvalidValue;
-    if (gmask) {
+    // one digit, group masks: the software-pipelined loop (PF; the same 128 registers)
+    const bool pf = gmask && nd <= 1;
+    if (pf) {
+        e = args(k_ks_f4s<LA, LB, RF, 1, 8, true, true>);
+    } else if (gmask) {
         if (nd <= 1) e = args(k_ks_f4s<LA, LB, RF, 1, 8, true>);
         else if (nd <= 2) e = args(k_ks_f4s<LA, LB, RF, 2, 8, true>);
         else if (nd <= 4) e = args(k_ks_f4s<LA, LB, RF, 4, 4, true>);
@@ -1648,11 +1736,19 @@ cudaError_t ks_a0_modup(const Context& c, uint32_t Q, uint64_t* qin, uint64_t* e
 
 bool ks_mdru_supported(const Context& c) {
     // the quotient's level has one digit, its q-limbs, and at most MAXSP extended limbs
-    // besides them (F5's thread groups take the conversions side by side)
+    // besides them (F5's thread groups take the conversions side by side); from the
+    // digits themselves, so that host-only contexts (schedule estimates) answer too
     if (!ks_mdr_supported(c, 2) || c.L < 2) return false;
-    const KsLevelConst& K = c.h_ksc[c.L - 2];
-    return K.nd == 1 && K.dstart[0] == 0 && K.dsz[0] == c.L - 1 && K.nlx - K.dsz[0] <= (uint32_t)MAXSP &&
-           K.dsz[0] <= 2;
+    const uint32_t lc = c.L - 2, l1 = lc + 1;
+    uint32_t nd = 0, ds = 0, d0 = 0;
+    for (const auto& dg : c.digits) {
+        if (dg.empty() || dg[0] > lc) continue;
+        nd++;
+        d0 = dg[0];
+        ds = 0;
+        for (uint32_t x : dg) ds += (x <= lc);
+    }
+    return nd == 1 && d0 == 0 && ds == l1 && ds <= 2 && c.alpha <= (uint32_t)MAXSP;
 }
 
 cudaError_t ks_moddown_rescale_modup(const Context& c, uint32_t T, uint64_t* e, uint64_t* const* d_out,

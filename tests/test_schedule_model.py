@@ -378,6 +378,36 @@ def test_deferred_division_matches_the_oracle_counts(preset, R, dim, part, Q):
 
 
 @pytest.mark.parametrize("preset,R,dim,part,Q", [("small4", 2500, 128, 16, 3), ("ring16", 6144, 128, 16, 1),
+                                                 ("ring16", 10000, 128, 16, 2)])
+def test_deferred_division_with_fused_compression_matches_the_oracle_counts(preset, R, dim, part, Q):
+    """The bench's default forms on the host-only schedule (the estimate of a context
+    with no device tables): the deferred division hands the fused tail its extension, so
+    the tail's ModUp is recorded with the division's launches and the counts stay the
+    oracle's -- one division per (query, group), one ModUp per group at the compression
+    level, one ModDown per pack."""
+    kind = (bm.BM_LAYOUT_HOISTED | bm.BM_LAYOUT_FUSED_EXPANSION | bm.BM_LAYOUT_DEFERRED_DIVISION
+            | bm.BM_LAYOUT_HOISTED_ROTSUM | bm.BM_LAYOUT_HOISTED_COMPRESSION | bm.BM_LAYOUT_DOUBLE_HOISTED
+            | bm.BM_LAYOUT_FUSED_COMPRESSION)
+    ops, plan_bytes = bm.bm_plan_estimate(preset, R, dim, part, Q, packing=kind)
+    log_n, n_q = PRESET[preset]
+    L, slots = n_q - 1, 1 << (log_n - 1)
+    n_in = dim // part
+    groups = sch.n_groups(R, part, slots)
+    packs = -(-groups // part)
+    ev = sch.CountingEvaluator()
+    sch.match(ev, [sch.SymCt(L)], [[None] * n_in for _ in range(groups)], [None] * n_in, object(), dim, part,
+              hoisted="deferred", hoisted_rotsum=True, hoisted_compress=True, double_hoisted=True,
+              fused_compress=True)
+    orc = ev.counts()
+    lib = library_counts(ops)
+    assert lib[("moddown", L)] == Q * orc[("ModDownRes2", L)] == Q * groups
+    assert lib[("modup", L - 2)] == Q * orc[("ModUp", L - 2)] == Q * groups
+    assert lib[("moddown", L - 2)] == Q * orc[("ModDown", L - 2)] == Q * packs
+    assert lib[("ip_sum", L - 2)] == Q * orc[("IPH", L - 2)]
+    assert plan_bytes > 0
+
+
+@pytest.mark.parametrize("preset,R,dim,part,Q", [("small4", 2500, 128, 16, 3), ("ring16", 6144, 128, 16, 1),
                                                  ("ring16", 1 << 20, 128, 4, 40), ("small4", 3000, 16, 4, 2)])
 def test_fused_expansion_matches_the_oracle_counts(preset, R, dim, part, Q):
     """Algorithm 1 with ModDown and Rescale fused: one basis extension and N_in - 1
