@@ -552,7 +552,11 @@ __device__ __forceinline__ void place4(uint64_t (&o)[4], const W4& g, uint32_t s
 // and reduced once.  With tpad (only with ntt_out), the sums of each run of tpad
 // consecutive targets go to slots 1..tpad of a run of tpad + 1, and slot 0 of the run
 // gets P times the run's source ciphertext: E_0, E_1..E_(N_in-1) of a query of the fused
-// Algorithm 1 in one launch.
+// Algorithm 1 in one launch.  GM: group-masked sums (the fused rotate-and-sum and
+// compression; flags in each element's Galois word mark its group's end and mask and the
+// unrotated term).  PF (one digit, with GM): the element loop software-pipelined, the next
+// element's key words, extension gather and permutation issued before the current
+// element's c0 gather and products.
 constexpr uint32_t kFoldElems = 12;
 
 // F3's target slices: every target limb of a digit in a block of its own while the
