@@ -259,3 +259,31 @@ def test_async_match_gives_the_synchronous_results():
         ref = wl.plaintext_scores(feats, qs[i])
         assert np.abs(scores - ref).max() < 1e-5
     stream.synchronize()
+
+
+def test_interleaved_async_matches_keep_each_query():
+    """A client with two matches in flight on one stream -- match k enqueued, then the
+    scores of match k - 1 read back -- as bench.py's end-to-end loop runs them: host
+    queries go through the plan's two staging buffers on its own copy stream while the
+    previous match runs, so each result must still be its own query's (different
+    queries in turn, every staging buffer reused several times)."""
+    import torch
+    c = gctx("small4")
+    m, s, R = 16, 4, 3000
+    feats = wl.gallery(R, m)
+    qs, _ = wl.queries(feats, 3)
+    sk, pk, ek = bm.bm_keygen_ex(c, KEY_SEED, m, s, bm.BM_KEYS_HOISTED)
+    g = bm.bm_encode_gallery_packed(c, feats, m, s, bm.BM_PACK_COMPLEX)
+    bm.bm_gallery_set_expansion(g, bm.BM_EXPAND_DEFERRED)
+    cts = [bm.bm_encrypt_query(c, pk, q, m, s, bm.BM_QUERY_TILED, 4, i) for i, q in enumerate(qs)]
+    want = [bm.bm_result_export(bm.bm_match(c, ek, g, [ct]), 0) for ct in cts]
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    prev = None
+    for qi in [0, 1, 2, 1, 0, 2, 2, 0, 1]:
+        r = bm.bm_match_async(c, ek, g, [cts[qi]], sp)
+        if prev is not None:
+            assert np.array_equal(bm.bm_result_export(prev[0], 0), want[prev[1]]), prev[1]
+        prev = (r, qi)
+    assert np.array_equal(bm.bm_result_export(prev[0], 0), want[prev[1]])
+    stream.synchronize()
