@@ -83,6 +83,21 @@ def test_launches_are_the_oracle_schedule_operations(preset, R, dim, part, Q):
     assert all(o["count"] <= 128 for o in ops if o["op"] in ("rotate", "rescale"))
 
 
+def test_query_staging_buffers_up_to_256_mib():
+    """Host queries are staged through two buffers of the plan's input size while that
+    input is at most 256 MiB (64 top-level ring-2^16 queries): one query more drops
+    both buffers, so the 65-query plan is smaller than the 64-query one by about two
+    staging buffers (less the 65th query's own share)."""
+    mib = 1 << 20
+    per_q = 2 * 4 * (8 << 16)                       # one query at level 3: 2 x 4 limbs of 512 KiB
+    b64 = bm.bm_plan_estimate("ring16", 65536, 16, 4, 64)[1]
+    b65 = bm.bm_plan_estimate("ring16", 65536, 16, 4, 65)[1]
+    b32 = bm.bm_plan_estimate("ring16", 65536, 16, 4, 32)[1]
+    assert b64 - b65 > 2 * 64 * per_q - 200 * mib
+    # 32 more queries: their own buffers plus twice their share of the staging
+    assert b64 - b32 > 3 * 32 * per_q
+
+
 def test_plan_bytes_are_its_buffers():
     # face gallery, one query: query ct (L = 3) and its two staging copies, Algorithm-1 outputs
     # at 3 and 2, accumulators at 2 and 1 for 3 groups, one score ct, key-switch scratch for 8
